@@ -1,0 +1,297 @@
+"""FP64 CPU oracle of the SED forward model + Gaussian log-likelihood.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+code with the GPU library (``paper_2609_30145_gb300``); both consume the seeded
+inputs of ``synth``.
+
+``build()`` compiles ``oracle.c`` with gcc (OpenMP) into ``_build/liboracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+BAD_THETA, BAD_Z, BAD_TMAX, NONFINITE = 1, 2, 4, 16
+
+
+def build(force=False):
+    src = os.path.join(_HERE, "oracle.c")
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= max(os.path.getmtime(src),
+                                              os.path.getmtime(os.path.join(_HERE, "oracle.h")))):
+        return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                           "-D_DEFAULT_SOURCE", "-o", tmp, src, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Grid(C.Structure):
+    _fields_ = [("n_age", C.c_int), ("n_feh", C.c_int), ("n_afe", C.c_int), ("n_lam", C.c_int),
+                ("log_age_yr", C.c_void_p), ("feh", C.c_void_p), ("afe", C.c_void_p),
+                ("lam", C.c_void_p), ("flux", C.c_void_p), ("sigma_lib_kms", C.c_void_p),
+                ("neb_n_logu", C.c_int), ("neb_n_logz", C.c_int),
+                ("neb_logu", C.c_void_p), ("neb_logz", C.c_void_p), ("neb_tab", C.c_void_p)]
+
+
+class _Model(C.Structure):
+    _fields_ = [("n_sfh", C.c_int), ("zf", C.c_double), ("zmode", C.c_int),
+                ("use_afe", C.c_int), ("use_nebular", C.c_int), ("dust_law", C.c_int),
+                ("bc_edge_log_age_yr", C.c_double), ("H0", C.c_double), ("Om0", C.c_double),
+                ("n_filt", C.c_int), ("filt_len", C.c_void_p), ("filt_lam", C.c_void_p),
+                ("filt_trans", C.c_void_p), ("phot_d", C.c_void_p), ("phot_sigma", C.c_void_p),
+                ("phot_mask", C.c_void_p), ("n_pix", C.c_int), ("spec_lam", C.c_void_p),
+                ("spec_d", C.c_void_p), ("spec_sigma", C.c_void_p), ("spec_mask", C.c_void_p),
+                ("lsf_mode", C.c_int), ("lsf_value", C.c_void_p),
+                ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_SO)
+        P = C.c_void_p
+        lib.orc_cosmology.argtypes = [C.c_double, C.c_double, C.c_double, P]
+        lib.orc_sfh_edges.argtypes = [C.c_int, C.c_double, P]
+        lib.orc_weights.argtypes = [P, P, P, P]
+        lib.orc_weights.restype = C.c_int
+        lib.orc_q.argtypes = [P, P]
+        lib.orc_dust_tau.argtypes = [C.c_int, P, C.c_int, C.c_double, C.c_double, P]
+        lib.orc_photometry.argtypes = [P, P, C.c_int, C.c_double, P, P]
+        lib.orc_spectrum.argtypes = [P, P, P, C.c_int, C.c_double, P, P, P]
+        lib.orc_row.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_row.restype = C.c_int
+        lib.orc_eval.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P, C.c_int]
+        lib.orc_grad_fd.argtypes = [P, P, P, C.c_int, C.c_int, C.c_double, P, C.c_int]
+        lib.orc_n_param.argtypes = [P]
+        lib.orc_n_param.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+PHYS = dict(H0=67.66, Om0=0.3097, bc_edge_log_age_yr=7.03)
+
+
+@dataclass
+class Oracle:
+    """Holds the grid and one model (fit) description; arrays are kept alive here."""
+
+    grid: object
+    n_sfh: int
+    zf: float
+    zmode: int
+    use_afe: int = 0
+    use_nebular: int = 0
+    dust_law: int = 0
+    filters: tuple | None = None     # (lens, lam, trans)
+    phot_d: np.ndarray | None = None
+    phot_sigma: np.ndarray | None = None
+    phot_mask: np.ndarray | None = None
+    spec_lam: np.ndarray | None = None
+    spec_d: np.ndarray | None = None
+    spec_sigma: np.ndarray | None = None
+    spec_mask: np.ndarray | None = None
+    lsf_mode: int = 0
+    lsf_value: np.ndarray | None = None
+    sigma_gal_kms: float = 0.0
+    z_ref: float = 0.0
+    H0: float = PHYS["H0"]
+    Om0: float = PHYS["Om0"]
+    bc_edge_log_age_yr: float = PHYS["bc_edge_log_age_yr"]
+
+    def __post_init__(self):
+        self._lib = _load()
+        g = self.grid
+        self._keep = []
+
+        def k(a, dt=np.float64):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a
+        self._g = _Grid()
+        self._g.n_afe, self._g.n_feh, self._g.n_age, self._g.n_lam = g.flux.shape
+        self._g.log_age_yr = _p(k(g.log_age_yr))
+        self._g.feh = _p(k(g.feh))
+        self._g.afe = _p(k(g.afe))
+        self._g.lam = _p(k(g.lam_aa))
+        self._g.flux = _p(k(g.flux))
+        self._g.sigma_lib_kms = _p(k(getattr(g, "sigma_lib_kms", None)))
+        if g.neb_tab is not None:
+            self._g.neb_n_logu, self._g.neb_n_logz = g.neb_tab.shape[:2]
+            self._g.neb_logu = _p(k(g.neb_logu))
+            self._g.neb_logz = _p(k(g.neb_logz))
+            self._g.neb_tab = _p(k(g.neb_tab))
+        self._rebuild_model()
+
+    def _rebuild_model(self):
+        def k(a, dt=np.float64):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a
+        m = _Model()
+        m.n_sfh, m.zf, m.zmode = self.n_sfh, self.zf, self.zmode
+        m.use_afe, m.use_nebular, m.dust_law = self.use_afe, self.use_nebular, self.dust_law
+        m.bc_edge_log_age_yr, m.H0, m.Om0 = self.bc_edge_log_age_yr, self.H0, self.Om0
+        if self.filters is not None:
+            lens, lam, tr = self.filters
+            m.n_filt = len(lens)
+            m.filt_len = _p(k(lens, np.int32))
+            m.filt_lam = _p(k(lam))
+            m.filt_trans = _p(k(tr))
+            m.phot_d = _p(k(self.phot_d))
+            m.phot_sigma = _p(k(self.phot_sigma))
+            m.phot_mask = _p(k(self.phot_mask, np.uint8))
+        if self.spec_lam is not None:
+            m.n_pix = len(self.spec_lam)
+            m.spec_lam = _p(k(self.spec_lam))
+            m.spec_d = _p(k(self.spec_d))
+            m.spec_sigma = _p(k(self.spec_sigma))
+            m.spec_mask = _p(k(self.spec_mask, np.uint8))
+            m.lsf_mode = self.lsf_mode
+            m.lsf_value = _p(k(self.lsf_value))
+            m.sigma_gal_kms, m.z_ref = self.sigma_gal_kms, self.z_ref
+        self._m = m
+
+    def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
+        if phot_d is not None:
+            self.phot_d, self.phot_sigma = phot_d, phot_sigma
+        if spec_d is not None:
+            self.spec_d, self.spec_sigma = spec_d, spec_sigma
+        self._rebuild_model()
+
+    # ---------------------------------------------------------------
+    @property
+    def n_param(self):
+        return self._lib.orc_n_param(C.byref(self._m))
+
+    @property
+    def n_filt(self):
+        return self._m.n_filt
+
+    @property
+    def n_pix(self):
+        return self._m.n_pix
+
+    def eval(self, theta, nthreads=0):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        n, ld = th.shape
+        phot = np.zeros((n, max(self.n_filt, 1)))
+        spec = np.zeros((n, max(self.n_pix, 1)))
+        lnl = np.zeros(n)
+        st = np.zeros(n, dtype=np.int32)
+        self._lib.orc_eval(C.byref(self._g), C.byref(self._m), _p(th), n, ld,
+                           _p(phot) if self.n_filt else None, _p(spec) if self.n_pix else None,
+                           _p(lnl), _p(st), int(nthreads))
+        return dict(phot=phot[:, :self.n_filt], spec=spec[:, :self.n_pix], lnl=lnl, status=st)
+
+    def row(self, theta_row):
+        th = np.ascontiguousarray(theta_row, dtype=np.float64)
+        g = self.grid
+        nsp = g.flux.shape[0] * g.flux.shape[1] * g.flux.shape[2]
+        nl = g.flux.shape[3]
+        W = np.zeros(nsp)
+        Y, O, F, fnu = (np.zeros(nl) for _ in range(4))
+        phot = np.zeros(max(self.n_filt, 1))
+        spec = np.zeros(max(self.n_pix, 1))
+        scal = np.zeros(6)
+        st = self._lib.orc_row(C.byref(self._g), C.byref(self._m), _p(th), _p(W), _p(Y), _p(O),
+                               _p(F), _p(fnu), _p(phot), _p(spec), _p(scal))
+        return dict(status=st, W=W.reshape(g.flux.shape[:3]), Y=Y, O=O, F=F, fnu=fnu,
+                    phot=phot[:self.n_filt], spec=spec[:self.n_pix], D_L=scal[0], t_univ=scal[1],
+                    T_max=scal[2], Q_young=scal[3], scale=scal[4], lnl=scal[5])
+
+    def weights(self, theta_row):
+        th = np.ascontiguousarray(theta_row, dtype=np.float64)
+        g = self.grid
+        W = np.zeros(g.flux.shape[:3])
+        st = self._lib.orc_weights(C.byref(self._g), C.byref(self._m), _p(th), _p(W))
+        return st, W
+
+    def q(self):
+        g = self.grid
+        Q = np.zeros(g.flux.shape[:3])
+        self._lib.orc_q(C.byref(self._g), _p(Q))
+        return Q
+
+    def photometry(self, lam_rest, fnu_obs, z):
+        lam_rest, fnu_obs = _f64(lam_rest), _f64(fnu_obs)
+        out = np.zeros(self.n_filt)
+        self._lib.orc_photometry(C.byref(self._m), _p(lam_rest), lam_rest.size, float(z),
+                                 _p(fnu_obs), _p(out))
+        return out
+
+    def spectrum(self, lam_rest, fnu_obs, z):
+        lam_rest, fnu_obs = _f64(lam_rest), _f64(fnu_obs)
+        out = np.zeros(self.n_pix)
+        valid = np.zeros(self.n_pix, dtype=np.uint8)
+        self._lib.orc_spectrum(C.byref(self._g), C.byref(self._m), _p(lam_rest), lam_rest.size,
+                               float(z), _p(fnu_obs), _p(out), _p(valid))
+        return out, valid
+
+    def grad_fd(self, theta, h_rel=1e-6, nthreads=0):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        n, ld = th.shape
+        out = np.zeros((n, ld))
+        self._lib.orc_grad_fd(C.byref(self._g), C.byref(self._m), _p(th), n, ld, float(h_rel),
+                              _p(out), int(nthreads))
+        return out
+
+
+def cosmology(H0, Om0, z):
+    lib = _load()
+    out = np.zeros(3)
+    lib.orc_cosmology(float(H0), float(Om0), float(z), _p(out))
+    return dict(D_L=out[0], t_univ=out[1], D_C=out[2])
+
+
+def sfh_edges(n_sfh, tmax_yr):
+    lib = _load()
+    T = np.zeros(n_sfh + 1)
+    lib.orc_sfh_edges(int(n_sfh), float(tmax_yr), _p(T))
+    return T
+
+
+def dust_tau(law, lam, tau, index):
+    lib = _load()
+    lam = _f64(lam)
+    out = np.zeros(lam.size)
+    lib.orc_dust_tau(int(law), _p(lam), lam.size, float(tau), float(index), _p(out))
+    return out
+
+
+def pack_theta(d, n_sfh, zmode):
+    """Parameter rows in the oracle's layout: sfh[N_T], logzsol[N_T or 1], then
+    afe, logmass, zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index,
+    gas_logz, gas_logu."""
+    nz = n_sfh if zmode == 0 else 1
+    n = d["sfh"].shape[0]
+    cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh),
+            np.asarray(d["logzsol"], dtype=np.float64).reshape(n, nz)]
+    for k in ("afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
+              "diffuse_dust_index", "gas_logz", "gas_logu"):
+        cols.append(np.asarray(d[k], dtype=np.float64).reshape(n, 1))
+    return np.ascontiguousarray(np.concatenate(cols, axis=1))

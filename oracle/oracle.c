@@ -1,0 +1,538 @@
+/*
+ * FP64 CPU oracle of the batched SED forward model and Gaussian log-likelihood.
+ *
+ * TEST INFRASTRUCTURE ONLY: the independent reference the GPU library is
+ * checked against.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark load it.  It shares no code with the library.
+ *
+ * Plain double precision, plainest loop order, one function per step of the
+ * paper's method (section and equation named at each function).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Physical constants (cgs unless noted). */
+static const double O_LSUN = 3.839e33;            /* erg/s, value adopted in Sec. 2.6 */
+static const double O_H = 6.62607015e-27;         /* erg s */
+static const double O_C_AA = 2.99792458e18;       /* Angstrom/s */
+static const double O_C_KMS = 299792.458;         /* km/s */
+static const double O_AB = 3.631e-20;             /* erg/s/cm^2/Hz, AB zero point, App. D */
+static const double O_PC_CM = 3.0856775814913673e18;
+static const double O_MPC_KM = 3.0856775814913673e19;
+static const double O_YR_S = 3.15576e7;           /* Julian year */
+static const double O_LYMAN = 912.0;              /* Angstrom, App. C */
+static const double O_FWHM_SIG = 2.3548200450309493; /* 2 sqrt(2 ln 2), Eq. "app_fwhm" */
+
+/* ------------------------------------------------------------------ */
+/* Adaptive Simpson quadrature                                          */
+/* ------------------------------------------------------------------ */
+typedef double (*orc_fn)(double, const double *);
+
+static double simpson_step(orc_fn f, const double *p, double a, double b, double fa, double fm,
+                           double fb, double whole, double eps, int depth) {
+  double m = 0.5 * (a + b), lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+  double flm = f(lm, p), frm = f(rm, p);
+  double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+  double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+  double delta = left + right - whole;
+  if (depth <= 0 || fabs(delta) <= 15.0 * eps) return left + right + delta / 15.0;
+  return simpson_step(f, p, a, m, fa, flm, fm, left, 0.5 * eps, depth - 1) +
+         simpson_step(f, p, m, b, fm, frm, fb, right, 0.5 * eps, depth - 1);
+}
+
+static double integrate(orc_fn f, const double *p, double a, double b, double rel) {
+  if (b == a) return 0.0;
+  /* coarse estimate sets the absolute tolerance */
+  double s = 0.0;
+  int n = 64;
+  double h = (b - a) / n;
+  for (int i = 0; i <= n; i++) {
+    double w = (i == 0 || i == n) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+    s += w * f(a + i * h, p);
+  }
+  s *= h / 3.0;
+  double eps = rel * fabs(s) + 1e-300;
+  double total = 0.0;
+  for (int i = 0; i < n; i++) { /* 64 panels, each adaptive */
+    double x0 = a + i * h, x1 = x0 + h, xm = 0.5 * (x0 + x1);
+    double f0 = f(x0, p), f1 = f(x1, p), fm = f(xm, p);
+    double whole = h / 6.0 * (f0 + 4.0 * fm + f1);
+    total += simpson_step(f, p, x0, x1, f0, fm, f1, whole, eps / n, 40);
+  }
+  return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* Cosmology, Sec. 2.6: flat LCDM without radiation                     */
+/* ------------------------------------------------------------------ */
+static double inv_E(double z, const double *p) { /* p[0] = Om */
+  double zp = 1.0 + z;
+  return 1.0 / sqrt(p[0] * zp * zp * zp + 1.0 - p[0]);
+}
+/* t = int_0^a da'/(a' H(a')), with a' = u^2: integrand 2u^2/sqrt(Om + OL u^6) (units 1/H0) */
+static double age_integrand(double u, const double *p) {
+  double u2 = u * u;
+  return 2.0 * u2 / sqrt(p[0] + (1.0 - p[0]) * u2 * u2 * u2);
+}
+
+void orc_cosmology(double H0, double Om0, double z, double *out) {
+  double p[1] = {Om0};
+  double dh_cm = O_C_KMS / H0 * 1e6 * O_PC_CM;          /* c/H0 in cm */
+  double th_yr = O_MPC_KM / H0 / O_YR_S;                 /* 1/H0 in yr */
+  double dc = dh_cm * integrate(inv_E, p, 0.0, z, 1e-13);
+  double umax = 1.0 / sqrt(1.0 + z);
+  double t = th_yr * integrate(age_integrand, p, 0.0, umax, 1e-13);
+  out[0] = (1.0 + z) * dc;
+  out[1] = t;
+  out[2] = dc;
+}
+
+/* ------------------------------------------------------------------ */
+/* SFH edges: 0, 5 Myr, 10 Myr, then log-uniform to T_max (Sec. 5, App. B) */
+/* ------------------------------------------------------------------ */
+void orc_sfh_edges(int n_sfh, double tmax_yr, double *T) {
+  T[0] = 0.0;
+  T[1] = 5e6;
+  T[2] = 1e7;
+  for (int i = 3; i <= n_sfh; i++)
+    T[i] = 1e7 * pow(tmax_yr / 1e7, (double)(i - 2) / (double)(n_sfh - 2));
+}
+
+/* Linear interpolation weights between the bracketing nodes, clamped to the
+ * end nodes outside the axis (App. B: "linear interpolation in log10(Z/Zsun)"). */
+static void bracket(const double *x, int n, double v, int *j0, double *w0, int *j1, double *w1) {
+  if (n == 1) { *j0 = *j1 = 0; *w0 = 1.0; *w1 = 0.0; return; }
+  if (v <= x[0]) { *j0 = 0; *j1 = 1; *w0 = 1.0; *w1 = 0.0; return; }
+  if (v >= x[n - 1]) { *j0 = n - 2; *j1 = n - 1; *w0 = 0.0; *w1 = 1.0; return; }
+  int j = 0;
+  while (!(x[j] <= v && v < x[j + 1])) j++;
+  double t = (v - x[j]) / (x[j + 1] - x[j]);
+  *j0 = j; *j1 = j + 1; *w0 = 1.0 - t; *w1 = t;
+}
+
+int orc_n_param(const orc_model *md) {
+  return md->n_sfh + (md->zmode == 0 ? md->n_sfh : 1) + 9;
+}
+
+/* parameter row decoding (layout: sfh[N_T], logzsol[N_T or 1], afe, logmass,
+ * zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index, gas_logz, gas_logu) */
+typedef struct {
+  const double *m, *zeta;
+  double afe, logmass, z, tau_bc, alpha_bc, tau_d, delta, gas_logz, gas_logu;
+} orc_theta;
+
+static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
+  int nz = md->zmode == 0 ? md->n_sfh : 1;
+  const double *s = th + md->n_sfh + nz;
+  o->m = th;
+  o->zeta = th + md->n_sfh;
+  o->afe = s[0]; o->logmass = s[1]; o->z = s[2]; o->tau_bc = s[3]; o->alpha_bc = s[4];
+  o->tau_d = s[5]; o->delta = s[6]; o->gas_logz = s[7]; o->gas_logu = s[8];
+}
+
+static int theta_status(const orc_model *md, const double *th, double *tmax_out, double *cos_out) {
+  int np = orc_n_param(md);
+  for (int j = 0; j < np; j++)
+    if (!isfinite(th[j])) return ORC_BAD_THETA;
+  orc_theta t;
+  decode_theta(md, th, &t);
+  if (t.z < 0.0 || t.z >= md->zf) return ORC_BAD_Z;
+  double cz[3], cf[3];
+  orc_cosmology(md->H0, md->Om0, t.z, cz);
+  orc_cosmology(md->H0, md->Om0, md->zf, cf);
+  double tmax = cz[1] - cf[1];
+  if (cos_out) { cos_out[0] = cz[0]; cos_out[1] = cz[1]; }
+  if (tmax_out) *tmax_out = tmax;
+  if (!(tmax > 1e7)) return ORC_BAD_TMAX;
+  return 0;
+}
+
+/* App. B step scheme: A_ia = m_i |[T_i,T_{i+1}] ∩ cell_a| / dT_i with cell_a the
+ * linear-time Voronoi cell of age node a (midpoints to its neighbours, first
+ * cell from 0, last cell to infinity); then the metallicity split of each bin
+ * and the [a/Fe] split (Sec. 5.4), W[n][m][a] = sum_i A_ia w_m(zeta_i) w_n(afe). */
+int orc_weights(const orc_grid *g, const orc_model *md, const double *theta, double *W) {
+  double tmax;
+  int st = theta_status(md, theta, &tmax, NULL);
+  size_t nW = (size_t)g->n_afe * g->n_feh * g->n_age;
+  memset(W, 0, nW * sizeof(double));
+  if (st) return st;
+  orc_theta t;
+  decode_theta(md, theta, &t);
+  int NT = md->n_sfh, NA = g->n_age;
+  double *T = (double *)malloc((NT + 1) * sizeof(double));
+  double *cm = (double *)malloc(NA * sizeof(double));
+  double *cp = (double *)malloc(NA * sizeof(double));
+  orc_sfh_edges(NT, tmax, T);
+  for (int a = 0; a < NA; a++) {
+    double ta = pow(10.0, g->log_age_yr[a]);
+    cm[a] = (a == 0) ? 0.0 : 0.5 * (pow(10.0, g->log_age_yr[a - 1]) + ta);
+    cp[a] = (a == NA - 1) ? INFINITY : 0.5 * (ta + pow(10.0, g->log_age_yr[a + 1]));
+  }
+  int n0, n1;
+  double wn0, wn1;
+  double afe = md->use_afe ? t.afe : 0.0;
+  bracket(g->afe, g->n_afe, afe, &n0, &wn0, &n1, &wn1);
+  for (int i = 0; i < NT; i++) {
+    double dT = T[i + 1] - T[i];
+    double zeta = t.zeta[md->zmode == 0 ? i : 0];
+    int m0, m1;
+    double wm0, wm1;
+    bracket(g->feh, g->n_feh, zeta, &m0, &wm0, &m1, &wm1);
+    for (int a = 0; a < NA; a++) {
+      double lo = T[i] > cm[a] ? T[i] : cm[a];
+      double hi = T[i + 1] < cp[a] ? T[i + 1] : cp[a];
+      double ov = hi - lo;
+      if (ov <= 0.0) continue;
+      double A = t.m[i] * ov / dT;
+      W[((size_t)n0 * g->n_feh + m0) * NA + a] += A * wm0 * wn0;
+      W[((size_t)n0 * g->n_feh + m1) * NA + a] += A * wm1 * wn0;
+      W[((size_t)n1 * g->n_feh + m0) * NA + a] += A * wm0 * wn1;
+      W[((size_t)n1 * g->n_feh + m1) * NA + a] += A * wm1 * wn1;
+    }
+  }
+  free(T); free(cm); free(cp);
+  return 0;
+}
+
+/* App. C, Eq. "app_q": Q = (Lsun/h) int_0^912 f(lam)/lam dlam, trapezoid over the
+ * nodes below 912 A plus the linearly interpolated piece up to 912 A. */
+void orc_q(const orc_grid *g, double *Q) {
+  size_t nsp = (size_t)g->n_afe * g->n_feh * g->n_age;
+  const double *lam = g->lam;
+  for (size_t s = 0; s < nsp; s++) {
+    const double *f = g->flux + s * g->n_lam;
+    double acc = 0.0;
+    for (int k = 0; k + 1 < g->n_lam; k++) {
+      if (lam[k] >= O_LYMAN) break;
+      double x1 = lam[k + 1], f1 = f[k + 1];
+      if (x1 > O_LYMAN) {
+        f1 = f[k] + (f[k + 1] - f[k]) * (O_LYMAN - lam[k]) / (lam[k + 1] - lam[k]);
+        x1 = O_LYMAN;
+      }
+      acc += 0.5 * (f[k] / lam[k] + f1 / x1) * (x1 - lam[k]);
+    }
+    Q[s] = O_LSUN / O_H * acc;
+  }
+}
+
+/* Calzetti et al. (2000) k'(lam), R_V = 4.05, lam in micron; the UV branch is
+ * used below 0.63 micron (also below 0.12 micron); clamped at zero. */
+static double calzetti_kprime(double lum) {
+  double k;
+  if (lum >= 0.63)
+    k = 2.659 * (-1.857 + 1.040 / lum) + 4.05;
+  else
+    k = 2.659 * (-2.156 + 1.509 / lum - 0.198 / (lum * lum) + 0.011 / (lum * lum * lum)) + 4.05;
+  return k > 0.0 ? k : 0.0;
+}
+
+/* Sec. 2.4: Kriek & Conroy (2013) diffuse law, tau(lam) = tau [k'(lam) +
+ * D(lam)] / 4.05 (lam/5500)^delta with a Drude bump of central wavelength
+ * 2175 A, width 350 A and strength E_b = 0.85 - 1.9 delta; power law:
+ * tau(lam) = tau (lam/5500)^index. */
+void orc_dust_tau(int law, const double *lam, int n, double tau, double index, double *out) {
+  for (int k = 0; k < n; k++) {
+    double p = pow(lam[k] / 5500.0, index);
+    if (law == 0) {
+      out[k] = tau * p;
+    } else {
+      double eb = 0.85 - 1.9 * index;
+      double x = lam[k] * 350.0;
+      double d = lam[k] * lam[k] - 2175.0 * 2175.0;
+      double drude = eb * x * x / (d * d + x * x);
+      out[k] = tau * (calzetti_kprime(lam[k] * 1e-4) + drude) / 4.05 * p;
+    }
+  }
+}
+
+/* App. D: m_b = sum_j R_b(l_j) l_j dl_j f_lam(l_j) / Z_b, with f_lam the linear
+ * interpolation (in observed wavelength) of c F_nu/lam_obs^2 over the redshifted
+ * model grid (zero outside it), dl_j the local spacing (half-interval at the
+ * ends) and Z_b = trapz_j l_j R_b(l_j) c 3.631e-20 / l_j^2. */
+void orc_photometry(const orc_model *md, const double *lam_rest, int n_lam, double z,
+                    const double *fnu_obs, double *maggies) {
+  double zp = 1.0 + z;
+  double lo = zp * lam_rest[0], hi = zp * lam_rest[n_lam - 1];
+  int off = 0;
+  for (int b = 0; b < md->n_filt; b++) {
+    int n = md->filt_len[b];
+    const double *L = md->filt_lam + off, *R = md->filt_trans + off;
+    off += n;
+    double zb = 0.0;
+    for (int j = 0; j + 1 < n; j++) {
+      double g0 = L[j] * R[j] * O_C_AA * O_AB / (L[j] * L[j]);
+      double g1 = L[j + 1] * R[j + 1] * O_C_AA * O_AB / (L[j + 1] * L[j + 1]);
+      zb += 0.5 * (g0 + g1) * (L[j + 1] - L[j]);
+    }
+    double acc = 0.0;
+    for (int j = 0; j < n; j++) {
+      double dl;
+      if (n == 1) dl = 0.0;
+      else if (j == 0) dl = 0.5 * (L[1] - L[0]);
+      else if (j == n - 1) dl = 0.5 * (L[n - 1] - L[n - 2]);
+      else dl = 0.5 * (L[j + 1] - L[j - 1]);
+      double x = L[j], flam = 0.0;
+      if (x >= lo && x <= hi) {
+        int k = 0, kh = n_lam - 1; /* binary search: zp*lam[k] <= x <= zp*lam[k+1] */
+        while (kh - k > 1) {
+          int mid = (k + kh) / 2;
+          if (zp * lam_rest[mid] <= x) k = mid; else kh = mid;
+        }
+        double xa = zp * lam_rest[k], xb = zp * lam_rest[k + 1];
+        double ga = O_C_AA * fnu_obs[k] / (xa * xa), gb = O_C_AA * fnu_obs[k + 1] / (xb * xb);
+        flam = ga + (gb - ga) * (x - xa) / (xb - xa);
+      }
+      acc += R[j] * x * dl * flam;
+    }
+    maggies[b] = acc / zb;
+  }
+}
+
+/* Eq. "app_siglib" two-pixel floor at the grid nodes, max with the documented
+ * library LSF when given. */
+static void siglib_nodes(const orc_grid *g, double *out) {
+  int n = g->n_lam;
+  const double *L = g->lam;
+  for (int k = 0; k < n; k++) {
+    double dl;
+    if (k == 0) dl = L[1] - L[0];
+    else if (k == n - 1) dl = L[n - 1] - L[n - 2];
+    else dl = 0.5 * (L[k + 1] - L[k - 1]);
+    double s = O_C_KMS / O_FWHM_SIG * 2.0 * dl / L[k];
+    if (g->sigma_lib_kms && g->sigma_lib_kms[k] > s) s = g->sigma_lib_kms[k];
+    out[k] = s;
+  }
+}
+
+/* Eq. "app_modes": instrumental velocity dispersion at an observed pixel. */
+static double sigma_inst_kms(int mode, double v, double lam_obs) {
+  switch (mode) {
+    case 0: return O_C_KMS / (O_FWHM_SIG * v);
+    case 1: return O_C_KMS / v;
+    case 2: return O_C_KMS * v / (O_FWHM_SIG * lam_obs);
+    case 3: return O_C_KMS * v / lam_obs;
+    case 4: return v;
+    default: return v / O_FWHM_SIG;
+  }
+}
+
+/* Per-pixel total dispersion in ln(lam): Eq. "app_sigeff" (fixed part at the
+ * projector's reference redshift) composed in quadrature with a fixed
+ * sigma_gal (Eq. "one_kernel"). */
+static void spec_widths(const orc_grid *g, const orc_model *md, double *s_ln) {
+  double *sl = (double *)malloc(g->n_lam * sizeof(double));
+  siglib_nodes(g, sl);
+  for (int i = 0; i < md->n_pix; i++) {
+    double lo = md->spec_lam[i];
+    double si = sigma_inst_kms(md->lsf_mode, md->lsf_value[i], lo);
+    double lr = lo / (1.0 + md->z_ref), slib;
+    if (lr <= g->lam[0]) slib = sl[0];
+    else if (lr >= g->lam[g->n_lam - 1]) slib = sl[g->n_lam - 1];
+    else {
+      int k = 0;
+      while (!(g->lam[k] <= lr && lr < g->lam[k + 1])) k++;
+      slib = sl[k] + (sl[k + 1] - sl[k]) * (lr - g->lam[k]) / (g->lam[k + 1] - g->lam[k]);
+    }
+    double fix2 = si * si - slib * slib;
+    if (fix2 < 0.0) fix2 = 0.0;
+    s_ln[i] = sqrt(fix2 + md->sigma_gal_kms * md->sigma_gal_kms) / O_C_KMS;
+  }
+  free(sl);
+}
+
+/* Eq. "app_response": Gaussian rows in ln(lam) centred on each pixel shifted
+ * by ln(1+z), truncated at five dispersions, normalised to unit sum; rows
+ * narrower than half a model log-pixel are linear interpolation in ln(lam). */
+void orc_spectrum(const orc_grid *g, const orc_model *md, const double *lam_rest, int n_lam,
+                  double z, const double *fnu_obs, double *pix, unsigned char *valid) {
+  double *s_ln = (double *)malloc(md->n_pix * sizeof(double));
+  double *ll = (double *)malloc(n_lam * sizeof(double));
+  spec_widths(g, md, s_ln);
+  for (int k = 0; k < n_lam; k++) ll[k] = log(lam_rest[k]);
+  double lz = log(1.0 + z);
+  for (int i = 0; i < md->n_pix; i++) {
+    double x = log(md->spec_lam[i]) - lz, s = s_ln[i];
+    pix[i] = 0.0;
+    valid[i] = 0;
+    if (x < ll[0] || x > ll[n_lam - 1]) continue;
+    int k = 0;
+    while (k + 2 < n_lam && !(ll[k] <= x && x < ll[k + 1])) k++;
+    double dln = ll[k + 1] - ll[k];
+    if (s < 0.5 * dln) {
+      double t = (x - ll[k]) / dln;
+      pix[i] = (1.0 - t) * fnu_obs[k] + t * fnu_obs[k + 1];
+      valid[i] = 1;
+      continue;
+    }
+    double sw = 0.0, sf = 0.0;
+    for (int j = 0; j < n_lam; j++) {
+      double u = (ll[j] - x) / s;
+      if (fabs(u) > 5.0) continue;
+      double w = exp(-0.5 * u * u);
+      sw += w;
+      sf += w * fnu_obs[j];
+    }
+    if (sw > 0.0) { pix[i] = sf / sw; valid[i] = 1; }
+  }
+  free(s_ln);
+  free(ll);
+}
+
+/* One parameter row through the whole forward model and likelihood. */
+int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double *W_out,
+            double *Y_out, double *O_out, double *F_out, double *fnu_out, double *phot,
+            double *spec, double *scal) {
+  int NA = g->n_age, NL = g->n_lam, NZ = g->n_feh, NAF = g->n_afe;
+  size_t nsp = (size_t)NAF * NZ * NA;
+  double *W = (double *)malloc(nsp * sizeof(double));
+  double *Q = (double *)malloc(nsp * sizeof(double));
+  double *Y = (double *)calloc(NL, sizeof(double));
+  double *O = (double *)calloc(NL, sizeof(double));
+  double *F = (double *)malloc(NL * sizeof(double));
+  double *fnu = (double *)malloc(NL * sizeof(double));
+  double *tbc = (double *)malloc(NL * sizeof(double));
+  double *td = (double *)malloc(NL * sizeof(double));
+  double cosm[2] = {0, 0}, tmax = 0;
+  int st = theta_status(md, theta, &tmax, cosm);
+  int st_w = orc_weights(g, md, theta, W);
+  if (!st) st = st_w;
+  double lnl = -INFINITY;
+  orc_theta t;
+  decode_theta(md, theta, &t);
+  if (!st) {
+    /* contraction, Eq. "csp_sum_main" split into birth-cloud (young) and
+     * older ages (Eq. "app_attn" with a two-bin age-to-bin matrix); the
+     * stellar flux below 912 A of nebular ages is removed (App. A, Fig. flow) */
+    orc_q(g, Q);
+    double qy = 0.0;
+    for (int n = 0; n < NAF; n++)
+      for (int m = 0; m < NZ; m++)
+        for (int a = 0; a < NA; a++) {
+          size_t s = ((size_t)n * NZ + m) * NA + a;
+          double w = W[s];
+          if (w == 0.0) continue; /* exact zero contributes nothing */
+          const double *f = g->flux + s * NL;
+          int young = g->log_age_yr[a] <= md->bc_edge_log_age_yr;
+          int neb = md->use_nebular && g->neb_tab && young;
+          double *acc = young ? Y : O;
+          for (int k = 0; k < NL; k++) {
+            if (neb && g->lam[k] < O_LYMAN) continue;
+            acc[k] += w * f[k];
+          }
+          if (young) qy += w * Q[s];
+        }
+    /* nebular continuum, App. C: Q_young * 10^(bilinear log10 template) */
+    if (md->use_nebular && g->neb_tab) {
+      int u0, u1, z0, z1;
+      double wu0, wu1, wz0, wz1;
+      bracket(g->neb_logu, g->neb_n_logu, t.gas_logu, &u0, &wu0, &u1, &wu1);
+      bracket(g->neb_logz, g->neb_n_logz, t.gas_logz, &z0, &wz0, &z1, &wz1);
+      const double *t00 = g->neb_tab + ((size_t)u0 * g->neb_n_logz + z0) * NL;
+      const double *t01 = g->neb_tab + ((size_t)u0 * g->neb_n_logz + z1) * NL;
+      const double *t10 = g->neb_tab + ((size_t)u1 * g->neb_n_logz + z0) * NL;
+      const double *t11 = g->neb_tab + ((size_t)u1 * g->neb_n_logz + z1) * NL;
+      for (int k = 0; k < NL; k++) {
+        double lg = wu0 * wz0 * t00[k] + wu0 * wz1 * t01[k] + wu1 * wz0 * t10[k] + wu1 * wz1 * t11[k];
+        Y[k] += qy * pow(10.0, lg);
+      }
+    }
+    /* two-component dust (Sec. 2.4) */
+    for (int k = 0; k < NL; k++) tbc[k] = t.tau_bc * pow(g->lam[k] / 5500.0, t.alpha_bc);
+    orc_dust_tau(md->dust_law, g->lam, NL, t.tau_d, t.delta, td);
+    for (int k = 0; k < NL; k++) F[k] = exp(-td[k]) * (exp(-tbc[k]) * Y[k] + O[k]);
+    /* observer frame, Sec. 2.6 */
+    double dl = cosm[0] > 10.0 * O_PC_CM ? cosm[0] : 10.0 * O_PC_CM;
+    double scale = pow(10.0, t.logmass) * O_LSUN * (1.0 + t.z) / (4.0 * M_PI * dl * dl);
+    for (int k = 0; k < NL; k++) fnu[k] = scale * F[k];
+    /* projections + likelihood, Eq. "total_lnlike" */
+    double *ph = (double *)malloc((md->n_filt > 0 ? md->n_filt : 1) * sizeof(double));
+    double *sp = (double *)malloc((md->n_pix > 0 ? md->n_pix : 1) * sizeof(double));
+    unsigned char *vd = (unsigned char *)malloc(md->n_pix > 0 ? md->n_pix : 1);
+    lnl = 0.0;
+    if (md->n_filt > 0) {
+      orc_photometry(md, g->lam, NL, t.z, fnu, ph);
+      for (int b = 0; b < md->n_filt; b++) {
+        if (phot) phot[b] = ph[b];
+        if (md->phot_d && (!md->phot_mask || md->phot_mask[b])) {
+          double s = md->phot_sigma[b], r = (md->phot_d[b] - ph[b]) / s;
+          lnl += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
+        }
+      }
+    }
+    if (md->n_pix > 0) {
+      orc_spectrum(g, md, g->lam, NL, t.z, fnu, sp, vd);
+      for (int i = 0; i < md->n_pix; i++) {
+        if (spec) spec[i] = sp[i];
+        if (md->spec_d && vd[i] && (!md->spec_mask || md->spec_mask[i])) {
+          double s = md->spec_sigma[i], r = (md->spec_d[i] - sp[i]) / s;
+          lnl += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
+        }
+      }
+    }
+    if (!isfinite(lnl)) { st = ORC_NONFINITE; lnl = -INFINITY; }
+    if (scal) { scal[0] = cosm[0]; scal[1] = cosm[1]; scal[2] = tmax; scal[3] = qy; scal[4] = scale; }
+    free(ph); free(sp); free(vd);
+  }
+  if (st) {
+    if (phot) for (int b = 0; b < md->n_filt; b++) phot[b] = 0.0;
+    if (spec) for (int i = 0; i < md->n_pix; i++) spec[i] = 0.0;
+  }
+  if (scal) scal[5] = lnl;
+  if (W_out) memcpy(W_out, W, nsp * sizeof(double));
+  if (Y_out) memcpy(Y_out, Y, NL * sizeof(double));
+  if (O_out) memcpy(O_out, O, NL * sizeof(double));
+  if (F_out) memcpy(F_out, F, NL * sizeof(double));
+  if (fnu_out) memcpy(fnu_out, fnu, NL * sizeof(double));
+  free(W); free(Q); free(Y); free(O); free(F); free(fnu); free(tbc); free(td);
+  return st;
+}
+
+void orc_eval(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld,
+              double *phot_out, double *spec_out, double *lnl_out, int *status_out,
+              int nthreads) {
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+#endif
+  for (int r = 0; r < n; r++) {
+    double scal[6];
+    int st = orc_row(g, md, theta + (size_t)r * ld, NULL, NULL, NULL, NULL, NULL,
+                     phot_out ? phot_out + (size_t)r * md->n_filt : NULL,
+                     spec_out ? spec_out + (size_t)r * md->n_pix : NULL, scal);
+    if (lnl_out) lnl_out[r] = st ? -INFINITY : scal[5];
+    if (status_out) status_out[r] = st;
+  }
+  (void)nthreads;
+}
+
+void orc_grad_fd(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld,
+                 double h_rel, double *grad_out, int nthreads) {
+  int np = orc_n_param(md);
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1) collapse(2)
+#endif
+  for (int r = 0; r < n; r++) {
+    for (int j = 0; j < np; j++) {
+      double *x = (double *)malloc(np * sizeof(double));
+      memcpy(x, theta + (size_t)r * ld, np * sizeof(double));
+      double x0 = x[j];
+      double h = h_rel * (fabs(x0) > 1.0 ? fabs(x0) : 1.0);
+      double sp[6], sm[6];
+      x[j] = x0 + h;
+      int a = orc_row(g, md, x, NULL, NULL, NULL, NULL, NULL, NULL, NULL, sp);
+      x[j] = x0 - h;
+      int b = orc_row(g, md, x, NULL, NULL, NULL, NULL, NULL, NULL, NULL, sm);
+      grad_out[(size_t)r * ld + j] = (a || b) ? NAN : (sp[5] - sm[5]) / (2.0 * h);
+      free(x);
+    }
+  }
+  (void)nthreads;
+}

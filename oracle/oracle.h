@@ -1,0 +1,112 @@
+/*
+ * FP64 CPU oracle of the batched SED forward model and Gaussian log-likelihood.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the independent reference that the
+ * GPU library is checked against.  It shares no code, header, table or
+ * constant with the library; only the test suite, the smoke check and the CPU
+ * baseline of the benchmark may load it.  The product path never calls it.
+ *
+ * Each function follows the paper's definitions directly, in the plainest loop
+ * order, in double precision:
+ *   cosmology            Sec. 2.6 (flat LCDM luminosity distance, age of the Universe)
+ *   SFH -> SSP weights   Sec. 2.2, App. B (step scheme, Voronoi cells in linear time),
+ *                        App. B metallicity split, Sec. 5.4 [a/Fe] axis
+ *   ionising photons     App. C, Eq. "app_q"
+ *   contraction          Eq. "csp_sum_main", Eq. "app_attn" (two age bins)
+ *   nebular              App. C (template interpolated in log10, scaled by Q)
+ *   dust                 Sec. 2.4 (birth-cloud power law + diffuse law)
+ *   observer frame       Sec. 2.6 (mass, flux factor (1+z)(10pc/D_L)^2)
+ *   photometry           App. D, Eqs. "app_phot_row", "app_phot_T"
+ *   spectrum             Eq. "one_kernel", App. E, Eqs. "app_siglib", "app_sigeff", "app_response"
+ *   likelihood           Eq. "total_lnlike", Eq. "app_spec_lndiag"
+ */
+#ifndef SED_ORACLE_H
+#define SED_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int n_age, n_feh, n_afe, n_lam;
+  const double *log_age_yr, *feh, *afe, *lam; /* lam: rest frame, Angstrom */
+  const double *flux;          /* [n_afe][n_feh][n_age][n_lam], Lsun/Hz per Msun formed */
+  const double *sigma_lib_kms; /* [n_lam] documented library LSF, or NULL */
+  int neb_n_logu, neb_n_logz;
+  const double *neb_logu, *neb_logz;
+  const double *neb_tab;       /* [n_logu][n_logz][n_lam] log10(L_nu/Q), or NULL */
+} orc_grid;
+
+typedef struct {
+  int n_sfh;                   /* SFH bins N_T (>= 3) */
+  double zf;                   /* formation redshift of the oldest edge */
+  int zmode;                   /* 0: one [Fe/H] per bin, 1: one constant [Fe/H] */
+  int use_afe, use_nebular;
+  int dust_law;                /* diffuse law: 0 power law, 1 Kriek & Conroy 2013 */
+  double bc_edge_log_age_yr;   /* ages <= this are in the birth cloud */
+  double H0, Om0;              /* flat LCDM, H0 in km/s/Mpc */
+  int n_filt;
+  const int *filt_len;
+  const double *filt_lam, *filt_trans;      /* concatenated, Angstrom */
+  const double *phot_d, *phot_sigma;        /* maggies */
+  const unsigned char *phot_mask;
+  int n_pix;
+  const double *spec_lam, *spec_d, *spec_sigma; /* observed frame, cgs F_nu */
+  const unsigned char *spec_mask;
+  int lsf_mode;                /* 0 R_fwhm, 1 R_sigma, 2 fwhm_aa, 3 sigma_aa, 4 sigma_kms, 5 fwhm_kms */
+  const double *lsf_value;     /* [n_pix] */
+  double sigma_gal_kms, z_ref;
+} orc_model;
+
+/* Row status bits (shared meaning with the library by documentation only). */
+#define ORC_BAD_THETA 1   /* non-finite parameter */
+#define ORC_BAD_Z 2       /* z < 0 or z >= zf */
+#define ORC_BAD_TMAX 4    /* oldest edge not older than 10 Myr */
+#define ORC_NONFINITE 16  /* non-finite model or likelihood */
+
+int orc_n_param(const orc_model *md);
+
+/* Cosmology: out[0] = D_L [cm] (not floored), out[1] = t_univ(z) [yr],
+ * out[2] = comoving distance [cm].  Adaptive Simpson quadrature. */
+void orc_cosmology(double H0, double Om0, double z, double *out);
+
+/* SFH edges (N_T + 1 values, yr). */
+void orc_sfh_edges(int n_sfh, double tmax_yr, double *T);
+
+/* Weights W[n][m][a] for one parameter row; returns row status. */
+int orc_weights(const orc_grid *g, const orc_model *md, const double *theta, double *W);
+
+/* Ionising photon rate per SSP node, Q[n][m][a] (photons/s per Msun). */
+void orc_q(const orc_grid *g, double *Q);
+
+/* Optical depth tau(lam) of a law (0 power law, 1 KC13). */
+void orc_dust_tau(int law, const double *lam, int n, double tau, double index, double *out);
+
+/* Photometric projection of an observer-frame F_nu given on the rest grid. */
+void orc_photometry(const orc_model *md, const double *lam_rest, int n_lam, double z,
+                    const double *fnu_obs, double *maggies);
+
+/* Spectral projection; valid[i] = 0 where the pixel has no model node. */
+void orc_spectrum(const orc_grid *g, const orc_model *md, const double *lam_rest, int n_lam,
+                  double z, const double *fnu_obs, double *pix, unsigned char *valid);
+
+/* Per-row intermediates: Y, O (young / old sums), F (attenuated rest-frame),
+ * fnu (observer frame, cgs) each [n_lam]; scal[0..5] = D_L cm, t_univ yr,
+ * T_max yr, Q_young, flux scale, lnL.  Any output may be NULL. Returns status. */
+int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double *W,
+            double *Y, double *O, double *F, double *fnu, double *phot, double *spec,
+            double *scal);
+
+/* Batched evaluation: phot_out [n][n_filt], spec_out [n][n_pix], lnl_out [n],
+ * status_out [n]; outputs may be NULL.  nthreads <= 0: all OpenMP threads. */
+void orc_eval(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld,
+              double *phot_out, double *spec_out, double *lnl_out, int *status_out,
+              int nthreads);
+
+/* Central finite-difference gradient of lnL (FP64), step h_j = h_rel*max(|x_j|, 1). */
+void orc_grad_fd(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld,
+                 double h_rel, double *grad_out, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

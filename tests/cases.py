@@ -1,0 +1,46 @@
+"""Test-side assembly of seeded cases: grid, filters, spectrum pixels,
+parameter rows and mock data (data = oracle model at a true parameter row,
+perturbed by Gaussian noise at S/N 20)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import synth
+
+
+def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_theta=4):
+    grid = grid if grid is not None else synth.make_grid(**w.grid_kw, seed=1)
+    filt = filters if filters is not None else synth.pack_filters(synth.workload_filters(w))
+    kw = dict(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
+              use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt)
+    nb = len(filt[0])
+    kw.update(phot_d=np.ones(nb), phot_sigma=np.ones(nb), phot_mask=np.ones(nb, np.uint8))
+    if w.spectrum is not None:
+        sp = w.spectrum
+        lam, r = synth.make_spectrum_pixels(sp["n_pix"], sp["lo_um"], sp["hi_um"], sp["r_lo"], sp["r_hi"])
+        kw.update(spec_lam=lam, spec_d=np.ones(lam.size), spec_sigma=np.ones(lam.size),
+                  spec_mask=np.ones(lam.size, np.uint8), lsf_mode=0, lsf_value=r,
+                  sigma_gal_kms=w.sigma_gal_kms, z_ref=w.z_ref)
+    orc = oracle.Oracle(**kw)
+    if with_data:
+        th_true = theta_rows(w, 1, seed=99)
+        th_true[0, w.n_sfh + (w.n_sfh if w.zmode == 0 else 1) + 2] = min(2.0, w.zf * 0.5)  # zred
+        res = orc.eval(th_true)
+        assert res["status"][0] == 0
+        nz = synth.noise(res["phot"].shape[1] + res["spec"].shape[1], seed=5)
+        ph = res["phot"][0]
+        sp_ = res["spec"][0]
+        snr = 20.0
+        orc.set_data(phot_d=ph * (1 + nz[:ph.size] / snr), phot_sigma=np.abs(ph) / snr,
+                     spec_d=(sp_ * (1 + nz[ph.size:] / snr)) if sp_.size else None,
+                     spec_sigma=(np.abs(sp_) / snr) if sp_.size else None)
+    return orc
+
+
+def theta_dict(w: synth.Workload, n, seed=4):
+    return synth.make_theta(n, w.n_sfh, w.zmode, w.ranges, seed=seed)
+
+
+def theta_rows(w: synth.Workload, n, seed=4):
+    return oracle.pack_theta(theta_dict(w, n, seed), w.n_sfh, w.zmode)
