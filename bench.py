@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched SED log-likelihood on GB300.
+
+Workload (default): the paper-scale photometric batch -- SSP grid 107 ages x
+12 [Fe/H] x 6000 wavelengths, 120 SFH bins with one [Fe/H] per bin,
+birth-cloud + Kriek & Conroy diffuse dust, nebular template 7 logU x 12 Z,
+20 filters, z in [0, 12], 1024 parameter rows per step.
+
+A step is one call of sed_loglike over the 1024-row batch (parameter
+preparation -> contraction -> fused epilogue -> lnL).  Inputs are resident
+in HBM when the timed region starts; L2 is flushed (256 MiB memset) before
+every timed step and the flush is outside the per-step CUDA-event timing.
+Under torchrun each rank evaluates its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on
+the host cores, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "phot_107x12x6000_b1024"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor ratio (recipe table)
+METRIC = "SED loglike evals/sec vs plain FP32 path at stated FP64-error; p50/p99 latency"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workload
+def build_workload(wname, ctx, seed_rows, device):
+    import torch
+    import synth
+
+    w = synth.WORKLOADS[wname]
+    grid = synth.make_grid(**w.grid_kw, seed=1)
+    filt = synth.pack_filters(synth.workload_filters(w))
+    nb = len(filt[0])
+    kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
+              phot_d=np.ones(nb), phot_sigma=np.ones(nb))
+    spec = None
+    if w.spectrum is not None:
+        sp = w.spectrum
+        lam, r = synth.make_spectrum_pixels(sp["n_pix"], sp["lo_um"], sp["hi_um"], sp["r_lo"], sp["r_hi"])
+        kw.update(spec_lam=lam, spec_d=np.ones(lam.size), spec_sigma=np.ones(lam.size), lsf_mode=0,
+                  lsf_value=r, sigma_gal_kms=w.sigma_gal_kms, z_ref=w.z_ref)
+        spec = lam
+    gid = ctx.load_grid(grid)
+    model = ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)
+    # mock data: the model at a true parameter row (z = 2), 5% Gaussian noise
+    d_true = synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99)
+    d_true["zred"][:] = 2.0
+    th_true = torch.from_numpy(model.pack(d_true)).to(device)
+    ph, sp_ = model.forward(th_true, "fp32")
+    torch.cuda.synchronize()
+    ph = ph.cpu().numpy()[0].astype(np.float64)
+    nz = synth.noise(nb + (0 if spec is None else spec.size), seed=5)
+    pd = ph * (1 + nz[:nb] / 20.0)
+    if spec is None:
+        model.set_data(phot_d=pd, phot_sigma=np.abs(ph) / 20.0)
+    else:
+        s0 = sp_.cpu().numpy()[0].astype(np.float64)
+        model.set_data(phot_d=pd, phot_sigma=np.abs(ph) / 20.0, spec_d=s0 * (1 + nz[nb:] / 20.0),
+                       spec_sigma=np.abs(s0) / 20.0)
+    d = synth.make_theta(w.batch, w.n_sfh, w.zmode, w.ranges, seed=seed_rows)
+    theta = model.pack(d)
+    return w, grid, filt, model, theta, (pd, np.abs(ph) / 20.0)
+
+
+# --------------------------------------------------------------------------- GPU leg
+def time_steps(model, ctx, t, prec, steps, flush, stream, profile=False):
+    import torch
+
+    per, stats = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        model.loglike(t, prec, stream=stream)
+        e1.record(stream)
+        if profile:
+            stats.append(ctx.last_stats(stream))
+        per.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in per]
+    return ms, stats
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_2609_30145_gb300 import Context
+
+    ctx = Context(local)
+    w, grid, filt, model, theta, data = build_workload(args.workload, ctx, 4 + rank, device)
+    B = w.batch
+    t = torch.from_numpy(theta).to(device)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    prec = args.precision
+
+    # warm-up
+    for _ in range(max(args.warmup, 3)):
+        model.loglike(t, prec, stream=stream)
+    torch.cuda.synchronize()
+
+    # timed region (profiling on: per-kernel events on the launching stream)
+    ctx.set_profiling(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, stats = time_steps(model, ctx, t, prec, args.steps, flush, stream, profile=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    ctx.set_profiling(False)
+    total_ms = sum(ms)
+    if dist:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_step = total_ms / args.steps
+    value = world * B * args.steps / (total_ms * 1e-3)
+
+    # stage statistics of the timed steps
+    contract_ms = [s["ms_contract"] for s in stats]
+    epi_ms = [s["ms_epilogue"] for s in stats]
+    prep_ms = [s["ms_prep"] for s in stats]
+    nnz = stats[-1]["nnz_w"]
+    n_lam = stats[-1]["n_lam"]
+    kpad = stats[-1]["dense_k"]
+    ldn = stats[-1]["ldn"]
+    c_ms = statistics.mean(contract_ms)
+    alg_flop = 2.0 * nnz * n_lam
+    pk, pk_kind = peaks()
+    if prec == "fp32":
+        peak_tf = pk["bf16_tflops_sustained"] * TF32_PER_BF16
+        issued = 3 * 2.0 * B * kpad * ldn
+        peak_note = f"TF32 dense peak = sustained BF16 {pk['bf16_tflops_sustained']} x {TF32_PER_BF16:.3f} (nominal ratio), of {pk_kind}"
+    elif prec == "bf16":
+        peak_tf = pk["bf16_tflops_sustained"]
+        issued = 2.0 * B * kpad * ldn
+        peak_note = f"sustained BF16 dense peak, of {pk_kind}"
+    else:
+        peak_tf = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FFMA: SMs x lanes x 2 x max clock
+        issued = 2.0 * B * kpad * ldn
+        peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz"
+    achieved = alg_flop / (c_ms * 1e-3) / 1e12
+    traffic = read_traffic()
+    e_ms = statistics.mean(epi_ms)
+    epi_bytes = B * n_lam * 8.0 + B * 8
+    roof = {"kernel": "k_contract_tc" if prec != "fp32_simt" else "k_contract_simt",
+            "bound": "tensor" if prec != "fp32_simt" else "alu", "achieved": round(achieved, 3),
+            "peak": round(peak_tf, 1), "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4),
+            "traffic": traffic, "peak_note": peak_note,
+            "algorithmic_flop_per_launch": alg_flop, "nnz_w_per_launch": nnz,
+            "issued_tensor_tflops": round(issued / (c_ms * 1e-3) / 1e12, 2),
+            "issued_frac": round(issued / (c_ms * 1e-3) / 1e12 / peak_tf, 4),
+            "contract_ms": round(c_ms, 4), "prep_ms": round(statistics.mean(prep_ms), 4),
+            "epilogue_ms": round(e_ms, 4),
+            "epilogue_hbm": {"bound": "hbm", "achieved_gbs": round(epi_bytes / (e_ms * 1e-3) / 1e9, 1),
+                             "peak": pk["hbm_gbs"], "frac": round(epi_bytes / (e_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                             "bytes_per_launch": epi_bytes}}
+
+    # latency percentiles of one step (device time, L2 flushed)
+    p50 = float(np.percentile(ms, 50))
+    p99 = float(np.percentile(ms, 99))
+
+    # other precisions, same timing method
+    variants = {}
+    for vp in ("fp32_simt", "bf16", "fp32"):
+        if vp == prec:
+            continue
+        for _ in range(3):
+            model.loglike(t, vp, stream=stream)
+        vms, _ = time_steps(model, ctx, t, vp, max(10, args.steps // 2), flush, stream)
+        variants[vp] = {"evals_per_s": round(B * len(vms) / (sum(vms) * 1e-3), 1),
+                        "ms_per_step": round(sum(vms) / len(vms), 4)}
+    variants[prec] = {"evals_per_s": round(B * args.steps / (sum(ms) * 1e-3), 1), "ms_per_step": round(sum(ms) / len(ms), 4)}
+
+    # end to end through the host-buffer entry point (pinned host theta, lnL back to host)
+    th_host = torch.from_numpy(theta).pin_memory()
+    lnl_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    st_host = torch.empty(B, dtype=torch.int32).pin_memory()
+    for _ in range(3):
+        model.loglike_host(th_host, prec, stream=stream, out=lnl_host, status=st_host)
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        model.loglike_host(th_host, prec, stream=stream, out=lnl_host, status=st_host)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if dist:
+        tt = torch.tensor([e2e_total], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    ld = theta.shape[1]
+    e2e = {"value": round(world * B * args.steps / e2e_total, 1), "unit": "evals/s",
+           "h2d_bytes_per_step": B * ld * 4, "d2h_bytes_per_step": B * 8 + B * 4,
+           "p50_ms": round(1e3 * float(np.percentile(e2e_t, 50)), 4),
+           "p99_ms": round(1e3 * float(np.percentile(e2e_t, 99)), 4)}
+
+    # GPU results for the accuracy comparison of the CPU-baseline leg
+    gpu_res = {}
+    for vp in ("fp32", "fp32_simt", "bf16"):
+        l, s = model.loglike(t, vp, stream=stream)
+        ph, _ = model.forward(t, vp, stream=stream)
+        torch.cuda.synchronize()
+        gpu_res[vp] = (l.cpu().numpy(), s.cpu().numpy(), ph.cpu().numpy())
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic: seeded SSP grid, nebular template, NIRCam-like filters and parameter rows "
+                   "shaped like the paper's workloads; mock data = model at a true row + 5% noise",
+           "config": {"workload": w.name, "batch_per_gpu": B, "n_age": int(grid.flux.shape[2]),
+                      "n_feh": int(grid.flux.shape[1]), "n_lam": int(grid.flux.shape[3]),
+                      "n_sfh": w.n_sfh, "n_filt": int(len(filt[0])), "nebular": bool(w.use_nebular),
+                      "dust": "birth-cloud power law + Kriek & Conroy 2013 diffuse",
+                      "precision": {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
+                                    "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
+                                    "fp32_simt": "FP32 FFMA contraction, FP64 lnL"}[prec],
+                      "l2": "flushed before every timed step (256 MiB memset, outside the timing)",
+                      "parallelism": f"replicas x{world} (independent batches per GPU)"},
+           "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "what": "device time of one 1024-row step"},
+           "variants": variants, "roofline": roof, "clocks": ck, "e2e": e2e,
+           "gpu_launches": 3 * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["accuracy_vs_fp64_oracle"] = cpu_baseline(w, grid, filt, data, theta, gpu_res,
+                                                                            args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def read_traffic():
+    """DRAM bytes per launch of the contraction from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", "k_contract_tc_phot_b1024.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            try:
+                return float(line.split(":")[1])
+            except ValueError:
+                return None
+    return None
+
+
+# --------------------------------------------------------------------------- CPU baseline / reference
+def _oracle_for(w, grid, filt, data):
+    import oracle
+
+    oracle.build()
+    return oracle.Oracle(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
+                         use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
+                         phot_d=data[0], phot_sigma=data[1])
+
+
+def cpu_baseline(w, grid, filt, data, theta32, gpu_res, seconds):
+    orc = _oracle_for(w, grid, filt, data)
+    cores = os.cpu_count() or 1
+    th64 = theta32.astype(np.float64)
+    rows, t_used, chunk = 0, 0.0, 64
+    ref_lnl, ref_ph, ref_st = [], [], []
+    while t_used < seconds and rows < th64.shape[0]:
+        sl = slice(rows, min(rows + chunk, th64.shape[0]))
+        t0 = time.perf_counter()
+        r = orc.eval(th64[sl], nthreads=cores)
+        t_used += time.perf_counter() - t0
+        ref_lnl.append(r["lnl"]); ref_ph.append(r["phot"]); ref_st.append(r["status"])
+        rows = sl.stop
+    cb = {"value": round(rows / t_used, 2), "unit": "evals/s", "cores": cores, "kind": "oracle",
+          "sample": f"first {rows} of the {th64.shape[0]} parameter rows of the workload, FP64 C oracle, "
+                    f"OpenMP over rows ({t_used:.1f} s)"}
+    ref_lnl, ref_ph, ref_st = np.concatenate(ref_lnl), np.concatenate(ref_ph), np.concatenate(ref_st)
+    ok = ref_st == 0
+    c = -0.5 * np.sum(np.log(2 * np.pi * data[1] ** 2))
+    scale = np.maximum(np.abs(ref_lnl[ok]), (c - ref_lnl[ok]) + abs(c))
+    acc = {}
+    for vp, (l, s, ph) in gpu_res.items():
+        l, ph = l[:rows][ok], ph[:rows][ok]
+        rp = ref_ph[ok]
+        good = rp > 0
+        e_f = np.abs(ph[good] - rp[good]) / rp[good]
+        e_l = np.abs(l - ref_lnl[ok]) / scale
+        e_l_raw = np.abs(l - ref_lnl[ok]) / np.abs(ref_lnl[ok])
+        acc[vp] = {"flux_rel_err": {"median": float(np.median(e_f)), "p99": float(np.percentile(e_f, 99)),
+                                    "max": float(e_f.max())},
+                   "lnl_err_over_term_scale": {"median": float(np.median(e_l)), "p99": float(np.percentile(e_l, 99)),
+                                               "max": float(e_l.max())},
+                   "lnl_rel_err": {"median": float(np.median(e_l_raw)), "max": float(e_l_raw.max())},
+                   "status_match": bool(np.array_equal(s[:rows], ref_st)), "rows": int(ok.sum())}
+    return cb, acc
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    import oracle
+
+    w = synth.WORKLOADS[args.workload]
+    grid = synth.make_grid(**w.grid_kw, seed=1)
+    filt = synth.pack_filters(synth.workload_filters(w))
+    nb = len(filt[0])
+    orc = oracle.Oracle(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
+                        use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
+                        phot_d=np.ones(nb), phot_sigma=np.ones(nb))
+    th_true = oracle.pack_theta(synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99), w.n_sfh, w.zmode)
+    th_true[0, w.n_sfh + (w.n_sfh if w.zmode == 0 else 1) + 2] = 2.0
+    ph = orc.eval(th_true)["phot"][0]
+    nz = synth.noise(nb, seed=5)
+    orc.set_data(phot_d=ph * (1 + nz / 20.0), phot_sigma=np.abs(ph) / 20.0)
+    theta = oracle.pack_theta(synth.make_theta(w.batch, w.n_sfh, w.zmode, w.ranges, seed=4), w.n_sfh,
+                              w.zmode).astype(np.float32).astype(np.float64)
+    cores = os.cpu_count() or 1
+    sample = 64
+    for i in range(args.warmup):
+        orc.eval(theta[:sample], nthreads=cores)
+    ts = []
+    for i in range(args.steps):
+        sl = slice((i * sample) % w.batch, (i * sample) % w.batch + sample)
+        t0 = time.perf_counter()
+        orc.eval(theta[sl], nthreads=cores)
+        ts.append(time.perf_counter() - t0)
+    value = sample * args.steps / sum(ts)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "evals/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * sum(ts) / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (same seeded workload as the GPU arm)",
+           "config": {"workload": w.name, "batch_per_step": sample,
+                      "what": "FP64 C oracle (plain loops, OpenMP over rows) on the host cores; each step a "
+                              f"{sample}-row sample of the {w.batch}-row workload"},
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(value, 2), "unit": "evals/s",
+                            "sample": f"{args.steps} steps x {sample} rows"},
+           "e2e": {"value": round(value, 2), "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

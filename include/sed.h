@@ -1,0 +1,228 @@
+/*
+ * sed.h -- C ABI of the GB300 (sm_103a) batched SED forward model and
+ * Gaussian log-likelihood.
+ *
+ * The library evaluates, for a batch of parameter rows theta (the live points
+ * of a nested sampler, or any batch), the stellar-population forward model of
+ * the paper and its log-likelihood:
+ *
+ *   SFH + [Fe/H] (+[a/Fe]) history -> SSP weights W      (Sec. 2.2, App. B, Sec. 5.4)
+ *   young / old contraction of W with the SSP grid        (Eq. csp_sum_main, Eq. app_attn)
+ *   + nebular template scaled by the ionising photons     (App. C, Eq. app_q)
+ *   two-component dust attenuation                        (Sec. 2.4)
+ *   mass, luminosity distance and (1+z) scaling           (Sec. 2.6)
+ *   photometric projection through filter curves         (App. D, Eq. app_phot_row/app_phot_T)
+ *   spectral projection with a Gaussian LSF               (Eq. one_kernel, App. E, Eq. app_response)
+ *   diagonal Gaussian log-likelihood, normalisation kept  (Eq. total_lnlike, Eq. app_spec_lndiag)
+ *
+ * Conventions for every entry point:
+ *  - Arguments that can be checked on the host are checked before anything is
+ *    launched; a failed check returns SED_EINVAL (or SED_ERANGE/SED_EUNSUPPORTED)
+ *    and nothing runs.  sed_last_error() then holds a one-line reason.
+ *  - Hot-path calls (sed_forward, sed_loglike, sed_loglike_grad) take DEVICE
+ *    pointers and a CUDA stream (cudaStream_t passed as void*; NULL = legacy
+ *    default stream).  They only enqueue work and return SED_OK; results are
+ *    ready when the stream reaches that point.  sed_loglike_host takes HOST
+ *    buffers, copies in, runs and copies out, and returns when done.
+ *  - Per-row problems found on the device (non-finite parameter, z outside
+ *    [0, zf), oldest SFH edge not older than 10 Myr, non-finite model) set the
+ *    row's bits in row_status (SED_ROW_*) and write lnL = -INFINITY for it;
+ *    the call itself still returns SED_OK.
+ *  - Ownership: host arrays passed in descriptors are copied; the caller keeps
+ *    ownership and may free them after the call returns.  Device memory owned
+ *    by the context (grids, models, per-stream workspaces) is freed by
+ *    sed_destroy_model / sed_destroy.  Output buffers belong to the caller.
+ *  - Threading: one context may be used from several host threads as long as
+ *    each thread uses its own CUDA stream.  The first call on a stream (or with
+ *    a larger batch than before on that stream) allocates that stream's
+ *    workspace with cudaMalloc, which synchronises the device.
+ *  - Memory budget: allocations beyond hbm_budget_bytes return SED_ENOMEM.
+ */
+#ifndef SED_H
+#define SED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SED_OK = 0,
+  SED_EINVAL = 1,       /* invalid argument or descriptor */
+  SED_ENOMEM = 2,       /* HBM budget or cudaMalloc exhausted */
+  SED_ECUDA = 3,        /* a CUDA runtime/driver call failed */
+  SED_ERANGE = 4,       /* a size exceeds a supported maximum */
+  SED_ENONFINITE = 5,   /* non-finite value in a host input */
+  SED_EBUSY = 6,        /* object still in use */
+  SED_ETIMEOUT = 7,     /* a bounded device wait gave up */
+  SED_EUNSUPPORTED = 8  /* feature/precision not available for this model */
+} sed_status;
+
+/* Contraction precision (argument `precision`). */
+enum {
+  SED_PREC_FP32 = 0,      /* tcgen05 tensor cores, 3xTF32 split (FP32-grade) */
+  SED_PREC_FP32_SIMT = 1, /* CUDA-core FP32 FFMA (independent cross-check) */
+  SED_PREC_BF16 = 2       /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+};
+
+/* Diffuse dust law (Sec. 2.4). */
+enum { SED_DUST_POWER_LAW = 0, SED_DUST_KC13 = 1 };
+
+/* Line-spread-function units (Eq. app_modes). */
+enum {
+  SED_LSF_R_FWHM = 0, SED_LSF_R_SIGMA = 1, SED_LSF_FWHM_AA = 2,
+  SED_LSF_SIGMA_AA = 3, SED_LSF_SIGMA_KMS = 4, SED_LSF_FWHM_KMS = 5
+};
+
+/* Row status bits. */
+#define SED_ROW_BAD_THETA 1u  /* a parameter is not finite */
+#define SED_ROW_BAD_Z 2u      /* zred < 0 or zred >= zf */
+#define SED_ROW_BAD_TMAX 4u   /* t_univ(z) - t_univ(zf) <= 10 Myr */
+#define SED_ROW_NONFINITE 16u /* model or log-likelihood not finite */
+#define SED_ROW_DEVICE_TIMEOUT 32u /* a bounded wait inside a kernel gave up: the call's results are invalid */
+
+/* Parameter keys (paper names, Fig. "ceridwen_flow"); index into the offsets
+ * returned by sed_model_layout. */
+enum {
+  SED_KEY_SFH = 0,            /* N_T formed-mass fractions, bin 0 = most recent */
+  SED_KEY_LOGZSOL = 1,        /* N_T per-bin [Fe/H] (zmode 0) or 1 constant (zmode 1) */
+  SED_KEY_AFE = 2,            /* [a/Fe] (used when use_afe) */
+  SED_KEY_LOGMASS = 3,        /* log10 total formed mass / Msun */
+  SED_KEY_ZRED = 4,           /* redshift */
+  SED_KEY_TAU_POW = 5,        /* birth-cloud optical depth at 5500 A */
+  SED_KEY_ALPHA_POW = 6,      /* birth-cloud power-law slope */
+  SED_KEY_DIFFUSE_TAU = 7,    /* diffuse optical depth at 5500 A */
+  SED_KEY_DIFFUSE_INDEX = 8,  /* diffuse slope delta (power-law index or KC13 delta) */
+  SED_KEY_GAS_LOGZ = 9,       /* log10 Z_gas/Zsun (used when use_nebular) */
+  SED_KEY_GAS_LOGU = 10,      /* log10 U (used when use_nebular) */
+  SED_NKEYS = 11
+};
+
+typedef struct sed_ctx sed_ctx;
+typedef int32_t sed_grid_id;
+typedef int32_t sed_model_id;
+
+/*
+ * SSP grid (Sec. 2.1): spectra on (age, [Fe/H], [a/Fe]) nodes and a common
+ * rest-frame wavelength axis.  All axes strictly increasing, fluxes finite and
+ * >= 0.  Copied to the device once (FP32 master, TF32 split and BF16 copies).
+ */
+typedef struct {
+  int n_age, n_feh, n_afe, n_lam;  /* n_afe = 1 for a 3-D grid */
+  const double *log_age_yr;        /* [n_age] log10 age / yr */
+  const double *feh;               /* [n_feh] log10 Z/Zsun */
+  const double *afe;               /* [n_afe] [a/Fe] nodes (NULL allowed when n_afe = 1) */
+  const double *lam_aa;            /* [n_lam] rest-frame Angstrom */
+  const double *flux;              /* [n_afe][n_feh][n_age][n_lam] Lsun/Hz per Msun formed */
+  const double *sigma_lib_kms;     /* [n_lam] documented library LSF, or NULL (Eq. app_siglib) */
+  int neb_n_logu, neb_n_logz;      /* nebular template axes (0 = no nebular) */
+  const double *neb_logu, *neb_logz;
+  const double *neb_log10_lnu_per_q; /* [n_logu][n_logz][n_lam] log10(L_nu/Q), (Lsun/Hz)/(photon/s) */
+} sed_grid_desc;
+
+/*
+ * One fit: model choices, observations and their uncertainties (Sec. 2, 3, 4.1).
+ * Filters are concatenated: band b has filt_len[b] samples (Angstrom, observed
+ * frame) with transmission filt_trans.  Photometric data and uncertainties are
+ * in maggies; spectral data in cgs F_nu on observed-frame pixels spec_lam_aa.
+ * n_filt or n_pix may be 0 (arm absent).  Masks may be NULL (all included).
+ */
+typedef struct {
+  sed_grid_id grid;
+  int n_sfh;                  /* N_T >= 3: edges 0, 5 Myr, 10 Myr, log-uniform to t_univ(z)-t_univ(zf) */
+  double zf;                  /* formation redshift of the oldest edge */
+  int zmode;                  /* 0: one [Fe/H] per SFH bin; 1: one constant [Fe/H] */
+  int use_afe;                /* interpolate the [a/Fe] axis (else [a/Fe] = 0) */
+  int use_nebular;            /* add the nebular template (grid must carry one) */
+  int dust_law;               /* SED_DUST_POWER_LAW or SED_DUST_KC13 (diffuse component) */
+  double bc_edge_log_age_yr;  /* birth-cloud edge; paper default log10(age/Gyr) = -1.97 -> 7.03 */
+  double H0, Om0;             /* flat LCDM, km/s/Mpc */
+  int n_filt;
+  const int *filt_len;
+  const double *filt_lam_aa, *filt_trans;
+  const double *phot_d, *phot_sigma;
+  const uint8_t *phot_mask;
+  int n_pix;
+  const double *spec_lam_aa, *spec_d, *spec_sigma;
+  const uint8_t *spec_mask;
+  int lsf_mode;               /* SED_LSF_* */
+  const double *lsf_value;    /* [n_pix] value in the unit of lsf_mode */
+  double sigma_gal_kms;       /* fixed stellar dispersion folded into the LSF kernel */
+  double z_ref;               /* reference redshift of the projector (Eq. app_sigeff) */
+} sed_model_desc;
+
+/* Context on one CUDA device; hbm_budget_bytes = 0 means no limit. */
+sed_status sed_create(sed_ctx **out, int device, size_t hbm_budget_bytes);
+sed_status sed_destroy(sed_ctx *ctx);
+const char *sed_status_string(sed_status s);
+/* One-line description of the last error on this context (never NULL). */
+const char *sed_last_error(const sed_ctx *ctx);
+/* Device bytes currently held by the context. */
+sed_status sed_memory_used(const sed_ctx *ctx, size_t *bytes);
+
+sed_status sed_load_grid(sed_ctx *ctx, const sed_grid_desc *desc, sed_grid_id *out);
+
+sed_status sed_create_model(sed_ctx *ctx, const sed_model_desc *desc, sed_model_id *out);
+/* n_param: columns a parameter row needs; offsets[SED_NKEYS]: first column of each key. */
+sed_status sed_model_layout(const sed_ctx *ctx, sed_model_id model, int *n_param, int *offsets);
+/* Replace the observed data/uncertainties of a model (host arrays, copied; NULL keeps). */
+sed_status sed_set_data(sed_ctx *ctx, sed_model_id model, const double *phot_d,
+                        const double *phot_sigma, const double *spec_d, const double *spec_sigma);
+sed_status sed_destroy_model(sed_ctx *ctx, sed_model_id model);
+
+/*
+ * Forward model: photometry phot_out [n][n_filt] in maggies and/or the
+ * projected spectrum spec_out [n][n_pix] in cgs F_nu (either may be NULL).
+ * theta: device, row-major [n][ld] FP32 with ld >= n_param.  0 <= n.
+ */
+sed_status sed_forward(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld,
+                       float *phot_out, float *spec_out, int precision, void *stream);
+
+/*
+ * Log-likelihood lnl_out [n] (FP64, device) and optional row_status [n]
+ * (device, may be NULL).  Eq. total_lnlike with the normalisation term kept.
+ */
+sed_status sed_loglike(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld,
+                       double *lnl_out, uint32_t *row_status, int precision, void *stream);
+
+/*
+ * Log-likelihood and its gradient with respect to every parameter column:
+ * grad_out [n][ld] (FP32, device; columns >= n_param are zeroed).  Columns the
+ * model does not use (e.g. gas_* without nebular) get 0.
+ */
+sed_status sed_loglike_grad(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld,
+                            double *lnl_out, float *grad_out, uint32_t *row_status,
+                            int precision, void *stream);
+
+/*
+ * sed_loglike with HOST buffers: theta [n][ld] FP32, lnl_out [n], row_status
+ * [n] or NULL.  Copies in, runs on `stream`, copies out and synchronises the
+ * stream before returning.
+ */
+sed_status sed_loglike_host(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld,
+                            double *lnl_out, uint32_t *row_status, int precision, void *stream);
+
+/*
+ * Per-stage timing and work counters of the last hot-path call on a stream.
+ * With profiling on, each hot-path call records CUDA events on its stream
+ * before and after each of its kernels (preparation, contraction, epilogue);
+ * sed_last_stats synchronises on the last event and reads them.  nnz_w is the
+ * number of non-zero SSP weights of the call's rows (the contraction's
+ * algorithmic work is 2 * nnz_w * n_lam FLOPs).
+ */
+typedef struct {
+  float ms_prep, ms_contract, ms_epilogue;
+  double nnz_w;          /* sum over rows of the non-zero weights W[theta][k] */
+  double dense_k;        /* padded K of the contraction (young + old) */
+  int n_rows, n_lam, ldn, precision;
+} sed_stage_stats;
+
+sed_status sed_set_profiling(sed_ctx *ctx, int on);
+sed_status sed_last_stats(sed_ctx *ctx, void *stream, sed_stage_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SED_H */

@@ -1,0 +1,88 @@
+"""ctypes declarations of the C ABI in include/sed.h (argument marshalling only).
+
+The shared library is ``_build/libsed.so`` next to this file; it is built by
+``paper_2609_30145_gb300.build.build()``.  Loading fails loudly when it is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsed.so")
+
+SED_OK, SED_EINVAL, SED_ENOMEM, SED_ECUDA, SED_ERANGE, SED_ENONFINITE, SED_EBUSY, SED_ETIMEOUT, \
+    SED_EUNSUPPORTED = range(9)
+PREC_FP32, PREC_FP32_SIMT, PREC_BF16 = 0, 1, 2
+DUST_POWER_LAW, DUST_KC13 = 0, 1
+LSF_R_FWHM, LSF_R_SIGMA, LSF_FWHM_AA, LSF_SIGMA_AA, LSF_SIGMA_KMS, LSF_FWHM_KMS = range(6)
+ROW_BAD_THETA, ROW_BAD_Z, ROW_BAD_TMAX, ROW_NONFINITE, ROW_DEVICE_TIMEOUT = 1, 2, 4, 16, 32
+KEYS = ("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
+        "diffuse_dust_index", "gas_logz", "gas_logu")
+NKEYS = len(KEYS)
+
+P = C.c_void_p
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n_age", C.c_int), ("n_feh", C.c_int), ("n_afe", C.c_int), ("n_lam", C.c_int),
+                ("log_age_yr", P), ("feh", P), ("afe", P), ("lam_aa", P), ("flux", P),
+                ("sigma_lib_kms", P), ("neb_n_logu", C.c_int), ("neb_n_logz", C.c_int),
+                ("neb_logu", P), ("neb_logz", P), ("neb_log10_lnu_per_q", P)]
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("grid", C.c_int32), ("n_sfh", C.c_int), ("zf", C.c_double), ("zmode", C.c_int),
+                ("use_afe", C.c_int), ("use_nebular", C.c_int), ("dust_law", C.c_int),
+                ("bc_edge_log_age_yr", C.c_double), ("H0", C.c_double), ("Om0", C.c_double),
+                ("n_filt", C.c_int), ("filt_len", P), ("filt_lam_aa", P), ("filt_trans", P),
+                ("phot_d", P), ("phot_sigma", P), ("phot_mask", P),
+                ("n_pix", C.c_int), ("spec_lam_aa", P), ("spec_d", P), ("spec_sigma", P),
+                ("spec_mask", P), ("lsf_mode", C.c_int), ("lsf_value", P),
+                ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double)]
+
+
+class StageStats(C.Structure):
+    _fields_ = [("ms_prep", C.c_float), ("ms_contract", C.c_float), ("ms_epilogue", C.c_float),
+                ("nnz_w", C.c_double), ("dense_k", C.c_double), ("n_rows", C.c_int),
+                ("n_lam", C.c_int), ("ldn", C.c_int), ("precision", C.c_int)]
+
+
+# exported symbols and their signatures (name -> (restype, argtypes))
+SIGNATURES = {
+    "sed_create": (C.c_int, [C.POINTER(P), C.c_int, C.c_size_t]),
+    "sed_destroy": (C.c_int, [P]),
+    "sed_status_string": (C.c_char_p, [C.c_int]),
+    "sed_last_error": (C.c_char_p, [P]),
+    "sed_memory_used": (C.c_int, [P, C.POINTER(C.c_size_t)]),
+    "sed_load_grid": (C.c_int, [P, C.POINTER(GridDesc), C.POINTER(C.c_int32)]),
+    "sed_create_model": (C.c_int, [P, C.POINTER(ModelDesc), C.POINTER(C.c_int32)]),
+    "sed_model_layout": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "sed_set_data": (C.c_int, [P, C.c_int32, P, P, P, P]),
+    "sed_destroy_model": (C.c_int, [P, C.c_int32]),
+    "sed_forward": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
+    "sed_loglike": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
+    "sed_loglike_grad": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, P, C.c_int, P]),
+    "sed_loglike_host": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
+    "sed_set_profiling": (C.c_int, [P, C.c_int]),
+    "sed_last_stats": (C.c_int, [P, P, C.POINTER(StageStats)]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libsed.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                              "(run paper_2609_30145_gb300.build.build())")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib

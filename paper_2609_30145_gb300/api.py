@@ -1,0 +1,238 @@
+"""Python binding of the C ABI (include/sed.h): argument marshalling only.
+
+Every step of the forward model and likelihood runs in the CUDA library; this
+module converts numpy/torch arguments into the pointers, sizes and streams
+the C functions take.  PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _ffi
+from ._ffi import KEYS, NKEYS
+
+PREC = {"fp32": _ffi.PREC_FP32, "fp32_simt": _ffi.PREC_FP32_SIMT, "bf16": _ffi.PREC_BF16}
+
+
+class SedError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status}: {msg}")
+        self.status = status
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._lib = _ffi.load()
+        self.device = int(device)
+        h = C.c_void_p()
+        st = self._lib.sed_create(C.byref(h), self.device, C.c_size_t(int(hbm_budget_bytes)))
+        if st:
+            raise SedError(st, "sed_create failed")
+        self._h = h
+        self._grids = []
+
+    def _check(self, st):
+        if st:
+            raise SedError(st, self._lib.sed_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sed_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_profiling(self, on: bool):
+        self._check(self._lib.sed_set_profiling(self._h, 1 if on else 0))
+
+    def last_stats(self, stream=None):
+        """Stage times (ms) and work counters of the last profiled call on `stream`."""
+        st = _ffi.StageStats()
+        self._check(self._lib.sed_last_stats(self._h, _stream_handle(stream), C.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def memory_used(self):
+        v = C.c_size_t()
+        self._check(self._lib.sed_memory_used(self._h, C.byref(v)))
+        return v.value
+
+    # ------------------------------------------------------------------
+    def load_grid(self, grid) -> int:
+        """grid: object with log_age_yr, feh, afe, lam_aa, flux[n_afe][n_feh][n_age][n_lam]
+        and optionally neb_logu, neb_logz, neb_tab, sigma_lib_kms."""
+        keep = [_f64(grid.log_age_yr), _f64(grid.feh), _f64(grid.afe), _f64(grid.lam_aa), _f64(grid.flux)]
+        d = _ffi.GridDesc()
+        d.n_afe, d.n_feh, d.n_age, d.n_lam = grid.flux.shape
+        d.log_age_yr, d.feh, d.afe, d.lam_aa, d.flux = (_ptr(a) for a in keep)
+        sl = _f64(getattr(grid, "sigma_lib_kms", None))
+        keep.append(sl)
+        d.sigma_lib_kms = _ptr(sl)
+        if getattr(grid, "neb_tab", None) is not None:
+            nu, nz, nt = _f64(grid.neb_logu), _f64(grid.neb_logz), _f64(grid.neb_tab)
+            keep += [nu, nz, nt]
+            d.neb_n_logu, d.neb_n_logz = nt.shape[:2]
+            d.neb_logu, d.neb_logz, d.neb_log10_lnu_per_q = _ptr(nu), _ptr(nz), _ptr(nt)
+        gid = C.c_int32()
+        self._check(self._lib.sed_load_grid(self._h, C.byref(d), C.byref(gid)))
+        return gid.value
+
+    def create_model(self, grid_id, n_sfh, zf, zmode, *, use_afe=0, use_nebular=0, dust_law=0,
+                     bc_edge_log_age_yr=7.03, H0=67.66, Om0=0.3097, filters=None,
+                     phot_d=None, phot_sigma=None, phot_mask=None, spec_lam=None, spec_d=None,
+                     spec_sigma=None, spec_mask=None, lsf_mode=0, lsf_value=None,
+                     sigma_gal_kms=0.0, z_ref=0.0) -> "Model":
+        d = _ffi.ModelDesc()
+        d.grid, d.n_sfh, d.zf, d.zmode = grid_id, n_sfh, zf, zmode
+        d.use_afe, d.use_nebular, d.dust_law = use_afe, use_nebular, dust_law
+        d.bc_edge_log_age_yr, d.H0, d.Om0 = bc_edge_log_age_yr, H0, Om0
+        keep = []
+        if filters is not None:
+            lens, lam, tr = filters
+            lens = np.ascontiguousarray(lens, dtype=np.int32)
+            lam, tr = _f64(lam), _f64(tr)
+            keep += [lens, lam, tr]
+            d.n_filt = len(lens)
+            d.filt_len, d.filt_lam_aa, d.filt_trans = _ptr(lens), _ptr(lam), _ptr(tr)
+            pd, ps = _f64(phot_d), _f64(phot_sigma)
+            pm = None if phot_mask is None else np.ascontiguousarray(phot_mask, dtype=np.uint8)
+            keep += [pd, ps, pm]
+            d.phot_d, d.phot_sigma, d.phot_mask = _ptr(pd), _ptr(ps), _ptr(pm)
+        if spec_lam is not None:
+            sl, sd, ss, lv = _f64(spec_lam), _f64(spec_d), _f64(spec_sigma), _f64(lsf_value)
+            sm = None if spec_mask is None else np.ascontiguousarray(spec_mask, dtype=np.uint8)
+            keep += [sl, sd, ss, lv, sm]
+            d.n_pix = sl.size
+            d.spec_lam_aa, d.spec_d, d.spec_sigma, d.spec_mask = _ptr(sl), _ptr(sd), _ptr(ss), _ptr(sm)
+            d.lsf_mode, d.lsf_value = lsf_mode, _ptr(lv)
+            d.sigma_gal_kms, d.z_ref = sigma_gal_kms, z_ref
+        mid = C.c_int32()
+        self._check(self._lib.sed_create_model(self._h, C.byref(d), C.byref(mid)))
+        return Model(self, mid.value, n_filt=d.n_filt, n_pix=d.n_pix)
+
+
+class Model:
+    """One fit (model description + observations) inside a Context."""
+
+    def __init__(self, ctx: Context, mid: int, n_filt: int, n_pix: int):
+        self.ctx, self.id, self.n_filt, self.n_pix = ctx, mid, n_filt, n_pix
+        n = C.c_int()
+        offs = (C.c_int * NKEYS)()
+        ctx._check(ctx._lib.sed_model_layout(ctx._h, mid, C.byref(n), offs))
+        self.n_param = n.value
+        self.offsets = dict(zip(KEYS, list(offs)))
+
+    def pack(self, d, dtype=np.float32):
+        """Parameter rows in this model's column layout from a dict of arrays."""
+        n = np.asarray(d["sfh"]).shape[0]
+        out = np.zeros((n, self.n_param), dtype=np.float64)
+        bounds = list(self.offsets.values()) + [self.n_param]
+        for i, k in enumerate(KEYS):
+            w = bounds[i + 1] - bounds[i]
+            out[:, bounds[i]:bounds[i] + w] = np.asarray(d[k], dtype=np.float64).reshape(n, w)
+        return out.astype(dtype)
+
+    def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
+        a = [_f64(phot_d), _f64(phot_sigma), _f64(spec_d), _f64(spec_sigma)]
+        self.ctx._check(self.ctx._lib.sed_set_data(self.ctx._h, self.id, *(_ptr(x) for x in a)))
+
+    def _theta(self, theta):
+        if not (theta.is_cuda and theta.dtype == torch.float32 and theta.dim() == 2 and theta.stride(1) == 1):
+            raise ValueError("theta must be a CUDA float32 [n, ld] tensor with unit column stride")
+        return theta.shape[0], theta.stride(0)
+
+    def forward(self, theta: torch.Tensor, precision="fp32", stream=None):
+        n, ld = self._theta(theta)
+        dev = theta.device
+        phot = torch.empty((n, self.n_filt), dtype=torch.float32, device=dev) if self.n_filt else None
+        spec = torch.empty((n, self.n_pix), dtype=torch.float32, device=dev) if self.n_pix else None
+        st = self.ctx._lib.sed_forward(self.ctx._h, self.id, C.c_void_p(theta.data_ptr()), n, ld,
+                                       None if phot is None else C.c_void_p(phot.data_ptr()),
+                                       None if spec is None else C.c_void_p(spec.data_ptr()),
+                                       _prec(precision), _stream_handle(stream))
+        self.ctx._check(st)
+        return phot, spec
+
+    def loglike(self, theta: torch.Tensor, precision="fp32", stream=None, out=None, status=None):
+        n, ld = self._theta(theta)
+        lnl = out if out is not None else torch.empty(n, dtype=torch.float64, device=theta.device)
+        stt = status if status is not None else torch.empty(n, dtype=torch.int32, device=theta.device)
+        st = self.ctx._lib.sed_loglike(self.ctx._h, self.id, C.c_void_p(theta.data_ptr()), n, ld,
+                                       C.c_void_p(lnl.data_ptr()), C.c_void_p(stt.data_ptr()),
+                                       _prec(precision), _stream_handle(stream))
+        self.ctx._check(st)
+        return lnl, stt
+
+    def loglike_grad(self, theta: torch.Tensor, precision="fp32", stream=None):
+        n, ld = self._theta(theta)
+        lnl = torch.empty(n, dtype=torch.float64, device=theta.device)
+        grad = torch.empty((n, ld), dtype=torch.float32, device=theta.device)
+        stt = torch.empty(n, dtype=torch.int32, device=theta.device)
+        st = self.ctx._lib.sed_loglike_grad(self.ctx._h, self.id, C.c_void_p(theta.data_ptr()), n, ld,
+                                            C.c_void_p(lnl.data_ptr()), C.c_void_p(grad.data_ptr()),
+                                            C.c_void_p(stt.data_ptr()), _prec(precision),
+                                            _stream_handle(stream))
+        self.ctx._check(st)
+        return lnl, grad, stt
+
+    def loglike_host(self, theta: np.ndarray, precision="fp32", stream=None, out=None, status=None):
+        """theta: host float32 [n, ld] (pinned memory recommended); returns host arrays."""
+        th = np.ascontiguousarray(theta, dtype=np.float32) if not isinstance(theta, torch.Tensor) else theta
+        if isinstance(th, torch.Tensor):
+            n, ld = th.shape[0], th.stride(0)
+            tp = th.data_ptr()
+        else:
+            n, ld = th.shape
+            tp = th.ctypes.data
+        lnl = out if out is not None else np.empty(n, dtype=np.float64)
+        stt = status if status is not None else np.empty(n, dtype=np.uint32)
+        lp = lnl.data_ptr() if isinstance(lnl, torch.Tensor) else lnl.ctypes.data
+        sp = stt.data_ptr() if isinstance(stt, torch.Tensor) else stt.ctypes.data
+        st = self.ctx._lib.sed_loglike_host(self.ctx._h, self.id, C.c_void_p(tp), n, ld, C.c_void_p(lp),
+                                            C.c_void_p(sp), _prec(precision), _stream_handle(stream))
+        self.ctx._check(st)
+        return lnl, stt
+
+
+class SedLogLike(torch.autograd.Function):
+    """lnL(theta) with the library's hand-written adjoint as the backward."""
+
+    @staticmethod
+    def forward(ctx, theta, model: Model, precision="fp32"):
+        if theta.requires_grad:
+            lnl, grad, st = model.loglike_grad(theta.detach().contiguous(), precision)
+            ctx.save_for_backward(grad)
+        else:
+            lnl, st = model.loglike(theta.detach().contiguous(), precision)
+            ctx.save_for_backward(None)
+        return lnl
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return (g[:, None].to(grad.dtype) * grad, None, None)

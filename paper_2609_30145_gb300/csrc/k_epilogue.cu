@@ -1,0 +1,195 @@
+// Fused epilogue: attenuation + nebular, observer-frame scaling, photometric
+// and spectral projections and the Gaussian log-likelihood.  One CTA per
+// parameter row; the attenuated rest-frame spectrum of the row is staged in
+// shared memory once and every projection gathers from it.
+//
+//  F(lam) = e^{-tau_d(lam)} [ e^{-tau_BC(lam)} (Y(lam) + neb(lam)) + O(lam) ]
+//     tau_BC = tau_pow (lam/5500)^alpha_pow (birth cloud, Sec. 2.4)
+//     tau_d  = diffuse power law, or Kriek & Conroy 2013 (Sec. 2.4)
+//     neb    = Q_young 10^(bilinear log10 template)        (App. C)
+//  photometry (App. D, Eq. app_phot_T): m_b = P sum_j w_j lerp(F/lam^2)(lam_j/(1+z))
+//  spectrum (App. E, Eq. app_response): m_i = s sum_j w_ij F_j / sum_j w_ij,
+//     Gaussian in ln(lam) truncated at 5 sigma, linear interpolation for
+//     kernels narrower than half a model log-pixel
+//  lnL (Eq. total_lnlike): sum over included data of -r^2/2 - ln(2 pi sigma^2)/2
+//
+// All reductions run in a fixed order, so the result is bitwise reproducible.
+#include "sed_internal.cuh"
+
+namespace sed {
+
+constexpr int EPI_THREADS = 256;
+constexpr int MAX_BANDS = 128;
+
+// last node k with lam[k] <= x (lam ascending), for lam[0] <= x <= lam[n-1];
+// clamped to n-2 so that k+1 is a valid node.
+__device__ __forceinline__ int locate_ln(const GridDev& g, float lnx, const float* lnl_hi) {
+  int q = (int)((lnx - g.lut_x0) * g.lut_inv_h);
+  q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
+  int k = g.lut[q];
+  const int top = g.n_lam - 2;
+  k = k > top ? top : k;
+#pragma unroll 1
+  for (int it = 0; it < 4 && k < top && lnl_hi[k + 1] <= lnx; ++it) ++k;
+#pragma unroll 1
+  for (int it = 0; it < 4 && k > 0 && lnl_hi[k] > lnx; ++it) --k;
+  return k;
+}
+
+__device__ __forceinline__ int locate_lin(const GridDev& g, float x) {
+  int k = locate_ln(g, logf(x), g.lnl_hi);
+  const int top = g.n_lam - 2;
+#pragma unroll 1
+  for (int it = 0; it < 4 && k < top && g.lam_f[k + 1] <= x; ++it) ++k;
+#pragma unroll 1
+  for (int it = 0; it < 4 && k > 0 && g.lam_f[k] > x; ++it) --k;
+  return k;
+}
+
+__global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant__ EpiArgs a) {
+  const ModelDev& md = a.md;
+  const GridDev& g = a.g;
+  const int r = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int N = g.n_lam;
+  extern __shared__ float smem[];
+  float* Gs = smem;          // F / lam^2
+  float* Fs = smem + N;      // F
+  __shared__ double band_v[MAX_BANDS];
+  __shared__ double red[EPI_THREADS / 32];
+
+  RowScal rs = a.rs[r];
+  if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
+  if (rs.status) {
+    for (int b = tid; b < md.n_filt; b += blockDim.x)
+      if (a.phot_out) a.phot_out[(size_t)r * md.n_filt + b] = 0.f;
+    for (int i = tid; i < md.n_pix; i += blockDim.x)
+      if (a.spec_out) a.spec_out[(size_t)r * md.n_pix + i] = 0.f;
+    if (tid == 0) {
+      if (a.lnl) a.lnl[r] = -INFINITY;
+      if (a.status) a.status[r] = rs.status;
+    }
+    return;
+  }
+
+  // ---- attenuated rest-frame spectrum into shared memory
+  const float* Yr = a.Y + (size_t)r * a.ldn;
+  const float* Or = a.O + (size_t)r * a.ldn;
+  const float eb = 0.85f - 1.9f * rs.delta;
+  for (int k = tid; k < N; k += blockDim.x) {
+    const float lnp = g.lnp[k];
+    const float tbc = rs.tau_bc * __expf(rs.alpha_bc * lnp);
+    const float pw = __expf(rs.delta * lnp);
+    const float td = md.dust_law == SED_DUST_POWER_LAW
+                         ? rs.tau_d * pw
+                         : rs.tau_d * (g.kprime[k] + eb * g.drude[k]) * (1.f / 4.05f) * pw;
+    float y = Yr[k];
+    if (md.use_neb) {
+      const float lg = rs.neb_w[0] * g.neb_tab[rs.neb_off[0] + k] + rs.neb_w[1] * g.neb_tab[rs.neb_off[1] + k] +
+                       rs.neb_w[2] * g.neb_tab[rs.neb_off[2] + k] + rs.neb_w[3] * g.neb_tab[rs.neb_off[3] + k];
+      y += exp2f(rs.log2_qy + 3.3219280948873623f * lg);
+    }
+    const float F = __expf(-td) * (__expf(-tbc) * y + Or[k]);
+    Fs[k] = F;
+    Gs[k] = F * g.inv_lam2[k];
+  }
+  __syncthreads();
+
+  // ---- photometry: one warp per band
+  const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
+  for (int b = warp; b < md.n_filt; b += EPI_THREADS / 32) {
+    float acc = 0.f;
+    for (int j = md.band_start[b] + lane; j < md.band_start[b + 1]; j += 32) {
+      const float x = md.samp_lam[j] * rs.inv1pz;
+      float v = 0.f;
+      if (x >= lam0 && x <= lamN) {
+        const int k = locate_lin(g, x);
+        const float la = g.lam_f[k], lb = g.lam_f[k + 1];
+        const float t = (x - la) / (lb - la);
+        v = Gs[k] + t * (Gs[k + 1] - Gs[k]);
+      }
+      acc = fmaf(md.samp_w[j], v, acc);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const float mb = rs.p_phot * acc;
+      if (a.phot_out) a.phot_out[(size_t)r * md.n_filt + b] = mb;
+      double v = 0.0;
+      if (md.phot_isig[b] != 0.0) {
+        const double rr = (md.phot_d[b] - (double)mb) * md.phot_isig[b];
+        v = -0.5 * rr * rr + md.phot_nlog[b];
+      }
+      band_v[b] = v;
+    }
+  }
+
+  // ---- spectrum: one thread per pixel
+  double part = 0.0;
+  const double l1 = (double)rs.ln1pz_hi + (double)rs.ln1pz_lo;
+  const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
+  for (int i = tid; i < md.n_pix; i += blockDim.x) {
+    const double xd = md.pix_ln[i] - l1;
+    const float xh = (float)xd, xl = (float)(xd - (double)xh);
+    float v = 0.f;
+    bool valid = false;
+    if (xh >= ll0 && xh <= llN) {
+      const float s = md.pix_s[i];
+      const int k = locate_ln(g, xh, g.lnl_hi);
+      const float dln = (g.lnl_hi[k + 1] - g.lnl_hi[k]) + (g.lnl_lo[k + 1] - g.lnl_lo[k]);
+      if (s < 0.5f * dln) {
+        const float t = ((xh - g.lnl_hi[k]) + (xl - g.lnl_lo[k])) / dln;
+        v = Fs[k] + t * (Fs[k + 1] - Fs[k]);
+        valid = true;
+      } else {
+        const float inv_s = 1.f / s;
+        const int jlo = locate_ln(g, fmaxf(xh - 5.f * s, ll0), g.lnl_hi);
+        const int jhi = locate_ln(g, fminf(xh + 5.f * s, llN), g.lnl_hi) + 1;
+        float sw = 0.f, sf = 0.f;
+        for (int j = jlo; j <= jhi; ++j) {
+          const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
+          const float u = d * inv_s;
+          if (fabsf(u) <= 5.f) {
+            const float w = __expf(-0.5f * u * u);
+            sw += w;
+            sf = fmaf(w, Fs[j], sf);
+          }
+        }
+        if (sw > 0.f) { v = sf / sw; valid = true; }
+      }
+    }
+    const float mi = rs.s_spec * v;
+    if (a.spec_out) a.spec_out[(size_t)r * md.n_pix + i] = mi;
+    if (valid && md.spec_isig[i] != 0.0) {
+      const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
+      part += -0.5 * rr * rr + md.spec_nlog[i];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int b = 0; b < md.n_filt; ++b) tot += band_v[b];
+    for (int w = 0; w < EPI_THREADS / 32; ++w) tot += red[w];
+    uint32_t st = 0;
+    if (!isfinite(tot)) { st = SED_ROW_NONFINITE; tot = -INFINITY; }
+    if (a.lnl) a.lnl[r] = tot;
+    if (a.status) a.status[r] = st;
+  }
+}
+
+cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)a.g.n_lam * 2 * sizeof(float);
+  static size_t set_for = 0;
+  if (smem > 48 * 1024 && smem > set_for) {
+    cudaError_t e = cudaFuncSetAttribute(k_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    set_for = smem;
+  }
+  k_epilogue<<<a.n, EPI_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sed

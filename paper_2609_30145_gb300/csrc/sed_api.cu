@@ -1,0 +1,899 @@
+// Host side of the C ABI declared in include/sed.h: validation, grid and
+// model set-up (all static precomputation in FP64 on the host), per-stream
+// workspaces and the dispatch of the hot-path kernels.
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "sed_internal.cuh"
+
+using namespace sed;
+
+namespace {
+
+sed_status fail(sed_ctx* ctx, sed_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return st;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(ctx, SED_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DevGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+sed_status dalloc(sed_ctx* ctx, void** p, size_t bytes, std::vector<void*>* owner, size_t* acct) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (ctx->budget && ctx->used + bytes > ctx->budget)
+    return fail(ctx, SED_ENOMEM, "HBM budget exceeded (%zu + %zu > %zu bytes)", ctx->used, bytes, ctx->budget);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, SED_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  if (acct) *acct += bytes;
+  if (owner) owner->push_back(*p);
+  return SED_OK;
+}
+
+template <class T>
+sed_status upload(sed_ctx* ctx, T** dst, const T* src, size_t n, std::vector<void*>* owner, size_t* acct) {
+  sed_status st = dalloc(ctx, (void**)dst, n * sizeof(T), owner, acct);
+  if (st) return st;
+  if (n) CK(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return SED_OK;
+}
+
+void free_all(sed_ctx* ctx, std::vector<void*>& v, size_t& acct) {
+  for (void* p : v) cudaFree(p);
+  v.clear();
+  ctx->used -= std::min(ctx->used, acct);
+  acct = 0;
+}
+
+bool strictly_increasing(const double* x, int n) {
+  for (int i = 0; i < n; i++)
+    if (!std::isfinite(x[i]) || (i && !(x[i] > x[i - 1]))) return false;
+  return true;
+}
+
+float tf32_rna_host(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;
+  u += 0x1000u;
+  u &= 0xffffe000u;
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+
+double calzetti_kprime(double lum) {  // Calzetti et al. 2000, R_V = 4.05, UV branch below 0.63 um
+  double k;
+  if (lum >= 0.63)
+    k = 2.659 * (-1.857 + 1.040 / lum) + 4.05;
+  else
+    k = 2.659 * (-2.156 + 1.509 / lum - 0.198 / (lum * lum) + 0.011 / (lum * lum * lum)) + 4.05;
+  return k > 0.0 ? k : 0.0;
+}
+
+sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, bool grad, sed_status* st);
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* sed_status_string(sed_status s) {
+  switch (s) {
+    case SED_OK: return "ok";
+    case SED_EINVAL: return "invalid argument";
+    case SED_ENOMEM: return "out of device memory or budget";
+    case SED_ECUDA: return "CUDA error";
+    case SED_ERANGE: return "size out of supported range";
+    case SED_ENONFINITE: return "non-finite input";
+    case SED_EBUSY: return "busy";
+    case SED_ETIMEOUT: return "device wait timed out";
+    case SED_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* sed_last_error(const sed_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+sed_status sed_create(sed_ctx** out, int device, size_t budget) {
+  if (!out) return SED_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SED_EINVAL;
+  }
+  sed_ctx* ctx = new sed_ctx();
+  ctx->device = device;
+  ctx->budget = budget;
+  DevGuard dg(device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete ctx;
+    return SED_ECUDA;
+  }
+  ctx->tc_ok = (prop.major == 10 && prop.minor == 3) ? 1 : 0;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    ctx->encode_fn = fn;
+  else
+    ctx->tc_ok = 0;
+  *out = ctx;
+  return SED_OK;
+}
+
+sed_status sed_destroy_model(sed_ctx* ctx, sed_model_id id);
+
+sed_status sed_destroy(sed_ctx* ctx) {
+  if (!ctx) return SED_EINVAL;
+  {
+    DevGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    for (size_t i = 0; i < ctx->models.size(); i++)
+      if (ctx->models[i]) sed_destroy_model(ctx, (sed_model_id)i);
+    for (Grid* g : ctx->grids) {
+      if (!g) continue;
+      for (Layout* L : g->layouts) delete L;
+      free_all(ctx, g->allocs, g->bytes);
+      delete g;
+    }
+    for (auto& kv : ctx->ws) {
+      Workspace* w = kv.second;
+      std::vector<void*> v = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
+                              w->theta_h, w->lnl_h, w->st_h, w->G, w->GO, w->dW, w->rgrad};
+      for (void* p : v)
+        if (p) cudaFree(p);
+      for (cudaEvent_t e : w->ev)
+        if (e) cudaEventDestroy(e);
+      delete w;
+    }
+  }
+  delete ctx;
+  return SED_OK;
+}
+
+sed_status sed_memory_used(const sed_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return SED_EINVAL;
+  *bytes = ctx->used;
+  return SED_OK;
+}
+
+// ---------------------------------------------------------------------------
+sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out) {
+  if (!ctx || !d || !out) return fail(ctx, SED_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DevGuard dg(ctx->device);
+  if (d->n_age < 2 || d->n_feh < 1 || d->n_afe < 1 || d->n_lam < 4)
+    return fail(ctx, SED_EINVAL, "grid needs n_age >= 2, n_feh >= 1, n_afe >= 1, n_lam >= 4");
+  if (d->n_age > MAX_AGE || d->n_feh > MAX_FEH || d->n_afe > MAX_AFE || d->n_lam > MAX_LAM)
+    return fail(ctx, SED_ERANGE, "grid axis too long (max age %d feh %d afe %d lam %d)", MAX_AGE, MAX_FEH, MAX_AFE, MAX_LAM);
+  if (!d->log_age_yr || !d->feh || !d->lam_aa || !d->flux || (d->n_afe > 1 && !d->afe))
+    return fail(ctx, SED_EINVAL, "grid axis or flux pointer is NULL");
+  if (!strictly_increasing(d->log_age_yr, d->n_age) || !strictly_increasing(d->feh, d->n_feh) ||
+      (d->afe && !strictly_increasing(d->afe, d->n_afe)) || !strictly_increasing(d->lam_aa, d->n_lam) ||
+      !(d->lam_aa[0] > 0))
+    return fail(ctx, SED_EINVAL, "grid axes must be finite and strictly increasing (lam > 0)");
+  const size_t nsp = (size_t)d->n_afe * d->n_feh * d->n_age, nl = d->n_lam;
+  double fmax = 0.0;
+  for (size_t i = 0; i < nsp * nl; i++) {
+    double v = d->flux[i];
+    if (!std::isfinite(v) || v < 0.0) return fail(ctx, SED_EINVAL, "flux must be finite and >= 0 (index %zu)", i);
+    fmax = std::max(fmax, v);
+  }
+  if (!(fmax > 0)) return fail(ctx, SED_EINVAL, "flux is identically zero");
+  const bool neb = d->neb_n_logu > 0 && d->neb_n_logz > 0 && d->neb_log10_lnu_per_q;
+  if (neb) {
+    if (d->neb_n_logu > 32 || d->neb_n_logz > 32) return fail(ctx, SED_ERANGE, "nebular axes longer than 32");
+    if (!d->neb_logu || !d->neb_logz || !strictly_increasing(d->neb_logu, d->neb_n_logu) ||
+        !strictly_increasing(d->neb_logz, d->neb_n_logz))
+      return fail(ctx, SED_EINVAL, "nebular axes must be strictly increasing");
+    size_t nt = (size_t)d->neb_n_logu * d->neb_n_logz * nl;
+    for (size_t i = 0; i < nt; i++)
+      if (!std::isfinite(d->neb_log10_lnu_per_q[i])) return fail(ctx, SED_EINVAL, "nebular template not finite");
+  }
+
+  Grid* g = new Grid();
+  g->n_age = d->n_age; g->n_feh = d->n_feh; g->n_afe = d->n_afe; g->n_lam = d->n_lam;
+  g->log_age.assign(d->log_age_yr, d->log_age_yr + d->n_age);
+  g->feh.assign(d->feh, d->feh + d->n_feh);
+  if (d->afe) g->afe.assign(d->afe, d->afe + d->n_afe); else g->afe.assign(1, 0.0);
+  g->lam.assign(d->lam_aa, d->lam_aa + nl);
+  g->flux.assign(d->flux, d->flux + nsp * nl);
+  g->f_log2 = -std::ceil(std::log2(fmax));
+
+  // Eq. app_q: Q = (Lsun/h) int_0^912 f/lam dlam (trapezoid to the last node
+  // below 912 A plus the linearly interpolated piece up to 912 A)
+  g->q.assign(nsp, 0.0);
+  double qmax = 0.0;
+  for (size_t s = 0; s < nsp; s++) {
+    const double* f = d->flux + s * nl;
+    double acc = 0.0;
+    for (size_t k = 0; k + 1 < nl && g->lam[k] < LYMAN_AA; k++) {
+      double x1 = g->lam[k + 1], f1 = f[k + 1];
+      if (x1 > LYMAN_AA) {
+        f1 = f[k] + (f[k + 1] - f[k]) * (LYMAN_AA - g->lam[k]) / (g->lam[k + 1] - g->lam[k]);
+        x1 = LYMAN_AA;
+      }
+      acc += 0.5 * (f[k] / g->lam[k] + f1 / x1) * (x1 - g->lam[k]);
+    }
+    g->q[s] = LSUN / HPLANCK * acc;
+    qmax = std::max(qmax, g->q[s]);
+  }
+  g->q_log2 = qmax > 0 ? std::ceil(std::log2(qmax)) : 0.0;
+
+  // per-node constants
+  std::vector<float> lam_f(nl), inv_lam2(nl), lnp(nl), kp(nl), dr(nl), lh(nl), lo(nl);
+  g->siglib_kms.resize(nl);
+  double hmin = 1e300;
+  for (size_t k = 0; k < nl; k++) {
+    const double L = g->lam[k];
+    lam_f[k] = (float)L;
+    inv_lam2[k] = (float)(1.0 / (L * L));
+    lnp[k] = (float)std::log(L / 5500.0);
+    kp[k] = (float)calzetti_kprime(L * 1e-4);
+    const double x = L * 350.0, dd = L * L - 2175.0 * 2175.0;
+    dr[k] = (float)(x * x / (dd * dd + x * x));
+    const double ll = std::log(L);
+    lh[k] = (float)ll;
+    lo[k] = (float)(ll - (double)lh[k]);
+    double dl = (k == 0) ? g->lam[1] - g->lam[0]
+                         : (k == nl - 1 ? g->lam[nl - 1] - g->lam[nl - 2] : 0.5 * (g->lam[k + 1] - g->lam[k - 1]));
+    double sl = C_KMS / FWHM_PER_SIGMA * 2.0 * dl / L;  // Eq. app_siglib two-pixel floor
+    if (d->sigma_lib_kms && d->sigma_lib_kms[k] > sl) sl = d->sigma_lib_kms[k];
+    g->siglib_kms[k] = sl;
+    if (k + 1 < nl) hmin = std::min(hmin, std::log(g->lam[k + 1]) - ll);
+  }
+  // index LUT over ln(lambda): cells of width h <= smallest log spacing
+  const double x0 = (double)lh[0];
+  const double h = hmin * 0.5;
+  const int lut_n = (int)std::ceil(((double)lh[nl - 1] - x0) / h) + 2;
+  if (lut_n > (1 << 24)) {
+    delete g;
+    return fail(ctx, SED_ERANGE, "wavelength axis too unevenly spaced for the index table");
+  }
+  std::vector<int> lut(lut_n);
+  {
+    size_t k = 0;
+    for (int q = 0; q < lut_n; q++) {
+      const double xq = x0 + q * h;
+      while (k + 1 < nl && (double)lh[k + 1] <= xq) k++;
+      lut[q] = (int)k;
+    }
+  }
+  // linear-time Voronoi cells (App. B step scheme)
+  std::vector<float> clo(d->n_age), chi(d->n_age);
+  for (int a = 0; a < d->n_age; a++) {
+    const double ta = std::pow(10.0, g->log_age[a]);
+    clo[a] = a == 0 ? 0.f : (float)(0.5 * (std::pow(10.0, g->log_age[a - 1]) + ta));
+    chi[a] = a == d->n_age - 1 ? INFINITY : (float)(0.5 * (ta + std::pow(10.0, g->log_age[a + 1])));
+  }
+
+  sed_status st = SED_OK;
+  GridDev& dv = g->dv;
+  dv.n_age = g->n_age; dv.n_feh = g->n_feh; dv.n_afe = g->n_afe; dv.n_lam = g->n_lam;
+  float* p;
+  int* pi;
+#define UPF(field, vec)                                                   \
+  if (!st) { st = upload(ctx, &p, vec.data(), vec.size(), &g->allocs, &g->bytes); dv.field = p; }
+  UPF(lam_f, lam_f) UPF(inv_lam2, inv_lam2) UPF(lnp, lnp) UPF(kprime, kp) UPF(drude, dr)
+  UPF(lnl_hi, lh) UPF(lnl_lo, lo) UPF(cell_lo, clo) UPF(cell_hi, chi)
+#undef UPF
+  if (!st) { st = upload(ctx, &pi, lut.data(), lut.size(), &g->allocs, &g->bytes); dv.lut = pi; }
+  dv.lut_n = lut_n;
+  dv.lut_x0 = (float)x0;
+  dv.lut_inv_h = (float)(1.0 / h);
+  if (neb && !st) {
+    g->neb_nu = d->neb_n_logu; g->neb_nz = d->neb_n_logz;
+    g->neb_logu.assign(d->neb_logu, d->neb_logu + g->neb_nu);
+    g->neb_logz.assign(d->neb_logz, d->neb_logz + g->neb_nz);
+    const size_t nt = (size_t)g->neb_nu * g->neb_nz * nl;
+    std::vector<float> tab(nt);
+    const double off = (g->f_log2 + g->q_log2) * std::log10(2.0);
+    for (size_t i = 0; i < nt; i++) tab[i] = (float)(d->neb_log10_lnu_per_q[i] + off);
+    st = upload(ctx, &p, tab.data(), nt, &g->allocs, &g->bytes);
+    dv.neb_tab = p;
+    dv.neb_nu = g->neb_nu; dv.neb_nz = g->neb_nz;
+  }
+  if (st) {
+    free_all(ctx, g->allocs, g->bytes);
+    delete g;
+    return st;
+  }
+  ctx->grids.push_back(g);
+  *out = (sed_grid_id)(ctx->grids.size() - 1);
+  return SED_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+namespace {
+
+// Layout of the grid for a given number of birth-cloud ages and 912 A removal.
+sed_status get_layout(sed_ctx* ctx, Grid* g, int n_young, int neb_cut, Layout** out) {
+  for (Layout* L : g->layouts)
+    if (L->n_young == n_young && L->neb_cut == neb_cut) { *out = L; return SED_OK; }
+  Layout* L = new Layout();
+  L->n_young = n_young;
+  L->neb_cut = neb_cut;
+  const int NA = g->n_age, NZ = g->n_feh, NAF = g->n_afe, NL = g->n_lam;
+  const int no = NA - n_young;
+  L->Ky = NAF * NZ * n_young;
+  L->Ko = NAF * NZ * no;
+  L->Ky_pad = (L->Ky + KT - 1) / KT * KT;
+  L->Kpad = L->Ky_pad + (L->Ko + KT - 1) / KT * KT;
+  const int Kpad = L->Kpad;
+  std::vector<int> code(Kpad, -1);
+  std::vector<float> qs(Kpad, 0.f);
+  for (int n = 0; n < NAF; n++)
+    for (int m = 0; m < NZ; m++) {
+      for (int a = 0; a < n_young; a++) {
+        int k = (n * NZ + m) * n_young + a;
+        code[k] = (n << 24) | (m << 16) | a;
+        qs[k] = (float)(g->q[((size_t)n * NZ + m) * NA + a] * std::exp2(-g->q_log2));
+      }
+      for (int a = n_young; a < NA; a++) {
+        int k = L->Ky_pad + (n * NZ + m) * no + (a - n_young);
+        code[k] = (n << 24) | (m << 16) | a;
+      }
+    }
+  L->q_log2 = g->q_log2;
+  sed_status st = upload(ctx, &L->k_code, code.data(), Kpad, &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &L->q_s, qs.data(), Kpad, &g->allocs, &g->bytes);
+  // SSP^T [lam][k], scaled by 2^f_log2, in FP32, TF32 hi/lo and BF16
+  const double sc = std::exp2(g->f_log2);
+  std::vector<float> f32((size_t)NL * Kpad), hi((size_t)NL * Kpad), lo((size_t)NL * Kpad);
+  std::vector<__nv_bfloat16> bf((size_t)NL * Kpad);
+  for (int k = 0; k < Kpad; k++) {
+    const int c = code[k];
+    for (int l = 0; l < NL; l++) {
+      float v = 0.f;
+      if (c >= 0) {
+        const int n = c >> 24, m = (c >> 16) & 0xff, a = c & 0xffff;
+        const bool cut = neb_cut && a < n_young && g->lam[l] < LYMAN_AA;
+        if (!cut) v = (float)(g->flux[(((size_t)n * NZ + m) * NA + a) * NL + l] * sc);
+      }
+      const size_t o = (size_t)l * Kpad + k;
+      f32[o] = v;
+      const float h = tf32_rna_host(v);
+      hi[o] = h;
+      lo[o] = v - h;
+      bf[o] = __float2bfloat16_rn(v);
+    }
+  }
+  if (!st) st = upload(ctx, &L->sspT_f32, f32.data(), f32.size(), &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &L->sspT_hi, hi.data(), hi.size(), &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &L->sspT_lo, lo.data(), lo.size(), &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &L->sspT_bf16, bf.data(), bf.size(), &g->allocs, &g->bytes);
+  if (st) {
+    delete L;
+    return st;
+  }
+  g->layouts.push_back(L);
+  *out = L;
+  return SED_OK;
+}
+
+double sigma_inst_kms(int mode, double v, double lam_obs) {  // Eq. app_modes
+  switch (mode) {
+    case SED_LSF_R_FWHM: return C_KMS / (FWHM_PER_SIGMA * v);
+    case SED_LSF_R_SIGMA: return C_KMS / v;
+    case SED_LSF_FWHM_AA: return C_KMS * v / (FWHM_PER_SIGMA * lam_obs);
+    case SED_LSF_SIGMA_AA: return C_KMS * v / lam_obs;
+    case SED_LSF_SIGMA_KMS: return v;
+    default: return v / FWHM_PER_SIGMA;
+  }
+}
+
+// t_univ(z) in yr, closed form for flat LCDM without radiation
+double t_univ_yr(double th_yr, double Om, double z) {
+  const double OL = 1.0 - Om;
+  return th_yr * 2.0 / (3.0 * std::sqrt(OL)) * std::asinh(std::sqrt(OL / Om) * std::pow(1.0 + z, -1.5));
+}
+
+sed_status set_data_dev(sed_ctx* ctx, Model* M, const double* pd, const double* ps, const double* sd,
+                        const double* ss) {
+  ModelDev& dv = M->dv;
+  if (pd || ps) {
+    const int nb = dv.n_filt;
+    std::vector<double> isig(nb), nlog(nb), dd(nb);
+    for (int b = 0; b < nb; b++) {
+      const bool on = M->phot_mask_h.empty() || M->phot_mask_h[b];
+      double s = ps ? ps[b] : 1.0, dv_ = pd ? pd[b] : 0.0;
+      if (on && !(std::isfinite(s) && s > 0 && std::isfinite(dv_)))
+        return fail(ctx, SED_EINVAL, "photometric datum %d: sigma must be > 0 and data finite", b);
+      dd[b] = on ? dv_ : 0.0;
+      isig[b] = on ? 1.0 / s : 0.0;
+      nlog[b] = on ? -0.5 * std::log(2.0 * M_PI * s * s) : 0.0;
+    }
+    if (nb) {
+      CK(cudaMemcpy((void*)dv.phot_d, dd.data(), nb * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy((void*)dv.phot_isig, isig.data(), nb * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy((void*)dv.phot_nlog, nlog.data(), nb * 8, cudaMemcpyHostToDevice));
+    }
+  }
+  if (sd || ss) {
+    const int np = dv.n_pix;
+    std::vector<double> isig(np), nlog(np), dd(np);
+    for (int i = 0; i < np; i++) {
+      const bool on = M->spec_mask_h.empty() || M->spec_mask_h[i];
+      double s = ss ? ss[i] : 1.0, dv_ = sd ? sd[i] : 0.0;
+      if (on && !(std::isfinite(s) && s > 0 && std::isfinite(dv_)))
+        return fail(ctx, SED_EINVAL, "spectral datum %d: sigma must be > 0 and data finite", i);
+      dd[i] = on ? dv_ : 0.0;
+      isig[i] = on ? 1.0 / s : 0.0;
+      nlog[i] = on ? -0.5 * std::log(2.0 * M_PI * s * s) : 0.0;
+    }
+    if (np) {
+      CK(cudaMemcpy((void*)dv.spec_d, dd.data(), np * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy((void*)dv.spec_isig, isig.data(), np * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy((void*)dv.spec_nlog, nlog.data(), np * 8, cudaMemcpyHostToDevice));
+    }
+  }
+  return SED_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id* out) {
+  if (!ctx || !d || !out) return fail(ctx, SED_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DevGuard dg(ctx->device);
+  if (d->grid < 0 || d->grid >= (int)ctx->grids.size() || !ctx->grids[d->grid])
+    return fail(ctx, SED_EINVAL, "unknown grid id %d", d->grid);
+  Grid* g = ctx->grids[d->grid];
+  if (d->n_sfh < 3 || d->n_sfh > MAX_SFH) return fail(ctx, SED_ERANGE, "n_sfh must be in [3, %d]", MAX_SFH);
+  if (!(d->zf > 0 && std::isfinite(d->zf))) return fail(ctx, SED_EINVAL, "zf must be > 0");
+  if (d->zmode != 0 && d->zmode != 1) return fail(ctx, SED_EINVAL, "zmode must be 0 or 1");
+  if (d->dust_law != SED_DUST_POWER_LAW && d->dust_law != SED_DUST_KC13) return fail(ctx, SED_EINVAL, "bad dust_law");
+  if (!(d->H0 > 0) || !(d->Om0 > 0 && d->Om0 < 1)) return fail(ctx, SED_EINVAL, "need H0 > 0 and 0 < Om0 < 1");
+  if (d->use_nebular && g->neb_nu == 0) return fail(ctx, SED_EINVAL, "use_nebular needs a grid with a nebular template");
+  if (d->use_afe && g->n_afe < 2) return fail(ctx, SED_EINVAL, "use_afe needs a grid with an [a/Fe] axis");
+  if (d->n_filt < 0 || d->n_filt > 128) return fail(ctx, SED_ERANGE, "n_filt must be in [0, 128]");
+  if (d->n_pix < 0) return fail(ctx, SED_EINVAL, "n_pix < 0");
+  if (d->n_filt == 0 && d->n_pix == 0) return fail(ctx, SED_EINVAL, "model has no observation");
+  if (!std::isfinite(d->bc_edge_log_age_yr)) return fail(ctx, SED_EINVAL, "bc edge not finite");
+  if (d->n_filt && (!d->filt_len || !d->filt_lam_aa || !d->filt_trans))
+    return fail(ctx, SED_EINVAL, "filter arrays are NULL");
+  if (d->n_pix && (!d->spec_lam_aa || !d->lsf_value)) return fail(ctx, SED_EINVAL, "spectrum arrays are NULL");
+  if (d->n_pix && (d->lsf_mode < 0 || d->lsf_mode > 5)) return fail(ctx, SED_EINVAL, "bad lsf_mode");
+  if (d->n_pix && !(d->sigma_gal_kms >= 0 && d->z_ref >= 0)) return fail(ctx, SED_EINVAL, "sigma_gal, z_ref must be >= 0");
+
+  Model* M = new Model();
+  M->grid = d->grid;
+  M->g = g;
+  M->bc_edge = d->bc_edge_log_age_yr;
+  M->H0 = d->H0;
+  ModelDev& dv = M->dv;
+  memset(&dv, 0, sizeof dv);
+  dv.n_sfh = d->n_sfh; dv.zmode = d->zmode; dv.use_afe = d->use_afe; dv.use_neb = d->use_nebular;
+  dv.dust_law = d->dust_law;
+  const int nz = d->zmode == 0 ? d->n_sfh : 1;
+  int o = 0;
+  dv.offs[SED_KEY_SFH] = o; o += d->n_sfh;
+  dv.offs[SED_KEY_LOGZSOL] = o; o += nz;
+  for (int k = SED_KEY_AFE; k < SED_NKEYS; k++) dv.offs[k] = o++;
+  dv.n_param = o;
+  dv.zf = d->zf;
+  dv.Om0 = d->Om0;
+  dv.dh_cm = C_KMS / d->H0 * 1e6 * PC_CM;
+  dv.th_yr = MPC_KM / d->H0 / YR_S;
+  dv.t_zf_yr = t_univ_yr(dv.th_yr, d->Om0, d->zf);
+  dv.f_log2 = g->f_log2;
+  dv.q_log2 = g->q_log2;
+  dv.n_feh = g->n_feh; dv.n_afe = g->n_afe;
+  for (int i = 0; i < g->n_feh; i++) dv.feh[i] = (float)g->feh[i];
+  for (int i = 0; i < g->n_afe; i++) dv.afe[i] = (float)g->afe[i];
+  dv.neb_nu = g->neb_nu; dv.neb_nz = g->neb_nz;
+  for (int i = 0; i < g->neb_nu; i++) dv.neb_logu[i] = (float)g->neb_logu[i];
+  for (int i = 0; i < g->neb_nz; i++) dv.neb_logz[i] = (float)g->neb_logz[i];
+
+  int n_young = 0;
+  while (n_young < g->n_age && g->log_age[n_young] <= d->bc_edge_log_age_yr) n_young++;
+  sed_status st = get_layout(ctx, g, n_young, d->use_nebular ? 1 : 0, &M->L);
+
+  // ---- photometry: App. D weights R lam dlam / Z_b, band-major samples
+  if (!st && d->n_filt) {
+    dv.n_filt = d->n_filt;
+    std::vector<int> bs(d->n_filt + 1, 0);
+    for (int b = 0; b < d->n_filt; b++) {
+      if (d->filt_len[b] < 2) { st = fail(ctx, SED_EINVAL, "filter %d has < 2 samples", b); break; }
+      bs[b + 1] = bs[b] + d->filt_len[b];
+    }
+    const int S = st ? 0 : bs[d->n_filt];
+    std::vector<float> sl(S), sw(S);
+    double lmin = 1e300, lmax = 0;
+    for (int b = 0; !st && b < d->n_filt; b++) {
+      const double* L = d->filt_lam_aa + bs[b];
+      const double* R = d->filt_trans + bs[b];
+      const int n = d->filt_len[b];
+      if (!strictly_increasing(L, n) || !(L[0] > 0)) { st = fail(ctx, SED_EINVAL, "filter %d wavelengths", b); break; }
+      double zb = 0.0;
+      for (int j = 0; j < n; j++)
+        if (!std::isfinite(R[j]) || R[j] < 0) { st = fail(ctx, SED_EINVAL, "filter %d transmission", b); break; }
+      for (int j = 0; j + 1 < n; j++) {
+        const double g0 = L[j] * R[j] * C_AA * AB_FNU / (L[j] * L[j]);
+        const double g1 = L[j + 1] * R[j + 1] * C_AA * AB_FNU / (L[j + 1] * L[j + 1]);
+        zb += 0.5 * (g0 + g1) * (L[j + 1] - L[j]);
+      }
+      if (!st && !(zb > 0)) st = fail(ctx, SED_EINVAL, "filter %d has zero throughput", b);
+      for (int j = 0; !st && j < n; j++) {
+        const double dl = j == 0 ? 0.5 * (L[1] - L[0])
+                                 : (j == n - 1 ? 0.5 * (L[n - 1] - L[n - 2]) : 0.5 * (L[j + 1] - L[j - 1]));
+        sl[bs[b] + j] = (float)L[j];
+        sw[bs[b] + j] = (float)(R[j] * L[j] * dl / zb);
+        lmin = std::min(lmin, L[j]);
+        lmax = std::max(lmax, L[j]);
+      }
+    }
+    dv.n_samp = S;
+    dv.samp_lam_min = (float)lmin;
+    dv.samp_lam_max = (float)lmax;
+    int* pi;
+    float* pf;
+    double* pd;
+    if (!st) { st = upload(ctx, &pi, bs.data(), bs.size(), &M->allocs, &M->bytes); dv.band_start = pi; }
+    if (!st) { st = upload(ctx, &pf, sl.data(), sl.size(), &M->allocs, &M->bytes); dv.samp_lam = pf; }
+    if (!st) { st = upload(ctx, &pf, sw.data(), sw.size(), &M->allocs, &M->bytes); dv.samp_w = pf; }
+    std::vector<double> zeros(d->n_filt, 0.0);
+    if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_d = pd; }
+    if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_isig = pd; }
+    if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_nlog = pd; }
+    if (d->phot_mask) M->phot_mask_h.assign(d->phot_mask, d->phot_mask + d->n_filt);
+  }
+  // ---- spectrum: per-pixel dispersion, Eq. app_sigeff + fixed sigma_gal (Eq. one_kernel)
+  if (!st && d->n_pix) {
+    const int np = d->n_pix;
+    dv.n_pix = np;
+    if (!strictly_increasing(d->spec_lam_aa, np) || !(d->spec_lam_aa[0] > 0))
+      st = fail(ctx, SED_EINVAL, "spectrum wavelengths must be strictly increasing and > 0");
+    std::vector<double> pl(np);
+    std::vector<float> ps(np);
+    double smax = 0;
+    for (int i = 0; !st && i < np; i++) {
+      const double lo_ = d->spec_lam_aa[i];
+      if (!(d->lsf_value[i] > 0 && std::isfinite(d->lsf_value[i]))) { st = fail(ctx, SED_EINVAL, "lsf_value[%d] must be > 0", i); break; }
+      const double si = sigma_inst_kms(d->lsf_mode, d->lsf_value[i], lo_);
+      const double lr = lo_ / (1.0 + d->z_ref);
+      double slib;
+      const auto& L = g->lam;
+      if (lr <= L[0]) slib = g->siglib_kms[0];
+      else if (lr >= L.back()) slib = g->siglib_kms.back();
+      else {
+        size_t k = std::upper_bound(L.begin(), L.end(), lr) - L.begin() - 1;
+        slib = g->siglib_kms[k] + (g->siglib_kms[k + 1] - g->siglib_kms[k]) * (lr - L[k]) / (L[k + 1] - L[k]);
+      }
+      double fix2 = si * si - slib * slib;
+      if (fix2 < 0) fix2 = 0;
+      const double s = std::sqrt(fix2 + d->sigma_gal_kms * d->sigma_gal_kms) / C_KMS;
+      pl[i] = std::log(lo_);
+      ps[i] = (float)s;
+      smax = std::max(smax, s);
+    }
+    dv.pix_ln_min = pl.empty() ? 0 : pl.front();
+    dv.pix_ln_max = pl.empty() ? 0 : pl.back();
+    dv.pix_s_max = (float)smax;
+    double* pd;
+    float* pf;
+    if (!st) { st = upload(ctx, &pd, pl.data(), pl.size(), &M->allocs, &M->bytes); dv.pix_ln = pd; }
+    if (!st) { st = upload(ctx, &pf, ps.data(), ps.size(), &M->allocs, &M->bytes); dv.pix_s = pf; }
+    std::vector<double> zeros(np, 0.0);
+    if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_d = pd; }
+    if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_isig = pd; }
+    if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_nlog = pd; }
+    if (d->spec_mask) M->spec_mask_h.assign(d->spec_mask, d->spec_mask + np);
+  }
+  if (!st && (d->phot_d || d->phot_sigma || d->spec_d || d->spec_sigma))
+    st = set_data_dev(ctx, M, d->phot_d, d->phot_sigma, d->spec_d, d->spec_sigma);
+  if (st) {
+    free_all(ctx, M->allocs, M->bytes);
+    delete M;
+    return st;
+  }
+  ctx->models.push_back(M);
+  *out = (sed_model_id)(ctx->models.size() - 1);
+  return SED_OK;
+}
+
+static Model* find_model(const sed_ctx* ctx, sed_model_id id) {
+  if (!ctx || id < 0 || id >= (int)ctx->models.size()) return nullptr;
+  return ctx->models[id];
+}
+
+sed_status sed_model_layout(const sed_ctx* ctx, sed_model_id id, int* n_param, int* offsets) {
+  Model* M = find_model(ctx, id);
+  if (!M) return SED_EINVAL;
+  if (n_param) *n_param = M->dv.n_param;
+  if (offsets)
+    for (int k = 0; k < SED_NKEYS; k++) offsets[k] = M->dv.offs[k];
+  return SED_OK;
+}
+
+sed_status sed_set_data(sed_ctx* ctx, sed_model_id id, const double* pd, const double* ps, const double* sd,
+                        const double* ss) {
+  if (!ctx) return SED_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  DevGuard dg(ctx->device);
+  Model* M = find_model(ctx, id);
+  if (!M) return fail(ctx, SED_EINVAL, "unknown model id %d", id);
+  if ((pd == nullptr) != (ps == nullptr) || (sd == nullptr) != (ss == nullptr))
+    return fail(ctx, SED_EINVAL, "data and sigma must be given together");
+  return set_data_dev(ctx, M, pd, ps, sd, ss);
+}
+
+sed_status sed_destroy_model(sed_ctx* ctx, sed_model_id id) {
+  Model* M = find_model(ctx, id);
+  if (!M) return fail(ctx, SED_EINVAL, "unknown model id %d", id);
+  DevGuard dg(ctx->device);
+  cudaDeviceSynchronize();
+  free_all(ctx, M->allocs, M->bytes);
+  delete M;
+  ctx->models[id] = nullptr;
+  return SED_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+namespace {
+
+sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, bool grad, sed_status* st) {
+  *st = SED_OK;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  Workspace*& w = ctx->ws[stream];
+  if (!w) w = new Workspace();
+  const bool need = rows > w->cap_rows || (size_t)kpad > w->cap_k || (size_t)ldn > w->cap_n || (grad && !w->dW);
+  if (!need) return w;
+  // grow: free and reallocate everything (the stream's previous work must finish first)
+  cudaStreamSynchronize((cudaStream_t)stream);
+  std::vector<void*> old = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
+                            w->theta_h, w->lnl_h, w->st_h, w->G, w->GO, w->dW, w->rgrad};
+  for (void* p : old)
+    if (p) cudaFree(p);
+  ctx->used -= std::min(ctx->used, w->bytes);
+  const bool had_grad = w->dW != nullptr;
+  *w = Workspace();
+  const int R = std::max(rows, 1);
+  const size_t K = std::max<size_t>(kpad, 1), N = std::max<size_t>(ldn, 1);
+  w->cap_rows = R;
+  w->cap_k = K;
+  w->cap_n = N;
+  w->ldn = (int)N;
+  std::vector<void*>* no = nullptr;
+  sed_status s = SED_OK;
+#define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
+  AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2);
+  AL(Y, R * N * 4); AL(O, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
+  AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
+  if (grad || had_grad) { AL(G, R * N * 4); AL(GO, R * N * 4); AL(dW, R * K * 4); AL(rgrad, R * 64 * 4); }
+#undef AL
+  if (!s) {
+    cudaError_t e = cudaMemset(w->err, 0, 64);
+    if (e != cudaSuccess) s = fail(ctx, SED_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  }
+  *st = s;
+  return s ? nullptr : w;
+}
+
+sed_status check_hot_args(sed_ctx* ctx, Model* M, const float* theta, int n, int ld, int precision) {
+  if (!M) return fail(ctx, SED_EINVAL, "unknown model");
+  if (n < 0) return fail(ctx, SED_EINVAL, "n < 0");
+  if (n > 0 && !theta) return fail(ctx, SED_EINVAL, "theta is NULL");
+  if (ld < M->dv.n_param) return fail(ctx, SED_EINVAL, "ld (%d) < n_param (%d)", ld, M->dv.n_param);
+  if (precision != SED_PREC_FP32 && precision != SED_PREC_FP32_SIMT && precision != SED_PREC_BF16)
+    return fail(ctx, SED_EINVAL, "unknown precision %d", precision);
+  if (n > (1 << 22)) return fail(ctx, SED_ERANGE, "batch larger than 4M rows");
+  return SED_OK;
+}
+
+sed_status prof_mark(sed_ctx* ctx, Workspace* w, int i, cudaStream_t s) {
+  if (!ctx->profiling) return SED_OK;
+  if (!w->ev[i]) CK(cudaEventCreate(&w->ev[i]));
+  CK(cudaEventRecord(w->ev[i], s));
+  return SED_OK;
+}
+
+// prep + contraction into ws->Y / ws->O
+sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* theta, int n, int ld,
+                            int precision, cudaStream_t s) {
+  Grid* g = M->g;
+  Layout* L = M->L;
+  if (ctx->profiling) {
+    w->last_n = n; w->last_prec = precision; w->last_kpad = L->Kpad; w->last_nlam = g->n_lam;
+    w->have_stats = true;
+  }
+  if (sed_status ps = prof_mark(ctx, w, 0, s)) return ps;
+  PrepArgs pa{};
+  pa.theta = theta; pa.n = n; pa.ld = ld;
+  pa.md = M->dv; pa.g = g->dv; pa.L = L->dv();
+  pa.W = w->W;
+  pa.W_hi = precision == SED_PREC_FP32 ? w->W_hi : nullptr;
+  pa.W_lo = precision == SED_PREC_FP32 ? w->W_lo : nullptr;
+  pa.W_bf16 = precision == SED_PREC_BF16 ? w->W_bf16 : nullptr;
+  pa.rs = w->rs;
+  pa.err = w->err;
+  CK(launch_prep(pa, s));
+  if (sed_status ps = prof_mark(ctx, w, 1, s)) return ps;
+  if (precision == SED_PREC_FP32_SIMT) {
+    ContractArgs ca{};
+    ca.n = n; ca.n_lam = g->n_lam; ca.ldn = w->ldn; ca.Ky_pad = L->Ky_pad; ca.Kpad = L->Kpad;
+    ca.W = w->W; ca.sspT = L->sspT_f32; ca.Y = w->Y; ca.O = w->O;
+    CK(launch_contract_simt(ca, s));
+    return prof_mark(ctx, w, 2, s);
+  }
+  if (ctx->tc_ok != 1)
+    return fail(ctx, SED_EUNSUPPORTED, "tensor-core precisions need an sm_103 device and cuTensorMapEncodeTiled");
+  const bool f32 = precision == SED_PREC_FP32;
+  TcMaps* maps = &w->maps;
+  const void* key = f32 ? (const void*)L->sspT_hi : (const void*)L->sspT_bf16;
+  if (!w->tmap_valid || w->tmap_for != key || w->tmap_n != n || w->tmap_prec != precision) {
+    int e = tc_encode_maps(ctx->encode_fn, maps, precision, f32 ? (void*)w->W_hi : (void*)w->W_bf16, w->W_lo,
+                           f32 ? (void*)L->sspT_hi : (void*)L->sspT_bf16, L->sspT_lo, n, g->n_lam, L->Kpad);
+    if (e) return fail(ctx, SED_ECUDA, "cuTensorMapEncodeTiled failed (operand %d)", e);
+    w->tmap_valid = true;
+    w->tmap_for = key;
+    w->tmap_n = n;
+    w->tmap_prec = precision;
+  }
+  TcArgs ta{};
+  ta.n = n; ta.n_lam = g->n_lam; ta.ldn = w->ldn; ta.Ky_pad = L->Ky_pad; ta.Kpad = L->Kpad; ta.prec = precision;
+  ta.maps = maps; ta.Y = w->Y; ta.O = w->O; ta.err = w->err;
+  CK(launch_contract_tc(ta, s));
+  return prof_mark(ctx, w, 2, s);
+}
+
+int ldn_for(const Grid* g) { return (g->n_lam + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" {
+
+sed_status sed_forward(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, float* phot_out,
+                       float* spec_out, int precision, void* stream) {
+  if (!ctx) return SED_EINVAL;
+  Model* M = find_model(ctx, id);
+  sed_status st = check_hot_args(ctx, M, theta, n, ld, precision);
+  if (st) return st;
+  if (n == 0) return SED_OK;
+  DevGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
+  if (!w) return st;
+  st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
+  if (st) return st;
+  EpiArgs ea{};
+  ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
+  ea.md = M->dv; ea.g = M->g->dv;
+  ea.phot_out = M->dv.n_filt ? phot_out : nullptr;
+  ea.spec_out = M->dv.n_pix ? spec_out : nullptr;
+  ea.lnl = nullptr; ea.status = nullptr; ea.err = w->err;
+  CK(launch_epilogue(ea, s));
+  return prof_mark(ctx, w, 3, s);
+}
+
+sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
+                       uint32_t* row_status, int precision, void* stream) {
+  if (!ctx) return SED_EINVAL;
+  Model* M = find_model(ctx, id);
+  sed_status st = check_hot_args(ctx, M, theta, n, ld, precision);
+  if (st) return st;
+  if (n > 0 && !lnl_out) return fail(ctx, SED_EINVAL, "lnl_out is NULL");
+  if (n == 0) return SED_OK;
+  DevGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
+  if (!w) return st;
+  st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
+  if (st) return st;
+  EpiArgs ea{};
+  ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
+  ea.md = M->dv; ea.g = M->g->dv;
+  ea.lnl = lnl_out; ea.status = row_status; ea.err = w->err;
+  CK(launch_epilogue(ea, s));
+  return prof_mark(ctx, w, 3, s);
+}
+
+sed_status sed_loglike_host(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
+                            uint32_t* row_status, int precision, void* stream) {
+  if (!ctx) return SED_EINVAL;
+  Model* M = find_model(ctx, id);
+  sed_status st = check_hot_args(ctx, M, theta, n, ld, precision);
+  if (st) return st;
+  if (n > 0 && !lnl_out) return fail(ctx, SED_EINVAL, "lnl_out is NULL");
+  if (ld > 1024) return fail(ctx, SED_ERANGE, "host path supports ld <= 1024");
+  if (n == 0) return SED_OK;
+  DevGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
+  if (!w) return st;
+  CK(cudaMemcpyAsync(w->theta_h, theta, (size_t)n * ld * 4, cudaMemcpyHostToDevice, s));
+  st = sed_loglike(ctx, id, w->theta_h, n, ld, w->lnl_h, w->st_h, precision, stream);
+  if (st) return st;
+  CK(cudaMemcpyAsync(lnl_out, w->lnl_h, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  if (row_status) CK(cudaMemcpyAsync(row_status, w->st_h, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return SED_OK;
+}
+
+sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
+                            float* grad_out, uint32_t* row_status, int precision, void* stream) {
+  (void)theta; (void)n; (void)ld; (void)lnl_out; (void)grad_out; (void)row_status; (void)precision; (void)stream;
+  if (!ctx) return SED_EINVAL;
+  if (!find_model(ctx, id)) return fail(ctx, SED_EINVAL, "unknown model");
+  return fail(ctx, SED_EUNSUPPORTED, "gradient not available in this build");
+}
+
+sed_status sed_set_profiling(sed_ctx* ctx, int on) {
+  if (!ctx) return SED_EINVAL;
+  ctx->profiling = on ? 1 : 0;
+  return SED_OK;
+}
+
+sed_status sed_last_stats(sed_ctx* ctx, void* stream, sed_stage_stats* out) {
+  if (!ctx || !out) return fail(ctx, SED_EINVAL, "null argument");
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->ws.find(stream);
+    if (it != ctx->ws.end()) w = it->second;
+  }
+  if (!w || !w->have_stats || !w->ev[3]) return fail(ctx, SED_EINVAL, "no profiled call on this stream");
+  DevGuard dg(ctx->device);
+  CK(cudaEventSynchronize(w->ev[3]));
+  memset(out, 0, sizeof *out);
+  CK(cudaEventElapsedTime(&out->ms_prep, w->ev[0], w->ev[1]));
+  CK(cudaEventElapsedTime(&out->ms_contract, w->ev[1], w->ev[2]));
+  CK(cudaEventElapsedTime(&out->ms_epilogue, w->ev[2], w->ev[3]));
+  std::vector<RowScal> rs(w->last_n);
+  CK(cudaMemcpy(rs.data(), w->rs, rs.size() * sizeof(RowScal), cudaMemcpyDeviceToHost));
+  double nnz = 0;
+  for (const RowScal& r : rs) nnz += r.nnz;
+  out->nnz_w = nnz;
+  out->dense_k = w->last_kpad;
+  out->n_rows = w->last_n;
+  out->n_lam = w->last_nlam;
+  out->ldn = w->ldn;
+  out->precision = w->last_prec;
+  return SED_OK;
+}
+
+}  // extern "C"

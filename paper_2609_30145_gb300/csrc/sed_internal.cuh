@@ -1,0 +1,260 @@
+// Internal declarations of the GB300 SED library (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sed.h"
+
+namespace sed {
+
+// ---------------------------------------------------------------------------
+// Tiling constants of the contraction.
+// K is tiled in 32 FP32 / 64 BF16 elements (128 bytes, one 128B-swizzle row).
+constexpr int KT = 64;           // K granule of the layouts: one 128-byte BF16 row, two FP32 rows
+constexpr int MAX_AGE = 256;
+constexpr int MAX_FEH = 64;
+constexpr int MAX_AFE = 16;
+constexpr int MAX_SFH = 512;
+constexpr int MAX_LAM = 24576;   // rest-frame nodes an epilogue row can stage in shared memory
+constexpr int GL_NODES = 32;     // Gauss-Legendre nodes of the comoving-distance integral
+
+// Physical constants (cgs unless noted).
+constexpr double LSUN = 3.839e33;              // erg/s (Sec. 2.6)
+constexpr double HPLANCK = 6.62607015e-27;     // erg s
+constexpr double C_AA = 2.99792458e18;         // Angstrom/s
+constexpr double C_KMS = 299792.458;
+constexpr double AB_FNU = 3.631e-20;           // erg/s/cm^2/Hz (App. D)
+constexpr double PC_CM = 3.0856775814913673e18;
+constexpr double MPC_KM = 3.0856775814913673e19;
+constexpr double YR_S = 3.15576e7;
+constexpr double LYMAN_AA = 912.0;
+constexpr double FWHM_PER_SIGMA = 2.3548200450309493;
+
+// ---------------------------------------------------------------------------
+// Per-row scalars produced by the preparation kernel and read by the epilogue
+// and the adjoint kernels.
+struct RowScal {
+  float p_phot;     // c * s * 2^-E / (1+z)^2 : maggie prefactor of sum_j w_j lerp(F/lam^2)
+  float s_spec;     // s * 2^-E : cgs F_nu per unit of device-scaled flux
+  float inv1pz;     // 1/(1+z)
+  float ln1pz_hi;   // ln(1+z) split in two floats
+  float ln1pz_lo;
+  float tau_bc, alpha_bc, tau_d, delta;
+  float log2_qy;    // log2(Q_young, device units) (-inf when Q_young = 0)
+  float neb_w[4];   // bilinear weights of the nebular template corners
+  int neb_off[4];   // corner offsets (rows of the template)
+  float dlnp_dz;    // d ln(p_phot)/dz (adjoint)
+  float dlns_dz;    // d ln(s_spec)/dz (adjoint)
+  float dtmax_dz;   // dT_max/dz in yr (adjoint)
+  float tmax;       // yr
+  uint32_t status;
+  int k_lo, k_hi;   // rest-frame node window this row needs
+  int nnz;          // non-zero weights of the row
+};
+
+// ---------------------------------------------------------------------------
+// Kernel-parameter views (plain data, device pointers only).
+struct GridDev {
+  int n_age, n_feh, n_afe, n_lam;
+  const float* lam_f;      // lambda (A)
+  const float* inv_lam2;   // 1/lambda^2
+  const float* lnp;        // ln(lambda/5500)
+  const float* kprime;     // Calzetti k'(lambda), R_V = 4.05, clamped >= 0
+  const float* drude;      // Drude profile with E_b = 1
+  const float* lnl_hi;     // ln(lambda) split in two floats
+  const float* lnl_lo;
+  const int* lut;          // lut[q] = last node with ln(lambda) <= x0 + q/inv_h
+  int lut_n;
+  float lut_x0, lut_inv_h;
+  const float* cell_lo;    // linear-time Voronoi cell of each age node (yr)
+  const float* cell_hi;
+  const float* neb_tab;    // [nu][nz][n_lam] log10 template + device-unit offset
+  int neb_nu, neb_nz;
+};
+
+struct LayoutDev {
+  int n_young, neb_cut, Ky, Ko, Ky_pad, Kpad;
+  const float* q_s;        // [Kpad]
+  const int* k_code;       // [Kpad]
+};
+
+struct ModelDev {
+  int n_sfh, zmode, use_afe, use_neb, dust_law, n_param;
+  int offs[SED_NKEYS];
+  double zf, t_zf_yr, dh_cm, th_yr, Om0;
+  double f_log2, q_log2;
+  int n_feh, n_afe;
+  float feh[MAX_FEH];
+  float afe[MAX_AFE];
+  int neb_nu, neb_nz;
+  float neb_logu[32], neb_logz[32];
+  // photometry (samples band-major)
+  int n_filt, n_samp;
+  const int* band_start;   // [n_filt + 1]
+  const float* samp_lam;   // [n_samp] observed-frame A
+  const float* samp_w;     // [n_samp] R lam dlam / Z_b
+  const double* phot_d;    // [n_filt]
+  const double* phot_isig; // [n_filt] 1/sigma (0 when masked out)
+  const double* phot_nlog; // [n_filt] -1/2 ln(2 pi sigma^2) (0 when masked out)
+  float samp_lam_min, samp_lam_max;
+  // spectrum
+  int n_pix;
+  const double* pix_ln;    // [n_pix] ln(lambda_obs)
+  const float* pix_s;      // [n_pix] total dispersion in ln(lambda)
+  const double* spec_d;
+  const double* spec_isig;
+  const double* spec_nlog;
+  double pix_ln_min, pix_ln_max;
+  float pix_s_max;
+};
+
+// ---------------------------------------------------------------------------
+// Device copy of a grid in one K order: [young block | old block], each block
+// ordered (afe n, feh m, age a) with age fastest, each block padded to KT.
+struct Layout {
+  int n_young = 0;    // ages <= birth-cloud edge
+  int neb_cut = 0;    // 1: stellar flux below 912 A removed for young ages
+  int Ky = 0, Ko = 0, Ky_pad = 0, Kpad = 0;
+  float* sspT_f32 = nullptr;         // [n_lam][Kpad] scaled flux, exact FP32
+  float* sspT_hi = nullptr;          // [n_lam][Kpad] TF32-rounded high part
+  float* sspT_lo = nullptr;          // [n_lam][Kpad] low part (x - hi)
+  __nv_bfloat16* sspT_bf16 = nullptr;
+  float* q_s = nullptr;              // [Kpad] scaled Q for young k, 0 elsewhere
+  int* k_code = nullptr;             // [Kpad] packed (n<<24 | m<<16 | a), -1 for padding
+  double q_log2 = 0.0;               // Q_dev = Q * 2^-q_log2
+  bool have_tmaps = false;
+  CUtensorMap tm_hi, tm_lo, tm_bf16;
+  LayoutDev dv() const { return LayoutDev{n_young, neb_cut, Ky, Ko, Ky_pad, Kpad, q_s, k_code}; }
+};
+
+struct Grid {
+  int n_age = 0, n_feh = 0, n_afe = 0, n_lam = 0;
+  std::vector<double> log_age, feh, afe, lam, flux;  // host master copy (FP64)
+  std::vector<double> siglib_kms;                    // Eq. app_siglib at the nodes
+  double f_log2 = 0.0;                               // f_dev = f * 2^f_log2
+  double q_log2 = 0.0;                               // Q_dev = Q * 2^-q_log2
+  std::vector<double> q;                             // [n_afe][n_feh][n_age] Eq. app_q
+  GridDev dv{};
+  int neb_nu = 0, neb_nz = 0;
+  std::vector<double> neb_logu, neb_logz;
+  std::vector<Layout*> layouts;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+};
+
+struct Model {
+  int grid = -1;
+  Grid* g = nullptr;
+  Layout* L = nullptr;
+  ModelDev dv{};
+  double bc_edge = 7.03, H0 = 0;
+  std::vector<uint8_t> phot_mask_h, spec_mask_h;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+};
+
+// Operand tensor maps of one tensor-core contraction.
+struct TcMaps {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+// Per-stream scratch.
+struct Workspace {
+  int cap_rows = 0;
+  size_t cap_k = 0, cap_n = 0;
+  float* W = nullptr;            // [rows][Kpad]  exact FP32 weights (also the TF32 hi part source)
+  float* W_hi = nullptr;         // [rows][Kpad]
+  float* W_lo = nullptr;
+  __nv_bfloat16* W_bf16 = nullptr;
+  float* Y = nullptr;            // [rows][ldn]
+  float* O = nullptr;
+  RowScal* rs = nullptr;
+  int* err = nullptr;            // device error word of bounded waits
+  float* theta_h = nullptr;      // host-path staging (device)
+  double* lnl_h = nullptr;
+  uint32_t* st_h = nullptr;
+  int ldn = 0;
+  // adjoint
+  float* G = nullptr;            // [rows][ldn] dlnL/dY (young) then dlnL/dO
+  float* GO = nullptr;
+  float* dW = nullptr;           // [rows][Kpad]
+  float* rgrad = nullptr;        // [rows][16] per-row scalar gradient pieces
+  size_t bytes = 0;
+  bool tmap_valid = false;
+  const void* tmap_for = nullptr;
+  int tmap_n = -1, tmap_prec = -1;
+  TcMaps maps;
+  // profiling: events before/after prep, contraction, epilogue of the last call
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int last_n = 0, last_prec = 0, last_kpad = 0, last_nlam = 0;
+  bool have_stats = false;
+};
+
+}  // namespace sed
+
+struct sed_ctx {
+  int device = 0;
+  size_t budget = 0, used = 0;
+  std::mutex mu;
+  std::string last_error = "ok";
+  std::vector<sed::Grid*> grids;
+  std::vector<sed::Model*> models;
+  std::map<void*, sed::Workspace*> ws;
+  void* encode_fn = nullptr;   // cuTensorMapEncodeTiled
+  int profiling = 0;
+  int tc_ok = -1;              // tcgen05 path usable on this device (sm_103)
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files).
+namespace sed {
+
+struct PrepArgs {
+  const float* theta; int n, ld;
+  ModelDev md; GridDev g; LayoutDev L;
+  float* W; float* W_hi; float* W_lo; __nv_bfloat16* W_bf16;
+  RowScal* rs;
+  int* err;            // device error word of the contraction, cleared by the prep kernel
+};
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+
+struct ContractArgs {
+  int n;               // rows (theta)
+  int n_lam, ldn;
+  int Ky_pad, Kpad;
+  const float* W;      // [n][Kpad]
+  const float* sspT;   // [n_lam][Kpad]
+  float* Y; float* O;  // [n][ldn]
+};
+cudaError_t launch_contract_simt(const ContractArgs& a, cudaStream_t s);
+
+struct TcArgs {
+  int n, n_lam, ldn, Ky_pad, Kpad, prec;   // prec: SED_PREC_FP32 or SED_PREC_BF16
+  const TcMaps* maps;
+  float* Y; float* O; int* err;
+};
+// encodes the four operand maps; returns 0 on success
+int tc_encode_maps(void* encode_fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo,
+                   const void* b_hi, const void* b_lo, int n, int n_lam, int kpad);
+cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s);
+
+struct EpiArgs {
+  int n; int ldn;
+  const float* Y; const float* O;
+  const RowScal* rs;
+  ModelDev md; GridDev g;
+  float* phot_out; float* spec_out;
+  double* lnl; uint32_t* status;
+  const int* err;      // device error word of the contraction (row status SED_ROW_DEVICE_TIMEOUT)
+};
+cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
+
+}  // namespace sed

@@ -58,7 +58,7 @@ def make_grid(n_age=16, log_age=(6.0, 10.1), feh=(-2.0, 0.2), n_feh=4,
               seed=1) -> Grid:
     """Blackbody-like SSP spectra with lognormal amplitudes and absorption dips.
 
-    f = 1e-14 * A_am * B_nu(lam; T_am) / max * prod_k (1 - d_k exp(-((lam-lam_k)/w_k)^2/2))
+    f = 1e-11 * A_am * B_nu(lam; T_am) / max * prod_k (1 - d_k exp(-((lam-lam_k)/w_k)^2/2))
     with T_am = 3e4 K * 10^(-0.35 (log age - 6)) * (1 + 0.05 [Fe/H]) * (1 - 0.03 [a/Fe]),
     log10 A spanning 0 .. -6 from the youngest to the oldest age plus 0.1 dex
     scatter, d_k in [0.05, 0.2], w_k in [5, 50] Angstrom, six dips per spectrum.
@@ -94,7 +94,7 @@ def make_grid(n_age=16, log_age=(6.0, 10.1), feh=(-2.0, 0.2), n_feh=4,
                     depth = (0.05 + 0.15 * dip_d[n, m, a, k]) * (1 + 0.5 * afe_v[n])
                     w = 5.0 + 45.0 * dip_w[n, m, a, k]
                     shape *= 1.0 - depth * np.exp(-0.5 * ((lam - lc) / w) ** 2)
-                flux[n, m, a] = 1e-14 * 10 ** logA * shape
+                flux[n, m, a] = 1e-11 * 10 ** logA * shape
     g = Grid(log_age_yr=log_age_yr, feh=feh_v, afe=afe_v, lam_aa=lam, flux=flux)
     if nebular is not None:
         g.neb_logu, g.neb_logz, g.neb_tab = make_nebular(lam, seed=nebular.get("seed", 2),

@@ -44,3 +44,33 @@ def theta_dict(w: synth.Workload, n, seed=4):
 
 def theta_rows(w: synth.Workload, n, seed=4):
     return oracle.pack_theta(theta_dict(w, n, seed), w.n_sfh, w.zmode)
+
+
+def gpu_model_for(ctx, orc, w: synth.Workload):
+    """A library model with exactly the oracle's inputs (grid loaded once per grid object)."""
+    cache = ctx.__dict__.setdefault("_grid_ids", {})
+    key = id(orc.grid)
+    if key not in cache:
+        cache[key] = (ctx.load_grid(orc.grid), orc.grid)
+    gid = cache[key][0]
+    kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law,
+              bc_edge_log_age_yr=orc.bc_edge_log_age_yr, H0=orc.H0, Om0=orc.Om0,
+              filters=orc.filters, phot_d=orc.phot_d, phot_sigma=orc.phot_sigma,
+              phot_mask=orc.phot_mask)
+    if orc.spec_lam is not None:
+        kw.update(spec_lam=orc.spec_lam, spec_d=orc.spec_d, spec_sigma=orc.spec_sigma,
+                  spec_mask=orc.spec_mask, lsf_mode=orc.lsf_mode, lsf_value=orc.lsf_value,
+                  sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref)
+    return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)
+
+
+def theta_pair(w: synth.Workload, n, seed=4):
+    """Parameter rows rounded to FP32 (library input) and the same values in FP64 (oracle input)."""
+    th32 = theta_rows(w, n, seed).astype(np.float32)
+    return th32, th32.astype(np.float64)
+
+
+def rel_err(a, b, floor=0.0):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b) / np.maximum(np.abs(b), floor)
