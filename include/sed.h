@@ -205,6 +205,34 @@ sed_status sed_loglike_host(sed_ctx *ctx, sed_model_id model, const float *theta
                             double *lnl_out, uint32_t *row_status, int precision, void *stream);
 
 /*
+ * sed_loglike without any device allocation by the library.  (An addition of
+ * this library; the paper has no counterpart.)
+ *
+ * For callers that cannot let the library call cudaMalloc during a call: a
+ * host framework whose own allocator already owns the GPU's memory, a
+ * sampler loop that cannot absorb the device synchronisation a cudaMalloc
+ * may cause, or a deployment that must fix the library's device footprint
+ * when it is loaded.  Same arguments, results and row-status semantics as
+ * sed_loglike (device pointers, asynchronous on `stream`), but every
+ * intermediate buffer comes from one fixed array of SED_NOALLOC_SCRATCH_BYTES
+ * in device global memory that each device loading the library holds until
+ * the process exits; no cudaMalloc, cudaFree or allocating library routine
+ * is called.
+ *  - Limit: the scratch a call needs grows with n (about 4*Kpad + 8*n_lam
+ *    bytes per row, plus 8*Kpad per row for SED_PREC_FP32); a call needing
+ *    more than SED_NOALLOC_SCRATCH_BYTES returns SED_ERANGE with the sizes in
+ *    sed_last_error() and launches nothing.  Split larger batches.
+ *  - The array is shared by all calls and keeps the contents of the last
+ *    one: calls that can overlap on the GPU (other streams or threads) race
+ *    on it and must be serialised by the caller.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ */
+#define SED_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+sed_status sed_loglike_noalloc(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld,
+                               double *lnl_out, uint32_t *row_status, int precision, void *stream);
+
+/*
  * Per-stage timing and work counters of the last hot-path call on a stream.
  * With profiling on, each hot-path call records CUDA events on its stream
  * before and after each of its kernels (preparation, contraction, epilogue);

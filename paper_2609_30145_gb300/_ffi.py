@@ -21,6 +21,7 @@ ROW_BAD_THETA, ROW_BAD_Z, ROW_BAD_TMAX, ROW_NONFINITE, ROW_DEVICE_TIMEOUT = 1, 2
 KEYS = ("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
         "diffuse_dust_index", "gas_logz", "gas_logu")
 NKEYS = len(KEYS)
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 P = C.c_void_p
 
@@ -65,6 +66,7 @@ SIGNATURES = {
     "sed_loglike": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
     "sed_loglike_grad": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, P, C.c_int, P]),
     "sed_loglike_host": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
+    "sed_loglike_noalloc": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
     "sed_set_profiling": (C.c_int, [P, C.c_int]),
     "sed_last_stats": (C.c_int, [P, P, C.POINTER(StageStats)]),
 }
