@@ -75,6 +75,7 @@ def _load():
         lib.orc_row.restype = C.c_int
         lib.orc_eval.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P, C.c_int]
         lib.orc_grad_fd.argtypes = [P, P, P, C.c_int, C.c_int, C.c_double, P, C.c_int]
+        lib.orc_grad.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, C.c_int]
         lib.orc_n_param.argtypes = [P]
         lib.orc_n_param.restype = C.c_int
         _lib = lib
@@ -251,6 +252,17 @@ class Oracle:
         self._lib.orc_spectrum(C.byref(self._g), C.byref(self._m), _p(lam_rest), lam_rest.size,
                                float(z), _p(fnu_obs), _p(out), _p(valid))
         return out, valid
+
+    def grad(self, theta, nthreads=0):
+        """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        n, ld = th.shape
+        out = np.zeros((n, ld))
+        lnl = np.zeros(n)
+        st = np.zeros(n, dtype=np.int32)
+        self._lib.orc_grad(C.byref(self._g), C.byref(self._m), _p(th), n, ld, _p(lnl), _p(out), _p(st),
+                           int(nthreads))
+        return dict(lnl=lnl, grad=out, status=st)
 
     def grad_fd(self, theta, h_rel=1e-6, nthreads=0):
         th = np.ascontiguousarray(theta, dtype=np.float64)

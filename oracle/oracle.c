@@ -536,3 +536,337 @@ void orc_grad_fd(const orc_grid *g, const orc_model *md, const double *theta, in
   }
   (void)nthreads;
 }
+
+/* ------------------------------------------------------------------ */
+/* Analytic gradient of lnL with respect to every parameter (FP64).     */
+/* ------------------------------------------------------------------ */
+/* Bracket of v on the node array x with the derivatives of the two weights
+ * with respect to v (zero where the value is clamped or the axis has one node). */
+static void bracket_d(const double *x, int n, double v, int *j0, double *w0, double *d0, int *j1,
+                      double *w1, double *d1) {
+  bracket(x, n, v, j0, w0, j1, w1);
+  *d0 = *d1 = 0.0;
+  if (n > 1 && v > x[0] && v < x[n - 1]) {
+    double h = x[*j1] - x[*j0];
+    *d0 = -1.0 / h;
+    *d1 = 1.0 / h;
+  }
+}
+
+/* Reverse pass of orc_row: the derivative of lnL (Eq. "total_lnlike") with
+ * respect to each parameter column, by the chain rule taken step by step
+ * backwards through the same definitions (likelihood -> projections -> observer
+ * frame -> dust and nebular -> contraction -> weights -> SFH edges -> cosmology).
+ * Everything is piecewise smooth; at a kink (a bracket node, a Voronoi cell
+ * edge, an interpolation node) the one-sided derivative of the branch the
+ * forward pass took is returned.  grad[n_param]; returns the row status
+ * (grad = 0 when it is not 0) and lnL in *lnl. */
+int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, double *grad, double *lnl) {
+  int NA = g->n_age, NL = g->n_lam, NZ = g->n_feh, NAF = g->n_afe, NT = md->n_sfh;
+  int np = orc_n_param(md);
+  for (int j = 0; j < np; j++) grad[j] = 0.0;
+  *lnl = -INFINITY;
+  double cz[3], cf[3], tmax;
+  int st = theta_status(md, theta, &tmax, NULL);
+  if (st) return st;
+  orc_theta t;
+  decode_theta(md, theta, &t);
+  orc_cosmology(md->H0, md->Om0, t.z, cz);
+  orc_cosmology(md->H0, md->Om0, md->zf, cf);
+  double zp = 1.0 + t.z;
+  size_t nsp = (size_t)NAF * NZ * NA;
+
+  /* ---------------- forward, keeping what the reverse pass needs */
+  double *T = (double *)malloc((NT + 1) * sizeof(double));
+  double *cm = (double *)malloc(NA * sizeof(double));
+  double *cp = (double *)malloc(NA * sizeof(double));
+  double *A = (double *)calloc((size_t)NT * NA, sizeof(double));
+  int *zm0 = (int *)malloc(NT * sizeof(int)), *zm1 = (int *)malloc(NT * sizeof(int));
+  double *wz0 = (double *)malloc(NT * sizeof(double)), *wz1 = (double *)malloc(NT * sizeof(double));
+  double *dz0 = (double *)malloc(NT * sizeof(double)), *dz1 = (double *)malloc(NT * sizeof(double));
+  double *W = (double *)calloc(nsp, sizeof(double));
+  double *Q = (double *)malloc(nsp * sizeof(double));
+  double *Y = (double *)calloc(NL, sizeof(double)), *O = (double *)calloc(NL, sizeof(double));
+  double *neb = (double *)calloc(NL, sizeof(double)), *lg = (double *)calloc(NL, sizeof(double));
+  double *tbc = (double *)malloc(NL * sizeof(double)), *td = (double *)malloc(NL * sizeof(double));
+  double *F = (double *)malloc(NL * sizeof(double)), *fnu = (double *)malloc(NL * sizeof(double));
+  double *gfnu = (double *)calloc(NL, sizeof(double));
+  double *gW = (double *)calloc(nsp, sizeof(double));
+
+  orc_sfh_edges(NT, tmax, T);
+  for (int a = 0; a < NA; a++) {
+    double ta = pow(10.0, g->log_age_yr[a]);
+    cm[a] = (a == 0) ? 0.0 : 0.5 * (pow(10.0, g->log_age_yr[a - 1]) + ta);
+    cp[a] = (a == NA - 1) ? INFINITY : 0.5 * (ta + pow(10.0, g->log_age_yr[a + 1]));
+  }
+  int an0, an1;
+  double wa0, wa1, da0, da1;
+  bracket_d(g->afe, NAF, md->use_afe ? t.afe : 0.0, &an0, &wa0, &da0, &an1, &wa1, &da1);
+  if (!md->use_afe) da0 = da1 = 0.0;
+  for (int i = 0; i < NT; i++) {
+    double dT = T[i + 1] - T[i];
+    bracket_d(g->feh, NZ, t.zeta[md->zmode == 0 ? i : 0], &zm0[i], &wz0[i], &dz0[i], &zm1[i], &wz1[i], &dz1[i]);
+    for (int a = 0; a < NA; a++) {
+      double lo = T[i] > cm[a] ? T[i] : cm[a];
+      double hi = T[i + 1] < cp[a] ? T[i + 1] : cp[a];
+      if (hi - lo <= 0.0) continue;
+      double Aia = t.m[i] * (hi - lo) / dT;
+      A[(size_t)i * NA + a] = Aia;
+      W[((size_t)an0 * NZ + zm0[i]) * NA + a] += Aia * wz0[i] * wa0;
+      W[((size_t)an0 * NZ + zm1[i]) * NA + a] += Aia * wz1[i] * wa0;
+      W[((size_t)an1 * NZ + zm0[i]) * NA + a] += Aia * wz0[i] * wa1;
+      W[((size_t)an1 * NZ + zm1[i]) * NA + a] += Aia * wz1[i] * wa1;
+    }
+  }
+  orc_q(g, Q);
+  double qy = 0.0;
+  int has_neb = md->use_nebular && g->neb_tab;
+  for (size_t s = 0; s < nsp; s++) {
+    int a = (int)(s % NA);
+    int young = g->log_age_yr[a] <= md->bc_edge_log_age_yr;
+    if (W[s] == 0.0) continue;
+    const double *f = g->flux + s * NL;
+    for (int k = 0; k < NL; k++) {
+      if (young && has_neb && g->lam[k] < O_LYMAN) continue;
+      (young ? Y : O)[k] += W[s] * f[k];
+    }
+    if (young) qy += W[s] * Q[s];
+  }
+  int u0 = 0, u1 = 0, zz0 = 0, zz1 = 0;
+  double wu0 = 0, wu1 = 0, du0 = 0, du1 = 0, wg0 = 0, wg1 = 0, dg0 = 0, dg1 = 0;
+  const double *t00 = NULL, *t01 = NULL, *t10 = NULL, *t11 = NULL;
+  if (has_neb) {
+    bracket_d(g->neb_logu, g->neb_n_logu, t.gas_logu, &u0, &wu0, &du0, &u1, &wu1, &du1);
+    bracket_d(g->neb_logz, g->neb_n_logz, t.gas_logz, &zz0, &wg0, &dg0, &zz1, &wg1, &dg1);
+    t00 = g->neb_tab + ((size_t)u0 * g->neb_n_logz + zz0) * NL;
+    t01 = g->neb_tab + ((size_t)u0 * g->neb_n_logz + zz1) * NL;
+    t10 = g->neb_tab + ((size_t)u1 * g->neb_n_logz + zz0) * NL;
+    t11 = g->neb_tab + ((size_t)u1 * g->neb_n_logz + zz1) * NL;
+    for (int k = 0; k < NL; k++) {
+      lg[k] = wu0 * wg0 * t00[k] + wu0 * wg1 * t01[k] + wu1 * wg0 * t10[k] + wu1 * wg1 * t11[k];
+      neb[k] = qy * pow(10.0, lg[k]);
+    }
+  }
+  for (int k = 0; k < NL; k++) tbc[k] = t.tau_bc * pow(g->lam[k] / 5500.0, t.alpha_bc);
+  orc_dust_tau(md->dust_law, g->lam, NL, t.tau_d, t.delta, td);
+  for (int k = 0; k < NL; k++) F[k] = exp(-td[k]) * (exp(-tbc[k]) * (Y[k] + neb[k]) + O[k]);
+  double dl = cz[0], ddl = cz[2] + zp * (O_C_KMS / md->H0 * 1e6 * O_PC_CM) * inv_E(t.z, &md->Om0);
+  if (dl < 10.0 * O_PC_CM) { dl = 10.0 * O_PC_CM; ddl = 0.0; }
+  double scale = pow(10.0, t.logmass) * O_LSUN * zp / (4.0 * M_PI * dl * dl);
+  double dlns_dz = 1.0 / zp - 2.0 * ddl / dl;
+  for (int k = 0; k < NL; k++) fnu[k] = scale * F[k];
+
+  /* ---------------- likelihood and its derivative with respect to the model */
+  double L = 0.0, gscale = 0.0, gz = 0.0;
+  if (md->n_filt > 0) {
+    double *ph = (double *)malloc(md->n_filt * sizeof(double));
+    orc_photometry(md, g->lam, NL, t.z, fnu, ph);
+    int off = 0;
+    for (int b = 0; b < md->n_filt; b++) {
+      int n = md->filt_len[b];
+      const double *Lf = md->filt_lam + off, *R = md->filt_trans + off;
+      off += n;
+      double ub = 0.0;
+      if (md->phot_d && (!md->phot_mask || md->phot_mask[b])) {
+        double s = md->phot_sigma[b], r = (md->phot_d[b] - ph[b]) / s;
+        L += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
+        ub = r / s;
+      }
+      if (ub == 0.0) continue;
+      /* m_b = sum_j R_j x_j dl_j flam(x_j) / Z_b (App. D), as in orc_photometry */
+      double zb = 0.0;
+      for (int j = 0; j + 1 < n; j++) {
+        double g0 = Lf[j] * R[j] * O_C_AA * O_AB / (Lf[j] * Lf[j]);
+        double g1 = Lf[j + 1] * R[j + 1] * O_C_AA * O_AB / (Lf[j + 1] * Lf[j + 1]);
+        zb += 0.5 * (g0 + g1) * (Lf[j + 1] - Lf[j]);
+      }
+      double lo = zp * g->lam[0], hi = zp * g->lam[NL - 1];
+      for (int j = 0; j < n; j++) {
+        double dlj;
+        if (n == 1) dlj = 0.0;
+        else if (j == 0) dlj = 0.5 * (Lf[1] - Lf[0]);
+        else if (j == n - 1) dlj = 0.5 * (Lf[n - 1] - Lf[n - 2]);
+        else dlj = 0.5 * (Lf[j + 1] - Lf[j - 1]);
+        double x = Lf[j];
+        if (!(x >= lo && x <= hi)) continue;
+        int k = 0, kh = NL - 1;
+        while (kh - k > 1) {
+          int mid = (k + kh) / 2;
+          if (zp * g->lam[mid] <= x) k = mid; else kh = mid;
+        }
+        double xa = zp * g->lam[k], xb = zp * g->lam[k + 1];
+        double tt = (x - xa) / (xb - xa);
+        double ga = O_C_AA * fnu[k] / (xa * xa), gb = O_C_AA * fnu[k + 1] / (xb * xb);
+        double c = ub * R[j] * x * dlj / zb;
+        gfnu[k] += c * (1.0 - tt) * O_C_AA / (xa * xa);
+        gfnu[k + 1] += c * tt * O_C_AA / (xb * xb);
+        /* the gather position moves with z: xa, xb = (1+z) lam */
+        double dflam = (1.0 - tt) * (-2.0 * ga / zp) + tt * (-2.0 * gb / zp) +
+                       (gb - ga) * (-x / (zp * zp * (g->lam[k + 1] - g->lam[k])));
+        gz += c * dflam;
+      }
+    }
+    free(ph);
+  }
+  if (md->n_pix > 0) {
+    double *sp = (double *)malloc(md->n_pix * sizeof(double));
+    unsigned char *vd = (unsigned char *)malloc(md->n_pix);
+    double *s_ln = (double *)malloc(md->n_pix * sizeof(double));
+    double *ll = (double *)malloc(NL * sizeof(double));
+    orc_spectrum(g, md, g->lam, NL, t.z, fnu, sp, vd);
+    spec_widths(g, md, s_ln);
+    for (int k = 0; k < NL; k++) ll[k] = log(g->lam[k]);
+    double lz = log(zp);
+    for (int i = 0; i < md->n_pix; i++) {
+      if (!(md->spec_d && vd[i] && (!md->spec_mask || md->spec_mask[i]))) continue;
+      double s = md->spec_sigma[i], r = (md->spec_d[i] - sp[i]) / s;
+      L += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
+      double ui = r / s;
+      /* Eq. "app_response" row of pixel i, as in orc_spectrum */
+      double x = log(md->spec_lam[i]) - lz, sg = s_ln[i];
+      int k = 0;
+      while (k + 2 < NL && !(ll[k] <= x && x < ll[k + 1])) k++;
+      double dln = ll[k + 1] - ll[k];
+      if (sg < 0.5 * dln) {
+        double tt = (x - ll[k]) / dln;
+        gfnu[k] += ui * (1.0 - tt);
+        gfnu[k + 1] += ui * tt;
+        gz += ui * (fnu[k + 1] - fnu[k]) / dln * (-1.0 / zp);
+        continue;
+      }
+      double sw = 0.0, sf = 0.0, swd = 0.0, sfd = 0.0;
+      for (int j = 0; j < NL; j++) {
+        double u = (ll[j] - x) / sg;
+        if (fabs(u) > 5.0) continue;
+        double w = exp(-0.5 * u * u), wd = w * u / sg; /* d w / d x */
+        sw += w; sf += w * fnu[j]; swd += wd; sfd += wd * fnu[j];
+      }
+      for (int j = 0; j < NL; j++) {
+        double u = (ll[j] - x) / sg;
+        if (fabs(u) > 5.0) continue;
+        gfnu[j] += ui * exp(-0.5 * u * u) / sw;
+      }
+      gz += ui * (sfd * sw - sf * swd) / (sw * sw) * (-1.0 / zp);
+    }
+    free(sp); free(vd); free(s_ln); free(ll);
+  }
+  *lnl = L;
+  if (!isfinite(L)) {
+    st = ORC_NONFINITE;
+    *lnl = -INFINITY;
+  } else {
+    /* ---------------- observer frame: fnu = scale F */
+    for (int k = 0; k < NL; k++) gscale += gfnu[k] * F[k];
+    double gl_mass = gscale * scale * log(10.0);
+    gz += gscale * scale * dlns_dz;
+    /* ---------------- dust and nebular (Sec. 2.4, App. C) */
+    double g_taubc = 0, g_alpha = 0, g_taud = 0, g_delta = 0, g_qy = 0, g_lu = 0, g_lz = 0;
+    double *gY = (double *)malloc(NL * sizeof(double)), *gO = (double *)malloc(NL * sizeof(double));
+    for (int k = 0; k < NL; k++) {
+      double gF = gfnu[k] * scale;
+      double ed = exp(-td[k]), eb = exp(-tbc[k]);
+      gY[k] = gF * ed * eb;
+      gO[k] = gF * ed;
+      double lp = log(g->lam[k] / 5500.0);
+      double gtbc = -gF * ed * eb * (Y[k] + neb[k]);
+      g_taubc += gtbc * pow(g->lam[k] / 5500.0, t.alpha_bc);
+      g_alpha += gtbc * tbc[k] * lp;
+      double gtd = -gF * F[k];
+      double p = pow(g->lam[k] / 5500.0, t.delta);
+      double shape, dshape;
+      if (md->dust_law == 0) {
+        shape = p;
+        dshape = p * lp;
+      } else {
+        double xx = g->lam[k] * 350.0, dd = g->lam[k] * g->lam[k] - 2175.0 * 2175.0;
+        double drude = xx * xx / (dd * dd + xx * xx);
+        double kp = calzetti_kprime(g->lam[k] * 1e-4);
+        shape = (kp + (0.85 - 1.9 * t.delta) * drude) / 4.05 * p;
+        dshape = (-1.9 * drude) / 4.05 * p + shape * lp;
+      }
+      g_taud += gtd * shape;
+      g_delta += gtd * t.tau_d * dshape;
+      if (has_neb) {
+        double gneb = gY[k];
+        g_qy += gneb * pow(10.0, lg[k]);
+        double glg = gneb * neb[k] * log(10.0);
+        g_lu += glg * (du0 * wg0 * t00[k] + du0 * wg1 * t01[k] + du1 * wg0 * t10[k] + du1 * wg1 * t11[k]);
+        g_lz += glg * (wu0 * dg0 * t00[k] + wu0 * dg1 * t01[k] + wu1 * dg0 * t10[k] + wu1 * dg1 * t11[k]);
+      }
+    }
+    /* ---------------- contraction (Eq. csp_sum_main / app_attn) and Q_young */
+    for (size_t s = 0; s < nsp; s++) {
+      int a = (int)(s % NA);
+      int young = g->log_age_yr[a] <= md->bc_edge_log_age_yr;
+      const double *f = g->flux + s * NL;
+      double acc = 0.0;
+      for (int k = 0; k < NL; k++) {
+        if (young && has_neb && g->lam[k] < O_LYMAN) continue;
+        acc += (young ? gY : gO)[k] * f[k];
+      }
+      if (young) acc += g_qy * Q[s];
+      gW[s] = acc;
+    }
+    /* ---------------- weights (App. B step scheme, metallicity and [a/Fe] splits) */
+    double *gT = (double *)calloc(NT + 1, sizeof(double));
+    double g_afe = 0.0;
+    int nz = md->zmode == 0 ? NT : 1;
+    const int offz = NT, offs = NT + nz;
+    for (int i = 0; i < NT; i++) {
+      double dT = T[i + 1] - T[i];
+      for (int a = 0; a < NA; a++) {
+        double Aia = A[(size_t)i * NA + a];
+        double lo = T[i] > cm[a] ? T[i] : cm[a];
+        double hi = T[i + 1] < cp[a] ? T[i + 1] : cp[a];
+        if (hi - lo <= 0.0) continue;
+        double g00 = gW[((size_t)an0 * NZ + zm0[i]) * NA + a], g01 = gW[((size_t)an0 * NZ + zm1[i]) * NA + a];
+        double g10 = gW[((size_t)an1 * NZ + zm0[i]) * NA + a], g11 = gW[((size_t)an1 * NZ + zm1[i]) * NA + a];
+        double gA = g00 * wz0[i] * wa0 + g01 * wz1[i] * wa0 + g10 * wz0[i] * wa1 + g11 * wz1[i] * wa1;
+        grad[offz + (md->zmode == 0 ? i : 0)] +=
+            Aia * (g00 * dz0[i] * wa0 + g01 * dz1[i] * wa0 + g10 * dz0[i] * wa1 + g11 * dz1[i] * wa1);
+        g_afe += Aia * (g00 * wz0[i] * da0 + g01 * wz1[i] * da0 + g10 * wz0[i] * da1 + g11 * wz1[i] * da1);
+        /* A = m_i (hi - lo) / dT */
+        grad[i] += gA * (hi - lo) / dT;
+        double ov = hi - lo;
+        gT[i + 1] += gA * t.m[i] * ((T[i + 1] < cp[a] ? 1.0 : 0.0) / dT - ov / (dT * dT));
+        gT[i] += gA * t.m[i] * (-(T[i] > cm[a] ? 1.0 : 0.0) / dT + ov / (dT * dT));
+      }
+    }
+    /* SFH edges: T_i = 1e7 (T_max/1e7)^((i-2)/(N_T-2)) for i >= 3; T_max = t(z) - t(z_f) */
+    double g_tmax = 0.0;
+    for (int i = 3; i <= NT; i++) g_tmax += gT[i] * T[i] * (double)(i - 2) / ((double)(NT - 2) * tmax);
+    double th_yr = O_MPC_KM / md->H0 / O_YR_S;
+    gz += g_tmax * (-th_yr * inv_E(t.z, &md->Om0) / zp);
+    grad[offs + 0] = md->use_afe ? g_afe : 0.0;
+    grad[offs + 1] = gl_mass;
+    grad[offs + 2] = gz;
+    grad[offs + 3] = g_taubc;
+    grad[offs + 4] = g_alpha;
+    grad[offs + 5] = g_taud;
+    grad[offs + 6] = g_delta;
+    grad[offs + 7] = has_neb ? g_lz : 0.0;
+    grad[offs + 8] = has_neb ? g_lu : 0.0;
+    free(gT); free(gY); free(gO);
+  }
+  if (st) for (int j = 0; j < np; j++) grad[j] = 0.0;
+  free(T); free(cm); free(cp); free(A); free(zm0); free(zm1); free(wz0); free(wz1); free(dz0); free(dz1);
+  free(W); free(Q); free(Y); free(O); free(neb); free(lg); free(tbc); free(td); free(F); free(fnu);
+  free(gfnu); free(gW);
+  (void)cf;
+  return st;
+}
+
+void orc_grad(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld, double *lnl_out,
+              double *grad_out, int *status_out, int nthreads) {
+#ifdef _OPENMP
+  int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
+#endif
+  for (int r = 0; r < n; r++) {
+    double l;
+    int st = orc_row_grad(g, md, theta + (size_t)r * ld, grad_out + (size_t)r * ld, &l);
+    if (lnl_out) lnl_out[r] = l;
+    if (status_out) status_out[r] = st;
+  }
+  (void)nthreads;
+}

@@ -19,6 +19,8 @@
  *   photometry           App. D, Eqs. "app_phot_row", "app_phot_T"
  *   spectrum             Eq. "one_kernel", App. E, Eqs. "app_siglib", "app_sigeff", "app_response"
  *   likelihood           Eq. "total_lnlike", Eq. "app_spec_lndiag"
+ *   gradient             the chain rule through all of the above (the paper takes its
+ *                        gradients by automatic differentiation, Sec. 4)
  */
 #ifndef SED_ORACLE_H
 #define SED_ORACLE_H
@@ -105,6 +107,15 @@ void orc_eval(const orc_grid *g, const orc_model *md, const double *theta, int n
 /* Central finite-difference gradient of lnL (FP64), step h_j = h_rel*max(|x_j|, 1). */
 void orc_grad_fd(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld,
                  double h_rel, double *grad_out, int nthreads);
+
+/* Analytic gradient of lnL (FP64 reverse pass through the same definitions):
+ * grad[n_param] for one row; returns the row status, lnL in *lnl. */
+int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, double *grad, double *lnl);
+
+/* Batched analytic gradient: grad_out [n][ld] (columns >= n_param untouched),
+ * lnl_out [n], status_out [n] (either may be NULL). */
+void orc_grad(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld, double *lnl_out,
+              double *grad_out, int *status_out, int nthreads);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,83 @@
+"""Pins of the oracle's analytic gradient (FP64 reverse pass) against facts
+that do not reuse its derivation:
+
+- central finite differences of the oracle's own forward model (which the
+  pins of test_oracle_pins.py tie to the paper), on every parameter column,
+  for the three workload shapes (photometry with a power-law diffuse law;
+  nebular + Kriek & Conroy dust; [a/Fe] + an LSF-convolved spectrum);
+- the closed form of d lnL / d logmass (every model datum scales with
+  10^logmass, Sec. 2.6);
+- homogeneity of the weights in the SFH masses (App. B: W is linear in m_i),
+  so that sum_i m_i dlnL/dm_i = dlnL/dlogmass / ln 10 exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import cases
+
+SHAPES = {
+    "tiny": ("tiny_phot_16x4x512", None),
+    "neb_kc13": ("phot_107x12x6000_b1024", dict(n_lam=1200, n_sfh=16)),
+    "afe_spec": ("specphot_afe_107x12x5x6000_b2048", dict(n_lam=1200, n_sfh=16, n_pix=240)),
+}
+
+
+@pytest.fixture(scope="module", params=list(SHAPES))
+def shape(request):
+    wname, sh = SHAPES[request.param]
+    w = synth.WORKLOADS[wname]
+    if sh:
+        w = synth.shrink(w, **sh)
+    return w, cases.oracle_for(w)
+
+
+def test_analytic_gradient_matches_central_differences(shape):
+    w, orc = shape
+    th = cases.theta_rows(w, 3, seed=31)
+    g = orc.grad(th)
+    fd = orc.grad_fd(th, h_rel=1e-7)
+    ref = orc.eval(th)
+    assert np.array_equal(g["status"], ref["status"])
+    assert np.array_equal(g["lnl"], ref["lnl"])
+    for r in range(th.shape[0]):
+        sc = np.abs(fd[r]).max()
+        err = np.abs(g["grad"][r] - fd[r]) / sc
+        assert err.max() < 2e-6, (r, int(err.argmax()), err.max())
+
+
+def test_dlogmass_closed_form_and_mass_homogeneity(shape):
+    w, orc = shape
+    th = cases.theta_rows(w, 3, seed=32)
+    g = orc.grad(th)["grad"]
+    res = orc.eval(th)
+    nz = w.n_sfh if w.zmode == 0 else 1
+    j_mass = w.n_sfh + nz + 1
+    for r in range(th.shape[0]):
+        want = 0.0
+        if orc.n_filt:
+            m = res["phot"][r]
+            want += math.log(10) * np.sum((orc.phot_d - m) / orc.phot_sigma ** 2 * m)
+        if orc.n_pix:
+            m = res["spec"][r]
+            # pixels without model nodes in reach are out of the likelihood (and have m = 0)
+            want += math.log(10) * np.sum((orc.spec_d - m) / orc.spec_sigma ** 2 * m)
+        assert g[r, j_mass] == pytest.approx(want, rel=1e-9, abs=1e-9 * abs(want))
+        euler = np.dot(th[r, :w.n_sfh], g[r, :w.n_sfh])
+        assert euler == pytest.approx(g[r, j_mass] / math.log(10), rel=1e-9, abs=1e-9 * abs(g[r, j_mass]))
+
+
+def test_bad_rows_have_zero_gradient():
+    w = synth.WORKLOADS["tiny_phot_16x4x512"]
+    orc = cases.oracle_for(w)
+    th = cases.theta_rows(w, 3, seed=33)
+    jz = w.n_sfh * 2 + 2
+    th[0, jz] = w.zf + 1
+    th[1, 0] = np.nan
+    g = orc.grad(th)
+    assert list(g["status"][:2]) == [oracle.BAD_Z, oracle.BAD_THETA]
+    assert np.all(g["grad"][:2] == 0) and np.isneginf(g["lnl"][:2]).all()
+    assert g["status"][2] == 0 and np.isfinite(g["lnl"][2])
