@@ -190,7 +190,24 @@ sed_status sed_loglike(sed_ctx *ctx, sed_model_id model, const float *theta, int
 /*
  * Log-likelihood and its gradient with respect to every parameter column:
  * grad_out [n][ld] (FP32, device; columns >= n_param are zeroed).  Columns the
- * model does not use (e.g. gas_* without nebular) get 0.
+ * model does not use (e.g. gas_* without nebular, afe without use_afe) get 0;
+ * rows with a non-zero row_status get an all-zero gradient row.
+ * The gradient is the analytic derivative of the forward model (the paper
+ * differentiates it automatically, Sec. 4): a hand-written reverse pass that
+ * recomputes the per-row spectrum from the contraction output, forms
+ * dlnL/dY and dlnL/dO, contracts them with the SSP grid for dlnL/dW (the
+ * transpose of Eq. csp_sum_main) and maps dlnL/dW back through the step-scheme
+ * weights, the metallicity / [a/Fe] splits and the SFH edges (App. B) to the
+ * parameters.  At a kink (an interpolation node, a bracket node, a Voronoi
+ * cell edge) the one-sided derivative of the branch the forward took is
+ * returned.
+ * precision: SED_PREC_FP32 (3xTF32 tensor-core contractions) or
+ * SED_PREC_FP32_SIMT; SED_PREC_BF16 returns SED_EUNSUPPORTED.
+ * The first gradient call on a grid layout builds its lambda-major copies
+ * (host work and synchronous copies to the device, ~3 x 4 x Kpad x n_lam
+ * bytes); later calls only enqueue kernels.  SED_ERANGE when the adjoint
+ * epilogue's shared-memory staging (8 n_lam + max(8 filter samples, 20 n_pix)
+ * bytes) exceeds 227 KB.
  */
 sed_status sed_loglike_grad(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld,
                             double *lnl_out, float *grad_out, uint32_t *row_status,

@@ -1,0 +1,471 @@
+// Adjoint of the epilogue and of the contraction (the reverse pass of
+// sed_loglike_grad).  The paper obtains its gradients by automatic
+// differentiation of the forward model (Sec. 4); here each step is
+// differentiated by hand, in reverse order:
+//
+//   lnL (Eq. total_lnlike)          u_b = dlnL/dm_b = (d_b - m_b)/sigma_b^2
+//   photometry (App. D)             dlnL/dF_k from the interpolation weights of
+//                                   every filter sample that touches node k
+//   spectrum (Eq. app_response)     dlnL/dF_k from every pixel whose Gaussian
+//                                   row reaches node k
+//   dust + nebular (Sec. 2.4, App. C)
+//                                   dlnL/dY, dlnL/dO and the sums over lambda
+//                                   giving d/dtau_BC, d/dalpha_BC, d/dtau_d,
+//                                   d/ddelta, d/dQ_young, d/dlogU, d/dlogZ_gas
+//   observer frame (Sec. 2.6)       d/dlogmass and the part of d/dz that comes
+//                                   from the flux scale and the redshift gather
+//   contraction (Eq. csp_sum_main)  dlnL/dW = [G_Y SSP_young^T | G_O SSP_old^T]
+//                                   (k_dw_simt here, or the tcgen05 kernel)
+//
+// k_epi_bwd takes one CTA per parameter row, recomputes the row's attenuated
+// spectrum from Y and O (the forward's contraction output) instead of storing
+// it, and accumulates dlnL/dF in shared memory.  Every sum runs in a fixed
+// order (node-owned gathers, no atomics), so the gradient is bitwise
+// reproducible.
+#include "locate.cuh"
+#include "sed_internal.cuh"
+
+namespace sed {
+
+constexpr int EB_THREADS = 256;
+constexpr int EB_WARPS = EB_THREADS / 32;
+constexpr int EB_MAX_BANDS = 128;
+constexpr int EB_NRED = 12;   // per-warp partial sums reduced in FP64
+
+__device__ __forceinline__ float tf32_rna_dev(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void put_g(const EpiBwdArgs& a, float* hi, float* lo, size_t o, float v) {
+  if (a.split) {
+    const float h = tf32_rna_dev(v);
+    hi[o] = h;
+    lo[o] = v - h;
+  } else {
+    hi[o] = v;
+  }
+}
+
+size_t epi_bwd_smem(const EpiBwdArgs& a) {
+  const size_t n = (size_t)a.g.n_lam;
+  const size_t samp = (size_t)a.md.n_samp * 8;    // node index + interpolation weight
+  const size_t pix = (size_t)a.md.n_pix * 20;     // node range + 4 floats
+  return 2 * n * sizeof(float) + (samp > pix ? samp : pix);
+}
+
+__global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
+  const ModelDev& md = a.md;
+  const GridDev& g = a.g;
+  const int r = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int N = g.n_lam;
+  extern __shared__ __align__(16) float smem[];
+  float* Fs = smem;                 // attenuated rest-frame spectrum F
+  float* phi = smem + N;            // dlnL/dF
+  void* U = smem + 2 * N;           // union: filter samples, then spectrum pixels
+  int* sk = reinterpret_cast<int*>(U);
+  float* st = reinterpret_cast<float*>(sk + md.n_samp);
+  int* prg = reinterpret_cast<int*>(U);
+  float* pxh = reinterpret_cast<float*>(prg + md.n_pix);
+  float* pxl = pxh + md.n_pix;
+  float* pc = pxl + md.n_pix;
+  float* pt = pc + md.n_pix;
+  __shared__ float ubp[EB_MAX_BANDS];
+  __shared__ int bk0[EB_MAX_BANDS], bk1[EB_MAX_BANDS];
+  __shared__ double band_l[EB_MAX_BANDS], band_um[EB_MAX_BANDS];
+  __shared__ double red[EB_WARPS][EB_NRED];
+
+  const size_t ro = (size_t)r * a.ldn;
+  RowScal rs = a.rs[r];
+  if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
+  if (rs.status) {
+    for (int k = tid; k < a.ldn; k += EB_THREADS) {
+      a.gy_hi[ro + k] = 0.f;
+      a.go_hi[ro + k] = 0.f;
+      if (a.split) { a.gy_lo[ro + k] = 0.f; a.go_lo[ro + k] = 0.f; }
+    }
+    if (tid < RGRAD) a.rgrad[(size_t)r * RGRAD + tid] = 0.0;
+    if (tid == 0) {
+      if (a.lnl) a.lnl[r] = -INFINITY;
+      if (a.status) a.status[r] = rs.status;
+    }
+    return;
+  }
+  const float* Yr = a.Y + ro;
+  const float* Or = a.O + ro;
+  const float eb_kc = 0.85f - 1.9f * rs.delta;
+
+  // ---- forward: attenuated spectrum (same arithmetic as the forward epilogue)
+  for (int k = tid; k < N; k += EB_THREADS) {
+    const float lnp = g.lnp[k];
+    const float tbc = rs.tau_bc * __expf(rs.alpha_bc * lnp);
+    const float pw = __expf(rs.delta * lnp);
+    const float td = md.dust_law == SED_DUST_POWER_LAW
+                         ? rs.tau_d * pw
+                         : rs.tau_d * (g.kprime[k] + eb_kc * g.drude[k]) * (1.f / 4.05f) * pw;
+    float y = Yr[k];
+    if (md.use_neb) {
+      const float lg = rs.neb_w[0] * g.neb_tab[rs.neb_off[0] + k] + rs.neb_w[1] * g.neb_tab[rs.neb_off[1] + k] +
+                       rs.neb_w[2] * g.neb_tab[rs.neb_off[2] + k] + rs.neb_w[3] * g.neb_tab[rs.neb_off[3] + k];
+      y += exp2f(rs.log2_qy + 3.3219280948873623f * lg);
+    }
+    Fs[k] = __expf(-td) * (__expf(-tbc) * y + Or[k]);
+    phi[k] = 0.f;
+  }
+  __syncthreads();
+
+  // ---- photometry forward (warp per band), the sample brackets, u_b and the
+  //      gather part of dlnL/dz (the sample positions lam_j/(1+z) move with z)
+  const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
+  float gz_gather = 0.f;
+  for (int b = warp; b < md.n_filt; b += EB_WARPS) {
+    const int js = md.band_start[b], je = md.band_start[b + 1];
+    float acc = 0.f;
+    int kmin = 0x7fffffff, kmax = -1;
+    for (int j = js + lane; j < je; j += 32) {
+      const float x = md.samp_lam[j] * rs.inv1pz;
+      float v = 0.f, t = 0.f;
+      int k;
+      if (x < lam0) {
+        k = -2;
+      } else if (x > lamN) {
+        k = N;
+      } else {
+        k = locate_lin(g, x);
+        const float la = g.lam_f[k], lb = g.lam_f[k + 1];
+        t = (x - la) / (lb - la);
+        const float G0 = Fs[k] * g.inv_lam2[k], G1 = Fs[k + 1] * g.inv_lam2[k + 1];
+        v = G0 + t * (G1 - G0);
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+      }
+      sk[j] = k;
+      st[j] = t;
+      acc = fmaf(md.samp_w[j], v, acc);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+      kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    const float mb = rs.p_phot * acc;
+    double v = 0.0, ub = 0.0;
+    if (md.phot_isig[b] != 0.0) {
+      const double rr = (md.phot_d[b] - (double)mb) * md.phot_isig[b];
+      v = -0.5 * rr * rr + md.phot_nlog[b];
+      ub = rr * md.phot_isig[b];
+    }
+    const float c_b = (float)(ub * (double)rs.p_phot);
+    if (lane == 0) {
+      band_l[b] = v;
+      band_um[b] = ub * (double)mb;
+      ubp[b] = c_b;
+      bk0[b] = kmin;
+      bk1[b] = kmax;
+    }
+    if (c_b != 0.f) {
+      for (int j = js + lane; j < je; j += 32) {
+        const int k = sk[j];
+        if (k < 0 || k >= N) continue;
+        const float x = md.samp_lam[j] * rs.inv1pz;
+        const float G0 = Fs[k] * g.inv_lam2[k], G1 = Fs[k + 1] * g.inv_lam2[k + 1];
+        const float dlerp = (G1 - G0) / (g.lam_f[k + 1] - g.lam_f[k]);
+        gz_gather += c_b * md.samp_w[j] * dlerp * (-x * rs.inv1pz);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- dlnL/dF from the photometry: node k gathers the samples bracketed by
+  //      [k-1, k] (weight t) and [k, k+1] (weight 1-t), band by band in order
+  for (int k = tid; k < N; k += EB_THREADS) {
+    float acc = 0.f;
+    for (int b = 0; b < md.n_filt; ++b) {
+      const float cb = ubp[b];
+      if (cb == 0.f || k < bk0[b] || k > bk1[b] + 1) continue;
+      const int js = md.band_start[b], je = md.band_start[b + 1];
+      int lo = js, hi = je;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sk[mid] < k - 1) lo = mid + 1; else hi = mid;
+      }
+      for (int j = lo; j < je && sk[j] <= k; ++j) {
+        const float c = cb * md.samp_w[j];
+        acc += sk[j] == k ? c * (1.f - st[j]) : c * st[j];
+      }
+    }
+    phi[k] = acc * g.inv_lam2[k];
+  }
+  __syncthreads();
+
+  // ---- spectrum forward (thread per pixel): m_i, u_i, each pixel's node window
+  double l_spec = 0.0, um_spec = 0.0;
+  float gz_spec = 0.f;
+  const double l1 = (double)rs.ln1pz_hi + (double)rs.ln1pz_lo;
+  const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
+  for (int i = tid; i < md.n_pix; i += EB_THREADS) {
+    const double xd = md.pix_ln[i] - l1;
+    const float xh = (float)xd, xl = (float)(xd - (double)xh);
+    float v = 0.f, dv = 0.f, cw = 0.f, tl = -1.f;
+    int jlo = 1, jhi = 0;
+    bool valid = false;
+    if (xh >= ll0 && xh <= llN) {
+      const float s = md.pix_s[i];
+      const int k = locate_ln(g, xh, g.lnl_hi);
+      const float dln = (g.lnl_hi[k + 1] - g.lnl_hi[k]) + (g.lnl_lo[k + 1] - g.lnl_lo[k]);
+      if (s < 0.5f * dln) {
+        const float t = ((xh - g.lnl_hi[k]) + (xl - g.lnl_lo[k])) / dln;
+        v = Fs[k] + t * (Fs[k + 1] - Fs[k]);
+        dv = (Fs[k + 1] - Fs[k]) / dln;
+        valid = true;
+        jlo = k; jhi = k + 1; tl = t; cw = 1.f;
+      } else {
+        const float inv_s = 1.f / s;
+        jlo = locate_ln(g, fmaxf(xh - 5.f * s, ll0), g.lnl_hi);
+        jhi = locate_ln(g, fminf(xh + 5.f * s, llN), g.lnl_hi) + 1;
+        float sw = 0.f, sf = 0.f, swd = 0.f, sfd = 0.f;
+        for (int j = jlo; j <= jhi; ++j) {
+          const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
+          const float u = d * inv_s;
+          if (fabsf(u) <= 5.f) {
+            const float w = __expf(-0.5f * u * u);
+            const float wd = w * u * inv_s;   // dw/dx
+            sw += w;
+            sf = fmaf(w, Fs[j], sf);
+            swd += wd;
+            sfd = fmaf(wd, Fs[j], sfd);
+          }
+        }
+        if (sw > 0.f) {
+          v = sf / sw;
+          dv = (sfd * sw - sf * swd) / (sw * sw);
+          valid = true;
+          cw = 1.f / sw;
+        }
+      }
+    }
+    const float mi = rs.s_spec * v;
+    float ci = 0.f;
+    if (valid && md.spec_isig[i] != 0.0) {
+      const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
+      l_spec += -0.5 * rr * rr + md.spec_nlog[i];
+      const double ui = rr * md.spec_isig[i];
+      um_spec += ui * (double)mi;
+      const float us = (float)(ui * (double)rs.s_spec);
+      gz_spec += us * dv * (-rs.inv1pz);
+      ci = us * cw;
+    }
+    if (ci == 0.f) { jlo = 1; jhi = 0; }
+    prg[i] = (jlo & 0xffff) | (jhi << 16);
+    pxh[i] = xh;
+    pxl[i] = xl;
+    pc[i] = ci;
+    pt[i] = tl;
+  }
+  __syncthreads();
+
+  // ---- dlnL/dF from the spectrum: warp w owns a contiguous chunk of nodes and
+  //      walks the pixels in order; its lanes cover the window's nodes
+  if (md.n_pix > 0) {
+    const int chunk = (N + EB_WARPS - 1) / EB_WARPS;
+    const int c0 = warp * chunk, c1 = min(N, c0 + chunk);
+    for (int i0 = 0; i0 < md.n_pix; i0 += 32) {
+      const int i = i0 + lane;
+      bool hit = false;
+      if (i < md.n_pix) {
+        const int lo = prg[i] & 0xffff, hi = prg[i] >> 16;
+        hit = lo <= hi && lo < c1 && hi >= c0;
+      }
+      unsigned mask = __ballot_sync(0xffffffffu, hit);
+      while (mask) {
+        const int p = i0 + __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int lo = prg[p] & 0xffff, hi = prg[p] >> 16;
+        const float c = pc[p], tl = pt[p], xh = pxh[p], xl = pxl[p];
+        const float inv_s = tl < 0.f ? 1.f / md.pix_s[p] : 0.f;
+        for (int j = max(lo, c0) + lane; j <= min(hi, c1 - 1); j += 32) {
+          float w;
+          if (tl >= 0.f) {
+            w = j == lo ? 1.f - tl : tl;
+          } else {
+            const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
+            const float u = d * inv_s;
+            w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
+          }
+          phi[j] += c * w;
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- dust and nebular: dlnL/dY, dlnL/dO and the parameter sums over lambda
+  float g_tbc = 0.f, g_abc = 0.f, g_td = 0.f, g_dl = 0.f, g_qy = 0.f, g_lu = 0.f, g_lz = 0.f;
+  for (int k = tid; k < a.ldn; k += EB_THREADS) {
+    if (k >= N) {
+      put_g(a, a.gy_hi, a.gy_lo, ro + k, 0.f);
+      put_g(a, a.go_hi, a.go_lo, ro + k, 0.f);
+      continue;
+    }
+    const float lnp = g.lnp[k];
+    const float pa = __expf(rs.alpha_bc * lnp);
+    const float tbc = rs.tau_bc * pa;
+    const float pw = __expf(rs.delta * lnp);
+    float shape, dshape;
+    if (md.dust_law == SED_DUST_POWER_LAW) {
+      shape = pw;
+      dshape = pw * lnp;
+    } else {
+      shape = (g.kprime[k] + eb_kc * g.drude[k]) * (1.f / 4.05f) * pw;
+      dshape = (-1.9f * g.drude[k]) * (1.f / 4.05f) * pw + shape * lnp;
+    }
+    const float td = rs.tau_d * shape;
+    const float ed = __expf(-td), eb = __expf(-tbc);
+    float y = Yr[k];
+    float lg = 0.f, nb = 0.f;
+    if (md.use_neb) {
+      lg = rs.neb_w[0] * g.neb_tab[rs.neb_off[0] + k] + rs.neb_w[1] * g.neb_tab[rs.neb_off[1] + k] +
+           rs.neb_w[2] * g.neb_tab[rs.neb_off[2] + k] + rs.neb_w[3] * g.neb_tab[rs.neb_off[3] + k];
+      nb = exp2f(rs.log2_qy + 3.3219280948873623f * lg);
+      y += nb;
+    }
+    const float gF = phi[k];
+    const float gy = gF * ed * eb, go = gF * ed;
+    put_g(a, a.gy_hi, a.gy_lo, ro + k, gy);
+    put_g(a, a.go_hi, a.go_lo, ro + k, go);
+    const float gtbc = -gy * y;
+    g_tbc += gtbc * pa;
+    g_abc += gtbc * tbc * lnp;
+    const float gtd = -gF * Fs[k];
+    g_td += gtd * shape;
+    g_dl += gtd * rs.tau_d * dshape;
+    if (md.use_neb) {
+      g_qy += gy * exp2f(3.3219280948873623f * lg);
+      const float glg = gy * nb * 2.302585092994046f;
+      float su = 0.f, sz = 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float tv = g.neb_tab[rs.neb_off[c] + k];
+        su += rs.neb_dwu[c] * tv;
+        sz += rs.neb_dwz[c] * tv;
+      }
+      g_lu += glg * su;
+      g_lz += glg * sz;
+    }
+  }
+
+  // ---- fixed-order FP64 reductions of the per-thread pieces
+  double v[EB_NRED] = {(double)g_tbc, (double)g_abc, (double)g_td, (double)g_dl, (double)g_lz, (double)g_lu,
+                       um_spec, (double)gz_gather + (double)gz_spec, (double)g_qy, l_spec, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < EB_NRED; ++q) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0) red[warp][q] = v[q];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double s[EB_NRED];
+    for (int q = 0; q < EB_NRED; ++q) {
+      s[q] = 0.0;
+      for (int w = 0; w < EB_WARPS; ++w) s[q] += red[w][q];
+    }
+    double lnl = s[9], um_phot = 0.0;
+    for (int b = 0; b < md.n_filt; ++b) {
+      lnl += band_l[b];
+      um_phot += band_um[b];
+    }
+    double* rg = a.rgrad + (size_t)r * RGRAD;
+    uint32_t stt = 0;
+    if (!isfinite(lnl)) { stt = SED_ROW_NONFINITE; lnl = -INFINITY; }
+    rg[RG_TAU_BC] = s[0];
+    rg[RG_ALPHA_BC] = s[1];
+    rg[RG_TAU_D] = s[2];
+    rg[RG_DELTA] = s[3];
+    rg[RG_GAS_LOGZ] = s[4];
+    rg[RG_GAS_LOGU] = s[5];
+    rg[RG_LOGMASS] = 2.302585092994046 * (um_phot + s[6]);
+    rg[RG_Z] = um_phot * (double)rs.dlnp_dz + s[6] * (double)rs.dlns_dz + s[7];
+    rg[RG_QY] = s[8];
+    rg[RG_BAD] = stt ? 1.0 : 0.0;
+    if (a.lnl) a.lnl[r] = lnl;
+    if (a.status) a.status[r] = stt;
+  }
+}
+
+cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s) {
+  const size_t smem = epi_bwd_smem(a);
+  if (smem_needed) *smem_needed = smem;
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  static size_t set_for = 0;
+  if (smem > 48 * 1024 && smem > set_for) {
+    cudaError_t e = cudaFuncSetAttribute(k_epi_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    set_for = smem;
+  }
+  k_epi_bwd<<<a.n, EB_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core adjoint contraction (FP32-SIMT precision):
+//   dW[r][k] = sum_lam G[r][lam] SSP[k][lam],  G = dlnL/dY (k young) or dlnL/dO (k old).
+// 128 x 64 tile per CTA, 8 x 4 outputs per thread, lambda in steps of 8.
+constexpr int DS_M = 128, DS_N = 64, DS_K = 8;
+
+__global__ void __launch_bounds__(256) k_dw_simt(const DwSimtArgs a) {
+  __shared__ __align__(16) float As[DS_K][DS_M];
+  __shared__ __align__(16) float Bs[DS_K][DS_N];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * DS_M, n0 = blockIdx.x * DS_N;
+  const float* G = n0 < a.Ky_pad ? a.gy : a.go;
+  const int lrow = tid >> 1, lk = (tid & 1) * 4;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int l0 = 0; l0 < a.ldk; l0 += DS_K) {
+    float4 va = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m0 + lrow < a.n) va = *reinterpret_cast<const float4*>(G + (size_t)(m0 + lrow) * a.ldg + l0 + lk);
+    As[lk + 0][lrow] = va.x; As[lk + 1][lrow] = va.y; As[lk + 2][lrow] = va.z; As[lk + 3][lrow] = va.w;
+    if (tid < 2 * DS_N) {
+      const float4 vb = *reinterpret_cast<const float4*>(a.sspK + (size_t)(n0 + lrow) * a.ldk + l0 + lk);
+      Bs[lk + 0][lrow] = vb.x; Bs[lk + 1][lrow] = vb.y; Bs[lk + 2][lrow] = vb.z; Bs[lk + 3][lrow] = vb.w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < DS_K; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 4 + 64]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[4] = {b0.x, b0.y, b0.z, b0.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;
+    if (gm >= a.n) continue;
+    *reinterpret_cast<float4*>(a.dW + (size_t)gm * a.Kpad + n0 + tx * 4) =
+        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
+cudaError_t launch_dw_simt(const DwSimtArgs& a, cudaStream_t s) {
+  dim3 grid(a.Kpad / DS_N, (a.n + DS_M - 1) / DS_M);
+  k_dw_simt<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sed

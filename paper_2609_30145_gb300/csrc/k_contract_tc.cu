@@ -1,17 +1,23 @@
-// Tensor-core contraction on sm_103a (tcgen05 + TMA + TMEM).
+// Tensor-core contractions on sm_103a (tcgen05 + TMA + TMEM).
 //
-// Computes the two partial sums of Eq. csp_sum_main split at the birth-cloud
-// age (Eq. app_attn with a two-bin age-to-bin matrix):
+// Forward (GRAD = false): the two partial sums of Eq. csp_sum_main split at the
+// birth-cloud age (Eq. app_attn with a two-bin age-to-bin matrix):
 //     Y[theta][lam] = sum_{k in young} W[theta][k] SSP[k][lam]
 //     O[theta][lam] = sum_{k in old}   W[theta][k] SSP[k][lam]
 // W (A operand, [n][Kpad]) and SSP^T (B operand, [n_lam][Kpad]) are both
 // K-major; K is ordered [young block | old block], each padded to 64.
 //
-// One CTA computes a 128 (theta) x BN (lambda) tile of Y and of O.  Warp roles:
+// Adjoint (GRAD = true): the same contraction transposed, reducing over lambda,
+//     dW[theta][k] = sum_lam G[theta][lam] SSP[k][lam]
+// with G = dlnL/dY for young columns k and dlnL/dO for old ones; A = G
+// ([n][ldn], lambda-major), B = SSP ([Kpad][ldn], lambda-major); a 128 x 64
+// tile lies wholly in the young or the old block (Ky_pad is a multiple of 64).
+//
+// One CTA computes a 128 (theta) x BN tile (of Y and of O, or of dW).  Warp roles:
 //   warp 0 lane 0 : TMA producer (128B-swizzled K tiles into a STAGES-deep ring)
 //   warp 1 lane 0 : MMA issuer (tcgen05.mma into a ping-pong pair of tensor-memory
 //                   accumulators; a commit frees a smem stage / hands over a buffer)
-//   warps 2-5     : drain the accumulators into FP32 registers and store Y, O
+//   warps 2-5     : drain the accumulators into FP32 registers and store the tile
 //   warp 2        : also allocates / frees tensor memory
 // Precision:
 //   SED_PREC_FP32 : 3xTF32 split, D += A_lo B_hi + A_hi B_lo + A_hi B_hi
@@ -20,6 +26,8 @@
 // Every wait on an mbarrier is bounded (about 2 s of %globaltimer); on
 // timeout the kernel records an error bit in *err and returns after freeing
 // its tensor memory.
+#include <string.h>
+
 #include "sed_internal.cuh"
 
 namespace sed {
@@ -115,8 +123,11 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 struct Params {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
+  CUtensorMap a2_hi, a2_lo;  // adjoint: A operand of the old columns (dlnL/dO)
   int n, n_lam, ldn, ky_tiles, k_tiles;
-  float* Y;
+  int n_split;               // adjoint: first old column (Ky_pad)
+  int ld_out;                // row stride of the outputs
+  float* Y;                  // forward: Y [n][ld_out]; adjoint: dW [n][ld_out]
   float* O;
   int* err;
 };
@@ -124,7 +135,7 @@ struct Params {
 constexpr int BM = 128;
 constexpr int ROWB = 128;  // bytes of one operand row in a K tile
 
-template <int PREC, int BN, int STAGES, int G>
+template <int PREC, int BN, int STAGES, int G, bool GRAD = false>
 struct Cfg {
   static constexpr int A_BYTES = BM * ROWB;
   static constexpr int B_BYTES = BN * ROWB;
@@ -147,9 +158,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // per partial sum (24 for 3xTF32 with G = 2) instead of one per MMA of the
 // whole K loop, which keeps its rounding bias below FP32-grade accuracy; the
 // stores of Y also overlap the old-age main loop.
-template <int PREC, int BN, int STAGES, int G>
+template <int PREC, int BN, int STAGES, int G, bool GRAD>
 __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ Params p) {
-  using C = Cfg<PREC, BN, STAGES, G>;
+  using C = Cfg<PREC, BN, STAGES, G, GRAD>;
+  constexpr int NPART = GRAD ? 1 : 2;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * STAGES + 4];
   __shared__ uint32_t tmem_base_s;
@@ -182,7 +194,10 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
-  const int KT = p.k_tiles, KY = p.ky_tiles;
+  const int KT = p.k_tiles, KY = GRAD ? p.k_tiles : p.ky_tiles;
+  const CUtensorMap* amap_hi = &p.a_hi;
+  const CUtensorMap* amap_lo = &p.a_lo;
+  if (GRAD && n0 >= p.n_split) { amap_hi = &p.a2_hi; amap_lo = &p.a2_lo; }
 
   if (warp == 0) {
     if (lane == 0) {
@@ -195,10 +210,10 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         mbar_expect_tx(fb, C::STAGE_BYTES);
         const uint32_t st = sbase + s * C::STAGE_BYTES;
         const int kc = PREC == SED_PREC_FP32 ? kt * 32 : kt * 64;  // element coordinate along K
-        tma_load_2d(st, &p.a_hi, fb, kc, m0);
+        tma_load_2d(st, amap_hi, fb, kc, m0);
         tma_load_2d(st + C::A_BYTES, &p.b_hi, fb, kc, n0);
         if constexpr (C::NOPS == 2) {
-          tma_load_2d(st + C::A_BYTES + C::B_BYTES, &p.a_lo, fb, kc, m0);
+          tma_load_2d(st + C::A_BYTES + C::B_BYTES, amap_lo, fb, kc, m0);
           tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &p.b_lo, fb, kc, n0);
         }
       }
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       constexpr uint32_t ID = idesc(PREC == SED_PREC_FP32 ? 2u : 1u, BM, BN);
       int g = 0, kt = 0;
       bool ok = true;
-      for (int part = 0; part < 2 && ok; ++part) {
+      for (int part = 0; part < NPART && ok; ++part) {
         const int kb = part ? KY : 0, ke = part ? KT : KY;
         for (int gs = kb; gs < ke && ok; gs += G, ++g) {
           const int b = g & 1;
@@ -252,7 +267,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     int g = 0;
     bool ok = true;
-    for (int part = 0; part < 2; ++part) {
+    for (int part = 0; part < NPART; ++part) {
       const int kb = part ? KY : 0, ke = part ? KT : KY;
       float run[BN];
 #pragma unroll
@@ -276,7 +291,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
       if (row < p.n) {
-        float4* dst = reinterpret_cast<float4*>((part ? p.O : p.Y) + (size_t)row * p.ldn + n0);
+        float4* dst = reinterpret_cast<float4*>((part ? p.O : p.Y) + (size_t)row * p.ld_out + n0);
 #pragma unroll
         for (int j = 0; j < BN / 4; ++j) dst[j] = make_float4(run[4 * j], run[4 * j + 1], run[4 * j + 2], run[4 * j + 3]);
       }
@@ -290,17 +305,17 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   }
 }
 
-template <int PREC, int BN, int STAGES, int G>
-cudaError_t launch_cfg(const Params& p, cudaStream_t s) {
-  using C = Cfg<PREC, BN, STAGES, G>;
-  auto k = k_contract_tc<PREC, BN, STAGES, G>;
+template <int PREC, int BN, int STAGES, int G, bool GRAD>
+cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
+  using C = Cfg<PREC, BN, STAGES, G, GRAD>;
+  auto k = k_contract_tc<PREC, BN, STAGES, G, GRAD>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(p.ldn / BN, (p.n + BM - 1) / BM);
+  dim3 grid(n_cols / BN, (p.n + BM - 1) / BM);
   k<<<grid, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
 }
@@ -343,17 +358,47 @@ int tc_encode_maps(void* fn, TcMaps* out, int prec, const void* a_hi, const void
 
 cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   tc::Params p;
+  memset(&p, 0, sizeof p);
   p.a_hi = a.maps->a_hi; p.a_lo = a.maps->a_lo; p.b_hi = a.maps->b_hi; p.b_lo = a.maps->b_lo;
-  p.n = a.n; p.n_lam = a.n_lam; p.ldn = a.ldn;
+  p.n = a.n; p.n_lam = a.n_lam; p.ldn = a.ldn; p.ld_out = a.ldn;
   p.Y = a.Y; p.O = a.O; p.err = a.err;
   if (a.prec == SED_PREC_FP32) {
     p.ky_tiles = a.Ky_pad / 32;
     p.k_tiles = a.Kpad / 32;
-    return tc::launch_cfg<SED_PREC_FP32, TC_BN, 3, 2>(p, s);
+    return tc::launch_cfg<SED_PREC_FP32, TC_BN, 3, 2, false>(p, a.ldn, s);
   }
   p.ky_tiles = a.Ky_pad / 64;
   p.k_tiles = a.Kpad / 64;
-  return tc::launch_cfg<SED_PREC_BF16, TC_BN, 6, 4>(p, s);
+  return tc::launch_cfg<SED_PREC_BF16, TC_BN, 6, 4, false>(p, a.ldn, s);
+}
+
+constexpr int DW_BN = 64;
+
+int tc_encode_dw_maps(void* fn, DwMaps* out, const float* gy_hi, const float* gy_lo, const float* go_hi,
+                      const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int ldg, int ldk, int kpad) {
+  const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  if (encode_kmajor(fn, &out->gy_hi, (void*)gy_hi, dt, 4, ldg, n, tc::BM) != CUDA_SUCCESS) return 1;
+  if (encode_kmajor(fn, &out->gy_lo, (void*)gy_lo, dt, 4, ldg, n, tc::BM) != CUDA_SUCCESS) return 2;
+  if (encode_kmajor(fn, &out->go_hi, (void*)go_hi, dt, 4, ldg, n, tc::BM) != CUDA_SUCCESS) return 3;
+  if (encode_kmajor(fn, &out->go_lo, (void*)go_lo, dt, 4, ldg, n, tc::BM) != CUDA_SUCCESS) return 4;
+  if (encode_kmajor(fn, &out->s_hi, (void*)sk_hi, dt, 4, ldk, kpad, DW_BN) != CUDA_SUCCESS) return 5;
+  if (encode_kmajor(fn, &out->s_lo, (void*)sk_lo, dt, 4, ldk, kpad, DW_BN) != CUDA_SUCCESS) return 6;
+  return 0;
+}
+
+cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s) {
+  tc::Params p;
+  memset(&p, 0, sizeof p);
+  p.a_hi = a.maps->gy_hi; p.a_lo = a.maps->gy_lo;
+  p.a2_hi = a.maps->go_hi; p.a2_lo = a.maps->go_lo;
+  p.b_hi = a.maps->s_hi; p.b_lo = a.maps->s_lo;
+  p.n = a.n; p.n_lam = a.ldk; p.ldn = a.ldk;
+  p.k_tiles = a.ldk / 32;
+  p.ky_tiles = p.k_tiles;
+  p.n_split = a.Ky_pad;
+  p.ld_out = a.Kpad;
+  p.Y = a.dW; p.O = nullptr; p.err = a.err;
+  return tc::launch_cfg<SED_PREC_FP32, DW_BN, 4, 2, true>(p, a.Kpad, s);
 }
 
 }  // namespace sed

@@ -15,36 +15,12 @@
 //
 // All reductions run in a fixed order, so the result is bitwise reproducible.
 #include "sed_internal.cuh"
+#include "locate.cuh"
 
 namespace sed {
 
 constexpr int EPI_THREADS = 256;
 constexpr int MAX_BANDS = 128;
-
-// last node k with lam[k] <= x (lam ascending), for lam[0] <= x <= lam[n-1];
-// clamped to n-2 so that k+1 is a valid node.
-__device__ __forceinline__ int locate_ln(const GridDev& g, float lnx, const float* lnl_hi) {
-  int q = (int)((lnx - g.lut_x0) * g.lut_inv_h);
-  q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
-  int k = g.lut[q];
-  const int top = g.n_lam - 2;
-  k = k > top ? top : k;
-#pragma unroll 1
-  for (int it = 0; it < 4 && k < top && lnl_hi[k + 1] <= lnx; ++it) ++k;
-#pragma unroll 1
-  for (int it = 0; it < 4 && k > 0 && lnl_hi[k] > lnx; ++it) --k;
-  return k;
-}
-
-__device__ __forceinline__ int locate_lin(const GridDev& g, float x) {
-  int k = locate_ln(g, logf(x), g.lnl_hi);
-  const int top = g.n_lam - 2;
-#pragma unroll 1
-  for (int it = 0; it < 4 && k < top && g.lam_f[k + 1] <= x; ++it) ++k;
-#pragma unroll 1
-  for (int it = 0; it < 4 && k > 0 && g.lam_f[k] > x; ++it) --k;
-  return k;
-}
 
 __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant__ EpiArgs a) {
   const ModelDev& md = a.md;

@@ -35,6 +35,25 @@ __device__ __forceinline__ void bracket_f(const float* x, int n, float v, int& j
   j0 = j; j1 = j + 1; w0 = 1.f - t; w1 = t;
 }
 
+// derivatives of the two bracket weights with respect to v (0 when clamped)
+__device__ __forceinline__ void bracket_df(const float* x, int n, float v, int j0, int j1, float& d0, float& d1) {
+  d0 = d1 = 0.f;
+  if (n > 1 && v > x[0] && v < x[n - 1]) {
+    const float h = x[j1] - x[j0];
+    d0 = -1.f / h;
+    d1 = 1.f / h;
+  }
+}
+
+// SFH edges of one row (FP32): 0, 5 Myr, 10 Myr, then log-uniform to T_max.
+__device__ __forceinline__ float sfh_edge(int i, int NT, double tmax, float lrat) {
+  if (i == 0) return 0.f;
+  if (i == 1) return 5e6f;
+  if (i == 2) return 1e7f;
+  if (i == NT) return (float)tmax;
+  return 1e7f * expf(lrat * (float)(i - 2) / (float)(NT - 2));
+}
+
 struct PrepKernelArgs {
   PrepArgs p;
   double gl_x[GL_NODES];
@@ -72,30 +91,38 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
   if (!status && !(z >= 0.f && (double)z < md.zf)) status = SED_ROW_BAD_Z;
 
-  // ---- cosmology in FP64 (warp 0)
+  // ---- cosmology in FP64 (warp 0).  GB300's FP64 pipe is narrow, so the FP64
+  //      work per row is kept to the quadrature (one node per lane) and a few
+  //      scalar operations: closed forms are rewritten with sqrt / rsqrt / log
+  //      and the constants of the model are folded on the host.
+  __shared__ float s_lrat;
   if (!status && warp == 0) {
     const double zp = 1.0 + (double)z;
     const double Om = md.Om0, OL = 1.0 - md.Om0;
-    const double u0 = 1.0 / sqrt(zp);
+    const double u0 = rsqrt(zp);
     const double half = 0.5 * (1.0 - u0), mid = 0.5 * (1.0 + u0);
     double acc = 0.0;
     for (int i = lane; i < GL_NODES; i += 32) {
-      double u = mid + half * ka.gl_x[i];
-      double u2 = u * u;
-      acc += ka.gl_w[i] * 2.0 / sqrt(Om + OL * u2 * u2 * u2);
+      const double u = mid + half * ka.gl_x[i];
+      const double u2 = u * u;
+      acc += ka.gl_w[i] * rsqrt(Om + OL * u2 * u2 * u2);
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
-      const double dc = md.dh_cm * half * acc;
+      const double dc = 2.0 * md.dh_cm * half * acc;
       const double ez = sqrt(Om * zp * zp * zp + OL);
-      const double t = md.th_yr * 2.0 / (3.0 * sqrt(OL)) * asinh(sqrt(OL / Om) * pow(zp, -1.5));
+      // t_univ = (2/(3 H0 sqrt(OL))) asinh(sqrt(OL/Om) (1+z)^-3/2), asinh(x) = ln(x + sqrt(x^2 + 1))
+      const double x = md.asinh_c * u0 * u0 * u0;
+      const double t = md.t_c * log(x + sqrt(x * x + 1.0));
       double dl = zp * dc;
       double ddl = dc + zp * md.dh_cm / ez;  // dD_L/dz
       if (dl < 10.0 * PC_CM) { dl = 10.0 * PC_CM; ddl = 0.0; }
+      const double tmx = t - md.t_zf_yr;
       s_cos[0] = dl;
-      s_cos[1] = t - md.t_zf_yr;                  // T_max
+      s_cos[1] = tmx;                             // T_max
       s_cos[2] = ddl / dl;                        // dlnD_L/dz
       s_cos[3] = -md.th_yr / (zp * ez);           // dt/dz
+      s_lrat = tmx > 1e7 ? (float)log(tmx * 1e-7) : 0.f;
     }
   }
   __syncthreads();
@@ -124,16 +151,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   // ---- SFH edges (FP32) and per-bin quantities
   const float* m = th + md.offs[SED_KEY_SFH];
   const float* zeta = th + md.offs[SED_KEY_LOGZSOL];
-  const float lrat = (float)log(tmax / 1e7);
-  for (int i = tid; i <= NT; i += blockDim.x) {
-    float v;
-    if (i == 0) v = 0.f;
-    else if (i == 1) v = 5e6f;
-    else if (i == 2) v = 1e7f;
-    else if (i == NT) v = (float)tmax;
-    else v = 1e7f * expf(lrat * (float)(i - 2) / (float)(NT - 2));
-    T[i] = v;
-  }
+  const float lrat = s_lrat;
+  for (int i = tid; i <= NT; i += blockDim.x) T[i] = sfh_edge(i, NT, tmax, lrat);
   for (int j = tid; j < NA * NZ; j += blockDim.x) Ws[j] = 0.f;
   __syncthreads();
   for (int i = tid; i < NT; i += blockDim.x) {
@@ -209,14 +228,14 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     const double zp = 1.0 + (double)z;
     const double logmass = (double)th[md.offs[SED_KEY_LOGMASS]];
     const double dl = s_cos[0];
-    // s = 10^logmass Lsun (1+z) / (4 pi D_L^2), in device flux units (x 2^-f_log2)
-    const double ls = logmass * 3.321928094887362 + log2(LSUN * zp / (4.0 * M_PI)) - 2.0 * log2(dl) - md.f_log2;
-    const double s = exp2(ls);
+    // s = 10^logmass Lsun (1+z) / (4 pi D_L^2), in device flux units (x 2^-f_log2);
+    // md.lsun_c = Lsun 2^-f_log2 / (4 pi)
+    const double s = exp(logmass * 2.302585092994046) * md.lsun_c * zp / (dl * dl);
     RowScal rs{};
     rs.p_phot = (float)(C_AA * s / (zp * zp));
     rs.s_spec = (float)s;
     rs.inv1pz = (float)(1.0 / zp);
-    const double l1 = log1p((double)z);
+    const double l1 = log(zp);
     rs.ln1pz_hi = (float)l1;
     rs.ln1pz_lo = (float)(l1 - (double)rs.ln1pz_hi);
     rs.tau_bc = th[md.offs[SED_KEY_TAU_POW]];
@@ -234,11 +253,17 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       rs.neb_w[1] = wu0 * wz1; rs.neb_off[1] = (u0 * md.neb_nz + z1) * nl;
       rs.neb_w[2] = wu1 * wz0; rs.neb_off[2] = (u1 * md.neb_nz + z0) * nl;
       rs.neb_w[3] = wu1 * wz1; rs.neb_off[3] = (u1 * md.neb_nz + z1) * nl;
+      float du0, du1, dz0, dz1;
+      bracket_df(md.neb_logu, md.neb_nu, th[md.offs[SED_KEY_GAS_LOGU]], u0, u1, du0, du1);
+      bracket_df(md.neb_logz, md.neb_nz, th[md.offs[SED_KEY_GAS_LOGZ]], z0, z1, dz0, dz1);
+      rs.neb_dwu[0] = du0 * wz0; rs.neb_dwu[1] = du0 * wz1; rs.neb_dwu[2] = du1 * wz0; rs.neb_dwu[3] = du1 * wz1;
+      rs.neb_dwz[0] = wu0 * dz0; rs.neb_dwz[1] = wu0 * dz1; rs.neb_dwz[2] = wu1 * dz0; rs.neb_dwz[3] = wu1 * dz1;
     }
     rs.dlns_dz = (float)(1.0 / zp - 2.0 * s_cos[2]);
     rs.dlnp_dz = (float)(-1.0 / zp - 2.0 * s_cos[2]);
     rs.dtmax_dz = (float)s_cos[3];
     rs.tmax = (float)tmax;
+    rs.lrat = lrat;
     rs.status = 0;
     rs.k_lo = 0;
     rs.k_hi = g.n_lam;
@@ -246,6 +271,175 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     for (int w = 0; w < PREP_THREADS / 32; ++w) rs.nnz += s_nnz[w];
     *out = rs;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the weights (App. B step scheme, metallicity and [a/Fe] splits)
+// and assembly of the gradient row.  One CTA per row.  Input: dlnL/dW from the
+// adjoint contraction, dlnL/dQ_young and the other per-row scalar pieces from
+// the adjoint epilogue.  W_k = w_n(afe) Ws[a][m], Ws[a][m] = sum_i A_ia w_m(zeta_i),
+// A_ia = m_i |bin_i ∩ cell_a| / dT_i, with the edges T_i (i >= 3) following T_max(z).
+constexpr int PREP_BWD_THREADS = 128;
+
+__global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_constant__ PrepBwdArgs a) {
+  const ModelDev& md = a.md;
+  const GridDev& g = a.g;
+  const LayoutDev& L = a.L;
+  const int r = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* th = a.theta + (size_t)r * a.ld;
+  float* out = a.grad + (size_t)r * a.ld;
+  const int NT = md.n_sfh, NA = g.n_age, NZ = g.n_feh;
+  const RowScal rs = a.rs[r];
+  if (rs.status || a.rgrad[(size_t)r * RGRAD + RG_BAD] != 0.0) {
+    for (int j = tid; j < a.ld; j += blockDim.x) out[j] = 0.f;
+    return;
+  }
+  extern __shared__ float smem[];
+  float* Ws = smem;               // [NA][NZ] forward Ws
+  float* gWs = smem + NA * NZ;    // [NA][NZ] dlnL/dWs
+  __shared__ float T[MAX_SFH + 1];
+  __shared__ int zb[MAX_SFH];
+  __shared__ float zt[MAX_SFH], zd0[MAX_SFH], zd1[MAX_SFH];
+  __shared__ float gTlo[MAX_SFH], gThi[MAX_SFH], gzeta[MAX_SFH];
+  __shared__ double red[PREP_BWD_THREADS / 32];
+  __shared__ double s_tmax_part[PREP_BWD_THREADS / 32];
+
+  const float* m = th + md.offs[SED_KEY_SFH];
+  const float* zeta = th + md.offs[SED_KEY_LOGZSOL];
+  const double tmax = (double)rs.tmax;
+  const float lrat = rs.lrat;   // the forward's edges, bit for bit
+  for (int i = tid; i <= NT; i += blockDim.x) T[i] = sfh_edge(i, NT, tmax, lrat);
+  for (int j = tid; j < NA * NZ; j += blockDim.x) Ws[j] = 0.f;
+  __syncthreads();
+  for (int i = tid; i < NT; i += blockDim.x) {
+    int j0, j1;
+    float w0, w1, d0, d1;
+    const float v = zeta[md.zmode == 0 ? i : 0];
+    bracket_f(md.feh, md.n_feh, v, j0, w0, j1, w1);
+    bracket_df(md.feh, md.n_feh, v, j0, j1, d0, d1);
+    zb[i] = j0;
+    zt[i] = w1;
+    zd0[i] = d0;
+    zd1[i] = d1;
+  }
+  __syncthreads();
+  // forward Ws (needed for the [a/Fe] derivative), thread per age node as in k_prep
+  for (int ag = tid; ag < NA; ag += blockDim.x) {
+    const float lo = g.cell_lo[ag], hi = g.cell_hi[ag];
+    int i0 = 0, i1 = NT;
+    while (i0 < i1) {
+      int mid = (i0 + i1) >> 1;
+      if (T[mid + 1] > lo) i1 = mid; else i0 = mid + 1;
+    }
+    float* row = Ws + ag * NZ;
+    for (int i = i0; i < NT && T[i] < hi; ++i) {
+      float ov = fminf(T[i + 1], hi) - fmaxf(T[i], lo);
+      if (ov <= 0.f) continue;
+      float A = m[i] / (T[i + 1] - T[i]) * ov;
+      row[zb[i]] += A * (1.f - zt[i]);
+      if (NZ > 1) row[zb[i] + 1] += A * zt[i];
+    }
+  }
+  // [a/Fe] bracket
+  int n0 = 0, n1 = 0;
+  float wn0 = 1.f, wn1 = 0.f, dn0 = 0.f, dn1 = 0.f;
+  if (md.n_afe > 1) {
+    const float afe = md.use_afe ? th[md.offs[SED_KEY_AFE]] : 0.f;
+    bracket_f(md.afe, md.n_afe, afe, n0, wn0, n1, wn1);
+    if (md.use_afe) bracket_df(md.afe, md.n_afe, afe, n0, n1, dn0, dn1);
+  }
+  __syncthreads();
+  // dlnL/dWs[a][m] and the [a/Fe] derivative; column k of (n, m, a) in the layout
+  const float* dW = a.dW + (size_t)r * L.Kpad;
+  const float gqy = (float)a.rgrad[(size_t)r * RGRAD + RG_QY];
+  const int n_old = NA - L.n_young;
+  float gafe = 0.f;
+  for (int j = tid; j < NA * NZ; j += blockDim.x) {
+    const int ag = j / NZ, mm = j % NZ;
+    const bool young = ag < L.n_young;
+    float gv[2];
+    const int nn[2] = {n0, n1};
+    for (int q = 0; q < 2; ++q) {
+      const int k = young ? (nn[q] * NZ + mm) * L.n_young + ag : L.Ky_pad + (nn[q] * NZ + mm) * n_old + (ag - L.n_young);
+      gv[q] = dW[k] + (young ? gqy * L.q_s[k] : 0.f);
+    }
+    gWs[j] = (n1 != n0) ? gv[0] * wn0 + gv[1] * wn1 : gv[0] * wn0;
+    if (n1 != n0) gafe += Ws[j] * (gv[0] * dn0 + gv[1] * dn1);
+  }
+  __syncthreads();
+  // thread per SFH bin: dlnL/dm_i, dlnL/dzeta_i and the edge derivatives
+  for (int i = tid; i < NT; i += blockDim.x) {
+    const float Ti = T[i], Ti1 = T[i + 1], dT = Ti1 - Ti;
+    // first age whose cell reaches above T_i
+    int a0 = 0, a1 = NA;
+    while (a0 < a1) {
+      int mid = (a0 + a1) >> 1;
+      if (g.cell_hi[mid] > Ti) a1 = mid; else a0 = mid + 1;
+    }
+    float gm = 0.f, gz = 0.f, glo = 0.f, ghi = 0.f;
+    const int j0 = zb[i];
+    const float t = zt[i];
+    for (int ag = a0; ag < NA && g.cell_lo[ag] < Ti1; ++ag) {
+      const float lo = g.cell_lo[ag], hi = g.cell_hi[ag];
+      const float ov = fminf(Ti1, hi) - fmaxf(Ti, lo);
+      if (ov <= 0.f) continue;
+      const float A = m[i] / dT * ov;
+      const float g0 = gWs[ag * NZ + j0];
+      const float g1 = NZ > 1 ? gWs[ag * NZ + j0 + 1] : 0.f;
+      const float gA = g0 * (1.f - t) + g1 * t;
+      gz += A * (g0 * zd0[i] + g1 * zd1[i]);
+      gm += gA * ov / dT;
+      ghi += gA * m[i] * ((Ti1 < hi ? 1.f : 0.f) / dT - ov / (dT * dT));
+      glo += gA * m[i] * (-(Ti > lo ? 1.f : 0.f) / dT + ov / (dT * dT));
+    }
+    out[md.offs[SED_KEY_SFH] + i] = gm;
+    gzeta[i] = gz;
+    gTlo[i] = glo;
+    gThi[i] = ghi;
+  }
+  __syncthreads();
+  // T_max(z) path: dT_i/dT_max = T_i (i-2) / ((N_T-2) T_max) for i >= 3
+  double part = 0.0;
+  for (int i = 3 + tid; i <= NT; i += blockDim.x) {
+    const float gT = gThi[i - 1] + (i < NT ? gTlo[i] : 0.f);
+    part += (double)gT * (double)T[i] * (double)(i - 2) / ((double)(NT - 2) * tmax);
+  }
+  double ga = (double)gafe;
+  for (int o = 16; o; o >>= 1) {
+    part += __shfl_xor_sync(0xffffffffu, part, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  if (lane == 0) { s_tmax_part[warp] = part; red[warp] = ga; }
+  __syncthreads();
+  if (tid == 0) {
+    double gtmax = 0.0, gafe_t = 0.0;
+    for (int w = 0; w < PREP_BWD_THREADS / 32; ++w) { gtmax += s_tmax_part[w]; gafe_t += red[w]; }
+    const double* rg = a.rgrad + (size_t)r * RGRAD;
+    if (md.zmode == 1) {
+      double gzs = 0.0;
+      for (int i = 0; i < NT; ++i) gzs += (double)gzeta[i];
+      out[md.offs[SED_KEY_LOGZSOL]] = (float)gzs;
+    }
+    out[md.offs[SED_KEY_AFE]] = md.use_afe ? (float)gafe_t : 0.f;
+    out[md.offs[SED_KEY_LOGMASS]] = (float)rg[RG_LOGMASS];
+    out[md.offs[SED_KEY_ZRED]] = (float)(rg[RG_Z] + gtmax * (double)rs.dtmax_dz);
+    out[md.offs[SED_KEY_TAU_POW]] = (float)rg[RG_TAU_BC];
+    out[md.offs[SED_KEY_ALPHA_POW]] = (float)rg[RG_ALPHA_BC];
+    out[md.offs[SED_KEY_DIFFUSE_TAU]] = (float)rg[RG_TAU_D];
+    out[md.offs[SED_KEY_DIFFUSE_INDEX]] = (float)rg[RG_DELTA];
+    out[md.offs[SED_KEY_GAS_LOGZ]] = md.use_neb ? (float)rg[RG_GAS_LOGZ] : 0.f;
+    out[md.offs[SED_KEY_GAS_LOGU]] = md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f;
+  }
+  if (md.zmode == 0)
+    for (int i = tid; i < NT; i += blockDim.x) out[md.offs[SED_KEY_LOGZSOL] + i] = gzeta[i];
+  for (int j = md.n_param + tid; j < a.ld; j += blockDim.x) out[j] = 0.f;
+}
+
+cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
+  const size_t smem = (size_t)2 * p.g.n_age * p.g.n_feh * sizeof(float);
+  k_prep_bwd<<<p.n, PREP_BWD_THREADS, smem, s>>>(p);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {

@@ -177,7 +177,8 @@ sed_status sed_destroy(sed_ctx* ctx) {
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
       std::vector<void*> v = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
-                              w->theta_h, w->lnl_h, w->st_h, w->G, w->GO, w->dW, w->rgrad};
+                              w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
+                              w->dW, w->rgrad};
       for (void* p : v)
         if (p) cudaFree(p);
       for (cudaEvent_t e : w->ev)
@@ -346,6 +347,41 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
 // ---------------------------------------------------------------------------
 namespace {
 
+// Device-scaled SSP flux of layout column k at node l (0 for padding columns
+// and, with nebular emission, for young ages below 912 A).
+float ssp_value(const Grid* g, const Layout* L, int k, int l) {
+  const int c = L->code_h[k];
+  if (c < 0) return 0.f;
+  const int n = c >> 24, m = (c >> 16) & 0xff, a = c & 0xffff;
+  if (L->neb_cut && a < L->n_young && g->lam[l] < LYMAN_AA) return 0.f;
+  return (float)(g->flux[(((size_t)n * g->n_feh + m) * g->n_age + a) * g->n_lam + l] * std::exp2(g->f_log2));
+}
+
+// Lambda-major copies of a layout for the adjoint contraction: [Kpad][ldn].
+sed_status ensure_grad_layout(sed_ctx* ctx, Grid* g, Layout* L, int ldn) {
+  if (L->sspK_f32) return SED_OK;
+  const int Kpad = L->Kpad, NL = g->n_lam;
+  std::vector<float> f32((size_t)Kpad * ldn, 0.f), hi((size_t)Kpad * ldn, 0.f), lo((size_t)Kpad * ldn, 0.f);
+  for (int k = 0; k < Kpad; k++)
+    for (int l = 0; l < NL; l++) {
+      const float v = ssp_value(g, L, k, l);
+      const size_t o = (size_t)k * ldn + l;
+      f32[o] = v;
+      hi[o] = tf32_rna_host(v);
+      lo[o] = v - hi[o];
+    }
+  float *a = nullptr, *b = nullptr, *c = nullptr;
+  sed_status st = upload(ctx, &a, f32.data(), f32.size(), &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &b, hi.data(), hi.size(), &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &c, lo.data(), lo.size(), &g->allocs, &g->bytes);
+  if (st) return st;
+  L->ldn = ldn;
+  L->sspK_f32 = a;
+  L->sspK_hi = b;
+  L->sspK_lo = c;
+  return SED_OK;
+}
+
 // Layout of the grid for a given number of birth-cloud ages and 912 A removal.
 sed_status get_layout(sed_ctx* ctx, Grid* g, int n_young, int neb_cut, Layout** out) {
   for (Layout* L : g->layouts)
@@ -378,18 +414,12 @@ sed_status get_layout(sed_ctx* ctx, Grid* g, int n_young, int neb_cut, Layout** 
   sed_status st = upload(ctx, &L->k_code, code.data(), Kpad, &g->allocs, &g->bytes);
   if (!st) st = upload(ctx, &L->q_s, qs.data(), Kpad, &g->allocs, &g->bytes);
   // SSP^T [lam][k], scaled by 2^f_log2, in FP32, TF32 hi/lo and BF16
-  const double sc = std::exp2(g->f_log2);
+  L->code_h = code;
   std::vector<float> f32((size_t)NL * Kpad), hi((size_t)NL * Kpad), lo((size_t)NL * Kpad);
   std::vector<__nv_bfloat16> bf((size_t)NL * Kpad);
   for (int k = 0; k < Kpad; k++) {
-    const int c = code[k];
     for (int l = 0; l < NL; l++) {
-      float v = 0.f;
-      if (c >= 0) {
-        const int n = c >> 24, m = (c >> 16) & 0xff, a = c & 0xffff;
-        const bool cut = neb_cut && a < n_young && g->lam[l] < LYMAN_AA;
-        if (!cut) v = (float)(g->flux[(((size_t)n * NZ + m) * NA + a) * NL + l] * sc);
-      }
+      const float v = ssp_value(g, L, k, l);
       const size_t o = (size_t)l * Kpad + k;
       f32[o] = v;
       const float h = tf32_rna_host(v);
@@ -518,6 +548,9 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   dv.dh_cm = C_KMS / d->H0 * 1e6 * PC_CM;
   dv.th_yr = MPC_KM / d->H0 / YR_S;
   dv.t_zf_yr = t_univ_yr(dv.th_yr, d->Om0, d->zf);
+  dv.asinh_c = std::sqrt((1.0 - d->Om0) / d->Om0);
+  dv.t_c = dv.th_yr * 2.0 / (3.0 * std::sqrt(1.0 - d->Om0));
+  dv.lsun_c = LSUN * std::exp2(-g->f_log2) / (4.0 * M_PI);
   dv.f_log2 = g->f_log2;
   dv.q_log2 = g->q_log2;
   dv.n_feh = g->n_feh; dv.n_afe = g->n_afe;
@@ -686,7 +719,8 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
   std::vector<void*> old = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
-                            w->theta_h, w->lnl_h, w->st_h, w->G, w->GO, w->dW, w->rgrad};
+                            w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
+                            w->dW, w->rgrad};
   for (void* p : old)
     if (p) cudaFree(p);
   ctx->used -= std::min(ctx->used, w->bytes);
@@ -704,7 +738,10 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2);
   AL(Y, R * N * 4); AL(O, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
   AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
-  if (grad || had_grad) { AL(G, R * N * 4); AL(GO, R * N * 4); AL(dW, R * K * 4); AL(rgrad, R * 64 * 4); }
+  if (grad || had_grad) {
+    AL(G_hi, R * N * 4); AL(G_lo, R * N * 4); AL(GO_hi, R * N * 4); AL(GO_lo, R * N * 4);
+    AL(dW, R * K * 4); AL(rgrad, R * RGRAD * 8);
+  }
 #undef AL
   if (!s) {
     cudaError_t e = cudaMemset(w->err, 0, 64);
@@ -856,10 +893,65 @@ sed_status sed_loglike_host(sed_ctx* ctx, sed_model_id id, const float* theta, i
 
 sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
                             float* grad_out, uint32_t* row_status, int precision, void* stream) {
-  (void)theta; (void)n; (void)ld; (void)lnl_out; (void)grad_out; (void)row_status; (void)precision; (void)stream;
   if (!ctx) return SED_EINVAL;
-  if (!find_model(ctx, id)) return fail(ctx, SED_EINVAL, "unknown model");
-  return fail(ctx, SED_EUNSUPPORTED, "gradient not available in this build");
+  Model* M = find_model(ctx, id);
+  sed_status st = check_hot_args(ctx, M, theta, n, ld, precision);
+  if (st) return st;
+  if (precision == SED_PREC_BF16)
+    return fail(ctx, SED_EUNSUPPORTED, "the gradient is available for SED_PREC_FP32 and SED_PREC_FP32_SIMT");
+  if (n > 0 && (!lnl_out || !grad_out)) return fail(ctx, SED_EINVAL, "lnl_out or grad_out is NULL");
+  if (n == 0) return SED_OK;
+  DevGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Grid* g = M->g;
+  Layout* L = M->L;
+  const int ldn = ldn_for(g);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    st = ensure_grad_layout(ctx, g, L, ldn);
+  }
+  if (st) return st;
+  Workspace* w = get_ws(ctx, stream, n, L->Kpad, ldn, true, &st);
+  if (!w) return st;
+  st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
+  if (st) return st;
+  const bool f32 = precision == SED_PREC_FP32;
+  EpiBwdArgs eb{};
+  eb.n = n; eb.ldn = w->ldn; eb.Y = w->Y; eb.O = w->O; eb.rs = w->rs;
+  eb.md = M->dv; eb.g = g->dv; eb.split = f32 ? 1 : 0;
+  eb.gy_hi = w->G_hi; eb.gy_lo = w->G_lo; eb.go_hi = w->GO_hi; eb.go_lo = w->GO_lo;
+  eb.rgrad = w->rgrad; eb.lnl = lnl_out; eb.status = row_status; eb.err = w->err;
+  size_t smem = 0;
+  cudaError_t e = launch_epilogue_bwd(eb, &smem, s);
+  if (e == cudaErrorInvalidConfiguration && smem > 227 * 1024)
+    return fail(ctx, SED_ERANGE, "adjoint epilogue needs %zu bytes of shared memory (max 227 KB)", smem);
+  CK(e);
+  if (f32) {
+    if (!w->dw_maps_valid || w->dw_maps_for != (const void*)L || w->dw_maps_n != n || w->dw_maps_g != w->G_hi) {
+      int ee = tc_encode_dw_maps(ctx->encode_fn, &w->dw_maps, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo, L->sspK_hi,
+                                 L->sspK_lo, n, w->ldn, L->ldn, L->Kpad);
+      if (ee) return fail(ctx, SED_ECUDA, "cuTensorMapEncodeTiled failed (adjoint operand %d)", ee);
+      w->dw_maps_valid = true;
+      w->dw_maps_for = L;
+      w->dw_maps_n = n;
+      w->dw_maps_g = w->G_hi;
+    }
+    DwArgs da{};
+    da.n = n; da.ldk = L->ldn; da.Ky_pad = L->Ky_pad; da.Kpad = L->Kpad;
+    da.maps = &w->dw_maps; da.dW = w->dW; da.err = w->err;
+    CK(launch_dw_tc(da, s));
+  } else {
+    DwSimtArgs da{};
+    da.n = n; da.ldg = w->ldn; da.ldk = L->ldn; da.Ky_pad = L->Ky_pad; da.Kpad = L->Kpad;
+    da.gy = w->G_hi; da.go = w->GO_hi; da.sspK = L->sspK_f32; da.dW = w->dW;
+    CK(launch_dw_simt(da, s));
+  }
+  PrepBwdArgs pb{};
+  pb.theta = theta; pb.n = n; pb.ld = ld;
+  pb.md = M->dv; pb.g = g->dv; pb.L = L->dv();
+  pb.rs = w->rs; pb.dW = w->dW; pb.rgrad = w->rgrad; pb.grad = grad_out;
+  CK(launch_prep_bwd(pb, s));
+  return prof_mark(ctx, w, 3, s);
 }
 
 sed_status sed_set_profiling(sed_ctx* ctx, int on) {

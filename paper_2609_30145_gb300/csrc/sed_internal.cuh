@@ -51,10 +51,13 @@ struct RowScal {
   float log2_qy;    // log2(Q_young, device units) (-inf when Q_young = 0)
   float neb_w[4];   // bilinear weights of the nebular template corners
   int neb_off[4];   // corner offsets (rows of the template)
+  float neb_dwu[4]; // d neb_w / d gas_logu (adjoint)
+  float neb_dwz[4]; // d neb_w / d gas_logz (adjoint)
   float dlnp_dz;    // d ln(p_phot)/dz (adjoint)
   float dlns_dz;    // d ln(s_spec)/dz (adjoint)
   float dtmax_dz;   // dT_max/dz in yr (adjoint)
   float tmax;       // yr
+  float lrat;       // ln(T_max / 10 Myr) as used for the SFH edges
   uint32_t status;
   int k_lo, k_hi;   // rest-frame node window this row needs
   int nnz;          // non-zero weights of the row
@@ -90,6 +93,8 @@ struct ModelDev {
   int n_sfh, zmode, use_afe, use_neb, dust_law, n_param;
   int offs[SED_NKEYS];
   double zf, t_zf_yr, dh_cm, th_yr, Om0;
+  double asinh_c, t_c;     // sqrt(OL/Om) and 2/(3 H0 sqrt(OL)) in yr (age of the Universe)
+  double lsun_c;           // Lsun 2^-f_log2 / (4 pi)
   double f_log2, q_log2;
   int n_feh, n_afe;
   float feh[MAX_FEH];
@@ -127,8 +132,15 @@ struct Layout {
   float* sspT_hi = nullptr;          // [n_lam][Kpad] TF32-rounded high part
   float* sspT_lo = nullptr;          // [n_lam][Kpad] low part (x - hi)
   __nv_bfloat16* sspT_bf16 = nullptr;
+  // adjoint copies, lambda-major: [Kpad][ldn] with ldn = n_lam rounded up to 256
+  // (zero beyond n_lam); built on the first gradient call
+  int ldn = 0;
+  float* sspK_f32 = nullptr;
+  float* sspK_hi = nullptr;
+  float* sspK_lo = nullptr;
   float* q_s = nullptr;              // [Kpad] scaled Q for young k, 0 elsewhere
   int* k_code = nullptr;             // [Kpad] packed (n<<24 | m<<16 | a), -1 for padding
+  std::vector<int> code_h;           // host copy of k_code
   double q_log2 = 0.0;               // Q_dev = Q * 2^-q_log2
   bool have_tmaps = false;
   CUtensorMap tm_hi, tm_lo, tm_bf16;
@@ -165,6 +177,17 @@ struct Model {
 struct TcMaps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
+// Operand maps of the adjoint contraction (A: dlnL/dY, dlnL/dO; B: SSP [k][lam]).
+struct DwMaps {
+  CUtensorMap gy_hi, gy_lo, go_hi, go_lo, s_hi, s_lo;
+};
+
+// Per-row scalar gradient pieces written by the adjoint epilogue.
+enum {
+  RG_TAU_BC = 0, RG_ALPHA_BC, RG_TAU_D, RG_DELTA, RG_GAS_LOGZ, RG_GAS_LOGU, RG_LOGMASS, RG_Z, RG_QY,
+  RG_BAD,   // non-zero: the row's likelihood is not finite (gradient row written as zeros)
+  RGRAD = 16
+};
 
 // Per-stream scratch.
 struct Workspace {
@@ -183,15 +206,22 @@ struct Workspace {
   uint32_t* st_h = nullptr;
   int ldn = 0;
   // adjoint
-  float* G = nullptr;            // [rows][ldn] dlnL/dY (young) then dlnL/dO
-  float* GO = nullptr;
-  float* dW = nullptr;           // [rows][Kpad]
-  float* rgrad = nullptr;        // [rows][16] per-row scalar gradient pieces
+  float* G_hi = nullptr;         // [rows][ldn] dlnL/dY (TF32 high part, or exact for FP32-SIMT)
+  float* G_lo = nullptr;         // [rows][ldn] low part
+  float* GO_hi = nullptr;        // [rows][ldn] dlnL/dO
+  float* GO_lo = nullptr;
+  float* dW = nullptr;           // [rows][Kpad] dlnL/dW
+  double* rgrad = nullptr;       // [rows][RGRAD] per-row scalar gradient pieces
+  bool dw_maps_valid = false;
+  const void* dw_maps_for = nullptr;
+  int dw_maps_n = -1;
+  const void* dw_maps_g = nullptr;
   size_t bytes = 0;
   bool tmap_valid = false;
   const void* tmap_for = nullptr;
   int tmap_n = -1, tmap_prec = -1;
   TcMaps maps;
+  DwMaps dw_maps;
   // profiling: events before/after prep, contraction, epilogue of the last call
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   int last_n = 0, last_prec = 0, last_kpad = 0, last_nlam = 0;
@@ -246,6 +276,17 @@ int tc_encode_maps(void* encode_fn, TcMaps* out, int prec, const void* a_hi, con
                    const void* b_hi, const void* b_lo, int n, int n_lam, int kpad);
 cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s);
 
+// Adjoint contraction dW = [G_Y SSP_young^T | G_O SSP_old^T] (3xTF32 on tcgen05).
+// G rows have stride ldg; SSP rows [Kpad][ldk] (ldk <= ldg is the reduction length).
+int tc_encode_dw_maps(void* encode_fn, DwMaps* out, const float* gy_hi, const float* gy_lo, const float* go_hi,
+                      const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int ldg, int ldk, int kpad);
+struct DwArgs {
+  int n, ldk, Ky_pad, Kpad;
+  const DwMaps* maps;
+  float* dW; int* err;
+};
+cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s);
+
 struct EpiArgs {
   int n; int ldn;
   const float* Y; const float* O;
@@ -256,5 +297,36 @@ struct EpiArgs {
   const int* err;      // device error word of the contraction (row status SED_ROW_DEVICE_TIMEOUT)
 };
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
+
+// ---- adjoint
+struct EpiBwdArgs {
+  int n; int ldn;
+  const float* Y; const float* O;
+  const RowScal* rs;
+  ModelDev md; GridDev g;
+  int split;            // 1: write G as TF32 hi/lo parts (3xTF32), 0: exact FP32 into *_hi
+  float* gy_hi; float* gy_lo; float* go_hi; float* go_lo;
+  double* rgrad;
+  double* lnl; uint32_t* status;
+  const int* err;
+};
+cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s);
+
+struct DwSimtArgs {
+  int n, ldg, ldk, Ky_pad, Kpad;
+  const float* gy; const float* go;   // [n][ldg]
+  const float* sspK;                  // [Kpad][ldk], ldk <= ldg: the reduction length
+  float* dW;                          // [n][Kpad]
+};
+cudaError_t launch_dw_simt(const DwSimtArgs& a, cudaStream_t s);
+
+struct PrepBwdArgs {
+  const float* theta; int n, ld;
+  ModelDev md; GridDev g; LayoutDev L;
+  const RowScal* rs;
+  const float* dW; const double* rgrad;
+  float* grad;          // [n][ld]
+};
+cudaError_t launch_prep_bwd(const PrepBwdArgs& a, cudaStream_t s);
 
 }  // namespace sed

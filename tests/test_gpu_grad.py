@@ -1,0 +1,152 @@
+"""GPU adjoint (sed_loglike_grad) against the FP64 oracle's analytic gradient
+and against central finite differences of the oracle's forward model, through
+the C ABI, element by element.
+
+Tolerance: the FP32 paths evaluate the model, and its derivatives, in FP32
+(3xTF32 or FFMA contractions, FP32 epilogue sums, FP64 final sums).  Every
+gradient column is a sum over data of u_b dm_b/dtheta with u_b = (d_b - m_b) /
+sigma_b^2, so its error is bounded by a few FP32 roundings of the largest
+terms of the row rather than of the column itself; a column that cancels to
+near zero keeps that absolute error.  The bar is therefore
+    |g_gpu - g_ref| <= GRAD_TOL * max(|g_ref|, 1e-3 * max_j |g_ref_j|)
+with GRAD_TOL = 2e-3 (FP32-grade through ~10^4-term sums and the 1e-3 floor).
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GRAD_TOL = 2e-3
+PRECS = ["fp32", "fp32_simt"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30145_gb300 import build
+    build.build()
+    from paper_2609_30145_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+_CACHE = {}
+
+
+def case(ctx, key):
+    if key not in _CACHE:
+        name = {"tiny": "tiny_phot_16x4x512", "phot": "phot_107x12x6000_b1024",
+                "spec": "specphot_afe_107x12x5x6000_b2048"}[key]
+        w = synth.WORKLOADS[name]
+        orc = cases.oracle_for(w)
+        _CACHE[key] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    return _CACHE[key]
+
+
+def gpu_grad(model, th32, prec, ld=None):
+    n = th32.shape[0]
+    ld = ld or th32.shape[1]
+    t = torch.zeros((n, ld), dtype=torch.float32, device="cuda")
+    t[:, :th32.shape[1]] = torch.from_numpy(th32).cuda()
+    lnl, g, st = model.loglike_grad(t, prec)
+    torch.cuda.synchronize()
+    return lnl.cpu().numpy(), g.cpu().numpy(), st.cpu().numpy()
+
+
+def check_grad(g_gpu, g_ref, status, tol=GRAD_TOL):
+    ok = status == 0
+    assert ok.any()
+    worst = 0.0
+    for r in np.nonzero(ok)[0]:
+        ref = g_ref[r]
+        floor = 1e-3 * np.abs(ref).max()
+        e = np.abs(g_gpu[r, :ref.size] - ref) / np.maximum(np.abs(ref), floor)
+        worst = max(worst, e.max())
+        assert e.max() < tol, f"row {r} column {int(e.argmax())}: {g_gpu[r, e.argmax()]} vs {ref[e.argmax()]}"
+    return worst
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tiny_grad_vs_oracle(ctx, prec):
+    """C1 shape at 200 rows (two 128-row tiles, ragged): every row, every column."""
+    w, orc, model = case(ctx, "tiny")
+    th32, th64 = cases.theta_pair(w, 200, seed=51)
+    lnl, g, st = gpu_grad(model, th32, prec)
+    ref = orc.grad(th64)
+    assert np.array_equal(st, ref["status"])
+    check_grad(g, ref["grad"], st)
+    ok = st == 0
+    fwd = orc.eval(th64)
+    assert np.allclose(lnl[ok], fwd["lnl"][ok], rtol=1e-5, atol=0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_paper_scale_phot_grad_sampled_rows(ctx, prec):
+    """107 x 12 x 6000 grid, 120 bins with per-bin [Fe/H], nebular, KC13 dust,
+    20 filters: the full 1024-row batch on the GPU, 12 sampled rows against the
+    oracle's analytic gradient (all 249 columns)."""
+    w, orc, model = case(ctx, "phot")
+    th32, th64 = cases.theta_pair(w, 1024, seed=52)
+    lnl, g, st = gpu_grad(model, th32, prec)
+    rows = np.unique(np.concatenate([[0, 1023], np.random.default_rng(9).choice(1024, 10, replace=False)]))
+    ref = orc.grad(th64[rows])
+    assert np.array_equal(st[rows], ref["status"])
+    check_grad(g[rows], ref["grad"], ref["status"])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_specphot_afe_grad_sampled_rows(ctx, prec):
+    """107 x 12 x 5 x 6000 grid with [a/Fe], 1500-pixel spectrum + 20 filters:
+    300 rows on the GPU, 8 sampled rows against the oracle's analytic gradient."""
+    w, orc, model = case(ctx, "spec")
+    th32, th64 = cases.theta_pair(w, 300, seed=53)
+    lnl, g, st = gpu_grad(model, th32, prec)
+    rows = np.array([0, 77, 150, 299, 11, 222, 45, 180])
+    ref = orc.grad(th64[rows])
+    assert np.array_equal(st[rows], ref["status"])
+    check_grad(g[rows], ref["grad"], ref["status"])
+
+
+def test_specphot_grad_vs_central_differences(ctx):
+    """The adjoint against central finite differences of the FP64 oracle's
+    forward model (h = 1e-7 relative) on 16 rows x all parameters."""
+    w, orc, model = case(ctx, "spec")
+    th32, th64 = cases.theta_pair(w, 16, seed=54)
+    lnl, g, st = gpu_grad(model, th32, "fp32")
+    fd = orc.grad_fd(th64, h_rel=1e-7)
+    check_grad(g, fd[:, :orc.n_param], st)
+
+
+def test_grad_bad_rows_padding_and_determinism(ctx):
+    w, orc, model = case(ctx, "tiny")
+    th32, _ = cases.theta_pair(w, 40, seed=55)
+    th32[0, model.offsets["zred"]] = w.zf + 1
+    th32[1, 2] = np.nan
+    ld = model.n_param + 5
+    a = gpu_grad(model, th32, "fp32", ld=ld)
+    b = gpu_grad(model, th32, "fp32", ld=ld)
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[0], b[0])
+    lnl, g, st = a
+    assert st[0] != 0 and st[1] != 0 and np.isneginf(lnl[:2]).all()
+    assert np.all(g[:2] == 0)
+    assert np.all(g[:, model.n_param:] == 0)
+    assert np.isfinite(g[2:]).all()
+
+
+def test_autograd_function_backward(ctx):
+    from paper_2609_30145_gb300 import SedLogLike
+    w, orc, model = case(ctx, "tiny")
+    th32, _ = cases.theta_pair(w, 30, seed=56)
+    t = torch.from_numpy(th32).cuda().requires_grad_(True)
+    lnl = SedLogLike.apply(t, model, "fp32")
+    wts = torch.linspace(0.5, 1.5, 30, device="cuda", dtype=torch.float64)
+    (lnl * wts).sum().backward()
+    _, g, _ = gpu_grad(model, th32, "fp32")
+    want = wts.cpu().numpy()[:, None] * g
+    assert np.allclose(t.grad.cpu().numpy(), want, rtol=1e-6, atol=0)
