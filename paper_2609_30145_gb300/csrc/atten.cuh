@@ -1,0 +1,33 @@
+// Attenuated rest-frame spectrum of one node (Sec. 2.4, App. C, Eq. app_attn),
+// shared by the forward epilogue and its adjoint so that both evaluate the
+// same FP32 arithmetic:
+//   F = e^{-tau_d} [ e^{-tau_BC} (Y + neb) + O ]
+//   tau_BC = tau_pow (lam/5500)^alpha_pow
+//   tau_d  = tau_diff (lam/5500)^delta                        (power law), or
+//            tau_diff [k'(lam) + E_b(delta) D(lam)]/4.05 (lam/5500)^delta  (Kriek & Conroy 2013)
+//   neb    = Q_young 10^(bilinear log10 template)
+#pragma once
+#include "sed_internal.cuh"
+
+namespace sed {
+
+__device__ __forceinline__ float dust_shape(const ModelDev& md, const float4& c, float eb, float pw) {
+  return md.dust_law == SED_DUST_POWER_LAW ? pw : (c.y + eb * c.z) * pw;
+}
+
+__device__ __forceinline__ float neb_log10(const RowScal& rs, const float* tab, int k) {
+  return rs.neb_w[0] * tab[rs.neb_off[0] + k] + rs.neb_w[1] * tab[rs.neb_off[1] + k] +
+         rs.neb_w[2] * tab[rs.neb_off[2] + k] + rs.neb_w[3] * tab[rs.neb_off[3] + k];
+}
+
+// c = {ln(lam/5500), k'/4.05, Drude/4.05, 1/lam^2}; eb = 0.85 - 1.9 delta
+__device__ __forceinline__ float attenuated(const ModelDev& md, const RowScal& rs, const float4& c, float eb, float y,
+                                           float o, const float* neb_tab, int k) {
+  const float tbc = rs.tau_bc * __expf(rs.alpha_bc * c.x);
+  const float pw = __expf(rs.delta * c.x);
+  const float td = rs.tau_d * dust_shape(md, c, eb, pw);
+  if (md.use_neb) y += exp2f(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, neb_tab, k));
+  return __expf(-td) * (__expf(-tbc) * y + o);
+}
+
+}  // namespace sed

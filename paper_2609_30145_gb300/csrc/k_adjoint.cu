@@ -22,6 +22,7 @@
 // it, and accumulates dlnL/dF in shared memory.  Every sum runs in a fixed
 // order (node-owned gathers, no atomics), so the gradient is bitwise
 // reproducible.
+#include "atten.cuh"
 #include "locate.cuh"
 #include "sed_internal.cuh"
 
@@ -97,21 +98,9 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
   const float* Or = a.O + ro;
   const float eb_kc = 0.85f - 1.9f * rs.delta;
 
-  // ---- forward: attenuated spectrum (same arithmetic as the forward epilogue)
+  // ---- forward: attenuated spectrum (the forward epilogue's arithmetic)
   for (int k = tid; k < N; k += EB_THREADS) {
-    const float lnp = g.lnp[k];
-    const float tbc = rs.tau_bc * __expf(rs.alpha_bc * lnp);
-    const float pw = __expf(rs.delta * lnp);
-    const float td = md.dust_law == SED_DUST_POWER_LAW
-                         ? rs.tau_d * pw
-                         : rs.tau_d * (g.kprime[k] + eb_kc * g.drude[k]) * (1.f / 4.05f) * pw;
-    float y = Yr[k];
-    if (md.use_neb) {
-      const float lg = rs.neb_w[0] * g.neb_tab[rs.neb_off[0] + k] + rs.neb_w[1] * g.neb_tab[rs.neb_off[1] + k] +
-                       rs.neb_w[2] * g.neb_tab[rs.neb_off[2] + k] + rs.neb_w[3] * g.neb_tab[rs.neb_off[3] + k];
-      y += exp2f(rs.log2_qy + 3.3219280948873623f * lg);
-    }
-    Fs[k] = __expf(-td) * (__expf(-tbc) * y + Or[k]);
+    Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], Or[k], g.neb_tab, k);
     phi[k] = 0.f;
   }
   __syncthreads();
@@ -311,25 +300,19 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
       put_g(a, a.go_hi, a.go_lo, ro + k, 0.f);
       continue;
     }
-    const float lnp = g.lnp[k];
+    const float4 c = g.att4[k];
+    const float lnp = c.x;
     const float pa = __expf(rs.alpha_bc * lnp);
     const float tbc = rs.tau_bc * pa;
     const float pw = __expf(rs.delta * lnp);
-    float shape, dshape;
-    if (md.dust_law == SED_DUST_POWER_LAW) {
-      shape = pw;
-      dshape = pw * lnp;
-    } else {
-      shape = (g.kprime[k] + eb_kc * g.drude[k]) * (1.f / 4.05f) * pw;
-      dshape = (-1.9f * g.drude[k]) * (1.f / 4.05f) * pw + shape * lnp;
-    }
+    const float shape = dust_shape(md, c, eb_kc, pw);
+    const float dshape = md.dust_law == SED_DUST_POWER_LAW ? pw * lnp : -1.9f * c.z * pw + shape * lnp;
     const float td = rs.tau_d * shape;
     const float ed = __expf(-td), eb = __expf(-tbc);
     float y = Yr[k];
     float lg = 0.f, nb = 0.f;
     if (md.use_neb) {
-      lg = rs.neb_w[0] * g.neb_tab[rs.neb_off[0] + k] + rs.neb_w[1] * g.neb_tab[rs.neb_off[1] + k] +
-           rs.neb_w[2] * g.neb_tab[rs.neb_off[2] + k] + rs.neb_w[3] * g.neb_tab[rs.neb_off[3] + k];
+      lg = neb_log10(rs, g.neb_tab, k);
       nb = exp2f(rs.log2_qy + 3.3219280948873623f * lg);
       y += nb;
     }

@@ -16,11 +16,28 @@
 // All reductions run in a fixed order, so the result is bitwise reproducible.
 #include "sed_internal.cuh"
 #include "locate.cuh"
+#include "atten.cuh"
 
 namespace sed {
 
 constexpr int EPI_THREADS = 256;
 constexpr int MAX_BANDS = 128;
+
+// Photometric brackets: the last node k in [lo, lo + n - 1] with lam[k] <= x, by a
+// fixed number of halving steps over the shared-memory copy of the wavelengths
+// (requires lam[lo] <= x; extra steps leave the result unchanged).
+__device__ __forceinline__ int bracket_lin(const float* lam, int lo, int n, int steps, float x) {
+  for (int it = 0; it < steps; ++it) {
+    const int half = n >> 1;
+    if (lam[lo + half] <= x) { lo += half; n -= half; } else { n = half; }
+  }
+  return lo;
+}
+
+size_t epilogue_smem(const EpiArgs& a) {
+  const size_t N = (size_t)a.g.n_lam;
+  return (N * (a.md.n_pix > 0 ? 3 : 2) + (size_t)a.md.n_samp) * sizeof(float);
+}
 
 __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant__ EpiArgs a) {
   const ModelDev& md = a.md;
@@ -29,10 +46,13 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = g.n_lam;
   extern __shared__ float smem[];
-  float* Gs = smem;          // F / lam^2
-  float* Fs = smem + N;      // F
+  float* Gs = smem;                   // F / lam^2
+  float* lam_s = smem + N;            // rest-frame wavelengths
+  float* contrib = smem + 2 * N;      // per filter sample: w_j * lerp(G)(x_j)
+  float* Fs = contrib + md.n_samp;    // F (spectral arm only)
   __shared__ double band_v[MAX_BANDS];
   __shared__ double red[EPI_THREADS / 32];
+  __shared__ int bk_lo[MAX_BANDS], bk_n[MAX_BANDS];
 
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
@@ -48,44 +68,66 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
     return;
   }
 
-  // ---- attenuated rest-frame spectrum into shared memory
+  // ---- attenuated rest-frame spectrum of the row's node window into shared memory
   const float* Yr = a.Y + (size_t)r * a.ldn;
   const float* Or = a.O + (size_t)r * a.ldn;
   const float eb = 0.85f - 1.9f * rs.delta;
-  for (int k = tid; k < N; k += blockDim.x) {
-    const float lnp = g.lnp[k];
-    const float tbc = rs.tau_bc * __expf(rs.alpha_bc * lnp);
-    const float pw = __expf(rs.delta * lnp);
-    const float td = md.dust_law == SED_DUST_POWER_LAW
-                         ? rs.tau_d * pw
-                         : rs.tau_d * (g.kprime[k] + eb * g.drude[k]) * (1.f / 4.05f) * pw;
-    float y = Yr[k];
-    if (md.use_neb) {
-      const float lg = rs.neb_w[0] * g.neb_tab[rs.neb_off[0] + k] + rs.neb_w[1] * g.neb_tab[rs.neb_off[1] + k] +
-                       rs.neb_w[2] * g.neb_tab[rs.neb_off[2] + k] + rs.neb_w[3] * g.neb_tab[rs.neb_off[3] + k];
-      y += exp2f(rs.log2_qy + 3.3219280948873623f * lg);
-    }
-    const float F = __expf(-td) * (__expf(-tbc) * y + Or[k]);
-    Fs[k] = F;
-    Gs[k] = F * g.inv_lam2[k];
+  const bool spec = md.n_pix > 0;
+  const int k_lo = rs.k_lo, k_hi = rs.k_hi;   // nodes [k_lo, k_hi] are the only ones read below
+#pragma unroll 4
+  for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
+    const float4 c = g.att4[k];
+    const float F = attenuated(md, rs, c, eb, Yr[k], Or[k], g.neb_tab, k);
+    if (spec) Fs[k] = F;
+    Gs[k] = F * c.w;
+    lam_s[k] = g.lam_f[k];
   }
   __syncthreads();
 
-  // ---- photometry: one warp per band
+  // ---- photometry.  Node window of each band (its samples are sorted); each
+  //      thread takes a contiguous run of samples, brackets the first one by
+  //      halving and walks forward for the rest; the per-sample terms are then
+  //      summed per band in a fixed order.
   const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
-  for (int b = warp; b < md.n_filt; b += EPI_THREADS / 32) {
-    float acc = 0.f;
-    for (int j = md.band_start[b] + lane; j < md.band_start[b + 1]; j += 32) {
-      const float x = md.samp_lam[j] * rs.inv1pz;
+  if (tid < md.n_filt) {
+    const int b = tid;
+    const float xa = md.samp_lam[md.band_start[b]] * rs.inv1pz;
+    const float xb = md.samp_lam[md.band_start[b + 1] - 1] * rs.inv1pz;
+    const int n0 = max(k_hi - k_lo, 1), st0 = 32 - __clz(n0);
+    const int lo = xa <= lam_s[k_lo] ? k_lo : bracket_lin(lam_s, k_lo, n0, st0, fminf(xa, lamN));
+    const int hi = xb >= lam_s[k_hi] ? k_hi - 1 : bracket_lin(lam_s, k_lo, n0, st0, fmaxf(xb, lam0));
+    bk_lo[b] = lo;
+    bk_n[b] = max(hi - lo + 1, 1);
+  }
+  __syncthreads();
+  {
+    const int run = (md.n_samp + EPI_THREADS - 1) / EPI_THREADS;
+    const int j0 = tid * run, j1 = min(md.n_samp, j0 + run);
+    int kc = -1, bc = -1, kend = 0;
+    for (int j = j0; j < j1; ++j) {
+      const float4 sp = md.samp4[j];
+      const int b = (int)sp.z;
+      const float x = sp.x * rs.inv1pz;
       float v = 0.f;
       if (x >= lam0 && x <= lamN) {
-        const int k = locate_lin(g, x);
-        const float la = g.lam_f[k], lb = g.lam_f[k + 1];
+        if (b != bc) {
+          kc = bracket_lin(lam_s, bk_lo[b], bk_n[b], 32 - __clz(bk_n[b]), x);
+          kend = bk_lo[b] + bk_n[b] - 1;
+          bc = b;
+        } else {
+          while (kc < kend && lam_s[kc + 1] <= x) ++kc;
+        }
+        const float la = lam_s[kc], lb = lam_s[kc + 1];
         const float t = (x - la) / (lb - la);
-        v = Gs[k] + t * (Gs[k + 1] - Gs[k]);
+        v = Gs[kc] + t * (Gs[kc + 1] - Gs[kc]);
       }
-      acc = fmaf(md.samp_w[j], v, acc);
+      contrib[j] = sp.y * v;
     }
+  }
+  __syncthreads();
+  for (int b = warp; b < md.n_filt; b += EPI_THREADS / 32) {
+    float acc = 0.f;
+    for (int j = md.band_start[b] + lane; j < md.band_start[b + 1]; j += 32) acc += contrib[j];
 #pragma unroll
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
@@ -157,7 +199,8 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
 }
 
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)a.g.n_lam * 2 * sizeof(float);
+  const size_t smem = epilogue_smem(a);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   static size_t set_for = 0;
   if (smem > 48 * 1024 && smem > set_for) {
     cudaError_t e = cudaFuncSetAttribute(k_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -14,6 +14,7 @@
 //    sums the bins overlapping its cell in order, so W is deterministic;
 //  - Q_young = sum over birth-cloud ages of W Q (App. C, Eq. app_q).
 #include "sed_internal.cuh"
+#include "locate.cuh"
 
 namespace sed {
 
@@ -54,10 +55,74 @@ __device__ __forceinline__ float sfh_edge(int i, int NT, double tmax, float lrat
   return 1e7f * expf(lrat * (float)(i - 2) / (float)(NT - 2));
 }
 
+struct CosmoKernelArgs {
+  const float* theta;
+  int n, ld, zoff, moff;
+  double zf, Om0, dh_cm, th_yr, t_zf_yr, lsun_c;
+  const double* ctab;   // [n_tab + 1][4]: D_C, dD_C/dz, t_univ, dt_univ/dz at z_i = i h
+  int n_tab;
+  double tab_h, tab_inv_h;
+  CosmoRow* out;
+};
+
+// Cosmology and observer-frame scalars of each row (Sec. 2.6), one thread per
+// row.  D_C(z) and t_univ(z) are cubic Hermite interpolants (FP64) of a table
+// the host fills once per model with the FP64 integral / closed form and their
+// exact derivatives (c/H0/E and -1/(H0 (1+z) E)); the interpolation error is
+// below 1e-10 relative, and GB300's narrow FP64 pipe sees ~30 FP64 operations
+// per row instead of a quadrature.
+//  D_L = (1+z) D_C, floored at 10 pc;  T_max = t(z) - t(zf);
+//  s = 10^logmass Lsun (1+z) / (4 pi D_L^2) in device flux units, with
+//  10^logmass = 2^n 2^f taken as an FP32 exp2 of the fraction (FP32-grade).
+__global__ void __launch_bounds__(32) k_cosmo(const __grid_constant__ CosmoKernelArgs a) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.n) return;
+  const float* th = a.theta + (size_t)r * a.ld;
+  const float z = th[a.zoff], lm = th[a.moff];
+  CosmoRow c{};
+  if (!isfinite(z) || !isfinite(lm)) {
+    c.status = SED_ROW_BAD_THETA;
+  } else if (!(z >= 0.f && (double)z < a.zf)) {
+    c.status = SED_ROW_BAD_Z;
+  } else {
+    const double zd = (double)z, zp = 1.0 + zd;
+    const double q = zd * a.tab_inv_h;
+    const int i = min((int)q, a.n_tab - 1);
+    const double u = q - (double)i, v = 1.0 - u;
+    const double* t0 = a.ctab + 4 * (size_t)i;
+    const double* t1 = t0 + 4;
+    const double h00 = (1.0 + 2.0 * u) * v * v, h10 = u * v * v * a.tab_h;
+    const double h01 = u * u * (3.0 - 2.0 * u), h11 = -u * u * v * a.tab_h;
+    const double dc = h00 * t0[0] + h10 * t0[1] + h01 * t1[0] + h11 * t1[1];
+    const double tu = h00 * t0[2] + h10 * t0[3] + h01 * t1[2] + h11 * t1[3];
+    const double ez = sqrt(a.Om0 * zp * zp * zp + (1.0 - a.Om0));
+    const double tmax = tu - a.t_zf_yr;
+    const double izp = 1.0 / zp;
+    double dl = zp * dc;
+    double ddl = dc + zp * a.dh_cm / ez;
+    if (dl < 10.0 * PC_CM) { dl = 10.0 * PC_CM; ddl = 0.0; }
+    const double dlnd = ddl / dl;
+    const double e2 = (double)lm * 3.321928094887362;
+    const double en = floor(e2);
+    const double sc = ldexp((double)exp2f((float)(e2 - en)), (int)en) * a.lsun_c * zp / (dl * dl);
+    c.p_phot = (float)(C_AA * sc * izp * izp);
+    c.s_spec = (float)sc;
+    c.inv1pz = (float)izp;
+    const double l1 = log(zp);
+    c.ln1pz_hi = (float)l1;
+    c.ln1pz_lo = (float)(l1 - (double)c.ln1pz_hi);
+    c.dlns_dz = (float)(izp - 2.0 * dlnd);
+    c.dlnp_dz = (float)(-izp - 2.0 * dlnd);
+    c.dtmax_dz = (float)(-a.th_yr * izp / ez);
+    c.tmax_d = tmax;
+    c.lrat = tmax > 1e7 ? logf((float)(tmax * 1e-7)) : 0.f;
+    c.status = tmax > 1e7 ? 0u : SED_ROW_BAD_TMAX;
+  }
+  a.out[r] = c;
+}
+
 struct PrepKernelArgs {
   PrepArgs p;
-  double gl_x[GL_NODES];
-  double gl_w[GL_NODES];
 };
 
 constexpr int PREP_THREADS = 128;
@@ -79,7 +144,6 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __shared__ float rate[MAX_SFH];       // m_i / dT_i
   __shared__ int zb[MAX_SFH];
   __shared__ float zt[MAX_SFH];
-  __shared__ double s_cos[4];
   __shared__ float s_red[PREP_THREADS / 32];
   __shared__ int s_nnz[PREP_THREADS / 32];
 
@@ -87,47 +151,12 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   int bad = 0;
   for (int j = tid; j < md.n_param; j += blockDim.x) bad |= !isfinite(th[j]);
   bad = __syncthreads_or(bad);
-  const float z = th[md.offs[SED_KEY_ZRED]];
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
-  if (!status && !(z >= 0.f && (double)z < md.zf)) status = SED_ROW_BAD_Z;
 
-  // ---- cosmology in FP64 (warp 0).  GB300's FP64 pipe is narrow, so the FP64
-  //      work per row is kept to the quadrature (one node per lane) and a few
-  //      scalar operations: closed forms are rewritten with sqrt / rsqrt / log
-  //      and the constants of the model are folded on the host.
-  __shared__ float s_lrat;
-  if (!status && warp == 0) {
-    const double zp = 1.0 + (double)z;
-    const double Om = md.Om0, OL = 1.0 - md.Om0;
-    const double u0 = rsqrt(zp);
-    const double half = 0.5 * (1.0 - u0), mid = 0.5 * (1.0 + u0);
-    double acc = 0.0;
-    for (int i = lane; i < GL_NODES; i += 32) {
-      const double u = mid + half * ka.gl_x[i];
-      const double u2 = u * u;
-      acc += ka.gl_w[i] * rsqrt(Om + OL * u2 * u2 * u2);
-    }
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const double dc = 2.0 * md.dh_cm * half * acc;
-      const double ez = sqrt(Om * zp * zp * zp + OL);
-      // t_univ = (2/(3 H0 sqrt(OL))) asinh(sqrt(OL/Om) (1+z)^-3/2), asinh(x) = ln(x + sqrt(x^2 + 1))
-      const double x = md.asinh_c * u0 * u0 * u0;
-      const double t = md.t_c * log(x + sqrt(x * x + 1.0));
-      double dl = zp * dc;
-      double ddl = dc + zp * md.dh_cm / ez;  // dD_L/dz
-      if (dl < 10.0 * PC_CM) { dl = 10.0 * PC_CM; ddl = 0.0; }
-      const double tmx = t - md.t_zf_yr;
-      s_cos[0] = dl;
-      s_cos[1] = tmx;                             // T_max
-      s_cos[2] = ddl / dl;                        // dlnD_L/dz
-      s_cos[3] = -md.th_yr / (zp * ez);           // dt/dz
-      s_lrat = tmx > 1e7 ? (float)log(tmx * 1e-7) : 0.f;
-    }
-  }
-  __syncthreads();
-  const double tmax = status ? 0.0 : s_cos[1];
-  if (!status && !(tmax > 1e7)) status = SED_ROW_BAD_TMAX;
+  // ---- cosmology of the row (k_cosmo, thread per row, ran just before)
+  const CosmoRow cr = a.cosmo[r];
+  if (!status) status = cr.status;
+  const double tmax = status ? 0.0 : (double)cr.tmax_d;
 
   RowScal* out = a.rs + r;
   const int Kpad = L.Kpad;
@@ -151,7 +180,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   // ---- SFH edges (FP32) and per-bin quantities
   const float* m = th + md.offs[SED_KEY_SFH];
   const float* zeta = th + md.offs[SED_KEY_LOGZSOL];
-  const float lrat = s_lrat;
+  const float lrat = cr.lrat;
   for (int i = tid; i <= NT; i += blockDim.x) T[i] = sfh_edge(i, NT, tmax, lrat);
   for (int j = tid; j < NA * NZ; j += blockDim.x) Ws[j] = 0.f;
   __syncthreads();
@@ -225,19 +254,12 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   if (tid == 0) {
     float qy = 0.f;
     for (int w = 0; w < PREP_THREADS / 32; ++w) qy += s_red[w];
-    const double zp = 1.0 + (double)z;
-    const double logmass = (double)th[md.offs[SED_KEY_LOGMASS]];
-    const double dl = s_cos[0];
-    // s = 10^logmass Lsun (1+z) / (4 pi D_L^2), in device flux units (x 2^-f_log2);
-    // md.lsun_c = Lsun 2^-f_log2 / (4 pi)
-    const double s = exp(logmass * 2.302585092994046) * md.lsun_c * zp / (dl * dl);
     RowScal rs{};
-    rs.p_phot = (float)(C_AA * s / (zp * zp));
-    rs.s_spec = (float)s;
-    rs.inv1pz = (float)(1.0 / zp);
-    const double l1 = log(zp);
-    rs.ln1pz_hi = (float)l1;
-    rs.ln1pz_lo = (float)(l1 - (double)rs.ln1pz_hi);
+    rs.p_phot = cr.p_phot;
+    rs.s_spec = cr.s_spec;
+    rs.inv1pz = cr.inv1pz;
+    rs.ln1pz_hi = cr.ln1pz_hi;
+    rs.ln1pz_lo = cr.ln1pz_lo;
     rs.tau_bc = th[md.offs[SED_KEY_TAU_POW]];
     rs.alpha_bc = th[md.offs[SED_KEY_ALPHA_POW]];
     rs.tau_d = th[md.offs[SED_KEY_DIFFUSE_TAU]];
@@ -259,14 +281,33 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       rs.neb_dwu[0] = du0 * wz0; rs.neb_dwu[1] = du0 * wz1; rs.neb_dwu[2] = du1 * wz0; rs.neb_dwu[3] = du1 * wz1;
       rs.neb_dwz[0] = wu0 * dz0; rs.neb_dwz[1] = wu0 * dz1; rs.neb_dwz[2] = wu1 * dz0; rs.neb_dwz[3] = wu1 * dz1;
     }
-    rs.dlns_dz = (float)(1.0 / zp - 2.0 * s_cos[2]);
-    rs.dlnp_dz = (float)(-1.0 / zp - 2.0 * s_cos[2]);
-    rs.dtmax_dz = (float)s_cos[3];
+    rs.dlns_dz = cr.dlns_dz;
+    rs.dlnp_dz = cr.dlnp_dz;
+    rs.dtmax_dz = cr.dtmax_dz;
     rs.tmax = (float)tmax;
     rs.lrat = lrat;
     rs.status = 0;
-    rs.k_lo = 0;
-    rs.k_hi = g.n_lam;
+    // rest-frame node window the epilogue reads: the redshifted filter samples
+    // and the spectral pixels with 5 dispersions on either side, with margins
+    {
+      const int N = g.n_lam;
+      const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
+      int lo = N - 1, hi = 0;
+      if (md.n_filt > 0) {
+        lo = min(lo, locate_lin(g, fminf(fmaxf(md.samp_lam_min * cr.inv1pz, lam0), lamN)));
+        hi = max(hi, locate_lin(g, fminf(fmaxf(md.samp_lam_max * cr.inv1pz, lam0), lamN)));
+      }
+      if (md.n_pix > 0) {
+        const double l1 = (double)cr.ln1pz_hi + (double)cr.ln1pz_lo;
+        const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
+        const float a = fminf(fmaxf((float)(md.pix_ln_min - l1) - 5.f * md.pix_s_max, ll0), llN);
+        const float b = fminf(fmaxf((float)(md.pix_ln_max - l1) + 5.f * md.pix_s_max, ll0), llN);
+        lo = min(lo, locate_ln(g, a, g.lnl_hi));
+        hi = max(hi, locate_ln(g, b, g.lnl_hi));
+      }
+      rs.k_lo = max(lo - 2, 0);
+      rs.k_hi = min(max(hi + 3, rs.k_lo + 1), N - 1);
+    }
     rs.nnz = 0;
     for (int w = 0; w < PREP_THREADS / 32; ++w) rs.nnz += s_nnz[w];
     *out = rs;
@@ -443,31 +484,18 @@ cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
-  static double gx[GL_NODES], gw[GL_NODES];
-  static bool init = false;
-  if (!init) {  // Gauss-Legendre nodes by Newton iteration on P_n
-    const int n = GL_NODES;
-    for (int i = 0; i < n; i++) {
-      double x = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0;
-      for (int it = 0; it < 100; it++) {
-        double p0 = 1.0, p1 = x;
-        for (int k = 2; k <= n; k++) {
-          double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-          p0 = p1; p1 = p2;
-        }
-        dp = n * (x * p1 - p0) / (x * x - 1.0);
-        double dx = p1 / dp;
-        x -= dx;
-        if (fabs(dx) < 1e-16) break;
-      }
-      gx[i] = x;
-      gw[i] = 2.0 / ((1.0 - x * x) * dp * dp);
-    }
-    init = true;
-  }
+  CosmoKernelArgs ca;
+  ca.theta = p.theta; ca.n = p.n; ca.ld = p.ld;
+  ca.zoff = p.md.offs[SED_KEY_ZRED]; ca.moff = p.md.offs[SED_KEY_LOGMASS];
+  ca.zf = p.md.zf; ca.Om0 = p.md.Om0; ca.dh_cm = p.md.dh_cm; ca.th_yr = p.md.th_yr; ca.t_zf_yr = p.md.t_zf_yr;
+  ca.lsun_c = p.md.lsun_c;
+  ca.ctab = p.md.ctab; ca.n_tab = p.md.n_ctab; ca.tab_h = p.md.ctab_h; ca.tab_inv_h = 1.0 / p.md.ctab_h;
+  ca.out = p.cosmo;
+  k_cosmo<<<(p.n + 31) / 32, 32, 0, s>>>(ca);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   PrepKernelArgs ka;
   ka.p = p;
-  for (int i = 0; i < GL_NODES; i++) { ka.gl_x[i] = gx[i]; ka.gl_w[i] = gw[i]; }
   const size_t smem = (size_t)p.g.n_age * p.g.n_feh * sizeof(float);
   k_prep<<<p.n, PREP_THREADS, smem, s>>>(ka);
   return cudaGetLastError();

@@ -177,7 +177,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
       std::vector<void*> v = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
-                              w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
+                              w->theta_h, w->lnl_h, w->st_h, w->cosmo, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                               w->dW, w->rgrad};
       for (void* p : v)
         if (p) cudaFree(p);
@@ -317,6 +317,18 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
   UPF(lnl_hi, lh) UPF(lnl_lo, lo) UPF(cell_lo, clo) UPF(cell_hi, chi)
 #undef UPF
   if (!st) { st = upload(ctx, &pi, lut.data(), lut.size(), &g->allocs, &g->bytes); dv.lut = pi; }
+  if (!st) {
+    std::vector<float4> a4(nl);
+    for (size_t k = 0; k < nl; k++)
+    {
+      const double L = g->lam[k], x = L * 350.0, dd = L * L - 2175.0 * 2175.0;
+      a4[k] = make_float4(lnp[k], (float)(calzetti_kprime(L * 1e-4) / 4.05), (float)(x * x / (dd * dd + x * x) / 4.05),
+                          inv_lam2[k]);
+    }
+    float4* p4;
+    st = upload(ctx, &p4, a4.data(), nl, &g->allocs, &g->bytes);
+    dv.att4 = p4;
+  }
   dv.lut_n = lut_n;
   dv.lut_x0 = (float)x0;
   dv.lut_inv_h = (float)(1.0 / h);
@@ -458,6 +470,35 @@ double t_univ_yr(double th_yr, double Om, double z) {
   return th_yr * 2.0 / (3.0 * std::sqrt(OL)) * std::asinh(std::sqrt(OL / Om) * std::pow(1.0 + z, -1.5));
 }
 
+// Cosmology table of a model (flat LCDM without radiation, Sec. 2.6): at
+// z_i = i zf / n, D_C(z_i) = (c/H0) int_0^z_i dz/E by 16-point Gauss-Legendre
+// on each interval (FP64, accumulated), its derivative c/(H0 E), the age of
+// the Universe t(z_i) in closed form and dt/dz = -1/(H0 (1+z) E).
+void cosmo_table(double H0, double Om, double zf, int n, std::vector<double>* out) {
+  static const double x16[8] = {0.0950125098376374, 0.2816035507792589, 0.4580167776572274, 0.6178762444026438,
+                                0.7554044083550030, 0.8656312023878318, 0.9445750230732326, 0.9894009349916499};
+  static const double w16[8] = {0.1894506104550685, 0.1826034150449236, 0.1691565193950025, 0.1495959888165767,
+                                0.1246289712555339, 0.0951585116824928, 0.0622535239386479, 0.0271524594117541};
+  const double OL = 1.0 - Om, dh = C_KMS / H0 * 1e6 * PC_CM, thy = MPC_KM / H0 / YR_S, h = zf / n;
+  auto E = [&](double z) { const double zp = 1.0 + z; return std::sqrt(Om * zp * zp * zp + OL); };
+  out->assign((size_t)(n + 1) * 4, 0.0);
+  double dc = 0.0;
+  for (int i = 0; i <= n; i++) {
+    const double z = i * h;
+    if (i > 0) {
+      const double a = z - h, mid = a + 0.5 * h, hw = 0.5 * h;
+      double acc = 0.0;
+      for (int k = 0; k < 8; k++) acc += w16[k] * (1.0 / E(mid - hw * x16[k]) + 1.0 / E(mid + hw * x16[k]));
+      dc += dh * hw * acc;
+    }
+    double* t = out->data() + 4 * (size_t)i;
+    t[0] = dc;
+    t[1] = dh / E(z);
+    t[2] = t_univ_yr(thy, Om, z);
+    t[3] = -thy / ((1.0 + z) * E(z));
+  }
+}
+
 sed_status set_data_dev(sed_ctx* ctx, Model* M, const double* pd, const double* ps, const double* sd,
                         const double* ss) {
   ModelDev& dv = M->dv;
@@ -548,8 +589,6 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   dv.dh_cm = C_KMS / d->H0 * 1e6 * PC_CM;
   dv.th_yr = MPC_KM / d->H0 / YR_S;
   dv.t_zf_yr = t_univ_yr(dv.th_yr, d->Om0, d->zf);
-  dv.asinh_c = std::sqrt((1.0 - d->Om0) / d->Om0);
-  dv.t_c = dv.th_yr * 2.0 / (3.0 * std::sqrt(1.0 - d->Om0));
   dv.lsun_c = LSUN * std::exp2(-g->f_log2) / (4.0 * M_PI);
   dv.f_log2 = g->f_log2;
   dv.q_log2 = g->q_log2;
@@ -563,6 +602,15 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   int n_young = 0;
   while (n_young < g->n_age && g->log_age[n_young] <= d->bc_edge_log_age_yr) n_young++;
   sed_status st = get_layout(ctx, g, n_young, d->use_nebular ? 1 : 0, &M->L);
+  if (!st) {
+    std::vector<double> tab;
+    cosmo_table(d->H0, d->Om0, d->zf, COSMO_TAB, &tab);
+    double* pd;
+    st = upload(ctx, &pd, tab.data(), tab.size(), &M->allocs, &M->bytes);
+    dv.ctab = pd;
+    dv.n_ctab = COSMO_TAB;
+    dv.ctab_h = d->zf / COSMO_TAB;
+  }
 
   // ---- photometry: App. D weights R lam dlam / Z_b, band-major samples
   if (!st && d->n_filt) {
@@ -607,6 +655,15 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     if (!st) { st = upload(ctx, &pi, bs.data(), bs.size(), &M->allocs, &M->bytes); dv.band_start = pi; }
     if (!st) { st = upload(ctx, &pf, sl.data(), sl.size(), &M->allocs, &M->bytes); dv.samp_lam = pf; }
     if (!st) { st = upload(ctx, &pf, sw.data(), sw.size(), &M->allocs, &M->bytes); dv.samp_w = pf; }
+    std::vector<uint8_t> sb(S);
+    for (int b = 0; b < d->n_filt && !st; b++)
+      for (int j = bs[b]; j < bs[b + 1]; j++) sb[j] = (uint8_t)b;
+    uint8_t* pb;
+    if (!st) { st = upload(ctx, &pb, sb.data(), sb.size(), &M->allocs, &M->bytes); dv.samp_band = pb; }
+    std::vector<float4> s4(S);
+    for (int j = 0; j < S; j++) s4[j] = make_float4(sl[j], sw[j], (float)sb[j], 0.f);
+    float4* p4;
+    if (!st) { st = upload(ctx, &p4, s4.data(), s4.size(), &M->allocs, &M->bytes); dv.samp4 = p4; }
     std::vector<double> zeros(d->n_filt, 0.0);
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_d = pd; }
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_isig = pd; }
@@ -719,7 +776,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
   std::vector<void*> old = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
-                            w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
+                            w->theta_h, w->lnl_h, w->st_h, w->cosmo, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                             w->dW, w->rgrad};
   for (void* p : old)
     if (p) cudaFree(p);
@@ -737,7 +794,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
   AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2);
   AL(Y, R * N * 4); AL(O, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
-  AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
+  AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4); AL(cosmo, R * sizeof(CosmoRow));
   if (grad || had_grad) {
     AL(G_hi, R * N * 4); AL(G_lo, R * N * 4); AL(GO_hi, R * N * 4); AL(GO_lo, R * N * 4);
     AL(dW, R * K * 4); AL(rgrad, R * RGRAD * 8);
@@ -787,6 +844,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   pa.W_lo = precision == SED_PREC_FP32 ? w->W_lo : nullptr;
   pa.W_bf16 = precision == SED_PREC_BF16 ? w->W_bf16 : nullptr;
   pa.rs = w->rs;
+  pa.cosmo = w->cosmo;
   pa.err = w->err;
   CK(launch_prep(pa, s));
   if (sed_status ps = prof_mark(ctx, w, 1, s)) return ps;

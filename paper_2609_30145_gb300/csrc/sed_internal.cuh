@@ -24,7 +24,7 @@ constexpr int MAX_FEH = 64;
 constexpr int MAX_AFE = 16;
 constexpr int MAX_SFH = 512;
 constexpr int MAX_LAM = 24576;   // rest-frame nodes an epilogue row can stage in shared memory
-constexpr int GL_NODES = 32;     // Gauss-Legendre nodes of the comoving-distance integral
+constexpr int COSMO_TAB = 4096;  // intervals of the cosmology table on [0, zf]
 
 // Physical constants (cgs unless noted).
 constexpr double LSUN = 3.839e33;              // erg/s (Sec. 2.6)
@@ -63,11 +63,19 @@ struct RowScal {
   int nnz;          // non-zero weights of the row
 };
 
+// Cosmology and observer-frame scalars of one row (written by k_cosmo).
+struct CosmoRow {
+  double tmax_d;    // T_max = t_univ(z) - t_univ(zf), yr
+  float p_phot, s_spec, inv1pz, ln1pz_hi, ln1pz_lo, dlnp_dz, dlns_dz, dtmax_dz, lrat;
+  uint32_t status;  // SED_ROW_BAD_THETA (z or logmass), SED_ROW_BAD_Z, SED_ROW_BAD_TMAX or 0
+};
+
 // ---------------------------------------------------------------------------
 // Kernel-parameter views (plain data, device pointers only).
 struct GridDev {
   int n_age, n_feh, n_afe, n_lam;
   const float* lam_f;      // lambda (A)
+  const float4* att4;      // per node: ln(lambda/5500), k'/4.05, Drude/4.05, 1/lambda^2
   const float* inv_lam2;   // 1/lambda^2
   const float* lnp;        // ln(lambda/5500)
   const float* kprime;     // Calzetti k'(lambda), R_V = 4.05, clamped >= 0
@@ -93,8 +101,10 @@ struct ModelDev {
   int n_sfh, zmode, use_afe, use_neb, dust_law, n_param;
   int offs[SED_NKEYS];
   double zf, t_zf_yr, dh_cm, th_yr, Om0;
-  double asinh_c, t_c;     // sqrt(OL/Om) and 2/(3 H0 sqrt(OL)) in yr (age of the Universe)
   double lsun_c;           // Lsun 2^-f_log2 / (4 pi)
+  const double* ctab;      // cosmology table [n_ctab + 1][4]: D_C (cm), dD_C/dz, t_univ (yr), dt/dz on z = i ctab_h
+  int n_ctab;
+  double ctab_h;
   double f_log2, q_log2;
   int n_feh, n_afe;
   float feh[MAX_FEH];
@@ -106,6 +116,8 @@ struct ModelDev {
   const int* band_start;   // [n_filt + 1]
   const float* samp_lam;   // [n_samp] observed-frame A
   const float* samp_w;     // [n_samp] R lam dlam / Z_b
+  const uint8_t* samp_band; // [n_samp] band of each sample
+  const float4* samp4;     // [n_samp] {observed lambda, weight, band, 0}
   const double* phot_d;    // [n_filt]
   const double* phot_isig; // [n_filt] 1/sigma (0 when masked out)
   const double* phot_nlog; // [n_filt] -1/2 ln(2 pi sigma^2) (0 when masked out)
@@ -200,6 +212,7 @@ struct Workspace {
   float* Y = nullptr;            // [rows][ldn]
   float* O = nullptr;
   RowScal* rs = nullptr;
+  CosmoRow* cosmo = nullptr;
   int* err = nullptr;            // device error word of bounded waits
   float* theta_h = nullptr;      // host-path staging (device)
   double* lnl_h = nullptr;
@@ -252,6 +265,7 @@ struct PrepArgs {
   ModelDev md; GridDev g; LayoutDev L;
   float* W; float* W_hi; float* W_lo; __nv_bfloat16* W_bf16;
   RowScal* rs;
+  CosmoRow* cosmo;     // [n] scratch between the cosmology and preparation kernels
   int* err;            // device error word of the contraction, cleared by the prep kernel
 };
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
