@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
   float* lam_s = smem + N;            // rest-frame wavelengths
   float* contrib = smem + 2 * N;      // per filter sample: w_j * lerp(G)(x_j)
   float* Fs = contrib + md.n_samp;    // F (spectral arm only)
-  __shared__ double band_v[MAX_BANDS];
+  __shared__ float mb_s[MAX_BANDS];
   __shared__ double red[EPI_THREADS / 32];
   __shared__ int bk_lo[MAX_BANDS], bk_n[MAX_BANDS];
 
@@ -133,12 +133,7 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
     if (lane == 0) {
       const float mb = rs.p_phot * acc;
       if (a.phot_out) a.phot_out[(size_t)r * md.n_filt + b] = mb;
-      double v = 0.0;
-      if (md.phot_isig[b] != 0.0) {
-        const double rr = (md.phot_d[b] - (double)mb) * md.phot_isig[b];
-        v = -0.5 * rr * rr + md.phot_nlog[b];
-      }
-      band_v[b] = v;
+      mb_s[b] = mb;
     }
   }
 
@@ -187,14 +182,26 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
   for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if (lane == 0) red[warp] = part;
   __syncthreads();
-  if (tid == 0) {
-    double tot = 0.0;
-    for (int b = 0; b < md.n_filt; ++b) tot += band_v[b];
-    for (int w = 0; w < EPI_THREADS / 32; ++w) tot += red[w];
-    uint32_t st = 0;
-    if (!isfinite(tot)) { st = SED_ROW_NONFINITE; tot = -INFINITY; }
-    if (a.lnl) a.lnl[r] = tot;
-    if (a.status) a.status[r] = st;
+  // photometric terms in FP64, one band per lane of warp 0 (GB300's FP64 pipe
+  // is narrow: one warp instruction serves all bands)
+  if (warp == 0) {
+    double pv = 0.0;
+    for (int b = lane; b < md.n_filt; b += 32) {
+      if (md.phot_isig[b] != 0.0) {
+        const double rr = (md.phot_d[b] - (double)mb_s[b]) * md.phot_isig[b];
+        pv += -0.5 * rr * rr + md.phot_nlog[b];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
+    if (lane == 0) {
+      double tot = pv;
+      for (int w = 0; w < EPI_THREADS / 32; ++w) tot += red[w];
+      uint32_t st = 0;
+      if (!isfinite(tot)) { st = SED_ROW_NONFINITE; tot = -INFINITY; }
+      if (a.lnl) a.lnl[r] = tot;
+      if (a.status) a.status[r] = st;
+    }
   }
 }
 

@@ -1,9 +1,8 @@
 // Per-row preparation: cosmology, SFH edges, SSP weights, Q_young and the
 // per-row scalars of the epilogue.  One CTA per parameter row.
 //
-//  - cosmology (Sec. 2.6): comoving distance by 32-node Gauss-Legendre in FP64
-//    on u = sqrt(a) (smooth integrand 2/sqrt(Om + OL u^6)), age of the
-//    Universe by its closed form, luminosity distance floored at 10 pc;
+//  - cosmology (Sec. 2.6): comoving distance and age of the Universe from a
+//    per-model FP64 table (cubic Hermite), luminosity distance floored at 10 pc;
 //  - SFH edges 0, 5 Myr, 10 Myr, then log-uniform to T_max = t(z) - t(zf),
 //    so the grid follows the sampled redshift and the bin masses are kept
 //    (Sec. 2.2, Sec. 2.6);
@@ -55,56 +54,42 @@ __device__ __forceinline__ float sfh_edge(int i, int NT, double tmax, float lrat
   return 1e7f * expf(lrat * (float)(i - 2) / (float)(NT - 2));
 }
 
-struct CosmoKernelArgs {
-  const float* theta;
-  int n, ld, zoff, moff;
-  double zf, Om0, dh_cm, th_yr, t_zf_yr, lsun_c;
-  const double* ctab;   // [n_tab + 1][4]: D_C, dD_C/dz, t_univ, dt_univ/dz at z_i = i h
-  int n_tab;
-  double tab_h, tab_inv_h;
-  CosmoRow* out;
-};
-
-// Cosmology and observer-frame scalars of each row (Sec. 2.6), one thread per
-// row.  D_C(z) and t_univ(z) are cubic Hermite interpolants (FP64) of a table
-// the host fills once per model with the FP64 integral / closed form and their
-// exact derivatives (c/H0/E and -1/(H0 (1+z) E)); the interpolation error is
-// below 1e-10 relative, and GB300's narrow FP64 pipe sees ~30 FP64 operations
-// per row instead of a quadrature.
+// Cosmology and observer-frame scalars of one row (Sec. 2.6).  D_C(z) and
+// t_univ(z) are cubic Hermite interpolants (FP64) of a table the host fills once
+// per model with the FP64 integral / closed form and their exact derivatives
+// (c/H0/E and -1/(H0 (1+z) E)); the interpolation error is below 1e-10
+// relative, and GB300's narrow FP64 pipe sees ~30 FP64 operations per row
+// instead of a quadrature.
 //  D_L = (1+z) D_C, floored at 10 pc;  T_max = t(z) - t(zf);
 //  s = 10^logmass Lsun (1+z) / (4 pi D_L^2) in device flux units, with
 //  10^logmass = 2^n 2^f taken as an FP32 exp2 of the fraction (FP32-grade).
-__global__ void __launch_bounds__(32) k_cosmo(const __grid_constant__ CosmoKernelArgs a) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= a.n) return;
-  const float* th = a.theta + (size_t)r * a.ld;
-  const float z = th[a.zoff], lm = th[a.moff];
+__device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm) {
   CosmoRow c{};
   if (!isfinite(z) || !isfinite(lm)) {
     c.status = SED_ROW_BAD_THETA;
-  } else if (!(z >= 0.f && (double)z < a.zf)) {
+  } else if (!(z >= 0.f && (double)z < md.zf)) {
     c.status = SED_ROW_BAD_Z;
   } else {
     const double zd = (double)z, zp = 1.0 + zd;
-    const double q = zd * a.tab_inv_h;
-    const int i = min((int)q, a.n_tab - 1);
+    const double q = zd / md.ctab_h;
+    const int i = min((int)q, md.n_ctab - 1);
     const double u = q - (double)i, v = 1.0 - u;
-    const double* t0 = a.ctab + 4 * (size_t)i;
+    const double* t0 = md.ctab + 4 * (size_t)i;
     const double* t1 = t0 + 4;
-    const double h00 = (1.0 + 2.0 * u) * v * v, h10 = u * v * v * a.tab_h;
-    const double h01 = u * u * (3.0 - 2.0 * u), h11 = -u * u * v * a.tab_h;
+    const double h00 = (1.0 + 2.0 * u) * v * v, h10 = u * v * v * md.ctab_h;
+    const double h01 = u * u * (3.0 - 2.0 * u), h11 = -u * u * v * md.ctab_h;
     const double dc = h00 * t0[0] + h10 * t0[1] + h01 * t1[0] + h11 * t1[1];
     const double tu = h00 * t0[2] + h10 * t0[3] + h01 * t1[2] + h11 * t1[3];
-    const double ez = sqrt(a.Om0 * zp * zp * zp + (1.0 - a.Om0));
-    const double tmax = tu - a.t_zf_yr;
+    const double ez = sqrt(md.Om0 * zp * zp * zp + (1.0 - md.Om0));
+    const double tmax = tu - md.t_zf_yr;
     const double izp = 1.0 / zp;
     double dl = zp * dc;
-    double ddl = dc + zp * a.dh_cm / ez;
+    double ddl = dc + zp * md.dh_cm / ez;
     if (dl < 10.0 * PC_CM) { dl = 10.0 * PC_CM; ddl = 0.0; }
     const double dlnd = ddl / dl;
     const double e2 = (double)lm * 3.321928094887362;
     const double en = floor(e2);
-    const double sc = ldexp((double)exp2f((float)(e2 - en)), (int)en) * a.lsun_c * zp / (dl * dl);
+    const double sc = ldexp((double)exp2f((float)(e2 - en)), (int)en) * md.lsun_c * zp / (dl * dl);
     c.p_phot = (float)(C_AA * sc * izp * izp);
     c.s_spec = (float)sc;
     c.inv1pz = (float)izp;
@@ -113,12 +98,12 @@ __global__ void __launch_bounds__(32) k_cosmo(const __grid_constant__ CosmoKerne
     c.ln1pz_lo = (float)(l1 - (double)c.ln1pz_hi);
     c.dlns_dz = (float)(izp - 2.0 * dlnd);
     c.dlnp_dz = (float)(-izp - 2.0 * dlnd);
-    c.dtmax_dz = (float)(-a.th_yr * izp / ez);
+    c.dtmax_dz = (float)(-md.th_yr * izp / ez);
     c.tmax_d = tmax;
     c.lrat = tmax > 1e7 ? logf((float)(tmax * 1e-7)) : 0.f;
     c.status = tmax > 1e7 ? 0u : SED_ROW_BAD_TMAX;
   }
-  a.out[r] = c;
+  return c;
 }
 
 struct PrepKernelArgs {
@@ -153,8 +138,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   bad = __syncthreads_or(bad);
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
 
-  // ---- cosmology of the row (k_cosmo, thread per row, ran just before)
-  const CosmoRow cr = a.cosmo[r];
+  // ---- cosmology of the row (one lane)
+  __shared__ CosmoRow s_cr;
+  if (tid == 0) s_cr = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]]);
+  __syncthreads();
+  const CosmoRow cr = s_cr;
   if (!status) status = cr.status;
   const double tmax = status ? 0.0 : (double)cr.tmax_d;
 
@@ -484,16 +472,6 @@ cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
-  CosmoKernelArgs ca;
-  ca.theta = p.theta; ca.n = p.n; ca.ld = p.ld;
-  ca.zoff = p.md.offs[SED_KEY_ZRED]; ca.moff = p.md.offs[SED_KEY_LOGMASS];
-  ca.zf = p.md.zf; ca.Om0 = p.md.Om0; ca.dh_cm = p.md.dh_cm; ca.th_yr = p.md.th_yr; ca.t_zf_yr = p.md.t_zf_yr;
-  ca.lsun_c = p.md.lsun_c;
-  ca.ctab = p.md.ctab; ca.n_tab = p.md.n_ctab; ca.tab_h = p.md.ctab_h; ca.tab_inv_h = 1.0 / p.md.ctab_h;
-  ca.out = p.cosmo;
-  k_cosmo<<<(p.n + 31) / 32, 32, 0, s>>>(ca);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   PrepKernelArgs ka;
   ka.p = p;
   const size_t smem = (size_t)p.g.n_age * p.g.n_feh * sizeof(float);

@@ -177,7 +177,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
       std::vector<void*> v = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
-                              w->theta_h, w->lnl_h, w->st_h, w->cosmo, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
+                              w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                               w->dW, w->rgrad};
       for (void* p : v)
         if (p) cudaFree(p);
@@ -776,7 +776,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
   std::vector<void*> old = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
-                            w->theta_h, w->lnl_h, w->st_h, w->cosmo, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
+                            w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                             w->dW, w->rgrad};
   for (void* p : old)
     if (p) cudaFree(p);
@@ -794,7 +794,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
   AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2);
   AL(Y, R * N * 4); AL(O, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
-  AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4); AL(cosmo, R * sizeof(CosmoRow));
+  AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
   if (grad || had_grad) {
     AL(G_hi, R * N * 4); AL(G_lo, R * N * 4); AL(GO_hi, R * N * 4); AL(GO_lo, R * N * 4);
     AL(dW, R * K * 4); AL(rgrad, R * RGRAD * 8);
@@ -844,7 +844,6 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   pa.W_lo = precision == SED_PREC_FP32 ? w->W_lo : nullptr;
   pa.W_bf16 = precision == SED_PREC_BF16 ? w->W_bf16 : nullptr;
   pa.rs = w->rs;
-  pa.cosmo = w->cosmo;
   pa.err = w->err;
   CK(launch_prep(pa, s));
   if (sed_status ps = prof_mark(ctx, w, 1, s)) return ps;

@@ -63,7 +63,7 @@ struct RowScal {
   int nnz;          // non-zero weights of the row
 };
 
-// Cosmology and observer-frame scalars of one row (written by k_cosmo).
+// Cosmology and observer-frame scalars of one row (computed at the start of k_prep).
 struct CosmoRow {
   double tmax_d;    // T_max = t_univ(z) - t_univ(zf), yr
   float p_phot, s_spec, inv1pz, ln1pz_hi, ln1pz_lo, dlnp_dz, dlns_dz, dtmax_dz, lrat;
@@ -212,7 +212,6 @@ struct Workspace {
   float* Y = nullptr;            // [rows][ldn]
   float* O = nullptr;
   RowScal* rs = nullptr;
-  CosmoRow* cosmo = nullptr;
   int* err = nullptr;            // device error word of bounded waits
   float* theta_h = nullptr;      // host-path staging (device)
   double* lnl_h = nullptr;
@@ -265,7 +264,6 @@ struct PrepArgs {
   ModelDev md; GridDev g; LayoutDev L;
   float* W; float* W_hi; float* W_lo; __nv_bfloat16* W_bf16;
   RowScal* rs;
-  CosmoRow* cosmo;     // [n] scratch between the cosmology and preparation kernels
   int* err;            // device error word of the contraction, cleared by the prep kernel
 };
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);

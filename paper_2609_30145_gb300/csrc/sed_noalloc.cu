@@ -87,12 +87,12 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   const int kpad = L->Kpad;
   const int ldn = (g->n_lam + 255) / 256 * 256;
   const bool f32 = precision == SED_PREC_FP32, bf = precision == SED_PREC_BF16;
-  // carve the scratch: err | RowScal | W | W_hi | W_lo | W_bf16 | Y | O | CosmoRow
+  // carve the scratch: err | RowScal | W | W_hi | W_lo | W_bf16 | Y | O
   const size_t nn = (size_t)n;
-  size_t off[9], need = 0;
-  const size_t sz[9] = {256, nn * sizeof(RowScal), nn * kpad * 4, f32 ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0,
-                        bf ? nn * kpad * 2 : 0, nn * ldn * 4, nn * ldn * 4, nn * sizeof(CosmoRow)};
-  for (int i = 0; i < 9; i++) {
+  size_t off[8], need = 0;
+  const size_t sz[8] = {256, nn * sizeof(RowScal), nn * kpad * 4, f32 ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0,
+                        bf ? nn * kpad * 2 : 0, nn * ldn * 4, nn * ldn * 4};
+  for (int i = 0; i < 8; i++) {
     off[i] = need;
     need += up256(sz[i]);
   }
@@ -120,14 +120,13 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   __nv_bfloat16* W_bf = bf ? reinterpret_cast<__nv_bfloat16*>(b + off[5]) : nullptr;
   float* Y = reinterpret_cast<float*>(b + off[6]);
   float* O = reinterpret_cast<float*>(b + off[7]);
-  CosmoRow* cosmo = reinterpret_cast<CosmoRow*>(b + off[8]);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   PrepArgs pa{};
   pa.theta = theta; pa.n = n; pa.ld = ld;
   pa.md = M->dv; pa.g = g->dv; pa.L = L->dv();
   pa.W = W; pa.W_hi = W_hi; pa.W_lo = W_lo; pa.W_bf16 = W_bf;
-  pa.rs = rs; pa.cosmo = cosmo; pa.err = err;
+  pa.rs = rs; pa.err = err;
   cudaError_t e = launch_prep(pa, s);
   if (e == cudaSuccess) {
     if (precision == SED_PREC_FP32_SIMT) {
