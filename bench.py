@@ -34,6 +34,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "phot_107x12x6000_b1024"
+GRAD_WORKLOAD = "specphot_afe_107x12x5x6000_b2048"
+PRECS = ("fp32", "fp32_simt", "bf16")
+PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
+             "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
+             "fp32_simt": "FP32 FFMA contraction, FP64 lnL"}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor ratio (recipe table)
 METRIC = "SED loglike evals/sec vs plain FP32 path at stated FP64-error; p50/p99 latency"
@@ -48,6 +53,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -158,23 +164,59 @@ def build_workload(wname, ctx, seed_rows, device):
 
 
 # --------------------------------------------------------------------------- GPU leg
-def time_steps(model, ctx, t, prec, steps, flush, stream, profile=False):
+def capture_step(fn, stream, warm=3):
+    """One step (a library call on `stream`) as a CUDA graph, after warm-up calls
+    on the same stream (the library keeps one workspace per stream)."""
     import torch
 
-    per, stats = [], []
-    for _ in range(steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        model.loglike(t, prec, stream=stream)
-        e1.record(stream)
-        if profile:
-            stats.append(ctx.last_stats(stream))
-        per.append((e0, e1))
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            fn(stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        fn(stream)
+    stream.synchronize()
+    return g
+
+
+def time_replays(g, stream, steps, flush, after=None):
+    """Device time of each replay (CUDA events on the launching stream), L2
+    flushed by a 256 MiB memset before every replay, outside the events."""
+    import torch
+
+    per = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            per.append((e0, e1))
+            if after is not None:
+                after()
     torch.cuda.synchronize()
-    ms = [a.elapsed_time(b) for a, b in per]
-    return ms, stats
+    return [a.elapsed_time(b) for a, b in per]
+
+
+def time_direct(fn, stream, steps, flush):
+    """Same, with the library called directly each step (no graph)."""
+    import torch
+
+    per = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(stream)
+            e1.record(stream)
+            per.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in per]
 
 
 def run_ours(args):
@@ -201,28 +243,31 @@ def run_ours(args):
     w, grid, filt, model, theta, data = build_workload(args.workload, ctx, 4 + rank, device)
     B = w.batch
     t = torch.from_numpy(theta).to(device)
-    stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
     prec = args.precision
+    lnl = torch.empty(B, dtype=torch.float64, device=device)
+    stt = torch.empty(B, dtype=torch.int32, device=device)
 
-    # warm-up
+    def step_fn(p):
+        return lambda s: model.loglike(t, p, stream=s, out=lnl, status=stt)
+
+    # one step = one sed_loglike over the batch, replayed as a CUDA graph
+    main_stream = torch.cuda.Stream(device=device)
+    graphs = {p: capture_step(step_fn(p), main_stream, warm=max(args.warmup, 3)) for p in PRECS}
     for _ in range(max(args.warmup, 3)):
-        model.loglike(t, prec, stream=stream)
+        graphs[prec].replay()
     torch.cuda.synchronize()
 
-    # timed region (profiling on: per-kernel events on the launching stream)
-    ctx.set_profiling(True)
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ms, stats = time_steps(model, ctx, t, prec, args.steps, flush, stream, profile=True)
+    ms = time_replays(graphs[prec], main_stream, args.steps, flush)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ck = clocks.stop()
-    ctx.set_profiling(False)
     total_ms = sum(ms)
     if dist:
         tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
@@ -231,7 +276,18 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     value = world * B * args.steps / (total_ms * 1e-3)
 
-    # stage statistics of the timed steps
+    # per-kernel times: direct calls with the library's per-stage events on the
+    # stream; a ~0.1 ms spin kernel ahead of each call lets the host enqueue all
+    # of the call's kernels before the GPU reaches them (no host gaps between them)
+    ctx.set_profiling(True)
+    stats = []
+    with torch.cuda.stream(main_stream):
+        for _ in range(max(5, args.steps // 2)):
+            flush.zero_()
+            torch.cuda._sleep(200000)
+            step_fn(prec)(main_stream)
+            stats.append(ctx.last_stats(main_stream))
+    ctx.set_profiling(False)
     contract_ms = [s["ms_contract"] for s in stats]
     epi_ms = [s["ms_epilogue"] for s in stats]
     prep_ms = [s["ms_prep"] for s in stats]
@@ -245,7 +301,8 @@ def run_ours(args):
     if prec == "fp32":
         peak_tf = pk["bf16_tflops_sustained"] * TF32_PER_BF16
         issued = 3 * 2.0 * B * kpad * ldn
-        peak_note = f"TF32 dense peak = sustained BF16 {pk['bf16_tflops_sustained']} x {TF32_PER_BF16:.3f} (nominal ratio), of {pk_kind}"
+        peak_note = (f"TF32 dense peak = sustained BF16 {pk['bf16_tflops_sustained']} x {TF32_PER_BF16:.3f} "
+                     f"(nominal ratio), of {pk_kind}")
     elif prec == "bf16":
         peak_tf = pk["bf16_tflops_sustained"]
         issued = 2.0 * B * kpad * ldn
@@ -255,42 +312,40 @@ def run_ours(args):
         issued = 2.0 * B * kpad * ldn
         peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz"
     achieved = alg_flop / (c_ms * 1e-3) / 1e12
-    traffic = read_traffic()
     e_ms = statistics.mean(epi_ms)
     epi_bytes = B * n_lam * 8.0 + B * 8
     roof = {"kernel": "k_contract_tc" if prec != "fp32_simt" else "k_contract_simt",
             "bound": "tensor" if prec != "fp32_simt" else "alu", "achieved": round(achieved, 3),
             "peak": round(peak_tf, 1), "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4),
-            "traffic": traffic, "peak_note": peak_note,
+            "traffic": read_traffic(), "peak_note": peak_note,
             "algorithmic_flop_per_launch": alg_flop, "nnz_w_per_launch": nnz,
             "issued_tensor_tflops": round(issued / (c_ms * 1e-3) / 1e12, 2),
             "issued_frac": round(issued / (c_ms * 1e-3) / 1e12 / peak_tf, 4),
             "contract_ms": round(c_ms, 4), "prep_ms": round(statistics.mean(prep_ms), 4),
             "epilogue_ms": round(e_ms, 4),
             "epilogue_hbm": {"bound": "hbm", "achieved_gbs": round(epi_bytes / (e_ms * 1e-3) / 1e9, 1),
-                             "peak": pk["hbm_gbs"], "frac": round(epi_bytes / (e_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                             "peak": pk["hbm_gbs"],
+                             "frac": round(epi_bytes / (e_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
                              "bytes_per_launch": epi_bytes}}
 
-    # latency percentiles of one step (device time, L2 flushed)
     p50 = float(np.percentile(ms, 50))
     p99 = float(np.percentile(ms, 99))
 
-    # other precisions, same timing method
+    # the other precisions (graph replays), and direct calls without a graph
     variants = {}
-    for vp in ("fp32_simt", "bf16", "fp32"):
-        if vp == prec:
-            continue
-        for _ in range(3):
-            model.loglike(t, vp, stream=stream)
-        vms, _ = time_steps(model, ctx, t, vp, max(10, args.steps // 2), flush, stream)
+    for vp in PRECS:
+        vms = ms if vp == prec else time_replays(graphs[vp], main_stream, max(10, args.steps // 2), flush)
         variants[vp] = {"evals_per_s": round(B * len(vms) / (sum(vms) * 1e-3), 1),
                         "ms_per_step": round(sum(vms) / len(vms), 4)}
-    variants[prec] = {"evals_per_s": round(B * args.steps / (sum(ms) * 1e-3), 1), "ms_per_step": round(sum(ms) / len(ms), 4)}
+    dms = time_direct(step_fn(prec), main_stream, max(10, args.steps // 2), flush)
+    variants[prec + "_direct_calls"] = {"evals_per_s": round(B * len(dms) / (sum(dms) * 1e-3), 1),
+                                        "ms_per_step": round(sum(dms) / len(dms), 4)}
 
     # end to end through the host-buffer entry point (pinned host theta, lnL back to host)
     th_host = torch.from_numpy(theta).pin_memory()
     lnl_host = torch.empty(B, dtype=torch.float64).pin_memory()
     st_host = torch.empty(B, dtype=torch.int32).pin_memory()
+    stream = torch.cuda.current_stream()
     for _ in range(3):
         model.loglike_host(th_host, prec, stream=stream, out=lnl_host, status=st_host)
     e2e_t = []
@@ -309,11 +364,12 @@ def run_ours(args):
     e2e = {"value": round(world * B * args.steps / e2e_total, 1), "unit": "evals/s",
            "h2d_bytes_per_step": B * ld * 4, "d2h_bytes_per_step": B * 8 + B * 4,
            "p50_ms": round(1e3 * float(np.percentile(e2e_t, 50)), 4),
-           "p99_ms": round(1e3 * float(np.percentile(e2e_t, 99)), 4)}
+           "p99_ms": round(1e3 * float(np.percentile(e2e_t, 99)), 4),
+           "what": "sed_loglike_host: pinned host theta -> device, prep/contraction/epilogue, lnL + status -> host"}
 
     # GPU results for the accuracy comparison of the CPU-baseline leg
     gpu_res = {}
-    for vp in ("fp32", "fp32_simt", "bf16"):
+    for vp in PRECS:
         l, s = model.loglike(t, vp, stream=stream)
         ph, _ = model.forward(t, vp, stream=stream)
         torch.cuda.synchronize()
@@ -328,14 +384,15 @@ def run_ours(args):
                       "n_feh": int(grid.flux.shape[1]), "n_lam": int(grid.flux.shape[3]),
                       "n_sfh": w.n_sfh, "n_filt": int(len(filt[0])), "nebular": bool(w.use_nebular),
                       "dust": "birth-cloud power law + Kriek & Conroy 2013 diffuse",
-                      "precision": {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
-                                    "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
-                                    "fp32_simt": "FP32 FFMA contraction, FP64 lnL"}[prec],
+                      "precision": PREC_NOTE[prec],
+                      "step": "one sed_loglike call over the batch (3 kernels), replayed as a CUDA graph",
                       "l2": "flushed before every timed step (256 MiB memset, outside the timing)",
                       "parallelism": f"replicas x{world} (independent batches per GPU)"},
-           "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "what": "device time of one 1024-row step"},
+           "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "what": "device time of one batch step"},
            "variants": variants, "roofline": roof, "clocks": ck, "e2e": e2e,
            "gpu_launches": 3 * args.steps}
+    if rank == 0 and world == 1 and not args.no_grad:
+        out["gradient"] = bench_gradient(ctx, device, flush, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy_vs_fp64_oracle"] = cpu_baseline(w, grid, filt, data, theta, gpu_res,
                                                                             args.cpu_seconds)
@@ -345,6 +402,32 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def bench_gradient(ctx, device, flush, args):
+    """Forward + adjoint (sed_loglike_grad) on the spectro-photometric [a/Fe]
+    workload (107 x 12 x 5 x 6000 grid, 1500-pixel spectrum + 20 filters,
+    2048 rows), one graph replay per step."""
+    import torch
+
+    w, grid, filt, model, theta, data = build_workload(GRAD_WORKLOAD, ctx, 4, device)
+    B = w.batch
+    t = torch.from_numpy(theta).to(device)
+    lnl = torch.empty(B, dtype=torch.float64, device=device)
+    grad = torch.empty_like(t)
+    stt = torch.empty(B, dtype=torch.int32, device=device)
+    s = torch.cuda.Stream(device=device)
+    res = {"workload": w.name, "batch": B, "n_param": int(theta.shape[1])}
+    for p in ("fp32", "fp32_simt"):
+        g = capture_step(lambda st, p=p: model.loglike_grad(t, p, stream=st, out=(lnl, grad, stt)), s)
+        gms = time_replays(g, s, max(5, args.steps // 4), flush)
+        fwd = capture_step(lambda st, p=p: model.loglike(t, p, stream=st, out=lnl, status=stt), s)
+        fms = time_replays(fwd, s, max(5, args.steps // 4), flush)
+        res[p] = {"grad_evals_per_s": round(B * len(gms) / (sum(gms) * 1e-3), 1),
+                  "grad_ms_per_step": round(sum(gms) / len(gms), 4),
+                  "loglike_evals_per_s": round(B * len(fms) / (sum(fms) * 1e-3), 1),
+                  "loglike_ms_per_step": round(sum(fms) / len(fms), 4)}
+    return res
 
 
 def read_traffic():
@@ -375,18 +458,23 @@ def cpu_baseline(w, grid, filt, data, theta32, gpu_res, seconds):
     orc = _oracle_for(w, grid, filt, data)
     cores = os.cpu_count() or 1
     th64 = theta32.astype(np.float64)
-    rows, t_used, chunk = 0, 0.0, 64
+    rows, evals, t_used, chunk = 0, 0, 0.0, 64
     ref_lnl, ref_ph, ref_st = [], [], []
-    while t_used < seconds and rows < th64.shape[0]:
-        sl = slice(rows, min(rows + chunk, th64.shape[0]))
+    # one pass over the batch for the accuracy comparison, then repeated passes
+    # until about `seconds` of CPU work have been timed
+    while t_used < seconds:
+        lo = evals % th64.shape[0]
+        sl = slice(lo, min(lo + chunk, th64.shape[0]))
         t0 = time.perf_counter()
         r = orc.eval(th64[sl], nthreads=cores)
         t_used += time.perf_counter() - t0
-        ref_lnl.append(r["lnl"]); ref_ph.append(r["phot"]); ref_st.append(r["status"])
-        rows = sl.stop
-    cb = {"value": round(rows / t_used, 2), "unit": "evals/s", "cores": cores, "kind": "oracle",
-          "sample": f"first {rows} of the {th64.shape[0]} parameter rows of the workload, FP64 C oracle, "
-                    f"OpenMP over rows ({t_used:.1f} s)"}
+        evals += sl.stop - sl.start
+        if rows < th64.shape[0] and sl.start == rows:
+            ref_lnl.append(r["lnl"]); ref_ph.append(r["phot"]); ref_st.append(r["status"])
+            rows = sl.stop
+    cb = {"value": round(evals / t_used, 2), "unit": "evals/s", "cores": cores, "kind": "oracle",
+          "sample": f"{evals} evaluations cycling over the {th64.shape[0]} parameter rows of the workload, "
+                    f"FP64 C oracle, OpenMP over rows ({t_used:.1f} s)"}
     ref_lnl, ref_ph, ref_st = np.concatenate(ref_lnl), np.concatenate(ref_ph), np.concatenate(ref_st)
     ok = ref_st == 0
     c = -0.5 * np.sum(np.log(2 * np.pi * data[1] ** 2))
@@ -395,7 +483,7 @@ def cpu_baseline(w, grid, filt, data, theta32, gpu_res, seconds):
     for vp, (l, s, ph) in gpu_res.items():
         l, ph = l[:rows][ok], ph[:rows][ok]
         rp = ref_ph[ok]
-        good = rp > 0
+        good = rp > 1e-6 * np.abs(rp).max(axis=1, keepdims=True)
         e_f = np.abs(ph[good] - rp[good]) / rp[good]
         e_l = np.abs(l - ref_lnl[ok]) / scale
         e_l_raw = np.abs(l - ref_lnl[ok]) / np.abs(ref_lnl[ok])

@@ -188,11 +188,16 @@ class Model:
         self.ctx._check(st)
         return lnl, stt
 
-    def loglike_grad(self, theta: torch.Tensor, precision="fp32", stream=None):
+    def loglike_grad(self, theta: torch.Tensor, precision="fp32", stream=None, out=None):
+        """lnL [n] (FP64), dlnL/dtheta [n, ld] (FP32) and row status [n]; `out` may
+        give the three output tensors."""
         n, ld = self._theta(theta)
-        lnl = torch.empty(n, dtype=torch.float64, device=theta.device)
-        grad = torch.empty((n, ld), dtype=torch.float32, device=theta.device)
-        stt = torch.empty(n, dtype=torch.int32, device=theta.device)
+        if out is not None:
+            lnl, grad, stt = out
+        else:
+            lnl = torch.empty(n, dtype=torch.float64, device=theta.device)
+            grad = torch.empty((n, ld), dtype=torch.float32, device=theta.device)
+            stt = torch.empty(n, dtype=torch.int32, device=theta.device)
         st = self.ctx._lib.sed_loglike_grad(self.ctx._h, self.id, C.c_void_p(theta.data_ptr()), n, ld,
                                             C.c_void_p(lnl.data_ptr()), C.c_void_p(grad.data_ptr()),
                                             C.c_void_p(stt.data_ptr()), _prec(precision),
