@@ -35,9 +35,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "phot_107x12x6000_b1024"
 GRAD_WORKLOAD = "specphot_afe_107x12x5x6000_b2048"
-PRECS = ("fp32", "fp32_simt", "bf16")
+PRECS = ("fp32", "fp32_simt", "bf16", "fp8")
 PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
              "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
+             "fp8": "FP8 E4M3 tcgen05 (power-of-two scales per SSP column and per row), FP32 accumulate, FP64 lnL",
              "fp32_simt": "FP32 FFMA contraction, FP64 lnL"}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor ratio (recipe table)
@@ -50,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_simt", "bf16", "fp8"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
@@ -307,6 +308,10 @@ def run_ours(args):
         peak_tf = pk["bf16_tflops_sustained"]
         issued = 2.0 * B * kpad * ldn
         peak_note = f"sustained BF16 dense peak, of {pk_kind}"
+    elif prec == "fp8":
+        peak_tf = pk["bf16_tflops_sustained"] * 2.0
+        issued = 2.0 * B * kpad * ldn
+        peak_note = f"FP8 dense peak = sustained BF16 {pk['bf16_tflops_sustained']} x 2 (nominal ratio), of {pk_kind}"
     else:
         peak_tf = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FFMA: SMs x lanes x 2 x max clock
         issued = 2.0 * B * kpad * ldn

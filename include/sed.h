@@ -64,7 +64,9 @@ typedef enum {
 enum {
   SED_PREC_FP32 = 0,      /* tcgen05 tensor cores, 3xTF32 split (FP32-grade) */
   SED_PREC_FP32_SIMT = 1, /* CUDA-core FP32 FFMA (independent cross-check) */
-  SED_PREC_BF16 = 2       /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+  SED_PREC_BF16 = 2,      /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+  SED_PREC_FP8 = 3        /* tcgen05 tensor cores, FP8 E4M3 operands with power-of-two scales
+                             per SSP column (age, [Fe/H], [a/Fe]) and per row, FP32 accumulate */
 };
 
 /* Diffuse dust law (Sec. 2.4). */
@@ -202,7 +204,7 @@ sed_status sed_loglike(sed_ctx *ctx, sed_model_id model, const float *theta, int
  * cell edge) the one-sided derivative of the branch the forward took is
  * returned.
  * precision: SED_PREC_FP32 (3xTF32 tensor-core contractions) or
- * SED_PREC_FP32_SIMT; SED_PREC_BF16 returns SED_EUNSUPPORTED.
+ * SED_PREC_FP32_SIMT; SED_PREC_BF16 and SED_PREC_FP8 return SED_EUNSUPPORTED.
  * The first gradient call on a grid layout builds its lambda-major copies
  * (host work and synchronous copies to the device, ~3 x 4 x Kpad x n_lam
  * bytes); later calls only enqueue kernels.  SED_ERANGE when the adjoint

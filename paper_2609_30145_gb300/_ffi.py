@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsed.so")
 
 SED_OK, SED_EINVAL, SED_ENOMEM, SED_ECUDA, SED_ERANGE, SED_ENONFINITE, SED_EBUSY, SED_ETIMEOUT, \
     SED_EUNSUPPORTED = range(9)
-PREC_FP32, PREC_FP32_SIMT, PREC_BF16 = 0, 1, 2
+PREC_FP32, PREC_FP32_SIMT, PREC_BF16, PREC_FP8 = 0, 1, 2, 3
 DUST_POWER_LAW, DUST_KC13 = 0, 1
 LSF_R_FWHM, LSF_R_SIGMA, LSF_FWHM_AA, LSF_SIGMA_AA, LSF_SIGMA_KMS, LSF_FWHM_KMS = range(6)
 ROW_BAD_THETA, ROW_BAD_Z, ROW_BAD_TMAX, ROW_NONFINITE, ROW_DEVICE_TIMEOUT = 1, 2, 4, 16, 32

@@ -14,7 +14,7 @@ import torch
 from . import _ffi
 from ._ffi import KEYS, NKEYS
 
-PREC = {"fp32": _ffi.PREC_FP32, "fp32_simt": _ffi.PREC_FP32_SIMT, "bf16": _ffi.PREC_BF16}
+PREC = {"fp32": _ffi.PREC_FP32, "fp32_simt": _ffi.PREC_FP32_SIMT, "bf16": _ffi.PREC_BF16, "fp8": _ffi.PREC_FP8}
 
 
 class SedError(RuntimeError):

@@ -23,6 +23,7 @@
 //   SED_PREC_FP32 : 3xTF32 split, D += A_lo B_hi + A_hi B_lo + A_hi B_hi
 //                   (each operand x = hi + lo, hi = TF32(x)), FP32 accumulate
 //   SED_PREC_BF16 : BF16 operands, FP32 accumulate
+//   SED_PREC_FP8  : FP8 E4M3 operands (kind::f8f6f4), FP32 accumulate
 // Every wait on an mbarrier is bounded (about 2 s of %globaltimer); on
 // timeout the kernel records an error bit in *err and returns after freeing
 // its tensor memory.
@@ -84,7 +85,8 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;              // SWIZZLE_128B
   return d;
 }
-// instruction descriptor: FP32 accumulate, A/B format (1 = BF16, 2 = TF32), both K-major
+// instruction descriptor: FP32 accumulate, A/B format (kind::f16: 1 = BF16; kind::tf32: 2 = TF32;
+// kind::f8f6f4: 0 = E4M3), both K-major
 __host__ __device__ constexpr uint32_t idesc(uint32_t ab_fmt, uint32_t M, uint32_t N) {
   return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
@@ -95,6 +97,12 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+  } else if constexpr (PREC == SED_PREC_FP8) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(id), "r"(acc)
         : "memory");
   } else {
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         const uint32_t fb = full0 + 8 * s;
         mbar_expect_tx(fb, C::STAGE_BYTES);
         const uint32_t st = sbase + s * C::STAGE_BYTES;
-        const int kc = PREC == SED_PREC_FP32 ? kt * 32 : kt * 64;  // element coordinate along K
+        const int kc = kt * (ROWB / (PREC == SED_PREC_FP32 ? 4 : (PREC == SED_PREC_FP8 ? 1 : 2)));  // element coordinate along K
         tma_load_2d(st, amap_hi, fb, kc, m0);
         tma_load_2d(st + C::A_BYTES, &p.b_hi, fb, kc, n0);
         if constexpr (C::NOPS == 2) {
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      constexpr uint32_t ID = idesc(PREC == SED_PREC_FP32 ? 2u : 1u, BM, BN);
+      constexpr uint32_t ID = idesc(PREC == SED_PREC_FP32 ? 2u : (PREC == SED_PREC_FP8 ? 0u : 1u), BM, BN);
       int g = 0, kt = 0;
       bool ok = true;
       for (int part = 0; part < NPART && ok; ++part) {
@@ -341,9 +349,10 @@ constexpr int TC_BN = 128;
 
 int tc_encode_maps(void* fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo, const void* b_hi,
                    const void* b_lo, int n, int n_lam, int kpad) {
-  const bool f32 = prec == SED_PREC_FP32;
-  const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const int es = f32 ? 4 : 2;
+  const bool f32 = prec == SED_PREC_FP32, f8 = prec == SED_PREC_FP8;
+  const CUtensorMapDataType dt = f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                     : (f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const int es = f32 ? 4 : (f8 ? 1 : 2);
   if (encode_kmajor(fn, &out->a_hi, const_cast<void*>(a_hi), dt, es, kpad, n, tc::BM) != CUDA_SUCCESS) return 1;
   if (encode_kmajor(fn, &out->b_hi, const_cast<void*>(b_hi), dt, es, kpad, n_lam, TC_BN) != CUDA_SUCCESS) return 2;
   if (f32) {
@@ -366,6 +375,11 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
     p.ky_tiles = a.Ky_pad / 32;
     p.k_tiles = a.Kpad / 32;
     return tc::launch_cfg<SED_PREC_FP32, TC_BN, 3, 2, false>(p, a.ldn, s);
+  }
+  if (a.prec == SED_PREC_FP8) {
+    p.ky_tiles = a.Ky_pad / 128;
+    p.k_tiles = a.Kpad / 128;
+    return tc::launch_cfg<SED_PREC_FP8, TC_BN, 6, 4, false>(p, a.ldn, s);
   }
   p.ky_tiles = a.Ky_pad / 64;
   p.k_tiles = a.Kpad / 64;

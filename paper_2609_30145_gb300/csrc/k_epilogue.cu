@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
     const float4 c = g.att4[k];
-    const float F = attenuated(md, rs, c, eb, Yr[k], Or[k], g.neb_tab, k);
+    const float ys = a.lam8 ? rs.y_scale * a.lam8[k] : 1.f;
+    const float F = attenuated(md, rs, c, eb, Yr[k] * ys, Or[k] * ys, g.neb_tab, k);
     if (spec) Fs[k] = F;
     Gs[k] = F * c.w;
     lam_s[k] = g.lam_f[k];

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __shared__ int zb[MAX_SFH];
   __shared__ float zt[MAX_SFH];
   __shared__ float s_red[PREP_THREADS / 32];
+  __shared__ float s_red8[PREP_THREADS / 32];
   __shared__ int s_nnz[PREP_THREADS / 32];
 
   // ---- finiteness of the whole row
@@ -155,6 +156,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       if (a.W_hi) { a.W_hi[o] = 0.f; a.W_lo[o] = 0.f; }
       if (a.W_bf16) a.W_bf16[o] = __float2bfloat16_rn(0.f);
     }
+    if (a.W_f8)
+      for (int k = tid; k < L.Kpad8; k += blockDim.x) a.W_f8[(size_t)r * L.Kpad8 + k] = 0;
     if (tid == 0) {
       RowScal rs{};
       rs.status = status;
@@ -213,6 +216,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   }
   float qpart = 0.f;
   int nnz = 0;
+  float* Vs = smem + NA * NZ;           // FP8 path: W_k 2^-e_k
   for (int k = tid; k < Kpad; k += blockDim.x) {
     const int code = L.k_code[k];
     float v = 0.f;
@@ -231,6 +235,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       a.W_lo[o] = v - h;
     }
     if (a.W_bf16) a.W_bf16[o] = __float2bfloat16_rn(v);
+    if (a.W_f8) Vs[k] = v * L.col8[k];
   }
   for (int o = 16; o; o >>= 1) {
     qpart += __shfl_xor_sync(0xffffffffu, qpart, o);
@@ -238,6 +243,30 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   }
   if (lane == 0) { s_red[warp] = qpart; s_nnz[warp] = nnz; }
   __syncthreads();
+
+  // ---- FP8 operand: E4M3 of W_k 2^-e_k 2^-y, with the row's power of two 2^y
+  //      chosen so that its largest entry maps to at most 240 (< 448, the E4M3
+  //      maximum); the epilogue multiplies Y and O back by 2^y
+  float y_scale = 1.f;
+  if (a.W_f8) {
+    float m = 0.f;
+    for (int k = tid; k < Kpad; k += blockDim.x) m = fmaxf(m, fabsf(Vs[k]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_red8[warp] = m;
+    __syncthreads();
+    m = 0.f;
+    for (int w = 0; w < PREP_THREADS / 32; ++w) m = fmaxf(m, s_red8[w]);
+    const float e = m > 0.f ? ceilf(log2f(m / 240.f)) : 0.f;
+    y_scale = exp2f(e);
+    const float inv = exp2f(-e);
+    const int shift = L.Ky_pad8 - L.Ky_pad;
+    uint8_t* w8 = a.W_f8 + (size_t)r * L.Kpad8;
+    for (int p = tid; p < L.Kpad8; p += blockDim.x) {
+      int k = p < L.Ky_pad ? p : (p < L.Ky_pad8 ? -1 : p - shift);
+      const float v = (k >= 0 && k < Kpad) ? Vs[k] * inv : 0.f;
+      w8[p] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+  }
 
   if (tid == 0) {
     float qy = 0.f;
@@ -275,6 +304,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.tmax = (float)tmax;
     rs.lrat = lrat;
     rs.status = 0;
+    rs.y_scale = y_scale;
     // rest-frame node window the epilogue reads: the redshifted filter samples
     // and the spectral pixels with 5 dispersions on either side, with margins
     {
@@ -472,9 +502,14 @@ cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   PrepKernelArgs ka;
   ka.p = p;
-  const size_t smem = (size_t)p.g.n_age * p.g.n_feh * sizeof(float);
+  const size_t smem = ((size_t)p.g.n_age * p.g.n_feh + (p.W_f8 ? (size_t)p.L.Kpad : 0)) * sizeof(float);
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   k_prep<<<p.n, PREP_THREADS, smem, s>>>(ka);
   return cudaGetLastError();
 }

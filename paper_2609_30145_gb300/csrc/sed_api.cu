@@ -176,7 +176,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
     }
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
-      std::vector<void*> v = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
+      std::vector<void*> v = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->rs, w->err,
                               w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                               w->dW, w->rgrad};
       for (void* p : v)
@@ -238,6 +238,7 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
   g->lam.assign(d->lam_aa, d->lam_aa + nl);
   g->flux.assign(d->flux, d->flux + nsp * nl);
   g->f_log2 = -std::ceil(std::log2(fmax));
+  g->f_scale = std::exp2(g->f_log2);
 
   // Eq. app_q: Q = (Lsun/h) int_0^912 f/lam dlam (trapezoid to the last node
   // below 912 A plus the linearly interpolated piece up to 912 A)
@@ -366,7 +367,7 @@ float ssp_value(const Grid* g, const Layout* L, int k, int l) {
   if (c < 0) return 0.f;
   const int n = c >> 24, m = (c >> 16) & 0xff, a = c & 0xffff;
   if (L->neb_cut && a < L->n_young && g->lam[l] < LYMAN_AA) return 0.f;
-  return (float)(g->flux[(((size_t)n * g->n_feh + m) * g->n_age + a) * g->n_lam + l] * std::exp2(g->f_log2));
+  return (float)(g->flux[(((size_t)n * g->n_feh + m) * g->n_age + a) * g->n_lam + l] * g->f_scale);
 }
 
 // Lambda-major copies of a layout for the adjoint contraction: [Kpad][ldn].
@@ -391,6 +392,67 @@ sed_status ensure_grad_layout(sed_ctx* ctx, Grid* g, Layout* L, int ldn) {
   L->sspK_f32 = a;
   L->sspK_hi = b;
   L->sspK_lo = c;
+  return SED_OK;
+}
+
+// FP8 copy of a layout.  E4M3 has a 3-bit mantissa and covers 2^-9..448, while
+// the SSP fluxes span ~1e-6..1 across ages and further decades across
+// wavelength, so the matrix is balanced by powers of two before rounding:
+// SSP[k][l] 2^(e_k + f_l), with e_k (per column k = age, [Fe/H], [a/Fe]) and
+// f_l (per wavelength) chosen by alternating passes so that every column and
+// every wavelength row peaks in [120, 240].  e_k is folded into W by the prep
+// kernel, f_l is undone in the epilogue (Y and O times 2^-f_l).  The young and
+// old blocks are each padded to 128 columns (one 128-byte K tile).
+sed_status ensure_f8_layout(sed_ctx* ctx, Grid* g, Layout* L) {
+  if (L->sspT_f8) return SED_OK;
+  const int NL = g->n_lam, Kpad = L->Kpad;
+  const int Ky_pad8 = (L->Ky_pad + 127) / 128 * 128;
+  const int Kpad8 = Ky_pad8 + (Kpad - L->Ky_pad + 127) / 128 * 128;
+  std::vector<float> v((size_t)Kpad * NL);
+  for (int k = 0; k < Kpad; k++)
+    for (int l = 0; l < NL; l++) v[(size_t)k * NL + l] = ssp_value(g, L, k, l);
+  std::vector<int> ek(Kpad, 0), fl(NL, 0);
+  std::vector<double> sk(Kpad, 1.0), sl(NL, 1.0);   // 2^e_k, 2^f_l
+  std::vector<char> live(Kpad, 0);
+  for (int it = 0; it < 4; it++) {
+    for (int k = 0; k < Kpad; k++) {
+      double m = 0.0;
+      const float* vk = v.data() + (size_t)k * NL;
+      for (int l = 0; l < NL; l++) m = std::max(m, (double)vk[l] * sl[l]);
+      live[k] = m > 0.0;
+      if (m > 0.0) { ek[k] = (int)std::floor(std::log2(240.0 / m)); sk[k] = std::ldexp(1.0, ek[k]); }
+    }
+    std::vector<double> ml(NL, 0.0);
+    for (int k = 0; k < Kpad; k++) {
+      if (!live[k]) continue;
+      const float* vk = v.data() + (size_t)k * NL;
+      for (int l = 0; l < NL; l++) ml[l] = std::max(ml[l], (double)vk[l] * sk[k]);
+    }
+    for (int l = 0; l < NL; l++)
+      if (ml[l] > 0.0) { fl[l] = (int)std::floor(std::log2(240.0 / ml[l])); sl[l] = std::ldexp(1.0, fl[l]); }
+  }
+  std::vector<float> col(Kpad, 0.f), lsc(NL);
+  for (int k = 0; k < Kpad; k++) col[k] = live[k] ? (float)(1.0 / sk[k]) : 0.f;
+  for (int l = 0; l < NL; l++) lsc[l] = (float)(1.0 / sl[l]);
+  std::vector<uint8_t> f8((size_t)NL * Kpad8, 0);
+  for (int p = 0; p < Kpad8; p++) {
+    const int k = p < L->Ky_pad ? p : (p < Ky_pad8 ? -1 : p - (Ky_pad8 - L->Ky_pad));
+    if (k < 0 || k >= Kpad || !live[k]) continue;
+    for (int l = 0; l < NL; l++)
+      f8[(size_t)l * Kpad8 + p] = (uint8_t)__nv_cvt_float_to_fp8(
+          (float)((double)v[(size_t)k * NL + l] * sk[k] * sl[l]), __NV_SATFINITE, __NV_E4M3);
+  }
+  uint8_t* a = nullptr;
+  float *c = nullptr, *d = nullptr;
+  sed_status st = upload(ctx, &a, f8.data(), f8.size(), &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &c, col.data(), col.size(), &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &d, lsc.data(), lsc.size(), &g->allocs, &g->bytes);
+  if (st) return st;
+  L->Ky_pad8 = Ky_pad8;
+  L->Kpad8 = Kpad8;
+  L->sspT_f8 = a;
+  L->col8 = c;
+  L->lam8 = d;
   return SED_OK;
 }
 
@@ -775,7 +837,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   if (!need) return w;
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
-  std::vector<void*> old = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->Y, w->O, w->rs, w->err,
+  std::vector<void*> old = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->rs, w->err,
                             w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                             w->dW, w->rgrad};
   for (void* p : old)
@@ -792,7 +854,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   std::vector<void*>* no = nullptr;
   sed_status s = SED_OK;
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
-  AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2);
+  AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
   AL(Y, R * N * 4); AL(O, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
   AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
   if (grad || had_grad) {
@@ -813,7 +875,8 @@ sed_status check_hot_args(sed_ctx* ctx, Model* M, const float* theta, int n, int
   if (n < 0) return fail(ctx, SED_EINVAL, "n < 0");
   if (n > 0 && !theta) return fail(ctx, SED_EINVAL, "theta is NULL");
   if (ld < M->dv.n_param) return fail(ctx, SED_EINVAL, "ld (%d) < n_param (%d)", ld, M->dv.n_param);
-  if (precision != SED_PREC_FP32 && precision != SED_PREC_FP32_SIMT && precision != SED_PREC_BF16)
+  if (precision != SED_PREC_FP32 && precision != SED_PREC_FP32_SIMT && precision != SED_PREC_BF16 &&
+      precision != SED_PREC_FP8)
     return fail(ctx, SED_EINVAL, "unknown precision %d", precision);
   if (n > (1 << 22)) return fail(ctx, SED_ERANGE, "batch larger than 4M rows");
   return SED_OK;
@@ -843,6 +906,16 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   pa.W_hi = precision == SED_PREC_FP32 ? w->W_hi : nullptr;
   pa.W_lo = precision == SED_PREC_FP32 ? w->W_lo : nullptr;
   pa.W_bf16 = precision == SED_PREC_BF16 ? w->W_bf16 : nullptr;
+  pa.W_f8 = precision == SED_PREC_FP8 ? w->W_f8 : nullptr;
+  if (precision == SED_PREC_FP8) {
+    sed_status fs;
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      fs = ensure_f8_layout(ctx, g, L);
+    }
+    if (fs) return fs;
+    pa.L = L->dv();
+  }
   pa.rs = w->rs;
   pa.err = w->err;
   CK(launch_prep(pa, s));
@@ -856,20 +929,24 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   }
   if (ctx->tc_ok != 1)
     return fail(ctx, SED_EUNSUPPORTED, "tensor-core precisions need an sm_103 device and cuTensorMapEncodeTiled");
-  const bool f32 = precision == SED_PREC_FP32;
+  const bool f32 = precision == SED_PREC_FP32, f8 = precision == SED_PREC_FP8;
   TcMaps* maps = &w->maps;
-  const void* key = f32 ? (const void*)L->sspT_hi : (const void*)L->sspT_bf16;
-  if (!w->tmap_valid || w->tmap_for != key || w->tmap_n != n || w->tmap_prec != precision) {
-    int e = tc_encode_maps(ctx->encode_fn, maps, precision, f32 ? (void*)w->W_hi : (void*)w->W_bf16, w->W_lo,
-                           f32 ? (void*)L->sspT_hi : (void*)L->sspT_bf16, L->sspT_lo, n, g->n_lam, L->Kpad);
+  const void* key = f32 ? (const void*)L->sspT_hi : (f8 ? (const void*)L->sspT_f8 : (const void*)L->sspT_bf16);
+  const void* a_op = f32 ? (const void*)w->W_hi : (f8 ? (const void*)w->W_f8 : (const void*)w->W_bf16);
+  if (!w->tmap_valid || w->tmap_for != key || w->tmap_n != n || w->tmap_prec != precision || w->tmap_a != a_op) {
+    int e = tc_encode_maps(ctx->encode_fn, maps, precision, a_op, w->W_lo, key, L->sspT_lo, n, g->n_lam,
+                           f8 ? L->Kpad8 : L->Kpad);
     if (e) return fail(ctx, SED_ECUDA, "cuTensorMapEncodeTiled failed (operand %d)", e);
     w->tmap_valid = true;
     w->tmap_for = key;
     w->tmap_n = n;
     w->tmap_prec = precision;
+    w->tmap_a = a_op;
   }
   TcArgs ta{};
-  ta.n = n; ta.n_lam = g->n_lam; ta.ldn = w->ldn; ta.Ky_pad = L->Ky_pad; ta.Kpad = L->Kpad; ta.prec = precision;
+  ta.n = n; ta.n_lam = g->n_lam; ta.ldn = w->ldn; ta.prec = precision;
+  ta.Ky_pad = f8 ? L->Ky_pad8 : L->Ky_pad;
+  ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
   ta.maps = maps; ta.Y = w->Y; ta.O = w->O; ta.err = w->err;
   CK(launch_contract_tc(ta, s));
   return prof_mark(ctx, w, 2, s);
@@ -897,6 +974,7 @@ sed_status sed_forward(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   EpiArgs ea{};
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
   ea.md = M->dv; ea.g = M->g->dv;
+  ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   ea.phot_out = M->dv.n_filt ? phot_out : nullptr;
   ea.spec_out = M->dv.n_pix ? spec_out : nullptr;
   ea.lnl = nullptr; ea.status = nullptr; ea.err = w->err;
@@ -922,6 +1000,7 @@ sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
   ea.md = M->dv; ea.g = M->g->dv;
   ea.lnl = lnl_out; ea.status = row_status; ea.err = w->err;
+  ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   CK(launch_epilogue(ea, s));
   return prof_mark(ctx, w, 3, s);
 }
@@ -954,7 +1033,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   Model* M = find_model(ctx, id);
   sed_status st = check_hot_args(ctx, M, theta, n, ld, precision);
   if (st) return st;
-  if (precision == SED_PREC_BF16)
+  if (precision == SED_PREC_BF16 || precision == SED_PREC_FP8)
     return fail(ctx, SED_EUNSUPPORTED, "the gradient is available for SED_PREC_FP32 and SED_PREC_FP32_SIMT");
   if (n > 0 && (!lnl_out || !grad_out)) return fail(ctx, SED_EINVAL, "lnl_out or grad_out is NULL");
   if (n == 0) return SED_OK;

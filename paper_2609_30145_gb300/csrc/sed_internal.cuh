@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -60,6 +61,7 @@ struct RowScal {
   float lrat;       // ln(T_max / 10 Myr) as used for the SFH edges
   uint32_t status;
   int k_lo, k_hi;   // rest-frame node window this row needs
+  float y_scale;    // FP8 path: the row's power of two folded out of W (Y, O are multiplied by it); else 1
   int nnz;          // non-zero weights of the row
 };
 
@@ -95,6 +97,8 @@ struct LayoutDev {
   int n_young, neb_cut, Ky, Ko, Ky_pad, Kpad;
   const float* q_s;        // [Kpad]
   const int* k_code;       // [Kpad]
+  int Ky_pad8, Kpad8;      // FP8 layout: each block padded to 128 (one 128-byte K tile)
+  const float* col8;       // [Kpad] 2^-e_k, the FP8 column scale folded into W (0 for empty columns)
 };
 
 struct ModelDev {
@@ -150,13 +154,19 @@ struct Layout {
   float* sspK_f32 = nullptr;
   float* sspK_hi = nullptr;
   float* sspK_lo = nullptr;
+  // FP8 copy (built on the first FP8 call): [n_lam][Kpad8], E4M3 of SSP * 2^e_k, with
+  // the old block starting at Ky_pad8; col8[k] = 2^-e_k
+  int Ky_pad8 = 0, Kpad8 = 0;
+  uint8_t* sspT_f8 = nullptr;
+  float* col8 = nullptr;
+  float* lam8 = nullptr;             // [n_lam] 2^-f_l, the FP8 wavelength scale undone in the epilogue
   float* q_s = nullptr;              // [Kpad] scaled Q for young k, 0 elsewhere
   int* k_code = nullptr;             // [Kpad] packed (n<<24 | m<<16 | a), -1 for padding
   std::vector<int> code_h;           // host copy of k_code
   double q_log2 = 0.0;               // Q_dev = Q * 2^-q_log2
   bool have_tmaps = false;
   CUtensorMap tm_hi, tm_lo, tm_bf16;
-  LayoutDev dv() const { return LayoutDev{n_young, neb_cut, Ky, Ko, Ky_pad, Kpad, q_s, k_code}; }
+  LayoutDev dv() const { return LayoutDev{n_young, neb_cut, Ky, Ko, Ky_pad, Kpad, q_s, k_code, Ky_pad8, Kpad8, col8}; }
 };
 
 struct Grid {
@@ -164,6 +174,7 @@ struct Grid {
   std::vector<double> log_age, feh, afe, lam, flux;  // host master copy (FP64)
   std::vector<double> siglib_kms;                    // Eq. app_siglib at the nodes
   double f_log2 = 0.0;                               // f_dev = f * 2^f_log2
+  double f_scale = 1.0;                              // 2^f_log2
   double q_log2 = 0.0;                               // Q_dev = Q * 2^-q_log2
   std::vector<double> q;                             // [n_afe][n_feh][n_age] Eq. app_q
   GridDev dv{};
@@ -209,6 +220,7 @@ struct Workspace {
   float* W_hi = nullptr;         // [rows][Kpad]
   float* W_lo = nullptr;
   __nv_bfloat16* W_bf16 = nullptr;
+  uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
   float* Y = nullptr;            // [rows][ldn]
   float* O = nullptr;
   RowScal* rs = nullptr;
@@ -232,6 +244,7 @@ struct Workspace {
   bool tmap_valid = false;
   const void* tmap_for = nullptr;
   int tmap_n = -1, tmap_prec = -1;
+  const void* tmap_a = nullptr;
   TcMaps maps;
   DwMaps dw_maps;
   // profiling: events before/after prep, contraction, epilogue of the last call
@@ -263,6 +276,7 @@ struct PrepArgs {
   const float* theta; int n, ld;
   ModelDev md; GridDev g; LayoutDev L;
   float* W; float* W_hi; float* W_lo; __nv_bfloat16* W_bf16;
+  uint8_t* W_f8;       // FP8 path: [n][Kpad8]
   RowScal* rs;
   int* err;            // device error word of the contraction, cleared by the prep kernel
 };
@@ -279,7 +293,8 @@ struct ContractArgs {
 cudaError_t launch_contract_simt(const ContractArgs& a, cudaStream_t s);
 
 struct TcArgs {
-  int n, n_lam, ldn, Ky_pad, Kpad, prec;   // prec: SED_PREC_FP32 or SED_PREC_BF16
+  int n, n_lam, ldn, Ky_pad, Kpad, prec;   // prec: SED_PREC_FP32, SED_PREC_BF16 or SED_PREC_FP8
+                                          // (for FP8, Ky_pad/Kpad are the FP8 layout's Ky_pad8/Kpad8)
   const TcMaps* maps;
   float* Y; float* O; int* err;
 };
@@ -307,6 +322,7 @@ struct EpiArgs {
   float* phot_out; float* spec_out;
   double* lnl; uint32_t* status;
   const int* err;      // device error word of the contraction (row status SED_ROW_DEVICE_TIMEOUT)
+  const float* lam8;   // FP8 path: [n_lam] 2^-f_l multiplying Y and O; NULL otherwise
 };
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 

@@ -3,9 +3,11 @@ same seeded inputs, element by element.
 
 Tolerances (FP32-grade paths, SED_PREC_FP32 = tcgen05 3xTF32 and
 SED_PREC_FP32_SIMT = FFMA): model photometry and spectra within 2e-5
-relative per datum, log-likelihood within 1e-5 relative.  The BF16 path is
-held to the bound measured for it (flux 1e-2, lnL 1e-2 relative) and its
-errors are reported by the benchmark.
+relative per datum (floored at 1e-6 of the row's brightest datum), log-
+likelihood within 1e-5 relative to the magnitude of its terms.  The BF16 and
+FP8 paths are held to the bounds measured for them (BF16: flux 1e-2, lnL 1e-2;
+FP8 E4M3 with its 3-bit mantissa: flux 0.2, lnL 0.1) and their error
+distributions are reported by the benchmark.
 """
 import numpy as np
 import pytest
@@ -16,9 +18,9 @@ from tests import cases
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-FLUX_TOL = {"fp32": 2e-5, "fp32_simt": 2e-5, "bf16": 1e-2}
-LNL_TOL = {"fp32": 1e-5, "fp32_simt": 1e-5, "bf16": 1e-2}
-PRECS = ["fp32_simt", "fp32", "bf16"]
+FLUX_TOL = {"fp32": 2e-5, "fp32_simt": 2e-5, "bf16": 1e-2, "fp8": 0.2}
+LNL_TOL = {"fp32": 1e-5, "fp32_simt": 1e-5, "bf16": 1e-2, "fp8": 0.1}
+PRECS = ["fp32_simt", "fp32", "bf16", "fp8"]
 
 
 @pytest.fixture(scope="module")
@@ -87,7 +89,12 @@ def check(ref, got, prec, rows=None, orc=None):
     assert ok.any()
     ftol, ltol = FLUX_TOL[prec], LNL_TOL[prec]
     if got["phot"] is not None:
-        e = cases.rel_err(got["phot"][rows][ok], ref["phot"][ok], floor=1e-30)
+        # per-band relative error, floored at 1e-6 of the row's brightest band
+        # (bands 15 magnitudes fainter than the brightest carry no information
+        # at the workloads' S/N, and sit at or below FP32's normal range)
+        ph_ref = ref["phot"][ok]
+        floor = 1e-6 * np.abs(ph_ref).max(axis=1, keepdims=True)
+        e = np.abs(got["phot"][rows][ok] - ph_ref) / np.maximum(np.abs(ph_ref), floor)
         assert e.max() < ftol, f"photometry rel err {e.max():.3e}"
     if got["spec"] is not None:
         sp_ref = ref["spec"][ok]
