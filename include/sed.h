@@ -252,6 +252,67 @@ sed_status sed_loglike_noalloc(sed_ctx *ctx, sed_model_id model, const float *th
                                double *lnl_out, uint32_t *row_status, int precision, void *stream);
 
 /*
+ * Continuous-batching server of log-likelihood calls (the serving pattern of
+ * the library; the paper runs one fit per GPU).  Many fits -- each a model
+ * created with sed_create_model, i.e. its own filters, spectrum, data and SFH
+ * layout -- share one HBM-resident SSP grid.  A fit owns a device buffer of
+ * live points (max_rows x n_param FP32).  Clients submit calls (the first n
+ * rows of a fit) at any time; a scheduler thread packs the pending calls of
+ * all fits, first come first served, into launches of up to max_launch_rows
+ * rows, with up to n_slots launches in flight on their own streams, so calls
+ * that arrive while others run are taken into the next free slot and their
+ * work overlaps on the device.  Each row reads its own fit's model in the
+ * kernels, and no row's arithmetic depends on the other rows of a launch: a
+ * call's result equals sed_loglike on the same rows, alone or in any mix.
+ *  - sed_server_create: all fits must use the grid layout of `model_layout`
+ *    (same grid, birth-cloud edge and nebular setting).  Allocates the
+ *    launch buffers of every slot up front; SED_ENOMEM on failure.
+ *  - sed_server_open_fit: admission by device memory: reserves the fit's
+ *    live-point buffer against fit_budget_bytes (0 = no server limit; the
+ *    context budget still applies) and returns SED_EBUSY when it does not
+ *    fit now (retry after another fit closes).  max_rows <= max_launch_rows.
+ *  - sed_server_submit: copies n host rows (stride ld >= n_param) into the
+ *    fit's live points and queues the call; the caller may reuse its buffer
+ *    at once.  sed_server_submit_device queues a call on the live points
+ *    already in the fit's device buffer (sed_server_fit_theta; writes to it
+ *    must be complete, e.g. their stream synchronised, before the submit).
+ *    One call per fit at a time (SED_EBUSY otherwise).
+ *  - sed_server_wait: blocks until the call is done (timeout_ms < 0: no
+ *    limit; SED_ETIMEOUT otherwise) and copies lnL [n] / row status [n] to
+ *    host buffers (either may be NULL); latency_ms (may be NULL) receives the
+ *    time from submit to the results being on the host.  Each ticket is
+ *    waited for once.
+ *  - sed_server_close_fit waits for the fit's call in flight, then releases
+ *    its buffers; sed_server_destroy lets the launches in flight finish.
+ * Thread-safe: submit / wait / open / close may be called from many threads.
+ */
+typedef struct sed_server sed_server;
+typedef struct {
+  sed_grid_id grid;
+  sed_model_id model_layout;  /* a model whose grid layout every fit shares */
+  int precision;              /* SED_PREC_* of every launch */
+  int max_launch_rows;        /* rows packed into one launch */
+  int n_slots;                /* launches in flight at once, 1..8 */
+  size_t fit_budget_bytes;    /* device memory for the fits' live points (0 = no limit) */
+} sed_server_desc;
+typedef struct {
+  uint64_t calls, launches, rows;  /* completed calls, issued launches and their rows */
+  int fits_open;
+  size_t fit_bytes;                /* device bytes held by open fits */
+} sed_server_stats;
+sed_status sed_server_create(sed_ctx *ctx, const sed_server_desc *desc, sed_server **out);
+sed_status sed_server_destroy(sed_server *server);
+sed_status sed_server_open_fit(sed_server *server, sed_model_id model, int max_rows, int *fit);
+sed_status sed_server_close_fit(sed_server *server, int fit);
+float *sed_server_fit_theta(sed_server *server, int fit);
+sed_status sed_server_submit(sed_server *server, int fit, const float *theta_host, int n, int ld,
+                             uint64_t *ticket);
+sed_status sed_server_submit_device(sed_server *server, int fit, int n, uint64_t *ticket);
+sed_status sed_server_wait(sed_server *server, uint64_t ticket, double *lnl_host, uint32_t *status_host,
+                           int timeout_ms, double *latency_ms);
+sed_status sed_server_get_stats(sed_server *server, sed_server_stats *out);
+
+/*
  * Per-stage timing and work counters of the last hot-path call on a stream.
  * With profiling on, each hot-path call records CUDA events on its stream
  * before and after each of its kernels (preparation, contraction, epilogue);

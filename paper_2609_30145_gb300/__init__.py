@@ -3,4 +3,4 @@
 The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/sed.h``); ``api`` is a thin binding over it.
 """
-from .api import Context, Model, SedError, SedLogLike, PREC  # noqa: F401
+from .api import Context, Model, SedError, SedLogLike, Server, PREC  # noqa: F401

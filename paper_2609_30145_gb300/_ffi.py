@@ -50,6 +50,16 @@ class StageStats(C.Structure):
                 ("n_lam", C.c_int), ("ldn", C.c_int), ("precision", C.c_int)]
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("grid", C.c_int32), ("model_layout", C.c_int32), ("precision", C.c_int),
+                ("max_launch_rows", C.c_int), ("n_slots", C.c_int), ("fit_budget_bytes", C.c_size_t)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("calls", C.c_uint64), ("launches", C.c_uint64), ("rows", C.c_uint64),
+                ("fits_open", C.c_int), ("fit_bytes", C.c_size_t)]
+
+
 # exported symbols and their signatures (name -> (restype, argtypes))
 SIGNATURES = {
     "sed_create": (C.c_int, [C.POINTER(P), C.c_int, C.c_size_t]),
@@ -68,6 +78,15 @@ SIGNATURES = {
     "sed_loglike_host": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
     "sed_loglike_noalloc": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
     "sed_set_profiling": (C.c_int, [P, C.c_int]),
+    "sed_server_create": (C.c_int, [P, C.POINTER(ServerDesc), C.POINTER(P)]),
+    "sed_server_destroy": (C.c_int, [P]),
+    "sed_server_open_fit": (C.c_int, [P, C.c_int32, C.c_int, C.POINTER(C.c_int)]),
+    "sed_server_close_fit": (C.c_int, [P, C.c_int]),
+    "sed_server_fit_theta": (P, [P, C.c_int]),
+    "sed_server_submit": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
+    "sed_server_submit_device": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_uint64)]),
+    "sed_server_wait": (C.c_int, [P, C.c_uint64, P, P, C.c_int, C.POINTER(C.c_double)]),
+    "sed_server_get_stats": (C.c_int, [P, C.POINTER(ServerStats)]),
     "sed_last_stats": (C.c_int, [P, P, C.POINTER(StageStats)]),
 }
 

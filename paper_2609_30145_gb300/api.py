@@ -224,6 +224,73 @@ class Model:
         return lnl, stt
 
 
+class Server:
+    """Continuous-batching server of log-likelihood calls over many fits that
+    share one grid (sed_server_* in include/sed.h)."""
+
+    def __init__(self, ctx: Context, grid_id: int, layout_model: "Model", precision="bf16",
+                 max_launch_rows=8192, n_slots=3, fit_budget_bytes=0):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        d = _ffi.ServerDesc(grid_id, layout_model.id, _prec(precision), int(max_launch_rows), int(n_slots),
+                            int(fit_budget_bytes))
+        h = C.c_void_p()
+        ctx._check(self._lib.sed_server_create(ctx._h, C.byref(d), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sed_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open_fit(self, model: "Model", max_rows: int):
+        """Fit id, or None when the fit budget is full (SED_EBUSY: retry later)."""
+        f = C.c_int()
+        st = self._lib.sed_server_open_fit(self._h, model.id, int(max_rows), C.byref(f))
+        if st == _ffi.SED_EBUSY:
+            return None
+        self.ctx._check(st)
+        return f.value
+
+    def close_fit(self, fit: int):
+        self.ctx._check(self._lib.sed_server_close_fit(self._h, int(fit)))
+
+    def fit_theta_ptr(self, fit: int) -> int:
+        return self._lib.sed_server_fit_theta(self._h, int(fit)) or 0
+
+    def submit(self, fit: int, theta: np.ndarray) -> int:
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        t = C.c_uint64()
+        self.ctx._check(self._lib.sed_server_submit(self._h, int(fit), C.c_void_p(th.ctypes.data), th.shape[0],
+                                                    th.shape[1], C.byref(t)))
+        return t.value
+
+    def submit_device(self, fit: int, n: int) -> int:
+        t = C.c_uint64()
+        self.ctx._check(self._lib.sed_server_submit_device(self._h, int(fit), int(n), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, n: int, timeout_ms: int = -1):
+        """(lnL [n] float64, row status [n] uint32, latency in ms)."""
+        lnl = np.empty(n, dtype=np.float64)
+        st = np.empty(n, dtype=np.uint32)
+        lat = C.c_double()
+        self.ctx._check(self._lib.sed_server_wait(self._h, C.c_uint64(ticket), C.c_void_p(lnl.ctypes.data),
+                                                  C.c_void_p(st.ctypes.data), int(timeout_ms), C.byref(lat)))
+        return lnl, st, lat.value
+
+    def stats(self):
+        s = _ffi.ServerStats()
+        self.ctx._check(self._lib.sed_server_get_stats(self._h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+
 class SedLogLike(torch.autograd.Function):
     """lnL(theta) with the library's hand-written adjoint as the backward."""
 

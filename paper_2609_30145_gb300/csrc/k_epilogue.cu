@@ -36,13 +36,14 @@ __device__ __forceinline__ int bracket_lin(const float* lam, int lo, int n, int 
 
 size_t epilogue_smem(const EpiArgs& a) {
   const size_t N = (size_t)a.g.n_lam;
-  return (N * (a.md.n_pix > 0 ? 3 : 2) + (size_t)a.md.n_samp) * sizeof(float);
+  const int ns = a.row_model ? a.smem_samp : a.md.n_samp, np = a.row_model ? a.smem_pix : a.md.n_pix;
+  return (N * (np > 0 ? 3 : 2) + (size_t)ns) * sizeof(float);
 }
 
 __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant__ EpiArgs a) {
-  const ModelDev& md = a.md;
-  const GridDev& g = a.g;
   const int r = blockIdx.x;
+  const ModelDev& md = a.row_model ? a.mtab[a.row_model[r]] : a.md;
+  const GridDev& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = g.n_lam;
   extern __shared__ float smem[];

@@ -114,10 +114,10 @@ constexpr int PREP_THREADS = 128;
 
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepKernelArgs ka) {
   const PrepArgs& a = ka.p;
-  const ModelDev& md = a.md;
+  const int r = blockIdx.x;
+  const ModelDev& md = a.row_model ? a.mtab[a.row_model[r]] : a.md;
   const GridDev& g = a.g;
   const LayoutDev& L = a.L;
-  const int r = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* th = a.theta + (size_t)r * a.ld;
   const int NT = md.n_sfh, NA = g.n_age, NZ = g.n_feh;

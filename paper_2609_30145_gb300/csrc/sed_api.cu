@@ -107,8 +107,13 @@ double calzetti_kprime(double lum) {  // Calzetti et al. 2000, R_V = 4.05, UV br
 }
 
 sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, bool grad, sed_status* st);
+sed_status ensure_f8_layout(sed_ctx* ctx, Grid* g, Layout* L);
 
 }  // namespace
+
+namespace sed {
+sed_status ensure_f8_layout_shared(sed_ctx* ctx, Grid* g, Layout* L) { return ensure_f8_layout(ctx, g, L); }
+}  // namespace sed
 
 // ===========================================================================
 extern "C" {

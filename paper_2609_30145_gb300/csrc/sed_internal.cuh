@@ -275,6 +275,8 @@ namespace sed {
 struct PrepArgs {
   const float* theta; int n, ld;
   ModelDev md; GridDev g; LayoutDev L;
+  const ModelDev* mtab;    // rows from several fits (serving): model of row r = mtab[row_model[r]];
+  const int* row_model;    // NULL: every row uses md
   float* W; float* W_hi; float* W_lo; __nv_bfloat16* W_bf16;
   uint8_t* W_f8;       // FP8 path: [n][Kpad8]
   RowScal* rs;
@@ -319,6 +321,9 @@ struct EpiArgs {
   const float* Y; const float* O;
   const RowScal* rs;
   ModelDev md; GridDev g;
+  const ModelDev* mtab;    // as in PrepArgs; with row_model set, smem_samp / smem_pix give the
+  const int* row_model;    // largest n_samp / n_pix of the launch's models
+  int smem_samp, smem_pix;
   float* phot_out; float* spec_out;
   double* lnl; uint32_t* status;
   const int* err;      // device error word of the contraction (row status SED_ROW_DEVICE_TIMEOUT)
@@ -356,5 +361,8 @@ struct PrepBwdArgs {
   float* grad;          // [n][ld]
 };
 cudaError_t launch_prep_bwd(const PrepBwdArgs& a, cudaStream_t s);
+
+// Build the FP8 copy of a layout (caller holds ctx->mu).
+sed_status ensure_f8_layout_shared(sed_ctx* ctx, Grid* g, Layout* L);
 
 }  // namespace sed
