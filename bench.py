@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-threads", type=int, default=48)
+    ap.add_argument("--serve-budget-mb", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     return ap.parse_args()
 
@@ -398,6 +401,8 @@ def run_ours(args):
            "gpu_launches": 3 * args.steps}
     if rank == 0 and world == 1 and not args.no_grad:
         out["gradient"] = bench_gradient(ctx, device, flush, args)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        out["serving"] = bench_serving(ctx, device, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy_vs_fp64_oracle"] = cpu_baseline(w, grid, filt, data, theta, gpu_res,
                                                                             args.cpu_seconds)
@@ -433,6 +438,145 @@ def bench_gradient(ctx, device, flush, args):
                   "loglike_evals_per_s": round(B * len(fms) / (sum(fms) * 1e-3), 1),
                   "loglike_ms_per_step": round(sum(fms) / len(fms), 4)}
     return res
+
+
+def make_serving_requests(n_req, seed=6, mean_calls=5.0):
+    """Seeded request mix shaped like the serving workload: photometry only
+    (8-30 filters) or spectrum + photometry (200-3000 pixels), z in [0, 12],
+    live-point batches log-uniform in 64..4096, 10-120 SFH bins, [a/Fe] on or
+    off, each a dependent chain of a geometric number of calls."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    reqs = []
+    for i in range(n_req):
+        spec = bool(rng.random() < 0.5)
+        reqs.append(dict(
+            n_filt=int(rng.integers(8, 31)), n_pix=int(rng.integers(200, 3001)) if spec else 0,
+            batch=int(np.exp(np.log(64) + rng.random() * (np.log(4096) - np.log(64)))),
+            n_sfh=int(rng.integers(10, 121)), zmode=int(rng.integers(0, 2)), use_afe=int(rng.random() < 0.5),
+            calls=int(min(4 * mean_calls, rng.geometric(1.0 / mean_calls))), seed=1000 + i))
+    return reqs
+
+
+def bench_serving(ctx, device, args):
+    """Serving mix on the shared 107 x 12 x 5 x 6000 [a/Fe] grid: a bounded
+    sample of seeded requests, first all arriving at once (saturated), then as
+    a Poisson stream at 70% of the saturated throughput; BF16 server with the
+    3xTF32 (FP32-grade) server timed beside it."""
+    import threading
+    import synth
+    from paper_2609_30145_gb300 import Server
+
+    base = synth.WORKLOADS[GRAD_WORKLOAD]
+    grid = synth.make_grid(**base.grid_kw, seed=1)
+    gid = ctx.load_grid(grid)
+    reqs = make_serving_requests(args.serve_requests)
+    models, thetas = [], []
+    t_setup = time.perf_counter()
+    for q in reqs:
+        rng = np.random.Generator(np.random.PCG64(q["seed"]))
+        nw = q["n_filt"] // 3
+        filt = synth.pack_filters(synth.make_filters_nircam_like(nw, q["n_filt"] - nw, seed=q["seed"]))
+        kw = dict(use_afe=q["use_afe"], dust_law=1, filters=filt, phot_d=np.ones(q["n_filt"]),
+                  phot_sigma=np.ones(q["n_filt"]))
+        if q["n_pix"]:
+            lam, r = synth.make_spectrum_pixels(q["n_pix"], 0.6, 5.3, 100.0, 1000.0)
+            kw.update(spec_lam=lam, spec_d=np.ones(q["n_pix"]), spec_sigma=np.ones(q["n_pix"]), lsf_mode=0,
+                      lsf_value=r, sigma_gal_kms=300.0, z_ref=6.0)
+        m = ctx.create_model(gid, q["n_sfh"], 30.0, q["zmode"], **kw)
+        ranges = dict(base.ranges, afe=(-0.2, 0.6) if q["use_afe"] else 0.0)
+        d_true = synth.make_theta(1, q["n_sfh"], q["zmode"], ranges, seed=q["seed"])
+        d_true["zred"][:] = float(rng.random() * 11.0 + 0.5)
+        ph, sp = m.forward(torch_from(m.pack(d_true), device), "fp32")
+        ph = ph.cpu().numpy()[0].astype(np.float64)
+        nz = synth.noise(q["n_filt"] + q["n_pix"], seed=q["seed"])
+        if q["n_pix"]:
+            s0 = sp.cpu().numpy()[0].astype(np.float64)
+            m.set_data(phot_d=ph * (1 + nz[:q["n_filt"]] / 20), phot_sigma=np.abs(ph) / 20 + 1e-40,
+                       spec_d=s0 * (1 + nz[q["n_filt"]:] / 20), spec_sigma=np.abs(s0) / 20 + 1e-60)
+        else:
+            m.set_data(phot_d=ph * (1 + nz / 20), phot_sigma=np.abs(ph) / 20 + 1e-40)
+        models.append(m)
+        thetas.append(m.pack(synth.make_theta(q["batch"], q["n_sfh"], q["zmode"], ranges, seed=q["seed"] + 1)))
+    t_setup = time.perf_counter() - t_setup
+    total_evals = sum(q["batch"] * q["calls"] for q in reqs)
+
+    def run(prec, rate):
+        srv = Server(ctx, gid, models[0], precision=prec, max_launch_rows=8192, n_slots=3,
+                     fit_budget_bytes=args.serve_budget_mb << 20)
+        call_lat, req_lat, admitted_wait = [], [], []
+        lock = threading.Lock()
+        rng = np.random.Generator(np.random.PCG64(7))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
+        t0 = time.perf_counter()
+        nxt = [0]
+
+        def worker():
+            while True:
+                with lock:
+                    i = nxt[0]
+                    nxt[0] += 1
+                if i >= len(reqs):
+                    return
+                q, m, th = reqs[i], models[i], thetas[i].copy()
+                delay = t0 + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                t_arr = time.perf_counter()
+                fit = srv.open_fit(m, q["batch"])
+                while fit is None:          # admission: wait for device memory
+                    time.sleep(0.0005)
+                    fit = srv.open_fit(m, q["batch"])
+                t_adm = time.perf_counter()
+                lat = []
+                jm = m.offsets["logmass"]
+                for c in range(q["calls"]):
+                    t = srv.submit(fit, th)
+                    lnl, st, ms = srv.wait(t, th.shape[0])
+                    lat.append(ms)
+                    # toy slice step: the next call's rows depend on this call's lnL
+                    good = np.isfinite(lnl)
+                    if good.any():
+                        med = np.median(lnl[good])
+                        th[good, jm] += np.where(lnl[good] > med, 0.02, -0.02).astype(np.float32)
+                srv.close_fit(fit)
+                with lock:
+                    call_lat.extend(lat)
+                    req_lat.append(1e3 * (time.perf_counter() - t_arr))
+                    admitted_wait.append(1e3 * (t_adm - t_arr))
+
+        threads = [threading.Thread(target=worker) for _ in range(args.serve_threads)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return {"evals_per_s": round(total_evals / wall, 1), "wall_s": round(wall, 3),
+                "call_latency_ms": {"p50": round(float(np.percentile(call_lat, 50)), 3),
+                                    "p99": round(float(np.percentile(call_lat, 99)), 3)},
+                "request_latency_ms": {"p50": round(float(np.percentile(req_lat, 50)), 3),
+                                       "p99": round(float(np.percentile(req_lat, 99)), 3)},
+                "admission_wait_ms_p99": round(float(np.percentile(admitted_wait, 99)), 3),
+                "launches": int(st["launches"]), "calls": int(st["calls"]),
+                "rows_per_launch": round(st["rows"] / max(st["launches"], 1), 1)}
+
+    out = {"requests": len(reqs), "calls": int(sum(q["calls"] for q in reqs)), "evals": int(total_evals),
+           "grid": "107 x 12 x 5 x 6000 (FP32 + BF16 copies resident)", "setup_s": round(t_setup, 1),
+           "clients": args.serve_threads, "fit_budget_mb": args.serve_budget_mb,
+           "what": "latency = submit -> lnL on the host per call; request = arrival -> last call's result; "
+                   "requests are dependent chains (each call's rows move with the previous call's lnL)"}
+    for prec in ("bf16", "fp32"):
+        sat = run(prec, 0.0)
+        rate = 0.7 * sat["evals_per_s"] / (total_evals / len(reqs))
+        out[prec] = {"saturated": sat, "poisson_0.7": run(prec, rate)}
+        out[prec]["poisson_0.7"]["arrival_rate_per_s"] = round(rate, 2)
+    return out
+
+
+def torch_from(a, device):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
 
 
 def read_traffic():

@@ -40,9 +40,12 @@ size_t epilogue_smem(const EpiArgs& a) {
   return (N * (np > 0 ? 3 : 2) + (size_t)ns) * sizeof(float);
 }
 
+// MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
+// otherwise every row reads the model in the kernel parameters.
+template <bool MULTI>
 __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant__ EpiArgs a) {
   const int r = blockIdx.x;
-  const ModelDev& md = a.row_model ? a.mtab[a.row_model[r]] : a.md;
+  const ModelDev& md = MULTI ? a.mtab[a.row_model[r]] : a.md;
   const GridDev& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = g.n_lam;
@@ -210,13 +213,16 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
   const size_t smem = epilogue_smem(a);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  static size_t set_for = 0;
-  if (smem > 48 * 1024 && smem > set_for) {
-    cudaError_t e = cudaFuncSetAttribute(k_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static size_t set_for[2] = {0, 0};
+  const int m = a.row_model ? 1 : 0;
+  if (smem > 48 * 1024 && smem > set_for[m]) {
+    cudaError_t e = m ? cudaFuncSetAttribute(k_epilogue<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                      : cudaFuncSetAttribute(k_epilogue<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    set_for = smem;
+    set_for[m] = smem;
   }
-  k_epilogue<<<a.n, EPI_THREADS, smem, s>>>(a);
+  if (m) k_epilogue<true><<<a.n, EPI_THREADS, smem, s>>>(a);
+  else k_epilogue<false><<<a.n, EPI_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -112,10 +112,12 @@ struct PrepKernelArgs {
 
 constexpr int PREP_THREADS = 128;
 
+// MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]].
+template <bool MULTI>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepKernelArgs ka) {
   const PrepArgs& a = ka.p;
   const int r = blockIdx.x;
-  const ModelDev& md = a.row_model ? a.mtab[a.row_model[r]] : a.md;
+  const ModelDev& md = MULTI ? a.mtab[a.row_model[r]] : a.md;
   const GridDev& g = a.g;
   const LayoutDev& L = a.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -507,10 +509,12 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   ka.p = p;
   const size_t smem = ((size_t)p.g.n_age * p.g.n_feh + (p.W_f8 ? (size_t)p.L.Kpad : 0)) * sizeof(float);
   if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = p.row_model ? cudaFuncSetAttribute(k_prep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                    : cudaFuncSetAttribute(k_prep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_prep<<<p.n, PREP_THREADS, smem, s>>>(ka);
+  if (p.row_model) k_prep<true><<<p.n, PREP_THREADS, smem, s>>>(ka);
+  else k_prep<false><<<p.n, PREP_THREADS, smem, s>>>(ka);
   return cudaGetLastError();
 }
 
