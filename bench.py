@@ -393,12 +393,12 @@ def run_ours(args):
                       "n_sfh": w.n_sfh, "n_filt": int(len(filt[0])), "nebular": bool(w.use_nebular),
                       "dust": "birth-cloud power law + Kriek & Conroy 2013 diffuse",
                       "precision": PREC_NOTE[prec],
-                      "step": "one sed_loglike call over the batch (3 kernels), replayed as a CUDA graph",
+                      "step": "one sed_loglike call over the batch (4 kernels: row order, prep, contraction, epilogue), replayed as a CUDA graph",
                       "l2": "flushed before every timed step (256 MiB memset, outside the timing)",
                       "parallelism": f"replicas x{world} (independent batches per GPU)"},
            "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "what": "device time of one batch step"},
            "variants": variants, "roofline": roof, "clocks": ck, "e2e": e2e,
-           "gpu_launches": 3 * args.steps}
+           "gpu_launches": 4 * args.steps}
     if rank == 0 and world == 1 and not args.no_grad:
         out["gradient"] = bench_gradient(ctx, device, flush, args)
     if rank == 0 and world == 1 and args.serve_requests > 0:

@@ -89,18 +89,19 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
     }
     if (tid < RGRAD) a.rgrad[(size_t)r * RGRAD + tid] = 0.0;
     if (tid == 0) {
-      if (a.lnl) a.lnl[r] = -INFINITY;
-      if (a.status) a.status[r] = rs.status;
+      if (a.lnl) a.lnl[rs.orig] = -INFINITY;
+      if (a.status) a.status[rs.orig] = rs.status;
     }
     return;
   }
+  const int k_lo = rs.k_lo, k_hi = rs.k_hi;   // the row's node window: dlnL/dF vanishes outside
   const float* Yr = a.Y + ro;
   const float* Or = a.O + ro;
   const float eb_kc = 0.85f - 1.9f * rs.delta;
 
-  // ---- forward: attenuated spectrum (the forward epilogue's arithmetic)
+  // ---- forward: attenuated spectrum in the window (the forward epilogue's arithmetic)
   for (int k = tid; k < N; k += EB_THREADS) {
-    Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], Or[k], g.neb_tab, k);
+    Fs[k] = (k >= k_lo && k <= k_hi) ? attenuated(md, rs, g.att4[k], eb_kc, Yr[k], Or[k], g.neb_tab, k) : 0.f;
     phi[k] = 0.f;
   }
   __syncthreads();
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
   // ---- dust and nebular: dlnL/dY, dlnL/dO and the parameter sums over lambda
   float g_tbc = 0.f, g_abc = 0.f, g_td = 0.f, g_dl = 0.f, g_qy = 0.f, g_lu = 0.f, g_lz = 0.f;
   for (int k = tid; k < a.ldn; k += EB_THREADS) {
-    if (k >= N) {
+    if (k < k_lo || k > k_hi) {
       put_g(a, a.gy_hi, a.gy_lo, ro + k, 0.f);
       put_g(a, a.go_hi, a.go_lo, ro + k, 0.f);
       continue;
@@ -375,8 +376,8 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
     rg[RG_Z] = um_phot * (double)rs.dlnp_dz + s[6] * (double)rs.dlns_dz + s[7];
     rg[RG_QY] = s[8];
     rg[RG_BAD] = stt ? 1.0 : 0.0;
-    if (a.lnl) a.lnl[r] = lnl;
-    if (a.status) a.status[r] = stt;
+    if (a.lnl) a.lnl[rs.orig] = lnl;
+    if (a.status) a.status[rs.orig] = stt;
   }
 }
 
@@ -407,13 +408,24 @@ __global__ void __launch_bounds__(256) k_dw_simt(const DwSimtArgs a) {
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * DS_M, n0 = blockIdx.x * DS_N;
   const float* G = n0 < a.Ky_pad ? a.gy : a.go;
+  // the reduction runs over the union of the tile's row windows (G vanishes outside)
+  __shared__ int s_klo, s_khi;
+  if (tid == 0) { s_klo = 0x7fffffff; s_khi = -1; }
+  __syncthreads();
+  if (tid < DS_M && m0 + tid < a.n) {
+    const RowScal& q = a.rs[m0 + tid];
+    if (q.status == 0) { atomicMin(&s_klo, q.k_lo); atomicMax(&s_khi, q.k_hi); }
+  }
+  __syncthreads();
+  if (s_khi < 0) return;
+  const int l_begin = s_klo / DS_K * DS_K, l_end = min(a.ldk, (s_khi / DS_K + 1) * DS_K);
   const int lrow = tid >> 1, lk = (tid & 1) * 4;
   float acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int l0 = 0; l0 < a.ldk; l0 += DS_K) {
+  for (int l0 = l_begin; l0 < l_end; l0 += DS_K) {
     float4 va = make_float4(0.f, 0.f, 0.f, 0.f);
     if (m0 + lrow < a.n) va = *reinterpret_cast<const float4*>(G + (size_t)(m0 + lrow) * a.ldg + l0 + lk);
     As[lk + 0][lrow] = va.x; As[lk + 1][lrow] = va.y; As[lk + 2][lrow] = va.z; As[lk + 3][lrow] = va.w;

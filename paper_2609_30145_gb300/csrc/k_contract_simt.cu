@@ -17,6 +17,18 @@ __global__ void __launch_bounds__(256) k_contract_simt(const ContractArgs a) {
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * SB_M, n0 = blockIdx.x * SB_N;
   const int lrow = tid >> 1, lk = (tid & 1) * 4;
+  // skip wavelength tiles outside the union of the tile's row windows
+  if (a.rs) {
+    __shared__ int s_klo, s_khi;
+    if (tid == 0) { s_klo = 0x7fffffff; s_khi = -1; }
+    __syncthreads();
+    if (tid < SB_M && m0 + tid < a.n) {
+      const RowScal& q = a.rs[m0 + tid];
+      if (q.status == 0) { atomicMin(&s_klo, q.k_lo); atomicMax(&s_khi, q.k_hi); }
+    }
+    __syncthreads();
+    if (s_khi < 0 || n0 > s_khi || n0 + SB_N - 1 < s_klo) return;
+  }
 
   for (int part = 0; part < 2; ++part) {
     const int kb = part ? a.Ky_pad : 0, ke = part ? a.Kpad : a.Ky_pad;

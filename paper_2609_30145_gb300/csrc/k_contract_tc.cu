@@ -130,6 +130,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 struct Params {
+  const RowScal* rs;         // per-row rest-frame node windows (NULL: no window)
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
   CUtensorMap a2_hi, a2_lo;  // adjoint: A operand of the old columns (dlnL/dO)
   int n, n_lam, ldn, ky_tiles, k_tiles;
@@ -176,6 +177,31 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+
+  // Union of the rest-frame node windows of the tile's rows (invalid rows have
+  // none).  Forward: a wavelength tile outside it is never read, so the CTA
+  // exits at once.  Adjoint: dlnL/dY and dlnL/dO vanish outside each row's
+  // window, so the reduction over wavelength runs over the union only.
+  __shared__ int s_klo, s_khi;
+  int K0 = 0, KY = p.ky_tiles, KT = p.k_tiles;
+  if (p.rs) {
+    if (threadIdx.x == 0) { s_klo = 0x7fffffff; s_khi = -1; }
+    __syncthreads();
+    if (threadIdx.x < BM && m0 + (int)threadIdx.x < p.n) {
+      const RowScal& q = p.rs[m0 + threadIdx.x];
+      if (q.status == 0) { atomicMin(&s_klo, q.k_lo); atomicMax(&s_khi, q.k_hi); }
+    }
+    __syncthreads();
+    const int klo = s_klo, khi = s_khi;
+    if (khi < 0) return;
+    if constexpr (!GRAD) {
+      if (n0 > khi || n0 + BN - 1 < klo) return;
+    } else {
+      K0 = klo / 32;
+      KT = min(p.k_tiles, khi / 32 + 1);
+      KY = KT;
+    }
+  }
   const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
   const uint32_t tfull0 = smem_u32(&bars[2 * STAGES]), tempty0 = smem_u32(&bars[2 * STAGES + 2]);
@@ -202,7 +228,6 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
-  const int KT = p.k_tiles, KY = GRAD ? p.k_tiles : p.ky_tiles;
   const CUtensorMap* amap_hi = &p.a_hi;
   const CUtensorMap* amap_lo = &p.a_lo;
   if (GRAD && n0 >= p.n_split) { amap_hi = &p.a2_hi; amap_lo = &p.a2_lo; }
@@ -210,9 +235,9 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      for (int kt = 0; kt < KT; ++kt) {
-        const int s = kt % STAGES;
-        const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      for (int kt = K0; kt < KT; ++kt) {
+        const int s = (kt - K0) % STAGES;
+        const uint32_t ph = (uint32_t)((kt - K0) / STAGES) & 1u;
         if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { atomicOr(p.err, 1); break; }
         const uint32_t fb = full0 + 8 * s;
         mbar_expect_tx(fb, C::STAGE_BYTES);
@@ -231,10 +256,10 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t ID = idesc(PREC == SED_PREC_FP32 ? 2u : (PREC == SED_PREC_FP8 ? 0u : 1u), BM, BN);
-      int g = 0, kt = 0;
+      int g = 0, kt = K0;
       bool ok = true;
       for (int part = 0; part < NPART && ok; ++part) {
-        const int kb = part ? KY : 0, ke = part ? KT : KY;
+        const int kb = part ? KY : K0, ke = part ? KT : KY;
         for (int gs = kb; gs < ke && ok; gs += G, ++g) {
           const int b = g & 1;
           if (!mbar_wait(tempty0 + 8 * b, (((uint32_t)g >> 1) & 1u) ^ 1u)) { atomicOr(p.err, 8); ok = false; break; }
@@ -242,8 +267,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
           const uint32_t d = tmem + (uint32_t)(b * BN);
           const int ge = gs + G < ke ? gs + G : ke;
           for (; kt < ge; ++kt) {
-            const int s = kt % STAGES;
-            const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+            const int s = (kt - K0) % STAGES;
+            const uint32_t ph = (uint32_t)((kt - K0) / STAGES) & 1u;
             if (!mbar_wait(full0 + 8 * s, ph)) { atomicOr(p.err, 2); ok = false; break; }
             tc_fence_after();
             const uint32_t st = sbase + s * C::STAGE_BYTES;
@@ -276,7 +301,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     int g = 0;
     bool ok = true;
     for (int part = 0; part < NPART; ++part) {
-      const int kb = part ? KY : 0, ke = part ? KT : KY;
+      const int kb = part ? KY : K0, ke = part ? KT : KY;
       float run[BN];
 #pragma unroll
       for (int j = 0; j < BN; ++j) run[j] = 0.f;
@@ -368,6 +393,7 @@ int tc_encode_maps(void* fn, TcMaps* out, int prec, const void* a_hi, const void
 cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   tc::Params p;
   memset(&p, 0, sizeof p);
+  p.rs = a.rs;
   p.a_hi = a.maps->a_hi; p.a_lo = a.maps->a_lo; p.b_hi = a.maps->b_hi; p.b_lo = a.maps->b_lo;
   p.n = a.n; p.n_lam = a.n_lam; p.ldn = a.ldn; p.ld_out = a.ldn;
   p.Y = a.Y; p.O = a.O; p.err = a.err;
@@ -403,6 +429,7 @@ int tc_encode_dw_maps(void* fn, DwMaps* out, const float* gy_hi, const float* gy
 cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s) {
   tc::Params p;
   memset(&p, 0, sizeof p);
+  p.rs = a.rs;
   p.a_hi = a.maps->gy_hi; p.a_lo = a.maps->gy_lo;
   p.a2_hi = a.maps->go_hi; p.a2_lo = a.maps->go_lo;
   p.b_hi = a.maps->s_hi; p.b_lo = a.maps->s_lo;

@@ -45,7 +45,7 @@ size_t epilogue_smem(const EpiArgs& a) {
 template <bool MULTI>
 __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant__ EpiArgs a) {
   const int r = blockIdx.x;
-  const ModelDev& md = MULTI ? a.mtab[a.row_model[r]] : a.md;
+  const ModelDev& md = MULTI ? a.mtab[a.row_model[a.rs[r].orig]] : a.md;
   const GridDev& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = g.n_lam;
@@ -60,14 +60,15 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
 
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
+  const int ro = rs.orig;   // the caller's row index
   if (rs.status) {
     for (int b = tid; b < md.n_filt; b += blockDim.x)
-      if (a.phot_out) a.phot_out[(size_t)r * md.n_filt + b] = 0.f;
+      if (a.phot_out) a.phot_out[(size_t)ro * md.n_filt + b] = 0.f;
     for (int i = tid; i < md.n_pix; i += blockDim.x)
-      if (a.spec_out) a.spec_out[(size_t)r * md.n_pix + i] = 0.f;
+      if (a.spec_out) a.spec_out[(size_t)ro * md.n_pix + i] = 0.f;
     if (tid == 0) {
-      if (a.lnl) a.lnl[r] = -INFINITY;
-      if (a.status) a.status[r] = rs.status;
+      if (a.lnl) a.lnl[ro] = -INFINITY;
+      if (a.status) a.status[ro] = rs.status;
     }
     return;
   }
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
       const float mb = rs.p_phot * acc;
-      if (a.phot_out) a.phot_out[(size_t)r * md.n_filt + b] = mb;
+      if (a.phot_out) a.phot_out[(size_t)ro * md.n_filt + b] = mb;
       mb_s[b] = mb;
     }
   }
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
       }
     }
     const float mi = rs.s_spec * v;
-    if (a.spec_out) a.spec_out[(size_t)r * md.n_pix + i] = mi;
+    if (a.spec_out) a.spec_out[(size_t)ro * md.n_pix + i] = mi;
     if (valid && md.spec_isig[i] != 0.0) {
       const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
       part += -0.5 * rr * rr + md.spec_nlog[i];
@@ -204,8 +205,8 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
       for (int w = 0; w < EPI_THREADS / 32; ++w) tot += red[w];
       uint32_t st = 0;
       if (!isfinite(tot)) { st = SED_ROW_NONFINITE; tot = -INFINITY; }
-      if (a.lnl) a.lnl[r] = tot;
-      if (a.status) a.status[r] = st;
+      if (a.lnl) a.lnl[ro] = tot;
+      if (a.status) a.status[ro] = st;
     }
   }
 }

@@ -110,20 +110,90 @@ struct PrepKernelArgs {
   PrepArgs p;
 };
 
+// Processing order: rows grouped by redshift within chunks of ORDER_CHUNK rows
+// (one CTA per chunk, counting sort into ORDER_BINS redshift bins; rows with
+// an invalid redshift go last).  Rows that are close in redshift need the same
+// rest-frame wavelengths, so a 128-row tile of grouped rows spans a narrow node
+// window and the contraction skips the wavelength tiles no row of the tile
+// reads.  The order within a bin follows shared-memory atomics and may change
+// from call to call; no row's result depends on the order or on which rows
+// share its tile.
+constexpr int ORDER_CHUNK = 4096;
+constexpr int ORDER_THREADS = 1024;
+constexpr int ORDER_BINS = 1024;
+
+__global__ void __launch_bounds__(ORDER_THREADS) k_order(const float* theta, int n, int ld, int zoff, double zf,
+                                                         int* perm) {
+  __shared__ int cnt[ORDER_BINS + 1];
+  __shared__ int wsum[ORDER_THREADS / 32];
+  const int base = blockIdx.x * ORDER_CHUNK;
+  const int m = min(ORDER_CHUNK, n - base);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int b = tid; b <= ORDER_BINS; b += ORDER_THREADS) cnt[b] = 0;
+  __syncthreads();
+  constexpr int PER = ORDER_CHUNK / ORDER_THREADS;
+  int bin[PER];
+  const float scale = (float)(ORDER_BINS / zf);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int i = tid + u * ORDER_THREADS;
+    bin[u] = -1;
+    if (i < m) {
+      const float z = theta[(size_t)(base + i) * ld + zoff];
+      bin[u] = (z >= 0.f && (double)z < zf) ? min(ORDER_BINS - 1, (int)(z * scale)) : ORDER_BINS;
+      atomicAdd(&cnt[bin[u]], 1);
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the bin counts (one bin per thread, plus the invalid bin)
+  int v = tid < ORDER_BINS ? cnt[tid] : 0;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  const int total_valid = wsum[ORDER_THREADS / 32 - 1];
+  const int excl = x - v + (warp ? wsum[warp - 1] : 0);
+  __syncthreads();
+  if (tid < ORDER_BINS) cnt[tid] = excl;
+  if (tid == 0) cnt[ORDER_BINS] = total_valid;
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int i = tid + u * ORDER_THREADS;
+    if (i < m) perm[base + atomicAdd(&cnt[bin[u]], 1)] = base + i;
+  }
+}
+
 constexpr int PREP_THREADS = 128;
 
-// MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]].
+// Row p of the launch processes the caller's row r = perm[p] and records r in
+// RowScal::orig; every later kernel indexes by p and writes results to r.
 template <bool MULTI>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepKernelArgs ka) {
   const PrepArgs& a = ka.p;
-  const int r = blockIdx.x;
+  const int p = blockIdx.x;
+  const int r = a.perm ? a.perm[p] : p;
   const ModelDev& md = MULTI ? a.mtab[a.row_model[r]] : a.md;
   const GridDev& g = a.g;
   const LayoutDev& L = a.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* th = a.theta + (size_t)r * a.ld;
   const int NT = md.n_sfh, NA = g.n_age, NZ = g.n_feh;
-  if (r == 0 && tid == 0 && a.err) *a.err = 0;
+  if (p == 0 && tid == 0 && a.err) *a.err = 0;
 
   extern __shared__ float smem[];
   float* Ws = smem;                     // [NA][NZ]
@@ -149,22 +219,23 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   if (!status) status = cr.status;
   const double tmax = status ? 0.0 : (double)cr.tmax_d;
 
-  RowScal* out = a.rs + r;
+  RowScal* out = a.rs + p;
   const int Kpad = L.Kpad;
   if (status) {
     for (int k = tid; k < Kpad; k += blockDim.x) {
-      size_t o = (size_t)r * Kpad + k;
+      size_t o = (size_t)p * Kpad + k;
       if (a.W) a.W[o] = 0.f;
       if (a.W_hi) { a.W_hi[o] = 0.f; a.W_lo[o] = 0.f; }
       if (a.W_bf16) a.W_bf16[o] = __float2bfloat16_rn(0.f);
     }
     if (a.W_f8)
-      for (int k = tid; k < L.Kpad8; k += blockDim.x) a.W_f8[(size_t)r * L.Kpad8 + k] = 0;
+      for (int k = tid; k < L.Kpad8; k += blockDim.x) a.W_f8[(size_t)p * L.Kpad8 + k] = 0;
     if (tid == 0) {
       RowScal rs{};
       rs.status = status;
       rs.k_lo = 0;
       rs.k_hi = 0;
+      rs.orig = r;
       *out = rs;
     }
     return;
@@ -229,7 +300,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     }
     if (k < L.Ky_pad) qpart += v * L.q_s[k];
     nnz += v != 0.f;
-    const size_t o = (size_t)r * Kpad + k;
+    const size_t o = (size_t)p * Kpad + k;
     if (a.W) a.W[o] = v;
     if (a.W_hi) {
       const float h = tf32_rna(v);
@@ -262,11 +333,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     y_scale = exp2f(e);
     const float inv = exp2f(-e);
     const int shift = L.Ky_pad8 - L.Ky_pad;
-    uint8_t* w8 = a.W_f8 + (size_t)r * L.Kpad8;
-    for (int p = tid; p < L.Kpad8; p += blockDim.x) {
-      int k = p < L.Ky_pad ? p : (p < L.Ky_pad8 ? -1 : p - shift);
+    uint8_t* w8 = a.W_f8 + (size_t)p * L.Kpad8;
+    for (int q = tid; q < L.Kpad8; q += blockDim.x) {
+      int k = q < L.Ky_pad ? q : (q < L.Ky_pad8 ? -1 : q - shift);
       const float v = (k >= 0 && k < Kpad) ? Vs[k] * inv : 0.f;
-      w8[p] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+      w8[q] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
     }
   }
 
@@ -306,6 +377,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.tmax = (float)tmax;
     rs.lrat = lrat;
     rs.status = 0;
+    rs.orig = r;
     rs.y_scale = y_scale;
     // rest-frame node window the epilogue reads: the redshifted filter samples
     // and the spectral pixels with 5 dispersions on either side, with margins
@@ -346,12 +418,12 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   const ModelDev& md = a.md;
   const GridDev& g = a.g;
   const LayoutDev& L = a.L;
-  const int r = blockIdx.x;
+  const int r = blockIdx.x;                 // processing order (dW, rgrad, RowScal)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const float* th = a.theta + (size_t)r * a.ld;
-  float* out = a.grad + (size_t)r * a.ld;
-  const int NT = md.n_sfh, NA = g.n_age, NZ = g.n_feh;
   const RowScal rs = a.rs[r];
+  const float* th = a.theta + (size_t)rs.orig * a.ld;
+  float* out = a.grad + (size_t)rs.orig * a.ld;
+  const int NT = md.n_sfh, NA = g.n_age, NZ = g.n_feh;
   if (rs.status || a.rgrad[(size_t)r * RGRAD + RG_BAD] != 0.0) {
     for (int j = tid; j < a.ld; j += blockDim.x) out[j] = 0.f;
     return;
@@ -505,6 +577,12 @@ cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
+  if (p.perm && !p.row_model) {
+    k_order<<<(p.n + ORDER_CHUNK - 1) / ORDER_CHUNK, ORDER_THREADS, 0, s>>>(p.theta, p.n, p.ld,
+                                                                          p.md.offs[SED_KEY_ZRED], p.md.zf, p.perm);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   PrepKernelArgs ka;
   ka.p = p;
   const size_t smem = ((size_t)p.g.n_age * p.g.n_feh + (p.W_f8 ? (size_t)p.L.Kpad : 0)) * sizeof(float);

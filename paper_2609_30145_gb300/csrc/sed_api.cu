@@ -181,7 +181,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
     }
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
-      std::vector<void*> v = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->rs, w->err,
+      std::vector<void*> v = {w->perm, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->rs, w->err,
                               w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                               w->dW, w->rgrad};
       for (void* p : v)
@@ -842,7 +842,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   if (!need) return w;
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
-  std::vector<void*> old = {w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->rs, w->err,
+  std::vector<void*> old = {w->perm, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->rs, w->err,
                             w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                             w->dW, w->rgrad};
   for (void* p : old)
@@ -859,7 +859,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   std::vector<void*>* no = nullptr;
   sed_status s = SED_OK;
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
-  AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
+  AL(perm, R * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
   AL(Y, R * N * 4); AL(O, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
   AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
   if (grad || had_grad) {
@@ -923,12 +923,13 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   }
   pa.rs = w->rs;
   pa.err = w->err;
+  pa.perm = w->perm;
   CK(launch_prep(pa, s));
   if (sed_status ps = prof_mark(ctx, w, 1, s)) return ps;
   if (precision == SED_PREC_FP32_SIMT) {
     ContractArgs ca{};
     ca.n = n; ca.n_lam = g->n_lam; ca.ldn = w->ldn; ca.Ky_pad = L->Ky_pad; ca.Kpad = L->Kpad;
-    ca.W = w->W; ca.sspT = L->sspT_f32; ca.Y = w->Y; ca.O = w->O;
+    ca.W = w->W; ca.sspT = L->sspT_f32; ca.Y = w->Y; ca.O = w->O; ca.rs = w->rs;
     CK(launch_contract_simt(ca, s));
     return prof_mark(ctx, w, 2, s);
   }
@@ -952,7 +953,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   ta.n = n; ta.n_lam = g->n_lam; ta.ldn = w->ldn; ta.prec = precision;
   ta.Ky_pad = f8 ? L->Ky_pad8 : L->Ky_pad;
   ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
-  ta.maps = maps; ta.Y = w->Y; ta.O = w->O; ta.err = w->err;
+  ta.maps = maps; ta.Y = w->Y; ta.O = w->O; ta.err = w->err; ta.rs = w->rs;
   CK(launch_contract_tc(ta, s));
   return prof_mark(ctx, w, 2, s);
 }
@@ -1079,12 +1080,12 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
     }
     DwArgs da{};
     da.n = n; da.ldk = L->ldn; da.Ky_pad = L->Ky_pad; da.Kpad = L->Kpad;
-    da.maps = &w->dw_maps; da.dW = w->dW; da.err = w->err;
+    da.maps = &w->dw_maps; da.dW = w->dW; da.err = w->err; da.rs = w->rs;
     CK(launch_dw_tc(da, s));
   } else {
     DwSimtArgs da{};
     da.n = n; da.ldg = w->ldn; da.ldk = L->ldn; da.Ky_pad = L->Ky_pad; da.Kpad = L->Kpad;
-    da.gy = w->G_hi; da.go = w->GO_hi; da.sspK = L->sspK_f32; da.dW = w->dW;
+    da.gy = w->G_hi; da.go = w->GO_hi; da.sspK = L->sspK_f32; da.dW = w->dW; da.rs = w->rs;
     CK(launch_dw_simt(da, s));
   }
   PrepBwdArgs pb{};

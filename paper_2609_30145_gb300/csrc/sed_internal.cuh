@@ -62,6 +62,7 @@ struct RowScal {
   uint32_t status;
   int k_lo, k_hi;   // rest-frame node window this row needs
   float y_scale;    // FP8 path: the row's power of two folded out of W (Y, O are multiplied by it); else 1
+  int orig;         // the caller's index of this row (rows are processed in redshift order)
   int nnz;          // non-zero weights of the row
 };
 
@@ -219,6 +220,7 @@ struct Workspace {
   float* W = nullptr;            // [rows][Kpad]  exact FP32 weights (also the TF32 hi part source)
   float* W_hi = nullptr;         // [rows][Kpad]
   float* W_lo = nullptr;
+  int* perm = nullptr;           // [rows] processing order
   __nv_bfloat16* W_bf16 = nullptr;
   uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
   float* Y = nullptr;            // [rows][ldn]
@@ -281,10 +283,12 @@ struct PrepArgs {
   uint8_t* W_f8;       // FP8 path: [n][Kpad8]
   RowScal* rs;
   int* err;            // device error word of the contraction, cleared by the prep kernel
+  int* perm;           // [n] scratch: processing order (rows sorted by redshift), or NULL = caller's order
 };
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 
 struct ContractArgs {
+  const RowScal* rs;   // per-row node windows: tiles outside every row's window are skipped
   int n;               // rows (theta)
   int n_lam, ldn;
   int Ky_pad, Kpad;
@@ -295,6 +299,7 @@ struct ContractArgs {
 cudaError_t launch_contract_simt(const ContractArgs& a, cudaStream_t s);
 
 struct TcArgs {
+  const RowScal* rs;   // per-row node windows: tiles outside every row's window are skipped
   int n, n_lam, ldn, Ky_pad, Kpad, prec;   // prec: SED_PREC_FP32, SED_PREC_BF16 or SED_PREC_FP8
                                           // (for FP8, Ky_pad/Kpad are the FP8 layout's Ky_pad8/Kpad8)
   const TcMaps* maps;
@@ -310,6 +315,7 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s);
 int tc_encode_dw_maps(void* encode_fn, DwMaps* out, const float* gy_hi, const float* gy_lo, const float* go_hi,
                       const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int ldg, int ldk, int kpad);
 struct DwArgs {
+  const RowScal* rs;   // per-row node windows bound the reduction over lambda
   int n, ldk, Ky_pad, Kpad;
   const DwMaps* maps;
   float* dW; int* err;
@@ -346,6 +352,7 @@ struct EpiBwdArgs {
 cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s);
 
 struct DwSimtArgs {
+  const RowScal* rs;
   int n, ldg, ldk, Ky_pad, Kpad;
   const float* gy; const float* go;   // [n][ldg]
   const float* sspK;                  // [Kpad][ldk], ldk <= ldg: the reduction length

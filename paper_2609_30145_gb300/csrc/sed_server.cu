@@ -183,7 +183,7 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
   if (sv->prec == SED_PREC_FP32_SIMT) {
     ContractArgs ca{};
     ca.n = n; ca.n_lam = g->n_lam; ca.ldn = sv->ldn; ca.Ky_pad = L->Ky_pad; ca.Kpad = L->Kpad;
-    ca.W = sl.W; ca.sspT = L->sspT_f32; ca.Y = sl.Y; ca.O = sl.O;
+    ca.W = sl.W; ca.sspT = L->sspT_f32; ca.Y = sl.Y; ca.O = sl.O; ca.rs = sl.rs;
     e = launch_contract_simt(ca, s);
   } else {
     if (sl.maps_n != n) {
@@ -198,7 +198,7 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
     ta.n = n; ta.n_lam = g->n_lam; ta.ldn = sv->ldn; ta.prec = sv->prec;
     ta.Ky_pad = f8 ? L->Ky_pad8 : L->Ky_pad;
     ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
-    ta.maps = &sl.maps; ta.Y = sl.Y; ta.O = sl.O; ta.err = sl.err;
+    ta.maps = &sl.maps; ta.Y = sl.Y; ta.O = sl.O; ta.err = sl.err; ta.rs = sl.rs;
     e = launch_contract_tc(ta, s);
   }
   if (e != cudaSuccess) return e;
