@@ -274,9 +274,8 @@ def run_ours(args):
     ck = clocks.stop()
     total_ms = sum(ms)
     if dist:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        from paper_2609_30145_gb300.shard import max_over_ranks
+        total_ms = max_over_ranks(total_ms, device=device)
     ms_step = total_ms / args.steps
     value = world * B * args.steps / (total_ms * 1e-3)
 
@@ -365,9 +364,8 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_t)
     if dist:
-        tt = torch.tensor([e2e_total], dtype=torch.float64, device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
+        from paper_2609_30145_gb300.shard import max_over_ranks
+        e2e_total = max_over_ranks(e2e_total, device=device)
     ld = theta.shape[1]
     e2e = {"value": round(world * B * args.steps / e2e_total, 1), "unit": "evals/s",
            "h2d_bytes_per_step": B * ld * 4, "d2h_bytes_per_step": B * 8 + B * 4,
