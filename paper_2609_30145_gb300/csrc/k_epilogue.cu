@@ -35,25 +35,27 @@ __device__ __forceinline__ int bracket_lin(const float* lam, int lo, int n, int 
 }
 
 size_t epilogue_smem(const EpiArgs& a) {
-  const size_t N = (size_t)a.g.n_lam;
   const int ns = a.row_model ? a.smem_samp : a.md.n_samp, np = a.row_model ? a.smem_pix : a.md.n_pix;
-  return (N * (np > 0 ? 3 : 2) + (size_t)ns) * sizeof(float);
+  const size_t W = (size_t)(a.row_model ? a.smem_win : a.md.win_max);
+  return (W * (np > 0 ? 3 : 2) + (size_t)ns) * sizeof(float);
 }
 
 // MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
 // otherwise every row reads the model in the kernel parameters.
 template <bool MULTI>
-__global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant__ EpiArgs a) {
+__global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_constant__ EpiArgs a) {
   const int r = blockIdx.x;
   const ModelDev& md = MULTI ? a.mtab[a.row_model[a.rs[r].orig]] : a.md;
   const GridDev& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = g.n_lam;
+  // shared memory holds the row's node window [k_lo, k_hi] only (at most
+  // md.win_max nodes); the pointers below are offset so that they are indexed
+  // by the global node k
   extern __shared__ float smem[];
-  float* Gs = smem;                   // F / lam^2
-  float* lam_s = smem + N;            // rest-frame wavelengths
-  float* contrib = smem + 2 * N;      // per filter sample: w_j * lerp(G)(x_j)
-  float* Fs = contrib + md.n_samp;    // F (spectral arm only)
+  const int WIN = MULTI ? a.smem_win : md.win_max;
+  const int NS = MULTI ? a.smem_samp : md.n_samp;
+  float* contrib = smem;              // per filter sample: w_j * lerp(G)(x_j)
   __shared__ float mb_s[MAX_BANDS];
   __shared__ double red[EPI_THREADS / 32];
   __shared__ int bk_lo[MAX_BANDS], bk_n[MAX_BANDS];
@@ -78,7 +80,10 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
   const float* Or = a.O + (size_t)r * a.ldn;
   const float eb = 0.85f - 1.9f * rs.delta;
   const bool spec = md.n_pix > 0;
-  const int k_lo = rs.k_lo, k_hi = rs.k_hi;   // nodes [k_lo, k_hi] are the only ones read below
+  const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);   // nodes [k_lo, k_hi] are the only ones read below
+  float* Gs = smem + NS - k_lo;                  // F / lam^2
+  float* lam_s = smem + NS + WIN - k_lo;         // rest-frame wavelengths
+  float* Fs = smem + NS + 2 * WIN - k_lo;        // F (spectral arm only)
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
     const float4 c = g.att4[k];
@@ -95,6 +100,7 @@ __global__ void __launch_bounds__(EPI_THREADS) k_epilogue(const __grid_constant_
   //      halving and walks forward for the rest; the per-sample terms are then
   //      summed per band in a fixed order.
   const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
+  (void)N;
   if (tid < md.n_filt) {
     const int b = tid;
     const float xa = md.samp_lam[md.band_start[b]] * rs.inv1pz;

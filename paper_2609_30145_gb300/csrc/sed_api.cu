@@ -779,6 +779,26 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_nlog = pd; }
     if (d->spec_mask) M->spec_mask_h.assign(d->spec_mask, d->spec_mask + np);
   }
+  // widest rest-frame window a row can need: the observed span of the filter
+  // samples and spectral pixels (5 dispersions out) is a fixed wavelength ratio
+  // at every redshift; count the most nodes that ratio covers from any node,
+  // plus the kernels' margins
+  if (!st) {
+    double lo = 1e300, hi = 0.0;
+    if (dv.n_filt) { lo = std::min(lo, (double)dv.samp_lam_min); hi = std::max(hi, (double)dv.samp_lam_max); }
+    if (dv.n_pix) {
+      lo = std::min(lo, std::exp(dv.pix_ln_min - 5.0 * dv.pix_s_max));
+      hi = std::max(hi, std::exp(dv.pix_ln_max + 5.0 * dv.pix_s_max));
+    }
+    const double ratio = hi / lo * (1.0 + 1e-6);
+    const auto& Lg = g->lam;
+    int wmax = 1;
+    for (size_t k0 = 0; k0 < Lg.size(); k0++) {
+      const size_t k1 = std::upper_bound(Lg.begin(), Lg.end(), Lg[k0] * ratio) - Lg.begin();
+      wmax = std::max(wmax, (int)(k1 - k0));
+    }
+    dv.win_max = std::min(g->n_lam, wmax + 16);
+  }
   if (!st && (d->phot_d || d->phot_sigma || d->spec_d || d->spec_sigma))
     st = set_data_dev(ctx, M, d->phot_d, d->phot_sigma, d->spec_d, d->spec_sigma);
   if (st) {

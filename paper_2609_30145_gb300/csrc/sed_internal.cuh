@@ -136,6 +136,7 @@ struct ModelDev {
   const double* spec_nlog;
   double pix_ln_min, pix_ln_max;
   float pix_s_max;
+  int win_max;             // most rest-frame nodes one row's window can span (any redshift)
 };
 
 // ---------------------------------------------------------------------------
@@ -329,7 +330,7 @@ struct EpiArgs {
   ModelDev md; GridDev g;
   const ModelDev* mtab;    // as in PrepArgs; with row_model set, smem_samp / smem_pix give the
   const int* row_model;    // largest n_samp / n_pix of the launch's models
-  int smem_samp, smem_pix;
+  int smem_samp, smem_pix, smem_win;
   float* phot_out; float* spec_out;
   double* lnl; uint32_t* status;
   const int* err;      // device error word of the contraction (row status SED_ROW_DEVICE_TIMEOUT)

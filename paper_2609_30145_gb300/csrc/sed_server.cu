@@ -93,7 +93,7 @@ struct sed_server {
   size_t budget = 0, used = 0;
   ModelDev* mtab = nullptr;
   std::vector<char> mtab_loaded;
-  int max_samp = 0, max_pix = 0;
+  int max_samp = 0, max_pix = 0, max_win = 1;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<SrvCall*> pending;
@@ -206,7 +206,7 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
   ea.n = n; ea.ldn = sv->ldn; ea.Y = sl.Y; ea.O = sl.O; ea.rs = sl.rs;
   ea.g = g->dv;
   ea.mtab = sv->mtab; ea.row_model = sl.rowm;
-  ea.smem_samp = sv->max_samp; ea.smem_pix = sv->max_pix;
+  ea.smem_samp = sv->max_samp; ea.smem_pix = sv->max_pix; ea.smem_win = sv->max_win;
   ea.lnl = sl.lnl; ea.status = sl.st; ea.err = sl.err;
   ea.lam8 = f8 ? L->lam8 : nullptr;
   e = launch_epilogue(ea, s);
@@ -443,6 +443,7 @@ sed_status sed_server_open_fit(sed_server* sv, sed_model_id model, int max_rows,
   sv->used += need;
   sv->max_samp = std::max(sv->max_samp, M->dv.n_samp);
   sv->max_pix = std::max(sv->max_pix, M->dv.n_pix);
+  sv->max_win = std::max(sv->max_win, M->dv.win_max);
   int id = -1;
   for (size_t i = 0; i < sv->fits.size(); ++i)
     if (!sv->fits[i].open && !sv->fits[i].theta_d) { id = (int)i; break; }
