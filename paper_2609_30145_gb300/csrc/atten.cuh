@@ -11,6 +11,13 @@
 
 namespace sed {
 
+// 2^x by the hardware's approximate base-2 exponential (relative error below 2^-22)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float dust_shape(const ModelDev& md, const float4& c, float eb, float pw) {
   return md.dust_law == SED_DUST_POWER_LAW ? pw : (c.y + eb * c.z) * pw;
 }
@@ -26,7 +33,7 @@ __device__ __forceinline__ float attenuated(const ModelDev& md, const RowScal& r
   const float tbc = rs.tau_bc * __expf(rs.alpha_bc * c.x);
   const float pw = __expf(rs.delta * c.x);
   const float td = rs.tau_d * dust_shape(md, c, eb, pw);
-  if (md.use_neb) y += exp2f(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, neb_tab, k));
+  if (md.use_neb) y += ex2_approx(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, neb_tab, k));
   return __expf(-td) * (__expf(-tbc) * y + o);
 }
 

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
     float lg = 0.f, nb = 0.f;
     if (md.use_neb) {
       lg = neb_log10(rs, g.neb_tab, k);
-      nb = exp2f(rs.log2_qy + 3.3219280948873623f * lg);
+      nb = ex2_approx(rs.log2_qy + 3.3219280948873623f * lg);
       y += nb;
     }
     const float gF = phi[k];
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
     g_td += gtd * shape;
     g_dl += gtd * rs.tau_d * dshape;
     if (md.use_neb) {
-      g_qy += gy * exp2f(3.3219280948873623f * lg);
+      g_qy += gy * ex2_approx(3.3219280948873623f * lg);
       const float glg = gy * nb * 2.302585092994046f;
       float su = 0.f, sz = 0.f;
 #pragma unroll

@@ -23,21 +23,10 @@ namespace sed {
 constexpr int EPI_THREADS = 256;
 constexpr int MAX_BANDS = 128;
 
-// Photometric brackets: the last node k in [lo, lo + n - 1] with lam[k] <= x, by a
-// fixed number of halving steps over the shared-memory copy of the wavelengths
-// (requires lam[lo] <= x; extra steps leave the result unchanged).
-__device__ __forceinline__ int bracket_lin(const float* lam, int lo, int n, int steps, float x) {
-  for (int it = 0; it < steps; ++it) {
-    const int half = n >> 1;
-    if (lam[lo + half] <= x) { lo += half; n -= half; } else { n = half; }
-  }
-  return lo;
-}
-
 size_t epilogue_smem(const EpiArgs& a) {
   const int ns = a.row_model ? a.smem_samp : a.md.n_samp, np = a.row_model ? a.smem_pix : a.md.n_pix;
   const size_t W = (size_t)(a.row_model ? a.smem_win : a.md.win_max);
-  return (W * (np > 0 ? 3 : 2) + (size_t)ns) * sizeof(float);
+  return (W * (np > 0 ? 4 : 3) + (size_t)ns) * sizeof(float);
 }
 
 // MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
@@ -58,7 +47,6 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
   float* contrib = smem;              // per filter sample: w_j * lerp(G)(x_j)
   __shared__ float mb_s[MAX_BANDS];
   __shared__ double red[EPI_THREADS / 32];
-  __shared__ int bk_lo[MAX_BANDS], bk_n[MAX_BANDS];
 
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
@@ -83,7 +71,8 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
   const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);   // nodes [k_lo, k_hi] are the only ones read below
   float* Gs = smem + NS - k_lo;                  // F / lam^2
   float* lam_s = smem + NS + WIN - k_lo;         // rest-frame wavelengths
-  float* Fs = smem + NS + 2 * WIN - k_lo;        // F (spectral arm only)
+  float* idl_s = smem + NS + 2 * WIN - k_lo;     // 1 / (lam[k+1] - lam[k])
+  float* Fs = smem + NS + 3 * WIN - k_lo;        // F (spectral arm only)
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
     const float4 c = g.att4[k];
@@ -92,45 +81,33 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
     if (spec) Fs[k] = F;
     Gs[k] = F * c.w;
     lam_s[k] = g.lam_f[k];
+    idl_s[k] = g.inv_dlam[k];
   }
   __syncthreads();
 
-  // ---- photometry.  Node window of each band (its samples are sorted); each
-  //      thread takes a contiguous run of samples, brackets the first one by
-  //      halving and walks forward for the rest; the per-sample terms are then
-  //      summed per band in a fixed order.
+  // ---- photometry.  Consecutive threads take consecutive filter samples
+  //      (coalesced loads); each sample's bracket starts from the index table
+  //      over ln(lambda) (the sample's table coordinate is precomputed, the
+  //      row's ln(1+z) shifts it) and is corrected within the row's window in
+  //      shared memory.  The per-sample terms are summed per band in a fixed order.
   const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
-  (void)N;
-  if (tid < md.n_filt) {
-    const int b = tid;
-    const float xa = md.samp_lam[md.band_start[b]] * rs.inv1pz;
-    const float xb = md.samp_lam[md.band_start[b + 1] - 1] * rs.inv1pz;
-    const int n0 = max(k_hi - k_lo, 1), st0 = 32 - __clz(n0);
-    const int lo = xa <= lam_s[k_lo] ? k_lo : bracket_lin(lam_s, k_lo, n0, st0, fminf(xa, lamN));
-    const int hi = xb >= lam_s[k_hi] ? k_hi - 1 : bracket_lin(lam_s, k_lo, n0, st0, fmaxf(xb, lam0));
-    bk_lo[b] = lo;
-    bk_n[b] = max(hi - lo + 1, 1);
-  }
-  __syncthreads();
   {
-    const int run = (md.n_samp + EPI_THREADS - 1) / EPI_THREADS;
-    const int j0 = tid * run, j1 = min(md.n_samp, j0 + run);
-    int kc = -1, bc = -1, kend = 0;
-    for (int j = j0; j < j1; ++j) {
-      const float4 sp = md.samp4[j];
-      const int b = (int)sp.z;
+    const float qz = rs.ln1pz_hi * g.lut_inv_h;
+    const int kmin = k_lo, kmax = k_hi - 1;
+#pragma unroll 4
+    for (int j = tid; j < md.n_samp; j += EPI_THREADS) {
+      const float4 sp = md.samp4[j];     // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
       const float x = sp.x * rs.inv1pz;
       float v = 0.f;
       if (x >= lam0 && x <= lamN) {
-        if (b != bc) {
-          kc = bracket_lin(lam_s, bk_lo[b], bk_n[b], 32 - __clz(bk_n[b]), x);
-          kend = bk_lo[b] + bk_n[b] - 1;
-          bc = b;
-        } else {
-          while (kc < kend && lam_s[kc + 1] <= x) ++kc;
-        }
-        const float la = lam_s[kc], lb = lam_s[kc + 1];
-        const float t = (x - la) / (lb - la);
+        int q = (int)(sp.z - qz);
+        q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
+        int kc = min(max(g.lut[q], kmin), kmax);
+#pragma unroll 1
+        while (kc < kmax && lam_s[kc + 1] <= x) ++kc;
+#pragma unroll 1
+        while (kc > kmin && lam_s[kc] > x) --kc;
+        const float t = (x - lam_s[kc]) * idl_s[kc];
         v = Gs[kc] + t * (Gs[kc + 1] - Gs[kc]);
       }
       contrib[j] = sp.y * v;

@@ -266,13 +266,14 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
   g->q_log2 = qmax > 0 ? std::ceil(std::log2(qmax)) : 0.0;
 
   // per-node constants
-  std::vector<float> lam_f(nl), inv_lam2(nl), lnp(nl), kp(nl), dr(nl), lh(nl), lo(nl);
+  std::vector<float> lam_f(nl), inv_lam2(nl), lnp(nl), kp(nl), dr(nl), lh(nl), lo(nl), idl(nl, 0.f);
   g->siglib_kms.resize(nl);
   double hmin = 1e300;
   for (size_t k = 0; k < nl; k++) {
     const double L = g->lam[k];
     lam_f[k] = (float)L;
     inv_lam2[k] = (float)(1.0 / (L * L));
+    if (k + 1 < nl) idl[k] = (float)(1.0 / (g->lam[k + 1] - L));
     lnp[k] = (float)std::log(L / 5500.0);
     kp[k] = (float)calzetti_kprime(L * 1e-4);
     const double x = L * 350.0, dd = L * L - 2175.0 * 2175.0;
@@ -319,7 +320,7 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
   int* pi;
 #define UPF(field, vec)                                                   \
   if (!st) { st = upload(ctx, &p, vec.data(), vec.size(), &g->allocs, &g->bytes); dv.field = p; }
-  UPF(lam_f, lam_f) UPF(inv_lam2, inv_lam2) UPF(lnp, lnp) UPF(kprime, kp) UPF(drude, dr)
+  UPF(lam_f, lam_f) UPF(inv_lam2, inv_lam2) UPF(inv_dlam, idl) UPF(lnp, lnp) UPF(kprime, kp) UPF(drude, dr)
   UPF(lnl_hi, lh) UPF(lnl_lo, lo) UPF(cell_lo, clo) UPF(cell_hi, chi)
 #undef UPF
   if (!st) { st = upload(ctx, &pi, lut.data(), lut.size(), &g->allocs, &g->bytes); dv.lut = pi; }
@@ -728,7 +729,9 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     uint8_t* pb;
     if (!st) { st = upload(ctx, &pb, sb.data(), sb.size(), &M->allocs, &M->bytes); dv.samp_band = pb; }
     std::vector<float4> s4(S);
-    for (int j = 0; j < S; j++) s4[j] = make_float4(sl[j], sw[j], (float)sb[j], 0.f);
+    for (int j = 0; j < S; j++)   // {lambda, weight, coordinate of ln(lambda) in the grid's index table, band}
+      s4[j] = make_float4(sl[j], sw[j], (float)((std::log((double)sl[j]) - (double)g->dv.lut_x0) * g->dv.lut_inv_h),
+                          (float)sb[j]);
     float4* p4;
     if (!st) { st = upload(ctx, &p4, s4.data(), s4.size(), &M->allocs, &M->bytes); dv.samp4 = p4; }
     std::vector<double> zeros(d->n_filt, 0.0);

@@ -80,6 +80,7 @@ struct GridDev {
   const float* lam_f;      // lambda (A)
   const float4* att4;      // per node: ln(lambda/5500), k'/4.05, Drude/4.05, 1/lambda^2
   const float* inv_lam2;   // 1/lambda^2
+  const float* inv_dlam;   // 1/(lambda[k+1] - lambda[k]) (0 at the last node)
   const float* lnp;        // ln(lambda/5500)
   const float* kprime;     // Calzetti k'(lambda), R_V = 4.05, clamped >= 0
   const float* drude;      // Drude profile with E_b = 1
@@ -122,7 +123,7 @@ struct ModelDev {
   const float* samp_lam;   // [n_samp] observed-frame A
   const float* samp_w;     // [n_samp] R lam dlam / Z_b
   const uint8_t* samp_band; // [n_samp] band of each sample
-  const float4* samp4;     // [n_samp] {observed lambda, weight, band, 0}
+  const float4* samp4;     // [n_samp] {observed lambda, weight, (ln lambda - lut_x0) lut_inv_h, band}
   const double* phot_d;    // [n_filt]
   const double* phot_isig; // [n_filt] 1/sigma (0 when masked out)
   const double* phot_nlog; // [n_filt] -1/2 ln(2 pi sigma^2) (0 when masked out)
