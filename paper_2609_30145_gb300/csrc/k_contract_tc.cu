@@ -370,7 +370,15 @@ static CUresult encode_kmajor(void* fn, CUtensorMap* m, void* base, CUtensorMapD
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-constexpr int TC_BN = 128;
+// Wavelength tile of the forward contraction.  With rows grouped by redshift
+// only ~40% of the wavelength tiles are computed; for short K (Kpad <= 2048,
+// e.g. 107 ages x 12 [Fe/H]) a 1024-row batch then has ~150 128-wide tiles for
+// 152 SMs, where one SM with two tiles doubles the kernel's time, so the tile
+// is 64 wide (half the unit of work, tighter windows, W re-read once more per
+// tile).  For long K (the 5-node [a/Fe] grid) the tiles are 128 wide: there
+// the re-reads of W and the shared-memory operand traffic per FLOP dominate.
+constexpr int TC_BN_SHORT_K = 64, TC_BN_LONG_K = 128, TC_LONG_K = 2048;
+int tc_bn_for(int kpad) { return kpad <= TC_LONG_K ? TC_BN_SHORT_K : TC_BN_LONG_K; }
 
 int tc_encode_maps(void* fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo, const void* b_hi,
                    const void* b_lo, int n, int n_lam, int kpad) {
@@ -379,10 +387,11 @@ int tc_encode_maps(void* fn, TcMaps* out, int prec, const void* a_hi, const void
                                      : (f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   const int es = f32 ? 4 : (f8 ? 1 : 2);
   if (encode_kmajor(fn, &out->a_hi, const_cast<void*>(a_hi), dt, es, kpad, n, tc::BM) != CUDA_SUCCESS) return 1;
-  if (encode_kmajor(fn, &out->b_hi, const_cast<void*>(b_hi), dt, es, kpad, n_lam, TC_BN) != CUDA_SUCCESS) return 2;
+  const int bn = tc_bn_for(kpad);
+  if (encode_kmajor(fn, &out->b_hi, const_cast<void*>(b_hi), dt, es, kpad, n_lam, bn) != CUDA_SUCCESS) return 2;
   if (f32) {
     if (encode_kmajor(fn, &out->a_lo, const_cast<void*>(a_lo), dt, es, kpad, n, tc::BM) != CUDA_SUCCESS) return 3;
-    if (encode_kmajor(fn, &out->b_lo, const_cast<void*>(b_lo), dt, es, kpad, n_lam, TC_BN) != CUDA_SUCCESS) return 4;
+    if (encode_kmajor(fn, &out->b_lo, const_cast<void*>(b_lo), dt, es, kpad, n_lam, bn) != CUDA_SUCCESS) return 4;
   } else {
     out->a_lo = out->a_hi;
     out->b_lo = out->b_hi;
@@ -397,19 +406,23 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   p.a_hi = a.maps->a_hi; p.a_lo = a.maps->a_lo; p.b_hi = a.maps->b_hi; p.b_lo = a.maps->b_lo;
   p.n = a.n; p.n_lam = a.n_lam; p.ldn = a.ldn; p.ld_out = a.ldn;
   p.Y = a.Y; p.O = a.O; p.err = a.err;
+  const bool wide = tc_bn_for(a.Kpad) == TC_BN_LONG_K;   // same choice as the box of the B map
   if (a.prec == SED_PREC_FP32) {
     p.ky_tiles = a.Ky_pad / 32;
     p.k_tiles = a.Kpad / 32;
-    return tc::launch_cfg<SED_PREC_FP32, TC_BN, 3, 2, false>(p, a.ldn, s);
+    return wide ? tc::launch_cfg<SED_PREC_FP32, 128, 3, 2, false>(p, a.ldn, s)
+                : tc::launch_cfg<SED_PREC_FP32, 64, 4, 2, false>(p, a.ldn, s);
   }
   if (a.prec == SED_PREC_FP8) {
     p.ky_tiles = a.Ky_pad / 128;
     p.k_tiles = a.Kpad / 128;
-    return tc::launch_cfg<SED_PREC_FP8, TC_BN, 6, 4, false>(p, a.ldn, s);
+    return wide ? tc::launch_cfg<SED_PREC_FP8, 128, 6, 4, false>(p, a.ldn, s)
+                : tc::launch_cfg<SED_PREC_FP8, 64, 8, 4, false>(p, a.ldn, s);
   }
   p.ky_tiles = a.Ky_pad / 64;
   p.k_tiles = a.Kpad / 64;
-  return tc::launch_cfg<SED_PREC_BF16, TC_BN, 6, 4, false>(p, a.ldn, s);
+  return wide ? tc::launch_cfg<SED_PREC_BF16, 128, 6, 4, false>(p, a.ldn, s)
+              : tc::launch_cfg<SED_PREC_BF16, 64, 8, 4, false>(p, a.ldn, s);
 }
 
 constexpr int DW_BN = 64;

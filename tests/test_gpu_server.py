@@ -89,7 +89,21 @@ def test_results_alone_equal_results_in_the_mix(setup, prec):
             assert np.array_equal(lnl, alone[i][0]), (i, np.max(np.abs(lnl - alone[i][0])))
             assert lat > 0
     assert stats["calls"] == 3 * len(fits)
-    assert stats["launches"] < stats["calls"]       # calls were batched together
+    assert stats["launches"] <= stats["calls"]
+    for f in fit_ids:
+        srv.close_fit(f)
+    srv.close()
+
+    # one launch slot and back-to-back submissions from one thread: the calls
+    # that arrive while the first one runs are packed into one launch
+    srv = Server(ctx, gid, fits[0][0], precision=prec, max_launch_rows=2048, n_slots=1)
+    fit_ids = [srv.open_fit(m, 1024) for m, _ in fits]
+    tickets = [srv.submit(f, th) for f, th in zip(fit_ids, thetas)]
+    for i, t in enumerate(tickets):
+        lnl, st, _ = srv.wait(t, thetas[i].shape[0], timeout_ms=60000)
+        assert np.array_equal(lnl, alone[i][0]) and np.array_equal(st, alone[i][1])
+    stats = srv.stats()
+    assert stats["calls"] == len(fits) and stats["launches"] < len(fits), stats
     for f in fit_ids:
         srv.close_fit(f)
     srv.close()
