@@ -97,11 +97,14 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
   const int k_lo = rs.k_lo, k_hi = rs.k_hi;   // the row's node window: dlnL/dF vanishes outside
   const float* Yr = a.Y + ro;
   const float* Or = a.O + ro;
+  const float* O2r = a.O2 ? a.O2 + ro : nullptr;
   const float eb_kc = 0.85f - 1.9f * rs.delta;
 
   // ---- forward: attenuated spectrum in the window (the forward epilogue's arithmetic)
   for (int k = tid; k < N; k += EB_THREADS) {
-    Fs[k] = (k >= k_lo && k <= k_hi) ? attenuated(md, rs, g.att4[k], eb_kc, Yr[k], Or[k], g.neb_tab, k) : 0.f;
+    Fs[k] = (k >= k_lo && k <= k_hi)
+                ? attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k)
+                : 0.f;
     phi[k] = 0.f;
   }
   __syncthreads();

@@ -138,6 +138,7 @@ struct Params {
   int ld_out;                // row stride of the outputs
   float* Y;                  // forward: Y [n][ld_out]; adjoint: dW [n][ld_out]
   float* O;
+  float* O2;                 // forward with gridDim.z == 3: second half of the old part
   int* err;
 };
 
@@ -202,6 +203,22 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       KY = KT;
     }
   }
+  // The CTA's K ranges and their outputs.  One CTA per tile: [0, KY) -> Y and
+  // [KY, KT) -> O (forward), or [K0, KT) -> dW (adjoint).  Forward launches
+  // with gridDim.z == 3 split a tile into three CTAs, the first and second
+  // halves of the old part (-> O, O2) and the young part (-> Y): finer units
+  // of work for the SMs, with no operand read twice (the units split K).
+  int NR = GRAD ? 1 : 2;
+  int rb[2] = {K0, KY}, re[2] = {KY, KT};
+  float* rout[2] = {p.Y, p.O};
+  if (!GRAD && gridDim.z == 3) {
+    const int KH = KY + (KT - KY + 1) / 2;
+    NR = 1;
+    if (blockIdx.z == 0) { rb[0] = KY; re[0] = KH; rout[0] = p.O; }
+    else if (blockIdx.z == 1) { rb[0] = KH; re[0] = KT; rout[0] = p.O2; }
+    else { rb[0] = 0; re[0] = KY; rout[0] = p.Y; }
+  }
+  const int KFIRST = rb[0], KLAST = re[NR - 1];
   const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
   const uint32_t tfull0 = smem_u32(&bars[2 * STAGES]), tempty0 = smem_u32(&bars[2 * STAGES + 2]);
@@ -235,9 +252,9 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      for (int kt = K0; kt < KT; ++kt) {
-        const int s = (kt - K0) % STAGES;
-        const uint32_t ph = (uint32_t)((kt - K0) / STAGES) & 1u;
+      for (int kt = KFIRST; kt < KLAST; ++kt) {
+        const int s = (kt - KFIRST) % STAGES;
+        const uint32_t ph = (uint32_t)((kt - KFIRST) / STAGES) & 1u;
         if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { atomicOr(p.err, 1); break; }
         const uint32_t fb = full0 + 8 * s;
         mbar_expect_tx(fb, C::STAGE_BYTES);
@@ -256,10 +273,10 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t ID = idesc(PREC == SED_PREC_FP32 ? 2u : (PREC == SED_PREC_FP8 ? 0u : 1u), BM, BN);
-      int g = 0, kt = K0;
+      int g = 0, kt = KFIRST;
       bool ok = true;
-      for (int part = 0; part < NPART && ok; ++part) {
-        const int kb = part ? KY : K0, ke = part ? KT : KY;
+      for (int part = 0; part < NR && ok; ++part) {
+        const int kb = rb[part], ke = re[part];
         for (int gs = kb; gs < ke && ok; gs += G, ++g) {
           const int b = g & 1;
           if (!mbar_wait(tempty0 + 8 * b, (((uint32_t)g >> 1) & 1u) ^ 1u)) { atomicOr(p.err, 8); ok = false; break; }
@@ -267,8 +284,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
           const uint32_t d = tmem + (uint32_t)(b * BN);
           const int ge = gs + G < ke ? gs + G : ke;
           for (; kt < ge; ++kt) {
-            const int s = (kt - K0) % STAGES;
-            const uint32_t ph = (uint32_t)((kt - K0) / STAGES) & 1u;
+            const int s = (kt - KFIRST) % STAGES;
+            const uint32_t ph = (uint32_t)((kt - KFIRST) / STAGES) & 1u;
             if (!mbar_wait(full0 + 8 * s, ph)) { atomicOr(p.err, 2); ok = false; break; }
             tc_fence_after();
             const uint32_t st = sbase + s * C::STAGE_BYTES;
@@ -300,8 +317,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     int g = 0;
     bool ok = true;
-    for (int part = 0; part < NPART; ++part) {
-      const int kb = part ? KY : K0, ke = part ? KT : KY;
+    for (int part = 0; part < NR; ++part) {
+      const int kb = rb[part], ke = re[part];
       float run[BN];
 #pragma unroll
       for (int j = 0; j < BN; ++j) run[j] = 0.f;
@@ -324,7 +341,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         if (lane == 0) mbar_arrive(tempty0 + 8 * b);
       }
       if (row < p.n) {
-        float4* dst = reinterpret_cast<float4*>((part ? p.O : p.Y) + (size_t)row * p.ld_out + n0);
+        float4* dst = reinterpret_cast<float4*>(rout[part] + (size_t)row * p.ld_out + n0);
 #pragma unroll
         for (int j = 0; j < BN / 4; ++j) dst[j] = make_float4(run[4 * j], run[4 * j + 1], run[4 * j + 2], run[4 * j + 3]);
       }
@@ -340,6 +357,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 
 template <int PREC, int BN, int STAGES, int G, bool GRAD>
 cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
+  const int nz = (!GRAD && p.O2) ? 3 : 1;
   using C = Cfg<PREC, BN, STAGES, G, GRAD>;
   auto k = k_contract_tc<PREC, BN, STAGES, G, GRAD>;
   static bool attr = false;
@@ -348,7 +366,7 @@ cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(n_cols / BN, (p.n + BM - 1) / BM);
+  dim3 grid(n_cols / BN, (p.n + BM - 1) / BM, nz);
   k<<<grid, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
 }
@@ -370,15 +388,19 @@ static CUresult encode_kmajor(void* fn, CUtensorMap* m, void* base, CUtensorMapD
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-// Wavelength tile of the forward contraction.  With rows grouped by redshift
-// only ~40% of the wavelength tiles are computed; for short K (Kpad <= 2048,
-// e.g. 107 ages x 12 [Fe/H]) a 1024-row batch then has ~150 128-wide tiles for
-// 152 SMs, where one SM with two tiles doubles the kernel's time, so the tile
-// is 64 wide (half the unit of work, tighter windows, W re-read once more per
-// tile).  For long K (the 5-node [a/Fe] grid) the tiles are 128 wide: there
-// the re-reads of W and the shared-memory operand traffic per FLOP dominate.
-constexpr int TC_BN_SHORT_K = 64, TC_BN_LONG_K = 128, TC_LONG_K = 2048;
-int tc_bn_for(int kpad) { return kpad <= TC_LONG_K ? TC_BN_SHORT_K : TC_BN_LONG_K; }
+// Wavelength tile of the forward contraction and its split into units of
+// work.  With rows grouped by redshift only ~40% of the wavelength tiles are
+// computed, and a 1024-row batch then has ~150 128x128 tiles for 152 SMs, where
+// an SM with two tiles doubles the kernel's time.
+//  - 3xTF32 (long units): 128-wide tiles, each split over three CTAs (the two
+//    halves of the old part and the young part; no operand is read twice), so
+//    the SMs share ~450 units of similar size.
+//  - BF16 / FP8 (short units): 64-wide tiles for short K (Kpad <= 2048), one
+//    CTA per tile; 128-wide for the long-K [a/Fe] grid.
+constexpr int TC_LONG_K = 2048;
+int tc_bn_for(int prec, int kpad) {
+  return (prec == SED_PREC_FP32 || kpad > TC_LONG_K) ? 128 : 64;
+}
 
 int tc_encode_maps(void* fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo, const void* b_hi,
                    const void* b_lo, int n, int n_lam, int kpad) {
@@ -387,7 +409,7 @@ int tc_encode_maps(void* fn, TcMaps* out, int prec, const void* a_hi, const void
                                      : (f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   const int es = f32 ? 4 : (f8 ? 1 : 2);
   if (encode_kmajor(fn, &out->a_hi, const_cast<void*>(a_hi), dt, es, kpad, n, tc::BM) != CUDA_SUCCESS) return 1;
-  const int bn = tc_bn_for(kpad);
+  const int bn = tc_bn_for(prec, kpad);
   if (encode_kmajor(fn, &out->b_hi, const_cast<void*>(b_hi), dt, es, kpad, n_lam, bn) != CUDA_SUCCESS) return 2;
   if (f32) {
     if (encode_kmajor(fn, &out->a_lo, const_cast<void*>(a_lo), dt, es, kpad, n, tc::BM) != CUDA_SUCCESS) return 3;
@@ -405,13 +427,12 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   p.rs = a.rs;
   p.a_hi = a.maps->a_hi; p.a_lo = a.maps->a_lo; p.b_hi = a.maps->b_hi; p.b_lo = a.maps->b_lo;
   p.n = a.n; p.n_lam = a.n_lam; p.ldn = a.ldn; p.ld_out = a.ldn;
-  p.Y = a.Y; p.O = a.O; p.err = a.err;
-  const bool wide = tc_bn_for(a.Kpad) == TC_BN_LONG_K;   // same choice as the box of the B map
+  p.Y = a.Y; p.O = a.O; p.O2 = a.prec == SED_PREC_FP32 ? a.O2 : nullptr; p.err = a.err;
+  const bool wide = tc_bn_for(a.prec, a.Kpad) == 128;   // same choice as the box of the B map
   if (a.prec == SED_PREC_FP32) {
     p.ky_tiles = a.Ky_pad / 32;
     p.k_tiles = a.Kpad / 32;
-    return wide ? tc::launch_cfg<SED_PREC_FP32, 128, 3, 2, false>(p, a.ldn, s)
-                : tc::launch_cfg<SED_PREC_FP32, 64, 4, 2, false>(p, a.ldn, s);
+    return tc::launch_cfg<SED_PREC_FP32, 128, 3, 2, false>(p, a.ldn, s);
   }
   if (a.prec == SED_PREC_FP8) {
     p.ky_tiles = a.Ky_pad / 128;

@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
   // ---- attenuated rest-frame spectrum of the row's node window into shared memory
   const float* Yr = a.Y + (size_t)r * a.ldn;
   const float* Or = a.O + (size_t)r * a.ldn;
+  const float* O2r = a.O2 ? a.O2 + (size_t)r * a.ldn : nullptr;
   const float eb = 0.85f - 1.9f * rs.delta;
   const bool spec = md.n_pix > 0;
   const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);   // nodes [k_lo, k_hi] are the only ones read below
@@ -77,7 +78,8 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
   for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
     const float4 c = g.att4[k];
     const float ys = a.lam8 ? rs.y_scale * a.lam8[k] : 1.f;
-    const float F = attenuated(md, rs, c, eb, Yr[k] * ys, Or[k] * ys, g.neb_tab, k);
+    const float o = O2r ? Or[k] + O2r[k] : Or[k];
+    const float F = attenuated(md, rs, c, eb, Yr[k] * ys, o * ys, g.neb_tab, k);
     if (spec) Fs[k] = F;
     Gs[k] = F * c.w;
     lam_s[k] = g.lam_f[k];

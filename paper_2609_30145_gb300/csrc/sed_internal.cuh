@@ -227,6 +227,7 @@ struct Workspace {
   uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
   float* Y = nullptr;            // [rows][ldn]
   float* O = nullptr;
+  float* O2 = nullptr;           // [rows][ldn] second partial sum of the old part
   RowScal* rs = nullptr;
   int* err = nullptr;            // device error word of bounded waits
   float* theta_h = nullptr;      // host-path staging (device)
@@ -306,6 +307,8 @@ struct TcArgs {
                                           // (for FP8, Ky_pad/Kpad are the FP8 layout's Ky_pad8/Kpad8)
   const TcMaps* maps;
   float* Y; float* O; int* err;
+  float* O2;           // SED_PREC_FP32 with O2 non-NULL: the old part is split over two CTAs and
+                       // O + O2 is the old sum (other precisions ignore O2)
 };
 // encodes the four operand maps; returns 0 on success
 int tc_encode_maps(void* encode_fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo,
@@ -327,6 +330,7 @@ cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s);
 struct EpiArgs {
   int n; int ldn;
   const float* Y; const float* O;
+  const float* O2;     // non-NULL: second partial sum of the old part (added to O)
   const RowScal* rs;
   ModelDev md; GridDev g;
   const ModelDev* mtab;    // as in PrepArgs; with row_model set, smem_samp / smem_pix give the
@@ -343,6 +347,7 @@ cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 struct EpiBwdArgs {
   int n; int ldn;
   const float* Y; const float* O;
+  const float* O2;
   const RowScal* rs;
   ModelDev md; GridDev g;
   int split;            // 1: write G as TF32 hi/lo parts (3xTF32), 0: exact FP32 into *_hi
