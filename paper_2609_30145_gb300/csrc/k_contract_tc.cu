@@ -139,6 +139,8 @@ struct Params {
   float* Y;                  // forward: Y [n][ld_out]; adjoint: dW [n][ld_out]
   float* O;
   float* O2;                 // forward with gridDim.z == 3: second half of the old part
+  const int* tile_win;       // forward, persistent schedule: [2][m_tiles] window (lo, hi) of each M tile
+  int m_tiles;
   int* err;
 };
 
@@ -167,25 +169,85 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // core's FP32 accumulator therefore takes at most 4*G*(2*NOPS-1) MMA updates
 // per partial sum (24 for 3xTF32 with G = 2) instead of one per MMA of the
 // whole K loop, which keeps its rounding bias below FP32-grade accuracy; the
-// stores of Y also overlap the old-age main loop.
+// stores of one range overlap the main loop of the next.
+//
+// Units of work.  A unit is one output tile (m0, n0) with up to two K ranges
+// and their outputs: [0, KY) -> Y and [KY, KT) -> O, or, when the 3xTF32
+// forward splits a tile three ways (p.O2 set), one of [KY, KH) -> O,
+// [KH, KT) -> O2, [0, KY) -> Y; the adjoint has [K0, KT) -> dW.
+//  - Grid schedule (p.tile_win NULL): one unit per CTA from blockIdx; the CTA
+//    exits at once when the tile lies outside the union of its rows' windows.
+//  - Persistent schedule (forward, p.tile_win set): one CTA per SM; every CTA
+//    enumerates the computed units from the per-M-tile windows written by the
+//    preparation kernel -- split kind outermost (old halves first, young last),
+//    then M tile, then the wavelength tiles of the window -- and takes every
+//    gridDim.x-th one.  Tensor memory, barriers and the smem ring are set up
+//    once, and one unit's drain overlaps the next unit's MMAs.
+constexpr int MAX_MT = 64;   // M tiles of a persistent launch (8192 rows)
+
+struct Unit {
+  int m0, n0, nr;
+  int rb[2], re[2];
+  float* out[2];
+};
+
+template <int BN, bool GRAD>
+__device__ __forceinline__ void unit_ranges(const Params& p, int z, int nz, int K0, int KY, int KT, Unit& u) {
+  u.nr = GRAD ? 1 : 2;
+  u.rb[0] = K0; u.re[0] = KY; u.out[0] = p.Y;
+  u.rb[1] = KY; u.re[1] = KT; u.out[1] = p.O;
+  if (!GRAD && nz == 3) {
+    const int KH = KY + (KT - KY + 1) / 2;
+    u.nr = 1;
+    if (z == 0) { u.rb[0] = KY; u.re[0] = KH; u.out[0] = p.O; }
+    else if (z == 1) { u.rb[0] = KH; u.re[0] = KT; u.out[0] = p.O2; }
+    else { u.rb[0] = 0; u.re[0] = KY; u.out[0] = p.Y; }
+  }
+}
+
 template <int PREC, int BN, int STAGES, int G, bool GRAD>
 __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ Params p) {
   using C = Cfg<PREC, BN, STAGES, G, GRAD>;
-  constexpr int NPART = GRAD ? 1 : 2;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * STAGES + 4];
   __shared__ uint32_t tmem_base_s;
+  __shared__ int s_klo, s_khi;
+  __shared__ int s_nlo[MAX_MT], s_pref[MAX_MT + 1];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-
-  // Union of the rest-frame node windows of the tile's rows (invalid rows have
-  // none).  Forward: a wavelength tile outside it is never read, so the CTA
-  // exits at once.  Adjoint: dlnL/dY and dlnL/dO vanish outside each row's
-  // window, so the reduction over wavelength runs over the union only.
-  __shared__ int s_klo, s_khi;
+  const bool persistent = !GRAD && p.tile_win;
+  const int nz = (!GRAD && p.O2) ? 3 : 1;
   int K0 = 0, KY = p.ky_tiles, KT = p.k_tiles;
-  if (p.rs) {
+  int n_units = 1, upz = 0;
+
+  if (persistent) {
+    // computed wavelength tiles of each M tile, and their prefix counts
+    const int MT = p.m_tiles, NTt = p.ldn / BN;
+    if (threadIdx.x < MT) {
+      const int lo = p.tile_win[threadIdx.x], hi = p.tile_win[MT + threadIdx.x];
+      int a = 0, c = 0;
+      if (hi >= 0) {
+        a = lo / BN;
+        c = min(hi / BN, NTt - 1) - a + 1;
+      }
+      s_nlo[threadIdx.x] = a;
+      s_pref[threadIdx.x + 1] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_pref[0] = 0;
+      for (int m = 0; m < MT; ++m) s_pref[m + 1] += s_pref[m];
+    }
+    __syncthreads();
+    upz = s_pref[MT];
+    const int total = upz * nz;
+    n_units = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  } else if (p.rs) {
+    // grid schedule: union of the rest-frame node windows of the tile's rows
+    // (invalid rows have none).  Forward: a wavelength tile outside it is never
+    // read, so the CTA exits.  Adjoint: dlnL/dY and dlnL/dO vanish outside each
+    // row's window, so the reduction over wavelength runs over the union only.
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     if (threadIdx.x == 0) { s_klo = 0x7fffffff; s_khi = -1; }
     __syncthreads();
     if (threadIdx.x < BM && m0 + (int)threadIdx.x < p.n) {
@@ -203,22 +265,26 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       KY = KT;
     }
   }
-  // The CTA's K ranges and their outputs.  One CTA per tile: [0, KY) -> Y and
-  // [KY, KT) -> O (forward), or [K0, KT) -> dW (adjoint).  Forward launches
-  // with gridDim.z == 3 split a tile into three CTAs, the first and second
-  // halves of the old part (-> O, O2) and the young part (-> Y): finer units
-  // of work for the SMs, with no operand read twice (the units split K).
-  int NR = GRAD ? 1 : 2;
-  int rb[2] = {K0, KY}, re[2] = {KY, KT};
-  float* rout[2] = {p.Y, p.O};
-  if (!GRAD && gridDim.z == 3) {
-    const int KH = KY + (KT - KY + 1) / 2;
-    NR = 1;
-    if (blockIdx.z == 0) { rb[0] = KY; re[0] = KH; rout[0] = p.O; }
-    else if (blockIdx.z == 1) { rb[0] = KH; re[0] = KT; rout[0] = p.O2; }
-    else { rb[0] = 0; re[0] = KY; rout[0] = p.Y; }
-  }
-  const int KFIRST = rb[0], KLAST = re[NR - 1];
+  if (n_units == 0) return;
+
+  // unit j of this CTA
+  auto get_unit = [&](int j, Unit& u) {
+    int z = GRAD ? 0 : (int)blockIdx.z;
+    if (persistent) {
+      const int idx = (int)blockIdx.x + j * (int)gridDim.x;
+      z = idx / upz;
+      const int rem = idx - z * upz;
+      int m = 0;
+      while (s_pref[m + 1] <= rem) ++m;
+      u.m0 = m * BM;
+      u.n0 = (s_nlo[m] + rem - s_pref[m]) * BN;
+    } else {
+      u.m0 = blockIdx.y * BM;
+      u.n0 = blockIdx.x * BN;
+    }
+    unit_ranges<BN, GRAD>(p, z, nz, K0, KY, KT, u);
+  };
+
   const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
   const uint32_t tfull0 = smem_u32(&bars[2 * STAGES]), tempty0 = smem_u32(&bars[2 * STAGES + 2]);
@@ -245,27 +311,34 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
-  const CUtensorMap* amap_hi = &p.a_hi;
-  const CUtensorMap* amap_lo = &p.a_lo;
-  if (GRAD && n0 >= p.n_split) { amap_hi = &p.a2_hi; amap_lo = &p.a2_lo; }
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      for (int kt = KFIRST; kt < KLAST; ++kt) {
-        const int s = (kt - KFIRST) % STAGES;
-        const uint32_t ph = (uint32_t)((kt - KFIRST) / STAGES) & 1u;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { atomicOr(p.err, 1); break; }
-        const uint32_t fb = full0 + 8 * s;
-        mbar_expect_tx(fb, C::STAGE_BYTES);
-        const uint32_t st = sbase + s * C::STAGE_BYTES;
-        const int kc = kt * (ROWB / (PREC == SED_PREC_FP32 ? 4 : (PREC == SED_PREC_FP8 ? 1 : 2)));  // element coordinate along K
-        tma_load_2d(st, amap_hi, fb, kc, m0);
-        tma_load_2d(st + C::A_BYTES, &p.b_hi, fb, kc, n0);
-        if constexpr (C::NOPS == 2) {
-          tma_load_2d(st + C::A_BYTES + C::B_BYTES, amap_lo, fb, kc, m0);
-          tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &p.b_lo, fb, kc, n0);
-        }
+      int it = 0;
+      bool ok = true;
+      for (int j = 0; j < n_units && ok; ++j) {
+        Unit u;
+        get_unit(j, u);
+        const CUtensorMap* amap_hi = &p.a_hi;
+        const CUtensorMap* amap_lo = &p.a_lo;
+        if (GRAD && u.n0 >= p.n_split) { amap_hi = &p.a2_hi; amap_lo = &p.a2_lo; }
+        for (int r = 0; r < u.nr && ok; ++r)
+          for (int kt = u.rb[r]; kt < u.re[r]; ++kt, ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+            if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { atomicOr(p.err, 1); ok = false; break; }
+            const uint32_t fb = full0 + 8 * s;
+            mbar_expect_tx(fb, C::STAGE_BYTES);
+            const uint32_t st = sbase + s * C::STAGE_BYTES;
+            const int kc = kt * (ROWB / (PREC == SED_PREC_FP32 ? 4 : (PREC == SED_PREC_FP8 ? 1 : 2)));  // element coordinate along K
+            tma_load_2d(st, amap_hi, fb, kc, u.m0);
+            tma_load_2d(st + C::A_BYTES, &p.b_hi, fb, kc, u.n0);
+            if constexpr (C::NOPS == 2) {
+              tma_load_2d(st + C::A_BYTES + C::B_BYTES, amap_lo, fb, kc, u.m0);
+              tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &p.b_lo, fb, kc, u.n0);
+            }
+          }
       }
     }
     __syncwarp();
@@ -273,77 +346,85 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     if (lane == 0) {
       // ---------------- MMA issuer
       constexpr uint32_t ID = idesc(PREC == SED_PREC_FP32 ? 2u : (PREC == SED_PREC_FP8 ? 0u : 1u), BM, BN);
-      int g = 0, kt = KFIRST;
+      int g = 0, it = 0;
       bool ok = true;
-      for (int part = 0; part < NR && ok; ++part) {
-        const int kb = rb[part], ke = re[part];
-        for (int gs = kb; gs < ke && ok; gs += G, ++g) {
-          const int b = g & 1;
-          if (!mbar_wait(tempty0 + 8 * b, (((uint32_t)g >> 1) & 1u) ^ 1u)) { atomicOr(p.err, 8); ok = false; break; }
-          tc_fence_after();
-          const uint32_t d = tmem + (uint32_t)(b * BN);
-          const int ge = gs + G < ke ? gs + G : ke;
-          for (; kt < ge; ++kt) {
-            const int s = (kt - KFIRST) % STAGES;
-            const uint32_t ph = (uint32_t)((kt - KFIRST) / STAGES) & 1u;
-            if (!mbar_wait(full0 + 8 * s, ph)) { atomicOr(p.err, 2); ok = false; break; }
+      for (int j = 0; j < n_units && ok; ++j) {
+        Unit u;
+        get_unit(j, u);
+        for (int r = 0; r < u.nr && ok; ++r) {
+          const int kb = u.rb[r], ke = u.re[r];
+          for (int gs = kb; gs < ke && ok; gs += G, ++g) {
+            const int b = g & 1;
+            if (!mbar_wait(tempty0 + 8 * b, (((uint32_t)g >> 1) & 1u) ^ 1u)) { atomicOr(p.err, 8); ok = false; break; }
             tc_fence_after();
-            const uint32_t st = sbase + s * C::STAGE_BYTES;
-            const uint32_t a_hi = st, b_hi = st + C::A_BYTES;
+            const uint32_t d = tmem + (uint32_t)(b * BN);
+            const int ge = gs + G < ke ? gs + G : ke;
+            for (int kt = gs; kt < ge; ++kt, ++it) {
+              const int s = it % STAGES;
+              const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+              if (!mbar_wait(full0 + 8 * s, ph)) { atomicOr(p.err, 2); ok = false; break; }
+              tc_fence_after();
+              const uint32_t st = sbase + s * C::STAGE_BYTES;
+              const uint32_t a_hi = st, b_hi = st + C::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K each
-              const uint32_t acc = (kt == gs && kk == 0) ? 0u : 1u;
-              const uint64_t da = sdesc(a_hi + kk * 32), db = sdesc(b_hi + kk * 32);
-              if constexpr (C::NOPS == 2) {
-                const uint32_t a_lo = st + C::A_BYTES + C::B_BYTES, b_lo = a_lo + C::A_BYTES;
-                mma<PREC>(d, sdesc(a_lo + kk * 32), db, ID, acc);
-                mma<PREC>(d, da, sdesc(b_lo + kk * 32), ID, 1u);
-                mma<PREC>(d, da, db, ID, 1u);
-              } else {
-                mma<PREC>(d, da, db, ID, acc);
+              for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K each
+                const uint32_t acc = (kt == gs && kk == 0) ? 0u : 1u;
+                const uint64_t da = sdesc(a_hi + kk * 32), db = sdesc(b_hi + kk * 32);
+                if constexpr (C::NOPS == 2) {
+                  const uint32_t a_lo = st + C::A_BYTES + C::B_BYTES, b_lo = a_lo + C::A_BYTES;
+                  mma<PREC>(d, sdesc(a_lo + kk * 32), db, ID, acc);
+                  mma<PREC>(d, da, sdesc(b_lo + kk * 32), ID, 1u);
+                  mma<PREC>(d, da, db, ID, 1u);
+                } else {
+                  mma<PREC>(d, da, db, ID, acc);
+                }
               }
+              mma_commit(empty0 + 8 * s);
             }
-            mma_commit(empty0 + 8 * s);
+            if (ok) mma_commit(tfull0 + 8 * b);
           }
-          if (ok) mma_commit(tfull0 + 8 * b);
         }
       }
     }
     __syncwarp();
   } else {
-    // ---------------- drain + epilogue: warps 2..5 cover TMEM lane quadrants 2,3,0,1
+    // ---------------- drain: warps 2..5 cover TMEM lane quadrants 2,3,0,1
     const int q = warp & 3;
-    const int row = m0 + q * 32 + lane;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     int g = 0;
     bool ok = true;
-    for (int part = 0; part < NR; ++part) {
-      const int kb = rb[part], ke = re[part];
-      float run[BN];
+    for (int j = 0; j < n_units; ++j) {
+      Unit u;
+      get_unit(j, u);
+      const int row = u.m0 + q * 32 + lane;
+      for (int r = 0; r < u.nr; ++r) {
+        const int kb = u.rb[r], ke = u.re[r];
+        float run[BN];
 #pragma unroll
-      for (int j = 0; j < BN; ++j) run[j] = 0.f;
-      for (int gs = kb; gs < ke; gs += G, ++g) {
-        const int b = g & 1;
-        if (ok && !mbar_wait(tfull0 + 8 * b, ((uint32_t)g >> 1) & 1u)) { atomicOr(p.err, 4); ok = false; }
-        tc_fence_after();
-        if (ok) {
+        for (int c = 0; c < BN; ++c) run[c] = 0.f;
+        for (int gs = kb; gs < ke; gs += G, ++g) {
+          const int b = g & 1;
+          if (ok && !mbar_wait(tfull0 + 8 * b, ((uint32_t)g >> 1) & 1u)) { atomicOr(p.err, 4); ok = false; }
+          tc_fence_after();
+          if (ok) {
 #pragma unroll
-          for (int c = 0; c < BN / 32; ++c) {
-            uint32_t r[32];
-            tmem_ld32(tmem + lane_off + (uint32_t)(b * BN + c * 32), r);
-            tmem_wait_ld();
+            for (int c = 0; c < BN / 32; ++c) {
+              uint32_t rr[32];
+              tmem_ld32(tmem + lane_off + (uint32_t)(b * BN + c * 32), rr);
+              tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) run[c * 32 + j] += __uint_as_float(r[j]);
+              for (int i = 0; i < 32; ++i) run[c * 32 + i] += __uint_as_float(rr[i]);
+            }
           }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * b);
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty0 + 8 * b);
-      }
-      if (row < p.n) {
-        float4* dst = reinterpret_cast<float4*>(rout[part] + (size_t)row * p.ld_out + n0);
+        if (row < p.n) {
+          float4* dst = reinterpret_cast<float4*>(u.out[r] + (size_t)row * p.ld_out + u.n0);
 #pragma unroll
-        for (int j = 0; j < BN / 4; ++j) dst[j] = make_float4(run[4 * j], run[4 * j + 1], run[4 * j + 2], run[4 * j + 3]);
+          for (int c = 0; c < BN / 4; ++c) dst[c] = make_float4(run[4 * c], run[4 * c + 1], run[4 * c + 2], run[4 * c + 3]);
+        }
       }
     }
   }
@@ -358,6 +439,12 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 template <int PREC, int BN, int STAGES, int G, bool GRAD>
 cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
   const int nz = (!GRAD && p.O2) ? 3 : 1;
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
+  }
   using C = Cfg<PREC, BN, STAGES, G, GRAD>;
   auto k = k_contract_tc<PREC, BN, STAGES, G, GRAD>;
   static bool attr = false;
@@ -366,8 +453,12 @@ cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(n_cols / BN, (p.n + BM - 1) / BM, nz);
-  k<<<grid, C::THREADS, C::SMEM, s>>>(p);
+  if (!GRAD && p.tile_win) {
+    k<<<dim3(n_sm, 1, 1), C::THREADS, C::SMEM, s>>>(p);   // persistent: one CTA per SM
+  } else {
+    dim3 grid(n_cols / BN, (p.n + BM - 1) / BM, nz);
+    k<<<grid, C::THREADS, C::SMEM, s>>>(p);
+  }
   return cudaGetLastError();
 }
 
@@ -428,6 +519,8 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   p.a_hi = a.maps->a_hi; p.a_lo = a.maps->a_lo; p.b_hi = a.maps->b_hi; p.b_lo = a.maps->b_lo;
   p.n = a.n; p.n_lam = a.n_lam; p.ldn = a.ldn; p.ld_out = a.ldn;
   p.Y = a.Y; p.O = a.O; p.O2 = a.prec == SED_PREC_FP32 ? a.O2 : nullptr; p.err = a.err;
+  p.m_tiles = (a.n + tc::BM - 1) / tc::BM;
+  p.tile_win = (a.tile_win && p.m_tiles <= tc::MAX_MT) ? a.tile_win : nullptr;
   const bool wide = tc_bn_for(a.prec, a.Kpad) == 128;   // same choice as the box of the B map
   if (a.prec == SED_PREC_FP32) {
     p.ky_tiles = a.Ky_pad / 32;

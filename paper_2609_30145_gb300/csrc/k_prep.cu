@@ -399,6 +399,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       }
       rs.k_lo = max(lo - 2, 0);
       rs.k_hi = min(max(hi + 3, rs.k_lo + 1), N - 1);
+      if (a.tile_win) {   // union of the windows of this row's 128-row tile
+        const int mt = (a.n + 127) >> 7;
+        atomicMin(&a.tile_win[p >> 7], rs.k_lo);
+        atomicMax(&a.tile_win[mt + (p >> 7)], rs.k_hi);
+      }
     }
     rs.nnz = 0;
     for (int w = 0; w < PREP_THREADS / 32; ++w) rs.nnz += s_nnz[w];

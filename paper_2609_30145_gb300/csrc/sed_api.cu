@@ -181,7 +181,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
     }
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
-      std::vector<void*> v = {w->perm, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
+      std::vector<void*> v = {w->perm, w->tile_win, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
                               w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                               w->dW, w->rgrad};
       for (void* p : v)
@@ -865,7 +865,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   if (!need) return w;
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
-  std::vector<void*> old = {w->perm, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
+  std::vector<void*> old = {w->perm, w->tile_win, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
                             w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                             w->dW, w->rgrad};
   for (void* p : old)
@@ -882,7 +882,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   std::vector<void*>* no = nullptr;
   sed_status s = SED_OK;
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
-  AL(perm, R * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
+  AL(perm, R * 4); AL(tile_win, 2 * ((R + 127) / 128) * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
   AL(Y, R * N * 4); AL(O, R * N * 4); AL(O2, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
   AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
   if (grad || had_grad) {
@@ -947,6 +947,12 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   pa.rs = w->rs;
   pa.err = w->err;
   pa.perm = w->perm;
+  pa.tile_win = w->tile_win;
+  {
+    const size_t mt = (size_t)(n + 127) / 128;
+    CK(cudaMemsetAsync(w->tile_win, 0x7f, mt * sizeof(int), s));
+    CK(cudaMemsetAsync(w->tile_win + mt, 0xff, mt * sizeof(int), s));
+  }
   CK(launch_prep(pa, s));
   if (sed_status ps = prof_mark(ctx, w, 1, s)) return ps;
   if (precision == SED_PREC_FP32_SIMT) {
@@ -977,6 +983,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   ta.Ky_pad = f8 ? L->Ky_pad8 : L->Ky_pad;
   ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
   ta.maps = maps; ta.Y = w->Y; ta.O = w->O; ta.O2 = w->O2; ta.err = w->err; ta.rs = w->rs;
+  ta.tile_win = w->tile_win;
   CK(launch_contract_tc(ta, s));
   return prof_mark(ctx, w, 2, s);
 }

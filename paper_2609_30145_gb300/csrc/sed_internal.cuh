@@ -223,6 +223,7 @@ struct Workspace {
   float* W_hi = nullptr;         // [rows][Kpad]
   float* W_lo = nullptr;
   int* perm = nullptr;           // [rows] processing order
+  int* tile_win = nullptr;       // [2][ceil(rows/128)] per-tile node windows
   __nv_bfloat16* W_bf16 = nullptr;
   uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
   float* Y = nullptr;            // [rows][ldn]
@@ -287,6 +288,8 @@ struct PrepArgs {
   RowScal* rs;
   int* err;            // device error word of the contraction, cleared by the prep kernel
   int* perm;           // [n] scratch: processing order (rows sorted by redshift), or NULL = caller's order
+  int* tile_win;       // [2][ceil(n/128)] union of the row windows of each 128-row tile (lo set to
+                       // 0x7f7f7f7f and hi to -1 beforehand), or NULL
 };
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 
@@ -309,6 +312,7 @@ struct TcArgs {
   float* Y; float* O; int* err;
   float* O2;           // SED_PREC_FP32 with O2 non-NULL: the old part is split over two CTAs and
                        // O + O2 is the old sum (other precisions ignore O2)
+  const int* tile_win; // non-NULL (and <= 64 M tiles): persistent schedule over the computed tiles
 };
 // encodes the four operand maps; returns 0 on success
 int tc_encode_maps(void* encode_fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo,
