@@ -301,22 +301,19 @@ def run_ours(args):
     c_ms = statistics.mean(contract_ms)
     alg_flop = 2.0 * nnz * n_lam
     pk, pk_kind = peaks()
+    issued = statistics.mean(s["issued_flop"] for s in stats)
     if prec == "fp32":
         peak_tf = pk["bf16_tflops_sustained"] * TF32_PER_BF16
-        issued = 3 * 2.0 * B * kpad * ldn
         peak_note = (f"TF32 dense peak = sustained BF16 {pk['bf16_tflops_sustained']} x {TF32_PER_BF16:.3f} "
                      f"(nominal ratio), of {pk_kind}")
     elif prec == "bf16":
         peak_tf = pk["bf16_tflops_sustained"]
-        issued = 2.0 * B * kpad * ldn
         peak_note = f"sustained BF16 dense peak, of {pk_kind}"
     elif prec == "fp8":
         peak_tf = pk["bf16_tflops_sustained"] * 2.0
-        issued = 2.0 * B * kpad * ldn
         peak_note = f"FP8 dense peak = sustained BF16 {pk['bf16_tflops_sustained']} x 2 (nominal ratio), of {pk_kind}"
     else:
         peak_tf = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FFMA: SMs x lanes x 2 x max clock
-        issued = 2.0 * B * kpad * ldn
         peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz"
     achieved = alg_flop / (c_ms * 1e-3) / 1e12
     e_ms = statistics.mean(epi_ms)

@@ -324,6 +324,8 @@ typedef struct {
   float ms_prep, ms_contract, ms_epilogue;
   double nnz_w;          /* sum over rows of the non-zero weights W[theta][k] */
   double dense_k;        /* padded K of the contraction (young + old) */
+  double issued_flop;    /* tensor (or FFMA) FLOPs the contraction issued over its computed tiles
+                            (x3 for the 3xTF32 split) */
   int n_rows, n_lam, ldn, precision;
 } sed_stage_stats;
 

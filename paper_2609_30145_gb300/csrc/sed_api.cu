@@ -923,7 +923,8 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   Grid* g = M->g;
   Layout* L = M->L;
   if (ctx->profiling) {
-    w->last_n = n; w->last_prec = precision; w->last_kpad = L->Kpad; w->last_nlam = g->n_lam;
+    w->last_n = n; w->last_prec = precision; w->last_nlam = g->n_lam;
+    w->last_kpad = precision == SED_PREC_FP8 ? L->Ky_pad8 == 0 ? L->Kpad : L->Kpad8 : L->Kpad;
     w->have_stats = true;
   }
   if (sed_status ps = prof_mark(ctx, w, 0, s)) return ps;
@@ -1156,6 +1157,19 @@ sed_status sed_last_stats(sed_ctx* ctx, void* stream, sed_stage_stats* out) {
   for (const RowScal& r : rs) nnz += r.nnz;
   out->nnz_w = nnz;
   out->dense_k = w->last_kpad;
+  // tensor work actually issued: the wavelength tiles of each 128-row tile's window union
+  {
+    const bool simt = w->last_prec == SED_PREC_FP32_SIMT;
+    const int bn = simt ? 128 : tc_bn_for(w->last_prec, w->last_kpad);
+    double tiles = 0;
+    for (size_t m0 = 0; m0 < rs.size(); m0 += 128) {
+      int lo = 0x7fffffff, hi = -1;
+      for (size_t r = m0; r < std::min(rs.size(), m0 + 128); ++r)
+        if (rs[r].status == 0) { lo = std::min(lo, rs[r].k_lo); hi = std::max(hi, rs[r].k_hi); }
+      if (hi >= 0) tiles += hi / bn - lo / bn + 1;
+    }
+    out->issued_flop = tiles * 2.0 * 128.0 * bn * w->last_kpad * (w->last_prec == SED_PREC_FP32 ? 3.0 : 1.0);
+  }
   out->n_rows = w->last_n;
   out->n_lam = w->last_nlam;
   out->ldn = w->ldn;

@@ -318,6 +318,8 @@ struct TcArgs {
 int tc_encode_maps(void* encode_fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo,
                    const void* b_hi, const void* b_lo, int n, int n_lam, int kpad);
 cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s);
+// wavelength width of the forward tensor-core tile for a precision and padded K
+int tc_bn_for(int prec, int kpad);
 
 // Adjoint contraction dW = [G_Y SSP_young^T | G_O SSP_old^T] (3xTF32 on tcgen05).
 // G rows have stride ldg; SSP rows [Kpad][ldk] (ldk <= ldg is the reduction length).
