@@ -54,12 +54,14 @@ __device__ __forceinline__ float sfh_edge(int i, int NT, double tmax, float lrat
   return 1e7f * expf(lrat * (float)(i - 2) / (float)(NT - 2));
 }
 
-// Cosmology and observer-frame scalars of one row (Sec. 2.6).  D_C(z) and
-// t_univ(z) are cubic Hermite interpolants (FP64) of a table the host fills once
-// per model with the FP64 integral / closed form and their exact derivatives
-// (c/H0/E and -1/(H0 (1+z) E)); the interpolation error is below 1e-10
-// relative, and GB300's narrow FP64 pipe sees ~30 FP64 operations per row
-// instead of a quadrature.
+// Cosmology and observer-frame scalars of one row (Sec. 2.6).  D_C(z),
+// t_univ(z), ln(1+z) and 1/(1+z) are cubic Hermite interpolants (FP64) of a
+// table the host fills once per model with FP64 values and their exact
+// derivatives (c/H0/E, -1/(H0 (1+z) E), 1/(1+z), -1/(1+z)^2); the
+// interpolation error is below 1e-10 relative.  GB300's FP64 pipe is narrow,
+// so FP64 is kept to D_L, T_max, ln(1+z) (hi + lo floats for the spectral
+// positions) and the flux scale, ~50 FP64 operations per row; the derivative
+// factors used only by the adjoint are FP32.
 //  D_L = (1+z) D_C, floored at 10 pc;  T_max = t(z) - t(zf);
 //  s = 10^logmass Lsun (1+z) / (4 pi D_L^2) in device flux units, with
 //  10^logmass = 2^n 2^f taken as an FP32 exp2 of the fraction (FP32-grade).
@@ -71,34 +73,37 @@ __device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm) {
     c.status = SED_ROW_BAD_Z;
   } else {
     const double zd = (double)z, zp = 1.0 + zd;
-    const double q = zd / md.ctab_h;
+    const double q = zd * md.ctab_inv_h;
     const int i = min((int)q, md.n_ctab - 1);
     const double u = q - (double)i, v = 1.0 - u;
-    const double* t0 = md.ctab + 4 * (size_t)i;
-    const double* t1 = t0 + 4;
+    const double* t0 = md.ctab + COSMO_COLS * (size_t)i;
+    const double* t1 = t0 + COSMO_COLS;
     const double h00 = (1.0 + 2.0 * u) * v * v, h10 = u * v * v * md.ctab_h;
     const double h01 = u * u * (3.0 - 2.0 * u), h11 = -u * u * v * md.ctab_h;
     const double dc = h00 * t0[0] + h10 * t0[1] + h01 * t1[0] + h11 * t1[1];
     const double tu = h00 * t0[2] + h10 * t0[3] + h01 * t1[2] + h11 * t1[3];
-    const double ez = sqrt(md.Om0 * zp * zp * zp + (1.0 - md.Om0));
+    const double l1 = h00 * t0[4] + h10 * t0[5] + h01 * t1[4] + h11 * t1[5];
+    const double izp = h00 * t0[6] + h10 * t0[7] + h01 * t1[6] + h11 * t1[7];
     const double tmax = tu - md.t_zf_yr;
-    const double izp = 1.0 / zp;
     double dl = zp * dc;
-    double ddl = dc + zp * md.dh_cm / ez;
-    if (dl < 10.0 * PC_CM) { dl = 10.0 * PC_CM; ddl = 0.0; }
-    const double dlnd = ddl / dl;
+    const bool floor10 = dl < 10.0 * PC_CM;
+    if (floor10) dl = 10.0 * PC_CM;
+    const double idl = 1.0 / dl;
     const double e2 = (double)lm * 3.321928094887362;
     const double en = floor(e2);
-    const double sc = ldexp((double)exp2f((float)(e2 - en)), (int)en) * md.lsun_c * zp / (dl * dl);
-    c.p_phot = (float)(C_AA * sc * izp * izp);
+    const double sc = ldexp((double)exp2f((float)(e2 - en)), (int)en) * md.lsun_c * zp * idl * idl;
+    const float izf = (float)izp;
     c.s_spec = (float)sc;
-    c.inv1pz = (float)izp;
-    const double l1 = log(zp);
+    c.p_phot = (float)(C_AA * sc) * izf * izf;
+    c.inv1pz = izf;
     c.ln1pz_hi = (float)l1;
     c.ln1pz_lo = (float)(l1 - (double)c.ln1pz_hi);
-    c.dlns_dz = (float)(izp - 2.0 * dlnd);
-    c.dlnp_dz = (float)(-izp - 2.0 * dlnd);
-    c.dtmax_dz = (float)(-md.th_yr * izp / ez);
+    // adjoint factors (FP32): dlnD_L/dz = (D_C + (1+z) c/(H0 E)) / D_L, dt/dz = -1/(H0 (1+z) E)
+    const float zpf = 1.f + z, ezf = sqrtf((float)md.Om0 * zpf * zpf * zpf + (1.f - (float)md.Om0));
+    const float dlnd = floor10 ? 0.f : ((float)dc + zpf * (float)md.dh_cm / ezf) * (float)idl;
+    c.dlns_dz = izf - 2.f * dlnd;
+    c.dlnp_dz = -izf - 2.f * dlnd;
+    c.dtmax_dz = -(float)md.th_yr * izf / ezf;
     c.tmax_d = tmax;
     c.lrat = tmax > 1e7 ? logf((float)(tmax * 1e-7)) : 0.f;
     c.status = tmax > 1e7 ? 0u : SED_ROW_BAD_TMAX;
@@ -122,8 +127,8 @@ constexpr int ORDER_CHUNK = 4096;
 constexpr int ORDER_THREADS = 1024;
 constexpr int ORDER_BINS = 1024;
 
-__global__ void __launch_bounds__(ORDER_THREADS) k_order(const float* theta, int n, int ld, int zoff, double zf,
-                                                         int* perm) {
+__global__ void __launch_bounds__(ORDER_THREADS) k_order(const float* theta, int n, int ld, int zoff, float zf,
+                                                         float scale, int* perm) {
   __shared__ int cnt[ORDER_BINS + 1];
   __shared__ int wsum[ORDER_THREADS / 32];
   const int base = blockIdx.x * ORDER_CHUNK;
@@ -133,14 +138,13 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_order(const float* theta, int
   __syncthreads();
   constexpr int PER = ORDER_CHUNK / ORDER_THREADS;
   int bin[PER];
-  const float scale = (float)(ORDER_BINS / zf);
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int i = tid + u * ORDER_THREADS;
     bin[u] = -1;
     if (i < m) {
       const float z = theta[(size_t)(base + i) * ld + zoff];
-      bin[u] = (z >= 0.f && (double)z < zf) ? min(ORDER_BINS - 1, (int)(z * scale)) : ORDER_BINS;
+      bin[u] = (z >= 0.f && z < zf) ? min(ORDER_BINS - 1, (int)(z * scale)) : ORDER_BINS;
       atomicAdd(&cnt[bin[u]], 1);
     }
   }
@@ -583,8 +587,8 @@ cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (p.perm && !p.row_model) {
-    k_order<<<(p.n + ORDER_CHUNK - 1) / ORDER_CHUNK, ORDER_THREADS, 0, s>>>(p.theta, p.n, p.ld,
-                                                                          p.md.offs[SED_KEY_ZRED], p.md.zf, p.perm);
+    k_order<<<(p.n + ORDER_CHUNK - 1) / ORDER_CHUNK, ORDER_THREADS, 0, s>>>(
+        p.theta, p.n, p.ld, p.md.offs[SED_KEY_ZRED], (float)p.md.zf, (float)(ORDER_BINS / p.md.zf), p.perm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -541,7 +541,8 @@ double t_univ_yr(double th_yr, double Om, double z) {
 // Cosmology table of a model (flat LCDM without radiation, Sec. 2.6): at
 // z_i = i zf / n, D_C(z_i) = (c/H0) int_0^z_i dz/E by 16-point Gauss-Legendre
 // on each interval (FP64, accumulated), its derivative c/(H0 E), the age of
-// the Universe t(z_i) in closed form and dt/dz = -1/(H0 (1+z) E).
+// the Universe t(z_i) in closed form and dt/dz = -1/(H0 (1+z) E), and
+// ln(1+z) and 1/(1+z) with their derivatives.
 void cosmo_table(double H0, double Om, double zf, int n, std::vector<double>* out) {
   static const double x16[8] = {0.0950125098376374, 0.2816035507792589, 0.4580167776572274, 0.6178762444026438,
                                 0.7554044083550030, 0.8656312023878318, 0.9445750230732326, 0.9894009349916499};
@@ -549,7 +550,7 @@ void cosmo_table(double H0, double Om, double zf, int n, std::vector<double>* ou
                                 0.1246289712555339, 0.0951585116824928, 0.0622535239386479, 0.0271524594117541};
   const double OL = 1.0 - Om, dh = C_KMS / H0 * 1e6 * PC_CM, thy = MPC_KM / H0 / YR_S, h = zf / n;
   auto E = [&](double z) { const double zp = 1.0 + z; return std::sqrt(Om * zp * zp * zp + OL); };
-  out->assign((size_t)(n + 1) * 4, 0.0);
+  out->assign((size_t)(n + 1) * COSMO_COLS, 0.0);
   double dc = 0.0;
   for (int i = 0; i <= n; i++) {
     const double z = i * h;
@@ -559,11 +560,15 @@ void cosmo_table(double H0, double Om, double zf, int n, std::vector<double>* ou
       for (int k = 0; k < 8; k++) acc += w16[k] * (1.0 / E(mid - hw * x16[k]) + 1.0 / E(mid + hw * x16[k]));
       dc += dh * hw * acc;
     }
-    double* t = out->data() + 4 * (size_t)i;
+    double* t = out->data() + COSMO_COLS * (size_t)i;
     t[0] = dc;
     t[1] = dh / E(z);
     t[2] = t_univ_yr(thy, Om, z);
     t[3] = -thy / ((1.0 + z) * E(z));
+    t[4] = std::log1p(z);
+    t[5] = 1.0 / (1.0 + z);
+    t[6] = 1.0 / (1.0 + z);
+    t[7] = -1.0 / ((1.0 + z) * (1.0 + z));
   }
 }
 
@@ -678,6 +683,7 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     dv.ctab = pd;
     dv.n_ctab = COSMO_TAB;
     dv.ctab_h = d->zf / COSMO_TAB;
+    dv.ctab_inv_h = COSMO_TAB / d->zf;
   }
 
   // ---- photometry: App. D weights R lam dlam / Z_b, band-major samples

@@ -26,6 +26,7 @@ constexpr int MAX_AFE = 16;
 constexpr int MAX_SFH = 512;
 constexpr int MAX_LAM = 24576;   // rest-frame nodes an epilogue row can stage in shared memory
 constexpr int COSMO_TAB = 4096;  // intervals of the cosmology table on [0, zf]
+constexpr int COSMO_COLS = 8;    // value / derivative pairs of D_C, t_univ, ln(1+z), 1/(1+z)
 
 // Physical constants (cgs unless noted).
 constexpr double LSUN = 3.839e33;              // erg/s (Sec. 2.6)
@@ -108,9 +109,10 @@ struct ModelDev {
   int offs[SED_NKEYS];
   double zf, t_zf_yr, dh_cm, th_yr, Om0;
   double lsun_c;           // Lsun 2^-f_log2 / (4 pi)
-  const double* ctab;      // cosmology table [n_ctab + 1][4]: D_C (cm), dD_C/dz, t_univ (yr), dt/dz on z = i ctab_h
+  const double* ctab;      // cosmology table [n_ctab + 1][COSMO_COLS] on z = i ctab_h: D_C (cm), dD_C/dz,
+                           // t_univ (yr), dt/dz, ln(1+z), 1/(1+z), 1/(1+z), -1/(1+z)^2
   int n_ctab;
-  double ctab_h;
+  double ctab_h, ctab_inv_h;
   double f_log2, q_log2;
   int n_feh, n_afe;
   float feh[MAX_FEH];
