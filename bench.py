@@ -432,6 +432,19 @@ def bench_gradient(ctx, device, flush, args):
                   "grad_ms_per_step": round(sum(gms) / len(gms), 4),
                   "loglike_evals_per_s": round(B * len(fms) / (sum(fms) * 1e-3), 1),
                   "loglike_ms_per_step": round(sum(fms) / len(fms), 4)}
+        # per-kernel times of the gradient call (library events, spin kernel ahead)
+        ctx.set_profiling(True)
+        stats = []
+        with torch.cuda.stream(s):
+            for _ in range(5):
+                flush.zero_()
+                torch.cuda._sleep(200000)
+                model.loglike_grad(t, p, stream=s, out=(lnl, grad, stt))
+                stats.append(ctx.last_stats(s))
+        ctx.set_profiling(False)
+        res[p]["stages_ms"] = {k: round(statistics.mean(st[f] for st in stats), 4) for k, f in
+                               (("prep", "ms_prep"), ("contract", "ms_contract"), ("adjoint_epilogue", "ms_epilogue"),
+                                ("dw", "ms_dw"), ("prep_bwd", "ms_prep_bwd"))}
     return res
 
 

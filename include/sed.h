@@ -315,10 +315,12 @@ sed_status sed_server_get_stats(sed_server *server, sed_server_stats *out);
 /*
  * Per-stage timing and work counters of the last hot-path call on a stream.
  * With profiling on, each hot-path call records CUDA events on its stream
- * before and after each of its kernels (preparation, contraction, epilogue);
- * sed_last_stats synchronises on the last event and reads them.  nnz_w is the
- * number of non-zero SSP weights of the call's rows (the contraction's
- * algorithmic work is 2 * nnz_w * n_lam FLOPs).
+ * before and after each of its kernels (preparation, contraction, epilogue;
+ * for sed_loglike_grad the epilogue is the adjoint epilogue, followed by the
+ * dW contraction and the weights' reverse pass); sed_last_stats synchronises
+ * on the last event and reads them.  nnz_w is the number of non-zero SSP
+ * weights of the call's rows (the contraction's algorithmic work is
+ * 2 * nnz_w * n_lam FLOPs).
  */
 typedef struct {
   float ms_prep, ms_contract, ms_epilogue;
@@ -327,6 +329,8 @@ typedef struct {
   double issued_flop;    /* tensor (or FFMA) FLOPs the contraction issued over its computed tiles
                             (x3 for the 3xTF32 split) */
   int n_rows, n_lam, ldn, precision;
+  int is_grad;           /* 1 if the call was sed_loglike_grad */
+  float ms_dw, ms_prep_bwd;  /* gradient calls: dW = G SSP^T contraction, weights / edges / cosmology reverse pass */
 } sed_stage_stats;
 
 sed_status sed_set_profiling(sed_ctx *ctx, int on);

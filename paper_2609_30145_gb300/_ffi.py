@@ -47,7 +47,8 @@ class ModelDesc(C.Structure):
 class StageStats(C.Structure):
     _fields_ = [("ms_prep", C.c_float), ("ms_contract", C.c_float), ("ms_epilogue", C.c_float),
                 ("nnz_w", C.c_double), ("dense_k", C.c_double), ("issued_flop", C.c_double), ("n_rows", C.c_int),
-                ("n_lam", C.c_int), ("ldn", C.c_int), ("precision", C.c_int)]
+                ("n_lam", C.c_int), ("ldn", C.c_int), ("precision", C.c_int), ("is_grad", C.c_int),
+                ("ms_dw", C.c_float), ("ms_prep_bwd", C.c_float)]
 
 
 class ServerDesc(C.Structure):

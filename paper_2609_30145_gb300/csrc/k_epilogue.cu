@@ -20,19 +20,23 @@
 
 namespace sed {
 
-constexpr int EPI_THREADS = 256;
+// 128 threads per row and a small shared-memory window keep every row of a
+// paper-scale batch resident at once (8 CTAs per SM): the kernel is bound by
+// the latency of its gathers, so rows in flight is what sets its speed.
+constexpr int EPI_THREADS = 128;
+constexpr int EPI_WARPS = EPI_THREADS / 32;
 constexpr int MAX_BANDS = 128;
 
 size_t epilogue_smem(const EpiArgs& a) {
-  const int ns = a.row_model ? a.smem_samp : a.md.n_samp, np = a.row_model ? a.smem_pix : a.md.n_pix;
+  const int np = a.row_model ? a.smem_pix : a.md.n_pix;
   const size_t W = (size_t)(a.row_model ? a.smem_win : a.md.win_max);
-  return (W * (np > 0 ? 4 : 3) + (size_t)ns) * sizeof(float);
+  return W * sizeof(float2) + (np > 0 ? W * sizeof(float) : 0);
 }
 
 // MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
 // otherwise every row reads the model in the kernel parameters.
 template <bool MULTI>
-__global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_constant__ EpiArgs a) {
+__global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_constant__ EpiArgs a) {
   const int r = blockIdx.x;
   const ModelDev& md = MULTI ? a.mtab[a.row_model[a.rs[r].orig]] : a.md;
   const GridDev& g = a.g;
@@ -41,12 +45,10 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
   // shared memory holds the row's node window [k_lo, k_hi] only (at most
   // md.win_max nodes); the pointers below are offset so that they are indexed
   // by the global node k
-  extern __shared__ float smem[];
+  extern __shared__ float4 smem4[];
   const int WIN = MULTI ? a.smem_win : md.win_max;
-  const int NS = MULTI ? a.smem_samp : md.n_samp;
-  float* contrib = smem;              // per filter sample: w_j * lerp(G)(x_j)
   __shared__ float mb_s[MAX_BANDS];
-  __shared__ double red[EPI_THREADS / 32];
+  __shared__ double red[EPI_WARPS];
 
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
@@ -70,10 +72,8 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
   const float eb = 0.85f - 1.9f * rs.delta;
   const bool spec = md.n_pix > 0;
   const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);   // nodes [k_lo, k_hi] are the only ones read below
-  float* Gs = smem + NS - k_lo;                  // F / lam^2
-  float* lam_s = smem + NS + WIN - k_lo;         // rest-frame wavelengths
-  float* idl_s = smem + NS + 2 * WIN - k_lo;     // 1 / (lam[k+1] - lam[k])
-  float* Fs = smem + NS + 3 * WIN - k_lo;        // F (spectral arm only)
+  float2* LG = reinterpret_cast<float2*>(smem4) - k_lo;               // {rest-frame lambda, F / lam^2}
+  float* Fs = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem4) + WIN) - k_lo;   // F (spectral arm only)
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
     const float4 c = g.att4[k];
@@ -81,50 +81,47 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
     const float o = O2r ? Or[k] + O2r[k] : Or[k];
     const float F = attenuated(md, rs, c, eb, Yr[k] * ys, o * ys, g.neb_tab, k);
     if (spec) Fs[k] = F;
-    Gs[k] = F * c.w;
-    lam_s[k] = g.lam_f[k];
-    idl_s[k] = g.inv_dlam[k];
+    LG[k] = make_float2(g.lam_f[k], F * c.w);
   }
   __syncthreads();
 
-  // ---- photometry.  Consecutive threads take consecutive filter samples
-  //      (coalesced loads); each sample's bracket starts from the index table
-  //      over ln(lambda) (the sample's table coordinate is precomputed, the
-  //      row's ln(1+z) shifts it) and is corrected within the row's window in
-  //      shared memory.  The per-sample terms are summed per band in a fixed order.
+  // ---- photometry, one band per warp.  Consecutive lanes take consecutive
+  //      filter samples (coalesced loads); each sample's bracket starts from
+  //      the index table over ln(lambda) (the sample's table coordinate is
+  //      precomputed, the row's ln(1+z) shifts it) and is corrected within the
+  //      row's window in shared memory.  Lane-strided sums and a fixed
+  //      shuffle tree keep the order of the band sum fixed.
   const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
   {
     const float qz = rs.ln1pz_hi * g.lut_inv_h;
     const int kmin = k_lo, kmax = k_hi - 1;
-#pragma unroll 4
-    for (int j = tid; j < md.n_samp; j += EPI_THREADS) {
-      const float4 sp = md.samp4[j];     // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
-      const float x = sp.x * rs.inv1pz;
-      float v = 0.f;
-      if (x >= lam0 && x <= lamN) {
-        int q = (int)(sp.z - qz);
-        q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
-        int kc = min(max(g.lut[q], kmin), kmax);
+    for (int b = warp; b < md.n_filt; b += EPI_WARPS) {
+      const int j1 = md.band_start[b + 1];
+      float acc = 0.f;
+#pragma unroll 2
+      for (int j = md.band_start[b] + lane; j < j1; j += 32) {
+        const float4 sp = md.samp4[j];     // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
+        const float x = sp.x * rs.inv1pz;
+        if (x >= lam0 && x <= lamN) {
+          int q = (int)(sp.z - qz);
+          q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
+          int kc = min(max(g.lut[q], kmin), kmax);
 #pragma unroll 1
-        while (kc < kmax && lam_s[kc + 1] <= x) ++kc;
+          while (kc < kmax && LG[kc + 1].x <= x) ++kc;
 #pragma unroll 1
-        while (kc > kmin && lam_s[kc] > x) --kc;
-        const float t = (x - lam_s[kc]) * idl_s[kc];
-        v = Gs[kc] + t * (Gs[kc + 1] - Gs[kc]);
+          while (kc > kmin && LG[kc].x > x) --kc;
+          const float2 p0 = LG[kc], p1 = LG[kc + 1];
+          const float t = __fdividef(x - p0.x, p1.x - p0.x);
+          acc = fmaf(sp.y, p0.y + t * (p1.y - p0.y), acc);
+        }
       }
-      contrib[j] = sp.y * v;
-    }
-  }
-  __syncthreads();
-  for (int b = warp; b < md.n_filt; b += EPI_THREADS / 32) {
-    float acc = 0.f;
-    for (int j = md.band_start[b] + lane; j < md.band_start[b + 1]; j += 32) acc += contrib[j];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const float mb = rs.p_phot * acc;
-      if (a.phot_out) a.phot_out[(size_t)ro * md.n_filt + b] = mb;
-      mb_s[b] = mb;
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        const float mb = rs.p_phot * acc;
+        if (a.phot_out) a.phot_out[(size_t)ro * md.n_filt + b] = mb;
+        mb_s[b] = mb;
+      }
     }
   }
 
@@ -187,7 +184,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 5) k_epilogue(const __grid_consta
     for (int o = 16; o; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
     if (lane == 0) {
       double tot = pv;
-      for (int w = 0; w < EPI_THREADS / 32; ++w) tot += red[w];
+      for (int w = 0; w < EPI_WARPS; ++w) tot += red[w];
       uint32_t st = 0;
       if (!isfinite(tot)) { st = SED_ROW_NONFINITE; tot = -INFINITY; }
       if (a.lnl) a.lnl[ro] = tot;

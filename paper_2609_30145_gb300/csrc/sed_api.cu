@@ -932,6 +932,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
     w->last_n = n; w->last_prec = precision; w->last_nlam = g->n_lam;
     w->last_kpad = precision == SED_PREC_FP8 ? L->Ky_pad8 == 0 ? L->Kpad : L->Kpad8 : L->Kpad;
     w->have_stats = true;
+    w->last_grad = false;
   }
   if (sed_status ps = prof_mark(ctx, w, 0, s)) return ps;
   PrepArgs pa{};
@@ -1096,6 +1097,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   if (!w) return st;
   st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
   if (st) return st;
+  if (ctx->profiling) w->last_grad = true;
   const bool f32 = precision == SED_PREC_FP32;
   EpiBwdArgs eb{};
   eb.n = n; eb.ldn = w->ldn; eb.Y = w->Y; eb.O = w->O; eb.rs = w->rs;
@@ -1108,6 +1110,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   if (e == cudaErrorInvalidConfiguration && smem > 227 * 1024)
     return fail(ctx, SED_ERANGE, "adjoint epilogue needs %zu bytes of shared memory (max 227 KB)", smem);
   CK(e);
+  if (sed_status ps = prof_mark(ctx, w, 4, s)) return ps;
   if (f32) {
     if (!w->dw_maps_valid || w->dw_maps_for != (const void*)L || w->dw_maps_n != n || w->dw_maps_g != w->G_hi) {
       int ee = tc_encode_dw_maps(ctx->encode_fn, &w->dw_maps, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo, L->sspK_hi,
@@ -1128,6 +1131,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
     da.gy = w->G_hi; da.go = w->GO_hi; da.sspK = L->sspK_f32; da.dW = w->dW; da.rs = w->rs;
     CK(launch_dw_simt(da, s));
   }
+  if (sed_status ps = prof_mark(ctx, w, 5, s)) return ps;
   PrepBwdArgs pb{};
   pb.theta = theta; pb.n = n; pb.ld = ld;
   pb.md = M->dv; pb.g = g->dv; pb.L = L->dv();
@@ -1156,7 +1160,14 @@ sed_status sed_last_stats(sed_ctx* ctx, void* stream, sed_stage_stats* out) {
   memset(out, 0, sizeof *out);
   CK(cudaEventElapsedTime(&out->ms_prep, w->ev[0], w->ev[1]));
   CK(cudaEventElapsedTime(&out->ms_contract, w->ev[1], w->ev[2]));
-  CK(cudaEventElapsedTime(&out->ms_epilogue, w->ev[2], w->ev[3]));
+  if (w->last_grad) {
+    CK(cudaEventElapsedTime(&out->ms_epilogue, w->ev[2], w->ev[4]));
+    CK(cudaEventElapsedTime(&out->ms_dw, w->ev[4], w->ev[5]));
+    CK(cudaEventElapsedTime(&out->ms_prep_bwd, w->ev[5], w->ev[3]));
+    out->is_grad = 1;
+  } else {
+    CK(cudaEventElapsedTime(&out->ms_epilogue, w->ev[2], w->ev[3]));
+  }
   std::vector<RowScal> rs(w->last_n);
   CK(cudaMemcpy(rs.data(), w->rs, rs.size() * sizeof(RowScal), cudaMemcpyDeviceToHost));
   double nnz = 0;

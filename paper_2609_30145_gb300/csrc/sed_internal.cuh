@@ -256,7 +256,9 @@ struct Workspace {
   TcMaps maps;
   DwMaps dw_maps;
   // profiling: events before/after prep, contraction, epilogue of the last call
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // prep, contract, epilogue, end,
+                                                                               // adjoint epilogue end, dW end
+  bool last_grad = false;
   int last_n = 0, last_prec = 0, last_kpad = 0, last_nlam = 0;
   bool have_stats = false;
 };
