@@ -49,30 +49,32 @@ __device__ __forceinline__ void put_g(const EpiBwdArgs& a, float* hi, float* lo,
   }
 }
 
+// Shared memory of one row: F and dlnL/dF over the row's node window, then a
+// union of the filter samples' brackets (photometry) and the pixels' node
+// ranges and positions (spectrum).
 size_t epi_bwd_smem(const EpiBwdArgs& a) {
-  const size_t n = (size_t)a.g.n_lam;
+  const size_t W = (size_t)a.md.win_max;
   const size_t samp = (size_t)a.md.n_samp * 8;    // node index + interpolation weight
   const size_t pix = (size_t)a.md.n_pix * 20;     // node range + 4 floats
-  return 2 * n * sizeof(float) + (samp > pix ? samp : pix);
+  return 2 * W * sizeof(float) + (samp > pix ? samp : pix);
 }
 
-__global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
+// first index i in [lo, hi) with v[i] >= x (v ascending), hi if none
+__device__ __forceinline__ int lower_bound_f(const float* v, int lo, int hi, float x) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
   const ModelDev& md = a.md;
   const GridDev& g = a.g;
   const int r = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = g.n_lam;
   extern __shared__ __align__(16) float smem[];
-  float* Fs = smem;                 // attenuated rest-frame spectrum F
-  float* phi = smem + N;            // dlnL/dF
-  void* U = smem + 2 * N;           // union: filter samples, then spectrum pixels
-  int* sk = reinterpret_cast<int*>(U);
-  float* st = reinterpret_cast<float*>(sk + md.n_samp);
-  int* prg = reinterpret_cast<int*>(U);
-  float* pxh = reinterpret_cast<float*>(prg + md.n_pix);
-  float* pxl = pxh + md.n_pix;
-  float* pc = pxl + md.n_pix;
-  float* pt = pc + md.n_pix;
   __shared__ float ubp[EB_MAX_BANDS];
   __shared__ int bk0[EB_MAX_BANDS], bk1[EB_MAX_BANDS];
   __shared__ double band_l[EB_MAX_BANDS], band_um[EB_MAX_BANDS];
@@ -94,31 +96,47 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
     }
     return;
   }
-  const int k_lo = rs.k_lo, k_hi = rs.k_hi;   // the row's node window: dlnL/dF vanishes outside
+  // the row's node window: F is read and dlnL/dF is non-zero only there
+  const int WIN = md.win_max;
+  const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);
+  float* Fs = smem - k_lo;                // attenuated rest-frame spectrum F
+  float* phi = smem + WIN - k_lo;         // dlnL/dF
+  void* U = smem + 2 * WIN;               // union: filter samples, then spectrum pixels
+  int* sk = reinterpret_cast<int*>(U);
+  float* st = reinterpret_cast<float*>(sk + md.n_samp);
+  int* prg = reinterpret_cast<int*>(U);
+  float* pxh = reinterpret_cast<float*>(prg + md.n_pix);
+  float* pxl = pxh + md.n_pix;
+  float* pc = pxl + md.n_pix;
+  float* pt = pc + md.n_pix;              // linear-kernel weight t >= 0, or -1/sigma for a Gaussian row
   const float* Yr = a.Y + ro;
   const float* Or = a.O + ro;
   const float* O2r = a.O2 ? a.O2 + ro : nullptr;
   const float eb_kc = 0.85f - 1.9f * rs.delta;
 
   // ---- forward: attenuated spectrum in the window (the forward epilogue's arithmetic)
-  for (int k = tid; k < N; k += EB_THREADS) {
-    Fs[k] = (k >= k_lo && k <= k_hi)
-                ? attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k)
-                : 0.f;
+#pragma unroll 4
+  for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
+    Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
     phi[k] = 0.f;
   }
   __syncthreads();
 
   // ---- photometry forward (warp per band), the sample brackets, u_b and the
-  //      gather part of dlnL/dz (the sample positions lam_j/(1+z) move with z)
+  //      gather part of dlnL/dz (the sample positions lam_j/(1+z) move with z).
+  //      Brackets start from the index table over ln(lambda) and are walked
+  //      within the window, as in the forward epilogue.
   const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
+  const float qz = rs.ln1pz_hi * g.lut_inv_h;
+  const int kmin = k_lo, kmax = k_hi - 1;
   float gz_gather = 0.f;
   for (int b = warp; b < md.n_filt; b += EB_WARPS) {
     const int js = md.band_start[b], je = md.band_start[b + 1];
     float acc = 0.f;
-    int kmin = 0x7fffffff, kmax = -1;
+    int bmin = 0x7fffffff, bmax = -1;
     for (int j = js + lane; j < je; j += 32) {
-      const float x = md.samp_lam[j] * rs.inv1pz;
+      const float4 sp = md.samp4[j];     // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
+      const float x = sp.x * rs.inv1pz;
       float v = 0.f, t = 0.f;
       int k;
       if (x < lam0) {
@@ -126,23 +144,29 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
       } else if (x > lamN) {
         k = N;
       } else {
-        k = locate_lin(g, x);
+        int q = (int)(sp.z - qz);
+        q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
+        k = min(max(g.lut[q], kmin), kmax);
+#pragma unroll 1
+        while (k < kmax && g.lam_f[k + 1] <= x) ++k;
+#pragma unroll 1
+        while (k > kmin && g.lam_f[k] > x) --k;
         const float la = g.lam_f[k], lb = g.lam_f[k + 1];
         t = (x - la) / (lb - la);
         const float G0 = Fs[k] * g.inv_lam2[k], G1 = Fs[k + 1] * g.inv_lam2[k + 1];
         v = G0 + t * (G1 - G0);
-        kmin = min(kmin, k);
-        kmax = max(kmax, k);
+        bmin = min(bmin, k);
+        bmax = max(bmax, k);
       }
       sk[j] = k;
       st[j] = t;
-      acc = fmaf(md.samp_w[j], v, acc);
+      acc = fmaf(sp.y, v, acc);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-      kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+      bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+      bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
     }
     const float mb = rs.p_phot * acc;
     double v = 0.0, ub = 0.0;
@@ -156,17 +180,18 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
       band_l[b] = v;
       band_um[b] = ub * (double)mb;
       ubp[b] = c_b;
-      bk0[b] = kmin;
-      bk1[b] = kmax;
+      bk0[b] = bmin;
+      bk1[b] = bmax;
     }
     if (c_b != 0.f) {
       for (int j = js + lane; j < je; j += 32) {
         const int k = sk[j];
         if (k < 0 || k >= N) continue;
-        const float x = md.samp_lam[j] * rs.inv1pz;
+        const float2 sp = *reinterpret_cast<const float2*>(&md.samp4[j]);
+        const float x = sp.x * rs.inv1pz;
         const float G0 = Fs[k] * g.inv_lam2[k], G1 = Fs[k + 1] * g.inv_lam2[k + 1];
         const float dlerp = (G1 - G0) / (g.lam_f[k + 1] - g.lam_f[k]);
-        gz_gather += c_b * md.samp_w[j] * dlerp * (-x * rs.inv1pz);
+        gz_gather += c_b * sp.y * dlerp * (-x * rs.inv1pz);
       }
     }
   }
@@ -174,7 +199,7 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
 
   // ---- dlnL/dF from the photometry: node k gathers the samples bracketed by
   //      [k-1, k] (weight t) and [k, k+1] (weight 1-t), band by band in order
-  for (int k = tid; k < N; k += EB_THREADS) {
+  for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
     float acc = 0.f;
     for (int b = 0; b < md.n_filt; ++b) {
       const float cb = ubp[b];
@@ -186,7 +211,7 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
         if (sk[mid] < k - 1) lo = mid + 1; else hi = mid;
       }
       for (int j = lo; j < je && sk[j] <= k; ++j) {
-        const float c = cb * md.samp_w[j];
+        const float c = cb * md.samp4[j].y;
         acc += sk[j] == k ? c * (1.f - st[j]) : c * st[j];
       }
     }
@@ -194,7 +219,7 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
   }
   __syncthreads();
 
-  // ---- spectrum forward (thread per pixel): m_i, u_i, each pixel's node window
+  // ---- spectrum forward (thread per pixel): m_i, u_i, each pixel's node range
   double l_spec = 0.0, um_spec = 0.0;
   float gz_spec = 0.f;
   const double l1 = (double)rs.ln1pz_hi + (double)rs.ln1pz_lo;
@@ -202,7 +227,7 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
   for (int i = tid; i < md.n_pix; i += EB_THREADS) {
     const double xd = md.pix_ln[i] - l1;
     const float xh = (float)xd, xl = (float)(xd - (double)xh);
-    float v = 0.f, dv = 0.f, cw = 0.f, tl = -1.f;
+    float v = 0.f, dv = 0.f, cw = 0.f, tl = 0.f;
     int jlo = 1, jhi = 0;
     bool valid = false;
     if (xh >= ll0 && xh <= llN) {
@@ -232,6 +257,7 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
             sfd = fmaf(wd, Fs[j], sfd);
           }
         }
+        tl = -inv_s;
         if (sw > 0.f) {
           v = sf / sw;
           dv = (sfd * sw - sf * swd) / (sw * sw);
@@ -253,45 +279,40 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
     }
     if (ci == 0.f) { jlo = 1; jhi = 0; }
     prg[i] = (jlo & 0xffff) | (jhi << 16);
-    pxh[i] = xh;
+    pxh[i] = xh;       // ascending in i: the pixels' wavelengths are strictly increasing
     pxl[i] = xl;
     pc[i] = ci;
     pt[i] = tl;
   }
   __syncthreads();
 
-  // ---- dlnL/dF from the spectrum: warp w owns a contiguous chunk of nodes and
-  //      walks the pixels in order; its lanes cover the window's nodes
+  // ---- dlnL/dF from the spectrum: node k gathers, in pixel order, every
+  //      pixel whose node range holds k.  Those pixels lie within R of ln(lam_k)
+  //      in ln(lambda) (R = 5 sigma_max for Gaussian rows, one node spacing for
+  //      linear ones), a contiguous run of the ascending pixel positions.
   if (md.n_pix > 0) {
-    const int chunk = (N + EB_WARPS - 1) / EB_WARPS;
-    const int c0 = warp * chunk, c1 = min(N, c0 + chunk);
-    for (int i0 = 0; i0 < md.n_pix; i0 += 32) {
-      const int i = i0 + lane;
-      bool hit = false;
-      if (i < md.n_pix) {
-        const int lo = prg[i] & 0xffff, hi = prg[i] >> 16;
-        hit = lo <= hi && lo < c1 && hi >= c0;
-      }
-      unsigned mask = __ballot_sync(0xffffffffu, hit);
-      while (mask) {
-        const int p = i0 + __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int lo = prg[p] & 0xffff, hi = prg[p] >> 16;
-        const float c = pc[p], tl = pt[p], xh = pxh[p], xl = pxl[p];
-        const float inv_s = tl < 0.f ? 1.f / md.pix_s[p] : 0.f;
-        for (int j = max(lo, c0) + lane; j <= min(hi, c1 - 1); j += 32) {
-          float w;
-          if (tl >= 0.f) {
-            w = j == lo ? 1.f - tl : tl;
-          } else {
-            const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
-            const float u = d * inv_s;
-            w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
-          }
-          phi[j] += c * w;
+    const float R = 5.f * md.pix_s_max * 1.0001f + g.dln_max * 1.0001f + 1e-6f;
+    for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
+      const float lh = g.lnl_hi[k], ll = g.lnl_lo[k];
+      const int p0 = lower_bound_f(pxh, 0, md.n_pix, lh - R);
+      const int p1 = lower_bound_f(pxh, p0, md.n_pix, lh + R);
+      float acc = 0.f;
+      for (int p = p0; p < p1; ++p) {
+        const float c = pc[p];
+        const int rg = prg[p], lo = rg & 0xffff, hi = rg >> 16;
+        if (c == 0.f || k < lo || k > hi) continue;
+        const float tl = pt[p];
+        float w;
+        if (tl >= 0.f) {
+          w = k == lo ? 1.f - tl : tl;
+        } else {
+          const float d = (lh - pxh[p]) + (ll - pxl[p]);
+          const float u = d * -tl;
+          w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
         }
-        __syncwarp();
+        acc = fmaf(c, w, acc);
       }
+      phi[k] += acc;
     }
   }
   __syncthreads();
@@ -387,13 +408,9 @@ __global__ void __launch_bounds__(EB_THREADS) k_epi_bwd(const __grid_constant__ 
 cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s) {
   const size_t smem = epi_bwd_smem(a);
   if (smem_needed) *smem_needed = smem;
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   static size_t set_for = 0;
-  if (smem > 48 * 1024 && smem > set_for) {
-    cudaError_t e = cudaFuncSetAttribute(k_epi_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    set_for = smem;
-  }
+  cudaError_t e = ensure_dyn_smem(k_epi_bwd, smem, &set_for);
+  if (e != cudaSuccess) return e;
   k_epi_bwd<<<a.n, EB_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -195,15 +195,11 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
 
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
   const size_t smem = epilogue_smem(a);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   static size_t set_for[2] = {0, 0};
   const int m = a.row_model ? 1 : 0;
-  if (smem > 48 * 1024 && smem > set_for[m]) {
-    cudaError_t e = m ? cudaFuncSetAttribute(k_epilogue<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                      : cudaFuncSetAttribute(k_epilogue<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    set_for[m] = smem;
-  }
+  cudaError_t e = m ? ensure_dyn_smem(k_epilogue<true>, smem, &set_for[1])
+                    : ensure_dyn_smem(k_epilogue<false>, smem, &set_for[0]);
+  if (e != cudaSuccess) return e;
   if (m) k_epilogue<true><<<a.n, EPI_THREADS, smem, s>>>(a);
   else k_epilogue<false><<<a.n, EPI_THREADS, smem, s>>>(a);
   return cudaGetLastError();

@@ -595,11 +595,9 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   PrepKernelArgs ka;
   ka.p = p;
   const size_t smem = ((size_t)p.g.n_age * p.g.n_feh + (p.W_f8 ? (size_t)p.L.Kpad : 0)) * sizeof(float);
-  if (smem > 48 * 1024) {
-    e = p.row_model ? cudaFuncSetAttribute(k_prep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                    : cudaFuncSetAttribute(k_prep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  static size_t set_for[2] = {0, 0};
+  e = p.row_model ? ensure_dyn_smem(k_prep<true>, smem, &set_for[1]) : ensure_dyn_smem(k_prep<false>, smem, &set_for[0]);
+  if (e != cudaSuccess) return e;
   if (p.row_model) k_prep<true><<<p.n, PREP_THREADS, smem, s>>>(ka);
   else k_prep<false><<<p.n, PREP_THREADS, smem, s>>>(ka);
   return cudaGetLastError();

@@ -268,7 +268,7 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
   // per-node constants
   std::vector<float> lam_f(nl), inv_lam2(nl), lnp(nl), kp(nl), dr(nl), lh(nl), lo(nl), idl(nl, 0.f);
   g->siglib_kms.resize(nl);
-  double hmin = 1e300;
+  double hmin = 1e300, hmax = 0.0;
   for (size_t k = 0; k < nl; k++) {
     const double L = g->lam[k];
     lam_f[k] = (float)L;
@@ -286,7 +286,10 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
     double sl = C_KMS / FWHM_PER_SIGMA * 2.0 * dl / L;  // Eq. app_siglib two-pixel floor
     if (d->sigma_lib_kms && d->sigma_lib_kms[k] > sl) sl = d->sigma_lib_kms[k];
     g->siglib_kms[k] = sl;
-    if (k + 1 < nl) hmin = std::min(hmin, std::log(g->lam[k + 1]) - ll);
+    if (k + 1 < nl) {
+      hmin = std::min(hmin, std::log(g->lam[k + 1]) - ll);
+      hmax = std::max(hmax, std::log(g->lam[k + 1]) - ll);
+    }
   }
   // index LUT over ln(lambda): cells of width h <= smallest log spacing
   const double x0 = (double)lh[0];
@@ -339,6 +342,7 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
   dv.lut_n = lut_n;
   dv.lut_x0 = (float)x0;
   dv.lut_inv_h = (float)(1.0 / h);
+  dv.dln_max = (float)hmax;
   if (neb && !st) {
     g->neb_nu = d->neb_n_logu; g->neb_nz = d->neb_n_logz;
     g->neb_logu.assign(d->neb_logu, d->neb_logu + g->neb_nu);
@@ -1107,8 +1111,8 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   eb.rgrad = w->rgrad; eb.lnl = lnl_out; eb.status = row_status; eb.err = w->err;
   size_t smem = 0;
   cudaError_t e = launch_epilogue_bwd(eb, &smem, s);
-  if (e == cudaErrorInvalidConfiguration && smem > 227 * 1024)
-    return fail(ctx, SED_ERANGE, "adjoint epilogue needs %zu bytes of shared memory (max 227 KB)", smem);
+  if (e == cudaErrorInvalidConfiguration)
+    return fail(ctx, SED_ERANGE, "adjoint epilogue needs %zu bytes of dynamic shared memory (227 KB per CTA in all)", smem);
   CK(e);
   if (sed_status ps = prof_mark(ctx, w, 4, s)) return ps;
   if (f32) {

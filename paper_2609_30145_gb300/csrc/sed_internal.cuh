@@ -90,6 +90,7 @@ struct GridDev {
   const int* lut;          // lut[q] = last node with ln(lambda) <= x0 + q/inv_h
   int lut_n;
   float lut_x0, lut_inv_h;
+  float dln_max;           // largest ln(lambda[k+1] / lambda[k])
   const float* cell_lo;    // linear-time Voronoi cell of each age node (yr)
   const float* cell_hi;
   const float* neb_tab;    // [nu][nz][n_lam] log10 template + device-unit offset
@@ -295,6 +296,24 @@ struct PrepArgs {
   int* tile_win;       // [2][ceil(n/128)] union of the row windows of each 128-row tile (lo set to
                        // 0x7f7f7f7f and hi to -1 beforehand), or NULL
 };
+// Raises a kernel's dynamic shared-memory limit once its static plus dynamic
+// shared memory passes the 48 KB default; *done caches the largest size set.
+// cudaErrorInvalidConfiguration if the total passes the 227 KB a CTA can have.
+template <typename K>
+cudaError_t ensure_dyn_smem(K* kernel, size_t dyn, size_t* done) {
+  if (dyn <= *done) return cudaSuccess;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if (dyn + fa.sharedSizeBytes > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (dyn + fa.sharedSizeBytes > 48 * 1024) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  *done = dyn;
+  return cudaSuccess;
+}
+
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 
 struct ContractArgs {
