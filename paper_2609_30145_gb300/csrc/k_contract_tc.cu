@@ -10,8 +10,10 @@
 // Adjoint (GRAD = true): the same contraction transposed, reducing over lambda,
 //     dW[theta][k] = sum_lam G[theta][lam] SSP[k][lam]
 // with G = dlnL/dY for young columns k and dlnL/dO for old ones; A = G
-// ([n][ldn], lambda-major), B = SSP ([Kpad][ldn], lambda-major); a 128 x 64
-// tile lies wholly in the young or the old block (Ky_pad is a multiple of 64).
+// ([n][ldn], lambda-major), B = SSP ([Kpad][ldn], lambda-major).  The column
+// tiles of the young block start at 0 and those of the old block at Ky_pad, so
+// every tile reads one A operand; the columns of a tile past the end of its
+// block are computed but not stored.
 //
 // One CTA computes a 128 (theta) x BN tile (of Y and of O, or of dW).  Warp roles:
 //   warp 0 lane 0 : TMA producer (128B-swizzled K tiles into a STAGES-deep ring)
@@ -135,6 +137,7 @@ struct Params {
   CUtensorMap a2_hi, a2_lo;  // adjoint: A operand of the old columns (dlnL/dO)
   int n, n_lam, ldn, ky_tiles, k_tiles;
   int n_split;               // adjoint: first old column (Ky_pad)
+  int ny_tiles;              // adjoint: column tiles of the young block
   int ld_out;                // row stride of the outputs
   float* Y;                  // forward: Y [n][ld_out]; adjoint: dW [n][ld_out]
   float* O;
@@ -187,6 +190,7 @@ constexpr int MAX_MT = 64;   // M tiles of a persistent launch (8192 rows)
 
 struct Unit {
   int m0, n0, nr;
+  int ncol;                  // columns of the tile that are stored (a multiple of 4)
   int rb[2], re[2];
   float* out[2];
 };
@@ -281,6 +285,12 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     } else {
       u.m0 = blockIdx.y * BM;
       u.n0 = blockIdx.x * BN;
+    }
+    u.ncol = BN;
+    if constexpr (GRAD) {
+      const int t = (int)blockIdx.x;
+      u.n0 = t < p.ny_tiles ? t * BN : p.n_split + (t - p.ny_tiles) * BN;
+      u.ncol = min(BN, (t < p.ny_tiles ? p.n_split : p.ld_out) - u.n0);
     }
     unit_ranges<BN, GRAD>(p, z, nz, K0, KY, KT, u);
   };
@@ -423,7 +433,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         if (row < p.n) {
           float4* dst = reinterpret_cast<float4*>(u.out[r] + (size_t)row * p.ld_out + u.n0);
 #pragma unroll
-          for (int c = 0; c < BN / 4; ++c) dst[c] = make_float4(run[4 * c], run[4 * c + 1], run[4 * c + 2], run[4 * c + 3]);
+          for (int c = 0; c < BN / 4; ++c)
+            if (4 * c < u.ncol) dst[c] = make_float4(run[4 * c], run[4 * c + 1], run[4 * c + 2], run[4 * c + 3]);
         }
       }
     }
@@ -539,7 +550,7 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
               : tc::launch_cfg<SED_PREC_BF16, 64, 8, 4, false>(p, a.ldn, s);
 }
 
-constexpr int DW_BN = 64;
+constexpr int DW_BN = 128;
 
 int tc_encode_dw_maps(void* fn, DwMaps* out, const float* gy_hi, const float* gy_lo, const float* go_hi,
                       const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int ldg, int ldk, int kpad) {
@@ -564,9 +575,11 @@ cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s) {
   p.k_tiles = a.ldk / 32;
   p.ky_tiles = p.k_tiles;
   p.n_split = a.Ky_pad;
+  p.ny_tiles = (a.Ky_pad + DW_BN - 1) / DW_BN;
+  const int no_tiles = (a.Kpad - a.Ky_pad + DW_BN - 1) / DW_BN;
   p.ld_out = a.Kpad;
   p.Y = a.dW; p.O = nullptr; p.err = a.err;
-  return tc::launch_cfg<SED_PREC_FP32, DW_BN, 4, 2, true>(p, a.Kpad, s);
+  return tc::launch_cfg<SED_PREC_FP32, DW_BN, 3, 2, true>(p, (p.ny_tiles + no_tiles) * DW_BN, s);
 }
 
 }  // namespace sed
