@@ -55,17 +55,8 @@ __device__ __forceinline__ void put_g(const EpiBwdArgs& a, float* hi, float* lo,
 size_t epi_bwd_smem(const EpiBwdArgs& a) {
   const size_t W = (size_t)a.md.win_max;
   const size_t samp = (size_t)a.md.n_samp * 8;    // node index + interpolation weight
-  const size_t pix = (size_t)a.md.n_pix * 20;     // node range + 4 floats
-  return 2 * W * sizeof(float) + (samp > pix ? samp : pix);
-}
-
-// first index i in [lo, hi) with v[i] >= x (v ascending), hi if none
-__device__ __forceinline__ int lower_bound_f(const float* v, int lo, int hi, float x) {
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (v[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
+  const size_t pix = (size_t)a.md.n_pix * 20;     // 4 floats + node range
+  return ((2 * W + 3) & ~(size_t)3) * sizeof(float) + (samp > pix ? samp : pix);
 }
 
 __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
@@ -101,66 +92,86 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);
   float* Fs = smem - k_lo;                // attenuated rest-frame spectrum F
   float* phi = smem + WIN - k_lo;         // dlnL/dF
-  void* U = smem + 2 * WIN;               // union: filter samples, then spectrum pixels
+  void* U = smem + ((2 * WIN + 3) & ~3);  // union: filter samples, then spectrum pixels
   int* sk = reinterpret_cast<int*>(U);
   float* st = reinterpret_cast<float*>(sk + md.n_samp);
-  int* prg = reinterpret_cast<int*>(U);
-  float* pxh = reinterpret_cast<float*>(prg + md.n_pix);
-  float* pxl = pxh + md.n_pix;
-  float* pc = pxl + md.n_pix;
-  float* pt = pc + md.n_pix;              // linear-kernel weight t >= 0, or -1/sigma for a Gaussian row
+  // per pixel {x_hi, x_lo, c, t}: position ln(lambda_obs/(1+z)) in two floats, its
+  // weight in dlnL/dF and the linear-kernel weight t >= 0, or -1/sigma for a Gaussian row
+  float4* px4 = reinterpret_cast<float4*>(U);
+  int* prg = reinterpret_cast<int*>(px4 + md.n_pix);   // node range lo | hi << 16
+  // each thread owns a contiguous run of CH window nodes (CH odd: the runs of a
+  // warp fall in distinct shared-memory banks) for the node-owned gathers
+  const int nw = k_hi - k_lo + 1;
+  const int CH = ((nw + EB_THREADS - 1) / EB_THREADS) | 1;
+  const int kr0 = k_lo + tid * CH, kr1 = min(kr0 + CH, k_hi + 1);   // this thread's nodes [kr0, kr1)
   const float* Yr = a.Y + ro;
   const float* Or = a.O + ro;
   const float* O2r = a.O2 ? a.O2 + ro : nullptr;
   const float eb_kc = 0.85f - 1.9f * rs.delta;
 
-  // ---- forward: attenuated spectrum in the window (the forward epilogue's arithmetic)
+  // ---- forward: attenuated spectrum in the window (the forward epilogue's
+  //      arithmetic); phi holds the window's wavelengths until the photometric
+  //      gather starts
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
     Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
-    phi[k] = 0.f;
+    phi[k] = g.lam_f[k];
   }
   __syncthreads();
 
-  // ---- photometry forward (warp per band), the sample brackets, u_b and the
-  //      gather part of dlnL/dz (the sample positions lam_j/(1+z) move with z).
-  //      Brackets start from the index table over ln(lambda) and are walked
-  //      within the window, as in the forward epilogue.
+  // ---- photometry forward (warp per band, four samples in flight per lane),
+  //      the sample brackets, u_b and the gather part of dlnL/dz (the sample
+  //      positions lam_j/(1+z) move with z).  Brackets start from the index
+  //      table over ln(lambda) and are walked within the window.
   const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
   const float qz = rs.ln1pz_hi * g.lut_inv_h;
   const int kmin = k_lo, kmax = k_hi - 1;
+  const float* lam_s = phi;
   float gz_gather = 0.f;
   for (int b = warp; b < md.n_filt; b += EB_WARPS) {
     const int js = md.band_start[b], je = md.band_start[b + 1];
-    float acc = 0.f;
+    float acc = 0.f, gzb = 0.f;
     int bmin = 0x7fffffff, bmax = -1;
-    for (int j = js + lane; j < je; j += 32) {
-      const float4 sp = md.samp4[j];     // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
-      const float x = sp.x * rs.inv1pz;
-      float v = 0.f, t = 0.f;
-      int k;
-      if (x < lam0) {
-        k = -2;
-      } else if (x > lamN) {
-        k = N;
-      } else {
-        int q = (int)(sp.z - qz);
+    for (int j0 = js + lane; j0 < je; j0 += 128) {
+      float4 sp[4];   // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
+      int kg[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sp[u] = j0 + 32 * u < je ? md.samp4[j0 + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        int q = (int)(sp[u].z - qz);
         q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
-        k = min(max(g.lut[q], kmin), kmax);
-#pragma unroll 1
-        while (k < kmax && g.lam_f[k + 1] <= x) ++k;
-#pragma unroll 1
-        while (k > kmin && g.lam_f[k] > x) --k;
-        const float la = g.lam_f[k], lb = g.lam_f[k + 1];
-        t = (x - la) / (lb - la);
-        const float G0 = Fs[k] * g.inv_lam2[k], G1 = Fs[k + 1] * g.inv_lam2[k + 1];
-        v = G0 + t * (G1 - G0);
-        bmin = min(bmin, k);
-        bmax = max(bmax, k);
+        kg[u] = g.lut[q];
       }
-      sk[j] = k;
-      st[j] = t;
-      acc = fmaf(sp.y, v, acc);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = j0 + 32 * u;
+        if (j >= je) continue;
+        const float x = sp[u].x * rs.inv1pz;
+        float v = 0.f, t = 0.f;
+        int k;
+        if (x < lam0) {
+          k = -2;
+        } else if (x > lamN) {
+          k = N;
+        } else {
+          k = min(max(kg[u], kmin), kmax);
+#pragma unroll 1
+          while (k < kmax && lam_s[k + 1] <= x) ++k;
+#pragma unroll 1
+          while (k > kmin && lam_s[k] > x) --k;
+          const float la = lam_s[k], lb = lam_s[k + 1];
+          t = (x - la) / (lb - la);
+          const float G0 = __fdividef(Fs[k], la * la), G1 = __fdividef(Fs[k + 1], lb * lb);
+          v = G0 + t * (G1 - G0);
+          gzb += sp[u].y * ((G1 - G0) / (lb - la)) * (-x * rs.inv1pz);
+          bmin = min(bmin, k);
+          bmax = max(bmax, k);
+        }
+        sk[j] = k;
+        st[j] = t;
+        acc = fmaf(sp[u].y, v, acc);
+      }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -183,43 +194,53 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       bk0[b] = bmin;
       bk1[b] = bmax;
     }
-    if (c_b != 0.f) {
-      for (int j = js + lane; j < je; j += 32) {
-        const int k = sk[j];
-        if (k < 0 || k >= N) continue;
-        const float2 sp = *reinterpret_cast<const float2*>(&md.samp4[j]);
-        const float x = sp.x * rs.inv1pz;
-        const float G0 = Fs[k] * g.inv_lam2[k], G1 = Fs[k + 1] * g.inv_lam2[k + 1];
-        const float dlerp = (G1 - G0) / (g.lam_f[k + 1] - g.lam_f[k]);
-        gz_gather += c_b * sp.y * dlerp * (-x * rs.inv1pz);
-      }
-    }
+    gz_gather += c_b * gzb;
   }
   __syncthreads();
 
   // ---- dlnL/dF from the photometry: node k gathers the samples bracketed by
   //      [k-1, k] (weight t) and [k, k+1] (weight 1-t), band by band in order
-  for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
-    float acc = 0.f;
-    for (int b = 0; b < md.n_filt; ++b) {
-      const float cb = ubp[b];
-      if (cb == 0.f || k < bk0[b] || k > bk1[b] + 1) continue;
-      const int js = md.band_start[b], je = md.band_start[b + 1];
-      int lo = js, hi = je;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (sk[mid] < k - 1) lo = mid + 1; else hi = mid;
+  //      and in sample order within a band.  Each thread owns a run of nodes and
+  //      walks the samples that reach it once per band, from one binary search
+  //      over the band's (ascending) brackets, with four sample weights in flight.
+  for (int k = kr0; k < kr1; ++k) phi[k] = 0.f;
+  for (int b = 0; b < md.n_filt; ++b) {
+    const float cb = ubp[b];
+    const int lo = max(bk0[b], kr0), hi = min(bk1[b] + 1, kr1 - 1);
+    if (cb == 0.f || lo > hi) continue;
+    const int je = md.band_start[b + 1];
+    int j = md.band_start[b], j1 = je;
+    while (j < j1) {
+      const int mid = (j + j1) >> 1;
+      if (sk[mid] < lo - 1) j = mid + 1; else j1 = mid;
+    }
+    for (; j < je && sk[j] <= hi; j += 4) {
+      int kk[4];
+      float ww[4], tt[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = j + u < je;
+        kk[u] = ok ? sk[j + u] : 0x7fffffff;
+        ww[u] = ok ? md.samp4[j + u].y : 0.f;
+        tt[u] = ok ? st[j + u] : 0.f;
       }
-      for (int j = lo; j < je && sk[j] <= k; ++j) {
-        const float c = cb * md.samp4[j].y;
-        acc += sk[j] == k ? c * (1.f - st[j]) : c * st[j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = kk[u];
+        if (k > hi) continue;   // brackets ascend: the later samples lie beyond the run too
+        const float c = cb * ww[u];
+        if (k >= lo) phi[k] += c * (1.f - tt[u]);
+        if (k + 1 >= lo && k + 1 <= hi) phi[k + 1] += c * tt[u];
       }
     }
-    phi[k] = acc * g.inv_lam2[k];
   }
+  for (int k = kr0; k < kr1; ++k) phi[k] *= g.inv_lam2[k];
   __syncthreads();
 
-  // ---- spectrum forward (thread per pixel): m_i, u_i, each pixel's node range
+  // ---- spectrum forward (thread per pixel): m_i, u_i, each pixel's node range.
+  //      A Gaussian row's range comes from the index table alone (a superset of
+  //      the nodes within 5 sigma, clamped to the window): the |u| <= 5 test
+  //      decides which nodes enter the sums.
   double l_spec = 0.0, um_spec = 0.0;
   float gz_spec = 0.f;
   const double l1 = (double)rs.ln1pz_hi + (double)rs.ln1pz_lo;
@@ -227,11 +248,11 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   for (int i = tid; i < md.n_pix; i += EB_THREADS) {
     const double xd = md.pix_ln[i] - l1;
     const float xh = (float)xd, xl = (float)(xd - (double)xh);
+    const float s = md.pix_s[i];
     float v = 0.f, dv = 0.f, cw = 0.f, tl = 0.f;
     int jlo = 1, jhi = 0;
     bool valid = false;
     if (xh >= ll0 && xh <= llN) {
-      const float s = md.pix_s[i];
       const int k = locate_ln(g, xh, g.lnl_hi);
       const float dln = (g.lnl_hi[k + 1] - g.lnl_hi[k]) + (g.lnl_lo[k + 1] - g.lnl_lo[k]);
       if (s < 0.5f * dln) {
@@ -242,8 +263,12 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         jlo = k; jhi = k + 1; tl = t; cw = 1.f;
       } else {
         const float inv_s = 1.f / s;
-        jlo = locate_ln(g, fmaxf(xh - 5.f * s, ll0), g.lnl_hi);
-        jhi = locate_ln(g, fminf(xh + 5.f * s, llN), g.lnl_hi) + 1;
+        int qa = (int)((fmaxf(xh - 5.f * s, ll0) - g.lut_x0) * g.lut_inv_h);
+        int qb = (int)((fminf(xh + 5.f * s, llN) - g.lut_x0) * g.lut_inv_h);
+        qa = min(max(qa, 0), g.lut_n - 1);
+        qb = min(max(qb, 0), g.lut_n - 1);
+        jlo = max(g.lut[qa] - 1, k_lo);
+        jhi = min(g.lut[qb] + 3, k_hi);
         float sw = 0.f, sf = 0.f, swd = 0.f, sfd = 0.f;
         for (int j = jlo; j <= jhi; ++j) {
           const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
@@ -279,38 +304,41 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     }
     if (ci == 0.f) { jlo = 1; jhi = 0; }
     prg[i] = (jlo & 0xffff) | (jhi << 16);
-    pxh[i] = xh;       // ascending in i: the pixels' wavelengths are strictly increasing
-    pxl[i] = xl;
-    pc[i] = ci;
-    pt[i] = tl;
+    px4[i] = make_float4(xh, xl, ci, tl);   // x_hi ascending in i: the pixels' wavelengths are strictly increasing
   }
   __syncthreads();
 
   // ---- dlnL/dF from the spectrum: node k gathers, in pixel order, every
   //      pixel whose node range holds k.  Those pixels lie within R of ln(lam_k)
   //      in ln(lambda) (R = 5 sigma_max for Gaussian rows, one node spacing for
-  //      linear ones), a contiguous run of the ascending pixel positions.
+  //      linear ones), a contiguous run of the ascending pixel positions found by
+  //      one binary search (neighbouring threads take neighbouring nodes, so the
+  //      searches and scans of a warp read nearby pixels).
   if (md.n_pix > 0) {
     const float R = 5.f * md.pix_s_max * 1.0001f + g.dln_max * 1.0001f + 1e-6f;
+    const int P = md.n_pix;
     for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
       const float lh = g.lnl_hi[k], ll = g.lnl_lo[k];
-      const int p0 = lower_bound_f(pxh, 0, md.n_pix, lh - R);
-      const int p1 = lower_bound_f(pxh, p0, md.n_pix, lh + R);
+      int p = 0, p1 = P;
+      while (p < p1) {
+        const int mid = (p + p1) >> 1;
+        if (px4[mid].x < lh - R) p = mid + 1; else p1 = mid;
+      }
       float acc = 0.f;
-      for (int p = p0; p < p1; ++p) {
-        const float c = pc[p];
+      for (; p < P; ++p) {
+        const float4 q = px4[p];
+        if (q.x >= lh + R) break;
         const int rg = prg[p], lo = rg & 0xffff, hi = rg >> 16;
-        if (c == 0.f || k < lo || k > hi) continue;
-        const float tl = pt[p];
+        if (q.z == 0.f || k < lo || k > hi) continue;
         float w;
-        if (tl >= 0.f) {
-          w = k == lo ? 1.f - tl : tl;
+        if (q.w >= 0.f) {
+          w = k == lo ? 1.f - q.w : q.w;
         } else {
-          const float d = (lh - pxh[p]) + (ll - pxl[p]);
-          const float u = d * -tl;
+          const float d = (lh - q.x) + (ll - q.y);
+          const float u = d * -q.w;
           w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
         }
-        acc = fmaf(c, w, acc);
+        acc = fmaf(q.z, w, acc);
       }
       phi[k] += acc;
     }
