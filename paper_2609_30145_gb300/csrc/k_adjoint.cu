@@ -250,7 +250,9 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     const float xh = (float)xd, xl = (float)(xd - (double)xh);
     const float s = md.pix_s[i];
     float v = 0.f, dv = 0.f, cw = 0.f, tl = 0.f;
-    int jlo = 1, jhi = 0;
+    // node range of the pixel; outside the grid a one-node range at the
+    // window's edge keeps the ranges in pixel order (the pixel has c = 0)
+    int jlo = xh < ll0 ? k_lo : k_hi, jhi = jlo;
     bool valid = false;
     if (xh >= ll0 && xh <= llN) {
       const int k = locate_ln(g, xh, g.lnl_hi);
@@ -302,43 +304,78 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       gz_spec += us * dv * (-rs.inv1pz);
       ci = us * cw;
     }
-    if (ci == 0.f) { jlo = 1; jhi = 0; }
     prg[i] = (jlo & 0xffff) | (jhi << 16);
     px4[i] = make_float4(xh, xl, ci, tl);   // x_hi ascending in i: the pixels' wavelengths are strictly increasing
   }
   __syncthreads();
 
   // ---- dlnL/dF from the spectrum: node k gathers, in pixel order, every
-  //      pixel whose node range holds k.  Those pixels lie within R of ln(lam_k)
-  //      in ln(lambda) (R = 5 sigma_max for Gaussian rows, one node spacing for
-  //      linear ones), a contiguous run of the ascending pixel positions found by
-  //      one binary search (neighbouring threads take neighbouring nodes, so the
-  //      searches and scans of a warp read nearby pixels).
+  //      pixel whose node range holds k.  When the ranges' ends ascend with the
+  //      pixel (the usual case: wavelengths ascend and the dispersion varies
+  //      slowly), those pixels are exactly [first p with hi_p >= k, last p with
+  //      lo_p <= k], two binary searches.  Otherwise they lie within R of
+  //      ln(lam_k) in ln(lambda) (R = 5 sigma_max for Gaussian rows, one node
+  //      spacing for linear ones), a run of the ascending pixel positions that is
+  //      tested pixel by pixel.  Neighbouring threads take neighbouring nodes, so
+  //      the searches and scans of a warp read nearby pixels.
   if (md.n_pix > 0) {
-    const float R = 5.f * md.pix_s_max * 1.0001f + g.dln_max * 1.0001f + 1e-6f;
     const int P = md.n_pix;
+    int mono = 1;
+    for (int i = tid + 1; i < P; i += EB_THREADS) {
+      const int r0 = prg[i - 1], r1 = prg[i];
+      if ((r1 & 0xffff) < (r0 & 0xffff) || (r1 >> 16) < (r0 >> 16)) mono = 0;
+    }
+    mono = __syncthreads_and(mono);
+    const float R = 5.f * md.pix_s_max * 1.0001f + g.dln_max * 1.0001f + 1e-6f;
     for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
       const float lh = g.lnl_hi[k], ll = g.lnl_lo[k];
-      int p = 0, p1 = P;
-      while (p < p1) {
-        const int mid = (p + p1) >> 1;
-        if (px4[mid].x < lh - R) p = mid + 1; else p1 = mid;
-      }
       float acc = 0.f;
-      for (; p < P; ++p) {
-        const float4 q = px4[p];
-        if (q.x >= lh + R) break;
-        const int rg = prg[p], lo = rg & 0xffff, hi = rg >> 16;
-        if (q.z == 0.f || k < lo || k > hi) continue;
-        float w;
-        if (q.w >= 0.f) {
-          w = k == lo ? 1.f - q.w : q.w;
-        } else {
-          const float d = (lh - q.x) + (ll - q.y);
-          const float u = d * -q.w;
-          w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
+      if (mono) {
+        int pa = 0, pe = P;
+        while (pa < pe) {
+          const int mid = (pa + pe) >> 1;
+          if ((prg[mid] >> 16) < k) pa = mid + 1; else pe = mid;
         }
-        acc = fmaf(q.z, w, acc);
+        int pb = pa;
+        pe = P;
+        while (pb < pe) {
+          const int mid = (pb + pe) >> 1;
+          if ((prg[mid] & 0xffff) <= k) pb = mid + 1; else pe = mid;
+        }
+        for (int p = pa; p < pb; ++p) {   // lo_p <= k <= hi_p for every p here
+          const float4 q = px4[p];
+          if (q.z == 0.f) continue;
+          float w;
+          if (q.w >= 0.f) {
+            w = k == (prg[p] & 0xffff) ? 1.f - q.w : q.w;
+          } else {
+            const float d = (lh - q.x) + (ll - q.y);
+            const float u = d * -q.w;
+            w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
+          }
+          acc = fmaf(q.z, w, acc);
+        }
+      } else {
+        int p = 0, p1 = P;
+        while (p < p1) {
+          const int mid = (p + p1) >> 1;
+          if (px4[mid].x < lh - R) p = mid + 1; else p1 = mid;
+        }
+        for (; p < P; ++p) {
+          const float4 q = px4[p];
+          if (q.x >= lh + R) break;
+          const int rg = prg[p], lo = rg & 0xffff, hi = rg >> 16;
+          if (q.z == 0.f || k < lo || k > hi) continue;
+          float w;
+          if (q.w >= 0.f) {
+            w = k == lo ? 1.f - q.w : q.w;
+          } else {
+            const float d = (lh - q.x) + (ll - q.y);
+            const float u = d * -q.w;
+            w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
+          }
+          acc = fmaf(q.z, w, acc);
+        }
       }
       phi[k] += acc;
     }

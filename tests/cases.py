@@ -9,7 +9,10 @@ import oracle
 import synth
 
 
-def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_theta=4):
+def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_theta=4, lsf_r=None,
+               spec_mask=None, sigma_gal_kms=None):
+    """lsf_r, spec_mask, sigma_gal_kms: optional replacements of the
+    workload's R_fwhm curve, pixel mask and stellar dispersion."""
     grid = grid if grid is not None else synth.make_grid(**w.grid_kw, seed=1)
     filt = filters if filters is not None else synth.pack_filters(synth.workload_filters(w))
     kw = dict(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
@@ -20,8 +23,9 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
         sp = w.spectrum
         lam, r = synth.make_spectrum_pixels(sp["n_pix"], sp["lo_um"], sp["hi_um"], sp["r_lo"], sp["r_hi"])
         kw.update(spec_lam=lam, spec_d=np.ones(lam.size), spec_sigma=np.ones(lam.size),
-                  spec_mask=np.ones(lam.size, np.uint8), lsf_mode=0, lsf_value=r,
-                  sigma_gal_kms=w.sigma_gal_kms, z_ref=w.z_ref)
+                  spec_mask=np.ones(lam.size, np.uint8) if spec_mask is None else spec_mask, lsf_mode=0,
+                  lsf_value=r if lsf_r is None else lsf_r,
+                  sigma_gal_kms=w.sigma_gal_kms if sigma_gal_kms is None else sigma_gal_kms, z_ref=w.z_ref)
     orc = oracle.Oracle(**kw)
     if with_data:
         th_true = theta_rows(w, 1, seed=99)

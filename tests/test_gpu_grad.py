@@ -113,6 +113,30 @@ def test_specphot_afe_grad_sampled_rows(ctx, prec):
     check_grad(g[rows], ref["grad"], ref["status"])
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_mixed_lsf_grad_vs_oracle(ctx, prec):
+    """A spectrum whose resolution alternates pixel by pixel between R = 40
+    (Gaussian rows several nodes wide) and R = 30000 with no stellar dispersion
+    (rows narrower than half a model log-pixel: linear interpolation), with
+    every seventh pixel masked.  The pixels' node ranges are then out of order,
+    which sends the adjoint's spectral gather down its tested-run path; every
+    row and column against the oracle's analytic gradient."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4, n_lam=1500,
+                     n_sfh=10, n_pix=240, batch=150)
+    n_pix = w.spectrum["n_pix"]
+    r = np.where(np.arange(n_pix) % 2 == 0, 40.0, 30000.0)
+    mask = (np.arange(n_pix) % 7 != 3).astype(np.uint8)
+    orc = cases.oracle_for(w, lsf_r=r, spec_mask=mask, sigma_gal_kms=0.0)
+    model = cases.gpu_model_for(ctx, orc, w)
+    th32, th64 = cases.theta_pair(w, w.batch, seed=57)
+    lnl, g, st = gpu_grad(model, th32, prec)
+    ref = orc.grad(th64)
+    assert np.array_equal(st, ref["status"])
+    check_grad(g, ref["grad"], st)
+    ok = st == 0
+    assert np.allclose(lnl[ok], orc.eval(th64)["lnl"][ok], rtol=1e-5, atol=0)
+
+
 def test_specphot_grad_vs_central_differences(ctx):
     """The adjoint against central finite differences of the FP64 oracle's
     forward model (h = 1e-7 relative) on 16 rows x all parameters."""
