@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     const float o = O2r ? Or[k] + O2r[k] : Or[k];
     const float F = attenuated(md, rs, c, eb, Yr[k] * ys, o * ys, g.neb_tab, k);
     if (spec) Fs[k] = F;
-    LG[k] = make_float2(g.lam_f[k], F * c.w);
+    LG[k] = make_float2(c.w, __fdividef(F, c.w * c.w));
   }
   __syncthreads();
 
@@ -98,21 +98,32 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     for (int b = warp; b < md.n_filt; b += EPI_WARPS) {
       const int j1 = md.band_start[b + 1];
       float acc = 0.f;
-#pragma unroll 2
-      for (int j = md.band_start[b] + lane; j < j1; j += 32) {
-        const float4 sp = md.samp4[j];     // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
-        const float x = sp.x * rs.inv1pz;
-        if (x >= lam0 && x <= lamN) {
-          int q = (int)(sp.z - qz);
+      for (int j0 = md.band_start[b] + lane; j0 < j1; j0 += 128) {
+        // four samples in flight per lane: their loads, then their table
+        // entries, then the walks
+        float4 sp[4];   // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
+        int kg[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sp[u] = j0 + 32 * u < j1 ? md.samp4[j0 + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int q = (int)(sp[u].z - qz);
           q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
-          int kc = min(max(g.lut[q], kmin), kmax);
+          kg[u] = g.lut[q];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float x = sp[u].x * rs.inv1pz;   // 0 past the band's end: below lam0
+          if (x >= lam0 && x <= lamN) {
+            int kc = min(max(kg[u], kmin), kmax);
 #pragma unroll 1
-          while (kc < kmax && LG[kc + 1].x <= x) ++kc;
+            while (kc < kmax && LG[kc + 1].x <= x) ++kc;
 #pragma unroll 1
-          while (kc > kmin && LG[kc].x > x) --kc;
-          const float2 p0 = LG[kc], p1 = LG[kc + 1];
-          const float t = __fdividef(x - p0.x, p1.x - p0.x);
-          acc = fmaf(sp.y, p0.y + t * (p1.y - p0.y), acc);
+            while (kc > kmin && LG[kc].x > x) --kc;
+            const float2 p0 = LG[kc], p1 = LG[kc + 1];
+            const float t = __fdividef(x - p0.x, p1.x - p0.x);
+            acc = fmaf(sp[u].y, p0.y + t * (p1.y - p0.y), acc);
+          }
         }
       }
 #pragma unroll

@@ -333,7 +333,7 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
     {
       const double L = g->lam[k], x = L * 350.0, dd = L * L - 2175.0 * 2175.0;
       a4[k] = make_float4(lnp[k], (float)(calzetti_kprime(L * 1e-4) / 4.05), (float)(x * x / (dd * dd + x * x) / 4.05),
-                          inv_lam2[k]);
+                          lam_f[k]);
     }
     float4* p4;
     st = upload(ctx, &p4, a4.data(), nl, &g->allocs, &g->bytes);

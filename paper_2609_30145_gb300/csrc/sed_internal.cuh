@@ -79,7 +79,7 @@ struct CosmoRow {
 struct GridDev {
   int n_age, n_feh, n_afe, n_lam;
   const float* lam_f;      // lambda (A)
-  const float4* att4;      // per node: ln(lambda/5500), k'/4.05, Drude/4.05, 1/lambda^2
+  const float4* att4;      // per node: ln(lambda/5500), k'/4.05, Drude/4.05, lambda
   const float* inv_lam2;   // 1/lambda^2
   const float* inv_dlam;   // 1/(lambda[k+1] - lambda[k]) (0 at the last node)
   const float* lnp;        // ln(lambda/5500)
