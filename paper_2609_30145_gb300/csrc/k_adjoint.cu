@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   // ---- photometry forward (warp per band, four samples in flight per lane),
   //      the sample brackets, u_b and the gather part of dlnL/dz (the sample
   //      positions lam_j/(1+z) move with z).  Brackets start from the index
-  //      table over ln(lambda) and are walked within the window.
+  //      table over ln(lambda) (fast logarithm: the walk within the window
+  //      ends on the same node from any start).
   const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
-  const float qz = rs.ln1pz_hi * g.lut_inv_h;
   const int kmin = k_lo, kmax = k_hi - 1;
   const float* lam_s = phi;
   float gz_gather = 0.f;
@@ -133,13 +133,13 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     float acc = 0.f, gzb = 0.f;
     int bmin = 0x7fffffff, bmax = -1;
     for (int j0 = js + lane; j0 < je; j0 += 128) {
-      float4 sp[4];   // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
+      float2 sp[4];   // {lambda_obs, weight}
       int kg[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) sp[u] = j0 + 32 * u < je ? md.samp4[j0 + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < 4; ++u) sp[u] = j0 + 32 * u < je ? md.samp2[j0 + 32 * u] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        int q = (int)(sp[u].z - qz);
+        int q = (int)((__logf(fmaxf(sp[u].x * rs.inv1pz, lam0)) - g.lut_x0) * g.lut_inv_h);
         q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
         kg[u] = g.lut[q];
       }
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       for (int u = 0; u < 4; ++u) {
         const bool ok = j + u < je;
         kk[u] = ok ? sk[j + u] : 0x7fffffff;
-        ww[u] = ok ? md.samp4[j + u].y : 0.f;
+        ww[u] = ok ? md.samp2[j + u].y : 0.f;
         tt[u] = ok ? st[j + u] : 0.f;
       }
 #pragma unroll

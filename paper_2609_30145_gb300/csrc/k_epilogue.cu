@@ -86,34 +86,32 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   __syncthreads();
 
   // ---- photometry, one band per warp.  Consecutive lanes take consecutive
-  //      filter samples (coalesced loads); each sample's bracket starts from
-  //      the index table over ln(lambda) (the sample's table coordinate is
-  //      precomputed, the row's ln(1+z) shifts it) and is corrected within the
-  //      row's window in shared memory.  Lane-strided sums and a fixed
-  //      shuffle tree keep the order of the band sum fixed.
+  //      filter samples (coalesced loads, eight in flight per lane); each
+  //      sample's bracket starts from the index table over ln(lambda) at the
+  //      sample's rest-frame wavelength and is corrected by a walk within the
+  //      row's window in shared memory (any start gives the same bracket, so a
+  //      fast logarithm serves).  Lane-strided sums and a fixed shuffle tree
+  //      keep the order of the band sum fixed.
   const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
   {
-    const float qz = rs.ln1pz_hi * g.lut_inv_h;
     const int kmin = k_lo, kmax = k_hi - 1;
     for (int b = warp; b < md.n_filt; b += EPI_WARPS) {
       const int j1 = md.band_start[b + 1];
       float acc = 0.f;
-      for (int j0 = md.band_start[b] + lane; j0 < j1; j0 += 128) {
-        // four samples in flight per lane: their loads, then their table
-        // entries, then the walks
-        float4 sp[4];   // {lambda_obs, weight, table coordinate of ln(lambda_obs), band}
-        int kg[4];
+      for (int j0 = md.band_start[b] + lane; j0 < j1; j0 += 256) {
+        float2 sp[8];   // {lambda_obs, weight}; past the band's end x = 0 < lam0
+        int kg[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sp[u] = j0 + 32 * u < j1 ? md.samp4[j0 + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int u = 0; u < 8; ++u) sp[u] = j0 + 32 * u < j1 ? md.samp2[j0 + 32 * u] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          int q = (int)(sp[u].z - qz);
+        for (int u = 0; u < 8; ++u) {
+          int q = (int)((__logf(fmaxf(sp[u].x * rs.inv1pz, lam0)) - g.lut_x0) * g.lut_inv_h);
           q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
           kg[u] = g.lut[q];
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float x = sp[u].x * rs.inv1pz;   // 0 past the band's end: below lam0
+        for (int u = 0; u < 8; ++u) {
+          const float x = sp[u].x * rs.inv1pz;
           if (x >= lam0 && x <= lamN) {
             int kc = min(max(kg[u], kmin), kmax);
 #pragma unroll 1

@@ -731,19 +731,10 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     float* pf;
     double* pd;
     if (!st) { st = upload(ctx, &pi, bs.data(), bs.size(), &M->allocs, &M->bytes); dv.band_start = pi; }
-    if (!st) { st = upload(ctx, &pf, sl.data(), sl.size(), &M->allocs, &M->bytes); dv.samp_lam = pf; }
-    if (!st) { st = upload(ctx, &pf, sw.data(), sw.size(), &M->allocs, &M->bytes); dv.samp_w = pf; }
-    std::vector<uint8_t> sb(S);
-    for (int b = 0; b < d->n_filt && !st; b++)
-      for (int j = bs[b]; j < bs[b + 1]; j++) sb[j] = (uint8_t)b;
-    uint8_t* pb;
-    if (!st) { st = upload(ctx, &pb, sb.data(), sb.size(), &M->allocs, &M->bytes); dv.samp_band = pb; }
-    std::vector<float4> s4(S);
-    for (int j = 0; j < S; j++)   // {lambda, weight, coordinate of ln(lambda) in the grid's index table, band}
-      s4[j] = make_float4(sl[j], sw[j], (float)((std::log((double)sl[j]) - (double)g->dv.lut_x0) * g->dv.lut_inv_h),
-                          (float)sb[j]);
-    float4* p4;
-    if (!st) { st = upload(ctx, &p4, s4.data(), s4.size(), &M->allocs, &M->bytes); dv.samp4 = p4; }
+    std::vector<float2> s2(S);
+    for (int j = 0; j < S; j++) s2[j] = make_float2(sl[j], sw[j]);
+    float2* p2;
+    if (!st) { st = upload(ctx, &p2, s2.data(), s2.size(), &M->allocs, &M->bytes); dv.samp2 = p2; }
     std::vector<double> zeros(d->n_filt, 0.0);
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_d = pd; }
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_isig = pd; }

@@ -123,10 +123,7 @@ struct ModelDev {
   // photometry (samples band-major)
   int n_filt, n_samp;
   const int* band_start;   // [n_filt + 1]
-  const float* samp_lam;   // [n_samp] observed-frame A
-  const float* samp_w;     // [n_samp] R lam dlam / Z_b
-  const uint8_t* samp_band; // [n_samp] band of each sample
-  const float4* samp4;     // [n_samp] {observed lambda, weight, (ln lambda - lut_x0) lut_inv_h, band}
+  const float2* samp2;     // [n_samp] {observed-frame lambda (A), weight R lam dlam / Z_b}
   const double* phot_d;    // [n_filt]
   const double* phot_isig; // [n_filt] 1/sigma (0 when masked out)
   const double* phot_nlog; // [n_filt] -1/2 ln(2 pi sigma^2) (0 when masked out)
