@@ -209,16 +209,14 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __shared__ float s_red8[PREP_THREADS / 32];
   __shared__ int s_nnz[PREP_THREADS / 32];
 
-  // ---- finiteness of the whole row
+  // ---- finiteness of the whole row, and the row's cosmology (one lane, in
+  //      the shadow of the row's loads)
+  __shared__ CosmoRow s_cr;
   int bad = 0;
   for (int j = tid; j < md.n_param; j += blockDim.x) bad |= !isfinite(th[j]);
+  if (tid == 0) s_cr = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]]);
   bad = __syncthreads_or(bad);
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
-
-  // ---- cosmology of the row (one lane)
-  __shared__ CosmoRow s_cr;
-  if (tid == 0) s_cr = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]]);
-  __syncthreads();
   const CosmoRow cr = s_cr;
   if (!status) status = cr.status;
   const double tmax = status ? 0.0 : (double)cr.tmax_d;
@@ -294,6 +292,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   float qpart = 0.f;
   int nnz = 0;
   float* Vs = smem + NA * NZ;           // FP8 path: W_k 2^-e_k
+#pragma unroll 4
   for (int k = tid; k < Kpad; k += blockDim.x) {
     const int code = L.k_code[k];
     float v = 0.f;
@@ -345,6 +344,42 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     }
   }
 
+  // ---- rest-frame node window the epilogue reads: the redshifted filter
+  //      samples and the spectral pixels with 5 dispersions on either side.
+  //      Lanes 0-3 of warp 0 look up its four candidate ends in the index table
+  //      over ln(lambda) (each entry lies within one node of the exact bracket);
+  //      the margins cover that slack and the interpolation's k + 1.
+  int win_lo = 0, win_hi = 0;
+  if (warp == 0) {
+    const int N = g.n_lam;
+    const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
+    int lo = N - 1, hi = 0;
+    float xl = 0.f;
+    bool use = false;
+    if (lane < 2 && md.n_filt > 0) {
+      xl = __logf(fminf(fmaxf((lane == 0 ? md.samp_lam_min : md.samp_lam_max) * cr.inv1pz, lam0), lamN));
+      use = true;
+    } else if (lane >= 2 && lane < 4 && md.n_pix > 0) {
+      const double l1 = (double)cr.ln1pz_hi + (double)cr.ln1pz_lo;
+      const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
+      xl = lane == 2 ? fminf(fmaxf((float)(md.pix_ln_min - l1) - 5.f * md.pix_s_max, ll0), llN)
+                     : fminf(fmaxf((float)(md.pix_ln_max - l1) + 5.f * md.pix_s_max, ll0), llN);
+      use = true;
+    }
+    if (use) {
+      int q = (int)((xl - g.lut_x0) * g.lut_inv_h);
+      q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
+      const int k = g.lut[q];
+      if ((lane & 1) == 0) lo = k; else hi = k;
+    }
+    for (int o = 2; o; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    win_lo = max(lo - 3, 0);
+    win_hi = min(max(hi + 4, win_lo + 1), N - 1);
+  }
+
   if (tid == 0) {
     float qy = 0.f;
     for (int w = 0; w < PREP_THREADS / 32; ++w) qy += s_red[w];
@@ -383,31 +418,12 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.status = 0;
     rs.orig = r;
     rs.y_scale = y_scale;
-    // rest-frame node window the epilogue reads: the redshifted filter samples
-    // and the spectral pixels with 5 dispersions on either side, with margins
-    {
-      const int N = g.n_lam;
-      const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
-      int lo = N - 1, hi = 0;
-      if (md.n_filt > 0) {
-        lo = min(lo, locate_lin(g, fminf(fmaxf(md.samp_lam_min * cr.inv1pz, lam0), lamN)));
-        hi = max(hi, locate_lin(g, fminf(fmaxf(md.samp_lam_max * cr.inv1pz, lam0), lamN)));
-      }
-      if (md.n_pix > 0) {
-        const double l1 = (double)cr.ln1pz_hi + (double)cr.ln1pz_lo;
-        const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
-        const float a = fminf(fmaxf((float)(md.pix_ln_min - l1) - 5.f * md.pix_s_max, ll0), llN);
-        const float b = fminf(fmaxf((float)(md.pix_ln_max - l1) + 5.f * md.pix_s_max, ll0), llN);
-        lo = min(lo, locate_ln(g, a, g.lnl_hi));
-        hi = max(hi, locate_ln(g, b, g.lnl_hi));
-      }
-      rs.k_lo = max(lo - 2, 0);
-      rs.k_hi = min(max(hi + 3, rs.k_lo + 1), N - 1);
-      if (a.tile_win) {   // union of the windows of this row's 128-row tile
-        const int mt = (a.n + 127) >> 7;
-        atomicMin(&a.tile_win[p >> 7], rs.k_lo);
-        atomicMax(&a.tile_win[mt + (p >> 7)], rs.k_hi);
-      }
+    rs.k_lo = win_lo;
+    rs.k_hi = win_hi;
+    if (a.tile_win) {   // union of the windows of this row's 128-row tile
+      const int mt = (a.n + 127) >> 7;
+      atomicMin(&a.tile_win[p >> 7], rs.k_lo);
+      atomicMax(&a.tile_win[mt + (p >> 7)], rs.k_hi);
     }
     rs.nnz = 0;
     for (int w = 0; w < PREP_THREADS / 32; ++w) rs.nnz += s_nnz[w];
