@@ -60,6 +60,7 @@ size_t epi_bwd_smem(const EpiBwdArgs& a) {
 }
 
 __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
+  pdl_enter();
   const ModelDev& md = a.md;
   const GridDev& g = a.g;
   const int r = blockIdx.x;
@@ -476,8 +477,7 @@ cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaSt
   static size_t set_for = 0;
   cudaError_t e = ensure_dyn_smem(k_epi_bwd, smem, &set_for);
   if (e != cudaSuccess) return e;
-  k_epi_bwd<<<a.n, EB_THREADS, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_epi_bwd, dim3(a.n), dim3(EB_THREADS), smem, s, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -487,6 +487,7 @@ cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaSt
 constexpr int DS_M = 128, DS_N = 64, DS_K = 8;
 
 __global__ void __launch_bounds__(256) k_dw_simt(const DwSimtArgs a) {
+  pdl_enter();
   __shared__ __align__(16) float As[DS_K][DS_M];
   __shared__ __align__(16) float Bs[DS_K][DS_N];
   const int tid = threadIdx.x;
@@ -544,8 +545,7 @@ __global__ void __launch_bounds__(256) k_dw_simt(const DwSimtArgs a) {
 
 cudaError_t launch_dw_simt(const DwSimtArgs& a, cudaStream_t s) {
   dim3 grid(a.Kpad / DS_N, (a.n + DS_M - 1) / DS_M);
-  k_dw_simt<<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_dw_simt, grid, dim3(256), 0, s, a);
 }
 
 }  // namespace sed

@@ -11,6 +11,7 @@ namespace sed {
 constexpr int SB_M = 128, SB_N = 128, SB_K = 8;
 
 __global__ void __launch_bounds__(256) k_contract_simt(const ContractArgs a) {
+  pdl_enter();
   __shared__ __align__(16) float As[SB_K][SB_M];
   __shared__ __align__(16) float Bs[SB_K][SB_N];
   const int tid = threadIdx.x;
@@ -80,8 +81,7 @@ __global__ void __launch_bounds__(256) k_contract_simt(const ContractArgs a) {
 
 cudaError_t launch_contract_simt(const ContractArgs& a, cudaStream_t s) {
   dim3 grid((a.ldn + SB_N - 1) / SB_N, (a.n + SB_M - 1) / SB_M);
-  k_contract_simt<<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_contract_simt, grid, dim3(256), 0, s, a);
 }
 
 }  // namespace sed

@@ -211,6 +211,7 @@ __device__ __forceinline__ void unit_ranges(const Params& p, int z, int nz, int 
 
 template <int PREC, int BN, int STAGES, int G, bool GRAD>
 __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ Params p) {
+  pdl_enter();
   using C = Cfg<PREC, BN, STAGES, G, GRAD>;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bars[2 * STAGES + 4];
@@ -464,13 +465,8 @@ cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  if (!GRAD && p.tile_win) {
-    k<<<dim3(n_sm, 1, 1), C::THREADS, C::SMEM, s>>>(p);   // persistent: one CTA per SM
-  } else {
-    dim3 grid(n_cols / BN, (p.n + BM - 1) / BM, nz);
-    k<<<grid, C::THREADS, C::SMEM, s>>>(p);
-  }
-  return cudaGetLastError();
+  if (!GRAD && p.tile_win) return launch_pdl(k, dim3(n_sm, 1, 1), dim3(C::THREADS), C::SMEM, s, p);   // persistent: one CTA per SM
+  return launch_pdl(k, dim3(n_cols / BN, (p.n + BM - 1) / BM, nz), dim3(C::THREADS), C::SMEM, s, p);
 }
 
 }  // namespace tc

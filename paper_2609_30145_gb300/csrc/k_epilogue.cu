@@ -37,6 +37,7 @@ size_t epilogue_smem(const EpiArgs& a) {
 // otherwise every row reads the model in the kernel parameters.
 template <bool MULTI>
 __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_constant__ EpiArgs a) {
+  pdl_enter();
   const int r = blockIdx.x;
   const ModelDev& md = MULTI ? a.mtab[a.row_model[a.rs[r].orig]] : a.md;
   const GridDev& g = a.g;
@@ -209,9 +210,8 @@ cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
   cudaError_t e = m ? ensure_dyn_smem(k_epilogue<true>, smem, &set_for[1])
                     : ensure_dyn_smem(k_epilogue<false>, smem, &set_for[0]);
   if (e != cudaSuccess) return e;
-  if (m) k_epilogue<true><<<a.n, EPI_THREADS, smem, s>>>(a);
-  else k_epilogue<false><<<a.n, EPI_THREADS, smem, s>>>(a);
-  return cudaGetLastError();
+  return m ? launch_pdl(k_epilogue<true>, dim3(a.n), dim3(EPI_THREADS), smem, s, a)
+           : launch_pdl(k_epilogue<false>, dim3(a.n), dim3(EPI_THREADS), smem, s, a);
 }
 
 }  // namespace sed

@@ -129,6 +129,7 @@ constexpr int ORDER_BINS = 1024;
 
 __global__ void __launch_bounds__(ORDER_THREADS) k_order(const float* theta, int n, int ld, int zoff, float zf,
                                                          float scale, int* perm) {
+  pdl_enter();
   __shared__ int cnt[ORDER_BINS + 1];
   __shared__ int wsum[ORDER_THREADS / 32];
   const int base = blockIdx.x * ORDER_CHUNK;
@@ -188,6 +189,7 @@ constexpr int PREP_THREADS = 128;
 // RowScal::orig; every later kernel indexes by p and writes results to r.
 template <bool MULTI>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepKernelArgs ka) {
+  pdl_enter();
   const PrepArgs& a = ka.p;
   const int p = blockIdx.x;
   const int r = a.perm ? a.perm[p] : p;
@@ -440,6 +442,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
 constexpr int PREP_BWD_THREADS = 128;
 
 __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_constant__ PrepBwdArgs a) {
+  pdl_enter();
   const ModelDev& md = a.md;
   const GridDev& g = a.g;
   const LayoutDev& L = a.L;
@@ -596,16 +599,17 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
 
 cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
   const size_t smem = (size_t)2 * p.g.n_age * p.g.n_feh * sizeof(float);
-  k_prep_bwd<<<p.n, PREP_BWD_THREADS, smem, s>>>(p);
-  return cudaGetLastError();
+  static size_t set_for = 0;
+  const cudaError_t e = ensure_dyn_smem(k_prep_bwd, smem, &set_for);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_prep_bwd, dim3(p.n), dim3(PREP_BWD_THREADS), smem, s, p);
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (p.perm && !p.row_model) {
-    k_order<<<(p.n + ORDER_CHUNK - 1) / ORDER_CHUNK, ORDER_THREADS, 0, s>>>(
-        p.theta, p.n, p.ld, p.md.offs[SED_KEY_ZRED], (float)p.md.zf, (float)(ORDER_BINS / p.md.zf), p.perm);
-    e = cudaGetLastError();
+    e = launch_pdl(k_order, dim3((p.n + ORDER_CHUNK - 1) / ORDER_CHUNK), dim3(ORDER_THREADS), 0, s, p.theta, p.n, p.ld,
+                   p.md.offs[SED_KEY_ZRED], (float)p.md.zf, (float)(ORDER_BINS / p.md.zf), p.perm);
     if (e != cudaSuccess) return e;
   }
   PrepKernelArgs ka;
@@ -614,9 +618,8 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   static size_t set_for[2] = {0, 0};
   e = p.row_model ? ensure_dyn_smem(k_prep<true>, smem, &set_for[1]) : ensure_dyn_smem(k_prep<false>, smem, &set_for[0]);
   if (e != cudaSuccess) return e;
-  if (p.row_model) k_prep<true><<<p.n, PREP_THREADS, smem, s>>>(ka);
-  else k_prep<false><<<p.n, PREP_THREADS, smem, s>>>(ka);
-  return cudaGetLastError();
+  return p.row_model ? launch_pdl(k_prep<true>, dim3(p.n), dim3(PREP_THREADS), smem, s, ka)
+                     : launch_pdl(k_prep<false>, dim3(p.n), dim3(PREP_THREADS), smem, s, ka);
 }
 
 }  // namespace sed

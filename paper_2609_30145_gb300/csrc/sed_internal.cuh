@@ -1,5 +1,6 @@
 // Internal declarations of the GB300 SED library (not part of the ABI).
 #pragma once
+#include <utility>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -293,6 +294,37 @@ struct PrepArgs {
   int* tile_win;       // [2][ceil(n/128)] union of the row windows of each 128-row tile (lo set to
                        // 0x7f7f7f7f and hi to -1 beforehand), or NULL
 };
+// Programmatic dependent launch.  Every kernel of the library begins with
+// pdl_enter(): it waits until the kernel before it on the stream has completed
+// and its writes are visible, then lets the next kernel be scheduled.  Launched
+// directly on a stream, a kernel carries programmatic stream serialisation, so
+// its launch and scheduling overlap the previous kernel's work; results are
+// those of plain stream order.  Under stream capture the attribute is left off:
+// a graph replay already launches back to back, and measured slower with it.
+// Without the attribute the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
+  cfg.attrs = at;
+  cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Raises a kernel's dynamic shared-memory limit once its static plus dynamic
 // shared memory passes the 48 KB default; *done caches the largest size set.
 // cudaErrorInvalidConfiguration if the total passes the 227 KB a CTA can have.
