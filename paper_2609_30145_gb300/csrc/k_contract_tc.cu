@@ -182,10 +182,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 //    exits at once when the tile lies outside the union of its rows' windows.
 //  - Persistent schedule (forward, p.tile_win set): one CTA per SM; every CTA
 //    enumerates the computed units from the per-M-tile windows written by the
-//    preparation kernel -- split kind outermost (old halves first, young last),
-//    then M tile, then the wavelength tiles of the window -- and takes every
-//    gridDim.x-th one.  Tensor memory, barriers and the smem ring are set up
-//    once, and one unit's drain overlaps the next unit's MMAs.
+//    preparation kernel and takes every gridDim.x-th one.  Per split kind the
+//    tiles (M tile, then the wavelength tiles of its window) are cut into full
+//    waves -- the largest multiple of gridDim.x, run as whole units, kind by
+//    kind (old halves first, young last), so every CTA takes the same number
+//    of units of each kind -- and a remainder whose tiles are split along the
+//    wavelength axis into up to four pieces of BN/npc columns (an MMA of N =
+//    BN/npc), so the last partial wave costs a fraction of a unit.  Tensor
+//    memory, barriers and the smem ring are set up once, and one unit's drain
+//    overlaps the next unit's MMAs.
 constexpr int MAX_MT = 64;   // M tiles of a persistent launch (8192 rows)
 
 struct Unit {
@@ -224,6 +229,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   const int nz = (!GRAD && p.O2) ? 3 : 1;
   int K0 = 0, KY = p.ky_tiles, KT = p.k_tiles;
   int n_units = 1, upz = 0;
+  int nfull = 0, nrem = 0, npc = 1;   // persistent: tiles per kind in full waves, leftover tiles, pieces per leftover tile
 
   if (persistent) {
     // computed wavelength tiles of each M tile, and their prefix counts
@@ -245,8 +251,19 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     }
     __syncthreads();
     upz = s_pref[MT];
-    const int total = upz * nz;
-    n_units = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // per split kind, the largest multiple of gridDim.x tiles runs as whole
+    // units (every CTA then takes the same number of units of each kind); the
+    // leftover tiles are cut along the wavelength axis into npc pieces of BN/npc
+    // columns so that the last partial wave spreads over the CTAs.  npc is 1, 2
+    // or 4 (BN/npc stays a multiple of 16: a valid MMA N and 16-byte aligned
+    // output columns)
+    const int G = (int)gridDim.x;
+    nfull = (upz / G) * G;
+    nrem = upz - nfull;
+    const int fit = nrem > 0 ? G / (nz * nrem) : 1;
+    npc = (fit >= 4 && BN / 4 >= 16) ? 4 : (fit >= 2 && BN / 2 >= 16 ? 2 : 1);
+    const int total = nz * nfull + nz * nrem * npc;
+    n_units = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
   } else if (p.rs) {
     // grid schedule: union of the rest-frame node windows of the tile's rows
     // (invalid rows have none).  Forward: a wavelength tile outside it is never
@@ -275,19 +292,28 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   // unit j of this CTA
   auto get_unit = [&](int j, Unit& u) {
     int z = GRAD ? 0 : (int)blockIdx.z;
+    u.ncol = BN;
     if (persistent) {
       const int idx = (int)blockIdx.x + j * (int)gridDim.x;
-      z = idx / upz;
-      const int rem = idx - z * upz;
+      int t, pc = 0;
+      if (idx < nz * nfull) {
+        z = idx / nfull;
+        t = idx - z * nfull;
+      } else {
+        const int q = idx - nz * nfull, rest = q / npc;
+        pc = q - rest * npc;
+        z = rest / nrem;
+        t = nfull + rest - z * nrem;
+      }
       int m = 0;
-      while (s_pref[m + 1] <= rem) ++m;
+      while (s_pref[m + 1] <= t) ++m;
       u.m0 = m * BM;
-      u.n0 = (s_nlo[m] + rem - s_pref[m]) * BN;
+      if (t >= nfull) u.ncol = BN / npc;   // a piece of a leftover tile
+      u.n0 = (s_nlo[m] + t - s_pref[m]) * BN + pc * u.ncol;
     } else {
       u.m0 = blockIdx.y * BM;
       u.n0 = blockIdx.x * BN;
     }
-    u.ncol = BN;
     if constexpr (GRAD) {
       const int t = (int)blockIdx.x;
       u.n0 = t < p.ny_tiles ? t * BN : p.n_split + (t - p.ny_tiles) * BN;
@@ -356,12 +382,13 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      constexpr uint32_t ID = idesc(PREC == SED_PREC_FP32 ? 2u : (PREC == SED_PREC_FP8 ? 0u : 1u), BM, BN);
+      constexpr uint32_t FMT = PREC == SED_PREC_FP32 ? 2u : (PREC == SED_PREC_FP8 ? 0u : 1u);
       int g = 0, it = 0;
       bool ok = true;
       for (int j = 0; j < n_units && ok; ++j) {
         Unit u;
         get_unit(j, u);
+        const uint32_t ID = idesc(FMT, BM, (uint32_t)u.ncol);   // N = the unit's columns
         for (int r = 0; r < u.nr && ok; ++r) {
           const int kb = u.rb[r], ke = u.re[r];
           for (int gs = kb; gs < ke && ok; gs += G, ++g) {
@@ -420,6 +447,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
           if (ok) {
 #pragma unroll
             for (int c = 0; c < BN / 32; ++c) {
+              if (c * 32 >= u.ncol) break;
               uint32_t rr[32];
               tmem_ld32(tmem + lane_off + (uint32_t)(b * BN + c * 32), rr);
               tmem_wait_ld();

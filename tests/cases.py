@@ -78,3 +78,16 @@ def rel_err(a, b, floor=0.0):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return np.abs(a - b) / np.maximum(np.abs(b), floor)
+
+
+def poison_rows(model, th32):
+    """Rows that fill a call's workspace with other values: the same rows with
+    their SFH mass fractions reversed in bin order (other weights, other
+    contraction outputs, same redshifts).  A call on these just before the call
+    under test leaves stale values of other rows in any output element the
+    tested call would fail to write."""
+    th = th32.copy()
+    a = model.offsets["sfh"]
+    b = model.offsets["logzsol"]
+    th[:, a:b] = th32[:, a:b][:, ::-1]
+    return th

@@ -53,6 +53,10 @@ def gpu_grad(model, th32, prec, ld=None):
     n = th32.shape[0]
     ld = ld or th32.shape[1]
     t = torch.zeros((n, ld), dtype=torch.float32, device="cuda")
+    # first a call on other rows of the same size (stale values in the workspace
+    # must not stand in for outputs the tested call fails to write)
+    t[:, :th32.shape[1]] = torch.from_numpy(cases.poison_rows(model, th32)).cuda()
+    model.loglike_grad(t, prec)
     t[:, :th32.shape[1]] = torch.from_numpy(th32).cuda()
     lnl, g, st = model.loglike_grad(t, prec)
     torch.cuda.synchronize()
