@@ -99,7 +99,8 @@ enum {
   SED_KEY_DIFFUSE_INDEX = 8,  /* diffuse slope delta (power-law index or KC13 delta) */
   SED_KEY_GAS_LOGZ = 9,       /* log10 Z_gas/Zsun (used when use_nebular) */
   SED_KEY_GAS_LOGU = 10,      /* log10 U (used when use_nebular) */
-  SED_NKEYS = 11
+  SED_KEY_SIGMA_GAL = 11,     /* stellar velocity dispersion, km/s (a column only when sample_sigma_gal) */
+  SED_NKEYS = 12
 };
 
 typedef struct sed_ctx sed_ctx;
@@ -153,6 +154,13 @@ typedef struct {
   const double *lsf_value;    /* [n_pix] value in the unit of lsf_mode */
   double sigma_gal_kms;       /* fixed stellar dispersion folded into the LSF kernel */
   double z_ref;               /* reference redshift of the projector (Eq. app_sigeff) */
+  /* Sampled stellar dispersion (Sec. 2.7 kinematics; App. E): with
+   * sample_sigma_gal = 1 each parameter row carries sigma_gal (km/s) in column
+   * offsets[SED_KEY_SIGMA_GAL] instead of the fixed sigma_gal_kms; a row whose
+   * value lies outside [0, sigma_gal_max_kms] gets SED_ROW_BAD_THETA.  The
+   * maximum bounds the spectral kernels' reach (shared-memory window sizes). */
+  int sample_sigma_gal;
+  double sigma_gal_max_kms;
 } sed_model_desc;
 
 /* Context on one CUDA device; hbm_budget_bytes = 0 means no limit. */

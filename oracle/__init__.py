@@ -54,7 +54,8 @@ class _Model(C.Structure):
                 ("phot_mask", C.c_void_p), ("n_pix", C.c_int), ("spec_lam", C.c_void_p),
                 ("spec_d", C.c_void_p), ("spec_sigma", C.c_void_p), ("spec_mask", C.c_void_p),
                 ("lsf_mode", C.c_int), ("lsf_value", C.c_void_p),
-                ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double)]
+                ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
+                ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double)]
 
 
 def _load():
@@ -70,7 +71,7 @@ def _load():
         lib.orc_q.argtypes = [P, P]
         lib.orc_dust_tau.argtypes = [C.c_int, P, C.c_int, C.c_double, C.c_double, P]
         lib.orc_photometry.argtypes = [P, P, C.c_int, C.c_double, P, P]
-        lib.orc_spectrum.argtypes = [P, P, P, C.c_int, C.c_double, P, P, P]
+        lib.orc_spectrum.argtypes = [P, P, P, C.c_int, C.c_double, C.c_double, P, P, P]
         lib.orc_row.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_row.restype = C.c_int
         lib.orc_eval.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P, C.c_int]
@@ -116,6 +117,8 @@ class Oracle:
     lsf_value: np.ndarray | None = None
     sigma_gal_kms: float = 0.0
     z_ref: float = 0.0
+    sample_sigma_gal: int = 0           # 1: sigma_gal (km/s) is the last parameter column
+    sigma_gal_max_kms: float = 1000.0   # sampled sigma_gal must lie in [0, this]
     H0: float = PHYS["H0"]
     Om0: float = PHYS["Om0"]
     bc_edge_log_age_yr: float = PHYS["bc_edge_log_age_yr"]
@@ -175,6 +178,7 @@ class Oracle:
             m.lsf_mode = self.lsf_mode
             m.lsf_value = _p(k(self.lsf_value))
             m.sigma_gal_kms, m.z_ref = self.sigma_gal_kms, self.z_ref
+        m.sample_sigma_gal, m.sigma_gal_max_kms = int(self.sample_sigma_gal), float(self.sigma_gal_max_kms)
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
@@ -245,12 +249,15 @@ class Oracle:
                                  _p(fnu_obs), _p(out))
         return out
 
-    def spectrum(self, lam_rest, fnu_obs, z):
+    def spectrum(self, lam_rest, fnu_obs, z, sigma_gal_kms=None):
+        """App. E projection of an observer-frame F_nu sampled at rest-frame
+        lam_rest onto the pixels; sigma_gal defaults to the model's fixed value."""
         lam_rest, fnu_obs = _f64(lam_rest), _f64(fnu_obs)
         out = np.zeros(self.n_pix)
         valid = np.zeros(self.n_pix, dtype=np.uint8)
+        sg = self.sigma_gal_kms if sigma_gal_kms is None else sigma_gal_kms
         self._lib.orc_spectrum(C.byref(self._g), C.byref(self._m), _p(lam_rest), lam_rest.size,
-                               float(z), _p(fnu_obs), _p(out), _p(valid))
+                               float(z), float(sg), _p(fnu_obs), _p(out), _p(valid))
         return out, valid
 
     def grad(self, theta, nthreads=0):
@@ -295,15 +302,15 @@ def dust_tau(law, lam, tau, index):
     return out
 
 
-def pack_theta(d, n_sfh, zmode):
+def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0):
     """Parameter rows in the oracle's layout: sfh[N_T], logzsol[N_T or 1], then
     afe, logmass, zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index,
-    gas_logz, gas_logu."""
+    gas_logz, gas_logu, and sigma_gal when the model samples it."""
     nz = n_sfh if zmode == 0 else 1
     n = d["sfh"].shape[0]
     cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh),
             np.asarray(d["logzsol"], dtype=np.float64).reshape(n, nz)]
     for k in ("afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
-              "diffuse_dust_index", "gas_logz", "gas_logu"):
+              "diffuse_dust_index", "gas_logz", "gas_logu") + (("sigma_gal",) if sample_sigma_gal else ()):
         cols.append(np.asarray(d[k], dtype=np.float64).reshape(n, 1))
     return np.ascontiguousarray(np.concatenate(cols, axis=1))

@@ -117,14 +117,15 @@ static void bracket(const double *x, int n, double v, int *j0, double *w0, int *
 }
 
 int orc_n_param(const orc_model *md) {
-  return md->n_sfh + (md->zmode == 0 ? md->n_sfh : 1) + 9;
+  return md->n_sfh + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0);
 }
 
 /* parameter row decoding (layout: sfh[N_T], logzsol[N_T or 1], afe, logmass,
- * zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index, gas_logz, gas_logu) */
+ * zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index, gas_logz, gas_logu,
+ * then sigma_gal when the model samples it) */
 typedef struct {
   const double *m, *zeta;
-  double afe, logmass, z, tau_bc, alpha_bc, tau_d, delta, gas_logz, gas_logu;
+  double afe, logmass, z, tau_bc, alpha_bc, tau_d, delta, gas_logz, gas_logu, sigma_gal;
 } orc_theta;
 
 static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
@@ -134,6 +135,7 @@ static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
   o->zeta = th + md->n_sfh;
   o->afe = s[0]; o->logmass = s[1]; o->z = s[2]; o->tau_bc = s[3]; o->alpha_bc = s[4];
   o->tau_d = s[5]; o->delta = s[6]; o->gas_logz = s[7]; o->gas_logu = s[8];
+  o->sigma_gal = md->sample_sigma_gal ? s[9] : md->sigma_gal_kms;
 }
 
 static int theta_status(const orc_model *md, const double *th, double *tmax_out, double *cos_out) {
@@ -142,6 +144,7 @@ static int theta_status(const orc_model *md, const double *th, double *tmax_out,
     if (!isfinite(th[j])) return ORC_BAD_THETA;
   orc_theta t;
   decode_theta(md, th, &t);
+  if (md->sample_sigma_gal && !(t.sigma_gal >= 0.0 && t.sigma_gal <= md->sigma_gal_max_kms)) return ORC_BAD_THETA;
   if (t.z < 0.0 || t.z >= md->zf) return ORC_BAD_Z;
   double cz[3], cf[3];
   orc_cosmology(md->H0, md->Om0, t.z, cz);
@@ -324,9 +327,10 @@ static double sigma_inst_kms(int mode, double v, double lam_obs) {
 }
 
 /* Per-pixel total dispersion in ln(lam): Eq. "app_sigeff" (fixed part at the
- * projector's reference redshift) composed in quadrature with a fixed
- * sigma_gal (Eq. "one_kernel"). */
-static void spec_widths(const orc_grid *g, const orc_model *md, double *s_ln) {
+ * projector's reference redshift) composed in quadrature with the row's
+ * sigma_gal (Eq. "one_kernel"; the paper's Fourier stage for sigma_gal and the
+ * banded sigma_fix response compose to this one Gaussian, App. E). */
+static void spec_widths(const orc_grid *g, const orc_model *md, double sigma_gal_kms, double *s_ln) {
   double *sl = (double *)malloc(g->n_lam * sizeof(double));
   siglib_nodes(g, sl);
   for (int i = 0; i < md->n_pix; i++) {
@@ -342,7 +346,7 @@ static void spec_widths(const orc_grid *g, const orc_model *md, double *s_ln) {
     }
     double fix2 = si * si - slib * slib;
     if (fix2 < 0.0) fix2 = 0.0;
-    s_ln[i] = sqrt(fix2 + md->sigma_gal_kms * md->sigma_gal_kms) / O_C_KMS;
+    s_ln[i] = sqrt(fix2 + sigma_gal_kms * sigma_gal_kms) / O_C_KMS;
   }
   free(sl);
 }
@@ -351,10 +355,10 @@ static void spec_widths(const orc_grid *g, const orc_model *md, double *s_ln) {
  * by ln(1+z), truncated at five dispersions, normalised to unit sum; rows
  * narrower than half a model log-pixel are linear interpolation in ln(lam). */
 void orc_spectrum(const orc_grid *g, const orc_model *md, const double *lam_rest, int n_lam,
-                  double z, const double *fnu_obs, double *pix, unsigned char *valid) {
+                  double z, double sigma_gal_kms, const double *fnu_obs, double *pix, unsigned char *valid) {
   double *s_ln = (double *)malloc(md->n_pix * sizeof(double));
   double *ll = (double *)malloc(n_lam * sizeof(double));
-  spec_widths(g, md, s_ln);
+  spec_widths(g, md, sigma_gal_kms, s_ln);
   for (int k = 0; k < n_lam; k++) ll[k] = log(lam_rest[k]);
   double lz = log(1.0 + z);
   for (int i = 0; i < md->n_pix; i++) {
@@ -467,7 +471,7 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
       }
     }
     if (md->n_pix > 0) {
-      orc_spectrum(g, md, g->lam, NL, t.z, fnu, sp, vd);
+      orc_spectrum(g, md, g->lam, NL, t.z, t.sigma_gal, fnu, sp, vd);
       for (int i = 0; i < md->n_pix; i++) {
         if (spec) spec[i] = sp[i];
         if (md->spec_d && vd[i] && (!md->spec_mask || md->spec_mask[i])) {
@@ -657,7 +661,7 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
   for (int k = 0; k < NL; k++) fnu[k] = scale * F[k];
 
   /* ---------------- likelihood and its derivative with respect to the model */
-  double L = 0.0, gscale = 0.0, gz = 0.0;
+  double L = 0.0, gscale = 0.0, gz = 0.0, g_sgal = 0.0;
   if (md->n_filt > 0) {
     double *ph = (double *)malloc(md->n_filt * sizeof(double));
     orc_photometry(md, g->lam, NL, t.z, fnu, ph);
@@ -713,8 +717,8 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     unsigned char *vd = (unsigned char *)malloc(md->n_pix);
     double *s_ln = (double *)malloc(md->n_pix * sizeof(double));
     double *ll = (double *)malloc(NL * sizeof(double));
-    orc_spectrum(g, md, g->lam, NL, t.z, fnu, sp, vd);
-    spec_widths(g, md, s_ln);
+    orc_spectrum(g, md, g->lam, NL, t.z, t.sigma_gal, fnu, sp, vd);
+    spec_widths(g, md, t.sigma_gal, s_ln);
     for (int k = 0; k < NL; k++) ll[k] = log(g->lam[k]);
     double lz = log(zp);
     for (int i = 0; i < md->n_pix; i++) {
@@ -734,13 +738,17 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
         gz += ui * (fnu[k + 1] - fnu[k]) / dln * (-1.0 / zp);
         continue;
       }
-      double sw = 0.0, sf = 0.0, swd = 0.0, sfd = 0.0;
+      double sw = 0.0, sf = 0.0, swd = 0.0, sfd = 0.0, sws = 0.0, sfs = 0.0;
       for (int j = 0; j < NL; j++) {
         double u = (ll[j] - x) / sg;
         if (fabs(u) > 5.0) continue;
         double w = exp(-0.5 * u * u), wd = w * u / sg; /* d w / d x */
-        sw += w; sf += w * fnu[j]; swd += wd; sfd += wd * fnu[j];
+        double ws = w * u * u / sg;                     /* d w / d s */
+        sw += w; sf += w * fnu[j]; swd += wd; sfd += wd * fnu[j]; sws += ws; sfs += ws * fnu[j];
       }
+      /* width of the row: s = sqrt(sigma_fix^2 + sigma_gal^2) / c, so
+       * ds/dsigma_gal = sigma_gal / (c^2 s) */
+      g_sgal += ui * (sfs * sw - sf * sws) / (sw * sw) * t.sigma_gal / (O_C_KMS * O_C_KMS * sg);
       for (int j = 0; j < NL; j++) {
         double u = (ll[j] - x) / sg;
         if (fabs(u) > 5.0) continue;
@@ -846,6 +854,7 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     grad[offs + 6] = g_delta;
     grad[offs + 7] = has_neb ? g_lz : 0.0;
     grad[offs + 8] = has_neb ? g_lu : 0.0;
+    if (md->sample_sigma_gal) grad[offs + 9] = g_sgal;
     free(gT); free(gY); free(gO);
   }
   if (st) for (int j = 0; j < np; j++) grad[j] = 0.0;

@@ -56,11 +56,13 @@ typedef struct {
   const unsigned char *spec_mask;
   int lsf_mode;                /* 0 R_fwhm, 1 R_sigma, 2 fwhm_aa, 3 sigma_aa, 4 sigma_kms, 5 fwhm_kms */
   const double *lsf_value;     /* [n_pix] */
-  double sigma_gal_kms, z_ref;
+  double sigma_gal_kms, z_ref;  /* fixed stellar dispersion (when not sampled), projector redshift */
+  int sample_sigma_gal;        /* 1: sigma_gal (km/s) is a parameter column (Sec. 2.7 kinematics) */
+  double sigma_gal_max_kms;    /* sampled sigma_gal must lie in [0, this] */
 } orc_model;
 
 /* Row status bits (shared meaning with the library by documentation only). */
-#define ORC_BAD_THETA 1   /* non-finite parameter */
+#define ORC_BAD_THETA 1   /* non-finite parameter, or a sampled sigma_gal outside [0, max] */
 #define ORC_BAD_Z 2       /* z < 0 or z >= zf */
 #define ORC_BAD_TMAX 4    /* oldest edge not older than 10 Myr */
 #define ORC_NONFINITE 16  /* non-finite model or likelihood */
@@ -89,7 +91,7 @@ void orc_photometry(const orc_model *md, const double *lam_rest, int n_lam, doub
 
 /* Spectral projection; valid[i] = 0 where the pixel has no model node. */
 void orc_spectrum(const orc_grid *g, const orc_model *md, const double *lam_rest, int n_lam,
-                  double z, const double *fnu_obs, double *pix, unsigned char *valid);
+                  double z, double sigma_gal_kms, const double *fnu_obs, double *pix, unsigned char *valid);
 
 /* Per-row intermediates: Y, O (young / old sums), F (attenuated rest-frame),
  * fnu (observer frame, cgs) each [n_lam]; scal[0..5] = D_L cm, t_univ yr,

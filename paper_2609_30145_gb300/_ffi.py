@@ -19,7 +19,7 @@ DUST_POWER_LAW, DUST_KC13 = 0, 1
 LSF_R_FWHM, LSF_R_SIGMA, LSF_FWHM_AA, LSF_SIGMA_AA, LSF_SIGMA_KMS, LSF_FWHM_KMS = range(6)
 ROW_BAD_THETA, ROW_BAD_Z, ROW_BAD_TMAX, ROW_NONFINITE, ROW_DEVICE_TIMEOUT = 1, 2, 4, 16, 32
 KEYS = ("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
-        "diffuse_dust_index", "gas_logz", "gas_logu")
+        "diffuse_dust_index", "gas_logz", "gas_logu", "sigma_gal")
 NKEYS = len(KEYS)
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -41,7 +41,8 @@ class ModelDesc(C.Structure):
                 ("phot_d", P), ("phot_sigma", P), ("phot_mask", P),
                 ("n_pix", C.c_int), ("spec_lam_aa", P), ("spec_d", P), ("spec_sigma", P),
                 ("spec_mask", P), ("lsf_mode", C.c_int), ("lsf_value", P),
-                ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double)]
+                ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
+                ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double)]
 
 
 class StageStats(C.Structure):

@@ -106,7 +106,7 @@ class Context:
                      bc_edge_log_age_yr=7.03, H0=67.66, Om0=0.3097, filters=None,
                      phot_d=None, phot_sigma=None, phot_mask=None, spec_lam=None, spec_d=None,
                      spec_sigma=None, spec_mask=None, lsf_mode=0, lsf_value=None,
-                     sigma_gal_kms=0.0, z_ref=0.0) -> "Model":
+                     sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0) -> "Model":
         d = _ffi.ModelDesc()
         d.grid, d.n_sfh, d.zf, d.zmode = grid_id, n_sfh, zf, zmode
         d.use_afe, d.use_nebular, d.dust_law = use_afe, use_nebular, dust_law
@@ -131,6 +131,7 @@ class Context:
             d.spec_lam_aa, d.spec_d, d.spec_sigma, d.spec_mask = _ptr(sl), _ptr(sd), _ptr(ss), _ptr(sm)
             d.lsf_mode, d.lsf_value = lsf_mode, _ptr(lv)
             d.sigma_gal_kms, d.z_ref = sigma_gal_kms, z_ref
+        d.sample_sigma_gal, d.sigma_gal_max_kms = int(sample_sigma_gal), float(sigma_gal_max_kms)
         mid = C.c_int32()
         self._check(self._lib.sed_create_model(self._h, C.byref(d), C.byref(mid)))
         return Model(self, mid.value, n_filt=d.n_filt, n_pix=d.n_pix)
@@ -154,6 +155,8 @@ class Model:
         bounds = list(self.offsets.values()) + [self.n_param]
         for i, k in enumerate(KEYS):
             w = bounds[i + 1] - bounds[i]
+            if w == 0:      # key without a column in this model (e.g. a fixed sigma_gal)
+                continue
             out[:, bounds[i]:bounds[i] + w] = np.asarray(d[k], dtype=np.float64).reshape(n, w)
         return out.astype(dtype)
 

@@ -97,7 +97,9 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   int* sk = reinterpret_cast<int*>(U);
   float* st = reinterpret_cast<float*>(sk + md.n_samp);
   // per pixel {x_hi, x_lo, c, t}: position ln(lambda_obs/(1+z)) in two floats, its
-  // weight in dlnL/dF and the linear-kernel weight t >= 0, or -1/sigma for a Gaussian row
+  // weight in dlnL/dF, and for a linear row its weight t (within rounding of
+  // [0, 1]; a pixel on a node can give t = -1e-9) or for a Gaussian row
+  // -1 - 1/sigma (below -1): the two never meet, whatever the rounding
   float4* px4 = reinterpret_cast<float4*>(U);
   int* prg = reinterpret_cast<int*>(px4 + md.n_pix);   // node range lo | hi << 16
   // each thread owns a contiguous run of CH window nodes (CH odd: the runs of a
@@ -243,14 +245,15 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   //      the nodes within 5 sigma, clamped to the window): the |u| <= 5 test
   //      decides which nodes enter the sums.
   double l_spec = 0.0, um_spec = 0.0;
-  float gz_spec = 0.f;
+  float gz_spec = 0.f, g_sgal = 0.f;
   const double l1 = (double)rs.ln1pz_hi + (double)rs.ln1pz_lo;
   const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
   for (int i = tid; i < md.n_pix; i += EB_THREADS) {
     const double xd = md.pix_ln[i] - l1;
     const float xh = (float)xd, xl = (float)(xd - (double)xh);
-    const float s = md.pix_s[i];
-    float v = 0.f, dv = 0.f, cw = 0.f, tl = 0.f;
+    // total dispersion: fixed, or sigma_fix composed with the row's sigma_gal (Eq. one_kernel)
+    const float s = md.sample_sgal ? sqrtf(md.pix_fix2[i] + rs.sg_ln * rs.sg_ln) : md.pix_s[i];
+    float v = 0.f, dv = 0.f, dvs = 0.f, cw = 0.f, tl = 0.f;
     // node range of the pixel; outside the grid a one-node range at the
     // window's edge keeps the ranges in pixel order (the pixel has c = 0)
     int jlo = xh < ll0 ? k_lo : k_hi, jhi = jlo;
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         qb = min(max(qb, 0), g.lut_n - 1);
         jlo = max(g.lut[qa] - 1, k_lo);
         jhi = min(g.lut[qb] + 3, k_hi);
-        float sw = 0.f, sf = 0.f, swd = 0.f, sfd = 0.f;
+        float sw = 0.f, sf = 0.f, swd = 0.f, sfd = 0.f, sws = 0.f, sfs = 0.f;
         for (int j = jlo; j <= jhi; ++j) {
           const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
           const float u = d * inv_s;
@@ -283,12 +286,18 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
             sf = fmaf(w, Fs[j], sf);
             swd += wd;
             sfd = fmaf(wd, Fs[j], sfd);
+            if (md.sample_sgal) {
+              const float ws = wd * u;          // dw/ds = w u^2 / s
+              sws += ws;
+              sfs = fmaf(ws, Fs[j], sfs);
+            }
           }
         }
-        tl = -inv_s;
+        tl = -1.f - inv_s;
         if (sw > 0.f) {
           v = sf / sw;
           dv = (sfd * sw - sf * swd) / (sw * sw);
+          dvs = (sfs * sw - sf * sws) / (sw * sw);
           valid = true;
           cw = 1.f / sw;
         }
@@ -303,6 +312,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       um_spec += ui * (double)mi;
       const float us = (float)(ui * (double)rs.s_spec);
       gz_spec += us * dv * (-rs.inv1pz);
+      // s = sqrt(sigma_fix^2 + sigma_gal^2) / c: ds/dsigma_gal = (sigma_gal / c) / (s c)
+      if (md.sample_sgal && s > 0.f) g_sgal += us * dvs * (rs.sg_ln / (s * (float)C_KMS));
       ci = us * cw;
     }
     prg[i] = (jlo & 0xffff) | (jhi << 16);
@@ -347,11 +358,11 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
           const float4 q = px4[p];
           if (q.z == 0.f) continue;
           float w;
-          if (q.w >= 0.f) {
+          if (q.w > -0.5f) {   // linear row
             w = k == (prg[p] & 0xffff) ? 1.f - q.w : q.w;
-          } else {
+          } else {              // Gaussian row, 1/sigma = -1 - q.w
             const float d = (lh - q.x) + (ll - q.y);
-            const float u = d * -q.w;
+            const float u = d * (-1.f - q.w);
             w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
           }
           acc = fmaf(q.z, w, acc);
@@ -368,11 +379,11 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
           const int rg = prg[p], lo = rg & 0xffff, hi = rg >> 16;
           if (q.z == 0.f || k < lo || k > hi) continue;
           float w;
-          if (q.w >= 0.f) {
+          if (q.w > -0.5f) {   // linear row
             w = k == lo ? 1.f - q.w : q.w;
-          } else {
+          } else {              // Gaussian row, 1/sigma = -1 - q.w
             const float d = (lh - q.x) + (ll - q.y);
-            const float u = d * -q.w;
+            const float u = d * (-1.f - q.w);
             w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
           }
           acc = fmaf(q.z, w, acc);
@@ -434,7 +445,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
 
   // ---- fixed-order FP64 reductions of the per-thread pieces
   double v[EB_NRED] = {(double)g_tbc, (double)g_abc, (double)g_td, (double)g_dl, (double)g_lz, (double)g_lu,
-                       um_spec, (double)gz_gather + (double)gz_spec, (double)g_qy, l_spec, 0.0, 0.0};
+                       um_spec, (double)gz_gather + (double)gz_spec, (double)g_qy, l_spec, (double)g_sgal, 0.0};
 #pragma unroll
   for (int q = 0; q < EB_NRED; ++q) {
 #pragma unroll
@@ -465,6 +476,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     rg[RG_LOGMASS] = 2.302585092994046 * (um_phot + s[6]);
     rg[RG_Z] = um_phot * (double)rs.dlnp_dz + s[6] * (double)rs.dlns_dz + s[7];
     rg[RG_QY] = s[8];
+    rg[RG_SIGMA_GAL] = s[10];
     rg[RG_BAD] = stt ? 1.0 : 0.0;
     if (a.lnl) a.lnl[rs.orig] = lnl;
     if (a.status) a.status[rs.orig] = stt;

@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     float v = 0.f;
     bool valid = false;
     if (xh >= ll0 && xh <= llN) {
-      const float s = md.pix_s[i];
+      // total dispersion: fixed, or sigma_fix composed with the row's sigma_gal (Eq. one_kernel)
+      const float s = md.sample_sgal ? sqrtf(md.pix_fix2[i] + rs.sg_ln * rs.sg_ln) : md.pix_s[i];
       const int k = locate_ln(g, xh, g.lnl_hi);
       const float dln = (g.lnl_hi[k + 1] - g.lnl_hi[k]) + (g.lnl_lo[k + 1] - g.lnl_lo[k]);
       if (s < 0.5f * dln) {

@@ -219,6 +219,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   if (tid == 0) s_cr = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]]);
   bad = __syncthreads_or(bad);
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
+  // a sampled sigma_gal outside the model's declared range [0, max]
+  if (!status && md.sample_sgal) {
+    const float sg = th[md.offs[SED_KEY_SIGMA_GAL]];
+    if (!(sg >= 0.f && sg <= md.sgal_max_kms)) status = SED_ROW_BAD_THETA;
+  }
   const CosmoRow cr = s_cr;
   if (!status) status = cr.status;
   const double tmax = status ? 0.0 : (double)cr.tmax_d;
@@ -420,6 +425,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.status = 0;
     rs.orig = r;
     rs.y_scale = y_scale;
+    rs.sg_ln = md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] / (float)C_KMS : 0.f;
     rs.k_lo = win_lo;
     rs.k_hi = win_hi;
     if (a.tile_win) {   // union of the windows of this row's 128-row tile
@@ -591,6 +597,7 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     out[md.offs[SED_KEY_DIFFUSE_INDEX]] = (float)rg[RG_DELTA];
     out[md.offs[SED_KEY_GAS_LOGZ]] = md.use_neb ? (float)rg[RG_GAS_LOGZ] : 0.f;
     out[md.offs[SED_KEY_GAS_LOGU]] = md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f;
+    if (md.sample_sgal) out[md.offs[SED_KEY_SIGMA_GAL]] = (float)rg[RG_SIGMA_GAL];
   }
   if (md.zmode == 0)
     for (int i = tid; i < NT; i += blockDim.x) out[md.offs[SED_KEY_LOGZSOL] + i] = gzeta[i];

@@ -645,6 +645,9 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   if (d->n_pix && (!d->spec_lam_aa || !d->lsf_value)) return fail(ctx, SED_EINVAL, "spectrum arrays are NULL");
   if (d->n_pix && (d->lsf_mode < 0 || d->lsf_mode > 5)) return fail(ctx, SED_EINVAL, "bad lsf_mode");
   if (d->n_pix && !(d->sigma_gal_kms >= 0 && d->z_ref >= 0)) return fail(ctx, SED_EINVAL, "sigma_gal, z_ref must be >= 0");
+  if (d->sample_sigma_gal != 0 && d->sample_sigma_gal != 1) return fail(ctx, SED_EINVAL, "sample_sigma_gal must be 0 or 1");
+  if (d->sample_sigma_gal && !(d->sigma_gal_max_kms > 0 && d->sigma_gal_max_kms < 1e5))
+    return fail(ctx, SED_EINVAL, "sigma_gal_max_kms must be in (0, 1e5) when sigma_gal is sampled");
 
   Model* M = new Model();
   M->grid = d->grid;
@@ -659,7 +662,9 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   int o = 0;
   dv.offs[SED_KEY_SFH] = o; o += d->n_sfh;
   dv.offs[SED_KEY_LOGZSOL] = o; o += nz;
-  for (int k = SED_KEY_AFE; k < SED_NKEYS; k++) dv.offs[k] = o++;
+  for (int k = SED_KEY_AFE; k <= SED_KEY_GAS_LOGU; k++) dv.offs[k] = o++;
+  dv.offs[SED_KEY_SIGMA_GAL] = o;
+  o += d->sample_sigma_gal ? 1 : 0;
   dv.n_param = o;
   dv.zf = d->zf;
   dv.Om0 = d->Om0;
@@ -741,15 +746,21 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_nlog = pd; }
     if (d->phot_mask) M->phot_mask_h.assign(d->phot_mask, d->phot_mask + d->n_filt);
   }
-  // ---- spectrum: per-pixel dispersion, Eq. app_sigeff + fixed sigma_gal (Eq. one_kernel)
+  // ---- spectrum: per-pixel dispersion, Eq. app_sigeff + fixed sigma_gal (Eq. one_kernel);
+  //      with a sampled sigma_gal the fixed part sigma_fix^2 / c^2 per pixel, the
+  //      row's sigma_gal joining it in the kernels, and the widest reach bounded
+  //      by sigma_gal_max
+  dv.sample_sgal = d->sample_sigma_gal;
+  dv.sgal_max_kms = (float)d->sigma_gal_max_kms;
   if (!st && d->n_pix) {
     const int np = d->n_pix;
     dv.n_pix = np;
     if (!strictly_increasing(d->spec_lam_aa, np) || !(d->spec_lam_aa[0] > 0))
       st = fail(ctx, SED_EINVAL, "spectrum wavelengths must be strictly increasing and > 0");
     std::vector<double> pl(np);
-    std::vector<float> ps(np);
+    std::vector<float> ps(np), pf2(np);
     double smax = 0;
+    const double sg = d->sample_sigma_gal ? d->sigma_gal_max_kms : d->sigma_gal_kms;
     for (int i = 0; !st && i < np; i++) {
       const double lo_ = d->spec_lam_aa[i];
       if (!(d->lsf_value[i] > 0 && std::isfinite(d->lsf_value[i]))) { st = fail(ctx, SED_EINVAL, "lsf_value[%d] must be > 0", i); break; }
@@ -768,7 +779,8 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
       const double s = std::sqrt(fix2 + d->sigma_gal_kms * d->sigma_gal_kms) / C_KMS;
       pl[i] = std::log(lo_);
       ps[i] = (float)s;
-      smax = std::max(smax, s);
+      pf2[i] = (float)(fix2 / (C_KMS * C_KMS));
+      smax = std::max(smax, std::sqrt(fix2 + sg * sg) / C_KMS);
     }
     dv.pix_ln_min = pl.empty() ? 0 : pl.front();
     dv.pix_ln_max = pl.empty() ? 0 : pl.back();
@@ -777,6 +789,10 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     float* pf;
     if (!st) { st = upload(ctx, &pd, pl.data(), pl.size(), &M->allocs, &M->bytes); dv.pix_ln = pd; }
     if (!st) { st = upload(ctx, &pf, ps.data(), ps.size(), &M->allocs, &M->bytes); dv.pix_s = pf; }
+    if (!st && d->sample_sigma_gal) {
+      st = upload(ctx, &pf, pf2.data(), pf2.size(), &M->allocs, &M->bytes);
+      dv.pix_fix2 = pf;
+    }
     std::vector<double> zeros(np, 0.0);
     if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_d = pd; }
     if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_isig = pd; }

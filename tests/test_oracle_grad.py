@@ -3,8 +3,9 @@ that do not reuse its derivation:
 
 - central finite differences of the oracle's own forward model (which the
   pins of test_oracle_pins.py tie to the paper), on every parameter column,
-  for the three workload shapes (photometry with a power-law diffuse law;
-  nebular + Kriek & Conroy dust; [a/Fe] + an LSF-convolved spectrum);
+  for four workload shapes (photometry with a power-law diffuse law;
+  nebular + Kriek & Conroy dust; [a/Fe] + an LSF-convolved spectrum; the same
+  with a sampled sigma_gal);
 - the closed form of d lnL / d logmass (every model datum scales with
   10^logmass, Sec. 2.6);
 - homogeneity of the weights in the SFH masses (App. B: W is linear in m_i),
@@ -23,6 +24,7 @@ SHAPES = {
     "tiny": ("tiny_phot_16x4x512", None),
     "neb_kc13": ("phot_107x12x6000_b1024", dict(n_lam=1200, n_sfh=16)),
     "afe_spec": ("specphot_afe_107x12x5x6000_b2048", dict(n_lam=1200, n_sfh=16, n_pix=240)),
+    "sgal_spec": ("specphot_afe_sgal_107x12x5x6000_b2048", dict(n_lam=1200, n_sfh=16, n_pix=240)),
 }
 
 
