@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "phot_107x12x6000_b1024"
 GRAD_WORKLOAD = "specphot_afe_107x12x5x6000_b2048"
+SGAL_WORKLOAD = "specphot_afe_sgal_107x12x5x6000_b2048"   # the same with a sampled sigma_gal
 PRECS = ("fp32", "fp32_simt", "bf16", "fp8")
 PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
              "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
@@ -137,7 +138,8 @@ def build_workload(wname, ctx, seed_rows, device):
     filt = synth.pack_filters(synth.workload_filters(w))
     nb = len(filt[0])
     kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
-              phot_d=np.ones(nb), phot_sigma=np.ones(nb))
+              phot_d=np.ones(nb), phot_sigma=np.ones(nb), sample_sigma_gal=w.sample_sigma_gal,
+              sigma_gal_max_kms=w.sigma_gal_max_kms)
     spec = None
     if w.spectrum is not None:
         sp = w.spectrum
@@ -423,6 +425,21 @@ def bench_gradient(ctx, device, flush, args):
     stt = torch.empty(B, dtype=torch.int32, device=device)
     s = torch.cuda.Stream(device=device)
     res = {"workload": w.name, "batch": B, "n_param": int(theta.shape[1])}
+    # the same workload with a sampled sigma_gal (one more parameter column; the
+    # spectral kernels' widths are per row): forward and gradient, 3xTF32
+    ws, _, _, model_s, theta_s, _ = build_workload(SGAL_WORKLOAD, ctx, 4, device)
+    ts = torch.from_numpy(theta_s).to(device)
+    grad_s = torch.empty_like(ts)
+    gs = capture_step(lambda st: model_s.loglike_grad(ts, "fp32", stream=st, out=(lnl, grad_s, stt)), s)
+    gsm = time_replays(gs, s, max(5, args.steps // 4), flush)
+    fs = capture_step(lambda st: model_s.loglike(ts, "fp32", stream=st, out=lnl, status=stt), s)
+    fsm = time_replays(fs, s, max(5, args.steps // 4), flush)
+    res["sampled_sigma_gal"] = {"workload": ws.name, "n_param": int(theta_s.shape[1]),
+                                "sigma_gal_kms": list(ws.ranges["sigma_gal"]),
+                                "grad_evals_per_s": round(B * len(gsm) / (sum(gsm) * 1e-3), 1),
+                                "grad_ms_per_step": round(sum(gsm) / len(gsm), 4),
+                                "loglike_evals_per_s": round(B * len(fsm) / (sum(fsm) * 1e-3), 1),
+                                "loglike_ms_per_step": round(sum(fsm) / len(fsm), 4)}
     for p in ("fp32", "fp32_simt"):
         g = capture_step(lambda st, p=p: model.loglike_grad(t, p, stream=st, out=(lnl, grad, stt)), s)
         gms = time_replays(g, s, max(5, args.steps // 4), flush)
