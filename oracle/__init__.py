@@ -55,7 +55,8 @@ class _Model(C.Structure):
                 ("spec_d", C.c_void_p), ("spec_sigma", C.c_void_p), ("spec_mask", C.c_void_p),
                 ("lsf_mode", C.c_int), ("lsf_value", C.c_void_p),
                 ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
-                ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double)]
+                ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
+                ("calib_n", C.c_int), ("calib_sigma", C.c_void_p)]
 
 
 def _load():
@@ -119,6 +120,7 @@ class Oracle:
     z_ref: float = 0.0
     sample_sigma_gal: int = 0           # 1: sigma_gal (km/s) is the last parameter column
     sigma_gal_max_kms: float = 1000.0   # sampled sigma_gal must lie in [0, this]
+    calib_sigma: np.ndarray | None = None   # prior widths s_m of a marginalised calibration polynomial
     H0: float = PHYS["H0"]
     Om0: float = PHYS["Om0"]
     bc_edge_log_age_yr: float = PHYS["bc_edge_log_age_yr"]
@@ -179,6 +181,9 @@ class Oracle:
             m.lsf_value = _p(k(self.lsf_value))
             m.sigma_gal_kms, m.z_ref = self.sigma_gal_kms, self.z_ref
         m.sample_sigma_gal, m.sigma_gal_max_kms = int(self.sample_sigma_gal), float(self.sigma_gal_max_kms)
+        if self.calib_sigma is not None and self.spec_lam is not None:
+            m.calib_n = len(self.calib_sigma)
+            m.calib_sigma = _p(k(self.calib_sigma))
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):

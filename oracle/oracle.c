@@ -389,6 +389,100 @@ void orc_spectrum(const orc_grid *g, const orc_model *md, const double *lam_rest
   free(ll);
 }
 
+/* App. E, marginalised calibration polynomial (Eq. app_polymarg).  The
+ * calibrated model is mu_i (1 + sum_m c_m T_m(x_i)), T_m the Chebyshev
+ * polynomials of the pixel wavelengths mapped linearly onto [-1, 1] (first and
+ * last pixel at -1 and 1); with the prior c ~ N(0, Lambda), Lambda = diag(s_m^2),
+ * the coefficients integrate out and lnL gains
+ *   b^T M^-1 b / 2 - ln|M| / 2 - ln|Lambda| / 2,
+ *   M = D^T C^-1 D + Lambda^-1,  b = D^T C^-1 r,  D = diag(mu) A,  A_im = T_m(x_i),
+ * r = d - mu, C = diag(sigma^2), over the included pixels inc[i] != 0.  Returns
+ * these terms; minv [n][n] = M^-1 and cstar [n] = M^-1 b when non-NULL. */
+static void cheb_row(double x, int n, double *T) {
+  T[0] = 1.0;
+  if (n > 1) T[1] = x;
+  for (int m = 2; m < n; m++) T[m] = 2.0 * x * T[m - 1] - T[m - 2];
+}
+static double cheb_x(const orc_model *md, int i) {
+  double lo = md->spec_lam[0], hi = md->spec_lam[md->n_pix - 1];
+  return md->n_pix > 1 ? (2.0 * md->spec_lam[i] - (lo + hi)) / (hi - lo) : 0.0;
+}
+static double calib_terms(const orc_model *md, const double *mu, const unsigned char *inc, double *minv,
+                          double *cstar) {
+  int n = md->calib_n;
+  double *M = (double *)calloc((size_t)n * n, sizeof(double));
+  double *L = (double *)calloc((size_t)n * n, sizeof(double));
+  double *b = (double *)calloc(n, sizeof(double));
+  double *c = (double *)calloc(n, sizeof(double));
+  double *T = (double *)malloc(n * sizeof(double));
+  for (int i = 0; i < md->n_pix; i++) {
+    if (!inc[i]) continue;
+    cheb_row(cheb_x(md, i), n, T);
+    double w = 1.0 / (md->spec_sigma[i] * md->spec_sigma[i]), r = md->spec_d[i] - mu[i];
+    for (int a = 0; a < n; a++) {
+      b[a] += mu[i] * T[a] * w * r;
+      for (int e = 0; e < n; e++) M[a * n + e] += mu[i] * T[a] * w * mu[i] * T[e];
+    }
+  }
+  double logdet_lam = 0.0;
+  for (int a = 0; a < n; a++) {
+    M[a * n + a] += 1.0 / (md->calib_sigma[a] * md->calib_sigma[a]);
+    logdet_lam += log(md->calib_sigma[a] * md->calib_sigma[a]);
+  }
+  /* Cholesky M = L L^T */
+  double logdet = 0.0;
+  int ok = 1;
+  for (int j = 0; j < n && ok; j++) {
+    double d = M[j * n + j];
+    for (int k = 0; k < j; k++) d -= L[j * n + k] * L[j * n + k];
+    if (!(d > 0.0)) { ok = 0; break; }
+    L[j * n + j] = sqrt(d);
+    logdet += log(d);
+    for (int i = j + 1; i < n; i++) {
+      double v = M[i * n + j];
+      for (int k = 0; k < j; k++) v -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = v / L[j * n + j];
+    }
+  }
+  double out = NAN;
+  if (ok) {
+    /* c = M^-1 b by forward and back substitution */
+    for (int i = 0; i < n; i++) {
+      double v = b[i];
+      for (int k = 0; k < i; k++) v -= L[i * n + k] * c[k];
+      c[i] = v / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; i--) {
+      double v = c[i];
+      for (int k = i + 1; k < n; k++) v -= L[k * n + i] * c[k];
+      c[i] = v / L[i * n + i];
+    }
+    double quad = 0.0;
+    for (int a = 0; a < n; a++) quad += b[a] * c[a];
+    out = 0.5 * quad - 0.5 * logdet - 0.5 * logdet_lam;
+    if (cstar) memcpy(cstar, c, n * sizeof(double));
+    if (minv) {
+      double *e = (double *)malloc(n * sizeof(double));
+      for (int col = 0; col < n; col++) {
+        for (int i = 0; i < n; i++) {
+          double v = i == col ? 1.0 : 0.0;
+          for (int k = 0; k < i; k++) v -= L[i * n + k] * e[k];
+          e[i] = v / L[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; i--) {
+          double v = e[i];
+          for (int k = i + 1; k < n; k++) v -= L[k * n + i] * e[k];
+          e[i] = v / L[i * n + i];
+        }
+        for (int i = 0; i < n; i++) minv[i * n + col] = e[i];
+      }
+      free(e);
+    }
+  }
+  free(M); free(L); free(b); free(c); free(T);
+  return out;
+}
+
 /* One parameter row through the whole forward model and likelihood. */
 int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double *W_out,
             double *Y_out, double *O_out, double *F_out, double *fnu_out, double *phot,
@@ -472,13 +566,17 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
     }
     if (md->n_pix > 0) {
       orc_spectrum(g, md, g->lam, NL, t.z, t.sigma_gal, fnu, sp, vd);
+      unsigned char *inc = (unsigned char *)calloc(md->n_pix, 1);
       for (int i = 0; i < md->n_pix; i++) {
         if (spec) spec[i] = sp[i];
         if (md->spec_d && vd[i] && (!md->spec_mask || md->spec_mask[i])) {
           double s = md->spec_sigma[i], r = (md->spec_d[i] - sp[i]) / s;
           lnl += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
+          inc[i] = 1;
         }
       }
+      if (md->calib_n > 0 && md->spec_d) lnl += calib_terms(md, sp, inc, NULL, NULL);
+      free(inc);
     }
     if (!isfinite(lnl)) { st = ORC_NONFINITE; lnl = -INFINITY; }
     if (scal) { scal[0] = cosm[0]; scal[1] = cosm[1]; scal[2] = tmax; scal[3] = qy; scal[4] = scale; }
@@ -721,11 +819,34 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     spec_widths(g, md, t.sigma_gal, s_ln);
     for (int k = 0; k < NL; k++) ll[k] = log(g->lam[k]);
     double lz = log(zp);
+    /* marginalised calibration polynomial: its lnL terms, and for every pixel
+     * d lnL / d mu_i = [(d_i - mu_i (1 + p_i)) (1 + p_i) - mu_i q_i] / sigma_i^2
+     * with p_i = sum_m c*_m T_m(x_i) (c* = M^-1 b) and q_i = T(x_i)^T M^-1 T(x_i) */
+    int nc = (md->calib_n > 0 && md->spec_d) ? md->calib_n : 0;
+    double *minv = NULL, *cst = NULL, *T = NULL, l_calib = 0.0;
+    if (nc) {
+      unsigned char *inc = (unsigned char *)calloc(md->n_pix, 1);
+      for (int i = 0; i < md->n_pix; i++) inc[i] = vd[i] && (!md->spec_mask || md->spec_mask[i]);
+      minv = (double *)malloc((size_t)nc * nc * sizeof(double));
+      cst = (double *)malloc(nc * sizeof(double));
+      T = (double *)malloc(nc * sizeof(double));
+      l_calib = calib_terms(md, sp, inc, minv, cst);   /* added after the pixel sum, as in orc_row */
+      free(inc);
+    }
     for (int i = 0; i < md->n_pix; i++) {
       if (!(md->spec_d && vd[i] && (!md->spec_mask || md->spec_mask[i]))) continue;
       double s = md->spec_sigma[i], r = (md->spec_d[i] - sp[i]) / s;
       L += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
       double ui = r / s;
+      if (nc) {
+        cheb_row(cheb_x(md, i), nc, T);
+        double p = 0.0, q = 0.0;
+        for (int a = 0; a < nc; a++) {
+          p += cst[a] * T[a];
+          for (int e = 0; e < nc; e++) q += T[a] * minv[a * nc + e] * T[e];
+        }
+        ui = ((md->spec_d[i] - sp[i] * (1.0 + p)) * (1.0 + p) - sp[i] * q) / (s * s);
+      }
       /* Eq. "app_response" row of pixel i, as in orc_spectrum */
       double x = log(md->spec_lam[i]) - lz, sg = s_ln[i];
       int k = 0;
@@ -756,7 +877,9 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
       }
       gz += ui * (sfd * sw - sf * swd) / (sw * sw) * (-1.0 / zp);
     }
+    if (nc) L += l_calib;
     free(sp); free(vd); free(s_ln); free(ll);
+    free(minv); free(cst); free(T);
   }
   *lnl = L;
   if (!isfinite(L)) {

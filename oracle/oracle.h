@@ -59,6 +59,8 @@ typedef struct {
   double sigma_gal_kms, z_ref;  /* fixed stellar dispersion (when not sampled), projector redshift */
   int sample_sigma_gal;        /* 1: sigma_gal (km/s) is a parameter column (Sec. 2.7 kinematics) */
   double sigma_gal_max_kms;    /* sampled sigma_gal must lie in [0, this] */
+  int calib_n;                 /* coefficients of the marginalised calibration polynomial (0: none) */
+  const double *calib_sigma;   /* [calib_n] prior widths s_m of the coefficients (App. E) */
 } orc_model;
 
 /* Row status bits (shared meaning with the library by documentation only). */

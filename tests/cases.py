@@ -10,9 +10,10 @@ import synth
 
 
 def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_theta=4, lsf_r=None,
-               spec_mask=None, sigma_gal_kms=None):
+               spec_mask=None, sigma_gal_kms=None, calib_sigma=None):
     """lsf_r, spec_mask, sigma_gal_kms: optional replacements of the
-    workload's R_fwhm curve, pixel mask and stellar dispersion."""
+    workload's R_fwhm curve, pixel mask and stellar dispersion; calib_sigma:
+    prior widths of a marginalised calibration polynomial (App. E)."""
     grid = grid if grid is not None else synth.make_grid(**w.grid_kw, seed=1)
     filt = filters if filters is not None else synth.pack_filters(synth.workload_filters(w))
     kw = dict(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
@@ -26,7 +27,8 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
         kw.update(spec_lam=lam, spec_d=np.ones(lam.size), spec_sigma=np.ones(lam.size),
                   spec_mask=np.ones(lam.size, np.uint8) if spec_mask is None else spec_mask, lsf_mode=0,
                   lsf_value=r if lsf_r is None else lsf_r,
-                  sigma_gal_kms=w.sigma_gal_kms if sigma_gal_kms is None else sigma_gal_kms, z_ref=w.z_ref)
+                  sigma_gal_kms=w.sigma_gal_kms if sigma_gal_kms is None else sigma_gal_kms, z_ref=w.z_ref,
+                  calib_sigma=None if calib_sigma is None else np.asarray(calib_sigma, dtype=np.float64))
     orc = oracle.Oracle(**kw)
     if with_data:
         th_true = theta_rows(w, 1, seed=99)

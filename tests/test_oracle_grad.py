@@ -3,9 +3,10 @@ that do not reuse its derivation:
 
 - central finite differences of the oracle's own forward model (which the
   pins of test_oracle_pins.py tie to the paper), on every parameter column,
-  for four workload shapes (photometry with a power-law diffuse law;
+  for five workload shapes (photometry with a power-law diffuse law;
   nebular + Kriek & Conroy dust; [a/Fe] + an LSF-convolved spectrum; the same
-  with a sampled sigma_gal);
+  with a sampled sigma_gal; the same with a marginalised calibration
+  polynomial);
 - the closed form of d lnL / d logmass (every model datum scales with
   10^logmass, Sec. 2.6);
 - homogeneity of the weights in the SFH masses (App. B: W is linear in m_i),
@@ -25,7 +26,9 @@ SHAPES = {
     "neb_kc13": ("phot_107x12x6000_b1024", dict(n_lam=1200, n_sfh=16)),
     "afe_spec": ("specphot_afe_107x12x5x6000_b2048", dict(n_lam=1200, n_sfh=16, n_pix=240)),
     "sgal_spec": ("specphot_afe_sgal_107x12x5x6000_b2048", dict(n_lam=1200, n_sfh=16, n_pix=240)),
+    "calib_spec": ("specphot_afe_107x12x5x6000_b2048", dict(n_lam=1200, n_sfh=16, n_pix=240)),
 }
+CALIB = {"calib_spec": [0.2, 0.1, 0.1, 0.05, 0.05]}   # prior widths of a 5-term calibration polynomial
 
 
 @pytest.fixture(scope="module", params=list(SHAPES))
@@ -34,7 +37,7 @@ def shape(request):
     w = synth.WORKLOADS[wname]
     if sh:
         w = synth.shrink(w, **sh)
-    return w, cases.oracle_for(w)
+    return w, cases.oracle_for(w, calib_sigma=CALIB.get(request.param))
 
 
 def test_analytic_gradient_matches_central_differences(shape):
@@ -66,7 +69,24 @@ def test_dlogmass_closed_form_and_mass_homogeneity(shape):
         if orc.n_pix:
             m = res["spec"][r]
             # pixels without model nodes in reach are out of the likelihood (and have m = 0)
-            want += math.log(10) * np.sum((orc.spec_d - m) / orc.spec_sigma ** 2 * m)
+            u = (orc.spec_d - m) / orc.spec_sigma ** 2
+            if orc.calib_sigma is not None:
+                # marginalised calibration (App. E): with p = A c*, c* = M^-1 b and
+                # q_i = A_i M^-1 A_i^T, d lnL / d mu_i = [(d - mu (1+p))(1+p) - mu q] / sigma^2
+                lam = np.asarray(orc.spec_lam)
+                x = (2.0 * lam - (lam[0] + lam[-1])) / (lam[-1] - lam[0])
+                n = len(orc.calib_sigma)
+                A = np.polynomial.chebyshev.chebvander(x, n - 1)
+                inc = m != 0
+                Dw = (m[:, None] * A / orc.spec_sigma[:, None])[inc]
+                M = Dw.T @ Dw + np.diag(1.0 / np.asarray(orc.calib_sigma) ** 2)
+                bvec = Dw.T @ ((orc.spec_d - m) / orc.spec_sigma)[inc]
+                Minv = np.linalg.inv(M)
+                pp = A @ (Minv @ bvec)
+                qq = np.einsum("im,mn,in->i", A, Minv, A)
+                u = ((orc.spec_d - m * (1 + pp)) * (1 + pp) - m * qq) / orc.spec_sigma ** 2
+                u[~inc] = 0.0
+            want += math.log(10) * np.sum(u * m)
         assert g[r, j_mass] == pytest.approx(want, rel=1e-9, abs=1e-9 * abs(want))
         euler = np.dot(th[r, :w.n_sfh], g[r, :w.n_sfh])
         assert euler == pytest.approx(g[r, j_mass] / math.log(10), rel=1e-9, abs=1e-9 * abs(g[r, j_mass]))
