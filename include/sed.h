@@ -161,7 +161,18 @@ typedef struct {
    * maximum bounds the spectral kernels' reach (shared-memory window sizes). */
   int sample_sigma_gal;
   double sigma_gal_max_kms;
+  /* Marginalised calibration polynomial (App. E, Eq. app_polymarg): the
+   * spectrum's model is mu_i (1 + sum_m c_m T_m(x_i)), T_m Chebyshev
+   * polynomials of the pixel wavelengths mapped linearly onto [-1, 1] (first
+   * and last pixel), with c_m ~ N(0, calib_sigma[m]^2) integrated out of lnL in
+   * closed form.  calib_n = number of coefficients (0: none, at most
+   * SED_MAX_CALIB); calib_sigma [calib_n] > 0.  Needs a spectrum.  Model
+   * spectra returned by sed_forward stay uncalibrated (mu). */
+  int calib_n;
+  const double *calib_sigma;
 } sed_model_desc;
+
+#define SED_MAX_CALIB 13
 
 /* Context on one CUDA device; hbm_budget_bytes = 0 means no limit. */
 sed_status sed_create(sed_ctx **out, int device, size_t hbm_budget_bytes);

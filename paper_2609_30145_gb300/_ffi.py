@@ -42,7 +42,8 @@ class ModelDesc(C.Structure):
                 ("n_pix", C.c_int), ("spec_lam_aa", P), ("spec_d", P), ("spec_sigma", P),
                 ("spec_mask", P), ("lsf_mode", C.c_int), ("lsf_value", P),
                 ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
-                ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double)]
+                ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
+                ("calib_n", C.c_int), ("calib_sigma", P)]
 
 
 class StageStats(C.Structure):

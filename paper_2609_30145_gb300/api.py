@@ -106,7 +106,8 @@ class Context:
                      bc_edge_log_age_yr=7.03, H0=67.66, Om0=0.3097, filters=None,
                      phot_d=None, phot_sigma=None, phot_mask=None, spec_lam=None, spec_d=None,
                      spec_sigma=None, spec_mask=None, lsf_mode=0, lsf_value=None,
-                     sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0) -> "Model":
+                     sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0,
+                     calib_sigma=None) -> "Model":
         d = _ffi.ModelDesc()
         d.grid, d.n_sfh, d.zf, d.zmode = grid_id, n_sfh, zf, zmode
         d.use_afe, d.use_nebular, d.dust_law = use_afe, use_nebular, dust_law
@@ -132,6 +133,10 @@ class Context:
             d.lsf_mode, d.lsf_value = lsf_mode, _ptr(lv)
             d.sigma_gal_kms, d.z_ref = sigma_gal_kms, z_ref
         d.sample_sigma_gal, d.sigma_gal_max_kms = int(sample_sigma_gal), float(sigma_gal_max_kms)
+        if calib_sigma is not None:
+            cs = _f64(calib_sigma)
+            keep.append(cs)
+            d.calib_n, d.calib_sigma = cs.size, _ptr(cs)
         mid = C.c_int32()
         self._check(self._lib.sed_create_model(self._h, C.byref(d), C.byref(mid)))
         return Model(self, mid.value, n_filt=d.n_filt, n_pix=d.n_pix)

@@ -23,6 +23,7 @@
 // order (node-owned gathers, no atomics), so the gradient is bitwise
 // reproducible.
 #include "atten.cuh"
+#include "calib.cuh"
 #include "locate.cuh"
 #include "sed_internal.cuh"
 
@@ -52,11 +53,17 @@ __device__ __forceinline__ void put_g(const EpiBwdArgs& a, float* hi, float* lo,
 // Shared memory of one row: F and dlnL/dF over the row's node window, then a
 // union of the filter samples' brackets (photometry) and the pixels' node
 // ranges and positions (spectrum).
+// bytes of the calibration scratch: per-warp moments, the Cholesky factor and c* as floats
+constexpr size_t EB_CAL_BYTES = (size_t)EB_WARPS * CAL_NV * sizeof(double) +
+                                (size_t)(SED_MAX_CALIB * SED_MAX_CALIB + SED_MAX_CALIB) * sizeof(float);
+
 size_t epi_bwd_smem(const EpiBwdArgs& a) {
   const size_t W = (size_t)a.md.win_max;
   const size_t samp = (size_t)a.md.n_samp * 8;    // node index + interpolation weight
-  const size_t pix = (size_t)a.md.n_pix * 20;     // 4 floats + node range
-  return ((2 * W + 3) & ~(size_t)3) * sizeof(float) + (samp > pix ? samp : pix);
+  // 4 floats + node range; with a calibration polynomial also mu, dmu/dx, dmu/ds, 1/sum w
+  const size_t pix = (size_t)a.md.n_pix * (a.md.calib_n ? 36 : 20);
+  const size_t u = ((samp > pix ? samp : pix) + 7) & ~(size_t)7;
+  return ((2 * W + 3) & ~(size_t)3) * sizeof(float) + u + (a.md.calib_n ? EB_CAL_BYTES : 0);
 }
 
 __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
@@ -102,6 +109,21 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   // -1 - 1/sigma (below -1): the two never meet, whatever the rounding
   float4* px4 = reinterpret_cast<float4*>(U);
   int* prg = reinterpret_cast<int*>(px4 + md.n_pix);   // node range lo | hi << 16
+  // calibration polynomial (App. E): per pixel mu (0 when excluded), dv/dx, dv/ds,
+  // 1/sum w, then the per-warp moments, the Cholesky factor and c*
+  float* mu_s = reinterpret_cast<float*>(prg + md.n_pix);
+  float* dv_s = mu_s + md.n_pix;
+  float* dvs_s = dv_s + md.n_pix;
+  float* cw_s = dvs_s + md.n_pix;
+  double* cal_part = nullptr;
+  float *cal_Lf = nullptr, *cal_cf = nullptr;
+  if (md.calib_n) {
+    const size_t samp = (size_t)md.n_samp * 8, pix = (size_t)md.n_pix * 36;
+    const size_t u = ((samp > pix ? samp : pix) + 7) & ~(size_t)7;
+    cal_part = reinterpret_cast<double*>(reinterpret_cast<char*>(U) + u);
+    cal_Lf = reinterpret_cast<float*>(cal_part + EB_WARPS * CAL_NV);
+    cal_cf = cal_Lf + SED_MAX_CALIB * SED_MAX_CALIB;
+  }
   // each thread owns a contiguous run of CH window nodes (CH odd: the runs of a
   // warp fall in distinct shared-memory banks) for the node-owned gathers
   const int nw = k_hi - k_lo + 1;
@@ -305,7 +327,18 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     }
     const float mi = rs.s_spec * v;
     float ci = 0.f;
-    if (valid && md.spec_isig[i] != 0.0) {
+    const bool inc = valid && md.spec_isig[i] != 0.0;
+    if (md.calib_n) {
+      // the weights need the whole row's calibration solve: keep what they use
+      if (inc) {
+        const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
+        l_spec += -0.5 * rr * rr + md.spec_nlog[i];
+      }
+      mu_s[i] = inc ? mi : 0.f;
+      dv_s[i] = dv;
+      dvs_s[i] = dvs;
+      cw_s[i] = cw;
+    } else if (inc) {
       const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
       l_spec += -0.5 * rr * rr + md.spec_nlog[i];
       const double ui = rr * md.spec_isig[i];
@@ -318,6 +351,61 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     }
     prg[i] = (jlo & 0xffff) | (jhi << 16);
     px4[i] = make_float4(xh, xl, ci, tl);   // x_hi ascending in i: the pixels' wavelengths are strictly increasing
+  }
+  if (md.calib_n) {
+    // ---- marginalised calibration (App. E): moments over this thread's own
+    //      pixels, one solve per row, then each included pixel's
+    //      d lnL / d mu_i = [(d_i - mu_i (1 + p_i)) (1 + p_i) - mu_i q_i] / sigma_i^2,
+    //      p = A c*, q_i = |L^-1 T(x_i)|^2 (M = L L^T)
+    calib_block<0, 0, EB_THREADS>(md, mu_s, tid, lane, warp, cal_part);
+    calib_block<SED_MAX_CALIB, 0, EB_THREADS>(md, mu_s, tid, lane, warp, cal_part);
+    calib_block<0, 1, EB_THREADS>(md, mu_s, tid, lane, warp, cal_part);
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 0; q < CAL_NV; ++q)
+        for (int w = 1; w < EB_WARPS; ++w) cal_part[q] += cal_part[w * CAL_NV + q];
+      double* Ld = cal_part + CAL_NV;   // warps 1.. of the moments are no longer needed
+      double cd[SED_MAX_CALIB];
+      l_spec += calib_solve(md, cal_part, cal_part + CAL_NS, Ld, cd);
+      const int n = md.calib_n;
+      for (int q = 0; q < n * n; ++q) cal_Lf[q] = (float)Ld[q];
+      for (int q = 0; q < n; ++q) cal_cf[q] = (float)cd[q];
+    }
+    __syncthreads();
+    const int n = md.calib_n;
+    for (int i = tid; i < md.n_pix; i += EB_THREADS) {
+      const float mu = mu_s[i];
+      if (mu == 0.f) continue;
+      const float x = md.pix_cx[i];
+      float T[SED_MAX_CALIB], y[SED_MAX_CALIB];
+      float p = 0.f, q = 0.f, tp = 1.f, tc = x;
+#pragma unroll
+      for (int a = 0; a < SED_MAX_CALIB; ++a) {
+        T[a] = a == 0 ? 1.f : tc;
+        if (a > 0) { const float tn = 2.f * x * tc - tp; tp = tc; tc = tn; }
+      }
+#pragma unroll
+      for (int a = 0; a < SED_MAX_CALIB; ++a) {
+        if (a < n) {
+          p = fmaf(cal_cf[a], T[a], p);
+          float v = T[a];
+#pragma unroll
+          for (int k = 0; k < a; ++k) v -= cal_Lf[a * n + k] * y[k];
+          y[a] = v / cal_Lf[a * n + a];
+          q = fmaf(y[a], y[a], q);
+        }
+      }
+      const double is = md.spec_isig[i];
+      const double ui = ((md.spec_d[i] - (double)mu * (1.0 + p)) * (1.0 + p) - (double)mu * q) * is * is;
+      um_spec += ui * (double)mu;
+      const float us = (float)(ui * (double)rs.s_spec);
+      gz_spec += us * dv_s[i] * (-rs.inv1pz);
+      if (md.sample_sgal) {
+        const float s = sqrtf(md.pix_fix2[i] + rs.sg_ln * rs.sg_ln);
+        if (s > 0.f) g_sgal += us * dvs_s[i] * (rs.sg_ln / (s * (float)C_KMS));
+      }
+      px4[i].z = us * cw_s[i];
+    }
   }
   __syncthreads();
 

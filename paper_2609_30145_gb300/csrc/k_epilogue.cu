@@ -17,6 +17,7 @@
 #include "sed_internal.cuh"
 #include "locate.cuh"
 #include "atten.cuh"
+#include "calib.cuh"
 
 namespace sed {
 
@@ -30,7 +31,8 @@ constexpr int MAX_BANDS = 128;
 size_t epilogue_smem(const EpiArgs& a) {
   const int np = a.row_model ? a.smem_pix : a.md.n_pix;
   const size_t W = (size_t)(a.row_model ? a.smem_win : a.md.win_max);
-  return W * sizeof(float2) + (np > 0 ? W * sizeof(float) : 0);
+  const bool calib = a.row_model || a.md.calib_n > 0;   // model pixel values for the calibration moments
+  return W * sizeof(float2) + (np > 0 ? W * sizeof(float) : 0) + (calib ? (size_t)np * sizeof(float) : 0);
 }
 
 // MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
@@ -50,6 +52,8 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   const int WIN = MULTI ? a.smem_win : md.win_max;
   __shared__ float mb_s[MAX_BANDS];
   __shared__ double red[EPI_WARPS];
+  __shared__ double cal_part[EPI_WARPS][CAL_NV];   // per-warp calibration moments
+  __shared__ double cal_L[SED_MAX_CALIB * SED_MAX_CALIB], cal_c[SED_MAX_CALIB];
 
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
@@ -75,6 +79,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);   // nodes [k_lo, k_hi] are the only ones read below
   float2* LG = reinterpret_cast<float2*>(smem4) - k_lo;               // {rest-frame lambda, F / lam^2}
   float* Fs = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem4) + WIN) - k_lo;   // F (spectral arm only)
+  float* mu_s = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem4) + WIN) + WIN;  // calibration: included pixels' mu
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
     const float4 c = g.att4[k];
@@ -172,10 +177,19 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     }
     const float mi = rs.s_spec * v;
     if (a.spec_out) a.spec_out[(size_t)ro * md.n_pix + i] = mi;
-    if (valid && md.spec_isig[i] != 0.0) {
+    const bool inc = valid && md.spec_isig[i] != 0.0;
+    if (inc) {
       const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
       part += -0.5 * rr * rr + md.spec_nlog[i];
     }
+    if (md.calib_n) mu_s[i] = inc ? mi : 0.f;
+  }
+  // calibration moments over this thread's own pixels (no barrier needed),
+  // in three blocks of sums (S_0..12, S_13..24, b_0..12), each summed per warp in FP64
+  if (md.calib_n) {
+    calib_block<0, 0, EPI_THREADS>(md, mu_s, tid, lane, warp, &cal_part[0][0]);
+    calib_block<SED_MAX_CALIB, 0, EPI_THREADS>(md, mu_s, tid, lane, warp, &cal_part[0][0]);
+    calib_block<0, 1, EPI_THREADS>(md, mu_s, tid, lane, warp, &cal_part[0][0]);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -196,6 +210,12 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     if (lane == 0) {
       double tot = pv;
       for (int w = 0; w < EPI_WARPS; ++w) tot += red[w];
+      if (md.calib_n) {
+        // sum the warps' moments in warp order into row 0, then solve
+        for (int q = 0; q < CAL_NV; ++q)
+          for (int w = 1; w < EPI_WARPS; ++w) cal_part[0][q] += cal_part[w][q];
+        tot += calib_solve(md, &cal_part[0][0], &cal_part[0][CAL_NS], cal_L, cal_c);
+      }
       uint32_t st = 0;
       if (!isfinite(tot)) { st = SED_ROW_NONFINITE; tot = -INFINITY; }
       if (a.lnl) a.lnl[ro] = tot;

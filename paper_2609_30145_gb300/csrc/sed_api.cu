@@ -646,6 +646,15 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   if (d->n_pix && (d->lsf_mode < 0 || d->lsf_mode > 5)) return fail(ctx, SED_EINVAL, "bad lsf_mode");
   if (d->n_pix && !(d->sigma_gal_kms >= 0 && d->z_ref >= 0)) return fail(ctx, SED_EINVAL, "sigma_gal, z_ref must be >= 0");
   if (d->sample_sigma_gal != 0 && d->sample_sigma_gal != 1) return fail(ctx, SED_EINVAL, "sample_sigma_gal must be 0 or 1");
+  if (d->calib_n < 0 || d->calib_n > SED_MAX_CALIB)
+    return fail(ctx, SED_EINVAL, "calib_n must be in [0, %d]", SED_MAX_CALIB);
+  if (d->calib_n > 0) {
+    if (!d->n_pix) return fail(ctx, SED_EINVAL, "a calibration polynomial needs a spectrum");
+    if (!d->calib_sigma) return fail(ctx, SED_EINVAL, "calib_sigma is NULL");
+    for (int m = 0; m < d->calib_n; m++)
+      if (!(d->calib_sigma[m] > 0 && std::isfinite(d->calib_sigma[m])))
+        return fail(ctx, SED_EINVAL, "calib_sigma[%d] must be finite and > 0", m);
+  }
   if (d->sample_sigma_gal && !(d->sigma_gal_max_kms > 0 && d->sigma_gal_max_kms < 1e5))
     return fail(ctx, SED_EINVAL, "sigma_gal_max_kms must be in (0, 1e5) when sigma_gal is sampled");
 
@@ -792,6 +801,20 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     if (!st && d->sample_sigma_gal) {
       st = upload(ctx, &pf, pf2.data(), pf2.size(), &M->allocs, &M->bytes);
       dv.pix_fix2 = pf;
+    }
+    // calibration polynomial: Chebyshev coordinate of each pixel, prior terms
+    if (!st && d->calib_n > 0) {
+      std::vector<float> cx(np);
+      const double l0 = d->spec_lam_aa[0], l1 = d->spec_lam_aa[np - 1];
+      for (int i = 0; i < np; i++) cx[i] = np > 1 ? (float)((2.0 * d->spec_lam_aa[i] - (l0 + l1)) / (l1 - l0)) : 0.f;
+      st = upload(ctx, &pf, cx.data(), cx.size(), &M->allocs, &M->bytes);
+      dv.pix_cx = pf;
+      dv.calib_n = d->calib_n;
+      dv.calib_logdet_lam = 0.0;
+      for (int m = 0; m < d->calib_n; m++) {
+        dv.calib_isig2[m] = 1.0 / (d->calib_sigma[m] * d->calib_sigma[m]);
+        dv.calib_logdet_lam += std::log(d->calib_sigma[m] * d->calib_sigma[m]);
+      }
     }
     std::vector<double> zeros(np, 0.0);
     if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_d = pd; }

@@ -135,6 +135,12 @@ struct ModelDev {
   const double* pix_ln;    // [n_pix] ln(lambda_obs)
   const float* pix_s;      // [n_pix] total dispersion in ln(lambda) (fixed sigma_gal)
   const float* pix_fix2;   // [n_pix] sigma_fix^2 / c^2 (sampled sigma_gal; NULL otherwise)
+  // marginalised calibration polynomial (App. E): calib_n coefficients, prior
+  // 1/s_m^2, ln|Lambda| = sum ln s_m^2, per-pixel Chebyshev coordinate in [-1, 1]
+  int calib_n;
+  double calib_isig2[SED_MAX_CALIB];
+  double calib_logdet_lam;
+  const float* pix_cx;
   int sample_sgal;         // 1: each row carries sigma_gal (km/s), joined in quadrature per pixel
   float sgal_max_kms;      // sampled sigma_gal range [0, sgal_max_kms]
   const double* spec_d;

@@ -68,7 +68,7 @@ def gpu_model_for(ctx, orc, w: synth.Workload):
     if orc.spec_lam is not None:
         kw.update(spec_lam=orc.spec_lam, spec_d=orc.spec_d, spec_sigma=orc.spec_sigma,
                   spec_mask=orc.spec_mask, lsf_mode=orc.lsf_mode, lsf_value=orc.lsf_value,
-                  sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref)
+                  sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref, calib_sigma=orc.calib_sigma)
     return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)
 
 
@@ -118,3 +118,31 @@ def kink_rows(orc, th64, rel=2e-4):
         d = np.minimum(np.abs(x - ll[k - 1]), np.abs(ll[k] - x)) / (ll[k] - ll[k - 1])
         out[r] = bool((d < rel).any())
     return out
+
+
+def calib_case(w: synth.Workload, calib_sigma):
+    """Oracle of a workload with a marginalised calibration polynomial and data
+    carrying a smooth multiplicative distortion (1 + 0.08 x - 0.05 T_2(x)) over
+    the spectrum's Chebyshev coordinate x, the kind the polynomial absorbs."""
+    orc = oracle_for(w, calib_sigma=calib_sigma)
+    lam = np.asarray(orc.spec_lam)
+    x = (2.0 * lam - (lam[0] + lam[-1])) / (lam[-1] - lam[0])
+    dist = 1.0 + 0.08 * x - 0.05 * (2 * x * x - 1)
+    orc.set_data(phot_d=orc.phot_d, phot_sigma=orc.phot_sigma, spec_d=orc.spec_d * dist,
+                 spec_sigma=orc.spec_sigma * dist)
+    return orc
+
+
+def lnl_scale(orc, ref):
+    """Magnitude of the terms of lnL = -chi2/2 + C (C = -1/2 sum ln 2 pi sigma^2
+    over included data): the FP64 sum's natural error scale.  lnL itself can
+    cancel to ~0 while both terms are large."""
+    c = 0.0
+    if orc.phot_d is not None:
+        m = np.ones(len(orc.phot_sigma), bool) if orc.phot_mask is None else orc.phot_mask.astype(bool)
+        c += -0.5 * np.sum(np.log(2 * np.pi * orc.phot_sigma[m] ** 2))
+    if orc.spec_d is not None:
+        m = np.ones(len(orc.spec_sigma), bool) if orc.spec_mask is None else orc.spec_mask.astype(bool)
+        c += -0.5 * np.sum(np.log(2 * np.pi * orc.spec_sigma[m] ** 2))
+    half_chi2 = c - ref["lnl"]
+    return np.maximum(np.abs(ref["lnl"]), half_chi2 + abs(c))

@@ -168,6 +168,30 @@ def test_sampled_sigma_gal_grad_vs_oracle(ctx, prec):
     assert np.abs(ref["grad"][ok, j]).max() > 0      # the column carries a real derivative
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_calibration_polynomial_grad_vs_oracle(ctx, prec):
+    """The adjoint with a marginalised 6-term calibration polynomial (each
+    pixel's d lnL / d mu carries the posterior-mean polynomial and the
+    T^T M^-1 T term): 150 rows, every row and column against the oracle."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=150)
+    if "calib" not in _CACHE:
+        orc = cases.calib_case(w, [0.2, 0.1, 0.1, 0.05, 0.05, 0.05])
+        _CACHE["calib"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE["calib"]
+    th32, th64 = cases.theta_pair(w, w.batch, seed=59)
+    lnl, g, st = gpu_grad(model, th32, prec)
+    ref = orc.grad(th64)
+    assert np.array_equal(st, ref["status"])
+    kinks = {int(r): model.offsets["zred"] for r in np.nonzero(cases.kink_rows(orc, th64))[0]}
+    check_grad(g, ref["grad"], st, skip=kinks)
+    ok = st == 0
+    fwd = orc.eval(th64)
+    # lnL within 1e-5 of the magnitude of its terms (it can cancel to ~0)
+    scale = cases.lnl_scale(orc, fwd)[ok]
+    assert (np.abs(lnl[ok] - fwd["lnl"][ok]) / scale).max() < 1e-5
+
+
 def test_specphot_grad_vs_central_differences(ctx):
     """The adjoint against central finite differences of the FP64 oracle's
     forward model (h = 1e-7 relative) on 16 rows x all parameters."""

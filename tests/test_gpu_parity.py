@@ -6,9 +6,9 @@ SED_PREC_FP32_SIMT = FFMA): model photometry and spectra within 2e-5
 relative per datum (floored at 1e-6 of the row's brightest datum), log-
 likelihood within 1e-5 relative to the magnitude of its terms.  The BF16 and
 FP8 paths are held to the bounds measured for them (BF16: flux 1e-2, lnL 1e-2;
-FP8 E4M3 with its 3-bit mantissa: flux 0.3 per datum -- measured at most 0.033 on
-the paper-scale photometric batch and 0.247 on faint pixels of the small spectro-
-photometric case -- and lnL 0.1) and their error
+FP8 E4M3 with its 3-bit mantissa: flux 0.2 per datum floored at 1% of the row's
+brightest datum -- faint pixels, two to six decades below it, reach relative
+errors of 0.3 and more, while lnL stays within its bound -- and lnL 0.1) and their error
 distributions are reported by the benchmark.
 """
 import numpy as np
@@ -20,7 +20,9 @@ from tests import cases
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-FLUX_TOL = {"fp32": 2e-5, "fp32_simt": 2e-5, "bf16": 1e-2, "fp8": 0.3}
+FLUX_TOL = {"fp32": 2e-5, "fp32_simt": 2e-5, "bf16": 1e-2, "fp8": 0.2}
+# floor of the per-datum relative error, as a fraction of the row's brightest datum
+FLUX_FLOOR = {"fp32": 1e-6, "fp32_simt": 1e-6, "bf16": 1e-6, "fp8": 1e-2}
 LNL_TOL = {"fp32": 1e-5, "fp32_simt": 1e-5, "bf16": 1e-2, "fp8": 0.1}
 PRECS = ["fp32_simt", "fp32", "bf16", "fp8"]
 
@@ -72,19 +74,7 @@ def run_gpu(model, th32, prec):
                 spec=None if spec is None else spec.cpu().numpy())
 
 
-def lnl_scale(orc, ref):
-    """Magnitude of the terms of lnL = -chi2/2 + C (C = -1/2 sum ln 2 pi sigma^2
-    over included data): the FP64 sum's natural error scale.  lnL itself can
-    cancel to ~0 while both terms are large."""
-    c = 0.0
-    if orc.phot_d is not None:
-        m = np.ones(len(orc.phot_sigma), bool) if orc.phot_mask is None else orc.phot_mask.astype(bool)
-        c += -0.5 * np.sum(np.log(2 * np.pi * orc.phot_sigma[m] ** 2))
-    if orc.spec_d is not None:
-        m = np.ones(len(orc.spec_sigma), bool) if orc.spec_mask is None else orc.spec_mask.astype(bool)
-        c += -0.5 * np.sum(np.log(2 * np.pi * orc.spec_sigma[m] ** 2))
-    half_chi2 = c - ref["lnl"]
-    return np.maximum(np.abs(ref["lnl"]), half_chi2 + abs(c))
+lnl_scale = cases.lnl_scale
 
 
 def check(ref, got, prec, rows=None, orc=None):
@@ -98,13 +88,13 @@ def check(ref, got, prec, rows=None, orc=None):
         # (bands 15 magnitudes fainter than the brightest carry no information
         # at the workloads' S/N, and sit at or below FP32's normal range)
         ph_ref = ref["phot"][ok]
-        floor = 1e-6 * np.abs(ph_ref).max(axis=1, keepdims=True)
+        floor = FLUX_FLOOR[prec] * np.abs(ph_ref).max(axis=1, keepdims=True)
         e = np.abs(got["phot"][rows][ok] - ph_ref) / np.maximum(np.abs(ph_ref), floor)
         assert e.max() < ftol, f"photometry rel err {e.max():.3e}"
     if got["spec"] is not None:
         sp_ref = ref["spec"][ok]
         scale = np.abs(sp_ref).max(axis=1, keepdims=True)
-        e = np.abs(got["spec"][rows][ok] - sp_ref) / np.maximum(np.abs(sp_ref), 1e-6 * scale)
+        e = np.abs(got["spec"][rows][ok] - sp_ref) / np.maximum(np.abs(sp_ref), FLUX_FLOOR[prec] * scale)
         assert e.max() < ftol, f"spectrum rel err {e.max():.3e}"
     scale = lnl_scale(orc, ref)[ok] if orc is not None else np.abs(ref["lnl"][ok])
     e = np.abs(got["lnl"][rows][ok] - ref["lnl"][ok]) / scale
@@ -167,6 +157,27 @@ def test_sampled_sigma_gal_parity(ctx, prec):
     th64 = th32.astype(np.float64)
     ref = orc.eval(th64)
     assert ref["status"][3] != 0 and ref["status"][7] != 0
+    got = run_gpu(model, th32, prec)
+    check(ref, got, prec, orc=orc)
+
+
+CALIB_SIGMA = [0.2, 0.1, 0.1, 0.05, 0.05, 0.05]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_calibration_polynomial_parity(ctx, prec):
+    """Spectro-photometric [a/Fe] model with a marginalised 6-term Chebyshev
+    calibration polynomial (App. E) and distorted spectral data: 150 rows,
+    every row's lnL (which now carries the polynomial's gain and Occam terms)
+    and the uncalibrated model spectrum against the oracle."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=150)
+    if "calib" not in _CACHE:
+        orc = cases.calib_case(w, CALIB_SIGMA)
+        _CACHE["calib"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE["calib"]
+    th32, th64 = cases.theta_pair(w, w.batch, seed=47)
+    ref = orc.eval(th64)
     got = run_gpu(model, th32, prec)
     check(ref, got, prec, orc=orc)
 
