@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "phot_107x12x6000_b1024"
 GRAD_WORKLOAD = "specphot_afe_107x12x5x6000_b2048"
 SGAL_WORKLOAD = "specphot_afe_sgal_107x12x5x6000_b2048"   # the same with a sampled sigma_gal
+CALIB_WORKLOAD = "specphot_afe_calib13_107x12x5x6000_b2048"  # the same with a 13-term calibration polynomial
 PRECS = ("fp32", "fp32_simt", "bf16", "fp8")
 PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
              "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
@@ -140,6 +141,8 @@ def build_workload(wname, ctx, seed_rows, device):
     kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
               phot_d=np.ones(nb), phot_sigma=np.ones(nb), sample_sigma_gal=w.sample_sigma_gal,
               sigma_gal_max_kms=w.sigma_gal_max_kms)
+    if w.spectrum is not None and w.extra.get("calib_sigma"):
+        kw.update(calib_sigma=np.asarray(w.extra["calib_sigma"]))
     spec = None
     if w.spectrum is not None:
         sp = w.spectrum
@@ -434,6 +437,19 @@ def bench_gradient(ctx, device, flush, args):
     gsm = time_replays(gs, s, max(5, args.steps // 4), flush)
     fs = capture_step(lambda st: model_s.loglike(ts, "fp32", stream=st, out=lnl, status=stt), s)
     fsm = time_replays(fs, s, max(5, args.steps // 4), flush)
+    # and with a marginalised 13-term calibration polynomial on the spectrum
+    wc, _, _, model_c, theta_c, _ = build_workload(CALIB_WORKLOAD, ctx, 4, device)
+    tc = torch.from_numpy(theta_c).to(device)
+    grad_c = torch.empty_like(tc)
+    gc = capture_step(lambda st: model_c.loglike_grad(tc, "fp32", stream=st, out=(lnl, grad_c, stt)), s)
+    gcm = time_replays(gc, s, max(5, args.steps // 4), flush)
+    fc = capture_step(lambda st: model_c.loglike(tc, "fp32", stream=st, out=lnl, status=stt), s)
+    fcm = time_replays(fc, s, max(5, args.steps // 4), flush)
+    res["calibration_polynomial"] = {"workload": wc.name, "n_coef": len(wc.extra["calib_sigma"]),
+                                     "grad_evals_per_s": round(B * len(gcm) / (sum(gcm) * 1e-3), 1),
+                                     "grad_ms_per_step": round(sum(gcm) / len(gcm), 4),
+                                     "loglike_evals_per_s": round(B * len(fcm) / (sum(fcm) * 1e-3), 1),
+                                     "loglike_ms_per_step": round(sum(fcm) / len(fcm), 4)}
     res["sampled_sigma_gal"] = {"workload": ws.name, "n_param": int(theta_s.shape[1]),
                                 "sigma_gal_kms": list(ws.ranges["sigma_gal"]),
                                 "grad_evals_per_s": round(B * len(gsm) / (sum(gsm) * 1e-3), 1),

@@ -299,6 +299,11 @@ _s = WORKLOADS["specphot_afe_107x12x5x6000_b2048"]
 WORKLOADS["specphot_afe_sgal_107x12x5x6000_b2048"] = Workload(**{
     **_s.__dict__, "name": "specphot_afe_sgal_107x12x5x6000_b2048", "sample_sigma_gal": 1,
     "sigma_gal_max_kms": 600.0, "ranges": {**_s.ranges, "sigma_gal": (50.0, 500.0)}})
+# the same fit with a marginalised 12th-order Chebyshev calibration polynomial
+# on the spectrum (App. E; the paper's spectral demonstrations use 12th order)
+WORKLOADS["specphot_afe_calib13_107x12x5x6000_b2048"] = Workload(**{
+    **_s.__dict__, "name": "specphot_afe_calib13_107x12x5x6000_b2048",
+    "extra": {"calib_sigma": [0.2] + [0.1] * 12}})
 # mixed-precision contraction: the paper-scale photometric batch at 4096 rows
 _w = WORKLOADS["phot_107x12x6000_b1024"]
 WORKLOADS["phot_107x12x6000_b4096"] = Workload(**{**_w.__dict__, "name": "phot_107x12x6000_b4096",
