@@ -6,18 +6,30 @@
 //   b_a  = sum_i w_i mu_i r_i T_a(x_i),   w_i = 1/sigma_i^2,  r_i = d_i - mu_i,
 // over the included pixels.  With T_a T_b = (T_{a+b} + T_{|a-b|}) / 2 the
 // Gram matrix needs only the 2n-1 moments S_k = sum_i w_i mu_i^2 T_k(x_i).
+//
+// The kernels evaluate it through the equivalent form at the optimum
+// c* = M^-1 b (ridge least squares):
+//   lnL_diag(r) + b^T M^-1 b / 2 = sum_i -((r_i - mu_i p_i) / sigma_i)^2 / 2 + const
+//                                  - c*^T Lambda^-1 c* / 2,   p_i = sum_m c*_m T_m(x_i),
+// which is stationary in c*, so rounding in c* enters lnL only at second
+// order; the gradient takes c* at first order.  Everything runs in FP32 on the
+// normalised values m_i = mu_i/sigma_i and r_i/sigma_i (of the order of the
+// S/N; GB300 issues FP64 at a small fraction of the FP32 rate): c* from the
+// FP32 moments, then one step of iterative refinement whose residual
+//   b - M c = sum_i T(x_i) m_i (r_i/sigma_i - m_i p_i) - Lambda^-1 c
+// is summed pixel by pixel, from each pixel's calibrated residual, so that it
+// carries no rounding of M (which the condition number of M would amplify).
 #pragma once
 #include "sed_internal.cuh"
 
 namespace sed {
 
 constexpr int CAL_NS = 2 * SED_MAX_CALIB - 1;   // moments S_k
-constexpr int CAL_NV = CAL_NS + SED_MAX_CALIB;  // S_k then b_a
+constexpr int CAL_NV = CAL_NS + SED_MAX_CALIB;  // S_k then b_a (or the refinement residual)
 
 // One pixel's share of a block of NK consecutive sums: moments k = K0 .. K0+NK-1
-// of coef * T_k(x), up to k < kmax (the moments S use coef = w mu^2 and
-// kmax = 2n - 1, the vector b uses coef = w mu r and kmax = n).  The sums are
-// taken in blocks of SED_MAX_CALIB to keep few of them live at a time.
+// of coef * T_k(x), up to k < kmax.  The sums are taken in blocks of
+// SED_MAX_CALIB to keep few of them live at a time.
 template <int K0, int NK>
 __device__ __forceinline__ void calib_accumulate(float x, float coef, int kmax, float (&v)[NK]) {
   float tp = 1.f, tc = x;   // T_{k-1}, T_k for k = 1
@@ -31,70 +43,122 @@ __device__ __forceinline__ void calib_accumulate(float x, float coef, int kmax, 
   }
 }
 
-// One block of calibration sums over the thread's own pixels (mu_s[i] != 0 for
-// an included pixel): B = 0 gives the moments S_K0 .. S_K0+12 of w mu^2,
-// B = 1 the vector b of w mu r; per-warp FP64 totals into part[warp][...].
+// p = sum_m c_m T_m(x) for one pixel (n terms)
+__device__ __forceinline__ float calib_poly(const float* c, int n, float x) {
+  float p = c[0], tp = 1.f, tc = x;
+#pragma unroll
+  for (int a = 1; a < SED_MAX_CALIB; ++a) {
+    if (a < n) p = fmaf(c[a], tc, p);
+    const float tn = 2.f * x * tc - tp;
+    tp = tc;
+    tc = tn;
+  }
+  return p;
+}
+
+// One block of calibration sums over the thread's own pixels, from m_i in ms_s
+// (0 for an excluded pixel) and the normalised datum d_i/sigma_i:
+//   B = 0: the moments S_K0 .. S_K0+12 of m^2,
+//   B = 1: the vector b of m r/sigma,
+//   B = 2: the refinement's pixel sums of m (r/sigma - m p), p from c.
+// Per-warp FP32 totals into part[warp][...] (B > 0: from index CAL_NS).
 template <int K0, int B, int NT>
-__device__ __forceinline__ void calib_block(const ModelDev& md, const float* mu_s, int tid, int lane, int warp,
-                                            double* part) {
+__device__ __forceinline__ void calib_block(const ModelDev& md, const float* ms_s, const float* c, int tid,
+                                            int lane, int warp, float* part) {
   constexpr int NK = SED_MAX_CALIB;
   float v[NK];
 #pragma unroll
   for (int q = 0; q < NK; ++q) v[q] = 0.f;
-  const int kmax = B ? md.calib_n : 2 * md.calib_n - 1;
+  const int n = md.calib_n;
+  const int kmax = B ? n : 2 * n - 1;
   for (int i = tid; i < md.n_pix; i += NT) {
-    const float mu = mu_s[i];
-    if (mu == 0.f) continue;
-    // w mu^2 = (mu/sigma)^2 and w mu r = (mu/sigma)(r/sigma), formed from the
-    // ratios (of the order of the S/N: cgs fluxes and 1/sigma^2 overflow FP32)
-    const double is = md.spec_isig[i];
-    const float mw = (float)((double)mu * is);
-    const float coef = B ? mw * (float)((md.spec_d[i] - (double)mu) * is) : mw * mw;
-    calib_accumulate<K0, NK>(md.pix_cx[i], coef, kmax, v);
+    const float m = ms_s[i];
+    if (m == 0.f) continue;
+    const float x = md.pix_cx[i];
+    float coef;
+    if (B == 0) coef = m * m;
+    else if (B == 1) coef = m * (md.spec_dn[i] - m);
+    else coef = m * fmaf(-m, calib_poly(c, n, x), md.spec_dn[i] - m);
+    calib_accumulate<K0, NK>(x, coef, kmax, v);
   }
   const int base = B ? CAL_NS : K0;
 #pragma unroll
   for (int q = 0; q < NK; ++q) {
     if (base + q >= (B ? CAL_NV : CAL_NS)) break;
-    double x = (double)v[q];
+    float x = v[q];
 #pragma unroll
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) part[warp * CAL_NV + base + q] = x;
   }
 }
 
-// Cholesky solve of the n x n system from the summed moments (one thread,
-// FP64).  Writes the lower factor L (row-major n x n) and c* = M^-1 b; returns
-// the lnL terms, or NaN when M is not positive definite.
-__device__ inline double calib_solve(const ModelDev& md, const double* S, const double* B, double* L, double* c) {
+// Sum of the per-warp partials into row 0, in warp order, of entries [q0, q1).
+__device__ __forceinline__ void calib_sum_warps(float* part, int nwarps, int q0, int q1) {
+  for (int q = q0; q < q1; ++q)
+    for (int w = 1; w < nwarps; ++w) part[q] += part[w * CAL_NV + q];
+}
+
+// M from the moments S (row 0 of the partials), factored in place into its
+// Cholesky factor L (lower triangle of the row-major n x n array L), by one
+// thread.  Returns -ln|M| / 2 - ln|Lambda| / 2 (ln|M| = 2 sum ln L_jj), or NaN
+// when M is not positive definite.
+__device__ inline double calib_factor(const ModelDev& md, const float* S, float* L) {
   const int n = md.calib_n;
-  double logdet = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j)
+      L[i * n + j] = 0.5f * (S[i + j] + S[i - j]) + (i == j ? (float)md.calib_isig2[i] : 0.f);
+  float logdet = 0.f;
   for (int j = 0; j < n; ++j) {
-    double d = 0.5 * (S[2 * j] + S[0]) + md.calib_isig2[j];
-    for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
-    if (!(d > 0.0)) return NAN;
-    const double ljj = sqrt(d);
+    float d = L[j * n + j];
+    for (int k = 0; k < j; ++k) d = fmaf(-L[j * n + k], L[j * n + k], d);
+    if (!(d > 0.f)) return NAN;
+    const float ljj = sqrtf(d), inv = 1.f / ljj;
     L[j * n + j] = ljj;
-    logdet += log(d);
+    logdet += 2.f * logf(ljj);
     for (int i = j + 1; i < n; ++i) {
-      double v = 0.5 * (S[i + j] + S[i - j]);
-      for (int k = 0; k < j; ++k) v -= L[i * n + k] * L[j * n + k];
-      L[i * n + j] = v / ljj;
+      float v = L[i * n + j];
+      for (int k = 0; k < j; ++k) v = fmaf(-L[i * n + k], L[j * n + k], v);
+      L[i * n + j] = v * inv;
     }
   }
+  return -0.5 * (double)logdet - 0.5 * md.calib_logdet_lam;
+}
+
+// c += (L L^T)^-1 rhs, by one thread (forward then back substitution).
+__device__ inline void calib_subst_add(const float* L, int n, const float* rhs, float* c) {
+  float y[SED_MAX_CALIB];
   for (int i = 0; i < n; ++i) {
-    double v = B[i];
-    for (int k = 0; k < i; ++k) v -= L[i * n + k] * c[k];
-    c[i] = v / L[i * n + i];
+    float v = rhs[i];
+    for (int k = 0; k < i; ++k) v = fmaf(-L[i * n + k], y[k], v);
+    y[i] = v / L[i * n + i];
   }
   for (int i = n - 1; i >= 0; --i) {
-    double v = c[i];
-    for (int k = i + 1; k < n; ++k) v -= L[k * n + i] * c[k];
-    c[i] = v / L[i * n + i];
+    float v = y[i];
+    for (int k = i + 1; k < n; ++k) v = fmaf(-L[k * n + i], y[k], v);
+    y[i] = v / L[i * n + i];
   }
-  double quad = 0.0;
-  for (int a = 0; a < n; ++a) quad += B[a] * c[a];
-  return 0.5 * quad - 0.5 * logdet - 0.5 * md.calib_logdet_lam;
+  for (int i = 0; i < n; ++i) c[i] += y[i];
+}
+
+// The refinement residual b - M c from the pixel sums (row 0 of the partials,
+// from index CAL_NS) minus Lambda^-1 c, its correction added to c, and the
+// prior term -c^T Lambda^-1 c / 2 of the refined c returned; one thread.
+__device__ inline double calib_refine(const ModelDev& md, const float* part, const float* L, float* c) {
+  const int n = md.calib_n;
+  float r[SED_MAX_CALIB];
+  for (int a = 0; a < n; ++a) r[a] = fmaf(-(float)md.calib_isig2[a], c[a], part[CAL_NS + a]);
+  calib_subst_add(L, n, r, c);
+  float prior = 0.f;
+  for (int a = 0; a < n; ++a) prior = fmaf(c[a] * c[a], (float)md.calib_isig2[a], prior);
+  return -0.5 * (double)prior;
+}
+
+// one included pixel's change of its diagonal lnL term under the calibration,
+// ((r/sigma)^2 - ((r - mu p)/sigma)^2) / 2 = m p (r/sigma - m p / 2), m = mu/sigma,
+// from rn = r/sigma
+__device__ __forceinline__ float calib_pixel_term(float rn, float m, float p) {
+  const float mp = m * p;
+  return mp * fmaf(-0.5f, mp, rn);
 }
 
 }  // namespace sed

@@ -53,14 +53,14 @@ __device__ __forceinline__ void put_g(const EpiBwdArgs& a, float* hi, float* lo,
 // Shared memory of one row: F and dlnL/dF over the row's node window, then a
 // union of the filter samples' brackets (photometry) and the pixels' node
 // ranges and positions (spectrum).
-// bytes of the calibration scratch: per-warp moments, the Cholesky factor and c* as floats
-constexpr size_t EB_CAL_BYTES = (size_t)EB_WARPS * CAL_NV * sizeof(double) +
+// bytes of the calibration scratch: per-warp sums, the Cholesky factor and c* as floats
+constexpr size_t EB_CAL_BYTES = (size_t)EB_WARPS * CAL_NV * sizeof(float) +
                                 (size_t)(SED_MAX_CALIB * SED_MAX_CALIB + SED_MAX_CALIB) * sizeof(float);
 
 size_t epi_bwd_smem(const EpiBwdArgs& a) {
   const size_t W = (size_t)a.md.win_max;
   const size_t samp = (size_t)a.md.n_samp * 8;    // node index + interpolation weight
-  // 4 floats + node range; with a calibration polynomial also mu, dmu/dx, dmu/ds, 1/sum w
+  // 4 floats + node range; with a calibration polynomial also mu/sigma, dmu/dx, dmu/ds, 1/sum w
   const size_t pix = (size_t)a.md.n_pix * (a.md.calib_n ? 36 : 20);
   const size_t u = ((samp > pix ? samp : pix) + 7) & ~(size_t)7;
   return ((2 * W + 3) & ~(size_t)3) * sizeof(float) + u + (a.md.calib_n ? EB_CAL_BYTES : 0);
@@ -109,20 +109,19 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   // -1 - 1/sigma (below -1): the two never meet, whatever the rounding
   float4* px4 = reinterpret_cast<float4*>(U);
   int* prg = reinterpret_cast<int*>(px4 + md.n_pix);   // node range lo | hi << 16
-  // calibration polynomial (App. E): per pixel mu (0 when excluded), dv/dx, dv/ds,
+  // calibration polynomial (App. E): per pixel mu/sigma (0 when excluded), dv/dx, dv/ds,
   // 1/sum w, then the per-warp moments, the Cholesky factor and c*
   float* mu_s = reinterpret_cast<float*>(prg + md.n_pix);
   float* dv_s = mu_s + md.n_pix;
   float* dvs_s = dv_s + md.n_pix;
   float* cw_s = dvs_s + md.n_pix;
-  double* cal_part = nullptr;
-  float *cal_Lf = nullptr, *cal_cf = nullptr;
+  float *cal_part = nullptr, *cal_Lf = nullptr, *cal_cf = nullptr;
   if (md.calib_n) {
     const size_t samp = (size_t)md.n_samp * 8, pix = (size_t)md.n_pix * 36;
     const size_t u = ((samp > pix ? samp : pix) + 7) & ~(size_t)7;
-    cal_part = reinterpret_cast<double*>(reinterpret_cast<char*>(U) + u);
+    cal_part = reinterpret_cast<float*>(reinterpret_cast<char*>(U) + u);
     cal_Lf = reinterpret_cast<float*>(cal_part + EB_WARPS * CAL_NV);
-    cal_cf = cal_Lf + SED_MAX_CALIB * SED_MAX_CALIB;
+    cal_cf = cal_Lf + SED_MAX_CALIB * SED_MAX_CALIB;   // after L
   }
   // each thread owns a contiguous run of CH window nodes (CH odd: the runs of a
   // warp fall in distinct shared-memory banks) for the node-owned gathers
@@ -266,13 +265,14 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   //      A Gaussian row's range comes from the index table alone (a superset of
   //      the nodes within 5 sigma, clamped to the window): the |u| <= 5 test
   //      decides which nodes enter the sums.
+  //      Per-pixel terms in FP32 on the normalised residual (d - mu)/sigma and
+  //      model mu/sigma; the constants -1/2 ln(2 pi sigma^2) in FP64.
   double l_spec = 0.0, um_spec = 0.0;
-  float gz_spec = 0.f, g_sgal = 0.f;
-  const double l1 = (double)rs.ln1pz_hi + (double)rs.ln1pz_lo;
+  float chi = 0.f, um_f = 0.f, gz_spec = 0.f, g_sgal = 0.f;
   const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
   for (int i = tid; i < md.n_pix; i += EB_THREADS) {
-    const double xd = md.pix_ln[i] - l1;
-    const float xh = (float)xd, xl = (float)(xd - (double)xh);
+    float xh, xl;
+    ln_rest(md.pix_ln2[i], rs.ln1pz_hi, rs.ln1pz_lo, xh, xl);
     // total dispersion: fixed, or sigma_fix composed with the row's sigma_gal (Eq. one_kernel)
     const float s = md.sample_sgal ? sqrtf(md.pix_fix2[i] + rs.sg_ln * rs.sg_ln) : md.pix_s[i];
     float v = 0.f, dv = 0.f, dvs = 0.f, cw = 0.f, tl = 0.f;
@@ -327,23 +327,24 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     }
     const float mi = rs.s_spec * v;
     float ci = 0.f;
-    const bool inc = valid && md.spec_isig[i] != 0.0;
+    const float isf = md.spec_isf[i];
+    const bool inc = valid && isf != 0.f;
+    const float ms = inc ? mi * isf : 0.f;   // mu / sigma
+    const float rn = md.spec_dn[i] - ms;     // (d - mu) / sigma where included
+    if (inc) {
+      chi = fmaf(-0.5f * rn, rn, chi);
+      l_spec += md.spec_nlog[i];
+    }
     if (md.calib_n) {
       // the weights need the whole row's calibration solve: keep what they use
-      if (inc) {
-        const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
-        l_spec += -0.5 * rr * rr + md.spec_nlog[i];
-      }
-      mu_s[i] = inc ? mi : 0.f;
+      mu_s[i] = ms;
       dv_s[i] = dv;
       dvs_s[i] = dvs;
       cw_s[i] = cw;
     } else if (inc) {
-      const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
-      l_spec += -0.5 * rr * rr + md.spec_nlog[i];
-      const double ui = rr * md.spec_isig[i];
-      um_spec += ui * (double)mi;
-      const float us = (float)(ui * (double)rs.s_spec);
+      // d lnL / d mu_i = r_i / sigma_i^2; d lnL / d v_i = that x s_spec (mu = s_spec v)
+      um_f = fmaf(rn, ms, um_f);
+      const float us = rn * (isf * rs.s_spec);
       gz_spec += us * dv * (-rs.inv1pz);
       // s = sqrt(sigma_fix^2 + sigma_gal^2) / c: ds/dsigma_gal = (sigma_gal / c) / (s c)
       if (md.sample_sgal && s > 0.f) g_sgal += us * dvs * (rs.sg_ln / (s * (float)C_KMS));
@@ -354,28 +355,35 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   }
   if (md.calib_n) {
     // ---- marginalised calibration (App. E): moments over this thread's own
-    //      pixels, one solve per row, then each included pixel's
-    //      d lnL / d mu_i = [(d_i - mu_i (1 + p_i)) (1 + p_i) - mu_i q_i] / sigma_i^2,
+    //      pixels, one solve per row, then each included pixel's lnL change
+    //      (calib_pixel_term) and
+    //      d lnL / d mu_i = [(d_i - mu_i (1 + p_i)) (1 + p_i) - mu_i q_i] / sigma_i^2
+    //      (all in FP32 on the normalised values),
     //      p = A c*, q_i = |L^-1 T(x_i)|^2 (M = L L^T)
-    calib_block<0, 0, EB_THREADS>(md, mu_s, tid, lane, warp, cal_part);
-    calib_block<SED_MAX_CALIB, 0, EB_THREADS>(md, mu_s, tid, lane, warp, cal_part);
-    calib_block<0, 1, EB_THREADS>(md, mu_s, tid, lane, warp, cal_part);
+    calib_block<0, 0, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
+    calib_block<SED_MAX_CALIB, 0, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
+    calib_block<0, 1, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
     __syncthreads();
     if (tid == 0) {
-      for (int q = 0; q < CAL_NV; ++q)
-        for (int w = 1; w < EB_WARPS; ++w) cal_part[q] += cal_part[w * CAL_NV + q];
-      double* Ld = cal_part + CAL_NV;   // warps 1.. of the moments are no longer needed
-      double cd[SED_MAX_CALIB];
-      l_spec += calib_solve(md, cal_part, cal_part + CAL_NS, Ld, cd);
-      const int n = md.calib_n;
-      for (int q = 0; q < n * n; ++q) cal_Lf[q] = (float)Ld[q];
-      for (int q = 0; q < n; ++q) cal_cf[q] = (float)cd[q];
+      calib_sum_warps(cal_part, EB_WARPS, 0, CAL_NV);
+      l_spec += calib_factor(md, cal_part, cal_Lf);
+      for (int q = 0; q < md.calib_n; ++q) cal_cf[q] = 0.f;
+      calib_subst_add(cal_Lf, md.calib_n, cal_part + CAL_NS, cal_cf);
+    }
+    __syncthreads();
+    // one refinement of c* from the pixels' calibrated residuals (the gradient
+    // takes c* at first order)
+    calib_block<0, 2, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
+    __syncthreads();
+    if (tid == 0) {
+      calib_sum_warps(cal_part, EB_WARPS, CAL_NS, CAL_NV);
+      l_spec += calib_refine(md, cal_part, cal_Lf, cal_cf);
     }
     __syncthreads();
     const int n = md.calib_n;
     for (int i = tid; i < md.n_pix; i += EB_THREADS) {
-      const float mu = mu_s[i];
-      if (mu == 0.f) continue;
+      const float m = mu_s[i];
+      if (m == 0.f) continue;
       const float x = md.pix_cx[i];
       float T[SED_MAX_CALIB], y[SED_MAX_CALIB];
       float p = 0.f, q = 0.f, tp = 1.f, tc = x;
@@ -395,10 +403,12 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
           q = fmaf(y[a], y[a], q);
         }
       }
-      const double is = md.spec_isig[i];
-      const double ui = ((md.spec_d[i] - (double)mu * (1.0 + p)) * (1.0 + p) - (double)mu * q) * is * is;
-      um_spec += ui * (double)mu;
-      const float us = (float)(ui * (double)rs.s_spec);
+      // sigma_i d lnL / d mu_i = (r_i - mu_i p_i)(1 + p_i)/sigma_i - (mu_i/sigma_i) q_i
+      const float rn = md.spec_dn[i] - m;
+      chi += calib_pixel_term(rn, m, p);
+      const float ws = fmaf(rn - m * p, 1.f + p, -m * q);
+      um_f = fmaf(ws, m, um_f);
+      const float us = ws * (md.spec_isf[i] * rs.s_spec);
       gz_spec += us * dv_s[i] * (-rs.inv1pz);
       if (md.sample_sgal) {
         const float s = sqrtf(md.pix_fix2[i] + rs.sg_ln * rs.sg_ln);
@@ -407,6 +417,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       px4[i].z = us * cw_s[i];
     }
   }
+  l_spec += (double)chi;
+  um_spec += (double)um_f;
   __syncthreads();
 
   // ---- dlnL/dF from the spectrum: node k gathers, in pixel order, every

@@ -52,8 +52,9 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   const int WIN = MULTI ? a.smem_win : md.win_max;
   __shared__ float mb_s[MAX_BANDS];
   __shared__ double red[EPI_WARPS];
-  __shared__ double cal_part[EPI_WARPS][CAL_NV];   // per-warp calibration moments
-  __shared__ double cal_L[SED_MAX_CALIB * SED_MAX_CALIB], cal_c[SED_MAX_CALIB];
+  __shared__ float cal_part[EPI_WARPS][CAL_NV];    // per-warp calibration sums
+  __shared__ float cal_L[SED_MAX_CALIB * SED_MAX_CALIB], cal_c[SED_MAX_CALIB];   // Cholesky factor of M, c*
+  __shared__ double cal_fix;                       // the row's lnL terms that do not sum over pixels
 
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);   // nodes [k_lo, k_hi] are the only ones read below
   float2* LG = reinterpret_cast<float2*>(smem4) - k_lo;               // {rest-frame lambda, F / lam^2}
   float* Fs = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem4) + WIN) - k_lo;   // F (spectral arm only)
-  float* mu_s = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem4) + WIN) + WIN;  // calibration: included pixels' mu
+  float* mu_s = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem4) + WIN) + WIN;  // calibration: included pixels' mu/sigma (0 elsewhere)
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
     const float4 c = g.att4[k];
@@ -141,12 +142,14 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   }
 
   // ---- spectrum: one thread per pixel
+  // per-pixel terms in FP32 on the normalised residual (d - mu)/sigma; the
+  // constants -1/2 ln(2 pi sigma^2) in FP64
   double part = 0.0;
-  const double l1 = (double)rs.ln1pz_hi + (double)rs.ln1pz_lo;
+  float chi = 0.f;
   const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
   for (int i = tid; i < md.n_pix; i += blockDim.x) {
-    const double xd = md.pix_ln[i] - l1;
-    const float xh = (float)xd, xl = (float)(xd - (double)xh);
+    float xh, xl;
+    ln_rest(md.pix_ln2[i], rs.ln1pz_hi, rs.ln1pz_lo, xh, xl);
     float v = 0.f;
     bool valid = false;
     if (xh >= ll0 && xh <= llN) {
@@ -177,24 +180,58 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     }
     const float mi = rs.s_spec * v;
     if (a.spec_out) a.spec_out[(size_t)ro * md.n_pix + i] = mi;
-    const bool inc = valid && md.spec_isig[i] != 0.0;
+    const float isf = md.spec_isf[i];
+    const bool inc = valid && isf != 0.f;
+    const float ms = inc ? mi * isf : 0.f;   // mu / sigma
     if (inc) {
-      const double rr = (md.spec_d[i] - (double)mi) * md.spec_isig[i];
-      part += -0.5 * rr * rr + md.spec_nlog[i];
+      const float rn = md.spec_dn[i] - ms;   // (d - mu) / sigma
+      chi = fmaf(-0.5f * rn, rn, chi);
+      part += md.spec_nlog[i];
     }
-    if (md.calib_n) mu_s[i] = inc ? mi : 0.f;
+    if (md.calib_n) mu_s[i] = ms;
   }
+  part += (double)chi;
   // calibration moments over this thread's own pixels (no barrier needed),
-  // in three blocks of sums (S_0..12, S_13..24, b_0..12), each summed per warp in FP64
+  // in three blocks of sums (S_0..12, S_13..24, b_0..12), each summed per warp
   if (md.calib_n) {
-    calib_block<0, 0, EPI_THREADS>(md, mu_s, tid, lane, warp, &cal_part[0][0]);
-    calib_block<SED_MAX_CALIB, 0, EPI_THREADS>(md, mu_s, tid, lane, warp, &cal_part[0][0]);
-    calib_block<0, 1, EPI_THREADS>(md, mu_s, tid, lane, warp, &cal_part[0][0]);
+    calib_block<0, 0, EPI_THREADS>(md, mu_s, cal_c, tid, lane, warp, &cal_part[0][0]);
+    calib_block<SED_MAX_CALIB, 0, EPI_THREADS>(md, mu_s, cal_c, tid, lane, warp, &cal_part[0][0]);
+    calib_block<0, 1, EPI_THREADS>(md, mu_s, cal_c, tid, lane, warp, &cal_part[0][0]);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if (lane == 0) red[warp] = part;
   __syncthreads();
+  if (md.calib_n) {
+    // sum the warps' moments in warp order into row 0, factor M and solve for
+    // c*; refine c* once from the pixels' calibrated residuals; then each
+    // included pixel's change of its term under the polynomial p = A c*
+    if (tid == 0) {
+      calib_sum_warps(&cal_part[0][0], EPI_WARPS, 0, CAL_NV);
+      cal_fix = calib_factor(md, &cal_part[0][0], cal_L);
+      for (int q = 0; q < md.calib_n; ++q) cal_c[q] = 0.f;
+      calib_subst_add(cal_L, md.calib_n, &cal_part[0][CAL_NS], cal_c);
+    }
+    __syncthreads();
+    calib_block<0, 2, EPI_THREADS>(md, mu_s, cal_c, tid, lane, warp, &cal_part[0][0]);
+    __syncthreads();
+    if (tid == 0) {
+      calib_sum_warps(&cal_part[0][0], EPI_WARPS, CAL_NS, CAL_NV);
+      cal_fix += calib_refine(md, &cal_part[0][0], cal_L, cal_c);
+    }
+    __syncthreads();
+    float cpf = 0.f;
+    for (int i = tid; i < md.n_pix; i += EPI_THREADS) {
+      const float ms = mu_s[i];
+      if (ms == 0.f) continue;
+      cpf += calib_pixel_term(md.spec_dn[i] - ms, ms, calib_poly(cal_c, md.calib_n, md.pix_cx[i]));
+    }
+    double cp = (double)cpf;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, o);
+    if (lane == 0) red[warp] += cp;
+    __syncthreads();
+  }
   // photometric terms in FP64, one band per lane of warp 0 (GB300's FP64 pipe
   // is narrow: one warp instruction serves all bands)
   if (warp == 0) {
@@ -210,12 +247,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     if (lane == 0) {
       double tot = pv;
       for (int w = 0; w < EPI_WARPS; ++w) tot += red[w];
-      if (md.calib_n) {
-        // sum the warps' moments in warp order into row 0, then solve
-        for (int q = 0; q < CAL_NV; ++q)
-          for (int w = 1; w < EPI_WARPS; ++w) cal_part[0][q] += cal_part[w][q];
-        tot += calib_solve(md, &cal_part[0][0], &cal_part[0][CAL_NS], cal_L, cal_c);
-      }
+      if (md.calib_n) tot += cal_fix;
       uint32_t st = 0;
       if (!isfinite(tot)) { st = SED_ROW_NONFINITE; tot = -INFINITY; }
       if (a.lnl) a.lnl[ro] = tot;

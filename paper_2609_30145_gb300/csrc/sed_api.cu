@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 
 #include "sed_internal.cuh"
@@ -599,19 +600,25 @@ sed_status set_data_dev(sed_ctx* ctx, Model* M, const double* pd, const double* 
   }
   if (sd || ss) {
     const int np = dv.n_pix;
-    std::vector<double> isig(np), nlog(np), dd(np);
+    std::vector<float> dn(np), isf(np);
+    std::vector<double> nlog(np);
     for (int i = 0; i < np; i++) {
       const bool on = M->spec_mask_h.empty() || M->spec_mask_h[i];
       double s = ss ? ss[i] : 1.0, dv_ = sd ? sd[i] : 0.0;
       if (on && !(std::isfinite(s) && s > 0 && std::isfinite(dv_)))
         return fail(ctx, SED_EINVAL, "spectral datum %d: sigma must be > 0 and data finite", i);
-      dd[i] = on ? dv_ : 0.0;
-      isig[i] = on ? 1.0 / s : 0.0;
+      // the kernels take d/sigma and 1/sigma in FP32: both must be finite there
+      // and 1/sigma a normal number
+      const double is = 1.0 / s, dn_ = dv_ * is;
+      if (on && !(is >= (double)FLT_MIN && is <= (double)FLT_MAX && std::fabs(dn_) <= (double)FLT_MAX))
+        return fail(ctx, SED_EINVAL, "spectral datum %d: 1/sigma and d/sigma must lie in FP32's normal range", i);
+      dn[i] = on ? (float)dn_ : 0.f;
+      isf[i] = on ? (float)is : 0.f;
       nlog[i] = on ? -0.5 * std::log(2.0 * M_PI * s * s) : 0.0;
     }
     if (np) {
-      CK(cudaMemcpy((void*)dv.spec_d, dd.data(), np * 8, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy((void*)dv.spec_isig, isig.data(), np * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy((void*)dv.spec_dn, dn.data(), np * 4, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy((void*)dv.spec_isf, isf.data(), np * 4, cudaMemcpyHostToDevice));
       CK(cudaMemcpy((void*)dv.spec_nlog, nlog.data(), np * 8, cudaMemcpyHostToDevice));
     }
   }
@@ -796,7 +803,16 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     dv.pix_s_max = (float)smax;
     double* pd;
     float* pf;
-    if (!st) { st = upload(ctx, &pd, pl.data(), pl.size(), &M->allocs, &M->bytes); dv.pix_ln = pd; }
+    std::vector<float2> pl2(np);
+    for (int i = 0; i < np; i++) {
+      pl2[i].x = (float)pl[i];
+      pl2[i].y = (float)(pl[i] - (double)pl2[i].x);
+    }
+    if (!st) {
+      float2* p2;
+      st = upload(ctx, &p2, pl2.data(), pl2.size(), &M->allocs, &M->bytes);
+      dv.pix_ln2 = p2;
+    }
     if (!st) { st = upload(ctx, &pf, ps.data(), ps.size(), &M->allocs, &M->bytes); dv.pix_s = pf; }
     if (!st && d->sample_sigma_gal) {
       st = upload(ctx, &pf, pf2.data(), pf2.size(), &M->allocs, &M->bytes);
@@ -817,8 +833,9 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
       }
     }
     std::vector<double> zeros(np, 0.0);
-    if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_d = pd; }
-    if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_isig = pd; }
+    std::vector<float> zerof(np, 0.f);
+    if (!st) { st = upload(ctx, &pf, zerof.data(), np, &M->allocs, &M->bytes); dv.spec_dn = pf; }
+    if (!st) { st = upload(ctx, &pf, zerof.data(), np, &M->allocs, &M->bytes); dv.spec_isf = pf; }
     if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_nlog = pd; }
     if (d->spec_mask) M->spec_mask_h.assign(d->spec_mask, d->spec_mask + np);
   }

@@ -132,7 +132,7 @@ struct ModelDev {
   float samp_lam_min, samp_lam_max;
   // spectrum
   int n_pix;
-  const double* pix_ln;    // [n_pix] ln(lambda_obs)
+  const float2* pix_ln2;   // [n_pix] ln(lambda_obs) as an FP32 pair {hi, lo}, hi + lo to 2^-48
   const float* pix_s;      // [n_pix] total dispersion in ln(lambda) (fixed sigma_gal)
   const float* pix_fix2;   // [n_pix] sigma_fix^2 / c^2 (sampled sigma_gal; NULL otherwise)
   // marginalised calibration polynomial (App. E): calib_n coefficients, prior
@@ -143,8 +143,11 @@ struct ModelDev {
   const float* pix_cx;
   int sample_sgal;         // 1: each row carries sigma_gal (km/s), joined in quadrature per pixel
   float sgal_max_kms;      // sampled sigma_gal range [0, sgal_max_kms]
-  const double* spec_d;
-  const double* spec_isig;
+  // spectral data, normalised per pixel so that the per-pixel terms stay in FP32
+  // (GB300's FP64 pipe issues a warp instruction every 16 SM cycles): d/sigma
+  // and 1/sigma (both 0 where the pixel is excluded), -1/2 ln(2 pi sigma^2)
+  const float* spec_dn;
+  const float* spec_isf;
   const double* spec_nlog;
   double pix_ln_min, pix_ln_max;
   float pix_s_max;         // largest total dispersion a row can have (ln units)
@@ -305,6 +308,20 @@ struct PrepArgs {
   int* tile_win;       // [2][ceil(n/128)] union of the row windows of each 128-row tile (lo set to
                        // 0x7f7f7f7f and hi to -1 beforehand), or NULL
 };
+// A pixel's rest-frame ln(lambda) = ln(lambda_obs) - ln(1+z), both given as
+// FP32 pairs {hi, lo}, returned as an FP32 pair: the high parts' difference is
+// made exact by Knuth's two-sum (s + e = p.hi - z_hi), the low parts join its
+// error term, and a final fast two-sum renormalises.  FP32 only (the FP64 pipe
+// is the scarce one).
+__device__ __forceinline__ void ln_rest(float2 p, float z_hi, float z_lo, float& x_hi, float& x_lo) {
+  const float s = p.x - z_hi;
+  const float bv = s - p.x;
+  const float e = (p.x - (s - bv)) + (-z_hi - bv);
+  const float t = e + (p.y - z_lo);
+  x_hi = s + t;
+  x_lo = t - (x_hi - s);
+}
+
 // Programmatic dependent launch.  Every kernel of the library begins with
 // pdl_enter(): it waits until the kernel before it on the stream has completed
 // and its writes are visible, then lets the next kernel be scheduled.  Launched

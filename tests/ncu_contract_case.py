@@ -9,6 +9,9 @@ FP8, adjoint.
 ``specphot``: the [a/Fe] spectro-photometric workload (107 x 12 x 5 x 6000
 grid, 1500-pixel spectrum + 20 filters) at 512 rows: one FP32 sed_loglike and
 two FP32 sed_loglike_grad calls.
+
+``calib``: the same with a marginalised 13-term Chebyshev calibration
+polynomial on the spectrum (prior widths 0.2, then 0.1).
 """
 import os
 import sys
@@ -21,7 +24,7 @@ import synth  # noqa: E402
 from paper_2609_30145_gb300 import Context  # noqa: E402
 
 
-def specphot():
+def specphot(calib=False):
     w = synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"]
     grid = synth.make_grid(**w.grid_kw, seed=1)
     filt = synth.pack_filters(synth.workload_filters(w))
@@ -33,7 +36,8 @@ def specphot():
     m = ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, use_afe=w.use_afe, use_nebular=w.use_nebular,
                          dust_law=w.dust_law, filters=filt, phot_d=np.ones(nb), phot_sigma=np.ones(nb),
                          spec_lam=lam, spec_d=np.ones(lam.size), spec_sigma=np.ones(lam.size), lsf_mode=0,
-                         lsf_value=r, sigma_gal_kms=w.sigma_gal_kms, z_ref=w.z_ref)
+                         lsf_value=r, sigma_gal_kms=w.sigma_gal_kms, z_ref=w.z_ref,
+                         calib_sigma=np.array([0.2] + [0.1] * 12) if calib else None)
     # mock data: the model at a true row (z = 2) with 5% offsets
     d_true = synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99)
     d_true["zred"][:] = 2.0
@@ -51,8 +55,8 @@ def specphot():
 
 
 def main():
-    if len(sys.argv) > 1 and sys.argv[1] == "specphot":
-        return specphot()
+    if len(sys.argv) > 1 and sys.argv[1] in ("specphot", "calib"):
+        return specphot(calib=sys.argv[1] == "calib")
     w = synth.WORKLOADS["phot_107x12x6000_b1024"]
     grid = synth.make_grid(**w.grid_kw, seed=1)
     filt = synth.pack_filters(synth.workload_filters(w))
