@@ -188,7 +188,11 @@ sed_status sed_load_grid(sed_ctx *ctx, const sed_grid_desc *desc, sed_grid_id *o
 sed_status sed_create_model(sed_ctx *ctx, const sed_model_desc *desc, sed_model_id *out);
 /* n_param: columns a parameter row needs; offsets[SED_NKEYS]: first column of each key. */
 sed_status sed_model_layout(const sed_ctx *ctx, sed_model_id model, int *n_param, int *offsets);
-/* Replace the observed data/uncertainties of a model (host arrays, copied; NULL keeps). */
+/* Replace the observed data/uncertainties of a model (host arrays, copied).  Data and
+ * sigma come in pairs (both or neither, else SED_EINVAL); a pair passed as NULL keeps
+ * its last value, and a block never given stays out of lnL.  Every datum is checked
+ * before anything changes (SED_EINVAL: sigma <= 0 or a non-finite value; spectral
+ * 1/sigma and d/sigma outside FP32's normal range, which the kernels work in). */
 sed_status sed_set_data(sed_ctx *ctx, sed_model_id model, const double *phot_d,
                         const double *phot_sigma, const double *spec_d, const double *spec_sigma);
 sed_status sed_destroy_model(sed_ctx *ctx, sed_model_id model);

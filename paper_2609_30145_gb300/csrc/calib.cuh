@@ -92,65 +92,117 @@ __device__ __forceinline__ void calib_block(const ModelDev& md, const float* ms_
   }
 }
 
+// The small solves run on one warp, lane i holding row i of M (n <= 13 <= 32):
+// the Cholesky factor, both substitutions and the warp sums are column steps
+// with shuffles between lanes, fully unrolled so that every row stays in
+// registers.  All 32 lanes of the warp must call them together.
+
 // Sum of the per-warp partials into row 0, in warp order, of entries [q0, q1).
-__device__ __forceinline__ void calib_sum_warps(float* part, int nwarps, int q0, int q1) {
-  for (int q = q0; q < q1; ++q)
-    for (int w = 1; w < nwarps; ++w) part[q] += part[w * CAL_NV + q];
+__device__ __forceinline__ void calib_sum_warps(float* part, int nwarps, int q0, int q1, int lane) {
+  for (int q = q0 + lane; q < q1; q += 32) {
+    float v = part[q];
+    for (int w = 1; w < nwarps; ++w) v += part[w * CAL_NV + q];
+    part[q] = v;
+  }
+  __syncwarp();
 }
 
-// M from the moments S (row 0 of the partials), factored in place into its
-// Cholesky factor L (lower triangle of the row-major n x n array L), by one
-// thread.  Returns -ln|M| / 2 - ln|Lambda| / 2 (ln|M| = 2 sum ln L_jj), or NaN
-// when M is not positive definite.
-__device__ inline double calib_factor(const ModelDev& md, const float* S, float* L) {
-  const int n = md.calib_n;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j <= i; ++j)
-      L[i * n + j] = 0.5f * (S[i + j] + S[i - j]) + (i == j ? (float)md.calib_isig2[i] : 0.f);
+// M from the moments S (row 0 of the partials), factored into its Cholesky
+// factor L, written to the lower triangle of the row-major n x n array L.
+// Returns -ln|M| / 2 - ln|Lambda| / 2 (ln|M| = 2 sum ln L_jj), or NaN when M
+// is not positive definite (every lane).
+__device__ inline double calib_factor(const ModelDev& md, const float* S, float* L, int lane) {
+  const int n = md.calib_n, i = lane;
+  const float isg = i < n ? (float)md.calib_isig2[i] : 0.f;
+  float a[SED_MAX_CALIB];   // row i of M, updated in place
+#pragma unroll
+  for (int k = 0; k < SED_MAX_CALIB; ++k)
+    a[k] = (i < n && k <= i) ? 0.5f * (S[i + k] + S[i - k]) + (i == k ? isg : 0.f) : 0.f;
   float logdet = 0.f;
-  for (int j = 0; j < n; ++j) {
-    float d = L[j * n + j];
-    for (int k = 0; k < j; ++k) d = fmaf(-L[j * n + k], L[j * n + k], d);
-    if (!(d > 0.f)) return NAN;
-    const float ljj = sqrtf(d), inv = 1.f / ljj;
-    L[j * n + j] = ljj;
-    logdet += 2.f * logf(ljj);
-    for (int i = j + 1; i < n; ++i) {
-      float v = L[i * n + j];
-      for (int k = 0; k < j; ++k) v = fmaf(-L[i * n + k], L[j * n + k], v);
-      L[i * n + j] = v * inv;
+  bool pd = true;
+#pragma unroll
+  for (int j = 0; j < SED_MAX_CALIB; ++j) {
+    if (j < n) {
+      const float d = __shfl_sync(0xffffffffu, a[j], j);   // the updated diagonal, from lane j
+      pd = pd && d > 0.f;
+      const float ljj = sqrtf(d), inv = 1.f / ljj;
+      const float lij = i == j ? ljj : a[j] * inv;          // column j of L (rows i >= j)
+      if (i >= j && i < n) L[i * n + j] = lij;
+      logdet += 2.f * logf(ljj);
+#pragma unroll
+      for (int k = j + 1; k < SED_MAX_CALIB; ++k) {
+        if (k < n) {
+          const float lkj = __shfl_sync(0xffffffffu, lij, k);
+          if (i >= k) a[k] = fmaf(-lij, lkj, a[k]);
+        }
+      }
     }
   }
-  return -0.5 * (double)logdet - 0.5 * md.calib_logdet_lam;
+  __syncwarp();
+  return pd ? -0.5 * (double)logdet - 0.5 * md.calib_logdet_lam : (double)NAN;
 }
 
-// c += (L L^T)^-1 rhs, by one thread (forward then back substitution).
-__device__ inline void calib_subst_add(const float* L, int n, const float* rhs, float* c) {
-  float y[SED_MAX_CALIB];
-  for (int i = 0; i < n; ++i) {
-    float v = rhs[i];
-    for (int k = 0; k < i; ++k) v = fmaf(-L[i * n + k], y[k], v);
-    y[i] = v / L[i * n + i];
+// x = (L L^T)^-1 rhs with rhs_i in lane i; returns x_i in lane i (0 for i >= n).
+// Lane i reads row i and column i of L.
+__device__ inline float calib_subst(const float* L, int n, float rhs, int lane) {
+  const int i = lane;
+  float row[SED_MAX_CALIB], col[SED_MAX_CALIB];   // L[i][k] (k <= i), L[k][i] (k >= i)
+#pragma unroll
+  for (int k = 0; k < SED_MAX_CALIB; ++k) {
+    row[k] = (i < n && k <= i) ? L[i * n + k] : 0.f;
+    col[k] = (i < n && k < n && k >= i) ? L[k * n + i] : 0.f;
   }
-  for (int i = n - 1; i >= 0; --i) {
-    float v = y[i];
-    for (int k = i + 1; k < n; ++k) v = fmaf(-L[k * n + i], y[k], v);
-    y[i] = v / L[i * n + i];
+  float v = rhs, y = 0.f;   // forward: L y = rhs
+#pragma unroll
+  for (int k = 0; k < SED_MAX_CALIB; ++k) {
+    if (k < n) {
+      const float yk = __shfl_sync(0xffffffffu, v / row[k], k);
+      if (i == k) y = yk;
+      if (i > k) v = fmaf(-row[k], yk, v);
+    }
   }
-  for (int i = 0; i < n; ++i) c[i] += y[i];
+  float w = y, x = 0.f;     // back: L^T x = y
+#pragma unroll
+  for (int k = SED_MAX_CALIB - 1; k >= 0; --k) {
+    if (k < n) {
+      const float xk = __shfl_sync(0xffffffffu, w / col[k], k);
+      if (i == k) x = xk;
+      if (i < k) w = fmaf(-col[k], xk, w);
+    }
+  }
+  return i < n ? x : 0.f;
 }
 
-// The refinement residual b - M c from the pixel sums (row 0 of the partials,
-// from index CAL_NS) minus Lambda^-1 c, its correction added to c, and the
-// prior term -c^T Lambda^-1 c / 2 of the refined c returned; one thread.
-__device__ inline double calib_refine(const ModelDev& md, const float* part, const float* L, float* c) {
+// c* from the first solve: the moments summed, M factored, c = M^-1 b written
+// to c; returns the calib_factor value (every lane).
+__device__ inline double calib_first_solve(const ModelDev& md, float* part, int nwarps, float* L, float* c,
+                                           int lane) {
   const int n = md.calib_n;
-  float r[SED_MAX_CALIB];
-  for (int a = 0; a < n; ++a) r[a] = fmaf(-(float)md.calib_isig2[a], c[a], part[CAL_NS + a]);
-  calib_subst_add(L, n, r, c);
-  float prior = 0.f;
-  for (int a = 0; a < n; ++a) prior = fmaf(c[a] * c[a], (float)md.calib_isig2[a], prior);
-  return -0.5 * (double)prior;
+  calib_sum_warps(part, nwarps, 0, CAL_NV, lane);
+  const double f = calib_factor(md, part, L, lane);
+  const float x = calib_subst(L, n, lane < n ? part[CAL_NS + lane] : 0.f, lane);
+  if (lane < n) c[lane] = x;
+  __syncwarp();
+  return f;
+}
+
+// The refinement: residual b - M c from the pixel sums (partials from index
+// CAL_NS) minus Lambda^-1 c, its correction added to c, and the prior term
+// -c^T Lambda^-1 c / 2 of the refined c returned (every lane).
+__device__ inline double calib_refine(const ModelDev& md, float* part, int nwarps, const float* L, float* c,
+                                      int lane) {
+  const int n = md.calib_n;
+  calib_sum_warps(part, nwarps, CAL_NS, CAL_NV, lane);
+  const float isg = lane < n ? (float)md.calib_isig2[lane] : 0.f;
+  const float ca = lane < n ? c[lane] : 0.f;
+  const float r = lane < n ? fmaf(-isg, ca, part[CAL_NS + lane]) : 0.f;
+  const float cn = ca + calib_subst(L, n, r, lane);
+  if (lane < n) c[lane] = cn;
+  float pr = cn * cn * isg;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
+  __syncwarp();
+  return -0.5 * (double)pr;
 }
 
 // one included pixel's change of its diagonal lnL term under the calibration,

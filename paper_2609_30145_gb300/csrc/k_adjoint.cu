@@ -364,20 +364,18 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     calib_block<SED_MAX_CALIB, 0, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
     calib_block<0, 1, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
     __syncthreads();
-    if (tid == 0) {
-      calib_sum_warps(cal_part, EB_WARPS, 0, CAL_NV);
-      l_spec += calib_factor(md, cal_part, cal_Lf);
-      for (int q = 0; q < md.calib_n; ++q) cal_cf[q] = 0.f;
-      calib_subst_add(cal_Lf, md.calib_n, cal_part + CAL_NS, cal_cf);
+    if (warp == 0) {
+      const double f = calib_first_solve(md, cal_part, EB_WARPS, cal_Lf, cal_cf, lane);
+      if (lane == 0) l_spec += f;
     }
     __syncthreads();
     // one refinement of c* from the pixels' calibrated residuals (the gradient
     // takes c* at first order)
     calib_block<0, 2, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
     __syncthreads();
-    if (tid == 0) {
-      calib_sum_warps(cal_part, EB_WARPS, CAL_NS, CAL_NV);
-      l_spec += calib_refine(md, cal_part, cal_Lf, cal_cf);
+    if (warp == 0) {
+      const double f = calib_refine(md, cal_part, EB_WARPS, cal_Lf, cal_cf, lane);
+      if (lane == 0) l_spec += f;
     }
     __syncthreads();
     const int n = md.calib_n;

@@ -206,18 +206,16 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     // sum the warps' moments in warp order into row 0, factor M and solve for
     // c*; refine c* once from the pixels' calibrated residuals; then each
     // included pixel's change of its term under the polynomial p = A c*
-    if (tid == 0) {
-      calib_sum_warps(&cal_part[0][0], EPI_WARPS, 0, CAL_NV);
-      cal_fix = calib_factor(md, &cal_part[0][0], cal_L);
-      for (int q = 0; q < md.calib_n; ++q) cal_c[q] = 0.f;
-      calib_subst_add(cal_L, md.calib_n, &cal_part[0][CAL_NS], cal_c);
+    if (warp == 0) {
+      const double f = calib_first_solve(md, &cal_part[0][0], EPI_WARPS, cal_L, cal_c, lane);
+      if (lane == 0) cal_fix = f;
     }
     __syncthreads();
     calib_block<0, 2, EPI_THREADS>(md, mu_s, cal_c, tid, lane, warp, &cal_part[0][0]);
     __syncthreads();
-    if (tid == 0) {
-      calib_sum_warps(&cal_part[0][0], EPI_WARPS, CAL_NS, CAL_NV);
-      cal_fix += calib_refine(md, &cal_part[0][0], cal_L, cal_c);
+    if (warp == 0) {
+      const double f = calib_refine(md, &cal_part[0][0], EPI_WARPS, cal_L, cal_c, lane);
+      if (lane == 0) cal_fix += f;
     }
     __syncthreads();
     float cpf = 0.f;

@@ -580,47 +580,63 @@ void cosmo_table(double H0, double Om, double zf, int n, std::vector<double>* ou
 sed_status set_data_dev(sed_ctx* ctx, Model* M, const double* pd, const double* ps, const double* sd,
                         const double* ss) {
   ModelDev& dv = M->dv;
-  if (pd || ps) {
-    const int nb = dv.n_filt;
-    std::vector<double> isig(nb), nlog(nb), dd(nb);
-    for (int b = 0; b < nb; b++) {
-      const bool on = M->phot_mask_h.empty() || M->phot_mask_h[b];
-      double s = ps ? ps[b] : 1.0, dv_ = pd ? pd[b] : 0.0;
-      if (on && !(std::isfinite(s) && s > 0 && std::isfinite(dv_)))
-        return fail(ctx, SED_EINVAL, "photometric datum %d: sigma must be > 0 and data finite", b);
-      dd[b] = on ? dv_ : 0.0;
-      isig[b] = on ? 1.0 / s : 0.0;
-      nlog[b] = on ? -0.5 * std::log(2.0 * M_PI * s * s) : 0.0;
-    }
-    if (nb) {
-      CK(cudaMemcpy((void*)dv.phot_d, dd.data(), nb * 8, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy((void*)dv.phot_isig, isig.data(), nb * 8, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy((void*)dv.phot_nlog, nlog.data(), nb * 8, cudaMemcpyHostToDevice));
-    }
+  // a pair passed as NULL keeps its last value; one never set stays out of lnL
+  // (its device arrays hold zeros).  Copies first (a caller's array may be the
+  // kept one), then every datum checked before anything is uploaded: the call
+  // changes all or nothing
+  const bool ph = pd || ps || !M->phot_d_h.empty(), sp = sd || ss || !M->spec_d_h.empty();
+  const int nb = ph ? dv.n_filt : 0, np = sp ? dv.n_pix : 0;
+  // (sed_create_model may give data without sigma: sigma 1 then)
+  auto pick = [](const double* given, const std::vector<double>& kept, int n, double dflt) {
+    if (given) return std::vector<double>(given, given + n);
+    if (kept.size() == (size_t)n) return kept;
+    return std::vector<double>(n, dflt);
+  };
+  std::vector<double> pdv = pick(pd, M->phot_d_h, nb, 0.0), psv = pick(ps, M->phot_s_h, nb, 1.0);
+  std::vector<double> sdv = pick(sd, M->spec_d_h, np, 0.0), ssv = pick(ss, M->spec_s_h, np, 1.0);
+  std::vector<double> p_d(nb), p_isig(nb), p_nlog(nb);
+  for (int b = 0; b < nb; b++) {
+    const bool on = M->phot_mask_h.empty() || M->phot_mask_h[b];
+    const double s = psv[b], dv_ = pdv[b];
+    if (on && !(std::isfinite(s) && s > 0 && std::isfinite(dv_)))
+      return fail(ctx, SED_EINVAL, "photometric datum %d: sigma must be > 0 and data finite", b);
+    p_d[b] = on ? dv_ : 0.0;
+    p_isig[b] = on ? 1.0 / s : 0.0;
+    p_nlog[b] = on ? -0.5 * std::log(2.0 * M_PI * s * s) : 0.0;
   }
-  if (sd || ss) {
-    const int np = dv.n_pix;
-    std::vector<float> dn(np), isf(np);
-    std::vector<double> nlog(np);
-    for (int i = 0; i < np; i++) {
-      const bool on = M->spec_mask_h.empty() || M->spec_mask_h[i];
-      double s = ss ? ss[i] : 1.0, dv_ = sd ? sd[i] : 0.0;
-      if (on && !(std::isfinite(s) && s > 0 && std::isfinite(dv_)))
-        return fail(ctx, SED_EINVAL, "spectral datum %d: sigma must be > 0 and data finite", i);
-      // the kernels take d/sigma and 1/sigma in FP32: both must be finite there
-      // and 1/sigma a normal number
-      const double is = 1.0 / s, dn_ = dv_ * is;
-      if (on && !(is >= (double)FLT_MIN && is <= (double)FLT_MAX && std::fabs(dn_) <= (double)FLT_MAX))
-        return fail(ctx, SED_EINVAL, "spectral datum %d: 1/sigma and d/sigma must lie in FP32's normal range", i);
-      dn[i] = on ? (float)dn_ : 0.f;
-      isf[i] = on ? (float)is : 0.f;
-      nlog[i] = on ? -0.5 * std::log(2.0 * M_PI * s * s) : 0.0;
-    }
-    if (np) {
-      CK(cudaMemcpy((void*)dv.spec_dn, dn.data(), np * 4, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy((void*)dv.spec_isf, isf.data(), np * 4, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy((void*)dv.spec_nlog, nlog.data(), np * 8, cudaMemcpyHostToDevice));
-    }
+  std::vector<float> s_dn(np), s_isf(np);
+  std::vector<double> s_nlog(np);
+  for (int i = 0; i < np; i++) {
+    const bool on = M->spec_mask_h.empty() || M->spec_mask_h[i];
+    const double s = ssv[i], dv_ = sdv[i];
+    if (on && !(std::isfinite(s) && s > 0 && std::isfinite(dv_)))
+      return fail(ctx, SED_EINVAL, "spectral datum %d: sigma must be > 0 and data finite", i);
+    // the kernels take d/sigma and 1/sigma in FP32: both must be finite there
+    // and 1/sigma a normal number
+    const double is = 1.0 / s, dn_ = dv_ * is;
+    if (on && !(is >= (double)FLT_MIN && is <= (double)FLT_MAX && std::fabs(dn_) <= (double)FLT_MAX))
+      return fail(ctx, SED_EINVAL, "spectral datum %d: 1/sigma and d/sigma must lie in FP32's normal range", i);
+    s_dn[i] = on ? (float)dn_ : 0.f;
+    s_isf[i] = on ? (float)is : 0.f;
+    s_nlog[i] = on ? -0.5 * std::log(2.0 * M_PI * s * s) : 0.0;
+  }
+  if (nb) {
+    CK(cudaMemcpy((void*)dv.phot_d, p_d.data(), nb * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)dv.phot_isig, p_isig.data(), nb * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)dv.phot_nlog, p_nlog.data(), nb * 8, cudaMemcpyHostToDevice));
+  }
+  if (np) {
+    CK(cudaMemcpy((void*)dv.spec_dn, s_dn.data(), np * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)dv.spec_isf, s_isf.data(), np * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)dv.spec_nlog, s_nlog.data(), np * 8, cudaMemcpyHostToDevice));
+  }
+  if (ph) {
+    M->phot_d_h.swap(pdv);
+    M->phot_s_h.swap(psv);
+  }
+  if (sp) {
+    M->spec_d_h.swap(sdv);
+    M->spec_s_h.swap(ssv);
   }
   return SED_OK;
 }

@@ -209,6 +209,9 @@ struct Model {
   ModelDev dv{};
   double bc_edge = 7.03, H0 = 0;
   std::vector<uint8_t> phot_mask_h, spec_mask_h;
+  // the data as last set (sed_set_data keeps a pair passed as NULL); empty
+  // until set, and a block never set stays out of lnL
+  std::vector<double> phot_d_h, phot_s_h, spec_d_h, spec_s_h;
   std::vector<void*> allocs;
   size_t bytes = 0;
 };

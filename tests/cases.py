@@ -53,8 +53,9 @@ def theta_rows(w: synth.Workload, n, seed=4):
     return oracle.pack_theta(theta_dict(w, n, seed), w.n_sfh, w.zmode, w.sample_sigma_gal)
 
 
-def gpu_model_for(ctx, orc, w: synth.Workload):
-    """A library model with exactly the oracle's inputs (grid loaded once per grid object)."""
+def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
+    """A library model with exactly the oracle's inputs (grid loaded once per grid
+    object); with_spec_data=False gives the spectrum's pixels but not its data."""
     cache = ctx.__dict__.setdefault("_grid_ids", {})
     key = id(orc.grid)
     if key not in cache:
@@ -66,7 +67,8 @@ def gpu_model_for(ctx, orc, w: synth.Workload):
               filters=orc.filters, phot_d=orc.phot_d, phot_sigma=orc.phot_sigma,
               phot_mask=orc.phot_mask)
     if orc.spec_lam is not None:
-        kw.update(spec_lam=orc.spec_lam, spec_d=orc.spec_d, spec_sigma=orc.spec_sigma,
+        kw.update(spec_lam=orc.spec_lam, spec_d=orc.spec_d if with_spec_data else None,
+                  spec_sigma=orc.spec_sigma if with_spec_data else None,
                   spec_mask=orc.spec_mask, lsf_mode=orc.lsf_mode, lsf_value=orc.lsf_value,
                   sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref, calib_sigma=orc.calib_sigma)
     return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)

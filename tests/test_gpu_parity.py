@@ -239,3 +239,50 @@ def test_host_buffer_entry_point(ctx):
     ok = ref["status"] == 0
     assert np.array_equal(st.astype(np.int64), ref["status"].astype(np.int64))
     assert (np.abs(lnl[ok] - ref["lnl"][ok]) / lnl_scale(orc, ref)[ok]).max() < 1e-5
+
+
+def test_set_data_keeps_null_pairs_and_rejects_atomically(ctx):
+    """sed_set_data: a pair passed as NULL keeps its last value; a call with a
+    bad datum (here a spectral 1/sigma beyond FP32's range) fails with
+    SED_EINVAL and changes nothing; after a good call lnL follows the oracle."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=40)
+    orc = cases.oracle_for(w)
+    model = cases.gpu_model_for(ctx, orc, w)
+    th32, th64 = cases.theta_pair(w, w.batch, seed=48)
+    t = torch.from_numpy(th32).cuda()
+    ref = orc.eval(th64)
+    ok = ref["status"] == 0
+    base = model.loglike(t, "fp32")[0].cpu().numpy()
+    assert (np.abs(base[ok] - ref["lnl"][ok]) / lnl_scale(orc, ref)[ok]).max() < 1e-5
+    # spectrum only: the photometric pair is kept
+    model.set_data(spec_d=orc.spec_d, spec_sigma=orc.spec_sigma)
+    assert np.array_equal(model.loglike(t, "fp32")[0].cpu().numpy(), base)
+    # a spectral sigma of 1e-40 (1/sigma overflows FP32): rejected, nothing changes
+    bad = np.array(orc.spec_sigma, dtype=np.float64)
+    bad[7] = 1e-40
+    with pytest.raises(Exception):
+        model.set_data(phot_d=orc.phot_d * 2, phot_sigma=orc.phot_sigma, spec_d=orc.spec_d, spec_sigma=bad)
+    assert np.array_equal(model.loglike(t, "fp32")[0].cpu().numpy(), base)
+    # new photometry alone: lnL follows the oracle with that photometry
+    pd2 = np.asarray(orc.phot_d) * 1.1
+    model.set_data(phot_d=pd2, phot_sigma=orc.phot_sigma)
+    orc.set_data(phot_d=pd2, phot_sigma=orc.phot_sigma, spec_d=orc.spec_d, spec_sigma=orc.spec_sigma)
+    ref2 = orc.eval(th64)
+    got = model.loglike(t, "fp32")[0].cpu().numpy()
+    assert (np.abs(got[ok] - ref2["lnl"][ok]) / lnl_scale(orc, ref2)[ok]).max() < 1e-5
+
+
+def test_spectrum_never_set_stays_out_of_lnl(ctx):
+    """A model created with a spectrum's wavelengths but without its data: lnL
+    is the photometric part alone (the oracle with every pixel masked)."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=40)
+    orc = cases.oracle_for(w, spec_mask=np.zeros(240, np.uint8))
+    full = cases.oracle_for(w)
+    model = cases.gpu_model_for(ctx, full, w, with_spec_data=False)
+    th32, th64 = cases.theta_pair(w, w.batch, seed=49)
+    ref = orc.eval(th64)
+    ok = ref["status"] == 0
+    got = model.loglike(torch.from_numpy(th32).cuda(), "fp32")[0].cpu().numpy()
+    assert (np.abs(got[ok] - ref["lnl"][ok]) / lnl_scale(orc, ref)[ok]).max() < 1e-5
