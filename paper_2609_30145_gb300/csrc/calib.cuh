@@ -94,8 +94,11 @@ __device__ __forceinline__ void calib_block(const ModelDev& md, const float* ms_
 
 // The small solves run on one warp, lane i holding row i of M (n <= 13 <= 32):
 // the Cholesky factor, both substitutions and the warp sums are column steps
-// with shuffles between lanes, fully unrolled so that every row stays in
-// registers.  All 32 lanes of the warp must call them together.
+// with shuffles between lanes, unrolled over all 13 rows so that every row
+// stays in registers.  The factor takes one reciprocal square root per column
+// and keeps the inverse diagonal, so the substitutions only multiply; ln|M|
+// comes from the diagonal at the end, one logarithm per lane.  All 32 lanes of
+// the warp must call them together.
 
 // Sum of the per-warp partials into row 0, in warp order, of entries [q0, q1).
 __device__ __forceinline__ void calib_sum_warps(float* part, int nwarps, int q0, int q1, int lane) {
@@ -108,28 +111,26 @@ __device__ __forceinline__ void calib_sum_warps(float* part, int nwarps, int q0,
 }
 
 // M from the moments S (row 0 of the partials), factored into its Cholesky
-// factor L, written to the lower triangle of the row-major n x n array L.
-// Returns -ln|M| / 2 - ln|Lambda| / 2 (ln|M| = 2 sum ln L_jj), or NaN when M
-// is not positive definite (every lane).
-__device__ inline double calib_factor(const ModelDev& md, const float* S, float* L, int lane) {
+// factor L, written to the lower triangle of the row-major n x n array L, and
+// 1/L_ii to Dinv.  Returns -ln|M| / 2 - ln|Lambda| / 2, or NaN when M is not
+// positive definite (every lane).
+__device__ inline double calib_factor(const ModelDev& md, const float* S, float* L, float* Dinv, int lane) {
   const int n = md.calib_n, i = lane;
   const float isg = i < n ? (float)md.calib_isig2[i] : 0.f;
   float a[SED_MAX_CALIB];   // row i of M, updated in place
-#pragma unroll
+#pragma unroll 13
   for (int k = 0; k < SED_MAX_CALIB; ++k)
     a[k] = (i < n && k <= i) ? 0.5f * (S[i + k] + S[i - k]) + (i == k ? isg : 0.f) : 0.f;
-  float logdet = 0.f;
-  bool pd = true;
-#pragma unroll
+  float dii = 1.f, iii = 1.f;   // this lane's pivot L_ii^2 and 1/L_ii
+#pragma unroll 13
   for (int j = 0; j < SED_MAX_CALIB; ++j) {
     if (j < n) {
-      const float d = __shfl_sync(0xffffffffu, a[j], j);   // the updated diagonal, from lane j
-      pd = pd && d > 0.f;
-      const float ljj = sqrtf(d), inv = 1.f / ljj;
-      const float lij = i == j ? ljj : a[j] * inv;          // column j of L (rows i >= j)
+      const float d = __shfl_sync(0xffffffffu, a[j], j);   // the updated pivot, from lane j
+      const float inv = rsqrtf(d);
+      const float lij = i == j ? d * inv : a[j] * inv;      // column j of L (rows i >= j)
+      if (i == j) { dii = d; iii = inv; }
       if (i >= j && i < n) L[i * n + j] = lij;
-      logdet += 2.f * logf(ljj);
-#pragma unroll
+#pragma unroll 12
       for (int k = j + 1; k < SED_MAX_CALIB; ++k) {
         if (k < n) {
           const float lkj = __shfl_sync(0xffffffffu, lij, k);
@@ -138,36 +139,45 @@ __device__ inline double calib_factor(const ModelDev& md, const float* S, float*
       }
     }
   }
+  if (i < n) Dinv[i] = iii;
+  float lg = i < n ? logf(dii) : 0.f;   // ln L_ii^2
+  int bad = i < n && !(dii > 0.f);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    lg += __shfl_xor_sync(0xffffffffu, lg, o);
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
   __syncwarp();
-  return pd ? -0.5 * (double)logdet - 0.5 * md.calib_logdet_lam : (double)NAN;
+  return bad ? (double)NAN : -0.5 * (double)lg - 0.5 * md.calib_logdet_lam;
 }
 
 // x = (L L^T)^-1 rhs with rhs_i in lane i; returns x_i in lane i (0 for i >= n).
-// Lane i reads row i and column i of L.
-__device__ inline float calib_subst(const float* L, int n, float rhs, int lane) {
+// Lane i reads row i and column i of L (off the diagonal) and 1/L_ii.
+__device__ inline float calib_subst(const float* L, const float* Dinv, int n, float rhs, int lane) {
   const int i = lane;
-  float row[SED_MAX_CALIB], col[SED_MAX_CALIB];   // L[i][k] (k <= i), L[k][i] (k >= i)
-#pragma unroll
+  float row[SED_MAX_CALIB], col[SED_MAX_CALIB];   // L[i][k] (k < i), L[k][i] (k > i)
+#pragma unroll 13
   for (int k = 0; k < SED_MAX_CALIB; ++k) {
-    row[k] = (i < n && k <= i) ? L[i * n + k] : 0.f;
-    col[k] = (i < n && k < n && k >= i) ? L[k * n + i] : 0.f;
+    row[k] = (i < n && k < i) ? L[i * n + k] : 0.f;
+    col[k] = (i < n && k < n && k > i) ? L[k * n + i] : 0.f;
   }
+  const float di = i < n ? Dinv[i] : 0.f;
   float v = rhs, y = 0.f;   // forward: L y = rhs
-#pragma unroll
+#pragma unroll 13
   for (int k = 0; k < SED_MAX_CALIB; ++k) {
     if (k < n) {
-      const float yk = __shfl_sync(0xffffffffu, v / row[k], k);
+      const float yk = __shfl_sync(0xffffffffu, v * di, k);
       if (i == k) y = yk;
-      if (i > k) v = fmaf(-row[k], yk, v);
+      v = fmaf(-row[k], yk, v);
     }
   }
   float w = y, x = 0.f;     // back: L^T x = y
-#pragma unroll
+#pragma unroll 13
   for (int k = SED_MAX_CALIB - 1; k >= 0; --k) {
     if (k < n) {
-      const float xk = __shfl_sync(0xffffffffu, w / col[k], k);
+      const float xk = __shfl_sync(0xffffffffu, w * di, k);
       if (i == k) x = xk;
-      if (i < k) w = fmaf(-col[k], xk, w);
+      w = fmaf(-col[k], xk, w);
     }
   }
   return i < n ? x : 0.f;
@@ -175,12 +185,12 @@ __device__ inline float calib_subst(const float* L, int n, float rhs, int lane) 
 
 // c* from the first solve: the moments summed, M factored, c = M^-1 b written
 // to c; returns the calib_factor value (every lane).
-__device__ inline double calib_first_solve(const ModelDev& md, float* part, int nwarps, float* L, float* c,
-                                           int lane) {
+__device__ inline double calib_first_solve(const ModelDev& md, float* part, int nwarps, float* L, float* Dinv,
+                                           float* c, int lane) {
   const int n = md.calib_n;
   calib_sum_warps(part, nwarps, 0, CAL_NV, lane);
-  const double f = calib_factor(md, part, L, lane);
-  const float x = calib_subst(L, n, lane < n ? part[CAL_NS + lane] : 0.f, lane);
+  const double f = calib_factor(md, part, L, Dinv, lane);
+  const float x = calib_subst(L, Dinv, n, lane < n ? part[CAL_NS + lane] : 0.f, lane);
   if (lane < n) c[lane] = x;
   __syncwarp();
   return f;
@@ -189,14 +199,14 @@ __device__ inline double calib_first_solve(const ModelDev& md, float* part, int 
 // The refinement: residual b - M c from the pixel sums (partials from index
 // CAL_NS) minus Lambda^-1 c, its correction added to c, and the prior term
 // -c^T Lambda^-1 c / 2 of the refined c returned (every lane).
-__device__ inline double calib_refine(const ModelDev& md, float* part, int nwarps, const float* L, float* c,
-                                      int lane) {
+__device__ inline double calib_refine(const ModelDev& md, float* part, int nwarps, const float* L,
+                                      const float* Dinv, float* c, int lane) {
   const int n = md.calib_n;
   calib_sum_warps(part, nwarps, CAL_NS, CAL_NV, lane);
   const float isg = lane < n ? (float)md.calib_isig2[lane] : 0.f;
   const float ca = lane < n ? c[lane] : 0.f;
   const float r = lane < n ? fmaf(-isg, ca, part[CAL_NS + lane]) : 0.f;
-  const float cn = ca + calib_subst(L, n, r, lane);
+  const float cn = ca + calib_subst(L, Dinv, n, r, lane);
   if (lane < n) c[lane] = cn;
   float pr = cn * cn * isg;
 #pragma unroll

@@ -53,9 +53,10 @@ __device__ __forceinline__ void put_g(const EpiBwdArgs& a, float* hi, float* lo,
 // Shared memory of one row: F and dlnL/dF over the row's node window, then a
 // union of the filter samples' brackets (photometry) and the pixels' node
 // ranges and positions (spectrum).
-// bytes of the calibration scratch: per-warp sums, the Cholesky factor and c* as floats
+// bytes of the calibration scratch: per-warp sums, the Cholesky factor, its
+// inverse diagonal and c* as floats
 constexpr size_t EB_CAL_BYTES = (size_t)EB_WARPS * CAL_NV * sizeof(float) +
-                                (size_t)(SED_MAX_CALIB * SED_MAX_CALIB + SED_MAX_CALIB) * sizeof(float);
+                                (size_t)(SED_MAX_CALIB * SED_MAX_CALIB + 2 * SED_MAX_CALIB) * sizeof(float);
 
 size_t epi_bwd_smem(const EpiBwdArgs& a) {
   const size_t W = (size_t)a.md.win_max;
@@ -115,13 +116,14 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   float* dv_s = mu_s + md.n_pix;
   float* dvs_s = dv_s + md.n_pix;
   float* cw_s = dvs_s + md.n_pix;
-  float *cal_part = nullptr, *cal_Lf = nullptr, *cal_cf = nullptr;
+  float *cal_part = nullptr, *cal_Lf = nullptr, *cal_Df = nullptr, *cal_cf = nullptr;
   if (md.calib_n) {
     const size_t samp = (size_t)md.n_samp * 8, pix = (size_t)md.n_pix * 36;
     const size_t u = ((samp > pix ? samp : pix) + 7) & ~(size_t)7;
     cal_part = reinterpret_cast<float*>(reinterpret_cast<char*>(U) + u);
     cal_Lf = reinterpret_cast<float*>(cal_part + EB_WARPS * CAL_NV);
-    cal_cf = cal_Lf + SED_MAX_CALIB * SED_MAX_CALIB;   // after L
+    cal_Df = cal_Lf + SED_MAX_CALIB * SED_MAX_CALIB;   // after L
+    cal_cf = cal_Df + SED_MAX_CALIB;
   }
   // each thread owns a contiguous run of CH window nodes (CH odd: the runs of a
   // warp fall in distinct shared-memory banks) for the node-owned gathers
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     calib_block<0, 1, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
     __syncthreads();
     if (warp == 0) {
-      const double f = calib_first_solve(md, cal_part, EB_WARPS, cal_Lf, cal_cf, lane);
+      const double f = calib_first_solve(md, cal_part, EB_WARPS, cal_Lf, cal_Df, cal_cf, lane);
       if (lane == 0) l_spec += f;
     }
     __syncthreads();
@@ -374,7 +376,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     calib_block<0, 2, EB_THREADS>(md, mu_s, cal_cf, tid, lane, warp, cal_part);
     __syncthreads();
     if (warp == 0) {
-      const double f = calib_refine(md, cal_part, EB_WARPS, cal_Lf, cal_cf, lane);
+      const double f = calib_refine(md, cal_part, EB_WARPS, cal_Lf, cal_Df, cal_cf, lane);
       if (lane == 0) l_spec += f;
     }
     __syncthreads();
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
           float v = T[a];
 #pragma unroll
           for (int k = 0; k < a; ++k) v -= cal_Lf[a * n + k] * y[k];
-          y[a] = v / cal_Lf[a * n + a];
+          y[a] = v * cal_Df[a];
           q = fmaf(y[a], y[a], q);
         }
       }

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   __shared__ float mb_s[MAX_BANDS];
   __shared__ double red[EPI_WARPS];
   __shared__ float cal_part[EPI_WARPS][CAL_NV];    // per-warp calibration sums
-  __shared__ float cal_L[SED_MAX_CALIB * SED_MAX_CALIB], cal_c[SED_MAX_CALIB];   // Cholesky factor of M, c*
+  __shared__ float cal_L[SED_MAX_CALIB * SED_MAX_CALIB], cal_D[SED_MAX_CALIB], cal_c[SED_MAX_CALIB];  // M = L L^T, 1/L_ii, c*
   __shared__ double cal_fix;                       // the row's lnL terms that do not sum over pixels
 
   RowScal rs = a.rs[r];
@@ -207,14 +207,14 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     // c*; refine c* once from the pixels' calibrated residuals; then each
     // included pixel's change of its term under the polynomial p = A c*
     if (warp == 0) {
-      const double f = calib_first_solve(md, &cal_part[0][0], EPI_WARPS, cal_L, cal_c, lane);
+      const double f = calib_first_solve(md, &cal_part[0][0], EPI_WARPS, cal_L, cal_D, cal_c, lane);
       if (lane == 0) cal_fix = f;
     }
     __syncthreads();
     calib_block<0, 2, EPI_THREADS>(md, mu_s, cal_c, tid, lane, warp, &cal_part[0][0]);
     __syncthreads();
     if (warp == 0) {
-      const double f = calib_refine(md, &cal_part[0][0], EPI_WARPS, cal_L, cal_c, lane);
+      const double f = calib_refine(md, &cal_part[0][0], EPI_WARPS, cal_L, cal_D, cal_c, lane);
       if (lane == 0) cal_fix += f;
     }
     __syncthreads();
