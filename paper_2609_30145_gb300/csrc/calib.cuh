@@ -92,13 +92,15 @@ __device__ __forceinline__ void calib_block(const ModelDev& md, const float* ms_
   }
 }
 
-// The small solves run on one warp, lane i holding row i of M (n <= 13 <= 32):
-// the Cholesky factor, both substitutions and the warp sums are column steps
-// with shuffles between lanes, unrolled over all 13 rows so that every row
-// stays in registers.  The factor takes one reciprocal square root per column
-// and keeps the inverse diagonal, so the substitutions only multiply; ln|M|
-// comes from the diagonal at the end, one logarithm per lane.  All 32 lanes of
-// the warp must call them together.
+// The small solves run on one warp, lane i owning row i of M (n <= 13 <= 32),
+// the matrix in shared memory.  They run once per row between long phases of
+// other code, so they are written as short runtime loops (a fully unrolled
+// form measured several times slower there, fetching its instructions cold):
+// the Cholesky factor is left-looking, one column per step with a dot product
+// per lane, one reciprocal square root and a warp barrier; the inverse
+// diagonal is kept so that the substitutions only multiply; ln|M| comes from
+// the pivots at the end, one logarithm per lane.  All 32 lanes of the warp
+// must call them together.
 
 // Sum of the per-warp partials into row 0, in warp order, of entries [q0, q1).
 __device__ __forceinline__ void calib_sum_warps(float* part, int nwarps, int q0, int q1, int lane) {
@@ -114,35 +116,30 @@ __device__ __forceinline__ void calib_sum_warps(float* part, int nwarps, int q0,
 // factor L, written to the lower triangle of the row-major n x n array L, and
 // 1/L_ii to Dinv.  Returns -ln|M| / 2 - ln|Lambda| / 2, or NaN when M is not
 // positive definite (every lane).
-__device__ inline double calib_factor(const ModelDev& md, const float* S, float* L, float* Dinv, int lane) {
+static __device__ __noinline__ double calib_factor(const ModelDev& md, const float* S, float* L, float* Dinv, int lane) {
   const int n = md.calib_n, i = lane;
-  const float isg = i < n ? (float)md.calib_isig2[i] : 0.f;
-  float a[SED_MAX_CALIB];   // row i of M, updated in place
-#pragma unroll 13
-  for (int k = 0; k < SED_MAX_CALIB; ++k)
-    a[k] = (i < n && k <= i) ? 0.5f * (S[i + k] + S[i - k]) + (i == k ? isg : 0.f) : 0.f;
+  if (i < n) {
+    const float isg = (float)md.calib_isig2[i];
+    for (int k = 0; k <= i; ++k) L[i * n + k] = 0.5f * (S[i + k] + S[i - k]) + (i == k ? isg : 0.f);
+  }
+  __syncwarp();
   float dii = 1.f, iii = 1.f;   // this lane's pivot L_ii^2 and 1/L_ii
-#pragma unroll 13
-  for (int j = 0; j < SED_MAX_CALIB; ++j) {
-    if (j < n) {
-      const float d = __shfl_sync(0xffffffffu, a[j], j);   // the updated pivot, from lane j
-      const float inv = rsqrtf(d);
-      const float lij = i == j ? d * inv : a[j] * inv;      // column j of L (rows i >= j)
-      if (i == j) { dii = d; iii = inv; }
-      if (i >= j && i < n) L[i * n + j] = lij;
-#pragma unroll 12
-      for (int k = j + 1; k < SED_MAX_CALIB; ++k) {
-        if (k < n) {
-          const float lkj = __shfl_sync(0xffffffffu, lij, k);
-          if (i >= k) a[k] = fmaf(-lij, lkj, a[k]);
-        }
-      }
+  for (int j = 0; j < n; ++j) {
+    // s_i = M_ij - sum_{k<j} L_ik L_jk for the rows i >= j
+    float s = 0.f;
+    if (i >= j && i < n) {
+      s = L[i * n + j];
+      for (int k = 0; k < j; ++k) s = fmaf(-L[i * n + k], L[j * n + k], s);
     }
+    const float d = __shfl_sync(0xffffffffu, s, j);
+    const float inv = rsqrtf(d);
+    if (i == j) { dii = d; iii = inv; }
+    if (i >= j && i < n) L[i * n + j] = i == j ? d * inv : s * inv;
+    __syncwarp();
   }
   if (i < n) Dinv[i] = iii;
   float lg = i < n ? logf(dii) : 0.f;   // ln L_ii^2
   int bad = i < n && !(dii > 0.f);
-#pragma unroll
   for (int o = 16; o; o >>= 1) {
     lg += __shfl_xor_sync(0xffffffffu, lg, o);
     bad |= __shfl_xor_sync(0xffffffffu, bad, o);
@@ -152,33 +149,20 @@ __device__ inline double calib_factor(const ModelDev& md, const float* S, float*
 }
 
 // x = (L L^T)^-1 rhs with rhs_i in lane i; returns x_i in lane i (0 for i >= n).
-// Lane i reads row i and column i of L (off the diagonal) and 1/L_ii.
-__device__ inline float calib_subst(const float* L, const float* Dinv, int n, float rhs, int lane) {
+static __device__ __noinline__ float calib_subst(const float* L, const float* Dinv, int n, float rhs, int lane) {
   const int i = lane;
-  float row[SED_MAX_CALIB], col[SED_MAX_CALIB];   // L[i][k] (k < i), L[k][i] (k > i)
-#pragma unroll 13
-  for (int k = 0; k < SED_MAX_CALIB; ++k) {
-    row[k] = (i < n && k < i) ? L[i * n + k] : 0.f;
-    col[k] = (i < n && k < n && k > i) ? L[k * n + i] : 0.f;
-  }
   const float di = i < n ? Dinv[i] : 0.f;
   float v = rhs, y = 0.f;   // forward: L y = rhs
-#pragma unroll 13
-  for (int k = 0; k < SED_MAX_CALIB; ++k) {
-    if (k < n) {
-      const float yk = __shfl_sync(0xffffffffu, v * di, k);
-      if (i == k) y = yk;
-      v = fmaf(-row[k], yk, v);
-    }
+  for (int k = 0; k < n; ++k) {
+    const float yk = __shfl_sync(0xffffffffu, v * di, k);
+    if (i == k) y = yk;
+    if (i > k && i < n) v = fmaf(-L[i * n + k], yk, v);
   }
   float w = y, x = 0.f;     // back: L^T x = y
-#pragma unroll 13
-  for (int k = SED_MAX_CALIB - 1; k >= 0; --k) {
-    if (k < n) {
-      const float xk = __shfl_sync(0xffffffffu, w * di, k);
-      if (i == k) x = xk;
-      w = fmaf(-col[k], xk, w);
-    }
+  for (int k = n - 1; k >= 0; --k) {
+    const float xk = __shfl_sync(0xffffffffu, w * di, k);
+    if (i == k) x = xk;
+    if (i < k) w = fmaf(-L[k * n + i], xk, w);
   }
   return i < n ? x : 0.f;
 }
