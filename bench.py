@@ -373,7 +373,10 @@ def run_ours(args):
            "h2d_bytes_per_step": B * ld * 4, "d2h_bytes_per_step": B * 8 + B * 4,
            "p50_ms": round(1e3 * float(np.percentile(e2e_t, 50)), 4),
            "p99_ms": round(1e3 * float(np.percentile(e2e_t, 99)), 4),
-           "what": "sed_loglike_host: pinned host theta -> device, prep/contraction/epilogue, lnL + status -> host"}
+           "what": "sed_loglike_host with pinned host buffers: theta host -> device, order/prep/contraction/"
+                   "epilogue, lnL + status device -> host, stream synchronised; wall clock around each call",
+           "host_path": ("in place: the kernels read theta and write lnL/status over the host link"
+                         if ctx.last_host_path() == 3 else "staged through device memory by async copies")}
 
     # GPU results for the accuracy comparison of the CPU-baseline leg
     gpu_res = {}

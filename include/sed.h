@@ -182,6 +182,11 @@ const char *sed_status_string(sed_status s);
 const char *sed_last_error(const sed_ctx *ctx);
 /* Device bytes currently held by the context. */
 sed_status sed_memory_used(const sed_ctx *ctx, size_t *bytes);
+/* How the last sed_loglike_host call on this context reached its buffers:
+ * bit 0 set = theta was read in place, bit 1 set = lnl_out was written in
+ * place (both page-locked and device-mapped); 0 = both were staged.  Only
+ * valid once such a call has returned SED_OK. */
+sed_status sed_last_host_path(const sed_ctx *ctx, int *mapped);
 
 sed_status sed_load_grid(sed_ctx *ctx, const sed_grid_desc *desc, sed_grid_id *out);
 
@@ -240,8 +245,14 @@ sed_status sed_loglike_grad(sed_ctx *ctx, sed_model_id model, const float *theta
 
 /*
  * sed_loglike with HOST buffers: theta [n][ld] FP32, lnl_out [n], row_status
- * [n] or NULL.  Copies in, runs on `stream`, copies out and synchronises the
- * stream before returning.
+ * [n] or NULL.  Runs on `stream` and synchronises the stream before
+ * returning.  A page-locked host buffer that the device can address (memory
+ * from cudaHostAlloc / cudaMallocHost, or cudaHostRegister'ed, on a 64-bit
+ * unified-address system) is used in place: the kernels read theta and write
+ * lnl_out / row_status over the host link (NVLink-C2C on a Grace host), so no
+ * separate copy sits on the call's critical path.  Any other buffer is staged
+ * through device memory with an asynchronous copy.  The result is the same
+ * either way, bit for bit.  ld <= 1024.
  */
 sed_status sed_loglike_host(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld,
                             double *lnl_out, uint32_t *row_status, int precision, void *stream);

@@ -70,6 +70,7 @@ SIGNATURES = {
     "sed_status_string": (C.c_char_p, [C.c_int]),
     "sed_last_error": (C.c_char_p, [P]),
     "sed_memory_used": (C.c_int, [P, C.POINTER(C.c_size_t)]),
+    "sed_last_host_path": (C.c_int, [P, C.POINTER(C.c_int)]),
     "sed_load_grid": (C.c_int, [P, C.POINTER(GridDesc), C.POINTER(C.c_int32)]),
     "sed_create_model": (C.c_int, [P, C.POINTER(ModelDesc), C.POINTER(C.c_int32)]),
     "sed_model_layout": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int), C.POINTER(C.c_int)]),

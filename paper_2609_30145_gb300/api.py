@@ -77,6 +77,13 @@ class Context:
         self._check(self._lib.sed_last_stats(self._h, _stream_handle(stream), C.byref(st)))
         return {f: getattr(st, f) for f, _ in st._fields_}
 
+    def last_host_path(self):
+        """Bits of the last loglike_host call: 1 = theta read in place, 2 = lnL
+        written in place (page-locked, device-mapped host buffers)."""
+        v = C.c_int()
+        self._check(self._lib.sed_last_host_path(self._h, C.byref(v)))
+        return v.value
+
     def memory_used(self):
         v = C.c_size_t()
         self._check(self._lib.sed_memory_used(self._h, C.byref(v)))

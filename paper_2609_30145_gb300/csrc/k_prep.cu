@@ -12,6 +12,8 @@
 //    two bracketing [a/Fe] nodes (Sec. 5.4).  A thread owns one age node and
 //    sums the bins overlapping its cell in order, so W is deterministic;
 //  - Q_young = sum over birth-cloud ages of W Q (App. C, Eq. app_q).
+#include <algorithm>
+
 #include "sed_internal.cuh"
 #include "locate.cuh"
 
@@ -203,6 +205,9 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
 
   extern __shared__ float smem[];
   float* Ws = smem;                     // [NA][NZ]
+  // the row's parameters, read once (coalesced) into the tail of the dynamic
+  // shared memory: theta may be the caller's pinned host buffer, read in place
+  float* th_s = smem + (size_t)NA * NZ + (a.W_f8 ? L.Kpad : 0);
   __shared__ float T[MAX_SFH + 1];      // edges
   __shared__ float rate[MAX_SFH];       // m_i / dT_i
   __shared__ int zb[MAX_SFH];
@@ -215,9 +220,14 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   //      the shadow of the row's loads)
   __shared__ CosmoRow s_cr;
   int bad = 0;
-  for (int j = tid; j < md.n_param; j += blockDim.x) bad |= !isfinite(th[j]);
+  for (int j = tid; j < md.n_param; j += blockDim.x) {
+    const float v = th[j];
+    th_s[j] = v;
+    bad |= !isfinite(v);
+  }
   if (tid == 0) s_cr = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]]);
   bad = __syncthreads_or(bad);
+  th = th_s;
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
   // a sampled sigma_gal outside the model's declared range [0, max]
   if (!status && md.sample_sgal) {
@@ -621,7 +631,10 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   }
   PrepKernelArgs ka;
   ka.p = p;
-  const size_t smem = ((size_t)p.g.n_age * p.g.n_feh + (p.W_f8 ? (size_t)p.L.Kpad : 0)) * sizeof(float);
+  // Ws [n_age][n_feh], the FP8 row scratch, the row's parameters (n_param <= ld
+  // and n_param <= 2 MAX_SFH + SED_NKEYS for every model)
+  const size_t npar = (size_t)std::min(p.ld, 2 * MAX_SFH + SED_NKEYS);
+  const size_t smem = ((size_t)p.g.n_age * p.g.n_feh + (p.W_f8 ? (size_t)p.L.Kpad : 0) + npar) * sizeof(float);
   static size_t set_for[2] = {0, 0};
   e = p.row_model ? ensure_dyn_smem(k_prep<true>, smem, &set_for[1]) : ensure_dyn_smem(k_prep<false>, smem, &set_for[0]);
   if (e != cudaSuccess) return e;

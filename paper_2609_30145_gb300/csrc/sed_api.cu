@@ -196,6 +196,12 @@ sed_status sed_destroy(sed_ctx* ctx) {
   return SED_OK;
 }
 
+sed_status sed_last_host_path(const sed_ctx* ctx, int* mapped) {
+  if (!ctx || !mapped) return SED_EINVAL;
+  *mapped = ctx->last_host_mapped;
+  return SED_OK;
+}
+
 sed_status sed_memory_used(const sed_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return SED_EINVAL;
   *bytes = ctx->used;
@@ -575,6 +581,17 @@ void cosmo_table(double H0, double Om, double zf, int n, std::vector<double>* ou
     t[6] = 1.0 / (1.0 + z);
     t[7] = -1.0 / ((1.0 + z) * (1.0 + z));
   }
+}
+
+// The device address of a page-locked, device-mapped host buffer, or NULL
+// (pageable or unknown memory).
+void* mapped_host(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
 sed_status set_data_dev(sed_ctx* ctx, Model* M, const double* pd, const double* ps, const double* sd,
@@ -1131,12 +1148,24 @@ sed_status sed_loglike_host(sed_ctx* ctx, sed_model_id id, const float* theta, i
   cudaStream_t s = (cudaStream_t)stream;
   Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
   if (!w) return st;
-  CK(cudaMemcpyAsync(w->theta_h, theta, (size_t)n * ld * 4, cudaMemcpyHostToDevice, s));
-  st = sed_loglike(ctx, id, w->theta_h, n, ld, w->lnl_h, w->st_h, precision, stream);
+  // page-locked, device-mapped host buffers are used in place: the kernels
+  // read theta and write lnL / status over the host link (NVLink-C2C on a
+  // Grace host), so no copy sits on the critical path; other buffers are
+  // staged through device memory
+  const float* th_d = (const float*)mapped_host(theta);
+  double* lnl_d = (double*)mapped_host(lnl_out);
+  uint32_t* st_d = row_status ? (uint32_t*)mapped_host(row_status) : nullptr;
+  if (!th_d) {
+    CK(cudaMemcpyAsync(w->theta_h, theta, (size_t)n * ld * 4, cudaMemcpyHostToDevice, s));
+    th_d = w->theta_h;
+  }
+  st = sed_loglike(ctx, id, th_d, n, ld, lnl_d ? lnl_d : w->lnl_h, row_status && !st_d ? w->st_h : st_d,
+                   precision, stream);
   if (st) return st;
-  CK(cudaMemcpyAsync(lnl_out, w->lnl_h, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
-  if (row_status) CK(cudaMemcpyAsync(row_status, w->st_h, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+  if (!lnl_d) CK(cudaMemcpyAsync(lnl_out, w->lnl_h, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  if (row_status && !st_d) CK(cudaMemcpyAsync(row_status, w->st_h, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  ctx->last_host_mapped = (th_d != w->theta_h ? 1 : 0) | (lnl_d ? 2 : 0);
   return SED_OK;
 }
 

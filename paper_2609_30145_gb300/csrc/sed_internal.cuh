@@ -292,6 +292,7 @@ struct sed_ctx {
   void* encode_fn = nullptr;   // cuTensorMapEncodeTiled
   int profiling = 0;
   int tc_ok = -1;              // tcgen05 path usable on this device (sm_103)
+  int last_host_mapped = 0;    // sed_last_host_path
 };
 
 // ---------------------------------------------------------------------------

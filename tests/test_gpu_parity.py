@@ -286,3 +286,27 @@ def test_spectrum_never_set_stays_out_of_lnl(ctx):
     ok = ref["status"] == 0
     got = model.loglike(torch.from_numpy(th32).cuda(), "fp32")[0].cpu().numpy()
     assert (np.abs(got[ok] - ref["lnl"][ok]) / lnl_scale(orc, ref)[ok]).max() < 1e-5
+
+
+def test_host_entry_point_pinned_in_place_and_pageable_staged(ctx):
+    """sed_loglike_host: page-locked buffers are read and written in place by
+    the kernels, pageable ones staged through device memory; both give the
+    same result, bit for bit, equal to the device entry point's, and both
+    match the oracle."""
+    w, orc, model = case(ctx, "spec")
+    th32, th64 = cases.theta_pair(w, 300, seed=50)
+    ref = orc.eval(th64[:24])
+    lnl_p, st_p = model.loglike_host(th32, "fp32")
+    assert ctx.last_host_path() == 0
+    th_pin = torch.from_numpy(th32).pin_memory()
+    out = torch.empty(300, dtype=torch.float64).pin_memory()
+    sto = torch.empty(300, dtype=torch.int32).pin_memory()
+    model.loglike_host(th_pin, "fp32", out=out, status=sto)
+    assert ctx.last_host_path() == 3
+    assert np.array_equal(out.numpy(), lnl_p)
+    assert np.array_equal(sto.numpy().astype(np.uint32), st_p)
+    lnl_d, st_d = model.loglike(torch.from_numpy(th32).cuda(), "fp32")
+    assert np.array_equal(lnl_d.cpu().numpy(), lnl_p)
+    ok = ref["status"] == 0
+    assert np.array_equal(st_p[:24].astype(np.int64), ref["status"].astype(np.int64))
+    assert (np.abs(lnl_p[:24][ok] - ref["lnl"][ok]) / lnl_scale(orc, ref)[ok]).max() < 1e-5
