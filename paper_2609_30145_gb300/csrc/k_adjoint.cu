@@ -32,7 +32,8 @@ namespace sed {
 constexpr int EB_THREADS = 256;
 constexpr int EB_WARPS = EB_THREADS / 32;
 constexpr int EB_MAX_BANDS = 128;
-constexpr int EB_NRED = 12;   // per-warp partial sums reduced in FP64
+constexpr int EB_NRED = 11;   // per-warp partial sums: 9 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
+constexpr int EB_NREDF = 9;
 
 __device__ __forceinline__ float tf32_rna_dev(float x) {
   uint32_t r;
@@ -75,9 +76,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int N = g.n_lam;
   extern __shared__ __align__(16) float smem[];
-  __shared__ float ubp[EB_MAX_BANDS];
+  __shared__ float ubp[EB_MAX_BANDS], mbp[EB_MAX_BANDS];
   __shared__ int bk0[EB_MAX_BANDS], bk1[EB_MAX_BANDS];
-  __shared__ double band_l[EB_MAX_BANDS], band_um[EB_MAX_BANDS];
   __shared__ double red[EB_WARPS][EB_NRED];
 
   const size_t ro = (size_t)r * a.ldn;
@@ -206,16 +206,12 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
     }
     const float mb = rs.p_phot * acc;
-    double v = 0.0, ub = 0.0;
-    if (md.phot_isig[b] != 0.0) {
-      const double rr = (md.phot_d[b] - (double)mb) * md.phot_isig[b];
-      v = -0.5 * rr * rr + md.phot_nlog[b];
-      ub = rr * md.phot_isig[b];
-    }
-    const float c_b = (float)(ub * (double)rs.p_phot);
+    // d lnL / d(band flux) = (d - m)/sigma^2, formed in FP32 from the normalised
+    // datum and 1/sigma (0 for a masked band); times p_phot it weighs F
+    const float isf = md.phot_isf[b];
+    const float c_b = (md.phot_dn[b] - mb * isf) * (isf * rs.p_phot);
     if (lane == 0) {
-      band_l[b] = v;
-      band_um[b] = ub * (double)mb;
+      mbp[b] = mb;
       ubp[b] = c_b;
       bk0[b] = bmin;
       bk1[b] = bmax;
@@ -543,43 +539,68 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     }
   }
 
-  // ---- fixed-order FP64 reductions of the per-thread pieces
-  double v[EB_NRED] = {(double)g_tbc, (double)g_abc, (double)g_td, (double)g_dl, (double)g_lz, (double)g_lu,
-                       um_spec, (double)gz_gather + (double)gz_spec, (double)g_qy, l_spec, (double)g_sgal, 0.0};
+  // ---- fixed-order reductions of the per-thread pieces: the FP32 sums within
+  //      the warp in FP32, lnL and d lnL/d ln(mass) in FP64; across the warps
+  //      in FP64, one column per lane of warp 0
+  float vf[EB_NREDF] = {g_tbc, g_abc, g_td, g_dl, g_lz, g_lu, gz_gather + gz_spec, g_qy, g_sgal};
 #pragma unroll
-  for (int q = 0; q < EB_NRED; ++q) {
+  for (int q = 0; q < EB_NREDF; ++q) {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    if (lane == 0) red[warp][q] = v[q];
+    for (int o = 16; o; o >>= 1) vf[q] += __shfl_xor_sync(0xffffffffu, vf[q], o);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    l_spec += __shfl_xor_sync(0xffffffffu, l_spec, o);
+    um_spec += __shfl_xor_sync(0xffffffffu, um_spec, o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < EB_NREDF; ++q) red[warp][q] = (double)vf[q];
+    red[warp][EB_NREDF] = l_spec;
+    red[warp][EB_NREDF + 1] = um_spec;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (warp == 0) {
+    double col = 0.0;
+    if (lane < EB_NRED)
+      for (int w = 0; w < EB_WARPS; ++w) col += red[w][lane];
+    // the photometric lnL terms and d lnL/d ln(mass) pieces in FP64, one band per lane
+    double bl = 0.0, bu = 0.0;
+    for (int b = lane; b < md.n_filt; b += 32) {
+      if (md.phot_isig[b] != 0.0) {
+        const double mb = (double)mbp[b], rr = (md.phot_d[b] - mb) * md.phot_isig[b];
+        bl += -0.5 * rr * rr + md.phot_nlog[b];
+        bu += rr * md.phot_isig[b] * mb;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      bl += __shfl_xor_sync(0xffffffffu, bl, o);
+      bu += __shfl_xor_sync(0xffffffffu, bu, o);
+    }
     double s[EB_NRED];
-    for (int q = 0; q < EB_NRED; ++q) {
-      s[q] = 0.0;
-      for (int w = 0; w < EB_WARPS; ++w) s[q] += red[w][q];
+#pragma unroll
+    for (int q = 0; q < EB_NRED; ++q) s[q] = __shfl_sync(0xffffffffu, col, q);
+    if (lane == 0) {
+      double lnl = s[EB_NREDF] + bl, um_phot = bu;
+      const double um_sp = s[EB_NREDF + 1];
+      double* rg = a.rgrad + (size_t)r * RGRAD;
+      uint32_t stt = 0;
+      if (!isfinite(lnl)) { stt = SED_ROW_NONFINITE; lnl = -INFINITY; }
+      rg[RG_TAU_BC] = s[0];
+      rg[RG_ALPHA_BC] = s[1];
+      rg[RG_TAU_D] = s[2];
+      rg[RG_DELTA] = s[3];
+      rg[RG_GAS_LOGZ] = s[4];
+      rg[RG_GAS_LOGU] = s[5];
+      rg[RG_LOGMASS] = 2.302585092994046 * (um_phot + um_sp);
+      rg[RG_Z] = um_phot * (double)rs.dlnp_dz + um_sp * (double)rs.dlns_dz + s[6];
+      rg[RG_QY] = s[7];
+      rg[RG_SIGMA_GAL] = s[8];
+      rg[RG_BAD] = stt ? 1.0 : 0.0;
+      if (a.lnl) a.lnl[rs.orig] = lnl;
+      if (a.status) a.status[rs.orig] = stt;
     }
-    double lnl = s[9], um_phot = 0.0;
-    for (int b = 0; b < md.n_filt; ++b) {
-      lnl += band_l[b];
-      um_phot += band_um[b];
-    }
-    double* rg = a.rgrad + (size_t)r * RGRAD;
-    uint32_t stt = 0;
-    if (!isfinite(lnl)) { stt = SED_ROW_NONFINITE; lnl = -INFINITY; }
-    rg[RG_TAU_BC] = s[0];
-    rg[RG_ALPHA_BC] = s[1];
-    rg[RG_TAU_D] = s[2];
-    rg[RG_DELTA] = s[3];
-    rg[RG_GAS_LOGZ] = s[4];
-    rg[RG_GAS_LOGU] = s[5];
-    rg[RG_LOGMASS] = 2.302585092994046 * (um_phot + s[6]);
-    rg[RG_Z] = um_phot * (double)rs.dlnp_dz + s[6] * (double)rs.dlns_dz + s[7];
-    rg[RG_QY] = s[8];
-    rg[RG_SIGMA_GAL] = s[10];
-    rg[RG_BAD] = stt ? 1.0 : 0.0;
-    if (a.lnl) a.lnl[rs.orig] = lnl;
-    if (a.status) a.status[rs.orig] = stt;
   }
 }
 

@@ -612,14 +612,20 @@ sed_status set_data_dev(sed_ctx* ctx, Model* M, const double* pd, const double* 
   std::vector<double> pdv = pick(pd, M->phot_d_h, nb, 0.0), psv = pick(ps, M->phot_s_h, nb, 1.0);
   std::vector<double> sdv = pick(sd, M->spec_d_h, np, 0.0), ssv = pick(ss, M->spec_s_h, np, 1.0);
   std::vector<double> p_d(nb), p_isig(nb), p_nlog(nb);
+  std::vector<float> p_dn(nb), p_isf(nb);
   for (int b = 0; b < nb; b++) {
     const bool on = M->phot_mask_h.empty() || M->phot_mask_h[b];
     const double s = psv[b], dv_ = pdv[b];
     if (on && !(std::isfinite(s) && s > 0 && std::isfinite(dv_)))
       return fail(ctx, SED_EINVAL, "photometric datum %d: sigma must be > 0 and data finite", b);
+    const double is = 1.0 / s, dn_ = dv_ * is;
+    if (on && !(is >= (double)FLT_MIN && is <= (double)FLT_MAX && std::fabs(dn_) <= (double)FLT_MAX))
+      return fail(ctx, SED_EINVAL, "photometric datum %d: 1/sigma and d/sigma must lie in FP32's normal range", b);
     p_d[b] = on ? dv_ : 0.0;
-    p_isig[b] = on ? 1.0 / s : 0.0;
+    p_isig[b] = on ? is : 0.0;
     p_nlog[b] = on ? -0.5 * std::log(2.0 * M_PI * s * s) : 0.0;
+    p_dn[b] = on ? (float)dn_ : 0.f;
+    p_isf[b] = on ? (float)is : 0.f;
   }
   std::vector<float> s_dn(np), s_isf(np);
   std::vector<double> s_nlog(np);
@@ -641,6 +647,8 @@ sed_status set_data_dev(sed_ctx* ctx, Model* M, const double* pd, const double* 
     CK(cudaMemcpy((void*)dv.phot_d, p_d.data(), nb * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy((void*)dv.phot_isig, p_isig.data(), nb * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy((void*)dv.phot_nlog, p_nlog.data(), nb * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)dv.phot_dn, p_dn.data(), nb * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)dv.phot_isf, p_isf.data(), nb * 4, cudaMemcpyHostToDevice));
   }
   if (np) {
     CK(cudaMemcpy((void*)dv.spec_dn, s_dn.data(), np * 4, cudaMemcpyHostToDevice));
@@ -793,6 +801,10 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_d = pd; }
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_isig = pd; }
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_nlog = pd; }
+    std::vector<float> zf(d->n_filt, 0.f);
+    float* pz;
+    if (!st) { st = upload(ctx, &pz, zf.data(), zf.size(), &M->allocs, &M->bytes); dv.phot_dn = pz; }
+    if (!st) { st = upload(ctx, &pz, zf.data(), zf.size(), &M->allocs, &M->bytes); dv.phot_isf = pz; }
     if (d->phot_mask) M->phot_mask_h.assign(d->phot_mask, d->phot_mask + d->n_filt);
   }
   // ---- spectrum: per-pixel dispersion, Eq. app_sigeff + fixed sigma_gal (Eq. one_kernel);

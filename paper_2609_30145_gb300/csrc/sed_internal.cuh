@@ -129,6 +129,8 @@ struct ModelDev {
   const double* phot_d;    // [n_filt]
   const double* phot_isig; // [n_filt] 1/sigma (0 when masked out)
   const double* phot_nlog; // [n_filt] -1/2 ln(2 pi sigma^2) (0 when masked out)
+  const float* phot_dn;    // [n_filt] d/sigma and 1/sigma in FP32 (0 when masked out), for the
+  const float* phot_isf;   //   adjoint's per-band weights
   float samp_lam_min, samp_lam_max;
   // spectrum
   int n_pix;
