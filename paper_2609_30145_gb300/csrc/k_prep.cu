@@ -60,14 +60,20 @@ __device__ __forceinline__ float sfh_edge(int i, int NT, double tmax, float lrat
 // t_univ(z), ln(1+z) and 1/(1+z) are cubic Hermite interpolants (FP64) of a
 // table the host fills once per model with FP64 values and their exact
 // derivatives (c/H0/E, -1/(H0 (1+z) E), 1/(1+z), -1/(1+z)^2); the
-// interpolation error is below 1e-10 relative.  GB300's FP64 pipe is narrow,
-// so FP64 is kept to D_L, T_max, ln(1+z) (hi + lo floats for the spectral
-// positions) and the flux scale, ~50 FP64 operations per row; the derivative
-// factors used only by the adjoint are FP32.
+// interpolation error is below 1e-10 relative.  GB300's FP64 pipe is narrow
+// (a warp instruction every 16 SM cycles, whatever the active lanes), so FP64
+// is kept to the interpolation, T_max, ln(1+z) (hi + lo floats for the
+// spectral positions) and a five-term product for the flux scale; 1/D_L, the
+// power of ten and the derivative factors used only by the adjoint are FP32.
 //  D_L = (1+z) D_C, floored at 10 pc;  T_max = t(z) - t(zf);
 //  s = 10^logmass Lsun (1+z) / (4 pi D_L^2) in device flux units, with
-//  10^logmass = 2^n 2^f taken as an FP32 exp2 of the fraction (FP32-grade).
-__device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm) {
+//  10^logmass = 2^n 2^f from an exact FP32 split of logmass log2(10) and an
+//  FP32 exp2 of the fraction (FP32-grade).
+__device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm, int lane) {
+  // All 32 lanes of a warp call it with the same z and lm; lane 0's result is
+  // complete.  Lanes 0-3 each evaluate one of the four interpolants in the same
+  // FP64 instructions (lane & 3 picks the column pair), the others follow by
+  // shuffles: a quarter of the FP64 work of one lane doing all four.
   CosmoRow c{};
   if (!isfinite(z) || !isfinite(lm)) {
     c.status = SED_ROW_BAD_THETA;
@@ -78,22 +84,31 @@ __device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm) {
     const double q = zd * md.ctab_inv_h;
     const int i = min((int)q, md.n_ctab - 1);
     const double u = q - (double)i, v = 1.0 - u;
-    const double* t0 = md.ctab + COSMO_COLS * (size_t)i;
+    const double* t0 = md.ctab + COSMO_COLS * (size_t)i + 2 * (lane & 3);
     const double* t1 = t0 + COSMO_COLS;
     const double h00 = (1.0 + 2.0 * u) * v * v, h10 = u * v * v * md.ctab_h;
     const double h01 = u * u * (3.0 - 2.0 * u), h11 = -u * u * v * md.ctab_h;
-    const double dc = h00 * t0[0] + h10 * t0[1] + h01 * t1[0] + h11 * t1[1];
-    const double tu = h00 * t0[2] + h10 * t0[3] + h01 * t1[2] + h11 * t1[3];
-    const double l1 = h00 * t0[4] + h10 * t0[5] + h01 * t1[4] + h11 * t1[5];
-    const double izp = h00 * t0[6] + h10 * t0[7] + h01 * t1[6] + h11 * t1[7];
+    const double val = h00 * t0[0] + h10 * t0[1] + h01 * t1[0] + h11 * t1[1];
+    const double dc = __shfl_sync(0xffffffffu, val, 0), tu = __shfl_sync(0xffffffffu, val, 1);
+    const double l1 = __shfl_sync(0xffffffffu, val, 2), izp = __shfl_sync(0xffffffffu, val, 3);
     const double tmax = tu - md.t_zf_yr;
     double dl = zp * dc;
     const bool floor10 = dl < 10.0 * PC_CM;
     if (floor10) dl = 10.0 * PC_CM;
-    const double idl = 1.0 / dl;
-    const double e2 = (double)lm * 3.321928094887362;
-    const double en = floor(e2);
-    const double sc = ldexp((double)exp2f((float)(e2 - en)), (int)en) * md.lsun_c * zp * idl * idl;
+    // 1/D_L: the FP32 reciprocal and one Newton step in FP64 (two FMAs instead
+    // of an FP64 division); the flux scale s carries no rounding of it that the
+    // likelihood of a well-fitting row would amplify
+    const float idlf = 1.f / (float)dl;
+    const double idl0 = (double)idlf, idl = fma(idl0, fma(-dl, idl0, 1.0), idl0);
+    // 2^(lm log2 10) from an exact FP32 split: e2 = hi + lo with hi the rounded
+    // product, floor(hi) as the binary exponent, exp2f of the small remainder
+    constexpr float L2T_HI = 3.32192802429199219f;                 // log2(10) rounded to FP32
+    constexpr float L2T_LO = (float)(3.32192809488736234787 - 3.32192802429199218750);  // the rest, 7.06e-8
+    const float hi = lm * L2T_HI;
+    const float lo = fmaf(lm, L2T_HI, -hi) + lm * L2T_LO;
+    const float en = floorf(hi);
+    const float m2 = exp2f((hi - en) + lo);
+    const double sc = (double)ldexpf(m2, (int)en) * md.lsun_c * zp * idl * idl;
     const float izf = (float)izp;
     c.s_spec = (float)sc;
     c.p_phot = (float)(C_AA * sc) * izf * izf;
@@ -102,7 +117,7 @@ __device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm) {
     c.ln1pz_lo = (float)(l1 - (double)c.ln1pz_hi);
     // adjoint factors (FP32): dlnD_L/dz = (D_C + (1+z) c/(H0 E)) / D_L, dt/dz = -1/(H0 (1+z) E)
     const float zpf = 1.f + z, ezf = sqrtf((float)md.Om0 * zpf * zpf * zpf + (1.f - (float)md.Om0));
-    const float dlnd = floor10 ? 0.f : ((float)dc + zpf * (float)md.dh_cm / ezf) * (float)idl;
+    const float dlnd = floor10 ? 0.f : ((float)dc + zpf * (float)md.dh_cm / ezf) * idlf;
     c.dlns_dz = izf - 2.f * dlnd;
     c.dlnp_dz = -izf - 2.f * dlnd;
     c.dtmax_dz = -(float)md.th_yr * izf / ezf;
@@ -225,7 +240,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     th_s[j] = v;
     bad |= !isfinite(v);
   }
-  if (tid == 0) s_cr = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]]);
+  if (warp == 0) {
+    const CosmoRow c = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]], lane);
+    if (lane == 0) s_cr = c;
+  }
   bad = __syncthreads_or(bad);
   th = th_s;
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
@@ -309,16 +327,18 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   float qpart = 0.f;
   int nnz = 0;
   float* Vs = smem + NA * NZ;           // FP8 path: W_k 2^-e_k
+  // the layout tables through the read-only path, so that the unrolled loads
+  // need not wait behind the stores of W
 #pragma unroll 4
   for (int k = tid; k < Kpad; k += blockDim.x) {
-    const int code = L.k_code[k];
+    const int code = __ldg(L.k_code + k);
     float v = 0.f;
     if (code >= 0) {
       const int n = code >> 24, mm = (code >> 16) & 0xff, ag = code & 0xffff;
       const float wn = (n == n0 ? wn0 : 0.f) + (n == n1 && n1 != n0 ? wn1 : 0.f);
       v = wn * Ws[ag * NZ + mm];
     }
-    if (k < L.Ky_pad) qpart += v * L.q_s[k];
+    if (k < L.Ky_pad) qpart += v * __ldg(L.q_s + k);
     nnz += v != 0.f;
     const size_t o = (size_t)p * Kpad + k;
     if (a.W) a.W[o] = v;

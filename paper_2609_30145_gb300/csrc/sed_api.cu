@@ -1034,7 +1034,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   PrepArgs pa{};
   pa.theta = theta; pa.n = n; pa.ld = ld;
   pa.md = M->dv; pa.g = g->dv; pa.L = L->dv();
-  pa.W = w->W;
+  pa.W = precision == SED_PREC_FP32_SIMT ? w->W : nullptr;   // only the CUDA-core contraction reads FP32 W
   pa.W_hi = precision == SED_PREC_FP32 ? w->W_hi : nullptr;
   pa.W_lo = precision == SED_PREC_FP32 ? w->W_lo : nullptr;
   pa.W_bf16 = precision == SED_PREC_BF16 ? w->W_bf16 : nullptr;

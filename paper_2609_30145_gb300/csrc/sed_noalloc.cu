@@ -125,7 +125,8 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   PrepArgs pa{};
   pa.theta = theta; pa.n = n; pa.ld = ld;
   pa.md = M->dv; pa.g = g->dv; pa.L = L->dv();
-  pa.W = W; pa.W_hi = W_hi; pa.W_lo = W_lo; pa.W_bf16 = W_bf;
+  pa.W = precision == SED_PREC_FP32_SIMT ? W : nullptr;   // only the CUDA-core contraction reads FP32 W
+  pa.W_hi = W_hi; pa.W_lo = W_lo; pa.W_bf16 = W_bf;
   pa.rs = rs; pa.err = err;
   cudaError_t e = launch_prep(pa, s);
   if (e == cudaSuccess) {

@@ -171,7 +171,7 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
   pa.theta = sl.theta; pa.n = n; pa.ld = SRV_LD;
   pa.g = g->dv; pa.L = L->dv();
   pa.mtab = sv->mtab; pa.row_model = sl.rowm;
-  pa.W = sl.W;
+  pa.W = sv->prec == SED_PREC_FP32_SIMT ? sl.W : nullptr;   // only the CUDA-core contraction reads FP32 W
   pa.W_hi = f32 ? sl.W_hi : nullptr;
   pa.W_lo = f32 ? sl.W_lo : nullptr;
   pa.W_bf16 = bf ? sl.W_bf16 : nullptr;
