@@ -354,7 +354,7 @@ def run_ours(args):
     th_host = torch.from_numpy(theta).pin_memory()
     lnl_host = torch.empty(B, dtype=torch.float64).pin_memory()
     st_host = torch.empty(B, dtype=torch.int32).pin_memory()
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()   # the caller's stream (a replayable graph needs one that is not the legacy default)
     for _ in range(3):
         model.loglike_host(th_host, prec, stream=stream, out=lnl_host, status=st_host)
     e2e_t = []
@@ -375,8 +375,9 @@ def run_ours(args):
            "p99_ms": round(1e3 * float(np.percentile(e2e_t, 99)), 4),
            "what": "sed_loglike_host with pinned host buffers: theta host -> device, order/prep/contraction/"
                    "epilogue, lnL + status device -> host, stream synchronised; wall clock around each call",
-           "host_path": ("in place: the kernels read theta and write lnL/status over the host link"
-                         if ctx.last_host_path() == 3 else "staged through device memory by async copies")}
+           "host_path": {3: "in place: the kernels read theta and write lnL/status over the host link",
+                         7: "in place over the host link, the call's launches replayed as a CUDA graph"}.get(
+                             ctx.last_host_path(), "staged through device memory by async copies")}
 
     # GPU results for the accuracy comparison of the CPU-baseline leg
     gpu_res = {}

@@ -182,10 +182,11 @@ const char *sed_status_string(sed_status s);
 const char *sed_last_error(const sed_ctx *ctx);
 /* Device bytes currently held by the context. */
 sed_status sed_memory_used(const sed_ctx *ctx, size_t *bytes);
-/* How the last sed_loglike_host call on this context reached its buffers:
- * bit 0 set = theta was read in place, bit 1 set = lnl_out was written in
- * place (both page-locked and device-mapped); 0 = both were staged.  Only
- * valid once such a call has returned SED_OK. */
+/* How the last sed_loglike_host call on this context ran: bit 0 set = theta
+ * was read in place, bit 1 set = lnl_out was written in place (both
+ * page-locked and device-mapped), 0 = both were staged; bit 2 set = the call
+ * replayed a CUDA graph of its launches.  Only valid once such a call has
+ * returned SED_OK. */
 sed_status sed_last_host_path(const sed_ctx *ctx, int *mapped);
 
 sed_status sed_load_grid(sed_ctx *ctx, const sed_grid_desc *desc, sed_grid_id *out);
@@ -251,8 +252,12 @@ sed_status sed_loglike_grad(sed_ctx *ctx, sed_model_id model, const float *theta
  * unified-address system) is used in place: the kernels read theta and write
  * lnl_out / row_status over the host link (NVLink-C2C on a Grace host), so no
  * separate copy sits on the call's critical path.  Any other buffer is staged
- * through device memory with an asynchronous copy.  The result is the same
- * either way, bit for bit.  ld <= 1024.
+ * through device memory with an asynchronous copy.  With every buffer used in
+ * place and a non-NULL stream (not while profiling), the second call with the
+ * same model, buffers, n, ld and precision captures the call's launches into
+ * a CUDA graph, kept with the stream's workspace, and later such calls replay
+ * it; the buffers' contents and the model's data may change between calls.
+ * The result is the same on every path, bit for bit.  ld <= 1024.
  */
 sed_status sed_loglike_host(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld,
                             double *lnl_out, uint32_t *row_status, int precision, void *stream);

@@ -279,6 +279,20 @@ struct Workspace {
   bool last_grad = false;
   int last_n = 0, last_prec = 0, last_kpad = 0, last_nlam = 0;
   bool have_stats = false;
+  // sed_loglike_host on buffers used in place: the call's launches as a CUDA
+  // graph, captured when the same call repeats and replayed after that (the
+  // graph holds this workspace's buffers, so it goes when they are reallocated)
+  struct HostKey {
+    int model = -1;
+    const void *mp = nullptr, *th = nullptr, *lnl = nullptr, *st = nullptr;
+    int n = 0, ld = 0, prec = -1;
+    bool operator==(const HostKey& o) const {
+      return model == o.model && mp == o.mp && th == o.th && lnl == o.lnl && st == o.st && n == o.n && ld == o.ld &&
+             prec == o.prec;
+    }
+  };
+  cudaGraphExec_t host_exec = nullptr;
+  HostKey host_key, host_seen;
 };
 
 }  // namespace sed

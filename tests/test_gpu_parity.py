@@ -310,3 +310,49 @@ def test_host_entry_point_pinned_in_place_and_pageable_staged(ctx):
     ok = ref["status"] == 0
     assert np.array_equal(st_p[:24].astype(np.int64), ref["status"].astype(np.int64))
     assert (np.abs(lnl_p[:24][ok] - ref["lnl"][ok]) / lnl_scale(orc, ref)[ok]).max() < 1e-5
+
+
+def test_host_entry_point_graph_replay_follows_live_data(ctx):
+    """sed_loglike_host on page-locked buffers and a caller's stream: the first
+    call runs the launches directly, the second captures them into a CUDA
+    graph, later ones replay it.  Every call equals the device entry point bit
+    for bit, including after the theta buffer's contents and the model's data
+    change between replays, and a new row count falls back to direct launches."""
+    w, orc, model = case(ctx, "tiny")
+    th32, _ = cases.theta_pair(w, 200, seed=52)
+    th_pin = torch.from_numpy(th32).pin_memory()
+    out = torch.empty(200, dtype=torch.float64).pin_memory()
+    sto = torch.empty(200, dtype=torch.int32).pin_memory()
+    stream = torch.cuda.Stream()
+
+    def device_ref(th):
+        lnl, st = model.loglike(torch.from_numpy(th).cuda(), "fp32")
+        torch.cuda.synchronize()
+        return lnl.cpu().numpy(), st.cpu().numpy()
+
+    paths = []
+    for _ in range(3):
+        model.loglike_host(th_pin, "fp32", stream=stream, out=out, status=sto)
+        paths.append(ctx.last_host_path())
+        ref, st_ref = device_ref(th32)
+        assert np.array_equal(out.numpy(), ref)
+        assert np.array_equal(sto.numpy(), st_ref)
+    assert paths == [3, 7, 7]
+    # new contents in the same page-locked buffer: the replay reads them
+    th2, _ = cases.theta_pair(w, 200, seed=53)
+    th_pin.copy_(torch.from_numpy(th2))
+    model.loglike_host(th_pin, "fp32", stream=stream, out=out, status=sto)
+    assert ctx.last_host_path() == 7
+    assert np.array_equal(out.numpy(), device_ref(th2)[0])
+    # new data for the model: updated in place, so the replay sees it too
+    model.set_data(phot_d=np.asarray(orc.phot_d) * 1.2, phot_sigma=orc.phot_sigma)
+    try:
+        model.loglike_host(th_pin, "fp32", stream=stream, out=out, status=sto)
+        assert ctx.last_host_path() == 7
+        assert np.array_equal(out.numpy(), device_ref(th2)[0])
+    finally:
+        model.set_data(phot_d=orc.phot_d, phot_sigma=orc.phot_sigma)
+    # another row count: a new call, launched directly
+    model.loglike_host(th_pin[:150], "fp32", stream=stream, out=out[:150], status=sto[:150])
+    assert ctx.last_host_path() == 3
+    assert np.array_equal(out.numpy()[:150], device_ref(th2[:150])[0])
