@@ -534,12 +534,17 @@ def bench_serving(ctx, device, args):
         ph, sp = m.forward(torch_from(m.pack(d_true), device), "fp32")
         ph = ph.cpu().numpy()[0].astype(np.float64)
         nz = synth.noise(q["n_filt"] + q["n_pix"], seed=q["seed"])
+        # S/N 20 with a noise floor of 1e-3 of the brightest datum's sigma (bands
+        # and pixels the model leaves dark keep a finite weight)
+        def sig(x):
+            a = np.abs(x)
+            return a / 20 + max(1e-3 * a.max() / 20, 1e-30)
         if q["n_pix"]:
             s0 = sp.cpu().numpy()[0].astype(np.float64)
-            m.set_data(phot_d=ph * (1 + nz[:q["n_filt"]] / 20), phot_sigma=np.abs(ph) / 20 + 1e-40,
-                       spec_d=s0 * (1 + nz[q["n_filt"]:] / 20), spec_sigma=np.abs(s0) / 20 + 1e-60)
+            m.set_data(phot_d=ph * (1 + nz[:q["n_filt"]] / 20), phot_sigma=sig(ph),
+                       spec_d=s0 * (1 + nz[q["n_filt"]:] / 20), spec_sigma=sig(s0))
         else:
-            m.set_data(phot_d=ph * (1 + nz / 20), phot_sigma=np.abs(ph) / 20 + 1e-40)
+            m.set_data(phot_d=ph * (1 + nz / 20), phot_sigma=sig(ph))
         models.append(m)
         thetas.append(m.pack(synth.make_theta(q["batch"], q["n_sfh"], q["zmode"], ranges, seed=q["seed"] + 1)))
     t_setup = time.perf_counter() - t_setup
