@@ -56,7 +56,8 @@ class _Model(C.Structure):
                 ("lsf_mode", C.c_int), ("lsf_value", C.c_void_p),
                 ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
-                ("calib_n", C.c_int), ("calib_sigma", C.c_void_p)]
+                ("calib_n", C.c_int), ("calib_sigma", C.c_void_p),
+                ("floor_phot", C.c_int), ("floor_spec", C.c_int)]
 
 
 def _load():
@@ -121,6 +122,8 @@ class Oracle:
     sample_sigma_gal: int = 0           # 1: sigma_gal (km/s) is the last parameter column
     sigma_gal_max_kms: float = 1000.0   # sampled sigma_gal must lie in [0, this]
     calib_sigma: np.ndarray | None = None   # prior widths s_m of a marginalised calibration polynomial
+    floor_phot: int = 0                 # noise-floor terms of each arm (App. sys_floor): FLOOR_* bits
+    floor_spec: int = 0
     H0: float = PHYS["H0"]
     Om0: float = PHYS["Om0"]
     bc_edge_log_age_yr: float = PHYS["bc_edge_log_age_yr"]
@@ -184,6 +187,9 @@ class Oracle:
         if self.calib_sigma is not None and self.spec_lam is not None:
             m.calib_n = len(self.calib_sigma)
             m.calib_sigma = _p(k(self.calib_sigma))
+            if self.floor_spec:
+                raise ValueError("a spectral noise floor with the marginalised calibration polynomial is not defined here")
+        m.floor_phot, m.floor_spec = int(self.floor_phot), int(self.floor_spec)
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
@@ -307,15 +313,27 @@ def dust_tau(law, lam, tau, index):
     return out
 
 
-def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0):
+FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
+FLOOR_NAMES = ("log_err_scale", "log_f_calib", "log_f_data", "log_jitter")
+
+
+def floor_keys(floor_phot=0, floor_spec=0):
+    """Column names of the noise-floor terms that are on, in the row's order."""
+    return tuple(f"{FLOOR_NAMES[k]}_{arm}" for arm, bits in (("phot", floor_phot), ("spec", floor_spec))
+                 for k in range(4) if (bits >> k) & 1)
+
+
+def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0):
     """Parameter rows in the oracle's layout: sfh[N_T], logzsol[N_T or 1], then
     afe, logmass, zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index,
-    gas_logz, gas_logu, and sigma_gal when the model samples it."""
+    gas_logz, gas_logu, sigma_gal when the model samples it, and the log10 of
+    each noise-floor term that is on (photometry, then spectrum)."""
     nz = n_sfh if zmode == 0 else 1
     n = d["sfh"].shape[0]
     cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh),
             np.asarray(d["logzsol"], dtype=np.float64).reshape(n, nz)]
     for k in ("afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
-              "diffuse_dust_index", "gas_logz", "gas_logu") + (("sigma_gal",) if sample_sigma_gal else ()):
+              "diffuse_dust_index", "gas_logz", "gas_logu") + (("sigma_gal",) if sample_sigma_gal else ()) + \
+            floor_keys(floor_phot, floor_spec):
         cols.append(np.asarray(d[k], dtype=np.float64).reshape(n, 1))
     return np.ascontiguousarray(np.concatenate(cols, axis=1))

@@ -116,8 +116,15 @@ static void bracket(const double *x, int n, double v, int *j0, double *w0, int *
   *j0 = j; *j1 = j + 1; *w0 = 1.0 - t; *w1 = t;
 }
 
+static int n_floor(int bits) {
+  int c = 0;
+  for (int k = 0; k < 4; k++) c += (bits >> k) & 1;
+  return c;
+}
+
 int orc_n_param(const orc_model *md) {
-  return md->n_sfh + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0);
+  return md->n_sfh + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0) +
+         n_floor(md->floor_phot) + n_floor(md->floor_spec);
 }
 
 /* parameter row decoding (layout: sfh[N_T], logzsol[N_T or 1], afe, logmass,
@@ -126,6 +133,8 @@ int orc_n_param(const orc_model *md) {
 typedef struct {
   const double *m, *zeta;
   double afe, logmass, z, tau_bc, alpha_bc, tau_d, delta, gas_logz, gas_logu, sigma_gal;
+  double fl[2][4];   /* noise floor {s, f_calib, f_data, j} of photometry [0] and spectrum [1] */
+  int fl_col[2][4];  /* column of each term in the row, -1 when the term is off */
 } orc_theta;
 
 static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
@@ -136,6 +145,40 @@ static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
   o->afe = s[0]; o->logmass = s[1]; o->z = s[2]; o->tau_bc = s[3]; o->alpha_bc = s[4];
   o->tau_d = s[5]; o->delta = s[6]; o->gas_logz = s[7]; o->gas_logu = s[8];
   o->sigma_gal = md->sample_sigma_gal ? s[9] : md->sigma_gal_kms;
+  /* App. "sys_floor": a term that is off leaves s = 1 and the others 0 */
+  int col = md->n_sfh + nz + 9 + (md->sample_sigma_gal ? 1 : 0);
+  for (int arm = 0; arm < 2; arm++) {
+    int bits = arm == 0 ? md->floor_phot : md->floor_spec;
+    for (int k = 0; k < 4; k++) {
+      o->fl[arm][k] = k == 0 ? 1.0 : 0.0;
+      o->fl_col[arm][k] = -1;
+      if ((bits >> k) & 1) {
+        o->fl[arm][k] = pow(10.0, th[col]);
+        o->fl_col[arm][k] = col++;
+      }
+    }
+  }
+}
+
+/* Eq. "app_noise_floor": the effective variance of a datum with formal error
+ * sigma, model m and datum d under the floor fl = {s, f_calib, f_data, j}. */
+static double eff_var(const double *fl, double sigma, double m, double d) {
+  return fl[0] * fl[0] * sigma * sigma + fl[1] * fl[1] * m * m + fl[2] * fl[2] * d * d + fl[3] * fl[3];
+}
+
+/* Derivatives of one datum's term -r^2/(2v) - ln(2 pi v)/2 (r = d - m, v its
+ * effective variance): returns d term / d m (v depends on m through the
+ * model-anchored f_calib), and adds d term / d log10 of each floor term,
+ * dv/dlog10 x = 2 ln(10) x^2 (sigma^2, m^2, d^2, 1 for s, f_calib, f_data, j). */
+static double floor_terms_grad(const double *fl, double v, double r, double sigma, double m, double d,
+                               double *g) {
+  const double gv = 0.5 * r * r / (v * v) - 0.5 / v;   /* d term / d v */
+  const double l10 = log(10.0);
+  g[0] += gv * 2.0 * l10 * fl[0] * fl[0] * sigma * sigma;
+  g[1] += gv * 2.0 * l10 * fl[1] * fl[1] * m * m;
+  g[2] += gv * 2.0 * l10 * fl[2] * fl[2] * d * d;
+  g[3] += gv * 2.0 * l10 * fl[3] * fl[3];
+  return r / v + gv * 2.0 * fl[1] * fl[1] * m;
 }
 
 static int theta_status(const orc_model *md, const double *th, double *tmax_out, double *cos_out) {
@@ -559,8 +602,9 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
       for (int b = 0; b < md->n_filt; b++) {
         if (phot) phot[b] = ph[b];
         if (md->phot_d && (!md->phot_mask || md->phot_mask[b])) {
-          double s = md->phot_sigma[b], r = (md->phot_d[b] - ph[b]) / s;
-          lnl += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
+          /* Eq. "total_lnlike" with sigma_eff of Eq. "app_noise_floor" (= sigma without a floor) */
+          double v = eff_var(t.fl[0], md->phot_sigma[b], ph[b], md->phot_d[b]), r = md->phot_d[b] - ph[b];
+          lnl += -0.5 * r * r / v - 0.5 * log(2.0 * M_PI * v);
         }
       }
     }
@@ -570,8 +614,8 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
       for (int i = 0; i < md->n_pix; i++) {
         if (spec) spec[i] = sp[i];
         if (md->spec_d && vd[i] && (!md->spec_mask || md->spec_mask[i])) {
-          double s = md->spec_sigma[i], r = (md->spec_d[i] - sp[i]) / s;
-          lnl += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
+          double v = eff_var(t.fl[1], md->spec_sigma[i], sp[i], md->spec_d[i]), r = md->spec_d[i] - sp[i];
+          lnl += -0.5 * r * r / v - 0.5 * log(2.0 * M_PI * v);
           inc[i] = 1;
         }
       }
@@ -760,6 +804,8 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
 
   /* ---------------- likelihood and its derivative with respect to the model */
   double L = 0.0, gscale = 0.0, gz = 0.0, g_sgal = 0.0;
+  /* noise floor (Eq. "app_noise_floor"): d lnL / d log10 of each term, per arm */
+  double gfl[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   if (md->n_filt > 0) {
     double *ph = (double *)malloc(md->n_filt * sizeof(double));
     orc_photometry(md, g->lam, NL, t.z, fnu, ph);
@@ -770,9 +816,10 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
       off += n;
       double ub = 0.0;
       if (md->phot_d && (!md->phot_mask || md->phot_mask[b])) {
-        double s = md->phot_sigma[b], r = (md->phot_d[b] - ph[b]) / s;
-        L += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
-        ub = r / s;
+        double d = md->phot_d[b], m = ph[b], sg = md->phot_sigma[b];
+        double v = eff_var(t.fl[0], sg, m, d), r = d - m;
+        L += -0.5 * r * r / v - 0.5 * log(2.0 * M_PI * v);
+        ub = floor_terms_grad(t.fl[0], v, r, sg, m, d, gfl[0]);
       }
       if (ub == 0.0) continue;
       /* m_b = sum_j R_j x_j dl_j flam(x_j) / Z_b (App. D), as in orc_photometry */
@@ -835,9 +882,10 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     }
     for (int i = 0; i < md->n_pix; i++) {
       if (!(md->spec_d && vd[i] && (!md->spec_mask || md->spec_mask[i]))) continue;
-      double s = md->spec_sigma[i], r = (md->spec_d[i] - sp[i]) / s;
-      L += -0.5 * r * r - 0.5 * log(2.0 * M_PI * s * s);
-      double ui = r / s;
+      double s = md->spec_sigma[i];
+      double v = eff_var(t.fl[1], s, sp[i], md->spec_d[i]), r = md->spec_d[i] - sp[i];
+      L += -0.5 * r * r / v - 0.5 * log(2.0 * M_PI * v);
+      double ui = floor_terms_grad(t.fl[1], v, r, s, sp[i], md->spec_d[i], gfl[1]);
       if (nc) {
         cheb_row(cheb_x(md, i), nc, T);
         double p = 0.0, q = 0.0;
@@ -978,6 +1026,9 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     grad[offs + 7] = has_neb ? g_lz : 0.0;
     grad[offs + 8] = has_neb ? g_lu : 0.0;
     if (md->sample_sigma_gal) grad[offs + 9] = g_sgal;
+    for (int arm = 0; arm < 2; arm++)
+      for (int k = 0; k < 4; k++)
+        if (t.fl_col[arm][k] >= 0) grad[t.fl_col[arm][k]] = gfl[arm][k];
     free(gT); free(gY); free(gO);
   }
   if (st) for (int j = 0; j < np; j++) grad[j] = 0.0;

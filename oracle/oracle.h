@@ -18,7 +18,8 @@
  *   observer frame       Sec. 2.6 (mass, flux factor (1+z)(10pc/D_L)^2)
  *   photometry           App. D, Eqs. "app_phot_row", "app_phot_T"
  *   spectrum             Eq. "one_kernel", App. E, Eqs. "app_siglib", "app_sigeff", "app_response"
- *   likelihood           Eq. "total_lnlike", Eq. "app_spec_lndiag"
+ *   likelihood           Eq. "total_lnlike", Eq. "app_spec_lndiag", the optional
+ *                        noise floor of App. "sys_floor", Eq. "app_noise_floor"
  *   gradient             the chain rule through all of the above (the paper takes its
  *                        gradients by automatic differentiation, Sec. 4)
  */
@@ -61,7 +62,18 @@ typedef struct {
   double sigma_gal_max_kms;    /* sampled sigma_gal must lie in [0, this] */
   int calib_n;                 /* coefficients of the marginalised calibration polynomial (0: none) */
   const double *calib_sigma;   /* [calib_n] prior widths s_m of the coefficients (App. E) */
+  int floor_phot, floor_spec;  /* systematic noise floor of each arm (App. "sys_floor"): ORC_FLOOR_* bits;
+                                  each term on adds a parameter column holding log10 of its value */
 } orc_model;
+
+/* Terms of the noise floor, Eq. "app_noise_floor":
+ * sigma_eff^2 = s^2 sigma^2 + (f_calib |m|)^2 + (f_data |d|)^2 + j^2.  Their
+ * columns follow sigma_gal (when sampled), photometry first, each arm in this
+ * bit order; the jitter j is in the arm's data units. */
+#define ORC_FLOOR_ERR_SCALE 1   /* log10 s */
+#define ORC_FLOOR_F_CALIB 2     /* log10 f_calib (model-anchored) */
+#define ORC_FLOOR_F_DATA 4      /* log10 f_data (data-anchored) */
+#define ORC_FLOOR_JITTER 8      /* log10 j */
 
 /* Row status bits (shared meaning with the library by documentation only). */
 #define ORC_BAD_THETA 1   /* non-finite parameter, or a sampled sigma_gal outside [0, max] */
