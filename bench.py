@@ -37,6 +37,7 @@ WORKLOAD = "phot_107x12x6000_b1024"
 GRAD_WORKLOAD = "specphot_afe_107x12x5x6000_b2048"
 SGAL_WORKLOAD = "specphot_afe_sgal_107x12x5x6000_b2048"   # the same with a sampled sigma_gal
 CALIB_WORKLOAD = "specphot_afe_calib13_107x12x5x6000_b2048"  # the same with a 13-term calibration polynomial
+FLOOR_WORKLOAD = "specphot_afe_floor_107x12x5x6000_b2048"    # the same with every noise-floor term on
 PRECS = ("fp32", "fp32_simt", "bf16", "fp8")
 PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
              "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
@@ -140,7 +141,8 @@ def build_workload(wname, ctx, seed_rows, device):
     nb = len(filt[0])
     kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
               phot_d=np.ones(nb), phot_sigma=np.ones(nb), sample_sigma_gal=w.sample_sigma_gal,
-              sigma_gal_max_kms=w.sigma_gal_max_kms)
+              sigma_gal_max_kms=w.sigma_gal_max_kms, noise_floor_phot=w.floor_phot,
+              noise_floor_spec=w.floor_spec)
     if w.spectrum is not None and w.extra.get("calib_sigma"):
         kw.update(calib_sigma=np.asarray(w.extra["calib_sigma"]))
     spec = None
@@ -155,6 +157,8 @@ def build_workload(wname, ctx, seed_rows, device):
     # mock data: the model at a true parameter row (z = 2), 5% Gaussian noise
     d_true = synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99)
     d_true["zred"][:] = 2.0
+    # noise-floor columns, if any: the model fluxes do not depend on them
+    d_true.update(synth.floor_theta(1, w.floor_phot, w.floor_spec, np.ones(nb), np.ones(1)))
     th_true = torch.from_numpy(model.pack(d_true)).to(device)
     ph, sp_ = model.forward(th_true, "fp32")
     torch.cuda.synchronize()
@@ -168,6 +172,8 @@ def build_workload(wname, ctx, seed_rows, device):
         model.set_data(phot_d=pd, phot_sigma=np.abs(ph) / 20.0, spec_d=s0 * (1 + nz[nb:] / 20.0),
                        spec_sigma=np.abs(s0) / 20.0)
     d = synth.make_theta(w.batch, w.n_sfh, w.zmode, w.ranges, seed=seed_rows)
+    d.update(synth.floor_theta(w.batch, w.floor_phot, w.floor_spec, np.abs(ph) / 20.0,
+                               None if spec is None else np.abs(s0) / 20.0, seed=seed_rows + 1000))
     theta = model.pack(d)
     return w, grid, filt, model, theta, (pd, np.abs(ph) / 20.0)
 
@@ -449,6 +455,20 @@ def bench_gradient(ctx, device, flush, args):
     gcm = time_replays(gc, s, max(5, args.steps // 4), flush)
     fc = capture_step(lambda st: model_c.loglike(tc, "fp32", stream=st, out=lnl, status=stt), s)
     fcm = time_replays(fc, s, max(5, args.steps // 4), flush)
+    # and with the systematic noise floor (all four terms, both arms)
+    wf, _, _, model_f, theta_f, _ = build_workload(FLOOR_WORKLOAD, ctx, 4, device)
+    tf = torch.from_numpy(theta_f).to(device)
+    grad_f = torch.empty_like(tf)
+    gf = capture_step(lambda st: model_f.loglike_grad(tf, "fp32", stream=st, out=(lnl, grad_f, stt)), s)
+    gfm = time_replays(gf, s, max(5, args.steps // 4), flush)
+    ff = capture_step(lambda st: model_f.loglike(tf, "fp32", stream=st, out=lnl, status=stt), s)
+    ffm = time_replays(ff, s, max(5, args.steps // 4), flush)
+    res["noise_floor"] = {"workload": wf.name, "n_param": int(theta_f.shape[1]),
+                          "terms": "error scale, f_calib, f_data, jitter on photometry and spectrum",
+                          "grad_evals_per_s": round(B * len(gfm) / (sum(gfm) * 1e-3), 1),
+                          "grad_ms_per_step": round(sum(gfm) / len(gfm), 4),
+                          "loglike_evals_per_s": round(B * len(ffm) / (sum(ffm) * 1e-3), 1),
+                          "loglike_ms_per_step": round(sum(ffm) / len(ffm), 4)}
     res["calibration_polynomial"] = {"workload": wc.name, "n_coef": len(wc.extra["calib_sigma"]),
                                      "grad_evals_per_s": round(B * len(gcm) / (sum(gcm) * 1e-3), 1),
                                      "grad_ms_per_step": round(sum(gcm) / len(gcm), 4),

@@ -100,7 +100,17 @@ enum {
   SED_KEY_GAS_LOGZ = 9,       /* log10 Z_gas/Zsun (used when use_nebular) */
   SED_KEY_GAS_LOGU = 10,      /* log10 U (used when use_nebular) */
   SED_KEY_SIGMA_GAL = 11,     /* stellar velocity dispersion, km/s (a column only when sample_sigma_gal) */
-  SED_NKEYS = 12
+  /* systematic noise floor (App. sys_floor, Eq. app_noise_floor), log10 of each
+   * term, a column only when the model switches that term on for that arm */
+  SED_KEY_LOG_ERR_SCALE_PHOT = 12,  /* s: scale of the formal errors */
+  SED_KEY_LOG_F_CALIB_PHOT = 13,    /* f_calib: fraction of |model| */
+  SED_KEY_LOG_F_DATA_PHOT = 14,     /* f_data: fraction of |datum| */
+  SED_KEY_LOG_JITTER_PHOT = 15,     /* j: additive, in the photometric data's units */
+  SED_KEY_LOG_ERR_SCALE_SPEC = 16,
+  SED_KEY_LOG_F_CALIB_SPEC = 17,
+  SED_KEY_LOG_F_DATA_SPEC = 18,
+  SED_KEY_LOG_JITTER_SPEC = 19,     /* j in the spectral data's units */
+  SED_NKEYS = 20
 };
 
 typedef struct sed_ctx sed_ctx;
@@ -170,9 +180,23 @@ typedef struct {
    * spectra returned by sed_forward stay uncalibrated (mu). */
   int calib_n;
   const double *calib_sigma;
+  /* Systematic noise floor (App. sys_floor, Eq. app_noise_floor), per arm: each
+   * datum's variance becomes sigma_eff^2 = s^2 sigma^2 + (f_calib |m|)^2 +
+   * (f_data |d|)^2 + j^2 and its lnL term -r^2/(2 sigma_eff^2) -
+   * ln(2 pi sigma_eff^2)/2, with m the model and d the datum.  A SED_FLOOR_*
+   * bit switches a term on and gives it a parameter column (key
+   * SED_KEY_LOG_*_PHOT / _SPEC) holding log10 of its value; a term that is off
+   * leaves s = 1, the others 0.  0 = the plain Gaussian (the default).  A
+   * spectral floor needs a spectrum and no calibration polynomial
+   * (SED_EUNSUPPORTED); a photometric one needs filters. */
+  int noise_floor_phot, noise_floor_spec;
 } sed_model_desc;
 
 #define SED_MAX_CALIB 13
+#define SED_FLOOR_ERR_SCALE 1
+#define SED_FLOOR_F_CALIB 2
+#define SED_FLOOR_F_DATA 4
+#define SED_FLOOR_JITTER 8
 
 /* Context on one CUDA device; hbm_budget_bytes = 0 means no limit. */
 sed_status sed_create(sed_ctx **out, int device, size_t hbm_budget_bytes);

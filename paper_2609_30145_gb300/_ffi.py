@@ -19,7 +19,10 @@ DUST_POWER_LAW, DUST_KC13 = 0, 1
 LSF_R_FWHM, LSF_R_SIGMA, LSF_FWHM_AA, LSF_SIGMA_AA, LSF_SIGMA_KMS, LSF_FWHM_KMS = range(6)
 ROW_BAD_THETA, ROW_BAD_Z, ROW_BAD_TMAX, ROW_NONFINITE, ROW_DEVICE_TIMEOUT = 1, 2, 4, 16, 32
 KEYS = ("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
-        "diffuse_dust_index", "gas_logz", "gas_logu", "sigma_gal")
+        "diffuse_dust_index", "gas_logz", "gas_logu", "sigma_gal",
+        "log_err_scale_phot", "log_f_calib_phot", "log_f_data_phot", "log_jitter_phot",
+        "log_err_scale_spec", "log_f_calib_spec", "log_f_data_spec", "log_jitter_spec")
+FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
 NKEYS = len(KEYS)
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -43,7 +46,8 @@ class ModelDesc(C.Structure):
                 ("spec_mask", P), ("lsf_mode", C.c_int), ("lsf_value", P),
                 ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
-                ("calib_n", C.c_int), ("calib_sigma", P)]
+                ("calib_n", C.c_int), ("calib_sigma", P),
+                ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int)]
 
 
 class StageStats(C.Structure):

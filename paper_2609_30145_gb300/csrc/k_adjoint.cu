@@ -24,6 +24,7 @@
 // reproducible.
 #include "atten.cuh"
 #include "calib.cuh"
+#include "floor.cuh"
 #include "locate.cuh"
 #include "sed_internal.cuh"
 
@@ -32,8 +33,8 @@ namespace sed {
 constexpr int EB_THREADS = 256;
 constexpr int EB_WARPS = EB_THREADS / 32;
 constexpr int EB_MAX_BANDS = 128;
-constexpr int EB_NRED = 11;   // per-warp partial sums: 9 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
-constexpr int EB_NREDF = 9;
+constexpr int EB_NRED = 15;   // per-warp partial sums: 13 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
+constexpr int EB_NREDF = 13;
 
 __device__ __forceinline__ float tf32_rna_dev(float x) {
   uint32_t r;
@@ -209,7 +210,12 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     // d lnL / d(band flux) = (d - m)/sigma^2, formed in FP32 from the normalised
     // datum and 1/sigma (0 for a masked band); times p_phot it weighs F
     const float isf = md.phot_isf[b];
-    const float c_b = (md.phot_dn[b] - mb * isf) * (isf * rs.p_phot);
+    float wb = md.phot_dn[b] - mb * isf;   // (d - m)/sigma; with a noise floor sigma d term / d m
+    if (md.floor_bits[0] && isf != 0.f) {
+      const float mn = mb * isf, dn = md.phot_dn[b], q = floor_q(rs.fl[0], mn, dn, rs.fl[0][3] * isf);
+      wb = floor_dm(rs.fl[0], wb, q, floor_gq(wb, q), mn);
+    }
+    const float c_b = wb * (isf * rs.p_phot);
     if (lane == 0) {
       mbp[b] = mb;
       ubp[b] = c_b;
@@ -267,6 +273,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   //      model mu/sigma; the constants -1/2 ln(2 pi sigma^2) in FP64.
   double l_spec = 0.0, um_spec = 0.0;
   float chi = 0.f, um_f = 0.f, gz_spec = 0.f, g_sgal = 0.f;
+  float gfs[4] = {0.f, 0.f, 0.f, 0.f};   // d lnL / d log10 of the spectral noise-floor terms
   const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
   for (int i = tid; i < md.n_pix; i += EB_THREADS) {
     float xh, xl;
@@ -329,8 +336,17 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     const bool inc = valid && isf != 0.f;
     const float ms = inc ? mi * isf : 0.f;   // mu / sigma
     const float rn = md.spec_dn[i] - ms;     // (d - mu) / sigma where included
+    float wsn = rn;                          // sigma d term / d mu
     if (inc) {
-      chi = fmaf(-0.5f * rn, rn, chi);
+      if (md.floor_bits[1]) {                // sigma_eff of Eq. app_noise_floor
+        const float dn = md.spec_dn[i], jn = rs.fl[1][3] * isf, q = floor_q(rs.fl[1], ms, dn, jn);
+        const float gq = floor_gq(rn, q);
+        chi -= 0.5f * (rn * rn / q + logf(q));
+        wsn = floor_dm(rs.fl[1], rn, q, gq, ms);
+        floor_dparam(rs.fl[1], gq, ms, dn, jn, gfs);
+      } else {
+        chi = fmaf(-0.5f * rn, rn, chi);
+      }
       l_spec += md.spec_nlog[i];
     }
     if (md.calib_n) {
@@ -340,9 +356,10 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       dvs_s[i] = dvs;
       cw_s[i] = cw;
     } else if (inc) {
-      // d lnL / d mu_i = r_i / sigma_i^2; d lnL / d v_i = that x s_spec (mu = s_spec v)
-      um_f = fmaf(rn, ms, um_f);
-      const float us = rn * (isf * rs.s_spec);
+      // d lnL / d mu_i = r_i / sigma_i^2 (wsn / sigma_i with a noise floor);
+      // d lnL / d v_i = that x s_spec (mu = s_spec v)
+      um_f = fmaf(wsn, ms, um_f);
+      const float us = wsn * (isf * rs.s_spec);
       gz_spec += us * dv * (-rs.inv1pz);
       // s = sqrt(sigma_fix^2 + sigma_gal^2) / c: ds/dsigma_gal = (sigma_gal / c) / (s c)
       if (md.sample_sgal && s > 0.f) g_sgal += us * dvs * (rs.sg_ln / (s * (float)C_KMS));
@@ -542,7 +559,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   // ---- fixed-order reductions of the per-thread pieces: the FP32 sums within
   //      the warp in FP32, lnL and d lnL/d ln(mass) in FP64; across the warps
   //      in FP64, one column per lane of warp 0
-  float vf[EB_NREDF] = {g_tbc, g_abc, g_td, g_dl, g_lz, g_lu, gz_gather + gz_spec, g_qy, g_sgal};
+  float vf[EB_NREDF] = {g_tbc, g_abc, g_td, g_dl, g_lz, g_lu, gz_gather + gz_spec, g_qy, g_sgal,
+                        gfs[0], gfs[1], gfs[2], gfs[3]};
 #pragma unroll
   for (int q = 0; q < EB_NREDF; ++q) {
 #pragma unroll
@@ -565,18 +583,27 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     if (lane < EB_NRED)
       for (int w = 0; w < EB_WARPS; ++w) col += red[w][lane];
     // the photometric lnL terms and d lnL/d ln(mass) pieces in FP64, one band per lane
-    double bl = 0.0, bu = 0.0;
+    double bl = 0.0, bu = 0.0, gfp[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = lane; b < md.n_filt; b += 32) {
       if (md.phot_isig[b] != 0.0) {
-        const double mb = (double)mbp[b], rr = (md.phot_d[b] - mb) * md.phot_isig[b];
-        bl += -0.5 * rr * rr + md.phot_nlog[b];
-        bu += rr * md.phot_isig[b] * mb;
+        const double is = md.phot_isig[b], mn = (double)mbp[b] * is, dn = md.phot_d[b] * is, rr = dn - mn;
+        if (md.floor_bits[0]) {   // sigma_eff of Eq. app_noise_floor
+          const double jn = (double)rs.fl[0][3] * is, q = floor_q(rs.fl[0], mn, dn, jn), gq = floor_gq(rr, q);
+          bl += -0.5 * (rr * rr / q + log(q)) + md.phot_nlog[b];
+          bu += floor_dm(rs.fl[0], rr, q, gq, mn) * mn;
+          floor_dparam(rs.fl[0], gq, mn, dn, jn, gfp);
+        } else {
+          bl += -0.5 * rr * rr + md.phot_nlog[b];
+          bu += rr * mn;
+        }
       }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       bl += __shfl_xor_sync(0xffffffffu, bl, o);
       bu += __shfl_xor_sync(0xffffffffu, bu, o);
+      if (md.floor_bits[0])
+        for (int k = 0; k < 4; ++k) gfp[k] += __shfl_xor_sync(0xffffffffu, gfp[k], o);
     }
     double s[EB_NRED];
 #pragma unroll
@@ -597,6 +624,10 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       rg[RG_Z] = um_phot * (double)rs.dlnp_dz + um_sp * (double)rs.dlns_dz + s[6];
       rg[RG_QY] = s[7];
       rg[RG_SIGMA_GAL] = s[8];
+      for (int k = 0; k < 4; ++k) {
+        rg[RG_FLOOR + k] = gfp[k];
+        rg[RG_FLOOR + 4 + k] = s[9 + k];
+      }
       rg[RG_BAD] = stt ? 1.0 : 0.0;
       if (a.lnl) a.lnl[rs.orig] = lnl;
       if (a.status) a.status[rs.orig] = stt;

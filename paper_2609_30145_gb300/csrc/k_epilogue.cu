@@ -18,6 +18,7 @@
 #include "locate.cuh"
 #include "atten.cuh"
 #include "calib.cuh"
+#include "floor.cuh"
 
 namespace sed {
 
@@ -184,8 +185,13 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     const bool inc = valid && isf != 0.f;
     const float ms = inc ? mi * isf : 0.f;   // mu / sigma
     if (inc) {
-      const float rn = md.spec_dn[i] - ms;   // (d - mu) / sigma
-      chi = fmaf(-0.5f * rn, rn, chi);
+      const float dn = md.spec_dn[i], rn = dn - ms;   // (d - mu) / sigma
+      if (md.floor_bits[1]) {                         // sigma_eff of Eq. app_noise_floor
+        const float q = floor_q(rs.fl[1], ms, dn, rs.fl[1][3] * isf);
+        chi -= 0.5f * (rn * rn / q + logf(q));
+      } else {
+        chi = fmaf(-0.5f * rn, rn, chi);
+      }
       part += md.spec_nlog[i];
     }
     if (md.calib_n) mu_s[i] = ms;
@@ -236,8 +242,13 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     double pv = 0.0;
     for (int b = lane; b < md.n_filt; b += 32) {
       if (md.phot_isig[b] != 0.0) {
-        const double rr = (md.phot_d[b] - (double)mb_s[b]) * md.phot_isig[b];
-        pv += -0.5 * rr * rr + md.phot_nlog[b];
+        const double is = md.phot_isig[b], mn = (double)mb_s[b] * is, dn = md.phot_d[b] * is, rr = dn - mn;
+        if (md.floor_bits[0]) {   // sigma_eff of Eq. app_noise_floor
+          const double q = floor_q(rs.fl[0], mn, dn, (double)rs.fl[0][3] * is);
+          pv += -0.5 * (rr * rr / q + log(q)) + md.phot_nlog[b];
+        } else {
+          pv += -0.5 * rr * rr + md.phot_nlog[b];
+        }
       }
     }
 #pragma unroll

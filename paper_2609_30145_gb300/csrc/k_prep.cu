@@ -430,6 +430,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.alpha_bc = th[md.offs[SED_KEY_ALPHA_POW]];
     rs.tau_d = th[md.offs[SED_KEY_DIFFUSE_TAU]];
     rs.delta = th[md.offs[SED_KEY_DIFFUSE_INDEX]];
+    // noise-floor terms (App. sys_floor): 10^column for a term that is on
+    for (int arm = 0; arm < 2; ++arm)
+      for (int k = 0; k < 4; ++k)
+        rs.fl[arm][k] = ((md.floor_bits[arm] >> k) & 1) ? exp10f(th[md.offs[SED_KEY_LOG_ERR_SCALE_PHOT + 4 * arm + k]])
+                                                        : (k == 0 ? 1.f : 0.f);
     rs.log2_qy = qy > 0.f ? log2f(qy) : -INFINITY;
     if (md.use_neb) {
       int u0, u1, z0, z1;
@@ -628,6 +633,10 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     out[md.offs[SED_KEY_GAS_LOGZ]] = md.use_neb ? (float)rg[RG_GAS_LOGZ] : 0.f;
     out[md.offs[SED_KEY_GAS_LOGU]] = md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f;
     if (md.sample_sgal) out[md.offs[SED_KEY_SIGMA_GAL]] = (float)rg[RG_SIGMA_GAL];
+    for (int arm = 0; arm < 2; ++arm)
+      for (int k = 0; k < 4; ++k)
+        if ((md.floor_bits[arm] >> k) & 1)
+          out[md.offs[SED_KEY_LOG_ERR_SCALE_PHOT + 4 * arm + k]] = (float)rg[RG_FLOOR + 4 * arm + k];
   }
   if (md.zmode == 0)
     for (int i = tid; i < NT; i += blockDim.x) out[md.offs[SED_KEY_LOGZSOL] + i] = gzeta[i];

@@ -706,6 +706,12 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   }
   if (d->sample_sigma_gal && !(d->sigma_gal_max_kms > 0 && d->sigma_gal_max_kms < 1e5))
     return fail(ctx, SED_EINVAL, "sigma_gal_max_kms must be in (0, 1e5) when sigma_gal is sampled");
+  if (d->noise_floor_phot < 0 || d->noise_floor_phot > 15 || d->noise_floor_spec < 0 || d->noise_floor_spec > 15)
+    return fail(ctx, SED_EINVAL, "noise_floor_phot / noise_floor_spec must be SED_FLOOR_* bits (0..15)");
+  if (d->noise_floor_phot && d->n_filt <= 0) return fail(ctx, SED_EINVAL, "a photometric noise floor needs filters");
+  if (d->noise_floor_spec && d->n_pix <= 0) return fail(ctx, SED_EINVAL, "a spectral noise floor needs a spectrum");
+  if (d->noise_floor_spec && d->calib_n > 0)
+    return fail(ctx, SED_EUNSUPPORTED, "a spectral noise floor with the calibration polynomial is not supported");
 
   Model* M = new Model();
   M->grid = d->grid;
@@ -723,6 +729,14 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   for (int k = SED_KEY_AFE; k <= SED_KEY_GAS_LOGU; k++) dv.offs[k] = o++;
   dv.offs[SED_KEY_SIGMA_GAL] = o;
   o += d->sample_sigma_gal ? 1 : 0;
+  // noise-floor terms (App. sys_floor): photometry then spectrum, in SED_FLOOR_* bit order
+  dv.floor_bits[0] = d->noise_floor_phot;
+  dv.floor_bits[1] = d->noise_floor_spec;
+  for (int arm = 0; arm < 2; arm++)
+    for (int k = 0; k < 4; k++) {
+      dv.offs[SED_KEY_LOG_ERR_SCALE_PHOT + 4 * arm + k] = o;
+      o += (dv.floor_bits[arm] >> k) & 1;
+    }
   dv.n_param = o;
   dv.zf = d->zf;
   dv.Om0 = d->Om0;

@@ -67,6 +67,7 @@ struct RowScal {
   int orig;         // the caller's index of this row (rows are processed in redshift order)
   int nnz;          // non-zero weights of the row
   float sg_ln;      // sampled sigma_gal / c (ln-lambda units); 0 with a fixed sigma_gal
+  float fl[2][4];   // noise floor {s, f_calib, f_data, j} of photometry [0] and spectrum [1]
 };
 
 // Cosmology and observer-frame scalars of one row (computed at the start of k_prep).
@@ -143,6 +144,7 @@ struct ModelDev {
   double calib_isig2[SED_MAX_CALIB];
   double calib_logdet_lam;
   const float* pix_cx;
+  int floor_bits[2];       // noise-floor terms on (SED_FLOOR_* bits) of photometry [0] and spectrum [1]
   int sample_sgal;         // 1: each row carries sigma_gal (km/s), joined in quadrature per pixel
   float sgal_max_kms;      // sampled sigma_gal range [0, sgal_max_kms]
   // spectral data, normalised per pixel so that the per-pixel terms stay in FP32
@@ -232,7 +234,8 @@ enum {
   RG_TAU_BC = 0, RG_ALPHA_BC, RG_TAU_D, RG_DELTA, RG_GAS_LOGZ, RG_GAS_LOGU, RG_LOGMASS, RG_Z, RG_QY,
   RG_BAD,   // non-zero: the row's likelihood is not finite (gradient row written as zeros)
   RG_SIGMA_GAL,   // dlnL/dsigma_gal (km/s) of a sampled sigma_gal
-  RGRAD = 16
+  RG_FLOOR,       // 8 slots: dlnL/dlog10 of the noise-floor terms, photometry then spectrum
+  RGRAD = 24
 };
 
 // Per-stream scratch.

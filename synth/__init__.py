@@ -230,6 +230,30 @@ def make_theta(n_rows, n_sfh, zmode, ranges, seed=4):
     return out
 
 
+FLOOR_NAMES = ("log_err_scale", "log_f_calib", "log_f_data", "log_jitter")
+
+
+def floor_theta(n_rows, floor_phot, floor_spec, phot_sigma=None, spec_sigma=None, seed=8):
+    """log10 values of the noise-floor terms that are on, keyed like the
+    library's columns: error scale in [-0.2, 0.3], fractions in [-2.5, -1], the
+    jitter (in the data's units) within a decade below the median error."""
+    rng = _rng(seed)
+    out = {}
+    for arm, bits, sg in (("phot", floor_phot, phot_sigma), ("spec", floor_spec, spec_sigma)):
+        for k, name in enumerate(FLOOR_NAMES):
+            if not (bits >> k) & 1:
+                continue
+            if k == 0:
+                lo, hi = -0.2, 0.3
+            elif k < 3:
+                lo, hi = -2.5, -1.0
+            else:
+                m = float(np.log10(np.median(np.abs(sg))))
+                lo, hi = m - 1.0, m
+            out[f"{name}_{arm}"] = lo + (hi - lo) * rng.random(n_rows)
+    return out
+
+
 def noise(shape, seed=5):
     return _rng(seed).standard_normal(shape)
 
@@ -255,6 +279,8 @@ class Workload:
     sigma_gal_kms: float = 0.0
     sample_sigma_gal: int = 0          # 1: sigma_gal (km/s) is a parameter, drawn from ranges["sigma_gal"]
     sigma_gal_max_kms: float = 1000.0
+    floor_phot: int = 0                # noise-floor terms on (bits: 1 err scale, 2 f_calib, 4 f_data, 8 jitter)
+    floor_spec: int = 0
     extra: dict = field(default_factory=dict)
 
 
@@ -304,6 +330,10 @@ WORKLOADS["specphot_afe_sgal_107x12x5x6000_b2048"] = Workload(**{
 WORKLOADS["specphot_afe_calib13_107x12x5x6000_b2048"] = Workload(**{
     **_s.__dict__, "name": "specphot_afe_calib13_107x12x5x6000_b2048",
     "extra": {"calib_sigma": [0.2] + [0.1] * 12}})
+# the same fit with every term of the systematic noise floor on for both arms
+# (App. sys_floor): error scale, model- and data-anchored fractions, jitter
+WORKLOADS["specphot_afe_floor_107x12x5x6000_b2048"] = Workload(**{
+    **_s.__dict__, "name": "specphot_afe_floor_107x12x5x6000_b2048", "floor_phot": 15, "floor_spec": 15})
 # mixed-precision contraction: the paper-scale photometric batch at 4096 rows
 _w = WORKLOADS["phot_107x12x6000_b1024"]
 WORKLOADS["phot_107x12x6000_b4096"] = Workload(**{**_w.__dict__, "name": "phot_107x12x6000_b4096",

@@ -18,7 +18,8 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
     filt = filters if filters is not None else synth.pack_filters(synth.workload_filters(w))
     kw = dict(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
               use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
-              sample_sigma_gal=w.sample_sigma_gal, sigma_gal_max_kms=w.sigma_gal_max_kms)
+              sample_sigma_gal=w.sample_sigma_gal, sigma_gal_max_kms=w.sigma_gal_max_kms,
+              floor_phot=w.floor_phot, floor_spec=w.floor_spec)
     nb = len(filt[0])
     kw.update(phot_d=np.ones(nb), phot_sigma=np.ones(nb), phot_mask=np.ones(nb, np.uint8))
     if w.spectrum is not None:
@@ -31,7 +32,11 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
                   calib_sigma=None if calib_sigma is None else np.asarray(calib_sigma, dtype=np.float64))
     orc = oracle.Oracle(**kw)
     if with_data:
-        th_true = theta_rows(w, 1, seed=99)
+        th_true = oracle.pack_theta(synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99), w.n_sfh, w.zmode,
+                                    w.sample_sigma_gal)
+        if w.floor_phot or w.floor_spec:   # the truth row only makes the data: floors off for it
+            orc.floor_phot, orc.floor_spec = 0, 0
+            orc._rebuild_model()
         th_true[0, w.n_sfh + (w.n_sfh if w.zmode == 0 else 1) + 2] = min(2.0, w.zf * 0.5)  # zred
         res = orc.eval(th_true)
         assert res["status"][0] == 0
@@ -42,15 +47,26 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
         orc.set_data(phot_d=ph * (1 + nz[:ph.size] / snr), phot_sigma=np.abs(ph) / snr,
                      spec_d=(sp_ * (1 + nz[ph.size:] / snr)) if sp_.size else None,
                      spec_sigma=(np.abs(sp_) / snr) if sp_.size else None)
+        if w.floor_phot or w.floor_spec:
+            orc.floor_phot, orc.floor_spec = w.floor_phot, w.floor_spec
+            orc._rebuild_model()
     return orc
 
 
-def theta_dict(w: synth.Workload, n, seed=4):
-    return synth.make_theta(n, w.n_sfh, w.zmode, w.ranges, seed=seed)
+def theta_dict(w: synth.Workload, n, seed=4, orc=None):
+    """Parameter draws; with a noise floor, its columns too (the jitter's range
+    follows the errors of the oracle `orc` holds)."""
+    d = synth.make_theta(n, w.n_sfh, w.zmode, w.ranges, seed=seed)
+    if w.floor_phot or w.floor_spec:
+        d.update(synth.floor_theta(n, w.floor_phot, w.floor_spec,
+                                   None if orc is None else orc.phot_sigma,
+                                   None if orc is None else orc.spec_sigma, seed=seed + 1000))
+    return d
 
 
-def theta_rows(w: synth.Workload, n, seed=4):
-    return oracle.pack_theta(theta_dict(w, n, seed), w.n_sfh, w.zmode, w.sample_sigma_gal)
+def theta_rows(w: synth.Workload, n, seed=4, orc=None):
+    return oracle.pack_theta(theta_dict(w, n, seed, orc), w.n_sfh, w.zmode, w.sample_sigma_gal,
+                             w.floor_phot, w.floor_spec)
 
 
 def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
@@ -63,6 +79,7 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
     gid = cache[key][0]
     kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law,
               sample_sigma_gal=orc.sample_sigma_gal, sigma_gal_max_kms=orc.sigma_gal_max_kms,
+              noise_floor_phot=orc.floor_phot, noise_floor_spec=orc.floor_spec,
               bc_edge_log_age_yr=orc.bc_edge_log_age_yr, H0=orc.H0, Om0=orc.Om0,
               filters=orc.filters, phot_d=orc.phot_d, phot_sigma=orc.phot_sigma,
               phot_mask=orc.phot_mask)
@@ -74,9 +91,9 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
     return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)
 
 
-def theta_pair(w: synth.Workload, n, seed=4):
+def theta_pair(w: synth.Workload, n, seed=4, orc=None):
     """Parameter rows rounded to FP32 (library input) and the same values in FP64 (oracle input)."""
-    th32 = theta_rows(w, n, seed).astype(np.float32)
+    th32 = theta_rows(w, n, seed, orc).astype(np.float32)
     return th32, th32.astype(np.float64)
 
 

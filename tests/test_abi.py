@@ -40,9 +40,14 @@ def test_enum_values_match_header():
     src = open(os.path.join(ROOT, "include", "sed.h")).read()
     for name, val in [("SED_PREC_FP32", _ffi.PREC_FP32), ("SED_PREC_FP32_SIMT", _ffi.PREC_FP32_SIMT),
                       ("SED_PREC_BF16", _ffi.PREC_BF16), ("SED_EUNSUPPORTED", _ffi.SED_EUNSUPPORTED),
-                      ("SED_KEY_GAS_LOGU", _ffi.NKEYS - 2), ("SED_KEY_SIGMA_GAL", _ffi.NKEYS - 1),
+                      ("SED_KEY_GAS_LOGU", _ffi.KEYS.index("gas_logu")),
+                      ("SED_KEY_SIGMA_GAL", _ffi.KEYS.index("sigma_gal")),
+                      ("SED_KEY_LOG_ERR_SCALE_PHOT", _ffi.KEYS.index("log_err_scale_phot")),
+                      ("SED_KEY_LOG_JITTER_SPEC", _ffi.NKEYS - 1),
+                      ("SED_FLOOR_ERR_SCALE", _ffi.FLOOR_ERR_SCALE), ("SED_FLOOR_F_CALIB", _ffi.FLOOR_F_CALIB),
+                      ("SED_FLOOR_F_DATA", _ffi.FLOOR_F_DATA), ("SED_FLOOR_JITTER", _ffi.FLOOR_JITTER),
                       ("SED_NKEYS", _ffi.NKEYS)]:
-        m = re.search(name + r"\s*=\s*(\d+)", src)
+        m = re.search(name + r"\b\s*=?\s*(\d+)", src)   # enum "NAME = v" or "#define NAME v"
         assert m and int(m.group(1)) == val, name
 
 
@@ -61,17 +66,23 @@ def test_layout_packing_matches_oracle_layout():
     import oracle
     import synth
     from paper_2609_30145_gb300.api import Model
+    from paper_2609_30145_gb300 import _ffi
     for zmode in (0, 1):
         for sgal in (0, 1):
-            ranges = dict(synth.WORKLOADS["tiny_phot_16x4x512"].ranges, sigma_gal=(50.0, 500.0))
-            d = synth.make_theta(5, 7, zmode, ranges, seed=3)
-            m = Model.__new__(Model)
-            nz = 7 if zmode == 0 else 1
-            offs = [0, 7] + [7 + nz + i for i in range(10)]
-            m.n_param = 7 + nz + 9 + sgal     # sigma_gal has a column only when sampled
-            m.offsets = dict(zip(("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow",
-                                  "diffuse_tau_kc", "diffuse_dust_index", "gas_logz", "gas_logu",
-                                  "sigma_gal"), offs))
-            a = m.pack(d, dtype=np.float64)
-            b = oracle.pack_theta(d, 7, zmode, sample_sigma_gal=sgal)
-            np.testing.assert_array_equal(a, b)
+            for fp, fs in ((0, 0), (5, 0), (0, 15), (9, 6)):
+                ranges = dict(synth.WORKLOADS["tiny_phot_16x4x512"].ranges, sigma_gal=(50.0, 500.0))
+                d = synth.make_theta(5, 7, zmode, ranges, seed=3)
+                rng = np.random.default_rng(4)
+                for k in _ffi.KEYS[12:]:
+                    d[k] = rng.uniform(-2.0, 0.5, 5)
+                m = Model.__new__(Model)
+                nz = 7 if zmode == 0 else 1
+                # the library's layout: sigma_gal and each floor term have a column only when on
+                widths = [7, nz] + [1] * 9 + [sgal] + [(fp >> k) & 1 for k in range(4)] + \
+                         [(fs >> k) & 1 for k in range(4)]
+                offs = list(np.cumsum([0] + widths[:-1]))
+                m.n_param = int(sum(widths))
+                m.offsets = dict(zip(_ffi.KEYS, offs))
+                a = m.pack(d, dtype=np.float64)
+                b = oracle.pack_theta(d, 7, zmode, sample_sigma_gal=sgal, floor_phot=fp, floor_spec=fs)
+                np.testing.assert_array_equal(a, b)

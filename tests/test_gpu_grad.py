@@ -192,6 +192,31 @@ def test_calibration_polynomial_grad_vs_oracle(ctx, prec):
     assert (np.abs(lnl[ok] - fwd["lnl"][ok]) / scale).max() < 1e-5
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_noise_floor_grad_vs_oracle(ctx, prec):
+    """The adjoint with every noise-floor term on for both arms: 150 rows, every
+    column (the eight floor columns and logmass, whose derivative gains the
+    model-anchored term) against the oracle's analytic gradient."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_floor_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=150)
+    if "floor" not in _CACHE:
+        orc = cases.oracle_for(w)
+        _CACHE["floor"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE["floor"]
+    th32, th64 = cases.theta_pair(w, w.batch, seed=62, orc=orc)
+    lnl, g, st = gpu_grad(model, th32, prec)
+    ref = orc.grad(th64)
+    assert np.array_equal(st, ref["status"])
+    kinks = {int(r): model.offsets["zred"] for r in np.nonzero(cases.kink_rows(orc, th64))[0]}
+    check_grad(g, ref["grad"], st, skip=kinks)
+    ok = st == 0
+    fwd = orc.eval(th64)
+    scale = cases.lnl_scale(orc, fwd)[ok]
+    assert (np.abs(lnl[ok] - fwd["lnl"][ok]) / scale).max() < 1e-5
+    # the floor columns carry a gradient
+    assert np.abs(g[ok][:, orc.n_param - 8:orc.n_param]).max() > 0
+
+
 def test_specphot_grad_vs_central_differences(ctx):
     """The adjoint against central finite differences of the FP64 oracle's
     forward model (h = 1e-7 relative) on 16 rows x all parameters."""

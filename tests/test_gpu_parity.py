@@ -356,3 +356,22 @@ def test_host_entry_point_graph_replay_follows_live_data(ctx):
     model.loglike_host(th_pin[:150], "fp32", stream=stream, out=out[:150], status=sto[:150])
     assert ctx.last_host_path() == 3
     assert np.array_equal(out.numpy()[:150], device_ref(th2[:150])[0])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_noise_floor_parity(ctx, prec):
+    """Spectro-photometric [a/Fe] model with every term of the systematic noise
+    floor on for both arms (App. sys_floor, Eq. app_noise_floor: error scale,
+    model- and data-anchored fractions, jitter; eight log10 columns): 150 rows,
+    every row's lnL and model against the oracle."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_floor_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=150)
+    if "floor" not in _CACHE:
+        orc = cases.oracle_for(w)
+        _CACHE["floor"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE["floor"]
+    assert model.n_param == orc.n_param
+    th32, th64 = cases.theta_pair(w, w.batch, seed=61, orc=orc)
+    ref = orc.eval(th64)
+    got = run_gpu(model, th32, prec)
+    check(ref, got, prec, orc=orc)
