@@ -57,7 +57,7 @@ class _Model(C.Structure):
                 ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", C.c_void_p),
-                ("floor_phot", C.c_int), ("floor_spec", C.c_int)]
+                ("sfh_scheme", C.c_int), ("floor_phot", C.c_int), ("floor_spec", C.c_int)]
 
 
 def _load():
@@ -122,6 +122,7 @@ class Oracle:
     sample_sigma_gal: int = 0           # 1: sigma_gal (km/s) is the last parameter column
     sigma_gal_max_kms: float = 1000.0   # sampled sigma_gal must lie in [0, this]
     calib_sigma: np.ndarray | None = None   # prior widths s_m of a marginalised calibration polynomial
+    sfh_scheme: int = 0                 # 0 step (N_T bin masses), 1 linear (N_T + 1 edge SFRs; App. B)
     floor_phot: int = 0                 # noise-floor terms of each arm (App. sys_floor): FLOOR_* bits
     floor_spec: int = 0
     H0: float = PHYS["H0"]
@@ -190,6 +191,7 @@ class Oracle:
             if self.floor_spec:
                 raise ValueError("a spectral noise floor with the marginalised calibration polynomial is not defined here")
         m.floor_phot, m.floor_spec = int(self.floor_phot), int(self.floor_spec)
+        m.sfh_scheme = int(self.sfh_scheme)
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
@@ -272,7 +274,10 @@ class Oracle:
         return out, valid
 
     def grad(self, theta, nthreads=0):
-        """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])."""
+        """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])
+        (step SFH scheme; grad_fd serves the linear one)."""
+        if self.sfh_scheme != 0:
+            raise NotImplementedError("the analytic gradient follows the step scheme; use grad_fd")
         th = np.ascontiguousarray(theta, dtype=np.float64)
         n, ld = th.shape
         out = np.zeros((n, ld))
@@ -323,14 +328,15 @@ def floor_keys(floor_phot=0, floor_spec=0):
                  for k in range(4) if (bits >> k) & 1)
 
 
-def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0):
-    """Parameter rows in the oracle's layout: sfh[N_T], logzsol[N_T or 1], then
+def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, sfh_scheme=0):
+    """Parameter rows in the oracle's layout: sfh[N_T] (bin masses; N_T + 1 edge
+    SFRs with the linear scheme), logzsol[N_T or 1], then
     afe, logmass, zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index,
     gas_logz, gas_logu, sigma_gal when the model samples it, and the log10 of
     each noise-floor term that is on (photometry, then spectrum)."""
     nz = n_sfh if zmode == 0 else 1
     n = d["sfh"].shape[0]
-    cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh),
+    cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh + (1 if sfh_scheme == 1 else 0)),
             np.asarray(d["logzsol"], dtype=np.float64).reshape(n, nz)]
     for k in ("afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
               "diffuse_dust_index", "gas_logz", "gas_logu") + (("sigma_gal",) if sample_sigma_gal else ()) + \

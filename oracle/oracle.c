@@ -122,8 +122,11 @@ static int n_floor(int bits) {
   return c;
 }
 
+/* columns of the SFH key: N_T bin masses (step scheme) or N_T + 1 edge SFRs (linear scheme) */
+static int sfh_cols(const orc_model *md) { return md->n_sfh + (md->sfh_scheme == 1 ? 1 : 0); }
+
 int orc_n_param(const orc_model *md) {
-  return md->n_sfh + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0) +
+  return sfh_cols(md) + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0) +
          n_floor(md->floor_phot) + n_floor(md->floor_spec);
 }
 
@@ -138,15 +141,15 @@ typedef struct {
 } orc_theta;
 
 static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
-  int nz = md->zmode == 0 ? md->n_sfh : 1;
-  const double *s = th + md->n_sfh + nz;
+  int nz = md->zmode == 0 ? md->n_sfh : 1, ns = sfh_cols(md);
+  const double *s = th + ns + nz;
   o->m = th;
-  o->zeta = th + md->n_sfh;
+  o->zeta = th + ns;
   o->afe = s[0]; o->logmass = s[1]; o->z = s[2]; o->tau_bc = s[3]; o->alpha_bc = s[4];
   o->tau_d = s[5]; o->delta = s[6]; o->gas_logz = s[7]; o->gas_logu = s[8];
   o->sigma_gal = md->sample_sigma_gal ? s[9] : md->sigma_gal_kms;
   /* App. "sys_floor": a term that is off leaves s = 1 and the others 0 */
-  int col = md->n_sfh + nz + 9 + (md->sample_sigma_gal ? 1 : 0);
+  int col = ns + nz + 9 + (md->sample_sigma_gal ? 1 : 0);
   for (int arm = 0; arm < 2; arm++) {
     int bits = arm == 0 ? md->floor_phot : md->floor_spec;
     for (int k = 0; k < 4; k++) {
@@ -203,6 +206,55 @@ static int theta_status(const orc_model *md, const double *th, double *tmax_out,
  * linear-time Voronoi cell of age node a (midpoints to its neighbours, first
  * cell from 0, last cell to infinity); then the metallicity split of each bin
  * and the [a/Fe] split (Sec. 5.4), W[n][m][a] = sum_i A_ia w_m(zeta_i) w_n(afe). */
+/* App. B linear scheme, Eq. "tent_integral": the SFR is linear in lookback
+ * time across the bin [T0, T1], from psi0 at T0 to psi1 at T1, and the mass an
+ * SSP age node receives is the integral of the SFR against that node's tent,
+ * the linear interpolation in log(age) between neighbouring nodes (a_j(t) =
+ * ln(t_{j+1}/t) / ln(t_{j+1}/t_j) on [t_j, t_{j+1}], b_{j+1} = 1 - a_j).  The
+ * bin is cut at the nodes and each piece integrated in closed form with the
+ * antiderivatives of psi(t) and psi(t) ln t; ages below the youngest node go
+ * to it, ages above the oldest to that one.  Negative pieces are clipped to 0,
+ * then the bin's masses are scaled to sum to its trapezoidal mass
+ * (psi0 + psi1)(T1 - T0)/2, itself clipped at 0.  A[NA] receives the bin's
+ * mass per node. */
+static void linear_bin_masses(const orc_grid *g, double T0, double T1, double psi0, double psi1, double *A) {
+  int NA = g->n_age;
+  for (int a = 0; a < NA; a++) A[a] = 0.0;
+  double dT = T1 - T0;
+  if (!(dT > 0.0)) return;
+  double beta = (psi1 - psi0) / dT, alpha = psi0 - beta * T0;   /* psi(t) = alpha + beta t */
+  /* P = antiderivative of psi, Q = antiderivative of psi ln t */
+#define LIN_P(x) (alpha * (x) + 0.5 * beta * (x) * (x))
+#define LIN_Q(x) (alpha * ((x) * log(x) - (x)) + beta * (0.5 * (x) * (x) * log(x) - 0.25 * (x) * (x)))
+  double t_first = pow(10.0, g->log_age_yr[0]), t_last = pow(10.0, g->log_age_yr[NA - 1]);
+  /* below the youngest node and above the oldest: wholly to the end node */
+  if (T0 < t_first) {
+    double hi = T1 < t_first ? T1 : t_first, m = LIN_P(hi) - LIN_P(T0);
+    A[0] += m > 0.0 ? m : 0.0;
+  }
+  if (T1 > t_last) {
+    double lo = T0 > t_last ? T0 : t_last, m = LIN_P(T1) - LIN_P(lo);
+    A[NA - 1] += m > 0.0 ? m : 0.0;
+  }
+  for (int j = 0; j + 1 < NA; j++) {
+    double tj = pow(10.0, g->log_age_yr[j]), tj1 = pow(10.0, g->log_age_yr[j + 1]);
+    double x0 = T0 > tj ? T0 : tj, x1 = T1 < tj1 ? T1 : tj1;
+    if (!(x1 > x0)) continue;
+    double mass = LIN_P(x1) - LIN_P(x0), mlog = LIN_Q(x1) - LIN_Q(x0);
+    double lj = log(tj), lj1 = log(tj1), d = lj1 - lj;
+    double to_j = (lj1 * mass - mlog) / d, to_j1 = (mlog - lj * mass) / d;
+    A[j] += to_j > 0.0 ? to_j : 0.0;
+    A[j + 1] += to_j1 > 0.0 ? to_j1 : 0.0;
+  }
+#undef LIN_P
+#undef LIN_Q
+  double s = 0.0, target = 0.5 * (psi0 + psi1) * dT;
+  if (target < 0.0) target = 0.0;   /* a bin whose rates average below 0 forms nothing */
+  for (int a = 0; a < NA; a++) s += A[a];
+  if (s > 0.0)
+    for (int a = 0; a < NA; a++) A[a] *= target / s;
+}
+
 int orc_weights(const orc_grid *g, const orc_model *md, const double *theta, double *W) {
   double tmax;
   int st = theta_status(md, theta, &tmax, NULL);
@@ -225,25 +277,33 @@ int orc_weights(const orc_grid *g, const orc_model *md, const double *theta, dou
   double wn0, wn1;
   double afe = md->use_afe ? t.afe : 0.0;
   bracket(g->afe, g->n_afe, afe, &n0, &wn0, &n1, &wn1);
+  double *A = (double *)malloc(NA * sizeof(double));
   for (int i = 0; i < NT; i++) {
     double dT = T[i + 1] - T[i];
     double zeta = t.zeta[md->zmode == 0 ? i : 0];
     int m0, m1;
     double wm0, wm1;
     bracket(g->feh, g->n_feh, zeta, &m0, &wm0, &m1, &wm1);
+    /* the mass bin i gives each age node */
+    if (md->sfh_scheme == 1) {
+      linear_bin_masses(g, T[i], T[i + 1], t.m[i], t.m[i + 1], A);
+    } else {
+      for (int a = 0; a < NA; a++) {
+        double lo = T[i] > cm[a] ? T[i] : cm[a];
+        double hi = T[i + 1] < cp[a] ? T[i + 1] : cp[a];
+        double ov = hi - lo;
+        A[a] = ov > 0.0 ? t.m[i] * ov / dT : 0.0;
+      }
+    }
     for (int a = 0; a < NA; a++) {
-      double lo = T[i] > cm[a] ? T[i] : cm[a];
-      double hi = T[i + 1] < cp[a] ? T[i + 1] : cp[a];
-      double ov = hi - lo;
-      if (ov <= 0.0) continue;
-      double A = t.m[i] * ov / dT;
-      W[((size_t)n0 * g->n_feh + m0) * NA + a] += A * wm0 * wn0;
-      W[((size_t)n0 * g->n_feh + m1) * NA + a] += A * wm1 * wn0;
-      W[((size_t)n1 * g->n_feh + m0) * NA + a] += A * wm0 * wn1;
-      W[((size_t)n1 * g->n_feh + m1) * NA + a] += A * wm1 * wn1;
+      if (A[a] == 0.0) continue;
+      W[((size_t)n0 * g->n_feh + m0) * NA + a] += A[a] * wm0 * wn0;
+      W[((size_t)n0 * g->n_feh + m1) * NA + a] += A[a] * wm1 * wn0;
+      W[((size_t)n1 * g->n_feh + m0) * NA + a] += A[a] * wm0 * wn1;
+      W[((size_t)n1 * g->n_feh + m1) * NA + a] += A[a] * wm1 * wn1;
     }
   }
-  free(T); free(cm); free(cp);
+  free(T); free(cm); free(cp); free(A);
   return 0;
 }
 

@@ -9,7 +9,8 @@
  * Each function follows the paper's definitions directly, in the plainest loop
  * order, in double precision:
  *   cosmology            Sec. 2.6 (flat LCDM luminosity distance, age of the Universe)
- *   SFH -> SSP weights   Sec. 2.2, App. B (step scheme, Voronoi cells in linear time),
+ *   SFH -> SSP weights   Sec. 2.2, App. B (step scheme, Voronoi cells in linear time; linear
+ *                        scheme, Eq. "tent_integral"),
  *                        App. B metallicity split, Sec. 5.4 [a/Fe] axis
  *   ionising photons     App. C, Eq. "app_q"
  *   contraction          Eq. "csp_sum_main", Eq. "app_attn" (two age bins)
@@ -62,6 +63,8 @@ typedef struct {
   double sigma_gal_max_kms;    /* sampled sigma_gal must lie in [0, this] */
   int calib_n;                 /* coefficients of the marginalised calibration polynomial (0: none) */
   const double *calib_sigma;   /* [calib_n] prior widths s_m of the coefficients (App. E) */
+  int sfh_scheme;              /* 0 step (per-bin masses m_i, N_T columns), 1 linear (per-edge SFRs psi_i,
+                                  N_T + 1 columns; App. B, Eq. "tent_integral") */
   int floor_phot, floor_spec;  /* systematic noise floor of each arm (App. "sys_floor"): ORC_FLOOR_* bits;
                                   each term on adds a parameter column holding log10 of its value */
 } orc_model;
