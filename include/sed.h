@@ -88,7 +88,8 @@ enum {
 /* Parameter keys (paper names, Fig. "ceridwen_flow"); index into the offsets
  * returned by sed_model_layout. */
 enum {
-  SED_KEY_SFH = 0,            /* N_T formed-mass fractions, bin 0 = most recent */
+  SED_KEY_SFH = 0,            /* N_T formed-mass fractions, bin 0 = most recent (step scheme), or
+                                 N_T + 1 SFRs (Msun/yr) at the bin edges, edge 0 = today (linear scheme) */
   SED_KEY_LOGZSOL = 1,        /* N_T per-bin [Fe/H] (zmode 0) or 1 constant (zmode 1) */
   SED_KEY_AFE = 2,            /* [a/Fe] (used when use_afe) */
   SED_KEY_LOGMASS = 3,        /* log10 total formed mass / Msun */
@@ -190,9 +191,20 @@ typedef struct {
    * spectral floor needs a spectrum and no calibration polynomial
    * (SED_EUNSUPPORTED); a photometric one needs filters. */
   int noise_floor_phot, noise_floor_spec;
+  /* SFH -> SSP age weights (App. B): SED_SFH_STEP (0, the default) spreads
+   * each bin's mass m_i over the age nodes by linear-time Voronoi overlap;
+   * SED_SFH_LINEAR (1) takes the SFR linear in lookback time across each bin
+   * through per-edge rates psi_0..psi_NT and integrates it against the nodes'
+   * log-age tents (Eq. tent_integral), pieces clipped at 0 and each bin scaled
+   * to its trapezoidal mass max(0, (psi_i + psi_{i+1}) dT_i / 2).  The linear
+   * scheme has N_T + 1 SFH columns; sed_loglike_grad supports the step scheme
+   * only (SED_EUNSUPPORTED). */
+  int sfh_scheme;
 } sed_model_desc;
 
 #define SED_MAX_CALIB 13
+#define SED_SFH_STEP 0
+#define SED_SFH_LINEAR 1
 #define SED_FLOOR_ERR_SCALE 1
 #define SED_FLOOR_F_CALIB 2
 #define SED_FLOOR_F_DATA 4

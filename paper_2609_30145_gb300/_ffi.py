@@ -23,6 +23,7 @@ KEYS = ("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow", "dif
         "log_err_scale_phot", "log_f_calib_phot", "log_f_data_phot", "log_jitter_phot",
         "log_err_scale_spec", "log_f_calib_spec", "log_f_data_spec", "log_jitter_spec")
 FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
+SFH_STEP, SFH_LINEAR = 0, 1
 NKEYS = len(KEYS)
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -47,7 +48,7 @@ class ModelDesc(C.Structure):
                 ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", P),
-                ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int)]
+                ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int), ("sfh_scheme", C.c_int)]
 
 
 class StageStats(C.Structure):

@@ -69,6 +69,31 @@ __device__ __forceinline__ float sfh_edge(int i, int NT, double tmax, float lrat
 //  s = 10^logmass Lsun (1+z) / (4 pi D_L^2) in device flux units, with
 //  10^logmass = 2^n 2^f from an exact FP32 split of logmass log2(10) and an
 //  FP32 exp2 of the fraction (FP32-grade).
+// App. B linear scheme (Eq. tent_integral).  Across an SFH bin [T0, T1] the
+// SFR is psi(t) = psi0 + g (t - T0); the piece [x0, x1] of the bin between age
+// nodes t_j < t_{j+1} (dl = ln(t_{j+1}/t_j)) gives node j+1 the share
+// int psi(t) ln(t/t_j) dt / dl of its mass M and node j the rest, each
+// clipped at 0.  With t = x0 (1 + u), r = (x1 - x0)/x0,
+//   int psi ln(t/t_j) dt = ln(x0/t_j) M + x0 [psi(x0) F1(r) + g x0 F2(r)],
+//   F1 = (1 + r) log1p(r) - r,   F2 = (r^2 - 1) log1p(r)/2 - r^2/4 + r/2,
+// all in FP32: F1 and F2 are formed from quantities of the size of r, so the
+// rounding of a share stays relative to M.
+__device__ __forceinline__ float lin_mass(float x0, float x1, float psi0, float g, float T0) {
+  return 0.5f * (fmaf(g, x0 - T0, psi0) + fmaf(g, x1 - T0, psi0)) * (x1 - x0);
+}
+__device__ __forceinline__ void tent_piece(float x0, float x1, float tj, float dl, float psi0, float g, float T0,
+                                           float& lo, float& hi) {
+  const float p0 = fmaf(g, x0 - T0, psi0);
+  const float M = lin_mass(x0, x1, psi0, g, T0);
+  const float r = (x1 - x0) / x0, L = log1pf(r);
+  const float F1 = fmaf(1.f + r, L, -r);
+  const float F2 = fmaf(0.5f * (r * r - 1.f), L, r * (0.5f - 0.25f * r));
+  const float lx = x0 > tj ? logf(x0 / tj) : 0.f;
+  const float up = fmaf(lx, M, x0 * fmaf(p0, F1, g * x0 * F2)) / dl;
+  hi = fmaxf(up, 0.f);
+  lo = fmaxf(M - up, 0.f);
+}
+
 __device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm, int lane) {
   // All 32 lanes of a warp call it with the same z and lm; lane 0's result is
   // complete.  Lanes 0-3 each evaluate one of the four interpolants in the same
@@ -285,8 +310,33 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   for (int i = tid; i <= NT; i += blockDim.x) T[i] = sfh_edge(i, NT, tmax, lrat);
   for (int j = tid; j < NA * NZ; j += blockDim.x) Ws[j] = 0.f;
   __syncthreads();
+  const int NA_ = g.n_age;
+  const float t_first = g.age_t[0], t_last = g.age_t[NA_ - 1];
   for (int i = tid; i < NT; i += blockDim.x) {
-    rate[i] = m[i] / (T[i + 1] - T[i]);
+    if (md.sfh_linear) {
+      // linear scheme, pass 1: the bin's clipped tent shares, summed, give the
+      // factor that scales them to its trapezoidal mass
+      const float T0 = T[i], T1 = T[i + 1], psi0 = m[i], gr = (m[i + 1] - psi0) / (T1 - T0);
+      float sum = 0.f;
+      if (T0 < t_first) sum += fmaxf(lin_mass(T0, fminf(T1, t_first), psi0, gr, T0), 0.f);
+      if (T1 > t_last) sum += fmaxf(lin_mass(fmaxf(T0, t_last), T1, psi0, gr, T0), 0.f);
+      int j = 0, jh = NA_ - 1;   // first node interval [t_j, t_{j+1}] reaching above T0
+      while (j < jh) {
+        const int mid = (j + jh) >> 1;
+        if (g.age_t[mid + 1] > T0) jh = mid; else j = mid + 1;
+      }
+      for (; j + 1 < NA_ && g.age_t[j] < T1; ++j) {
+        const float x0 = fmaxf(T0, g.age_t[j]), x1 = fminf(T1, g.age_t[j + 1]);
+        if (!(x1 > x0)) continue;
+        float lo, hi;
+        tent_piece(x0, x1, g.age_t[j], g.age_dl[j], psi0, gr, T0, lo, hi);
+        sum += lo + hi;
+      }
+      const float target = fmaxf(0.5f * (psi0 + m[i + 1]) * (T1 - T0), 0.f);
+      rate[i] = sum > 0.f ? target / sum : 0.f;
+    } else {
+      rate[i] = m[i] / (T[i + 1] - T[i]);
+    }
     int j0, j1;
     float w0, w1;
     bracket_f(md.feh, md.n_feh, zeta[md.zmode == 0 ? i : 0], j0, w0, j1, w1);
@@ -296,6 +346,48 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __syncthreads();
 
   // ---- weights on (age, feh): thread per age node
+  if (md.sfh_linear) {
+    // linear scheme, pass 2: node a gathers the tent shares of the bins over
+    // its support [t_{a-1}, t_{a+1}] (and the ages beyond the axis at the end
+    // nodes), scaled by each bin's factor and split by the bin's [Fe/H]
+    for (int ag = tid; ag < NA; ag += blockDim.x) {
+      const float lo_s = ag == 0 ? 0.f : g.age_t[ag - 1];
+      const float hi_s = ag == NA - 1 ? INFINITY : g.age_t[ag + 1];
+      int i0 = 0, i1 = NT;
+      while (i0 < i1) {
+        const int mid = (i0 + i1) >> 1;
+        if (T[mid + 1] > lo_s) i1 = mid; else i0 = mid + 1;
+      }
+      float* row = Ws + ag * NZ;
+      for (int i = i0; i < NT && T[i] < hi_s; ++i) {
+        const float sc = rate[i];
+        if (sc == 0.f) continue;
+        const float T0 = T[i], T1 = T[i + 1], psi0 = m[i], gr = (m[i + 1] - psi0) / (T1 - T0);
+        float A = 0.f, lo, hi;
+        if (ag == 0 && T0 < t_first) A += fmaxf(lin_mass(T0, fminf(T1, t_first), psi0, gr, T0), 0.f);
+        if (ag == NA - 1 && T1 > t_last) A += fmaxf(lin_mass(fmaxf(T0, t_last), T1, psi0, gr, T0), 0.f);
+        if (ag > 0) {
+          const float x0 = fmaxf(T0, g.age_t[ag - 1]), x1 = fminf(T1, g.age_t[ag]);
+          if (x1 > x0) {
+            tent_piece(x0, x1, g.age_t[ag - 1], g.age_dl[ag - 1], psi0, gr, T0, lo, hi);
+            A += hi;
+          }
+        }
+        if (ag + 1 < NA) {
+          const float x0 = fmaxf(T0, g.age_t[ag]), x1 = fminf(T1, g.age_t[ag + 1]);
+          if (x1 > x0) {
+            tent_piece(x0, x1, g.age_t[ag], g.age_dl[ag], psi0, gr, T0, lo, hi);
+            A += lo;
+          }
+        }
+        A *= sc;
+        const int j = zb[i];
+        const float t = zt[i];
+        row[j] += A * (1.f - t);
+        if (NZ > 1) row[j + 1] += A * t;
+      }
+    }
+  } else
   for (int ag = tid; ag < NA; ag += blockDim.x) {
     const float lo = g.cell_lo[ag], hi = g.cell_hi[ag];
     // first bin whose upper edge is above the cell's lower edge

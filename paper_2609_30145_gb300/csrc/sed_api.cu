@@ -317,7 +317,11 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
     }
   }
   // linear-time Voronoi cells (App. B step scheme)
-  std::vector<float> clo(d->n_age), chi(d->n_age);
+  std::vector<float> clo(d->n_age), chi(d->n_age), at(d->n_age), adl(d->n_age, 0.f);
+  for (int a = 0; a < d->n_age; a++) {
+    at[a] = (float)std::pow(10.0, g->log_age[a]);
+    if (a + 1 < d->n_age) adl[a] = (float)((g->log_age[a + 1] - g->log_age[a]) * std::log(10.0));
+  }
   for (int a = 0; a < d->n_age; a++) {
     const double ta = std::pow(10.0, g->log_age[a]);
     clo[a] = a == 0 ? 0.f : (float)(0.5 * (std::pow(10.0, g->log_age[a - 1]) + ta));
@@ -332,7 +336,7 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
 #define UPF(field, vec)                                                   \
   if (!st) { st = upload(ctx, &p, vec.data(), vec.size(), &g->allocs, &g->bytes); dv.field = p; }
   UPF(lam_f, lam_f) UPF(inv_lam2, inv_lam2) UPF(inv_dlam, idl) UPF(lnp, lnp) UPF(kprime, kp) UPF(drude, dr)
-  UPF(lnl_hi, lh) UPF(lnl_lo, lo) UPF(cell_lo, clo) UPF(cell_hi, chi)
+  UPF(lnl_hi, lh) UPF(lnl_lo, lo) UPF(cell_lo, clo) UPF(cell_hi, chi) UPF(age_t, at) UPF(age_dl, adl)
 #undef UPF
   if (!st) { st = upload(ctx, &pi, lut.data(), lut.size(), &g->allocs, &g->bytes); dv.lut = pi; }
   if (!st) {
@@ -706,6 +710,8 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   }
   if (d->sample_sigma_gal && !(d->sigma_gal_max_kms > 0 && d->sigma_gal_max_kms < 1e5))
     return fail(ctx, SED_EINVAL, "sigma_gal_max_kms must be in (0, 1e5) when sigma_gal is sampled");
+  if (d->sfh_scheme != SED_SFH_STEP && d->sfh_scheme != SED_SFH_LINEAR)
+    return fail(ctx, SED_EINVAL, "sfh_scheme must be SED_SFH_STEP or SED_SFH_LINEAR");
   if (d->noise_floor_phot < 0 || d->noise_floor_phot > 15 || d->noise_floor_spec < 0 || d->noise_floor_spec > 15)
     return fail(ctx, SED_EINVAL, "noise_floor_phot / noise_floor_spec must be SED_FLOOR_* bits (0..15)");
   if (d->noise_floor_phot && d->n_filt <= 0) return fail(ctx, SED_EINVAL, "a photometric noise floor needs filters");
@@ -724,7 +730,8 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   dv.dust_law = d->dust_law;
   const int nz = d->zmode == 0 ? d->n_sfh : 1;
   int o = 0;
-  dv.offs[SED_KEY_SFH] = o; o += d->n_sfh;
+  dv.sfh_linear = d->sfh_scheme == SED_SFH_LINEAR ? 1 : 0;
+  dv.offs[SED_KEY_SFH] = o; o += d->n_sfh + dv.sfh_linear;   // bin masses, or edge SFRs (one more)
   dv.offs[SED_KEY_LOGZSOL] = o; o += nz;
   for (int k = SED_KEY_AFE; k <= SED_KEY_GAS_LOGU; k++) dv.offs[k] = o++;
   dv.offs[SED_KEY_SIGMA_GAL] = o;
@@ -1246,6 +1253,8 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   if (st) return st;
   if (precision == SED_PREC_BF16 || precision == SED_PREC_FP8)
     return fail(ctx, SED_EUNSUPPORTED, "the gradient is available for SED_PREC_FP32 and SED_PREC_FP32_SIMT");
+  if (M->dv.sfh_linear)
+    return fail(ctx, SED_EUNSUPPORTED, "the gradient is available for the step SFH scheme");
   if (n > 0 && (!lnl_out || !grad_out)) return fail(ctx, SED_EINVAL, "lnl_out or grad_out is NULL");
   if (n == 0) return SED_OK;
   DevGuard dg(ctx->device);

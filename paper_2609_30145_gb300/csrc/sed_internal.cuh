@@ -96,6 +96,8 @@ struct GridDev {
   float dln_max;           // largest ln(lambda[k+1] / lambda[k])
   const float* cell_lo;    // linear-time Voronoi cell of each age node (yr)
   const float* cell_hi;
+  const float* age_t;      // age of each node (yr), for the linear SFH scheme's tents
+  const float* age_dl;     // ln(t_{a+1} / t_a) (last entry unused)
   const float* neb_tab;    // [nu][nz][n_lam] log10 template + device-unit offset
   int neb_nu, neb_nz;
 };
@@ -145,6 +147,7 @@ struct ModelDev {
   double calib_logdet_lam;
   const float* pix_cx;
   int floor_bits[2];       // noise-floor terms on (SED_FLOOR_* bits) of photometry [0] and spectrum [1]
+  int sfh_linear;          // 1: SFH key = N_T + 1 per-edge SFRs, linear scheme (App. B, Eq. tent_integral)
   int sample_sgal;         // 1: each row carries sigma_gal (km/s), joined in quadrature per pixel
   float sgal_max_kms;      // sampled sigma_gal range [0, sgal_max_kms]
   // spectral data, normalised per pixel so that the per-pixel terms stay in FP32

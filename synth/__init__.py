@@ -230,6 +230,12 @@ def make_theta(n_rows, n_sfh, zmode, ranges, seed=4):
     return out
 
 
+def edge_sfr(n_rows, n_sfh, seed=4):
+    """Per-edge SFRs (Msun/yr) for the linear SFH scheme: positive, varied
+    (Gamma(1.5)), ~1e-10 so that a bin's mass is of order its width / 1e10 yr."""
+    return 1e-10 * _rng(seed).gamma(1.5, 1.0, (n_rows, n_sfh + 1))
+
+
 FLOOR_NAMES = ("log_err_scale", "log_f_calib", "log_f_data", "log_jitter")
 
 
@@ -279,6 +285,7 @@ class Workload:
     sigma_gal_kms: float = 0.0
     sample_sigma_gal: int = 0          # 1: sigma_gal (km/s) is a parameter, drawn from ranges["sigma_gal"]
     sigma_gal_max_kms: float = 1000.0
+    sfh_scheme: int = 0                # 0 step (N_T bin masses), 1 linear (N_T + 1 edge SFRs)
     floor_phot: int = 0                # noise-floor terms on (bits: 1 err scale, 2 f_calib, 4 f_data, 8 jitter)
     floor_spec: int = 0
     extra: dict = field(default_factory=dict)
@@ -334,6 +341,10 @@ WORKLOADS["specphot_afe_calib13_107x12x5x6000_b2048"] = Workload(**{
 # (App. sys_floor): error scale, model- and data-anchored fractions, jitter
 WORKLOADS["specphot_afe_floor_107x12x5x6000_b2048"] = Workload(**{
     **_s.__dict__, "name": "specphot_afe_floor_107x12x5x6000_b2048", "floor_phot": 15, "floor_spec": 15})
+# the paper-scale photometric fit with the linear SFH scheme (App. B, Eq.
+# tent_integral): per-edge SFRs, N_T + 1 columns
+WORKLOADS["phot_linsfh_107x12x6000_b1024"] = Workload(**{
+    **WORKLOADS["phot_107x12x6000_b1024"].__dict__, "name": "phot_linsfh_107x12x6000_b1024", "sfh_scheme": 1})
 # mixed-precision contraction: the paper-scale photometric batch at 4096 rows
 _w = WORKLOADS["phot_107x12x6000_b1024"]
 WORKLOADS["phot_107x12x6000_b4096"] = Workload(**{**_w.__dict__, "name": "phot_107x12x6000_b4096",

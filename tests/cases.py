@@ -19,7 +19,7 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
     kw = dict(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
               use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
               sample_sigma_gal=w.sample_sigma_gal, sigma_gal_max_kms=w.sigma_gal_max_kms,
-              floor_phot=w.floor_phot, floor_spec=w.floor_spec)
+              floor_phot=w.floor_phot, floor_spec=w.floor_spec, sfh_scheme=w.sfh_scheme)
     nb = len(filt[0])
     kw.update(phot_d=np.ones(nb), phot_sigma=np.ones(nb), phot_mask=np.ones(nb, np.uint8))
     if w.spectrum is not None:
@@ -32,8 +32,10 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
                   calib_sigma=None if calib_sigma is None else np.asarray(calib_sigma, dtype=np.float64))
     orc = oracle.Oracle(**kw)
     if with_data:
-        th_true = oracle.pack_theta(synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99), w.n_sfh, w.zmode,
-                                    w.sample_sigma_gal)
+        d_true = synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99)
+        if w.sfh_scheme == 1:
+            d_true["sfh"] = synth.edge_sfr(1, w.n_sfh, seed=99)
+        th_true = oracle.pack_theta(d_true, w.n_sfh, w.zmode, w.sample_sigma_gal, sfh_scheme=w.sfh_scheme)
         if w.floor_phot or w.floor_spec:   # the truth row only makes the data: floors off for it
             orc.floor_phot, orc.floor_spec = 0, 0
             orc._rebuild_model()
@@ -57,6 +59,8 @@ def theta_dict(w: synth.Workload, n, seed=4, orc=None):
     """Parameter draws; with a noise floor, its columns too (the jitter's range
     follows the errors of the oracle `orc` holds)."""
     d = synth.make_theta(n, w.n_sfh, w.zmode, w.ranges, seed=seed)
+    if w.sfh_scheme == 1:
+        d["sfh"] = synth.edge_sfr(n, w.n_sfh, seed=seed)
     if w.floor_phot or w.floor_spec:
         d.update(synth.floor_theta(n, w.floor_phot, w.floor_spec,
                                    None if orc is None else orc.phot_sigma,
@@ -66,7 +70,7 @@ def theta_dict(w: synth.Workload, n, seed=4, orc=None):
 
 def theta_rows(w: synth.Workload, n, seed=4, orc=None):
     return oracle.pack_theta(theta_dict(w, n, seed, orc), w.n_sfh, w.zmode, w.sample_sigma_gal,
-                             w.floor_phot, w.floor_spec)
+                             w.floor_phot, w.floor_spec, w.sfh_scheme)
 
 
 def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
@@ -79,7 +83,7 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
     gid = cache[key][0]
     kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law,
               sample_sigma_gal=orc.sample_sigma_gal, sigma_gal_max_kms=orc.sigma_gal_max_kms,
-              noise_floor_phot=orc.floor_phot, noise_floor_spec=orc.floor_spec,
+              noise_floor_phot=orc.floor_phot, noise_floor_spec=orc.floor_spec, sfh_scheme=orc.sfh_scheme,
               bc_edge_log_age_yr=orc.bc_edge_log_age_yr, H0=orc.H0, Om0=orc.Om0,
               filters=orc.filters, phot_d=orc.phot_d, phot_sigma=orc.phot_sigma,
               phot_mask=orc.phot_mask)

@@ -375,3 +375,26 @@ def test_noise_floor_parity(ctx, prec):
     ref = orc.eval(th64)
     got = run_gpu(model, th32, prec)
     check(ref, got, prec, orc=orc)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_linear_sfh_parity(ctx, prec):
+    """The paper-scale photometric fit with the linear SFH scheme (App. B, Eq.
+    tent_integral: per-edge SFRs, N_T + 1 columns, tent integrals per age
+    node): 300 rows on the GPU, 30 sampled rows' photometry and lnL against the
+    oracle; the gradient is refused for this scheme."""
+    w = synth.WORKLOADS["phot_linsfh_107x12x6000_b1024"]
+    if "linsfh" not in _CACHE:
+        orc = cases.oracle_for(w)
+        _CACHE["linsfh"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE["linsfh"]
+    assert model.n_param == orc.n_param == 2 * w.n_sfh + 1 + 9
+    th32, th64 = cases.theta_pair(w, 300, seed=63)
+    got = run_gpu(model, th32, prec)
+    rows = np.unique(np.concatenate([[0, 299], np.random.default_rng(10).choice(300, 28, replace=False)]))
+    ref = orc.eval(th64[rows])
+    check(ref, got, prec, rows, orc=orc)
+    if prec == "fp32":
+        from paper_2609_30145_gb300.api import SedError
+        with pytest.raises(SedError):
+            model.loglike_grad(torch.from_numpy(th32).cuda(), "fp32")
