@@ -38,6 +38,7 @@ GRAD_WORKLOAD = "specphot_afe_107x12x5x6000_b2048"
 SGAL_WORKLOAD = "specphot_afe_sgal_107x12x5x6000_b2048"   # the same with a sampled sigma_gal
 CALIB_WORKLOAD = "specphot_afe_calib13_107x12x5x6000_b2048"  # the same with a 13-term calibration polynomial
 FLOOR_WORKLOAD = "specphot_afe_floor_107x12x5x6000_b2048"    # the same with every noise-floor term on
+LINSFH_WORKLOAD = "phot_linsfh_107x12x6000_b1024"   # the headline fit with the linear SFH scheme
 PRECS = ("fp32", "fp32_simt", "bf16", "fp8")
 PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
              "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
@@ -142,7 +143,7 @@ def build_workload(wname, ctx, seed_rows, device):
     kw = dict(use_afe=w.use_afe, use_nebular=w.use_nebular, dust_law=w.dust_law, filters=filt,
               phot_d=np.ones(nb), phot_sigma=np.ones(nb), sample_sigma_gal=w.sample_sigma_gal,
               sigma_gal_max_kms=w.sigma_gal_max_kms, noise_floor_phot=w.floor_phot,
-              noise_floor_spec=w.floor_spec)
+              noise_floor_spec=w.floor_spec, sfh_scheme=w.sfh_scheme)
     if w.spectrum is not None and w.extra.get("calib_sigma"):
         kw.update(calib_sigma=np.asarray(w.extra["calib_sigma"]))
     spec = None
@@ -156,6 +157,8 @@ def build_workload(wname, ctx, seed_rows, device):
     model = ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)
     # mock data: the model at a true parameter row (z = 2), 5% Gaussian noise
     d_true = synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99)
+    if w.sfh_scheme == 1:   # linear SFH scheme: per-edge SFRs
+        d_true["sfh"] = synth.edge_sfr(1, w.n_sfh, seed=99)
     d_true["zred"][:] = 2.0
     # noise-floor columns, if any: the model fluxes do not depend on them
     d_true.update(synth.floor_theta(1, w.floor_phot, w.floor_spec, np.ones(nb), np.ones(1)))
@@ -172,6 +175,8 @@ def build_workload(wname, ctx, seed_rows, device):
         model.set_data(phot_d=pd, phot_sigma=np.abs(ph) / 20.0, spec_d=s0 * (1 + nz[nb:] / 20.0),
                        spec_sigma=np.abs(s0) / 20.0)
     d = synth.make_theta(w.batch, w.n_sfh, w.zmode, w.ranges, seed=seed_rows)
+    if w.sfh_scheme == 1:
+        d["sfh"] = synth.edge_sfr(w.batch, w.n_sfh, seed=seed_rows)
     d.update(synth.floor_theta(w.batch, w.floor_phot, w.floor_spec, np.abs(ph) / 20.0,
                                None if spec is None else np.abs(s0) / 20.0, seed=seed_rows + 1000))
     theta = model.pack(d)
@@ -355,6 +360,15 @@ def run_ours(args):
     dms = time_direct(step_fn(prec), main_stream, max(10, args.steps // 2), flush)
     variants[prec + "_direct_calls"] = {"evals_per_s": round(B * len(dms) / (sum(dms) * 1e-3), 1),
                                         "ms_per_step": round(sum(dms) / len(dms), 4)}
+    # the same fit with the linear SFH scheme (per-edge SFRs, tent integrals)
+    if args.workload == "phot_107x12x6000_b1024":
+        wl, _, _, model_l, theta_l, _ = build_workload(LINSFH_WORKLOAD, ctx, 4 + rank, device)
+        tl = torch.from_numpy(theta_l).to(device)
+        gl = capture_step(lambda s: model_l.loglike(tl, prec, stream=s, out=lnl, status=stt), main_stream)
+        lms = time_replays(gl, main_stream, max(10, args.steps // 2), flush)
+        variants[prec + "_linear_sfh"] = {"evals_per_s": round(B * len(lms) / (sum(lms) * 1e-3), 1),
+                                          "ms_per_step": round(sum(lms) / len(lms), 4),
+                                          "workload": wl.name}
 
     # end to end through the host-buffer entry point (pinned host theta, lnL back to host)
     th_host = torch.from_numpy(theta).pin_memory()
