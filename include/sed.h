@@ -197,8 +197,8 @@ typedef struct {
    * through per-edge rates psi_0..psi_NT and integrates it against the nodes'
    * log-age tents (Eq. tent_integral), pieces clipped at 0 and each bin scaled
    * to its trapezoidal mass max(0, (psi_i + psi_{i+1}) dT_i / 2).  The linear
-   * scheme has N_T + 1 SFH columns; sed_loglike_grad supports the step scheme
-   * only (SED_EUNSUPPORTED). */
+   * scheme has N_T + 1 SFH columns, and sed_loglike_grad returns d lnL / d psi
+   * for each edge. */
   int sfh_scheme;
 } sed_model_desc;
 

@@ -81,17 +81,177 @@ __device__ __forceinline__ float sfh_edge(int i, int NT, double tmax, float lrat
 __device__ __forceinline__ float lin_mass(float x0, float x1, float psi0, float g, float T0) {
   return 0.5f * (fmaf(g, x0 - T0, psi0) + fmaf(g, x1 - T0, psi0)) * (x1 - x0);
 }
-__device__ __forceinline__ void tent_piece(float x0, float x1, float tj, float dl, float psi0, float g, float T0,
-                                           float& lo, float& hi) {
+// unclipped shares (linear in psi0 and g)
+__device__ __forceinline__ void tent_piece_raw(float x0, float x1, float tj, float dl, float psi0, float g, float T0,
+                                               float& lo, float& hi) {
   const float p0 = fmaf(g, x0 - T0, psi0);
   const float M = lin_mass(x0, x1, psi0, g, T0);
   const float r = (x1 - x0) / x0, L = log1pf(r);
   const float F1 = fmaf(1.f + r, L, -r);
   const float F2 = fmaf(0.5f * (r * r - 1.f), L, r * (0.5f - 0.25f * r));
   const float lx = x0 > tj ? logf(x0 / tj) : 0.f;
-  const float up = fmaf(lx, M, x0 * fmaf(p0, F1, g * x0 * F2)) / dl;
-  hi = fmaxf(up, 0.f);
-  lo = fmaxf(M - up, 0.f);
+  hi = fmaf(lx, M, x0 * fmaf(p0, F1, g * x0 * F2)) / dl;
+  lo = M - hi;
+}
+__device__ __forceinline__ void tent_piece(float x0, float x1, float tj, float dl, float psi0, float g, float T0,
+                                           float& lo, float& hi) {
+  tent_piece_raw(x0, x1, tj, dl, psi0, g, T0, lo, hi);
+  lo = fmaxf(lo, 0.f);
+  hi = fmaxf(hi, 0.f);
+}
+
+// Reverse pass of the linear scheme for bin [T0, T1] with edge rates psi0,
+// psi1: the bin's masses per node are W_a = sc S_a, S_a the clipped shares and
+// sc = target / sum_a S_a.  Given G_a = dlnL/dW_a (from the node's gradient
+// row split by the bin's [Fe/H], gsel), returns dlnL/d{psi0, psi1, T0, T1} and
+// dlnL/dzeta of the bin.  A share depends on the rates linearly (unit-rate
+// shares), on an edge through the integral's limit (-+psi tau at the edge) and
+// through psi(t) = psi0 + (psi1 - psi0)(t - T0)/(T1 - T0) (the shares of the
+// linear functions dpsi/dT0, dpsi/dT1); a clipped share carries no derivative.
+struct LinGrad {
+  float p0, p1, t0, t1, zeta;
+};
+template <typename GFn>
+__device__ LinGrad lin_bin_grad(const GridDev& g, float T0, float T1, float psi0, float psi1, GFn gsel) {
+  const int NA = g.n_age;
+  const float D = T1 - T0, gr = (psi1 - psi0) / D;
+  const float t_first = g.age_t[0], t_last = g.age_t[NA - 1];
+  // accumulators: sum S, its derivatives, and the same weighted by G
+  float S = 0.f, SP0 = 0.f, SP1 = 0.f, ST0 = 0.f, ST1 = 0.f;
+  float GS = 0.f, GP0 = 0.f, GP1 = 0.f, GT0 = 0.f, GT1 = 0.f, GZ = 0.f;
+  const float hT0_0 = -gr, hT0_g = gr / D;      // dpsi/dT0 = (psi1-psi0)(t - T1)/D^2: value at T0, slope
+  const float hT1_g = -gr / D;                  // dpsi/dT1 = -(psi1-psi0)(t - T0)/D^2: 0 at T0
+  auto add = [&](int a, float s, float dp0, float dp1, float dt0, float dt1) {
+    if (!(s > 0.f)) return;   // clipped: no mass, no derivative
+    float G, Gz;
+    gsel(a, G, Gz);
+    S += s; SP0 += dp0; SP1 += dp1; ST0 += dt0; ST1 += dt1;
+    GS += G * s; GP0 += G * dp0; GP1 += G * dp1; GT0 += G * dt0; GT1 += G * dt1; GZ += Gz * s;
+  };
+  // ages beyond the axis: the piece's mass goes to the end node (tau = 1)
+  if (T0 < t_first) {
+    const float x1 = fminf(T1, t_first);
+    const float m = lin_mass(T0, x1, psi0, gr, T0);
+    const float dp0 = lin_mass(T0, x1, 1.f, -1.f / D, T0), dp1 = lin_mass(T0, x1, 0.f, 1.f / D, T0);
+    const float dt0 = -psi0 + lin_mass(T0, x1, hT0_0, hT0_g, T0);
+    const float dt1 = (T1 < t_first ? psi1 : 0.f) + lin_mass(T0, x1, 0.f, hT1_g, T0);
+    add(0, m, dp0, dp1, dt0, dt1);
+  }
+  if (T1 > t_last) {
+    const float x0 = fmaxf(T0, t_last);
+    const float m = lin_mass(x0, T1, psi0, gr, T0);
+    const float dp0 = lin_mass(x0, T1, 1.f, -1.f / D, T0), dp1 = lin_mass(x0, T1, 0.f, 1.f / D, T0);
+    const float dt0 = (T0 > t_last ? -psi0 : 0.f) + lin_mass(x0, T1, hT0_0, hT0_g, T0);
+    const float dt1 = psi1 + lin_mass(x0, T1, 0.f, hT1_g, T0);
+    add(NA - 1, m, dp0, dp1, dt0, dt1);
+  }
+  int j = 0, jh = NA - 1;
+  while (j < jh) {
+    const int mid = (j + jh) >> 1;
+    if (g.age_t[mid + 1] > T0) jh = mid; else j = mid + 1;
+  }
+  for (; j + 1 < NA && g.age_t[j] < T1; ++j) {
+    const float tj = g.age_t[j], tj1 = g.age_t[j + 1], dl = g.age_dl[j];
+    const float x0 = fmaxf(T0, tj), x1 = fminf(T1, tj1);
+    if (!(x1 > x0)) continue;
+    float lo, hi, lp0, hp0, lp1, hp1, lt0, ht0, lt1, ht1;
+    tent_piece_raw(x0, x1, tj, dl, psi0, gr, T0, lo, hi);
+    tent_piece_raw(x0, x1, tj, dl, 1.f, -1.f / D, T0, lp0, hp0);
+    tent_piece_raw(x0, x1, tj, dl, 0.f, 1.f / D, T0, lp1, hp1);
+    tent_piece_raw(x0, x1, tj, dl, hT0_0, hT0_g, T0, lt0, ht0);
+    tent_piece_raw(x0, x1, tj, dl, 0.f, hT1_g, T0, lt1, ht1);
+    // moving limits: the piece starts at T0 / ends at T1 when the edge lies inside the interval
+    if (T0 > tj) {
+      const float tau = logf(T0 / tj) / dl;
+      ht0 -= psi0 * tau;
+      lt0 -= psi0 * (1.f - tau);
+    }
+    if (T1 < tj1) {
+      const float tau = logf(T1 / tj) / dl;
+      ht1 += psi1 * tau;
+      lt1 += psi1 * (1.f - tau);
+    }
+    add(j, lo, lp0, lp1, lt0, lt1);
+    add(j + 1, hi, hp0, hp1, ht0, ht1);
+  }
+  LinGrad out{0.f, 0.f, 0.f, 0.f, 0.f};
+  if (!(S > 0.f)) return out;
+  const float tgt = 0.5f * (psi0 + psi1) * D;
+  const bool on = tgt > 0.f;
+  const float target = on ? tgt : 0.f, sc = target / S;
+  // dsc/dx = (dtarget/dx - sc dS/dx) / S
+  const float tP = on ? 0.5f * D : 0.f, tT0 = on ? -0.5f * (psi0 + psi1) : 0.f, tT1 = -tT0;
+  out.p0 = sc * GP0 + GS * (tP - sc * SP0) / S;
+  out.p1 = sc * GP1 + GS * (tP - sc * SP1) / S;
+  out.t0 = sc * GT0 + GS * (tT0 - sc * ST0) / S;
+  out.t1 = sc * GT1 + GS * (tT1 - sc * ST1) / S;
+  out.zeta = sc * GZ;
+  return out;
+}
+
+// Linear scheme, pass 1: the factor that scales bin [T0, T1]'s clipped tent
+// shares to its trapezoidal mass max(0, (psi0 + psi1)(T1 - T0)/2).
+__device__ float lin_bin_scale(const GridDev& g, float T0, float T1, float psi0, float psi1) {
+  const int NA = g.n_age;
+  const float t_first = g.age_t[0], t_last = g.age_t[NA - 1], gr = (psi1 - psi0) / (T1 - T0);
+  float sum = 0.f;
+  if (T0 < t_first) sum += fmaxf(lin_mass(T0, fminf(T1, t_first), psi0, gr, T0), 0.f);
+  if (T1 > t_last) sum += fmaxf(lin_mass(fmaxf(T0, t_last), T1, psi0, gr, T0), 0.f);
+  int j = 0, jh = NA - 1;   // first node interval [t_j, t_{j+1}] reaching above T0
+  while (j < jh) {
+    const int mid = (j + jh) >> 1;
+    if (g.age_t[mid + 1] > T0) jh = mid; else j = mid + 1;
+  }
+  for (; j + 1 < NA && g.age_t[j] < T1; ++j) {
+    const float x0 = fmaxf(T0, g.age_t[j]), x1 = fminf(T1, g.age_t[j + 1]);
+    if (!(x1 > x0)) continue;
+    float lo, hi;
+    tent_piece(x0, x1, g.age_t[j], g.age_dl[j], psi0, gr, T0, lo, hi);
+    sum += lo + hi;
+  }
+  const float target = fmaxf(0.5f * (psi0 + psi1) * (T1 - T0), 0.f);
+  return sum > 0.f ? target / sum : 0.f;
+}
+
+// Linear scheme, pass 2: node ag gathers the tent shares of the bins over its
+// support [t_{a-1}, t_{a+1}] (and the ages beyond the axis at the end nodes),
+// scaled by each bin's factor sc[i] and split by the bin's [Fe/H] (zb, zt),
+// into row[NZ].
+__device__ void lin_node_fill(const GridDev& g, int ag, int NT, const float* T, const float* m, const float* sc,
+                              const int* zb, const float* zt, float* row, int NZ) {
+  const int NA = g.n_age;
+  const float t_first = g.age_t[0], t_last = g.age_t[NA - 1];
+  const float lo_s = ag == 0 ? 0.f : g.age_t[ag - 1];
+  const float hi_s = ag == NA - 1 ? INFINITY : g.age_t[ag + 1];
+  int i0 = 0, i1 = NT;
+  while (i0 < i1) {
+    const int mid = (i0 + i1) >> 1;
+    if (T[mid + 1] > lo_s) i1 = mid; else i0 = mid + 1;
+  }
+  for (int i = i0; i < NT && T[i] < hi_s; ++i) {
+    if (sc[i] == 0.f) continue;
+    const float T0 = T[i], T1 = T[i + 1], psi0 = m[i], gr = (m[i + 1] - psi0) / (T1 - T0);
+    float A = 0.f, lo, hi;
+    if (ag == 0 && T0 < t_first) A += fmaxf(lin_mass(T0, fminf(T1, t_first), psi0, gr, T0), 0.f);
+    if (ag == NA - 1 && T1 > t_last) A += fmaxf(lin_mass(fmaxf(T0, t_last), T1, psi0, gr, T0), 0.f);
+    if (ag > 0) {
+      const float x0 = fmaxf(T0, g.age_t[ag - 1]), x1 = fminf(T1, g.age_t[ag]);
+      if (x1 > x0) {
+        tent_piece(x0, x1, g.age_t[ag - 1], g.age_dl[ag - 1], psi0, gr, T0, lo, hi);
+        A += hi;
+      }
+    }
+    if (ag + 1 < NA) {
+      const float x0 = fmaxf(T0, g.age_t[ag]), x1 = fminf(T1, g.age_t[ag + 1]);
+      if (x1 > x0) {
+        tent_piece(x0, x1, g.age_t[ag], g.age_dl[ag], psi0, gr, T0, lo, hi);
+        A += lo;
+      }
+    }
+    A *= sc[i];
+    row[zb[i]] += A * (1.f - zt[i]);
+    if (NZ > 1) row[zb[i] + 1] += A * zt[i];
+  }
 }
 
 __device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm, int lane) {
@@ -310,30 +470,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   for (int i = tid; i <= NT; i += blockDim.x) T[i] = sfh_edge(i, NT, tmax, lrat);
   for (int j = tid; j < NA * NZ; j += blockDim.x) Ws[j] = 0.f;
   __syncthreads();
-  const int NA_ = g.n_age;
-  const float t_first = g.age_t[0], t_last = g.age_t[NA_ - 1];
   for (int i = tid; i < NT; i += blockDim.x) {
     if (md.sfh_linear) {
-      // linear scheme, pass 1: the bin's clipped tent shares, summed, give the
-      // factor that scales them to its trapezoidal mass
-      const float T0 = T[i], T1 = T[i + 1], psi0 = m[i], gr = (m[i + 1] - psi0) / (T1 - T0);
-      float sum = 0.f;
-      if (T0 < t_first) sum += fmaxf(lin_mass(T0, fminf(T1, t_first), psi0, gr, T0), 0.f);
-      if (T1 > t_last) sum += fmaxf(lin_mass(fmaxf(T0, t_last), T1, psi0, gr, T0), 0.f);
-      int j = 0, jh = NA_ - 1;   // first node interval [t_j, t_{j+1}] reaching above T0
-      while (j < jh) {
-        const int mid = (j + jh) >> 1;
-        if (g.age_t[mid + 1] > T0) jh = mid; else j = mid + 1;
-      }
-      for (; j + 1 < NA_ && g.age_t[j] < T1; ++j) {
-        const float x0 = fmaxf(T0, g.age_t[j]), x1 = fminf(T1, g.age_t[j + 1]);
-        if (!(x1 > x0)) continue;
-        float lo, hi;
-        tent_piece(x0, x1, g.age_t[j], g.age_dl[j], psi0, gr, T0, lo, hi);
-        sum += lo + hi;
-      }
-      const float target = fmaxf(0.5f * (psi0 + m[i + 1]) * (T1 - T0), 0.f);
-      rate[i] = sum > 0.f ? target / sum : 0.f;
+      // linear scheme, pass 1: the factor scaling the bin's tent shares
+      rate[i] = lin_bin_scale(g, T[i], T[i + 1], m[i], m[i + 1]);
     } else {
       rate[i] = m[i] / (T[i + 1] - T[i]);
     }
@@ -350,43 +490,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     // linear scheme, pass 2: node a gathers the tent shares of the bins over
     // its support [t_{a-1}, t_{a+1}] (and the ages beyond the axis at the end
     // nodes), scaled by each bin's factor and split by the bin's [Fe/H]
-    for (int ag = tid; ag < NA; ag += blockDim.x) {
-      const float lo_s = ag == 0 ? 0.f : g.age_t[ag - 1];
-      const float hi_s = ag == NA - 1 ? INFINITY : g.age_t[ag + 1];
-      int i0 = 0, i1 = NT;
-      while (i0 < i1) {
-        const int mid = (i0 + i1) >> 1;
-        if (T[mid + 1] > lo_s) i1 = mid; else i0 = mid + 1;
-      }
-      float* row = Ws + ag * NZ;
-      for (int i = i0; i < NT && T[i] < hi_s; ++i) {
-        const float sc = rate[i];
-        if (sc == 0.f) continue;
-        const float T0 = T[i], T1 = T[i + 1], psi0 = m[i], gr = (m[i + 1] - psi0) / (T1 - T0);
-        float A = 0.f, lo, hi;
-        if (ag == 0 && T0 < t_first) A += fmaxf(lin_mass(T0, fminf(T1, t_first), psi0, gr, T0), 0.f);
-        if (ag == NA - 1 && T1 > t_last) A += fmaxf(lin_mass(fmaxf(T0, t_last), T1, psi0, gr, T0), 0.f);
-        if (ag > 0) {
-          const float x0 = fmaxf(T0, g.age_t[ag - 1]), x1 = fminf(T1, g.age_t[ag]);
-          if (x1 > x0) {
-            tent_piece(x0, x1, g.age_t[ag - 1], g.age_dl[ag - 1], psi0, gr, T0, lo, hi);
-            A += hi;
-          }
-        }
-        if (ag + 1 < NA) {
-          const float x0 = fmaxf(T0, g.age_t[ag]), x1 = fminf(T1, g.age_t[ag + 1]);
-          if (x1 > x0) {
-            tent_piece(x0, x1, g.age_t[ag], g.age_dl[ag], psi0, gr, T0, lo, hi);
-            A += lo;
-          }
-        }
-        A *= sc;
-        const int j = zb[i];
-        const float t = zt[i];
-        row[j] += A * (1.f - t);
-        if (NZ > 1) row[j + 1] += A * t;
-      }
-    }
+    for (int ag = tid; ag < NA; ag += blockDim.x) lin_node_fill(g, ag, NT, T, m, rate, zb, zt, Ws + ag * NZ, NZ);
   } else
   for (int ag = tid; ag < NA; ag += blockDim.x) {
     const float lo = g.cell_lo[ag], hi = g.cell_hi[ag];
@@ -596,6 +700,7 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   __shared__ int zb[MAX_SFH];
   __shared__ float zt[MAX_SFH], zd0[MAX_SFH], zd1[MAX_SFH];
   __shared__ float gTlo[MAX_SFH], gThi[MAX_SFH], gzeta[MAX_SFH];
+  __shared__ float lin_sc[MAX_SFH], gps0[MAX_SFH], gps1[MAX_SFH];   // linear scheme
   __shared__ double red[PREP_BWD_THREADS / 32];
   __shared__ double s_tmax_part[PREP_BWD_THREADS / 32];
 
@@ -616,9 +721,13 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     zt[i] = w1;
     zd0[i] = d0;
     zd1[i] = d1;
+    if (md.sfh_linear) lin_sc[i] = lin_bin_scale(g, T[i], T[i + 1], m[i], m[i + 1]);
   }
   __syncthreads();
   // forward Ws (needed for the [a/Fe] derivative), thread per age node as in k_prep
+  if (md.sfh_linear) {
+    for (int ag = tid; ag < NA; ag += blockDim.x) lin_node_fill(g, ag, NT, T, m, lin_sc, zb, zt, Ws + ag * NZ, NZ);
+  } else
   for (int ag = tid; ag < NA; ag += blockDim.x) {
     const float lo = g.cell_lo[ag], hi = g.cell_hi[ag];
     int i0 = 0, i1 = NT;
@@ -662,7 +771,27 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     if (n1 != n0) gafe += Ws[j] * (gv[0] * dn0 + gv[1] * dn1);
   }
   __syncthreads();
-  // thread per SFH bin: dlnL/dm_i, dlnL/dzeta_i and the edge derivatives
+  // thread per SFH bin: dlnL/dm_i (linear scheme: d/dpsi of its two edges),
+  // dlnL/dzeta_i and the edge derivatives
+  if (md.sfh_linear) {
+    for (int i = tid; i < NT; i += blockDim.x) {
+      const int j0 = zb[i];
+      const float t = zt[i], d0 = zd0[i], d1 = zd1[i];
+      const LinGrad lg = lin_bin_grad(g, T[i], T[i + 1], m[i], m[i + 1], [&](int ag, float& G, float& Gz) {
+        const float g0 = gWs[ag * NZ + j0], g1 = NZ > 1 ? gWs[ag * NZ + j0 + 1] : 0.f;
+        G = g0 * (1.f - t) + g1 * t;
+        Gz = g0 * d0 + g1 * d1;
+      });
+      gps0[i] = lg.p0;
+      gps1[i] = lg.p1;
+      gzeta[i] = lg.zeta;
+      gTlo[i] = lg.t0;
+      gThi[i] = lg.t1;
+    }
+    __syncthreads();
+    for (int k = tid; k <= NT; k += blockDim.x)
+      out[md.offs[SED_KEY_SFH] + k] = (k < NT ? gps0[k] : 0.f) + (k > 0 ? gps1[k - 1] : 0.f);
+  } else
   for (int i = tid; i < NT; i += blockDim.x) {
     const float Ti = T[i], Ti1 = T[i + 1], dT = Ti1 - Ti;
     // first age whose cell reaches above T_i

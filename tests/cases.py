@@ -9,6 +9,12 @@ import oracle
 import synth
 
 
+def z_column(n_sfh, zmode, sfh_scheme=0):
+    """Column of the redshift in the oracle's parameter layout: the SFH key (N_T
+    masses, or N_T + 1 edge SFRs), logzsol (N_T or 1), afe, logmass, zred."""
+    return n_sfh + (1 if sfh_scheme == 1 else 0) + (n_sfh if zmode == 0 else 1) + 2
+
+
 def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_theta=4, lsf_r=None,
                spec_mask=None, sigma_gal_kms=None, calib_sigma=None):
     """lsf_r, spec_mask, sigma_gal_kms: optional replacements of the
@@ -39,7 +45,7 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
         if w.floor_phot or w.floor_spec:   # the truth row only makes the data: floors off for it
             orc.floor_phot, orc.floor_spec = 0, 0
             orc._rebuild_model()
-        th_true[0, w.n_sfh + (w.n_sfh if w.zmode == 0 else 1) + 2] = min(2.0, w.zf * 0.5)  # zred
+        th_true[0, z_column(w.n_sfh, w.zmode, w.sfh_scheme)] = min(2.0, w.zf * 0.5)
         res = orc.eval(th_true)
         assert res["status"][0] == 0
         nz = synth.noise(res["phot"].shape[1] + res["spec"].shape[1], seed=5)
@@ -132,8 +138,7 @@ def kink_rows(orc, th64, rel=2e-4):
     to show."""
     ll = np.log(np.asarray(orc.grid.lam_aa, dtype=np.float64))
     pos = np.log(np.asarray(orc.spec_lam, dtype=np.float64))
-    nz = orc.n_sfh if orc.zmode == 0 else 1
-    jz = orc.n_sfh + nz + 2
+    jz = z_column(orc.n_sfh, orc.zmode, orc.sfh_scheme)
     out = np.zeros(th64.shape[0], bool)
     for r in range(th64.shape[0]):
         x = pos - np.log1p(th64[r, jz])

@@ -217,6 +217,44 @@ def test_noise_floor_grad_vs_oracle(ctx, prec):
     assert np.abs(g[ok][:, orc.n_param - 8:orc.n_param]).max() > 0
 
 
+def central_differences(orc, th64, rel=1e-5):
+    """d lnL / d theta by central differences of the oracle's forward model, each
+    column stepped by rel x |value| (rel where the value is 0)."""
+    g = np.zeros_like(th64)
+    for j in range(th64.shape[1]):
+        h = rel * np.maximum(np.abs(th64[:, j]), 1e-300)
+        h = np.where(th64[:, j] == 0, rel, h)
+        a, b = th64.copy(), th64.copy()
+        a[:, j] += h
+        b[:, j] -= h
+        g[:, j] = (orc.eval(a)["lnl"] - orc.eval(b)["lnl"]) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("zmode", [0, 1])
+def test_linear_sfh_grad_vs_central_differences(ctx, zmode):
+    """The adjoint of the linear SFH scheme (App. B, Eq. tent_integral): d lnL /
+    d psi at every edge (each rate feeds two bins' tent shares and their
+    scale to the trapezoidal mass), d/dzeta, and d/dz through the edges'
+    dependence on T_max, against central differences of the oracle's forward
+    model on 12 rows of the tiny workload."""
+    import dataclasses
+    w = dataclasses.replace(synth.WORKLOADS["tiny_phot_16x4x512"], sfh_scheme=1, zmode=zmode)
+    key = f"linsfh_tiny_{zmode}"
+    if key not in _CACHE:
+        orc = cases.oracle_for(w)
+        _CACHE[key] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE[key]
+    th32, th64 = cases.theta_pair(w, 12, seed=64)
+    lnl, g, st = gpu_grad(model, th32, "fp32")
+    ok = st == 0
+    assert ok.sum() >= 8
+    fd = central_differences(orc, th64[ok])
+    check_grad(g[ok], fd[:, :orc.n_param], st[ok])
+    ref = orc.eval(th64)
+    assert (np.abs(lnl[ok] - ref["lnl"][ok]) / cases.lnl_scale(orc, ref)[ok]).max() < 1e-5
+
+
 def test_specphot_grad_vs_central_differences(ctx):
     """The adjoint against central finite differences of the FP64 oracle's
     forward model (h = 1e-7 relative) on 16 rows x all parameters."""

@@ -382,7 +382,7 @@ def test_linear_sfh_parity(ctx, prec):
     """The paper-scale photometric fit with the linear SFH scheme (App. B, Eq.
     tent_integral: per-edge SFRs, N_T + 1 columns, tent integrals per age
     node): 300 rows on the GPU, 30 sampled rows' photometry and lnL against the
-    oracle; the gradient is refused for this scheme."""
+    oracle."""
     w = synth.WORKLOADS["phot_linsfh_107x12x6000_b1024"]
     if "linsfh" not in _CACHE:
         orc = cases.oracle_for(w)
@@ -394,7 +394,3 @@ def test_linear_sfh_parity(ctx, prec):
     rows = np.unique(np.concatenate([[0, 299], np.random.default_rng(10).choice(300, 28, replace=False)]))
     ref = orc.eval(th64[rows])
     check(ref, got, prec, rows, orc=orc)
-    if prec == "fp32":
-        from paper_2609_30145_gb300.api import SedError
-        with pytest.raises(SedError):
-            model.loglike_grad(torch.from_numpy(th32).cuda(), "fp32")
