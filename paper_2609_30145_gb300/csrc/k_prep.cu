@@ -678,6 +678,9 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
 // A_ia = m_i |bin_i ∩ cell_a| / dT_i, with the edges T_i (i >= 3) following T_max(z).
 constexpr int PREP_BWD_THREADS = 128;
 
+// LINEAR: the weights' reverse pass of the linear SFH scheme (a separate
+// instance, so the step scheme's keeps its registers and shared memory)
+template <bool LINEAR>
 __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_constant__ PrepBwdArgs a) {
   pdl_enter();
   const ModelDev& md = a.md;
@@ -700,7 +703,10 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   __shared__ int zb[MAX_SFH];
   __shared__ float zt[MAX_SFH], zd0[MAX_SFH], zd1[MAX_SFH];
   __shared__ float gTlo[MAX_SFH], gThi[MAX_SFH], gzeta[MAX_SFH];
-  __shared__ float lin_sc[MAX_SFH], gps0[MAX_SFH], gps1[MAX_SFH];   // linear scheme
+  __shared__ float lin_buf[LINEAR ? 3 * MAX_SFH : 1];   // linear scheme: bin scales, d/dpsi of each bin's edges
+  float* lin_sc = lin_buf;
+  float* gps0 = lin_buf + (LINEAR ? MAX_SFH : 0);
+  float* gps1 = lin_buf + (LINEAR ? 2 * MAX_SFH : 0);
   __shared__ double red[PREP_BWD_THREADS / 32];
   __shared__ double s_tmax_part[PREP_BWD_THREADS / 32];
 
@@ -721,11 +727,11 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     zt[i] = w1;
     zd0[i] = d0;
     zd1[i] = d1;
-    if (md.sfh_linear) lin_sc[i] = lin_bin_scale(g, T[i], T[i + 1], m[i], m[i + 1]);
+    if constexpr (LINEAR) lin_sc[i] = lin_bin_scale(g, T[i], T[i + 1], m[i], m[i + 1]);
   }
   __syncthreads();
   // forward Ws (needed for the [a/Fe] derivative), thread per age node as in k_prep
-  if (md.sfh_linear) {
+  if constexpr (LINEAR) {
     for (int ag = tid; ag < NA; ag += blockDim.x) lin_node_fill(g, ag, NT, T, m, lin_sc, zb, zt, Ws + ag * NZ, NZ);
   } else
   for (int ag = tid; ag < NA; ag += blockDim.x) {
@@ -773,7 +779,7 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   __syncthreads();
   // thread per SFH bin: dlnL/dm_i (linear scheme: d/dpsi of its two edges),
   // dlnL/dzeta_i and the edge derivatives
-  if (md.sfh_linear) {
+  if constexpr (LINEAR) {
     for (int i = tid; i < NT; i += blockDim.x) {
       const int j0 = zb[i];
       const float t = zt[i], d0 = zd0[i], d1 = zd1[i];
@@ -867,9 +873,15 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
 cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
   const size_t smem = (size_t)2 * p.g.n_age * p.g.n_feh * sizeof(float);
   static size_t set_for = 0;
-  const cudaError_t e = ensure_dyn_smem(k_prep_bwd, smem, &set_for);
+  static size_t set_for_lin = 0;
+  if (p.md.sfh_linear) {
+    const cudaError_t e = ensure_dyn_smem(k_prep_bwd<true>, smem, &set_for_lin);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k_prep_bwd<true>, dim3(p.n), dim3(PREP_BWD_THREADS), smem, s, p);
+  }
+  const cudaError_t e = ensure_dyn_smem(k_prep_bwd<false>, smem, &set_for);
   if (e != cudaSuccess) return e;
-  return launch_pdl(k_prep_bwd, dim3(p.n), dim3(PREP_BWD_THREADS), smem, s, p);
+  return launch_pdl(k_prep_bwd<false>, dim3(p.n), dim3(PREP_BWD_THREADS), smem, s, p);
 }
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
