@@ -394,3 +394,31 @@ def test_linear_sfh_parity(ctx, prec):
     rows = np.unique(np.concatenate([[0, 299], np.random.default_rng(10).choice(300, 28, replace=False)]))
     ref = orc.eval(th64[rows])
     check(ref, got, prec, rows, orc=orc)
+
+
+def test_model_descriptor_validation(ctx):
+    """sed_create_model refuses what it cannot evaluate, before anything runs:
+    an unknown SFH scheme or noise-floor bits (SED_EINVAL), a floor on an arm
+    without data (SED_EINVAL), and a spectral floor together with the
+    calibration polynomial (SED_EUNSUPPORTED)."""
+    from paper_2609_30145_gb300.api import SedError
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=8)
+    orc = cases.oracle_for(w)
+    gid = ctx.load_grid(orc.grid)
+    base = dict(use_afe=w.use_afe, dust_law=w.dust_law, filters=orc.filters, phot_d=orc.phot_d,
+                phot_sigma=orc.phot_sigma)
+    spec = dict(spec_lam=orc.spec_lam, spec_d=orc.spec_d, spec_sigma=orc.spec_sigma, lsf_mode=orc.lsf_mode,
+                lsf_value=orc.lsf_value, sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref)
+
+    def refused(code, **kw):
+        with pytest.raises(SedError) as e:
+            ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)
+        assert e.value.status == code, str(e.value)
+
+    refused(1, **base, sfh_scheme=2)
+    refused(1, **base, noise_floor_phot=16)
+    refused(1, **base, noise_floor_spec=1)                      # no spectrum
+    refused(8, **base, **spec, calib_sigma=[0.1, 0.1], noise_floor_spec=2)
+    ok = ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **base, **spec, noise_floor_phot=9, sfh_scheme=1)
+    assert ok.n_param == orc.n_param + 1 + 2
