@@ -40,10 +40,10 @@ CALIB_WORKLOAD = "specphot_afe_calib13_107x12x5x6000_b2048"  # the same with a 1
 FLOOR_WORKLOAD = "specphot_afe_floor_107x12x5x6000_b2048"    # the same with every noise-floor term on
 LINSFH_WORKLOAD = "phot_linsfh_107x12x6000_b1024"   # the headline fit with the linear SFH scheme
 PRECS = ("fp32", "fp32_simt", "bf16", "fp8")
-PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 lnL",
-             "bf16": "BF16 tcgen05, FP32 accumulate, FP64 lnL",
-             "fp8": "FP8 E4M3 tcgen05 (power-of-two scales per SSP column and per row), FP32 accumulate, FP64 lnL",
-             "fp32_simt": "FP32 FFMA contraction, FP64 lnL"}
+PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 likelihood sums",
+             "bf16": "BF16 tcgen05, FP32 accumulate, FP64 likelihood sums",
+             "fp8": "FP8 E4M3 tcgen05 (power-of-two scales per SSP column and per row), FP32 accumulate, FP64 likelihood sums",
+             "fp32_simt": "FP32 FFMA contraction, FP64 likelihood sums"}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor ratio (recipe table)
 METRIC = "SED loglike evals/sec vs plain FP32 path at stated FP64-error; p50/p99 latency"

@@ -3,7 +3,10 @@
 // differentiation of the forward model (Sec. 4); here each step is
 // differentiated by hand, in reverse order:
 //
-//   lnL (Eq. total_lnlike)          u_b = dlnL/dm_b = (d_b - m_b)/sigma_b^2
+//   lnL (Eq. total_lnlike)          u_b = dlnL/dm_b = (d_b - m_b)/sigma_b^2 (with
+//                                   the noise floor's sigma_eff and its f_calib
+//                                   dependence on m, App. sys_floor; with the
+//                                   calibration polynomial, App. E)
 //   photometry (App. D)             dlnL/dF_k from the interpolation weights of
 //                                   every filter sample that touches node k
 //   spectrum (Eq. app_response)     dlnL/dF_k from every pixel whose Gaussian

@@ -12,6 +12,10 @@
 //     Gaussian in ln(lam) truncated at 5 sigma, linear interpolation for
 //     kernels narrower than half a model log-pixel
 //  lnL (Eq. total_lnlike): sum over included data of -r^2/2 - ln(2 pi sigma^2)/2
+//     (r = (d - m)/sigma), with sigma_eff for sigma under the optional noise
+//     floor (App. sys_floor) and the marginalised calibration polynomial's
+//     terms (App. E); spectral residuals in FP32 on the host's d/sigma and
+//     1/sigma, the bands' terms and every sum across threads in FP64
 //
 // All reductions run in a fixed order, so the result is bitwise reproducible.
 #include "sed_internal.cuh"
