@@ -261,13 +261,13 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     // columns so that the last partial wave spreads over the CTAs.  npc is 1, 2
     // or 4 (BN/npc stays a multiple of 16: a valid MMA N and 16-byte aligned
     // output columns)
-    const int G = (int)gridDim.x;
-    nfull = (upz / G) * G;
+    const int nctas = (int)gridDim.x;
+    nfull = (upz / nctas) * nctas;
     nrem = upz - nfull;
-    const int fit = nrem > 0 ? G / (nz * nrem) : 1;
+    const int fit = nrem > 0 ? nctas / (nz * nrem) : 1;
     npc = (fit >= 4 && BN / 4 >= 16) ? 4 : (fit >= 2 && BN / 2 >= 16 ? 2 : 1);
     const int total = nz * nfull + nz * nrem * npc;
-    n_units = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
+    n_units = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / nctas + 1 : 0;
   } else if (p.rs) {
     // grid schedule: union of the rest-frame node windows of the tile's rows
     // (invalid rows have none).  Forward: a wavelength tile outside it is never

@@ -812,7 +812,6 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     dv.samp_lam_min = (float)lmin;
     dv.samp_lam_max = (float)lmax;
     int* pi;
-    float* pf;
     double* pd;
     if (!st) { st = upload(ctx, &pi, bs.data(), bs.size(), &M->allocs, &M->bytes); dv.band_start = pi; }
     std::vector<float2> s2(S);
