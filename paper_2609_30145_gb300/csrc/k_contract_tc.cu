@@ -569,13 +569,13 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   if (a.prec == SED_PREC_FP8) {
     p.ky_tiles = a.Ky_pad / 128;
     p.k_tiles = a.Kpad / 128;
-    return wide ? tc::launch_cfg<SED_PREC_FP8, 128, 6, 4, false>(p, a.ldn, s)
-                : tc::launch_cfg<SED_PREC_FP8, 64, 8, 4, false>(p, a.ldn, s);
+    return wide ? tc::launch_cfg<SED_PREC_FP8, 128, 6, 8, false>(p, a.ldn, s)
+                : tc::launch_cfg<SED_PREC_FP8, 64, 8, 8, false>(p, a.ldn, s);
   }
   p.ky_tiles = a.Ky_pad / 64;
   p.k_tiles = a.Kpad / 64;
-  return wide ? tc::launch_cfg<SED_PREC_BF16, 128, 6, 4, false>(p, a.ldn, s)
-              : tc::launch_cfg<SED_PREC_BF16, 64, 8, 4, false>(p, a.ldn, s);
+  return wide ? tc::launch_cfg<SED_PREC_BF16, 128, 6, 8, false>(p, a.ldn, s)
+              : tc::launch_cfg<SED_PREC_BF16, 64, 8, 8, false>(p, a.ldn, s);
 }
 
 constexpr int DW_BN = 128;
