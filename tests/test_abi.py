@@ -70,19 +70,24 @@ def test_layout_packing_matches_oracle_layout():
     for zmode in (0, 1):
         for sgal in (0, 1):
             for fp, fs in ((0, 0), (5, 0), (0, 15), (9, 6)):
-                ranges = dict(synth.WORKLOADS["tiny_phot_16x4x512"].ranges, sigma_gal=(50.0, 500.0))
-                d = synth.make_theta(5, 7, zmode, ranges, seed=3)
-                rng = np.random.default_rng(4)
-                for k in _ffi.KEYS[12:]:
-                    d[k] = rng.uniform(-2.0, 0.5, 5)
-                m = Model.__new__(Model)
-                nz = 7 if zmode == 0 else 1
-                # the library's layout: sigma_gal and each floor term have a column only when on
-                widths = [7, nz] + [1] * 9 + [sgal] + [(fp >> k) & 1 for k in range(4)] + \
-                         [(fs >> k) & 1 for k in range(4)]
-                offs = list(np.cumsum([0] + widths[:-1]))
-                m.n_param = int(sum(widths))
-                m.offsets = dict(zip(_ffi.KEYS, offs))
-                a = m.pack(d, dtype=np.float64)
-                b = oracle.pack_theta(d, 7, zmode, sample_sigma_gal=sgal, floor_phot=fp, floor_spec=fs)
-                np.testing.assert_array_equal(a, b)
+                for scheme in (0, 1):
+                    ranges = dict(synth.WORKLOADS["tiny_phot_16x4x512"].ranges, sigma_gal=(50.0, 500.0))
+                    d = synth.make_theta(5, 7, zmode, ranges, seed=3)
+                    if scheme == 1:   # linear SFH scheme: one SFR per bin edge
+                        d["sfh"] = synth.edge_sfr(5, 7, seed=3)
+                    rng = np.random.default_rng(4)
+                    for k in _ffi.KEYS[12:]:
+                        d[k] = rng.uniform(-2.0, 0.5, 5)
+                    m = Model.__new__(Model)
+                    nz = 7 if zmode == 0 else 1
+                    # the library's layout: the SFH key has N_T (+1 for the linear
+                    # scheme) columns; sigma_gal and each floor term one only when on
+                    widths = [7 + scheme, nz] + [1] * 9 + [sgal] + [(fp >> k) & 1 for k in range(4)] + \
+                             [(fs >> k) & 1 for k in range(4)]
+                    offs = list(np.cumsum([0] + widths[:-1]))
+                    m.n_param = int(sum(widths))
+                    m.offsets = dict(zip(_ffi.KEYS, offs))
+                    a = m.pack(d, dtype=np.float64)
+                    b = oracle.pack_theta(d, 7, zmode, sample_sigma_gal=sgal, floor_phot=fp, floor_spec=fs,
+                                          sfh_scheme=scheme)
+                    np.testing.assert_array_equal(a, b)
