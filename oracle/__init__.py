@@ -57,7 +57,8 @@ class _Model(C.Structure):
                 ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", C.c_void_p),
-                ("sfh_scheme", C.c_int), ("floor_phot", C.c_int), ("floor_spec", C.c_int)]
+                ("sfh_scheme", C.c_int), ("floor_phot", C.c_int), ("floor_spec", C.c_int),
+                ("phot_upper", C.c_void_p)]
 
 
 def _load():
@@ -111,6 +112,7 @@ class Oracle:
     phot_d: np.ndarray | None = None
     phot_sigma: np.ndarray | None = None
     phot_mask: np.ndarray | None = None
+    phot_upper: np.ndarray | None = None   # nonzero: the band's datum is an upper limit (Eq. app_line_chi2_UL)
     spec_lam: np.ndarray | None = None
     spec_d: np.ndarray | None = None
     spec_sigma: np.ndarray | None = None
@@ -175,6 +177,7 @@ class Oracle:
             m.phot_d = _p(k(self.phot_d))
             m.phot_sigma = _p(k(self.phot_sigma))
             m.phot_mask = _p(k(self.phot_mask, np.uint8))
+            m.phot_upper = _p(k(self.phot_upper, np.uint8))
         if self.spec_lam is not None:
             m.n_pix = len(self.spec_lam)
             m.spec_lam = _p(k(self.spec_lam))

@@ -184,6 +184,15 @@ static double floor_terms_grad(const double *fl, double v, double r, double sigm
   return r / v + gv * 2.0 * fl[1] * fl[1] * m;
 }
 
+/* The residual d - m of photometric band b in Eq. "total_lnlike".  A band
+ * flagged as an upper limit (Sec. 4.1, Eq. "app_line_chi2_UL") costs nothing
+ * while the model stays at or below the limit d (residual 0) and the Gaussian
+ * residual against d once it exceeds it; its normalisation term stays. */
+static double phot_residual(const orc_model *md, int b, double d, double m) {
+  if (md->phot_upper && md->phot_upper[b] && m <= d) return 0.0;
+  return d - m;
+}
+
 static int theta_status(const orc_model *md, const double *th, double *tmax_out, double *cos_out) {
   int np = orc_n_param(md);
   for (int j = 0; j < np; j++)
@@ -663,7 +672,8 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
         if (phot) phot[b] = ph[b];
         if (md->phot_d && (!md->phot_mask || md->phot_mask[b])) {
           /* Eq. "total_lnlike" with sigma_eff of Eq. "app_noise_floor" (= sigma without a floor) */
-          double v = eff_var(t.fl[0], md->phot_sigma[b], ph[b], md->phot_d[b]), r = md->phot_d[b] - ph[b];
+          double v = eff_var(t.fl[0], md->phot_sigma[b], ph[b], md->phot_d[b]);
+          double r = phot_residual(md, b, md->phot_d[b], ph[b]);
           lnl += -0.5 * r * r / v - 0.5 * log(2.0 * M_PI * v);
         }
       }
@@ -877,7 +887,7 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
       double ub = 0.0;
       if (md->phot_d && (!md->phot_mask || md->phot_mask[b])) {
         double d = md->phot_d[b], m = ph[b], sg = md->phot_sigma[b];
-        double v = eff_var(t.fl[0], sg, m, d), r = d - m;
+        double v = eff_var(t.fl[0], sg, m, d), r = phot_residual(md, b, d, m);
         L += -0.5 * r * r / v - 0.5 * log(2.0 * M_PI * v);
         ub = floor_terms_grad(t.fl[0], v, r, sg, m, d, gfl[0]);
       }

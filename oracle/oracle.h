@@ -67,6 +67,8 @@ typedef struct {
                                   N_T + 1 columns; App. B, Eq. "tent_integral") */
   int floor_phot, floor_spec;  /* systematic noise floor of each arm (App. "sys_floor"): ORC_FLOOR_* bits;
                                   each term on adds a parameter column holding log10 of its value */
+  const unsigned char *phot_upper; /* [n_filt] nonzero: phot_d[b] is an upper limit (Sec. 4.1 likelihood,
+                                      Eq. "app_line_chi2_UL"), or NULL (none) */
 } orc_model;
 
 /* Terms of the noise floor, Eq. "app_noise_floor":
