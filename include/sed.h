@@ -200,6 +200,14 @@ typedef struct {
    * scheme has N_T + 1 SFH columns, and sed_loglike_grad returns d lnL / d psi
    * for each edge. */
   int sfh_scheme;
+  /* Photometric upper limits (Sec. 4.1 likelihood, App. line_lik, Eq.
+   * app_line_chi2_UL): [n_filt], nonzero marks phot_d[b] as an upper limit.
+   * Such a band adds ((d - m)/sigma_eff)^2 to chi^2 only while its model m
+   * exceeds the limit d and nothing while m <= d; its -1/2 ln(2 pi
+   * sigma_eff^2) stays in lnL, with sigma_eff of the noise floor when one is
+   * on.  NULL = no limits (the default).  Copied; a band the mask excludes
+   * stays out of lnL whatever its flag. */
+  const uint8_t *phot_upper;
 } sed_model_desc;
 
 #define SED_MAX_CALIB 13

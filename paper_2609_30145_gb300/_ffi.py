@@ -48,7 +48,8 @@ class ModelDesc(C.Structure):
                 ("sigma_gal_kms", C.c_double), ("z_ref", C.c_double),
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", P),
-                ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int), ("sfh_scheme", C.c_int)]
+                ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int), ("sfh_scheme", C.c_int),
+                ("phot_upper", P)]
 
 
 class StageStats(C.Structure):

@@ -114,7 +114,8 @@ class Context:
                      phot_d=None, phot_sigma=None, phot_mask=None, spec_lam=None, spec_d=None,
                      spec_sigma=None, spec_mask=None, lsf_mode=0, lsf_value=None,
                      sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0,
-                     calib_sigma=None, noise_floor_phot=0, noise_floor_spec=0, sfh_scheme=0) -> "Model":
+                     calib_sigma=None, noise_floor_phot=0, noise_floor_spec=0, sfh_scheme=0,
+                     phot_upper=None) -> "Model":
         d = _ffi.ModelDesc()
         d.grid, d.n_sfh, d.zf, d.zmode = grid_id, n_sfh, zf, zmode
         d.use_afe, d.use_nebular, d.dust_law = use_afe, use_nebular, dust_law
@@ -129,8 +130,10 @@ class Context:
             d.filt_len, d.filt_lam_aa, d.filt_trans = _ptr(lens), _ptr(lam), _ptr(tr)
             pd, ps = _f64(phot_d), _f64(phot_sigma)
             pm = None if phot_mask is None else np.ascontiguousarray(phot_mask, dtype=np.uint8)
-            keep += [pd, ps, pm]
+            pu = None if phot_upper is None else np.ascontiguousarray(phot_upper, dtype=np.uint8)
+            keep += [pd, ps, pm, pu]
             d.phot_d, d.phot_sigma, d.phot_mask = _ptr(pd), _ptr(ps), _ptr(pm)
+            d.phot_upper = _ptr(pu)
         if spec_lam is not None:
             sl, sd, ss, lv = _f64(spec_lam), _f64(spec_d), _f64(spec_sigma), _f64(lsf_value)
             sm = None if spec_mask is None else np.ascontiguousarray(spec_mask, dtype=np.uint8)

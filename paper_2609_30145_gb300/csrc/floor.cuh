@@ -44,4 +44,15 @@ __device__ __forceinline__ void floor_dparam(const float (&fl)[4], T gq, T mn, T
   g[3] += c * jn * jn;
 }
 
+// Residual (d - m)/sigma of photometric band b from dn = d/sigma and mn =
+// m/sigma.  A band flagged as an upper limit (Sec. 4.1 likelihood, Eq.
+// app_line_chi2_UL) costs nothing while the model stays at or below the limit:
+// its residual is then 0, which also zeroes its share of d lnL / d m (the
+// derivative of -min(r, 0)^2 / 2 is min(r, 0)).
+template <typename T>
+__device__ __forceinline__ T phot_resid(const ModelDev& md, int b, T dn, T mn) {
+  const T r = dn - mn;
+  return (md.phot_ul != nullptr && md.phot_ul[b] && r > (T)0) ? (T)0 : r;
+}
+
 }  // namespace sed

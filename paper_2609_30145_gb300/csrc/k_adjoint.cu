@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     // d lnL / d(band flux) = (d - m)/sigma^2, formed in FP32 from the normalised
     // datum and 1/sigma (0 for a masked band); times p_phot it weighs F
     const float isf = md.phot_isf[b];
-    float wb = md.phot_dn[b] - mb * isf;   // (d - m)/sigma; with a noise floor sigma d term / d m
+    float wb = phot_resid(md, b, md.phot_dn[b], mb * isf);   // (d - m)/sigma; with a noise floor sigma d term / d m
     if (md.floor_bits[0] && isf != 0.f) {
       const float mn = mb * isf, dn = md.phot_dn[b], q = floor_q(rs.fl[0], mn, dn, rs.fl[0][3] * isf);
       wb = floor_dm(rs.fl[0], wb, q, floor_gq(wb, q), mn);
@@ -589,7 +589,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     double bl = 0.0, bu = 0.0, gfp[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = lane; b < md.n_filt; b += 32) {
       if (md.phot_isig[b] != 0.0) {
-        const double is = md.phot_isig[b], mn = (double)mbp[b] * is, dn = md.phot_d[b] * is, rr = dn - mn;
+        const double is = md.phot_isig[b], mn = (double)mbp[b] * is, dn = md.phot_d[b] * is;
+        const double rr = phot_resid(md, b, dn, mn);
         if (md.floor_bits[0]) {   // sigma_eff of Eq. app_noise_floor
           const double jn = (double)rs.fl[0][3] * is, q = floor_q(rs.fl[0], mn, dn, jn), gq = floor_gq(rr, q);
           bl += -0.5 * (rr * rr / q + log(q)) + md.phot_nlog[b];

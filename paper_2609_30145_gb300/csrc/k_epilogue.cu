@@ -12,7 +12,8 @@
 //     Gaussian in ln(lam) truncated at 5 sigma, linear interpolation for
 //     kernels narrower than half a model log-pixel
 //  lnL (Eq. total_lnlike): sum over included data of -r^2/2 - ln(2 pi sigma^2)/2
-//     (r = (d - m)/sigma), with sigma_eff for sigma under the optional noise
+//     (r = (d - m)/sigma, min(r, 0) for a band that is an upper limit, Eq.
+//     app_line_chi2_UL), with sigma_eff for sigma under the optional noise
 //     floor (App. sys_floor) and the marginalised calibration polynomial's
 //     terms (App. E); spectral residuals in FP32 on the host's d/sigma and
 //     1/sigma, the bands' terms and every sum across threads in FP64
@@ -246,7 +247,8 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     double pv = 0.0;
     for (int b = lane; b < md.n_filt; b += 32) {
       if (md.phot_isig[b] != 0.0) {
-        const double is = md.phot_isig[b], mn = (double)mb_s[b] * is, dn = md.phot_d[b] * is, rr = dn - mn;
+        const double is = md.phot_isig[b], mn = (double)mb_s[b] * is, dn = md.phot_d[b] * is;
+        const double rr = phot_resid(md, b, dn, mn);
         if (md.floor_bits[0]) {   // sigma_eff of Eq. app_noise_floor
           const double q = floor_q(rs.fl[0], mn, dn, (double)rs.fl[0][3] * is);
           pv += -0.5 * (rr * rr / q + log(q)) + md.phot_nlog[b];

@@ -827,6 +827,14 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     if (!st) { st = upload(ctx, &pz, zf.data(), zf.size(), &M->allocs, &M->bytes); dv.phot_dn = pz; }
     if (!st) { st = upload(ctx, &pz, zf.data(), zf.size(), &M->allocs, &M->bytes); dv.phot_isf = pz; }
     if (d->phot_mask) M->phot_mask_h.assign(d->phot_mask, d->phot_mask + d->n_filt);
+    // upper-limit flags (Eq. app_line_chi2_UL): uploaded only when a band has one
+    if (!st && d->phot_upper) {
+      std::vector<uint8_t> ul(d->n_filt);
+      bool any = false;
+      for (int b = 0; b < d->n_filt; b++) any |= (ul[b] = d->phot_upper[b] ? 1 : 0) != 0;
+      uint8_t* pu;
+      if (any) { st = upload(ctx, &pu, ul.data(), ul.size(), &M->allocs, &M->bytes); dv.phot_ul = pu; }
+    }
   }
   // ---- spectrum: per-pixel dispersion, Eq. app_sigeff + fixed sigma_gal (Eq. one_kernel);
   //      with a sampled sigma_gal the fixed part sigma_fix^2 / c^2 per pixel, the

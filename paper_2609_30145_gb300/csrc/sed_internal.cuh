@@ -134,6 +134,7 @@ struct ModelDev {
   const double* phot_nlog; // [n_filt] -1/2 ln(2 pi sigma^2) (0 when masked out)
   const float* phot_dn;    // [n_filt] d/sigma and 1/sigma in FP32 (0 when masked out), for the
   const float* phot_isf;   //   adjoint's per-band weights
+  const uint8_t* phot_ul;  // [n_filt] 1: the datum is an upper limit (Eq. app_line_chi2_UL); NULL: none
   float samp_lam_min, samp_lam_max;
   // spectrum
   int n_pix;

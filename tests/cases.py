@@ -3,6 +3,8 @@ parameter rows and mock data (data = oracle model at a true parameter row,
 perturbed by Gaussian noise at S/N 20)."""
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 
 import oracle
@@ -92,7 +94,7 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
               noise_floor_phot=orc.floor_phot, noise_floor_spec=orc.floor_spec, sfh_scheme=orc.sfh_scheme,
               bc_edge_log_age_yr=orc.bc_edge_log_age_yr, H0=orc.H0, Om0=orc.Om0,
               filters=orc.filters, phot_d=orc.phot_d, phot_sigma=orc.phot_sigma,
-              phot_mask=orc.phot_mask)
+              phot_mask=orc.phot_mask, phot_upper=orc.phot_upper)
     if orc.spec_lam is not None:
         kw.update(spec_lam=orc.spec_lam, spec_d=orc.spec_d if with_spec_data else None,
                   spec_sigma=orc.spec_sigma if with_spec_data else None,
@@ -174,3 +176,18 @@ def lnl_scale(orc, ref):
         c += -0.5 * np.sum(np.log(2 * np.pi * orc.spec_sigma[m] ** 2))
     half_chi2 = c - ref["lnl"]
     return np.maximum(np.abs(ref["lnl"]), half_chi2 + abs(c))
+
+
+def with_upper_limits(orc):
+    """The oracle `orc` with every other photometric band's datum taken as an
+    upper limit (Sec. 4.1 likelihood, Eq. app_line_chi2_UL)."""
+    return dataclasses.replace(orc, phot_upper=(np.arange(len(orc.phot_sigma)) % 2).astype(np.uint8))
+
+
+def limit_regimes(orc, phot):
+    """(limits the rows' models exceed, limits they respect), counted over the
+    flagged bands of `orc` and the rows' band fluxes `phot`."""
+    up = np.asarray(orc.phot_upper).astype(bool)
+    d = np.asarray(orc.phot_d)[up]
+    m = np.asarray(phot)[:, up]
+    return int(np.sum(m > d)), int(np.sum(m <= d))

@@ -91,3 +91,32 @@ def test_layout_packing_matches_oracle_layout():
                     b = oracle.pack_theta(d, 7, zmode, sample_sigma_gal=sgal, floor_phot=fp, floor_spec=fs,
                                           sfh_scheme=scheme)
                     np.testing.assert_array_equal(a, b)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every descriptor the binding passes by pointer has, field by field, the
+    offsets and size a C compiler gives the header's struct."""
+    import shutil
+    import subprocess
+    from paper_2609_30145_gb300 import _ffi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sed_grid_desc": _ffi.GridDesc, "sed_model_desc": _ffi.ModelDesc,
+               "sed_stage_stats": _ffi.StageStats, "sed_server_desc": _ffi.ServerDesc,
+               "sed_server_stats": _ffi.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sed.h"', "int main(void) {"]
+    want = []
+    for cname, cls in structs.items():
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(C.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+            want.append(getattr(cls, f).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == want

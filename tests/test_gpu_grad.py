@@ -217,6 +217,31 @@ def test_noise_floor_grad_vs_oracle(ctx, prec):
     assert np.abs(g[ok][:, orc.n_param - 8:orc.n_param]).max() > 0
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_upper_limits_grad_vs_oracle(ctx, prec):
+    """The adjoint with every other band an upper limit (Eq. app_line_chi2_UL)
+    and the full noise floor: 150 rows, every column against the oracle's
+    analytic gradient (the one-sided term is continuous in value and slope)."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_floor_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=150)
+    if "floor_ul" not in _CACHE:
+        orc = cases.with_upper_limits(cases.oracle_for(w))
+        _CACHE["floor_ul"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE["floor_ul"]
+    th32, th64 = cases.theta_pair(w, w.batch, seed=65, orc=orc)
+    lnl, g, st = gpu_grad(model, th32, prec)
+    ref = orc.grad(th64)
+    assert np.array_equal(st, ref["status"])
+    kinks = {int(r): model.offsets["zred"] for r in np.nonzero(cases.kink_rows(orc, th64))[0]}
+    check_grad(g, ref["grad"], st, skip=kinks)
+    ok = st == 0
+    fwd = orc.eval(th64)
+    exceeded, respected = cases.limit_regimes(orc, fwd["phot"][ok])
+    assert exceeded > 20 and respected > 20
+    scale = cases.lnl_scale(orc, fwd)[ok]
+    assert (np.abs(lnl[ok] - fwd["lnl"][ok]) / scale).max() < 1e-5
+
+
 def central_differences(orc, th64, rel=1e-5):
     """d lnL / d theta by central differences of the oracle's forward model, each
     column stepped by rel x |value| (rel where the value is 0)."""

@@ -396,6 +396,26 @@ def test_linear_sfh_parity(ctx, prec):
     check(ref, got, prec, rows, orc=orc)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_upper_limits_parity(ctx, prec):
+    """Every other band an upper limit (Sec. 4.1 likelihood, Eq.
+    app_line_chi2_UL) in the spectro-photometric fit with the full noise floor
+    on both arms: 150 rows' lnL and models against the oracle, the rows
+    exceeding some limits and respecting others."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_floor_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=150)
+    if "floor_ul" not in _CACHE:
+        orc = cases.with_upper_limits(cases.oracle_for(w))
+        _CACHE["floor_ul"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE["floor_ul"]
+    th32, th64 = cases.theta_pair(w, w.batch, seed=64, orc=orc)
+    ref = orc.eval(th64)
+    exceeded, respected = cases.limit_regimes(orc, ref["phot"][ref["status"] == 0])
+    assert exceeded > 20 and respected > 20
+    got = run_gpu(model, th32, prec)
+    check(ref, got, prec, orc=orc)
+
+
 def test_model_descriptor_validation(ctx):
     """sed_create_model refuses what it cannot evaluate, before anything runs:
     an unknown SFH scheme or noise-floor bits (SED_EINVAL), a floor on an arm
