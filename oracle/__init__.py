@@ -58,7 +58,7 @@ class _Model(C.Structure):
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", C.c_void_p),
                 ("sfh_scheme", C.c_int), ("floor_phot", C.c_int), ("floor_spec", C.c_int),
-                ("phot_upper", C.c_void_p)]
+                ("phot_upper", C.c_void_p), ("fesc_geometry", C.c_int)]
 
 
 def _load():
@@ -127,6 +127,7 @@ class Oracle:
     sfh_scheme: int = 0                 # 0 step (N_T bin masses), 1 linear (N_T + 1 edge SFRs; App. B)
     floor_phot: int = 0                 # noise-floor terms of each arm (App. sys_floor): FLOOR_* bits
     floor_spec: int = 0
+    fesc_geometry: int = 0              # ionising-photon escape (Sec. frac_obrun): FESC_*; adds the frac_obrun column
     H0: float = PHYS["H0"]
     Om0: float = PHYS["Om0"]
     bc_edge_log_age_yr: float = PHYS["bc_edge_log_age_yr"]
@@ -195,6 +196,7 @@ class Oracle:
                 raise ValueError("a spectral noise floor with the marginalised calibration polynomial is not defined here")
         m.floor_phot, m.floor_spec = int(self.floor_phot), int(self.floor_spec)
         m.sfh_scheme = int(self.sfh_scheme)
+        m.fesc_geometry = int(self.fesc_geometry)
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
@@ -279,8 +281,9 @@ class Oracle:
     def grad(self, theta, nthreads=0):
         """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])
         (step SFH scheme; grad_fd serves the linear one)."""
-        if self.sfh_scheme != 0:
-            raise NotImplementedError("the analytic gradient follows the step scheme; use grad_fd")
+        if self.sfh_scheme != 0 or self.fesc_geometry != 0:
+            raise NotImplementedError("the analytic gradient follows the step scheme without an escape "
+                                      "geometry; use grad_fd")
         th = np.ascontiguousarray(theta, dtype=np.float64)
         n, ld = th.shape
         out = np.zeros((n, ld))
@@ -322,6 +325,7 @@ def dust_tau(law, lam, tau, index):
 
 
 FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
+FESC_NONE, FESC_RUNAWAY_BC, FESC_PICKET = 0, 1, 2
 FLOOR_NAMES = ("log_err_scale", "log_f_calib", "log_f_data", "log_jitter")
 
 
@@ -331,18 +335,19 @@ def floor_keys(floor_phot=0, floor_spec=0):
                  for k in range(4) if (bits >> k) & 1)
 
 
-def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, sfh_scheme=0):
+def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, sfh_scheme=0, fesc_geometry=0):
     """Parameter rows in the oracle's layout: sfh[N_T] (bin masses; N_T + 1 edge
     SFRs with the linear scheme), logzsol[N_T or 1], then
     afe, logmass, zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index,
     gas_logz, gas_logu, sigma_gal when the model samples it, and the log10 of
-    each noise-floor term that is on (photometry, then spectrum)."""
+    each noise-floor term that is on (photometry, then spectrum), and frac_obrun
+    with an escape geometry."""
     nz = n_sfh if zmode == 0 else 1
     n = d["sfh"].shape[0]
     cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh + (1 if sfh_scheme == 1 else 0)),
             np.asarray(d["logzsol"], dtype=np.float64).reshape(n, nz)]
     for k in ("afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
               "diffuse_dust_index", "gas_logz", "gas_logu") + (("sigma_gal",) if sample_sigma_gal else ()) + \
-            floor_keys(floor_phot, floor_spec):
+            floor_keys(floor_phot, floor_spec) + (("frac_obrun",) if fesc_geometry else ()):
         cols.append(np.asarray(d[k], dtype=np.float64).reshape(n, 1))
     return np.ascontiguousarray(np.concatenate(cols, axis=1))

@@ -127,7 +127,7 @@ static int sfh_cols(const orc_model *md) { return md->n_sfh + (md->sfh_scheme ==
 
 int orc_n_param(const orc_model *md) {
   return sfh_cols(md) + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0) +
-         n_floor(md->floor_phot) + n_floor(md->floor_spec);
+         n_floor(md->floor_phot) + n_floor(md->floor_spec) + (md->fesc_geometry ? 1 : 0);
 }
 
 /* parameter row decoding (layout: sfh[N_T], logzsol[N_T or 1], afe, logmass,
@@ -138,6 +138,7 @@ typedef struct {
   double afe, logmass, z, tau_bc, alpha_bc, tau_d, delta, gas_logz, gas_logu, sigma_gal;
   double fl[2][4];   /* noise floor {s, f_calib, f_data, j} of photometry [0] and spectrum [1] */
   int fl_col[2][4];  /* column of each term in the row, -1 when the term is off */
+  double fob;        /* runaway fraction f_ob (0 without an escape geometry) */
 } orc_theta;
 
 static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
@@ -161,6 +162,7 @@ static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
       }
     }
   }
+  o->fob = md->fesc_geometry ? th[col] : 0.0;
 }
 
 /* Eq. "app_noise_floor": the effective variance of a datum with formal error
@@ -200,6 +202,7 @@ static int theta_status(const orc_model *md, const double *th, double *tmax_out,
   orc_theta t;
   decode_theta(md, th, &t);
   if (md->sample_sigma_gal && !(t.sigma_gal >= 0.0 && t.sigma_gal <= md->sigma_gal_max_kms)) return ORC_BAD_THETA;
+  if (md->fesc_geometry && !(t.fob >= 0.0 && t.fob <= 1.0)) return ORC_BAD_THETA;
   if (t.z < 0.0 || t.z >= md->zf) return ORC_BAD_Z;
   double cz[3], cf[3];
   orc_cosmology(md->H0, md->Om0, t.z, cz);
@@ -606,6 +609,8 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
   double *Y = (double *)calloc(NL, sizeof(double));
   double *O = (double *)calloc(NL, sizeof(double));
   double *F = (double *)malloc(NL * sizeof(double));
+  double *YL = (double *)calloc(NL, sizeof(double)); /* young ionising continuum (nebular ages, < 912 A) */
+  double *N = (double *)calloc(NL, sizeof(double));  /* nebular continuum */
   double *fnu = (double *)malloc(NL * sizeof(double));
   double *tbc = (double *)malloc(NL * sizeof(double));
   double *td = (double *)malloc(NL * sizeof(double));
@@ -633,8 +638,8 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
           int neb = md->use_nebular && g->neb_tab && young;
           double *acc = young ? Y : O;
           for (int k = 0; k < NL; k++) {
-            if (neb && g->lam[k] < O_LYMAN) continue;
-            acc[k] += w * f[k];
+            if (neb && g->lam[k] < O_LYMAN) YL[k] += w * f[k];
+            else acc[k] += w * f[k];
           }
           if (young) qy += w * Q[s];
         }
@@ -650,13 +655,31 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
       const double *t11 = g->neb_tab + ((size_t)u1 * g->neb_n_logz + z1) * NL;
       for (int k = 0; k < NL; k++) {
         double lg = wu0 * wz0 * t00[k] + wu0 * wz1 * t01[k] + wu1 * wz0 * t10[k] + wu1 * wz1 * t11[k];
-        Y[k] += qy * pow(10.0, lg);
+        N[k] = qy * pow(10.0, lg);
       }
     }
     /* two-component dust (Sec. 2.4) */
     for (int k = 0; k < NL; k++) tbc[k] = t.tau_bc * pow(g->lam[k] / 5500.0, t.alpha_bc);
     orc_dust_tau(md->dust_law, g->lam, NL, t.tau_d, t.delta, td);
-    for (int k = 0; k < NL; k++) F[k] = exp(-td[k]) * (exp(-tbc[k]) * Y[k] + O[k]);
+    /* Eq. "app_attn" with the escape geometries of Sec. "frac_obrun".  The
+     * covered fraction 1 - f_ob powers the nebular continuum; the ionising
+     * continuum of the nebular ages is absorbed except for the fraction f_ob
+     * that escapes, which bypasses the birth cloud.  runaway_bc: the young
+     * array (stellar + nebular continuum) crosses T = (1 - f_ob) e^{-tau_BC} +
+     * f_ob, then everything the diffuse screen.  picket: f_ob of the young
+     * stellar light, ionising continuum included, escapes both screens; the
+     * rest crosses both.  f_ob = 0 (or no geometry) is Eq. "app_attn". */
+    const double fob = t.fob;
+    for (int k = 0; k < NL; k++) {
+      const double ed = exp(-td[k]), eb = exp(-tbc[k]);
+      if (md->fesc_geometry == ORC_FESC_PICKET) {
+        F[k] = fob * (Y[k] + YL[k]) + ed * ((1.0 - fob) * eb * (Y[k] + N[k]) + O[k]);
+      } else {
+        const double T = (1.0 - fob) * eb + fob;
+        F[k] = ed * (T * (Y[k] + (1.0 - fob) * N[k]) + fob * YL[k] + O[k]);
+      }
+      Y[k] += N[k];   /* Y_out: young stellar flux (ionising continuum removed) plus nebular */
+    }
     /* observer frame, Sec. 2.6 */
     double dl = cosm[0] > 10.0 * O_PC_CM ? cosm[0] : 10.0 * O_PC_CM;
     double scale = pow(10.0, t.logmass) * O_LSUN * (1.0 + t.z) / (4.0 * M_PI * dl * dl);
@@ -706,7 +729,7 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
   if (O_out) memcpy(O_out, O, NL * sizeof(double));
   if (F_out) memcpy(F_out, F, NL * sizeof(double));
   if (fnu_out) memcpy(fnu_out, fnu, NL * sizeof(double));
-  free(W); free(Q); free(Y); free(O); free(F); free(fnu); free(tbc); free(td);
+  free(W); free(Q); free(Y); free(O); free(F); free(YL); free(N); free(fnu); free(tbc); free(td);
   return st;
 }
 

@@ -69,7 +69,14 @@ typedef struct {
                                   each term on adds a parameter column holding log10 of its value */
   const unsigned char *phot_upper; /* [n_filt] nonzero: phot_d[b] is an upper limit (Sec. 4.1 likelihood,
                                       Eq. "app_line_chi2_UL"), or NULL (none) */
+  int fesc_geometry;           /* ionising-photon escape (Sec. "frac_obrun"): ORC_FESC_*; with a geometry the
+                                  row's last column is the runaway fraction f_ob in [0, 1] */
 } orc_model;
+
+/* Escape geometries of the young light, Sec. "frac_obrun" */
+#define ORC_FESC_NONE 0
+#define ORC_FESC_RUNAWAY_BC 1   /* Eq. "runaway_mix": T_BC -> (1 - f_ob) e^{-tau_BC} + f_ob */
+#define ORC_FESC_PICKET 2       /* f_ob of the young light escapes both dust components */
 
 /* Terms of the noise floor, Eq. "app_noise_floor":
  * sigma_eff^2 = s^2 sigma^2 + (f_calib |m|)^2 + (f_data |d|)^2 + j^2.  Their
