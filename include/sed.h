@@ -111,7 +111,8 @@ enum {
   SED_KEY_LOG_F_CALIB_SPEC = 17,
   SED_KEY_LOG_F_DATA_SPEC = 18,
   SED_KEY_LOG_JITTER_SPEC = 19,     /* j in the spectral data's units */
-  SED_NKEYS = 20
+  SED_KEY_FRAC_OBRUN = 20,    /* runaway fraction f_ob in [0, 1] (a column only with an escape geometry) */
+  SED_NKEYS = 21
 };
 
 typedef struct sed_ctx sed_ctx;
@@ -208,9 +209,23 @@ typedef struct {
    * on.  NULL = no limits (the default).  Copied; a band the mask excludes
    * stays out of lnL whatever its flag. */
   const uint8_t *phot_upper;
+  /* Ionising-photon escape (Sec. frac_obrun): SED_FESC_NONE (0, the default),
+   * SED_FESC_RUNAWAY_BC (Eq. runaway_mix: the young light, stellar and
+   * nebular continuum, crosses (1 - f_ob) e^{-tau_BC} + f_ob, then the
+   * diffuse screen) or SED_FESC_PICKET (a fraction f_ob of the young stellar
+   * light escapes both screens, the rest crosses both).  Either way only the
+   * covered fraction 1 - f_ob powers the nebular continuum, and the fraction
+   * f_ob of the nebular ages' ionising continuum (below 912 A) escapes instead
+   * of being absorbed, bypassing the birth cloud.  A geometry adds the column
+   * SED_KEY_FRAC_OBRUN; a row whose f_ob lies outside [0, 1] gets
+   * SED_ROW_BAD_THETA.  With f_ob = 0 the model is the one without a geometry. */
+  int fesc_geometry;
 } sed_model_desc;
 
 #define SED_MAX_CALIB 13
+#define SED_FESC_NONE 0
+#define SED_FESC_RUNAWAY_BC 1
+#define SED_FESC_PICKET 2
 #define SED_SFH_STEP 0
 #define SED_SFH_LINEAR 1
 #define SED_FLOOR_ERR_SCALE 1

@@ -21,9 +21,10 @@ ROW_BAD_THETA, ROW_BAD_Z, ROW_BAD_TMAX, ROW_NONFINITE, ROW_DEVICE_TIMEOUT = 1, 2
 KEYS = ("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
         "diffuse_dust_index", "gas_logz", "gas_logu", "sigma_gal",
         "log_err_scale_phot", "log_f_calib_phot", "log_f_data_phot", "log_jitter_phot",
-        "log_err_scale_spec", "log_f_calib_spec", "log_f_data_spec", "log_jitter_spec")
+        "log_err_scale_spec", "log_f_calib_spec", "log_f_data_spec", "log_jitter_spec", "frac_obrun")
 FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
 SFH_STEP, SFH_LINEAR = 0, 1
+FESC_NONE, FESC_RUNAWAY_BC, FESC_PICKET = 0, 1, 2
 NKEYS = len(KEYS)
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -49,7 +50,7 @@ class ModelDesc(C.Structure):
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", P),
                 ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int), ("sfh_scheme", C.c_int),
-                ("phot_upper", P)]
+                ("phot_upper", P), ("fesc_geometry", C.c_int)]
 
 
 class StageStats(C.Structure):

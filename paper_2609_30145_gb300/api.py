@@ -115,7 +115,7 @@ class Context:
                      spec_sigma=None, spec_mask=None, lsf_mode=0, lsf_value=None,
                      sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0,
                      calib_sigma=None, noise_floor_phot=0, noise_floor_spec=0, sfh_scheme=0,
-                     phot_upper=None) -> "Model":
+                     phot_upper=None, fesc_geometry=0) -> "Model":
         d = _ffi.ModelDesc()
         d.grid, d.n_sfh, d.zf, d.zmode = grid_id, n_sfh, zf, zmode
         d.use_afe, d.use_nebular, d.dust_law = use_afe, use_nebular, dust_law
@@ -149,6 +149,7 @@ class Context:
             d.calib_n, d.calib_sigma = cs.size, _ptr(cs)
         d.noise_floor_phot, d.noise_floor_spec = int(noise_floor_phot), int(noise_floor_spec)
         d.sfh_scheme = int(sfh_scheme)
+        d.fesc_geometry = int(fesc_geometry)
         mid = C.c_int32()
         self._check(self._lib.sed_create_model(self._h, C.byref(d), C.byref(mid)))
         return Model(self, mid.value, n_filt=d.n_filt, n_pix=d.n_pix)

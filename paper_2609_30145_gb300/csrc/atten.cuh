@@ -6,6 +6,13 @@
 //   tau_d  = tau_diff (lam/5500)^delta                        (power law), or
 //            tau_diff [k'(lam) + E_b(delta) D(lam)]/4.05 (lam/5500)^delta  (Kriek & Conroy 2013)
 //   neb    = Q_young 10^(bilinear log10 template)
+// With an escape geometry (Sec. frac_obrun) and runaway fraction f, the
+// nebular ages' ionising continuum Y_ion (nodes below 912 A, kept in Y) is
+// split off, Y_s = Y - Y_ion, and
+//   runaway_bc (Eq. runaway_mix):
+//     F = e^{-tau_d} [ T (Y_s + (1-f) neb) + f Y_ion + O ],  T = (1-f) e^{-tau_BC} + f
+//   picket:
+//     F = f Y + e^{-tau_d} [ (1-f) e^{-tau_BC} (Y_s + neb) + O ]
 #pragma once
 #include "sed_internal.cuh"
 
@@ -33,8 +40,16 @@ __device__ __forceinline__ float attenuated(const ModelDev& md, const RowScal& r
   const float tbc = rs.tau_bc * __expf(rs.alpha_bc * c.x);
   const float pw = __expf(rs.delta * c.x);
   const float td = rs.tau_d * dust_shape(md, c, eb, pw);
-  if (md.use_neb) y += ex2_approx(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, neb_tab, k));
-  return __expf(-td) * (__expf(-tbc) * y + o);
+  if (md.fesc_geom == SED_FESC_NONE) {
+    if (md.use_neb) y += ex2_approx(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, neb_tab, k));
+    return __expf(-td) * (__expf(-tbc) * y + o);
+  }
+  const float nb = md.use_neb ? ex2_approx(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, neb_tab, k)) : 0.f;
+  const bool lyc = md.use_neb && k < md.n_lyc;
+  const float ys = lyc ? 0.f : y, f = rs.fob, ed = __expf(-td), ebc = __expf(-tbc);
+  if (md.fesc_geom == SED_FESC_PICKET) return f * y + ed * ((1.f - f) * ebc * (ys + nb) + o);
+  const float T = (1.f - f) * ebc + f;
+  return ed * (T * (ys + (1.f - f) * nb) + (lyc ? f * y : 0.f) + o);
 }
 
 }  // namespace sed

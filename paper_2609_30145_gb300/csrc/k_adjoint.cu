@@ -36,8 +36,8 @@ namespace sed {
 constexpr int EB_THREADS = 256;
 constexpr int EB_WARPS = EB_THREADS / 32;
 constexpr int EB_MAX_BANDS = 128;
-constexpr int EB_NRED = 15;   // per-warp partial sums: 13 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
-constexpr int EB_NREDF = 13;
+constexpr int EB_NRED = 16;   // per-warp partial sums: 14 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
+constexpr int EB_NREDF = 14;
 
 __device__ __forceinline__ float tf32_rna_dev(float x) {
   uint32_t r;
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   __syncthreads();
 
   // ---- dust and nebular: dlnL/dY, dlnL/dO and the parameter sums over lambda
-  float g_tbc = 0.f, g_abc = 0.f, g_td = 0.f, g_dl = 0.f, g_qy = 0.f, g_lu = 0.f, g_lz = 0.f;
+  float g_tbc = 0.f, g_abc = 0.f, g_td = 0.f, g_dl = 0.f, g_qy = 0.f, g_lu = 0.f, g_lz = 0.f, g_fob = 0.f;
   for (int k = tid; k < a.ldn; k += EB_THREADS) {
     if (k < k_lo || k > k_hi) {
       put_g(a, a.gy_hi, a.gy_lo, ro + k, 0.f);
@@ -527,26 +527,47 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     const float dshape = md.dust_law == SED_DUST_POWER_LAW ? pw * lnp : -1.9f * c.z * pw + shape * lnp;
     const float td = rs.tau_d * shape;
     const float ed = __expf(-td), eb = __expf(-tbc);
-    float y = Yr[k];
+    const float y = Yr[k];
     float lg = 0.f, nb = 0.f;
     if (md.use_neb) {
       lg = neb_log10(rs, g.neb_tab, k);
       nb = ex2_approx(rs.log2_qy + 3.3219280948873623f * lg);
-      y += nb;
     }
     const float gF = phi[k];
-    const float gy = gF * ed * eb, go = gF * ed;
+    // dF/dY, dF/dtau_BC (as gtbc), dF/dneb and dF/df of the node (atten.cuh's F)
+    float gy, gtbc, gnb;
+    float gtd = -gF * Fs[k];
+    if (md.fesc_geom == SED_FESC_NONE) {
+      gy = gF * ed * eb;
+      gtbc = -gy * (y + nb);
+      gnb = gy;
+    } else {
+      const float f = rs.fob, c = (md.use_neb && k < md.n_lyc) ? 0.f : 1.f;
+      if (md.fesc_geom == SED_FESC_PICKET) {
+        const float b = c * y + nb, se = ed * (1.f - f) * eb;
+        gy = gF * (f + se * c);
+        gtbc = -gF * se * b;
+        gnb = gF * se;
+        g_fob += gF * (y - ed * eb * b);
+        gtd = -gF * (Fs[k] - f * y);   // the escaping light crosses no screen
+      } else {
+        const float T = (1.f - f) * eb + f, av = c * y + (1.f - f) * nb;
+        gy = gF * ed * (T * c + f * (1.f - c));
+        gtbc = -gF * ed * (1.f - f) * eb * av;
+        gnb = gF * ed * T * (1.f - f);
+        g_fob += gF * ed * ((1.f - eb) * av - T * nb + (1.f - c) * y);
+      }
+    }
+    const float go = gF * ed;
     put_g(a, a.gy_hi, a.gy_lo, ro + k, gy);
     put_g(a, a.go_hi, a.go_lo, ro + k, go);
-    const float gtbc = -gy * y;
     g_tbc += gtbc * pa;
     g_abc += gtbc * tbc * lnp;
-    const float gtd = -gF * Fs[k];
     g_td += gtd * shape;
     g_dl += gtd * rs.tau_d * dshape;
     if (md.use_neb) {
-      g_qy += gy * ex2_approx(3.3219280948873623f * lg);
-      const float glg = gy * nb * 2.302585092994046f;
+      g_qy += gnb * ex2_approx(3.3219280948873623f * lg);
+      const float glg = gnb * nb * 2.302585092994046f;
       float su = 0.f, sz = 0.f;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -563,7 +584,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   //      the warp in FP32, lnL and d lnL/d ln(mass) in FP64; across the warps
   //      in FP64, one column per lane of warp 0
   float vf[EB_NREDF] = {g_tbc, g_abc, g_td, g_dl, g_lz, g_lu, gz_gather + gz_spec, g_qy, g_sgal,
-                        gfs[0], gfs[1], gfs[2], gfs[3]};
+                        gfs[0], gfs[1], gfs[2], gfs[3], g_fob};
 #pragma unroll
   for (int q = 0; q < EB_NREDF; ++q) {
 #pragma unroll
@@ -628,6 +649,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       rg[RG_Z] = um_phot * (double)rs.dlnp_dz + um_sp * (double)rs.dlns_dz + s[6];
       rg[RG_QY] = s[7];
       rg[RG_SIGMA_GAL] = s[8];
+      rg[RG_FOB] = s[13];
       for (int k = 0; k < 4; ++k) {
         rg[RG_FLOOR + k] = gfp[k];
         rg[RG_FLOOR + 4 + k] = s[9 + k];

@@ -437,6 +437,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     const float sg = th[md.offs[SED_KEY_SIGMA_GAL]];
     if (!(sg >= 0.f && sg <= md.sgal_max_kms)) status = SED_ROW_BAD_THETA;
   }
+  // a runaway fraction outside [0, 1] (Sec. frac_obrun)
+  if (!status && md.fesc_geom) {
+    const float f = th[md.offs[SED_KEY_FRAC_OBRUN]];
+    if (!(f >= 0.f && f <= 1.f)) status = SED_ROW_BAD_THETA;
+  }
   const CosmoRow cr = s_cr;
   if (!status) status = cr.status;
   const double tmax = status ? 0.0 : (double)cr.tmax_d;
@@ -657,6 +662,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.orig = r;
     rs.y_scale = y_scale;
     rs.sg_ln = md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] / (float)C_KMS : 0.f;
+    rs.fob = md.fesc_geom ? th[md.offs[SED_KEY_FRAC_OBRUN]] : 0.f;
     rs.k_lo = win_lo;
     rs.k_hi = win_hi;
     if (a.tile_win) {   // union of the windows of this row's 128-row tile
@@ -860,6 +866,7 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     out[md.offs[SED_KEY_GAS_LOGZ]] = md.use_neb ? (float)rg[RG_GAS_LOGZ] : 0.f;
     out[md.offs[SED_KEY_GAS_LOGU]] = md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f;
     if (md.sample_sgal) out[md.offs[SED_KEY_SIGMA_GAL]] = (float)rg[RG_SIGMA_GAL];
+    if (md.fesc_geom) out[md.offs[SED_KEY_FRAC_OBRUN]] = (float)rg[RG_FOB];
     for (int arm = 0; arm < 2; ++arm)
       for (int k = 0; k < 4; ++k)
         if ((md.floor_bits[arm] >> k) & 1)

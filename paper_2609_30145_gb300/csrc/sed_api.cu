@@ -712,6 +712,8 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     return fail(ctx, SED_EINVAL, "sigma_gal_max_kms must be in (0, 1e5) when sigma_gal is sampled");
   if (d->sfh_scheme != SED_SFH_STEP && d->sfh_scheme != SED_SFH_LINEAR)
     return fail(ctx, SED_EINVAL, "sfh_scheme must be SED_SFH_STEP or SED_SFH_LINEAR");
+  if (d->fesc_geometry < SED_FESC_NONE || d->fesc_geometry > SED_FESC_PICKET)
+    return fail(ctx, SED_EINVAL, "fesc_geometry must be SED_FESC_NONE, SED_FESC_RUNAWAY_BC or SED_FESC_PICKET");
   if (d->noise_floor_phot < 0 || d->noise_floor_phot > 15 || d->noise_floor_spec < 0 || d->noise_floor_spec > 15)
     return fail(ctx, SED_EINVAL, "noise_floor_phot / noise_floor_spec must be SED_FLOOR_* bits (0..15)");
   if (d->noise_floor_phot && d->n_filt <= 0) return fail(ctx, SED_EINVAL, "a photometric noise floor needs filters");
@@ -744,6 +746,10 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
       dv.offs[SED_KEY_LOG_ERR_SCALE_PHOT + 4 * arm + k] = o;
       o += (dv.floor_bits[arm] >> k) & 1;
     }
+  // runaway fraction of an escape geometry (Sec. frac_obrun)
+  dv.fesc_geom = d->fesc_geometry;
+  dv.offs[SED_KEY_FRAC_OBRUN] = o;
+  o += d->fesc_geometry ? 1 : 0;
   dv.n_param = o;
   dv.zf = d->zf;
   dv.Om0 = d->Om0;
@@ -762,7 +768,11 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
 
   int n_young = 0;
   while (n_young < g->n_age && g->log_age[n_young] <= d->bc_edge_log_age_yr) n_young++;
-  sed_status st = get_layout(ctx, g, n_young, d->use_nebular ? 1 : 0, &M->L);
+  // the young ages' flux below 912 A is removed from the SSP copy when the
+  // nebular emission absorbs all of it; with an escape geometry the copy keeps
+  // it and the epilogues split it off (nodes below n_lyc)
+  while (dv.n_lyc < g->n_lam && g->lam[dv.n_lyc] < LYMAN_AA) dv.n_lyc++;
+  sed_status st = get_layout(ctx, g, n_young, d->use_nebular && !d->fesc_geometry ? 1 : 0, &M->L);
   if (!st) {
     std::vector<double> tab;
     cosmo_table(d->H0, d->Om0, d->zf, COSMO_TAB, &tab);

@@ -68,6 +68,7 @@ struct RowScal {
   int nnz;          // non-zero weights of the row
   float sg_ln;      // sampled sigma_gal / c (ln-lambda units); 0 with a fixed sigma_gal
   float fl[2][4];   // noise floor {s, f_calib, f_data, j} of photometry [0] and spectrum [1]
+  float fob;        // runaway fraction f_ob (0 without an escape geometry)
 };
 
 // Cosmology and observer-frame scalars of one row (computed at the start of k_prep).
@@ -149,6 +150,8 @@ struct ModelDev {
   const float* pix_cx;
   int floor_bits[2];       // noise-floor terms on (SED_FLOOR_* bits) of photometry [0] and spectrum [1]
   int sfh_linear;          // 1: SFH key = N_T + 1 per-edge SFRs, linear scheme (App. B, Eq. tent_integral)
+  int fesc_geom;           // SED_FESC_*: escape geometry of the young light (Sec. frac_obrun)
+  int n_lyc;               // rest-frame nodes below 912 A (the ionising continuum)
   int sample_sgal;         // 1: each row carries sigma_gal (km/s), joined in quadrature per pixel
   float sgal_max_kms;      // sampled sigma_gal range [0, sgal_max_kms]
   // spectral data, normalised per pixel so that the per-pixel terms stay in FP32
@@ -239,6 +242,7 @@ enum {
   RG_BAD,   // non-zero: the row's likelihood is not finite (gradient row written as zeros)
   RG_SIGMA_GAL,   // dlnL/dsigma_gal (km/s) of a sampled sigma_gal
   RG_FLOOR,       // 8 slots: dlnL/dlog10 of the noise-floor terms, photometry then spectrum
+  RG_FOB = RG_FLOOR + 8,   // dlnL/df_ob
   RGRAD = 24
 };
 

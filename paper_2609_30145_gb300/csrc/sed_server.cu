@@ -32,9 +32,10 @@ using namespace sed;
 namespace {
 
 constexpr int SRV_LD = 1048;          // row pitch of the packed launch buffer (a multiple of 4 floats)
-// the widest parameter row: SFH and per-bin [Fe/H] (2 MAX_SFH), 9 scalars,
-// sigma_gal and 8 noise-floor terms = 2 MAX_SFH + SED_NKEYS - 2
-static_assert(SRV_LD >= 2 * MAX_SFH + SED_NKEYS - 2, "server row pitch below the widest parameter row");
+// the widest parameter row: SFH (one more column with the linear scheme) and
+// per-bin [Fe/H] (2 MAX_SFH + 1), 9 scalars, sigma_gal, 8 noise-floor terms and
+// f_ob = 2 MAX_SFH + SED_NKEYS - 2 + 1
+static_assert(SRV_LD >= 2 * MAX_SFH + SED_NKEYS - 1, "server row pitch below the widest parameter row");
 constexpr int SRV_MAX_MODELS = 4096;  // entries of the device model table
 constexpr int SRV_MAX_SLOTS = 8;
 

@@ -94,7 +94,7 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
               noise_floor_phot=orc.floor_phot, noise_floor_spec=orc.floor_spec, sfh_scheme=orc.sfh_scheme,
               bc_edge_log_age_yr=orc.bc_edge_log_age_yr, H0=orc.H0, Om0=orc.Om0,
               filters=orc.filters, phot_d=orc.phot_d, phot_sigma=orc.phot_sigma,
-              phot_mask=orc.phot_mask, phot_upper=orc.phot_upper)
+              phot_mask=orc.phot_mask, phot_upper=orc.phot_upper, fesc_geometry=orc.fesc_geometry)
     if orc.spec_lam is not None:
         kw.update(spec_lam=orc.spec_lam, spec_d=orc.spec_d if with_spec_data else None,
                   spec_sigma=orc.spec_sigma if with_spec_data else None,
@@ -191,3 +191,14 @@ def limit_regimes(orc, phot):
     d = np.asarray(orc.phot_d)[up]
     m = np.asarray(phot)[:, up]
     return int(np.sum(m > d)), int(np.sum(m <= d))
+
+
+def escape_pair(w: synth.Workload, n, seed, geometry):
+    """Parameter rows (FP32 and the same values in FP64) of a model with an
+    escape geometry (Sec. frac_obrun): the workload's draws plus the runaway
+    fraction f_ob ~ U[0.05, 0.95] in the last column."""
+    d = theta_dict(w, n, seed)
+    d["frac_obrun"] = np.random.default_rng(seed + 2000).uniform(0.05, 0.95, n)
+    th32 = oracle.pack_theta(d, w.n_sfh, w.zmode, w.sample_sigma_gal, w.floor_phot, w.floor_spec,
+                             w.sfh_scheme, geometry).astype(np.float32)
+    return th32, th32.astype(np.float64)

@@ -242,6 +242,31 @@ def test_upper_limits_grad_vs_oracle(ctx, prec):
     assert (np.abs(lnl[ok] - fwd["lnl"][ok]) / scale).max() < 1e-5
 
 
+@pytest.mark.parametrize("geometry", [1, 2])
+def test_escape_geometry_grad_vs_central_differences(ctx, geometry):
+    """The adjoint with an escape geometry (Sec. frac_obrun; runaway_bc and
+    picket): every column, d lnL / d f_ob included, against central differences
+    of the oracle's forward model on 16 rows of the photometric fit with
+    nebular emission."""
+    import dataclasses
+    w = synth.shrink(synth.WORKLOADS["phot_107x12x6000_b1024"], n_age=20, n_feh=4, n_lam=1500, n_sfh=10,
+                     batch=150)
+    key = f"fesc{geometry}"
+    if key not in _CACHE:
+        orc = dataclasses.replace(cases.oracle_for(w), fesc_geometry=geometry)
+        _CACHE[key] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE[key]
+    th32, th64 = cases.escape_pair(w, 16, seed=67, geometry=geometry)
+    lnl, g, st = gpu_grad(model, th32, "fp32")
+    ok = st == 0
+    assert ok.sum() >= 12
+    fd = orc.grad_fd(th64, h_rel=1e-7)
+    check_grad(g, fd[:, :orc.n_param], st)
+    assert np.abs(g[ok, model.offsets["frac_obrun"]]).max() > 0
+    ref = orc.eval(th64)
+    assert (np.abs(lnl[ok] - ref["lnl"][ok]) / cases.lnl_scale(orc, ref)[ok]).max() < 1e-5
+
+
 def central_differences(orc, th64, rel=1e-5):
     """d lnL / d theta by central differences of the oracle's forward model, each
     column stepped by rel x |value| (rel where the value is 0)."""

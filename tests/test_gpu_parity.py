@@ -416,6 +416,37 @@ def test_upper_limits_parity(ctx, prec):
     check(ref, got, prec, orc=orc)
 
 
+def escape_case(ctx, geometry):
+    """The paper-scale photometric fit (nebular emission, KC13 dust) on a
+    smaller grid, with an escape geometry (Sec. frac_obrun)."""
+    import dataclasses
+    w = synth.shrink(synth.WORKLOADS["phot_107x12x6000_b1024"], n_age=20, n_feh=4, n_lam=1500, n_sfh=10,
+                     batch=150)
+    key = f"fesc{geometry}"
+    if key not in _CACHE:
+        orc = dataclasses.replace(cases.oracle_for(w), fesc_geometry=geometry)
+        _CACHE[key] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    return _CACHE[key]
+
+
+@pytest.mark.parametrize("geometry", [1, 2])
+@pytest.mark.parametrize("prec", PRECS)
+def test_escape_geometry_parity(ctx, prec, geometry):
+    """runaway_bc (Eq. runaway_mix) and picket escape of the young light with
+    f_ob ~ U[0.05, 0.95] (Sec. frac_obrun): 150 rows' photometry and lnL
+    against the oracle, two rows with f_ob outside [0, 1] refused."""
+    w, orc, model = escape_case(ctx, geometry)
+    assert model.n_param == orc.n_param and model.offsets["frac_obrun"] == orc.n_param - 1
+    th32, _ = cases.escape_pair(w, w.batch, seed=66, geometry=geometry)
+    th32[5, -1] = -0.1
+    th32[9, -1] = 1.2
+    th64 = th32.astype(np.float64)
+    ref = orc.eval(th64)
+    assert ref["status"][5] != 0 and ref["status"][9] != 0
+    got = run_gpu(model, th32, prec)
+    check(ref, got, prec, orc=orc)
+
+
 def test_model_descriptor_validation(ctx):
     """sed_create_model refuses what it cannot evaluate, before anything runs:
     an unknown SFH scheme or noise-floor bits (SED_EINVAL), a floor on an arm
