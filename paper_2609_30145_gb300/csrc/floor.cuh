@@ -1,5 +1,7 @@
-// Systematic noise floor (App. sys_floor, Eq. app_noise_floor), shared by the
-// forward epilogue and its adjoint.  Each datum's variance becomes
+// Per-datum likelihood pieces shared by the forward epilogue and its adjoint:
+// the one-sided residual of a photometric upper limit (phot_resid, below) and
+// the systematic noise floor (App. sys_floor, Eq. app_noise_floor), under
+// which each datum's variance becomes
 //   sigma_eff^2 = s^2 sigma^2 + (f_calib |m|)^2 + (f_data |d|)^2 + j^2,
 // fl = {s, f_calib, f_data, j} (s = 1 and the others 0 for a term that is off).
 // The kernels work in units of the formal error: with mn = m/sigma,
