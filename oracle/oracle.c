@@ -827,6 +827,7 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
   double *Q = (double *)malloc(nsp * sizeof(double));
   double *Y = (double *)calloc(NL, sizeof(double)), *O = (double *)calloc(NL, sizeof(double));
   double *neb = (double *)calloc(NL, sizeof(double)), *lg = (double *)calloc(NL, sizeof(double));
+  double *YL = (double *)calloc(NL, sizeof(double)); /* young ionising continuum (nebular ages, < 912 A) */
   double *tbc = (double *)malloc(NL * sizeof(double)), *td = (double *)malloc(NL * sizeof(double));
   double *F = (double *)malloc(NL * sizeof(double)), *fnu = (double *)malloc(NL * sizeof(double));
   double *gfnu = (double *)calloc(NL, sizeof(double));
@@ -866,8 +867,8 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     if (W[s] == 0.0) continue;
     const double *f = g->flux + s * NL;
     for (int k = 0; k < NL; k++) {
-      if (young && has_neb && g->lam[k] < O_LYMAN) continue;
-      (young ? Y : O)[k] += W[s] * f[k];
+      if (young && has_neb && g->lam[k] < O_LYMAN) YL[k] += W[s] * f[k];
+      else (young ? Y : O)[k] += W[s] * f[k];
     }
     if (young) qy += W[s] * Q[s];
   }
@@ -888,7 +889,15 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
   }
   for (int k = 0; k < NL; k++) tbc[k] = t.tau_bc * pow(g->lam[k] / 5500.0, t.alpha_bc);
   orc_dust_tau(md->dust_law, g->lam, NL, t.tau_d, t.delta, td);
-  for (int k = 0; k < NL; k++) F[k] = exp(-td[k]) * (exp(-tbc[k]) * (Y[k] + neb[k]) + O[k]);
+  /* Eq. "app_attn" with the escape geometry of Sec. "frac_obrun" (as in orc_row) */
+  const double fob = t.fob;
+  for (int k = 0; k < NL; k++) {
+    const double ed = exp(-td[k]), eb = exp(-tbc[k]);
+    if (md->fesc_geometry == ORC_FESC_PICKET)
+      F[k] = fob * (Y[k] + YL[k]) + ed * ((1.0 - fob) * eb * (Y[k] + neb[k]) + O[k]);
+    else
+      F[k] = ed * (((1.0 - fob) * eb + fob) * (Y[k] + (1.0 - fob) * neb[k]) + fob * YL[k] + O[k]);
+  }
   double dl = cz[0], ddl = cz[2] + zp * (O_C_KMS / md->H0 * 1e6 * O_PC_CM) * inv_E(t.z, &md->Om0);
   if (dl < 10.0 * O_PC_CM) { dl = 10.0 * O_PC_CM; ddl = 0.0; }
   double scale = pow(10.0, t.logmass) * O_LSUN * zp / (4.0 * M_PI * dl * dl);
@@ -1032,18 +1041,36 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     double gl_mass = gscale * scale * log(10.0);
     gz += gscale * scale * dlns_dz;
     /* ---------------- dust and nebular (Sec. 2.4, App. C) */
-    double g_taubc = 0, g_alpha = 0, g_taud = 0, g_delta = 0, g_qy = 0, g_lu = 0, g_lz = 0;
+    double g_taubc = 0, g_alpha = 0, g_taud = 0, g_delta = 0, g_qy = 0, g_lu = 0, g_lz = 0, g_fob = 0;
     double *gY = (double *)malloc(NL * sizeof(double)), *gO = (double *)malloc(NL * sizeof(double));
+    double *gYL = (double *)malloc(NL * sizeof(double)), *gN = (double *)malloc(NL * sizeof(double));
     for (int k = 0; k < NL; k++) {
       double gF = gfnu[k] * scale;
       double ed = exp(-td[k]), eb = exp(-tbc[k]);
-      gY[k] = gF * ed * eb;
+      /* derivatives of F with respect to Y (young stellar, ionising continuum
+       * apart), YL (that continuum), O, the birth-cloud depth and the nebular
+       * continuum, under the row's escape geometry */
+      double gtbc, gtd = -gF * F[k];
       gO[k] = gF * ed;
+      if (md->fesc_geometry == ORC_FESC_PICKET) {
+        const double b = Y[k] + neb[k];
+        gY[k] = gF * (fob + ed * (1.0 - fob) * eb);
+        gYL[k] = gF * fob;
+        gtbc = -gF * ed * (1.0 - fob) * eb * b;
+        gN[k] = gF * ed * (1.0 - fob) * eb;
+        gtd = -gF * (F[k] - fob * (Y[k] + YL[k]));
+        g_fob += gF * (Y[k] + YL[k] - ed * eb * b);
+      } else {
+        const double T = (1.0 - fob) * eb + fob, av = Y[k] + (1.0 - fob) * neb[k];
+        gY[k] = gF * ed * T;
+        gYL[k] = gF * ed * fob;
+        gtbc = -gF * ed * (1.0 - fob) * eb * av;
+        gN[k] = gF * ed * T * (1.0 - fob);
+        g_fob += gF * ed * ((1.0 - eb) * av - T * neb[k] + YL[k]);
+      }
       double lp = log(g->lam[k] / 5500.0);
-      double gtbc = -gF * ed * eb * (Y[k] + neb[k]);
       g_taubc += gtbc * pow(g->lam[k] / 5500.0, t.alpha_bc);
       g_alpha += gtbc * tbc[k] * lp;
-      double gtd = -gF * F[k];
       double p = pow(g->lam[k] / 5500.0, t.delta);
       double shape, dshape;
       if (md->dust_law == 0) {
@@ -1059,7 +1086,7 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
       g_taud += gtd * shape;
       g_delta += gtd * t.tau_d * dshape;
       if (has_neb) {
-        double gneb = gY[k];
+        double gneb = gN[k];
         g_qy += gneb * pow(10.0, lg[k]);
         double glg = gneb * neb[k] * log(10.0);
         g_lu += glg * (du0 * wg0 * t00[k] + du0 * wg1 * t01[k] + du1 * wg0 * t10[k] + du1 * wg1 * t11[k]);
@@ -1073,8 +1100,8 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
       const double *f = g->flux + s * NL;
       double acc = 0.0;
       for (int k = 0; k < NL; k++) {
-        if (young && has_neb && g->lam[k] < O_LYMAN) continue;
-        acc += (young ? gY : gO)[k] * f[k];
+        if (young && has_neb && g->lam[k] < O_LYMAN) acc += gYL[k] * f[k];
+        else acc += (young ? gY : gO)[k] * f[k];
       }
       if (young) acc += g_qy * Q[s];
       gW[s] = acc;
@@ -1122,11 +1149,12 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     for (int arm = 0; arm < 2; arm++)
       for (int k = 0; k < 4; k++)
         if (t.fl_col[arm][k] >= 0) grad[t.fl_col[arm][k]] = gfl[arm][k];
-    free(gT); free(gY); free(gO);
+    if (md->fesc_geometry) grad[np - 1] = g_fob;
+    free(gT); free(gY); free(gO); free(gYL); free(gN);
   }
   if (st) for (int j = 0; j < np; j++) grad[j] = 0.0;
   free(T); free(cm); free(cp); free(A); free(zm0); free(zm1); free(wz0); free(wz1); free(dz0); free(dz1);
-  free(W); free(Q); free(Y); free(O); free(neb); free(lg); free(tbc); free(td); free(F); free(fnu);
+  free(W); free(Q); free(Y); free(O); free(neb); free(lg); free(YL); free(tbc); free(td); free(F); free(fnu);
   free(gfnu); free(gW);
   (void)cf;
   return st;

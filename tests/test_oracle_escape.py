@@ -136,3 +136,31 @@ def test_escape_fraction_outside_the_unit_interval_is_refused(base, g):
     st = o.eval(th)["status"]
     assert st[0] == 0 and st[3] == 0
     assert st[1] == st[2] == 1   # ORC_BAD_THETA
+
+
+@pytest.mark.parametrize("g", [1, 2])
+def test_analytic_gradient_against_central_differences(base, g):
+    """The oracle's hand-derived reverse pass under each geometry (d lnL / d f_ob
+    included) against central differences of its forward model."""
+    w, orc, d = base
+    o = geom(orc, g)
+    d = dict(d, frac_obrun=np.array([0.1, 0.35, 0.6, 0.9]))
+    th = oracle.pack_theta(d, w.n_sfh, w.zmode, fesc_geometry=g)
+    ga = o.grad(th)
+    assert np.all(ga["status"] == 0)
+    assert np.allclose(ga["lnl"], o.eval(th)["lnl"], rtol=1e-14, atol=0)
+    fd = o.grad_fd(th, h_rel=1e-6)
+    for r in range(th.shape[0]):
+        ref = fd[r, :o.n_param]
+        # every column within 1e-5 of the row's largest derivative (the central
+        # differences' round-off, ~1e-16 |lnL| / h, is ~1e-7 here), and the f_ob
+        # column within 1e-4 of itself
+        err = np.abs(ga["grad"][r] - ref) / np.abs(ref).max()
+        # (the redshift column's difference quotient spans kinks of the filter
+        # samples' interpolation between model nodes: 1e-4 there)
+        jz = cases.z_column(w.n_sfh, w.zmode)
+        assert err[jz] < 1e-4
+        err[jz] = 0.0
+        assert err.max() < 1e-5, (r, int(err.argmax()))
+        assert abs(ga["grad"][r, -1] - ref[-1]) < 1e-4 * abs(ref[-1])
+    assert np.abs(ga["grad"][:, -1]).min() > 0
