@@ -452,9 +452,9 @@ def test_escape_geometry_parity(ctx, prec, geometry):
 
 def test_model_descriptor_validation(ctx):
     """sed_create_model refuses what it cannot evaluate, before anything runs:
-    an unknown SFH scheme or noise-floor bits (SED_EINVAL), a floor on an arm
-    without data (SED_EINVAL), and a spectral floor together with the
-    calibration polynomial (SED_EUNSUPPORTED)."""
+    an unknown SFH scheme, noise-floor bits or escape geometry (SED_EINVAL), a
+    floor on an arm without data (SED_EINVAL), and a spectral floor together
+    with the calibration polynomial (SED_EUNSUPPORTED)."""
     from paper_2609_30145_gb300.api import SedError
     w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4,
                      n_lam=1500, n_sfh=10, n_pix=240, batch=8)
@@ -474,5 +474,9 @@ def test_model_descriptor_validation(ctx):
     refused(1, **base, noise_floor_phot=16)
     refused(1, **base, noise_floor_spec=1)                      # no spectrum
     refused(8, **base, **spec, calib_sigma=[0.1, 0.1], noise_floor_spec=2)
+    refused(1, **base, fesc_geometry=3)
+    refused(1, **base, fesc_geometry=-1)
     ok = ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **base, **spec, noise_floor_phot=9, sfh_scheme=1)
     assert ok.n_param == orc.n_param + 1 + 2
+    esc = ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **base, fesc_geometry=2)
+    assert esc.n_param == orc.n_param + 1 and esc.offsets["frac_obrun"] == orc.n_param
