@@ -279,10 +279,7 @@ class Oracle:
         return out, valid
 
     def grad(self, theta, nthreads=0):
-        """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])
-        (step SFH scheme; grad_fd serves the linear one)."""
-        if self.sfh_scheme != 0:
-            raise NotImplementedError("the analytic gradient follows the step scheme; use grad_fd")
+        """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
         n, ld = th.shape
         out = np.zeros((n, ld))

@@ -267,6 +267,95 @@ static void linear_bin_masses(const orc_grid *g, double T0, double T1, double ps
     for (int a = 0; a < NA; a++) A[a] *= target / s;
 }
 
+/* One piece of the linear scheme's bin: the integral over [x0, x1] of the rate
+ * alpha + beta t against the weight of its kind (0: 1, the end pieces; 1: the
+ * tent of node j, (l1 - ln t)/(l1 - l0); 2: the tent of node j + 1,
+ * (ln t - l0)/(l1 - l0)), with l0 = ln t_j, l1 = ln t_{j+1}. */
+static double lin_piece(double alpha, double beta, double x0, double x1, int kind, double l0, double l1) {
+  double mass = alpha * (x1 - x0) + 0.5 * beta * (x1 * x1 - x0 * x0);
+  if (kind == 0) return mass;
+  double mlog = alpha * (x1 * log(x1) - x1 - x0 * log(x0) + x0) +
+                beta * (0.5 * x1 * x1 * log(x1) - 0.25 * x1 * x1 - 0.5 * x0 * x0 * log(x0) + 0.25 * x0 * x0);
+  double d = l1 - l0;
+  return kind == 1 ? (l1 * mass - mlog) / d : (mlog - l0 * mass) / d;
+}
+
+static double lin_weight(double x, int kind, double l0, double l1) {
+  if (kind == 0) return 1.0;
+  return kind == 1 ? (l1 - log(x)) / (l1 - l0) : (log(x) - l0) / (l1 - l0);
+}
+
+/* Reverse of linear_bin_masses.  Given gA[a] = dL/dA[a] for the bin's node
+ * masses, returns d4 = dL/d{psi0, psi1, T0, T1}.  Each piece is linear in the
+ * rate: its derivative in psi0 (psi1) is the same piece for the unit rate
+ * falling from 1 to 0 (rising from 0 to 1) across the bin.  An edge moves a
+ * piece through the integral's limit (minus or plus the integrand there, when
+ * the piece starts or ends at that edge) and through the rate itself:
+ * dpsi/dT0 = c (t - T1) and dpsi/dT1 = -c (t - T0), c = (psi1 - psi0)/dT^2,
+ * both again linear rates.  A clipped piece carries no derivative.  The scale
+ * to the trapezoidal mass enters by the quotient rule. */
+static void linear_bin_grad(const orc_grid *g, double T0, double T1, double psi0, double psi1,
+                            const double *gA, double *d4) {
+  int NA = g->n_age;
+  d4[0] = d4[1] = d4[2] = d4[3] = 0.0;
+  double dT = T1 - T0;
+  if (!(dT > 0.0)) return;
+  double c = (psi1 - psi0) / (dT * dT);
+  /* rates (alpha, beta): the row's psi, d/dpsi0, d/dpsi1, d/dT0, d/dT1 */
+  double rb[5] = {(psi1 - psi0) / dT, -1.0 / dT, 1.0 / dT, c, -c};
+  double ra[5] = {psi0 - rb[0] * T0, 1.0 - rb[1] * T0, -rb[2] * T0, -c * T1, c * T0};
+  double *raw = (double *)calloc(NA, sizeof(double));
+  double *dr = (double *)calloc((size_t)4 * NA, sizeof(double));
+  double t_first = pow(10.0, g->log_age_yr[0]), t_last = pow(10.0, g->log_age_yr[NA - 1]);
+  /* the pieces in the forward's order: (node, kind, x0, x1, l0, l1) */
+  for (int j = -1; j < NA; j++) {
+    int nodes[2], kinds[2], np_ = 0;
+    double x0, x1, l0 = 0.0, l1 = 0.0;
+    if (j == -1) {                 /* below the youngest node */
+      if (!(T0 < t_first)) continue;
+      x0 = T0; x1 = T1 < t_first ? T1 : t_first;
+      nodes[0] = 0; kinds[0] = 0; np_ = 1;
+    } else if (j == NA - 1) {      /* above the oldest node */
+      if (!(T1 > t_last)) continue;
+      x0 = T0 > t_last ? T0 : t_last; x1 = T1;
+      nodes[0] = NA - 1; kinds[0] = 0; np_ = 1;
+    } else {
+      double tj = pow(10.0, g->log_age_yr[j]), tj1 = pow(10.0, g->log_age_yr[j + 1]);
+      x0 = T0 > tj ? T0 : tj; x1 = T1 < tj1 ? T1 : tj1;
+      if (!(x1 > x0)) continue;
+      l0 = log(tj); l1 = log(tj1);
+      nodes[0] = j; kinds[0] = 1; nodes[1] = j + 1; kinds[1] = 2; np_ = 2;
+    }
+    if (np_ == 1 && !(x1 > x0)) continue;
+    for (int q = 0; q < np_; q++) {
+      int a = nodes[q], kd = kinds[q];
+      double v = lin_piece(ra[0], rb[0], x0, x1, kd, l0, l1);
+      if (!(v > 0.0)) continue;   /* clipped */
+      raw[a] += v;
+      dr[4 * a + 0] += lin_piece(ra[1], rb[1], x0, x1, kd, l0, l1);
+      dr[4 * a + 1] += lin_piece(ra[2], rb[2], x0, x1, kd, l0, l1);
+      dr[4 * a + 2] += lin_piece(ra[3], rb[3], x0, x1, kd, l0, l1) - (x0 == T0 ? psi0 * lin_weight(T0, kd, l0, l1) : 0.0);
+      dr[4 * a + 3] += lin_piece(ra[4], rb[4], x0, x1, kd, l0, l1) + (x1 == T1 ? psi1 * lin_weight(T1, kd, l0, l1) : 0.0);
+    }
+  }
+  double sum = 0.0, ds[4] = {0, 0, 0, 0};
+  for (int a = 0; a < NA; a++) {
+    sum += raw[a];
+    for (int p = 0; p < 4; p++) ds[p] += dr[4 * a + p];
+  }
+  double target = 0.5 * (psi0 + psi1) * dT, dtg[4] = {0, 0, 0, 0};
+  if (target > 0.0) {
+    dtg[0] = 0.5 * dT; dtg[1] = 0.5 * dT; dtg[2] = -0.5 * (psi0 + psi1); dtg[3] = 0.5 * (psi0 + psi1);
+  } else {
+    target = 0.0;
+  }
+  if (sum > 0.0)
+    for (int a = 0; a < NA; a++)
+      for (int p = 0; p < 4; p++)
+        d4[p] += gA[a] * (dr[4 * a + p] * target / sum + raw[a] * (dtg[p] * sum - target * ds[p]) / (sum * sum));
+  free(raw); free(dr);
+}
+
 int orc_weights(const orc_grid *g, const orc_model *md, const double *theta, double *W) {
   double tmax;
   int st = theta_status(md, theta, &tmax, NULL);
@@ -846,12 +935,19 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
   for (int i = 0; i < NT; i++) {
     double dT = T[i + 1] - T[i];
     bracket_d(g->feh, NZ, t.zeta[md->zmode == 0 ? i : 0], &zm0[i], &wz0[i], &dz0[i], &zm1[i], &wz1[i], &dz1[i]);
+    if (md->sfh_scheme == 1) linear_bin_masses(g, T[i], T[i + 1], t.m[i], t.m[i + 1], A + (size_t)i * NA);
     for (int a = 0; a < NA; a++) {
-      double lo = T[i] > cm[a] ? T[i] : cm[a];
-      double hi = T[i + 1] < cp[a] ? T[i + 1] : cp[a];
-      if (hi - lo <= 0.0) continue;
-      double Aia = t.m[i] * (hi - lo) / dT;
-      A[(size_t)i * NA + a] = Aia;
+      double Aia;
+      if (md->sfh_scheme == 1) {
+        Aia = A[(size_t)i * NA + a];
+        if (Aia == 0.0) continue;
+      } else {
+        double lo = T[i] > cm[a] ? T[i] : cm[a];
+        double hi = T[i + 1] < cp[a] ? T[i + 1] : cp[a];
+        if (hi - lo <= 0.0) continue;
+        Aia = t.m[i] * (hi - lo) / dT;
+        A[(size_t)i * NA + a] = Aia;
+      }
       W[((size_t)an0 * NZ + zm0[i]) * NA + a] += Aia * wz0[i] * wa0;
       W[((size_t)an0 * NZ + zm1[i]) * NA + a] += Aia * wz1[i] * wa0;
       W[((size_t)an1 * NZ + zm0[i]) * NA + a] += Aia * wz0[i] * wa1;
@@ -1110,9 +1206,29 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
     double *gT = (double *)calloc(NT + 1, sizeof(double));
     double g_afe = 0.0;
     int nz = md->zmode == 0 ? NT : 1;
-    const int offz = NT, offs = NT + nz;
+    const int offz = sfh_cols(md), offs = offz + nz;
+    double *gAl = (double *)malloc(NA * sizeof(double));
     for (int i = 0; i < NT; i++) {
       double dT = T[i + 1] - T[i];
+      if (md->sfh_scheme == 1) {   /* linear scheme: node masses from the edge rates */
+        for (int a = 0; a < NA; a++) {
+          double Aia = A[(size_t)i * NA + a];
+          double g00 = gW[((size_t)an0 * NZ + zm0[i]) * NA + a], g01 = gW[((size_t)an0 * NZ + zm1[i]) * NA + a];
+          double g10 = gW[((size_t)an1 * NZ + zm0[i]) * NA + a], g11 = gW[((size_t)an1 * NZ + zm1[i]) * NA + a];
+          gAl[a] = g00 * wz0[i] * wa0 + g01 * wz1[i] * wa0 + g10 * wz0[i] * wa1 + g11 * wz1[i] * wa1;
+          if (Aia == 0.0) continue;
+          grad[offz + (md->zmode == 0 ? i : 0)] +=
+              Aia * (g00 * dz0[i] * wa0 + g01 * dz1[i] * wa0 + g10 * dz0[i] * wa1 + g11 * dz1[i] * wa1);
+          g_afe += Aia * (g00 * wz0[i] * da0 + g01 * wz1[i] * da0 + g10 * wz0[i] * da1 + g11 * wz1[i] * da1);
+        }
+        double d4[4];
+        linear_bin_grad(g, T[i], T[i + 1], t.m[i], t.m[i + 1], gAl, d4);
+        grad[i] += d4[0];
+        grad[i + 1] += d4[1];
+        gT[i] += d4[2];
+        gT[i + 1] += d4[3];
+        continue;
+      }
       for (int a = 0; a < NA; a++) {
         double Aia = A[(size_t)i * NA + a];
         double lo = T[i] > cm[a] ? T[i] : cm[a];
@@ -1150,7 +1266,7 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
       for (int k = 0; k < 4; k++)
         if (t.fl_col[arm][k] >= 0) grad[t.fl_col[arm][k]] = gfl[arm][k];
     if (md->fesc_geometry) grad[np - 1] = g_fob;
-    free(gT); free(gY); free(gO); free(gYL); free(gN);
+    free(gT); free(gY); free(gO); free(gYL); free(gN); free(gAl);
   }
   if (st) for (int j = 0; j < np; j++) grad[j] = 0.0;
   free(T); free(cm); free(cp); free(A); free(zm0); free(zm1); free(wz0); free(wz1); free(dz0); free(dz1);

@@ -148,3 +148,47 @@ def test_layout_has_one_more_sfh_column_and_forward_runs():
     th = np.stack([row(w, orc, p, z=1.0 + 0.5 * k) for k, p in enumerate(psi)])
     r = orc.eval(th)
     assert np.all(r["status"] == 0) and np.all(np.isfinite(r["lnl"]))
+
+
+@pytest.mark.parametrize("clip", [False, True])
+@pytest.mark.parametrize("zmode", [0, 1])
+def test_analytic_gradient_against_central_differences(zmode, clip):
+    """The oracle's hand-derived reverse pass of the linear scheme (each edge
+    rate through two bins' tent shares and their scale to the trapezoidal
+    mass, each edge's lookback time through T_max) against central differences
+    of its forward model, every column.  With clip, every third edge rate is
+    negative, so pieces are clipped and the scale to the trapezoidal mass
+    differs from 1 (without clipping the shares sum to the trapezoid exactly
+    and the scale's derivative vanishes)."""
+    import dataclasses
+    w = dataclasses.replace(synth.WORKLOADS["tiny_phot_16x4x512"], sfh_scheme=1, zmode=zmode)
+    orc = cases.oracle_for(w)
+    th = cases.theta_rows(w, 6, seed=31)
+    if clip:
+        th[:, 1:w.n_sfh + 1:3] *= -0.4
+    ga = orc.grad(th)
+    ok = ga["status"] == 0
+    assert ok.sum() >= 4
+    assert np.allclose(ga["lnl"][ok], orc.eval(th)["lnl"][ok], rtol=1e-14, atol=0)
+    # central differences with steps relative to each value (edge SFRs are
+    # ~1e-10 Msun/yr, far below the unit floor of the oracle's own grad_fd)
+    fd = np.zeros_like(th)
+    for j in range(th.shape[1]):
+        h = np.where(th[:, j] == 0, 1e-6, 1e-6 * np.abs(th[:, j]))
+        a, b = th.copy(), th.copy()
+        a[:, j] += h
+        b[:, j] -= h
+        fd[:, j] = (orc.eval(a)["lnl"] - orc.eval(b)["lnl"]) / (2 * h)
+    jz = cases.z_column(w.n_sfh, w.zmode, 1)
+    for r in np.nonzero(ok)[0]:
+        ref = fd[r, :orc.n_param]
+        err = np.abs(ga["grad"][r] - ref) / np.abs(ref).max()
+        # (the redshift column's difference quotient spans kinks of the filter
+        # samples' interpolation between model nodes: 1e-4 there)
+        assert err[jz] < 1e-4
+        err[jz] = 0.0
+        assert err.max() < 1e-5, (r, int(err.argmax()))
+        # the edge rates: each within 1e-4 of itself where it is not tiny
+        js = np.arange(w.n_sfh + 1)
+        big = np.abs(ref[js]) > 1e-3 * np.abs(ref[js]).max()
+        assert np.all(np.abs(ga["grad"][r, js][big] - ref[js][big]) < 1e-4 * np.abs(ref[js][big]))
