@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--serve-threads", type=int, default=48)
     ap.add_argument("--serve-budget-mb", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-config accuracy and throughput leg (tiny, paper-scale photometric at 1024 "
+                         "and 4096 rows, spectro-photometric [a/Fe], serving mix)")
+    ap.add_argument("--profile-case", default=None, choices=["phot", "specphot", "calib"],
+                    help="run one small case of the hot path for an ncu capture and exit (no timing, no JSON)")
     return ap.parse_args()
 
 
@@ -183,6 +188,57 @@ def build_workload(wname, ctx, seed_rows, device):
     return w, grid, filt, model, theta, (pd, np.abs(ph) / 20.0)
 
 
+# --------------------------------------------------------------------------- roofline
+def contraction_peak(prec, pk, pk_kind):
+    """Dense peak of the contraction's instruction kind.  The contraction is
+    timed per launch inside a ~0.1 ms step, so the burst figure applies; TF32
+    and FP8 take the measured BF16 burst peak times the nominal dense ratio."""
+    bf = pk["bf16_tflops"]
+    if prec == "fp32":
+        return bf * TF32_PER_BF16, f"TF32 dense = burst BF16 {bf} x {TF32_PER_BF16:.3f} (nominal ratio), of {pk_kind}"
+    if prec == "bf16":
+        return bf, f"burst BF16 dense, of {pk_kind}"
+    if prec == "fp8":
+        return bf * 2.0, f"FP8 dense = burst BF16 {bf} x 2 (nominal ratio), of {pk_kind}"
+    return 152 * 128 * 2 * 2.07e9 / 1e12, "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts)"
+
+
+def stage_roofline(ctx, fn, stream, flush, prec, B, pk, pk_kind, reps):
+    """Per-kernel times of `reps` direct calls (the library's events), and the
+    contraction's algorithmic and issued rates against its dense peak; the
+    epilogue's algorithmic bytes (Y and O per row) against measured HBM."""
+    import torch
+
+    ctx.set_profiling(True)
+    stats = []
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda._sleep(200000)
+            fn(stream)
+            stats.append(ctx.last_stats(stream))
+    ctx.set_profiling(False)
+    c_ms = statistics.mean(st["ms_contract"] for st in stats)
+    e_ms = statistics.mean(st["ms_epilogue"] for st in stats)
+    p_ms = statistics.mean(st["ms_prep"] for st in stats)
+    nnz, n_lam = stats[-1]["nnz_w"], stats[-1]["n_lam"]
+    issued = statistics.mean(st["issued_flop"] for st in stats)
+    alg_flop = 2.0 * nnz * n_lam
+    peak_tf, note = contraction_peak(prec, pk, pk_kind)
+    achieved = alg_flop / (c_ms * 1e-3) / 1e12
+    epi_bytes = B * n_lam * 8.0 + B * 8
+    return {"kernel": "k_contract_tc" if prec != "fp32_simt" else "k_contract_simt",
+            "bound": "tensor" if prec != "fp32_simt" else "alu", "achieved": round(achieved, 3),
+            "peak": round(peak_tf, 1), "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4),
+            "peak_note": note, "algorithmic_flop_per_launch": alg_flop, "nnz_w_per_launch": nnz,
+            "issued_tflops": round(issued / (c_ms * 1e-3) / 1e12, 2),
+            "issued_frac": round(issued / (c_ms * 1e-3) / 1e12 / peak_tf, 4),
+            "contract_ms": round(c_ms, 4), "prep_ms": round(p_ms, 4), "epilogue_ms": round(e_ms, 4),
+            "epilogue_hbm": {"bound": "hbm", "achieved_gbs": round(epi_bytes / (e_ms * 1e-3) / 1e9, 1),
+                             "peak": pk["hbm_gbs"], "frac": round(epi_bytes / (e_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
+                             "bytes_per_launch": epi_bytes}}
+
+
 # --------------------------------------------------------------------------- GPU leg
 def capture_step(fn, stream, warm=3):
     """One step (a library call on `stream`) as a CUDA graph, after warm-up calls
@@ -294,59 +350,32 @@ def run_ours(args):
         total_ms = max_over_ranks(total_ms, device=device)
     ms_step = total_ms / args.steps
     value = world * B * args.steps / (total_ms * 1e-3)
+    comm = None
+    if dist:
+        # the one exchange of the row-sharded path: every rank's lnL rows to all
+        # ranks (outside the timed region), and a check that they all arrived
+        from paper_2609_30145_gb300.shard import gather_rows
+        full = gather_rows(lnl, world * B, world)
+        torch.cuda.synchronize()
+        comm = {"backend": dist.get_backend(), "world_size": dist.get_world_size(),
+                "gathered_rows": int(full.shape[0]),
+                "gathered_ok": bool(full.shape[0] == world * B and torch.equal(full[rank * B:(rank + 1) * B], lnl))}
 
     # per-kernel times: direct calls with the library's per-stage events on the
     # stream; a ~0.1 ms spin kernel ahead of each call lets the host enqueue all
     # of the call's kernels before the GPU reaches them (no host gaps between them)
-    ctx.set_profiling(True)
-    stats = []
-    with torch.cuda.stream(main_stream):
-        for _ in range(max(5, args.steps // 2)):
-            flush.zero_()
-            torch.cuda._sleep(200000)
-            step_fn(prec)(main_stream)
-            stats.append(ctx.last_stats(main_stream))
-    ctx.set_profiling(False)
-    contract_ms = [s["ms_contract"] for s in stats]
-    epi_ms = [s["ms_epilogue"] for s in stats]
-    prep_ms = [s["ms_prep"] for s in stats]
-    nnz = stats[-1]["nnz_w"]
-    n_lam = stats[-1]["n_lam"]
-    kpad = stats[-1]["dense_k"]
-    ldn = stats[-1]["ldn"]
-    c_ms = statistics.mean(contract_ms)
-    alg_flop = 2.0 * nnz * n_lam
     pk, pk_kind = peaks()
-    issued = statistics.mean(s["issued_flop"] for s in stats)
-    if prec == "fp32":
-        peak_tf = pk["bf16_tflops_sustained"] * TF32_PER_BF16
-        peak_note = (f"TF32 dense peak = sustained BF16 {pk['bf16_tflops_sustained']} x {TF32_PER_BF16:.3f} "
-                     f"(nominal ratio), of {pk_kind}")
-    elif prec == "bf16":
-        peak_tf = pk["bf16_tflops_sustained"]
-        peak_note = f"sustained BF16 dense peak, of {pk_kind}"
-    elif prec == "fp8":
-        peak_tf = pk["bf16_tflops_sustained"] * 2.0
-        peak_note = f"FP8 dense peak = sustained BF16 {pk['bf16_tflops_sustained']} x 2 (nominal ratio), of {pk_kind}"
-    else:
-        peak_tf = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 FFMA: SMs x lanes x 2 x max clock
-        peak_note = "FP32 FFMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz"
-    achieved = alg_flop / (c_ms * 1e-3) / 1e12
-    e_ms = statistics.mean(epi_ms)
-    epi_bytes = B * n_lam * 8.0 + B * 8
-    roof = {"kernel": "k_contract_tc" if prec != "fp32_simt" else "k_contract_simt",
-            "bound": "tensor" if prec != "fp32_simt" else "alu", "achieved": round(achieved, 3),
-            "peak": round(peak_tf, 1), "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4),
-            "traffic": read_traffic(), "peak_note": peak_note,
-            "algorithmic_flop_per_launch": alg_flop, "nnz_w_per_launch": nnz,
-            "issued_tensor_tflops": round(issued / (c_ms * 1e-3) / 1e12, 2),
-            "issued_frac": round(issued / (c_ms * 1e-3) / 1e12 / peak_tf, 4),
-            "contract_ms": round(c_ms, 4), "prep_ms": round(statistics.mean(prep_ms), 4),
-            "epilogue_ms": round(e_ms, 4),
-            "epilogue_hbm": {"bound": "hbm", "achieved_gbs": round(epi_bytes / (e_ms * 1e-3) / 1e9, 1),
-                             "peak": pk["hbm_gbs"],
-                             "frac": round(epi_bytes / (e_ms * 1e-3) / 1e9 / pk["hbm_gbs"], 4),
-                             "bytes_per_launch": epi_bytes}}
+    by_prec = {p: stage_roofline(ctx, step_fn(p), main_stream, flush, p, B, pk, pk_kind,
+                                 max(5, args.steps // 2)) for p in PRECS}
+    roof = dict(by_prec[prec])
+    roof["traffic"] = read_traffic() if prec == "fp32" else None
+    roof["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of one k_contract_tc launch "
+                            "(3xTF32) from the ncu capture in profiles/k_contract_tc_phot_b1024.md, taken on "
+                            "the current kernel source (null when the source changed since)")
+    roof["stage_times_note"] = ("contract/prep/epilogue times come from direct calls with the library's "
+                                "CUDA events around each kernel, so they include the launch gaps that the "
+                                "graph-replayed step (ms_per_step) does not have")
+    roof["other_precisions"] = {p: v for p, v in by_prec.items() if p != prec}
 
     p50 = float(np.percentile(ms, 50))
     p99 = float(np.percentile(ms, 99))
@@ -419,7 +448,8 @@ def run_ours(args):
                       "precision": PREC_NOTE[prec],
                       "step": "one sed_loglike call over the batch (4 kernels: row order, prep, contraction, epilogue), replayed as a CUDA graph",
                       "l2": "flushed before every timed step (256 MiB memset, outside the timing)",
-                      "parallelism": f"replicas x{world} (independent batches per GPU)"},
+                      "parallelism": f"replicas x{world} (independent batches per GPU)",
+                      "comm": comm},
            "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "what": "device time of one batch step"},
            "variants": variants, "roofline": roof, "clocks": ck, "e2e": e2e,
            "gpu_launches": 4 * args.steps}
@@ -427,6 +457,8 @@ def run_ours(args):
         out["gradient"] = bench_gradient(ctx, device, flush, args)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = bench_serving(ctx, device, args)
+    if rank == 0 and world == 1 and not args.no_configs:
+        out["configs"] = bench_configs(ctx, device, flush, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["accuracy_vs_fp64_oracle"] = cpu_baseline(w, grid, filt, data, theta, gpu_res,
                                                                             args.cpu_seconds)
@@ -516,6 +548,158 @@ def bench_gradient(ctx, device, flush, args):
         res[p]["stages_ms"] = {k: round(statistics.mean(st[f] for st in stats), 4) for k, f in
                                (("prep", "ms_prep"), ("contract", "ms_contract"), ("adjoint_epilogue", "ms_epilogue"),
                                 ("dw", "ms_dw"), ("prep_bwd", "ms_prep_bwd"))}
+    return res
+
+
+# --------------------------------------------------------------------------- per-config accuracy and speed
+CONFIGS = [  # (label, workload, rows on the GPU, rows sampled for the oracle)
+    ("C1", "tiny_phot_16x4x512", 64, 64),
+    ("C2", "phot_107x12x6000_b1024", 1024, 256),
+    ("C3", "specphot_afe_107x12x5x6000_b2048", 2048, 128),
+    ("C4", "phot_107x12x6000_b4096", 4096, 256),
+]
+
+
+def _q(x):
+    x = np.asarray(x, dtype=np.float64)
+    return {"median": float(np.median(x)), "p99": float(np.percentile(x, 99)), "max": float(x.max())}
+
+
+def norm_const(orc):
+    """C = -1/2 sum ln(2 pi sigma^2) over the data in the likelihood (lnL = -chi2/2 + C)."""
+    c = 0.0
+    for sig, mask in ((orc.phot_sigma, orc.phot_mask), (orc.spec_sigma, orc.spec_mask)):
+        if sig is None or len(sig) == 0:
+            continue
+        m = np.ones(len(sig), bool) if mask is None else np.asarray(mask).astype(bool)
+        c += -0.5 * np.sum(np.log(2 * np.pi * np.asarray(sig)[m] ** 2))
+    return c
+
+
+def err_stats(orc, ref, lnl, status, phot=None, spec=None):
+    """Errors of GPU results against the FP64 oracle on the same rows: per datum
+    relative flux error (floored at 1e-6 of the row's brightest datum), lnL
+    error over the magnitude of its terms, absolute lnL error (what a sampler
+    feels), relative error of chi2 alone (the normalisation C is the same on
+    both sides and can hide chi2 errors), and the plain relative lnL error."""
+    ok = ref["status"] == 0
+    out = {"rows": int(ok.sum()), "status_match": bool(np.array_equal(status, ref["status"]))}
+    fe = []
+    for got, key in ((phot, "phot"), (spec, "spec")):
+        if got is None or ref[key].size == 0:
+            continue
+        r, g = ref[key][ok], got[ok]
+        floor = 1e-6 * np.abs(r).max(axis=1, keepdims=True)
+        fe.append((np.abs(g - r) / np.maximum(np.abs(r), floor)).ravel())
+    if fe:
+        out["flux_rel_err"] = _q(np.concatenate(fe))
+    c = norm_const(orc)
+    lr = ref["lnl"][ok]
+    d = np.abs(lnl[ok] - lr)
+    chi2 = 2.0 * (c - lr)
+    out["lnl_err_over_term_scale"] = _q(d / np.maximum(np.abs(lr), chi2 / 2 + abs(c)))
+    out["lnl_abs_err"] = _q(d)
+    out["chi2_rel_err"] = _q(2.0 * d / np.maximum(chi2, 1e-300))
+    out["lnl_rel_err"] = _q(d / np.abs(lr))
+    return out
+
+
+def near_truth_rows(w, n, seed):
+    """Rows around the row the mock data were made from (what a sampler's live
+    points look like late in a run): its SFH masses times 1 + 5% noise and
+    small Gaussian steps in the scalar keys (0.02 dex in metallicity, 0.01 dex
+    in mass, 0.002 in redshift, 0.02 in the dust and gas keys), in the
+    oracle's layout."""
+    import oracle
+    import synth
+    from tests import cases
+
+    d = synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99)
+    d["zred"][:] = min(2.0, w.zf * 0.5)
+    rng = np.random.default_rng(seed)
+    out = {}
+    for k, v in d.items():
+        v = np.repeat(np.asarray(v, dtype=np.float64), n, axis=0)
+        step = {"sfh": None, "logzsol": 0.02, "afe": 0.02, "logmass": 0.01, "zred": 0.002, "tau_pow": 0.02,
+                "diffuse_tau_kc": 0.02, "diffuse_dust_index": 0.02, "gas_logz": 0.02, "gas_logu": 0.02}.get(k, 0.0)
+        if k == "sfh":
+            v = v * (1.0 + 0.05 * rng.standard_normal(v.shape))
+        elif step and np.ptp(np.atleast_1d(w.ranges.get(k, 0.0))) > 0:
+            v = v + step * rng.standard_normal(v.shape)
+        out[k] = v
+    out["tau_pow"] = np.clip(out["tau_pow"], 0.0, None)
+    out["diffuse_tau_kc"] = np.clip(out["diffuse_tau_kc"], 0.0, None)
+    th = oracle.pack_theta(out, w.n_sfh, w.zmode).astype(np.float32)
+    assert th.shape[1] == cases.z_column(w.n_sfh, w.zmode) + 7
+    return th
+
+
+def bench_configs(ctx, device, flush, args):
+    """Every stated config on the GPU at its batch, in every precision: graph-
+    replayed sed_loglike throughput, and errors against the FP64 oracle on
+    sampled rows (C3 also the gradient against the oracle's analytic one)."""
+    import torch
+    import synth
+    from tests import cases
+
+    res = {}
+    s = torch.cuda.Stream(device=device)
+    for label, wname, n, n_orc in CONFIGS:
+        w = synth.WORKLOADS[wname]
+        orc = cases.oracle_for(w)
+        model = cases.gpu_model_for(ctx, orc, w)
+        th32, th64 = cases.theta_pair(w, n, seed=4)
+        t = torch.from_numpy(th32).to(device)
+        rows = np.arange(n) if n_orc >= n else np.sort(np.random.default_rng(11).choice(n, n_orc, replace=False))
+        t0 = time.perf_counter()
+        ref = orc.eval(th64[rows], nthreads=os.cpu_count() or 1)
+        t_orc = time.perf_counter() - t0
+        th_near = near_truth_rows(w, min(n, 128), seed=13)
+        ref_near = orc.eval(th_near.astype(np.float64), nthreads=os.cpu_count() or 1)
+        chi2_near = 2.0 * (norm_const(orc) - ref_near["lnl"])
+        n_data = len(orc.phot_sigma) + (0 if orc.spec_sigma is None else len(orc.spec_sigma))
+        lnl = torch.empty(n, dtype=torch.float64, device=device)
+        stt = torch.empty(n, dtype=torch.int32, device=device)
+        block = {"workload": w.name, "rows": n, "oracle_rows": int(rows.size),
+                 "oracle_s": round(t_orc, 2), "precisions": {}}
+        for p in PRECS:
+            g = capture_step(lambda st, p=p: model.loglike(t, p, stream=st, out=lnl, status=stt), s)
+            ms = time_replays(g, s, max(10, args.steps // 2), flush)
+            l, st = model.loglike(t, p, stream=s)
+            ph, sp = model.forward(t, p, stream=s)
+            torch.cuda.synchronize()
+            l, st = l.cpu().numpy()[rows], st.cpu().numpy()[rows]
+            ph = None if ph is None else ph.cpu().numpy()[rows]
+            sp = None if sp is None else sp.cpu().numpy()[rows]
+            e = err_stats(orc, ref, l, st, ph, sp)
+            # absolute lnL error where a sampler spends its late iterations
+            tn = torch.from_numpy(th_near).to(device)
+            ln, stn = model.loglike(tn, p, stream=s)
+            torch.cuda.synchronize()
+            ln, stn = ln.cpu().numpy(), stn.cpu().numpy()
+            okn = (stn == 0) & (ref_near["status"] == 0)
+            dn = np.abs(ln[okn] - ref_near["lnl"][okn])
+            e["near_truth"] = {"rows": int(okn.sum()), "lnl_abs_err": _q(dn),
+                               "chi2_per_datum_median": float(np.median(chi2_near[okn]) / n_data)}
+            e["evals_per_s"] = round(n * len(ms) / (sum(ms) * 1e-3), 1)
+            e["ms_per_step"] = round(sum(ms) / len(ms), 4)
+            block["precisions"][p] = e
+            del g
+        if label == "C3":
+            gr = [0, 1, n - 1] + list(np.random.default_rng(12).choice(n, 9, replace=False))
+            gr = np.array(sorted(set(int(x) for x in gr)))
+            _, gg, gst = model.loglike_grad(t, "fp32", stream=s)
+            torch.cuda.synchronize()
+            gg, gst = gg.cpu().numpy()[gr], gst.cpu().numpy()[gr]
+            gref = orc.grad(th64[gr])["grad"]
+            ok = gst == 0
+            e = [np.max(np.abs(gg[i, :gref.shape[1]] - gref[i]) /
+                        np.maximum(np.abs(gref[i]), 1e-3 * np.abs(gref[i]).max())) for i in np.nonzero(ok)[0]]
+            block["gradient_fp32"] = {"rows": int(ok.sum()), "rel_err_max": float(max(e)),
+                                      "what": "|g - g_oracle| / max(|g_oracle|, 1e-3 max_j |g_oracle_j|) over "
+                                              "every column of each sampled row, worst row"}
+        res[label] = block
+        model.close()
     return res
 
 
@@ -663,18 +847,71 @@ def torch_from(a, device):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
 
 
+def kernel_source_sha16(path="paper_2609_30145_gb300/csrc/k_contract_tc.cu"):
+    import hashlib
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def read_traffic():
-    """DRAM bytes per launch of the contraction from the committed ncu summary, if any."""
+    """DRAM bytes per launch of the 3xTF32 contraction from the committed ncu
+    summary, if it was taken on the current kernel source (its
+    kernel_source_sha16 line), else None."""
     p = os.path.join(ROOT, "profiles", "k_contract_tc_phot_b1024.md")
     if not os.path.exists(p):
         return None
+    vals = {}
     for line in open(p):
-        if line.startswith("traffic_bytes_per_launch:"):
-            try:
-                return float(line.split(":")[1])
-            except ValueError:
-                return None
-    return None
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha16") != kernel_source_sha16():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------- ncu cases
+def profile_case(which):
+    """Small cases of the hot path for ncu captures (the commands in profiles/).
+
+    phot: the paper-scale photometric batch (107 x 12 x 6000 grid, 120 bins,
+    20 filters, 1024 rows): three FP32 (3xTF32) sed_loglike calls, then one
+    BF16, one FP8 and one FP32-SIMT call, then one FP32 sed_loglike_grad;
+    about 1 GB of device memory.  Launch order of k_contract_tc: 3xTF32 x3,
+    BF16, FP8, adjoint.
+    specphot: the [a/Fe] spectro-photometric workload (107 x 12 x 5 x 6000
+    grid, 1500-pixel spectrum + 20 filters) at 512 rows: one FP32 sed_loglike,
+    then two FP32 sed_loglike_grad calls.
+    calib: the same with the marginalised 13-term calibration polynomial."""
+    import torch
+    import synth
+
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2609_30145_gb300 import Context
+
+    ctx = Context(0)
+    if which == "phot":
+        w, _, _, m, theta, _ = build_workload(WORKLOAD, ctx, 5, device)
+        t = torch.from_numpy(theta).to(device)
+        for prec in ["fp32", "fp32", "fp32", "bf16", "fp8", "fp32_simt"]:
+            m.loglike(t, prec)
+        m.loglike_grad(t, "fp32")
+    else:
+        wname = CALIB_WORKLOAD if which == "calib" else GRAD_WORKLOAD
+        w, _, _, m, theta, _ = build_workload(wname, ctx, 5, device)
+        t = torch.from_numpy(theta[:512]).to(device)
+        m.loglike(t, "fp32")
+        m.loglike_grad(t, "fp32")
+        m.loglike_grad(t, "fp32")
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ok")
 
 
 # --------------------------------------------------------------------------- CPU baseline / reference
@@ -775,8 +1012,28 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def relaunch_under_torchrun(n):
+    """`bench.py --gpus N` started as a single process: start it again under
+    torchrun with one rank per GPU (the driver's own N > 1 launch sets
+    WORLD_SIZE and never comes here)."""
+    import socket
+
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_under_torchrun(args.gpus))
     if args.impl == "reference":
         run_reference(args)
     else:

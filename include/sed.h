@@ -135,7 +135,21 @@ typedef struct {
   int neb_n_logu, neb_n_logz;      /* nebular template axes (0 = no nebular) */
   const double *neb_logu, *neb_logz;
   const double *neb_log10_lnu_per_q; /* [n_logu][n_logz][n_lam] log10(L_nu/Q), (Lsun/Hz)/(photon/s) */
+  /* Operand copies of the grid to keep on the device, as SED_GRID_COPY_* bits
+   * (one per precision; 0 = the default: the 3xTF32, FP32 and BF16 copies at
+   * load, the FP8 copy on the first FP8 call).  With a mask, only the named
+   * precisions are available -- a call in another one returns
+   * SED_EUNSUPPORTED -- and a requested FP8 copy is built at load.  Per
+   * layout the copies take 8 (3xTF32), 4 (FP32), 2 (BF16) and 1 (FP8) bytes
+   * x Kpad x n_lam: a server that runs BF16 only keeps a fifth of the default
+   * footprint.  The gradient needs the copy of its precision (3xTF32 or FP32). */
+  unsigned precision_mask;
 } sed_grid_desc;
+
+#define SED_GRID_COPY_FP32 (1u << SED_PREC_FP32)           /* TF32 hi/lo parts (3xTF32 path) */
+#define SED_GRID_COPY_FP32_SIMT (1u << SED_PREC_FP32_SIMT) /* exact FP32 (FFMA path) */
+#define SED_GRID_COPY_BF16 (1u << SED_PREC_BF16)
+#define SED_GRID_COPY_FP8 (1u << SED_PREC_FP8)
 
 /*
  * One fit: model choices, observations and their uncertainties (Sec. 2, 3, 4.1).
@@ -220,6 +234,18 @@ typedef struct {
    * SED_KEY_FRAC_OBRUN; a row whose f_ob lies outside [0, 1] gets
    * SED_ROW_BAD_THETA.  With f_ob = 0 the model is the one without a geometry. */
   int fesc_geometry;
+  /* Fixed and sampled keys (the paper's parameter dictionary, Sec. 4: each
+   * key is either sampled or fixed at a value): fixed[k] != 0 fixes key k at
+   * fixed_val[k] for every row, and the key then has no column in the
+   * parameter rows (sed_model_layout gives it zero width) and no gradient.
+   * Only one-column keys can be fixed: logzsol with one constant [Fe/H]
+   * (zmode 1), afe, logmass, zred, the dust and gas keys, and sigma_gal, the
+   * noise-floor terms and f_ob where the model samples them; SED_EINVAL
+   * otherwise, or for a non-finite value.  A fixed value goes through the same
+   * per-row checks as a column (e.g. zred outside [0, zf) marks every row).
+   * All zero (the default) = every key sampled. */
+  int fixed[SED_NKEYS];
+  double fixed_val[SED_NKEYS];
 } sed_model_desc;
 
 #define SED_MAX_CALIB 13
@@ -251,7 +277,8 @@ sed_status sed_last_host_path(const sed_ctx *ctx, int *mapped);
 sed_status sed_load_grid(sed_ctx *ctx, const sed_grid_desc *desc, sed_grid_id *out);
 
 sed_status sed_create_model(sed_ctx *ctx, const sed_model_desc *desc, sed_model_id *out);
-/* n_param: columns a parameter row needs; offsets[SED_NKEYS]: first column of each key. */
+/* n_param: columns a parameter row needs; offsets[SED_NKEYS]: first column of each key (a key
+ * without a column -- unused option or fixed -- has the next key's offset, i.e. zero width). */
 sed_status sed_model_layout(const sed_ctx *ctx, sed_model_id model, int *n_param, int *offsets);
 /* Replace the observed data/uncertainties of a model (host arrays, copied).  Data and
  * sigma come in pairs (both or neither, else SED_EINVAL); a pair passed as NULL keeps
@@ -329,15 +356,22 @@ sed_status sed_loglike_host(sed_ctx *ctx, sed_model_id model, const float *theta
  * host framework whose own allocator already owns the GPU's memory, a
  * sampler loop that cannot absorb the device synchronisation a cudaMalloc
  * may cause, or a deployment that must fix the library's device footprint
- * when it is loaded.  Same arguments, results and row-status semantics as
- * sed_loglike (device pointers, asynchronous on `stream`), but every
- * intermediate buffer comes from one fixed array of SED_NOALLOC_SCRATCH_BYTES
- * in device global memory that each device loading the library holds until
- * the process exits; no cudaMalloc, cudaFree or allocating library routine
- * is called.
- *  - Limit: the scratch a call needs grows with n (about 4*Kpad + 8*n_lam
- *    bytes per row, plus 8*Kpad per row for SED_PREC_FP32); a call needing
- *    more than SED_NOALLOC_SCRATCH_BYTES returns SED_ERANGE with the sizes in
+ * when it is loaded.  Same arguments, row-status semantics and kernels as
+ * sed_loglike (device pointers, asynchronous on `stream`; the same row
+ * order, wavelength windows and contraction schedule, so the same results),
+ * but every intermediate buffer comes from one fixed array of
+ * SED_NOALLOC_SCRATCH_BYTES in device global memory that each device loading
+ * the library holds until the process exits; no cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ *  - Precisions: SED_PREC_FP32, SED_PREC_FP32_SIMT and SED_PREC_BF16.
+ *    SED_PREC_FP8 returns SED_EUNSUPPORTED: its copy of the grid is built by
+ *    an allocation on the first FP8 call of sed_loglike.
+ *  - Limit: the scratch a call needs grows with n: per row 3 x 4 x ldn bytes
+ *    for SED_PREC_FP32 (2 x 4 x ldn otherwise; ldn = n_lam rounded up to
+ *    256) plus 8 x Kpad (FP32), 2 x Kpad (BF16) or 4 x Kpad (FP32_SIMT) and
+ *    about 250 bytes of row scalars -- about 390 rows of a 107 x 12 x 6000
+ *    grid in FP32, thousands for small grids.  A call needing more than
+ *    SED_NOALLOC_SCRATCH_BYTES returns SED_ERANGE with the sizes in
  *    sed_last_error() and launches nothing.  Split larger batches.
  *  - The array is shared by all calls and keeps the contents of the last
  *    one: calls that can overlap on the GPU (other streams or threads) race

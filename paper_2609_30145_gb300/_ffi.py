@@ -26,6 +26,7 @@ FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
 SFH_STEP, SFH_LINEAR = 0, 1
 FESC_NONE, FESC_RUNAWAY_BC, FESC_PICKET = 0, 1, 2
 NKEYS = len(KEYS)
+GRID_COPY_FP32, GRID_COPY_FP32_SIMT, GRID_COPY_BF16, GRID_COPY_FP8 = 1, 2, 4, 8
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 P = C.c_void_p
@@ -35,7 +36,7 @@ class GridDesc(C.Structure):
     _fields_ = [("n_age", C.c_int), ("n_feh", C.c_int), ("n_afe", C.c_int), ("n_lam", C.c_int),
                 ("log_age_yr", P), ("feh", P), ("afe", P), ("lam_aa", P), ("flux", P),
                 ("sigma_lib_kms", P), ("neb_n_logu", C.c_int), ("neb_n_logz", C.c_int),
-                ("neb_logu", P), ("neb_logz", P), ("neb_log10_lnu_per_q", P)]
+                ("neb_logu", P), ("neb_logz", P), ("neb_log10_lnu_per_q", P), ("precision_mask", C.c_uint)]
 
 
 class ModelDesc(C.Structure):
@@ -50,7 +51,8 @@ class ModelDesc(C.Structure):
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", P),
                 ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int), ("sfh_scheme", C.c_int),
-                ("phot_upper", P), ("fesc_geometry", C.c_int)]
+                ("phot_upper", P), ("fesc_geometry", C.c_int),
+                ("fixed", C.c_int * NKEYS), ("fixed_val", C.c_double * NKEYS)]
 
 
 class StageStats(C.Structure):

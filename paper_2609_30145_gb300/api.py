@@ -90,7 +90,7 @@ class Context:
         return v.value
 
     # ------------------------------------------------------------------
-    def load_grid(self, grid) -> int:
+    def load_grid(self, grid, precision_mask=0) -> int:
         """grid: object with log_age_yr, feh, afe, lam_aa, flux[n_afe][n_feh][n_age][n_lam]
         and optionally neb_logu, neb_logz, neb_tab, sigma_lib_kms."""
         keep = [_f64(grid.log_age_yr), _f64(grid.feh), _f64(grid.afe), _f64(grid.lam_aa), _f64(grid.flux)]
@@ -105,6 +105,7 @@ class Context:
             keep += [nu, nz, nt]
             d.neb_n_logu, d.neb_n_logz = nt.shape[:2]
             d.neb_logu, d.neb_logz, d.neb_log10_lnu_per_q = _ptr(nu), _ptr(nz), _ptr(nt)
+        d.precision_mask = int(precision_mask)
         gid = C.c_int32()
         self._check(self._lib.sed_load_grid(self._h, C.byref(d), C.byref(gid)))
         return gid.value
@@ -115,7 +116,9 @@ class Context:
                      spec_sigma=None, spec_mask=None, lsf_mode=0, lsf_value=None,
                      sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0,
                      calib_sigma=None, noise_floor_phot=0, noise_floor_spec=0, sfh_scheme=0,
-                     phot_upper=None, fesc_geometry=0) -> "Model":
+                     phot_upper=None, fesc_geometry=0, fixed=None) -> "Model":
+        """fixed: optional {key name: value} of keys fixed for every row (no
+        column in the parameter rows, no gradient); key names as in _ffi.KEYS."""
         d = _ffi.ModelDesc()
         d.grid, d.n_sfh, d.zf, d.zmode = grid_id, n_sfh, zf, zmode
         d.use_afe, d.use_nebular, d.dust_law = use_afe, use_nebular, dust_law
@@ -150,6 +153,10 @@ class Context:
         d.noise_floor_phot, d.noise_floor_spec = int(noise_floor_phot), int(noise_floor_spec)
         d.sfh_scheme = int(sfh_scheme)
         d.fesc_geometry = int(fesc_geometry)
+        for k, v in (fixed or {}).items():
+            i = KEYS.index(k)
+            d.fixed[i] = 1
+            d.fixed_val[i] = float(v)
         mid = C.c_int32()
         self._check(self._lib.sed_create_model(self._h, C.byref(d), C.byref(mid)))
         return Model(self, mid.value, n_filt=d.n_filt, n_pix=d.n_pix)
@@ -177,6 +184,12 @@ class Model:
                 continue
             out[:, bounds[i]:bounds[i] + w] = np.asarray(d[k], dtype=np.float64).reshape(n, w)
         return out.astype(dtype)
+
+    def close(self):
+        """Release the model's device memory (sed_destroy_model)."""
+        if self.id is not None and getattr(self.ctx, "_h", None):
+            self.ctx._check(self.ctx._lib.sed_destroy_model(self.ctx._h, self.id))
+        self.id = None
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
         a = [_f64(phot_d), _f64(phot_sigma), _f64(spec_d), _f64(spec_sigma)]
@@ -206,6 +219,20 @@ class Model:
         st = self.ctx._lib.sed_loglike(self.ctx._h, self.id, C.c_void_p(theta.data_ptr()), n, ld,
                                        C.c_void_p(lnl.data_ptr()), C.c_void_p(stt.data_ptr()),
                                        _prec(precision), _stream_handle(stream))
+        self.ctx._check(st)
+        return lnl, stt
+
+    def loglike_noalloc(self, theta: torch.Tensor, precision="fp32", stream=None, out=None, status=None):
+        """sed_loglike_noalloc: the same lnL and row status as loglike, with every
+        intermediate buffer taken from the library's fixed device scratch array
+        (no device allocation by the library; calls on different streams must
+        not overlap)."""
+        n, ld = self._theta(theta)
+        lnl = out if out is not None else torch.empty(n, dtype=torch.float64, device=theta.device)
+        stt = status if status is not None else torch.empty(n, dtype=torch.int32, device=theta.device)
+        st = self.ctx._lib.sed_loglike_noalloc(self.ctx._h, self.id, C.c_void_p(theta.data_ptr()), n, ld,
+                                               C.c_void_p(lnl.data_ptr()), C.c_void_p(stt.data_ptr()),
+                                               _prec(precision), _stream_handle(stream))
         self.ctx._check(st)
         return lnl, stt
 

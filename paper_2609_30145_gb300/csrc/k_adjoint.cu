@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
 cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s) {
   const size_t smem = epi_bwd_smem(a);
   if (smem_needed) *smem_needed = smem;
-  static size_t set_for = 0;
+  static DynSmemCache set_for;
   cudaError_t e = ensure_dyn_smem(k_epi_bwd, smem, &set_for);
   if (e != cudaSuccess) return e;
   return launch_pdl(k_epi_bwd, dim3(a.n), dim3(EB_THREADS), smem, s, a);

@@ -483,20 +483,11 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 template <int PREC, int BN, int STAGES, int G, bool GRAD>
 cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
   const int nz = (!GRAD && p.O2) ? 3 : 1;
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
-  }
+  const int n_sm = device_sm_count();
   using C = Cfg<PREC, BN, STAGES, G, GRAD>;
   auto k = k_contract_tc<PREC, BN, STAGES, G, GRAD>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static DynSmemCache attr;   // the raised shared-memory limit, set once per device
+  if (cudaError_t e = ensure_dyn_smem(k, (size_t)C::SMEM, &attr)) return e;
   if (!GRAD && p.tile_win) return launch_pdl(k, dim3(n_sm, 1, 1), dim3(C::THREADS), C::SMEM, s, p);   // persistent: one CTA per SM
   return launch_pdl(k, dim3(n_cols / BN, (p.n + BM - 1) / BM, nz), dim3(C::THREADS), C::SMEM, s, p);
 }

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
 
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
   const size_t smem = epilogue_smem(a);
-  static size_t set_for[2] = {0, 0};
+  static DynSmemCache set_for[2];
   const int m = a.row_model ? 1 : 0;
   cudaError_t e = m ? ensure_dyn_smem(k_epilogue<true>, smem, &set_for[1])
                     : ensure_dyn_smem(k_epilogue<false>, smem, &set_for[0]);

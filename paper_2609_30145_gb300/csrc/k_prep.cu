@@ -425,8 +425,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     th_s[j] = v;
     bad |= !isfinite(v);
   }
+  for (int j = tid; j < md.n_fixed; j += blockDim.x) th_s[md.n_param + j] = md.fixed_v[j];   // fixed keys
   if (warp == 0) {
-    const CosmoRow c = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]], lane);
+    const CosmoRow c = row_cosmo(md, theta_col(md, th, md.offs[SED_KEY_ZRED]),
+                                 theta_col(md, th, md.offs[SED_KEY_LOGMASS]), lane);
     if (lane == 0) s_cr = c;
   }
   bad = __syncthreads_or(bad);
@@ -726,7 +728,7 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   for (int i = tid; i < NT; i += blockDim.x) {
     int j0, j1;
     float w0, w1, d0, d1;
-    const float v = zeta[md.zmode == 0 ? i : 0];
+    const float v = md.zmode == 0 ? zeta[i] : theta_col(md, th, md.offs[SED_KEY_LOGZSOL]);
     bracket_f(md.feh, md.n_feh, v, j0, w0, j1, w1);
     bracket_df(md.feh, md.n_feh, v, j0, j1, d0, d1);
     zb[i] = j0;
@@ -760,7 +762,7 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   int n0 = 0, n1 = 0;
   float wn0 = 1.f, wn1 = 0.f, dn0 = 0.f, dn1 = 0.f;
   if (md.n_afe > 1) {
-    const float afe = md.use_afe ? th[md.offs[SED_KEY_AFE]] : 0.f;
+    const float afe = md.use_afe ? theta_col(md, th, md.offs[SED_KEY_AFE]) : 0.f;
     bracket_f(md.afe, md.n_afe, afe, n0, wn0, n1, wn1);
     if (md.use_afe) bracket_df(md.afe, md.n_afe, afe, n0, n1, dn0, dn1);
   }
@@ -850,27 +852,31 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   if (tid == 0) {
     double gtmax = 0.0, gafe_t = 0.0;
     for (int w = 0; w < PREP_BWD_THREADS / 32; ++w) { gtmax += s_tmax_part[w]; gafe_t += red[w]; }
+    // a fixed key has no column in the caller's rows (and no gradient)
+    auto put = [&](int key, float v) {
+      if (md.offs[key] < md.n_param) out[md.offs[key]] = v;
+    };
     const double* rg = a.rgrad + (size_t)r * RGRAD;
     if (md.zmode == 1) {
       double gzs = 0.0;
       for (int i = 0; i < NT; ++i) gzs += (double)gzeta[i];
-      out[md.offs[SED_KEY_LOGZSOL]] = (float)gzs;
+      put(SED_KEY_LOGZSOL, (float)gzs);
     }
-    out[md.offs[SED_KEY_AFE]] = md.use_afe ? (float)gafe_t : 0.f;
-    out[md.offs[SED_KEY_LOGMASS]] = (float)rg[RG_LOGMASS];
-    out[md.offs[SED_KEY_ZRED]] = (float)(rg[RG_Z] + gtmax * (double)rs.dtmax_dz);
-    out[md.offs[SED_KEY_TAU_POW]] = (float)rg[RG_TAU_BC];
-    out[md.offs[SED_KEY_ALPHA_POW]] = (float)rg[RG_ALPHA_BC];
-    out[md.offs[SED_KEY_DIFFUSE_TAU]] = (float)rg[RG_TAU_D];
-    out[md.offs[SED_KEY_DIFFUSE_INDEX]] = (float)rg[RG_DELTA];
-    out[md.offs[SED_KEY_GAS_LOGZ]] = md.use_neb ? (float)rg[RG_GAS_LOGZ] : 0.f;
-    out[md.offs[SED_KEY_GAS_LOGU]] = md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f;
-    if (md.sample_sgal) out[md.offs[SED_KEY_SIGMA_GAL]] = (float)rg[RG_SIGMA_GAL];
-    if (md.fesc_geom) out[md.offs[SED_KEY_FRAC_OBRUN]] = (float)rg[RG_FOB];
+    put(SED_KEY_AFE, md.use_afe ? (float)gafe_t : 0.f);
+    put(SED_KEY_LOGMASS, (float)rg[RG_LOGMASS]);
+    put(SED_KEY_ZRED, (float)(rg[RG_Z] + gtmax * (double)rs.dtmax_dz));
+    put(SED_KEY_TAU_POW, (float)rg[RG_TAU_BC]);
+    put(SED_KEY_ALPHA_POW, (float)rg[RG_ALPHA_BC]);
+    put(SED_KEY_DIFFUSE_TAU, (float)rg[RG_TAU_D]);
+    put(SED_KEY_DIFFUSE_INDEX, (float)rg[RG_DELTA]);
+    put(SED_KEY_GAS_LOGZ, md.use_neb ? (float)rg[RG_GAS_LOGZ] : 0.f);
+    put(SED_KEY_GAS_LOGU, md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f);
+    if (md.sample_sgal) put(SED_KEY_SIGMA_GAL, (float)rg[RG_SIGMA_GAL]);
+    if (md.fesc_geom) put(SED_KEY_FRAC_OBRUN, (float)rg[RG_FOB]);
     for (int arm = 0; arm < 2; ++arm)
       for (int k = 0; k < 4; ++k)
         if ((md.floor_bits[arm] >> k) & 1)
-          out[md.offs[SED_KEY_LOG_ERR_SCALE_PHOT + 4 * arm + k]] = (float)rg[RG_FLOOR + 4 * arm + k];
+          put(SED_KEY_LOG_ERR_SCALE_PHOT + 4 * arm + k, (float)rg[RG_FLOOR + 4 * arm + k]);
   }
   if (md.zmode == 0)
     for (int i = tid; i < NT; i += blockDim.x) out[md.offs[SED_KEY_LOGZSOL] + i] = gzeta[i];
@@ -879,8 +885,8 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
 
 cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
   const size_t smem = (size_t)2 * p.g.n_age * p.g.n_feh * sizeof(float);
-  static size_t set_for = 0;
-  static size_t set_for_lin = 0;
+  static DynSmemCache set_for;
+  static DynSmemCache set_for_lin;
   if (p.md.sfh_linear) {
     const cudaError_t e = ensure_dyn_smem(k_prep_bwd<true>, smem, &set_for_lin);
     if (e != cudaSuccess) return e;
@@ -893,18 +899,22 @@ cudaError_t launch_prep_bwd(const PrepBwdArgs& p, cudaStream_t s) {
 
 cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (p.perm && !p.row_model) {
+  // a fixed redshift (no column) needs no redshift order: the caller's order is kept
+  const bool z_col = p.md.offs[SED_KEY_ZRED] < p.md.n_param;
+  if (p.perm && !p.row_model && z_col) {
     e = launch_pdl(k_order, dim3((p.n + ORDER_CHUNK - 1) / ORDER_CHUNK), dim3(ORDER_THREADS), 0, s, p.theta, p.n, p.ld,
                    p.md.offs[SED_KEY_ZRED], (float)p.md.zf, (float)(ORDER_BINS / p.md.zf), p.perm);
     if (e != cudaSuccess) return e;
   }
   PrepKernelArgs ka;
   ka.p = p;
+  if (!p.row_model && !z_col) ka.p.perm = nullptr;
   // Ws [n_age][n_feh], the FP8 row scratch, the row's parameters (n_param <= ld
   // and n_param <= 2 MAX_SFH + SED_NKEYS for every model)
-  const size_t npar = (size_t)std::min(p.ld, 2 * MAX_SFH + SED_NKEYS);
+  // (+ the fixed keys' values past the caller's columns)
+  const size_t npar = (size_t)std::min(p.ld, 2 * MAX_SFH + SED_NKEYS) + SED_NKEYS;
   const size_t smem = ((size_t)p.g.n_age * p.g.n_feh + (p.W_f8 ? (size_t)p.L.Kpad : 0) + npar) * sizeof(float);
-  static size_t set_for[2] = {0, 0};
+  static DynSmemCache set_for[2];
   e = p.row_model ? ensure_dyn_smem(k_prep<true>, smem, &set_for[1]) : ensure_dyn_smem(k_prep<false>, smem, &set_for[0]);
   if (e != cudaSuccess) return e;
   return p.row_model ? launch_pdl(k_prep<true>, dim3(p.n), dim3(PREP_THREADS), smem, s, ka)

@@ -52,15 +52,15 @@ sed_status dalloc(sed_ctx* ctx, void** p, size_t bytes, std::vector<void*>* owne
   *p = nullptr;
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~(size_t)255;
-  if (ctx->budget && ctx->used + bytes > ctx->budget)
-    return fail(ctx, SED_ENOMEM, "HBM budget exceeded (%zu + %zu > %zu bytes)", ctx->used, bytes, ctx->budget);
+  if (!budget_reserve(ctx, bytes))
+    return fail(ctx, SED_ENOMEM, "HBM budget exceeded (%zu + %zu > %zu bytes)", ctx->used.load(), bytes, ctx->budget);
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
+    budget_release(ctx, bytes);
     return fail(ctx, SED_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
   }
-  ctx->used += bytes;
   if (acct) *acct += bytes;
   if (owner) owner->push_back(*p);
   return SED_OK;
@@ -77,7 +77,7 @@ sed_status upload(sed_ctx* ctx, T** dst, const T* src, size_t n, std::vector<voi
 void free_all(sed_ctx* ctx, std::vector<void*>& v, size_t& acct) {
   for (void* p : v) cudaFree(p);
   v.clear();
-  ctx->used -= std::min(ctx->used, acct);
+  budget_release(ctx, acct);
   acct = 0;
 }
 
@@ -205,7 +205,7 @@ sed_status sed_last_host_path(const sed_ctx* ctx, int* mapped) {
 
 sed_status sed_memory_used(const sed_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return SED_EINVAL;
-  *bytes = ctx->used;
+  *bytes = ctx->used.load();
   return SED_OK;
 }
 
@@ -232,6 +232,7 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
     fmax = std::max(fmax, v);
   }
   if (!(fmax > 0)) return fail(ctx, SED_EINVAL, "flux is identically zero");
+  if (d->precision_mask > 15u) return fail(ctx, SED_EINVAL, "precision_mask has bits other than SED_GRID_COPY_*");
   const bool neb = d->neb_n_logu > 0 && d->neb_n_logz > 0 && d->neb_log10_lnu_per_q;
   if (neb) {
     if (d->neb_n_logu > 32 || d->neb_n_logz > 32) return fail(ctx, SED_ERANGE, "nebular axes longer than 32");
@@ -245,6 +246,8 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
 
   Grid* g = new Grid();
   g->n_age = d->n_age; g->n_feh = d->n_feh; g->n_afe = d->n_afe; g->n_lam = d->n_lam;
+  g->copies = d->precision_mask ? d->precision_mask : (SED_GRID_COPY_FP32 | SED_GRID_COPY_FP32_SIMT | SED_GRID_COPY_BF16);
+  g->avail = d->precision_mask ? d->precision_mask : 15u;
   g->log_age.assign(d->log_age_yr, d->log_age_yr + d->n_age);
   g->feh.assign(d->feh, d->feh + d->n_feh);
   if (d->afe) g->afe.assign(d->afe, d->afe + d->n_afe); else g->afe.assign(1, 0.0);
@@ -509,25 +512,32 @@ sed_status get_layout(sed_ctx* ctx, Grid* g, int n_young, int neb_cut, Layout** 
   L->q_log2 = g->q_log2;
   sed_status st = upload(ctx, &L->k_code, code.data(), Kpad, &g->allocs, &g->bytes);
   if (!st) st = upload(ctx, &L->q_s, qs.data(), Kpad, &g->allocs, &g->bytes);
-  // SSP^T [lam][k], scaled by 2^f_log2, in FP32, TF32 hi/lo and BF16
+  // SSP^T [lam][k], scaled by 2^f_log2, in FP32, TF32 hi/lo and BF16 (the
+  // copies the grid keeps; FP8 below when it is asked for at load)
   L->code_h = code;
-  std::vector<float> f32((size_t)NL * Kpad), hi((size_t)NL * Kpad), lo((size_t)NL * Kpad);
-  std::vector<__nv_bfloat16> bf((size_t)NL * Kpad);
+  const bool c_hl = g->copies & SED_GRID_COPY_FP32, c_f = g->copies & SED_GRID_COPY_FP32_SIMT,
+             c_b = g->copies & SED_GRID_COPY_BF16;
+  const size_t NE = (size_t)NL * Kpad;
+  std::vector<float> f32(c_f ? NE : 0), hi(c_hl ? NE : 0), lo(c_hl ? NE : 0);
+  std::vector<__nv_bfloat16> bf(c_b ? NE : 0);
   for (int k = 0; k < Kpad; k++) {
     for (int l = 0; l < NL; l++) {
       const float v = ssp_value(g, L, k, l);
       const size_t o = (size_t)l * Kpad + k;
-      f32[o] = v;
-      const float h = tf32_rna_host(v);
-      hi[o] = h;
-      lo[o] = v - h;
-      bf[o] = __float2bfloat16_rn(v);
+      if (c_f) f32[o] = v;
+      if (c_hl) {
+        const float h = tf32_rna_host(v);
+        hi[o] = h;
+        lo[o] = v - h;
+      }
+      if (c_b) bf[o] = __float2bfloat16_rn(v);
     }
   }
-  if (!st) st = upload(ctx, &L->sspT_f32, f32.data(), f32.size(), &g->allocs, &g->bytes);
-  if (!st) st = upload(ctx, &L->sspT_hi, hi.data(), hi.size(), &g->allocs, &g->bytes);
-  if (!st) st = upload(ctx, &L->sspT_lo, lo.data(), lo.size(), &g->allocs, &g->bytes);
-  if (!st) st = upload(ctx, &L->sspT_bf16, bf.data(), bf.size(), &g->allocs, &g->bytes);
+  if (!st && c_f) st = upload(ctx, &L->sspT_f32, f32.data(), f32.size(), &g->allocs, &g->bytes);
+  if (!st && c_hl) st = upload(ctx, &L->sspT_hi, hi.data(), hi.size(), &g->allocs, &g->bytes);
+  if (!st && c_hl) st = upload(ctx, &L->sspT_lo, lo.data(), lo.size(), &g->allocs, &g->bytes);
+  if (!st && c_b) st = upload(ctx, &L->sspT_bf16, bf.data(), bf.size(), &g->allocs, &g->bytes);
+  if (!st && (g->copies & SED_GRID_COPY_FP8)) st = ensure_f8_layout(ctx, g, L);
   if (st) {
     delete L;
     return st;
@@ -750,6 +760,39 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   dv.fesc_geom = d->fesc_geometry;
   dv.offs[SED_KEY_FRAC_OBRUN] = o;
   o += d->fesc_geometry ? 1 : 0;
+  // fixed keys (Sec. 4 parameter dictionary): a fixed one-column key leaves the
+  // caller's rows; the kernels read it past the caller's columns
+  {
+    int width[SED_NKEYS];
+    for (int k = 0; k < SED_NKEYS; k++) width[k] = (k + 1 < SED_NKEYS ? dv.offs[k + 1] : o) - dv.offs[k];
+    for (int k = 0; k < SED_NKEYS; k++) {
+      if (!d->fixed[k]) continue;
+      if (k == SED_KEY_SFH || width[k] != 1) {
+        delete M;
+        return fail(ctx, SED_EINVAL, "key %d cannot be fixed (only keys with one column in this model)", k);
+      }
+      if (!std::isfinite(d->fixed_val[k])) {
+        delete M;
+        return fail(ctx, SED_EINVAL, "fixed_val[%d] is not finite", k);
+      }
+    }
+    int c = 0, nf = 0;
+    int in_off[SED_NKEYS];
+    for (int k = 0; k < SED_NKEYS; k++) {
+      M->offs_caller[k] = c;
+      in_off[k] = c;
+      if (!d->fixed[k]) c += width[k];
+    }
+    for (int k = 0; k < SED_NKEYS; k++) {
+      if (d->fixed[k]) {
+        in_off[k] = c + nf;
+        dv.fixed_v[nf++] = (float)d->fixed_val[k];
+      }
+      dv.offs[k] = in_off[k];
+    }
+    o = c;
+    dv.n_fixed = nf;
+  }
   dv.n_param = o;
   dv.zf = d->zf;
   dv.Om0 = d->Om0;
@@ -965,7 +1008,7 @@ sed_status sed_model_layout(const sed_ctx* ctx, sed_model_id id, int* n_param, i
   if (!M) return SED_EINVAL;
   if (n_param) *n_param = M->dv.n_param;
   if (offsets)
-    for (int k = 0; k < SED_NKEYS; k++) offsets[k] = M->dv.offs[k];
+    for (int k = 0; k < SED_NKEYS; k++) offsets[k] = M->offs_caller[k];
   return SED_OK;
 }
 
@@ -1011,7 +1054,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
                             w->dW, w->rgrad};
   for (void* p : old)
     if (p) cudaFree(p);
-  ctx->used -= std::min(ctx->used, w->bytes);
+  budget_release(ctx, w->bytes);
   const bool had_grad = w->dW != nullptr;
   if (w->host_exec) cudaGraphExecDestroy(w->host_exec);   // it holds the old buffers
   *w = Workspace();
@@ -1049,6 +1092,8 @@ sed_status check_hot_args(sed_ctx* ctx, Model* M, const float* theta, int n, int
       precision != SED_PREC_FP8)
     return fail(ctx, SED_EINVAL, "unknown precision %d", precision);
   if (n > (1 << 22)) return fail(ctx, SED_ERANGE, "batch larger than 4M rows");
+  if (!(M->g->avail & (1u << precision)))
+    return fail(ctx, SED_EUNSUPPORTED, "precision %d: its copy of the grid was not kept (precision_mask)", precision);
   return SED_OK;
 }
 

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -163,7 +164,18 @@ struct ModelDev {
   double pix_ln_min, pix_ln_max;
   float pix_s_max;         // largest total dispersion a row can have (ln units)
   int win_max;             // most rest-frame nodes one row's window can span (any redshift)
+  // fixed keys (sed_model_desc.fixed): the caller's rows have n_param columns;
+  // fixed key j is read from column n_param + j of the row as the kernels stage
+  // it (offs[] points there), filled from fixed_v[j]
+  int n_fixed;
+  float fixed_v[SED_NKEYS];
 };
+
+// Value of column `col` of a parameter row in the kernels' layout: a caller's
+// column, or a fixed key's value past the caller's columns.
+__host__ __device__ __forceinline__ float theta_col(const ModelDev& md, const float* row, int col) {
+  return col < md.n_param ? row[col] : md.fixed_v[col - md.n_param];
+}
 
 // ---------------------------------------------------------------------------
 // Device copy of a grid in one K order: [young block | old block], each block
@@ -199,6 +211,8 @@ struct Layout {
 
 struct Grid {
   int n_age = 0, n_feh = 0, n_afe = 0, n_lam = 0;
+  unsigned copies = 0;     // SED_GRID_COPY_* bits built with each layout
+  unsigned avail = 0;      // precisions a call may use (FP8 built on first use when not in `copies`)
   std::vector<double> log_age, feh, afe, lam, flux;  // host master copy (FP64)
   std::vector<double> siglib_kms;                    // Eq. app_siglib at the nodes
   double f_log2 = 0.0;                               // f_dev = f * 2^f_log2
@@ -215,6 +229,7 @@ struct Grid {
 
 struct Model {
   int grid = -1;
+  int offs_caller[SED_NKEYS] = {};   // first column of each key in the caller's rows (sed_model_layout)
   Grid* g = nullptr;
   Layout* L = nullptr;
   ModelDev dv{};
@@ -310,7 +325,8 @@ struct Workspace {
 
 struct sed_ctx {
   int device = 0;
-  size_t budget = 0, used = 0;
+  size_t budget = 0;
+  std::atomic<size_t> used{0};   // device bytes held; changed only through sed::budget_reserve / budget_release
   std::mutex mu;
   std::string last_error = "ok";
   std::vector<sed::Grid*> grids;
@@ -321,6 +337,26 @@ struct sed_ctx {
   int tc_ok = -1;              // tcgen05 path usable on this device (sm_103)
   int last_host_mapped = 0;    // sed_last_host_path
 };
+
+namespace sed {
+// Device-memory accounting of a context against its budget.  The context's
+// allocations (grids, models, per-stream workspaces) and the server's (launch
+// slots, fits' live points) can run on different host threads under different
+// locks, so the count is atomic and a reservation is one compare-exchange:
+// either the whole amount fits under the budget and is added, or nothing is.
+inline bool budget_reserve(sed_ctx* ctx, size_t bytes) {
+  size_t cur = ctx->used.load(std::memory_order_relaxed);
+  do {
+    if (ctx->budget && cur + bytes > ctx->budget) return false;
+  } while (!ctx->used.compare_exchange_weak(cur, cur + bytes, std::memory_order_relaxed));
+  return true;
+}
+inline void budget_release(sed_ctx* ctx, size_t bytes) {
+  size_t cur = ctx->used.load(std::memory_order_relaxed);
+  while (!ctx->used.compare_exchange_weak(cur, cur - std::min(cur, bytes), std::memory_order_relaxed)) {
+  }
+}
+}  // namespace sed
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).
@@ -385,21 +421,49 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 // Raises a kernel's dynamic shared-memory limit once its static plus dynamic
-// shared memory passes the 48 KB default; *done caches the largest size set.
-// cudaErrorInvalidConfiguration if the total passes the 227 KB a CTA can have.
+// shared memory passes the 48 KB default.  The attribute belongs to the
+// current device, so the largest size set is cached per device; one lock
+// orders the updates of every cache (a launch on another thread never sees a
+// limit lowered under it).  cudaErrorInvalidConfiguration if the total passes
+// the 227 KB a CTA can have.
+constexpr int MAX_DEVICES = 64;
+struct DynSmemCache {
+  size_t v[MAX_DEVICES] = {};
+};
+inline std::mutex& dyn_smem_mutex() {
+  static std::mutex m;
+  return m;
+}
 template <typename K>
-cudaError_t ensure_dyn_smem(K* kernel, size_t dyn, size_t* done) {
-  if (dyn <= *done) return cudaSuccess;
+cudaError_t ensure_dyn_smem(K* kernel, size_t dyn, DynSmemCache* cache) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(dyn_smem_mutex());
+  if (dyn <= cache->v[dev]) return cudaSuccess;
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  e = cudaFuncGetAttributes(&fa, kernel);
   if (e != cudaSuccess) return e;
   if (dyn + fa.sharedSizeBytes > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (dyn + fa.sharedSizeBytes > 48 * 1024) {
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
   }
-  *done = dyn;
+  cache->v[dev] = dyn;
   return cudaSuccess;
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+inline int device_sm_count() {
+  static std::atomic<int> n_sm[MAX_DEVICES];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return 1;
+  int v = n_sm[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+  n_sm[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);

@@ -8,18 +8,25 @@
 // fragments its pool), a sampler loop that cannot tolerate the implicit
 // device synchronisation a cudaMalloc may cause in the middle of a step, or
 // a deployment that must know the library's device footprint exactly at load
-// time.  This entry point runs the same three kernels as sed_loglike but
-// takes every intermediate buffer from one fixed array in device global
-// memory, declared below, and calls no cudaMalloc, cudaFree or allocating
-// library routine.
+// time.  This entry point runs the same kernels as sed_loglike, in the same
+// order and with the same schedule (the redshift row order, the per-tile
+// wavelength windows, the three-way split of the 3xTF32 contraction), so its
+// results equal sed_loglike's bit for bit, but it takes every intermediate
+// buffer from one fixed array in device global memory, declared below, and
+// calls no cudaMalloc, cudaFree or allocating library routine.
 //
 // The array is SED_NOALLOC_SCRATCH_BYTES long and lives for the life of the
 // process on every device that loads the library.  All calls share it:
 // calls whose kernels can overlap on the GPU (different streams, or
 // different host threads) race on it and must be serialised by the caller.
-// Each call overwrites what it uses; the one word that must start at zero
-// (the device error word of the contraction) is cleared by the first kernel
-// of every call.
+// Each call overwrites what it uses.  What must start from a known value is
+// set on the call's stream before its kernels: the per-tile window bounds
+// (two memsets, as in sed_loglike); the device error word of the
+// contraction is cleared by the first kernel of every call.
+//
+// FP8 is refused (SED_EUNSUPPORTED): its operand copy of the grid is built
+// with cudaMalloc on the first FP8 call of sed_loglike, so an allocation-free
+// call cannot rely on it.
 #include <stdarg.h>
 #include <stdio.h>
 
@@ -76,23 +83,31 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   if (n < 0) return na_fail(ctx, SED_EINVAL, "n < 0");
   if (n > 0 && (!theta || !lnl_out)) return na_fail(ctx, SED_EINVAL, "theta or lnl_out is NULL");
   if (ld < M->dv.n_param) return na_fail(ctx, SED_EINVAL, "ld (%d) < n_param (%d)", ld, M->dv.n_param);
+  if (precision == SED_PREC_FP8)
+    return na_fail(ctx, SED_EUNSUPPORTED,
+                   "sed_loglike_noalloc: FP8 needs the grid's FP8 copy, which sed_loglike allocates on first use");
   if (precision != SED_PREC_FP32 && precision != SED_PREC_FP32_SIMT && precision != SED_PREC_BF16)
     return na_fail(ctx, SED_EINVAL, "unknown precision %d", precision);
   if (precision != SED_PREC_FP32_SIMT && ctx->tc_ok != 1)
     return na_fail(ctx, SED_EUNSUPPORTED, "tensor-core precisions need an sm_103 device");
+  if (!(M->g->avail & (1u << precision)))
+    return na_fail(ctx, SED_EUNSUPPORTED, "precision %d: its copy of the grid was not kept (precision_mask)", precision);
+  if (n > (1 << 22)) return na_fail(ctx, SED_ERANGE, "batch larger than 4M rows");
   if (n == 0) return SED_OK;
 
   const Grid* g = M->g;
   const Layout* L = M->L;
   const int kpad = L->Kpad;
   const int ldn = (g->n_lam + 255) / 256 * 256;
-  const bool f32 = precision == SED_PREC_FP32, bf = precision == SED_PREC_BF16;
-  // carve the scratch: err | RowScal | W | W_hi | W_lo | W_bf16 | Y | O
-  const size_t nn = (size_t)n;
-  size_t off[8], need = 0;
-  const size_t sz[8] = {256, nn * sizeof(RowScal), nn * kpad * 4, f32 ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0,
-                        bf ? nn * kpad * 2 : 0, nn * ldn * 4, nn * ldn * 4};
-  for (int i = 0; i < 8; i++) {
+  const bool f32 = precision == SED_PREC_FP32, bf = precision == SED_PREC_BF16, simt = !f32 && !bf;
+  // carve the scratch: err | perm | tile windows | RowScal | W (FFMA) | W_hi | W_lo | W_bf16 | Y | O | O2 (3xTF32)
+  const size_t nn = (size_t)n, mt = (nn + 127) / 128;
+  constexpr int NB = 11;
+  size_t off[NB], need = 0;
+  const size_t sz[NB] = {256, nn * 4, 2 * mt * 4, nn * sizeof(RowScal), simt ? nn * kpad * 4 : 0,
+                         f32 ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0, bf ? nn * kpad * 2 : 0,
+                         nn * ldn * 4, nn * ldn * 4, f32 ? nn * ldn * 4 : 0};
+  for (int i = 0; i < NB; i++) {
     off[i] = need;
     need += up256(sz[i]);
   }
@@ -112,28 +127,34 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   void* base = nullptr;
   if (sed_status st = noalloc_scratch_ptr(ctx, &base)) return st;
   unsigned char* b = static_cast<unsigned char*>(base);
-  int* err = reinterpret_cast<int*>(b + off[0]);
-  RowScal* rs = reinterpret_cast<RowScal*>(b + off[1]);
-  float* W = reinterpret_cast<float*>(b + off[2]);
-  float* W_hi = f32 ? reinterpret_cast<float*>(b + off[3]) : nullptr;
-  float* W_lo = f32 ? reinterpret_cast<float*>(b + off[4]) : nullptr;
-  __nv_bfloat16* W_bf = bf ? reinterpret_cast<__nv_bfloat16*>(b + off[5]) : nullptr;
-  float* Y = reinterpret_cast<float*>(b + off[6]);
-  float* O = reinterpret_cast<float*>(b + off[7]);
+  auto at = [&](int i) { return sz[i] ? static_cast<void*>(b + off[i]) : nullptr; };
+  int* err = static_cast<int*>(at(0));
+  int* perm = static_cast<int*>(at(1));
+  int* tile_win = static_cast<int*>(at(2));
+  RowScal* rs = static_cast<RowScal*>(at(3));
+  float* W = static_cast<float*>(at(4));
+  float* W_hi = static_cast<float*>(at(5));
+  float* W_lo = static_cast<float*>(at(6));
+  __nv_bfloat16* W_bf = static_cast<__nv_bfloat16*>(at(7));
+  float* Y = static_cast<float*>(at(8));
+  float* O = static_cast<float*>(at(9));
+  float* O2 = static_cast<float*>(at(10));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
+  // per-tile window bounds start empty: lo = a large positive int, hi = -1
+  cudaError_t e = cudaMemsetAsync(tile_win, 0x7f, mt * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tile_win + mt, 0xff, mt * sizeof(int), s);
   PrepArgs pa{};
   pa.theta = theta; pa.n = n; pa.ld = ld;
   pa.md = M->dv; pa.g = g->dv; pa.L = L->dv();
-  pa.W = precision == SED_PREC_FP32_SIMT ? W : nullptr;   // only the CUDA-core contraction reads FP32 W
-  pa.W_hi = W_hi; pa.W_lo = W_lo; pa.W_bf16 = W_bf;
-  pa.rs = rs; pa.err = err;
-  cudaError_t e = launch_prep(pa, s);
+  pa.W = W; pa.W_hi = W_hi; pa.W_lo = W_lo; pa.W_bf16 = W_bf;
+  pa.rs = rs; pa.err = err; pa.perm = perm; pa.tile_win = tile_win;
+  if (e == cudaSuccess) e = launch_prep(pa, s);
   if (e == cudaSuccess) {
-    if (precision == SED_PREC_FP32_SIMT) {
+    if (simt) {
       ContractArgs ca{};
       ca.n = n; ca.n_lam = g->n_lam; ca.ldn = ldn; ca.Ky_pad = L->Ky_pad; ca.Kpad = kpad;
-      ca.W = W; ca.sspT = L->sspT_f32; ca.Y = Y; ca.O = O;
+      ca.W = W; ca.sspT = L->sspT_f32; ca.Y = Y; ca.O = O; ca.rs = rs;
       e = launch_contract_simt(ca, s);
     } else {
       TcMaps maps;
@@ -143,13 +164,13 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
         return na_fail(ctx, SED_ECUDA, "cuTensorMapEncodeTiled failed");
       TcArgs ta{};
       ta.n = n; ta.n_lam = g->n_lam; ta.ldn = ldn; ta.Ky_pad = L->Ky_pad; ta.Kpad = kpad; ta.prec = precision;
-      ta.maps = &maps; ta.Y = Y; ta.O = O; ta.err = err;
+      ta.maps = &maps; ta.Y = Y; ta.O = O; ta.O2 = O2; ta.err = err; ta.rs = rs; ta.tile_win = tile_win;
       e = launch_contract_tc(ta, s);
     }
   }
   if (e == cudaSuccess) {
     EpiArgs ea{};
-    ea.n = n; ea.ldn = ldn; ea.Y = Y; ea.O = O; ea.rs = rs;
+    ea.n = n; ea.ldn = ldn; ea.Y = Y; ea.O = O; ea.O2 = O2; ea.rs = rs;
     ea.md = M->dv; ea.g = g->dv;
     ea.lnl = lnl_out; ea.status = row_status; ea.err = err;
     e = launch_epilogue(ea, s);

@@ -130,13 +130,13 @@ sed_status sfail(sed_server* sv, sed_status st, const char* fmt, ...) {
 template <class T>
 bool dmalloc(sed_server* sv, std::vector<void*>& own, T** p, size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
-  if (sv->ctx->budget && sv->ctx->used + bytes > sv->ctx->budget) return false;
+  if (!budget_reserve(sv->ctx, bytes)) return false;
   if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
+    budget_release(sv->ctx, bytes);
     return false;
   }
-  sv->ctx->used += bytes;
   own.push_back(*p);
   return true;
 }
@@ -306,6 +306,7 @@ sed_status sed_server_create(sed_ctx* ctx, const sed_server_desc* d, sed_server*
     return SED_EINVAL;
   if (d->precision < SED_PREC_FP32 || d->precision > SED_PREC_FP8) return SED_EINVAL;
   if (d->precision != SED_PREC_FP32_SIMT && ctx->tc_ok != 1) return SED_EUNSUPPORTED;
+  if (!(ctx->grids[d->grid]->avail & (1u << d->precision))) return SED_EUNSUPPORTED;   // copy not kept
   if (d->max_launch_rows < 1 || d->max_launch_rows > (1 << 20)) return SED_ERANGE;
   if (d->n_slots < 1 || d->n_slots > SRV_MAX_SLOTS) return SED_ERANGE;
   if (d->model_layout < 0 || d->model_layout >= (int)ctx->models.size() || !ctx->models[d->model_layout])
@@ -428,7 +429,8 @@ sed_status sed_server_open_fit(sed_server* sv, sed_model_id model, int max_rows,
   f.ld = ld;
   f.bytes = need;
   sed_status st = SED_OK;
-  if (ctx->budget && ctx->used + need > ctx->budget) st = SED_ENOMEM;
+  const bool reserved = budget_reserve(ctx, need);
+  if (!reserved) st = SED_ENOMEM;
   if (!st && cudaMalloc((void**)&f.theta_d, need) != cudaSuccess) st = SED_ENOMEM;
   if (!st && cudaMallocHost((void**)&f.stage_h, (size_t)max_rows * ld * 4) != cudaSuccess) st = SED_ENOMEM;
   if (!st && cudaEventCreateWithFlags(&f.uploaded, cudaEventDisableTiming) != cudaSuccess) st = SED_ECUDA;
@@ -442,10 +444,10 @@ sed_status sed_server_open_fit(sed_server* sv, sed_model_id model, int max_rows,
     if (f.theta_d) cudaFree(f.theta_d);
     if (f.stage_h) cudaFreeHost(f.stage_h);
     if (f.uploaded) cudaEventDestroy(f.uploaded);
+    if (reserved) budget_release(ctx, need);
     if (prev >= 0) cudaSetDevice(prev);
     return sfail(sv, st, "could not allocate the fit's buffers");
   }
-  ctx->used += need;
   sv->used += need;
   sv->max_samp = std::max(sv->max_samp, M->dv.n_samp);
   sv->max_pix = std::max(sv->max_pix, M->dv.n_pix);
@@ -475,7 +477,7 @@ sed_status sed_server_close_fit(sed_server* sv, int fit) {
   cudaFree(f.theta_d);
   cudaFreeHost(f.stage_h);
   cudaEventDestroy(f.uploaded);
-  sv->ctx->used -= std::min(sv->ctx->used, f.bytes);
+  budget_release(sv->ctx, f.bytes);
   sv->used -= std::min(sv->used, f.bytes);
   f = SrvFit();
   sv->stats.fits_open--;

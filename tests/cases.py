@@ -81,9 +81,10 @@ def theta_rows(w: synth.Workload, n, seed=4, orc=None):
                              w.floor_phot, w.floor_spec, w.sfh_scheme)
 
 
-def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
+def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True, fixed=None):
     """A library model with exactly the oracle's inputs (grid loaded once per grid
-    object); with_spec_data=False gives the spectrum's pixels but not its data."""
+    object); with_spec_data=False gives the spectrum's pixels but not its data;
+    fixed: {key: value} of keys fixed for every row (no column)."""
     cache = ctx.__dict__.setdefault("_grid_ids", {})
     key = id(orc.grid)
     if key not in cache:
@@ -100,7 +101,7 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True):
                   spec_sigma=orc.spec_sigma if with_spec_data else None,
                   spec_mask=orc.spec_mask, lsf_mode=orc.lsf_mode, lsf_value=orc.lsf_value,
                   sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref, calib_sigma=orc.calib_sigma)
-    return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)
+    return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, fixed=fixed, **kw)
 
 
 def theta_pair(w: synth.Workload, n, seed=4, orc=None):

@@ -116,6 +116,10 @@ def test_struct_layouts_match_header(tmp_path):
         for f, _ in cls._fields_:
             lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
             want.append(getattr(cls, f).offset)
+    for name in ("SED_GRID_COPY_FP32", "SED_GRID_COPY_FP32_SIMT", "SED_GRID_COPY_BF16", "SED_GRID_COPY_FP8",
+                 "SED_NOALLOC_SCRATCH_BYTES"):
+        lines.append(f'  printf("%zu\\n", (size_t)({name}));')
+        want.append(getattr(_ffi, name[4:]))
     lines += ["  return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")

@@ -8,9 +8,14 @@ gradient column is a sum over data of u_b dm_b/dtheta with u_b = (d_b - m_b) /
 sigma_b^2, so its error is bounded by a few FP32 roundings of the largest
 terms of the row rather than of the column itself; a column that cancels to
 near zero keeps that absolute error.  The bar is therefore
-    |g_gpu - g_ref| <= GRAD_TOL * max(|g_ref|, 1e-3 * max_j |g_ref_j|)
-with GRAD_TOL = 2e-3 (FP32-grade through ~10^4-term sums and the 1e-3 floor).
+    |g_gpu - g_ref| <= tol * max(|g_ref|, 1e-3 * max_j |g_ref_j|)
+with tol per workload (GRAD_TOL) about three times the worst error measured
+on a GB300 over both FP32 paths (setting SED_TEST_ERR_LOG to a file path
+makes the tests log each row's error there).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -20,7 +25,20 @@ from tests import cases
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-GRAD_TOL = 2e-3
+# worst measured error (both FP32 paths) -> tolerance
+GRAD_TOL = {
+    "tiny": 8e-4,          # 2.4e-4
+    "phot": 4e-4,          # 1.2e-4
+    "specphot": 6e-4,      # 2.1e-4
+    "mixed_lsf": 6e-4,     # 1.8e-4
+    "sigma_gal": 1.5e-3,   # 4.4e-4
+    "calib": 1e-3,         # 3.2e-4
+    "floor": 4e-4,         # 1.1e-4
+    "upper": 1.5e-3,       # 4.4e-4
+    "escape": 6e-4,        # 1.9e-4 (picket), 2.5e-5 (runaway_bc)
+    "linear_sfh": 2e-5,    # 4.9e-6
+    "specphot_fd": 1e-3,   # 3.0e-4
+}
 PRECS = ["fp32", "fp32_simt"]
 
 
@@ -63,7 +81,7 @@ def gpu_grad(model, th32, prec, ld=None):
     return lnl.cpu().numpy(), g.cpu().numpy(), st.cpu().numpy()
 
 
-def check_grad(g_gpu, g_ref, status, tol=GRAD_TOL, skip=None):
+def check_grad(g_gpu, g_ref, status, tol, skip=None):
     """skip: optional {row: column} entries left out (a one-sided derivative at a kink)."""
     ok = status == 0
     assert ok.any()
@@ -75,6 +93,10 @@ def check_grad(g_gpu, g_ref, status, tol=GRAD_TOL, skip=None):
         if skip and r in skip:
             e[skip[r]] = 0.0
         worst = max(worst, e.max())
+        if os.environ.get("SED_TEST_ERR_LOG"):   # measured worst errors, for setting the tolerances
+            with open(os.environ["SED_TEST_ERR_LOG"], "a") as f:
+                f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", "?"), "row": int(r),
+                                    "err": float(e.max()), "col": int(e.argmax())}) + "\n")
         assert e.max() < tol, f"row {r} column {int(e.argmax())}: {g_gpu[r, e.argmax()]} vs {ref[e.argmax()]}"
     return worst
 
@@ -87,7 +109,7 @@ def test_tiny_grad_vs_oracle(ctx, prec):
     lnl, g, st = gpu_grad(model, th32, prec)
     ref = orc.grad(th64)
     assert np.array_equal(st, ref["status"])
-    check_grad(g, ref["grad"], st)
+    check_grad(g, ref["grad"], st, GRAD_TOL["tiny"])
     ok = st == 0
     fwd = orc.eval(th64)
     assert np.allclose(lnl[ok], fwd["lnl"][ok], rtol=1e-5, atol=0)
@@ -104,7 +126,7 @@ def test_paper_scale_phot_grad_sampled_rows(ctx, prec):
     rows = np.unique(np.concatenate([[0, 1023], np.random.default_rng(9).choice(1024, 10, replace=False)]))
     ref = orc.grad(th64[rows])
     assert np.array_equal(st[rows], ref["status"])
-    check_grad(g[rows], ref["grad"], ref["status"])
+    check_grad(g[rows], ref["grad"], ref["status"], GRAD_TOL["phot"])
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -117,7 +139,7 @@ def test_specphot_afe_grad_sampled_rows(ctx, prec):
     rows = np.array([0, 77, 150, 299, 11, 222, 45, 180])
     ref = orc.grad(th64[rows])
     assert np.array_equal(st[rows], ref["status"])
-    check_grad(g[rows], ref["grad"], ref["status"])
+    check_grad(g[rows], ref["grad"], ref["status"], GRAD_TOL["specphot"])
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -139,7 +161,7 @@ def test_mixed_lsf_grad_vs_oracle(ctx, prec):
     lnl, g, st = gpu_grad(model, th32, prec)
     ref = orc.grad(th64)
     assert np.array_equal(st, ref["status"])
-    check_grad(g, ref["grad"], st)
+    check_grad(g, ref["grad"], st, GRAD_TOL["mixed_lsf"])
     ok = st == 0
     assert np.allclose(lnl[ok], orc.eval(th64)["lnl"][ok], rtol=1e-5, atol=0)
 
@@ -162,7 +184,7 @@ def test_sampled_sigma_gal_grad_vs_oracle(ctx, prec):
     # redshift column of rows with a spectral pixel on a model node: a kink
     kinks = {int(r): model.offsets["zred"] for r in np.nonzero(cases.kink_rows(orc, th64))[0]}
     assert len(kinks) < 20
-    check_grad(g, ref["grad"], st, skip=kinks)
+    check_grad(g, ref["grad"], st, GRAD_TOL["sigma_gal"], skip=kinks)
     j = model.offsets["sigma_gal"]
     ok = st == 0
     assert np.abs(ref["grad"][ok, j]).max() > 0      # the column carries a real derivative
@@ -184,7 +206,7 @@ def test_calibration_polynomial_grad_vs_oracle(ctx, prec):
     ref = orc.grad(th64)
     assert np.array_equal(st, ref["status"])
     kinks = {int(r): model.offsets["zred"] for r in np.nonzero(cases.kink_rows(orc, th64))[0]}
-    check_grad(g, ref["grad"], st, skip=kinks)
+    check_grad(g, ref["grad"], st, GRAD_TOL["calib"], skip=kinks)
     ok = st == 0
     fwd = orc.eval(th64)
     # lnL within 1e-5 of the magnitude of its terms (it can cancel to ~0)
@@ -208,7 +230,7 @@ def test_noise_floor_grad_vs_oracle(ctx, prec):
     ref = orc.grad(th64)
     assert np.array_equal(st, ref["status"])
     kinks = {int(r): model.offsets["zred"] for r in np.nonzero(cases.kink_rows(orc, th64))[0]}
-    check_grad(g, ref["grad"], st, skip=kinks)
+    check_grad(g, ref["grad"], st, GRAD_TOL["floor"], skip=kinks)
     ok = st == 0
     fwd = orc.eval(th64)
     scale = cases.lnl_scale(orc, fwd)[ok]
@@ -233,7 +255,7 @@ def test_upper_limits_grad_vs_oracle(ctx, prec):
     ref = orc.grad(th64)
     assert np.array_equal(st, ref["status"])
     kinks = {int(r): model.offsets["zred"] for r in np.nonzero(cases.kink_rows(orc, th64))[0]}
-    check_grad(g, ref["grad"], st, skip=kinks)
+    check_grad(g, ref["grad"], st, GRAD_TOL["upper"], skip=kinks)
     ok = st == 0
     fwd = orc.eval(th64)
     exceeded, respected = cases.limit_regimes(orc, fwd["phot"][ok])
@@ -261,7 +283,7 @@ def test_escape_geometry_grad_vs_central_differences(ctx, geometry):
     ok = st == 0
     assert ok.sum() >= 12
     fd = orc.grad_fd(th64, h_rel=1e-7)
-    check_grad(g, fd[:, :orc.n_param], st)
+    check_grad(g, fd[:, :orc.n_param], st, GRAD_TOL["escape"])
     assert np.abs(g[ok, model.offsets["frac_obrun"]]).max() > 0
     ref = orc.eval(th64)
     assert (np.abs(lnl[ok] - ref["lnl"][ok]) / cases.lnl_scale(orc, ref)[ok]).max() < 1e-5
@@ -300,7 +322,7 @@ def test_linear_sfh_grad_vs_central_differences(ctx, zmode):
     ok = st == 0
     assert ok.sum() >= 8
     fd = central_differences(orc, th64[ok])
-    check_grad(g[ok], fd[:, :orc.n_param], st[ok])
+    check_grad(g[ok], fd[:, :orc.n_param], st[ok], GRAD_TOL["linear_sfh"])
     ref = orc.eval(th64)
     assert (np.abs(lnl[ok] - ref["lnl"][ok]) / cases.lnl_scale(orc, ref)[ok]).max() < 1e-5
 
@@ -312,7 +334,7 @@ def test_specphot_grad_vs_central_differences(ctx):
     th32, th64 = cases.theta_pair(w, 16, seed=54)
     lnl, g, st = gpu_grad(model, th32, "fp32")
     fd = orc.grad_fd(th64, h_rel=1e-7)
-    check_grad(g, fd[:, :orc.n_param], st)
+    check_grad(g, fd[:, :orc.n_param], st, GRAD_TOL["specphot_fd"])
 
 
 def test_grad_bad_rows_padding_and_determinism(ctx):

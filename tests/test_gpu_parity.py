@@ -480,3 +480,90 @@ def test_model_descriptor_validation(ctx):
     assert ok.n_param == orc.n_param + 1 + 2
     esc = ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **base, fesc_geometry=2)
     assert esc.n_param == orc.n_param + 1 and esc.offsets["frac_obrun"] == orc.n_param
+
+
+def test_fixed_keys_match_the_sampled_model(ctx):
+    """Keys fixed in the model descriptor (the paper's fixed vs sampled keys,
+    Sec. 4) leave the parameter rows and the gradient, and give the same
+    lnL, model and remaining gradient columns as the sampled model whose rows
+    carry the same values, bit for bit; the redshift fixed too (the calls then
+    keep the caller's row order).  lnL against the oracle on the full rows."""
+    w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4,
+                     n_lam=1500, n_sfh=10, n_pix=240, batch=150)
+    orc = cases.oracle_for(w)
+    full = cases.gpu_model_for(ctx, orc, w)
+    fixed = {"logzsol": np.float32(-0.3), "afe": np.float32(0.15), "zred": np.float32(1.75),
+             "diffuse_dust_index": np.float32(-0.4), "alpha_pow": np.float32(-1.0)}
+    fix = cases.gpu_model_for(ctx, orc, w, fixed={k: float(v) for k, v in fixed.items()})
+    assert fix.n_param == full.n_param - len(fixed)
+    for k in fixed:   # zero width in the fixed model's layout
+        i = list(fix.offsets).index(k)
+        nxt = list(fix.offsets.values())[i + 1] if i + 1 < len(fix.offsets) else fix.n_param
+        assert fix.offsets[k] == nxt
+    th32, th64 = cases.theta_pair(w, w.batch, seed=71)
+    for k, v in fixed.items():
+        th32[:, full.offsets[k]] = v
+    th64 = th32.astype(np.float64)
+    keep = np.ones(full.n_param, bool)
+    keep[[full.offsets[k] for k in fixed]] = False
+    t_full = torch.from_numpy(th32).cuda()
+    t_fix = torch.from_numpy(np.ascontiguousarray(th32[:, keep])).cuda()
+    for prec in ("fp32", "bf16"):
+        a = run_gpu(full, th32, prec)
+        b = run_gpu(fix, np.ascontiguousarray(th32[:, keep]), prec)
+        for key in ("lnl", "status", "phot", "spec"):
+            assert np.array_equal(a[key], b[key]), (prec, key)
+    la, ga, sa = full.loglike_grad(t_full, "fp32")
+    lb, gb, sb = fix.loglike_grad(t_fix, "fp32")
+    torch.cuda.synchronize()
+    assert np.array_equal(la.cpu().numpy(), lb.cpu().numpy())
+    assert np.array_equal(ga.cpu().numpy()[:, keep], gb.cpu().numpy())
+    ref = orc.eval(th64)
+    check(ref, run_gpu(fix, np.ascontiguousarray(th32[:, keep]), "fp32"), "fp32", orc=orc)
+    # what cannot be fixed
+    from paper_2609_30145_gb300.api import SedError
+    for bad in ({"sfh": 0.1}, {"sigma_gal": 100.0}, {"log_jitter_phot": -3.0}, {"logmass": float("nan")}):
+        with pytest.raises(SedError) as e:
+            cases.gpu_model_for(ctx, orc, w, fixed=bad)
+        assert e.value.status == 1, bad
+    w0 = synth.shrink(synth.WORKLOADS["tiny_phot_16x4x512"], batch=8)   # per-bin [Fe/H]: logzsol has N_T columns
+    orc0 = cases.oracle_for(w0)
+    with pytest.raises(SedError):
+        cases.gpu_model_for(ctx, orc0, w0, fixed={"logzsol": 0.0})
+
+
+def test_grid_precision_mask_keeps_only_the_named_copies(ctx):
+    """A grid loaded with precision_mask keeps only those operand copies: a
+    BF16-only grid takes less device memory, refuses the other precisions
+    (SED_EUNSUPPORTED) and gives the default grid's BF16 results bit for bit; an
+    FP8 copy asked for at load gives the FP8 results of the copy that the
+    default grid builds on first use."""
+    from paper_2609_30145_gb300 import _ffi
+    from paper_2609_30145_gb300.api import SedError
+    w = synth.shrink(synth.WORKLOADS["phot_107x12x6000_b1024"], n_age=30, n_feh=6, n_lam=2000, n_sfh=20,
+                     batch=200)
+    orc = cases.oracle_for(w)
+    ref_model = cases.gpu_model_for(ctx, orc, w)
+    th32, _ = cases.theta_pair(w, w.batch, seed=73)
+    want = {p: run_gpu(ref_model, th32, p) for p in ("bf16", "fp8")}
+    kw = dict(use_nebular=w.use_nebular, dust_law=w.dust_law, filters=orc.filters, phot_d=orc.phot_d,
+              phot_sigma=orc.phot_sigma, phot_mask=orc.phot_mask, H0=orc.H0, Om0=orc.Om0)
+    before = ctx.memory_used()
+    ctx.create_model(ctx.load_grid(orc.grid), w.n_sfh, w.zf, w.zmode, **kw)
+    grown_default = ctx.memory_used() - before
+    for mask, precs in ((_ffi.GRID_COPY_BF16, ("bf16",)), (_ffi.GRID_COPY_FP8, ("fp8",))):
+        before = ctx.memory_used()
+        gid = ctx.load_grid(orc.grid, precision_mask=mask)
+        m = ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, **kw)
+        grown = ctx.memory_used() - before
+        for p in ("fp32", "fp32_simt", "bf16", "fp8"):
+            if p in precs:
+                got = run_gpu(m, th32, p)
+                for key in ("lnl", "status", "phot"):
+                    assert np.array_equal(got[key], want[p][key]), (mask, p, key)
+            else:
+                with pytest.raises(SedError) as e:
+                    m.loglike(torch.from_numpy(th32).cuda(), p)
+                assert e.value.status == _ffi.SED_EUNSUPPORTED, (mask, p)
+        # one copy of 2 (BF16) or 1 (FP8) bytes per element instead of 8 + 4 + 2
+        assert grown < 0.3 * grown_default, (mask, grown, grown_default)
