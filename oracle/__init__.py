@@ -58,7 +58,7 @@ class _Model(C.Structure):
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", C.c_void_p),
                 ("sfh_scheme", C.c_int), ("floor_phot", C.c_int), ("floor_spec", C.c_int),
-                ("phot_upper", C.c_void_p), ("fesc_geometry", C.c_int)]
+                ("phot_upper", C.c_void_p), ("fesc_geometry", C.c_int), ("calib_mode", C.c_int)]
 
 
 def _load():
@@ -123,7 +123,8 @@ class Oracle:
     z_ref: float = 0.0
     sample_sigma_gal: int = 0           # 1: sigma_gal (km/s) is the last parameter column
     sigma_gal_max_kms: float = 1000.0   # sampled sigma_gal must lie in [0, this]
-    calib_sigma: np.ndarray | None = None   # prior widths s_m of a marginalised calibration polynomial
+    calib_sigma: np.ndarray | None = None   # prior widths s_m of the calibration polynomial's coefficients
+    calib_mode: int = 0                 # 0 marginalised (Eq. app_polymarg), 1 optimised at each call
     sfh_scheme: int = 0                 # 0 step (N_T bin masses), 1 linear (N_T + 1 edge SFRs; App. B)
     floor_phot: int = 0                 # noise-floor terms of each arm (App. sys_floor): FLOOR_* bits
     floor_spec: int = 0
@@ -197,6 +198,7 @@ class Oracle:
         m.floor_phot, m.floor_spec = int(self.floor_phot), int(self.floor_spec)
         m.sfh_scheme = int(self.sfh_scheme)
         m.fesc_geometry = int(self.fesc_geometry)
+        m.calib_mode = int(self.calib_mode)
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):

@@ -600,8 +600,11 @@ void orc_spectrum(const orc_grid *g, const orc_model *md, const double *lam_rest
  * the coefficients integrate out and lnL gains
  *   b^T M^-1 b / 2 - ln|M| / 2 - ln|Lambda| / 2,
  *   M = D^T C^-1 D + Lambda^-1,  b = D^T C^-1 r,  D = diag(mu) A,  A_im = T_m(x_i),
- * r = d - mu, C = diag(sigma^2), over the included pixels inc[i] != 0.  Returns
- * these terms; minv [n][n] = M^-1 and cstar [n] = M^-1 b when non-NULL. */
+ * r = d - mu, C = diag(sigma^2), over the included pixels inc[i] != 0.  With
+ * the polynomial optimised instead (calib_mode ORC_CALIB_OPTIMISED) the gain is
+ * b^T M^-1 b / 2 alone: the maximum over c of lnL_diag(r - D c) - c^T
+ * Lambda^-1 c / 2, reached at c = M^-1 b.  Returns these terms; minv [n][n] =
+ * M^-1 and cstar [n] = M^-1 b when non-NULL. */
 static void cheb_row(double x, int n, double *T) {
   T[0] = 1.0;
   if (n > 1) T[1] = x;
@@ -663,7 +666,9 @@ static double calib_terms(const orc_model *md, const double *mu, const unsigned 
     }
     double quad = 0.0;
     for (int a = 0; a < n; a++) quad += b[a] * c[a];
-    out = 0.5 * quad - 0.5 * logdet - 0.5 * logdet_lam;
+    /* optimised polynomial: max over c of lnL_diag(r - D c) - c^T Lambda^-1 c / 2
+     * = lnL_diag(r) + b^T M^-1 b / 2; marginalised: minus the Occam terms */
+    out = md->calib_mode == ORC_CALIB_OPTIMISED ? 0.5 * quad : 0.5 * quad - 0.5 * logdet - 0.5 * logdet_lam;
     if (cstar) memcpy(cstar, c, n * sizeof(double));
     if (minv) {
       double *e = (double *)malloc(n * sizeof(double));
@@ -1091,6 +1096,9 @@ int orc_row_grad(const orc_grid *g, const orc_model *md, const double *theta, do
           p += cst[a] * T[a];
           for (int e = 0; e < nc; e++) q += T[a] * minv[a * nc + e] * T[e];
         }
+        /* the optimised polynomial has no ln|M| term: c* is stationary, so only
+         * the explicit dependence on mu_i remains (q_i comes from -ln|M|/2) */
+        if (md->calib_mode == ORC_CALIB_OPTIMISED) q = 0.0;
         ui = ((md->spec_d[i] - sp[i] * (1.0 + p)) * (1.0 + p) - sp[i] * q) / (s * s);
       }
       /* Eq. "app_response" row of pixel i, as in orc_spectrum */

@@ -71,7 +71,17 @@ typedef struct {
                                       Eq. "app_line_chi2_UL"), or NULL (none) */
   int fesc_geometry;           /* ionising-photon escape (Sec. "frac_obrun"): ORC_FESC_*; with a geometry the
                                   row's last column is the runaway fraction f_ob in [0, 1] */
+  int calib_mode;              /* ORC_CALIB_MARGINAL (Eq. "app_polymarg") or ORC_CALIB_OPTIMISED (the
+                                  polynomial optimised at each call, Sec. 3.2 / App. E) */
 } orc_model;
+/* The calibration polynomial of the spectrum, App. E.  MARGINAL integrates the
+ * coefficients out under their Gaussian prior (Eq. "app_polymarg").  OPTIMISED
+ * takes, at every evaluation, the coefficients that maximise the spectrum's
+ * lnL plus their log prior (the weighted least-squares solve regularised by
+ * 1/s_m, whose solution is the mean M^-1 b of the marginal form): lnL gains
+ * b^T M^-1 b / 2 and no Occam terms. */
+#define ORC_CALIB_MARGINAL 0
+#define ORC_CALIB_OPTIMISED 1
 
 /* Escape geometries of the young light, Sec. "frac_obrun" */
 #define ORC_FESC_NONE 0

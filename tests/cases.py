@@ -18,10 +18,11 @@ def z_column(n_sfh, zmode, sfh_scheme=0):
 
 
 def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_theta=4, lsf_r=None,
-               spec_mask=None, sigma_gal_kms=None, calib_sigma=None):
+               spec_mask=None, sigma_gal_kms=None, calib_sigma=None, calib_mode=0):
     """lsf_r, spec_mask, sigma_gal_kms: optional replacements of the
     workload's R_fwhm curve, pixel mask and stellar dispersion; calib_sigma:
-    prior widths of a marginalised calibration polynomial (App. E)."""
+    prior widths of a calibration polynomial (App. E), marginalised
+    (calib_mode 0) or optimised at each call (1)."""
     grid = grid if grid is not None else synth.make_grid(**w.grid_kw, seed=1)
     filt = filters if filters is not None else synth.pack_filters(synth.workload_filters(w))
     kw = dict(grid=grid, n_sfh=w.n_sfh, zf=w.zf, zmode=w.zmode, use_afe=w.use_afe,
@@ -37,7 +38,8 @@ def oracle_for(w: synth.Workload, grid=None, filters=None, with_data=True, seed_
                   spec_mask=np.ones(lam.size, np.uint8) if spec_mask is None else spec_mask, lsf_mode=0,
                   lsf_value=r if lsf_r is None else lsf_r,
                   sigma_gal_kms=w.sigma_gal_kms if sigma_gal_kms is None else sigma_gal_kms, z_ref=w.z_ref,
-                  calib_sigma=None if calib_sigma is None else np.asarray(calib_sigma, dtype=np.float64))
+                  calib_sigma=None if calib_sigma is None else np.asarray(calib_sigma, dtype=np.float64),
+                  calib_mode=calib_mode)
     orc = oracle.Oracle(**kw)
     if with_data:
         d_true = synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99)
@@ -100,7 +102,8 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True, fixed=None):
         kw.update(spec_lam=orc.spec_lam, spec_d=orc.spec_d if with_spec_data else None,
                   spec_sigma=orc.spec_sigma if with_spec_data else None,
                   spec_mask=orc.spec_mask, lsf_mode=orc.lsf_mode, lsf_value=orc.lsf_value,
-                  sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref, calib_sigma=orc.calib_sigma)
+                  sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref, calib_sigma=orc.calib_sigma,
+                  calib_mode=orc.calib_mode)
     return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, fixed=fixed, **kw)
 
 
@@ -151,11 +154,12 @@ def kink_rows(orc, th64, rel=2e-4):
     return out
 
 
-def calib_case(w: synth.Workload, calib_sigma):
-    """Oracle of a workload with a marginalised calibration polynomial and data
-    carrying a smooth multiplicative distortion (1 + 0.08 x - 0.05 T_2(x)) over
-    the spectrum's Chebyshev coordinate x, the kind the polynomial absorbs."""
-    orc = oracle_for(w, calib_sigma=calib_sigma)
+def calib_case(w: synth.Workload, calib_sigma, calib_mode=0):
+    """Oracle of a workload with a calibration polynomial (marginalised, or
+    optimised with calib_mode 1) and data carrying a smooth multiplicative
+    distortion (1 + 0.08 x - 0.05 T_2(x)) over the spectrum's Chebyshev
+    coordinate x, the kind the polynomial absorbs."""
+    orc = oracle_for(w, calib_sigma=calib_sigma, calib_mode=calib_mode)
     lam = np.asarray(orc.spec_lam)
     x = (2.0 * lam - (lam[0] + lam[-1])) / (lam[-1] - lam[0])
     dist = 1.0 + 0.08 * x - 0.05 * (2 * x * x - 1)

@@ -8,7 +8,11 @@ Gaussian prior on the coefficients, integrated out in closed form.
   integrated by quadrature with numpy, plus the photometric terms.
 - s_m -> 0 gives back the uncalibrated lnL (the paper states this limit).
 - The gradient with the calibration on is pinned by central differences in
-  test_oracle_grad.py (shape "calib_spec").
+  test_oracle_grad.py (shapes "calib_spec" and "calib_opt_spec").
+- The optimised polynomial (calib_mode 1; App. E: the mean of the marginal
+  form is the optimised polynomial regularised by 1/s_m): lnL is the maximum
+  over the coefficients from numpy's least-squares solver, and it exceeds the
+  marginal lnL by exactly the Occam terms ln|M|/2 + ln|Lambda|/2.
 """
 import math
 
@@ -92,3 +96,60 @@ def test_calibration_raises_the_likelihood_of_a_miscalibrated_model():
     orc_c.set_data(phot_d=orc_0.phot_d, phot_sigma=orc_0.phot_sigma, spec_d=d, spec_sigma=sig)
     a, b = orc_c.eval(th)["lnl"][0], orc_0.eval(th)["lnl"][0]
     assert a > b + 100.0
+
+
+def _lnl_parts(orc_0, th, r):
+    """The spectrum's uncalibrated model, its data and the photometric lnL terms."""
+    b = orc_0.eval(th)
+    mu = b["spec"][r]
+    d, sig = np.asarray(orc_0.spec_d), np.asarray(orc_0.spec_sigma)
+    lnl_spec0 = np.sum(-0.5 * ((d - mu) / sig) ** 2 - 0.5 * np.log(2 * np.pi * sig ** 2))
+    return mu, d, sig, b["lnl"][r] - lnl_spec0
+
+
+@pytest.mark.parametrize("s", [[1e6] * 4, [0.3, 0.2, 0.1]])
+def test_optimised_polynomial_is_the_regularised_least_squares_maximum(s):
+    """The optimised polynomial (calib_mode 1): lnL is the maximum over the
+    coefficients of lnL_diag(d - mu (1 + A c)) - c^T Lambda^-1 c / 2, found here
+    by numpy's least-squares solver on the stacked system [C^-1/2 D; Lambda^-1/2]
+    c = [C^-1/2 r; 0] -- with very wide priors, the plain weighted fit of
+    Johnson et al. that the paper follows."""
+    orc_o = cases.oracle_for(W_SMALL, calib_sigma=s, calib_mode=1)
+    orc_0 = cases.oracle_for(W_SMALL)
+    th = cases.theta_rows(W_SMALL, 3, seed=74)
+    a = orc_o.eval(th)
+    lam = np.asarray(orc_0.spec_lam)
+    x = (2.0 * lam - (lam[0] + lam[-1])) / (lam[-1] - lam[0])
+    A = cheb(x, len(s))
+    for r in range(th.shape[0]):
+        mu, d, sig, lnl_rest = _lnl_parts(orc_0, th, r)
+        Dw = mu[:, None] * A / sig[:, None]
+        rw = (d - mu) / sig
+        G = np.vstack([Dw, np.diag(1.0 / np.asarray(s))])
+        c = np.linalg.lstsq(G, np.concatenate([rw, np.zeros(len(s))]), rcond=None)[0]
+        resid = (d - mu * (1.0 + A @ c)) / sig
+        want = (np.sum(-0.5 * resid ** 2 - 0.5 * np.log(2 * np.pi * sig ** 2)) - 0.5 * np.sum((c / np.asarray(s)) ** 2)
+                + lnl_rest)
+        assert abs(a["lnl"][r] - want) < 1e-7 * max(1.0, abs(want)), (r, a["lnl"][r], want)
+
+
+def test_optimised_and_marginalised_differ_by_the_occam_terms():
+    """lnL(optimised) - lnL(marginalised) = ln|M| / 2 + ln|Lambda| / 2 (Eq.
+    app_polymarg's last two terms), with M = D^T C^-1 D + Lambda^-1 from numpy."""
+    s = [0.2, 0.1, 0.1, 0.05]
+    orc_o = cases.oracle_for(W_SMALL, calib_sigma=s, calib_mode=1)
+    orc_m = cases.oracle_for(W_SMALL, calib_sigma=s)
+    orc_0 = cases.oracle_for(W_SMALL)
+    th = cases.theta_rows(W_SMALL, 3, seed=75)
+    lo, lm = orc_o.eval(th)["lnl"], orc_m.eval(th)["lnl"]
+    lam = np.asarray(orc_0.spec_lam)
+    x = (2.0 * lam - (lam[0] + lam[-1])) / (lam[-1] - lam[0])
+    A = cheb(x, len(s))
+    for r in range(th.shape[0]):
+        mu, d, sig, _ = _lnl_parts(orc_0, th, r)
+        Dw = mu[:, None] * A / sig[:, None]
+        M = Dw.T @ Dw + np.diag(1.0 / np.asarray(s) ** 2)
+        want = 0.5 * np.linalg.slogdet(M)[1] + 0.5 * np.sum(np.log(np.asarray(s) ** 2))
+        # both lnL are large for random rows (far from the data): the difference
+        # carries their FP64 rounding
+        assert lo[r] - lm[r] == pytest.approx(want, rel=1e-8, abs=1e-8 + 4e-16 * abs(lm[r]))
