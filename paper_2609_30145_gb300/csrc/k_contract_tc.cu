@@ -144,8 +144,29 @@ struct Params {
   float* O2;                 // forward with gridDim.z == 3: second half of the old part
   const int* tile_win;       // forward, persistent schedule: [2][m_tiles] window (lo, hi) of each M tile
   int m_tiles;
+  const uint32_t* kmask;     // [m_tiles][kmask_w] K tiles some row of the M tile touches (NULL: all);
+  int kmask_w;               // adjoint: 32-column tiles of dW's columns
   int* err;
 };
+
+// K tiles of a unit's range.  A K tile that no row of the M tile touches holds
+// zero weights in every row, so its products are exact zeros: it is neither
+// loaded nor multiplied.  The accumulation groups stay at their fixed places
+// (G tiles from the start of the range), and a group with no touched tile is
+// skipped as a whole, so every output element is the same sum, rounded the same
+// way, as without skipping -- whichever rows share its tile.
+__device__ __forceinline__ int knext(const uint32_t* km, int kt, int end) {
+  if (!km) return kt < end ? kt : end;
+  while (kt < end) {
+    const uint32_t w = km[kt >> 5] >> (kt & 31);
+    if (w) {
+      kt += __ffs(w) - 1;
+      return kt < end ? kt : end;
+    }
+    kt = (kt | 31) + 1;
+  }
+  return end;
+}
 
 constexpr int BM = 128;
 constexpr int ROWB = 128;  // bytes of one operand row in a K tile
@@ -198,6 +219,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 constexpr int MAX_MT = 64;   // M tiles of a persistent launch (8192 rows)
 
 struct Unit {
+  const uint32_t* km;        // K-tile mask row of the unit's M tile (NULL: every K tile)
   int m0, n0, nr;
   int ncol;                  // columns of the tile that are stored (a multiple of 4)
   int rb[2], re[2];
@@ -218,7 +240,9 @@ __device__ __forceinline__ void unit_ranges(const Params& p, int z, int nz, int 
   }
 }
 
-template <int PREC, int BN, int STAGES, int G, bool GRAD>
+// KSKIP: the forward with K-tile masks (an instance of its own, so that the
+// unmasked loops carry no mask test)
+template <int PREC, int BN, int STAGES, int G, bool GRAD, bool KSKIP = false>
 __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ Params p) {
   pdl_enter();
   using C = Cfg<PREC, BN, STAGES, G, GRAD>;
@@ -286,12 +310,28 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     if constexpr (!GRAD) {
       if (n0 > khi || n0 + BN - 1 < klo) return;
     } else {
-      K0 = klo / 32;
+      // the reduction over lambda covers the union of the tile's row windows
+      // (dlnL/dY and dlnL/dO are zero outside each row's own); its start is
+      // rounded down to a whole accumulation group, so that the groups sit at
+      // the same wavelengths whichever rows share the tile and every row's dW
+      // is the same sum, rounded the same way
+      K0 = (klo / 32) / G * G;
       KT = min(p.k_tiles, khi / 32 + 1);
       KY = KT;
+      if (p.kmask) {   // dW columns of this tile: none touched by the tile's rows -> not needed
+        const int t = (int)blockIdx.x;
+        const int c0 = t < p.ny_tiles ? t * BN : p.n_split + (t - p.ny_tiles) * BN;
+        const int c1 = min(c0 + BN, t < p.ny_tiles ? p.n_split : p.ld_out);
+        if (knext(p.kmask + (size_t)blockIdx.y * p.kmask_w, c0 / 32, (c1 + 31) / 32) >= (c1 + 31) / 32) return;
+      }
     }
   }
   if (n_units == 0) return;
+  // next touched K tile at or after kt in [kt, end), or end
+  auto kn = [](const uint32_t* km, int kt, int end) {
+    if constexpr (KSKIP) return knext(km, kt, end);
+    else return kt < end ? kt : end;
+  };
 
   // unit j of this CTA
   auto get_unit = [&](int j, Unit& u) {
@@ -312,12 +352,15 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       int m = 0;
       while (s_pref[m + 1] <= t) ++m;
       u.m0 = m * BM;
+      u.km = KSKIP ? p.kmask + m * p.kmask_w : nullptr;   // read through L1 (a few words per M tile)
       if (t >= nfull) u.ncol = BN / npc;   // a piece of a leftover tile
       u.n0 = (s_nlo[m] + t - s_pref[m]) * BN + pc * u.ncol;
     } else {
       u.m0 = blockIdx.y * BM;
       u.n0 = blockIdx.x * BN;
+      u.km = KSKIP ? p.kmask + (size_t)blockIdx.y * p.kmask_w : nullptr;
     }
+    if constexpr (GRAD) u.km = nullptr;   // the adjoint reduces over lambda
     if constexpr (GRAD) {
       const int t = (int)blockIdx.x;
       u.n0 = t < p.ny_tiles ? t * BN : p.n_split + (t - p.ny_tiles) * BN;
@@ -365,7 +408,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         const CUtensorMap* amap_lo = &p.a_lo;
         if (GRAD && u.n0 >= p.n_split) { amap_hi = &p.a2_hi; amap_lo = &p.a2_lo; }
         for (int r = 0; r < u.nr && ok; ++r)
-          for (int kt = u.rb[r]; kt < u.re[r]; ++kt, ++it) {
+          for (int kt = kn(u.km, u.rb[r], u.re[r]); kt < u.re[r]; kt = kn(u.km, kt + 1, u.re[r]), ++it) {
             const int s = it % STAGES;
             const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
             if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { atomicOr(p.err, 1); ok = false; break; }
@@ -395,13 +438,15 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         const uint32_t ID = idesc(FMT, BM, (uint32_t)u.ncol);   // N = the unit's columns
         for (int r = 0; r < u.nr && ok; ++r) {
           const int kb = u.rb[r], ke = u.re[r];
-          for (int gs = kb; gs < ke && ok; gs += G, ++g) {
+          for (int gs = kb; gs < ke && ok; gs += G) {
+            const int ge = gs + G < ke ? gs + G : ke;
+            const int k_first = kn(u.km, gs, ge);
+            if (KSKIP && k_first >= ge) continue;   // no touched K tile in this group
             const int b = g & 1;
             if (!mbar_wait(tempty0 + 8 * b, (((uint32_t)g >> 1) & 1u) ^ 1u)) { atomicOr(p.err, 8); ok = false; break; }
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(b * BN);
-            const int ge = gs + G < ke ? gs + G : ke;
-            for (int kt = gs; kt < ge; ++kt, ++it) {
+            for (int kt = k_first; kt < ge; kt = kn(u.km, kt + 1, ge), ++it) {
               const int s = it % STAGES;
               const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
               if (!mbar_wait(full0 + 8 * s, ph)) { atomicOr(p.err, 2); ok = false; break; }
@@ -410,7 +455,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
               const uint32_t a_hi = st, b_hi = st + C::A_BYTES;
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk) {   // 4 MMAs of 32 bytes of K each
-                const uint32_t acc = (kt == gs && kk == 0) ? 0u : 1u;
+                const uint32_t acc = (kt == k_first && kk == 0) ? 0u : 1u;
                 const uint64_t da = sdesc(a_hi + kk * 32), db = sdesc(b_hi + kk * 32);
                 if constexpr (C::NOPS == 2) {
                   const uint32_t a_lo = st + C::A_BYTES + C::B_BYTES, b_lo = a_lo + C::A_BYTES;
@@ -424,6 +469,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
               mma_commit(empty0 + 8 * s);
             }
             if (ok) mma_commit(tfull0 + 8 * b);
+            ++g;
           }
         }
       }
@@ -444,7 +490,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         float run[BN];
 #pragma unroll
         for (int c = 0; c < BN; ++c) run[c] = 0.f;
-        for (int gs = kb; gs < ke; gs += G, ++g) {
+        for (int gs = kb; gs < ke; gs += G) {
+          if (KSKIP && knext(u.km, gs, gs + G < ke ? gs + G : ke) >= (gs + G < ke ? gs + G : ke)) continue;
           const int b = g & 1;
           if (ok && !mbar_wait(tfull0 + 8 * b, ((uint32_t)g >> 1) & 1u)) { atomicOr(p.err, 4); ok = false; }
           tc_fence_after();
@@ -462,6 +509,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+          ++g;
         }
         if (row < p.n) {
           float4* dst = reinterpret_cast<float4*>(u.out[r] + (size_t)row * p.ld_out + u.n0);
@@ -480,12 +528,12 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
   }
 }
 
-template <int PREC, int BN, int STAGES, int G, bool GRAD>
+template <int PREC, int BN, int STAGES, int G, bool GRAD, bool KSKIP = false>
 cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
   const int nz = (!GRAD && p.O2) ? 3 : 1;
   const int n_sm = device_sm_count();
   using C = Cfg<PREC, BN, STAGES, G, GRAD>;
-  auto k = k_contract_tc<PREC, BN, STAGES, G, GRAD>;
+  auto k = k_contract_tc<PREC, BN, STAGES, G, GRAD, KSKIP>;
   static DynSmemCache attr;   // the raised shared-memory limit, set once per device
   if (cudaError_t e = ensure_dyn_smem(k, (size_t)C::SMEM, &attr)) return e;
   if (!GRAD && p.tile_win) return launch_pdl(k, dim3(n_sm, 1, 1), dim3(C::THREADS), C::SMEM, s, p);   // persistent: one CTA per SM
@@ -551,11 +599,15 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   p.Y = a.Y; p.O = a.O; p.O2 = a.prec == SED_PREC_FP32 ? a.O2 : nullptr; p.err = a.err;
   p.m_tiles = (a.n + tc::BM - 1) / tc::BM;
   p.tile_win = (a.tile_win && p.m_tiles <= tc::MAX_MT) ? a.tile_win : nullptr;
+  // K-tile masks: the 3xTF32 forward only (the host gives no other precision any)
+  p.kmask = a.prec == SED_PREC_FP32 && a.kmask_w > 0 && a.kmask_w <= KMASK_WORDS ? a.kmask : nullptr;
+  p.kmask_w = a.kmask_w;
   const bool wide = tc_bn_for(a.prec, a.Kpad) == 128;   // same choice as the box of the B map
   if (a.prec == SED_PREC_FP32) {
     p.ky_tiles = a.Ky_pad / 32;
     p.k_tiles = a.Kpad / 32;
-    return tc::launch_cfg<SED_PREC_FP32, 128, 3, 8, false>(p, a.ldn, s);
+    return p.kmask ? tc::launch_cfg<SED_PREC_FP32, 128, 3, 8, false, true>(p, a.ldn, s)
+                   : tc::launch_cfg<SED_PREC_FP32, 128, 3, 8, false>(p, a.ldn, s);
   }
   if (a.prec == SED_PREC_FP8) {
     p.ky_tiles = a.Ky_pad / 128;
@@ -598,6 +650,8 @@ cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s) {
   const int no_tiles = (a.Kpad - a.Ky_pad + DW_BN - 1) / DW_BN;
   p.ld_out = a.Kpad;
   p.Y = a.dW; p.O = nullptr; p.err = a.err;
+  p.kmask = a.kmask_w > 0 && a.kmask_w <= KMASK_WORDS ? a.kmask : nullptr;
+  p.kmask_w = a.kmask_w;
   return tc::launch_cfg<SED_PREC_FP32, DW_BN, 3, 8, true>(p, (p.ny_tiles + no_tiles) * DW_BN, s);
 }
 

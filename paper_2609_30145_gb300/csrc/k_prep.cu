@@ -318,36 +318,94 @@ struct PrepKernelArgs {
 };
 
 // Processing order: rows grouped by redshift within chunks of ORDER_CHUNK rows
-// (one CTA per chunk, counting sort into ORDER_BINS redshift bins; rows with
-// an invalid redshift go last).  Rows that are close in redshift need the same
+// (one CTA per chunk, counting sort into ORDER_BINS bins; rows with an invalid
+// redshift go last).  Rows that are close in redshift need the same
 // rest-frame wavelengths, so a 128-row tile of grouped rows spans a narrow node
 // window and the contraction skips the wavelength tiles no row of the tile
-// reads.  The order within a bin follows shared-memory atomics and may change
-// from call to call; no row's result depends on the order or on which rows
-// share its tile.
+// reads.  With one constant [Fe/H] (and [a/Fe]) per row, a row's weights sit
+// in the four (a/Fe, Fe/H) blocks of its bracket pair: the rows are then
+// grouped by that pair first and by redshift within it, so a 128-row tile
+// touches few K tiles and the contraction skips the rest (K-tile masks).
+// The order within a bin follows shared-memory atomics and may change from
+// call to call; no row's result depends on the order or on which rows share
+// its tile.
 constexpr int ORDER_CHUNK = 4096;
 constexpr int ORDER_THREADS = 1024;
 constexpr int ORDER_BINS = 1024;
 
-__global__ void __launch_bounds__(ORDER_THREADS) k_order(const float* theta, int n, int ld, int zoff, float zf,
-                                                         float scale, int* perm) {
+struct OrderArgs {
+  const float* theta;
+  int n, ld;
+  int* perm;
+  ModelDev md;
+  int by_pair;       // 1: two redshift halves, bracket pair, then redshift
+  int n_pairs;       // bracket pairs (by_pair)
+};
+
+__global__ void __launch_bounds__(ORDER_THREADS) k_order(const __grid_constant__ OrderArgs oa) {
   pdl_enter();
   __shared__ int cnt[ORDER_BINS + 1];
   __shared__ int wsum[ORDER_THREADS / 32];
+  const ModelDev& md = oa.md;
   const int base = blockIdx.x * ORDER_CHUNK;
-  const int m = min(ORDER_CHUNK, n - base);
+  const int m = min(ORDER_CHUNK, oa.n - base);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float zf = (float)md.zf;
+  const int zoff = md.offs[SED_KEY_ZRED];
+  __shared__ int s_zlo, s_zhi;   // redshift range of the chunk's valid rows (float bits: z >= 0)
   for (int b = tid; b <= ORDER_BINS; b += ORDER_THREADS) cnt[b] = 0;
+  if (tid == 0) { s_zlo = 0x7f7fffff; s_zhi = 0; }
   __syncthreads();
   constexpr int PER = ORDER_CHUNK / ORDER_THREADS;
   int bin[PER];
+  float zv[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int i = tid + u * ORDER_THREADS;
+    zv[u] = -1.f;
+    if (i < m) {
+      const float z = oa.theta[(size_t)(base + i) * oa.ld + zoff];
+      if (z >= 0.f && z < zf) zv[u] = z;
+    }
+  }
+  {
+    // range of the valid redshifts (z >= 0: their float bits order like ints),
+    // one shared atomic per warp
+    int lo = 0x7f7fffff, hi = 0;
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (zv[u] >= 0.f) { lo = min(lo, __float_as_int(zv[u])); hi = max(hi, __float_as_int(zv[u])); }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) { atomicMin(&s_zlo, lo); atomicMax(&s_zhi, hi); }
+  }
+  __syncthreads();
+  // bins over the chunk's own redshift range: by_pair, two halves of it, the
+  // bracket pair, then fine redshift bins; else fine redshift bins only
+  const float zlo = __int_as_float(s_zlo), zr = fmaxf(__int_as_float(s_zhi) - zlo, 1e-6f);
+  const int nf = oa.by_pair ? ORDER_BINS / (2 * oa.n_pairs) : ORDER_BINS;
+  const float fscale = (float)nf / zr;
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int i = tid + u * ORDER_THREADS;
     bin[u] = -1;
     if (i < m) {
-      const float z = theta[(size_t)(base + i) * ld + zoff];
-      bin[u] = (z >= 0.f && z < zf) ? min(ORDER_BINS - 1, (int)(z * scale)) : ORDER_BINS;
+      const float z = zv[u];
+      if (z >= 0.f) {
+        int b = min(nf - 1, (int)((z - zlo) * fscale));
+        if (oa.by_pair) {
+          const float* row = oa.theta + (size_t)(base + i) * oa.ld;
+          int j0, j1, n0 = 0, n1;
+          float w0, w1;
+          bracket_f(md.feh, md.n_feh, theta_col(md, row, md.offs[SED_KEY_LOGZSOL]), j0, w0, j1, w1);
+          if (md.use_afe && md.n_afe > 1) bracket_f(md.afe, md.n_afe, theta_col(md, row, md.offs[SED_KEY_AFE]), n0, w0, n1, w1);
+          const int half = (z - zlo) * 2.f >= zr ? 1 : 0;
+          b += (half * oa.n_pairs + n0 * max(md.n_feh - 1, 1) + j0) * nf;
+        }
+        bin[u] = b;
+      } else {
+        bin[u] = ORDER_BINS;
+      }
       atomicAdd(&cnt[bin[u]], 1);
     }
   }
@@ -381,7 +439,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_order(const float* theta, int
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
     const int i = tid + u * ORDER_THREADS;
-    if (i < m) perm[base + atomicAdd(&cnt[bin[u]], 1)] = base + i;
+    if (i < m) oa.perm[base + atomicAdd(&cnt[bin[u]], 1)] = base + i;
   }
 }
 
@@ -415,6 +473,13 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __shared__ float s_red[PREP_THREADS / 32];
   __shared__ float s_red8[PREP_THREADS / 32];
   __shared__ int s_nnz[PREP_THREADS / 32];
+  // K tiles the row touches: [Fe/H] nodes that bracket some bin, ages whose
+  // cell (or tent) reaches below T_max, and both [a/Fe] nodes of the bracket
+  __shared__ unsigned long long s_mset;
+  __shared__ int s_alim;
+  __shared__ uint32_t s_km[KMASK_WORDS];
+  if (tid == 0) { s_mset = 0ull; s_alim = 0; }
+  if (tid < KMASK_WORDS) s_km[tid] = 0u;
 
   // ---- finiteness of the whole row, and the row's cosmology (one lane, in
   //      the shadow of the row's loads)
@@ -489,7 +554,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     bracket_f(md.feh, md.n_feh, zeta[md.zmode == 0 ? i : 0], j0, w0, j1, w1);
     zb[i] = j0;
     zt[i] = w1;   // weight of j0 + 1 (0 when n_feh == 1)
+    if (a.kmask) atomicOr(&s_mset, (1ull << j0) | (1ull << j1));
   }
+  if (a.kmask)
+    for (int ag = tid; ag < NA; ag += blockDim.x)
+      if (g.cell_lo[ag] < T[NT]) atomicMax(&s_alim, ag + 1);
   __syncthreads();
 
   // ---- weights on (age, feh): thread per age node
@@ -530,6 +599,12 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   float qpart = 0.f;
   int nnz = 0;
   float* Vs = smem + NA * NZ;           // FP8 path: W_k 2^-e_k
+  // touched columns: the bracket nodes (also where a weight is 0 at a node: the
+  // adjoint reads their derivative) and one age past the last cell below T_max
+  // (the linear scheme's tents reach one node further)
+  const unsigned long long mset = s_mset;
+  const int alim = s_alim + 1;
+  const int f8_shift = L.Ky_pad8 - L.Ky_pad;
   // the layout tables through the read-only path, so that the unrolled loads
   // need not wait behind the stores of W
 #pragma unroll 4
@@ -543,6 +618,19 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     }
     if (k < L.Ky_pad) qpart += v * __ldg(L.q_s + k);
     nnz += v != 0.f;
+    if (a.kmask) {
+      // 32 consecutive columns per warp step: one K tile of every layout
+      bool touched = false;
+      if (code >= 0) {
+        const int n = code >> 24, mm = (code >> 16) & 0xff, ag = code & 0xffff;
+        touched = (n == n0 || (n == n1 && (md.use_afe || wn1 != 0.f))) && ((mset >> mm) & 1ull) && ag < alim;
+      }
+      if (__ballot_sync(0xffffffffu, touched) && lane == 0) {
+        const int q = a.W_f8 ? (k < L.Ky_pad ? k : k + f8_shift) : k;
+        const int t = q >> a.kt_shift;
+        atomicOr(&s_km[t >> 5], 1u << (t & 31));
+      }
+    }
     const size_t o = (size_t)p * Kpad + k;
     if (a.W) a.W[o] = v;
     if (a.W_hi) {
@@ -559,6 +647,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   }
   if (lane == 0) { s_red[warp] = qpart; s_nnz[warp] = nnz; }
   __syncthreads();
+  if (a.kmask && tid < a.kmask_w && s_km[tid]) atomicOr(&a.kmask[(size_t)(p >> 7) * a.kmask_w + tid], s_km[tid]);
 
   // ---- FP8 operand: E4M3 of W_k 2^-e_k 2^-y, with the row's power of two 2^y
   //      chosen so that its largest entry maps to at most 240 (< 448, the E4M3
@@ -771,18 +860,23 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   const float* dW = a.dW + (size_t)r * L.Kpad;
   const float gqy = (float)a.rgrad[(size_t)r * RGRAD + RG_QY];
   const int n_old = NA - L.n_young;
+  // dW holds values only in the columns the forward's rows touched (the
+  // contraction skips the others): the second [a/Fe] node's block only when it
+  // carries weight or the [a/Fe] derivative, and only (age, [Fe/H]) pairs with
+  // Ws != 0 enter the [a/Fe] derivative
+  const bool use_n1 = n1 != n0 && (md.use_afe || wn1 != 0.f);
   float gafe = 0.f;
   for (int j = tid; j < NA * NZ; j += blockDim.x) {
     const int ag = j / NZ, mm = j % NZ;
     const bool young = ag < L.n_young;
-    float gv[2];
+    float gv[2] = {0.f, 0.f};
     const int nn[2] = {n0, n1};
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < (use_n1 ? 2 : 1); ++q) {
       const int k = young ? (nn[q] * NZ + mm) * L.n_young + ag : L.Ky_pad + (nn[q] * NZ + mm) * n_old + (ag - L.n_young);
       gv[q] = dW[k] + (young ? gqy * L.q_s[k] : 0.f);
     }
-    gWs[j] = (n1 != n0) ? gv[0] * wn0 + gv[1] * wn1 : gv[0] * wn0;
-    if (n1 != n0) gafe += Ws[j] * (gv[0] * dn0 + gv[1] * dn1);
+    gWs[j] = use_n1 ? gv[0] * wn0 + gv[1] * wn1 : gv[0] * wn0;
+    if (use_n1 && Ws[j] != 0.f) gafe += Ws[j] * (gv[0] * dn0 + gv[1] * dn1);
   }
   __syncthreads();
   // thread per SFH bin: dlnL/dm_i (linear scheme: d/dpsi of its two edges),
@@ -902,8 +996,14 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   // a fixed redshift (no column) needs no redshift order: the caller's order is kept
   const bool z_col = p.md.offs[SED_KEY_ZRED] < p.md.n_param;
   if (p.perm && !p.row_model && z_col) {
-    e = launch_pdl(k_order, dim3((p.n + ORDER_CHUNK - 1) / ORDER_CHUNK), dim3(ORDER_THREADS), 0, s, p.theta, p.n, p.ld,
-                   p.md.offs[SED_KEY_ZRED], (float)p.md.zf, (float)(ORDER_BINS / p.md.zf), p.perm);
+    OrderArgs oa;
+    oa.theta = p.theta; oa.n = p.n; oa.ld = p.ld; oa.perm = p.perm; oa.md = p.md;
+    // bracket pair major when the contraction skips K tiles (the host gives
+    // masks only to models with one [Fe/H], and [a/Fe], per row)
+    const int pairs = std::max(p.md.n_feh - 1, 1) * (p.md.use_afe ? std::max(p.md.n_afe - 1, 1) : 1);
+    oa.by_pair = p.kmask && pairs > 1 && pairs <= ORDER_BINS / 4;
+    oa.n_pairs = pairs;
+    e = launch_pdl(k_order, dim3((p.n + ORDER_CHUNK - 1) / ORDER_CHUNK), dim3(ORDER_THREADS), 0, s, oa);
     if (e != cudaSuccess) return e;
   }
   PrepKernelArgs ka;

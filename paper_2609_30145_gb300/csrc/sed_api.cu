@@ -182,7 +182,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
     }
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
-      std::vector<void*> v = {w->perm, w->tile_win, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
+      std::vector<void*> v = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
                               w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                               w->dW, w->rgrad};
       for (void* p : v)
@@ -709,6 +709,8 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   if (d->n_pix && (d->lsf_mode < 0 || d->lsf_mode > 5)) return fail(ctx, SED_EINVAL, "bad lsf_mode");
   if (d->n_pix && !(d->sigma_gal_kms >= 0 && d->z_ref >= 0)) return fail(ctx, SED_EINVAL, "sigma_gal, z_ref must be >= 0");
   if (d->sample_sigma_gal != 0 && d->sample_sigma_gal != 1) return fail(ctx, SED_EINVAL, "sample_sigma_gal must be 0 or 1");
+  if (d->calib_mode != SED_CALIB_MARGINAL && d->calib_mode != SED_CALIB_OPTIMISED)
+    return fail(ctx, SED_EINVAL, "calib_mode must be SED_CALIB_MARGINAL or SED_CALIB_OPTIMISED");
   if (d->calib_n < 0 || d->calib_n > SED_MAX_CALIB)
     return fail(ctx, SED_EINVAL, "calib_n must be in [0, %d]", SED_MAX_CALIB);
   if (d->calib_n > 0) {
@@ -953,6 +955,7 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
       st = upload(ctx, &pf, cx.data(), cx.size(), &M->allocs, &M->bytes);
       dv.pix_cx = pf;
       dv.calib_n = d->calib_n;
+      dv.calib_opt = d->calib_mode == SED_CALIB_OPTIMISED ? 1 : 0;
       dv.calib_logdet_lam = 0.0;
       for (int m = 0; m < d->calib_n; m++) {
         dv.calib_isig2[m] = 1.0 / (d->calib_sigma[m] * d->calib_sigma[m]);
@@ -1049,7 +1052,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   if (!need) return w;
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
-  std::vector<void*> old = {w->perm, w->tile_win, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
+  std::vector<void*> old = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
                             w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                             w->dW, w->rgrad};
   for (void* p : old)
@@ -1067,7 +1070,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   std::vector<void*>* no = nullptr;
   sed_status s = SED_OK;
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
-  AL(perm, R * 4); AL(tile_win, 2 * ((R + 127) / 128) * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
+  AL(perm, R * 4); AL(tile_win, 2 * ((R + 127) / 128) * 4); AL(kmask, ((R + 127) / 128) * KMASK_WORDS * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
   AL(Y, R * N * 4); AL(O, R * N * 4); AL(O2, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
   AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
   if (grad || had_grad) {
@@ -1137,10 +1140,28 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   pa.err = w->err;
   pa.perm = w->perm;
   pa.tile_win = w->tile_win;
+  // K-tile masks for the tensor-core contractions (32 / 64 / 128 columns per tile)
+  {
+    const int shift = precision == SED_PREC_FP8 ? 7 : (precision == SED_PREC_BF16 ? 6 : 5);
+    const int kp = precision == SED_PREC_FP8 ? L->Kpad8 : L->Kpad;
+    const int kw = ((kp >> shift) + 31) / 32;
+    // skipping pays where the rows' weights sit in few (a/Fe, Fe/H) blocks
+    // (one constant [Fe/H] per row) and the K tiles are narrowest (3xTF32):
+    // measured, the wider BF16 / FP8 tiles lose more to the looser redshift
+    // windows of the bracket-pair row order than they save
+    const int pairs = std::max(g->n_feh - 1, 1) * (M->dv.use_afe ? std::max(g->n_afe - 1, 1) : 1);
+    const bool use = precision == SED_PREC_FP32 && M->dv.zmode == 1 && pairs > 1 && kw <= KMASK_WORDS;
+    pa.kmask = use ? w->kmask : nullptr;
+    pa.kmask_w = use ? kw : 0;
+    pa.kt_shift = shift;
+    w->kmask_w_call = pa.kmask_w;
+    if (ctx->profiling) { w->last_kmask_w = pa.kmask_w; w->last_kt_shift = shift; }
+  }
   {
     const size_t mt = (size_t)(n + 127) / 128;
     CK(cudaMemsetAsync(w->tile_win, 0x7f, mt * sizeof(int), s));
     CK(cudaMemsetAsync(w->tile_win + mt, 0xff, mt * sizeof(int), s));
+    if (pa.kmask) CK(cudaMemsetAsync(w->kmask, 0, mt * pa.kmask_w * sizeof(uint32_t), s));
   }
   CK(launch_prep(pa, s));
   if (sed_status ps = prof_mark(ctx, w, 1, s)) return ps;
@@ -1173,6 +1194,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
   ta.maps = maps; ta.Y = w->Y; ta.O = w->O; ta.O2 = w->O2; ta.err = w->err; ta.rs = w->rs;
   ta.tile_win = w->tile_win;
+  ta.kmask = pa.kmask; ta.kmask_w = pa.kmask_w;
   CK(launch_contract_tc(ta, s));
   return prof_mark(ctx, w, 2, s);
 }
@@ -1358,6 +1380,10 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
     DwArgs da{};
     da.n = n; da.ldk = L->ldn; da.Ky_pad = L->Ky_pad; da.Kpad = L->Kpad;
     da.maps = &w->dw_maps; da.dW = w->dW; da.err = w->err; da.rs = w->rs;
+    // the forward's K-tile masks (3xTF32: 32-column tiles), when it had any,
+    // select dW's output tiles
+    da.kmask = w->kmask_w_call > 0 ? w->kmask : nullptr;
+    da.kmask_w = w->kmask_w_call;
     CK(launch_dw_tc(da, s));
   } else {
     DwSimtArgs da{};
@@ -1408,18 +1434,29 @@ sed_status sed_last_stats(sed_ctx* ctx, void* stream, sed_stage_stats* out) {
   for (const RowScal& r : rs) nnz += r.nnz;
   out->nnz_w = nnz;
   out->dense_k = w->last_kpad;
-  // tensor work actually issued: the wavelength tiles of each 128-row tile's window union
+  // tensor work actually issued
   {
     const bool simt = w->last_prec == SED_PREC_FP32_SIMT;
     const int bn = simt ? 128 : tc_bn_for(w->last_prec, w->last_kpad);
-    double tiles = 0;
+    // K columns each 128-row tile multiplies: its touched K tiles when the call skipped the others
+    std::vector<double> kcols((rs.size() + 127) / 128, (double)w->last_kpad);
+    if (w->last_kmask_w > 0 && !simt) {
+      std::vector<uint32_t> km(kcols.size() * w->last_kmask_w);
+      CK(cudaMemcpy(km.data(), w->kmask, km.size() * 4, cudaMemcpyDeviceToHost));
+      for (size_t t = 0; t < kcols.size(); ++t) {
+        int bits = 0;
+        for (int j = 0; j < w->last_kmask_w; ++j) bits += __builtin_popcount(km[t * w->last_kmask_w + j]);
+        kcols[t] = (double)bits * (1 << w->last_kt_shift);
+      }
+    }
+    double issued = 0;   // wavelength tiles of each 128-row tile's window union x its K columns
     for (size_t m0 = 0; m0 < rs.size(); m0 += 128) {
       int lo = 0x7fffffff, hi = -1;
       for (size_t r = m0; r < std::min(rs.size(), m0 + 128); ++r)
         if (rs[r].status == 0) { lo = std::min(lo, rs[r].k_lo); hi = std::max(hi, rs[r].k_hi); }
-      if (hi >= 0) tiles += hi / bn - lo / bn + 1;
+      if (hi >= 0) issued += (hi / bn - lo / bn + 1) * kcols[m0 / 128];
     }
-    out->issued_flop = tiles * 2.0 * 128.0 * bn * w->last_kpad * (w->last_prec == SED_PREC_FP32 ? 3.0 : 1.0);
+    out->issued_flop = issued * 2.0 * 128.0 * bn * (w->last_prec == SED_PREC_FP32 ? 3.0 : 1.0);
   }
   out->n_rows = w->last_n;
   out->n_lam = w->last_nlam;

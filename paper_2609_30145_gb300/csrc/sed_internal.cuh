@@ -29,6 +29,10 @@ constexpr int MAX_SFH = 512;
 constexpr int MAX_LAM = 24576;   // rest-frame nodes an epilogue row can stage in shared memory
 constexpr int COSMO_TAB = 4096;  // intervals of the cosmology table on [0, zf]
 constexpr int COSMO_COLS = 8;    // value / derivative pairs of D_C, t_univ, ln(1+z), 1/(1+z)
+// K-tile occupancy masks of the contraction: one bit per K tile of the
+// precision's operand layout (32 FP32 / 64 BF16 / 128 FP8 columns), one row of
+// KMASK_WORDS words per 128-row tile; grids with more K tiles run unmasked
+constexpr int KMASK_WORDS = 8;
 
 // Physical constants (cgs unless noted).
 constexpr double LSUN = 3.839e33;              // erg/s (Sec. 2.6)
@@ -146,6 +150,7 @@ struct ModelDev {
   // marginalised calibration polynomial (App. E): calib_n coefficients, prior
   // 1/s_m^2, ln|Lambda| = sum ln s_m^2, per-pixel Chebyshev coordinate in [-1, 1]
   int calib_n;
+  int calib_opt;           // 1: the polynomial optimised at each call (no Occam terms), 0: marginalised
   double calib_isig2[SED_MAX_CALIB];
   double calib_logdet_lam;
   const float* pix_cx;
@@ -270,6 +275,8 @@ struct Workspace {
   float* W_lo = nullptr;
   int* perm = nullptr;           // [rows] processing order
   int* tile_win = nullptr;       // [2][ceil(rows/128)] per-tile node windows
+  uint32_t* kmask = nullptr;     // [ceil(rows/128)][KMASK_WORDS] per-tile K-tile occupancy
+  int kmask_w_call = 0;          // words per tile of the current call's masks (0: the call has none)
   __nv_bfloat16* W_bf16 = nullptr;
   uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
   float* Y = nullptr;            // [rows][ldn]
@@ -304,6 +311,7 @@ struct Workspace {
                                                                                // adjoint epilogue end, dW end
   bool last_grad = false;
   int last_n = 0, last_prec = 0, last_kpad = 0, last_nlam = 0;
+  int last_kmask_w = 0, last_kt_shift = 0;   // the last call's K-tile masks (0 words: unmasked)
   bool have_stats = false;
   // sed_loglike_host on buffers used in place: the call's launches as a CUDA
   // graph, captured when the same call repeats and replayed after that (the
@@ -374,6 +382,10 @@ struct PrepArgs {
   int* perm;           // [n] scratch: processing order (rows sorted by redshift), or NULL = caller's order
   int* tile_win;       // [2][ceil(n/128)] union of the row windows of each 128-row tile (lo set to
                        // 0x7f7f7f7f and hi to -1 beforehand), or NULL
+  uint32_t* kmask;     // [ceil(n/128)][kmask_w] K tiles that some row of each 128-row tile touches
+                       // (zeroed beforehand), or NULL
+  int kmask_w;         // words per 128-row tile (<= KMASK_WORDS)
+  int kt_shift;        // log2 of the columns of one K tile of the contraction's layout (5, 6 or 7)
 };
 // A pixel's rest-frame ln(lambda) = ln(lambda_obs) - ln(1+z), both given as
 // FP32 pairs {hi, lo}, returned as an FP32 pair: the high parts' difference is
@@ -488,6 +500,7 @@ struct TcArgs {
   float* O2;           // SED_PREC_FP32 with O2 non-NULL: the old part is split over two CTAs and
                        // O + O2 is the old sum (other precisions ignore O2)
   const int* tile_win; // non-NULL (and <= 64 M tiles): persistent schedule over the computed tiles
+  const uint32_t* kmask; int kmask_w;   // K tiles some row of each 128-row tile touches (NULL: all)
 };
 // encodes the four operand maps; returns 0 on success
 int tc_encode_maps(void* encode_fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo,
@@ -502,6 +515,8 @@ int tc_encode_dw_maps(void* encode_fn, DwMaps* out, const float* gy_hi, const fl
                       const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int ldg, int ldk, int kpad);
 struct DwArgs {
   const RowScal* rs;   // per-row node windows bound the reduction over lambda
+  const uint32_t* kmask; int kmask_w;   // 32-column K tiles some row of each 128-row tile touches (NULL: all);
+                                        // output tiles of dW no row touches are not computed
   int n, ldk, Ky_pad, Kpad;
   const DwMaps* maps;
   float* dW; int* err;

@@ -30,6 +30,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "sed_internal.cuh"
@@ -100,13 +101,19 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   const int kpad = L->Kpad;
   const int ldn = (g->n_lam + 255) / 256 * 256;
   const bool f32 = precision == SED_PREC_FP32, bf = precision == SED_PREC_BF16, simt = !f32 && !bf;
-  // carve the scratch: err | perm | tile windows | RowScal | W (FFMA) | W_hi | W_lo | W_bf16 | Y | O | O2 (3xTF32)
+  // K-tile masks of the tensor-core contraction, as in sed_loglike
+  const int kt_shift = bf ? 6 : 5;
+  const int kmask_w = ((kpad >> kt_shift) + 31) / 32;
+  const int pairs = std::max(g->n_feh - 1, 1) * (M->dv.use_afe ? std::max(g->n_afe - 1, 1) : 1);
+  const bool use_km = f32 && M->dv.zmode == 1 && pairs > 1 && kmask_w <= KMASK_WORDS;
+  // carve the scratch: err | perm | tile windows | K-tile masks | RowScal | W (FFMA) | W_hi | W_lo | W_bf16 |
+  // Y | O | O2 (3xTF32)
   const size_t nn = (size_t)n, mt = (nn + 127) / 128;
-  constexpr int NB = 11;
+  constexpr int NB = 12;
   size_t off[NB], need = 0;
-  const size_t sz[NB] = {256, nn * 4, 2 * mt * 4, nn * sizeof(RowScal), simt ? nn * kpad * 4 : 0,
-                         f32 ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0, bf ? nn * kpad * 2 : 0,
-                         nn * ldn * 4, nn * ldn * 4, f32 ? nn * ldn * 4 : 0};
+  const size_t sz[NB] = {256, nn * 4, 2 * mt * 4, use_km ? mt * kmask_w * 4 : 0, nn * sizeof(RowScal),
+                         simt ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0,
+                         bf ? nn * kpad * 2 : 0, nn * ldn * 4, nn * ldn * 4, f32 ? nn * ldn * 4 : 0};
   for (int i = 0; i < NB; i++) {
     off[i] = need;
     need += up256(sz[i]);
@@ -131,24 +138,27 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   int* err = static_cast<int*>(at(0));
   int* perm = static_cast<int*>(at(1));
   int* tile_win = static_cast<int*>(at(2));
-  RowScal* rs = static_cast<RowScal*>(at(3));
-  float* W = static_cast<float*>(at(4));
-  float* W_hi = static_cast<float*>(at(5));
-  float* W_lo = static_cast<float*>(at(6));
-  __nv_bfloat16* W_bf = static_cast<__nv_bfloat16*>(at(7));
-  float* Y = static_cast<float*>(at(8));
-  float* O = static_cast<float*>(at(9));
-  float* O2 = static_cast<float*>(at(10));
+  uint32_t* kmask = static_cast<uint32_t*>(at(3));
+  RowScal* rs = static_cast<RowScal*>(at(4));
+  float* W = static_cast<float*>(at(5));
+  float* W_hi = static_cast<float*>(at(6));
+  float* W_lo = static_cast<float*>(at(7));
+  __nv_bfloat16* W_bf = static_cast<__nv_bfloat16*>(at(8));
+  float* Y = static_cast<float*>(at(9));
+  float* O = static_cast<float*>(at(10));
+  float* O2 = static_cast<float*>(at(11));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // per-tile window bounds start empty: lo = a large positive int, hi = -1
   cudaError_t e = cudaMemsetAsync(tile_win, 0x7f, mt * sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(tile_win + mt, 0xff, mt * sizeof(int), s);
+  if (e == cudaSuccess && use_km) e = cudaMemsetAsync(kmask, 0, mt * kmask_w * sizeof(uint32_t), s);
   PrepArgs pa{};
   pa.theta = theta; pa.n = n; pa.ld = ld;
   pa.md = M->dv; pa.g = g->dv; pa.L = L->dv();
   pa.W = W; pa.W_hi = W_hi; pa.W_lo = W_lo; pa.W_bf16 = W_bf;
   pa.rs = rs; pa.err = err; pa.perm = perm; pa.tile_win = tile_win;
+  pa.kmask = use_km ? kmask : nullptr; pa.kmask_w = use_km ? kmask_w : 0; pa.kt_shift = kt_shift;
   if (e == cudaSuccess) e = launch_prep(pa, s);
   if (e == cudaSuccess) {
     if (simt) {
@@ -165,6 +175,7 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
       TcArgs ta{};
       ta.n = n; ta.n_lam = g->n_lam; ta.ldn = ldn; ta.Ky_pad = L->Ky_pad; ta.Kpad = kpad; ta.prec = precision;
       ta.maps = &maps; ta.Y = Y; ta.O = O; ta.O2 = O2; ta.err = err; ta.rs = rs; ta.tile_win = tile_win;
+      ta.kmask = pa.kmask; ta.kmask_w = pa.kmask_w;
       e = launch_contract_tc(ta, s);
     }
   }
