@@ -246,7 +246,18 @@ typedef struct {
    * All zero (the default) = every key sampled. */
   int fixed[SED_NKEYS];
   double fixed_val[SED_NKEYS];
+  /* How the calibration polynomial (calib_n > 0) enters lnL (App. E):
+   * SED_CALIB_MARGINAL (0, the default) integrates the coefficients out
+   * (Eq. app_polymarg); SED_CALIB_OPTIMISED (1) takes at every evaluation the
+   * coefficients that maximise the spectrum's lnL plus their log prior (the
+   * weighted least-squares fit regularised by 1/calib_sigma; very wide
+   * calib_sigma give the unregularised fit), i.e. lnL gains b^T M^-1 b / 2
+   * and not the Occam terms -ln|M|/2 - ln|Lambda|/2. */
+  int calib_mode;
 } sed_model_desc;
+
+#define SED_CALIB_MARGINAL 0
+#define SED_CALIB_OPTIMISED 1
 
 #define SED_MAX_CALIB 13
 #define SED_FESC_NONE 0

@@ -27,6 +27,7 @@ SFH_STEP, SFH_LINEAR = 0, 1
 FESC_NONE, FESC_RUNAWAY_BC, FESC_PICKET = 0, 1, 2
 NKEYS = len(KEYS)
 GRID_COPY_FP32, GRID_COPY_FP32_SIMT, GRID_COPY_BF16, GRID_COPY_FP8 = 1, 2, 4, 8
+CALIB_MARGINAL, CALIB_OPTIMISED = 0, 1
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 P = C.c_void_p
@@ -52,7 +53,7 @@ class ModelDesc(C.Structure):
                 ("calib_n", C.c_int), ("calib_sigma", P),
                 ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int), ("sfh_scheme", C.c_int),
                 ("phot_upper", P), ("fesc_geometry", C.c_int),
-                ("fixed", C.c_int * NKEYS), ("fixed_val", C.c_double * NKEYS)]
+                ("fixed", C.c_int * NKEYS), ("fixed_val", C.c_double * NKEYS), ("calib_mode", C.c_int)]
 
 
 class StageStats(C.Structure):

@@ -116,7 +116,7 @@ class Context:
                      spec_sigma=None, spec_mask=None, lsf_mode=0, lsf_value=None,
                      sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0,
                      calib_sigma=None, noise_floor_phot=0, noise_floor_spec=0, sfh_scheme=0,
-                     phot_upper=None, fesc_geometry=0, fixed=None) -> "Model":
+                     phot_upper=None, fesc_geometry=0, fixed=None, calib_mode=0) -> "Model":
         """fixed: optional {key name: value} of keys fixed for every row (no
         column in the parameter rows, no gradient); key names as in _ffi.KEYS."""
         d = _ffi.ModelDesc()
@@ -150,6 +150,7 @@ class Context:
             cs = _f64(calib_sigma)
             keep.append(cs)
             d.calib_n, d.calib_sigma = cs.size, _ptr(cs)
+        d.calib_mode = int(calib_mode)
         d.noise_floor_phot, d.noise_floor_spec = int(noise_floor_phot), int(noise_floor_spec)
         d.sfh_scheme = int(sfh_scheme)
         d.fesc_geometry = int(fesc_geometry)

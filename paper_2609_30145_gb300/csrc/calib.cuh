@@ -114,8 +114,9 @@ __device__ __forceinline__ void calib_sum_warps(float* part, int nwarps, int q0,
 
 // M from the moments S (row 0 of the partials), factored into its Cholesky
 // factor L, written to the lower triangle of the row-major n x n array L, and
-// 1/L_ii to Dinv.  Returns -ln|M| / 2 - ln|Lambda| / 2, or NaN when M is not
-// positive definite (every lane).
+// 1/L_ii to Dinv.  Returns -ln|M| / 2 - ln|Lambda| / 2 (0 for the optimised
+// polynomial, which has no Occam terms), or NaN when M is not positive
+// definite (every lane).
 static __device__ __noinline__ double calib_factor(const ModelDev& md, const float* S, float* L, float* Dinv, int lane) {
   const int n = md.calib_n, i = lane;
   if (i < n) {
@@ -145,7 +146,8 @@ static __device__ __noinline__ double calib_factor(const ModelDev& md, const flo
     bad |= __shfl_xor_sync(0xffffffffu, bad, o);
   }
   __syncwarp();
-  return bad ? (double)NAN : -0.5 * (double)lg - 0.5 * md.calib_logdet_lam;
+  if (bad) return (double)NAN;
+  return md.calib_opt ? 0.0 : -0.5 * (double)lg - 0.5 * md.calib_logdet_lam;
 }
 
 // x = (L L^T)^-1 rhs with rhs_i in lane i; returns x_i in lane i (0 for i >= n).

@@ -412,11 +412,13 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       for (int a = 0; a < SED_MAX_CALIB; ++a) {
         if (a < n) {
           p = fmaf(cal_cf[a], T[a], p);
-          float v = T[a];
+          if (!md.calib_opt) {   // the optimised polynomial has no ln|M| term
+            float v = T[a];
 #pragma unroll
-          for (int k = 0; k < a; ++k) v -= cal_Lf[a * n + k] * y[k];
-          y[a] = v * cal_Df[a];
-          q = fmaf(y[a], y[a], q);
+            for (int k = 0; k < a; ++k) v -= cal_Lf[a * n + k] * y[k];
+            y[a] = v * cal_Df[a];
+            q = fmaf(y[a], y[a], q);
+          }
         }
       }
       // sigma_i d lnL / d mu_i = (r_i - mu_i p_i)(1 + p_i)/sigma_i - (mu_i/sigma_i) q_i

@@ -190,17 +190,20 @@ def test_sampled_sigma_gal_grad_vs_oracle(ctx, prec):
     assert np.abs(ref["grad"][ok, j]).max() > 0      # the column carries a real derivative
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("prec", PRECS)
-def test_calibration_polynomial_grad_vs_oracle(ctx, prec):
-    """The adjoint with a marginalised 6-term calibration polynomial (each
+def test_calibration_polynomial_grad_vs_oracle(ctx, prec, mode):
+    """The adjoint with a 6-term calibration polynomial, marginalised (each
     pixel's d lnL / d mu carries the posterior-mean polynomial and the
-    T^T M^-1 T term): 150 rows, every row and column against the oracle."""
+    T^T M^-1 T term) or optimised at each call (no ln|M| term): 150 rows,
+    every row and column against the oracle."""
     w = synth.shrink(synth.WORKLOADS["specphot_afe_107x12x5x6000_b2048"], n_age=20, n_feh=4,
                      n_lam=1500, n_sfh=10, n_pix=240, batch=150)
-    if "calib" not in _CACHE:
-        orc = cases.calib_case(w, [0.2, 0.1, 0.1, 0.05, 0.05, 0.05])
-        _CACHE["calib"] = (w, orc, cases.gpu_model_for(ctx, orc, w))
-    w, orc, model = _CACHE["calib"]
+    key = f"calib{mode}"
+    if key not in _CACHE:
+        orc = cases.calib_case(w, [0.2, 0.1, 0.1, 0.05, 0.05, 0.05], calib_mode=mode)
+        _CACHE[key] = (w, orc, cases.gpu_model_for(ctx, orc, w))
+    w, orc, model = _CACHE[key]
     th32, th64 = cases.theta_pair(w, w.batch, seed=59)
     lnl, g, st = gpu_grad(model, th32, prec)
     ref = orc.grad(th64)
