@@ -42,7 +42,8 @@ class _Grid(C.Structure):
                 ("log_age_yr", C.c_void_p), ("feh", C.c_void_p), ("afe", C.c_void_p),
                 ("lam", C.c_void_p), ("flux", C.c_void_p), ("sigma_lib_kms", C.c_void_p),
                 ("neb_n_logu", C.c_int), ("neb_n_logz", C.c_int),
-                ("neb_logu", C.c_void_p), ("neb_logz", C.c_void_p), ("neb_tab", C.c_void_p)]
+                ("neb_logu", C.c_void_p), ("neb_logz", C.c_void_p), ("neb_tab", C.c_void_p),
+                ("neb_n_line", C.c_int), ("neb_line_lam", C.c_void_p), ("neb_line_tab", C.c_void_p)]
 
 
 class _Model(C.Structure):
@@ -58,7 +59,11 @@ class _Model(C.Structure):
                 ("sample_sigma_gal", C.c_int), ("sigma_gal_max_kms", C.c_double),
                 ("calib_n", C.c_int), ("calib_sigma", C.c_void_p),
                 ("sfh_scheme", C.c_int), ("floor_phot", C.c_int), ("floor_spec", C.c_int),
-                ("phot_upper", C.c_void_p), ("fesc_geometry", C.c_int), ("calib_mode", C.c_int)]
+                ("phot_upper", C.c_void_p), ("fesc_geometry", C.c_int), ("calib_mode", C.c_int),
+                ("use_lines", C.c_int), ("gas_sigma_mode", C.c_int), ("sigma_gas_kms", C.c_double),
+                ("sigma_gas_max_kms", C.c_double), ("n_lcat", C.c_int), ("lcat_start", C.c_void_p),
+                ("lcat_line", C.c_void_p), ("lcat_d", C.c_void_p), ("lcat_sigma", C.c_void_p),
+                ("lcat_mask", C.c_void_p), ("lcat_upper", C.c_void_p)]
 
 
 def _load():
@@ -78,6 +83,7 @@ def _load():
         lib.orc_row.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
         lib.orc_row.restype = C.c_int
         lib.orc_eval.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P, C.c_int]
+        lib.orc_line_fluxes.argtypes = [P, P, P, C.c_int, C.c_int, P]
         lib.orc_grad_fd.argtypes = [P, P, P, C.c_int, C.c_int, C.c_double, P, C.c_int]
         lib.orc_grad.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, C.c_int]
         lib.orc_n_param.argtypes = [P]
@@ -125,6 +131,12 @@ class Oracle:
     sigma_gal_max_kms: float = 1000.0   # sampled sigma_gal must lie in [0, this]
     calib_sigma: np.ndarray | None = None   # prior widths s_m of the calibration polynomial's coefficients
     calib_mode: int = 0                 # 0 marginalised (Eq. app_polymarg), 1 optimised at each call
+    use_lines: int = 0                  # 1: the grid's emission lines enter photometry and spectrum (App. C)
+    gas_sigma_mode: int = 0             # GAS_SIGMA_TIED (= sigma_gal), _FIXED (sigma_gas_kms) or _SAMPLED (last column)
+    sigma_gas_kms: float = 300.0
+    sigma_gas_max_kms: float = 1000.0
+    lcat: tuple | None = None           # line catalogue (Sec. 3.3): (blends: list of lists of grid-line
+                                        # indices, d, sigma, mask or None, upper or None), erg/s/cm^2
     sfh_scheme: int = 0                 # 0 step (N_T bin masses), 1 linear (N_T + 1 edge SFRs; App. B)
     floor_phot: int = 0                 # noise-floor terms of each arm (App. sys_floor): FLOOR_* bits
     floor_spec: int = 0
@@ -157,6 +169,10 @@ class Oracle:
             self._g.neb_logu = _p(k(g.neb_logu))
             self._g.neb_logz = _p(k(g.neb_logz))
             self._g.neb_tab = _p(k(g.neb_tab))
+            if getattr(g, "line_tab", None) is not None:
+                self._g.neb_n_line = g.line_tab.shape[2]
+                self._g.neb_line_lam = _p(k(g.line_lam))
+                self._g.neb_line_tab = _p(k(g.line_tab))
         self._rebuild_model()
 
     def _rebuild_model(self):
@@ -199,6 +215,18 @@ class Oracle:
         m.sfh_scheme = int(self.sfh_scheme)
         m.fesc_geometry = int(self.fesc_geometry)
         m.calib_mode = int(self.calib_mode)
+        m.use_lines = int(self.use_lines)
+        m.gas_sigma_mode = int(self.gas_sigma_mode)
+        m.sigma_gas_kms, m.sigma_gas_max_kms = float(self.sigma_gas_kms), float(self.sigma_gas_max_kms)
+        if self.lcat is not None:
+            blends, d, s, mask, upper = self.lcat
+            start = np.concatenate([[0], np.cumsum([len(b) for b in blends])]).astype(np.int32)
+            m.n_lcat = len(blends)
+            m.lcat_start = _p(k(start, np.int32))
+            m.lcat_line = _p(k(np.concatenate([np.asarray(b, dtype=np.int32) for b in blends]), np.int32))
+            m.lcat_d, m.lcat_sigma = _p(k(d)), _p(k(s))
+            m.lcat_mask = _p(k(mask, np.uint8))
+            m.lcat_upper = _p(k(upper, np.uint8))
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
@@ -280,8 +308,19 @@ class Oracle:
                                float(z), float(sg), _p(fnu_obs), _p(out), _p(valid))
         return out, valid
 
+    def line_fluxes(self, theta):
+        """Observer-frame integrated flux of every grid line [n][n_line], erg/s/cm^2."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        n, ld = th.shape
+        nl = self._g.neb_n_line
+        out = np.zeros((n, max(nl, 1)))
+        self._lib.orc_line_fluxes(C.byref(self._g), C.byref(self._m), _p(th), n, ld, _p(out))
+        return out[:, :nl]
+
     def grad(self, theta, nthreads=0):
         """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])."""
+        if self.use_lines or self.lcat is not None:
+            raise NotImplementedError("the analytic gradient does not cover emission lines: use grad_fd")
         th = np.ascontiguousarray(theta, dtype=np.float64)
         n, ld = th.shape
         out = np.zeros((n, ld))
@@ -324,6 +363,7 @@ def dust_tau(law, lam, tau, index):
 
 FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
 FESC_NONE, FESC_RUNAWAY_BC, FESC_PICKET = 0, 1, 2
+GAS_SIGMA_TIED, GAS_SIGMA_FIXED, GAS_SIGMA_SAMPLED = 0, 1, 2
 FLOOR_NAMES = ("log_err_scale", "log_f_calib", "log_f_data", "log_jitter")
 
 
@@ -333,19 +373,21 @@ def floor_keys(floor_phot=0, floor_spec=0):
                  for k in range(4) if (bits >> k) & 1)
 
 
-def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, sfh_scheme=0, fesc_geometry=0):
+def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, sfh_scheme=0, fesc_geometry=0,
+               sample_sigma_gas=0):
     """Parameter rows in the oracle's layout: sfh[N_T] (bin masses; N_T + 1 edge
     SFRs with the linear scheme), logzsol[N_T or 1], then
     afe, logmass, zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index,
     gas_logz, gas_logu, sigma_gal when the model samples it, and the log10 of
     each noise-floor term that is on (photometry, then spectrum), and frac_obrun
-    with an escape geometry."""
+    with an escape geometry, sigma_gas when the model samples the gas dispersion."""
     nz = n_sfh if zmode == 0 else 1
     n = d["sfh"].shape[0]
     cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh + (1 if sfh_scheme == 1 else 0)),
             np.asarray(d["logzsol"], dtype=np.float64).reshape(n, nz)]
     for k in ("afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
               "diffuse_dust_index", "gas_logz", "gas_logu") + (("sigma_gal",) if sample_sigma_gal else ()) + \
-            floor_keys(floor_phot, floor_spec) + (("frac_obrun",) if fesc_geometry else ()):
+            floor_keys(floor_phot, floor_spec) + (("frac_obrun",) if fesc_geometry else ()) + \
+            (("sigma_gas",) if sample_sigma_gas else ()):
         cols.append(np.asarray(d[k], dtype=np.float64).reshape(n, 1))
     return np.ascontiguousarray(np.concatenate(cols, axis=1))

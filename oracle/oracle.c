@@ -127,7 +127,8 @@ static int sfh_cols(const orc_model *md) { return md->n_sfh + (md->sfh_scheme ==
 
 int orc_n_param(const orc_model *md) {
   return sfh_cols(md) + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0) +
-         n_floor(md->floor_phot) + n_floor(md->floor_spec) + (md->fesc_geometry ? 1 : 0);
+         n_floor(md->floor_phot) + n_floor(md->floor_spec) + (md->fesc_geometry ? 1 : 0) +
+         (md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED ? 1 : 0);
 }
 
 /* parameter row decoding (layout: sfh[N_T], logzsol[N_T or 1], afe, logmass,
@@ -139,6 +140,7 @@ typedef struct {
   double fl[2][4];   /* noise floor {s, f_calib, f_data, j} of photometry [0] and spectrum [1] */
   int fl_col[2][4];  /* column of each term in the row, -1 when the term is off */
   double fob;        /* runaway fraction f_ob (0 without an escape geometry) */
+  double sigma_gas;  /* gas dispersion of the emission lines, km/s */
 } orc_theta;
 
 static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
@@ -162,7 +164,9 @@ static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
       }
     }
   }
-  o->fob = md->fesc_geometry ? th[col] : 0.0;
+  o->fob = md->fesc_geometry ? th[col++] : 0.0;
+  o->sigma_gas = md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED ? th[col]
+               : (md->gas_sigma_mode == ORC_GAS_SIGMA_FIXED ? md->sigma_gas_kms : o->sigma_gal);
 }
 
 /* Eq. "app_noise_floor": the effective variance of a datum with formal error
@@ -203,6 +207,8 @@ static int theta_status(const orc_model *md, const double *th, double *tmax_out,
   decode_theta(md, th, &t);
   if (md->sample_sigma_gal && !(t.sigma_gal >= 0.0 && t.sigma_gal <= md->sigma_gal_max_kms)) return ORC_BAD_THETA;
   if (md->fesc_geometry && !(t.fob >= 0.0 && t.fob <= 1.0)) return ORC_BAD_THETA;
+  if (md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED && !(t.sigma_gas >= 0.0 && t.sigma_gas <= md->sigma_gas_max_kms))
+    return ORC_BAD_THETA;
   if (t.z < 0.0 || t.z >= md->zf) return ORC_BAD_Z;
   double cz[3], cf[3];
   orc_cosmology(md->H0, md->Om0, t.z, cz);
@@ -692,6 +698,75 @@ static double calib_terms(const orc_model *md, const double *mu, const unsigned 
   return out;
 }
 
+/* ---- emission lines (App. C, App. "line_proj", Eq. "app_line_profile") ---- */
+
+/* App. D normalisation of band b (samples from off): Z_b, the trapezoid of
+ * lam R c AB / lam^2, as in orc_photometry. */
+static double band_norm(const orc_model *md, int b, int off) {
+  int n = md->filt_len[b];
+  const double *L = md->filt_lam + off, *R = md->filt_trans + off;
+  double zb = 0.0;
+  for (int j = 0; j + 1 < n; j++) {
+    double g0 = L[j] * R[j] * O_C_AA * O_AB / (L[j] * L[j]);
+    double g1 = L[j + 1] * R[j + 1] * O_C_AA * O_AB / (L[j + 1] * L[j + 1]);
+    zb += 0.5 * (g0 + g1) * (L[j + 1] - L[j]);
+  }
+  return zb;
+}
+
+/* Transmission of band b at observed wavelength x: linear between its
+ * samples, zero outside them. */
+static double band_trans(const orc_model *md, int b, int off, double x) {
+  int n = md->filt_len[b];
+  const double *L = md->filt_lam + off, *R = md->filt_trans + off;
+  if (!(x >= L[0] && x <= L[n - 1])) return 0.0;
+  for (int j = 0; j + 1 < n; j++)
+    if (x >= L[j] && x <= L[j + 1]) return R[j] + (R[j + 1] - R[j]) * (x - L[j]) / (L[j + 1] - L[j]);
+  return 0.0;
+}
+
+/* Instrumental dispersion (km/s) at observed wavelength x: the spectrum's LSF
+ * at its pixels, linear in wavelength between them, constant past the ends. */
+static double sigma_inst_at(const orc_model *md, double x) {
+  int n = md->n_pix;
+  if (x <= md->spec_lam[0]) return sigma_inst_kms(md->lsf_mode, md->lsf_value[0], md->spec_lam[0]);
+  if (x >= md->spec_lam[n - 1]) return sigma_inst_kms(md->lsf_mode, md->lsf_value[n - 1], md->spec_lam[n - 1]);
+  int i = 0;
+  while (i + 2 < n && md->spec_lam[i + 1] <= x) i++;
+  double a = sigma_inst_kms(md->lsf_mode, md->lsf_value[i], md->spec_lam[i]);
+  double b = sigma_inst_kms(md->lsf_mode, md->lsf_value[i + 1], md->spec_lam[i + 1]);
+  return a + (b - a) * (x - md->spec_lam[i]) / (md->spec_lam[i + 1] - md->spec_lam[i]);
+}
+
+/* Observer-frame integrated flux of every grid line, erg/s/cm^2 (App.
+ * "line_proj"): L = Q_young 10^(bilinear log10 line table at (log U, log
+ * Z_gas)) (App. C, the same interpolation as the nebular continuum), through
+ * the attenuation the nebular continuum meets at the line's wavelength
+ * (birth cloud and diffuse screen, Eq. "app_attn"; with an escape geometry
+ * the covered fraction 1 - f_ob as in Sec. "frac_obrun"), times
+ * scale = 10^logmass Lsun / (4 pi D_L^2): the flux factor of Sec. 2.6 without
+ * its (1+z), since an integrated flux has no bandwidth. */
+static void line_fluxes(const orc_grid *g, const orc_model *md, const orc_theta *t, double qy, double scale,
+                        double *Fl) {
+  int u0, u1, z0, z1;
+  double wu0, wu1, wz0, wz1;
+  bracket(g->neb_logu, g->neb_n_logu, t->gas_logu, &u0, &wu0, &u1, &wu1);
+  bracket(g->neb_logz, g->neb_n_logz, t->gas_logz, &z0, &wz0, &z1, &wz1);
+  int NLn = g->neb_n_line, NZg = g->neb_n_logz;
+  for (int l = 0; l < NLn; l++) {
+    double lg = wu0 * wz0 * g->neb_line_tab[((size_t)u0 * NZg + z0) * NLn + l] +
+                wu0 * wz1 * g->neb_line_tab[((size_t)u0 * NZg + z1) * NLn + l] +
+                wu1 * wz0 * g->neb_line_tab[((size_t)u1 * NZg + z0) * NLn + l] +
+                wu1 * wz1 * g->neb_line_tab[((size_t)u1 * NZg + z1) * NLn + l];
+    double lam = g->neb_line_lam[l], td = 0.0;
+    orc_dust_tau(md->dust_law, &lam, 1, t->tau_d, t->delta, &td);
+    double ed = exp(-td), eb = exp(-t->tau_bc * pow(lam / 5500.0, t->alpha_bc)), f = t->fob, fac;
+    if (md->fesc_geometry == ORC_FESC_PICKET) fac = ed * (1.0 - f) * eb;
+    else fac = ed * ((1.0 - f) * eb + f) * (1.0 - f);
+    Fl[l] = qy * pow(10.0, lg) * fac * scale;
+  }
+}
+
 /* One parameter row through the whole forward model and likelihood. */
 int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double *W_out,
             double *Y_out, double *O_out, double *F_out, double *fnu_out, double *phot,
@@ -778,6 +853,10 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
     double dl = cosm[0] > 10.0 * O_PC_CM ? cosm[0] : 10.0 * O_PC_CM;
     double scale = pow(10.0, t.logmass) * O_LSUN * (1.0 + t.z) / (4.0 * M_PI * dl * dl);
     for (int k = 0; k < NL; k++) fnu[k] = scale * F[k];
+    /* the grid's emission lines, App. "line_proj" */
+    const int nline = (md->use_lines && md->use_nebular && g->neb_line_tab) ? g->neb_n_line : 0;
+    double *Fl = (double *)calloc(nline > 0 ? nline : 1, sizeof(double));
+    if (nline) line_fluxes(g, md, &t, qy, pow(10.0, t.logmass) * O_LSUN / (4.0 * M_PI * dl * dl), Fl);
     /* projections + likelihood, Eq. "total_lnlike" */
     double *ph = (double *)malloc((md->n_filt > 0 ? md->n_filt : 1) * sizeof(double));
     double *sp = (double *)malloc((md->n_pix > 0 ? md->n_pix : 1) * sizeof(double));
@@ -785,6 +864,14 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
     lnl = 0.0;
     if (md->n_filt > 0) {
       orc_photometry(md, g->lam, NL, t.z, fnu, ph);
+      /* a line in a band: its integrated flux at its observed wavelength
+       * through the band's photon-counting response, F R_b(lam_obs) lam_obs / Z_b
+       * (App. D; the limit of a line much narrower than the band) */
+      for (int b = 0, off = 0; b < md->n_filt; off += md->filt_len[b], b++)
+        for (int l = 0; l < nline; l++) {
+          double xo = g->neb_line_lam[l] * (1.0 + t.z);
+          ph[b] += Fl[l] * band_trans(md, b, off, xo) * xo / band_norm(md, b, off);
+        }
       for (int b = 0; b < md->n_filt; b++) {
         if (phot) phot[b] = ph[b];
         if (md->phot_d && (!md->phot_mask || md->phot_mask[b])) {
@@ -797,6 +884,20 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
     }
     if (md->n_pix > 0) {
       orc_spectrum(g, md, g->lam, NL, t.z, t.sigma_gal, fnu, sp, vd);
+      /* Eq. "app_line_profile": each line a unit-area Gaussian in ln(lambda) of
+       * width s = sqrt(sigma_gas^2 + sigma_inst^2(lam_obs)) / c, sampled at the
+       * pixel centres (truncated at 5 s, not renormalised), as a flux density
+       * per unit frequency through lambda / c */
+      for (int l = 0; l < nline; l++) {
+        double xo = g->neb_line_lam[l] * (1.0 + t.z), si = sigma_inst_at(md, xo);
+        double s = sqrt(t.sigma_gas * t.sigma_gas + si * si) / O_C_KMS;
+        if (!(s > 0.0)) continue;
+        for (int i = 0; i < md->n_pix; i++) {
+          double u = (log(md->spec_lam[i]) - log(xo)) / s;
+          if (fabs(u) > 5.0) continue;
+          sp[i] += Fl[l] * (md->spec_lam[i] / O_C_AA) * exp(-0.5 * u * u) / (sqrt(2.0 * M_PI) * s);
+        }
+      }
       unsigned char *inc = (unsigned char *)calloc(md->n_pix, 1);
       for (int i = 0; i < md->n_pix; i++) {
         if (spec) spec[i] = sp[i];
@@ -809,9 +910,22 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
       if (md->calib_n > 0 && md->spec_d) lnl += calib_terms(md, sp, inc, NULL, NULL);
       free(inc);
     }
+    /* the line-catalogue arm (Sec. 3.3, App. "line_lik"): a blend's model is the
+     * sum of its grid lines' fluxes; detections by Eq. "app_line_chi2_det",
+     * upper limits by the one-sided Eq. "app_line_chi2_UL" (residual 0 while
+     * the model stays at or below the limit); the normalisation of every
+     * included entry is kept, as in Eq. "total_lnlike" */
+    for (int k = 0; k < md->n_lcat; k++) {
+      double m = 0.0;
+      for (int j = md->lcat_start[k]; j < md->lcat_start[k + 1]; j++) m += nline ? Fl[md->lcat_line[j]] : 0.0;
+      if (md->lcat_mask && !md->lcat_mask[k]) continue;
+      double d = md->lcat_d[k], sg = md->lcat_sigma[k];
+      double r = (md->lcat_upper && md->lcat_upper[k] && m <= d) ? 0.0 : d - m;
+      lnl += -0.5 * r * r / (sg * sg) - 0.5 * log(2.0 * M_PI * sg * sg);
+    }
     if (!isfinite(lnl)) { st = ORC_NONFINITE; lnl = -INFINITY; }
     if (scal) { scal[0] = cosm[0]; scal[1] = cosm[1]; scal[2] = tmax; scal[3] = qy; scal[4] = scale; }
-    free(ph); free(sp); free(vd);
+    free(ph); free(sp); free(vd); free(Fl);
   }
   if (st) {
     if (phot) for (int b = 0; b < md->n_filt; b++) phot[b] = 0.0;
@@ -843,6 +957,22 @@ void orc_eval(const orc_grid *g, const orc_model *md, const double *theta, int n
     if (status_out) status_out[r] = st;
   }
   (void)nthreads;
+}
+
+void orc_line_fluxes(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld, double *out) {
+  int nl = g->neb_n_line > 0 ? g->neb_n_line : 0;
+  for (int r = 0; r < n; r++) {
+    const double *th = theta + (size_t)r * ld;
+    double scal[6];
+    int st = orc_row(g, md, th, NULL, NULL, NULL, NULL, NULL, NULL, NULL, scal);
+    double *o = out + (size_t)r * nl;
+    for (int l = 0; l < nl; l++) o[l] = 0.0;
+    if (st || !nl || !g->neb_line_tab || !md->use_nebular) continue;
+    orc_theta t;
+    decode_theta(md, th, &t);
+    double dl = scal[0] > 10.0 * O_PC_CM ? scal[0] : 10.0 * O_PC_CM;
+    line_fluxes(g, md, &t, scal[3], pow(10.0, t.logmass) * O_LSUN / (4.0 * M_PI * dl * dl), o);
+  }
 }
 
 void orc_grad_fd(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld,

@@ -38,6 +38,9 @@ typedef struct {
   int neb_n_logu, neb_n_logz;
   const double *neb_logu, *neb_logz;
   const double *neb_tab;       /* [n_logu][n_logz][n_lam] log10(L_nu/Q), or NULL */
+  int neb_n_line;              /* emission lines of the nebular grid (App. C), 0: none */
+  const double *neb_line_lam;  /* [n_line] rest-frame wavelength, Angstrom */
+  const double *neb_line_tab;  /* [n_logu][n_logz][n_line] log10(L_line/Q), Lsun / (photon/s) */
 } orc_grid;
 
 typedef struct {
@@ -73,7 +76,25 @@ typedef struct {
                                   row's last column is the runaway fraction f_ob in [0, 1] */
   int calib_mode;              /* ORC_CALIB_MARGINAL (Eq. "app_polymarg") or ORC_CALIB_OPTIMISED (the
                                   polynomial optimised at each call, Sec. 3.2 / App. E) */
+  int use_lines;               /* 1: the grid's emission lines (App. C, App. "line_proj") enter the
+                                  photometry and the spectrum (needs use_nebular) */
+  int gas_sigma_mode;          /* ORC_GAS_SIGMA_*: the gas dispersion sigma_gas of the line profiles */
+  double sigma_gas_kms;        /* ORC_GAS_SIGMA_FIXED: its value */
+  double sigma_gas_max_kms;    /* ORC_GAS_SIGMA_SAMPLED: the column must lie in [0, this] */
+  int n_lcat;                  /* entries of the line-catalogue arm (Sec. 3.3 "Lines"), 0: none */
+  const int *lcat_start;       /* [n_lcat + 1]: entry k is the blend of grid lines
+                                  lcat_line[lcat_start[k] .. lcat_start[k + 1]) */
+  const int *lcat_line;
+  const double *lcat_d, *lcat_sigma;   /* observed integrated fluxes and errors, erg/s/cm^2 */
+  const unsigned char *lcat_mask;      /* [n_lcat] or NULL (all included) */
+  const unsigned char *lcat_upper;     /* [n_lcat] nonzero: lcat_d[k] is an upper limit, or NULL */
 } orc_model;
+/* The gas velocity dispersion of the emission lines (Sec. 2.7): tied to the
+ * stellar sigma_gal (the paper's default), a fixed value, or a parameter
+ * column (the last one of the row). */
+#define ORC_GAS_SIGMA_TIED 0
+#define ORC_GAS_SIGMA_FIXED 1
+#define ORC_GAS_SIGMA_SAMPLED 2
 /* The calibration polynomial of the spectrum, App. E.  MARGINAL integrates the
  * coefficients out under their Gaussian prior (Eq. "app_polymarg").  OPTIMISED
  * takes, at every evaluation, the coefficients that maximise the spectrum's
@@ -142,6 +163,9 @@ void orc_eval(const orc_grid *g, const orc_model *md, const double *theta, int n
               double *phot_out, double *spec_out, double *lnl_out, int *status_out,
               int nthreads);
 
+/* Observer-frame integrated flux of every grid line (erg/s/cm^2, App.
+ * "line_proj"), out [n][neb_n_line]; zeros for rows with a nonzero status. */
+void orc_line_fluxes(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld, double *out);
 /* Central finite-difference gradient of lnL (FP64), step h_j = h_rel*max(|x_j|, 1). */
 void orc_grad_fd(const orc_grid *g, const orc_model *md, const double *theta, int n, int ld,
                  double h_rel, double *grad_out, int nthreads);

@@ -47,6 +47,8 @@ class Grid:
     neb_logu: np.ndarray | None = None
     neb_logz: np.ndarray | None = None
     neb_tab: np.ndarray | None = None   # [n_logu][n_logz][n_lam] log10(L_nu/Q), (Lsun/Hz)/(photon/s)
+    line_lam: np.ndarray | None = None  # [n_line] rest-frame wavelengths of the emission-line cube, Angstrom
+    line_tab: np.ndarray | None = None  # [n_logu][n_logz][n_line] log10(L_line/Q), Lsun/(photon/s)
 
     @property
     def shape(self):
@@ -97,10 +99,31 @@ def make_grid(n_age=16, log_age=(6.0, 10.1), feh=(-2.0, 0.2), n_feh=4,
                 flux[n, m, a] = 1e-11 * 10 ** logA * shape
     g = Grid(log_age_yr=log_age_yr, feh=feh_v, afe=afe_v, lam_aa=lam, flux=flux)
     if nebular is not None:
+        n_cube = nebular.get("line_cube", 0)
+        # with a separate line cube the continuum template carries no lines
         g.neb_logu, g.neb_logz, g.neb_tab = make_nebular(lam, seed=nebular.get("seed", 2),
                                                         n_logu=nebular.get("n_logu", 7),
-                                                        n_logz=nebular.get("n_logz", 12))
+                                                        n_logz=nebular.get("n_logz", 12),
+                                                        n_lines=0 if n_cube else 30)
+        if n_cube:
+            g.line_lam, g.line_tab = make_line_cube(g.neb_logu, g.neb_logz, n_cube, seed=nebular.get("seed", 2) + 10)
     return g
+
+
+def make_line_cube(logu, logz, n_lines, seed=12, lam_aa=(1000.0, 22000.0)):
+    """Emission-line cube log10(L_line/Q) in Lsun/(photon/s) on the nebular
+    (log U, log Z_gas) axes: `n_lines` seeded rest wavelengths, log-uniform in
+    lam_aa, sorted, and strengths around 1e-46 Lsun per ionising photon per
+    second (an H-beta-like line is ~1.2e-46) times 0.1..3, varying linearly
+    with log U and log Z_gas."""
+    rng = _rng(seed)
+    lam = np.sort(np.exp(np.log(lam_aa[0]) + rng.random(n_lines) * (np.log(lam_aa[1]) - np.log(lam_aa[0]))))
+    base = -46.0 + np.log10(0.1 + 2.9 * rng.random(n_lines))
+    su = 0.3 * (rng.random(n_lines) - 0.5)
+    sz = 0.4 * (rng.random(n_lines) - 0.5)
+    lu, lz = np.asarray(logu), np.asarray(logz)
+    tab = base[None, None, :] + su[None, None, :] * (lu[:, None, None] + 2.5) + sz[None, None, :] * (lz[None, :, None] + 0.5)
+    return lam, tab
 
 
 def make_nebular(lam, seed=2, n_logu=7, n_logz=12, logu=(-4.0, -1.0), logz=(-1.3, 0.3),
