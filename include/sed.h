@@ -112,7 +112,9 @@ enum {
   SED_KEY_LOG_F_DATA_SPEC = 18,
   SED_KEY_LOG_JITTER_SPEC = 19,     /* j in the spectral data's units */
   SED_KEY_FRAC_OBRUN = 20,    /* runaway fraction f_ob in [0, 1] (a column only with an escape geometry) */
-  SED_NKEYS = 21
+  SED_KEY_SIGMA_GAS = 21,     /* gas velocity dispersion of the emission lines, km/s (a column only when
+                                 gas_sigma_mode = SED_GAS_SIGMA_SAMPLED) */
+  SED_NKEYS = 22
 };
 
 typedef struct sed_ctx sed_ctx;
@@ -144,6 +146,12 @@ typedef struct {
    * x Kpad x n_lam: a server that runs BF16 only keeps a fifth of the default
    * footprint.  The gradient needs the copy of its precision (3xTF32 or FP32). */
   unsigned precision_mask;
+  /* Emission-line cube of the nebular grid (App. C): line luminosity per
+   * ionising photon on the same (log U, log Z_gas) axes as the continuum
+   * template, kept apart from the continuum (Sec. 2.5): 0 lines = none. */
+  int neb_n_line;
+  const double *neb_line_lam_aa;       /* [n_line] rest-frame wavelengths, Angstrom */
+  const double *neb_log10_line_per_q;  /* [n_logu][n_logz][n_line] log10(L_line/Q), Lsun/(photon/s) */
 } sed_grid_desc;
 
 #define SED_GRID_COPY_FP32 (1u << SED_PREC_FP32)           /* TF32 hi/lo parts (3xTF32 path) */
@@ -254,7 +262,36 @@ typedef struct {
    * calib_sigma give the unregularised fit), i.e. lnL gains b^T M^-1 b / 2
    * and not the Occam terms -ln|M|/2 - ln|Lambda|/2. */
   int calib_mode;
+  /* Emission lines (App. C, App. line_proj; needs use_nebular and a grid with
+   * a line cube): each line's flux, L = Q_young 10^(bilinear log10 cube) through
+   * the nebular attenuation at its wavelength, times 10^logmass Lsun /
+   * (4 pi D_L^2), enters the photometry as F R_b(lam_obs) lam_obs / Z_b and
+   * the spectrum as a unit-area Gaussian in ln(lambda) of width
+   * sqrt(sigma_gas^2 + sigma_inst^2(lam_obs)) / c sampled at the pixels
+   * (Eq. app_line_profile; sigma_inst interpolated linearly in wavelength
+   * between the pixels' LSF).  sigma_gas: SED_GAS_SIGMA_TIED to the stellar
+   * sigma_gal (fixed or sampled), SED_GAS_SIGMA_FIXED at sigma_gas_kms, or
+   * SED_GAS_SIGMA_SAMPLED as the column SED_KEY_SIGMA_GAS in
+   * [0, sigma_gas_max_kms] (else SED_ROW_BAD_THETA). */
+  int use_lines;
+  int gas_sigma_mode;
+  double sigma_gas_kms, sigma_gas_max_kms;
+  /* Line catalogue arm (Sec. 3.3 "Lines", App. line_lik; needs use_lines):
+   * n_lcat entries, entry k the blend of lcat_len[k] grid lines listed in
+   * lcat_line (concatenated), observed integrated flux lcat_d[k] and error
+   * lcat_sigma[k] in erg/s/cm^2; the model is the blend's summed flux (no
+   * profile); detections add -((d - m)/sigma)^2/2 - ln(2 pi sigma^2)/2, an
+   * entry flagged in lcat_upper (may be NULL) adds the residual only while
+   * m > d (Eq. app_line_chi2_UL); lcat_mask (may be NULL) excludes entries. */
+  int n_lcat;
+  const int *lcat_len, *lcat_line;
+  const double *lcat_d, *lcat_sigma;
+  const uint8_t *lcat_mask, *lcat_upper;
 } sed_model_desc;
+
+#define SED_GAS_SIGMA_TIED 0
+#define SED_GAS_SIGMA_FIXED 1
+#define SED_GAS_SIGMA_SAMPLED 2
 
 #define SED_CALIB_MARGINAL 0
 #define SED_CALIB_OPTIMISED 1

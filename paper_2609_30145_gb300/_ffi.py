@@ -21,13 +21,15 @@ ROW_BAD_THETA, ROW_BAD_Z, ROW_BAD_TMAX, ROW_NONFINITE, ROW_DEVICE_TIMEOUT = 1, 2
 KEYS = ("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow", "diffuse_tau_kc",
         "diffuse_dust_index", "gas_logz", "gas_logu", "sigma_gal",
         "log_err_scale_phot", "log_f_calib_phot", "log_f_data_phot", "log_jitter_phot",
-        "log_err_scale_spec", "log_f_calib_spec", "log_f_data_spec", "log_jitter_spec", "frac_obrun")
+        "log_err_scale_spec", "log_f_calib_spec", "log_f_data_spec", "log_jitter_spec", "frac_obrun",
+        "sigma_gas")
 FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
 SFH_STEP, SFH_LINEAR = 0, 1
 FESC_NONE, FESC_RUNAWAY_BC, FESC_PICKET = 0, 1, 2
 NKEYS = len(KEYS)
 GRID_COPY_FP32, GRID_COPY_FP32_SIMT, GRID_COPY_BF16, GRID_COPY_FP8 = 1, 2, 4, 8
 CALIB_MARGINAL, CALIB_OPTIMISED = 0, 1
+GAS_SIGMA_TIED, GAS_SIGMA_FIXED, GAS_SIGMA_SAMPLED = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 P = C.c_void_p
@@ -37,7 +39,8 @@ class GridDesc(C.Structure):
     _fields_ = [("n_age", C.c_int), ("n_feh", C.c_int), ("n_afe", C.c_int), ("n_lam", C.c_int),
                 ("log_age_yr", P), ("feh", P), ("afe", P), ("lam_aa", P), ("flux", P),
                 ("sigma_lib_kms", P), ("neb_n_logu", C.c_int), ("neb_n_logz", C.c_int),
-                ("neb_logu", P), ("neb_logz", P), ("neb_log10_lnu_per_q", P), ("precision_mask", C.c_uint)]
+                ("neb_logu", P), ("neb_logz", P), ("neb_log10_lnu_per_q", P), ("precision_mask", C.c_uint),
+                ("neb_n_line", C.c_int), ("neb_line_lam_aa", P), ("neb_log10_line_per_q", P)]
 
 
 class ModelDesc(C.Structure):
@@ -53,7 +56,10 @@ class ModelDesc(C.Structure):
                 ("calib_n", C.c_int), ("calib_sigma", P),
                 ("noise_floor_phot", C.c_int), ("noise_floor_spec", C.c_int), ("sfh_scheme", C.c_int),
                 ("phot_upper", P), ("fesc_geometry", C.c_int),
-                ("fixed", C.c_int * NKEYS), ("fixed_val", C.c_double * NKEYS), ("calib_mode", C.c_int)]
+                ("fixed", C.c_int * NKEYS), ("fixed_val", C.c_double * NKEYS), ("calib_mode", C.c_int),
+                ("use_lines", C.c_int), ("gas_sigma_mode", C.c_int), ("sigma_gas_kms", C.c_double),
+                ("sigma_gas_max_kms", C.c_double), ("n_lcat", C.c_int), ("lcat_len", P), ("lcat_line", P),
+                ("lcat_d", P), ("lcat_sigma", P), ("lcat_mask", P), ("lcat_upper", P)]
 
 
 class StageStats(C.Structure):

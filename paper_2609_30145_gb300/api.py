@@ -105,6 +105,11 @@ class Context:
             keep += [nu, nz, nt]
             d.neb_n_logu, d.neb_n_logz = nt.shape[:2]
             d.neb_logu, d.neb_logz, d.neb_log10_lnu_per_q = _ptr(nu), _ptr(nz), _ptr(nt)
+            if getattr(grid, "line_tab", None) is not None:
+                ll, lt = _f64(grid.line_lam), _f64(grid.line_tab)
+                keep += [ll, lt]
+                d.neb_n_line = ll.size
+                d.neb_line_lam_aa, d.neb_log10_line_per_q = _ptr(ll), _ptr(lt)
         d.precision_mask = int(precision_mask)
         gid = C.c_int32()
         self._check(self._lib.sed_load_grid(self._h, C.byref(d), C.byref(gid)))
@@ -116,9 +121,12 @@ class Context:
                      spec_sigma=None, spec_mask=None, lsf_mode=0, lsf_value=None,
                      sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0,
                      calib_sigma=None, noise_floor_phot=0, noise_floor_spec=0, sfh_scheme=0,
-                     phot_upper=None, fesc_geometry=0, fixed=None, calib_mode=0) -> "Model":
+                     phot_upper=None, fesc_geometry=0, fixed=None, calib_mode=0, use_lines=0,
+                     gas_sigma_mode=0, sigma_gas_kms=300.0, sigma_gas_max_kms=1000.0, lcat=None) -> "Model":
         """fixed: optional {key name: value} of keys fixed for every row (no
-        column in the parameter rows, no gradient); key names as in _ffi.KEYS."""
+        column in the parameter rows, no gradient); key names as in _ffi.KEYS.
+        lcat: optional line catalogue (blends: list of lists of grid-line
+        indices, data, sigma, mask or None, upper-limit flags or None)."""
         d = _ffi.ModelDesc()
         d.grid, d.n_sfh, d.zf, d.zmode = grid_id, n_sfh, zf, zmode
         d.use_afe, d.use_nebular, d.dust_law = use_afe, use_nebular, dust_law
@@ -151,6 +159,19 @@ class Context:
             keep.append(cs)
             d.calib_n, d.calib_sigma = cs.size, _ptr(cs)
         d.calib_mode = int(calib_mode)
+        d.use_lines, d.gas_sigma_mode = int(use_lines), int(gas_sigma_mode)
+        d.sigma_gas_kms, d.sigma_gas_max_kms = float(sigma_gas_kms), float(sigma_gas_max_kms)
+        if lcat is not None:
+            blends, ld, ls, lm, lu = lcat
+            lens = np.ascontiguousarray([len(b) for b in blends], dtype=np.int32)
+            lines = np.ascontiguousarray(np.concatenate([np.asarray(b, dtype=np.int32) for b in blends]), dtype=np.int32)
+            ld, ls = _f64(ld), _f64(ls)
+            lm = None if lm is None else np.ascontiguousarray(lm, dtype=np.uint8)
+            lu = None if lu is None else np.ascontiguousarray(lu, dtype=np.uint8)
+            keep += [lens, lines, ld, ls, lm, lu]
+            d.n_lcat = len(blends)
+            d.lcat_len, d.lcat_line, d.lcat_d, d.lcat_sigma = _ptr(lens), _ptr(lines), _ptr(ld), _ptr(ls)
+            d.lcat_mask, d.lcat_upper = _ptr(lm), _ptr(lu)
         d.noise_floor_phot, d.noise_floor_spec = int(noise_floor_phot), int(noise_floor_spec)
         d.sfh_scheme = int(sfh_scheme)
         d.fesc_geometry = int(fesc_geometry)

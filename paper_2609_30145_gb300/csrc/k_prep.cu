@@ -509,6 +509,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     const float f = th[md.offs[SED_KEY_FRAC_OBRUN]];
     if (!(f >= 0.f && f <= 1.f)) status = SED_ROW_BAD_THETA;
   }
+  // a sampled gas dispersion outside its declared range [0, max]
+  if (!status && md.gas_mode == SED_GAS_SIGMA_SAMPLED) {
+    const float sg = th[md.offs[SED_KEY_SIGMA_GAS]];
+    if (!(sg >= 0.f && sg <= md.sgas_max_kms)) status = SED_ROW_BAD_THETA;
+  }
   const CosmoRow cr = s_cr;
   if (!status) status = cr.status;
   const double tmax = status ? 0.0 : (double)cr.tmax_d;
@@ -754,6 +759,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.y_scale = y_scale;
     rs.sg_ln = md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] / (float)C_KMS : 0.f;
     rs.fob = md.fesc_geom ? th[md.offs[SED_KEY_FRAC_OBRUN]] : 0.f;
+    // the emission lines' gas dispersion (km/s): a column, a fixed value, or
+    // tied to the stellar dispersion (the row's sampled sigma_gal, else the fixed one)
+    rs.sgas = md.gas_mode == SED_GAS_SIGMA_SAMPLED ? th[md.offs[SED_KEY_SIGMA_GAS]]
+            : md.gas_mode == SED_GAS_SIGMA_FIXED ? md.sgas_fix_kms
+            : (md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] : md.sgal_fix_kms);
     rs.k_lo = win_lo;
     rs.k_hi = win_hi;
     if (a.tile_win) {   // union of the windows of this row's 128-row tile

@@ -243,6 +243,18 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
     for (size_t i = 0; i < nt; i++)
       if (!std::isfinite(d->neb_log10_lnu_per_q[i])) return fail(ctx, SED_EINVAL, "nebular template not finite");
   }
+  if (d->neb_n_line < 0 || d->neb_n_line > MAX_LINES)
+    return fail(ctx, SED_ERANGE, "neb_n_line must be in [0, %d]", MAX_LINES);
+  if (d->neb_n_line > 0) {
+    if (!neb) return fail(ctx, SED_EINVAL, "an emission-line cube needs the nebular template and its axes");
+    if (!d->neb_line_lam_aa || !d->neb_log10_line_per_q) return fail(ctx, SED_EINVAL, "line cube pointer is NULL");
+    for (int l = 0; l < d->neb_n_line; l++)
+      if (!(d->neb_line_lam_aa[l] > 0 && std::isfinite(d->neb_line_lam_aa[l])))
+        return fail(ctx, SED_EINVAL, "line wavelength %d must be finite and > 0", l);
+    const size_t nt = (size_t)d->neb_n_logu * d->neb_n_logz * d->neb_n_line;
+    for (size_t i = 0; i < nt; i++)
+      if (!std::isfinite(d->neb_log10_line_per_q[i])) return fail(ctx, SED_EINVAL, "line cube not finite");
+  }
 
   Grid* g = new Grid();
   g->n_age = d->n_age; g->n_feh = d->n_feh; g->n_afe = d->n_afe; g->n_lam = d->n_lam;
@@ -369,6 +381,33 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
     st = upload(ctx, &p, tab.data(), nt, &g->allocs, &g->bytes);
     dv.neb_tab = p;
     dv.neb_nu = g->neb_nu; dv.neb_nz = g->neb_nz;
+    // emission-line cube: per line the constants of the attenuation at its
+    // wavelength, ln(lambda) as an FP32 pair, and log10(L/Q) with the same
+    // device-unit offset as the continuum template
+    if (!st && d->neb_n_line > 0) {
+      const int NLn = d->neb_n_line;
+      g->n_line = NLn;
+      std::vector<float4> a4(NLn);
+      std::vector<float2> l2(NLn);
+      for (int l = 0; l < NLn; l++) {
+        const double L = d->neb_line_lam_aa[l], x = L * 350.0, dd = L * L - 2175.0 * 2175.0;
+        a4[l] = make_float4((float)std::log(L / 5500.0), (float)(calzetti_kprime(L * 1e-4) / 4.05),
+                            (float)(x * x / (dd * dd + x * x) / 4.05), (float)L);
+        const double ll = std::log(L);
+        l2[l].x = (float)ll;
+        l2[l].y = (float)(ll - (double)l2[l].x);
+      }
+      const size_t ntl = (size_t)g->neb_nu * g->neb_nz * NLn;
+      std::vector<float> lt(ntl);
+      for (size_t i = 0; i < ntl; i++) lt[i] = (float)(d->neb_log10_line_per_q[i] + off);
+      float4* p4;
+      float2* p2;
+      st = upload(ctx, &p4, a4.data(), NLn, &g->allocs, &g->bytes);
+      dv.line_att4 = p4;
+      if (!st) { st = upload(ctx, &p2, l2.data(), NLn, &g->allocs, &g->bytes); dv.line_ln2 = p2; }
+      if (!st) { st = upload(ctx, &p, lt.data(), ntl, &g->allocs, &g->bytes); dv.line_tab = p; }
+      dv.n_line = NLn;
+    }
   }
   if (st) {
     free_all(ctx, g->allocs, g->bytes);
@@ -701,7 +740,7 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   if (d->use_afe && g->n_afe < 2) return fail(ctx, SED_EINVAL, "use_afe needs a grid with an [a/Fe] axis");
   if (d->n_filt < 0 || d->n_filt > 128) return fail(ctx, SED_ERANGE, "n_filt must be in [0, 128]");
   if (d->n_pix < 0) return fail(ctx, SED_EINVAL, "n_pix < 0");
-  if (d->n_filt == 0 && d->n_pix == 0) return fail(ctx, SED_EINVAL, "model has no observation");
+  if (d->n_filt == 0 && d->n_pix == 0 && d->n_lcat <= 0) return fail(ctx, SED_EINVAL, "model has no observation");
   if (!std::isfinite(d->bc_edge_log_age_yr)) return fail(ctx, SED_EINVAL, "bc edge not finite");
   if (d->n_filt && (!d->filt_len || !d->filt_lam_aa || !d->filt_trans))
     return fail(ctx, SED_EINVAL, "filter arrays are NULL");
@@ -732,6 +771,31 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   if (d->noise_floor_spec && d->n_pix <= 0) return fail(ctx, SED_EINVAL, "a spectral noise floor needs a spectrum");
   if (d->noise_floor_spec && d->calib_n > 0)
     return fail(ctx, SED_EUNSUPPORTED, "a spectral noise floor with the calibration polynomial is not supported");
+  if (d->use_lines != 0 && d->use_lines != 1) return fail(ctx, SED_EINVAL, "use_lines must be 0 or 1");
+  if (d->use_lines && (!d->use_nebular || g->n_line == 0))
+    return fail(ctx, SED_EINVAL, "emission lines need use_nebular and a grid with a line cube");
+  if (d->gas_sigma_mode < SED_GAS_SIGMA_TIED || d->gas_sigma_mode > SED_GAS_SIGMA_SAMPLED)
+    return fail(ctx, SED_EINVAL, "gas_sigma_mode must be SED_GAS_SIGMA_TIED, _FIXED or _SAMPLED");
+  if (d->use_lines && d->gas_sigma_mode == SED_GAS_SIGMA_FIXED && !(d->sigma_gas_kms >= 0 && d->sigma_gas_kms < 1e5))
+    return fail(ctx, SED_EINVAL, "sigma_gas_kms must be in [0, 1e5)");
+  if (d->use_lines && d->gas_sigma_mode == SED_GAS_SIGMA_SAMPLED &&
+      !(d->sigma_gas_max_kms > 0 && d->sigma_gas_max_kms < 1e5))
+    return fail(ctx, SED_EINVAL, "sigma_gas_max_kms must be in (0, 1e5) when sigma_gas is sampled");
+  if (d->n_lcat < 0 || d->n_lcat > 1024) return fail(ctx, SED_ERANGE, "n_lcat must be in [0, 1024]");
+  if (d->n_lcat > 0) {
+    if (!d->use_lines) return fail(ctx, SED_EINVAL, "a line catalogue needs use_lines");
+    if (!d->lcat_len || !d->lcat_line || !d->lcat_d || !d->lcat_sigma)
+      return fail(ctx, SED_EINVAL, "line catalogue arrays are NULL");
+    int c = 0;
+    for (int k = 0; k < d->n_lcat; k++) {
+      if (d->lcat_len[k] < 1 || d->lcat_len[k] > MAX_LINES) return fail(ctx, SED_EINVAL, "lcat_len[%d] out of range", k);
+      for (int j = 0; j < d->lcat_len[k]; j++, c++)
+        if (d->lcat_line[c] < 0 || d->lcat_line[c] >= g->n_line)
+          return fail(ctx, SED_EINVAL, "line catalogue entry %d names line %d of %d", k, d->lcat_line[c], g->n_line);
+      if (!std::isfinite(d->lcat_d[k]) || !(d->lcat_sigma[k] > 0 && std::isfinite(d->lcat_sigma[k])))
+        return fail(ctx, SED_EINVAL, "line catalogue entry %d: datum not finite or sigma <= 0", k);
+    }
+  }
 
   Model* M = new Model();
   M->grid = d->grid;
@@ -762,6 +826,14 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   dv.fesc_geom = d->fesc_geometry;
   dv.offs[SED_KEY_FRAC_OBRUN] = o;
   o += d->fesc_geometry ? 1 : 0;
+  // gas dispersion of the emission lines when sampled (Sec. 2.7)
+  dv.use_lines = d->use_lines;
+  dv.gas_mode = d->use_lines ? d->gas_sigma_mode : SED_GAS_SIGMA_FIXED;
+  dv.sgas_fix_kms = (float)d->sigma_gas_kms;
+  dv.sgas_max_kms = (float)d->sigma_gas_max_kms;
+  dv.sgal_fix_kms = (float)d->sigma_gal_kms;
+  dv.offs[SED_KEY_SIGMA_GAS] = o;
+  o += dv.gas_mode == SED_GAS_SIGMA_SAMPLED ? 1 : 0;
   // fixed keys (Sec. 4 parameter dictionary): a fixed one-column key leaves the
   // caller's rows; the kernels read it past the caller's columns
   {
@@ -838,7 +910,7 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
       bs[b + 1] = bs[b] + d->filt_len[b];
     }
     const int S = st ? 0 : bs[d->n_filt];
-    std::vector<float> sl(S), sw(S);
+    std::vector<float> sl(S), sw(S), srz(S);
     double lmin = 1e300, lmax = 0;
     for (int b = 0; !st && b < d->n_filt; b++) {
       const double* L = d->filt_lam_aa + bs[b];
@@ -859,6 +931,7 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
                                  : (j == n - 1 ? 0.5 * (L[n - 1] - L[n - 2]) : 0.5 * (L[j + 1] - L[j - 1]));
         sl[bs[b] + j] = (float)L[j];
         sw[bs[b] + j] = (float)(R[j] * L[j] * dl / zb);
+        srz[bs[b] + j] = (float)(R[j] / zb);
         lmin = std::min(lmin, L[j]);
         lmax = std::max(lmax, L[j]);
       }
@@ -873,6 +946,11 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     for (int j = 0; j < S; j++) s2[j] = make_float2(sl[j], sw[j]);
     float2* p2;
     if (!st) { st = upload(ctx, &p2, s2.data(), s2.size(), &M->allocs, &M->bytes); dv.samp2 = p2; }
+    if (!st && d->use_lines) {   // a line's photometry: R / Z_b at the samples
+      float* pr;
+      st = upload(ctx, &pr, srz.data(), srz.size(), &M->allocs, &M->bytes);
+      dv.samp_rz = pr;
+    }
     std::vector<double> zeros(d->n_filt, 0.0);
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_d = pd; }
     if (!st) { st = upload(ctx, &pd, zeros.data(), zeros.size(), &M->allocs, &M->bytes); dv.phot_isig = pd; }
@@ -903,13 +981,15 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     if (!strictly_increasing(d->spec_lam_aa, np) || !(d->spec_lam_aa[0] > 0))
       st = fail(ctx, SED_EINVAL, "spectrum wavelengths must be strictly increasing and > 0");
     std::vector<double> pl(np);
-    std::vector<float> ps(np), pf2(np);
+    std::vector<float> ps(np), pf2(np), psi(np), plc(np);
     double smax = 0;
     const double sg = d->sample_sigma_gal ? d->sigma_gal_max_kms : d->sigma_gal_kms;
     for (int i = 0; !st && i < np; i++) {
       const double lo_ = d->spec_lam_aa[i];
       if (!(d->lsf_value[i] > 0 && std::isfinite(d->lsf_value[i]))) { st = fail(ctx, SED_EINVAL, "lsf_value[%d] must be > 0", i); break; }
       const double si = sigma_inst_kms(d->lsf_mode, d->lsf_value[i], lo_);
+      psi[i] = (float)si;
+      plc[i] = (float)(lo_ / C_AA);
       const double lr = lo_ / (1.0 + d->z_ref);
       double slib;
       const auto& L = g->lam;
@@ -947,6 +1027,11 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
       st = upload(ctx, &pf, pf2.data(), pf2.size(), &M->allocs, &M->bytes);
       dv.pix_fix2 = pf;
     }
+    if (!st && d->use_lines) {   // the line profiles: instrumental dispersion and lambda / c per pixel
+      st = upload(ctx, &pf, psi.data(), np, &M->allocs, &M->bytes);
+      dv.pix_sinst = pf;
+      if (!st) { st = upload(ctx, &pf, plc.data(), np, &M->allocs, &M->bytes); dv.pix_lamc = pf; }
+    }
     // calibration polynomial: Chebyshev coordinate of each pixel, prior terms
     if (!st && d->calib_n > 0) {
       std::vector<float> cx(np);
@@ -968,6 +1053,37 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     if (!st) { st = upload(ctx, &pf, zerof.data(), np, &M->allocs, &M->bytes); dv.spec_isf = pf; }
     if (!st) { st = upload(ctx, &pd, zeros.data(), np, &M->allocs, &M->bytes); dv.spec_nlog = pd; }
     if (d->spec_mask) M->spec_mask_h.assign(d->spec_mask, d->spec_mask + np);
+  }
+  // ---- line catalogue (Sec. 3.3): blends, data in FP64, masked entries out of lnL
+  if (!st && d->n_lcat > 0) {
+    const int nk = d->n_lcat;
+    std::vector<int> start(nk + 1, 0);
+    for (int k = 0; k < nk; k++) start[k + 1] = start[k] + d->lcat_len[k];
+    std::vector<int> lines(d->lcat_line, d->lcat_line + start[nk]);
+    std::vector<double> ld(nk), li(nk), ln(nk);
+    std::vector<uint8_t> ul(nk, 0);
+    bool any_ul = false;
+    for (int k = 0; k < nk; k++) {
+      const bool inc = !d->lcat_mask || d->lcat_mask[k];
+      ld[k] = d->lcat_d[k];
+      li[k] = inc ? 1.0 / d->lcat_sigma[k] : 0.0;
+      ln[k] = inc ? -0.5 * std::log(2.0 * M_PI * d->lcat_sigma[k] * d->lcat_sigma[k]) : 0.0;
+      any_ul |= (ul[k] = d->lcat_upper && d->lcat_upper[k] ? 1 : 0) != 0;
+    }
+    int* pi;
+    double* pd;
+    st = upload(ctx, &pi, start.data(), start.size(), &M->allocs, &M->bytes);
+    dv.lcat_start = pi;
+    if (!st) { st = upload(ctx, &pi, lines.data(), lines.size(), &M->allocs, &M->bytes); dv.lcat_line = pi; }
+    if (!st) { st = upload(ctx, &pd, ld.data(), nk, &M->allocs, &M->bytes); dv.lcat_d = pd; }
+    if (!st) { st = upload(ctx, &pd, li.data(), nk, &M->allocs, &M->bytes); dv.lcat_isig = pd; }
+    if (!st) { st = upload(ctx, &pd, ln.data(), nk, &M->allocs, &M->bytes); dv.lcat_nlog = pd; }
+    if (!st && any_ul) {
+      uint8_t* pu;
+      st = upload(ctx, &pu, ul.data(), nk, &M->allocs, &M->bytes);
+      dv.lcat_ul = pu;
+    }
+    dv.n_lcat = nk;
   }
   // widest rest-frame window a row can need: the observed span of the filter
   // samples and spectral pixels (5 dispersions out) is a fixed wavelength ratio
@@ -1337,6 +1453,8 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   if (st) return st;
   if (precision == SED_PREC_BF16 || precision == SED_PREC_FP8)
     return fail(ctx, SED_EUNSUPPORTED, "the gradient is available for SED_PREC_FP32 and SED_PREC_FP32_SIMT");
+  if (M->dv.use_lines || M->dv.n_lcat > 0)
+    return fail(ctx, SED_EUNSUPPORTED, "the adjoint does not cover emission lines: use sed_loglike / sed_forward");
   if (n > 0 && (!lnl_out || !grad_out)) return fail(ctx, SED_EINVAL, "lnl_out or grad_out is NULL");
   if (n == 0) return SED_OK;
   DevGuard dg(ctx->device);

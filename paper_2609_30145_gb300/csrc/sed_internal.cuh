@@ -33,6 +33,7 @@ constexpr int COSMO_COLS = 8;    // value / derivative pairs of D_C, t_univ, ln(
 // precision's operand layout (32 FP32 / 64 BF16 / 128 FP8 columns), one row of
 // KMASK_WORDS words per 128-row tile; grids with more K tiles run unmasked
 constexpr int KMASK_WORDS = 8;
+constexpr int MAX_LINES = 128;   // emission lines of a nebular grid
 
 // Physical constants (cgs unless noted).
 constexpr double LSUN = 3.839e33;              // erg/s (Sec. 2.6)
@@ -74,6 +75,7 @@ struct RowScal {
   float sg_ln;      // sampled sigma_gal / c (ln-lambda units); 0 with a fixed sigma_gal
   float fl[2][4];   // noise floor {s, f_calib, f_data, j} of photometry [0] and spectrum [1]
   float fob;        // runaway fraction f_ob (0 without an escape geometry)
+  float sgas;       // gas velocity dispersion of the emission lines, km/s
 };
 
 // Cosmology and observer-frame scalars of one row (computed at the start of k_prep).
@@ -106,6 +108,12 @@ struct GridDev {
   const float* age_dl;     // ln(t_{a+1} / t_a) (last entry unused)
   const float* neb_tab;    // [nu][nz][n_lam] log10 template + device-unit offset
   int neb_nu, neb_nz;
+  // emission-line cube: per line {ln(lam/5500), k'/4.05, Drude/4.05, lam},
+  // ln(lam) as an FP32 pair, and [nu][nz][n_line] log10(L/Q) + device-unit offset
+  int n_line;
+  const float4* line_att4;
+  const float2* line_ln2;
+  const float* line_tab;
 };
 
 struct LayoutDev {
@@ -174,6 +182,20 @@ struct ModelDev {
   // it (offs[] points there), filled from fixed_v[j]
   int n_fixed;
   float fixed_v[SED_NKEYS];
+  // emission lines (App. C, App. line_proj, Eq. app_line_profile)
+  int use_lines, gas_mode;   // SED_GAS_SIGMA_*
+  float sgas_fix_kms, sgas_max_kms, sgal_fix_kms;
+  const float* samp_rz;      // [n_samp] filter transmission R_j / Z_b (the photometry of a line)
+  const float* pix_sinst;    // [n_pix] instrumental dispersion, km/s
+  const float* pix_lamc;     // [n_pix] lambda_obs / c, s
+  // line catalogue (Sec. 3.3): entry k sums the lines lcat_line[lcat_start[k] .. lcat_start[k+1])
+  int n_lcat;
+  const int* lcat_start;
+  const int* lcat_line;
+  const double* lcat_d;      // datum, 1/sigma (0 when masked out), -ln(2 pi sigma^2)/2 (0 when masked out)
+  const double* lcat_isig;
+  const double* lcat_nlog;
+  const uint8_t* lcat_ul;    // 1: an upper limit (Eq. app_line_chi2_UL); NULL: none
 };
 
 // Value of column `col` of a parameter row in the kernels' layout: a caller's
@@ -216,6 +238,7 @@ struct Layout {
 
 struct Grid {
   int n_age = 0, n_feh = 0, n_afe = 0, n_lam = 0;
+  int n_line = 0;          // emission lines of the nebular grid
   unsigned copies = 0;     // SED_GRID_COPY_* bits built with each layout
   unsigned avail = 0;      // precisions a call may use (FP8 built on first use when not in `copies`)
   std::vector<double> log_age, feh, afe, lam, flux;  // host master copy (FP64)
@@ -536,6 +559,7 @@ struct EpiArgs {
   double* lnl; uint32_t* status;
   const int* err;      // device error word of the contraction (row status SED_ROW_DEVICE_TIMEOUT)
   const float* lam8;   // FP8 path: [n_lam] 2^-f_l multiplying Y and O; NULL otherwise
+  int lines_off;       // set by launch_epilogue: float offset of the emission lines' shared arrays
 };
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 

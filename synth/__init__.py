@@ -374,6 +374,20 @@ WORKLOADS["phot_107x12x6000_b4096"] = Workload(**{**_w.__dict__, "name": "phot_1
                                                   "batch": 4096})
 
 
+# JADES-like spectro-photometric fit with the nebular grid's emission lines
+# apart from its continuum (App. C): the paper-scale photometric grid with a
+# 30-line cube, a 1500-pixel R = 100-1000 spectrum, 20 filters and a line
+# catalogue (Sec. 3.3); sigma_gas sampled in U[50, 400] km/s (bound 600)
+_p = WORKLOADS["phot_107x12x6000_b1024"]
+WORKLOADS["specphot_lines_107x12x6000_b1024"] = Workload(**{
+    **_p.__dict__, "name": "specphot_lines_107x12x6000_b1024",
+    "grid_kw": dict(_p.grid_kw, nebular=dict(seed=2, n_logu=7, n_logz=12, line_cube=30)),
+    "spectrum": dict(n_pix=1500, lo_um=0.6, hi_um=5.3, r_lo=100.0, r_hi=1000.0, snr=20.0),
+    "z_ref": 6.0, "sigma_gal_kms": 300.0,
+    "ranges": {**_p.ranges, "sigma_gas": (50.0, 400.0)},
+    "extra": {"lines": dict(gas_sigma_mode=2, sigma_gas_max_kms=600.0, n_lcat=12)}})
+
+
 def workload_filters(w: Workload):
     if w.filters == "gauss8":
         return make_filters_gauss(8, 0.6, 4.5, 0.2, 200)

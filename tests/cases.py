@@ -104,6 +104,8 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True, fixed=None):
                   spec_mask=orc.spec_mask, lsf_mode=orc.lsf_mode, lsf_value=orc.lsf_value,
                   sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref, calib_sigma=orc.calib_sigma,
                   calib_mode=orc.calib_mode)
+    kw.update(use_lines=orc.use_lines, gas_sigma_mode=orc.gas_sigma_mode, sigma_gas_kms=orc.sigma_gas_kms,
+              sigma_gas_max_kms=orc.sigma_gas_max_kms, lcat=orc.lcat)
     return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, fixed=fixed, **kw)
 
 
@@ -206,4 +208,61 @@ def escape_pair(w: synth.Workload, n, seed, geometry):
     d["frac_obrun"] = np.random.default_rng(seed + 2000).uniform(0.05, 0.95, n)
     th32 = oracle.pack_theta(d, w.n_sfh, w.zmode, w.sample_sigma_gal, w.floor_phot, w.floor_spec,
                              w.sfh_scheme, geometry).astype(np.float32)
+    return th32, th32.astype(np.float64)
+
+
+def lines_case(w: synth.Workload, gas_sigma_mode=2, sigma_gas_kms=300.0, sigma_gas_max_kms=600.0, n_lcat=12,
+               seed=7):
+    """Oracle of a workload whose grid carries an emission-line cube, with the
+    lines on (App. C, App. line_proj), the given gas dispersion mode, and a line
+    catalogue of n_lcat entries (Sec. 3.3): single lines and blends of two or
+    three neighbours, two upper limits (one exceeded at the truth, one not) and
+    one masked entry.  Photometry, spectrum and catalogue data are the model
+    of a true row (z = 2, sigma_gas = 150 km/s when sampled) with 5% noise."""
+    orc = oracle_for(w, with_data=False)
+    orc = dataclasses.replace(orc, use_lines=1, gas_sigma_mode=gas_sigma_mode, sigma_gas_kms=sigma_gas_kms,
+                              sigma_gas_max_kms=sigma_gas_max_kms)
+    d_true = synth.make_theta(1, w.n_sfh, w.zmode, w.ranges, seed=99)
+    d_true["zred"][:] = min(2.0, w.zf * 0.5)
+    sampled = gas_sigma_mode == 2
+    if sampled:
+        d_true["sigma_gas"] = np.array([150.0])
+    th = oracle.pack_theta(d_true, w.n_sfh, w.zmode, w.sample_sigma_gal, sample_sigma_gas=int(sampled))
+    res = orc.eval(th)
+    assert res["status"][0] == 0
+    fl = orc.line_fluxes(th)[0]
+    nl = fl.size
+    rng = np.random.default_rng(seed)
+    blends, k = [], 0
+    while len(blends) < n_lcat and k < nl:
+        size = 1 + int(rng.integers(0, 3)) if len(blends) % 3 == 1 else 1
+        blends.append(list(range(k, min(k + size, nl))))
+        k += size
+    m = np.array([fl[b].sum() for b in blends])
+    nz = synth.noise(res["phot"].shape[1] + res["spec"].shape[1] + len(blends), seed=5)
+    ph, sp_ = res["phot"][0], res["spec"][0]
+    snr = 20.0
+    ld = m * (1 + nz[-len(blends):] / snr)
+    upper = np.zeros(len(blends), np.uint8)
+    mask = np.ones(len(blends), np.uint8)
+    if len(blends) >= 4:
+        upper[1], ld[1] = 1, 0.5 * m[1]      # exceeded at the truth
+        upper[2], ld[2] = 1, 3.0 * m[2]      # respected
+        mask[3] = 0
+    orc = dataclasses.replace(orc, lcat=(blends, ld, np.abs(m) / snr, mask, upper))
+    orc.set_data(phot_d=ph * (1 + nz[:ph.size] / snr), phot_sigma=np.abs(ph) / snr,
+                 spec_d=(sp_ * (1 + nz[ph.size:ph.size + sp_.size] / snr)) if sp_.size else None,
+                 spec_sigma=(np.abs(sp_) / snr) if sp_.size else None)
+    return orc
+
+
+def lines_theta_pair(w: synth.Workload, orc, n, seed=4):
+    """Parameter rows of a lines case: the workload's draws plus sigma_gas
+    ~ U[50, 400] km/s in the last column when the model samples it."""
+    d = theta_dict(w, n, seed)
+    sampled = orc.gas_sigma_mode == 2
+    if sampled:
+        d["sigma_gas"] = np.random.default_rng(seed + 3000).uniform(50.0, 400.0, n)
+    th32 = oracle.pack_theta(d, w.n_sfh, w.zmode, w.sample_sigma_gal, w.floor_phot, w.floor_spec, w.sfh_scheme,
+                             sample_sigma_gas=int(sampled)).astype(np.float32)
     return th32, th32.astype(np.float64)

@@ -45,6 +45,8 @@ def test_enum_values_match_header():
                       ("SED_KEY_LOG_ERR_SCALE_PHOT", _ffi.KEYS.index("log_err_scale_phot")),
                       ("SED_KEY_LOG_JITTER_SPEC", _ffi.KEYS.index("log_jitter_spec")),
                       ("SED_KEY_FRAC_OBRUN", _ffi.KEYS.index("frac_obrun")),
+                      ("SED_KEY_SIGMA_GAS", _ffi.KEYS.index("sigma_gas")),
+                      ("SED_GAS_SIGMA_SAMPLED", _ffi.GAS_SIGMA_SAMPLED),
                       ("SED_FESC_RUNAWAY_BC", _ffi.FESC_RUNAWAY_BC), ("SED_FESC_PICKET", _ffi.FESC_PICKET),
                       ("SED_FLOOR_ERR_SCALE", _ffi.FLOOR_ERR_SCALE), ("SED_FLOOR_F_CALIB", _ffi.FLOOR_F_CALIB),
                       ("SED_FLOOR_F_DATA", _ffi.FLOOR_F_DATA), ("SED_FLOOR_JITTER", _ffi.FLOOR_JITTER),
@@ -71,7 +73,7 @@ def test_layout_packing_matches_oracle_layout():
     from paper_2609_30145_gb300 import _ffi
     for zmode in (0, 1):
         for sgal in (0, 1):
-            for fp, fs, fe in ((0, 0, 0), (5, 0, 1), (0, 15, 2), (9, 6, 0)):
+            for fp, fs, fe, sgas in ((0, 0, 0, 0), (5, 0, 1, 1), (0, 15, 2, 0), (9, 6, 0, 1)):
                 for scheme in (0, 1):
                     ranges = dict(synth.WORKLOADS["tiny_phot_16x4x512"].ranges, sigma_gal=(50.0, 500.0))
                     d = synth.make_theta(5, 7, zmode, ranges, seed=3)
@@ -81,18 +83,19 @@ def test_layout_packing_matches_oracle_layout():
                     for k in _ffi.KEYS[12:]:
                         d[k] = rng.uniform(-2.0, 0.5, 5)
                     d["frac_obrun"] = rng.uniform(0.0, 1.0, 5)
+                    d["sigma_gas"] = rng.uniform(50.0, 400.0, 5)
                     m = Model.__new__(Model)
                     nz = 7 if zmode == 0 else 1
                     # the library's layout: the SFH key has N_T (+1 for the linear
-                    # scheme) columns; sigma_gal, each floor term and f_ob one only when on
+                    # scheme) columns; sigma_gal, each floor term, f_ob and sigma_gas one only when on
                     widths = [7 + scheme, nz] + [1] * 9 + [sgal] + [(fp >> k) & 1 for k in range(4)] + \
-                             [(fs >> k) & 1 for k in range(4)] + [1 if fe else 0]
+                             [(fs >> k) & 1 for k in range(4)] + [1 if fe else 0] + [sgas]
                     offs = list(np.cumsum([0] + widths[:-1]))
                     m.n_param = int(sum(widths))
                     m.offsets = dict(zip(_ffi.KEYS, offs))
                     a = m.pack(d, dtype=np.float64)
                     b = oracle.pack_theta(d, 7, zmode, sample_sigma_gal=sgal, floor_phot=fp, floor_spec=fs,
-                                          sfh_scheme=scheme, fesc_geometry=fe)
+                                          sfh_scheme=scheme, fesc_geometry=fe, sample_sigma_gas=sgas)
                     np.testing.assert_array_equal(a, b)
 
 
