@@ -17,6 +17,12 @@
 //                                   d/ddelta, d/dQ_young, d/dlogU, d/dlogZ_gas
 //   observer frame (Sec. 2.6)       d/dlogmass and the part of d/dz that comes
 //                                   from the flux scale and the redshift gather
+//   emission lines (App. C, App. line_proj, Eq. app_line_profile), line catalogue
+//                                   dlnL/dF_l, d/d ln(lam_obs), d/ds_l of each
+//                                   line from the pixels, bands and catalogue
+//                                   entries it enters, then through the line's
+//                                   flux and width to the dust, nebular, mass,
+//                                   redshift and gas-dispersion parameters
 //   contraction (Eq. csp_sum_main)  dlnL/dW = [G_Y SSP_young^T | G_O SSP_old^T]
 //                                   (k_dw_simt here, or the tcgen05 kernel)
 //
@@ -28,6 +34,7 @@
 #include "atten.cuh"
 #include "calib.cuh"
 #include "floor.cuh"
+#include "lines.cuh"
 #include "locate.cuh"
 #include "sed_internal.cuh"
 
@@ -36,8 +43,8 @@ namespace sed {
 constexpr int EB_THREADS = 256;
 constexpr int EB_WARPS = EB_THREADS / 32;
 constexpr int EB_MAX_BANDS = 128;
-constexpr int EB_NRED = 16;   // per-warp partial sums: 14 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
-constexpr int EB_NREDF = 14;
+constexpr int EB_NRED = 18;   // per-warp partial sums: 16 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
+constexpr int EB_NREDF = 16;
 
 __device__ __forceinline__ float tf32_rna_dev(float x) {
   uint32_t r;
@@ -63,13 +70,21 @@ __device__ __forceinline__ void put_g(const EpiBwdArgs& a, float* hi, float* lo,
 constexpr size_t EB_CAL_BYTES = (size_t)EB_WARPS * CAL_NV * sizeof(float) +
                                 (size_t)(SED_MAX_CALIB * SED_MAX_CALIB + 2 * SED_MAX_CALIB) * sizeof(float);
 
-size_t epi_bwd_smem(const EpiBwdArgs& a) {
+size_t epi_bwd_lines_off(const EpiBwdArgs& a) {   // bytes, 8-aligned
   const size_t W = (size_t)a.md.win_max;
   const size_t samp = (size_t)a.md.n_samp * 8;    // node index + interpolation weight
   // 4 floats + node range; with a calibration polynomial also mu/sigma, dmu/dx, dmu/ds, 1/sum w
   const size_t pix = (size_t)a.md.n_pix * (a.md.calib_n ? 36 : 20);
   const size_t u = ((samp > pix ? samp : pix) + 7) & ~(size_t)7;
-  return ((2 * W + 3) & ~(size_t)3) * sizeof(float) + u + (a.md.calib_n ? EB_CAL_BYTES : 0);
+  return ((((2 * W + 3) & ~(size_t)3) * sizeof(float) + u + (a.md.calib_n ? EB_CAL_BYTES : 0)) + 7) & ~(size_t)7;
+}
+// with emission lines: per line ln(lam_obs) (FP32 pair), F_l, A_l, 1/s_l; per
+// pixel dlnL/dmu (the line part of mu/sigma until the calibration solve); per
+// catalogue entry dlnL/dm
+size_t epi_bwd_smem(const EpiBwdArgs& a) {
+  const size_t lines = a.md.use_lines
+                           ? (size_t)a.g.n_line * 20 + (size_t)a.md.n_pix * 4 + (size_t)a.md.n_lcat * 4 : 0;
+  return epi_bwd_lines_off(a) + lines;
 }
 
 __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
@@ -82,6 +97,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   extern __shared__ __align__(16) float smem[];
   __shared__ float ubp[EB_MAX_BANDS], mbp[EB_MAX_BANDS];
   __shared__ int bk0[EB_MAX_BANDS], bk1[EB_MAX_BANDS];
+  __shared__ float mlb[EB_MAX_BANDS], ubm[EB_MAX_BANDS];   // lines: each band's line part, dlnL/dm_b
   __shared__ double red[EB_WARPS][EB_NRED];
 
   const size_t ro = (size_t)r * a.ldn;
@@ -129,6 +145,15 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     cal_Df = cal_Lf + SED_MAX_CALIB * SED_MAX_CALIB;   // after L
     cal_cf = cal_Df + SED_MAX_CALIB;
   }
+  // emission lines: per line ln(lam_obs), F_l, A_l, 1/s_l; per pixel dlnL/dmu;
+  // per catalogue entry dlnL/dm
+  const int NLn = md.use_lines ? g.n_line : 0;
+  float2* ln_x = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem) + a.lines_off);
+  float* ln_F = reinterpret_cast<float*>(ln_x + NLn);
+  float* ln_A = ln_F + NLn;
+  float* ln_is = ln_A + NLn;
+  float* upx = ln_is + NLn;
+  float* ulc = upx + (NLn ? md.n_pix : 0);
   // each thread owns a contiguous run of CH window nodes (CH odd: the runs of a
   // warp fall in distinct shared-memory banks) for the node-owned gathers
   const int nw = k_hi - k_lo + 1;
@@ -147,7 +172,20 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
     phi[k] = g.lam_f[k];
   }
+  for (int l = tid; l < NLn; l += EB_THREADS) line_setup(md, g, rs, eb_kc, l, ln_F, ln_A, ln_is, ln_x);
   __syncthreads();
+  // the catalogue entries' sigma dlnL/dm = (d - m)/sigma, 0 for a respected
+  // upper limit or an entry outside the mask (Eq. app_line_chi2_det,
+  // app_line_chi2_UL)
+  for (int k = tid; k < md.n_lcat; k += EB_THREADS) {
+    const double is = md.lcat_isig[k];
+    float m = 0.f;
+    for (int j = md.lcat_start[k]; j < md.lcat_start[k + 1]; ++j) m += ln_F[md.lcat_line[j]];
+    const double d = md.lcat_d[k];
+    double u = (d - (double)m) * is;
+    if (md.lcat_ul && md.lcat_ul[k] && (double)m <= d) u = 0.0;
+    ulc[k] = (float)u;
+  }
 
   // ---- photometry forward (warp per band, four samples in flight per lane),
   //      the sample brackets, u_b and the gather part of dlnL/dz (the sample
@@ -209,7 +247,12 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
       bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
     }
-    const float mb = rs.p_phot * acc;
+    float lsum = 0.f;   // the band's lines (maggies), one line per lane as in the forward
+    for (int l = lane; l < NLn; l += 32) lsum += line_in_band(md, g, rs, b, l, ln_F[l]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    const float mc = rs.p_phot * acc;   // the continuum part
+    const float mb = NLn ? fmaf(rs.p_phot, acc, lsum) : mc;
     // d lnL / d(band flux) = (d - m)/sigma^2, formed in FP32 from the normalised
     // datum and 1/sigma (0 for a masked band); times p_phot it weighs F
     const float isf = md.phot_isf[b];
@@ -220,7 +263,9 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     }
     const float c_b = wb * (isf * rs.p_phot);
     if (lane == 0) {
-      mbp[b] = mb;
+      mbp[b] = mc;
+      mlb[b] = mb - mc;
+      ubm[b] = wb;   // sigma_b dlnL/dm_b
       ubp[b] = c_b;
       bk0[b] = bmin;
       bk1[b] = bmax;
@@ -333,11 +378,13 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         }
       }
     }
-    const float mi = rs.s_spec * v;
+    const float mline = NLn ? lines_at_pixel(md, i, NLn, ln_A, ln_is, ln_x) : 0.f;
+    const float mi = NLn ? fmaf(rs.s_spec, v, mline) : rs.s_spec * v;
     float ci = 0.f;
     const float isf = md.spec_isf[i];
     const bool inc = valid && isf != 0.f;
     const float ms = inc ? mi * isf : 0.f;   // mu / sigma
+    const float lms = inc ? mline * isf : 0.f;   // its line part
     const float rn = md.spec_dn[i] - ms;     // (d - mu) / sigma where included
     float wsn = rn;                          // sigma d term / d mu
     if (inc) {
@@ -358,16 +405,19 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       dv_s[i] = dv;
       dvs_s[i] = dvs;
       cw_s[i] = cw;
+      if (NLn) upx[i] = lms;
     } else if (inc) {
       // d lnL / d mu_i = r_i / sigma_i^2 (wsn / sigma_i with a noise floor);
-      // d lnL / d v_i = that x s_spec (mu = s_spec v)
-      um_f = fmaf(wsn, ms, um_f);
+      // d lnL / d v_i = that x s_spec (mu = s_spec v); the mass derivative
+      // takes the continuum part (the lines' is in their own pass)
+      um_f = fmaf(wsn, ms - lms, um_f);
       const float us = wsn * (isf * rs.s_spec);
       gz_spec += us * dv * (-rs.inv1pz);
       // s = sqrt(sigma_fix^2 + sigma_gal^2) / c: ds/dsigma_gal = (sigma_gal / c) / (s c)
       if (md.sample_sgal && s > 0.f) g_sgal += us * dvs * (rs.sg_ln / (s * (float)C_KMS));
       ci = us * cw;
     }
+    if (NLn && !md.calib_n) upx[i] = inc ? wsn : 0.f;   // sigma_i d lnL / d mu_i
     prg[i] = (jlo & 0xffff) | (jhi << 16);
     px4[i] = make_float4(xh, xl, ci, tl);   // x_hi ascending in i: the pixels' wavelengths are strictly increasing
   }
@@ -399,7 +449,10 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     const int n = md.calib_n;
     for (int i = tid; i < md.n_pix; i += EB_THREADS) {
       const float m = mu_s[i];
-      if (m == 0.f) continue;
+      if (m == 0.f) {
+        if (NLn) upx[i] = 0.f;
+        continue;
+      }
       const float x = md.pix_cx[i];
       float T[SED_MAX_CALIB], y[SED_MAX_CALIB];
       float p = 0.f, q = 0.f, tp = 1.f, tc = x;
@@ -425,7 +478,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       const float rn = md.spec_dn[i] - m;
       chi += calib_pixel_term(rn, m, p);
       const float ws = fmaf(rn - m * p, 1.f + p, -m * q);
-      um_f = fmaf(ws, m, um_f);
+      um_f = fmaf(ws, NLn ? m - upx[i] : m, um_f);
+      if (NLn) upx[i] = ws;   // sigma_i d lnL / d mu_i
       const float us = ws * (md.spec_isf[i] * rs.s_spec);
       gz_spec += us * dv_s[i] * (-rs.inv1pz);
       if (md.sample_sgal) {
@@ -514,6 +568,109 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
 
   // ---- dust and nebular: dlnL/dY, dlnL/dO and the parameter sums over lambda
   float g_tbc = 0.f, g_abc = 0.f, g_td = 0.f, g_dl = 0.f, g_qy = 0.f, g_lu = 0.f, g_lz = 0.f, g_fob = 0.f;
+  float g_sgas = 0.f, g_lm = 0.f;   // lines: d/dsigma_gas (sampled), d/dln F summed over lines (mass)
+
+  // ---- emission lines, thread per line.  F_l = Q fac_l B_l with Q = Q_young
+  //      (device units), fac_l the attenuation factor and B_l = 10^(lg_l)
+  //      s_spec/(1+z) the flux per unit of both.  The derivatives are gathered
+  //      per unit of B_l from the normalised ones of the data (sigma dlnL/dm
+  //      times m's sensitivity over sigma), which stay within FP32's range:
+  //      G = B dlnL/dF, Gx and Gs the centre's and width's (per unit of Q fac)
+  //      from the pixels within 5 s_l (pixel order), every band (in order) and
+  //      the catalogue entries naming the line; then to the parameters
+  for (int l = tid; l < NLn; l += EB_THREADS) {
+    const float is = ln_is[l];
+    const float2 xlp = ln_x[l];
+    const float4 c = g.line_att4[l];
+    const float lam_obs = c.w / rs.inv1pz;
+    float lg = 0.f, su = 0.f, sz = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float tv = g.line_tab[(rs.neb_off[q] / N) * g.n_line + l];
+      lg = fmaf(rs.neb_w[q], tv, lg);
+      su = fmaf(rs.neb_dwu[q], tv, su);
+      sz = fmaf(rs.neb_dwz[q], tv, sz);
+    }
+    const float B = ex2_approx(3.3219280948873623f * lg) * rs.s_spec * rs.inv1pz;
+    float G = 0.f, Gx = 0.f, Gs = 0.f, Gzp = 0.f;
+    if (md.n_pix > 0 && is > 0.f) {
+      const float sw = 5.0001f / is;
+      int i = 0, i1 = md.n_pix;
+      while (i < i1) {   // first pixel with ln(lambda) >= x - 5 s
+        const int mid = (i + i1) >> 1;
+        if (md.pix_ln2[mid].x < xlp.x - sw) i = mid + 1; else i1 = mid;
+      }
+      for (; i < md.n_pix && md.pix_ln2[i].x <= xlp.x + sw; ++i) {
+        const float up = upx[i];
+        if (up == 0.f) continue;
+        const float2 p = md.pix_ln2[i];
+        const float u = ((p.x - xlp.x) + (p.y - xlp.y)) * is;
+        if (fabsf(u) > 5.f) continue;
+        // B dmu_i/dF_l / sigma_i: the profile at the pixel per unit of Q fac, normalised
+        const float eb = md.spec_isf[i] * md.pix_lamc[i] * B * (__expf(-0.5f * u * u) * is * 0.3989422804014327f);
+        const float w = up * eb;
+        G += w;
+        Gx = fmaf(w, u * is, Gx);                 // dmu / d ln(lam_obs) = F e u / s
+        Gs = fmaf(w, fmaf(u, u, -1.f) * is, Gs);  // dmu / ds = F e (u^2 - 1) / s
+      }
+    }
+    for (int b = 0; b < md.n_filt; ++b) {
+      const float ub = ubm[b];
+      if (ub == 0.f) continue;
+      float rz, drz;
+      line_band_resp(md, b, lam_obs, rz, drz);
+      const float wb = ub * (md.phot_isf[b] * B);
+      G = fmaf(wb, rz * lam_obs, G);
+      Gzp = fmaf(wb, fmaf(lam_obs, drz, rz) * c.w, Gzp);   // d(rz x)/dx, dx/dz = lam_l
+    }
+    for (int k = 0; k < md.n_lcat; ++k)
+      for (int j = md.lcat_start[k]; j < md.lcat_start[k + 1]; ++j)
+        if (md.lcat_line[j] == l) G = fmaf(ulc[k], (float)(md.lcat_isig[k] * (double)B), G);
+    // attenuation factor of the line (atten.cuh's factor of the nebular emission)
+    const float pa = __expf(rs.alpha_bc * c.x), tbc = rs.tau_bc * pa;
+    const float pw = __expf(rs.delta * c.x), shape = dust_shape(md, c, eb_kc, pw);
+    const float dshape = md.dust_law == SED_DUST_POWER_LAW ? pw * c.x : -1.9f * c.z * pw + shape * c.x;
+    const float ed = __expf(-rs.tau_d * shape), ebc = __expf(-tbc), f = rs.fob;
+    float fac, dfac_tbc, dfac_f;
+    if (md.fesc_geom == SED_FESC_PICKET) {
+      fac = ed * (1.f - f) * ebc;
+      dfac_tbc = -fac;
+      dfac_f = -ed * ebc;
+    } else {
+      const float T = (1.f - f) * ebc + f;
+      fac = ed * T * (1.f - f);
+      dfac_tbc = -ed * (1.f - f) * (1.f - f) * ebc;
+      dfac_f = ed * fmaf(1.f - ebc, 1.f - f, -T);
+    }
+    const float Q = ex2_approx(rs.log2_qy);
+    const float gfac = G * Q;          // dlnL / dfac
+    const float gF = gfac * fac;       // dlnL / d ln F_l
+    g_tbc = fmaf(gfac * dfac_tbc, pa, g_tbc);
+    g_abc = fmaf(gfac * dfac_tbc, tbc * c.x, g_abc);
+    const float gtd = -gF;             // dlnL / dtau_d(lam_l)
+    g_td = fmaf(gtd, shape, g_td);
+    g_dl = fmaf(gtd, rs.tau_d * dshape, g_dl);
+    if (md.fesc_geom) g_fob = fmaf(gfac, dfac_f, g_fob);
+    g_qy = fmaf(G, fac, g_qy);        // dlnL / dQ_young
+    g_lu = fmaf(gF * 2.302585092994046f, su, g_lu);
+    g_lz = fmaf(gF * 2.302585092994046f, sz, g_lz);
+    g_lm += gF;
+    // redshift: the flux factor s_spec/(1+z), the profile's centre on the
+    // pixels, its width through sigma_inst(lam_obs), the bands' response
+    const float qf = Q * fac;
+    float gzl = gF * (rs.dlns_dz - rs.inv1pz) + qf * (Gx * rs.inv1pz + Gzp);
+    if (md.n_pix > 0 && is > 0.f) {
+      float si, dsi;
+      line_sigma_inst(md, xlp.x, lam_obs, si, dsi);
+      const float kc2 = (float)(1.0 / (C_KMS * C_KMS));
+      const float gs = qf * Gs;
+      gzl = fmaf(gs, si * dsi * c.w * is * kc2, gzl);        // ds/dz = sigma_inst sigma_inst' lam_l / (c^2 s)
+      const float gsg = gs * rs.sgas * is * kc2;              // ds/dsigma_gas = sigma_gas / (c^2 s)
+      if (md.gas_mode == SED_GAS_SIGMA_SAMPLED) g_sgas += gsg;
+      else if (md.gas_mode == SED_GAS_SIGMA_TIED && md.sample_sgal) g_sgal += gsg;
+    }
+    gz_spec += gzl;
+  }
   for (int k = tid; k < a.ldn; k += EB_THREADS) {
     if (k < k_lo || k > k_hi) {
       put_g(a, a.gy_hi, a.gy_lo, ro + k, 0.f);
@@ -586,7 +743,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   //      the warp in FP32, lnL and d lnL/d ln(mass) in FP64; across the warps
   //      in FP64, one column per lane of warp 0
   float vf[EB_NREDF] = {g_tbc, g_abc, g_td, g_dl, g_lz, g_lu, gz_gather + gz_spec, g_qy, g_sgal,
-                        gfs[0], gfs[1], gfs[2], gfs[3], g_fob};
+                        gfs[0], gfs[1], gfs[2], gfs[3], g_fob, g_sgas, g_lm};
 #pragma unroll
   for (int q = 0; q < EB_NREDF; ++q) {
 #pragma unroll
@@ -612,19 +769,23 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     double bl = 0.0, bu = 0.0, gfp[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = lane; b < md.n_filt; b += 32) {
       if (md.phot_isig[b] != 0.0) {
-        const double is = md.phot_isig[b], mn = (double)mbp[b] * is, dn = md.phot_d[b] * is;
+        // the band's model (continuum + lines) for lnL; its continuum part for
+        // the mass derivative (the lines' runs through their own pass)
+        const double is = md.phot_isig[b], mc = (double)mbp[b] * is;
+        const double mn = NLn ? (double)(mbp[b] + mlb[b]) * is : mc, dn = md.phot_d[b] * is;
         const double rr = phot_resid(md, b, dn, mn);
         if (md.floor_bits[0]) {   // sigma_eff of Eq. app_noise_floor
           const double jn = (double)rs.fl[0][3] * is, q = floor_q(rs.fl[0], mn, dn, jn), gq = floor_gq(rr, q);
           bl += -0.5 * (rr * rr / q + log(q)) + md.phot_nlog[b];
-          bu += floor_dm(rs.fl[0], rr, q, gq, mn) * mn;
+          bu += floor_dm(rs.fl[0], rr, q, gq, mn) * mc;
           floor_dparam(rs.fl[0], gq, mn, dn, jn, gfp);
         } else {
           bl += -0.5 * rr * rr + md.phot_nlog[b];
-          bu += rr * mn;
+          bu += rr * mc;
         }
       }
     }
+    for (int k = lane; k < md.n_lcat; k += 32) bl += lcat_term(md, k, ln_F);   // the line catalogue
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       bl += __shfl_xor_sync(0xffffffffu, bl, o);
@@ -647,11 +808,12 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       rg[RG_DELTA] = s[3];
       rg[RG_GAS_LOGZ] = s[4];
       rg[RG_GAS_LOGU] = s[5];
-      rg[RG_LOGMASS] = 2.302585092994046 * (um_phot + um_sp);
+      rg[RG_LOGMASS] = 2.302585092994046 * (um_phot + um_sp + s[15]);
       rg[RG_Z] = um_phot * (double)rs.dlnp_dz + um_sp * (double)rs.dlns_dz + s[6];
       rg[RG_QY] = s[7];
       rg[RG_SIGMA_GAL] = s[8];
       rg[RG_FOB] = s[13];
+      rg[RG_SIGMA_GAS] = s[14];
       for (int k = 0; k < 4; ++k) {
         rg[RG_FLOOR + k] = gfp[k];
         rg[RG_FLOOR + 4 + k] = s[9 + k];
@@ -663,7 +825,9 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   }
 }
 
-cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s) {
+cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a_in, size_t* smem_needed, cudaStream_t s) {
+  EpiBwdArgs a = a_in;
+  a.lines_off = (int)epi_bwd_lines_off(a);
   const size_t smem = epi_bwd_smem(a);
   if (smem_needed) *smem_needed = smem;
   static DynSmemCache set_for;

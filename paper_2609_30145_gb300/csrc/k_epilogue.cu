@@ -30,6 +30,7 @@
 #include "atten.cuh"
 #include "calib.cuh"
 #include "floor.cuh"
+#include "lines.cuh"
 
 namespace sed {
 
@@ -53,106 +54,6 @@ size_t epilogue_lines_off(const EpiArgs& a) {   // in floats, even (float2 align
 size_t epilogue_smem(const EpiArgs& a) {
   const bool lines = a.row_model ? a.g.n_line > 0 : a.md.use_lines != 0;
   return (epilogue_lines_off(a) + (lines ? (size_t)5 * a.g.n_line : 0)) * sizeof(float);
-}
-
-// ---- emission lines (App. C, App. line_proj, Eq. app_line_profile)
-// Line l of the row: its flux F_l (erg/s/cm^2), the spectral profile's peak
-// factor A_l = F_l / (sqrt(2 pi) s_l), 1/s_l, and ln(lam_obs) as an FP32 pair.
-// L_l = Q_young 10^(bilinear log10 cube) in device units (the cube carries the
-// device-unit offset of the continuum template), times the attenuation the
-// nebular continuum meets at lam_l (atten.cuh's factor of neb), times
-// s_spec / (1+z): the flux factor without its (1+z).  s_l takes sigma_inst
-// at lam_obs by linear interpolation in wavelength between the pixels (their
-// value past the ends).
-__device__ __forceinline__ void line_setup(const ModelDev& md, const GridDev& g, const RowScal& rs, float eb, int l,
-                                           float* F_s, float* A_s, float* is_s, float2* x_s) {
-  const int nl = g.n_lam, NLn = g.n_line;
-  float lg = 0.f;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) lg = fmaf(rs.neb_w[c], g.line_tab[(rs.neb_off[c] / nl) * NLn + l], lg);
-  const float L = ex2_approx(rs.log2_qy + 3.3219280948873623f * lg);
-  const float4 c = g.line_att4[l];
-  const float tbc = rs.tau_bc * __expf(rs.alpha_bc * c.x);
-  const float td = rs.tau_d * dust_shape(md, c, eb, __expf(rs.delta * c.x));
-  const float ed = __expf(-td), ebc = __expf(-tbc), f = rs.fob;
-  const float fac = md.fesc_geom == SED_FESC_PICKET ? ed * (1.f - f) * ebc : ed * ((1.f - f) * ebc + f) * (1.f - f);
-  const float F = L * fac * rs.s_spec * rs.inv1pz;
-  F_s[l] = F;
-  // observed ln(lambda) = ln(lam_l) + ln(1+z): the FP32 pairs summed by two-sum
-  const float2 lr = g.line_ln2[l];
-  const float sh = lr.x + rs.ln1pz_hi, bv = sh - lr.x;
-  const float e = (lr.x - (sh - bv)) + (rs.ln1pz_hi - bv);
-  const float t = e + (lr.y + rs.ln1pz_lo);
-  const float xh = sh + t, xl = t - (xh - sh);
-  x_s[l] = make_float2(xh, xl);
-  float inv_s = 0.f, A = 0.f;
-  if (md.n_pix > 0) {
-    // sigma_inst at lam_obs: the pixel bracket by bisection on ln(lambda)
-    int lo = 0, hi = md.n_pix - 1;
-    float si;
-    if (xh <= md.pix_ln2[0].x) si = md.pix_sinst[0];
-    else if (xh >= md.pix_ln2[hi].x) si = md.pix_sinst[hi];
-    else {
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (md.pix_ln2[mid].x <= xh) lo = mid; else hi = mid;
-      }
-      const float l0 = md.pix_lamc[lo] * (float)C_AA, l1 = md.pix_lamc[hi] * (float)C_AA;
-      const float w = (c.w / rs.inv1pz - l0) / (l1 - l0);
-      si = md.pix_sinst[lo] + fminf(fmaxf(w, 0.f), 1.f) * (md.pix_sinst[hi] - md.pix_sinst[lo]);
-    }
-    const float s = sqrtf(rs.sgas * rs.sgas + si * si) * (float)(1.0 / C_KMS);
-    if (s > 0.f) {
-      inv_s = 1.f / s;
-      A = F * inv_s * 0.3989422804014327f;
-    }
-  }
-  A_s[l] = A;
-  is_s[l] = inv_s;
-}
-
-// Sum of the line profiles at pixel i (cgs F_nu), lines in index order, each
-// truncated at 5 s_l (Eq. app_line_profile, not renormalised).
-__device__ __forceinline__ float lines_at_pixel(const ModelDev& md, int i, int NLn, const float* A_s, const float* is_s,
-                                                const float2* x_s) {
-  const float2 p = md.pix_ln2[i];
-  float acc = 0.f;
-  for (int l = 0; l < NLn; ++l) {
-    const float u = ((p.x - x_s[l].x) + (p.y - x_s[l].y)) * is_s[l];
-    if (fabsf(u) <= 5.f) acc = fmaf(A_s[l], __expf(-0.5f * u * u), acc);
-  }
-  return acc * md.pix_lamc[i];
-}
-
-// Band b's photometry of line l (maggies): F R_b(lam_obs) lam_obs / Z_b, R_b
-// linear between the band's samples (0 outside them).
-__device__ __forceinline__ float line_in_band(const ModelDev& md, const GridDev& g, const RowScal& rs, int b, int l,
-                                             float F) {
-  const float x = g.line_att4[l].w / rs.inv1pz;   // observed wavelength, Angstrom
-  int lo = md.band_start[b], hi = md.band_start[b + 1] - 1;
-  if (!(x >= md.samp2[lo].x && x <= md.samp2[hi].x)) return 0.f;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (md.samp2[mid].x <= x) lo = mid; else hi = mid;
-  }
-  const float x0 = md.samp2[lo].x, x1 = md.samp2[hi].x;
-  const float t = x1 > x0 ? (x - x0) / (x1 - x0) : 0.f;
-  const float rz = md.samp_rz[lo] + t * (md.samp_rz[hi] - md.samp_rz[lo]);
-  return F * rz * x;
-}
-
-// Line-catalogue entry k's lnL term (FP64): model = the blend's summed line
-// fluxes; the one-sided residual of an upper limit (Eq. app_line_chi2_UL);
-// 0 for an entry outside the mask.
-__device__ __forceinline__ double lcat_term(const ModelDev& md, int k, const float* F_s) {
-  const double is = md.lcat_isig[k];
-  if (is == 0.0) return 0.0;
-  float m = 0.f;
-  for (int j = md.lcat_start[k]; j < md.lcat_start[k + 1]; ++j) m += F_s[md.lcat_line[j]];
-  const double d = md.lcat_d[k];
-  double r = (d - (double)m) * is;
-  if (md.lcat_ul && md.lcat_ul[k] && (double)m <= d) r = 0.0;
-  return -0.5 * r * r + md.lcat_nlog[k];
 }
 
 // MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
@@ -311,8 +212,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
         if (sw > 0.f) { v = sf / sw; valid = true; }
       }
     }
-    float mi = rs.s_spec * v;
-    if (NLn) mi += lines_at_pixel(md, i, NLn, ln_A, ln_is, ln_x);
+    const float mi = NLn ? fmaf(rs.s_spec, v, lines_at_pixel(md, i, NLn, ln_A, ln_is, ln_x)) : rs.s_spec * v;
     if (a.spec_out) a.spec_out[(size_t)ro * md.n_pix + i] = mi;
     const float isf = md.spec_isf[i];
     const bool inc = valid && isf != 0.f;

@@ -977,6 +977,7 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     put(SED_KEY_GAS_LOGU, md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f);
     if (md.sample_sgal) put(SED_KEY_SIGMA_GAL, (float)rg[RG_SIGMA_GAL]);
     if (md.fesc_geom) put(SED_KEY_FRAC_OBRUN, (float)rg[RG_FOB]);
+    if (md.gas_mode == SED_GAS_SIGMA_SAMPLED) put(SED_KEY_SIGMA_GAS, (float)rg[RG_SIGMA_GAS]);
     for (int arm = 0; arm < 2; ++arm)
       for (int k = 0; k < 4; ++k)
         if ((md.floor_bits[arm] >> k) & 1)

@@ -1453,8 +1453,6 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   if (st) return st;
   if (precision == SED_PREC_BF16 || precision == SED_PREC_FP8)
     return fail(ctx, SED_EUNSUPPORTED, "the gradient is available for SED_PREC_FP32 and SED_PREC_FP32_SIMT");
-  if (M->dv.use_lines || M->dv.n_lcat > 0)
-    return fail(ctx, SED_EUNSUPPORTED, "the adjoint does not cover emission lines: use sed_loglike / sed_forward");
   if (n > 0 && (!lnl_out || !grad_out)) return fail(ctx, SED_EINVAL, "lnl_out or grad_out is NULL");
   if (n == 0) return SED_OK;
   DevGuard dg(ctx->device);

@@ -286,6 +286,7 @@ enum {
   RG_SIGMA_GAL,   // dlnL/dsigma_gal (km/s) of a sampled sigma_gal
   RG_FLOOR,       // 8 slots: dlnL/dlog10 of the noise-floor terms, photometry then spectrum
   RG_FOB = RG_FLOOR + 8,   // dlnL/df_ob
+  RG_SIGMA_GAS,            // dlnL/dsigma_gas (km/s) of a sampled gas dispersion
   RGRAD = 24
 };
 
@@ -575,6 +576,7 @@ struct EpiBwdArgs {
   double* rgrad;
   double* lnl; uint32_t* status;
   const int* err;
+  int lines_off;        // set by launch_epilogue_bwd: byte offset of the emission lines' shared arrays
 };
 cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s);
 
