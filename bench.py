@@ -39,6 +39,7 @@ SGAL_WORKLOAD = "specphot_afe_sgal_107x12x5x6000_b2048"   # the same with a samp
 CALIB_WORKLOAD = "specphot_afe_calib13_107x12x5x6000_b2048"  # the same with a 13-term calibration polynomial
 FLOOR_WORKLOAD = "specphot_afe_floor_107x12x5x6000_b2048"    # the same with every noise-floor term on
 LINSFH_WORKLOAD = "phot_linsfh_107x12x6000_b1024"   # the headline fit with the linear SFH scheme
+LINES_WORKLOAD = "specphot_lines_107x12x6000_b1024"  # JADES-like: emission lines, spectrum, line catalogue
 PRECS = ("fp32", "fp32_simt", "bf16", "fp8")
 PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 likelihood sums",
              "bf16": "BF16 tcgen05, FP32 accumulate, FP64 likelihood sums",
@@ -61,6 +62,9 @@ def parse():
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-threads", type=int, default=48)
+    ap.add_argument("--serve-mean-calls", type=float, default=5.0,
+                    help="mean calls per request of the serving mix (the full serving config: 20, with "
+                         "--serve-requests 10000)")
     ap.add_argument("--serve-budget-mb", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-configs", action="store_true",
@@ -141,7 +145,10 @@ def build_workload(wname, ctx, seed_rows, device):
     import torch
     import synth
 
-    w = synth.WORKLOADS[wname]
+    optimised = wname.endswith(":optimised")   # the same workload, calibration optimised at each call
+    w = synth.WORKLOADS[wname.split(":")[0]]
+    if optimised:
+        w = synth.Workload(**{**w.__dict__, "name": w.name + "_optimised", "extra": {**w.extra, "calib_mode": 1}})
     grid = synth.make_grid(**w.grid_kw, seed=1)
     filt = synth.pack_filters(synth.workload_filters(w))
     nb = len(filt[0])
@@ -150,7 +157,21 @@ def build_workload(wname, ctx, seed_rows, device):
               sigma_gal_max_kms=w.sigma_gal_max_kms, noise_floor_phot=w.floor_phot,
               noise_floor_spec=w.floor_spec, sfh_scheme=w.sfh_scheme)
     if w.spectrum is not None and w.extra.get("calib_sigma"):
-        kw.update(calib_sigma=np.asarray(w.extra["calib_sigma"]))
+        kw.update(calib_sigma=np.asarray(w.extra["calib_sigma"]), calib_mode=w.extra.get("calib_mode", 0))
+    ln = w.extra.get("lines")
+    if ln:
+        # emission lines and a line catalogue of single lines and blends; its data
+        # are seeded values at the level of a strong line (the timing does not
+        # depend on them)
+        rng = np.random.default_rng(17)
+        blends, k = [], 0
+        while len(blends) < ln["n_lcat"]:
+            size = 1 + (len(blends) % 3 == 1) * int(rng.integers(0, 3))
+            blends.append(list(range(k, k + size)))
+            k += size
+        kw.update(use_lines=1, gas_sigma_mode=ln["gas_sigma_mode"], sigma_gas_max_kms=ln["sigma_gas_max_kms"],
+                  lcat=(blends, 1e-18 * (1 + 0.05 * rng.standard_normal(len(blends))),
+                        np.full(len(blends), 5e-20), None, None))
     spec = None
     if w.spectrum is not None:
         sp = w.spectrum
@@ -167,6 +188,8 @@ def build_workload(wname, ctx, seed_rows, device):
     d_true["zred"][:] = 2.0
     # noise-floor columns, if any: the model fluxes do not depend on them
     d_true.update(synth.floor_theta(1, w.floor_phot, w.floor_spec, np.ones(nb), np.ones(1)))
+    if "sigma_gas" in w.ranges:
+        d_true["sigma_gas"] = np.array([150.0])
     th_true = torch.from_numpy(model.pack(d_true)).to(device)
     ph, sp_ = model.forward(th_true, "fp32")
     torch.cuda.synchronize()
@@ -184,6 +207,9 @@ def build_workload(wname, ctx, seed_rows, device):
         d["sfh"] = synth.edge_sfr(w.batch, w.n_sfh, seed=seed_rows)
     d.update(synth.floor_theta(w.batch, w.floor_phot, w.floor_spec, np.abs(ph) / 20.0,
                                None if spec is None else np.abs(s0) / 20.0, seed=seed_rows + 1000))
+    if "sigma_gas" in w.ranges:
+        lo, hi = w.ranges["sigma_gas"]
+        d["sigma_gas"] = np.random.default_rng(seed_rows + 3000).uniform(lo, hi, w.batch)
     theta = model.pack(d)
     return w, grid, filt, model, theta, (pd, np.abs(ph) / 20.0)
 
@@ -509,6 +535,36 @@ def bench_gradient(ctx, device, flush, args):
     gfm = time_replays(gf, s, max(5, args.steps // 4), flush)
     ff = capture_step(lambda st: model_f.loglike(tf, "fp32", stream=st, out=lnl, status=stt), s)
     ffm = time_replays(ff, s, max(5, args.steps // 4), flush)
+    # emission lines on the spectrum and photometry plus a line catalogue
+    wl, _, _, model_l, theta_l, _ = build_workload(LINES_WORKLOAD, ctx, 4, device)
+    tl = torch.from_numpy(theta_l).to(device)
+    Bl = wl.batch
+    lnl_l = torch.empty(Bl, dtype=torch.float64, device=device)
+    stt_l = torch.empty(Bl, dtype=torch.int32, device=device)
+    grad_l = torch.empty_like(tl)
+    gl = capture_step(lambda st: model_l.loglike_grad(tl, "fp32", stream=st, out=(lnl_l, grad_l, stt_l)), s)
+    glm = time_replays(gl, s, max(5, args.steps // 4), flush)
+    fl = capture_step(lambda st: model_l.loglike(tl, "fp32", stream=st, out=lnl_l, status=stt_l), s)
+    flm = time_replays(fl, s, max(5, args.steps // 4), flush)
+    res["emission_lines"] = {"workload": wl.name, "batch": Bl, "n_param": int(theta_l.shape[1]),
+                             "lines": 30, "catalogue_entries": wl.extra["lines"]["n_lcat"],
+                             "grad_evals_per_s": round(Bl * len(glm) / (sum(glm) * 1e-3), 1),
+                             "grad_ms_per_step": round(sum(glm) / len(glm), 4),
+                             "loglike_evals_per_s": round(Bl * len(flm) / (sum(flm) * 1e-3), 1),
+                             "loglike_ms_per_step": round(sum(flm) / len(flm), 4)}
+    # the calibration polynomial optimised at each call instead of marginalised
+    wo, _, _, model_o, theta_o, _ = build_workload(CALIB_WORKLOAD + ":optimised", ctx, 4, device)
+    to = torch.from_numpy(theta_o).to(device)
+    grad_o = torch.empty_like(to)
+    go = capture_step(lambda st: model_o.loglike_grad(to, "fp32", stream=st, out=(lnl, grad_o, stt)), s)
+    gom = time_replays(go, s, max(5, args.steps // 4), flush)
+    fo = capture_step(lambda st: model_o.loglike(to, "fp32", stream=st, out=lnl, status=stt), s)
+    fom = time_replays(fo, s, max(5, args.steps // 4), flush)
+    res["calibration_polynomial_optimised"] = {
+        "workload": wo.name, "grad_evals_per_s": round(B * len(gom) / (sum(gom) * 1e-3), 1),
+        "grad_ms_per_step": round(sum(gom) / len(gom), 4),
+        "loglike_evals_per_s": round(B * len(fom) / (sum(fom) * 1e-3), 1),
+        "loglike_ms_per_step": round(sum(fom) / len(fom), 4)}
     res["noise_floor"] = {"workload": wf.name, "n_param": int(theta_f.shape[1]),
                           "terms": "error scale, f_calib, f_data, jitter on photometry and spectrum",
                           "grad_evals_per_s": round(B * len(gfm) / (sum(gfm) * 1e-3), 1),
@@ -732,7 +788,7 @@ def bench_serving(ctx, device, args):
     base = synth.WORKLOADS[GRAD_WORKLOAD]
     grid = synth.make_grid(**base.grid_kw, seed=1)
     gid = ctx.load_grid(grid)
-    reqs = make_serving_requests(args.serve_requests)
+    reqs = make_serving_requests(args.serve_requests, mean_calls=args.serve_mean_calls)
     models, thetas = [], []
     t_setup = time.perf_counter()
     for q in reqs:
@@ -767,6 +823,60 @@ def bench_serving(ctx, device, args):
         thetas.append(m.pack(synth.make_theta(q["batch"], q["n_sfh"], q["zmode"], ranges, seed=q["seed"] + 1)))
     t_setup = time.perf_counter() - t_setup
     total_evals = sum(q["batch"] * q["calls"] for q in reqs)
+
+    def run_direct(prec, rate):
+        """The same mix through plain batched sed_loglike calls: each client
+        calls the library on its own CUDA stream and waits for its result (the
+        plain FP32 batched path, no server)."""
+        import torch
+        call_lat, req_lat = [], []
+        lock = threading.Lock()
+        rng = np.random.Generator(np.random.PCG64(7))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
+        t0 = time.perf_counter()
+        nxt = [0]
+
+        def worker():
+            st_ = torch.cuda.Stream(device=device)
+            while True:
+                with lock:
+                    i = nxt[0]
+                    nxt[0] += 1
+                if i >= len(reqs):
+                    return
+                q, m, th = reqs[i], models[i], thetas[i].copy()
+                delay = t0 + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                t_arr = time.perf_counter()
+                jm = m.offsets["logmass"]
+                lat = []
+                for c in range(q["calls"]):
+                    tc0 = time.perf_counter()
+                    td = torch.from_numpy(th).to(device, non_blocking=False)
+                    with torch.cuda.stream(st_):
+                        l_, s_ = m.loglike(td, prec, stream=st_)
+                        lnl = l_.cpu().numpy()
+                    lat.append(1e3 * (time.perf_counter() - tc0))
+                    good = np.isfinite(lnl)
+                    if good.any():
+                        med = np.median(lnl[good])
+                        th[good, jm] += np.where(lnl[good] > med, 0.02, -0.02).astype(np.float32)
+                with lock:
+                    call_lat.extend(lat)
+                    req_lat.append(1e3 * (time.perf_counter() - t_arr))
+
+        threads = [threading.Thread(target=worker) for _ in range(args.serve_threads)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        wall = time.perf_counter() - t0
+        return {"evals_per_s": round(total_evals / wall, 1), "wall_s": round(wall, 3),
+                "call_latency_ms": {"p50": round(float(np.percentile(call_lat, 50)), 3),
+                                    "p99": round(float(np.percentile(call_lat, 99)), 3)},
+                "request_latency_ms": {"p50": round(float(np.percentile(req_lat, 50)), 3),
+                                       "p99": round(float(np.percentile(req_lat, 99)), 3)}}
 
     def run(prec, rate):
         srv = Server(ctx, gid, models[0], precision=prec, max_launch_rows=8192, n_slots=3,
@@ -839,6 +949,12 @@ def bench_serving(ctx, device, args):
         rate = 0.7 * sat["evals_per_s"] / (total_evals / len(reqs))
         out[prec] = {"saturated": sat, "poisson_0.7": run(prec, rate)}
         out[prec]["poisson_0.7"]["arrival_rate_per_s"] = round(rate, 2)
+    # like for like: the same mix through plain FP32 batched sed_loglike calls
+    sat = run_direct("fp32", 0.0)
+    rate = 0.7 * sat["evals_per_s"] / (total_evals / len(reqs))
+    out["fp32_plain_batched"] = {"saturated": sat, "poisson_0.7": run_direct("fp32", rate),
+                                 "what": "each client calls sed_loglike on its own stream and waits (no server)"}
+    out["fp32_plain_batched"]["poisson_0.7"]["arrival_rate_per_s"] = round(rate, 2)
     return out
 
 

@@ -87,6 +87,8 @@ size_t epi_bwd_smem(const EpiBwdArgs& a) {
   return epi_bwd_lines_off(a) + lines;
 }
 
+// LINES: an instance with the emission lines (the one without keeps its code free of them)
+template <bool LINES>
 __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
   pdl_enter();
   const ModelDev& md = a.md;
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   }
   // emission lines: per line ln(lam_obs), F_l, A_l, 1/s_l; per pixel dlnL/dmu;
   // per catalogue entry dlnL/dm
-  const int NLn = md.use_lines ? g.n_line : 0;
+  const int NLn = LINES && md.use_lines ? g.n_line : 0;
   float2* ln_x = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem) + a.lines_off);
   float* ln_F = reinterpret_cast<float*>(ln_x + NLn);
   float* ln_A = ln_F + NLn;
@@ -248,11 +250,13 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
     }
     float lsum = 0.f;   // the band's lines (maggies), one line per lane as in the forward
-    for (int l = lane; l < NLn; l += 32) lsum += line_in_band(md, g, rs, b, l, ln_F[l]);
+    if (LINES && NLn) {
+      for (int l = lane; l < NLn; l += 32) lsum += line_in_band(md, g, rs, b, l, ln_F[l]);
 #pragma unroll
-    for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+      for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    }
     const float mc = rs.p_phot * acc;   // the continuum part
-    const float mb = NLn ? fmaf(rs.p_phot, acc, lsum) : mc;
+    const float mb = LINES && NLn ? fmaf(rs.p_phot, acc, lsum) : mc;
     // d lnL / d(band flux) = (d - m)/sigma^2, formed in FP32 from the normalised
     // datum and 1/sigma (0 for a masked band); times p_phot it weighs F
     const float isf = md.phot_isf[b];
@@ -378,8 +382,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         }
       }
     }
-    const float mline = NLn ? lines_at_pixel(md, i, NLn, ln_A, ln_is, ln_x) : 0.f;
-    const float mi = NLn ? fmaf(rs.s_spec, v, mline) : rs.s_spec * v;
+    const float mline = LINES && NLn ? lines_at_pixel(md, i, NLn, ln_A, ln_is, ln_x) : 0.f;
+    const float mi = LINES && NLn ? fmaf(rs.s_spec, v, mline) : rs.s_spec * v;
     float ci = 0.f;
     const float isf = md.spec_isf[i];
     const bool inc = valid && isf != 0.f;
@@ -785,7 +789,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         }
       }
     }
-    for (int k = lane; k < md.n_lcat; k += 32) bl += lcat_term(md, k, ln_F);   // the line catalogue
+    if (LINES)
+      for (int k = lane; k < md.n_lcat; k += 32) bl += lcat_term(md, k, ln_F);   // the line catalogue
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       bl += __shfl_xor_sync(0xffffffffu, bl, o);
@@ -830,10 +835,11 @@ cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a_in, size_t* smem_needed, cud
   a.lines_off = (int)epi_bwd_lines_off(a);
   const size_t smem = epi_bwd_smem(a);
   if (smem_needed) *smem_needed = smem;
-  static DynSmemCache set_for;
-  cudaError_t e = ensure_dyn_smem(k_epi_bwd, smem, &set_for);
+  static DynSmemCache set_for[2];
+  auto k = a.md.use_lines ? k_epi_bwd<true> : k_epi_bwd<false>;
+  cudaError_t e = ensure_dyn_smem(k, smem, &set_for[a.md.use_lines ? 1 : 0]);
   if (e != cudaSuccess) return e;
-  return launch_pdl(k_epi_bwd, dim3(a.n), dim3(EB_THREADS), smem, s, a);
+  return launch_pdl(k, dim3(a.n), dim3(EB_THREADS), smem, s, a);
 }
 
 // ---------------------------------------------------------------------------

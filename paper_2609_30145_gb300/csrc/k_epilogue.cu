@@ -57,8 +57,9 @@ size_t epilogue_smem(const EpiArgs& a) {
 }
 
 // MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
-// otherwise every row reads the model in the kernel parameters.
-template <bool MULTI>
+// otherwise every row reads the model in the kernel parameters.  LINES: an
+// instance with the emission lines (the one without keeps its code free of them).
+template <bool MULTI, bool LINES>
 __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_constant__ EpiArgs a) {
   pdl_enter();
   const int r = blockIdx.x;
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   }
   // emission lines: ln(lam_obs) pairs, fluxes F_l, profile peaks A_l = F_l /
   // (sqrt(2 pi) s_l) and 1/s_l in the tail of the dynamic shared memory
-  const int NLn = md.use_lines ? g.n_line : 0;
+  const int NLn = LINES && md.use_lines ? g.n_line : 0;
   float2* ln_x = reinterpret_cast<float2*>(reinterpret_cast<float*>(smem4) + a.lines_off);
   float* ln_F = reinterpret_cast<float*>(ln_x + NLn);
   float* ln_A = ln_F + NLn;
@@ -164,11 +165,13 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
       for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       // the lines in this band, one line per lane
       float lsum = 0.f;
-      for (int l = lane; l < NLn; l += 32) lsum += line_in_band(md, g, rs, b, l, ln_F[l]);
+      if (LINES && NLn) {
+        for (int l = lane; l < NLn; l += 32) lsum += line_in_band(md, g, rs, b, l, ln_F[l]);
 #pragma unroll
-      for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+      }
       if (lane == 0) {
-        const float mb = fmaf(rs.p_phot, acc, lsum);
+        const float mb = LINES && NLn ? fmaf(rs.p_phot, acc, lsum) : rs.p_phot * acc;
         if (a.phot_out) a.phot_out[(size_t)ro * md.n_filt + b] = mb;
         mb_s[b] = mb;
       }
@@ -212,7 +215,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
         if (sw > 0.f) { v = sf / sw; valid = true; }
       }
     }
-    const float mi = NLn ? fmaf(rs.s_spec, v, lines_at_pixel(md, i, NLn, ln_A, ln_is, ln_x)) : rs.s_spec * v;
+    const float mi = LINES && NLn ? fmaf(rs.s_spec, v, lines_at_pixel(md, i, NLn, ln_A, ln_is, ln_x)) : rs.s_spec * v;
     if (a.spec_out) a.spec_out[(size_t)ro * md.n_pix + i] = mi;
     const float isf = md.spec_isf[i];
     const bool inc = valid && isf != 0.f;
@@ -286,7 +289,8 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
       }
     }
     // the line catalogue (Sec. 3.3), one entry per lane in FP64
-    for (int k = lane; k < md.n_lcat; k += 32) pv += lcat_term(md, k, ln_F);
+    if (LINES)
+      for (int k = lane; k < md.n_lcat; k += 32) pv += lcat_term(md, k, ln_F);
 #pragma unroll
     for (int o = 16; o; o >>= 1) pv += __shfl_xor_sync(0xffffffffu, pv, o);
     if (lane == 0) {
@@ -305,13 +309,15 @@ cudaError_t launch_epilogue(const EpiArgs& a_in, cudaStream_t s) {
   EpiArgs a = a_in;
   a.lines_off = (int)epilogue_lines_off(a);
   const size_t smem = epilogue_smem(a);
-  static DynSmemCache set_for[2];
-  const int m = a.row_model ? 1 : 0;
-  cudaError_t e = m ? ensure_dyn_smem(k_epilogue<true>, smem, &set_for[1])
-                    : ensure_dyn_smem(k_epilogue<false>, smem, &set_for[0]);
+  static DynSmemCache set_for[4];
+  const bool lines = a.row_model ? a.g.n_line > 0 : a.md.use_lines != 0;
+  const int m = (a.row_model ? 1 : 0) + (lines ? 2 : 0);
+  auto k = m == 0 ? k_epilogue<false, false>
+         : m == 1 ? k_epilogue<true, false>
+         : m == 2 ? k_epilogue<false, true> : k_epilogue<true, true>;
+  cudaError_t e = ensure_dyn_smem(k, smem, &set_for[m]);
   if (e != cudaSuccess) return e;
-  return m ? launch_pdl(k_epilogue<true>, dim3(a.n), dim3(EPI_THREADS), smem, s, a)
-           : launch_pdl(k_epilogue<false>, dim3(a.n), dim3(EPI_THREADS), smem, s, a);
+  return launch_pdl(k, dim3(a.n), dim3(EPI_THREADS), smem, s, a);
 }
 
 }  // namespace sed
