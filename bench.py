@@ -789,7 +789,7 @@ def bench_serving(ctx, device, args):
     grid = synth.make_grid(**base.grid_kw, seed=1)
     gid = ctx.load_grid(grid)
     reqs = make_serving_requests(args.serve_requests, mean_calls=args.serve_mean_calls)
-    models, thetas = [], []
+    models, thetas, okws = [], [], []
     t_setup = time.perf_counter()
     for q in reqs:
         rng = np.random.Generator(np.random.PCG64(q["seed"]))
@@ -815,10 +815,13 @@ def bench_serving(ctx, device, args):
             return a / 20 + max(1e-3 * a.max() / 20, 1e-30)
         if q["n_pix"]:
             s0 = sp.cpu().numpy()[0].astype(np.float64)
-            m.set_data(phot_d=ph * (1 + nz[:q["n_filt"]] / 20), phot_sigma=sig(ph),
-                       spec_d=s0 * (1 + nz[q["n_filt"]:] / 20), spec_sigma=sig(s0))
+            data = dict(phot_d=ph * (1 + nz[:q["n_filt"]] / 20), phot_sigma=sig(ph),
+                        spec_d=s0 * (1 + nz[q["n_filt"]:] / 20), spec_sigma=sig(s0))
         else:
-            m.set_data(phot_d=ph * (1 + nz / 20), phot_sigma=sig(ph))
+            data = dict(phot_d=ph * (1 + nz / 20), phot_sigma=sig(ph))
+        m.set_data(**data)
+        kw.update(data)
+        okws.append(dict(kw, n_sfh=q["n_sfh"], zf=30.0, zmode=q["zmode"]))
         models.append(m)
         thetas.append(m.pack(synth.make_theta(q["batch"], q["n_sfh"], q["zmode"], ranges, seed=q["seed"] + 1)))
     t_setup = time.perf_counter() - t_setup
@@ -949,12 +952,58 @@ def bench_serving(ctx, device, args):
         rate = 0.7 * sat["evals_per_s"] / (total_evals / len(reqs))
         out[prec] = {"saturated": sat, "poisson_0.7": run(prec, rate)}
         out[prec]["poisson_0.7"]["arrival_rate_per_s"] = round(rate, 2)
+    out["accuracy_vs_fp64_oracle"] = serving_accuracy(ctx, gid, grid, reqs, models, thetas, okws)
     # like for like: the same mix through plain FP32 batched sed_loglike calls
     sat = run_direct("fp32", 0.0)
     rate = 0.7 * sat["evals_per_s"] / (total_evals / len(reqs))
     out["fp32_plain_batched"] = {"saturated": sat, "poisson_0.7": run_direct("fp32", rate),
                                  "what": "each client calls sed_loglike on its own stream and waits (no server)"}
     out["fp32_plain_batched"]["poisson_0.7"]["arrival_rate_per_s"] = round(rate, 2)
+    return out
+
+
+def serving_accuracy(ctx, gid, grid, reqs, models, thetas, okws, n_req=8, n_rows=16):
+    """Errors of the served lnL against the FP64 oracle on the mix: the first
+    n_rows live points of the first n_req requests (photometric and
+    spectro-photometric fits, with and without [a/Fe]), each request's rows
+    submitted through a server of each precision."""
+    import oracle
+    from paper_2609_30145_gb300 import Server
+
+    sel = list(range(min(n_req, len(reqs))))
+    refs, orcs = [], []
+    for i in sel:
+        okw = okws[i]
+        orc = oracle.Oracle(grid=grid, n_sfh=okw["n_sfh"], zf=okw["zf"], zmode=okw["zmode"], use_afe=okw["use_afe"],
+                            dust_law=okw["dust_law"], filters=okw["filters"], phot_d=okw["phot_d"],
+                            phot_sigma=okw["phot_sigma"], spec_lam=okw.get("spec_lam"), spec_d=okw.get("spec_d"),
+                            spec_sigma=okw.get("spec_sigma"), lsf_mode=okw.get("lsf_mode", 0),
+                            lsf_value=okw.get("lsf_value"), sigma_gal_kms=okw.get("sigma_gal_kms", 0.0),
+                            z_ref=okw.get("z_ref", 0.0))
+        th = thetas[i][:n_rows]
+        refs.append(orc.eval(th.astype(np.float64)))
+        orcs.append(orc)
+    out = {"requests": len(sel), "rows_per_request": n_rows,
+           "what": "first live points of the first requests of the mix, served, against the FP64 oracle"}
+    for prec in ("fp32", "bf16"):
+        srv = Server(ctx, gid, models[0], precision=prec, max_launch_rows=8192, n_slots=1)
+        rel, ab, match = [], [], True
+        for j, i in enumerate(sel):
+            th = np.ascontiguousarray(thetas[i][:n_rows])
+            fit = srv.open_fit(models[i], th.shape[0])
+            lnl, st, _ = srv.wait(srv.submit(fit, th), th.shape[0])
+            srv.close_fit(fit)
+            ref = refs[j]
+            match &= bool(np.array_equal(st, ref["status"]))
+            ok = ref["status"] == 0
+            c = norm_const(orcs[j])
+            lr = ref["lnl"][ok]
+            d = np.abs(lnl[ok] - lr)
+            rel.append(d / np.maximum(np.abs(lr), (c - lr) + abs(c)))
+            ab.append(d)
+        srv.close()
+        out[prec] = {"status_match": match, "rows": int(sum(a.size for a in ab)),
+                     "lnl_err_over_term_scale": _q(np.concatenate(rel)), "lnl_abs_err": _q(np.concatenate(ab))}
     return out
 
 

@@ -125,6 +125,48 @@ def test_paper_scale_phot_sampled_rows(ctx, prec):
     check(ref, got, prec, rows, orc=orc)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "fp32"])
+def test_mixed_precision_batch_4096(ctx, prec):
+    """The mixed-precision batch of the paper-scale photometric fit: 4096 rows
+    (32 M tiles, four of the persistent schedule's waves per kind) on the GPU,
+    48 sampled rows -- the first, the last and rows of every 1024-row quarter
+    -- against the oracle."""
+    w, orc, model = case(ctx, "phot")
+    th32, th64 = cases.theta_pair(w, 4096, seed=43)
+    got = run_gpu(model, th32, prec)
+    rows = np.unique(np.concatenate([[0, 4095], np.random.default_rng(13).choice(4096, 46, replace=False)]))
+    ref = orc.eval(th64[rows])
+    check(ref, got, prec, rows, orc=orc)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_batch_past_the_persistent_schedule(ctx, prec):
+    """8300 rows = 65 M tiles, one more than the persistent contraction
+    schedules: the launch takes the grid schedule (one CTA per tile), and
+    sampled rows -- including the last tile's ragged tail -- still match the
+    oracle."""
+    w, orc, model = case(ctx, "phot")
+    n = 8300
+    th32, th64 = cases.theta_pair(w, n, seed=44)
+    got = run_gpu(model, th32, prec)
+    rows = np.unique(np.concatenate([[0, 8191, 8192, n - 1], np.random.default_rng(14).choice(n, 28, replace=False)]))
+    ref = orc.eval(th64[rows])
+    check(ref, got, prec, rows, orc=orc)
+
+
+def test_k_tile_masks_past_the_persistent_schedule(ctx):
+    """The [a/Fe] spectro-photometric fit (one [Fe/H] and [a/Fe] per row, so
+    the 3xTF32 contraction skips K tiles) at 8300 rows: the grid schedule with
+    each M tile's K-tile mask; sampled rows against the oracle."""
+    w, orc, model = case(ctx, "spec")
+    n = 8300
+    th32, th64 = cases.theta_pair(w, n, seed=45)
+    got = run_gpu(model, th32, "fp32")
+    rows = np.unique(np.concatenate([[0, 8192, n - 1], np.random.default_rng(15).choice(n, 13, replace=False)]))
+    ref = orc.eval(th64[rows])
+    check(ref, got, "fp32", rows, orc=orc)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_specphot_afe_sampled_rows(ctx, prec):
     """107 x 12 x 5 x 6000 grid with [a/Fe], 1500-pixel R=100-1000 spectrum +
