@@ -516,6 +516,66 @@ typedef struct {
 sed_status sed_set_profiling(sed_ctx *ctx, int on);
 sed_status sed_last_stats(sed_ctx *ctx, void *stream, sed_stage_stats *out);
 
+/*
+ * Nested slice sampling (Sec. 4.3): a nested-sampling run (Skilling 2006) on
+ * the GPU whose likelihood is sed_loglike of one model.  The live points start
+ * uniform in a box prior (one interval per parameter column: lo[j] < hi[j]);
+ * each iteration removes the n_replace live points of lowest lnL and replaces
+ * them by as many hit-and-run slice chains, run in parallel, each started at a
+ * random surviving live point with lnL above the removed ones and making
+ * n_slice_steps slice steps inside the likelihood contour (stepping out, then
+ * shrinking) along directions drawn from the surviving live points'
+ * covariance.  Every chain's proposals of one round go through one
+ * sed_loglike call; the proposals, the contour, the covariance and its
+ * Cholesky factor, the evidence sums and the stop test run in the library's
+ * kernels, the host only sequences the rounds.  Random numbers: Philox4x32-10
+ * keyed by seed.  The prior volume after removing the j-th of the n live
+ * points of lowest lnL shrinks by exp(-1 / (n - j)) (the expectation of the log
+ * shrinkage); the removed point's weight is X_before - X_after.  The run stops
+ * when ln(Z_live / Z) < stop_dlnz, Z_live = X * mean(L_live) (the paper: -5),
+ * or after max_iter iterations; the final live points are then added with
+ * weight X / n each.
+ */
+typedef struct {
+  int n_live;              /* live points, 2 <= n_live <= 4096 */
+  int n_replace;           /* live points replaced per iteration, 1 <= n_replace <= n_live / 2 */
+  int n_slice_steps;       /* slice steps per replacement chain, >= 1 */
+  int max_iter;            /* iteration limit, >= 1 */
+  double stop_dlnz;        /* stop when ln(Z_live / Z) < stop_dlnz */
+  double slice_width;      /* initial slice bracket, in units of the live points' spread along the
+                              direction (0 = sqrt(n_param + 2)) */
+  uint64_t seed;
+  int precision;           /* SED_PREC_* of the likelihood calls */
+  const double *lo, *hi;   /* [n_param] HOST: the box prior of each parameter column */
+} sed_nss_desc;
+
+typedef struct {
+  double lnz;              /* ln of the evidence (the mean likelihood over the box prior) */
+  double info_h;           /* information H = sum_i p_i ln(L_i / Z), nats; ln Z's spread is ~ sqrt(H / n_live) */
+  int n_iter;              /* iterations run */
+  int n_dead;              /* points returned: every removed point, then the final live points */
+  int converged;           /* 1: the stop test was met; 0: max_iter was reached */
+  int64_t n_like;          /* likelihood evaluations of proposals */
+  int64_t n_rows;          /* rows sent through sed_loglike (idle chains included) */
+} sed_nss_result;
+
+/*
+ * Runs nested slice sampling for `model` on `stream` and waits for it.  The
+ * host buffers (each may be NULL) receive, for max_dead points at most, in
+ * the order of removal and then the final live points in increasing lnL: the
+ * parameter rows dead_theta [max_dead][n_param], their lnL dead_lnl, their
+ * log posterior weights dead_logw (ln(L_i w_i / Z), summing to 1 in exp), and
+ * ins_rank [max_dead] the insertion rank of each replacement among the live
+ * points that survived its iteration (n_iter * n_replace entries; uniform on
+ * 0..n_live - n_replace for a correct constrained sampler).  SED_ERANGE when
+ * max_dead is below the points the run produced (the run's results are still
+ * in *out); SED_EINVAL for a bad descriptor; the library allocates and frees
+ * the run's device buffers.
+ */
+sed_status sed_nss_run(sed_ctx *ctx, sed_model_id model, const sed_nss_desc *desc, float *dead_theta,
+                       double *dead_lnl, double *dead_logw, int32_t *ins_rank, int max_dead,
+                       sed_nss_result *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

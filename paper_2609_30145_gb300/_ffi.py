@@ -79,6 +79,17 @@ class ServerStats(C.Structure):
                 ("fits_open", C.c_int), ("fit_bytes", C.c_size_t)]
 
 
+class NssDesc(C.Structure):
+    _fields_ = [("n_live", C.c_int), ("n_replace", C.c_int), ("n_slice_steps", C.c_int), ("max_iter", C.c_int),
+                ("stop_dlnz", C.c_double), ("slice_width", C.c_double), ("seed", C.c_uint64),
+                ("precision", C.c_int), ("lo", P), ("hi", P)]
+
+
+class NssResult(C.Structure):
+    _fields_ = [("lnz", C.c_double), ("info_h", C.c_double), ("n_iter", C.c_int), ("n_dead", C.c_int),
+                ("converged", C.c_int), ("n_like", C.c_int64), ("n_rows", C.c_int64)]
+
+
 # exported symbols and their signatures (name -> (restype, argtypes))
 SIGNATURES = {
     "sed_create": (C.c_int, [C.POINTER(P), C.c_int, C.c_size_t]),
@@ -108,6 +119,7 @@ SIGNATURES = {
     "sed_server_wait": (C.c_int, [P, C.c_uint64, P, P, C.c_int, C.POINTER(C.c_double)]),
     "sed_server_get_stats": (C.c_int, [P, C.POINTER(ServerStats)]),
     "sed_last_stats": (C.c_int, [P, P, C.POINTER(StageStats)]),
+    "sed_nss_run": (C.c_int, [P, C.c_int32, C.POINTER(NssDesc), P, P, P, P, C.c_int, C.POINTER(NssResult), P]),
 }
 
 _lib = None

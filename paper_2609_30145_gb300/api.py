@@ -293,6 +293,36 @@ class Model:
         self.ctx._check(st)
         return lnl, stt
 
+    def nss(self, lo, hi, n_live=300, n_replace=64, n_slice_steps=40, max_iter=20000, stop_dlnz=-5.0,
+            slice_width=0.0, seed=1, precision="fp32", max_dead=None, stream=None):
+        """Nested slice sampling of this model's likelihood over the box prior
+        [lo, hi] of each parameter column (sed_nss_run).  Returns a dict with
+        lnz, info_h, n_iter, converged, n_like, n_rows, and the dead points
+        (removed points, then the final live points): theta [n_dead, n_param],
+        lnl, logw (ln posterior weights) and ins_rank (insertion ranks of the
+        replacements)."""
+        lo, hi = _f64(lo), _f64(hi)
+        if lo.size != self.n_param or hi.size != self.n_param:
+            raise ValueError(f"lo/hi need {self.n_param} entries")
+        d = _ffi.NssDesc()
+        d.n_live, d.n_replace, d.n_slice_steps, d.max_iter = n_live, n_replace, n_slice_steps, max_iter
+        d.stop_dlnz, d.slice_width, d.seed, d.precision = stop_dlnz, slice_width, seed, _prec(precision)
+        d.lo, d.hi = _ptr(lo), _ptr(hi)
+        cap = int(max_dead) if max_dead is not None else n_live + max_iter * n_replace
+        th = np.empty((cap, self.n_param), dtype=np.float32)
+        lnl = np.empty(cap, dtype=np.float64)
+        logw = np.empty(cap, dtype=np.float64)
+        rank = np.empty(cap, dtype=np.int32)
+        res = _ffi.NssResult()
+        st = self.ctx._lib.sed_nss_run(self.ctx._h, self.id, C.byref(d), C.c_void_p(th.ctypes.data),
+                                       C.c_void_p(lnl.ctypes.data), C.c_void_p(logw.ctypes.data),
+                                       C.c_void_p(rank.ctypes.data), cap, C.byref(res), _stream_handle(stream))
+        self.ctx._check(st)
+        nd = res.n_dead
+        return dict(lnz=res.lnz, info_h=res.info_h, n_iter=res.n_iter, converged=bool(res.converged),
+                    n_like=res.n_like, n_rows=res.n_rows, theta=th[:nd], lnl=lnl[:nd], logw=logw[:nd],
+                    ins_rank=rank[:res.n_iter * n_replace])
+
 
 class Server:
     """Continuous-batching server of log-likelihood calls over many fits that

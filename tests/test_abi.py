@@ -110,7 +110,8 @@ def test_struct_layouts_match_header(tmp_path):
         pytest.skip("no C compiler")
     structs = {"sed_grid_desc": _ffi.GridDesc, "sed_model_desc": _ffi.ModelDesc,
                "sed_stage_stats": _ffi.StageStats, "sed_server_desc": _ffi.ServerDesc,
-               "sed_server_stats": _ffi.ServerStats}
+               "sed_server_stats": _ffi.ServerStats, "sed_nss_desc": _ffi.NssDesc,
+               "sed_nss_result": _ffi.NssResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sed.h"', "int main(void) {"]
     want = []
     for cname, cls in structs.items():
