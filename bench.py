@@ -67,6 +67,8 @@ def parse():
                          "--serve-requests 10000)")
     ap.add_argument("--serve-budget-mb", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-sampler", action="store_true",
+                    help="skip the nested-slice-sampling leg (time per fit of a JADES-like model)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the per-config accuracy and throughput leg (tiny, paper-scale photometric at 1024 "
                          "and 4096 rows, spectro-photometric [a/Fe], serving mix)")
@@ -483,6 +485,8 @@ def run_ours(args):
         out["gradient"] = bench_gradient(ctx, device, flush, args)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = bench_serving(ctx, device, args)
+    if rank == 0 and world == 1 and not args.no_sampler:
+        out["sampler"] = bench_sampler(ctx, device)
     if rank == 0 and world == 1 and not args.no_configs:
         out["configs"] = bench_configs(ctx, device, flush, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -960,6 +964,64 @@ def bench_serving(ctx, device, args):
                                  "what": "each client calls sed_loglike on its own stream and waits (no server)"}
     out["fp32_plain_batched"]["poisson_0.7"]["arrival_rate_per_s"] = round(rate, 2)
     return out
+
+
+def bench_sampler(ctx, device, n_fits=2):
+    """Nested slice sampling of a fit shaped like the paper's JADES benchmark:
+    15 NIRCam-like bands and a 22-entry emission-line catalogue, 8 SFH bins, one
+    constant [Fe/H], nebular continuum and lines (30-line cube), birth-cloud +
+    Kriek & Conroy dust, redshift fixed; 15 sampled columns over a box prior;
+    300 live points, 64 replaced per iteration, 40 slice steps per replacement,
+    stop at ln(Z_live / Z) < -5.  Data: the model of a true row with 5% noise
+    on the bands and 10% on the lines.  Wall time per fit includes every host
+    sync of the run."""
+    import torch
+    import synth
+
+    wl = synth.WORKLOADS["specphot_lines_107x12x6000_b1024"]
+    grid = synth.make_grid(**wl.grid_kw, seed=1)
+    gid = ctx.load_grid(grid)
+    filt = synth.pack_filters(synth.make_filters_nircam_like(6, 9, seed=17))
+    n_sfh, nl = 8, len(grid.line_lam)
+    blends = [[i] for i in range(0, min(nl, 19))] + [[19, 20], [21, 22, 23], [24, 25]]
+    fixed = {"afe": 0.0, "zred": 5.0, "alpha_pow": -1.0}
+    kw = dict(use_nebular=1, dust_law=1, use_lines=1, filters=filt, phot_d=np.ones(15), phot_sigma=np.ones(15),
+              fixed=fixed)
+    truth = synth.make_theta(1, n_sfh, 1, dict(wl.ranges, feh=(-0.7, -0.7)), seed=99)
+    truth.update(logmass=np.array([9.3]), tau_pow=np.array([0.4]), diffuse_tau_kc=np.array([0.3]),
+                 diffuse_dust_index=np.array([-0.3]), gas_logz=np.array([-0.5]), gas_logu=np.array([-2.5]))
+    m0 = ctx.create_model(gid, n_sfh, 30.0, 1, **kw)
+    th0 = torch_from(m0.pack(truth), device)
+    ph = m0.forward(th0, "fp32")[0].cpu().numpy()[0].astype(np.float64)
+    fl = m0.line_fluxes(th0, "fp32").cpu().numpy()[0].astype(np.float64)
+    m0.close()
+    nz = synth.noise(15 + len(blends), seed=21)
+    lf = np.array([fl[b].sum() for b in blends])
+    lcat = (blends, lf * (1 + nz[15:] / 10.0), np.abs(lf) / 10.0, None, None)
+    kw.update(phot_d=ph * (1 + nz[:15] / 20.0), phot_sigma=np.abs(ph) / 20.0)
+    model = ctx.create_model(gid, n_sfh, 30.0, 1, lcat=lcat, **kw)
+    lo = np.concatenate([np.zeros(n_sfh), [-2.0, 7.0, 0.0, 0.0, -1.0, -1.3, -4.0]])
+    hi = np.concatenate([np.ones(n_sfh), [0.3, 12.0, 2.0, 2.0, 0.4, 0.3, -1.0]])
+    assert model.n_param == lo.size
+    model.nss(lo, hi, n_live=300, n_replace=64, n_slice_steps=40, max_iter=4, seed=1)   # warm-up
+    fits = []
+    for f in range(n_fits):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = model.nss(lo, hi, n_live=300, n_replace=64, n_slice_steps=40, max_iter=5000, seed=100 + f)
+        dt = time.perf_counter() - t0
+        fits.append({"seconds": round(dt, 3), "lnz": round(r["lnz"], 3), "info_h": round(r["info_h"], 3),
+                     "n_iter": r["n_iter"], "n_like": int(r["n_like"]), "n_rows": int(r["n_rows"]),
+                     "converged": r["converged"], "like_evals_per_s": round(r["n_like"] / dt, 1)})
+    model.close()
+    return {"model": "15 bands + 22 line-catalogue entries, 8 SFH bins, constant [Fe/H], nebular + lines, "
+                     "birth-cloud + KC13 dust, z fixed; 15 sampled columns, box prior",
+            "settings": {"n_live": 300, "n_replace": 64, "n_slice_steps": 40, "stop_dlnz": -5.0,
+                         "precision": "fp32"},
+            "fits": fits,
+            "seconds_per_fit_median": round(float(np.median([f["seconds"] for f in fits])), 3),
+            "paper_context": "4.0 min per fit and ~1.4e6 likelihood evaluations on one A100 (JADES 170891, "
+                             "15 bands + 22 lines; other model and hardware)"}
 
 
 def serving_accuracy(ctx, gid, grid, reqs, models, thetas, okws, n_req=8, n_rows=16):

@@ -379,6 +379,17 @@ sed_status sed_loglike_grad(sed_ctx *ctx, sed_model_id model, const float *theta
                             int precision, void *stream);
 
 /*
+ * Observer-frame integrated fluxes of the grid's emission lines (App. C, App.
+ * line_proj), erg/s/cm^2, for a model with use_lines: flux_out is a DEVICE
+ * buffer [n][neb_n_line] (row-major, the grid's line order), the quantities
+ * the line catalogue's entries sum (Sec. 3.3).  Rows with a non-zero status
+ * get zeros.  SED_EUNSUPPORTED for a model without lines; otherwise as
+ * sed_forward (asynchronous on `stream`).
+ */
+sed_status sed_line_fluxes(sed_ctx *ctx, sed_model_id model, const float *theta, int n, int ld, float *flux_out,
+                           int precision, void *stream);
+
+/*
  * sed_loglike with HOST buffers: theta [n][ld] FP32, lnl_out [n], row_status
  * [n] or NULL.  Runs on `stream` and synchronises the stream before
  * returning.  A page-locked host buffer that the device can address (memory

@@ -105,6 +105,7 @@ SIGNATURES = {
     "sed_destroy_model": (C.c_int, [P, C.c_int32]),
     "sed_forward": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
     "sed_loglike": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
+    "sed_line_fluxes": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, C.c_int, P]),
     "sed_loglike_grad": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, P, C.c_int, P]),
     "sed_loglike_host": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),
     "sed_loglike_noalloc": (C.c_int, [P, C.c_int32, P, C.c_int, C.c_int, P, P, C.c_int, P]),

@@ -113,6 +113,7 @@ class Context:
         d.precision_mask = int(precision_mask)
         gid = C.c_int32()
         self._check(self._lib.sed_load_grid(self._h, C.byref(d), C.byref(gid)))
+        self.__dict__.setdefault("_grid_lines", {})[gid.value] = int(d.neb_n_line)
         return gid.value
 
     def create_model(self, grid_id, n_sfh, zf, zmode, *, use_afe=0, use_nebular=0, dust_law=0,
@@ -181,6 +182,7 @@ class Context:
             d.fixed_val[i] = float(v)
         mid = C.c_int32()
         self._check(self._lib.sed_create_model(self._h, C.byref(d), C.byref(mid)))
+        self.__dict__.setdefault("_n_line", {})[mid.value] = self.__dict__.get("_grid_lines", {}).get(grid_id, 0)
         return Model(self, mid.value, n_filt=d.n_filt, n_pix=d.n_pix)
 
 
@@ -243,6 +245,19 @@ class Model:
                                        _prec(precision), _stream_handle(stream))
         self.ctx._check(st)
         return lnl, stt
+
+    def line_fluxes(self, theta: torch.Tensor, precision="fp32", stream=None):
+        """Observer-frame fluxes of the grid's emission lines, erg/s/cm^2, as a
+        CUDA float32 tensor [n, n_line] (sed_line_fluxes)."""
+        n, ld = self._theta(theta)
+        n_line = self.ctx.__dict__.get("_n_line", {}).get(self.id)
+        if n_line is None:
+            raise ValueError("line_fluxes needs the model's grid line count (create the model through Context)")
+        out = torch.empty((n, n_line), dtype=torch.float32, device=theta.device)
+        st = self.ctx._lib.sed_line_fluxes(self.ctx._h, self.id, C.c_void_p(theta.data_ptr()), n, ld,
+                                           C.c_void_p(out.data_ptr()), _prec(precision), _stream_handle(stream))
+        self.ctx._check(st)
+        return out
 
     def loglike_noalloc(self, theta: torch.Tensor, precision="fp32", stream=None, out=None, status=None):
         """sed_loglike_noalloc: the same lnL and row status as loglike, with every

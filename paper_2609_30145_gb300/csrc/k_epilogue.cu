@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
       if (a.phot_out) a.phot_out[(size_t)ro * md.n_filt + b] = 0.f;
     for (int i = tid; i < md.n_pix; i += blockDim.x)
       if (a.spec_out) a.spec_out[(size_t)ro * md.n_pix + i] = 0.f;
+    if (LINES && a.lines_out)
+      for (int l = tid; l < g.n_line; l += blockDim.x) a.lines_out[(size_t)ro * g.n_line + l] = 0.f;
     if (tid == 0) {
       if (a.lnl) a.lnl[ro] = -INFINITY;
       if (a.status) a.status[ro] = rs.status;
@@ -121,6 +123,10 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   float* ln_is = ln_A + NLn;
   for (int l = tid; l < NLn; l += EPI_THREADS) line_setup(md, g, rs, eb, l, ln_F, ln_A, ln_is, ln_x);
   __syncthreads();
+  if (LINES && a.lines_out) {   // the lines' fluxes only (sed_line_fluxes)
+    for (int l = tid; l < NLn; l += EPI_THREADS) a.lines_out[(size_t)ro * NLn + l] = ln_F[l];
+    if (!a.lnl && !a.phot_out && !a.spec_out) return;
+  }
 
   // ---- photometry, one band per warp.  Consecutive lanes take consecutive
   //      filter samples (coalesced loads, eight in flight per lane); each

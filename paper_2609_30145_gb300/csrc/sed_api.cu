@@ -1346,6 +1346,32 @@ sed_status sed_forward(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   return prof_mark(ctx, w, 3, s);
 }
 
+sed_status sed_line_fluxes(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, float* flux_out,
+                           int precision, void* stream) {
+  if (!ctx) return SED_EINVAL;
+  Model* M = find_model(ctx, id);
+  sed_status st = check_hot_args(ctx, M, theta, n, ld, precision);
+  if (st) return st;
+  if (!M->dv.use_lines) return fail(ctx, SED_EUNSUPPORTED, "the model has no emission lines");
+  if (n > 0 && !flux_out) return fail(ctx, SED_EINVAL, "flux_out is NULL");
+  if (n == 0) return SED_OK;
+  DevGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
+  if (!w) return st;
+  st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
+  if (st) return st;
+  EpiArgs ea{};
+  ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
+  ea.O2 = precision == SED_PREC_FP32 ? w->O2 : nullptr;
+  ea.md = M->dv; ea.g = M->g->dv;
+  ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
+  ea.lines_out = flux_out;
+  ea.err = w->err;
+  CK(launch_epilogue(ea, s));
+  return prof_mark(ctx, w, 3, s);
+}
+
 sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
                        uint32_t* row_status, int precision, void* stream) {
   if (!ctx) return SED_EINVAL;

@@ -557,6 +557,7 @@ struct EpiArgs {
   const int* row_model;    // largest n_samp / n_pix of the launch's models
   int smem_samp, smem_pix, smem_win;
   float* phot_out; float* spec_out;
+  float* lines_out;    // [n][n_line] observer-frame line fluxes (erg/s/cm^2), or NULL
   double* lnl; uint32_t* status;
   const int* err;      // device error word of the contraction (row status SED_ROW_DEVICE_TIMEOUT)
   const float* lam8;   // FP8 path: [n_lam] 2^-f_l multiplying Y and O; NULL otherwise

@@ -68,6 +68,31 @@ def test_lines_parity_paper_scale(ctx, prec):
     check(ref, got, prec, rows, orc=orc)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_line_fluxes_match_the_oracle(ctx, prec):
+    """sed_line_fluxes: every grid line's observer-frame flux of 150 rows
+    (sampled sigma_gas) against the oracle's, 2e-5 relative per line (the fluxes
+    do not pass through the contraction, so every precision gives FP32-grade
+    values); rows with a bad status give zeros."""
+    orc, model = lines_model(ctx, W_SMALL, 2)
+    th32, th64 = cases.lines_theta_pair(W_SMALL, orc, W_SMALL.batch, seed=95)
+    th32[3, model.offsets["sigma_gas"]] = -5.0          # refused row
+    th64 = th32.astype(np.float64)
+    got = model.line_fluxes(torch.from_numpy(th32).cuda(), prec).cpu().numpy().astype(np.float64)
+    ref = orc.line_fluxes(th64)
+    st = orc.eval(th64)["status"]
+    ok = st == 0
+    assert not ok[3] and np.all(got[3] == 0.0)
+    e = np.abs(got[ok] - ref[ok]) / np.maximum(np.abs(ref[ok]), 1e-6 * np.abs(ref[ok]).max(axis=1, keepdims=True))
+    assert e.max() < 2e-5, e.max()
+    base = cases.gpu_model_for(ctx, cases.oracle_for(W_SMALL), W_SMALL)
+    from paper_2609_30145_gb300 import _ffi
+    from paper_2609_30145_gb300.api import SedError
+    with pytest.raises(SedError) as e:
+        base.line_fluxes(torch.from_numpy(np.ascontiguousarray(th32[:, :base.n_param])).cuda(), prec)
+    assert e.value.status == _ffi.SED_EUNSUPPORTED
+
+
 def test_lines_change_the_model_where_the_paper_puts_them(ctx):
     """The line part of the GPU model (lines on minus lines off) sits on the
     pixels within 5 s_l of each line's observed wavelength and is positive
