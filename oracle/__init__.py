@@ -63,7 +63,8 @@ class _Model(C.Structure):
                 ("use_lines", C.c_int), ("gas_sigma_mode", C.c_int), ("sigma_gas_kms", C.c_double),
                 ("sigma_gas_max_kms", C.c_double), ("n_lcat", C.c_int), ("lcat_start", C.c_void_p),
                 ("lcat_line", C.c_void_p), ("lcat_d", C.c_void_p), ("lcat_sigma", C.c_void_p),
-                ("lcat_mask", C.c_void_p), ("lcat_upper", C.c_void_p)]
+                ("lcat_mask", C.c_void_p), ("lcat_upper", C.c_void_p), ("dust_n_bin", C.c_int),
+                ("dust_bin_M", C.c_void_p), ("dust_bin_law", C.c_void_p)]
 
 
 def _load():
@@ -138,6 +139,8 @@ class Oracle:
     lcat: tuple | None = None           # line catalogue (Sec. 3.3): (blends: list of lists of grid-line
                                         # indices, d, sigma, mask or None, upper or None), erg/s/cm^2
     sfh_scheme: int = 0                 # 0 step (N_T bin masses), 1 linear (N_T + 1 edge SFRs; App. B)
+    dust_bins: tuple | None = None      # age-binned attenuation (App. "dust_attn"): (M [n_age][n_bin], laws
+                                        # [n_bin], 0 power law / 1 KC13); adds 2 n_bin columns at the row's end
     floor_phot: int = 0                 # noise-floor terms of each arm (App. sys_floor): FLOOR_* bits
     floor_spec: int = 0
     fesc_geometry: int = 0              # ionising-photon escape (Sec. frac_obrun): FESC_*; adds the frac_obrun column
@@ -227,6 +230,19 @@ class Oracle:
             m.lcat_d, m.lcat_sigma = _p(k(d)), _p(k(s))
             m.lcat_mask = _p(k(mask, np.uint8))
             m.lcat_upper = _p(k(upper, np.uint8))
+        if self.dust_bins is not None:
+            M, laws = self.dust_bins
+            M = np.asarray(M, dtype=np.float64)
+            if M.ndim != 2 or M.shape[0] != self.grid.flux.shape[2] or not 1 <= M.shape[1] <= 4:
+                raise ValueError("dust_bins: M must be [n_age][n_bin], 1 <= n_bin <= 4")
+            sums = M.sum(axis=1)
+            if np.any(M < 0) or np.any(M > 1) or not np.all((np.abs(sums - 1) < 1e-9) | (sums == 0)):
+                raise ValueError("dust_bins: rows of M in [0, 1] summing to 1 or all zero")
+            if self.use_lines or self.fesc_geometry:
+                raise ValueError("dust_bins: not combined with emission lines or an escape geometry")
+            m.dust_n_bin = M.shape[1]
+            m.dust_bin_M = _p(k(M))
+            m.dust_bin_law = _p(k(np.asarray(laws), np.int32))
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
@@ -319,8 +335,9 @@ class Oracle:
 
     def grad(self, theta, nthreads=0):
         """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])."""
-        if self.use_lines or self.lcat is not None:
-            raise NotImplementedError("the analytic gradient does not cover emission lines: use grad_fd")
+        if self.use_lines or self.lcat is not None or self.dust_bins is not None:
+            raise NotImplementedError("the analytic gradient does not cover emission lines or age-binned dust: "
+                                      "use grad_fd")
         th = np.ascontiguousarray(theta, dtype=np.float64)
         n, ld = th.shape
         out = np.zeros((n, ld))
@@ -374,13 +391,14 @@ def floor_keys(floor_phot=0, floor_spec=0):
 
 
 def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, sfh_scheme=0, fesc_geometry=0,
-               sample_sigma_gas=0):
+               sample_sigma_gas=0, dust_n_bin=0):
     """Parameter rows in the oracle's layout: sfh[N_T] (bin masses; N_T + 1 edge
     SFRs with the linear scheme), logzsol[N_T or 1], then
     afe, logmass, zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index,
     gas_logz, gas_logu, sigma_gal when the model samples it, and the log10 of
     each noise-floor term that is on (photometry, then spectrum), and frac_obrun
-    with an escape geometry, sigma_gas when the model samples the gas dispersion."""
+    with an escape geometry, sigma_gas when the model samples the gas dispersion, and
+    with age-binned dust the 2 n_bin columns of d["dust_bins"] (tau_b, slope_b of each bin)."""
     nz = n_sfh if zmode == 0 else 1
     n = d["sfh"].shape[0]
     cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh + (1 if sfh_scheme == 1 else 0)),
@@ -390,4 +408,6 @@ def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, 
             floor_keys(floor_phot, floor_spec) + (("frac_obrun",) if fesc_geometry else ()) + \
             (("sigma_gas",) if sample_sigma_gas else ()):
         cols.append(np.asarray(d[k], dtype=np.float64).reshape(n, 1))
+    if dust_n_bin:
+        cols.append(np.asarray(d["dust_bins"], dtype=np.float64).reshape(n, 2 * dust_n_bin))
     return np.ascontiguousarray(np.concatenate(cols, axis=1))

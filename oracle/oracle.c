@@ -128,7 +128,7 @@ static int sfh_cols(const orc_model *md) { return md->n_sfh + (md->sfh_scheme ==
 int orc_n_param(const orc_model *md) {
   return sfh_cols(md) + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0) +
          n_floor(md->floor_phot) + n_floor(md->floor_spec) + (md->fesc_geometry ? 1 : 0) +
-         (md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED ? 1 : 0);
+         (md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED ? 1 : 0) + 2 * md->dust_n_bin;
 }
 
 /* parameter row decoding (layout: sfh[N_T], logzsol[N_T or 1], afe, logmass,
@@ -141,6 +141,7 @@ typedef struct {
   int fl_col[2][4];  /* column of each term in the row, -1 when the term is off */
   double fob;        /* runaway fraction f_ob (0 without an escape geometry) */
   double sigma_gas;  /* gas dispersion of the emission lines, km/s */
+  double bin_tau[ORC_MAX_DUST_BIN], bin_slope[ORC_MAX_DUST_BIN];   /* age-binned laws' parameters */
 } orc_theta;
 
 static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
@@ -165,8 +166,12 @@ static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
     }
   }
   o->fob = md->fesc_geometry ? th[col++] : 0.0;
-  o->sigma_gas = md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED ? th[col]
+  o->sigma_gas = md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED ? th[col++]
                : (md->gas_sigma_mode == ORC_GAS_SIGMA_FIXED ? md->sigma_gas_kms : o->sigma_gal);
+  for (int b = 0; b < md->dust_n_bin && b < ORC_MAX_DUST_BIN; b++) {
+    o->bin_tau[b] = th[col++];
+    o->bin_slope[b] = th[col++];
+  }
 }
 
 /* Eq. "app_noise_floor": the effective variance of a datum with formal error
@@ -791,11 +796,62 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
   orc_theta t;
   decode_theta(md, theta, &t);
   if (!st) {
+    orc_q(g, Q);
+    double qy = 0.0;
+    if (md->dust_n_bin > 0) {
+      /* App. "dust_attn": per age node a the optical depth tau_a = sum_b M_ab
+       * kappa_b(lam; theta_b) (Eq. "app_tau_bin"), applied to the node's
+       * stellar plus nebular light inside the contraction and followed by the
+       * diffuse screen (Eq. "app_attn"); nebular ages lose their stellar flux
+       * below 912 A and carry Q_ma 10^(bilinear log10 template) instead */
+      const int nb = md->dust_n_bin;
+      double *kap = (double *)malloc((size_t)nb * NL * sizeof(double));
+      double *shp = (double *)malloc(NL * sizeof(double));
+      double *att = (double *)malloc(NL * sizeof(double));
+      for (int b = 0; b < nb; b++) orc_dust_tau(md->dust_bin_law[b], g->lam, NL, t.bin_tau[b], t.bin_slope[b], kap + (size_t)b * NL);
+      const int has_neb = md->use_nebular && g->neb_tab;
+      if (has_neb) {
+        int u0, u1, z0, z1;
+        double wu0, wu1, wz0, wz1;
+        bracket(g->neb_logu, g->neb_n_logu, t.gas_logu, &u0, &wu0, &u1, &wu1);
+        bracket(g->neb_logz, g->neb_n_logz, t.gas_logz, &z0, &wz0, &z1, &wz1);
+        const double *t00 = g->neb_tab + ((size_t)u0 * g->neb_n_logz + z0) * NL;
+        const double *t01 = g->neb_tab + ((size_t)u0 * g->neb_n_logz + z1) * NL;
+        const double *t10 = g->neb_tab + ((size_t)u1 * g->neb_n_logz + z0) * NL;
+        const double *t11 = g->neb_tab + ((size_t)u1 * g->neb_n_logz + z1) * NL;
+        for (int k = 0; k < NL; k++)
+          shp[k] = pow(10.0, wu0 * wz0 * t00[k] + wu0 * wz1 * t01[k] + wu1 * wz0 * t10[k] + wu1 * wz1 * t11[k]);
+      }
+      for (int k = 0; k < NL; k++) F[k] = 0.0;
+      for (int a = 0; a < NA; a++) {
+        for (int k = 0; k < NL; k++) {
+          double tau = 0.0;
+          for (int b = 0; b < nb; b++) tau += md->dust_bin_M[(size_t)a * nb + b] * kap[(size_t)b * NL + k];
+          att[k] = exp(-tau);
+        }
+        const int neb = has_neb && g->log_age_yr[a] <= md->bc_edge_log_age_yr;
+        for (int n = 0; n < NAF; n++)
+          for (int m = 0; m < NZ; m++) {
+            size_t s = ((size_t)n * NZ + m) * NA + a;
+            double w = W[s];
+            if (w == 0.0) continue;
+            const double *f = g->flux + s * NL;
+            for (int k = 0; k < NL; k++) {
+              double v = (neb && g->lam[k] < O_LYMAN) ? 0.0 : f[k];
+              if (neb) v += Q[s] * shp[k];
+              F[k] += w * v * att[k];
+              (g->log_age_yr[a] <= md->bc_edge_log_age_yr ? Y : O)[k] += w * v;
+            }
+            if (g->log_age_yr[a] <= md->bc_edge_log_age_yr) qy += w * Q[s];
+          }
+      }
+      orc_dust_tau(md->dust_law, g->lam, NL, t.tau_d, t.delta, td);
+      for (int k = 0; k < NL; k++) F[k] *= exp(-td[k]);
+      free(kap); free(shp); free(att);
+    } else {
     /* contraction, Eq. "csp_sum_main" split into birth-cloud (young) and
      * older ages (Eq. "app_attn" with a two-bin age-to-bin matrix); the
      * stellar flux below 912 A of nebular ages is removed (App. A, Fig. flow) */
-    orc_q(g, Q);
-    double qy = 0.0;
     for (int n = 0; n < NAF; n++)
       for (int m = 0; m < NZ; m++)
         for (int a = 0; a < NA; a++) {
@@ -848,6 +904,7 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
         F[k] = ed * (T * (Y[k] + (1.0 - fob) * N[k]) + fob * YL[k] + O[k]);
       }
       Y[k] += N[k];   /* Y_out: young stellar flux (ionising continuum removed) plus nebular */
+    }
     }
     /* observer frame, Sec. 2.6 */
     double dl = cosm[0] > 10.0 * O_PC_CM ? cosm[0] : 10.0 * O_PC_CM;

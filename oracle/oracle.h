@@ -88,7 +88,13 @@ typedef struct {
   const double *lcat_d, *lcat_sigma;   /* observed integrated fluxes and errors, erg/s/cm^2 */
   const unsigned char *lcat_mask;      /* [n_lcat] or NULL (all included) */
   const unsigned char *lcat_upper;     /* [n_lcat] nonzero: lcat_d[k] is an upper limit, or NULL */
+  int dust_n_bin;              /* age-binned attenuation (App. "dust_attn"): 0 = the birth-cloud power law;
+                                  n > 0 replaces it by n laws over the age axis, each with two columns
+                                  (optical depth at 5500 A, slope) after every other key of the row */
+  const double *dust_bin_M;    /* [n_age][n_bin] age-to-bin matrix, rows summing to 1 or all zero */
+  const int *dust_bin_law;     /* [n_bin] 0 power law, 1 Kriek & Conroy 2013 */
 } orc_model;
+#define ORC_MAX_DUST_BIN 4
 /* The gas velocity dispersion of the emission lines (Sec. 2.7): tied to the
  * stellar sigma_gal (the paper's default), a fixed value, or a parameter
  * column (the last one of the row). */
