@@ -114,7 +114,9 @@ enum {
   SED_KEY_FRAC_OBRUN = 20,    /* runaway fraction f_ob in [0, 1] (a column only with an escape geometry) */
   SED_KEY_SIGMA_GAS = 21,     /* gas velocity dispersion of the emission lines, km/s (a column only when
                                  gas_sigma_mode = SED_GAS_SIGMA_SAMPLED) */
-  SED_NKEYS = 22
+  SED_KEY_DUST_BINS = 22,     /* age-binned attenuation: 2 dust_n_bin columns, each bin's optical depth at
+                                 5500 A then its slope (power-law index or KC13 delta) */
+  SED_NKEYS = 23
 };
 
 typedef struct sed_ctx sed_ctx;
@@ -287,7 +289,28 @@ typedef struct {
   const int *lcat_len, *lcat_line;
   const double *lcat_d, *lcat_sigma;
   const uint8_t *lcat_mask, *lcat_upper;
+  /* Age-binned attenuation (App. dust_attn, Eq. app_tau_bin): dust_n_bin > 0
+   * replaces the birth-cloud power law by dust_n_bin laws over the SSP age
+   * axis.  dust_bin_M [n_age][dust_n_bin] is the age-to-bin matrix: each row
+   * in [0, 1] summing to 1 (a node in one bin, or shared between overlapping
+   * bins) or all zero (no bin: the node sees the diffuse screen only); the
+   * optical depth at age node a is tau_a = sum_b M_ab kappa_b(lambda), with
+   * kappa_b of law dust_bin_law[b] (SED_DUST_POWER_LAW: tau_b (lam/5500)^s_b;
+   * SED_DUST_KC13: the Kriek & Conroy form of the diffuse component with
+   * delta = s_b), and it attenuates the node's stellar and nebular light before
+   * the diffuse screen.  The columns SED_KEY_DUST_BINS hold (tau_b, s_b) per
+   * bin; tau_pow and alpha_pow keep their columns and are not read.  The ages
+   * sharing one non-zero row form one of the contraction's attenuated blocks
+   * (at most SED_MAX_DUST_SEG distinct non-zero rows).  Not combined with emission
+   * lines or an escape geometry (SED_EUNSUPPORTED), nor served by sed_server_*
+   * or sed_loglike_noalloc. */
+  int dust_n_bin;
+  const double *dust_bin_M;
+  const int *dust_bin_law;
 } sed_model_desc;
+
+#define SED_MAX_DUST_BIN 4
+#define SED_MAX_DUST_SEG 4
 
 #define SED_GAS_SIGMA_TIED 0
 #define SED_GAS_SIGMA_FIXED 1

@@ -123,11 +123,14 @@ class Context:
                      sigma_gal_kms=0.0, z_ref=0.0, sample_sigma_gal=0, sigma_gal_max_kms=1000.0,
                      calib_sigma=None, noise_floor_phot=0, noise_floor_spec=0, sfh_scheme=0,
                      phot_upper=None, fesc_geometry=0, fixed=None, calib_mode=0, use_lines=0,
-                     gas_sigma_mode=0, sigma_gas_kms=300.0, sigma_gas_max_kms=1000.0, lcat=None) -> "Model":
+                     gas_sigma_mode=0, sigma_gas_kms=300.0, sigma_gas_max_kms=1000.0, lcat=None,
+                     dust_bins=None) -> "Model":
         """fixed: optional {key name: value} of keys fixed for every row (no
         column in the parameter rows, no gradient); key names as in _ffi.KEYS.
         lcat: optional line catalogue (blends: list of lists of grid-line
-        indices, data, sigma, mask or None, upper-limit flags or None)."""
+        indices, data, sigma, mask or None, upper-limit flags or None).
+        dust_bins: optional age-binned attenuation (M [n_age][n_bin] age-to-bin
+        matrix, laws [n_bin] of DUST_POWER_LAW / DUST_KC13)."""
         d = _ffi.ModelDesc()
         d.grid, d.n_sfh, d.zf, d.zmode = grid_id, n_sfh, zf, zmode
         d.use_afe, d.use_nebular, d.dust_law = use_afe, use_nebular, dust_law
@@ -160,6 +163,13 @@ class Context:
             keep.append(cs)
             d.calib_n, d.calib_sigma = cs.size, _ptr(cs)
         d.calib_mode = int(calib_mode)
+        if dust_bins is not None:
+            bm, bl = dust_bins
+            bm = np.ascontiguousarray(bm, dtype=np.float64)
+            bl = np.ascontiguousarray(bl, dtype=np.int32)
+            keep += [bm, bl]
+            d.dust_n_bin = bm.shape[1]
+            d.dust_bin_M, d.dust_bin_law = _ptr(bm), _ptr(bl)
         d.use_lines, d.gas_sigma_mode = int(use_lines), int(gas_sigma_mode)
         d.sigma_gas_kms, d.sigma_gas_max_kms = float(sigma_gas_kms), float(sigma_gas_max_kms)
         if lcat is not None:

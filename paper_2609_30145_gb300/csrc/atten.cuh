@@ -52,4 +52,38 @@ __device__ __forceinline__ float attenuated(const ModelDev& md, const RowScal& r
   return ed * (T * (ys + (1.f - f) * nb) + (lyc ? f * y : 0.f) + o);
 }
 
+// Age-binned attenuation (App. dust_attn, Eq. app_tau_bin, Eq. app_attn):
+// attenuated block s of the young part (its ages share one row of the
+// age-to-bin matrix) sees tau_s = sum_b M_sb kappa_b with kappa_b = tau_b
+// shape_b(lam) of bin b's law; the nebular emission of each block's ages
+// (Q_s 10^template) is attenuated with its block, and the ages outside every
+// bin see the diffuse screen only:
+//   F = e^{-tau_d} [ sum_s e^{-tau_s} (Y_s + Q_s neb) + O + Q_rest neb ]
+__device__ __forceinline__ float bin_shape(int law, const float4& c, float slope) {
+  const float pw = __expf(slope * c.x);
+  return law == SED_DUST_POWER_LAW ? pw : (c.y + (0.85f - 1.9f * slope) * c.z) * pw;
+}
+
+__device__ __forceinline__ float attenuated_bins(const ModelDev& md, const RowScal& rs, const float4& c, float eb,
+                                                const float* y, float o, const float* neb_tab, int k) {
+  float kap[MAX_DUST_BIN];
+#pragma unroll
+  for (int b = 0; b < MAX_DUST_BIN; ++b)
+    kap[b] = b < md.n_bin ? rs.bin_tau[b] * bin_shape(md.bin_law[b], c, rs.bin_slope[b]) : 0.f;
+  const float lg = md.use_neb ? 3.3219280948873623f * neb_log10(rs, neb_tab, k) : 0.f;
+  float acc = o;
+  if (md.use_neb) acc += ex2_approx(rs.log2_qs[MAX_SEG] + lg);
+#pragma unroll
+  for (int sg = 0; sg < MAX_SEG; ++sg) {
+    if (sg >= md.n_seg) break;
+    float tau = 0.f;
+#pragma unroll
+    for (int b = 0; b < MAX_DUST_BIN; ++b) tau = fmaf(md.seg_M[sg][b], kap[b], tau);
+    const float v = md.use_neb ? y[sg] + ex2_approx(rs.log2_qs[sg] + lg) : y[sg];
+    acc = fmaf(__expf(-tau), v, acc);
+  }
+  const float td = rs.tau_d * dust_shape(md, c, eb, __expf(rs.delta * c.x));
+  return __expf(-td) * acc;
+}
+
 }  // namespace sed

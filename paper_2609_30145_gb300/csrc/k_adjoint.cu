@@ -45,6 +45,7 @@ constexpr int EB_WARPS = EB_THREADS / 32;
 constexpr int EB_MAX_BANDS = 128;
 constexpr int EB_NRED = 18;   // per-warp partial sums: 16 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
 constexpr int EB_NREDF = 16;
+constexpr int EB_NREDB = 2 * MAX_DUST_BIN + MAX_SEG + 1;   // age-binned dust: d/d(tau_b, slope_b), d/dQ of each block
 
 __device__ __forceinline__ float tf32_rna_dev(float x) {
   uint32_t r;
@@ -87,8 +88,9 @@ size_t epi_bwd_smem(const EpiBwdArgs& a) {
   return epi_bwd_lines_off(a) + lines;
 }
 
-// LINES: an instance with the emission lines (the one without keeps its code free of them)
-template <bool LINES>
+// LINES: an instance with the emission lines (the one without keeps its code free of them);
+// BINS: the age-binned attenuation (one Y and one dlnL/dY per attenuated block)
+template <bool LINES, bool BINS = false>
 __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
   pdl_enter();
   const ModelDev& md = a.md;
@@ -100,16 +102,19 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   __shared__ float ubp[EB_MAX_BANDS], mbp[EB_MAX_BANDS];
   __shared__ int bk0[EB_MAX_BANDS], bk1[EB_MAX_BANDS];
   __shared__ float mlb[EB_MAX_BANDS], ubm[EB_MAX_BANDS];   // lines: each band's line part, dlnL/dm_b
-  __shared__ double red[EB_WARPS][EB_NRED];
+  __shared__ double red[EB_WARPS][EB_NRED + EB_NREDB];
 
   const size_t ro = (size_t)r * a.ldn;
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
   if (rs.status) {
     for (int k = tid; k < a.ldn; k += EB_THREADS) {
-      a.gy_hi[ro + k] = 0.f;
+      for (int sg = 0; sg < (BINS ? md.n_seg : 1); ++sg) {
+        a.gy_hi[sg * a.seg_stride + ro + k] = 0.f;
+        if (a.split) a.gy_lo[sg * a.seg_stride + ro + k] = 0.f;
+      }
       a.go_hi[ro + k] = 0.f;
-      if (a.split) { a.gy_lo[ro + k] = 0.f; a.go_lo[ro + k] = 0.f; }
+      if (a.split) a.go_lo[ro + k] = 0.f;
     }
     if (tid < RGRAD) a.rgrad[(size_t)r * RGRAD + tid] = 0.0;
     if (tid == 0) {
@@ -171,7 +176,14 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   //      gather starts
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
-    Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
+    if constexpr (BINS) {
+      float yv[MAX_SEG];
+#pragma unroll
+      for (int sg = 0; sg < MAX_SEG; ++sg) yv[sg] = sg < md.n_seg ? Yr[sg * a.seg_stride + k] : 0.f;
+      Fs[k] = attenuated_bins(md, rs, g.att4[k], eb_kc, yv, O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
+    } else {
+      Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
+    }
     phi[k] = g.lam_f[k];
   }
   for (int l = tid; l < NLn; l += EB_THREADS) line_setup(md, g, rs, eb_kc, l, ln_F, ln_A, ln_is, ln_x);
@@ -675,6 +687,86 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     }
     gz_spec += gzl;
   }
+  // age-binned dust: d/d(tau_b, slope_b) of each bin, d/dQ of each block
+  float g_bin[2 * MAX_DUST_BIN] = {}, g_qs[MAX_SEG + 1] = {};
+  if constexpr (BINS) {
+    // F = e^{-tau_d} [ sum_s A_s (Y_s + Q_s neb) + O + Q_rest neb ], A_s = e^{-tau_s},
+    // tau_s = sum_b M_sb tau_b shape_b (atten.cuh's attenuated_bins)
+    for (int k = tid; k < a.ldn; k += EB_THREADS) {
+      if (k < k_lo || k > k_hi) {
+        for (int sg = 0; sg < md.n_seg; ++sg) put_g(a, a.gy_hi, a.gy_lo, sg * a.seg_stride + ro + k, 0.f);
+        put_g(a, a.go_hi, a.go_lo, ro + k, 0.f);
+        continue;
+      }
+      const float4 c = g.att4[k];
+      const float pw = __expf(rs.delta * c.x);
+      const float shape = dust_shape(md, c, eb_kc, pw);
+      const float dshape = md.dust_law == SED_DUST_POWER_LAW ? pw * c.x : -1.9f * c.z * pw + shape * c.x;
+      const float ed = __expf(-rs.tau_d * shape);
+      float lg = 0.f, nbu = 0.f;   // log10 and value of the nebular template per unit Q
+      if (md.use_neb) {
+        lg = neb_log10(rs, g.neb_tab, k);
+        nbu = ex2_approx(3.3219280948873623f * lg);
+      }
+      const float gF = phi[k];
+      const float gtd = -gF * Fs[k];
+      const float go = gF * ed;
+      put_g(a, a.go_hi, a.go_lo, ro + k, go);
+      float shp[MAX_DUST_BIN], dsh[MAX_DUST_BIN], kap[MAX_DUST_BIN], gk[MAX_DUST_BIN];
+#pragma unroll
+      for (int b = 0; b < MAX_DUST_BIN; ++b) {
+        shp[b] = dsh[b] = kap[b] = gk[b] = 0.f;
+        if (b < md.n_bin) {
+          const float sl = rs.bin_slope[b], pb = __expf(sl * c.x);
+          shp[b] = md.bin_law[b] == SED_DUST_POWER_LAW ? pb : (c.y + (0.85f - 1.9f * sl) * c.z) * pb;
+          dsh[b] = md.bin_law[b] == SED_DUST_POWER_LAW ? pb * c.x : -1.9f * c.z * pb + shp[b] * c.x;
+          kap[b] = rs.bin_tau[b] * shp[b];
+        }
+      }
+      float gneb = 0.f;   // dlnL / d(neb per unit Q) summed over the blocks, times Q
+      if (md.use_neb) {
+        const float qr = ex2_approx(rs.log2_qs[MAX_SEG]);
+        g_qs[MAX_SEG] = fmaf(go, nbu, g_qs[MAX_SEG]);
+        gneb = go * qr;
+      }
+#pragma unroll
+      for (int sg = 0; sg < MAX_SEG; ++sg) {
+        if (sg >= md.n_seg) break;
+        float tau = 0.f;
+#pragma unroll
+        for (int b = 0; b < MAX_DUST_BIN; ++b) tau = fmaf(md.seg_M[sg][b], kap[b], tau);
+        const float gys = go * __expf(-tau);
+        put_g(a, a.gy_hi, a.gy_lo, sg * a.seg_stride + ro + k, gys);
+        const float qs = md.use_neb ? ex2_approx(rs.log2_qs[sg]) : 0.f;
+        const float gtau = -gys * fmaf(qs, nbu, Yr[sg * a.seg_stride + k]);
+#pragma unroll
+        for (int b = 0; b < MAX_DUST_BIN; ++b) gk[b] = fmaf(gtau, md.seg_M[sg][b], gk[b]);
+        if (md.use_neb) {
+          g_qs[sg] = fmaf(gys, nbu, g_qs[sg]);
+          gneb = fmaf(gys, qs, gneb);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < MAX_DUST_BIN; ++b) {
+        g_bin[2 * b] = fmaf(gk[b], shp[b], g_bin[2 * b]);
+        g_bin[2 * b + 1] = fmaf(gk[b] * rs.bin_tau[b], dsh[b], g_bin[2 * b + 1]);
+      }
+      g_td += gtd * shape;
+      g_dl += gtd * rs.tau_d * dshape;
+      if (md.use_neb) {
+        const float glg = gneb * nbu * 2.302585092994046f;
+        float su = 0.f, sz = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const float tv = g.neb_tab[rs.neb_off[cc] + k];
+          su += rs.neb_dwu[cc] * tv;
+          sz += rs.neb_dwz[cc] * tv;
+        }
+        g_lu += glg * su;
+        g_lz += glg * sz;
+      }
+    }
+  } else
   for (int k = tid; k < a.ldn; k += EB_THREADS) {
     if (k < k_lo || k > k_hi) {
       put_g(a, a.gy_hi, a.gy_lo, ro + k, 0.f);
@@ -758,16 +850,32 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     l_spec += __shfl_xor_sync(0xffffffffu, l_spec, o);
     um_spec += __shfl_xor_sync(0xffffffffu, um_spec, o);
   }
+  if constexpr (BINS) {
+#pragma unroll
+    for (int q = 0; q < 2 * MAX_DUST_BIN; ++q)
+#pragma unroll
+      for (int o = 16; o; o >>= 1) g_bin[q] += __shfl_xor_sync(0xffffffffu, g_bin[q], o);
+#pragma unroll
+    for (int q = 0; q <= MAX_SEG; ++q)
+#pragma unroll
+      for (int o = 16; o; o >>= 1) g_qs[q] += __shfl_xor_sync(0xffffffffu, g_qs[q], o);
+  }
   if (lane == 0) {
 #pragma unroll
     for (int q = 0; q < EB_NREDF; ++q) red[warp][q] = (double)vf[q];
     red[warp][EB_NREDF] = l_spec;
     red[warp][EB_NREDF + 1] = um_spec;
+    if constexpr (BINS) {
+#pragma unroll
+      for (int q = 0; q < 2 * MAX_DUST_BIN; ++q) red[warp][EB_NRED + q] = (double)g_bin[q];
+#pragma unroll
+      for (int q = 0; q <= MAX_SEG; ++q) red[warp][EB_NRED + 2 * MAX_DUST_BIN + q] = (double)g_qs[q];
+    }
   }
   __syncthreads();
   if (warp == 0) {
     double col = 0.0;
-    if (lane < EB_NRED)
+    if (lane < (BINS ? EB_NRED + EB_NREDB : EB_NRED))
       for (int w = 0; w < EB_WARPS; ++w) col += red[w][lane];
     // the photometric lnL terms and d lnL/d ln(mass) pieces in FP64, one band per lane
     double bl = 0.0, bu = 0.0, gfp[4] = {0.0, 0.0, 0.0, 0.0};
@@ -798,9 +906,9 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       if (md.floor_bits[0])
         for (int k = 0; k < 4; ++k) gfp[k] += __shfl_xor_sync(0xffffffffu, gfp[k], o);
     }
-    double s[EB_NRED];
+    double s[EB_NRED + EB_NREDB];
 #pragma unroll
-    for (int q = 0; q < EB_NRED; ++q) s[q] = __shfl_sync(0xffffffffu, col, q);
+    for (int q = 0; q < EB_NRED + EB_NREDB; ++q) s[q] = __shfl_sync(0xffffffffu, col, q);
     if (lane == 0) {
       double lnl = s[EB_NREDF] + bl, um_phot = bu;
       const double um_sp = s[EB_NREDF + 1];
@@ -823,6 +931,11 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         rg[RG_FLOOR + k] = gfp[k];
         rg[RG_FLOOR + 4 + k] = s[9 + k];
       }
+      if constexpr (BINS) {
+        for (int q = 0; q < 2 * MAX_DUST_BIN; ++q) rg[RG_BIN + q] = s[EB_NRED + q];
+        for (int q = 0; q <= MAX_SEG; ++q) rg[RG_QSEG + q] = s[EB_NRED + 2 * MAX_DUST_BIN + q];
+        rg[RG_QY] = s[EB_NRED + 2 * MAX_DUST_BIN];
+      }
       rg[RG_BAD] = stt ? 1.0 : 0.0;
       if (a.lnl) a.lnl[rs.orig] = lnl;
       if (a.status) a.status[rs.orig] = stt;
@@ -835,9 +948,10 @@ cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a_in, size_t* smem_needed, cud
   a.lines_off = (int)epi_bwd_lines_off(a);
   const size_t smem = epi_bwd_smem(a);
   if (smem_needed) *smem_needed = smem;
-  static DynSmemCache set_for[2];
-  auto k = a.md.use_lines ? k_epi_bwd<true> : k_epi_bwd<false>;
-  cudaError_t e = ensure_dyn_smem(k, smem, &set_for[a.md.use_lines ? 1 : 0]);
+  static DynSmemCache set_for[3];
+  const int m = a.md.n_bin > 0 ? 2 : (a.md.use_lines ? 1 : 0);
+  auto k = m == 2 ? k_epi_bwd<false, true> : (m == 1 ? k_epi_bwd<true> : k_epi_bwd<false>);
+  cudaError_t e = ensure_dyn_smem(k, smem, &set_for[m]);
   if (e != cudaSuccess) return e;
   return launch_pdl(k, dim3(a.n), dim3(EB_THREADS), smem, s, a);
 }
@@ -856,6 +970,8 @@ __global__ void __launch_bounds__(256) k_dw_simt(const DwSimtArgs a) {
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * DS_M, n0 = blockIdx.x * DS_N;
   const float* G = n0 < a.Ky_pad ? a.gy : a.go;
+  for (int sg = 1; sg < a.n_seg; ++sg)   // age-binned dust: the attenuated block of these columns
+    if (n0 >= a.seg_k0[sg] && n0 < a.Ky_pad) G = a.gy + sg * a.seg_stride;
   // the reduction runs over the union of the tile's row windows (G vanishes outside)
   __shared__ int s_klo, s_khi;
   if (tid == 0) { s_klo = 0x7fffffff; s_khi = -1; }

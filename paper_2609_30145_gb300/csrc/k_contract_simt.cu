@@ -1,7 +1,8 @@
 // CUDA-core FP32 contraction (precision SED_PREC_FP32_SIMT): the weighted sum
 // of Eq. csp_sum_main evaluated separately over the young (birth-cloud) and the
 // old K blocks, Y = W[:, young] SSP[young, :], O = W[:, old] SSP[old, :]
-// (Eq. app_attn with the two-bin age split).  Plain register-tiled SGEMM,
+// (Eq. app_attn with the two-bin age split), the young part per attenuated
+// block with age-binned dust.  Plain register-tiled SGEMM,
 // 128x128 tile, 8x8 outputs per thread.  Kept as an independent FFMA
 // cross-check of the tensor-core paths.
 #include "sed_internal.cuh"
@@ -31,8 +32,12 @@ __global__ void __launch_bounds__(256) k_contract_simt(const ContractArgs a) {
     if (s_khi < 0 || n0 > s_khi || n0 + SB_N - 1 < s_klo) return;
   }
 
-  for (int part = 0; part < 2; ++part) {
-    const int kb = part ? a.Ky_pad : 0, ke = part ? a.Kpad : a.Ky_pad;
+  // the attenuated blocks of the young part (one without age-binned dust), then the old part
+  const int nseg = a.n_seg > 0 ? a.n_seg : 1;
+  for (int part = 0; part <= nseg; ++part) {
+    const bool old = part == nseg;
+    const int kb = old ? a.Ky_pad : (part == 0 ? 0 : a.seg_k0[part]);
+    const int ke = old ? a.Kpad : (part + 1 == nseg ? a.Ky_pad : a.seg_k0[part + 1]);
     float acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(256) k_contract_simt(const ContractArgs a) {
       }
       __syncthreads();
     }
-    float* out = part ? a.O : a.Y;
+    float* out = old ? a.O : a.Y + part * a.seg_stride;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int gm = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;

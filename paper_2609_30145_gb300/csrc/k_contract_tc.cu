@@ -147,6 +147,15 @@ struct Params {
   const uint32_t* kmask;     // [m_tiles][kmask_w] K tiles some row of the M tile touches (NULL: all);
   int kmask_w;               // adjoint: 32-column tiles of dW's columns
   int* err;
+  // attenuated blocks of the young part (age-binned dust; one block without it):
+  // forward: block s = K tiles [seg_kt[s], seg_kt[s+1]) -> Y + s seg_stride;
+  // adjoint: dW columns [seg_col[s], seg_col[s+1]) read dlnL/dY of block s,
+  // rows s seg_rows + m of the A map
+  int n_seg;
+  int seg_kt[MAX_SEG + 1];
+  int seg_col[MAX_SEG + 1];
+  int seg_rows;
+  size_t seg_stride;
 };
 
 // K tiles of a unit's range.  A K tile that no row of the M tile touches holds
@@ -222,22 +231,34 @@ struct Unit {
   const uint32_t* km;        // K-tile mask row of the unit's M tile (NULL: every K tile)
   int m0, n0, nr;
   int ncol;                  // columns of the tile that are stored (a multiple of 4)
-  int rb[2], re[2];
-  float* out[2];
+  int kind;                  // 0, 1: the old part's halves (3-way split); 2: the young blocks, then the
+                             // old part unless split; the adjoint has one range
+  int K0, KY, KT;
 };
+
+// K range r of a unit and its output: each attenuated block of the young part
+// into its own output (Y + s seg_stride), the old part into O (or its halves
+// into O and O2).  Computed from scalars and the kernel parameters, so that no
+// per-unit array lives in local memory.
+template <bool GRAD>
+__device__ __forceinline__ void unit_range(const Params& p, const Unit& u, int r, int& rb, int& re, float*& out) {
+  if (GRAD) { rb = u.K0; re = u.KY; out = p.Y; return; }
+  if (u.kind < 2) {
+    const int KH = u.KY + (u.KT - u.KY + 1) / 2;
+    if (u.kind == 0) { rb = u.KY; re = KH; out = p.O; }
+    else { rb = KH; re = u.KT; out = p.O2; }
+    return;
+  }
+  if (r < p.n_seg) { rb = p.seg_kt[r]; re = p.seg_kt[r + 1]; out = p.Y + r * p.seg_stride; }
+  else { rb = u.KY; re = u.KT; out = p.O; }
+}
 
 template <int BN, bool GRAD>
 __device__ __forceinline__ void unit_ranges(const Params& p, int z, int nz, int K0, int KY, int KT, Unit& u) {
-  u.nr = GRAD ? 1 : 2;
-  u.rb[0] = K0; u.re[0] = KY; u.out[0] = p.Y;
-  u.rb[1] = KY; u.re[1] = KT; u.out[1] = p.O;
-  if (!GRAD && nz == 3) {
-    const int KH = KY + (KT - KY + 1) / 2;
-    u.nr = 1;
-    if (z == 0) { u.rb[0] = KY; u.re[0] = KH; u.out[0] = p.O; }
-    else if (z == 1) { u.rb[0] = KH; u.re[0] = KT; u.out[0] = p.O2; }
-    else { u.rb[0] = 0; u.re[0] = KY; u.out[0] = p.Y; }
-  }
+  u.K0 = K0; u.KY = KY; u.KT = KT;
+  if (GRAD) { u.kind = 2; u.nr = 1; return; }
+  u.kind = nz == 3 ? z : 2;
+  u.nr = u.kind < 2 ? 1 : p.n_seg + (nz == 3 ? 0 : 1);
 }
 
 // KSKIP: the forward with K-tile masks (an instance of its own, so that the
@@ -406,9 +427,16 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         get_unit(j, u);
         const CUtensorMap* amap_hi = &p.a_hi;
         const CUtensorMap* amap_lo = &p.a_lo;
+        int arow = u.m0;   // adjoint: block s of the young columns reads rows s seg_rows + m of its A map
         if (GRAD && u.n0 >= p.n_split) { amap_hi = &p.a2_hi; amap_lo = &p.a2_lo; }
-        for (int r = 0; r < u.nr && ok; ++r)
-          for (int kt = kn(u.km, u.rb[r], u.re[r]); kt < u.re[r]; kt = kn(u.km, kt + 1, u.re[r]), ++it) {
+        else if (GRAD)
+          for (int sg = 1; sg < p.n_seg; ++sg)
+            if (u.n0 >= p.seg_col[sg]) arow = u.m0 + sg * p.seg_rows;
+        for (int r = 0; r < u.nr && ok; ++r) {
+          int rb, re;
+          float* ro_;
+          unit_range<GRAD>(p, u, r, rb, re, ro_);
+          for (int kt = kn(u.km, rb, re); kt < re; kt = kn(u.km, kt + 1, re), ++it) {
             const int s = it % STAGES;
             const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
             if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { atomicOr(p.err, 1); ok = false; break; }
@@ -416,13 +444,14 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
             mbar_expect_tx(fb, C::STAGE_BYTES);
             const uint32_t st = sbase + s * C::STAGE_BYTES;
             const int kc = kt * (ROWB / (PREC == SED_PREC_FP32 ? 4 : (PREC == SED_PREC_FP8 ? 1 : 2)));  // element coordinate along K
-            tma_load_2d(st, amap_hi, fb, kc, u.m0);
+            tma_load_2d(st, amap_hi, fb, kc, arow);
             tma_load_2d(st + C::A_BYTES, &p.b_hi, fb, kc, u.n0);
             if constexpr (C::NOPS == 2) {
-              tma_load_2d(st + C::A_BYTES + C::B_BYTES, amap_lo, fb, kc, u.m0);
+              tma_load_2d(st + C::A_BYTES + C::B_BYTES, amap_lo, fb, kc, arow);
               tma_load_2d(st + 2 * C::A_BYTES + C::B_BYTES, &p.b_lo, fb, kc, u.n0);
             }
           }
+        }
       }
     }
     __syncwarp();
@@ -437,7 +466,9 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         get_unit(j, u);
         const uint32_t ID = idesc(FMT, BM, (uint32_t)u.ncol);   // N = the unit's columns
         for (int r = 0; r < u.nr && ok; ++r) {
-          const int kb = u.rb[r], ke = u.re[r];
+          int kb, ke;
+          float* ro_;
+          unit_range<GRAD>(p, u, r, kb, ke, ro_);
           for (int gs = kb; gs < ke && ok; gs += G) {
             const int ge = gs + G < ke ? gs + G : ke;
             const int k_first = kn(u.km, gs, ge);
@@ -486,7 +517,9 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       get_unit(j, u);
       const int row = u.m0 + q * 32 + lane;
       for (int r = 0; r < u.nr; ++r) {
-        const int kb = u.rb[r], ke = u.re[r];
+        int kb, ke;
+        float* out;
+        unit_range<GRAD>(p, u, r, kb, ke, out);
         float run[BN];
 #pragma unroll
         for (int c = 0; c < BN; ++c) run[c] = 0.f;
@@ -512,7 +545,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
           ++g;
         }
         if (row < p.n) {
-          float4* dst = reinterpret_cast<float4*>(u.out[r] + (size_t)row * p.ld_out + u.n0);
+          float4* dst = reinterpret_cast<float4*>(out + (size_t)row * p.ld_out + u.n0);
 #pragma unroll
           for (int c = 0; c < BN / 4; ++c)
             if (4 * c < u.ncol) dst[c] = make_float4(run[4 * c], run[4 * c + 1], run[4 * c + 2], run[4 * c + 3]);
@@ -603,6 +636,13 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   p.kmask = a.prec == SED_PREC_FP32 && a.kmask_w > 0 && a.kmask_w <= KMASK_WORDS ? a.kmask : nullptr;
   p.kmask_w = a.kmask_w;
   const bool wide = tc_bn_for(a.prec, a.Kpad) == 128;   // same choice as the box of the B map
+  // the attenuated blocks in K tiles of the precision's layout (several blocks
+  // are padded to 128 columns each, so they start on a tile of every layout)
+  const int kcols = a.prec == SED_PREC_FP32 ? 32 : (a.prec == SED_PREC_FP8 ? 128 : 64);
+  p.n_seg = a.n_seg > 0 ? a.n_seg : 1;
+  p.seg_stride = a.seg_stride;
+  for (int sg = 0; sg <= MAX_SEG; ++sg)
+    p.seg_kt[sg] = sg == 0 ? 0 : (sg >= p.n_seg ? a.Ky_pad / kcols : a.seg_k0[sg] / kcols);
   if (a.prec == SED_PREC_FP32) {
     p.ky_tiles = a.Ky_pad / 32;
     p.k_tiles = a.Kpad / 32;
@@ -624,10 +664,11 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
 constexpr int DW_BN = 128;
 
 int tc_encode_dw_maps(void* fn, DwMaps* out, const float* gy_hi, const float* gy_lo, const float* go_hi,
-                      const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int ldg, int ldk, int kpad) {
+                      const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int n_gy, int ldg, int ldk,
+                      int kpad) {
   const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  if (encode_kmajor(fn, &out->gy_hi, (void*)gy_hi, dt, 4, ldg, n, tc::BM) != CUDA_SUCCESS) return 1;
-  if (encode_kmajor(fn, &out->gy_lo, (void*)gy_lo, dt, 4, ldg, n, tc::BM) != CUDA_SUCCESS) return 2;
+  if (encode_kmajor(fn, &out->gy_hi, (void*)gy_hi, dt, 4, ldg, n_gy, tc::BM) != CUDA_SUCCESS) return 1;
+  if (encode_kmajor(fn, &out->gy_lo, (void*)gy_lo, dt, 4, ldg, n_gy, tc::BM) != CUDA_SUCCESS) return 2;
   if (encode_kmajor(fn, &out->go_hi, (void*)go_hi, dt, 4, ldg, n, tc::BM) != CUDA_SUCCESS) return 3;
   if (encode_kmajor(fn, &out->go_lo, (void*)go_lo, dt, 4, ldg, n, tc::BM) != CUDA_SUCCESS) return 4;
   if (encode_kmajor(fn, &out->s_hi, (void*)sk_hi, dt, 4, ldk, kpad, DW_BN) != CUDA_SUCCESS) return 5;
@@ -652,6 +693,9 @@ cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s) {
   p.Y = a.dW; p.O = nullptr; p.err = a.err;
   p.kmask = a.kmask_w > 0 && a.kmask_w <= KMASK_WORDS ? a.kmask : nullptr;
   p.kmask_w = a.kmask_w;
+  p.n_seg = a.n_seg > 0 ? a.n_seg : 1;
+  p.seg_rows = a.seg_rows;
+  for (int sg = 0; sg <= MAX_SEG; ++sg) p.seg_col[sg] = sg < p.n_seg ? a.seg_k0[sg] : a.Ky_pad;
   return tc::launch_cfg<SED_PREC_FP32, DW_BN, 3, 8, true>(p, (p.ny_tiles + no_tiles) * DW_BN, s);
 }
 

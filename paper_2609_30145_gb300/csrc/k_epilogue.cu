@@ -59,7 +59,8 @@ size_t epilogue_smem(const EpiArgs& a) {
 // MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
 // otherwise every row reads the model in the kernel parameters.  LINES: an
 // instance with the emission lines (the one without keeps its code free of them).
-template <bool MULTI, bool LINES>
+// BINS: the age-binned attenuation (one Y per attenuated block).
+template <bool MULTI, bool LINES, bool BINS = false>
 __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_constant__ EpiArgs a) {
   pdl_enter();
   const int r = blockIdx.x;
@@ -110,7 +111,15 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     const float4 c = g.att4[k];
     const float ys = a.lam8 ? rs.y_scale * a.lam8[k] : 1.f;
     const float o = O2r ? Or[k] + O2r[k] : Or[k];
-    const float F = attenuated(md, rs, c, eb, Yr[k] * ys, o * ys, g.neb_tab, k);
+    float F;
+    if constexpr (BINS) {
+      float yv[MAX_SEG];
+#pragma unroll
+      for (int sg = 0; sg < MAX_SEG; ++sg) yv[sg] = sg < md.n_seg ? Yr[sg * a.seg_stride + k] * ys : 0.f;
+      F = attenuated_bins(md, rs, c, eb, yv, o * ys, g.neb_tab, k);
+    } else {
+      F = attenuated(md, rs, c, eb, Yr[k] * ys, o * ys, g.neb_tab, k);
+    }
     if (spec) Fs[k] = F;
     LG[k] = make_float2(c.w, __fdividef(F, c.w * c.w));
   }
@@ -315,12 +324,14 @@ cudaError_t launch_epilogue(const EpiArgs& a_in, cudaStream_t s) {
   EpiArgs a = a_in;
   a.lines_off = (int)epilogue_lines_off(a);
   const size_t smem = epilogue_smem(a);
-  static DynSmemCache set_for[4];
+  static DynSmemCache set_for[5];
   const bool lines = a.row_model ? a.g.n_line > 0 : a.md.use_lines != 0;
-  const int m = (a.row_model ? 1 : 0) + (lines ? 2 : 0);
+  const bool bins = !a.row_model && a.md.n_bin > 0;   // age-binned dust: neither served nor with lines
+  const int m = bins ? 4 : (a.row_model ? 1 : 0) + (lines ? 2 : 0);
   auto k = m == 0 ? k_epilogue<false, false>
          : m == 1 ? k_epilogue<true, false>
-         : m == 2 ? k_epilogue<false, true> : k_epilogue<true, true>;
+         : m == 2 ? k_epilogue<false, true>
+         : m == 3 ? k_epilogue<true, true> : k_epilogue<false, false, true>;
   cudaError_t e = ensure_dyn_smem(k, smem, &set_for[m]);
   if (e != cudaSuccess) return e;
   return launch_pdl(k, dim3(a.n), dim3(EPI_THREADS), smem, s, a);

@@ -471,6 +471,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __shared__ int zb[MAX_SFH];
   __shared__ float zt[MAX_SFH];
   __shared__ float s_red[PREP_THREADS / 32];
+  __shared__ float s_redq[MAX_SEG + 1][PREP_THREADS / 32];   // age-binned dust: Q of each block
   __shared__ float s_red8[PREP_THREADS / 32];
   __shared__ int s_nnz[PREP_THREADS / 32];
   // K tiles the row touches: [Fe/H] nodes that bracket some bin, ages whose
@@ -650,6 +651,26 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     qpart += __shfl_xor_sync(0xffffffffu, qpart, o);
     nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
   }
+  if (md.n_bin > 0) {
+    // age-binned dust: Q of each attenuated block and of the ages outside
+    // every block, from the nebular ages' weights (W_k = w_n Ws[a][m] with the
+    // [a/Fe] bracket weights w_n)
+    float qb[MAX_SEG + 1] = {};
+    for (int j = tid; j < L.n_young * NZ; j += blockDim.x) {
+      const int ag = j / NZ, mm = j - ag * NZ;
+      const int4 ac = L.age_col[ag];
+      const float wv = Ws[ag * NZ + mm];
+      float q = wn0 * wv * __ldg(L.q_s + ac.x + (n0 * NZ + mm) * ac.y);
+      if (n1 != n0) q += wn1 * wv * __ldg(L.q_s + ac.x + (n1 * NZ + mm) * ac.y);
+#pragma unroll
+      for (int jj = 0; jj <= MAX_SEG; ++jj) qb[jj] += ac.z == jj ? q : 0.f;
+    }
+#pragma unroll
+    for (int jj = 0; jj <= MAX_SEG; ++jj) {
+      for (int o = 16; o; o >>= 1) qb[jj] += __shfl_xor_sync(0xffffffffu, qb[jj], o);
+      if (lane == 0) s_redq[jj][warp] = qb[jj];
+    }
+  }
   if (lane == 0) { s_red[warp] = qpart; s_nnz[warp] = nnz; }
   __syncthreads();
   if (a.kmask && tid < a.kmask_w && s_km[tid]) atomicOr(&a.kmask[(size_t)(p >> 7) * a.kmask_w + tid], s_km[tid]);
@@ -774,6 +795,17 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.nnz = 0;
     for (int w = 0; w < PREP_THREADS / 32; ++w) rs.nnz += s_nnz[w];
     *out = rs;
+    if (md.n_bin > 0) {   // age-binned dust (App. dust_attn): each bin's law parameters, Q of each block
+      for (int b = 0; b < md.n_bin; ++b) {
+        out->bin_tau[b] = th[md.offs[SED_KEY_DUST_BINS] + 2 * b];
+        out->bin_slope[b] = th[md.offs[SED_KEY_DUST_BINS] + 2 * b + 1];
+      }
+      for (int j = 0; j <= MAX_SEG; ++j) {
+        float q = 0.f;
+        for (int w = 0; w < PREP_THREADS / 32; ++w) q += s_redq[j][w];
+        out->log2_qs[j] = q > 0.f ? log2f(q) : -INFINITY;
+      }
+    }
   }
 }
 
@@ -869,7 +901,9 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   // dlnL/dWs[a][m] and the [a/Fe] derivative; column k of (n, m, a) in the layout
   const float* dW = a.dW + (size_t)r * L.Kpad;
   const float gqy = (float)a.rgrad[(size_t)r * RGRAD + RG_QY];
-  const int n_old = NA - L.n_young;
+  float gqb[MAX_SEG + 1];   // age-binned dust: dlnL/dQ of each block
+#pragma unroll
+  for (int j = 0; j <= MAX_SEG; ++j) gqb[j] = md.n_bin > 0 ? (float)a.rgrad[(size_t)r * RGRAD + RG_QSEG + j] : 0.f;
   // dW holds values only in the columns the forward's rows touched (the
   // contraction skips the others): the second [a/Fe] node's block only when it
   // carries weight or the [a/Fe] derivative, and only (age, [Fe/H]) pairs with
@@ -878,12 +912,18 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   float gafe = 0.f;
   for (int j = tid; j < NA * NZ; j += blockDim.x) {
     const int ag = j / NZ, mm = j % NZ;
-    const bool young = ag < L.n_young;
+    const bool young = ag < L.n_young;   // a nebular age: Q enters through it
+    const int4 ac = L.age_col[ag];
+    float gq = gqy;
+    if (md.n_bin > 0) {
+#pragma unroll
+      for (int jj = 0; jj <= MAX_SEG; ++jj) gq = ac.z == jj ? gqb[jj] : gq;
+    }
     float gv[2] = {0.f, 0.f};
     const int nn[2] = {n0, n1};
     for (int q = 0; q < (use_n1 ? 2 : 1); ++q) {
-      const int k = young ? (nn[q] * NZ + mm) * L.n_young + ag : L.Ky_pad + (nn[q] * NZ + mm) * n_old + (ag - L.n_young);
-      gv[q] = dW[k] + (young ? gqy * L.q_s[k] : 0.f);
+      const int k = ac.x + (nn[q] * NZ + mm) * ac.y;
+      gv[q] = dW[k] + (young ? gq * L.q_s[k] : 0.f);
     }
     gWs[j] = use_n1 ? gv[0] * wn0 + gv[1] * wn1 : gv[0] * wn0;
     if (use_n1 && Ws[j] != 0.f) gafe += Ws[j] * (gv[0] * dn0 + gv[1] * dn1);
@@ -975,6 +1015,10 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     put(SED_KEY_DIFFUSE_INDEX, (float)rg[RG_DELTA]);
     put(SED_KEY_GAS_LOGZ, md.use_neb ? (float)rg[RG_GAS_LOGZ] : 0.f);
     put(SED_KEY_GAS_LOGU, md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f);
+    for (int b = 0; b < md.n_bin; ++b) {   // age-binned dust: (tau_b, slope_b), never fixed
+      out[md.offs[SED_KEY_DUST_BINS] + 2 * b] = (float)rg[RG_BIN + 2 * b];
+      out[md.offs[SED_KEY_DUST_BINS] + 2 * b + 1] = (float)rg[RG_BIN + 2 * b + 1];
+    }
     if (md.sample_sgal) put(SED_KEY_SIGMA_GAL, (float)rg[RG_SIGMA_GAL]);
     if (md.fesc_geom) put(SED_KEY_FRAC_OBRUN, (float)rg[RG_FOB]);
     if (md.gas_mode == SED_GAS_SIGMA_SAMPLED) put(SED_KEY_SIGMA_GAS, (float)rg[RG_SIGMA_GAS]);

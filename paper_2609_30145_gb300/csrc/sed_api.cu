@@ -107,7 +107,8 @@ double calzetti_kprime(double lum) {  // Calzetti et al. 2000, R_V = 4.05, UV br
   return k > 0.0 ? k : 0.0;
 }
 
-sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, bool grad, sed_status* st);
+sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, bool grad, sed_status* st,
+                       int nseg = 1);
 sed_status ensure_f8_layout(sed_ctx* ctx, Grid* g, Layout* L);
 
 }  // namespace
@@ -520,36 +521,58 @@ sed_status ensure_f8_layout(sed_ctx* ctx, Grid* g, Layout* L) {
   return SED_OK;
 }
 
-// Layout of the grid for a given number of birth-cloud ages and 912 A removal.
-sed_status get_layout(sed_ctx* ctx, Grid* g, int n_young, int neb_cut, Layout** out) {
+// Layout of the grid for a block assignment of the ages and 912 A removal:
+// the attenuated blocks (age a in block blk[a] >= 0), then the ages outside
+// every block (blk[a] = -1), each block ordered (afe n, feh m, age a) with age
+// fastest.  One attenuated block is padded to KT; several are padded to 128
+// columns each, so that every precision's K tiles (32, 64 and 128 columns)
+// and the adjoint's 128-column output tiles lie within one block.  Nebular
+// ages (the first n_neb) carry Q and, with neb_cut, lose their flux below 912 A.
+sed_status get_layout(sed_ctx* ctx, Grid* g, const std::vector<int>& blk, int n_neb, int neb_cut, Layout** out) {
   for (Layout* L : g->layouts)
-    if (L->n_young == n_young && L->neb_cut == neb_cut) { *out = L; return SED_OK; }
+    if (L->blk == blk && L->n_young == n_neb && L->neb_cut == neb_cut) { *out = L; return SED_OK; }
   Layout* L = new Layout();
-  L->n_young = n_young;
+  L->blk = blk;
+  L->n_young = n_neb;
   L->neb_cut = neb_cut;
   const int NA = g->n_age, NZ = g->n_feh, NAF = g->n_afe, NL = g->n_lam;
-  const int no = NA - n_young;
-  L->Ky = NAF * NZ * n_young;
-  L->Ko = NAF * NZ * no;
-  L->Ky_pad = (L->Ky + KT - 1) / KT * KT;
+  int n_seg = 0;
+  for (int a = 0; a < NA; a++) n_seg = std::max(n_seg, blk[a] + 1);
+  n_seg = std::max(n_seg, 1);
+  L->n_seg = n_seg;
+  // ages of each block in age order (block n_seg: outside every bin)
+  std::vector<std::vector<int>> ages(n_seg + 1);
+  for (int a = 0; a < NA; a++) ages[blk[a] >= 0 ? blk[a] : n_seg].push_back(a);
+  const int pad = n_seg > 1 ? 128 : KT;
+  int k0 = 0;
+  for (int s = 0; s < n_seg; s++) {
+    L->seg_k0[s] = k0;
+    k0 += ((int)(NAF * NZ * ages[s].size()) + pad - 1) / pad * pad;
+  }
+  for (int s = n_seg; s <= MAX_SEG; s++) L->seg_k0[s] = k0;
+  L->Ky_pad = k0;
+  L->Ky = n_seg > 1 ? k0 : NAF * NZ * (int)ages[0].size();
+  L->Ko = NAF * NZ * (int)ages[n_seg].size();
   L->Kpad = L->Ky_pad + (L->Ko + KT - 1) / KT * KT;
   const int Kpad = L->Kpad;
   std::vector<int> code(Kpad, -1);
   std::vector<float> qs(Kpad, 0.f);
-  for (int n = 0; n < NAF; n++)
-    for (int m = 0; m < NZ; m++) {
-      for (int a = 0; a < n_young; a++) {
-        int k = (n * NZ + m) * n_young + a;
-        code[k] = (n << 24) | (m << 16) | a;
-        qs[k] = (float)(g->q[((size_t)n * NZ + m) * NA + a] * std::exp2(-g->q_log2));
-      }
-      for (int a = n_young; a < NA; a++) {
-        int k = L->Ky_pad + (n * NZ + m) * no + (a - n_young);
-        code[k] = (n << 24) | (m << 16) | a;
-      }
-    }
+  std::vector<int4> acol(NA);
+  for (int s = 0; s <= n_seg; s++) {
+    const int base = s < n_seg ? L->seg_k0[s] : L->Ky_pad, len = (int)ages[s].size();
+    for (int i = 0; i < len; i++) acol[ages[s][i]] = make_int4(base + i, len, s < n_seg ? s : MAX_SEG, 0);
+    for (int n = 0; n < NAF; n++)
+      for (int m = 0; m < NZ; m++)
+        for (int i = 0; i < len; i++) {
+          const int a = ages[s][i];
+          const int k = base + (n * NZ + m) * len + i;
+          code[k] = (n << 24) | (m << 16) | a;
+          if (a < n_neb) qs[k] = (float)(g->q[((size_t)n * NZ + m) * NA + a] * std::exp2(-g->q_log2));
+        }
+  }
   L->q_log2 = g->q_log2;
   sed_status st = upload(ctx, &L->k_code, code.data(), Kpad, &g->allocs, &g->bytes);
+  if (!st) st = upload(ctx, &L->age_col, acol.data(), NA, &g->allocs, &g->bytes);
   if (!st) st = upload(ctx, &L->q_s, qs.data(), Kpad, &g->allocs, &g->bytes);
   // SSP^T [lam][k], scaled by 2^f_log2, in FP32, TF32 hi/lo and BF16 (the
   // copies the grid keeps; FP8 below when it is asked for at load)
@@ -796,6 +819,40 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
         return fail(ctx, SED_EINVAL, "line catalogue entry %d: datum not finite or sigma <= 0", k);
     }
   }
+  if (d->dust_n_bin < 0 || d->dust_n_bin > MAX_DUST_BIN)
+    return fail(ctx, SED_EINVAL, "dust_n_bin must be in [0, %d]", MAX_DUST_BIN);
+  // age-binned attenuation: the ages with one non-zero row of M form one
+  // attenuated block
+  std::vector<int> blk(g->n_age, -1);
+  std::vector<std::vector<double>> seg_rows;
+  if (d->dust_n_bin > 0) {
+    const int nb = d->dust_n_bin;
+    if (!d->dust_bin_M || !d->dust_bin_law) return fail(ctx, SED_EINVAL, "dust_bin_M / dust_bin_law is NULL");
+    if (d->use_lines || d->fesc_geometry)
+      return fail(ctx, SED_EUNSUPPORTED, "age-binned dust is not combined with emission lines or an escape geometry");
+    for (int b = 0; b < nb; b++)
+      if (d->dust_bin_law[b] != SED_DUST_POWER_LAW && d->dust_bin_law[b] != SED_DUST_KC13)
+        return fail(ctx, SED_EINVAL, "dust_bin_law[%d] must be SED_DUST_POWER_LAW or SED_DUST_KC13", b);
+    for (int a = 0; a < g->n_age; a++) {
+      const double* row = d->dust_bin_M + (size_t)a * nb;
+      double sum = 0.0;
+      for (int b = 0; b < nb; b++) {
+        if (!(row[b] >= 0.0 && row[b] <= 1.0)) return fail(ctx, SED_EINVAL, "dust_bin_M[%d][%d] not in [0, 1]", a, b);
+        sum += row[b];
+      }
+      if (sum == 0.0) continue;
+      if (std::fabs(sum - 1.0) > 1e-9) return fail(ctx, SED_EINVAL, "row %d of dust_bin_M sums to %g (not 0 or 1)", a, sum);
+      std::vector<double> r(row, row + nb);
+      int s = 0;
+      while (s < (int)seg_rows.size() && seg_rows[s] != r) s++;
+      if (s == (int)seg_rows.size()) {
+        if (s == MAX_SEG)
+          return fail(ctx, SED_EUNSUPPORTED, "dust_bin_M has more than %d distinct non-zero rows", MAX_SEG);
+        seg_rows.push_back(r);
+      }
+      blk[a] = s;
+    }
+  }
 
   Model* M = new Model();
   M->grid = d->grid;
@@ -834,6 +891,14 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   dv.sgal_fix_kms = (float)d->sigma_gal_kms;
   dv.offs[SED_KEY_SIGMA_GAS] = o;
   o += dv.gas_mode == SED_GAS_SIGMA_SAMPLED ? 1 : 0;
+  // age-binned attenuation (App. dust_attn): (tau_b, slope_b) per bin
+  dv.n_bin = d->dust_n_bin;
+  dv.n_seg = d->dust_n_bin > 0 ? std::max((int)seg_rows.size(), 1) : 1;
+  for (int b = 0; b < dv.n_bin; b++) dv.bin_law[b] = d->dust_bin_law[b];
+  for (int s = 0; s < (int)seg_rows.size(); s++)
+    for (int b = 0; b < dv.n_bin; b++) dv.seg_M[s][b] = (float)seg_rows[s][b];
+  dv.offs[SED_KEY_DUST_BINS] = o;
+  o += 2 * d->dust_n_bin;
   // fixed keys (Sec. 4 parameter dictionary): a fixed one-column key leaves the
   // caller's rows; the kernels read it past the caller's columns
   {
@@ -889,7 +954,9 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   // nebular emission absorbs all of it; with an escape geometry the copy keeps
   // it and the epilogues split it off (nodes below n_lyc)
   while (dv.n_lyc < g->n_lam && g->lam[dv.n_lyc] < LYMAN_AA) dv.n_lyc++;
-  sed_status st = get_layout(ctx, g, n_young, d->use_nebular && !d->fesc_geometry ? 1 : 0, &M->L);
+  if (d->dust_n_bin == 0)
+    for (int a = 0; a < g->n_age; a++) blk[a] = a < n_young ? 0 : -1;
+  sed_status st = get_layout(ctx, g, blk, n_young, d->use_nebular && !d->fesc_geometry ? 1 : 0, &M->L);
   if (!st) {
     std::vector<double> tab;
     cosmo_table(d->H0, d->Om0, d->zf, COSMO_TAB, &tab);
@@ -1159,12 +1226,14 @@ sed_status sed_destroy_model(sed_ctx* ctx, sed_model_id id) {
 // ---------------------------------------------------------------------------
 namespace {
 
-sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, bool grad, sed_status* st) {
+sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, bool grad, sed_status* st,
+                       int nseg) {
   *st = SED_OK;
   std::lock_guard<std::mutex> lk(ctx->mu);
   Workspace*& w = ctx->ws[stream];
   if (!w) w = new Workspace();
-  const bool need = rows > w->cap_rows || (size_t)kpad > w->cap_k || (size_t)ldn > w->cap_n || (grad && !w->dW);
+  const bool need = rows > w->cap_rows || (size_t)kpad > w->cap_k || (size_t)ldn > w->cap_n || (grad && !w->dW) ||
+                    nseg > w->cap_seg;
   if (!need) return w;
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
@@ -1175,6 +1244,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
     if (p) cudaFree(p);
   budget_release(ctx, w->bytes);
   const bool had_grad = w->dW != nullptr;
+  const int seg = std::max(nseg, w->cap_seg);
   if (w->host_exec) cudaGraphExecDestroy(w->host_exec);   // it holds the old buffers
   *w = Workspace();
   const int R = std::max(rows, 1);
@@ -1182,15 +1252,16 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   w->cap_rows = R;
   w->cap_k = K;
   w->cap_n = N;
+  w->cap_seg = std::max(seg, 1);
   w->ldn = (int)N;
   std::vector<void*>* no = nullptr;
   sed_status s = SED_OK;
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
   AL(perm, R * 4); AL(tile_win, 2 * ((R + 127) / 128) * 4); AL(kmask, ((R + 127) / 128) * KMASK_WORDS * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
-  AL(Y, R * N * 4); AL(O, R * N * 4); AL(O2, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
+  AL(Y, R * N * 4 * w->cap_seg); AL(O, R * N * 4); AL(O2, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
   AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
   if (grad || had_grad) {
-    AL(G_hi, R * N * 4); AL(G_lo, R * N * 4); AL(GO_hi, R * N * 4); AL(GO_lo, R * N * 4);
+    AL(G_hi, R * N * 4 * w->cap_seg); AL(G_lo, R * N * 4 * w->cap_seg); AL(GO_hi, R * N * 4); AL(GO_lo, R * N * 4);
     AL(dW, R * K * 4); AL(rgrad, R * RGRAD * 8);
   }
 #undef AL
@@ -1285,6 +1356,8 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
     ContractArgs ca{};
     ca.n = n; ca.n_lam = g->n_lam; ca.ldn = w->ldn; ca.Ky_pad = L->Ky_pad; ca.Kpad = L->Kpad;
     ca.W = w->W; ca.sspT = L->sspT_f32; ca.Y = w->Y; ca.O = w->O; ca.rs = w->rs;
+    ca.n_seg = L->n_seg; ca.seg_stride = (size_t)w->cap_rows * w->ldn;
+    for (int sg = 0; sg <= MAX_SEG; ++sg) ca.seg_k0[sg] = L->seg_k0[sg];
     CK(launch_contract_simt(ca, s));
     return prof_mark(ctx, w, 2, s);
   }
@@ -1311,6 +1384,8 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   ta.maps = maps; ta.Y = w->Y; ta.O = w->O; ta.O2 = w->O2; ta.err = w->err; ta.rs = w->rs;
   ta.tile_win = w->tile_win;
   ta.kmask = pa.kmask; ta.kmask_w = pa.kmask_w;
+  ta.n_seg = L->n_seg; ta.seg_stride = (size_t)w->cap_rows * w->ldn;
+  for (int sg = 0; sg <= MAX_SEG; ++sg) ta.seg_k0[sg] = L->seg_k0[sg];
   CK(launch_contract_tc(ta, s));
   return prof_mark(ctx, w, 2, s);
 }
@@ -1330,7 +1405,7 @@ sed_status sed_forward(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   if (n == 0) return SED_OK;
   DevGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
+  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st, M->L->n_seg);
   if (!w) return st;
   st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
   if (st) return st;
@@ -1338,6 +1413,7 @@ sed_status sed_forward(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
   ea.O2 = precision == SED_PREC_FP32 ? w->O2 : nullptr;   // the 3xTF32 contraction's split old part
   ea.md = M->dv; ea.g = M->g->dv;
+  ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   ea.phot_out = M->dv.n_filt ? phot_out : nullptr;
   ea.spec_out = M->dv.n_pix ? spec_out : nullptr;
@@ -1357,7 +1433,7 @@ sed_status sed_line_fluxes(sed_ctx* ctx, sed_model_id id, const float* theta, in
   if (n == 0) return SED_OK;
   DevGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
+  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st, M->L->n_seg);
   if (!w) return st;
   st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
   if (st) return st;
@@ -1365,6 +1441,7 @@ sed_status sed_line_fluxes(sed_ctx* ctx, sed_model_id id, const float* theta, in
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
   ea.O2 = precision == SED_PREC_FP32 ? w->O2 : nullptr;
   ea.md = M->dv; ea.g = M->g->dv;
+  ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   ea.lines_out = flux_out;
   ea.err = w->err;
@@ -1382,7 +1459,7 @@ sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   if (n == 0) return SED_OK;
   DevGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
+  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st, M->L->n_seg);
   if (!w) return st;
   st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
   if (st) return st;
@@ -1390,6 +1467,7 @@ sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
   ea.O2 = precision == SED_PREC_FP32 ? w->O2 : nullptr;   // the 3xTF32 contraction's split old part
   ea.md = M->dv; ea.g = M->g->dv;
+  ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.lnl = lnl_out; ea.status = row_status; ea.err = w->err;
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   CK(launch_epilogue(ea, s));
@@ -1407,7 +1485,7 @@ sed_status sed_loglike_host(sed_ctx* ctx, sed_model_id id, const float* theta, i
   if (n == 0) return SED_OK;
   DevGuard dg(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st);
+  Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st, M->L->n_seg);
   if (!w) return st;
   // page-locked, device-mapped host buffers are used in place: the kernels
   // read theta and write lnL / status over the host link (NVLink-C2C on a
@@ -1491,7 +1569,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
     st = ensure_grad_layout(ctx, g, L, ldn);
   }
   if (st) return st;
-  Workspace* w = get_ws(ctx, stream, n, L->Kpad, ldn, true, &st);
+  Workspace* w = get_ws(ctx, stream, n, L->Kpad, ldn, true, &st, L->n_seg);
   if (!w) return st;
   st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
   if (st) return st;
@@ -1503,6 +1581,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   eb.md = M->dv; eb.g = g->dv; eb.split = f32 ? 1 : 0;
   eb.gy_hi = w->G_hi; eb.gy_lo = w->G_lo; eb.go_hi = w->GO_hi; eb.go_lo = w->GO_lo;
   eb.rgrad = w->rgrad; eb.lnl = lnl_out; eb.status = row_status; eb.err = w->err;
+  eb.seg_stride = (size_t)w->cap_rows * w->ldn;
   size_t smem = 0;
   cudaError_t e = launch_epilogue_bwd(eb, &smem, s);
   if (e == cudaErrorInvalidConfiguration)
@@ -1511,8 +1590,10 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   if (sed_status ps = prof_mark(ctx, w, 4, s)) return ps;
   if (f32) {
     if (!w->dw_maps_valid || w->dw_maps_for != (const void*)L || w->dw_maps_n != n || w->dw_maps_g != w->G_hi) {
+      // dlnL/dY of the attenuated blocks: slab s at rows s cap_rows + m of one map
+      const int n_gy = (L->n_seg - 1) * w->cap_rows + n;
       int ee = tc_encode_dw_maps(ctx->encode_fn, &w->dw_maps, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo, L->sspK_hi,
-                                 L->sspK_lo, n, w->ldn, L->ldn, L->Kpad);
+                                 L->sspK_lo, n, n_gy, w->ldn, L->ldn, L->Kpad);
       if (ee) return fail(ctx, SED_ECUDA, "cuTensorMapEncodeTiled failed (adjoint operand %d)", ee);
       w->dw_maps_valid = true;
       w->dw_maps_for = L;
@@ -1526,11 +1607,15 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
     // select dW's output tiles
     da.kmask = w->kmask_w_call > 0 ? w->kmask : nullptr;
     da.kmask_w = w->kmask_w_call;
+    da.n_seg = L->n_seg; da.seg_rows = w->cap_rows;
+    for (int sg = 0; sg <= MAX_SEG; ++sg) da.seg_k0[sg] = L->seg_k0[sg];
     CK(launch_dw_tc(da, s));
   } else {
     DwSimtArgs da{};
     da.n = n; da.ldg = w->ldn; da.ldk = L->ldn; da.Ky_pad = L->Ky_pad; da.Kpad = L->Kpad;
     da.gy = w->G_hi; da.go = w->GO_hi; da.sspK = L->sspK_f32; da.dW = w->dW; da.rs = w->rs;
+    da.n_seg = L->n_seg; da.seg_stride = (size_t)w->cap_rows * w->ldn;
+    for (int sg = 0; sg <= MAX_SEG; ++sg) da.seg_k0[sg] = L->seg_k0[sg];
     CK(launch_dw_simt(da, s));
   }
   if (sed_status ps = prof_mark(ctx, w, 5, s)) return ps;

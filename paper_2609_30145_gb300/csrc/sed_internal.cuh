@@ -34,6 +34,8 @@ constexpr int COSMO_COLS = 8;    // value / derivative pairs of D_C, t_univ, ln(
 // KMASK_WORDS words per 128-row tile; grids with more K tiles run unmasked
 constexpr int KMASK_WORDS = 8;
 constexpr int MAX_LINES = 128;   // emission lines of a nebular grid
+constexpr int MAX_DUST_BIN = SED_MAX_DUST_BIN;   // age-binned attenuation laws
+constexpr int MAX_SEG = SED_MAX_DUST_SEG;        // attenuated K blocks (runs of ages with one non-zero row of M)
 
 // Physical constants (cgs unless noted).
 constexpr double LSUN = 3.839e33;              // erg/s (Sec. 2.6)
@@ -76,6 +78,11 @@ struct RowScal {
   float fl[2][4];   // noise floor {s, f_calib, f_data, j} of photometry [0] and spectrum [1]
   float fob;        // runaway fraction f_ob (0 without an escape geometry)
   float sgas;       // gas velocity dispersion of the emission lines, km/s
+  // age-binned attenuation (App. dust_attn): each bin's optical depth and slope,
+  // and log2 of Q (device units) of each attenuated block, then of the block
+  // outside every bin (-inf when zero)
+  float bin_tau[MAX_DUST_BIN], bin_slope[MAX_DUST_BIN];
+  float log2_qs[MAX_SEG + 1];
 };
 
 // Cosmology and observer-frame scalars of one row (computed at the start of k_prep).
@@ -122,6 +129,10 @@ struct LayoutDev {
   const int* k_code;       // [Kpad]
   int Ky_pad8, Kpad8;      // FP8 layout: each block padded to 128 (one 128-byte K tile)
   const float* col8;       // [Kpad] 2^-e_k, the FP8 column scale folded into W (0 for empty columns)
+  int n_seg;               // attenuated blocks in [0, Ky_pad): block s = columns [seg_k0[s], seg_k0[s+1])
+  int seg_k0[MAX_SEG + 1];
+  const int4* age_col;     // [n_age] column of (afe n, feh m, age a) = x + (n n_feh + m) y; z = a's block
+                           // (MAX_SEG: outside every attenuated block)
 };
 
 struct ModelDev {
@@ -196,6 +207,12 @@ struct ModelDev {
   const double* lcat_isig;
   const double* lcat_nlog;
   const uint8_t* lcat_ul;    // 1: an upper limit (Eq. app_line_chi2_UL); NULL: none
+  // age-binned attenuation (App. dust_attn, Eq. app_tau_bin): n_bin laws
+  // (SED_DUST_*), n_seg attenuated K blocks; block s sees tau_s = sum_b
+  // seg_M[s][b] kappa_b.  n_bin = 0: the birth-cloud power law
+  int n_bin, n_seg;
+  int bin_law[MAX_DUST_BIN];
+  float seg_M[MAX_SEG][MAX_DUST_BIN];
 };
 
 // Value of column `col` of a parameter row in the kernels' layout: a caller's
@@ -208,8 +225,14 @@ __host__ __device__ __forceinline__ float theta_col(const ModelDev& md, const fl
 // Device copy of a grid in one K order: [young block | old block], each block
 // ordered (afe n, feh m, age a) with age fastest, each block padded to KT.
 struct Layout {
-  int n_young = 0;    // ages <= birth-cloud edge
-  int neb_cut = 0;    // 1: stellar flux below 912 A removed for young ages
+  int n_young = 0;    // nebular ages (<= birth-cloud edge): Q and the 912 A cut
+  int neb_cut = 0;    // 1: stellar flux below 912 A removed for nebular ages
+  // the attenuated blocks: age a is in block blk[a] (0 .. n_seg - 1) or, for
+  // -1, in the block after them (no age-dependent attenuation); without
+  // age-binned dust there is one block, the birth-cloud ages
+  std::vector<int> blk;
+  int n_seg = 1;
+  int seg_k0[MAX_SEG + 1] = {};
   int Ky = 0, Ko = 0, Ky_pad = 0, Kpad = 0;
   float* sspT_f32 = nullptr;         // [n_lam][Kpad] scaled flux, exact FP32
   float* sspT_hi = nullptr;          // [n_lam][Kpad] TF32-rounded high part
@@ -228,12 +251,17 @@ struct Layout {
   float* col8 = nullptr;
   float* lam8 = nullptr;             // [n_lam] 2^-f_l, the FP8 wavelength scale undone in the epilogue
   float* q_s = nullptr;              // [Kpad] scaled Q for young k, 0 elsewhere
+  int4* age_col = nullptr;           // [n_age] see LayoutDev
   int* k_code = nullptr;             // [Kpad] packed (n<<24 | m<<16 | a), -1 for padding
   std::vector<int> code_h;           // host copy of k_code
   double q_log2 = 0.0;               // Q_dev = Q * 2^-q_log2
   bool have_tmaps = false;
   CUtensorMap tm_hi, tm_lo, tm_bf16;
-  LayoutDev dv() const { return LayoutDev{n_young, neb_cut, Ky, Ko, Ky_pad, Kpad, q_s, k_code, Ky_pad8, Kpad8, col8}; }
+  LayoutDev dv() const {
+    LayoutDev d{n_young, neb_cut, Ky, Ko, Ky_pad, Kpad, q_s, k_code, Ky_pad8, Kpad8, col8, n_seg, {}, age_col};
+    for (int s = 0; s <= MAX_SEG; ++s) d.seg_k0[s] = seg_k0[s];
+    return d;
+  }
 };
 
 struct Grid {
@@ -287,13 +315,17 @@ enum {
   RG_FLOOR,       // 8 slots: dlnL/dlog10 of the noise-floor terms, photometry then spectrum
   RG_FOB = RG_FLOOR + 8,   // dlnL/df_ob
   RG_SIGMA_GAS,            // dlnL/dsigma_gas (km/s) of a sampled gas dispersion
-  RGRAD = 24
+  RG_BIN,                  // 2 MAX_DUST_BIN slots: dlnL/dtau_b, dlnL/dslope_b of each attenuation bin
+  RG_QSEG = RG_BIN + 2 * MAX_DUST_BIN,   // MAX_SEG + 1 slots: dlnL/dQ of each attenuated block, then
+                                        // of the block outside every bin
+  RGRAD = 40
 };
 
 // Per-stream scratch.
 struct Workspace {
   int cap_rows = 0;
   size_t cap_k = 0, cap_n = 0;
+  int cap_seg = 1;               // attenuated blocks Y and G hold (slabs of [cap_rows][ldn])
   float* W = nullptr;            // [rows][Kpad]  exact FP32 weights (also the TF32 hi part source)
   float* W_hi = nullptr;         // [rows][Kpad]
   float* W_lo = nullptr;
@@ -303,7 +335,7 @@ struct Workspace {
   int kmask_w_call = 0;          // words per tile of the current call's masks (0: the call has none)
   __nv_bfloat16* W_bf16 = nullptr;
   uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
-  float* Y = nullptr;            // [rows][ldn]
+  float* Y = nullptr;            // [cap_seg][cap_rows][ldn]: one slab per attenuated block
   float* O = nullptr;
   float* O2 = nullptr;           // [rows][ldn] second partial sum of the old part
   RowScal* rs = nullptr;
@@ -512,6 +544,9 @@ struct ContractArgs {
   const float* W;      // [n][Kpad]
   const float* sspT;   // [n_lam][Kpad]
   float* Y; float* O;  // [n][ldn]
+  int n_seg;           // attenuated blocks: columns [seg_k0[s], seg_k0[s+1]) into Y + s seg_stride
+  int seg_k0[MAX_SEG + 1];
+  size_t seg_stride;
 };
 cudaError_t launch_contract_simt(const ContractArgs& a, cudaStream_t s);
 
@@ -525,6 +560,9 @@ struct TcArgs {
                        // O + O2 is the old sum (other precisions ignore O2)
   const int* tile_win; // non-NULL (and <= 64 M tiles): persistent schedule over the computed tiles
   const uint32_t* kmask; int kmask_w;   // K tiles some row of each 128-row tile touches (NULL: all)
+  int n_seg;           // attenuated blocks of the young part (0 or 1: one), block s of the main layout's
+  int seg_k0[MAX_SEG + 1];   // columns [seg_k0[s], seg_k0[s+1]) into Y + s seg_stride
+  size_t seg_stride;
 };
 // encodes the four operand maps; returns 0 on success
 int tc_encode_maps(void* encode_fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo,
@@ -536,7 +574,8 @@ int tc_bn_for(int prec, int kpad);
 // Adjoint contraction dW = [G_Y SSP_young^T | G_O SSP_old^T] (3xTF32 on tcgen05).
 // G rows have stride ldg; SSP rows [Kpad][ldk] (ldk <= ldg is the reduction length).
 int tc_encode_dw_maps(void* encode_fn, DwMaps* out, const float* gy_hi, const float* gy_lo, const float* go_hi,
-                      const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int ldg, int ldk, int kpad);
+                      const float* go_lo, const float* sk_hi, const float* sk_lo, int n, int n_gy, int ldg, int ldk,
+                      int kpad);
 struct DwArgs {
   const RowScal* rs;   // per-row node windows bound the reduction over lambda
   const uint32_t* kmask; int kmask_w;   // 32-column K tiles some row of each 128-row tile touches (NULL: all);
@@ -544,6 +583,8 @@ struct DwArgs {
   int n, ldk, Ky_pad, Kpad;
   const DwMaps* maps;
   float* dW; int* err;
+  int n_seg, seg_rows;       // attenuated blocks: dW columns [seg_k0[s], seg_k0[s+1]) read dlnL/dY of block s
+  int seg_k0[MAX_SEG + 1];   // (rows s seg_rows + m of the dlnL/dY map)
 };
 cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s);
 
@@ -562,6 +603,7 @@ struct EpiArgs {
   const int* err;      // device error word of the contraction (row status SED_ROW_DEVICE_TIMEOUT)
   const float* lam8;   // FP8 path: [n_lam] 2^-f_l multiplying Y and O; NULL otherwise
   int lines_off;       // set by launch_epilogue: float offset of the emission lines' shared arrays
+  size_t seg_stride;   // age-binned dust: Y of attenuated block s at Y + s seg_stride
 };
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 
@@ -578,12 +620,16 @@ struct EpiBwdArgs {
   double* lnl; uint32_t* status;
   const int* err;
   int lines_off;        // set by launch_epilogue_bwd: byte offset of the emission lines' shared arrays
+  size_t seg_stride;    // age-binned dust: Y and dlnL/dY of attenuated block s at + s seg_stride
 };
 cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s);
 
 struct DwSimtArgs {
   const RowScal* rs;
   int n, ldg, ldk, Ky_pad, Kpad;
+  int n_seg;                          // attenuated blocks: columns [seg_k0[s], seg_k0[s+1]) read gy + s seg_stride
+  int seg_k0[MAX_SEG + 1];
+  size_t seg_stride;
   const float* gy; const float* go;   // [n][ldg]
   const float* sspK;                  // [Kpad][ldk], ldk <= ldg: the reduction length
   float* dW;                          // [n][Kpad]
