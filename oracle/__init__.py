@@ -64,7 +64,7 @@ class _Model(C.Structure):
                 ("sigma_gas_max_kms", C.c_double), ("n_lcat", C.c_int), ("lcat_start", C.c_void_p),
                 ("lcat_line", C.c_void_p), ("lcat_d", C.c_void_p), ("lcat_sigma", C.c_void_p),
                 ("lcat_mask", C.c_void_p), ("lcat_upper", C.c_void_p), ("dust_n_bin", C.c_int),
-                ("dust_bin_M", C.c_void_p), ("dust_bin_law", C.c_void_p)]
+                ("dust_bin_M", C.c_void_p), ("dust_bin_law", C.c_void_p), ("use_igm", C.c_int)]
 
 
 def _load():
@@ -88,6 +88,7 @@ def _load():
         lib.orc_grad_fd.argtypes = [P, P, P, C.c_int, C.c_int, C.c_double, P, C.c_int]
         lib.orc_grad.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, C.c_int]
         lib.orc_n_param.argtypes = [P]
+        lib.orc_igm_tau.argtypes = [P, C.c_int, C.c_double, P]
         lib.orc_n_param.restype = C.c_int
         _lib = lib
     return _lib
@@ -139,6 +140,7 @@ class Oracle:
     lcat: tuple | None = None           # line catalogue (Sec. 3.3): (blends: list of lists of grid-line
                                         # indices, d, sigma, mask or None, upper or None), erg/s/cm^2
     sfh_scheme: int = 0                 # 0 step (N_T bin masses), 1 linear (N_T + 1 edge SFRs; App. B)
+    use_igm: int = 0                    # 1: Madau (1995) IGM transmission, scaled by the last column (igm_factor)
     dust_bins: tuple | None = None      # age-binned attenuation (App. "dust_attn"): (M [n_age][n_bin], laws
                                         # [n_bin], 0 power law / 1 KC13); adds 2 n_bin columns at the row's end
     floor_phot: int = 0                 # noise-floor terms of each arm (App. sys_floor): FLOOR_* bits
@@ -243,6 +245,7 @@ class Oracle:
             m.dust_n_bin = M.shape[1]
             m.dust_bin_M = _p(k(M))
             m.dust_bin_law = _p(k(np.asarray(laws), np.int32))
+        m.use_igm = int(self.use_igm)
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
@@ -335,9 +338,9 @@ class Oracle:
 
     def grad(self, theta, nthreads=0):
         """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])."""
-        if self.use_lines or self.lcat is not None or self.dust_bins is not None:
-            raise NotImplementedError("the analytic gradient does not cover emission lines or age-binned dust: "
-                                      "use grad_fd")
+        if self.use_lines or self.lcat is not None or self.dust_bins is not None or self.use_igm:
+            raise NotImplementedError("the analytic gradient does not cover emission lines, age-binned dust or the "
+                                      "IGM: use grad_fd")
         th = np.ascontiguousarray(theta, dtype=np.float64)
         n, ld = th.shape
         out = np.zeros((n, ld))
@@ -384,6 +387,16 @@ GAS_SIGMA_TIED, GAS_SIGMA_FIXED, GAS_SIGMA_SAMPLED = 0, 1, 2
 FLOOR_NAMES = ("log_err_scale", "log_f_calib", "log_f_data", "log_jitter")
 
 
+def igm_tau(lam_rest, z):
+    """Madau (1995) IGM optical depth (factor 1) at the rest wavelengths lam_rest
+    (Angstrom) of a source at redshift z."""
+    lib = _load()
+    lam = np.ascontiguousarray(lam_rest, dtype=np.float64)
+    out = np.zeros(lam.size)
+    lib.orc_igm_tau(_p(lam), lam.size, float(z), _p(out))
+    return out
+
+
 def floor_keys(floor_phot=0, floor_spec=0):
     """Column names of the noise-floor terms that are on, in the row's order."""
     return tuple(f"{FLOOR_NAMES[k]}_{arm}" for arm, bits in (("phot", floor_phot), ("spec", floor_spec))
@@ -391,14 +404,15 @@ def floor_keys(floor_phot=0, floor_spec=0):
 
 
 def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, sfh_scheme=0, fesc_geometry=0,
-               sample_sigma_gas=0, dust_n_bin=0):
+               sample_sigma_gas=0, dust_n_bin=0, use_igm=0):
     """Parameter rows in the oracle's layout: sfh[N_T] (bin masses; N_T + 1 edge
     SFRs with the linear scheme), logzsol[N_T or 1], then
     afe, logmass, zred, tau_pow, alpha_pow, diffuse_tau_kc, diffuse_dust_index,
     gas_logz, gas_logu, sigma_gal when the model samples it, and the log10 of
     each noise-floor term that is on (photometry, then spectrum), and frac_obrun
     with an escape geometry, sigma_gas when the model samples the gas dispersion, and
-    with age-binned dust the 2 n_bin columns of d["dust_bins"] (tau_b, slope_b of each bin)."""
+    with age-binned dust the 2 n_bin columns of d["dust_bins"] (tau_b, slope_b of each bin), and
+    with the IGM its scaling igm_factor."""
     nz = n_sfh if zmode == 0 else 1
     n = d["sfh"].shape[0]
     cols = [np.asarray(d["sfh"], dtype=np.float64).reshape(n, n_sfh + (1 if sfh_scheme == 1 else 0)),
@@ -410,4 +424,6 @@ def pack_theta(d, n_sfh, zmode, sample_sigma_gal=0, floor_phot=0, floor_spec=0, 
         cols.append(np.asarray(d[k], dtype=np.float64).reshape(n, 1))
     if dust_n_bin:
         cols.append(np.asarray(d["dust_bins"], dtype=np.float64).reshape(n, 2 * dust_n_bin))
+    if use_igm:
+        cols.append(np.asarray(d["igm_factor"], dtype=np.float64).reshape(n, 1))
     return np.ascontiguousarray(np.concatenate(cols, axis=1))

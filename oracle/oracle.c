@@ -128,7 +128,7 @@ static int sfh_cols(const orc_model *md) { return md->n_sfh + (md->sfh_scheme ==
 int orc_n_param(const orc_model *md) {
   return sfh_cols(md) + (md->zmode == 0 ? md->n_sfh : 1) + 9 + (md->sample_sigma_gal ? 1 : 0) +
          n_floor(md->floor_phot) + n_floor(md->floor_spec) + (md->fesc_geometry ? 1 : 0) +
-         (md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED ? 1 : 0) + 2 * md->dust_n_bin;
+         (md->gas_sigma_mode == ORC_GAS_SIGMA_SAMPLED ? 1 : 0) + 2 * md->dust_n_bin + (md->use_igm ? 1 : 0);
 }
 
 /* parameter row decoding (layout: sfh[N_T], logzsol[N_T or 1], afe, logmass,
@@ -142,6 +142,7 @@ typedef struct {
   double fob;        /* runaway fraction f_ob (0 without an escape geometry) */
   double sigma_gas;  /* gas dispersion of the emission lines, km/s */
   double bin_tau[ORC_MAX_DUST_BIN], bin_slope[ORC_MAX_DUST_BIN];   /* age-binned laws' parameters */
+  double igm_f;      /* scaling of the IGM optical depth (1 without a column) */
 } orc_theta;
 
 static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
@@ -172,6 +173,36 @@ static void decode_theta(const orc_model *md, const double *th, orc_theta *o) {
     o->bin_tau[b] = th[col++];
     o->bin_slope[b] = th[col++];
   }
+  o->igm_f = md->use_igm ? th[col++] : 1.0;
+}
+
+/* Madau (1995) mean IGM optical depth seen at the observed wavelength
+ * lam_obs = lam_rest (1 + z) from a source at z (Sec. 2.6 names the
+ * prescription): line blanketing by the Lyman series, A_j (lam_obs/lam_j)^3.46
+ * for each line j with lam_j < lam_obs < lam_j (1 + z) (Ly-alpha to Ly-delta,
+ * A_j = 3.6e-3, 1.7e-3, 1.1846e-3, 9.316e-4), plus photoelectric absorption by
+ * Lyman-limit systems for lam_obs < lam_L (1 + z), lam_L = 911.75 A, with
+ * x_c = lam_obs / lam_L (not below 1) and x_e = 1 + z:
+ *   0.25 x_c^3 (x_e^0.46 - x_c^0.46) + 9.4 x_c^1.5 (x_e^0.18 - x_c^0.18)
+ *   - 0.7 x_c^3 (x_c^-1.32 - x_e^-1.32) - 0.023 (x_e^1.68 - x_c^1.68). */
+static double igm_madau_tau(double lam_rest, double z) {
+  static const double lj[4] = {1215.67, 1025.72, 972.537, 949.743};
+  static const double aj[4] = {3.6e-3, 1.7e-3, 1.1846e-3, 9.316e-4};
+  const double lo = lam_rest * (1.0 + z);
+  double tau = 0.0;
+  for (int j = 0; j < 4; j++)
+    if (lam_rest < lj[j] && lo > lj[j]) tau += aj[j] * pow(lo / lj[j], 3.46);
+  if (lam_rest < 911.75) {
+    double xc = lo / 911.75, xe = 1.0 + z;
+    if (xc < 1.0) xc = 1.0;
+    tau += 0.25 * xc * xc * xc * (pow(xe, 0.46) - pow(xc, 0.46)) + 9.4 * pow(xc, 1.5) * (pow(xe, 0.18) - pow(xc, 0.18)) -
+           0.7 * xc * xc * xc * (pow(xc, -1.32) - pow(xe, -1.32)) - 0.023 * (pow(xe, 1.68) - pow(xc, 1.68));
+  }
+  return tau;
+}
+
+void orc_igm_tau(const double *lam_rest, int n, double z, double *tau) {
+  for (int k = 0; k < n; k++) tau[k] = igm_madau_tau(lam_rest[k], z);
 }
 
 /* Eq. "app_noise_floor": the effective variance of a datum with formal error
@@ -910,10 +941,15 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
     double dl = cosm[0] > 10.0 * O_PC_CM ? cosm[0] : 10.0 * O_PC_CM;
     double scale = pow(10.0, t.logmass) * O_LSUN * (1.0 + t.z) / (4.0 * M_PI * dl * dl);
     for (int k = 0; k < NL; k++) fnu[k] = scale * F[k];
-    /* the grid's emission lines, App. "line_proj" */
+    /* the IGM transmission at each node's observed wavelength (Sec. 2.6) */
+    if (md->use_igm)
+      for (int k = 0; k < NL; k++) fnu[k] *= exp(-t.igm_f * igm_madau_tau(g->lam[k], t.z));
+    /* the grid's emission lines, App. "line_proj" (through the same IGM transmission) */
     const int nline = (md->use_lines && md->use_nebular && g->neb_line_tab) ? g->neb_n_line : 0;
     double *Fl = (double *)calloc(nline > 0 ? nline : 1, sizeof(double));
     if (nline) line_fluxes(g, md, &t, qy, pow(10.0, t.logmass) * O_LSUN / (4.0 * M_PI * dl * dl), Fl);
+    if (nline && md->use_igm)
+      for (int l = 0; l < nline; l++) Fl[l] *= exp(-t.igm_f * igm_madau_tau(g->neb_line_lam[l], t.z));
     /* projections + likelihood, Eq. "total_lnlike" */
     double *ph = (double *)malloc((md->n_filt > 0 ? md->n_filt : 1) * sizeof(double));
     double *sp = (double *)malloc((md->n_pix > 0 ? md->n_pix : 1) * sizeof(double));
@@ -1029,6 +1065,8 @@ void orc_line_fluxes(const orc_grid *g, const orc_model *md, const double *theta
     decode_theta(md, th, &t);
     double dl = scal[0] > 10.0 * O_PC_CM ? scal[0] : 10.0 * O_PC_CM;
     line_fluxes(g, md, &t, scal[3], pow(10.0, t.logmass) * O_LSUN / (4.0 * M_PI * dl * dl), o);
+    if (md->use_igm)
+      for (int l = 0; l < nl; l++) o[l] *= exp(-t.igm_f * igm_madau_tau(g->neb_line_lam[l], t.z));
   }
 }
 

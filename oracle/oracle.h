@@ -93,8 +93,13 @@ typedef struct {
                                   (optical depth at 5500 A, slope) after every other key of the row */
   const double *dust_bin_M;    /* [n_age][n_bin] age-to-bin matrix, rows summing to 1 or all zero */
   const int *dust_bin_law;     /* [n_bin] 0 power law, 1 Kriek & Conroy 2013 */
+  int use_igm;                 /* 1: the Madau (1995) IGM transmission (Sec. 2.6), scaled by the row's last
+                                  column igm_factor: T = exp(-igm_factor tau_IGM(lam_obs, z)) */
 } orc_model;
 #define ORC_MAX_DUST_BIN 4
+/* Madau (1995) effective IGM optical depth at the rest wavelengths lam_rest[n] (Angstrom) of a source
+ * at redshift z (factor 1) */
+void orc_igm_tau(const double *lam_rest, int n, double z, double *tau);
 /* The gas velocity dispersion of the emission lines (Sec. 2.7): tied to the
  * stellar sigma_gal (the paper's default), a fixed value, or a parameter
  * column (the last one of the row). */
