@@ -116,7 +116,8 @@ enum {
                                  gas_sigma_mode = SED_GAS_SIGMA_SAMPLED) */
   SED_KEY_DUST_BINS = 22,     /* age-binned attenuation: 2 dust_n_bin columns, each bin's optical depth at
                                  5500 A then its slope (power-law index or KC13 delta) */
-  SED_NKEYS = 23
+  SED_KEY_IGM_FACTOR = 23,    /* scaling of the IGM optical depth (a column only with use_igm) */
+  SED_NKEYS = 24
 };
 
 typedef struct sed_ctx sed_ctx;
@@ -307,7 +308,17 @@ typedef struct {
   int dust_n_bin;
   const double *dust_bin_M;
   const int *dust_bin_law;
+  /* IGM transmission (Sec. 2.6): SED_IGM_MADAU multiplies the rest-frame model
+   * at each node, and each emission line, by exp(-f tau(lam_obs, z)), tau the
+   * Madau (1995) mean optical depth (Lyman-series blanketing, Ly-alpha to
+   * Ly-delta, and Lyman-limit photoelectric absorption), f the column
+   * SED_KEY_IGM_FACTOR (fix it at 1 for the plain prescription).  Applied to
+   * the nodes before the spectral kernel. */
+  int use_igm;
 } sed_model_desc;
+
+#define SED_IGM_NONE 0
+#define SED_IGM_MADAU 1
 
 #define SED_MAX_DUST_BIN 4
 #define SED_MAX_DUST_SEG 4

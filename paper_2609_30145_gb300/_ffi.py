@@ -22,7 +22,7 @@ KEYS = ("sfh", "logzsol", "afe", "logmass", "zred", "tau_pow", "alpha_pow", "dif
         "diffuse_dust_index", "gas_logz", "gas_logu", "sigma_gal",
         "log_err_scale_phot", "log_f_calib_phot", "log_f_data_phot", "log_jitter_phot",
         "log_err_scale_spec", "log_f_calib_spec", "log_f_data_spec", "log_jitter_spec", "frac_obrun",
-        "sigma_gas", "dust_bins")
+        "sigma_gas", "dust_bins", "igm_factor")
 FLOOR_ERR_SCALE, FLOOR_F_CALIB, FLOOR_F_DATA, FLOOR_JITTER = 1, 2, 4, 8
 SFH_STEP, SFH_LINEAR = 0, 1
 FESC_NONE, FESC_RUNAWAY_BC, FESC_PICKET = 0, 1, 2
@@ -60,7 +60,7 @@ class ModelDesc(C.Structure):
                 ("use_lines", C.c_int), ("gas_sigma_mode", C.c_int), ("sigma_gas_kms", C.c_double),
                 ("sigma_gas_max_kms", C.c_double), ("n_lcat", C.c_int), ("lcat_len", P), ("lcat_line", P),
                 ("lcat_d", P), ("lcat_sigma", P), ("lcat_mask", P), ("lcat_upper", P), ("dust_n_bin", C.c_int),
-                ("dust_bin_M", P), ("dust_bin_law", P)]
+                ("dust_bin_M", P), ("dust_bin_law", P), ("use_igm", C.c_int)]
 
 
 class StageStats(C.Structure):

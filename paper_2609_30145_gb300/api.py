@@ -124,7 +124,7 @@ class Context:
                      calib_sigma=None, noise_floor_phot=0, noise_floor_spec=0, sfh_scheme=0,
                      phot_upper=None, fesc_geometry=0, fixed=None, calib_mode=0, use_lines=0,
                      gas_sigma_mode=0, sigma_gas_kms=300.0, sigma_gas_max_kms=1000.0, lcat=None,
-                     dust_bins=None) -> "Model":
+                     dust_bins=None, use_igm=0) -> "Model":
         """fixed: optional {key name: value} of keys fixed for every row (no
         column in the parameter rows, no gradient); key names as in _ffi.KEYS.
         lcat: optional line catalogue (blends: list of lists of grid-line
@@ -163,6 +163,7 @@ class Context:
             keep.append(cs)
             d.calib_n, d.calib_sigma = cs.size, _ptr(cs)
         d.calib_mode = int(calib_mode)
+        d.use_igm = int(use_igm)
         if dust_bins is not None:
             bm, bl = dust_bins
             bm = np.ascontiguousarray(bm, dtype=np.float64)

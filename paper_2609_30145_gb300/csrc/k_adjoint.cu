@@ -34,6 +34,7 @@
 #include "atten.cuh"
 #include "calib.cuh"
 #include "floor.cuh"
+#include "igm.cuh"
 #include "lines.cuh"
 #include "locate.cuh"
 #include "sed_internal.cuh"
@@ -43,8 +44,8 @@ namespace sed {
 constexpr int EB_THREADS = 256;
 constexpr int EB_WARPS = EB_THREADS / 32;
 constexpr int EB_MAX_BANDS = 128;
-constexpr int EB_NRED = 18;   // per-warp partial sums: 16 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
-constexpr int EB_NREDF = 16;
+constexpr int EB_NRED = 19;   // per-warp partial sums: 17 FP32 sums, then lnL and d lnL/d ln(mass) in FP64
+constexpr int EB_NREDF = 17;
 constexpr int EB_NREDB = 2 * MAX_DUST_BIN + MAX_SEG + 1;   // age-binned dust: d/d(tau_b, slope_b), d/dQ of each block
 
 __device__ __forceinline__ float tf32_rna_dev(float x) {
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   const float* Or = a.O + ro;
   const float* O2r = a.O2 ? a.O2 + ro : nullptr;
   const float eb_kc = 0.85f - 1.9f * rs.delta;
+  const float opz = 1.f / rs.inv1pz;
 
   // ---- forward: attenuated spectrum in the window (the forward epilogue's
   //      arithmetic); phi holds the window's wavelengths until the photometric
@@ -183,6 +185,11 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       Fs[k] = attenuated_bins(md, rs, g.att4[k], eb_kc, yv, O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
     } else {
       Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
+    }
+    if (md.use_igm && g.lam_f[k] < IGM_LYA) {   // the IGM transmission (the forward epilogue's)
+      float tau, dtau;
+      igm_madau(g.att4[k].w, opz, tau, dtau);
+      Fs[k] *= __expf(-rs.igm_f * tau);
     }
     phi[k] = g.lam_f[k];
   }
@@ -585,6 +592,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   // ---- dust and nebular: dlnL/dY, dlnL/dO and the parameter sums over lambda
   float g_tbc = 0.f, g_abc = 0.f, g_td = 0.f, g_dl = 0.f, g_qy = 0.f, g_lu = 0.f, g_lz = 0.f, g_fob = 0.f;
   float g_sgas = 0.f, g_lm = 0.f;   // lines: d/dsigma_gas (sampled), d/dln F summed over lines (mass)
+  float g_igm = 0.f;                // d/digm_factor (the IGM's redshift derivative joins gz_spec)
 
   // ---- emission lines, thread per line.  F_l = Q fac_l B_l with Q = Q_young
   //      (device units), fac_l the attenuation factor and B_l = 10^(lg_l)
@@ -607,7 +615,12 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       su = fmaf(rs.neb_dwu[q], tv, su);
       sz = fmaf(rs.neb_dwz[q], tv, sz);
     }
-    const float B = ex2_approx(3.3219280948873623f * lg) * rs.s_spec * rs.inv1pz;
+    float B = ex2_approx(3.3219280948873623f * lg) * rs.s_spec * rs.inv1pz;
+    float ltau = 0.f, ldtau = 0.f;   // the IGM at the line (B carries its transmission)
+    if (md.use_igm && c.w < IGM_LYA) {
+      igm_madau(c.w, opz, ltau, ldtau);
+      B *= __expf(-rs.igm_f * ltau);
+    }
     float G = 0.f, Gx = 0.f, Gs = 0.f, Gzp = 0.f;
     if (md.n_pix > 0 && is > 0.f) {
       const float sw = 5.0001f / is;
@@ -674,7 +687,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     // redshift: the flux factor s_spec/(1+z), the profile's centre on the
     // pixels, its width through sigma_inst(lam_obs), the bands' response
     const float qf = Q * fac;
-    float gzl = gF * (rs.dlns_dz - rs.inv1pz) + qf * (Gx * rs.inv1pz + Gzp);
+    float gzl = gF * (rs.dlns_dz - rs.inv1pz - rs.igm_f * ldtau) + qf * (Gx * rs.inv1pz + Gzp);
+    g_igm = fmaf(-gF, ltau, g_igm);
     if (md.n_pix > 0 && is > 0.f) {
       float si, dsi;
       line_sigma_inst(md, xlp.x, lam_obs, si, dsi);
@@ -708,8 +722,19 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         lg = neb_log10(rs, g.neb_tab, k);
         nbu = ex2_approx(3.3219280948873623f * lg);
       }
-      const float gF = phi[k];
-      const float gtd = -gF * Fs[k];
+      // with the IGM, F = T F0: dlnL/dF0 = T dlnL/dF, and ln T = -f tau moves with f and z
+      float T = 1.f, F0 = Fs[k];
+      if (md.use_igm && c.w < IGM_LYA) {
+        float tau, dtau;
+        igm_madau(c.w, opz, tau, dtau);
+        T = __expf(-rs.igm_f * tau);
+        const float gl = phi[k] * Fs[k];   // dlnL / d ln T
+        g_igm = fmaf(-gl, tau, g_igm);
+        gz_spec = fmaf(-gl * rs.igm_f, dtau, gz_spec);
+        F0 = T > 0.f ? Fs[k] / T : 0.f;
+      }
+      const float gF = phi[k] * T;
+      const float gtd = -gF * F0;
       const float go = gF * ed;
       put_g(a, a.go_hi, a.go_lo, ro + k, go);
       float shp[MAX_DUST_BIN], dsh[MAX_DUST_BIN], kap[MAX_DUST_BIN], gk[MAX_DUST_BIN];
@@ -788,10 +813,21 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       lg = neb_log10(rs, g.neb_tab, k);
       nb = ex2_approx(rs.log2_qy + 3.3219280948873623f * lg);
     }
-    const float gF = phi[k];
+    // with the IGM, F = T F0: dlnL/dF0 = T dlnL/dF, and ln T = -f tau moves with f and z
+    float T = 1.f, F0 = Fs[k];
+    if (md.use_igm && c.w < IGM_LYA) {
+      float tau, dtau;
+      igm_madau(c.w, opz, tau, dtau);
+      T = __expf(-rs.igm_f * tau);
+      const float gl = phi[k] * Fs[k];   // dlnL / d ln T
+      g_igm = fmaf(-gl, tau, g_igm);
+      gz_spec = fmaf(-gl * rs.igm_f, dtau, gz_spec);
+      F0 = T > 0.f ? Fs[k] / T : 0.f;
+    }
+    const float gF = phi[k] * T;
     // dF/dY, dF/dtau_BC (as gtbc), dF/dneb and dF/df of the node (atten.cuh's F)
     float gy, gtbc, gnb;
-    float gtd = -gF * Fs[k];
+    float gtd = -gF * F0;
     if (md.fesc_geom == SED_FESC_NONE) {
       gy = gF * ed * eb;
       gtbc = -gy * (y + nb);
@@ -804,7 +840,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         gtbc = -gF * se * b;
         gnb = gF * se;
         g_fob += gF * (y - ed * eb * b);
-        gtd = -gF * (Fs[k] - f * y);   // the escaping light crosses no screen
+        gtd = -gF * (F0 - f * y);   // the escaping light crosses no screen
       } else {
         const float T = (1.f - f) * eb + f, av = c * y + (1.f - f) * nb;
         gy = gF * ed * (T * c + f * (1.f - c));
@@ -839,7 +875,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   //      the warp in FP32, lnL and d lnL/d ln(mass) in FP64; across the warps
   //      in FP64, one column per lane of warp 0
   float vf[EB_NREDF] = {g_tbc, g_abc, g_td, g_dl, g_lz, g_lu, gz_gather + gz_spec, g_qy, g_sgal,
-                        gfs[0], gfs[1], gfs[2], gfs[3], g_fob, g_sgas, g_lm};
+                        gfs[0], gfs[1], gfs[2], gfs[3], g_fob, g_sgas, g_lm, g_igm};
 #pragma unroll
   for (int q = 0; q < EB_NREDF; ++q) {
 #pragma unroll
@@ -927,6 +963,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       rg[RG_SIGMA_GAL] = s[8];
       rg[RG_FOB] = s[13];
       rg[RG_SIGMA_GAS] = s[14];
+      rg[RG_IGM] = s[16];
       for (int k = 0; k < 4; ++k) {
         rg[RG_FLOOR + k] = gfp[k];
         rg[RG_FLOOR + 4 + k] = s[9 + k];

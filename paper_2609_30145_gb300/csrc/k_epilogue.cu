@@ -30,6 +30,7 @@
 #include "atten.cuh"
 #include "calib.cuh"
 #include "floor.cuh"
+#include "igm.cuh"
 #include "lines.cuh"
 
 namespace sed {
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   const float* Or = a.O + (size_t)r * a.ldn;
   const float* O2r = a.O2 ? a.O2 + (size_t)r * a.ldn : nullptr;
   const float eb = 0.85f - 1.9f * rs.delta;
+  const float opz = 1.f / rs.inv1pz;
   const bool spec = md.n_pix > 0;
   const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);   // nodes [k_lo, k_hi] are the only ones read below
   float2* LG = reinterpret_cast<float2*>(smem4) - k_lo;               // {rest-frame lambda, F / lam^2}
@@ -119,6 +121,11 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
       F = attenuated_bins(md, rs, c, eb, yv, o * ys, g.neb_tab, k);
     } else {
       F = attenuated(md, rs, c, eb, Yr[k] * ys, o * ys, g.neb_tab, k);
+    }
+    if (md.use_igm && c.w < IGM_LYA) {   // the IGM transmission at the node's observed wavelength
+      float tau, dtau;
+      igm_madau(c.w, opz, tau, dtau);
+      F *= __expf(-rs.igm_f * tau);
     }
     if (spec) Fs[k] = F;
     LG[k] = make_float2(c.w, __fdividef(F, c.w * c.w));

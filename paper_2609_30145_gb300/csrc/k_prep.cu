@@ -785,6 +785,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     rs.sgas = md.gas_mode == SED_GAS_SIGMA_SAMPLED ? th[md.offs[SED_KEY_SIGMA_GAS]]
             : md.gas_mode == SED_GAS_SIGMA_FIXED ? md.sgas_fix_kms
             : (md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] : md.sgal_fix_kms);
+    rs.igm_f = md.use_igm ? th[md.offs[SED_KEY_IGM_FACTOR]] : 0.f;
     rs.k_lo = win_lo;
     rs.k_hi = win_hi;
     if (a.tile_win) {   // union of the windows of this row's 128-row tile
@@ -1015,6 +1016,7 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     put(SED_KEY_DIFFUSE_INDEX, (float)rg[RG_DELTA]);
     put(SED_KEY_GAS_LOGZ, md.use_neb ? (float)rg[RG_GAS_LOGZ] : 0.f);
     put(SED_KEY_GAS_LOGU, md.use_neb ? (float)rg[RG_GAS_LOGU] : 0.f);
+    put(SED_KEY_IGM_FACTOR, md.use_igm ? (float)rg[RG_IGM] : 0.f);
     for (int b = 0; b < md.n_bin; ++b) {   // age-binned dust: (tau_b, slope_b), never fixed
       out[md.offs[SED_KEY_DUST_BINS] + 2 * b] = (float)rg[RG_BIN + 2 * b];
       out[md.offs[SED_KEY_DUST_BINS] + 2 * b + 1] = (float)rg[RG_BIN + 2 * b + 1];
@@ -1065,9 +1067,9 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   ka.p = p;
   if (!p.row_model && !z_col) ka.p.perm = nullptr;
   // Ws [n_age][n_feh], the FP8 row scratch, the row's parameters (n_param <= ld
-  // and n_param <= 2 MAX_SFH + SED_NKEYS for every model)
+  // and n_param <= 2 MAX_SFH + SED_NKEYS + 2 MAX_DUST_BIN for every model)
   // (+ the fixed keys' values past the caller's columns)
-  const size_t npar = (size_t)std::min(p.ld, 2 * MAX_SFH + SED_NKEYS) + SED_NKEYS;
+  const size_t npar = (size_t)std::min(p.ld, 2 * MAX_SFH + SED_NKEYS + 2 * MAX_DUST_BIN) + SED_NKEYS;
   const size_t smem = ((size_t)p.g.n_age * p.g.n_feh + (p.W_f8 ? (size_t)p.L.Kpad : 0) + npar) * sizeof(float);
   static DynSmemCache set_for[2];
   e = p.row_model ? ensure_dyn_smem(k_prep<true>, smem, &set_for[1]) : ensure_dyn_smem(k_prep<false>, smem, &set_for[0]);

@@ -4,6 +4,7 @@
 // same FP32 arithmetic.
 #pragma once
 #include "atten.cuh"
+#include "igm.cuh"
 #include "sed_internal.cuh"
 
 namespace sed {
@@ -48,7 +49,12 @@ __device__ __forceinline__ void line_setup(const ModelDev& md, const GridDev& g,
   const float td = rs.tau_d * dust_shape(md, c, eb, __expf(rs.delta * c.x));
   const float ed = __expf(-td), ebc = __expf(-tbc), f = rs.fob;
   const float fac = md.fesc_geom == SED_FESC_PICKET ? ed * (1.f - f) * ebc : ed * ((1.f - f) * ebc + f) * (1.f - f);
-  const float F = L * fac * rs.s_spec * rs.inv1pz;
+  float F = L * fac * rs.s_spec * rs.inv1pz;
+  if (md.use_igm && c.w < IGM_LYA) {   // the IGM transmission at the line's observed wavelength
+    float tau, dtau;
+    igm_madau(c.w, 1.f / rs.inv1pz, tau, dtau);
+    F *= __expf(-rs.igm_f * tau);
+  }
   F_s[l] = F;
   // observed ln(lambda) = ln(lam_l) + ln(1+z): the FP32 pairs summed by two-sum
   const float2 lr = g.line_ln2[l];

@@ -819,6 +819,8 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
         return fail(ctx, SED_EINVAL, "line catalogue entry %d: datum not finite or sigma <= 0", k);
     }
   }
+  if (d->use_igm != SED_IGM_NONE && d->use_igm != SED_IGM_MADAU)
+    return fail(ctx, SED_EINVAL, "use_igm must be SED_IGM_NONE or SED_IGM_MADAU");
   if (d->dust_n_bin < 0 || d->dust_n_bin > MAX_DUST_BIN)
     return fail(ctx, SED_EINVAL, "dust_n_bin must be in [0, %d]", MAX_DUST_BIN);
   // age-binned attenuation: the ages with one non-zero row of M form one
@@ -899,6 +901,10 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
     for (int b = 0; b < dv.n_bin; b++) dv.seg_M[s][b] = (float)seg_rows[s][b];
   dv.offs[SED_KEY_DUST_BINS] = o;
   o += 2 * d->dust_n_bin;
+  // the IGM transmission's scaling (Sec. 2.6)
+  dv.use_igm = d->use_igm;
+  dv.offs[SED_KEY_IGM_FACTOR] = o;
+  o += d->use_igm ? 1 : 0;
   // fixed keys (Sec. 4 parameter dictionary): a fixed one-column key leaves the
   // caller's rows; the kernels read it past the caller's columns
   {

@@ -83,6 +83,7 @@ struct RowScal {
   // outside every bin (-inf when zero)
   float bin_tau[MAX_DUST_BIN], bin_slope[MAX_DUST_BIN];
   float log2_qs[MAX_SEG + 1];
+  float igm_f;      // scaling of the IGM optical depth (with use_igm)
 };
 
 // Cosmology and observer-frame scalars of one row (computed at the start of k_prep).
@@ -213,6 +214,7 @@ struct ModelDev {
   int n_bin, n_seg;
   int bin_law[MAX_DUST_BIN];
   float seg_M[MAX_SEG][MAX_DUST_BIN];
+  int use_igm;             // SED_IGM_MADAU: the Madau (1995) IGM transmission (Sec. 2.6)
 };
 
 // Value of column `col` of a parameter row in the kernels' layout: a caller's
@@ -318,6 +320,7 @@ enum {
   RG_BIN,                  // 2 MAX_DUST_BIN slots: dlnL/dtau_b, dlnL/dslope_b of each attenuation bin
   RG_QSEG = RG_BIN + 2 * MAX_DUST_BIN,   // MAX_SEG + 1 slots: dlnL/dQ of each attenuated block, then
                                         // of the block outside every bin
+  RG_IGM = RG_QSEG + MAX_SEG + 1,       // dlnL/digm_factor
   RGRAD = 40
 };
 

@@ -105,7 +105,8 @@ def gpu_model_for(ctx, orc, w: synth.Workload, with_spec_data=True, fixed=None):
                   sigma_gal_kms=orc.sigma_gal_kms, z_ref=orc.z_ref, calib_sigma=orc.calib_sigma,
                   calib_mode=orc.calib_mode)
     kw.update(use_lines=orc.use_lines, gas_sigma_mode=orc.gas_sigma_mode, sigma_gas_kms=orc.sigma_gas_kms,
-              sigma_gas_max_kms=orc.sigma_gas_max_kms, lcat=orc.lcat, dust_bins=orc.dust_bins)
+              sigma_gas_max_kms=orc.sigma_gas_max_kms, lcat=orc.lcat, dust_bins=orc.dust_bins,
+              use_igm=orc.use_igm)
     return ctx.create_model(gid, w.n_sfh, w.zf, w.zmode, fixed=fixed, **kw)
 
 

@@ -47,6 +47,7 @@ def test_enum_values_match_header():
                       ("SED_KEY_FRAC_OBRUN", _ffi.KEYS.index("frac_obrun")),
                       ("SED_KEY_SIGMA_GAS", _ffi.KEYS.index("sigma_gas")),
                       ("SED_KEY_DUST_BINS", _ffi.KEYS.index("dust_bins")),
+                      ("SED_KEY_IGM_FACTOR", _ffi.KEYS.index("igm_factor")),
                       ("SED_GAS_SIGMA_SAMPLED", _ffi.GAS_SIGMA_SAMPLED),
                       ("SED_FESC_RUNAWAY_BC", _ffi.FESC_RUNAWAY_BC), ("SED_FESC_PICKET", _ffi.FESC_PICKET),
                       ("SED_FLOOR_ERR_SCALE", _ffi.FLOOR_ERR_SCALE), ("SED_FLOOR_F_CALIB", _ffi.FLOOR_F_CALIB),
@@ -87,20 +88,22 @@ def test_layout_packing_matches_oracle_layout():
                     d["sigma_gas"] = rng.uniform(50.0, 400.0, 5)
                     nb = 2 * scheme + fe % 2   # 0..3 age-binned dust laws
                     d["dust_bins"] = rng.uniform(-1.0, 1.5, (5, 2 * nb))
+                    igm = (fp + scheme) % 2
+                    d["igm_factor"] = rng.uniform(0.5, 1.5, 5)
                     m = Model.__new__(Model)
                     nz = 7 if zmode == 0 else 1
                     # the library's layout: the SFH key has N_T (+1 for the linear
                     # scheme) columns; sigma_gal, each floor term, f_ob and sigma_gas one only
                     # when on; two per age-binned dust law
                     widths = [7 + scheme, nz] + [1] * 9 + [sgal] + [(fp >> k) & 1 for k in range(4)] + \
-                             [(fs >> k) & 1 for k in range(4)] + [1 if fe else 0] + [sgas] + [2 * nb]
+                             [(fs >> k) & 1 for k in range(4)] + [1 if fe else 0] + [sgas] + [2 * nb] + [igm]
                     offs = list(np.cumsum([0] + widths[:-1]))
                     m.n_param = int(sum(widths))
                     m.offsets = dict(zip(_ffi.KEYS, offs))
                     a = m.pack(d, dtype=np.float64)
                     b = oracle.pack_theta(d, 7, zmode, sample_sigma_gal=sgal, floor_phot=fp, floor_spec=fs,
                                           sfh_scheme=scheme, fesc_geometry=fe, sample_sigma_gas=sgas,
-                                          dust_n_bin=nb)
+                                          dust_n_bin=nb, use_igm=igm)
                     np.testing.assert_array_equal(a, b)
 
 
