@@ -43,7 +43,8 @@ class _Grid(C.Structure):
                 ("lam", C.c_void_p), ("flux", C.c_void_p), ("sigma_lib_kms", C.c_void_p),
                 ("neb_n_logu", C.c_int), ("neb_n_logz", C.c_int),
                 ("neb_logu", C.c_void_p), ("neb_logz", C.c_void_p), ("neb_tab", C.c_void_p),
-                ("neb_n_line", C.c_int), ("neb_line_lam", C.c_void_p), ("neb_line_tab", C.c_void_p)]
+                ("neb_n_line", C.c_int), ("neb_line_lam", C.c_void_p), ("neb_line_tab", C.c_void_p),
+                ("neb_n_age", C.c_int), ("neb_log_age", C.c_void_p)]
 
 
 class _Model(C.Structure):
@@ -170,7 +171,13 @@ class Oracle:
         self._g.flux = _p(k(g.flux))
         self._g.sigma_lib_kms = _p(k(getattr(g, "sigma_lib_kms", None)))
         if g.neb_tab is not None:
-            self._g.neb_n_logu, self._g.neb_n_logz = g.neb_tab.shape[:2]
+            na = getattr(g, "neb_log_age", None)
+            if na is not None:   # nebular age axis: neb_tab [n_age][n_logu][n_logz][n_lam]
+                self._g.neb_n_age = len(na)
+                self._g.neb_log_age = _p(k(na))
+                self._g.neb_n_logu, self._g.neb_n_logz = g.neb_tab.shape[1:3]
+            else:
+                self._g.neb_n_logu, self._g.neb_n_logz = g.neb_tab.shape[:2]
             self._g.neb_logu = _p(k(g.neb_logu))
             self._g.neb_logz = _p(k(g.neb_logz))
             self._g.neb_tab = _p(k(g.neb_tab))
@@ -246,6 +253,15 @@ class Oracle:
             m.dust_bin_M = _p(k(M))
             m.dust_bin_law = _p(k(np.asarray(laws), np.int32))
         m.use_igm = int(self.use_igm)
+        na = getattr(self.grid, "neb_log_age", None)
+        if na is not None and self.use_nebular:
+            la = np.asarray(self.grid.log_age_yr)
+            inside = (la >= na[0]) & (la <= na[-1])
+            if np.any(la[inside] > self.bc_edge_log_age_yr):
+                raise ValueError("nebular age axis: the cube's ages reach past the birth-cloud edge")
+            if self.use_lines or self.fesc_geometry or self.dust_bins is not None:
+                raise ValueError("nebular age axis: not combined with emission lines, an escape geometry or "
+                                 "age-binned dust")
         self._m = m
 
     def set_data(self, phot_d=None, phot_sigma=None, spec_d=None, spec_sigma=None):
@@ -338,7 +354,8 @@ class Oracle:
 
     def grad(self, theta, nthreads=0):
         """Analytic FP64 gradient of lnL: dict(lnl [n], grad [n][n_param], status [n])."""
-        if self.use_lines or self.lcat is not None or self.dust_bins is not None or self.use_igm:
+        if (self.use_lines or self.lcat is not None or self.dust_bins is not None or self.use_igm
+                or getattr(self.grid, "neb_log_age", None) is not None):
             raise NotImplementedError("the analytic gradient does not cover emission lines, age-binned dust or the "
                                       "IGM: use grad_fd")
         th = np.ascontiguousarray(theta, dtype=np.float64)

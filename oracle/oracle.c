@@ -803,6 +803,16 @@ static void line_fluxes(const orc_grid *g, const orc_model *md, const orc_theta 
   }
 }
 
+/* Whether SSP age node a powers the nebular emission (App. C): a birth-cloud
+ * age, and with a nebular age axis one inside the cube's tabulated ages. */
+static int nebular_age(const orc_grid *g, const orc_model *md, int a) {
+  if (!md->use_nebular || !g->neb_tab) return 0;
+  const double la = g->log_age_yr[a];
+  if (la > md->bc_edge_log_age_yr) return 0;
+  if (g->neb_n_age <= 0) return 1;
+  return la >= g->neb_log_age[0] && la <= g->neb_log_age[g->neb_n_age - 1];
+}
+
 /* One parameter row through the whole forward model and likelihood. */
 int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double *W_out,
             double *Y_out, double *O_out, double *F_out, double *fnu_out, double *phot,
@@ -829,6 +839,7 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
   if (!st) {
     orc_q(g, Q);
     double qy = 0.0;
+    double *qa = (double *)calloc(NA, sizeof(double));   /* Q-weighted weight of each nebular age */
     if (md->dust_n_bin > 0) {
       /* App. "dust_attn": per age node a the optical depth tau_a = sum_b M_ab
        * kappa_b(lam; theta_b) (Eq. "app_tau_bin"), applied to the node's
@@ -891,16 +902,46 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
           if (w == 0.0) continue; /* exact zero contributes nothing */
           const double *f = g->flux + s * NL;
           int young = g->log_age_yr[a] <= md->bc_edge_log_age_yr;
-          int neb = md->use_nebular && g->neb_tab && young;
+          int neb = nebular_age(g, md, a);
           double *acc = young ? Y : O;
           for (int k = 0; k < NL; k++) {
             if (neb && g->lam[k] < O_LYMAN) YL[k] += w * f[k];
             else acc[k] += w * f[k];
           }
-          if (young) qy += w * Q[s];
+          if (g->neb_n_age > 0 ? neb : young) qy += w * Q[s];
+          if (neb) qa[a] += w * Q[s];
         }
-    /* nebular continuum, App. C: Q_young * 10^(bilinear log10 template) */
-    if (md->use_nebular && g->neb_tab) {
+    /* nebular continuum, App. C: Q_young * 10^(bilinear log10 template); with
+     * an age axis, each nebular SSP age a contributes Q_a 10^(the cube
+     * interpolated trilinearly: bilinear in (log U, log Z_gas) on the two
+     * planes of ionising-source age bracketing the node's age, linear in log
+     * age between them) */
+    if (md->use_nebular && g->neb_tab && g->neb_n_age > 0) {
+      int u0, u1, z0, z1;
+      double wu0, wu1, wz0, wz1;
+      bracket(g->neb_logu, g->neb_n_logu, t.gas_logu, &u0, &wu0, &u1, &wu1);
+      bracket(g->neb_logz, g->neb_n_logz, t.gas_logz, &z0, &wz0, &z1, &wz1);
+      const size_t plane = (size_t)g->neb_n_logu * g->neb_n_logz * NL;
+      for (int a = 0; a < NA; a++) {
+        if (qa[a] == 0.0) continue;
+        int i0, i1;
+        double wa0, wa1;
+        bracket(g->neb_log_age, g->neb_n_age, g->log_age_yr[a], &i0, &wa0, &i1, &wa1);
+        for (int k = 0; k < NL; k++) {
+          double lg = 0.0;
+          for (int e = 0; e < 2; e++) {
+            const double we = e ? wa1 : wa0;
+            if (we == 0.0) continue;
+            const double *b = g->neb_tab + (size_t)(e ? i1 : i0) * plane;
+            lg += we * (wu0 * wz0 * b[((size_t)u0 * g->neb_n_logz + z0) * NL + k] +
+                        wu0 * wz1 * b[((size_t)u0 * g->neb_n_logz + z1) * NL + k] +
+                        wu1 * wz0 * b[((size_t)u1 * g->neb_n_logz + z0) * NL + k] +
+                        wu1 * wz1 * b[((size_t)u1 * g->neb_n_logz + z1) * NL + k]);
+          }
+          N[k] += qa[a] * pow(10.0, lg);
+        }
+      }
+    } else if (md->use_nebular && g->neb_tab) {
       int u0, u1, z0, z1;
       double wu0, wu1, wz0, wz1;
       bracket(g->neb_logu, g->neb_n_logu, t.gas_logu, &u0, &wu0, &u1, &wu1);
@@ -937,6 +978,7 @@ int orc_row(const orc_grid *g, const orc_model *md, const double *theta, double 
       Y[k] += N[k];   /* Y_out: young stellar flux (ionising continuum removed) plus nebular */
     }
     }
+    free(qa);
     /* observer frame, Sec. 2.6 */
     double dl = cosm[0] > 10.0 * O_PC_CM ? cosm[0] : 10.0 * O_PC_CM;
     double scale = pow(10.0, t.logmass) * O_LSUN * (1.0 + t.z) / (4.0 * M_PI * dl * dl);

@@ -41,6 +41,9 @@ typedef struct {
   int neb_n_line;              /* emission lines of the nebular grid (App. C), 0: none */
   const double *neb_line_lam;  /* [n_line] rest-frame wavelength, Angstrom */
   const double *neb_line_tab;  /* [n_logu][n_logz][n_line] log10(L_line/Q), Lsun / (photon/s) */
+  int neb_n_age;               /* nebular age axis (App. C), 0: none; with one, neb_tab is
+                                  [n_age][n_logu][n_logz][n_lam] on the ionising-source ages neb_log_age */
+  const double *neb_log_age;   /* [neb_n_age] log10 age / yr, increasing */
 } orc_grid;
 
 typedef struct {

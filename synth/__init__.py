@@ -49,6 +49,7 @@ class Grid:
     neb_tab: np.ndarray | None = None   # [n_logu][n_logz][n_lam] log10(L_nu/Q), (Lsun/Hz)/(photon/s)
     line_lam: np.ndarray | None = None  # [n_line] rest-frame wavelengths of the emission-line cube, Angstrom
     line_tab: np.ndarray | None = None  # [n_logu][n_logz][n_line] log10(L_line/Q), Lsun/(photon/s)
+    neb_log_age: np.ndarray | None = None  # nebular age axis (log10 yr): neb_tab is then [n_age][n_logu][n_logz][n_lam]
 
     @property
     def shape(self):
@@ -107,7 +108,29 @@ def make_grid(n_age=16, log_age=(6.0, 10.1), feh=(-2.0, 0.2), n_feh=4,
                                                         n_lines=0 if n_cube else 30)
         if n_cube:
             g.line_lam, g.line_tab = make_line_cube(g.neb_logu, g.neb_logz, n_cube, seed=nebular.get("seed", 2) + 10)
+        if nebular.get("age_axis"):
+            g.neb_log_age, g.neb_tab = nebular_age_axis(g.neb_tab, g.neb_logu, lam, *nebular["age_axis"],
+                                                        seed=nebular.get("seed", 2) + 20)
     return g
+
+
+def nebular_age_axis(tab, logu, lam, n_age, lo, hi, seed=22):
+    """A nebular cube with an ionising-source age axis: n_age planes at log10
+    ages lo..hi (yr), plane i = the age-free template dimmed by 0.8 dex per dex
+    of age (the ionising output fading with age), with a seeded slope that
+    steepens towards high log U and a seeded wavelength ripple of 0.05 dex; -99
+    below 912 Angstrom as in the template."""
+    rng = _rng(seed)
+    ages = np.linspace(lo, hi, n_age)
+    du = (np.asarray(logu) + 2.5)[:, None, None]
+    ripple = 0.05 * np.sin(np.log(lam) * rng.uniform(5.0, 15.0) + rng.uniform(0, 2 * np.pi))[None, None, :]
+    out = np.empty((n_age,) + tab.shape)
+    for i, t in enumerate(ages):
+        dt = t - lo
+        plane = tab - 0.8 * dt - 0.2 * dt * du + dt * ripple
+        plane[:, :, lam < 912.0] = -99.0
+        out[i] = plane
+    return ages, out
 
 
 def make_line_cube(logu, logz, n_lines, seed=12, lam_aa=(1000.0, 22000.0)):
