@@ -155,6 +155,18 @@ typedef struct {
   int neb_n_line;
   const double *neb_line_lam_aa;       /* [n_line] rest-frame wavelengths, Angstrom */
   const double *neb_log10_line_per_q;  /* [n_logu][n_logz][n_line] log10(L_line/Q), Lsun/(photon/s) */
+  /* Nebular age axis (App. C): neb_n_age > 0 gives the continuum cube an
+   * ionising-source age axis, neb_log10_lnu_per_q then being
+   * [neb_n_age][n_logu][n_logz][n_lam] on the increasing log10 ages
+   * neb_log_age_yr.  The cube is queried at each SSP age inside its tabulated
+   * ages (linear in log age between its planes, bilinear in log U and
+   * log Z_gas): those SSP ages, at most 32 and all within a model's
+   * birth-cloud ages (else SED_EUNSUPPORTED at model creation), power the
+   * nebular emission with their own Q.  Not combined with a line cube
+   * (SED_EUNSUPPORTED), nor, in a model, with an escape geometry or
+   * age-binned dust; not served by sed_server_* or sed_loglike_noalloc. */
+  int neb_n_age;
+  const double *neb_log_age_yr;
 } sed_grid_desc;
 
 #define SED_GRID_COPY_FP32 (1u << SED_PREC_FP32)           /* TF32 hi/lo parts (3xTF32 path) */

@@ -40,7 +40,8 @@ class GridDesc(C.Structure):
                 ("log_age_yr", P), ("feh", P), ("afe", P), ("lam_aa", P), ("flux", P),
                 ("sigma_lib_kms", P), ("neb_n_logu", C.c_int), ("neb_n_logz", C.c_int),
                 ("neb_logu", P), ("neb_logz", P), ("neb_log10_lnu_per_q", P), ("precision_mask", C.c_uint),
-                ("neb_n_line", C.c_int), ("neb_line_lam_aa", P), ("neb_log10_line_per_q", P)]
+                ("neb_n_line", C.c_int), ("neb_line_lam_aa", P), ("neb_log10_line_per_q", P),
+                ("neb_n_age", C.c_int), ("neb_log_age_yr", P)]
 
 
 class ModelDesc(C.Structure):

@@ -103,7 +103,14 @@ class Context:
         if getattr(grid, "neb_tab", None) is not None:
             nu, nz, nt = _f64(grid.neb_logu), _f64(grid.neb_logz), _f64(grid.neb_tab)
             keep += [nu, nz, nt]
-            d.neb_n_logu, d.neb_n_logz = nt.shape[:2]
+            na = getattr(grid, "neb_log_age", None)
+            if na is not None:   # nebular age axis: neb_tab [n_age][n_logu][n_logz][n_lam]
+                na = _f64(na)
+                keep.append(na)
+                d.neb_n_age, d.neb_log_age_yr = na.size, _ptr(na)
+                d.neb_n_logu, d.neb_n_logz = nt.shape[1:3]
+            else:
+                d.neb_n_logu, d.neb_n_logz = nt.shape[:2]
             d.neb_logu, d.neb_logz, d.neb_log10_lnu_per_q = _ptr(nu), _ptr(nz), _ptr(nt)
             if getattr(grid, "line_tab", None) is not None:
                 ll, lt = _f64(grid.line_lam), _f64(grid.line_tab)

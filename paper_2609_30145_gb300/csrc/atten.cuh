@@ -34,17 +34,33 @@ __device__ __forceinline__ float neb_log10(const RowScal& rs, const float* tab, 
          rs.neb_w[2] * tab[rs.neb_off[2] + k] + rs.neb_w[3] * tab[rs.neb_off[3] + k];
 }
 
+// Nebular emission at node k (device units): Q_young 10^template, or with a
+// nebular age axis (App. C) the sum over the nebular SSP ages of q_a 10^(the
+// cube at that age), qa the row's q_a (NULL without an axis).
+__device__ __forceinline__ float neb_emission(const RowScal& rs, const GridDev& g, const float* qa, int k) {
+  if (qa) {
+    const size_t plane = (size_t)g.neb_nu * g.neb_nz * g.n_lam;
+    float acc = 0.f;
+    for (int i = 0; i < g.neb_na; ++i) {
+      const float q = qa[i];
+      if (q != 0.f) acc = fmaf(q, ex2_approx(3.3219280948873623f * neb_log10(rs, g.neb_tab + i * plane, k)), acc);
+    }
+    return acc;
+  }
+  return ex2_approx(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, g.neb_tab, k));
+}
+
 // c = {ln(lam/5500), k'/4.05, Drude/4.05, 1/lam^2}; eb = 0.85 - 1.9 delta
 __device__ __forceinline__ float attenuated(const ModelDev& md, const RowScal& rs, const float4& c, float eb, float y,
-                                           float o, const float* neb_tab, int k) {
+                                           float o, const GridDev& g, const float* qa, int k) {
   const float tbc = rs.tau_bc * __expf(rs.alpha_bc * c.x);
   const float pw = __expf(rs.delta * c.x);
   const float td = rs.tau_d * dust_shape(md, c, eb, pw);
   if (md.fesc_geom == SED_FESC_NONE) {
-    if (md.use_neb) y += ex2_approx(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, neb_tab, k));
+    if (md.use_neb) y += neb_emission(rs, g, qa, k);
     return __expf(-td) * (__expf(-tbc) * y + o);
   }
-  const float nb = md.use_neb ? ex2_approx(rs.log2_qy + 3.3219280948873623f * neb_log10(rs, neb_tab, k)) : 0.f;
+  const float nb = md.use_neb ? neb_emission(rs, g, qa, k) : 0.f;
   const bool lyc = md.use_neb && k < md.n_lyc;
   const float ys = lyc ? 0.f : y, f = rs.fob, ed = __expf(-td), ebc = __expf(-tbc);
   if (md.fesc_geom == SED_FESC_PICKET) return f * y + ed * ((1.f - f) * ebc * (ys + nb) + o);

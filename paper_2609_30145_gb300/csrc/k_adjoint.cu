@@ -172,6 +172,15 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   const float* O2r = a.O2 ? a.O2 + ro : nullptr;
   const float eb_kc = 0.85f - 1.9f * rs.delta;
   const float opz = 1.f / rs.inv1pz;
+  // nebular age axis: the row's Q-weighted weight of each nebular SSP age, and
+  // dlnL/dq of each (the second pass after the node loop)
+  __shared__ float qa_s[MAX_NEB_AGE], gqa_s[MAX_NEB_AGE];
+  const float* qa = nullptr;
+  if (!BINS && a.qneb) {
+    for (int i = tid; i < g.neb_na; i += EB_THREADS) qa_s[i] = a.qneb[(size_t)r * MAX_NEB_AGE + i];
+    __syncthreads();
+    qa = qa_s;
+  }
 
   // ---- forward: attenuated spectrum in the window (the forward epilogue's
   //      arithmetic); phi holds the window's wavelengths until the photometric
@@ -184,7 +193,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       for (int sg = 0; sg < MAX_SEG; ++sg) yv[sg] = sg < md.n_seg ? Yr[sg * a.seg_stride + k] : 0.f;
       Fs[k] = attenuated_bins(md, rs, g.att4[k], eb_kc, yv, O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
     } else {
-      Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
+      Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g, qa, k);
     }
     if (md.use_igm && g.lam_f[k] < IGM_LYA) {   // the IGM transmission (the forward epilogue's)
       float tau, dtau;
@@ -810,8 +819,12 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     const float y = Yr[k];
     float lg = 0.f, nb = 0.f;
     if (md.use_neb) {
-      lg = neb_log10(rs, g.neb_tab, k);
-      nb = ex2_approx(rs.log2_qy + 3.3219280948873623f * lg);
+      if (qa) {
+        nb = neb_emission(rs, g, qa, k);
+      } else {
+        lg = neb_log10(rs, g.neb_tab, k);
+        nb = ex2_approx(rs.log2_qy + 3.3219280948873623f * lg);
+      }
     }
     // with the IGM, F = T F0: dlnL/dF0 = T dlnL/dF, and ln T = -f tau moves with f and z
     float T = 1.f, F0 = Fs[k];
@@ -856,7 +869,9 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     g_abc += gtbc * tbc * lnp;
     g_td += gtd * shape;
     g_dl += gtd * rs.tau_d * dshape;
-    if (md.use_neb) {
+    if (md.use_neb && qa) {
+      phi[k] = gnb;   // dlnL / d(nebular emission) of the node, for the per-age pass below
+    } else if (md.use_neb) {
       g_qy += gnb * ex2_approx(3.3219280948873623f * lg);
       const float glg = gnb * nb * 2.302585092994046f;
       float su = 0.f, sz = 0.f;
@@ -868,6 +883,38 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       }
       g_lu += glg * su;
       g_lz += glg * sz;
+    }
+  }
+  if (qa) {
+    // nebular age axis: warp per nebular SSP age, lanes over the window's
+    // nodes (node order, fixed shuffle tree): dlnL/dq_a = sum_k g_k e_a(k) and
+    // the (log U, log Z_gas) derivative of each age's plane, g_k = dlnL/d(neb)
+    // at node k (phi), e_a(k) = 10^(the cube at age a)
+    __syncthreads();
+    const size_t plane = (size_t)g.neb_nu * g.neb_nz * N;
+    for (int i = warp; i < g.neb_na; i += EB_WARPS) {
+      const float q = qa[i];
+      const float* tb = g.neb_tab + i * plane;
+      float sq = 0.f;
+      for (int k = k_lo + lane; k <= k_hi; k += 32) {
+        float lgi = 0.f, su = 0.f, sz = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const float tv = tb[rs.neb_off[cc] + k];
+          lgi = fmaf(rs.neb_w[cc], tv, lgi);
+          su = fmaf(rs.neb_dwu[cc], tv, su);
+          sz = fmaf(rs.neb_dwz[cc], tv, sz);
+        }
+        const float e = ex2_approx(3.3219280948873623f * lgi);
+        const float gn = phi[k];
+        sq = fmaf(gn, e, sq);
+        const float glg = gn * q * e * 2.302585092994046f;
+        g_lu = fmaf(glg, su, g_lu);
+        g_lz = fmaf(glg, sz, g_lz);
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) gqa_s[i] = sq;
     }
   }
 
@@ -964,6 +1011,8 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       rg[RG_FOB] = s[13];
       rg[RG_SIGMA_GAS] = s[14];
       rg[RG_IGM] = s[16];
+      if (qa)
+        for (int i = 0; i < g.neb_na; ++i) rg[RG_QAGE + i] = (double)gqa_s[i];
       for (int k = 0; k < 4; ++k) {
         rg[RG_FLOOR + k] = gfp[k];
         rg[RG_FLOOR + 4 + k] = s[9 + k];

@@ -103,6 +103,14 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   const float* O2r = a.O2 ? a.O2 + (size_t)r * a.ldn : nullptr;
   const float eb = 0.85f - 1.9f * rs.delta;
   const float opz = 1.f / rs.inv1pz;
+  // nebular age axis: the row's Q-weighted weight of each nebular SSP age
+  __shared__ float qa_s[MAX_NEB_AGE];
+  const float* qa = nullptr;
+  if (!BINS && a.qneb) {
+    for (int i = tid; i < g.neb_na; i += blockDim.x) qa_s[i] = a.qneb[(size_t)r * MAX_NEB_AGE + i];
+    __syncthreads();
+    qa = qa_s;
+  }
   const bool spec = md.n_pix > 0;
   const int k_lo = rs.k_lo, k_hi = min(rs.k_hi, rs.k_lo + WIN - 1);   // nodes [k_lo, k_hi] are the only ones read below
   float2* LG = reinterpret_cast<float2*>(smem4) - k_lo;               // {rest-frame lambda, F / lam^2}
@@ -120,7 +128,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
       for (int sg = 0; sg < MAX_SEG; ++sg) yv[sg] = sg < md.n_seg ? Yr[sg * a.seg_stride + k] * ys : 0.f;
       F = attenuated_bins(md, rs, c, eb, yv, o * ys, g.neb_tab, k);
     } else {
-      F = attenuated(md, rs, c, eb, Yr[k] * ys, o * ys, g.neb_tab, k);
+      F = attenuated(md, rs, c, eb, Yr[k] * ys, o * ys, g, qa, k);
     }
     if (md.use_igm && c.w < IGM_LYA) {   // the IGM transmission at the node's observed wavelength
       float tau, dtau;

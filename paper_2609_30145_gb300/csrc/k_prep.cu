@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     // every block, from the nebular ages' weights (W_k = w_n Ws[a][m] with the
     // [a/Fe] bracket weights w_n)
     float qb[MAX_SEG + 1] = {};
-    for (int j = tid; j < L.n_young * NZ; j += blockDim.x) {
+    for (int j = tid + L.neb_a0 * NZ; j < L.n_young * NZ; j += blockDim.x) {
       const int ag = j / NZ, mm = j - ag * NZ;
       const int4 ac = L.age_col[ag];
       const float wv = Ws[ag * NZ + mm];
@@ -669,6 +669,21 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     for (int jj = 0; jj <= MAX_SEG; ++jj) {
       for (int o = 16; o; o >>= 1) qb[jj] += __shfl_xor_sync(0xffffffffu, qb[jj], o);
       if (lane == 0) s_redq[jj][warp] = qb[jj];
+    }
+  }
+  if (a.qneb && g.neb_na > 0) {
+    // nebular age axis: the Q-weighted weight of each nebular SSP age (the
+    // epilogue weights each age's plane of the nebular cube by it)
+    for (int i = tid; i < g.neb_na; i += blockDim.x) {
+      const int ag = g.neb_a0 + i;
+      const int4 ac = L.age_col[ag];
+      float q = 0.f;
+      for (int mm = 0; mm < NZ; ++mm) {
+        const float wv = Ws[ag * NZ + mm];
+        q += wn0 * wv * __ldg(L.q_s + ac.x + (n0 * NZ + mm) * ac.y);
+        if (n1 != n0) q += wn1 * wv * __ldg(L.q_s + ac.x + (n1 * NZ + mm) * ac.y);
+      }
+      a.qneb[(size_t)p * MAX_NEB_AGE + i] = q;
     }
   }
   if (lane == 0) { s_red[warp] = qpart; s_nnz[warp] = nnz; }
@@ -913,9 +928,11 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   float gafe = 0.f;
   for (int j = tid; j < NA * NZ; j += blockDim.x) {
     const int ag = j / NZ, mm = j % NZ;
-    const bool young = ag < L.n_young;   // a nebular age: Q enters through it
+    const bool young = ag >= L.neb_a0 && ag < L.n_young;   // a nebular age: Q enters through it
     const int4 ac = L.age_col[ag];
     float gq = gqy;
+    if (g.neb_na > 0 && md.use_neb && young)   // nebular age axis: this age's own dlnL/dQ
+      gq = (float)a.rgrad[(size_t)r * RGRAD + RG_QAGE + (ag - g.neb_a0)];
     if (md.n_bin > 0) {
 #pragma unroll
       for (int jj = 0; jj <= MAX_SEG; ++jj) gq = ac.z == jj ? gqb[jj] : gq;

@@ -185,7 +185,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
       Workspace* w = kv.second;
       std::vector<void*> v = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
                               w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
-                              w->dW, w->rgrad};
+                              w->dW, w->rgrad, w->qneb};
       for (void* p : v)
         if (p) cudaFree(p);
       for (cudaEvent_t e : w->ev)
@@ -240,9 +240,24 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
     if (!d->neb_logu || !d->neb_logz || !strictly_increasing(d->neb_logu, d->neb_n_logu) ||
         !strictly_increasing(d->neb_logz, d->neb_n_logz))
       return fail(ctx, SED_EINVAL, "nebular axes must be strictly increasing");
-    size_t nt = (size_t)d->neb_n_logu * d->neb_n_logz * nl;
+    if (d->neb_n_age < 0 || d->neb_n_age > 64) return fail(ctx, SED_ERANGE, "neb_n_age must be in [0, 64]");
+    if (d->neb_n_age > 0) {
+      if (!d->neb_log_age_yr || !strictly_increasing(d->neb_log_age_yr, d->neb_n_age))
+        return fail(ctx, SED_EINVAL, "the nebular age axis must be finite and strictly increasing");
+      if (d->neb_n_line > 0) return fail(ctx, SED_EUNSUPPORTED, "a line cube with a nebular age axis is not supported");
+    }
+    size_t nt = (size_t)std::max(d->neb_n_age, 1) * d->neb_n_logu * d->neb_n_logz * nl;
     for (size_t i = 0; i < nt; i++)
       if (!std::isfinite(d->neb_log10_lnu_per_q[i])) return fail(ctx, SED_EINVAL, "nebular template not finite");
+  }
+  // the SSP ages inside a nebular age axis's tabulated ages
+  int neb_a0 = 0, neb_na = 0;
+  if (neb && d->neb_n_age > 0) {
+    const double lo = d->neb_log_age_yr[0], hi = d->neb_log_age_yr[d->neb_n_age - 1];
+    while (neb_a0 < d->n_age && d->log_age_yr[neb_a0] < lo) neb_a0++;
+    while (neb_a0 + neb_na < d->n_age && d->log_age_yr[neb_a0 + neb_na] <= hi) neb_na++;
+    if (neb_na == 0) return fail(ctx, SED_EINVAL, "no SSP age lies inside the nebular age axis");
+    if (neb_na > MAX_NEB_AGE) return fail(ctx, SED_ERANGE, "the nebular age axis spans more than %d SSP ages", MAX_NEB_AGE);
   }
   if (d->neb_n_line < 0 || d->neb_n_line > MAX_LINES)
     return fail(ctx, SED_ERANGE, "neb_n_line must be in [0, %d]", MAX_LINES);
@@ -375,13 +390,32 @@ sed_status sed_load_grid(sed_ctx* ctx, const sed_grid_desc* d, sed_grid_id* out)
     g->neb_nu = d->neb_n_logu; g->neb_nz = d->neb_n_logz;
     g->neb_logu.assign(d->neb_logu, d->neb_logu + g->neb_nu);
     g->neb_logz.assign(d->neb_logz, d->neb_logz + g->neb_nz);
-    const size_t nt = (size_t)g->neb_nu * g->neb_nz * nl;
-    std::vector<float> tab(nt);
+    const size_t plane = (size_t)g->neb_nu * g->neb_nz * nl;
     const double off = (g->f_log2 + g->q_log2) * std::log10(2.0);
-    for (size_t i = 0; i < nt; i++) tab[i] = (float)(d->neb_log10_lnu_per_q[i] + off);
-    st = upload(ctx, &p, tab.data(), nt, &g->allocs, &g->bytes);
+    std::vector<float> tab(plane * std::max(neb_na, 1));
+    if (neb_na == 0) {
+      for (size_t i = 0; i < plane; i++) tab[i] = (float)(d->neb_log10_lnu_per_q[i] + off);
+    } else {
+      // the cube at each SSP age inside it: linear in log age between the two
+      // planes bracketing the age (App. C's trilinear interpolation; the bilinear
+      // part in log U and log Z_gas is the row's)
+      const int na = d->neb_n_age;
+      for (int i = 0; i < neb_na; i++) {
+        const double la = d->log_age_yr[neb_a0 + i];
+        int j = 0;
+        while (j + 2 < na && la >= d->neb_log_age_yr[j + 1]) j++;
+        const double t = na == 1 ? 0.0 : std::min(std::max((la - d->neb_log_age_yr[j]) /
+                                                            (d->neb_log_age_yr[j + 1] - d->neb_log_age_yr[j]), 0.0), 1.0);
+        const double* c0 = d->neb_log10_lnu_per_q + (size_t)j * plane;
+        const double* c1 = d->neb_log10_lnu_per_q + (size_t)(na == 1 ? j : j + 1) * plane;
+        for (size_t q = 0; q < plane; q++) tab[(size_t)i * plane + q] = (float)((1.0 - t) * c0[q] + t * c1[q] + off);
+      }
+    }
+    st = upload(ctx, &p, tab.data(), tab.size(), &g->allocs, &g->bytes);
     dv.neb_tab = p;
     dv.neb_nu = g->neb_nu; dv.neb_nz = g->neb_nz;
+    g->neb_a0 = dv.neb_a0 = neb_a0;
+    g->neb_na = dv.neb_na = neb_na;
     // emission-line cube: per line the constants of the attenuation at its
     // wavelength, ln(lambda) as an FP32 pair, and log10(L/Q) with the same
     // device-unit offset as the continuum template
@@ -431,7 +465,7 @@ float ssp_value(const Grid* g, const Layout* L, int k, int l) {
   const int c = L->code_h[k];
   if (c < 0) return 0.f;
   const int n = c >> 24, m = (c >> 16) & 0xff, a = c & 0xffff;
-  if (L->neb_cut && a < L->n_young && g->lam[l] < LYMAN_AA) return 0.f;
+  if (L->neb_cut && a >= L->neb_a0 && a < L->n_young && g->lam[l] < LYMAN_AA) return 0.f;
   return (float)(g->flux[(((size_t)n * g->n_feh + m) * g->n_age + a) * g->n_lam + l] * g->f_scale);
 }
 
@@ -528,11 +562,13 @@ sed_status ensure_f8_layout(sed_ctx* ctx, Grid* g, Layout* L) {
 // columns each, so that every precision's K tiles (32, 64 and 128 columns)
 // and the adjoint's 128-column output tiles lie within one block.  Nebular
 // ages (the first n_neb) carry Q and, with neb_cut, lose their flux below 912 A.
-sed_status get_layout(sed_ctx* ctx, Grid* g, const std::vector<int>& blk, int n_neb, int neb_cut, Layout** out) {
+sed_status get_layout(sed_ctx* ctx, Grid* g, const std::vector<int>& blk, int neb0, int n_neb, int neb_cut,
+                      Layout** out) {
   for (Layout* L : g->layouts)
-    if (L->blk == blk && L->n_young == n_neb && L->neb_cut == neb_cut) { *out = L; return SED_OK; }
+    if (L->blk == blk && L->neb_a0 == neb0 && L->n_young == n_neb && L->neb_cut == neb_cut) { *out = L; return SED_OK; }
   Layout* L = new Layout();
   L->blk = blk;
+  L->neb_a0 = neb0;
   L->n_young = n_neb;
   L->neb_cut = neb_cut;
   const int NA = g->n_age, NZ = g->n_feh, NAF = g->n_afe, NL = g->n_lam;
@@ -567,7 +603,7 @@ sed_status get_layout(sed_ctx* ctx, Grid* g, const std::vector<int>& blk, int n_
           const int a = ages[s][i];
           const int k = base + (n * NZ + m) * len + i;
           code[k] = (n << 24) | (m << 16) | a;
-          if (a < n_neb) qs[k] = (float)(g->q[((size_t)n * NZ + m) * NA + a] * std::exp2(-g->q_log2));
+          if (a >= neb0 && a < n_neb) qs[k] = (float)(g->q[((size_t)n * NZ + m) * NA + a] * std::exp2(-g->q_log2));
         }
   }
   L->q_log2 = g->q_log2;
@@ -819,6 +855,13 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
         return fail(ctx, SED_EINVAL, "line catalogue entry %d: datum not finite or sigma <= 0", k);
     }
   }
+  if (d->use_nebular && g->neb_na > 0) {
+    if (d->fesc_geometry || d->dust_n_bin > 0 || d->use_lines)
+      return fail(ctx, SED_EUNSUPPORTED, "a nebular age axis is not combined with an escape geometry, age-binned "
+                                         "dust or emission lines");
+    if (g->log_age[g->neb_a0 + g->neb_na - 1] > d->bc_edge_log_age_yr)
+      return fail(ctx, SED_EUNSUPPORTED, "the nebular age axis reaches past the birth-cloud edge");
+  }
   if (d->use_igm != SED_IGM_NONE && d->use_igm != SED_IGM_MADAU)
     return fail(ctx, SED_EINVAL, "use_igm must be SED_IGM_NONE or SED_IGM_MADAU");
   if (d->dust_n_bin < 0 || d->dust_n_bin > MAX_DUST_BIN)
@@ -962,7 +1005,10 @@ sed_status sed_create_model(sed_ctx* ctx, const sed_model_desc* d, sed_model_id*
   while (dv.n_lyc < g->n_lam && g->lam[dv.n_lyc] < LYMAN_AA) dv.n_lyc++;
   if (d->dust_n_bin == 0)
     for (int a = 0; a < g->n_age; a++) blk[a] = a < n_young ? 0 : -1;
-  sed_status st = get_layout(ctx, g, blk, n_young, d->use_nebular && !d->fesc_geometry ? 1 : 0, &M->L);
+  // the nebular ages: the birth-cloud ages, or those a nebular age axis spans
+  const bool axis = d->use_nebular && g->neb_na > 0;
+  sed_status st = get_layout(ctx, g, blk, axis ? g->neb_a0 : 0, axis ? g->neb_a0 + g->neb_na : n_young,
+                             d->use_nebular && !d->fesc_geometry ? 1 : 0, &M->L);
   if (!st) {
     std::vector<double> tab;
     cosmo_table(d->H0, d->Om0, d->zf, COSMO_TAB, &tab);
@@ -1245,7 +1291,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   cudaStreamSynchronize((cudaStream_t)stream);
   std::vector<void*> old = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
                             w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
-                            w->dW, w->rgrad};
+                            w->dW, w->rgrad, w->qneb};
   for (void* p : old)
     if (p) cudaFree(p);
   budget_release(ctx, w->bytes);
@@ -1265,7 +1311,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
   AL(perm, R * 4); AL(tile_win, 2 * ((R + 127) / 128) * 4); AL(kmask, ((R + 127) / 128) * KMASK_WORDS * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
   AL(Y, R * N * 4 * w->cap_seg); AL(O, R * N * 4); AL(O2, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
-  AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4);
+  AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4); AL(qneb, R * MAX_NEB_AGE * 4);
   if (grad || had_grad) {
     AL(G_hi, R * N * 4 * w->cap_seg); AL(G_lo, R * N * 4 * w->cap_seg); AL(GO_hi, R * N * 4); AL(GO_lo, R * N * 4);
     AL(dW, R * K * 4); AL(rgrad, R * RGRAD * 8);
@@ -1332,6 +1378,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   pa.rs = w->rs;
   pa.err = w->err;
   pa.perm = w->perm;
+  pa.qneb = M->dv.use_neb && g->neb_na > 0 ? w->qneb : nullptr;
   pa.tile_win = w->tile_win;
   // K-tile masks for the tensor-core contractions (32 / 64 / 128 columns per tile)
   {
@@ -1420,6 +1467,7 @@ sed_status sed_forward(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   ea.O2 = precision == SED_PREC_FP32 ? w->O2 : nullptr;   // the 3xTF32 contraction's split old part
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
+  ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   ea.phot_out = M->dv.n_filt ? phot_out : nullptr;
   ea.spec_out = M->dv.n_pix ? spec_out : nullptr;
@@ -1448,6 +1496,7 @@ sed_status sed_line_fluxes(sed_ctx* ctx, sed_model_id id, const float* theta, in
   ea.O2 = precision == SED_PREC_FP32 ? w->O2 : nullptr;
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
+  ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   ea.lines_out = flux_out;
   ea.err = w->err;
@@ -1474,6 +1523,7 @@ sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   ea.O2 = precision == SED_PREC_FP32 ? w->O2 : nullptr;   // the 3xTF32 contraction's split old part
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
+  ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
   ea.lnl = lnl_out; ea.status = row_status; ea.err = w->err;
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   CK(launch_epilogue(ea, s));
@@ -1588,6 +1638,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   eb.gy_hi = w->G_hi; eb.gy_lo = w->G_lo; eb.go_hi = w->GO_hi; eb.go_lo = w->GO_lo;
   eb.rgrad = w->rgrad; eb.lnl = lnl_out; eb.status = row_status; eb.err = w->err;
   eb.seg_stride = (size_t)w->cap_rows * w->ldn;
+  eb.qneb = M->dv.use_neb && g->neb_na > 0 ? w->qneb : nullptr;
   size_t smem = 0;
   cudaError_t e = launch_epilogue_bwd(eb, &smem, s);
   if (e == cudaErrorInvalidConfiguration)

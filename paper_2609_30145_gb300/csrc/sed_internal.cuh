@@ -36,6 +36,7 @@ constexpr int KMASK_WORDS = 8;
 constexpr int MAX_LINES = 128;   // emission lines of a nebular grid
 constexpr int MAX_DUST_BIN = SED_MAX_DUST_BIN;   // age-binned attenuation laws
 constexpr int MAX_SEG = SED_MAX_DUST_SEG;        // attenuated K blocks (runs of ages with one non-zero row of M)
+constexpr int MAX_NEB_AGE = 32;  // SSP ages a nebular age axis spans
 
 // Physical constants (cgs unless noted).
 constexpr double LSUN = 3.839e33;              // erg/s (Sec. 2.6)
@@ -114,8 +115,10 @@ struct GridDev {
   const float* cell_hi;
   const float* age_t;      // age of each node (yr), for the linear SFH scheme's tents
   const float* age_dl;     // ln(t_{a+1} / t_a) (last entry unused)
-  const float* neb_tab;    // [nu][nz][n_lam] log10 template + device-unit offset
+  const float* neb_tab;    // [nu][nz][n_lam] log10 template + device-unit offset; with an age axis
+                           // [neb_na][nu][nz][n_lam], plane i the cube at SSP age neb_a0 + i
   int neb_nu, neb_nz;
+  int neb_a0, neb_na;      // nebular age axis: the SSP ages [neb_a0, neb_a0 + neb_na) (neb_na = 0: none)
   // emission-line cube: per line {ln(lam/5500), k'/4.05, Drude/4.05, lam},
   // ln(lam) as an FP32 pair, and [nu][nz][n_line] log10(L/Q) + device-unit offset
   int n_line;
@@ -130,6 +133,7 @@ struct LayoutDev {
   const int* k_code;       // [Kpad]
   int Ky_pad8, Kpad8;      // FP8 layout: each block padded to 128 (one 128-byte K tile)
   const float* col8;       // [Kpad] 2^-e_k, the FP8 column scale folded into W (0 for empty columns)
+  int neb_a0;              // nebular ages: [neb_a0, n_young)
   int n_seg;               // attenuated blocks in [0, Ky_pad): block s = columns [seg_k0[s], seg_k0[s+1])
   int seg_k0[MAX_SEG + 1];
   const int4* age_col;     // [n_age] column of (afe n, feh m, age a) = x + (n n_feh + m) y; z = a's block
@@ -227,7 +231,8 @@ __host__ __device__ __forceinline__ float theta_col(const ModelDev& md, const fl
 // Device copy of a grid in one K order: [young block | old block], each block
 // ordered (afe n, feh m, age a) with age fastest, each block padded to KT.
 struct Layout {
-  int n_young = 0;    // nebular ages (<= birth-cloud edge): Q and the 912 A cut
+  int n_young = 0;    // nebular ages [neb_a0, n_young) (<= birth-cloud edge): Q and the 912 A cut
+  int neb_a0 = 0;
   int neb_cut = 0;    // 1: stellar flux below 912 A removed for nebular ages
   // the attenuated blocks: age a is in block blk[a] (0 .. n_seg - 1) or, for
   // -1, in the block after them (no age-dependent attenuation); without
@@ -260,7 +265,7 @@ struct Layout {
   bool have_tmaps = false;
   CUtensorMap tm_hi, tm_lo, tm_bf16;
   LayoutDev dv() const {
-    LayoutDev d{n_young, neb_cut, Ky, Ko, Ky_pad, Kpad, q_s, k_code, Ky_pad8, Kpad8, col8, n_seg, {}, age_col};
+    LayoutDev d{n_young, neb_cut, Ky, Ko, Ky_pad, Kpad, q_s, k_code, Ky_pad8, Kpad8, col8, neb_a0, n_seg, {}, age_col};
     for (int s = 0; s <= MAX_SEG; ++s) d.seg_k0[s] = seg_k0[s];
     return d;
   }
@@ -279,6 +284,7 @@ struct Grid {
   std::vector<double> q;                             // [n_afe][n_feh][n_age] Eq. app_q
   GridDev dv{};
   int neb_nu = 0, neb_nz = 0;
+  int neb_a0 = 0, neb_na = 0;  // nebular age axis: the SSP ages it spans (neb_na = 0: none)
   std::vector<double> neb_logu, neb_logz;
   std::vector<Layout*> layouts;
   std::vector<void*> allocs;
@@ -321,7 +327,8 @@ enum {
   RG_QSEG = RG_BIN + 2 * MAX_DUST_BIN,   // MAX_SEG + 1 slots: dlnL/dQ of each attenuated block, then
                                         // of the block outside every bin
   RG_IGM = RG_QSEG + MAX_SEG + 1,       // dlnL/digm_factor
-  RGRAD = 40
+  RG_QAGE,                              // MAX_NEB_AGE slots: dlnL/dQ of each SSP age of a nebular age axis
+  RGRAD = RG_QAGE + MAX_NEB_AGE + 4
 };
 
 // Per-stream scratch.
@@ -354,6 +361,7 @@ struct Workspace {
   float* GO_lo = nullptr;
   float* dW = nullptr;           // [rows][Kpad] dlnL/dW
   double* rgrad = nullptr;       // [rows][RGRAD] per-row scalar gradient pieces
+  float* qneb = nullptr;         // [rows][MAX_NEB_AGE] nebular age axis: Q-weighted weight of each nebular age
   bool dw_maps_valid = false;
   const void* dw_maps_for = nullptr;
   int dw_maps_n = -1;
@@ -445,6 +453,7 @@ struct PrepArgs {
                        // (zeroed beforehand), or NULL
   int kmask_w;         // words per 128-row tile (<= KMASK_WORDS)
   int kt_shift;        // log2 of the columns of one K tile of the contraction's layout (5, 6 or 7)
+  float* qneb;         // nebular age axis: [n][MAX_NEB_AGE] Q-weighted weight of each nebular SSP age, or NULL
 };
 // A pixel's rest-frame ln(lambda) = ln(lambda_obs) - ln(1+z), both given as
 // FP32 pairs {hi, lo}, returned as an FP32 pair: the high parts' difference is
@@ -607,6 +616,7 @@ struct EpiArgs {
   const float* lam8;   // FP8 path: [n_lam] 2^-f_l multiplying Y and O; NULL otherwise
   int lines_off;       // set by launch_epilogue: float offset of the emission lines' shared arrays
   size_t seg_stride;   // age-binned dust: Y of attenuated block s at Y + s seg_stride
+  const float* qneb;   // nebular age axis: [n][MAX_NEB_AGE] (k_prep's), or NULL
 };
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 
@@ -624,6 +634,7 @@ struct EpiBwdArgs {
   const int* err;
   int lines_off;        // set by launch_epilogue_bwd: byte offset of the emission lines' shared arrays
   size_t seg_stride;    // age-binned dust: Y and dlnL/dY of attenuated block s at + s seg_stride
+  const float* qneb;    // nebular age axis: [n][MAX_NEB_AGE] (k_prep's), or NULL
 };
 cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s);
 

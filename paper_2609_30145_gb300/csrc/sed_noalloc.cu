@@ -82,6 +82,8 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   if (id < 0 || id >= (int)ctx->models.size() || !ctx->models[id]) return na_fail(ctx, SED_EINVAL, "unknown model");
   Model* M = ctx->models[id];
   if (M->dv.n_bin > 0) return na_fail(ctx, SED_EUNSUPPORTED, "age-binned dust needs sed_loglike (one slab per block)");
+  if (M->dv.use_neb && M->g->neb_na > 0)
+    return na_fail(ctx, SED_EUNSUPPORTED, "a nebular age axis needs sed_loglike (per-age weights)");
   if (n < 0) return na_fail(ctx, SED_EINVAL, "n < 0");
   if (n > 0 && (!theta || !lnl_out)) return na_fail(ctx, SED_EINVAL, "theta or lnl_out is NULL");
   if (ld < M->dv.n_param) return na_fail(ctx, SED_EINVAL, "ld (%d) < n_param (%d)", ld, M->dv.n_param);

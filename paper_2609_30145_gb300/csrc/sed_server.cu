@@ -314,6 +314,7 @@ sed_status sed_server_create(sed_ctx* ctx, const sed_server_desc* d, sed_server*
   sed::Model* M0 = ctx->models[d->model_layout];
   if (M0->grid != d->grid) return SED_EINVAL;
   if (M0->dv.n_bin > 0) return SED_EUNSUPPORTED;   // age-binned dust is not served
+  if (M0->dv.use_neb && M0->g->neb_na > 0) return SED_EUNSUPPORTED;   // nor a nebular age axis
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
@@ -414,6 +415,8 @@ sed_status sed_server_open_fit(sed_server* sv, sed_model_id model, int max_rows,
   sed::Model* M = ctx->models[model];
   if (M->L != sv->L) return sfail(sv, SED_EINVAL, "model %d uses another grid layout than the server", model);
   if (M->dv.n_bin > 0) return sfail(sv, SED_EUNSUPPORTED, "model %d has age-binned dust (not served)", model);
+  if (M->dv.use_neb && M->g->neb_na > 0)
+    return sfail(sv, SED_EUNSUPPORTED, "model %d has a nebular age axis (not served)", model);
   if (max_rows < 1 || max_rows > sv->max_rows)
     return sfail(sv, SED_ERANGE, "max_rows must be in [1, %d]", sv->max_rows);
   const int ld = M->dv.n_param;
