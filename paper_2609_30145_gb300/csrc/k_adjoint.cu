@@ -90,8 +90,9 @@ size_t epi_bwd_smem(const EpiBwdArgs& a) {
 }
 
 // LINES: an instance with the emission lines (the one without keeps its code free of them);
-// BINS: the age-binned attenuation (one Y and one dlnL/dY per attenuated block)
-template <bool LINES, bool BINS = false>
+// VAR: 1 the age-binned attenuation (one Y and one dlnL/dY per attenuated
+// block), 2 the nebular age axis (per-age ionising weights); 0 neither
+template <bool LINES, int VAR = 0>
 __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant__ EpiBwdArgs a) {
   pdl_enter();
   const ModelDev& md = a.md;
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
   if (rs.status) {
     for (int k = tid; k < a.ldn; k += EB_THREADS) {
-      for (int sg = 0; sg < (BINS ? md.n_seg : 1); ++sg) {
+      for (int sg = 0; sg < (VAR == 1 ? md.n_seg : 1); ++sg) {
         a.gy_hi[sg * a.seg_stride + ro + k] = 0.f;
         if (a.split) a.gy_lo[sg * a.seg_stride + ro + k] = 0.f;
       }
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   // dlnL/dq of each (the second pass after the node loop)
   __shared__ float qa_s[MAX_NEB_AGE], gqa_s[MAX_NEB_AGE];
   const float* qa = nullptr;
-  if (!BINS && a.qneb) {
+  if constexpr (VAR == 2) {
     for (int i = tid; i < g.neb_na; i += EB_THREADS) qa_s[i] = a.qneb[(size_t)r * MAX_NEB_AGE + i];
     __syncthreads();
     qa = qa_s;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   //      gather starts
 #pragma unroll 4
   for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
-    if constexpr (BINS) {
+    if constexpr (VAR == 1) {
       float yv[MAX_SEG];
 #pragma unroll
       for (int sg = 0; sg < MAX_SEG; ++sg) yv[sg] = sg < md.n_seg ? Yr[sg * a.seg_stride + k] : 0.f;
@@ -712,7 +713,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   }
   // age-binned dust: d/d(tau_b, slope_b) of each bin, d/dQ of each block
   float g_bin[2 * MAX_DUST_BIN] = {}, g_qs[MAX_SEG + 1] = {};
-  if constexpr (BINS) {
+  if constexpr (VAR == 1) {
     // F = e^{-tau_d} [ sum_s A_s (Y_s + Q_s neb) + O + Q_rest neb ], A_s = e^{-tau_s},
     // tau_s = sum_b M_sb tau_b shape_b (atten.cuh's attenuated_bins)
     for (int k = tid; k < a.ldn; k += EB_THREADS) {
@@ -933,7 +934,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     l_spec += __shfl_xor_sync(0xffffffffu, l_spec, o);
     um_spec += __shfl_xor_sync(0xffffffffu, um_spec, o);
   }
-  if constexpr (BINS) {
+  if constexpr (VAR == 1) {
 #pragma unroll
     for (int q = 0; q < 2 * MAX_DUST_BIN; ++q)
 #pragma unroll
@@ -948,7 +949,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
     for (int q = 0; q < EB_NREDF; ++q) red[warp][q] = (double)vf[q];
     red[warp][EB_NREDF] = l_spec;
     red[warp][EB_NREDF + 1] = um_spec;
-    if constexpr (BINS) {
+    if constexpr (VAR == 1) {
 #pragma unroll
       for (int q = 0; q < 2 * MAX_DUST_BIN; ++q) red[warp][EB_NRED + q] = (double)g_bin[q];
 #pragma unroll
@@ -958,7 +959,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   __syncthreads();
   if (warp == 0) {
     double col = 0.0;
-    if (lane < (BINS ? EB_NRED + EB_NREDB : EB_NRED))
+    if (lane < (VAR == 1 ? EB_NRED + EB_NREDB : EB_NRED))
       for (int w = 0; w < EB_WARPS; ++w) col += red[w][lane];
     // the photometric lnL terms and d lnL/d ln(mass) pieces in FP64, one band per lane
     double bl = 0.0, bu = 0.0, gfp[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1017,7 +1018,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         rg[RG_FLOOR + k] = gfp[k];
         rg[RG_FLOOR + 4 + k] = s[9 + k];
       }
-      if constexpr (BINS) {
+      if constexpr (VAR == 1) {
         for (int q = 0; q < 2 * MAX_DUST_BIN; ++q) rg[RG_BIN + q] = s[EB_NRED + q];
         for (int q = 0; q <= MAX_SEG; ++q) rg[RG_QSEG + q] = s[EB_NRED + 2 * MAX_DUST_BIN + q];
         rg[RG_QY] = s[EB_NRED + 2 * MAX_DUST_BIN];
@@ -1034,9 +1035,9 @@ cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a_in, size_t* smem_needed, cud
   a.lines_off = (int)epi_bwd_lines_off(a);
   const size_t smem = epi_bwd_smem(a);
   if (smem_needed) *smem_needed = smem;
-  static DynSmemCache set_for[3];
-  const int m = a.md.n_bin > 0 ? 2 : (a.md.use_lines ? 1 : 0);
-  auto k = m == 2 ? k_epi_bwd<false, true> : (m == 1 ? k_epi_bwd<true> : k_epi_bwd<false>);
+  static DynSmemCache set_for[4];
+  const int m = a.md.n_bin > 0 ? 2 : a.qneb ? 3 : (a.md.use_lines ? 1 : 0);
+  auto k = m == 3 ? k_epi_bwd<false, 2> : m == 2 ? k_epi_bwd<false, 1> : (m == 1 ? k_epi_bwd<true> : k_epi_bwd<false>);
   cudaError_t e = ensure_dyn_smem(k, smem, &set_for[m]);
   if (e != cudaSuccess) return e;
   return launch_pdl(k, dim3(a.n), dim3(EB_THREADS), smem, s, a);

@@ -60,8 +60,9 @@ size_t epilogue_smem(const EpiArgs& a) {
 // MULTI: rows of several fits (serving), row r reads model mtab[row_model[r]];
 // otherwise every row reads the model in the kernel parameters.  LINES: an
 // instance with the emission lines (the one without keeps its code free of them).
-// BINS: the age-binned attenuation (one Y per attenuated block).
-template <bool MULTI, bool LINES, bool BINS = false>
+// VAR: 1 the age-binned attenuation (one Y per attenuated block), 2 the
+// nebular age axis (per-age ionising weights); 0 neither.
+template <bool MULTI, bool LINES, int VAR = 0>
 __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_constant__ EpiArgs a) {
   pdl_enter();
   const int r = blockIdx.x;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
   // nebular age axis: the row's Q-weighted weight of each nebular SSP age
   __shared__ float qa_s[MAX_NEB_AGE];
   const float* qa = nullptr;
-  if (!BINS && a.qneb) {
+  if constexpr (VAR == 2) {
     for (int i = tid; i < g.neb_na; i += blockDim.x) qa_s[i] = a.qneb[(size_t)r * MAX_NEB_AGE + i];
     __syncthreads();
     qa = qa_s;
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 8) k_epilogue(const __grid_consta
     const float ys = a.lam8 ? rs.y_scale * a.lam8[k] : 1.f;
     const float o = O2r ? Or[k] + O2r[k] : Or[k];
     float F;
-    if constexpr (BINS) {
+    if constexpr (VAR == 1) {
       float yv[MAX_SEG];
 #pragma unroll
       for (int sg = 0; sg < MAX_SEG; ++sg) yv[sg] = sg < md.n_seg ? Yr[sg * a.seg_stride + k] * ys : 0.f;
@@ -339,14 +340,16 @@ cudaError_t launch_epilogue(const EpiArgs& a_in, cudaStream_t s) {
   EpiArgs a = a_in;
   a.lines_off = (int)epilogue_lines_off(a);
   const size_t smem = epilogue_smem(a);
-  static DynSmemCache set_for[5];
+  static DynSmemCache set_for[6];
   const bool lines = a.row_model ? a.g.n_line > 0 : a.md.use_lines != 0;
-  const bool bins = !a.row_model && a.md.n_bin > 0;   // age-binned dust: neither served nor with lines
-  const int m = bins ? 4 : (a.row_model ? 1 : 0) + (lines ? 2 : 0);
+  // age-binned dust and the nebular age axis: neither served nor with lines
+  const bool bins = !a.row_model && a.md.n_bin > 0, axis = !a.row_model && a.qneb;
+  const int m = bins ? 4 : axis ? 5 : (a.row_model ? 1 : 0) + (lines ? 2 : 0);
   auto k = m == 0 ? k_epilogue<false, false>
          : m == 1 ? k_epilogue<true, false>
          : m == 2 ? k_epilogue<false, true>
-         : m == 3 ? k_epilogue<true, true> : k_epilogue<false, false, true>;
+         : m == 3 ? k_epilogue<true, true>
+         : m == 4 ? k_epilogue<false, false, 1> : k_epilogue<false, false, 2>;
   cudaError_t e = ensure_dyn_smem(k, smem, &set_for[m]);
   if (e != cudaSuccess) return e;
   return launch_pdl(k, dim3(a.n), dim3(EPI_THREADS), smem, s, a);
