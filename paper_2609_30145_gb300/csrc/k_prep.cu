@@ -338,6 +338,8 @@ struct OrderArgs {
   int n, ld;
   int* perm;
   ModelDev md;
+  const ModelDev* mtab;   // rows of several fits (serving): row r's model is mtab[row_model[r]]
+  const int* row_model;   // NULL: every row uses md
   int by_pair;       // 1: two redshift halves, bracket pair, then redshift
   int n_pairs;       // bracket pairs (by_pair)
 };
@@ -350,8 +352,6 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_order(const __grid_constant__
   const int base = blockIdx.x * ORDER_CHUNK;
   const int m = min(ORDER_CHUNK, oa.n - base);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const float zf = (float)md.zf;
-  const int zoff = md.offs[SED_KEY_ZRED];
   __shared__ int s_zlo, s_zhi;   // redshift range of the chunk's valid rows (float bits: z >= 0)
   for (int b = tid; b <= ORDER_BINS; b += ORDER_THREADS) cnt[b] = 0;
   if (tid == 0) { s_zlo = 0x7f7fffff; s_zhi = 0; }
@@ -364,8 +364,12 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_order(const __grid_constant__
     const int i = tid + u * ORDER_THREADS;
     zv[u] = -1.f;
     if (i < m) {
-      const float z = oa.theta[(size_t)(base + i) * oa.ld + zoff];
-      if (z >= 0.f && z < zf) zv[u] = z;
+      // the row's own model (serving: fits with their own layouts and z_f); a
+      // fixed redshift is read past the caller's columns
+      const ModelDev& mr = oa.row_model ? oa.mtab[oa.row_model[base + i]] : md;
+      const int zoff = mr.offs[SED_KEY_ZRED];
+      const float z = zoff < mr.n_param ? oa.theta[(size_t)(base + i) * oa.ld + zoff] : mr.fixed_v[zoff - mr.n_param];
+      if (z >= 0.f && z < (float)mr.zf) zv[u] = z;
     }
   }
   {
@@ -1069,13 +1073,14 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   // a fixed redshift (no column) needs no redshift order: the caller's order is kept
   const bool z_col = p.md.offs[SED_KEY_ZRED] < p.md.n_param;
-  if (p.perm && !p.row_model && z_col) {
+  if (p.perm && (p.row_model || z_col)) {
     OrderArgs oa;
     oa.theta = p.theta; oa.n = p.n; oa.ld = p.ld; oa.perm = p.perm; oa.md = p.md;
+    oa.mtab = p.mtab; oa.row_model = p.row_model;
     // bracket pair major when the contraction skips K tiles (the host gives
     // masks only to models with one [Fe/H], and [a/Fe], per row)
     const int pairs = std::max(p.md.n_feh - 1, 1) * (p.md.use_afe ? std::max(p.md.n_afe - 1, 1) : 1);
-    oa.by_pair = p.kmask && pairs > 1 && pairs <= ORDER_BINS / 4;
+    oa.by_pair = !p.row_model && p.kmask && pairs > 1 && pairs <= ORDER_BINS / 4;
     oa.n_pairs = pairs;
     e = launch_pdl(k_order, dim3((p.n + ORDER_CHUNK - 1) / ORDER_CHUNK), dim3(ORDER_THREADS), 0, s, oa);
     if (e != cudaSuccess) return e;

@@ -64,6 +64,8 @@ struct SrvSlot {
   // launch buffers (device)
   float* theta = nullptr;       // [max_rows][SRV_LD]
   int* rowm = nullptr;          // [max_rows]
+  int* perm = nullptr;          // [max_rows] processing order (rows grouped by redshift)
+  int* tile_win = nullptr;      // [2][ceil(max_rows/128)] node windows of the 128-row tiles
   double* lnl = nullptr;
   uint32_t* st = nullptr;
   float *W = nullptr, *W_hi = nullptr, *W_lo = nullptr, *Y = nullptr, *O = nullptr, *O2 = nullptr;
@@ -182,6 +184,17 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
   pa.W_f8 = f8 ? sl.W_f8 : nullptr;
   pa.rs = sl.rs;
   pa.err = sl.err;
+  // rows grouped by redshift (each row's own model) and each 128-row tile's
+  // node window, as sed_loglike does: the contraction then computes only the
+  // wavelength tiles its rows read, on the persistent schedule
+  pa.perm = sl.perm;
+  pa.tile_win = sl.tile_win;
+  {
+    const size_t mt = (size_t)(n + 127) / 128;
+    e = cudaMemsetAsync(sl.tile_win, 0x7f, mt * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sl.tile_win + mt, 0xff, mt * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   e = launch_prep(pa, s);
   if (e != cudaSuccess) return e;
   if (sv->prec == SED_PREC_FP32_SIMT) {
@@ -203,6 +216,7 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
     ta.Ky_pad = f8 ? L->Ky_pad8 : L->Ky_pad;
     ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
     ta.maps = &sl.maps; ta.Y = sl.Y; ta.O = sl.O; ta.O2 = sl.O2; ta.err = sl.err; ta.rs = sl.rs;
+    ta.tile_win = sl.tile_win;
     e = launch_contract_tc(ta, s);
   }
   if (e != cudaSuccess) return e;
@@ -345,7 +359,8 @@ sed_status sed_server_create(sed_ctx* ctx, const sed_server_desc* d, sed_server*
          dmalloc(sv, sl.dev, &sl.W, R * K * 4) && dmalloc(sv, sl.dev, &sl.Y, R * N * 4) &&
          dmalloc(sv, sl.dev, &sl.O, R * N * 4) && dmalloc(sv, sl.dev, &sl.O2, R * N * 4) &&
          dmalloc(sv, sl.dev, &sl.rs, R * sizeof(RowScal)) &&
-         dmalloc(sv, sl.dev, &sl.err, 256);
+         dmalloc(sv, sl.dev, &sl.err, 256) && dmalloc(sv, sl.dev, &sl.perm, R * 4) &&
+         dmalloc(sv, sl.dev, &sl.tile_win, 2 * ((R + 127) / 128) * 4);
     if (ok && sv->prec == SED_PREC_FP32)
       ok = dmalloc(sv, sl.dev, &sl.W_hi, R * K * 4) && dmalloc(sv, sl.dev, &sl.W_lo, R * K * 4);
     if (ok && sv->prec == SED_PREC_BF16) ok = dmalloc(sv, sl.dev, &sl.W_bf16, R * K * 2);
