@@ -72,7 +72,7 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the per-config accuracy and throughput leg (tiny, paper-scale photometric at 1024 "
                          "and 4096 rows, spectro-photometric [a/Fe], serving mix)")
-    ap.add_argument("--profile-case", default=None, choices=["phot", "specphot", "calib"],
+    ap.add_argument("--profile-case", default=None, choices=["phot", "specphot", "calib", "nss"],
                     help="run one small case of the hot path for an ncu capture and exit (no timing, no JSON)")
     return ap.parse_args()
 
@@ -966,7 +966,7 @@ def bench_serving(ctx, device, args):
     return out
 
 
-def bench_sampler(ctx, device, n_fits=2):
+def bench_sampler(ctx, device, n_fits=2, max_iter=5000):
     """Nested slice sampling of a fit shaped like the paper's JADES benchmark:
     15 NIRCam-like bands and a 22-entry emission-line catalogue, 8 SFH bins, one
     constant [Fe/H], nebular continuum and lines (30-line cube), birth-cloud +
@@ -1003,12 +1003,13 @@ def bench_sampler(ctx, device, n_fits=2):
     lo = np.concatenate([np.zeros(n_sfh), [-2.0, 7.0, 0.0, 0.0, -1.0, -1.3, -4.0]])
     hi = np.concatenate([np.ones(n_sfh), [0.3, 12.0, 2.0, 2.0, 0.4, 0.3, -1.0]])
     assert model.n_param == lo.size
-    model.nss(lo, hi, n_live=300, n_replace=64, n_slice_steps=40, max_iter=4, seed=1)   # warm-up
+    model.nss(lo, hi, n_live=300, n_replace=64, n_slice_steps=40, max_iter=min(4, max_iter) if n_fits else max_iter,
+              seed=1)   # warm-up (the whole run for a profile case)
     fits = []
     for f in range(n_fits):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = model.nss(lo, hi, n_live=300, n_replace=64, n_slice_steps=40, max_iter=5000, seed=100 + f)
+        r = model.nss(lo, hi, n_live=300, n_replace=64, n_slice_steps=40, max_iter=max_iter, seed=100 + f)
         dt = time.perf_counter() - t0
         fits.append({"seconds": round(dt, 3), "lnz": round(r["lnz"], 3), "info_h": round(r["info_h"], 3),
                      "n_iter": r["n_iter"], "n_like": int(r["n_like"]), "n_rows": int(r["n_rows"]),
@@ -1019,7 +1020,7 @@ def bench_sampler(ctx, device, n_fits=2):
             "settings": {"n_live": 300, "n_replace": 64, "n_slice_steps": 40, "stop_dlnz": -5.0,
                          "precision": "fp32"},
             "fits": fits,
-            "seconds_per_fit_median": round(float(np.median([f["seconds"] for f in fits])), 3),
+            "seconds_per_fit_median": round(float(np.median([f["seconds"] for f in fits])), 3) if fits else None,
             "paper_context": "4.0 min per fit and ~1.4e6 likelihood evaluations on one A100 (JADES 170891, "
                              "15 bands + 22 lines; other model and hardware)"}
 
@@ -1112,7 +1113,9 @@ def profile_case(which):
     specphot: the [a/Fe] spectro-photometric workload (107 x 12 x 5 x 6000
     grid, 1500-pixel spectrum + 20 filters) at 512 rows: one FP32 sed_loglike,
     then two FP32 sed_loglike_grad calls.
-    calib: the same with the marginalised 13-term calibration polynomial."""
+    calib: the same with the marginalised 13-term calibration polynomial.
+    nss: 30 iterations of nested slice sampling of the JADES-like fit of the
+    sampler leg (300 live points, 64 replaced, 40 slice steps)."""
     import torch
     import synth
 
@@ -1123,6 +1126,12 @@ def profile_case(which):
     from paper_2609_30145_gb300 import Context
 
     ctx = Context(0)
+    if which == "nss":
+        bench_sampler(ctx, device, n_fits=0, max_iter=30)
+        torch.cuda.synchronize()
+        ctx.close()
+        print("ok")
+        return
     if which == "phot":
         w, _, _, m, theta, _ = build_workload(WORKLOAD, ctx, 5, device)
         t = torch.from_numpy(theta).to(device)

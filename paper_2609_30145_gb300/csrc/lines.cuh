@@ -92,15 +92,21 @@ __device__ __forceinline__ float lines_at_pixel(const ModelDev& md, int i, int N
 
 // Band b's response to a line at observed wavelength x: rz = R_b(x) / Z_b, R_b
 // linear between the band's samples (0 outside them), and its slope drz in x.
+// The bracket (the last sample at or below x; the last interval at the band's
+// end) is found from the position of x between the band's ends and a walk to
+// it: one or two loads for evenly spaced samples instead of a bisection's chain
+// of dependent loads, and the same bracket for any spacing.
 __device__ __forceinline__ void line_band_resp(const ModelDev& md, int b, float x, float& rz, float& drz) {
-  int lo = md.band_start[b], hi = md.band_start[b + 1] - 1;
+  const int b0 = md.band_start[b], b1 = md.band_start[b + 1] - 1;
   rz = 0.f;
   drz = 0.f;
-  if (!(x >= md.samp2[lo].x && x <= md.samp2[hi].x)) return;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (md.samp2[mid].x <= x) lo = mid; else hi = mid;
-  }
+  const float xa = md.samp2[b0].x, xb = md.samp2[b1].x;
+  if (!(x >= xa && x <= xb)) return;
+  int j = b1 > b0 ? b0 + (int)((x - xa) / (xb - xa) * (float)(b1 - b0)) : b0;
+  j = min(max(j, b0), max(b1 - 1, b0));
+  while (j > b0 && md.samp2[j].x > x) --j;
+  while (j + 1 < b1 && md.samp2[j + 1].x <= x) ++j;
+  const int lo = j, hi = b1 > b0 ? j + 1 : b0;
   const float x0 = md.samp2[lo].x, x1 = md.samp2[hi].x;
   if (!(x1 > x0)) { rz = md.samp_rz[lo]; return; }
   const float t = (x - x0) / (x1 - x0);

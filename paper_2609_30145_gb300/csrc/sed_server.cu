@@ -203,13 +203,15 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
     ca.W = sl.W; ca.sspT = L->sspT_f32; ca.Y = sl.Y; ca.O = sl.O; ca.rs = sl.rs;
     e = launch_contract_simt(ca, s);
   } else {
-    if (sl.maps_n != n) {
+    // the operand maps are encoded once per slot, over its max_launch_rows rows:
+    // rows past a launch's n are read by its last M tile but never stored
+    if (sl.maps_n != sv->max_rows) {
       const void* a_op = f32 ? (const void*)sl.W_hi : (f8 ? (const void*)sl.W_f8 : (const void*)sl.W_bf16);
       const void* b_op = f32 ? (const void*)L->sspT_hi : (f8 ? (const void*)L->sspT_f8 : (const void*)L->sspT_bf16);
-      if (tc_encode_maps(sv->ctx->encode_fn, &sl.maps, sv->prec, a_op, sl.W_lo, b_op, L->sspT_lo, n, g->n_lam,
-                         f8 ? L->Kpad8 : L->Kpad))
+      if (tc_encode_maps(sv->ctx->encode_fn, &sl.maps, sv->prec, a_op, sl.W_lo, b_op, L->sspT_lo, sv->max_rows,
+                         g->n_lam, f8 ? L->Kpad8 : L->Kpad))
         return cudaErrorInvalidValue;
-      sl.maps_n = n;
+      sl.maps_n = sv->max_rows;
     }
     TcArgs ta{};
     ta.n = n; ta.n_lam = g->n_lam; ta.ldn = sv->ldn; ta.prec = sv->prec;
