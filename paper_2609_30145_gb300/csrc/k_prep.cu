@@ -254,6 +254,41 @@ __device__ void lin_node_fill(const GridDev& g, int ag, int NT, const float* T, 
   }
 }
 
+// Cubic Hermite interpolant (FP64) of column pair c of the cosmology table
+// (value, derivative) at redshift zd.
+__device__ __forceinline__ double cosmo_interp(const ModelDev& md, double zd, int c) {
+  const double q = zd * md.ctab_inv_h;
+  const int i = min((int)q, md.n_ctab - 1);
+  const double u = q - (double)i, v = 1.0 - u;
+  const double* t0 = md.ctab + COSMO_COLS * (size_t)i + 2 * c;
+  const double* t1 = t0 + COSMO_COLS;
+  const double h00 = (1.0 + 2.0 * u) * v * v, h10 = u * v * v * md.ctab_h;
+  const double h01 = u * u * (3.0 - 2.0 * u), h11 = -u * u * v * md.ctab_h;
+  return h00 * t0[0] + h10 * t0[1] + h01 * t1[0] + h11 * t1[1];
+}
+
+// T_max = t_univ(z) - t_univ(z_f) and ln(T_max / 10 Myr) alone, with the
+// row's redshift status: the SFH edges wait for it, the rest of the row's
+// cosmology (row_cosmo) does not.
+struct TmaxRow {
+  double tmax;
+  float lrat;
+  uint32_t status;   // SED_ROW_BAD_THETA (z or logmass), SED_ROW_BAD_Z, SED_ROW_BAD_TMAX or 0
+};
+__device__ TmaxRow row_tmax(const ModelDev& md, float z, float lm) {
+  TmaxRow t{0.0, 0.f, 0u};
+  if (!isfinite(z) || !isfinite(lm)) {
+    t.status = SED_ROW_BAD_THETA;
+  } else if (!(z >= 0.f && (double)z < md.zf)) {
+    t.status = SED_ROW_BAD_Z;
+  } else {
+    t.tmax = cosmo_interp(md, (double)z, 1) - md.t_zf_yr;
+    t.lrat = t.tmax > 1e7 ? logf((float)(t.tmax * 1e-7)) : 0.f;
+    t.status = t.tmax > 1e7 ? 0u : SED_ROW_BAD_TMAX;
+  }
+  return t;
+}
+
 __device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm, int lane) {
   // All 32 lanes of a warp call it with the same z and lm; lane 0's result is
   // complete.  Lanes 0-3 each evaluate one of the four interpolants in the same
@@ -266,14 +301,7 @@ __device__ CosmoRow row_cosmo(const ModelDev& md, float z, float lm, int lane) {
     c.status = SED_ROW_BAD_Z;
   } else {
     const double zd = (double)z, zp = 1.0 + zd;
-    const double q = zd * md.ctab_inv_h;
-    const int i = min((int)q, md.n_ctab - 1);
-    const double u = q - (double)i, v = 1.0 - u;
-    const double* t0 = md.ctab + COSMO_COLS * (size_t)i + 2 * (lane & 3);
-    const double* t1 = t0 + COSMO_COLS;
-    const double h00 = (1.0 + 2.0 * u) * v * v, h10 = u * v * v * md.ctab_h;
-    const double h01 = u * u * (3.0 - 2.0 * u), h11 = -u * u * v * md.ctab_h;
-    const double val = h00 * t0[0] + h10 * t0[1] + h01 * t1[0] + h11 * t1[1];
+    const double val = cosmo_interp(md, zd, lane & 3);
     const double dc = __shfl_sync(0xffffffffu, val, 0), tu = __shfl_sync(0xffffffffu, val, 1);
     const double l1 = __shfl_sync(0xffffffffu, val, 2), izp = __shfl_sync(0xffffffffu, val, 3);
     const double tmax = tu - md.t_zf_yr;
@@ -448,13 +476,14 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_order(const __grid_constant__
 }
 
 constexpr int PREP_THREADS = 128;
+constexpr int PREP_KWARPS = PREP_THREADS / 32 - 1;   // warps writing W; the last one assembles the row's scalars
 
 // Row p of the launch processes the caller's row r = perm[p] and records r in
 // RowScal::orig; every later kernel indexes by p and writes results to r.
 template <bool MULTI>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepKernelArgs ka) {
-  pdl_enter();
   const PrepArgs& a = ka.p;
+  pdl_enter();
   const int p = blockIdx.x;
   const int r = a.perm ? a.perm[p] : p;
   const ModelDev& md = MULTI ? a.mtab[a.row_model[r]] : a.md;
@@ -480,15 +509,20 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __shared__ int s_nnz[PREP_THREADS / 32];
   // K tiles the row touches: [Fe/H] nodes that bracket some bin, ages whose
   // cell (or tent) reaches below T_max, and both [a/Fe] nodes of the bracket
-  __shared__ unsigned long long s_mset;
+  __shared__ unsigned long long s_mpart[PREP_THREADS / 32];   // per warp
   __shared__ int s_alim;
   __shared__ uint32_t s_km[KMASK_WORDS];
-  if (tid == 0) { s_mset = 0ull; s_alim = 0; }
+  if (tid == 0) s_alim = 0;
   if (tid < KMASK_WORDS) s_km[tid] = 0u;
 
-  // ---- finiteness of the whole row, and the row's cosmology (one lane, in
-  //      the shadow of the row's loads)
+  // ---- in the shadow of the row's loads: finiteness of the whole row; T_max
+  //      (warp 0: the SFH edges wait for it); the rest of the row's cosmology
+  //      (the last warp: only the epilogue needs it); the bins' [Fe/H] brackets
+  //      and the cleared weight table (the warps between)
   __shared__ CosmoRow s_cr;
+  __shared__ double s_tmax;
+  __shared__ float s_lrat;
+  __shared__ uint32_t s_zst;
   int bad = 0;
   for (int j = tid; j < md.n_param; j += blockDim.x) {
     const float v = th[j];
@@ -496,11 +530,28 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     bad |= !isfinite(v);
   }
   for (int j = tid; j < md.n_fixed; j += blockDim.x) th_s[md.n_param + j] = md.fixed_v[j];   // fixed keys
+  unsigned long long mpart = 0ull;
   if (warp == 0) {
+    const TmaxRow t = row_tmax(md, theta_col(md, th, md.offs[SED_KEY_ZRED]), theta_col(md, th, md.offs[SED_KEY_LOGMASS]));
+    if (lane == 0) { s_tmax = t.tmax; s_lrat = t.lrat; s_zst = t.status; }
+  } else if (warp == PREP_KWARPS) {
     const CosmoRow c = row_cosmo(md, theta_col(md, th, md.offs[SED_KEY_ZRED]),
                                  theta_col(md, th, md.offs[SED_KEY_LOGMASS]), lane);
     if (lane == 0) s_cr = c;
+  } else {
+    constexpr int NB = PREP_THREADS - 64;   // the threads of the warps between
+    for (int j = tid - 32; j < NA * NZ; j += NB) Ws[j] = 0.f;
+    for (int i = tid - 32; i < NT; i += NB) {
+      int j0, j1;
+      float w0, w1;
+      bracket_f(md.feh, md.n_feh, theta_col(md, th, md.offs[SED_KEY_LOGZSOL] + (md.zmode == 0 ? i : 0)), j0, w0, j1, w1);
+      zb[i] = j0;
+      zt[i] = w1;   // weight of j0 + 1 (0 when n_feh == 1)
+      mpart |= (1ull << j0) | (1ull << j1);
+    }
   }
+  for (int o = 16; o; o >>= 1) mpart |= __shfl_xor_sync(0xffffffffu, mpart, o);
+  if (lane == 0) s_mpart[warp] = mpart;
   bad = __syncthreads_or(bad);
   th = th_s;
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
@@ -519,9 +570,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     const float sg = th[md.offs[SED_KEY_SIGMA_GAS]];
     if (!(sg >= 0.f && sg <= md.sgas_max_kms)) status = SED_ROW_BAD_THETA;
   }
-  const CosmoRow cr = s_cr;
-  if (!status) status = cr.status;
-  const double tmax = status ? 0.0 : (double)cr.tmax_d;
+  if (!status) status = s_zst;
+  const double tmax = status ? 0.0 : s_tmax;
 
   RowScal* out = a.rs + p;
   const int Kpad = L.Kpad;
@@ -545,30 +595,22 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     return;
   }
 
-  // ---- SFH edges (FP32) and per-bin quantities
+  // ---- SFH edges (FP32) and per-bin rates: thread i forms both edges of bin
+  //      i (the same function of i, so neighbours agree on the shared edge)
   const float* m = th + md.offs[SED_KEY_SFH];
-  const float* zeta = th + md.offs[SED_KEY_LOGZSOL];
-  const float lrat = cr.lrat;
-  for (int i = tid; i <= NT; i += blockDim.x) T[i] = sfh_edge(i, NT, tmax, lrat);
-  for (int j = tid; j < NA * NZ; j += blockDim.x) Ws[j] = 0.f;
-  __syncthreads();
+  const float lrat = s_lrat;
   for (int i = tid; i < NT; i += blockDim.x) {
-    if (md.sfh_linear) {
-      // linear scheme, pass 1: the factor scaling the bin's tent shares
-      rate[i] = lin_bin_scale(g, T[i], T[i + 1], m[i], m[i + 1]);
-    } else {
-      rate[i] = m[i] / (T[i + 1] - T[i]);
-    }
-    int j0, j1;
-    float w0, w1;
-    bracket_f(md.feh, md.n_feh, zeta[md.zmode == 0 ? i : 0], j0, w0, j1, w1);
-    zb[i] = j0;
-    zt[i] = w1;   // weight of j0 + 1 (0 when n_feh == 1)
-    if (a.kmask) atomicOr(&s_mset, (1ull << j0) | (1ull << j1));
+    const float t0 = sfh_edge(i, NT, tmax, lrat), t1 = sfh_edge(i + 1, NT, tmax, lrat);
+    T[i] = t0;
+    if (i == NT - 1) T[NT] = t1;
+    // linear scheme, pass 1: the factor scaling the bin's tent shares
+    rate[i] = md.sfh_linear ? lin_bin_scale(g, t0, t1, m[i], m[i + 1]) : m[i] / (t1 - t0);
   }
-  if (a.kmask)
+  if (a.kmask) {
+    const float tn = sfh_edge(NT, NT, tmax, lrat);
     for (int ag = tid; ag < NA; ag += blockDim.x)
-      if (g.cell_lo[ag] < T[NT]) atomicMax(&s_alim, ag + 1);
+      if (g.cell_lo[ag] < tn) atomicMax(&s_alim, ag + 1);
+  }
   __syncthreads();
 
   // ---- weights on (age, feh): thread per age node
@@ -609,51 +651,179 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   float qpart = 0.f;
   int nnz = 0;
   float* Vs = smem + NA * NZ;           // FP8 path: W_k 2^-e_k
-  // touched columns: the bracket nodes (also where a weight is 0 at a node: the
-  // adjoint reads their derivative) and one age past the last cell below T_max
-  // (the linear scheme's tents reach one node further)
-  const unsigned long long mset = s_mset;
-  const int alim = s_alim + 1;
-  const int f8_shift = L.Ky_pad8 - L.Ky_pad;
-  // the layout tables through the read-only path, so that the unrolled loads
-  // need not wait behind the stores of W
-#pragma unroll 4
-  for (int k = tid; k < Kpad; k += blockDim.x) {
-    const int code = __ldg(L.k_code + k);
-    float v = 0.f;
-    if (code >= 0) {
-      const int n = code >> 24, mm = (code >> 16) & 0xff, ag = code & 0xffff;
-      const float wn = (n == n0 ? wn0 : 0.f) + (n == n1 && n1 != n0 ? wn1 : 0.f);
-      v = wn * Ws[ag * NZ + mm];
-    }
-    if (k < L.Ky_pad) qpart += v * __ldg(L.q_s + k);
-    nnz += v != 0.f;
-    if (a.kmask) {
-      // 32 consecutive columns per warp step: one K tile of every layout
+  // the row's scalars, assembled by the last warp while the others write W
+  static_assert(sizeof(RowScal) % 4 == 0, "RowScal is cleared and copied as words");
+  __shared__ RowScal s_rs;
+  if (warp < PREP_KWARPS) {
+    // touched columns: the bracket nodes (also where a weight is 0 at a node:
+    // the adjoint reads their derivative) and one age past the last cell below
+    // T_max (the linear scheme's tents reach one node further)
+    unsigned long long mset = 0ull;
+    for (int w = 0; w < PREP_THREADS / 32; ++w) mset |= s_mpart[w];
+    const int alim = s_alim + 1;
+    const int f8_shift = L.Ky_pad8 - L.Ky_pad;
+    // four consecutive columns per lane (one int4 of column codes, vector
+    // stores); a warp step spans 128 columns, so the loop is uniform per warp
+    // and the K-tile mask needs no partial-warp ballot
+    for (int kb = warp * 128; kb < Kpad; kb += PREP_KWARPS * 128) {
+      const int k4 = kb + 4 * lane;
+      const bool in = k4 < Kpad;   // Kpad is a multiple of 32, so a lane's four columns are all in or all out
+      int4 cd = make_int4(-1, -1, -1, -1);
+      float4 qs = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (in) {
+        cd = __ldg(reinterpret_cast<const int4*>(L.k_code + k4));
+        if (k4 < L.Ky_pad) qs = __ldg(reinterpret_cast<const float4*>(L.q_s + k4));
+      }
+      const int cc[4] = {cd.x, cd.y, cd.z, cd.w};
+      const float qq[4] = {qs.x, qs.y, qs.z, qs.w};
+      float v[4];
       bool touched = false;
-      if (code >= 0) {
-        const int n = code >> 24, mm = (code >> 16) & 0xff, ag = code & 0xffff;
-        touched = (n == n0 || (n == n1 && (md.use_afe || wn1 != 0.f))) && ((mset >> mm) & 1ull) && ag < alim;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        v[j] = 0.f;
+        const int code = cc[j];
+        if (code >= 0) {
+          const int n = code >> 24, mm = (code >> 16) & 0xff, ag = code & 0xffff;
+          const float wn = (n == n0 ? wn0 : 0.f) + (n == n1 && n1 != n0 ? wn1 : 0.f);
+          v[j] = wn * Ws[ag * NZ + mm];
+          touched |= (n == n0 || (n == n1 && (md.use_afe || wn1 != 0.f))) && ((mset >> mm) & 1ull) && ag < alim;
+        }
+        qpart = fmaf(v[j], qq[j], qpart);   // q_s is 0 past the young block
+        nnz += v[j] != 0.f;
       }
-      if (__ballot_sync(0xffffffffu, touched) && lane == 0) {
-        const int q = a.W_f8 ? (k < L.Ky_pad ? k : k + f8_shift) : k;
+      if (a.kmask) {
+        // one K tile holds 32, 64 or 128 columns, i.e. 8, 16 or 32 lanes' quads:
+        // the lowest lane of each tile's group sets its bit
+        const int q = a.W_f8 ? (k4 < L.Ky_pad ? k4 : k4 + f8_shift) : k4;
         const int t = q >> a.kt_shift;
-        atomicOr(&s_km[t >> 5], 1u << (t & 31));
+        const unsigned grp = __match_any_sync(0xffffffffu, t);
+        const unsigned tb = __ballot_sync(0xffffffffu, touched && in);
+        if ((tb & grp) && lane == __ffs(grp) - 1) atomicOr(&s_km[t >> 5], 1u << (t & 31));
+      }
+      if (!in) continue;
+      const size_t o = (size_t)p * Kpad + k4;
+      if (a.W) *reinterpret_cast<float4*>(a.W + o) = make_float4(v[0], v[1], v[2], v[3]);
+      if (a.W_hi) {
+        const float4 h = make_float4(tf32_rna(v[0]), tf32_rna(v[1]), tf32_rna(v[2]), tf32_rna(v[3]));
+        *reinterpret_cast<float4*>(a.W_hi + o) = h;
+        *reinterpret_cast<float4*>(a.W_lo + o) = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
+      }
+      if (a.W_bf16) {
+        const __nv_bfloat162 b01 = __floats2bfloat162_rn(v[0], v[1]), b23 = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t*>(&b01);
+        u.y = *reinterpret_cast<const uint32_t*>(&b23);
+        *reinterpret_cast<uint2*>(a.W_bf16 + o) = u;
+      }
+      if (a.W_f8) {
+        const float4 c8 = __ldg(reinterpret_cast<const float4*>(L.col8 + k4));
+        Vs[k4] = v[0] * c8.x;
+        Vs[k4 + 1] = v[1] * c8.y;
+        Vs[k4 + 2] = v[2] * c8.z;
+        Vs[k4 + 3] = v[3] * c8.w;
       }
     }
-    const size_t o = (size_t)p * Kpad + k;
-    if (a.W) a.W[o] = v;
-    if (a.W_hi) {
-      const float h = tf32_rna(v);
-      a.W_hi[o] = h;
-      a.W_lo[o] = v - h;
+    for (int o = 16; o; o >>= 1) {
+      qpart += __shfl_xor_sync(0xffffffffu, qpart, o);
+      nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
     }
-    if (a.W_bf16) a.W_bf16[o] = __float2bfloat16_rn(v);
-    if (a.W_f8) Vs[k] = v * L.col8[k];
-  }
-  for (int o = 16; o; o >>= 1) {
-    qpart += __shfl_xor_sync(0xffffffffu, qpart, o);
-    nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+  } else {
+    const CosmoRow cr = s_cr;
+    // ---- rest-frame node window the epilogue reads: the redshifted filter
+    //      samples and the spectral pixels with 5 dispersions on either side.
+    //      Lanes 0-3 look up its four candidate ends in the index table over
+    //      ln(lambda) (each entry lies within one node of the exact bracket);
+    //      the margins cover that slack and the interpolation's k + 1.
+    const int N = g.n_lam;
+    const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
+    int lo = N - 1, hi = 0;
+    float xl = 0.f;
+    bool use = false;
+    if (lane < 2 && md.n_filt > 0) {
+      xl = __logf(fminf(fmaxf((lane == 0 ? md.samp_lam_min : md.samp_lam_max) * cr.inv1pz, lam0), lamN));
+      use = true;
+    } else if (lane >= 2 && lane < 4 && md.n_pix > 0) {
+      const double l1 = (double)cr.ln1pz_hi + (double)cr.ln1pz_lo;
+      const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
+      xl = lane == 2 ? fminf(fmaxf((float)(md.pix_ln_min - l1) - 5.f * md.pix_s_max, ll0), llN)
+                     : fminf(fmaxf((float)(md.pix_ln_max - l1) + 5.f * md.pix_s_max, ll0), llN);
+      use = true;
+    }
+    if (use) {
+      int q = (int)((xl - g.lut_x0) * g.lut_inv_h);
+      q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
+      const int k = g.lut[q];
+      if ((lane & 1) == 0) lo = k; else hi = k;
+    }
+    for (int o = 2; o; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int win_lo = max(lo - 3, 0);
+    const int win_hi = min(max(hi + 4, win_lo + 1), N - 1);
+    for (int i = lane; i < (int)(sizeof(RowScal) / 4); i += 32) reinterpret_cast<uint32_t*>(&s_rs)[i] = 0u;
+    __syncwarp();
+    if (lane == 0) {
+      RowScal& rs = s_rs;   // fields set in place (shared memory; no local copy)
+      rs.p_phot = cr.p_phot;
+      rs.s_spec = cr.s_spec;
+      rs.inv1pz = cr.inv1pz;
+      rs.ln1pz_hi = cr.ln1pz_hi;
+      rs.ln1pz_lo = cr.ln1pz_lo;
+      rs.tau_bc = th[md.offs[SED_KEY_TAU_POW]];
+      rs.alpha_bc = th[md.offs[SED_KEY_ALPHA_POW]];
+      rs.tau_d = th[md.offs[SED_KEY_DIFFUSE_TAU]];
+      rs.delta = th[md.offs[SED_KEY_DIFFUSE_INDEX]];
+      // noise-floor terms (App. sys_floor): 10^column for a term that is on
+      for (int arm = 0; arm < 2; ++arm)
+        for (int k = 0; k < 4; ++k)
+          rs.fl[arm][k] = ((md.floor_bits[arm] >> k) & 1) ? exp10f(th[md.offs[SED_KEY_LOG_ERR_SCALE_PHOT + 4 * arm + k]])
+                                                          : (k == 0 ? 1.f : 0.f);
+      if (md.use_neb) {
+        int u0, u1, z0, z1;
+        float wu0, wu1, wz0, wz1;
+        bracket_f(md.neb_logu, md.neb_nu, th[md.offs[SED_KEY_GAS_LOGU]], u0, wu0, u1, wu1);
+        bracket_f(md.neb_logz, md.neb_nz, th[md.offs[SED_KEY_GAS_LOGZ]], z0, wz0, z1, wz1);
+        const int nl = g.n_lam;
+        rs.neb_w[0] = wu0 * wz0; rs.neb_off[0] = (u0 * md.neb_nz + z0) * nl;
+        rs.neb_w[1] = wu0 * wz1; rs.neb_off[1] = (u0 * md.neb_nz + z1) * nl;
+        rs.neb_w[2] = wu1 * wz0; rs.neb_off[2] = (u1 * md.neb_nz + z0) * nl;
+        rs.neb_w[3] = wu1 * wz1; rs.neb_off[3] = (u1 * md.neb_nz + z1) * nl;
+        float du0, du1, dz0, dz1;
+        bracket_df(md.neb_logu, md.neb_nu, th[md.offs[SED_KEY_GAS_LOGU]], u0, u1, du0, du1);
+        bracket_df(md.neb_logz, md.neb_nz, th[md.offs[SED_KEY_GAS_LOGZ]], z0, z1, dz0, dz1);
+        rs.neb_dwu[0] = du0 * wz0; rs.neb_dwu[1] = du0 * wz1; rs.neb_dwu[2] = du1 * wz0; rs.neb_dwu[3] = du1 * wz1;
+        rs.neb_dwz[0] = wu0 * dz0; rs.neb_dwz[1] = wu0 * dz1; rs.neb_dwz[2] = wu1 * dz0; rs.neb_dwz[3] = wu1 * dz1;
+      }
+      rs.dlns_dz = cr.dlns_dz;
+      rs.dlnp_dz = cr.dlnp_dz;
+      rs.dtmax_dz = cr.dtmax_dz;
+      rs.tmax = (float)tmax;
+      rs.lrat = lrat;
+      rs.status = 0;
+      rs.orig = r;
+      rs.y_scale = 1.f;
+      rs.sg_ln = md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] / (float)C_KMS : 0.f;
+      rs.fob = md.fesc_geom ? th[md.offs[SED_KEY_FRAC_OBRUN]] : 0.f;
+      // the emission lines' gas dispersion (km/s): a column, a fixed value, or
+      // tied to the stellar dispersion (the row's sampled sigma_gal, else the fixed one)
+      rs.sgas = md.gas_mode == SED_GAS_SIGMA_SAMPLED ? th[md.offs[SED_KEY_SIGMA_GAS]]
+              : md.gas_mode == SED_GAS_SIGMA_FIXED ? md.sgas_fix_kms
+              : (md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] : md.sgal_fix_kms);
+      rs.igm_f = md.use_igm ? th[md.offs[SED_KEY_IGM_FACTOR]] : 0.f;
+      rs.k_lo = win_lo;
+      rs.k_hi = win_hi;
+      if (md.n_bin > 0)   // age-binned dust (App. dust_attn): each bin's law parameters
+        for (int b = 0; b < md.n_bin; ++b) {
+          rs.bin_tau[b] = th[md.offs[SED_KEY_DUST_BINS] + 2 * b];
+          rs.bin_slope[b] = th[md.offs[SED_KEY_DUST_BINS] + 2 * b + 1];
+        }
+      if (a.tile_win) {   // union of the windows of this row's 128-row tile
+        const int mt = (a.n + 127) >> 7;
+        atomicMin(&a.tile_win[p >> 7], win_lo);
+        atomicMax(&a.tile_win[mt + (p >> 7)], win_hi);
+      }
+    }
   }
   if (md.n_bin > 0) {
     // age-binned dust: Q of each attenuated block and of the ages outside
@@ -690,7 +860,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       a.qneb[(size_t)p * MAX_NEB_AGE + i] = q;
     }
   }
-  if (lane == 0) { s_red[warp] = qpart; s_nnz[warp] = nnz; }
+  if (lane == 0) { s_red[warp] = qpart; s_nnz[warp] = nnz; }   // 0 from the last warp
   __syncthreads();
   if (a.kmask && tid < a.kmask_w && s_km[tid]) atomicOr(&a.kmask[(size_t)(p >> 7) * a.kmask_w + tid], s_km[tid]);
 
@@ -718,115 +888,27 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     }
   }
 
-  // ---- rest-frame node window the epilogue reads: the redshifted filter
-  //      samples and the spectral pixels with 5 dispersions on either side.
-  //      Lanes 0-3 of warp 0 look up its four candidate ends in the index table
-  //      over ln(lambda) (each entry lies within one node of the exact bracket);
-  //      the margins cover that slack and the interpolation's k + 1.
-  int win_lo = 0, win_hi = 0;
-  if (warp == 0) {
-    const int N = g.n_lam;
-    const float lam0 = g.lam_f[0], lamN = g.lam_f[N - 1];
-    int lo = N - 1, hi = 0;
-    float xl = 0.f;
-    bool use = false;
-    if (lane < 2 && md.n_filt > 0) {
-      xl = __logf(fminf(fmaxf((lane == 0 ? md.samp_lam_min : md.samp_lam_max) * cr.inv1pz, lam0), lamN));
-      use = true;
-    } else if (lane >= 2 && lane < 4 && md.n_pix > 0) {
-      const double l1 = (double)cr.ln1pz_hi + (double)cr.ln1pz_lo;
-      const float ll0 = g.lnl_hi[0], llN = g.lnl_hi[N - 1];
-      xl = lane == 2 ? fminf(fmaxf((float)(md.pix_ln_min - l1) - 5.f * md.pix_s_max, ll0), llN)
-                     : fminf(fmaxf((float)(md.pix_ln_max - l1) + 5.f * md.pix_s_max, ll0), llN);
-      use = true;
-    }
-    if (use) {
-      int q = (int)((xl - g.lut_x0) * g.lut_inv_h);
-      q = q < 0 ? 0 : (q >= g.lut_n ? g.lut_n - 1 : q);
-      const int k = g.lut[q];
-      if ((lane & 1) == 0) lo = k; else hi = k;
-    }
-    for (int o = 2; o; o >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    win_lo = max(lo - 3, 0);
-    win_hi = min(max(hi + 4, win_lo + 1), N - 1);
-  }
-
+  // ---- the sums over warps, then the row's scalars to global memory (one word per thread)
   if (tid == 0) {
     float qy = 0.f;
-    for (int w = 0; w < PREP_THREADS / 32; ++w) qy += s_red[w];
-    RowScal rs{};
-    rs.p_phot = cr.p_phot;
-    rs.s_spec = cr.s_spec;
-    rs.inv1pz = cr.inv1pz;
-    rs.ln1pz_hi = cr.ln1pz_hi;
-    rs.ln1pz_lo = cr.ln1pz_lo;
-    rs.tau_bc = th[md.offs[SED_KEY_TAU_POW]];
-    rs.alpha_bc = th[md.offs[SED_KEY_ALPHA_POW]];
-    rs.tau_d = th[md.offs[SED_KEY_DIFFUSE_TAU]];
-    rs.delta = th[md.offs[SED_KEY_DIFFUSE_INDEX]];
-    // noise-floor terms (App. sys_floor): 10^column for a term that is on
-    for (int arm = 0; arm < 2; ++arm)
-      for (int k = 0; k < 4; ++k)
-        rs.fl[arm][k] = ((md.floor_bits[arm] >> k) & 1) ? exp10f(th[md.offs[SED_KEY_LOG_ERR_SCALE_PHOT + 4 * arm + k]])
-                                                        : (k == 0 ? 1.f : 0.f);
-    rs.log2_qy = qy > 0.f ? log2f(qy) : -INFINITY;
-    if (md.use_neb) {
-      int u0, u1, z0, z1;
-      float wu0, wu1, wz0, wz1;
-      bracket_f(md.neb_logu, md.neb_nu, th[md.offs[SED_KEY_GAS_LOGU]], u0, wu0, u1, wu1);
-      bracket_f(md.neb_logz, md.neb_nz, th[md.offs[SED_KEY_GAS_LOGZ]], z0, wz0, z1, wz1);
-      const int nl = g.n_lam;
-      rs.neb_w[0] = wu0 * wz0; rs.neb_off[0] = (u0 * md.neb_nz + z0) * nl;
-      rs.neb_w[1] = wu0 * wz1; rs.neb_off[1] = (u0 * md.neb_nz + z1) * nl;
-      rs.neb_w[2] = wu1 * wz0; rs.neb_off[2] = (u1 * md.neb_nz + z0) * nl;
-      rs.neb_w[3] = wu1 * wz1; rs.neb_off[3] = (u1 * md.neb_nz + z1) * nl;
-      float du0, du1, dz0, dz1;
-      bracket_df(md.neb_logu, md.neb_nu, th[md.offs[SED_KEY_GAS_LOGU]], u0, u1, du0, du1);
-      bracket_df(md.neb_logz, md.neb_nz, th[md.offs[SED_KEY_GAS_LOGZ]], z0, z1, dz0, dz1);
-      rs.neb_dwu[0] = du0 * wz0; rs.neb_dwu[1] = du0 * wz1; rs.neb_dwu[2] = du1 * wz0; rs.neb_dwu[3] = du1 * wz1;
-      rs.neb_dwz[0] = wu0 * dz0; rs.neb_dwz[1] = wu0 * dz1; rs.neb_dwz[2] = wu1 * dz0; rs.neb_dwz[3] = wu1 * dz1;
+    int nz = 0;
+    for (int w = 0; w < PREP_THREADS / 32; ++w) {
+      qy += s_red[w];
+      nz += s_nnz[w];
     }
-    rs.dlns_dz = cr.dlns_dz;
-    rs.dlnp_dz = cr.dlnp_dz;
-    rs.dtmax_dz = cr.dtmax_dz;
-    rs.tmax = (float)tmax;
-    rs.lrat = lrat;
-    rs.status = 0;
-    rs.orig = r;
-    rs.y_scale = y_scale;
-    rs.sg_ln = md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] / (float)C_KMS : 0.f;
-    rs.fob = md.fesc_geom ? th[md.offs[SED_KEY_FRAC_OBRUN]] : 0.f;
-    // the emission lines' gas dispersion (km/s): a column, a fixed value, or
-    // tied to the stellar dispersion (the row's sampled sigma_gal, else the fixed one)
-    rs.sgas = md.gas_mode == SED_GAS_SIGMA_SAMPLED ? th[md.offs[SED_KEY_SIGMA_GAS]]
-            : md.gas_mode == SED_GAS_SIGMA_FIXED ? md.sgas_fix_kms
-            : (md.sample_sgal ? th[md.offs[SED_KEY_SIGMA_GAL]] : md.sgal_fix_kms);
-    rs.igm_f = md.use_igm ? th[md.offs[SED_KEY_IGM_FACTOR]] : 0.f;
-    rs.k_lo = win_lo;
-    rs.k_hi = win_hi;
-    if (a.tile_win) {   // union of the windows of this row's 128-row tile
-      const int mt = (a.n + 127) >> 7;
-      atomicMin(&a.tile_win[p >> 7], rs.k_lo);
-      atomicMax(&a.tile_win[mt + (p >> 7)], rs.k_hi);
-    }
-    rs.nnz = 0;
-    for (int w = 0; w < PREP_THREADS / 32; ++w) rs.nnz += s_nnz[w];
-    *out = rs;
-    if (md.n_bin > 0) {   // age-binned dust (App. dust_attn): each bin's law parameters, Q of each block
-      for (int b = 0; b < md.n_bin; ++b) {
-        out->bin_tau[b] = th[md.offs[SED_KEY_DUST_BINS] + 2 * b];
-        out->bin_slope[b] = th[md.offs[SED_KEY_DUST_BINS] + 2 * b + 1];
-      }
+    s_rs.log2_qy = qy > 0.f ? log2f(qy) : -INFINITY;
+    s_rs.nnz = nz;
+    s_rs.y_scale = y_scale;
+    if (md.n_bin > 0)   // log2 of Q of each attenuated block
       for (int j = 0; j <= MAX_SEG; ++j) {
         float q = 0.f;
         for (int w = 0; w < PREP_THREADS / 32; ++w) q += s_redq[j][w];
-        out->log2_qs[j] = q > 0.f ? log2f(q) : -INFINITY;
+        s_rs.log2_qs[j] = q > 0.f ? log2f(q) : -INFINITY;
       }
-    }
   }
+  __syncthreads();
+  for (int i = tid; i < (int)(sizeof(RowScal) / 4); i += blockDim.x)
+    reinterpret_cast<uint32_t*>(out)[i] = reinterpret_cast<const uint32_t*>(&s_rs)[i];
 }
 
 // ---------------------------------------------------------------------------
