@@ -516,10 +516,9 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   if (tid < KMASK_WORDS) s_km[tid] = 0u;
 
   // ---- in the shadow of the row's loads: finiteness of the whole row; T_max
-  //      (warp 0: the SFH edges wait for it); the rest of the row's cosmology
-  //      (the last warp: only the epilogue needs it); the bins' [Fe/H] brackets
-  //      and the cleared weight table (the warps between)
-  __shared__ CosmoRow s_cr;
+  //      (warp 0: the SFH edges wait for it); the bins' [Fe/H] brackets and the
+  //      cleared weight table (the other warps).  The rest of the row's
+  //      cosmology waits for the last warp, beside the writes of W.
   __shared__ double s_tmax;
   __shared__ float s_lrat;
   __shared__ uint32_t s_zst;
@@ -534,12 +533,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   if (warp == 0) {
     const TmaxRow t = row_tmax(md, theta_col(md, th, md.offs[SED_KEY_ZRED]), theta_col(md, th, md.offs[SED_KEY_LOGMASS]));
     if (lane == 0) { s_tmax = t.tmax; s_lrat = t.lrat; s_zst = t.status; }
-  } else if (warp == PREP_KWARPS) {
-    const CosmoRow c = row_cosmo(md, theta_col(md, th, md.offs[SED_KEY_ZRED]),
-                                 theta_col(md, th, md.offs[SED_KEY_LOGMASS]), lane);
-    if (lane == 0) s_cr = c;
   } else {
-    constexpr int NB = PREP_THREADS - 64;   // the threads of the warps between
+    constexpr int NB = PREP_THREADS - 32;
     for (int j = tid - 32; j < NA * NZ; j += NB) Ws[j] = 0.f;
     for (int i = tid - 32; i < NT; i += NB) {
       int j0, j1;
@@ -728,7 +723,10 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
     }
   } else {
-    const CosmoRow cr = s_cr;
+    // ---- the row's cosmology and observer-frame scalars (FP64 interpolants;
+    //      measured slower when run beside T_max at the start: the two warps
+    //      then share the SM's FP64 pipe on the critical path)
+    const CosmoRow cr = row_cosmo(md, th[md.offs[SED_KEY_ZRED]], th[md.offs[SED_KEY_LOGMASS]], lane);
     // ---- rest-frame node window the epilogue reads: the redshifted filter
     //      samples and the spectral pixels with 5 dispersions on either side.
     //      Lanes 0-3 look up its four candidate ends in the index table over
