@@ -370,10 +370,22 @@ struct OrderArgs {
   const int* row_model;   // NULL: every row uses md
   int by_pair;       // 1: two redshift halves, bracket pair, then redshift
   int n_pairs;       // bracket pairs (by_pair)
+  int* tile_win;     // set to empty windows by CTA 0 (lo = 0x7f7f7f7f, hi = -1), or NULL
+  uint32_t* kmask;   // cleared by CTA 0, or NULL
+  int mt, kmask_w;   // 128-row tiles; mask words per tile
 };
 
 __global__ void __launch_bounds__(ORDER_THREADS) k_order(const __grid_constant__ OrderArgs oa) {
   pdl_enter();
+  // the per-tile windows and K-tile masks the preparation kernel accumulates
+  // into start empty (done here rather than by separate memsets)
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < oa.mt && oa.tile_win; i += ORDER_THREADS) {
+      oa.tile_win[i] = 0x7f7f7f7f;
+      oa.tile_win[oa.mt + i] = -1;
+    }
+    for (int i = threadIdx.x; i < oa.mt * oa.kmask_w && oa.kmask; i += ORDER_THREADS) oa.kmask[i] = 0u;
+  }
   __shared__ int cnt[ORDER_BINS + 1];
   __shared__ int wsum[ORDER_THREADS / 32];
   const ModelDev& md = oa.md;
@@ -1153,7 +1165,17 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   // a fixed redshift (no column) needs no redshift order: the caller's order is kept
   const bool z_col = p.md.offs[SED_KEY_ZRED] < p.md.n_param;
-  if (p.perm && (p.row_model || z_col)) {
+  const int mt = (p.n + 127) / 128;
+  const bool order = p.perm && (p.row_model || z_col);
+  if (!order) {   // no ordering kernel to start the windows and masks empty
+    if (p.tile_win) {
+      e = cudaMemsetAsync(p.tile_win, 0x7f, mt * sizeof(int), s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(p.tile_win + mt, 0xff, mt * sizeof(int), s);
+    }
+    if (e == cudaSuccess && p.kmask) e = cudaMemsetAsync(p.kmask, 0, (size_t)mt * p.kmask_w * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (order) {
     OrderArgs oa;
     oa.theta = p.theta; oa.n = p.n; oa.ld = p.ld; oa.perm = p.perm; oa.md = p.md;
     oa.mtab = p.mtab; oa.row_model = p.row_model;
@@ -1162,6 +1184,10 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
     const int pairs = std::max(p.md.n_feh - 1, 1) * (p.md.use_afe ? std::max(p.md.n_afe - 1, 1) : 1);
     oa.by_pair = !p.row_model && p.kmask && pairs > 1 && pairs <= ORDER_BINS / 4;
     oa.n_pairs = pairs;
+    oa.tile_win = p.tile_win;
+    oa.kmask = p.kmask;
+    oa.mt = mt;
+    oa.kmask_w = p.kmask ? p.kmask_w : 0;
     e = launch_pdl(k_order, dim3((p.n + ORDER_CHUNK - 1) / ORDER_CHUNK), dim3(ORDER_THREADS), 0, s, oa);
     if (e != cudaSuccess) return e;
   }

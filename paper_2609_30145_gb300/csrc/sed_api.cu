@@ -1397,12 +1397,6 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
     w->kmask_w_call = pa.kmask_w;
     if (ctx->profiling) { w->last_kmask_w = pa.kmask_w; w->last_kt_shift = shift; }
   }
-  {
-    const size_t mt = (size_t)(n + 127) / 128;
-    CK(cudaMemsetAsync(w->tile_win, 0x7f, mt * sizeof(int), s));
-    CK(cudaMemsetAsync(w->tile_win + mt, 0xff, mt * sizeof(int), s));
-    if (pa.kmask) CK(cudaMemsetAsync(w->kmask, 0, mt * pa.kmask_w * sizeof(uint32_t), s));
-  }
   CK(launch_prep(pa, s));
   if (sed_status ps = prof_mark(ctx, w, 1, s)) return ps;
   if (precision == SED_PREC_FP32_SIMT) {

@@ -447,10 +447,10 @@ struct PrepArgs {
   RowScal* rs;
   int* err;            // device error word of the contraction, cleared by the prep kernel
   int* perm;           // [n] scratch: processing order (rows sorted by redshift), or NULL = caller's order
-  int* tile_win;       // [2][ceil(n/128)] union of the row windows of each 128-row tile (lo set to
-                       // 0x7f7f7f7f and hi to -1 beforehand), or NULL
+  int* tile_win;       // [2][ceil(n/128)] union of the row windows of each 128-row tile (launch_prep
+                       // starts them empty: lo 0x7f7f7f7f, hi -1), or NULL
   uint32_t* kmask;     // [ceil(n/128)][kmask_w] K tiles that some row of each 128-row tile touches
-                       // (zeroed beforehand), or NULL
+                       // (launch_prep clears them), or NULL
   int kmask_w;         // words per 128-row tile (<= KMASK_WORDS)
   int kt_shift;        // log2 of the columns of one K tile of the contraction's layout (5, 6 or 7)
   float* qneb;         // nebular age axis: [n][MAX_NEB_AGE] Q-weighted weight of each nebular SSP age, or NULL

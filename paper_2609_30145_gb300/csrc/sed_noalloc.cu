@@ -152,10 +152,7 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   float* O2 = static_cast<float*>(at(11));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // per-tile window bounds start empty: lo = a large positive int, hi = -1
-  cudaError_t e = cudaMemsetAsync(tile_win, 0x7f, mt * sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(tile_win + mt, 0xff, mt * sizeof(int), s);
-  if (e == cudaSuccess && use_km) e = cudaMemsetAsync(kmask, 0, mt * kmask_w * sizeof(uint32_t), s);
+  cudaError_t e = cudaSuccess;   // launch_prep starts the per-tile windows and masks empty
   PrepArgs pa{};
   pa.theta = theta; pa.n = n; pa.ld = ld;
   pa.md = M->dv; pa.g = g->dv; pa.L = L->dv();

@@ -188,13 +188,7 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
   // node window, as sed_loglike does: the contraction then computes only the
   // wavelength tiles its rows read, on the persistent schedule
   pa.perm = sl.perm;
-  pa.tile_win = sl.tile_win;
-  {
-    const size_t mt = (size_t)(n + 127) / 128;
-    e = cudaMemsetAsync(sl.tile_win, 0x7f, mt * sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sl.tile_win + mt, 0xff, mt * sizeof(int), s);
-    if (e != cudaSuccess) return e;
-  }
+  pa.tile_win = sl.tile_win;   // launch_prep starts its windows empty
   e = launch_prep(pa, s);
   if (e != cudaSuccess) return e;
   if (sv->prec == SED_PREC_FP32_SIMT) {
