@@ -141,7 +141,6 @@ struct Params {
   int ld_out;                // row stride of the outputs
   float* Y;                  // forward: Y [n][ld_out]; adjoint: dW [n][ld_out]
   float* O;
-  float* O2;                 // forward with gridDim.z == 3: second half of the old part
   const int* tile_win;       // forward, persistent schedule: [2][m_tiles] window (lo, hi) of each M tile
   int m_tiles;
   const uint32_t* kmask;     // [m_tiles][kmask_w] K tiles some row of the M tile touches (NULL: all);
@@ -208,57 +207,49 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // (4.3e-6 and 2.7e-6 at G = 8), while each drain is a pass of tensor-memory
 // loads and FP32 adds that G = 8 makes a quarter as frequent as G = 2.
 //
-// Units of work.  A unit is one output tile (m0, n0) with up to two K ranges
-// and their outputs: [0, KY) -> Y and [KY, KT) -> O, or, when the 3xTF32
-// forward splits a tile three ways (p.O2 set), one of [KY, KH) -> O,
-// [KH, KT) -> O2, [0, KY) -> Y; the adjoint has [K0, KT) -> dW.
+// Units of work.  A unit is one output tile (m0, n0) with its K ranges and
+// their outputs: each attenuated block of the young part [seg_kt[s],
+// seg_kt[s+1]) -> Y + s seg_stride, then [KY, KT) -> O; the adjoint has
+// [K0, KT) -> dW.  (Splitting a 3xTF32 tile over three CTAs -- the old part's
+// two halves and the young part -- measured slower on every workload once the
+// schedule below cut its leftover tiles into pieces: 1024-row photometric step
+// 0.0948 against 0.0927 ms unsplit, 4096 rows 0.3125 against 0.2960 ms, the
+// 2048-row [a/Fe] spectro-photometric forward 0.3865 against 0.3648 ms.)
 //  - Grid schedule (p.tile_win NULL): one unit per CTA from blockIdx; the CTA
 //    exits at once when the tile lies outside the union of its rows' windows.
 //  - Persistent schedule (forward, p.tile_win set): one CTA per SM; every CTA
 //    enumerates the computed units from the per-M-tile windows written by the
-//    preparation kernel and takes every gridDim.x-th one.  Per split kind the
-//    tiles (M tile, then the wavelength tiles of its window) are cut into full
-//    waves -- the largest multiple of gridDim.x, run as whole units, kind by
-//    kind (old halves first, young last), so every CTA takes the same number
-//    of units of each kind -- and a remainder whose tiles are split along the
-//    wavelength axis into up to four pieces of BN/npc columns (an MMA of N =
-//    BN/npc), so the last partial wave costs a fraction of a unit.  Tensor
-//    memory, barriers and the smem ring are set up once, and one unit's drain
-//    overlaps the next unit's MMAs.
+//    preparation kernel and takes every gridDim.x-th one.  The tiles (M tile,
+//    then the wavelength tiles of its window) are cut into full waves -- the
+//    largest multiple of gridDim.x, run as whole units -- and a remainder whose
+//    tiles are split along the wavelength axis into up to four pieces of
+//    BN/npc columns (an MMA of N = BN/npc), so the last partial wave costs a
+//    fraction of a unit.  Tensor memory, barriers and the smem ring are set up
+//    once, and one unit's drain overlaps the next unit's MMAs.
 constexpr int MAX_MT = 64;   // M tiles of a persistent launch (8192 rows)
 
 struct Unit {
   const uint32_t* km;        // K-tile mask row of the unit's M tile (NULL: every K tile)
   int m0, n0, nr;
   int ncol;                  // columns of the tile that are stored (a multiple of 4)
-  int kind;                  // 0, 1: the old part's halves (3-way split); 2: the young blocks, then the
-                             // old part unless split; the adjoint has one range
   int K0, KY, KT;
 };
 
 // K range r of a unit and its output: each attenuated block of the young part
-// into its own output (Y + s seg_stride), the old part into O (or its halves
-// into O and O2).  Computed from scalars and the kernel parameters, so that no
-// per-unit array lives in local memory.
+// into its own output (Y + s seg_stride), then the old part into O.  Computed
+// from scalars and the kernel parameters, so that no per-unit array lives in
+// local memory.
 template <bool GRAD>
 __device__ __forceinline__ void unit_range(const Params& p, const Unit& u, int r, int& rb, int& re, float*& out) {
   if (GRAD) { rb = u.K0; re = u.KY; out = p.Y; return; }
-  if (u.kind < 2) {
-    const int KH = u.KY + (u.KT - u.KY + 1) / 2;
-    if (u.kind == 0) { rb = u.KY; re = KH; out = p.O; }
-    else { rb = KH; re = u.KT; out = p.O2; }
-    return;
-  }
   if (r < p.n_seg) { rb = p.seg_kt[r]; re = p.seg_kt[r + 1]; out = p.Y + r * p.seg_stride; }
   else { rb = u.KY; re = u.KT; out = p.O; }
 }
 
-template <int BN, bool GRAD>
-__device__ __forceinline__ void unit_ranges(const Params& p, int z, int nz, int K0, int KY, int KT, Unit& u) {
+template <bool GRAD>
+__device__ __forceinline__ void unit_ranges(const Params& p, int K0, int KY, int KT, Unit& u) {
   u.K0 = K0; u.KY = KY; u.KT = KT;
-  if (GRAD) { u.kind = 2; u.nr = 1; return; }
-  u.kind = nz == 3 ? z : 2;
-  u.nr = u.kind < 2 ? 1 : p.n_seg + (nz == 3 ? 0 : 1);
+  u.nr = GRAD ? 1 : p.n_seg + 1;
 }
 
 // KSKIP: the forward with K-tile masks (an instance of its own, so that the
@@ -275,12 +266,39 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool persistent = !GRAD && p.tile_win;
-  const int nz = (!GRAD && p.O2) ? 3 : 1;
   int K0 = 0, KY = p.ky_tiles, KT = p.k_tiles;
   int n_units = 1, upz = 0;
-  int nfull = 0, nrem = 0, npc = 1;   // persistent: tiles per kind in full waves, leftover tiles, pieces per leftover tile
+  int nfull = 0, nrem = 0, npc = 1;   // persistent: tiles in full waves, leftover tiles, pieces per leftover tile
+
+  const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
+  const uint32_t tfull0 = smem_u32(&bars[2 * STAGES]), tempty0 = smem_u32(&bars[2 * STAGES + 2]);
+  // barriers and tensor memory (made visible by the barrier before the roles)
+  auto setup = [&]() {
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < STAGES; ++s) {
+        mbar_init(full0 + 8 * s, 1);
+        mbar_init(empty0 + 8 * s, 1);
+      }
+      for (int b = 0; b < 2; ++b) {
+        mbar_init(tfull0 + 8 * b, 1);
+        mbar_init(tempty0 + 8 * b, 4);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                   "r"(C::TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+  };
 
   if (persistent) {
+    // the persistent CTA always works (or frees its tensor memory below):
+    // set up first, so that the allocation overlaps the reads of the windows
+    setup();
     // computed wavelength tiles of each M tile, and their prefix counts
     const int MT = p.m_tiles, NTt = p.ldn / BN;
     if (threadIdx.x < MT) {
@@ -300,19 +318,28 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     }
     __syncthreads();
     upz = s_pref[MT];
-    // per split kind, the largest multiple of gridDim.x tiles runs as whole
-    // units (every CTA then takes the same number of units of each kind); the
-    // leftover tiles are cut along the wavelength axis into npc pieces of BN/npc
-    // columns so that the last partial wave spreads over the CTAs.  npc is 1, 2
-    // or 4 (BN/npc stays a multiple of 16: a valid MMA N and 16-byte aligned
-    // output columns)
+    // the largest multiple of gridDim.x tiles runs as whole units (every CTA
+    // then takes the same number of them); the leftover tiles are cut along the
+    // wavelength axis into npc pieces of BN/npc columns so that the last
+    // partial wave spreads over the CTAs.  npc is 1, 2 or 4 (BN/npc stays a
+    // multiple of 16: a valid MMA N and 16-byte aligned output columns)
     const int nctas = (int)gridDim.x;
     nfull = (upz / nctas) * nctas;
     nrem = upz - nfull;
-    const int fit = nrem > 0 ? nctas / (nz * nrem) : 1;
+    const int fit = nrem > 0 ? nctas / nrem : 1;
     npc = (fit >= 4 && BN / 4 >= 16) ? 4 : (fit >= 2 && BN / 2 >= 16 ? 2 : 1);
-    const int total = nz * nfull + nz * nrem * npc;
+    const int total = nfull + nrem * npc;
     n_units = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / nctas + 1 : 0;
+    if (n_units == 0) {   // no unit for this CTA: free the tensor memory and leave
+      tc_fence_before();
+      __syncthreads();
+      if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(C::TMEM_COLS)
+                     : "memory");
+      }
+      return;
+    }
   } else if (p.rs) {
     // grid schedule: union of the rest-frame node windows of the tile's rows
     // (invalid rows have none).  Forward: a wavelength tile outside it is never
@@ -356,19 +383,14 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 
   // unit j of this CTA
   auto get_unit = [&](int j, Unit& u) {
-    int z = GRAD ? 0 : (int)blockIdx.z;
     u.ncol = BN;
     if (persistent) {
       const int idx = (int)blockIdx.x + j * (int)gridDim.x;
-      int t, pc = 0;
-      if (idx < nz * nfull) {
-        z = idx / nfull;
-        t = idx - z * nfull;
-      } else {
-        const int q = idx - nz * nfull, rest = q / npc;
-        pc = q - rest * npc;
-        z = rest / nrem;
-        t = nfull + rest - z * nrem;
+      int t = idx, pc = 0;
+      if (idx >= nfull) {
+        const int q = idx - nfull;
+        t = nfull + q / npc;
+        pc = q - (q / npc) * npc;
       }
       int m = 0;
       while (s_pref[m + 1] <= t) ++m;
@@ -387,31 +409,10 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       u.n0 = t < p.ny_tiles ? t * BN : p.n_split + (t - p.ny_tiles) * BN;
       u.ncol = min(BN, (t < p.ny_tiles ? p.n_split : p.ld_out) - u.n0);
     }
-    unit_ranges<BN, GRAD>(p, z, nz, K0, KY, KT, u);
+    unit_ranges<GRAD>(p, K0, KY, KT, u);
   };
 
-  const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
-  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]);
-  const uint32_t tfull0 = smem_u32(&bars[2 * STAGES]), tempty0 = smem_u32(&bars[2 * STAGES + 2]);
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, 4);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  if (warp == 2) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
-                 "r"(C::TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (!persistent) setup();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -563,14 +564,13 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 
 template <int PREC, int BN, int STAGES, int G, bool GRAD, bool KSKIP = false>
 cudaError_t launch_cfg(const Params& p, int n_cols, cudaStream_t s) {
-  const int nz = (!GRAD && p.O2) ? 3 : 1;
   const int n_sm = device_sm_count();
   using C = Cfg<PREC, BN, STAGES, G, GRAD>;
   auto k = k_contract_tc<PREC, BN, STAGES, G, GRAD, KSKIP>;
   static DynSmemCache attr;   // the raised shared-memory limit, set once per device
   if (cudaError_t e = ensure_dyn_smem(k, (size_t)C::SMEM, &attr)) return e;
   if (!GRAD && p.tile_win) return launch_pdl(k, dim3(n_sm, 1, 1), dim3(C::THREADS), C::SMEM, s, p);   // persistent: one CTA per SM
-  return launch_pdl(k, dim3(n_cols / BN, (p.n + BM - 1) / BM, nz), dim3(C::THREADS), C::SMEM, s, p);
+  return launch_pdl(k, dim3(n_cols / BN, (p.n + BM - 1) / BM, 1), dim3(C::THREADS), C::SMEM, s, p);
 }
 
 }  // namespace tc
@@ -590,13 +590,11 @@ static CUresult encode_kmajor(void* fn, CUtensorMap* m, void* base, CUtensorMapD
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
-// Wavelength tile of the forward contraction and its split into units of
-// work.  With rows grouped by redshift only ~40% of the wavelength tiles are
-// computed, and a 1024-row batch then has ~150 128x128 tiles for 152 SMs, where
-// an SM with two tiles doubles the kernel's time.
-//  - 3xTF32 (long units): 128-wide tiles, each split over three CTAs (the two
-//    halves of the old part and the young part; no operand is read twice), so
-//    the SMs share ~450 units of similar size.
+// Wavelength tile of the forward contraction.  With rows grouped by redshift
+// only ~40% of the wavelength tiles are computed: a 1024-row batch has ~150
+// 128x128 tiles for 152 SMs (the persistent schedule cuts a partial last wave
+// into pieces).
+//  - 3xTF32: 128-wide tiles, one CTA per tile.
 //  - BF16: 128-wide tiles, one CTA per tile (measured on the paper-scale
 //    photometric batch: 20.5 us against 24.6 us with 64-wide tiles, which
 //    read every W tile twice as often).
@@ -632,7 +630,7 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   p.rs = a.rs;
   p.a_hi = a.maps->a_hi; p.a_lo = a.maps->a_lo; p.b_hi = a.maps->b_hi; p.b_lo = a.maps->b_lo;
   p.n = a.n; p.n_lam = a.n_lam; p.ldn = a.ldn; p.ld_out = a.ldn;
-  p.Y = a.Y; p.O = a.O; p.O2 = a.prec == SED_PREC_FP32 ? a.O2 : nullptr; p.err = a.err;
+  p.Y = a.Y; p.O = a.O; p.err = a.err;
   p.m_tiles = (a.n + tc::BM - 1) / tc::BM;
   p.tile_win = (a.tile_win && p.m_tiles <= tc::MAX_MT) ? a.tile_win : nullptr;
   // K-tile masks: the 3xTF32 forward only (the host gives no other precision any)

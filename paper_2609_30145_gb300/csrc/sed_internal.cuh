@@ -347,7 +347,6 @@ struct Workspace {
   uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
   float* Y = nullptr;            // [cap_seg][cap_rows][ldn]: one slab per attenuated block
   float* O = nullptr;
-  float* O2 = nullptr;           // [rows][ldn] second partial sum of the old part
   RowScal* rs = nullptr;
   int* err = nullptr;            // device error word of bounded waits
   float* theta_h = nullptr;      // host-path staging (device)
@@ -568,8 +567,6 @@ struct TcArgs {
                                           // (for FP8, Ky_pad/Kpad are the FP8 layout's Ky_pad8/Kpad8)
   const TcMaps* maps;
   float* Y; float* O; int* err;
-  float* O2;           // SED_PREC_FP32 with O2 non-NULL: the old part is split over two CTAs and
-                       // O + O2 is the old sum (other precisions ignore O2)
   const int* tile_win; // non-NULL (and <= 64 M tiles): persistent schedule over the computed tiles
   const uint32_t* kmask; int kmask_w;   // K tiles some row of each 128-row tile touches (NULL: all)
   int n_seg;           // attenuated blocks of the young part (0 or 1: one), block s of the main layout's
@@ -603,7 +600,6 @@ cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s);
 struct EpiArgs {
   int n; int ldn;
   const float* Y; const float* O;
-  const float* O2;     // non-NULL: second partial sum of the old part (added to O)
   const RowScal* rs;
   ModelDev md; GridDev g;
   const ModelDev* mtab;    // as in PrepArgs; with row_model set, smem_samp / smem_pix give the
@@ -624,7 +620,6 @@ cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 struct EpiBwdArgs {
   int n; int ldn;
   const float* Y; const float* O;
-  const float* O2;
   const RowScal* rs;
   ModelDev md; GridDev g;
   int split;            // 1: write G as TF32 hi/lo parts (3xTF32), 0: exact FP32 into *_hi

@@ -110,13 +110,13 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   const int pairs = std::max(g->n_feh - 1, 1) * (M->dv.use_afe ? std::max(g->n_afe - 1, 1) : 1);
   const bool use_km = f32 && M->dv.zmode == 1 && pairs > 1 && kmask_w <= KMASK_WORDS;
   // carve the scratch: err | perm | tile windows | K-tile masks | RowScal | W (FFMA) | W_hi | W_lo | W_bf16 |
-  // Y | O | O2 (3xTF32)
+  // Y | O
   const size_t nn = (size_t)n, mt = (nn + 127) / 128;
-  constexpr int NB = 12;
+  constexpr int NB = 11;
   size_t off[NB], need = 0;
   const size_t sz[NB] = {256, nn * 4, 2 * mt * 4, use_km ? mt * kmask_w * 4 : 0, nn * sizeof(RowScal),
                          simt ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0, f32 ? nn * kpad * 4 : 0,
-                         bf ? nn * kpad * 2 : 0, nn * ldn * 4, nn * ldn * 4, f32 ? nn * ldn * 4 : 0};
+                         bf ? nn * kpad * 2 : 0, nn * ldn * 4, nn * ldn * 4};
   for (int i = 0; i < NB; i++) {
     off[i] = need;
     need += up256(sz[i]);
@@ -149,7 +149,6 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
   __nv_bfloat16* W_bf = static_cast<__nv_bfloat16*>(at(8));
   float* Y = static_cast<float*>(at(9));
   float* O = static_cast<float*>(at(10));
-  float* O2 = static_cast<float*>(at(11));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   cudaError_t e = cudaSuccess;   // launch_prep starts the per-tile windows and masks empty
@@ -174,14 +173,14 @@ extern "C" sed_status sed_loglike_noalloc(sed_ctx* ctx, sed_model_id id, const f
         return na_fail(ctx, SED_ECUDA, "cuTensorMapEncodeTiled failed");
       TcArgs ta{};
       ta.n = n; ta.n_lam = g->n_lam; ta.ldn = ldn; ta.Ky_pad = L->Ky_pad; ta.Kpad = kpad; ta.prec = precision;
-      ta.maps = &maps; ta.Y = Y; ta.O = O; ta.O2 = O2; ta.err = err; ta.rs = rs; ta.tile_win = tile_win;
+      ta.maps = &maps; ta.Y = Y; ta.O = O; ta.err = err; ta.rs = rs; ta.tile_win = tile_win;
       ta.kmask = pa.kmask; ta.kmask_w = pa.kmask_w;
       e = launch_contract_tc(ta, s);
     }
   }
   if (e == cudaSuccess) {
     EpiArgs ea{};
-    ea.n = n; ea.ldn = ldn; ea.Y = Y; ea.O = O; ea.O2 = O2; ea.rs = rs;
+    ea.n = n; ea.ldn = ldn; ea.Y = Y; ea.O = O; ea.rs = rs;
     ea.md = M->dv; ea.g = g->dv;
     ea.lnl = lnl_out; ea.status = row_status; ea.err = err;
     e = launch_epilogue(ea, s);

@@ -68,7 +68,7 @@ struct SrvSlot {
   int* tile_win = nullptr;      // [2][ceil(max_rows/128)] node windows of the 128-row tiles
   double* lnl = nullptr;
   uint32_t* st = nullptr;
-  float *W = nullptr, *W_hi = nullptr, *W_lo = nullptr, *Y = nullptr, *O = nullptr, *O2 = nullptr;
+  float *W = nullptr, *W_hi = nullptr, *W_lo = nullptr, *Y = nullptr, *O = nullptr;
   __nv_bfloat16* W_bf16 = nullptr;
   uint8_t* W_f8 = nullptr;
   RowScal* rs = nullptr;
@@ -211,14 +211,13 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
     ta.n = n; ta.n_lam = g->n_lam; ta.ldn = sv->ldn; ta.prec = sv->prec;
     ta.Ky_pad = f8 ? L->Ky_pad8 : L->Ky_pad;
     ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
-    ta.maps = &sl.maps; ta.Y = sl.Y; ta.O = sl.O; ta.O2 = sl.O2; ta.err = sl.err; ta.rs = sl.rs;
+    ta.maps = &sl.maps; ta.Y = sl.Y; ta.O = sl.O; ta.err = sl.err; ta.rs = sl.rs;
     ta.tile_win = sl.tile_win;
     e = launch_contract_tc(ta, s);
   }
   if (e != cudaSuccess) return e;
   EpiArgs ea{};
   ea.n = n; ea.ldn = sv->ldn; ea.Y = sl.Y; ea.O = sl.O; ea.rs = sl.rs;
-  ea.O2 = sv->prec == SED_PREC_FP32 ? sl.O2 : nullptr;   // same partial sums as sed_loglike
   ea.g = g->dv;
   ea.mtab = sv->mtab; ea.row_model = sl.rowm;
   ea.smem_samp = sv->max_samp; ea.smem_pix = sv->max_pix; ea.smem_win = sv->max_win;
@@ -353,7 +352,7 @@ sed_status sed_server_create(sed_ctx* ctx, const sed_server_desc* d, sed_server*
     ok = ok && dmalloc(sv, sl.dev, &sl.theta, R * SRV_LD * 4) && dmalloc(sv, sl.dev, &sl.rowm, R * 4) &&
          dmalloc(sv, sl.dev, &sl.lnl, R * 8) && dmalloc(sv, sl.dev, &sl.st, R * 4) &&
          dmalloc(sv, sl.dev, &sl.W, R * K * 4) && dmalloc(sv, sl.dev, &sl.Y, R * N * 4) &&
-         dmalloc(sv, sl.dev, &sl.O, R * N * 4) && dmalloc(sv, sl.dev, &sl.O2, R * N * 4) &&
+         dmalloc(sv, sl.dev, &sl.O, R * N * 4) &&
          dmalloc(sv, sl.dev, &sl.rs, R * sizeof(RowScal)) &&
          dmalloc(sv, sl.dev, &sl.err, 256) && dmalloc(sv, sl.dev, &sl.perm, R * 4) &&
          dmalloc(sv, sl.dev, &sl.tile_win, 2 * ((R + 127) / 128) * 4);

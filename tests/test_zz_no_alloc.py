@@ -108,8 +108,8 @@ def test_noalloc_refuses_fp8_and_batches_beyond_scratch(ctx):
     with pytest.raises(SedError) as ei:
         model.loglike_noalloc(t, "fp8")
     assert ei.value.status == _ffi.SED_EUNSUPPORTED
-    # rows x (3 x 4 x 6144 bytes of contraction output) alone exceed the scratch
-    n = SCRATCH // (3 * 4 * 6144) + 1
+    # rows x (2 x 4 x 6144 bytes of contraction output, Y and O) alone exceed the scratch
+    n = SCRATCH // (2 * 4 * 6144) + 1
     big = torch.zeros((n, model.n_param), dtype=torch.float32, device="cuda")
     with pytest.raises(SedError) as ei:
         model.loglike_noalloc(big, "fp32")
