@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   const int kr0 = k_lo + tid * CH, kr1 = min(kr0 + CH, k_hi + 1);   // this thread's nodes [kr0, kr1)
   const float* Yr = a.Y + ro;
   const float* Or = a.O + ro;
+  const float* O2r = a.O2 && a.o2_split && *a.o2_split ? a.O2 + ro : nullptr;
   const float eb_kc = 0.85f - 1.9f * rs.delta;
   const float opz = 1.f / rs.inv1pz;
   // nebular age axis: the row's Q-weighted weight of each nebular SSP age, and
@@ -191,9 +192,9 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
       float yv[MAX_SEG];
 #pragma unroll
       for (int sg = 0; sg < MAX_SEG; ++sg) yv[sg] = sg < md.n_seg ? Yr[sg * a.seg_stride + k] : 0.f;
-      Fs[k] = attenuated_bins(md, rs, g.att4[k], eb_kc, yv, Or[k], g.neb_tab, k);
+      Fs[k] = attenuated_bins(md, rs, g.att4[k], eb_kc, yv, O2r ? Or[k] + O2r[k] : Or[k], g.neb_tab, k);
     } else {
-      Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], Or[k], g, qa, k);
+      Fs[k] = attenuated(md, rs, g.att4[k], eb_kc, Yr[k], O2r ? Or[k] + O2r[k] : Or[k], g, qa, k);
     }
     if (md.use_igm && g.lam_f[k] < IGM_LYA) {   // the IGM transmission (the forward epilogue's)
       float tau, dtau;

@@ -130,6 +130,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 consecutive columns of this thread's tensor-memory lane from 32 registers
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 struct Params {
   const RowScal* rs;         // per-row rest-frame node windows (NULL: no window)
@@ -141,6 +150,9 @@ struct Params {
   int ld_out;                // row stride of the outputs
   float* Y;                  // forward: Y [n][ld_out]; adjoint: dW [n][ld_out]
   float* O;
+  float* O2;                 // forward, persistent schedule: second half of the old part when the
+                             // launch splits its tiles three ways (NULL: never split)
+  int* split_out;            // forward: the launch's choice (1 = split, O + O2 is the old part), or NULL
   const int* tile_win;       // forward, persistent schedule: [2][m_tiles] window (lo, hi) of each M tile
   int m_tiles;
   const uint32_t* kmask;     // [m_tiles][kmask_w] K tiles some row of the M tile touches (NULL: all);
@@ -186,7 +198,10 @@ struct Cfg {
   static constexpr int NOPS = PREC == SED_PREC_FP32 ? 2 : 1;  // hi/lo parts
   static constexpr int STAGE_BYTES = NOPS * (A_BYTES + B_BYTES);
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;    // + alignment slack
-  static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : (2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512));
+  // the two accumulator buffers; the 3xTF32 forward adds BN columns where an unsplit unit keeps the
+  // old part's first half (see unit_range)
+  static constexpr int COLS_USED = 2 * BN + (PREC == SED_PREC_FP32 && !GRAD ? BN : 0);
+  static constexpr uint32_t TMEM_COLS = COLS_USED <= 64 ? 64 : (COLS_USED <= 128 ? 128 : (COLS_USED <= 256 ? 256 : 512));
   static constexpr int THREADS = 192;                         // 6 warps
 };
 
@@ -210,11 +225,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // Units of work.  A unit is one output tile (m0, n0) with its K ranges and
 // their outputs: each attenuated block of the young part [seg_kt[s],
 // seg_kt[s+1]) -> Y + s seg_stride, then [KY, KT) -> O; the adjoint has
-// [K0, KT) -> dW.  (Splitting a 3xTF32 tile over three CTAs -- the old part's
-// two halves and the young part -- measured slower on every workload once the
-// schedule below cut its leftover tiles into pieces: 1024-row photometric step
-// 0.0948 against 0.0927 ms unsplit, 4096 rows 0.3125 against 0.2960 ms, the
-// 2048-row [a/Fe] spectro-photometric forward 0.3865 against 0.3648 ms.)
+// [K0, KT) -> dW.  A persistent 3xTF32 launch may instead split each tile
+// three ways (kinds 0, 1: the old part's halves [KY, KH) -> O and [KH, KT) ->
+// O2; kind 2: the young blocks), when that shortens its longest CTA (see
+// split_pays): one unit per tile has less overhead (1024-row photometric
+// step 0.0927 against 0.0948 ms split, 4096 rows 0.2960 against 0.3125 ms, the
+// 2048-row [a/Fe] spectro-photometric forward 0.3648 against 0.3865 ms), but
+// with a few tiles more than SMs its leftover tiles leave a few CTAs a second
+// unit (154 tiles on 152 SMs: 0.109 against 0.099 ms split).
 //  - Grid schedule (p.tile_win NULL): one unit per CTA from blockIdx; the CTA
 //    exits at once when the tile lies outside the union of its rows' windows.
 //  - Persistent schedule (forward, p.tile_win set): one CTA per SM; every CTA
@@ -232,24 +250,75 @@ struct Unit {
   const uint32_t* km;        // K-tile mask row of the unit's M tile (NULL: every K tile)
   int m0, n0, nr;
   int ncol;                  // columns of the tile that are stored (a multiple of 4)
+  int kind;                  // 0, 1: the old part's halves (3-way split); 2: the young blocks, then the
+                             // old part unless split; the adjoint has one range
   int K0, KY, KT;
 };
 
 // K range r of a unit and its output: each attenuated block of the young part
-// into its own output (Y + s seg_stride), then the old part into O.  Computed
-// from scalars and the kernel parameters, so that no per-unit array lives in
-// local memory.
-template <bool GRAD>
-__device__ __forceinline__ void unit_range(const Params& p, const Unit& u, int r, int& rb, int& re, float*& out) {
+// into its own output (Y + s seg_stride), then the old part.  The 3xTF32
+// forward sums the old part as two halves [KY, KH) and [KH, KT) and adds them
+// in FP32: split, into O and O2 (the epilogues add them); one unit per tile,
+// the first half kept in tensor memory (mode 1) and added to the second
+// before the store (mode 2) -- so that an output is the same sum, rounded the
+// same way, whichever way the launch ran.  Other precisions sum the old part
+// as one range.  Computed from scalars and the kernel parameters, so that no
+// per-unit array lives in local memory.
+template <int PREC, bool GRAD>
+__device__ __forceinline__ void unit_range(const Params& p, const Unit& u, int r, int& rb, int& re, float*& out,
+                                           int& mode) {
+  mode = 0;
   if (GRAD) { rb = u.K0; re = u.KY; out = p.Y; return; }
+  const int KH = u.KY + (u.KT - u.KY + 1) / 2;
+  if (u.kind < 2) {
+    if (u.kind == 0) { rb = u.KY; re = KH; out = p.O; }
+    else { rb = KH; re = u.KT; out = p.O2; }
+    return;
+  }
   if (r < p.n_seg) { rb = p.seg_kt[r]; re = p.seg_kt[r + 1]; out = p.Y + r * p.seg_stride; }
-  else { rb = u.KY; re = u.KT; out = p.O; }
+  else if (PREC != SED_PREC_FP32) { rb = u.KY; re = u.KT; out = p.O; }
+  else if (r == p.n_seg) { rb = u.KY; re = KH; out = p.O; mode = 1; }
+  else { rb = KH; re = u.KT; out = p.O; mode = 2; }
 }
 
-template <bool GRAD>
-__device__ __forceinline__ void unit_ranges(const Params& p, int K0, int KY, int KT, Unit& u) {
+template <int PREC, bool GRAD>
+__device__ __forceinline__ void unit_ranges(const Params& p, int z, int nz, int K0, int KY, int KT, Unit& u) {
   u.K0 = K0; u.KY = KY; u.KT = KT;
-  u.nr = GRAD ? 1 : p.n_seg + 1;
+  if (GRAD) { u.kind = 2; u.nr = 1; return; }
+  u.kind = nz == 3 ? z : 2;
+  u.nr = u.kind < 2 ? 1 : p.n_seg + (nz == 3 ? 0 : (PREC == SED_PREC_FP32 ? 2 : 1));
+}
+
+// Pieces of a leftover tile (1, 2 or 4 along the wavelength axis: BN/npc stays
+// a multiple of 16) when nz units per tile leave nrem tiles past the full waves.
+template <int BN>
+__device__ __forceinline__ int pieces_for(int P, int nz, int nrem) {
+  const int fit = nrem > 0 ? P / (nz * nrem) : 1;
+  return (fit >= 4 && BN / 4 >= 16) ? 4 : (fit >= 2 && BN / 2 >= 16 ? 2 : 1);
+}
+// The longest CTA's work, in K tiles, of a persistent launch over `tiles`
+// tiles on P CTAs with nz units per tile of kmax K tiles at most (kt in all):
+// the full waves, then the leftover tiles' pieces spread over the CTAs, a
+// piece costing about 0.6 (two) or 0.4 (four pieces) of its unit (the A tile
+// and the MMA issue do not shrink with N).
+template <int BN>
+__device__ __forceinline__ float sched_longest(int tiles, int P, int nz, int kt, int kmax) {
+  const int nfull = (tiles / P) * P, nrem = tiles - nfull;
+  float w = (float)(nfull / P) * (float)kt;
+  if (nrem > 0) {
+    const int npc = pieces_for<BN>(P, nz, nrem);
+    const int per_cta = (nz * nrem * npc + P - 1) / P;
+    w += (float)per_cta * (float)kmax * (npc == 1 ? 1.f : (npc == 2 ? 0.6f : 0.4f));
+  }
+  return w;
+}
+// Whether the 3-way split shortens the launch by more than 5 %.
+template <int BN>
+__device__ __forceinline__ bool split_pays(int tiles, int P, int ky, int kt) {
+  const int ko = kt - ky, kh = (ko + 1) / 2;
+  const float one = sched_longest<BN>(tiles, P, 1, kt, kt);
+  const float three = sched_longest<BN>(tiles, P, 3, kt, max(kh, ky));
+  return three < 0.95f * one;
 }
 
 // KSKIP: the forward with K-tile masks (an instance of its own, so that the
@@ -266,6 +335,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool persistent = !GRAD && p.tile_win;
+  int nz = 1;   // units per tile (3: the persistent launch splits its tiles)
   int K0 = 0, KY = p.ky_tiles, KT = p.k_tiles;
   int n_units = 1, upz = 0;
   int nfull = 0, nrem = 0, npc = 1;   // persistent: tiles in full waves, leftover tiles, pieces per leftover tile
@@ -295,6 +365,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     }
   };
 
+  // a launch that cannot split records that it did not
+  if (!GRAD && !persistent && p.split_out && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *p.split_out = 0;
   if (persistent) {
     // the persistent CTA always works (or frees its tensor memory below):
     // set up first, so that the allocation overlaps the reads of the windows
@@ -318,17 +390,21 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     }
     __syncthreads();
     upz = s_pref[MT];
-    // the largest multiple of gridDim.x tiles runs as whole units (every CTA
-    // then takes the same number of them); the leftover tiles are cut along the
-    // wavelength axis into npc pieces of BN/npc columns so that the last
-    // partial wave spreads over the CTAs.  npc is 1, 2 or 4 (BN/npc stays a
-    // multiple of 16: a valid MMA N and 16-byte aligned output columns)
+    // one unit per tile, or the 3-way split where it shortens the longest CTA
+    // (every CTA takes the same decision; CTA 0 records it for the epilogues).
+    // Per kind, the largest multiple of gridDim.x tiles runs as whole units
+    // (every CTA then takes the same number of units of each kind); the
+    // leftover tiles are cut along the wavelength axis into npc pieces of BN/npc
+    // columns so that the last partial wave spreads over the CTAs.  npc is 1, 2
+    // or 4 (BN/npc stays a multiple of 16: a valid MMA N and 16-byte aligned
+    // output columns)
     const int nctas = (int)gridDim.x;
+    nz = p.O2 && split_pays<BN>(upz, nctas, KY, KT) ? 3 : 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p.split_out) *p.split_out = nz == 3 ? 1 : 0;
     nfull = (upz / nctas) * nctas;
     nrem = upz - nfull;
-    const int fit = nrem > 0 ? nctas / nrem : 1;
-    npc = (fit >= 4 && BN / 4 >= 16) ? 4 : (fit >= 2 && BN / 2 >= 16 ? 2 : 1);
-    const int total = nfull + nrem * npc;
+    npc = pieces_for<BN>(nctas, nz, nrem);
+    const int total = nz * nfull + nz * nrem * npc;
     n_units = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / nctas + 1 : 0;
     if (n_units == 0) {   // no unit for this CTA: free the tensor memory and leave
       tc_fence_before();
@@ -341,7 +417,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       return;
     }
   } else if (p.rs) {
-    // grid schedule: union of the rest-frame node windows of the tile's rows
+    // grid schedule (never split): union of the rest-frame node windows of the tile's rows
     // (invalid rows have none).  Forward: a wavelength tile outside it is never
     // read, so the CTA exits.  Adjoint: dlnL/dY and dlnL/dO vanish outside each
     // row's window, so the reduction over wavelength runs over the union only.
@@ -383,14 +459,19 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
 
   // unit j of this CTA
   auto get_unit = [&](int j, Unit& u) {
+    int z = 0;
     u.ncol = BN;
     if (persistent) {
       const int idx = (int)blockIdx.x + j * (int)gridDim.x;
-      int t = idx, pc = 0;
-      if (idx >= nfull) {
-        const int q = idx - nfull;
-        t = nfull + q / npc;
-        pc = q - (q / npc) * npc;
+      int t, pc = 0;
+      if (idx < nz * nfull) {
+        z = idx / nfull;
+        t = idx - z * nfull;
+      } else {
+        const int q = idx - nz * nfull, rest = q / npc;
+        pc = q - rest * npc;
+        z = rest / nrem;
+        t = nfull + rest - z * nrem;
       }
       int m = 0;
       while (s_pref[m + 1] <= t) ++m;
@@ -409,7 +490,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       u.n0 = t < p.ny_tiles ? t * BN : p.n_split + (t - p.ny_tiles) * BN;
       u.ncol = min(BN, (t < p.ny_tiles ? p.n_split : p.ld_out) - u.n0);
     }
-    unit_ranges<GRAD>(p, K0, KY, KT, u);
+    unit_ranges<PREC, GRAD>(p, z, nz, K0, KY, KT, u);
   };
 
   if (!persistent) setup();
@@ -436,7 +517,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         for (int r = 0; r < u.nr && ok; ++r) {
           int rb, re;
           float* ro_;
-          unit_range<GRAD>(p, u, r, rb, re, ro_);
+          int mode_;
+          unit_range<PREC, GRAD>(p, u, r, rb, re, ro_, mode_);
           for (int kt = kn(u.km, rb, re); kt < re; kt = kn(u.km, kt + 1, re), ++it) {
             const int s = it % STAGES;
             const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -469,7 +551,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
         for (int r = 0; r < u.nr && ok; ++r) {
           int kb, ke;
           float* ro_;
-          unit_range<GRAD>(p, u, r, kb, ke, ro_);
+          int mode_;
+          unit_range<PREC, GRAD>(p, u, r, kb, ke, ro_, mode_);
           for (int gs = kb; gs < ke && ok; gs += G) {
             const int ge = gs + G < ke ? gs + G : ke;
             const int k_first = kn(u.km, gs, ge);
@@ -520,7 +603,8 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       for (int r = 0; r < u.nr; ++r) {
         int kb, ke;
         float* out;
-        unit_range<GRAD>(p, u, r, kb, ke, out);
+        int mode;
+        unit_range<PREC, GRAD>(p, u, r, kb, ke, out, mode);
         float run[BN];
 #pragma unroll
         for (int c = 0; c < BN; ++c) run[c] = 0.f;
@@ -544,6 +628,28 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty0 + 8 * b);
           ++g;
+        }
+        // mode 1: keep the old part's first half in this lane's scratch columns of
+        // tensor memory; mode 2: add it (first half + second half) before the store
+        if (mode != 0) {
+          const uint32_t scr = tmem + lane_off + (uint32_t)(2 * BN);
+#pragma unroll
+          for (int c = 0; c < BN / 32; ++c) {
+            if (c * 32 >= u.ncol) break;
+            if (mode == 1) {
+              tmem_st32(scr + (uint32_t)(c * 32), &run[c * 32]);
+            } else {
+              uint32_t rr[32];
+              tmem_ld32(scr + (uint32_t)(c * 32), rr);
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 32; ++i) run[c * 32 + i] = __uint_as_float(rr[i]) + run[c * 32 + i];
+            }
+          }
+          if (mode == 1) {
+            tmem_wait_st();
+            continue;
+          }
         }
         if (row < p.n) {
           float4* dst = reinterpret_cast<float4*>(out + (size_t)row * p.ld_out + u.n0);
@@ -631,8 +737,11 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   p.a_hi = a.maps->a_hi; p.a_lo = a.maps->a_lo; p.b_hi = a.maps->b_hi; p.b_lo = a.maps->b_lo;
   p.n = a.n; p.n_lam = a.n_lam; p.ldn = a.ldn; p.ld_out = a.ldn;
   p.Y = a.Y; p.O = a.O; p.err = a.err;
+  p.split_out = a.split_out;
   p.m_tiles = (a.n + tc::BM - 1) / tc::BM;
   p.tile_win = (a.tile_win && p.m_tiles <= tc::MAX_MT) ? a.tile_win : nullptr;
+  // the 3-way split is a choice of the persistent 3xTF32 launch
+  p.O2 = a.prec == SED_PREC_FP32 && p.tile_win ? a.O2 : nullptr;
   // K-tile masks: the 3xTF32 forward only (the host gives no other precision any)
   p.kmask = a.prec == SED_PREC_FP32 && a.kmask_w > 0 && a.kmask_w <= KMASK_WORDS ? a.kmask : nullptr;
   p.kmask_w = a.kmask_w;

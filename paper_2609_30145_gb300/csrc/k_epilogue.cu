@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 7) k_epilogue(const __grid_consta
   // ---- attenuated rest-frame spectrum of the row's node window into shared memory
   const float* Yr = a.Y + (size_t)r * a.ldn;
   const float* Or = a.O + (size_t)r * a.ldn;
+  const float* O2r = a.O2 && a.split && *a.split ? a.O2 + (size_t)r * a.ldn : nullptr;
   const float eb = 0.85f - 1.9f * rs.delta;
   const float opz = 1.f / rs.inv1pz;
   // nebular age axis: the row's Q-weighted weight of each nebular SSP age
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 7) k_epilogue(const __grid_consta
   for (int k = k_lo + tid; k <= k_hi; k += EPI_THREADS) {
     const float4 c = g.att4[k];
     const float ys = a.lam8 ? rs.y_scale * a.lam8[k] : 1.f;
-    const float o = Or[k];
+    const float o = O2r ? Or[k] + O2r[k] : Or[k];
     float F;
     if constexpr (VAR == 1) {
       float yv[MAX_SEG];

@@ -183,7 +183,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
     }
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
-      std::vector<void*> v = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->rs, w->err,
+      std::vector<void*> v = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
                               w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                               w->dW, w->rgrad, w->qneb};
       for (void* p : v)
@@ -1289,7 +1289,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   if (!need) return w;
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
-  std::vector<void*> old = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->rs, w->err,
+  std::vector<void*> old = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
                             w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                             w->dW, w->rgrad, w->qneb};
   for (void* p : old)
@@ -1310,7 +1310,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   sed_status s = SED_OK;
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
   AL(perm, R * 4); AL(tile_win, 2 * ((R + 127) / 128) * 4); AL(kmask, ((R + 127) / 128) * KMASK_WORDS * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
-  AL(Y, R * N * 4 * w->cap_seg); AL(O, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
+  AL(Y, R * N * 4 * w->cap_seg); AL(O, R * N * 4); AL(O2, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
   AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4); AL(qneb, R * MAX_NEB_AGE * 4);
   if (grad || had_grad) {
     AL(G_hi, R * N * 4 * w->cap_seg); AL(G_lo, R * N * 4 * w->cap_seg); AL(GO_hi, R * N * 4); AL(GO_lo, R * N * 4);
@@ -1429,6 +1429,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   ta.Ky_pad = f8 ? L->Ky_pad8 : L->Ky_pad;
   ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
   ta.maps = maps; ta.Y = w->Y; ta.O = w->O; ta.err = w->err; ta.rs = w->rs;
+  ta.O2 = w->O2; ta.split_out = w->err + 8;   // err[8]: the launch records whether it split its tiles
   ta.tile_win = w->tile_win;
   ta.kmask = pa.kmask; ta.kmask_w = pa.kmask_w;
   ta.n_seg = L->n_seg; ta.seg_stride = (size_t)w->cap_rows * w->ldn;
@@ -1458,6 +1459,7 @@ sed_status sed_forward(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   if (st) return st;
   EpiArgs ea{};
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
+  ea.O2 = w->O2; ea.split = precision == SED_PREC_FP32 ? w->err + 8 : nullptr;   // the 3xTF32 launch's split choice
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
@@ -1486,6 +1488,7 @@ sed_status sed_line_fluxes(sed_ctx* ctx, sed_model_id id, const float* theta, in
   if (st) return st;
   EpiArgs ea{};
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
+  ea.O2 = w->O2; ea.split = precision == SED_PREC_FP32 ? w->err + 8 : nullptr;   // the 3xTF32 launch's split choice
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
@@ -1512,6 +1515,7 @@ sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   if (st) return st;
   EpiArgs ea{};
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
+  ea.O2 = w->O2; ea.split = precision == SED_PREC_FP32 ? w->err + 8 : nullptr;   // the 3xTF32 launch's split choice
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
@@ -1624,6 +1628,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   const bool f32 = precision == SED_PREC_FP32;
   EpiBwdArgs eb{};
   eb.n = n; eb.ldn = w->ldn; eb.Y = w->Y; eb.O = w->O; eb.rs = w->rs;
+  eb.O2 = w->O2; eb.o2_split = precision == SED_PREC_FP32 ? w->err + 8 : nullptr;
   eb.md = M->dv; eb.g = g->dv; eb.split = f32 ? 1 : 0;
   eb.gy_hi = w->G_hi; eb.gy_lo = w->G_lo; eb.go_hi = w->GO_hi; eb.go_lo = w->GO_lo;
   eb.rgrad = w->rgrad; eb.lnl = lnl_out; eb.status = row_status; eb.err = w->err;

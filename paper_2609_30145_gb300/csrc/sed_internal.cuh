@@ -347,8 +347,10 @@ struct Workspace {
   uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
   float* Y = nullptr;            // [cap_seg][cap_rows][ldn]: one slab per attenuated block
   float* O = nullptr;
+  float* O2 = nullptr;           // [rows][ldn] second half of the old part (a split 3xTF32 launch)
   RowScal* rs = nullptr;
-  int* err = nullptr;            // device error word of bounded waits
+  int* err = nullptr;            // device error word of bounded waits (err[0]); err[8]: the 3xTF32
+                                 // launch's split choice
   float* theta_h = nullptr;      // host-path staging (device)
   double* lnl_h = nullptr;
   uint32_t* st_h = nullptr;
@@ -567,6 +569,8 @@ struct TcArgs {
                                           // (for FP8, Ky_pad/Kpad are the FP8 layout's Ky_pad8/Kpad8)
   const TcMaps* maps;
   float* Y; float* O; int* err;
+  float* O2;           // 3xTF32: second half of the old part if the launch splits its tiles, or NULL
+  int* split_out;      // the launch's choice (1: the old part is O + O2), or NULL
   const int* tile_win; // non-NULL (and <= 64 M tiles): persistent schedule over the computed tiles
   const uint32_t* kmask; int kmask_w;   // K tiles some row of each 128-row tile touches (NULL: all)
   int n_seg;           // attenuated blocks of the young part (0 or 1: one), block s of the main layout's
@@ -600,6 +604,8 @@ cudaError_t launch_dw_tc(const DwArgs& a, cudaStream_t s);
 struct EpiArgs {
   int n; int ldn;
   const float* Y; const float* O;
+  const float* O2;       // second half of the old part, added to O where *split is 1 (NULL: none)
+  const int* split;      // the contraction's choice (written by it before this kernel runs), or NULL
   const RowScal* rs;
   ModelDev md; GridDev g;
   const ModelDev* mtab;    // as in PrepArgs; with row_model set, smem_samp / smem_pix give the
@@ -620,6 +626,8 @@ cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 struct EpiBwdArgs {
   int n; int ldn;
   const float* Y; const float* O;
+  const float* O2;       // as in EpiArgs
+  const int* o2_split;
   const RowScal* rs;
   ModelDev md; GridDev g;
   int split;            // 1: write G as TF32 hi/lo parts (3xTF32), 0: exact FP32 into *_hi

@@ -68,7 +68,7 @@ struct SrvSlot {
   int* tile_win = nullptr;      // [2][ceil(max_rows/128)] node windows of the 128-row tiles
   double* lnl = nullptr;
   uint32_t* st = nullptr;
-  float *W = nullptr, *W_hi = nullptr, *W_lo = nullptr, *Y = nullptr, *O = nullptr;
+  float *W = nullptr, *W_hi = nullptr, *W_lo = nullptr, *Y = nullptr, *O = nullptr, *O2 = nullptr;
   __nv_bfloat16* W_bf16 = nullptr;
   uint8_t* W_f8 = nullptr;
   RowScal* rs = nullptr;
@@ -213,11 +213,13 @@ cudaError_t issue_launch(sed_server* sv, SrvSlot& sl) {
     ta.Kpad = f8 ? L->Kpad8 : L->Kpad;
     ta.maps = &sl.maps; ta.Y = sl.Y; ta.O = sl.O; ta.err = sl.err; ta.rs = sl.rs;
     ta.tile_win = sl.tile_win;
+    ta.O2 = sl.O2; ta.split_out = sl.err + 8;   // err[8]: the launch records whether it split its tiles
     e = launch_contract_tc(ta, s);
   }
   if (e != cudaSuccess) return e;
   EpiArgs ea{};
   ea.n = n; ea.ldn = sv->ldn; ea.Y = sl.Y; ea.O = sl.O; ea.rs = sl.rs;
+  ea.O2 = sl.O2; ea.split = sv->prec == SED_PREC_FP32 ? sl.err + 8 : nullptr;   // same choice as sed_loglike
   ea.g = g->dv;
   ea.mtab = sv->mtab; ea.row_model = sl.rowm;
   ea.smem_samp = sv->max_samp; ea.smem_pix = sv->max_pix; ea.smem_win = sv->max_win;
@@ -352,7 +354,7 @@ sed_status sed_server_create(sed_ctx* ctx, const sed_server_desc* d, sed_server*
     ok = ok && dmalloc(sv, sl.dev, &sl.theta, R * SRV_LD * 4) && dmalloc(sv, sl.dev, &sl.rowm, R * 4) &&
          dmalloc(sv, sl.dev, &sl.lnl, R * 8) && dmalloc(sv, sl.dev, &sl.st, R * 4) &&
          dmalloc(sv, sl.dev, &sl.W, R * K * 4) && dmalloc(sv, sl.dev, &sl.Y, R * N * 4) &&
-         dmalloc(sv, sl.dev, &sl.O, R * N * 4) &&
+         dmalloc(sv, sl.dev, &sl.O, R * N * 4) && dmalloc(sv, sl.dev, &sl.O2, R * N * 4) &&
          dmalloc(sv, sl.dev, &sl.rs, R * sizeof(RowScal)) &&
          dmalloc(sv, sl.dev, &sl.err, 256) && dmalloc(sv, sl.dev, &sl.perm, R * 4) &&
          dmalloc(sv, sl.dev, &sl.tile_win, 2 * ((R + 127) / 128) * 4);
