@@ -233,18 +233,26 @@ __global__ void __launch_bounds__(EPI_THREADS, 7) k_epilogue(const __grid_consta
         v = Fs[k] + t * (Fs[k + 1] - Fs[k]);
         valid = true;
       } else {
+        // the nodes within 5 dispersions: a superset of them from the index
+        // table alone (each entry within one node of the exact bracket; the
+        // margins cover that), clamped to the row's window, which holds every
+        // node within 5 dispersions of a pixel; a node past 5 dispersions
+        // weighs exactly 0, so the sums are those over the nodes inside, in
+        // the same order, and the loop carries no branch (its loads pipeline)
         const float inv_s = 1.f / s;
-        const int jlo = locate_ln(g, fmaxf(xh - 5.f * s, ll0), g.lnl_hi);
-        const int jhi = locate_ln(g, fminf(xh + 5.f * s, llN), g.lnl_hi) + 1;
+        int qa = (int)((fmaxf(xh - 5.f * s, ll0) - g.lut_x0) * g.lut_inv_h);
+        int qb = (int)((fminf(xh + 5.f * s, llN) - g.lut_x0) * g.lut_inv_h);
+        qa = min(max(qa, 0), g.lut_n - 1);
+        qb = min(max(qb, 0), g.lut_n - 1);
+        const int jlo = max(g.lut[qa] - 1, k_lo), jhi = min(g.lut[qb] + 3, k_hi);
         float sw = 0.f, sf = 0.f;
+#pragma unroll 4
         for (int j = jlo; j <= jhi; ++j) {
           const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
           const float u = d * inv_s;
-          if (fabsf(u) <= 5.f) {
-            const float w = __expf(-0.5f * u * u);
-            sw += w;
-            sf = fmaf(w, Fs[j], sf);
-          }
+          const float w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
+          sw += w;
+          sf = fmaf(w, Fs[j], sf);
         }
         if (sw > 0.f) { v = sf / sw; valid = true; }
       }
