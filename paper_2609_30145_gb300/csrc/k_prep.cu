@@ -524,8 +524,12 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __shared__ unsigned long long s_mpart[PREP_THREADS / 32];   // per warp
   __shared__ int s_alim;
   __shared__ uint32_t s_km[KMASK_WORDS];
+  __shared__ uint32_t s_wprev[KMASK_WORDS];   // K tiles of this W row that may hold non-zeros from before
   if (tid == 0) s_alim = 0;
-  if (tid < KMASK_WORDS) s_km[tid] = 0u;
+  if (tid < KMASK_WORDS) {
+    s_km[tid] = 0u;
+    s_wprev[tid] = a.wmask ? a.wmask[(size_t)p * KMASK_WORDS + tid] : 0xffffffffu;
+  }
 
   // ---- in the shadow of the row's loads: finiteness of the whole row; T_max
   //      (warp 0: the SFH edges wait for it); the bins' [Fe/H] brackets and the
@@ -591,6 +595,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     }
     if (a.W_f8)
       for (int k = tid; k < L.Kpad8; k += blockDim.x) a.W_f8[(size_t)p * L.Kpad8 + k] = 0;
+    if (a.wmask && tid < KMASK_WORDS) a.wmask[(size_t)p * KMASK_WORDS + tid] = 0u;   // the row is all zeros now
     if (tid == 0) {
       RowScal rs{};
       rs.status = status;
@@ -698,6 +703,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
         qpart = fmaf(v[j], qq[j], qpart);   // q_s is 0 past the young block
         nnz += v[j] != 0.f;
       }
+      bool store = in;
       if (a.kmask) {
         // one K tile holds 32, 64 or 128 columns, i.e. 8, 16 or 32 lanes' quads:
         // the lowest lane of each tile's group sets its bit
@@ -706,8 +712,11 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
         const unsigned grp = __match_any_sync(0xffffffffu, t);
         const unsigned tb = __ballot_sync(0xffffffffu, touched && in);
         if ((tb & grp) && lane == __ffs(grp) - 1) atomicOr(&s_km[t >> 5], 1u << (t & 31));
+        // a tile this row does not touch holds zeros: written only where the
+        // row at this position may have left non-zeros
+        if (a.wmask) store = in && ((tb & grp) != 0u || ((s_wprev[t >> 5] >> (t & 31)) & 1u));
       }
-      if (!in) continue;
+      if (!store) continue;
       const size_t o = (size_t)p * Kpad + k4;
       if (a.W) *reinterpret_cast<float4*>(a.W + o) = make_float4(v[0], v[1], v[2], v[3]);
       if (a.W_hi) {
@@ -873,6 +882,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   if (lane == 0) { s_red[warp] = qpart; s_nnz[warp] = nnz; }   // 0 from the last warp
   __syncthreads();
   if (a.kmask && tid < a.kmask_w && s_km[tid]) atomicOr(&a.kmask[(size_t)(p >> 7) * a.kmask_w + tid], s_km[tid]);
+  if (a.wmask && tid < KMASK_WORDS) a.wmask[(size_t)p * KMASK_WORDS + tid] = s_km[tid];   // the tiles written now
 
   // ---- FP8 operand: E4M3 of W_k 2^-e_k 2^-y, with the row's power of two 2^y
   //      chosen so that its largest entry maps to at most 240 (< 448, the E4M3

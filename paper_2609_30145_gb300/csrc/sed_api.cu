@@ -184,7 +184,7 @@ sed_status sed_destroy(sed_ctx* ctx) {
     for (auto& kv : ctx->ws) {
       Workspace* w = kv.second;
       std::vector<void*> v = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
-                              w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
+                              w->wmask, w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                               w->dW, w->rgrad, w->qneb};
       for (void* p : v)
         if (p) cudaFree(p);
@@ -1290,7 +1290,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   // grow: free and reallocate everything (the stream's previous work must finish first)
   cudaStreamSynchronize((cudaStream_t)stream);
   std::vector<void*> old = {w->perm, w->tile_win, w->kmask, w->W, w->W_hi, w->W_lo, w->W_bf16, w->W_f8, w->Y, w->O, w->O2, w->rs, w->err,
-                            w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
+                            w->wmask, w->theta_h, w->lnl_h, w->st_h, w->G_hi, w->G_lo, w->GO_hi, w->GO_lo,
                             w->dW, w->rgrad, w->qneb};
   for (void* p : old)
     if (p) cudaFree(p);
@@ -1310,7 +1310,7 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
   sed_status s = SED_OK;
 #define AL(ptr, nb) if (!s) s = dalloc(ctx, (void**)&w->ptr, nb, no, &w->bytes)
   AL(perm, R * 4); AL(tile_win, 2 * ((R + 127) / 128) * 4); AL(kmask, ((R + 127) / 128) * KMASK_WORDS * 4); AL(W, R * K * 4); AL(W_hi, R * K * 4); AL(W_lo, R * K * 4); AL(W_bf16, R * K * 2); AL(W_f8, R * (K + 128));
-  AL(Y, R * N * 4 * w->cap_seg); AL(O, R * N * 4); AL(O2, R * N * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
+  AL(Y, R * N * 4 * w->cap_seg); AL(O, R * N * 4); AL(O2, R * N * 4); AL(wmask, R * KMASK_WORDS * 4); AL(rs, R * sizeof(RowScal)); AL(err, 64);
   AL(theta_h, R * 1024 * 4); AL(lnl_h, R * 8); AL(st_h, R * 4); AL(qneb, R * MAX_NEB_AGE * 4);
   if (grad || had_grad) {
     AL(G_hi, R * N * 4 * w->cap_seg); AL(G_lo, R * N * 4 * w->cap_seg); AL(GO_hi, R * N * 4); AL(GO_lo, R * N * 4);
@@ -1393,6 +1393,19 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
     const bool use = precision == SED_PREC_FP32 && M->dv.zmode == 1 && pairs > 1 && kw <= KMASK_WORDS;
     pa.kmask = use ? w->kmask : nullptr;
     pa.kmask_w = use ? kw : 0;
+    // the masked 3xTF32 fit writes only its rows' touched K tiles of W (and
+    // zeros where the row at the same position had non-zeros); other writes of
+    // W_hi/W_lo are dense and leave the tracked tiles unknown
+    pa.wmask = nullptr;
+    if (use && pa.W_hi) {
+      if (w->wmask_kpad != L->Kpad) {
+        CK(cudaMemsetAsync(w->wmask, 0xff, (size_t)w->cap_rows * KMASK_WORDS * sizeof(uint32_t), s));
+        w->wmask_kpad = L->Kpad;
+      }
+      pa.wmask = w->wmask;
+    } else if (pa.W_hi) {
+      w->wmask_kpad = 0;
+    }
     pa.kt_shift = shift;
     w->kmask_w_call = pa.kmask_w;
     if (ctx->profiling) { w->last_kmask_w = pa.kmask_w; w->last_kt_shift = shift; }

@@ -343,6 +343,12 @@ struct Workspace {
   int* tile_win = nullptr;       // [2][ceil(rows/128)] per-tile node windows
   uint32_t* kmask = nullptr;     // [ceil(rows/128)][KMASK_WORDS] per-tile K-tile occupancy
   int kmask_w_call = 0;          // words per tile of the current call's masks (0: the call has none)
+  // The K tiles of W_hi/W_lo row p that may hold non-zeros (bit set), for the
+  // layout of row stride wmask_kpad (0: unknown -- every bit set first): a
+  // K-tile-masked 3xTF32 call writes only its rows' touched tiles and zeros
+  // over the tiles the row at that position touched before
+  uint32_t* wmask = nullptr;     // [rows][KMASK_WORDS]
+  int wmask_kpad = 0;
   __nv_bfloat16* W_bf16 = nullptr;
   uint8_t* W_f8 = nullptr;       // [rows][Kpad8] E4M3
   float* Y = nullptr;            // [cap_seg][cap_rows][ldn]: one slab per attenuated block
@@ -454,6 +460,9 @@ struct PrepArgs {
                        // (launch_prep clears them), or NULL
   int kmask_w;         // words per 128-row tile (<= KMASK_WORDS)
   int kt_shift;        // log2 of the columns of one K tile of the contraction's layout (5, 6 or 7)
+  uint32_t* wmask;     // with kmask and W_hi: [n][KMASK_WORDS] K tiles of each W row that may hold
+                       // non-zeros from before (read) and that hold them now (written); the row's
+                       // other tiles are zeros and are not written.  NULL: every column written
   float* qneb;         // nebular age axis: [n][MAX_NEB_AGE] Q-weighted weight of each nebular SSP age, or NULL
 };
 // A pixel's rest-frame ln(lambda) = ln(lambda_obs) - ln(1+z), both given as
