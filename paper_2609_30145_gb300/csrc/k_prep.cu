@@ -677,15 +677,27 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
     // four consecutive columns per lane (one int4 of column codes, vector
     // stores); a warp step spans 128 columns, so the loop is uniform per warp
     // and the K-tile mask needs no partial-warp ballot
-    for (int kb = warp * 128; kb < Kpad; kb += PREP_KWARPS * 128) {
+    // the column codes and Q of the next step are loaded before this step's
+    // work (the loop's latency is these loads, not its arithmetic)
+    constexpr int KSTEP = PREP_KWARPS * 128;
+    auto load_cols = [&](int kb, int4& cd, float4& qs) {
       const int k4 = kb + 4 * lane;
-      const bool in = k4 < Kpad;   // Kpad is a multiple of 32, so a lane's four columns are all in or all out
-      int4 cd = make_int4(-1, -1, -1, -1);
-      float4 qs = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (in) {
+      cd = make_int4(-1, -1, -1, -1);
+      qs = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k4 < Kpad) {
         cd = __ldg(reinterpret_cast<const int4*>(L.k_code + k4));
         if (k4 < L.Ky_pad) qs = __ldg(reinterpret_cast<const float4*>(L.q_s + k4));
       }
+    };
+    int4 cd_next;
+    float4 qs_next;
+    load_cols(warp * 128, cd_next, qs_next);
+    for (int kb = warp * 128; kb < Kpad; kb += KSTEP) {
+      const int k4 = kb + 4 * lane;
+      const bool in = k4 < Kpad;   // Kpad is a multiple of 32, so a lane's four columns are all in or all out
+      const int4 cd = cd_next;
+      const float4 qs = qs_next;
+      if (kb + KSTEP < Kpad) load_cols(kb + KSTEP, cd_next, qs_next);
       const int cc[4] = {cd.x, cd.y, cd.z, cd.w};
       const float qq[4] = {qs.x, qs.y, qs.z, qs.w};
       float v[4];
@@ -709,7 +721,9 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
         // the lowest lane of each tile's group sets its bit
         const int q = a.W_f8 ? (k4 < L.Ky_pad ? k4 : k4 + f8_shift) : k4;
         const int t = q >> a.kt_shift;
-        const unsigned grp = __match_any_sync(0xffffffffu, t);
+        // 32-column tiles (3xTF32) are the quads of lanes 8g..8g+7 (a warp step
+        // starts on a 128-column boundary); other layouts group by tile
+        const unsigned grp = a.kt_shift == 5 && !a.W_f8 ? 0xffu << (lane & ~7) : __match_any_sync(0xffffffffu, t);
         const unsigned tb = __ballot_sync(0xffffffffu, touched && in);
         if ((tb & grp) && lane == __ffs(grp) - 1) atomicOr(&s_km[t >> 5], 1u << (t & 31));
         // a tile this row does not touch holds zeros: written only where the
