@@ -41,6 +41,7 @@ FLOOR_WORKLOAD = "specphot_afe_floor_107x12x5x6000_b2048"    # the same with eve
 LINSFH_WORKLOAD = "phot_linsfh_107x12x6000_b1024"   # the headline fit with the linear SFH scheme
 LINES_WORKLOAD = "specphot_lines_107x12x6000_b1024"  # JADES-like: emission lines, spectrum, line catalogue
 PRECS = ("fp32", "fp32_simt", "bf16", "fp8")
+SELF_ORDER_MAX = 1024   # a device-theta batch of at most this many rows (one fit, no K-tile masks) runs no ordering kernel
 PREC_NOTE = {"fp32": "3xTF32 split on tcgen05, FP32 accumulate, FP64 likelihood sums",
              "bf16": "BF16 tcgen05, FP32 accumulate, FP64 likelihood sums",
              "fp8": "FP8 E4M3 tcgen05 (power-of-two scales per SSP column and per row), FP32 accumulate, FP64 likelihood sums",
@@ -474,13 +475,15 @@ def run_ours(args):
                       "n_sfh": w.n_sfh, "n_filt": int(len(filt[0])), "nebular": bool(w.use_nebular),
                       "dust": "birth-cloud power law + Kriek & Conroy 2013 diffuse",
                       "precision": PREC_NOTE[prec],
-                      "step": "one sed_loglike call over the batch (4 kernels: row order, prep, contraction, epilogue), replayed as a CUDA graph",
+                      "step": "one sed_loglike call over the batch (%s), replayed as a CUDA graph" % (
+                          "3 kernels: prep (rows placed in redshift order by the prep kernel itself), contraction, epilogue"
+                          if B <= SELF_ORDER_MAX else "4 kernels: row order, prep, contraction, epilogue"),
                       "l2": "flushed before every timed step (256 MiB memset, outside the timing)",
                       "parallelism": f"replicas x{world} (independent batches per GPU)",
                       "comm": comm},
            "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "what": "device time of one batch step"},
            "variants": variants, "roofline": roof, "clocks": ck, "e2e": e2e,
-           "gpu_launches": 4 * args.steps}
+           "gpu_launches": (3 if B <= SELF_ORDER_MAX else 4) * args.steps}
     if rank == 0 and world == 1 and not args.no_grad:
         out["gradient"] = bench_gradient(ctx, device, flush, args)
     if rank == 0 and world == 1 and args.serve_requests > 0:

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   __shared__ float mlb[EB_MAX_BANDS], ubm[EB_MAX_BANDS];   // lines: each band's line part, dlnL/dm_b
   __shared__ double red[EB_WARPS][EB_NRED + EB_NREDB];
 
+  if (a.win_reset && r == 0) empty_windows(a.win_reset, a.win_mt);
   const size_t ro = (size_t)r * a.ldn;
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(EPI_THREADS, 7) k_epilogue(const __grid_consta
   __shared__ float cal_L[SED_MAX_CALIB * SED_MAX_CALIB], cal_D[SED_MAX_CALIB], cal_c[SED_MAX_CALIB];  // M = L L^T, 1/L_ii, c*
   __shared__ double cal_fix;                       // the row's lnL terms that do not sum over pixels
 
+  if (a.win_reset && r == 0) empty_windows(a.win_reset, a.win_mt);
   RowScal rs = a.rs[r];
   if (a.err && *a.err) rs.status |= SED_ROW_DEVICE_TIMEOUT;
   const int ro = rs.orig;   // the caller's row index

@@ -489,30 +489,42 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_order(const __grid_constant__
 
 constexpr int PREP_THREADS = 128;
 constexpr int PREP_KWARPS = PREP_THREADS / 32 - 1;   // warps writing W; the last one assembles the row's scalars
+// Largest launch that orders itself (PrepArgs::self_order): each CTA reads
+// every row's redshift, so the cost grows with n^2
+constexpr int SELF_ORDER_MAX = 1024;
+static_assert(SELF_ORDER_MAX <= 2 * MAX_SFH + 1, "the redshifts are staged in the edge and rate arrays");
 
 // Row p of the launch processes the caller's row r = perm[p] and records r in
 // RowScal::orig; every later kernel indexes by p and writes results to r.
+// Self-ordered (a.self_order): CTA b processes the caller's row r = b, and its
+// last warp finds p, the row's place in the order k_order would give by
+// counting the rows whose (redshift bin, index) key is below its own (stable
+// counting sort over the same bins; every CTA forms the same keys).
 template <bool MULTI>
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepKernelArgs ka) {
   const PrepArgs& a = ka.p;
   pdl_enter();
-  const int p = blockIdx.x;
-  const int r = a.perm ? a.perm[p] : p;
+  const int b = blockIdx.x;
+  const int r = a.self_order ? b : (a.perm ? a.perm[b] : b);
   const ModelDev& md = MULTI ? a.mtab[a.row_model[r]] : a.md;
   const GridDev& g = a.g;
   const LayoutDev& L = a.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* th = a.theta + (size_t)r * a.ld;
   const int NT = md.n_sfh, NA = g.n_age, NZ = g.n_feh;
-  if (p == 0 && tid == 0 && a.err) *a.err = 0;
+  if (b == 0 && tid == 0 && a.err) *a.err = 0;
 
   extern __shared__ float smem[];
   float* Ws = smem;                     // [NA][NZ]
   // the row's parameters, read once (coalesced) into the tail of the dynamic
   // shared memory: theta may be the caller's pinned host buffer, read in place
   float* th_s = smem + (size_t)NA * NZ + (a.W_f8 ? L.Kpad : 0);
-  __shared__ float T[MAX_SFH + 1];      // edges
-  __shared__ float rate[MAX_SFH];       // m_i / dT_i
+  // edges T[0..NT] and rates m_i / dT_i; before them (self-ordered launch) the
+  // launch's redshifts
+  __shared__ float s_trate[2 * MAX_SFH + 1];
+  float* T = s_trate;
+  float* rate = s_trate + MAX_SFH + 1;
+  __shared__ int s_pos;
   __shared__ int zb[MAX_SFH];
   __shared__ float zt[MAX_SFH];
   __shared__ float s_red[PREP_THREADS / 32];
@@ -526,10 +538,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   __shared__ uint32_t s_km[KMASK_WORDS];
   __shared__ uint32_t s_wprev[KMASK_WORDS];   // K tiles of this W row that may hold non-zeros from before
   if (tid == 0) s_alim = 0;
-  if (tid < KMASK_WORDS) {
-    s_km[tid] = 0u;
-    s_wprev[tid] = a.wmask ? a.wmask[(size_t)p * KMASK_WORDS + tid] : 0xffffffffu;
-  }
+  if (tid < KMASK_WORDS) s_km[tid] = 0u;
 
   // ---- in the shadow of the row's loads: finiteness of the whole row; T_max
   //      (warp 0: the SFH edges wait for it); the bins' [Fe/H] brackets and the
@@ -546,11 +555,41 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   }
   for (int j = tid; j < md.n_fixed; j += blockDim.x) th_s[md.n_param + j] = md.fixed_v[j];   // fixed keys
   unsigned long long mpart = 0ull;
+  const bool rank_warp = a.self_order && warp == PREP_THREADS / 32 - 1;
   if (warp == 0) {
     const TmaxRow t = row_tmax(md, theta_col(md, th, md.offs[SED_KEY_ZRED]), theta_col(md, th, md.offs[SED_KEY_LOGMASS]));
     if (lane == 0) { s_tmax = t.tmax; s_lrat = t.lrat; s_zst = t.status; }
+  } else if (rank_warp) {
+    // the row's place in the redshift order: the valid redshifts (z in
+    // [0, z_f), others -1) and their range, then the keys of k_order's bins
+    // over that range (invalid rows in the last bin) and the count of rows
+    // whose (key, index) is below this row's
+    float* zs = s_trate;
+    const int zoff = md.offs[SED_KEY_ZRED];
+    int lo = 0x7f7fffff, hi = 0;
+#pragma unroll 8
+    for (int j = lane; j < a.n; j += 32) {
+      const float z = a.theta[(size_t)j * a.ld + zoff];
+      const float zv = z >= 0.f && z < (float)md.zf ? z : -1.f;
+      zs[j] = zv;
+      if (zv >= 0.f) { lo = min(lo, __float_as_int(zv)); hi = max(hi, __float_as_int(zv)); }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    __syncwarp();
+    const float zlo = __int_as_float(lo), zr = fmaxf(__int_as_float(hi) - zlo, 1e-6f);
+    const float fscale = (float)ORDER_BINS / zr;
+    auto key = [&](float z) { return z >= 0.f ? min(ORDER_BINS - 1, (int)((z - zlo) * fscale)) : ORDER_BINS; };
+    const int kb = key(zs[b]);
+    int below = 0;
+    for (int j = lane; j < a.n; j += 32) {
+      const int kj = key(zs[j]);
+      below += kj < kb || (kj == kb && j < b);
+    }
+    below = __reduce_add_sync(0xffffffffu, below);
+    if (lane == 0) s_pos = below;
   } else {
-    constexpr int NB = PREP_THREADS - 32;
+    const int NB = PREP_THREADS - 32 - (a.self_order ? 32 : 0);
     for (int j = tid - 32; j < NA * NZ; j += NB) Ws[j] = 0.f;
     for (int i = tid - 32; i < NT; i += NB) {
       int j0, j1;
@@ -565,6 +604,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   if (lane == 0) s_mpart[warp] = mpart;
   bad = __syncthreads_or(bad);
   th = th_s;
+  const int p = a.self_order ? s_pos : b;   // the row's place in the launch's order
+  if (tid < KMASK_WORDS) s_wprev[tid] = a.wmask ? a.wmask[(size_t)p * KMASK_WORDS + tid] : 0xffffffffu;
   uint32_t status = bad ? SED_ROW_BAD_THETA : 0u;
   // a sampled sigma_gal outside the model's declared range [0, max]
   if (!status && md.sample_sgal) {
@@ -1190,8 +1231,12 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   // a fixed redshift (no column) needs no redshift order: the caller's order is kept
   const bool z_col = p.md.offs[SED_KEY_ZRED] < p.md.n_param;
   const int mt = (p.n + 127) / 128;
-  const bool order = p.perm && (p.row_model || z_col);
-  if (!order) {   // no ordering kernel to start the windows and masks empty
+  // a small single-fit launch without K-tile masks orders itself; its windows
+  // start empty because the last kernel of every call that filled them (the
+  // epilogue) empties them again, and the workspace starts them empty
+  const bool self = p.self_order && z_col && !p.row_model && !p.kmask && p.n <= SELF_ORDER_MAX;
+  const bool order = !self && p.perm && (p.row_model || z_col);
+  if (!order && !self) {   // no ordering kernel to start the windows and masks empty
     if (p.tile_win) {
       e = cudaMemsetAsync(p.tile_win, 0x7f, mt * sizeof(int), s);
       if (e == cudaSuccess) e = cudaMemsetAsync(p.tile_win + mt, 0xff, mt * sizeof(int), s);
@@ -1217,7 +1262,8 @@ cudaError_t launch_prep(const PrepArgs& p, cudaStream_t s) {
   }
   PrepKernelArgs ka;
   ka.p = p;
-  if (!p.row_model && !z_col) ka.p.perm = nullptr;
+  ka.p.self_order = self ? 1 : 0;
+  if (self || (!p.row_model && !z_col)) ka.p.perm = nullptr;
   // Ws [n_age][n_feh], the FP8 row scratch, the row's parameters (n_param <= ld
   // and n_param <= 2 MAX_SFH + SED_NKEYS + 2 MAX_DUST_BIN for every model)
   // (+ the fixed keys' values past the caller's columns)

@@ -1317,8 +1317,11 @@ sed::Workspace* get_ws(sed_ctx* ctx, void* stream, int rows, int kpad, int ldn, 
     AL(dW, R * K * 4); AL(rgrad, R * RGRAD * 8);
   }
 #undef AL
-  if (!s) {
+  if (!s) {   // the error words cleared, the per-tile windows empty (k_prep's self-ordered launches expect it)
     cudaError_t e = cudaMemset(w->err, 0, 64);
+    const size_t mt = (R + 127) / 128;
+    if (e == cudaSuccess) e = cudaMemset(w->tile_win, 0x7f, mt * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(w->tile_win + mt, 0xff, mt * sizeof(int));
     if (e != cudaSuccess) s = fail(ctx, SED_ECUDA, "cudaMemset: %s", cudaGetErrorString(e));
   }
   *st = s;
@@ -1346,9 +1349,10 @@ sed_status prof_mark(sed_ctx* ctx, Workspace* w, int i, cudaStream_t s) {
   return SED_OK;
 }
 
-// prep + contraction into ws->Y / ws->O
+// prep + contraction into ws->Y / ws->O; theta_dev: theta is device memory
+// (not a mapped host buffer), so the prep kernel may order the rows itself
 sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* theta, int n, int ld,
-                            int precision, cudaStream_t s) {
+                            int precision, cudaStream_t s, bool theta_dev = true) {
   Grid* g = M->g;
   Layout* L = M->L;
   if (ctx->profiling) {
@@ -1380,6 +1384,7 @@ sed_status run_forward_core(sed_ctx* ctx, Model* M, Workspace* w, const float* t
   pa.perm = w->perm;
   pa.qneb = M->dv.use_neb && g->neb_na > 0 ? w->qneb : nullptr;
   pa.tile_win = w->tile_win;
+  pa.self_order = theta_dev ? 1 : 0;
   // K-tile masks for the tensor-core contractions (32 / 64 / 128 columns per tile)
   {
     const int shift = precision == SED_PREC_FP8 ? 7 : (precision == SED_PREC_BF16 ? 6 : 5);
@@ -1476,6 +1481,7 @@ sed_status sed_forward(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
+  ea.win_reset = w->tile_win; ea.win_mt = (n + 127) / 128;   // read by the contraction, emptied for the next call
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   ea.phot_out = M->dv.n_filt ? phot_out : nullptr;
   ea.spec_out = M->dv.n_pix ? spec_out : nullptr;
@@ -1505,6 +1511,7 @@ sed_status sed_line_fluxes(sed_ctx* ctx, sed_model_id id, const float* theta, in
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
+  ea.win_reset = w->tile_win; ea.win_mt = (n + 127) / 128;   // read by the contraction, emptied for the next call
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   ea.lines_out = flux_out;
   ea.err = w->err;
@@ -1512,8 +1519,9 @@ sed_status sed_line_fluxes(sed_ctx* ctx, sed_model_id id, const float* theta, in
   return prof_mark(ctx, w, 3, s);
 }
 
-sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
-                       uint32_t* row_status, int precision, void* stream) {
+// sed_loglike; theta_dev false for a mapped host theta (sed_loglike_host)
+static sed_status loglike_impl(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
+                               uint32_t* row_status, int precision, void* stream, bool theta_dev) {
   if (!ctx) return SED_EINVAL;
   Model* M = find_model(ctx, id);
   sed_status st = check_hot_args(ctx, M, theta, n, ld, precision);
@@ -1524,7 +1532,7 @@ sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   cudaStream_t s = (cudaStream_t)stream;
   Workspace* w = get_ws(ctx, stream, n, M->L->Kpad, ldn_for(M->g), false, &st, M->L->n_seg);
   if (!w) return st;
-  st = run_forward_core(ctx, M, w, theta, n, ld, precision, s);
+  st = run_forward_core(ctx, M, w, theta, n, ld, precision, s, theta_dev);
   if (st) return st;
   EpiArgs ea{};
   ea.n = n; ea.ldn = w->ldn; ea.Y = w->Y; ea.O = w->O; ea.rs = w->rs;
@@ -1532,10 +1540,16 @@ sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n,
   ea.md = M->dv; ea.g = M->g->dv;
   ea.seg_stride = (size_t)w->cap_rows * w->ldn;
   ea.qneb = M->dv.use_neb && M->g->neb_na > 0 ? w->qneb : nullptr;
+  ea.win_reset = w->tile_win; ea.win_mt = (n + 127) / 128;   // read by the contraction, emptied for the next call
   ea.lnl = lnl_out; ea.status = row_status; ea.err = w->err;
   ea.lam8 = precision == SED_PREC_FP8 ? M->L->lam8 : nullptr;
   CK(launch_epilogue(ea, s));
   return prof_mark(ctx, w, 3, s);
+}
+
+sed_status sed_loglike(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
+                       uint32_t* row_status, int precision, void* stream) {
+  return loglike_impl(ctx, id, theta, n, ld, lnl_out, row_status, precision, stream, true);
 }
 
 sed_status sed_loglike_host(sed_ctx* ctx, sed_model_id id, const float* theta, int n, int ld, double* lnl_out,
@@ -1575,7 +1589,7 @@ sed_status sed_loglike_host(sed_ctx* ctx, sed_model_id id, const float* theta, i
         sed_status cs = SED_OK;
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          cs = sed_loglike(ctx, id, th_d, n, ld, lnl_d, st_d, precision, stream);
+          cs = loglike_impl(ctx, id, th_d, n, ld, lnl_d, st_d, precision, stream, false);
           e = cudaStreamEndCapture(s, &gr);
         }
         if (e == cudaSuccess && cs == SED_OK && gr) e = cudaGraphInstantiate(&w->host_exec, gr, 0);
@@ -1603,8 +1617,8 @@ sed_status sed_loglike_host(sed_ctx* ctx, sed_model_id id, const float* theta, i
     CK(cudaMemcpyAsync(w->theta_h, theta, (size_t)n * ld * 4, cudaMemcpyHostToDevice, s));
     th_d = w->theta_h;
   }
-  st = sed_loglike(ctx, id, th_d, n, ld, lnl_d ? lnl_d : w->lnl_h, row_status && !st_d ? w->st_h : st_d,
-                   precision, stream);
+  st = loglike_impl(ctx, id, th_d, n, ld, lnl_d ? lnl_d : w->lnl_h, row_status && !st_d ? w->st_h : st_d,
+                    precision, stream, th_d == w->theta_h);
   if (st) return st;
   if (!lnl_d) CK(cudaMemcpyAsync(lnl_out, w->lnl_h, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
   if (row_status && !st_d) CK(cudaMemcpyAsync(row_status, w->st_h, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
@@ -1647,6 +1661,7 @@ sed_status sed_loglike_grad(sed_ctx* ctx, sed_model_id id, const float* theta, i
   eb.rgrad = w->rgrad; eb.lnl = lnl_out; eb.status = row_status; eb.err = w->err;
   eb.seg_stride = (size_t)w->cap_rows * w->ldn;
   eb.qneb = M->dv.use_neb && g->neb_na > 0 ? w->qneb : nullptr;
+  eb.win_reset = w->tile_win; eb.win_mt = (n + 127) / 128;   // read by the contraction, emptied for the next call
   size_t smem = 0;
   cudaError_t e = launch_epilogue_bwd(eb, &smem, s);
   if (e == cudaErrorInvalidConfiguration)

@@ -464,7 +464,20 @@ struct PrepArgs {
                        // non-zeros from before (read) and that hold them now (written); the row's
                        // other tiles are zeros and are not written.  NULL: every column written
   float* qneb;         // nebular age axis: [n][MAX_NEB_AGE] Q-weighted weight of each nebular SSP age, or NULL
+  int self_order;      // 1: the prep kernel finds each row's place in the redshift order itself (no
+                       // k_order launch) where launch_prep allows it: one fit, no K-tile masks, a
+                       // redshift column, n <= SELF_ORDER_MAX, theta in device memory (each CTA
+                       // reads every row's redshift), and tile_win already empty
 };
+// Per-tile windows (lo, hi) of the contraction back to empty (lo 0x7f7f7f7f,
+// hi -1) once their reader has finished, by one CTA, so that the next call's
+// prep kernel can fill them without an ordering kernel or memsets before it.
+__device__ __forceinline__ void empty_windows(int* win, int mt) {
+  for (int i = threadIdx.x; i < mt; i += blockDim.x) {
+    win[i] = 0x7f7f7f7f;
+    win[mt + i] = -1;
+  }
+}
 // A pixel's rest-frame ln(lambda) = ln(lambda_obs) - ln(1+z), both given as
 // FP32 pairs {hi, lo}, returned as an FP32 pair: the high parts' difference is
 // made exact by Knuth's two-sum (s + e = p.hi - z_hi), the low parts join its
@@ -628,6 +641,8 @@ struct EpiArgs {
   int lines_off;       // set by launch_epilogue: float offset of the emission lines' shared arrays
   size_t seg_stride;   // age-binned dust: Y of attenuated block s at Y + s seg_stride
   const float* qneb;   // nebular age axis: [n][MAX_NEB_AGE] (k_prep's), or NULL
+  int* win_reset;      // [2][win_mt] per-tile windows set back to empty by CTA 0 (the contraction,
+  int win_mt;          // their reader, has finished), or NULL
 };
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 
@@ -647,6 +662,8 @@ struct EpiBwdArgs {
   int lines_off;        // set by launch_epilogue_bwd: byte offset of the emission lines' shared arrays
   size_t seg_stride;    // age-binned dust: Y and dlnL/dY of attenuated block s at + s seg_stride
   const float* qneb;    // nebular age axis: [n][MAX_NEB_AGE] (k_prep's), or NULL
+  int* win_reset;       // as in EpiArgs
+  int win_mt;
 };
 cudaError_t launch_epilogue_bwd(const EpiBwdArgs& a, size_t* smem_needed, cudaStream_t s);
 
