@@ -384,22 +384,37 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
         qb = min(max(qb, 0), g.lut_n - 1);
         jlo = max(g.lut[qa] - 1, k_lo);
         jhi = min(g.lut[qb] + 3, k_hi);
+        // a node past 5 dispersions weighs exactly 0 (its terms add zeros), so
+        // the loop carries no branch and its loads pipeline
         float sw = 0.f, sf = 0.f, swd = 0.f, sfd = 0.f, sws = 0.f, sfs = 0.f;
-        for (int j = jlo; j <= jhi; ++j) {
-          const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
-          const float u = d * inv_s;
-          if (fabsf(u) <= 5.f) {
-            const float w = __expf(-0.5f * u * u);
+        if (md.sample_sgal) {
+#pragma unroll 4
+          for (int j = jlo; j <= jhi; ++j) {
+            const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
+            const float u = d * inv_s;
+            const float w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
             const float wd = w * u * inv_s;   // dw/dx
+            const float ws = wd * u;          // dw/ds = w u^2 / s
+            const float f = Fs[j];
             sw += w;
-            sf = fmaf(w, Fs[j], sf);
+            sf = fmaf(w, f, sf);
             swd += wd;
-            sfd = fmaf(wd, Fs[j], sfd);
-            if (md.sample_sgal) {
-              const float ws = wd * u;          // dw/ds = w u^2 / s
-              sws += ws;
-              sfs = fmaf(ws, Fs[j], sfs);
-            }
+            sfd = fmaf(wd, f, sfd);
+            sws += ws;
+            sfs = fmaf(ws, f, sfs);
+          }
+        } else {
+#pragma unroll 4
+          for (int j = jlo; j <= jhi; ++j) {
+            const float d = (g.lnl_hi[j] - xh) + (g.lnl_lo[j] - xl);
+            const float u = d * inv_s;
+            const float w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
+            const float wd = w * u * inv_s;   // dw/dx
+            const float f = Fs[j];
+            sw += w;
+            sf = fmaf(w, f, sf);
+            swd += wd;
+            sfd = fmaf(wd, f, sfd);
           }
         }
         tl = -1.f - inv_s;
@@ -560,18 +575,16 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
           const int mid = (pb + pe) >> 1;
           if ((prg[mid] & 0xffff) <= k) pb = mid + 1; else pe = mid;
         }
-        for (int p = pa; p < pb; ++p) {   // lo_p <= k <= hi_p for every p here
+        // lo_p <= k <= hi_p for every p here; a pixel with c = 0 (excluded)
+        // adds an exact zero, so the loop carries no branch
+#pragma unroll 4
+        for (int p = pa; p < pb; ++p) {
           const float4 q = px4[p];
-          if (q.z == 0.f) continue;
-          float w;
-          if (q.w > -0.5f) {   // linear row
-            w = k == (prg[p] & 0xffff) ? 1.f - q.w : q.w;
-          } else {              // Gaussian row, 1/sigma = -1 - q.w
-            const float d = (lh - q.x) + (ll - q.y);
-            const float u = d * (-1.f - q.w);
-            w = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
-          }
-          acc = fmaf(q.z, w, acc);
+          const float d = (lh - q.x) + (ll - q.y);
+          const float u = d * (-1.f - q.w);   // Gaussian row: 1/sigma = -1 - q.w
+          const float wg = fabsf(u) <= 5.f ? __expf(-0.5f * u * u) : 0.f;
+          const float wl = k == (prg[p] & 0xffff) ? 1.f - q.w : q.w;   // linear row: q.w = t in [0, 1]
+          acc = fmaf(q.z, q.w > -0.5f ? wl : wg, acc);
         }
       } else {
         int p = 0, p1 = P;
