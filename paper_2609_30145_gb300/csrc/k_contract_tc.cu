@@ -312,12 +312,18 @@ __device__ __forceinline__ float sched_longest(int tiles, int P, int nz, int kt,
   }
   return w;
 }
-// Whether the 3-way split shortens the launch by more than 5 %.
+// Whether the 3-way split shortens the launch by more than 5 % once the
+// epilogue's extra reads are counted: it then reads O2 beside O, a 128 x 128
+// FP32 tile more per tile, about 0.04 of one K tile of a CTA's MMA time per
+// tile of the launch (measured on the photometric fit: 4096 rows split gave a
+// 16 us longer epilogue for no shorter contraction; at 1024 rows, 154 tiles,
+// the split step took 0.099 against 0.109 ms unsplit).
+constexpr float SPLIT_EPI_KT_PER_TILE = 0.04f;
 template <int BN>
 __device__ __forceinline__ bool split_pays(int tiles, int P, int ky, int kt) {
   const int ko = kt - ky, kh = (ko + 1) / 2;
   const float one = sched_longest<BN>(tiles, P, 1, kt, kt);
-  const float three = sched_longest<BN>(tiles, P, 3, kt, max(kh, ky));
+  const float three = sched_longest<BN>(tiles, P, 3, kt, max(kh, ky)) + SPLIT_EPI_KT_PER_TILE * (float)tiles;
   return three < 0.95f * one;
 }
 
@@ -371,16 +377,22 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
     // the persistent CTA always works (or frees its tensor memory below):
     // set up first, so that the allocation overlaps the reads of the windows
     setup();
-    // computed wavelength tiles of each M tile, and their prefix counts
-    const int MT = p.m_tiles, NTt = p.ldn / BN;
+    // computed wavelength tiles of each M tile, and their prefix counts.  The
+    // tiles of an M tile start at its window's first node rounded down to 16
+    // columns (not to a whole tile), shifted down where the last one would pass
+    // ldn: every column of the window is computed, with fewer columns outside
+    // it than whole-tile alignment leaves.  A column's sum does not depend on
+    // which tile or tile position computes it.
+    const int MT = p.m_tiles;
     if (threadIdx.x < MT) {
       const int lo = p.tile_win[threadIdx.x], hi = p.tile_win[MT + threadIdx.x];
       int a = 0, c = 0;
       if (hi >= 0) {
-        a = lo / BN;
-        c = min(hi / BN, NTt - 1) - a + 1;
+        a = lo & ~15;
+        c = (min(hi, p.ldn - 1) - a) / BN + 1;
+        a = min(a, p.ldn - c * BN);
       }
-      s_nlo[threadIdx.x] = a;
+      s_nlo[threadIdx.x] = a;   // first column
       s_pref[threadIdx.x + 1] = c;
     }
     __syncthreads();
@@ -478,7 +490,7 @@ __global__ void __launch_bounds__(192, 1) k_contract_tc(const __grid_constant__ 
       u.m0 = m * BM;
       u.km = KSKIP ? p.kmask + m * p.kmask_w : nullptr;   // read through L1 (a few words per M tile)
       if (t >= nfull) u.ncol = BN / npc;   // a piece of a leftover tile
-      u.n0 = (s_nlo[m] + t - s_pref[m]) * BN + pc * u.ncol;
+      u.n0 = s_nlo[m] + (t - s_pref[m]) * BN + pc * u.ncol;
     } else {
       u.m0 = blockIdx.y * BM;
       u.n0 = blockIdx.x * BN;
@@ -707,6 +719,8 @@ static CUresult encode_kmajor(void* fn, CUtensorMap* m, void* base, CUtensorMapD
 //  - FP8 (short units): 64-wide tiles for short K (Kpad <= 2048), one CTA per
 //    tile; 128-wide for the long-K [a/Fe] grid.
 constexpr int TC_LONG_K = 2048;
+int tc_max_m_tiles() { return tc::MAX_MT; }
+
 int tc_bn_for(int prec, int kpad) {
   return (prec != SED_PREC_FP8 || kpad > TC_LONG_K) ? 128 : 64;
 }

@@ -1756,12 +1756,18 @@ sed_status sed_last_stats(sed_ctx* ctx, void* stream, sed_stage_stats* out) {
         kcols[t] = (double)bits * (1 << w->last_kt_shift);
       }
     }
-    double issued = 0;   // wavelength tiles of each 128-row tile's window union x its K columns
+    // wavelength tiles of each 128-row tile's window union x its K columns; the
+    // persistent tensor-core schedule starts a tile's run at the window's first
+    // node rounded down to 16 columns, the grid schedules at a whole tile
+    const bool unaligned = !simt && kcols.size() <= (size_t)tc_max_m_tiles();
+    double issued = 0;
     for (size_t m0 = 0; m0 < rs.size(); m0 += 128) {
       int lo = 0x7fffffff, hi = -1;
       for (size_t r = m0; r < std::min(rs.size(), m0 + 128); ++r)
         if (rs[r].status == 0) { lo = std::min(lo, rs[r].k_lo); hi = std::max(hi, rs[r].k_hi); }
-      if (hi >= 0) issued += (hi / bn - lo / bn + 1) * kcols[m0 / 128];
+      if (hi < 0) continue;
+      const int tiles = unaligned ? (std::min(hi, w->ldn - 1) - (lo & ~15)) / bn + 1 : hi / bn - lo / bn + 1;
+      issued += tiles * kcols[m0 / 128];
     }
     out->issued_flop = issued * 2.0 * 128.0 * bn * (w->last_prec == SED_PREC_FP32 ? 3.0 : 1.0);
   }

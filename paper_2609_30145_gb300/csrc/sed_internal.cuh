@@ -605,6 +605,7 @@ int tc_encode_maps(void* encode_fn, TcMaps* out, int prec, const void* a_hi, con
 cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s);
 // wavelength width of the forward tensor-core tile for a precision and padded K
 int tc_bn_for(int prec, int kpad);
+int tc_max_m_tiles();   // 128-row tiles of the largest launch that runs the persistent schedule
 
 // Adjoint contraction dW = [G_Y SSP_young^T | G_O SSP_old^T] (3xTF32 on tcgen05).
 // G rows have stride ldg; SSP rows [Kpad][ldk] (ldk <= ldg is the reduction length).
