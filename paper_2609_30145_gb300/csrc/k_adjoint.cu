@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(EB_THREADS, 4) k_epi_bwd(const __grid_constant
   // ---- forward: attenuated spectrum in the window (the forward epilogue's
   //      arithmetic); phi holds the window's wavelengths until the photometric
   //      gather starts
-#pragma unroll 4
+#pragma unroll 1
   for (int k = k_lo + tid; k <= k_hi; k += EB_THREADS) {
     if constexpr (VAR == 1) {
       float yv[MAX_SEG];
