@@ -666,14 +666,18 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
   }
   __syncthreads();
 
-  // ---- weights on (age, feh): thread per age node
+  // ---- weights on (age, feh): thread per age node, by the warps that write W
+  //      (a named barrier joins them); the last warp goes straight on to the
+  //      row's cosmology and scalars, which do not read the weights
+  constexpr int NKT = PREP_KWARPS * 32;
+  if (warp < PREP_KWARPS) {
   if (md.sfh_linear) {
     // linear scheme, pass 2: node a gathers the tent shares of the bins over
     // its support [t_{a-1}, t_{a+1}] (and the ages beyond the axis at the end
     // nodes), scaled by each bin's factor and split by the bin's [Fe/H]
-    for (int ag = tid; ag < NA; ag += blockDim.x) lin_node_fill(g, ag, NT, T, m, rate, zb, zt, Ws + ag * NZ, NZ);
+    for (int ag = tid; ag < NA; ag += NKT) lin_node_fill(g, ag, NT, T, m, rate, zb, zt, Ws + ag * NZ, NZ);
   } else
-  for (int ag = tid; ag < NA; ag += blockDim.x) {
+  for (int ag = tid; ag < NA; ag += NKT) {
     const float lo = g.cell_lo[ag], hi = g.cell_hi[ag];
     // first bin whose upper edge is above the cell's lower edge
     int i0 = 0, i1 = NT;
@@ -692,7 +696,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       if (NZ > 1) row[j + 1] += A * t;
     }
   }
-  __syncthreads();
+  asm volatile("bar.sync 1, %0;" ::"r"(NKT) : "memory");
+  }
 
   // ---- [a/Fe] split and the K-ordered row of W; Q_young
   int n0 = 0, n1 = 0;
@@ -899,6 +904,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ P
       }
     }
   }
+  // the passes below read the weights with every warp
+  if (md.n_bin > 0 || (a.qneb && g.neb_na > 0)) __syncthreads();
   if (md.n_bin > 0) {
     // age-binned dust: Q of each attenuated block and of the ages outside
     // every block, from the nebular ages' weights (W_k = w_n Ws[a][m] with the
