@@ -716,14 +716,12 @@ static CUresult encode_kmajor(void* fn, CUtensorMap* m, void* base, CUtensorMapD
 //  - BF16: 128-wide tiles, one CTA per tile (measured on the paper-scale
 //    photometric batch: 20.5 us against 24.6 us with 64-wide tiles, which
 //    read every W tile twice as often).
-//  - FP8 (short units): 64-wide tiles for short K (Kpad <= 2048), one CTA per
-//    tile; 128-wide for the long-K [a/Fe] grid.
-constexpr int TC_LONG_K = 2048;
+//  - FP8: 128-wide tiles as well (measured on the photometric batch, K = 1344:
+//    contraction 18.4 against 20.5 us with 64-wide tiles at 1024 rows, 47.1
+//    against 55.3 us at 4096 rows).
 int tc_max_m_tiles() { return tc::MAX_MT; }
 
-int tc_bn_for(int prec, int kpad) {
-  return (prec != SED_PREC_FP8 || kpad > TC_LONG_K) ? 128 : 64;
-}
+int tc_bn_for(int, int) { return 128; }
 
 int tc_encode_maps(void* fn, TcMaps* out, int prec, const void* a_hi, const void* a_lo, const void* b_hi,
                    const void* b_lo, int n, int n_lam, int kpad) {
@@ -759,7 +757,6 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   // K-tile masks: the 3xTF32 forward only (the host gives no other precision any)
   p.kmask = a.prec == SED_PREC_FP32 && a.kmask_w > 0 && a.kmask_w <= KMASK_WORDS ? a.kmask : nullptr;
   p.kmask_w = a.kmask_w;
-  const bool wide = tc_bn_for(a.prec, a.Kpad) == 128;   // same choice as the box of the B map
   // the attenuated blocks in K tiles of the precision's layout (several blocks
   // are padded to 128 columns each, so they start on a tile of every layout)
   const int kcols = a.prec == SED_PREC_FP32 ? 32 : (a.prec == SED_PREC_FP8 ? 128 : 64);
@@ -776,13 +773,11 @@ cudaError_t launch_contract_tc(const TcArgs& a, cudaStream_t s) {
   if (a.prec == SED_PREC_FP8) {
     p.ky_tiles = a.Ky_pad / 128;
     p.k_tiles = a.Kpad / 128;
-    return wide ? tc::launch_cfg<SED_PREC_FP8, 128, 6, 8, false>(p, a.ldn, s)
-                : tc::launch_cfg<SED_PREC_FP8, 64, 8, 8, false>(p, a.ldn, s);
+    return tc::launch_cfg<SED_PREC_FP8, 128, 6, 8, false>(p, a.ldn, s);
   }
   p.ky_tiles = a.Ky_pad / 64;
   p.k_tiles = a.Kpad / 64;
-  return wide ? tc::launch_cfg<SED_PREC_BF16, 128, 6, 8, false>(p, a.ldn, s)
-              : tc::launch_cfg<SED_PREC_BF16, 64, 8, 8, false>(p, a.ldn, s);
+  return tc::launch_cfg<SED_PREC_BF16, 128, 6, 8, false>(p, a.ldn, s);
 }
 
 constexpr int DW_BN = 128;
