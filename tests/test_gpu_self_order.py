@@ -9,7 +9,8 @@ the host link).  No row's result depends on the order or on which rows share
 its 128-row tile, so both launches must give the same lnL and status bit for
 bit, and agree with the FP64 oracle on sampled rows.  Cases: rows spread in
 redshift, every row at one redshift (all keys equal: the caller's order), rows
-with invalid redshifts (the last bin), one row, a ragged batch, and the limit.
+with invalid redshifts (the last bin), every row invalid, one row, a ragged batch, and the
+limit.
 
 Each call's epilogue empties the per-tile windows that the contraction read,
 so that the next self-ordered call starts from empty windows; a sequence of
@@ -59,6 +60,8 @@ def rows(w, model, n, seed, kind, z_range=None):
         th32[:, zc] = rng.uniform(*z_range, n).astype(np.float32)
     if kind == "one_z":
         th32[:, zc] = np.float32(3.0)
+    elif kind == "all_bad":
+        th32[:, zc] = np.float32(w.zf + 1.0)
     elif kind == "bad_z":
         k = max(n // 7, 1)
         bad = rng.choice(n, k, replace=False)
@@ -83,7 +86,7 @@ def via_ordering_kernel(ctx, model, th32, prec):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp32_simt"])
 @pytest.mark.parametrize("n,kind", [(1, "spread"), (77, "spread"), (300, "one_z"), (300, "bad_z"),
-                                    (1000, "spread"), (1024, "bad_z")])
+                                    (1000, "spread"), (1024, "bad_z"), (1024, "all_bad")])
 def test_self_ordered_launch_matches_ordering_kernel(ctx, prec, n, kind):
     w, orc, model = phot_case(ctx)
     th32 = rows(w, model, n, 100 + n, kind)
@@ -94,6 +97,9 @@ def test_self_ordered_launch_matches_ordering_kernel(ctx, prec, n, kind):
     ok = s_self == 0
     if kind == "bad_z":
         assert (~ok).sum() == max(n // 7, 1) and np.isneginf(l_self[~ok]).all()
+    if kind == "all_bad":   # every row in the invalid bin: no tile is computed, every lnL is -inf
+        assert not ok.any() and np.isneginf(l_self).all()
+        return
     # the FP64 oracle on sampled rows
     idx = np.nonzero(ok)[0]
     sample = np.unique(np.concatenate([idx[:2], idx[-2:], np.random.default_rng(n).choice(idx, min(8, len(idx)),
