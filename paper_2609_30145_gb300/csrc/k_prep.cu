@@ -1173,25 +1173,28 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
     part += (double)gT * (double)T[i] * (double)(i - 2) / ((double)(NT - 2) * tmax);
   }
   double ga = (double)gafe;
+  // one [Fe/H] for every bin: its derivative sums the bins' (thread-strided,
+  // then a fixed tree)
+  double gzp = 0.0;
+  if (md.zmode == 1)
+    for (int i = tid; i < NT; i += blockDim.x) gzp += (double)gzeta[i];
   for (int o = 16; o; o >>= 1) {
     part += __shfl_xor_sync(0xffffffffu, part, o);
     ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    gzp += __shfl_xor_sync(0xffffffffu, gzp, o);
   }
-  if (lane == 0) { s_tmax_part[warp] = part; red[warp] = ga; }
+  __shared__ double s_zeta_part[PREP_BWD_THREADS / 32];
+  if (lane == 0) { s_tmax_part[warp] = part; red[warp] = ga; s_zeta_part[warp] = gzp; }
   __syncthreads();
   if (tid == 0) {
-    double gtmax = 0.0, gafe_t = 0.0;
-    for (int w = 0; w < PREP_BWD_THREADS / 32; ++w) { gtmax += s_tmax_part[w]; gafe_t += red[w]; }
+    double gtmax = 0.0, gafe_t = 0.0, gzs = 0.0;
+    for (int w = 0; w < PREP_BWD_THREADS / 32; ++w) { gtmax += s_tmax_part[w]; gafe_t += red[w]; gzs += s_zeta_part[w]; }
     // a fixed key has no column in the caller's rows (and no gradient)
     auto put = [&](int key, float v) {
       if (md.offs[key] < md.n_param) out[md.offs[key]] = v;
     };
     const double* rg = a.rgrad + (size_t)r * RGRAD;
-    if (md.zmode == 1) {
-      double gzs = 0.0;
-      for (int i = 0; i < NT; ++i) gzs += (double)gzeta[i];
-      put(SED_KEY_LOGZSOL, (float)gzs);
-    }
+    if (md.zmode == 1) put(SED_KEY_LOGZSOL, (float)gzs);
     put(SED_KEY_AFE, md.use_afe ? (float)gafe_t : 0.f);
     put(SED_KEY_LOGMASS, (float)rg[RG_LOGMASS]);
     put(SED_KEY_ZRED, (float)(rg[RG_Z] + gtmax * (double)rs.dtmax_dz));
