@@ -1168,9 +1168,10 @@ __global__ void __launch_bounds__(PREP_BWD_THREADS) k_prep_bwd(const __grid_cons
   __syncthreads();
   // T_max(z) path: dT_i/dT_max = T_i (i-2) / ((N_T-2) T_max) for i >= 3
   double part = 0.0;
+  const double inv_den = 1.0 / ((double)(NT - 2) * tmax);   // one FP64 division per row, not per edge
   for (int i = 3 + tid; i <= NT; i += blockDim.x) {
     const float gT = gThi[i - 1] + (i < NT ? gTlo[i] : 0.f);
-    part += (double)gT * (double)T[i] * (double)(i - 2) / ((double)(NT - 2) * tmax);
+    part += (double)gT * (double)T[i] * (double)(i - 2) * inv_den;
   }
   double ga = (double)gafe;
   // one [Fe/H] for every bin: its derivative sums the bins' (thread-strided,
